@@ -1,0 +1,494 @@
+"""CPU FP64 oracle for the Sparse Bessel Decomposition (SBD) discrete convolution.
+
+TEST INFRASTRUCTURE ONLY.  Nothing on the product path may import, call or
+execute this module: only ``tests/``, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` use it.  It shares
+no code with the CUDA path (no kernels, tables or helpers); the two meet only
+in the seeded input generators of ``workloads``.
+
+It is deliberately plain and slow: NumPy/SciPy in float64, library special
+functions, Gauss-Legendre quadrature, a Cholesky solve, and direct exponential
+sums in place of any fast transform.  Every function names the passage of
+M. Averseng, "Fast discrete convolution in R^2 using Sparse Bessel
+Decomposition" (arXiv:1711.07877) that it restates.
+
+Readings taken where the paper is silent or ambiguous (each also listed in the
+design notes):
+  R1  The self interaction l = k is excluded from the sum of Eq. (discreteConv)
+      (G is singular at 0); D_kk = -G_approx(0) cancels the far part's self term.
+  R2  delta_max is taken as 2 max_k |z_k - c| (c = bounding-box centre), an upper
+      bound of the diameter (Sec. 3.1 allows any bound).
+  R3  The Bessel argument of the Sec. 1 series reads J0(rho_p r / delta_max).
+  R4  Coefficients are expressed on the normalised basis e_p = C_p J0(rho_p r)
+      (Sec. 2.1), so omega_hat = alpha_p C_p / M_p (Sec. 6.2).
+  R5  The off-diagonal closed form of A^P (Sec. 3.2) is used with the opposite
+      sign (denominator rho_i^2 - rho_j^2); the printed sign disagrees with the
+      integral definition, which the quadrature Gram follows.
+  R6  The circle size M_p is the smallest even M >= rho_p with
+      2 sum_{j>=1} |J_{jM}(rho_p)| |alpha_p C_p| <= eps_q / P  (the exact aliasing
+      series of Sec. 5, worst case at |x| = delta_max); evenness makes the node
+      set symmetric under xi -> -xi so G_approx is real for a real kernel.
+  R7  eps is split into eps/3 for the fit, eps/3 for the circular quadrature and
+      eps/3 left to the fast transform of the CUDA path (the paper splits
+      eps/2 + eps/2 between fit and quadrature, Sec. 6.1).
+  R8  Pairs at distance exactly delta_min are near pairs (<=, Sec. 1).
+  R9  Helmholtz: G(x) = (i/4) H0^(1)(kappa |x|) = (i/4) J0 - (1/4) Y0; the J0 part is
+      one circle of radius kappa (Sec. 1 circle identity), the Y0 part is an SBD
+      of Y0(k' s) with k' the first root of Y0 >= kappa delta_max, scaled by
+      R = k'/kappa (Sec. 4.2).
+  R10 The L_inf stopping test of the P search (Sec. 1) is evaluated on the
+      fixed sample set ``fit_error_samples`` of [a, 1], dense near a.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass
+
+import numpy as np
+import scipy.linalg as sla
+import scipy.special as sp
+
+TWO_PI = 2.0 * math.pi
+
+
+# ---------------------------------------------------------------------------
+# Kernels and the direct sum (Introduction, Eq. discreteConv; Sec. 4.1, 4.2)
+# ---------------------------------------------------------------------------
+
+def kernel_G(r: np.ndarray, kind: str, kappa: float = 0.0) -> np.ndarray:
+    """G(r): Laplace -log(r)/(2 pi) (Introduction) or Helmholtz (i/4) H0^(1)(kappa r) (R9)."""
+    r = np.asarray(r, dtype=np.float64)
+    if kind == "laplace":
+        return -np.log(r) / TWO_PI
+    if kind == "helmholtz":
+        return 0.25j * sp.hankel1(0, kappa * r)
+    raise ValueError(kind)
+
+
+def direct_sum(z: np.ndarray, f: np.ndarray, kind: str, kappa: float = 0.0,
+               targets: np.ndarray | None = None, chunk: int = 512) -> np.ndarray:
+    """q_k = sum_{l != k} G(z_k - z_l) f_l, Eq. (discreteConv), reading R1.
+
+    ``targets`` (indices into z) restricts k to a subsample; all l are summed.
+    f may be (N,) or (nrhs, N); the result has the matching leading shape.
+    """
+    z = np.asarray(z, dtype=np.float64)
+    f = np.asarray(f)
+    single = f.ndim == 1
+    F = f[None, :] if single else f
+    idx = np.arange(len(z)) if targets is None else np.asarray(targets)
+    out_dtype = np.complex128 if (kind == "helmholtz" or np.iscomplexobj(F)) else np.float64
+    q = np.zeros((F.shape[0], len(idx)), dtype=out_dtype)
+    for s in range(0, len(idx), chunk):
+        ks = idx[s:s + chunk]
+        d = np.hypot(z[ks, 0][:, None] - z[None, :, 0], z[ks, 1][:, None] - z[None, :, 1])
+        self_mask = d == 0.0
+        d_safe = np.where(self_mask, 1.0, d)
+        g = kernel_G(d_safe, kind, kappa)
+        g = np.where(self_mask, 0.0, g)
+        q[:, s:s + len(ks)] = (g @ F.T).T
+    return q[0] if single else q
+
+
+# ---------------------------------------------------------------------------
+# Bessel roots and the normalised basis (Sec. 2.1)
+# ---------------------------------------------------------------------------
+
+def j0_roots(P: int) -> np.ndarray:
+    """rho_1 < ... < rho_P, the positive roots of J0 (Definition of Sec. 2.1)."""
+    return sp.jn_zeros(0, P).astype(np.float64)
+
+
+def y0_first_root_at_least(x: float) -> float:
+    """The first root of Y0 that is >= x (Sec. 4.2, choice of k')."""
+    s = max(1, int(x / math.pi) - 2)
+    while True:
+        roots = sp.yn_zeros(0, s + 8)
+        hit = roots[roots >= x]
+        if hit.size:
+            return float(hit[0])
+        s += 8
+
+
+def normalisation_C(rho: np.ndarray) -> np.ndarray:
+    """C_p = 1 / (sqrt(pi) rho_p |J1(rho_p)|) so that ||e_p||_{H^1_0} = 1 (Sec. 2.1)."""
+    return 1.0 / (math.sqrt(math.pi) * rho * np.abs(sp.j1(rho)))
+
+
+# ---------------------------------------------------------------------------
+# Gauss-Legendre quadrature on [a, 1] (composite, graded panels)
+# ---------------------------------------------------------------------------
+
+def gauss_legendre(a: float, b: float, h: float, order: int = 24):
+    """Composite Gauss-Legendre rule on [a, b] with panels of length <= h.
+
+    Panels grow geometrically (ratio 2) from a until they reach h, so that
+    integrands with a singularity at 0 (1/s, Y1) stay resolved next to a.
+    """
+    x, w = sp.roots_legendre(order)
+    edges = [a]
+    step = min(h, a) if a > 0 else h
+    while edges[-1] < b:
+        edges.append(min(b, edges[-1] + step))
+        step = min(h, 2.0 * step)
+    edges = np.asarray(edges)
+    half = 0.5 * np.diff(edges)
+    mid = 0.5 * (edges[1:] + edges[:-1])
+    nodes = (mid[:, None] + half[:, None] * x[None, :]).ravel()
+    weights = (half[:, None] * w[None, :]).ravel()
+    return nodes, weights
+
+
+def _panel_length(rho_max: float, extra_freq: float = 0.0) -> float:
+    # integrands oscillate with angular frequency <= 2 rho_max (+ extra_freq);
+    # a 24-point Gauss panel spanning about one period integrates that to rounding
+    return min(0.125, 6.0 / (2.0 * rho_max + extra_freq))
+
+
+# ---------------------------------------------------------------------------
+# The SBD fit: Gram matrix, right-hand side, solve (Sec. 3.1, 3.2)
+# ---------------------------------------------------------------------------
+
+def gram_quadrature(rho: np.ndarray, a: float, C: np.ndarray | None = None) -> np.ndarray:
+    """A_pq = int_{A(a)} grad e_p . grad e_q = 2 pi C_p C_q rho_p rho_q int_a^1 s J1(rho_p s) J1(rho_q s) ds.
+
+    Gram matrix of the quadratic form Q^P (Sec. 3.1) on the annulus A(a), by
+    composite Gauss-Legendre quadrature of its integral definition (Sec. 3.2).
+    """
+    C = normalisation_C(rho) if C is None else C
+    s, w = gauss_legendre(a, 1.0, _panel_length(float(rho.max())))
+    B = (C * rho)[:, None] * sp.j1(rho[:, None] * s[None, :])  # (P, nq): -(d/ds) e_p
+    return TWO_PI * (B * (w * s)[None, :]) @ B.T
+
+
+def gram_closed_form(rho: np.ndarray, a: float) -> np.ndarray:
+    """The explicit A^P of Sec. 3.2 (Green's formula), reading R5 for the off-diagonal sign.
+
+    F_ij(r) = rho_i r J0(rho_i r) J0'(rho_j r), F_i(r) as printed; valid for any rho.
+    """
+    C = normalisation_C(rho)
+    P = len(rho)
+
+    def F_ij(ri, rj, r):
+        return ri * r * sp.j0(ri * r) * (-sp.j1(rj * r))
+
+    def F_i(ri, r):
+        j0v = sp.j0(ri * r)
+        dj0 = -sp.j1(ri * r)
+        return ri * ri * r * r * (0.5 * j0v * j0v + 0.5 * dj0 * dj0) + ri * r * j0v * dj0
+
+    A = np.empty((P, P))
+    ri = rho[:, None]
+    rj = rho[None, :]
+    with np.errstate(divide="ignore", invalid="ignore"):
+        bracket = (F_ij(ri, rj, 1.0) - F_ij(rj, ri, 1.0) - F_ij(ri, rj, a) + F_ij(rj, ri, a))
+        off = TWO_PI * C[:, None] * C[None, :] * ri * rj / (ri * ri - rj * rj) * bracket
+    A[:] = off
+    diag = TWO_PI * C * C * (F_i(rho, 1.0) - F_i(rho, a))
+    A[np.arange(P), np.arange(P)] = diag
+    return A
+
+
+def rhs_quadrature(g_prime, rho: np.ndarray, a: float, C: np.ndarray | None = None,
+                   extra_freq: float = 0.0) -> np.ndarray:
+    """b_p = int_{A(a)} grad g . grad e_p = 2 pi int_a^1 s g'(s) (-C_p rho_p J1(rho_p s)) ds.
+
+    Right-hand side of the normal equations Eq. (LinearSystem) in the e_p basis.
+    """
+    C = normalisation_C(rho) if C is None else C
+    s, w = gauss_legendre(a, 1.0, _panel_length(float(rho.max()), extra_freq))
+    B = (C * rho)[:, None] * sp.j1(rho[:, None] * s[None, :])
+    return -TWO_PI * (B * (w * s * g_prime(s))[None, :]).sum(axis=1)
+
+
+def sbd_coefficients(g_prime, a: float, P: int, extra_freq: float = 0.0):
+    """SBD coefficients of order P: minimiser of Q^P (Sec. 3.1) by Cholesky (Sec. 3.2).
+
+    Returns (rho, C, alpha) with g(s) ~ sum_p alpha_p C_p J0(rho_p s) on (a, 1).
+    """
+    rho = j0_roots(P)
+    C = normalisation_C(rho)
+    A = gram_quadrature(rho, a, C)
+    b = rhs_quadrature(g_prime, rho, a, C, extra_freq)
+    L = np.linalg.cholesky(A)
+    y = sla.solve_triangular(L, b, lower=True)
+    alpha = sla.solve_triangular(L.T, y, lower=False)
+    return rho, C, alpha
+
+
+def fit_error_samples(a: float, P: int) -> np.ndarray:
+    """Sample set of [a, 1] for the L_inf stopping test (reading R10).
+
+    8P + 400 points uniform in [a, 1] plus 400 points geometrically dense near a
+    (the paper monitors the error near delta_min, Sec. 1).
+    """
+    uni = np.linspace(a, 1.0, 8 * P + 400)
+    near = a + (np.geomspace(1e-6, 1.0, 400) * min(1.0 - a, 20.0 * a))
+    return np.unique(np.concatenate([uni, near]))
+
+
+def series_value(s: np.ndarray, rho: np.ndarray, C: np.ndarray, alpha: np.ndarray) -> np.ndarray:
+    """sum_p alpha_p C_p J0(rho_p s)."""
+    s = np.atleast_1d(s)
+    out = np.zeros(s.shape, dtype=np.result_type(alpha.dtype, np.float64))
+    for i in range(0, len(rho), 256):
+        out += (alpha[i:i + 256] * C[i:i + 256]) @ sp.j0(rho[i:i + 256, None] * s[None, :])
+    return out
+
+
+def fit_linf_error(g, rho, C, alpha, a: float) -> float:
+    """max_{s in samples} |g(s) - sum_p alpha_p C_p J0(rho_p s)| (reading R10)."""
+    s = fit_error_samples(a, len(rho))
+    return float(np.max(np.abs(g(s) - series_value(s, rho, C, alpha))))
+
+
+def choose_P(g, g_prime, a: float, tol: float, P_start: int, extra_freq: float = 0.0,
+             P_max: int = 4000):
+    """Smallest P whose fit error is <= tol, by doubling then dichotomy (Sec. 1).
+
+    Returns (P, rho, C, alpha, err).
+    """
+    cache = {}
+
+    def err_of(P):
+        if P not in cache:
+            rho, C, alpha = sbd_coefficients(g_prime, a, P, extra_freq)
+            cache[P] = (fit_linf_error(g, rho, C, alpha, a), rho, C, alpha)
+        return cache[P][0]
+
+    hi = max(1, P_start)
+    while err_of(hi) > tol:
+        if hi >= P_max:
+            raise RuntimeError(f"SBD fit does not reach {tol:g} with P <= {P_max}")
+        hi = min(P_max, 2 * hi)
+    lo = 0  # invariant: err(hi) <= tol, and lo == 0 or err(lo) > tol
+    probe = hi // 2
+    while probe > 0 and err_of(probe) <= tol:
+        hi = probe
+        probe //= 2
+    lo = probe
+    while hi - lo > 1:
+        mid = (lo + hi) // 2
+        if err_of(mid) <= tol:
+            hi = mid
+        else:
+            lo = mid
+    e, rho, C, alpha = cache[hi]
+    return hi, rho, C, alpha, e
+
+
+# ---------------------------------------------------------------------------
+# Circular quadrature (Sec. 5; nodes Eq. defXimp)
+# ---------------------------------------------------------------------------
+
+def aliasing_bound(M: int, r: float, n_terms: int = 4) -> float:
+    """2 sum_{j=1..n_terms} |J_{jM}(r)|: the modulus bound of the aliasing series of Sec. 5."""
+    return 2.0 * float(sum(abs(sp.jv(j * M, r)) for j in range(1, n_terms + 1)))
+
+
+def circle_size(r: float, weight: float, tol: float) -> int:
+    """Smallest even M >= r with aliasing_bound(M, r) * |weight| <= tol (reading R6).
+
+    For M >= r every |J_{jM}| is increasing on [0, r] (its first maximum lies
+    beyond order jM), so the aliasing error of Sec. 5 over all |x| <= scale is
+    largest at the circle argument r itself.
+    """
+    M = max(2, 2 * int(math.ceil(0.5 * r)))
+    while aliasing_bound(M, r) * abs(weight) > tol:
+        M += 2
+    return M
+
+
+def circle_nodes(radius: float, M: int) -> np.ndarray:
+    """xi_m = radius (cos 2 pi m / M, sin 2 pi m / M), m = 0..M-1 (Eq. defXimp)."""
+    t = TWO_PI * np.arange(M) / M
+    return radius * np.stack([np.cos(t), np.sin(t)], axis=1)
+
+
+# ---------------------------------------------------------------------------
+# The plan: weights omega_hat and frequencies xi (Sec. 1, Sec. 6.1, 6.2)
+# ---------------------------------------------------------------------------
+
+@dataclass
+class OraclePlan:
+    kind: str
+    kappa: float
+    z: np.ndarray
+    delta_min: float
+    delta_max: float
+    eps: float
+    scale_R: float          # radius scale of the Bessel circles (delta_max, or R for Y0)
+    a: float                # delta_min / scale_R
+    P: int
+    rho: np.ndarray
+    C: np.ndarray
+    alpha: np.ndarray
+    fit_err: float
+    M: np.ndarray           # nodes per circle (Bessel circles first; Helmholtz J0 circle last)
+    circle_radius: np.ndarray
+    circle_weight: np.ndarray   # omega_hat per node of each circle (complex)
+    w0: complex             # weight of the xi = 0 node (G(delta_max), Laplace)
+    xi: np.ndarray          # (N_xi, 2)
+    omega: np.ndarray       # (N_xi,) complex
+    pairs: tuple | None = None
+    D: np.ndarray | None = None   # values per pair (k, l), aligned with pairs
+
+
+def make_plan(z: np.ndarray, kind: str, delta_min: float, eps: float, kappa: float = 0.0,
+              P: int | None = None, P_start: int | None = None) -> OraclePlan:
+    """Off-line part (Sec. 1): SBD fit, circular quadrature, weights and frequencies.
+
+    ``P`` fixes the number of Bessel terms; otherwise it is chosen by choose_P.
+    """
+    z = np.asarray(z, dtype=np.float64)
+    c = 0.5 * (z.min(axis=0) + z.max(axis=0))
+    delta_max = 2.0 * float(np.sqrt(np.max(np.sum((z - c) ** 2, axis=1))))   # R2
+    if not (0.0 < delta_min < delta_max):
+        raise ValueError("need 0 < delta_min < delta_max")
+    eps_fit = eps / 3.0        # R7
+    eps_q = eps / 3.0
+    if kind == "laplace":
+        # -log(r)/(2pi) = -(1/2pi) [log(delta_max) + log(s)], s = r / delta_max  (Sec. 4.1)
+        scale_R = delta_max
+        g = np.log
+        g_prime = lambda s: 1.0 / s  # noqa: E731
+        gscale = -1.0 / TWO_PI
+        extra = 0.0
+        w0 = complex(-math.log(delta_max) / TWO_PI)      # G(delta_max): the xi = 0 term (Sec. 1)
+    elif kind == "helmholtz":
+        kp = y0_first_root_at_least(kappa * delta_max)   # k' (Sec. 4.2)
+        scale_R = kp / kappa
+        g = lambda s: sp.y0(kp * s)  # noqa: E731
+        g_prime = lambda s: -kp * sp.y1(kp * s)  # noqa: E731
+        gscale = -0.25
+        extra = 2.0 * kp
+        w0 = 0.0j
+    else:
+        raise ValueError(kind)
+    a = delta_min / scale_R
+    tol_fit = eps_fit / abs(gscale)
+    if P is None:
+        if P_start is None:
+            P_start = max(4, int(math.ceil(1.5 / a)) + (int(extra / (2 * math.pi)) if extra else 0))
+        P, rho, C, alpha, err = choose_P(g, g_prime, a, tol_fit, P_start, extra)
+    else:
+        rho, C, alpha = sbd_coefficients(g_prime, a, P, extra)
+        err = fit_linf_error(g, rho, C, alpha, a)
+    coef = gscale * alpha * C      # kernel units: G ~ const + sum_p coef_p J0(rho_p r / scale_R)
+    n_circles = P + (1 if kind == "helmholtz" else 0)
+    M = np.array([circle_size(float(rho[p]), float(coef[p]), eps_q / n_circles) for p in range(P)],
+                 dtype=np.int64)
+    radius = rho / scale_R
+    weight = (coef / M).astype(np.complex128)                # omega_hat = alpha_p C_p / M_p (Sec. 6.2)
+    if kind == "helmholtz":
+        # (i/4) J0(kappa r): one circle of radius kappa, exact by the identity of Sec. 1
+        kd = kappa * delta_max
+        Mj = circle_size(kd, 0.25, eps_q / n_circles)
+        M = np.append(M, Mj)
+        radius = np.append(radius, kappa)
+        weight = np.append(weight, 0.25j / Mj)
+    xi = [np.zeros((1, 2))] if w0 != 0 else []
+    om = [np.array([w0])] if w0 != 0 else []
+    for Mp, rp, wp in zip(M, radius, weight):
+        xi.append(circle_nodes(float(rp), int(Mp)))
+        om.append(np.full(int(Mp), wp, dtype=np.complex128))
+    xi = np.concatenate(xi, axis=0)
+    om = np.concatenate(om)
+    return OraclePlan(kind, kappa, z, delta_min, delta_max, eps, scale_R, a, P, rho, C, alpha, err,
+                      M, radius, weight, w0, xi, om)
+
+
+# ---------------------------------------------------------------------------
+# Type-3 transforms by definition (Introduction: NUFFT_{+-}[z, xi])
+# ---------------------------------------------------------------------------
+
+def nufft_direct(src: np.ndarray, dst: np.ndarray, c: np.ndarray, sign: int, chunk: int = 2048) -> np.ndarray:
+    """out_j = sum_k exp(sign * i src_k . dst_j) c_k, by direct summation.
+
+    NUFFT_{+-}[z, xi] of the Introduction: with src = z, dst = xi it maps C^{N_z}
+    to C^{N_xi}; Eq. (far convolution) also applies it with the roles of z and
+    xi exchanged (src = xi, dst = z), which is the same exponential sum.
+    """
+    c = np.asarray(c, dtype=np.complex128)
+    out = np.zeros(len(dst), dtype=np.complex128)
+    for s in range(0, len(dst), chunk):
+        ph = dst[s:s + chunk] @ src.T
+        out[s:s + chunk] = np.exp(sign * 1j * ph) @ c
+    return out
+
+
+# ---------------------------------------------------------------------------
+# Near pairs and the close-correction matrix D (Sec. 1 Eq. defD; Sec. 6.1)
+# ---------------------------------------------------------------------------
+
+def near_pairs(z: np.ndarray, delta_min: float):
+    """All ordered pairs (k, l), k != l, with |z_k - z_l| <= delta_min (R8), by brute force."""
+    rows, cols = [], []
+    for s in range(0, len(z), 1024):
+        d2 = (z[s:s + 1024, 0][:, None] - z[None, :, 0]) ** 2 + (z[s:s + 1024, 1][:, None] - z[None, :, 1]) ** 2
+        k, l = np.nonzero(d2 <= delta_min * delta_min)
+        keep = (k + s) != l
+        rows.append(k[keep] + s)
+        cols.append(l[keep])
+    return np.concatenate(rows), np.concatenate(cols)
+
+
+def g_approx_direct(y: np.ndarray, xi: np.ndarray, omega: np.ndarray, chunk: int = 1024) -> np.ndarray:
+    """G_approx(y) = sum_nu omega_nu exp(i y . xi_nu), Eq. (Gapprox), by direct summation."""
+    out = np.zeros(len(y), dtype=np.complex128)
+    for s in range(0, len(y), chunk):
+        out[s:s + chunk] = np.exp(1j * (y[s:s + chunk] @ xi.T)) @ omega
+    return out
+
+
+def close_matrix(plan: OraclePlan):
+    """D of Eq. (defD): G(z_k - z_l) - G_approx(z_k - z_l) on near pairs; D_kk = -G_approx(0) (R1).
+
+    Returns (rows, cols, values) including the diagonal.
+    """
+    z = plan.z
+    k, l = near_pairs(z, plan.delta_min)
+    y = z[k] - z[l]
+    r = np.hypot(y[:, 0], y[:, 1])
+    gap = g_approx_direct(y, plan.xi, plan.omega)
+    coincide = r == 0.0
+    gval = np.where(coincide, 0.0, kernel_G(np.where(coincide, 1.0, r), plan.kind, plan.kappa))
+    vals = gval - gap
+    n = len(z)
+    g0 = plan.omega.sum()
+    rows = np.concatenate([k, np.arange(n)])
+    cols = np.concatenate([l, np.arange(n)])
+    vals = np.concatenate([vals, np.full(n, -g0)])
+    return rows, cols, vals
+
+
+# ---------------------------------------------------------------------------
+# On-line part (Sec. 1; Sec. 6.2)
+# ---------------------------------------------------------------------------
+
+def far_part(plan: OraclePlan, f: np.ndarray) -> np.ndarray:
+    """q_far = NUFFT_+[z, xi](omega_hat . NUFFT_-[z, xi](f)), Eq. (far convolution), steps (i)-(iii)."""
+    fhat = nufft_direct(plan.z, plan.xi, f, -1)       # (i)  space -> Fourier
+    ghat = plan.omega * fhat                         # (ii) Fourier multiply
+    return nufft_direct(plan.xi, plan.z, ghat, +1)   # (iii) Fourier -> space
+
+
+def close_part(plan: OraclePlan, f: np.ndarray) -> np.ndarray:
+    """q_close = D f (Sec. 1, close correction)."""
+    if plan.D is None:
+        plan.D = close_matrix(plan)
+    rows, cols, vals = plan.D
+    out = np.zeros(len(plan.z), dtype=np.complex128)
+    np.add.at(out, rows, vals * f[cols])
+    return out
+
+
+def sbd_matvec(plan: OraclePlan, f: np.ndarray) -> np.ndarray:
+    """q = q_far + q_close (Sec. 1, on-line output).  Real for a real kernel and real f."""
+    f = np.asarray(f)
+    if f.ndim == 2:
+        return np.stack([sbd_matvec(plan, fi) for fi in f])
+    q = far_part(plan, f) + close_part(plan, f)
+    if plan.kind == "laplace" and not np.iscomplexobj(f):
+        return q.real
+    return q

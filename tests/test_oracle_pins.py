@@ -1,0 +1,358 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+Each test checks one oracle function against something other than itself:
+numbers printed in the paper (tests/golden/paper_values.json, each cited),
+closed forms, special cases that reduce to a library routine, brute force on
+tiny inputs, and the paper's error bound.  A planted mistake in the oracle
+(wrong sign, dropped term, transposed operand) fails at least one of them;
+the last tests plant a few such mistakes and check that they are caught.
+"""
+import json
+import math
+import os
+
+import mpmath
+import numpy as np
+import pytest
+import scipy.special as sp
+
+import workloads as W
+from oracle import sbd_oracle as O
+
+GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_values.json")))
+
+
+# --- Sec. 2.1: roots and normalisation ------------------------------------------------------
+
+def test_rho_bracket_and_roots():
+    g = GOLD["rho_bracket"]
+    rho = O.j0_roots(1000)
+    p = np.arange(1, 1001)
+    assert np.all(rho >= math.pi * (p - g["lower_shift"]) - 1e-12)
+    assert np.all(rho <= math.pi * (p - g["upper_shift"]) + 1e-12)
+    # they are roots, and consecutive (no root skipped: spacing ~ pi)
+    assert np.max(np.abs(sp.j0(rho))) < 1e-13
+    assert np.all(np.abs(np.diff(rho) - math.pi) < 0.1)
+
+
+def test_normalisation_matches_integral_definition():
+    rho = O.j0_roots(60)
+    C = O.normalisation_C(rho)
+    s, w = O.gauss_legendre(0.0, 1.0, 0.02)
+    integral = 2 * math.pi * ((s * w)[None, :] * (rho[:, None] ** 2) * sp.j1(rho[:, None] * s[None, :]) ** 2).sum(1)
+    assert np.allclose(C, 1.0 / np.sqrt(integral), rtol=1e-13, atol=0)
+
+
+def test_Cp_conjecture_bounds():
+    g = GOLD["Cp_conjecture"]
+    p = np.arange(1, g["p_max"] + 1)
+    C = O.normalisation_C(O.j0_roots(g["p_max"]))
+    assert np.all(C >= 1 / np.sqrt(2 * math.pi * p))
+    assert np.all(C <= 1 / np.sqrt(2 * math.pi * (p - 0.25)))
+
+
+# --- Sec. 3.2: Gram matrix ---------------------------------------------------------------------
+
+def test_gram_orthonormal_without_hole():
+    # Theorem 1 (Hilbert basis of H^1_0,rad): on the whole ball the e_p are orthonormal
+    rho = O.j0_roots(50)
+    A = O.gram_quadrature(rho, 0.0)
+    assert np.max(np.abs(A - np.eye(50))) < 1e-13
+
+
+@pytest.mark.parametrize("a", [0.05, 0.3])
+def test_gram_quadrature_vs_closed_form(a):
+    rho = O.j0_roots(40)
+    Aq = O.gram_quadrature(rho, a)
+    Ac = O.gram_closed_form(rho, a)
+    assert np.max(np.abs(Aq - Ac)) < 1e-13
+    # reading R5: with the sign as printed the off-diagonal entries disagree
+    off = ~np.eye(40, dtype=bool)
+    assert np.max(np.abs(-Ac[off] - Aq[off])) > 1e-2
+
+
+def _F(gamma):
+    # F(gamma) = 1 - int_0^{pi gamma} (t/2)(J1^2 - J0 J2) dt (Theorem 3)
+    s, w = O.gauss_legendre(0.0, math.pi * gamma, 0.05)
+    return 1.0 - np.sum(w * s / 2 * (sp.j1(s) ** 2 - sp.j0(s) * sp.jv(2, s)))
+
+
+def test_gamma_star_and_small_gamma_eigen_bounds():
+    g = GOLD["gamma_star"]
+    lo, hi = 1.0, 2.0
+    for _ in range(60):
+        mid = 0.5 * (lo + hi)
+        lo, hi = (mid, hi) if _F(mid) > 0 else (lo, mid)
+    assert round(lo, g["digits"]) == pytest.approx(g["value"], abs=1.5e-3)
+    assert 1.0 / _F(1.0) < 2.2   # the paper states < 2; 1/F(1) = 2.17
+    # proof of Theorem 3: A <= I, so lambda_min >= 1 - tr(I - A), and each diagonal entry is
+    # 1 - 2 pi C_p^2 int_0^{rho_p a} u J1(u)^2 du = 1 - 2 pi C_p^2 (t^2/2)(J1^2 - J0 J2)(t), t = rho_p a
+    for P, gamma in [(50, 0.5), (50, 1.0), (100, 1.2)]:
+        rho = O.j0_roots(P)
+        C = O.normalisation_C(rho)
+        A = O.gram_quadrature(rho, gamma / P, C)
+        t = rho * gamma / P
+        diag = 1 - 2 * math.pi * C ** 2 * t ** 2 / 2 * (sp.j1(t) ** 2 - sp.j0(t) * sp.jv(2, t))
+        assert np.max(np.abs(np.diag(A) - diag)) < 1e-13
+        ev = np.linalg.eigvalsh(A)
+        assert ev[-1] <= 1 + 1e-12
+        assert ev[0] >= 1 - np.trace(np.eye(P) - A) - 1e-12
+        # the theorem's F(gamma) is the large-P limit of 1 - tr(I - A); the printed bound
+        # F - pi^4 gamma^4 / (144 P) is slightly violated at small P (the proof bounds an
+        # increasing sum by a smaller integral), so only closeness is checked here
+        assert abs(ev[0] - _F(gamma)) < 0.05
+
+
+def test_lambda_min_exponential_bound():
+    g = GOLD["lambda_min_bound"]
+    for P in (g["P_min"] + 10, 60):
+        for gamma in (1.4, 2.0, 3.0, 4.0, 5.0):
+            ev = np.linalg.eigvalsh(O.gram_quadrature(O.j0_roots(P), gamma / P))
+            assert ev[0] >= g["c"] * math.exp(-g["rate"] * gamma)
+
+
+# --- Sec. 3.2 Eq. (LinearSystem), Sec. 4.1: right-hand side and fit -------------------------------
+
+def test_rhs_laplace_closed_form():
+    # for g = log s: b_p = -2 pi C_p rho_p int_a^1 J1(rho_p s) ds = -2 pi C_p J0(rho_p a) as J0(rho_p) = 0
+    for a in (0.001, 0.05, 0.4):
+        rho = O.j0_roots(80)
+        C = O.normalisation_C(rho)
+        b = O.rhs_quadrature(lambda s: 1 / s, rho, a, C)
+        assert np.max(np.abs(b + 2 * math.pi * C * sp.j0(rho * a))) < 1e-12
+
+
+def _laplace_err(a, P):
+    rho, C, al = O.sbd_coefficients(lambda s: 1 / s, a, P)
+    return O.fit_linf_error(np.log, rho, C, al, a), rho, C, al
+
+
+def test_laplace_fit_rate_and_thresholds():
+    a = GOLD["fig4_a"]["a"]
+    e18, rho, C, _ = _laplace_err(a, int(round(GOLD["laplace_1e-3"]["gamma"] / a)))
+    assert e18 <= GOLD["laplace_1e-3"]["eps"]                        # gamma ~ 1.8 suffices for 1e-3
+    ev = np.linalg.eigvalsh(O.gram_quadrature(rho, a, C))
+    cond = ev[-1] / ev[0]
+    assert GOLD["laplace_1e-3"]["condition"] / 10 < cond < GOLD["laplace_1e-3"]["condition"] * 10
+    errs = {g: _laplace_err(a, int(round(g / a)))[0] for g in (2.0, 3.0, 4.0, 5.0)}
+    rate = math.log(errs[2.0] / errs[5.0]) / 3.0                     # exp(-l2 gamma)
+    assert abs(rate - GOLD["laplace_rate"]["l2"]) < 0.5
+    assert all(errs[g] > errs[g + 1] for g in (2.0, 3.0, 4.0))
+
+
+def test_laplace_fit_floor():
+    a = GOLD["fig4_a"]["a"]
+    g = GOLD["laplace_floor"]
+    e = _laplace_err(a, int(round(g["gamma"] / a)))[0]
+    assert g["e_min"] / 10 < e < g["e_min"] * 10
+
+
+def test_fit_is_invariant_in_gamma():
+    # Remark 2: the situation depends on gamma = P a only
+    e1 = _laplace_err(0.05, 60)[0]
+    e2 = _laplace_err(0.025, 120)[0]
+    assert 0.3 < e1 / e2 < 3.0
+
+
+def test_y0_root_and_fit():
+    g = GOLD["y0_example"]
+    assert O.y0_first_root_at_least(7.0) == pytest.approx(g["k"], abs=1e-3)
+    assert O.y0_first_root_at_least(0.5) == pytest.approx(float(sp.yn_zeros(0, 1)[0]), abs=1e-12)
+    kp = O.y0_first_root_at_least(50.0)
+    assert abs(sp.y0(kp)) < 1e-13 and kp >= 50.0
+    # Sec. 4.2: exponential convergence once P exceeds the frequency, at the Laplace-like rate
+    errs = []
+    for gamma in (2, 3, 4):
+        P = int(kp / math.pi + gamma / 0.05)
+        rho, C, al = O.sbd_coefficients(lambda s: -kp * sp.y1(kp * s), 0.05, P, 2 * kp)
+        errs.append(O.fit_linf_error(lambda s: sp.y0(kp * s), rho, C, al, 0.05))
+    assert errs[0] > 10 * errs[1] > 100 * errs[2]
+    assert errs[2] < 1e-7
+
+
+def test_choose_P_is_minimal():
+    P, rho, C, al, e = O.choose_P(np.log, lambda s: 1 / s, 0.05, 1e-5, 10)
+    assert e <= 1e-5
+    assert _laplace_err(0.05, P - 1)[0] > 1e-5
+
+
+# --- Sec. 5: circular quadrature -----------------------------------------------------------------
+
+@pytest.mark.parametrize("M", [6, 11, 24])
+def test_circle_quadrature_aliasing_series(M):
+    # (1/M) sum_m exp(i x.xi_m) = J0(r) + sum_{k != 0} i^{kM} J_{kM}(r) exp(-i k M psi)
+    # (the Lemma of Sec. 5 applied through Jacobi-Anger; x = r (cos psi, sin psi))
+    rng = np.random.default_rng(0)
+    xi = O.circle_nodes(1.0, M)
+    for _ in range(20):
+        r, psi = 15 * rng.random(), 2 * math.pi * rng.random()
+        x = np.array([r * math.cos(psi), r * math.sin(psi)])
+        lhs = np.mean(np.exp(1j * xi @ x))
+        rhs = sp.j0(r) + sum((1j) ** (k * M) * sp.jv(k * M, r) * np.exp(-1j * k * M * psi)
+                             for k in list(range(-8, 0)) + list(range(1, 9)))
+        assert abs(lhs - rhs) < 1e-13
+
+
+def test_circle_integral_identity():
+    # J0(rho |x|) = (1/2 pi) int_{|xi|=1} exp(i rho x.xi)  (Sec. 1): a fine circle reproduces J0
+    xi = O.circle_nodes(1.0, 400)
+    for r in (0.3, 5.0, 40.0):
+        assert abs(np.mean(np.exp(1j * r * xi[:, 0])) - sp.j0(r)) < 1e-14
+
+
+def test_circle_size_meets_tolerance():
+    rng = np.random.default_rng(1)
+    for rho, wgt, tol in [(30.0, 0.1, 1e-9), (200.0, 1e-3, 1e-12), (2.4, 0.5, 1e-7)]:
+        M = O.circle_size(rho, wgt, tol)
+        assert M % 2 == 0 and M >= rho
+        xi = O.circle_nodes(1.0, M)
+        worst = 0.0
+        for r in np.linspace(0, rho, 60):
+            for psi in 2 * math.pi * rng.random(4):
+                x = r * np.array([math.cos(psi), math.sin(psi)])
+                worst = max(worst, abs(np.mean(np.exp(1j * xi @ x)) - sp.j0(r)))
+        assert worst * wgt <= tol * 1.0001
+        # and M - 2 would not satisfy the criterion (smallest even M)
+        if M - 2 >= rho:
+            assert O.aliasing_bound(M - 2, rho) * wgt > tol
+
+
+# --- Introduction: NUFFT and the direct sum ------------------------------------------------------
+
+def test_nufft_direct_reduces_to_fft2():
+    n = 12
+    rng = np.random.default_rng(2)
+    c = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+    j = np.stack(np.meshgrid(np.arange(n), np.arange(n), indexing="ij"), -1).reshape(-1, 2).astype(float)
+    xi = 2 * math.pi * j / n
+    out = O.nufft_direct(j, xi, c.ravel(), -1)
+    assert np.max(np.abs(out - np.fft.fft2(c).ravel())) < 1e-11
+    back = O.nufft_direct(xi, j, out, +1) / n ** 2
+    assert np.max(np.abs(back - c.ravel())) < 1e-12
+
+
+def test_direct_sum_bruteforce_tiny():
+    rng = np.random.default_rng(3)
+    z = rng.random((7, 2))
+    f = rng.standard_normal(7)
+    fc = f + 1j * rng.standard_normal(7)
+    qL = O.direct_sum(z, f, "laplace")
+    qH = O.direct_sum(z, fc, "helmholtz", kappa=9.0)
+    for k in range(7):
+        sL, sH = 0.0, 0.0
+        for l in range(7):
+            if l == k:
+                continue
+            r = math.hypot(z[k, 0] - z[l, 0], z[k, 1] - z[l, 1])
+            sL += -math.log(r) / (2 * math.pi) * f[l]
+            sH += complex(0.25j * mpmath.hankel1(0, 9.0 * r)) * fc[l]
+        assert abs(qL[k] - sL) < 1e-13
+        assert abs(qH[k] - sH) < 1e-12
+    # subsampled targets and multiple right-hand sides
+    F = np.stack([f, 2 * f])
+    assert np.allclose(O.direct_sum(z, F, "laplace", targets=[1, 4]), np.stack([qL[[1, 4]], 2 * qL[[1, 4]]]))
+
+
+def test_near_pairs_bruteforce():
+    z = W.disk_points(200, 5)
+    k, l = O.near_pairs(z, 0.15)
+    got = set(zip(k.tolist(), l.tolist()))
+    want = {(i, j) for i in range(200) for j in range(200)
+            if i != j and math.hypot(*(z[i] - z[j])) <= 0.15}
+    assert got == want
+
+
+# --- Sec. 1 / Sec. 6: the whole SBD against the direct sum --------------------------------------
+
+@pytest.fixture(scope="module")
+def laplace_case():
+    z = W.disk_points(500, 3)
+    f = W.rhs(500, 4)
+    return z, f, O.direct_sum(z, f, "laplace")
+
+
+@pytest.mark.parametrize("eps", [1e-3, 1e-6, 1e-9])
+def test_sbd_laplace_within_eps(laplace_case, eps):
+    z, f, qd = laplace_case
+    pl = O.make_plan(z, "laplace", math.sqrt(20 / 500), eps)
+    assert pl.fit_err * (1 / (2 * math.pi)) <= eps / 3
+    q = O.sbd_matvec(pl, f)
+    assert np.max(np.abs(q - qd)) <= eps * np.abs(f).sum()          # Sec. 1 output bound
+
+
+def test_sbd_helmholtz_within_eps():
+    z = W.disk_points(300, 7)
+    f = W.rhs(300, 8, complex_valued=True)
+    kappa, eps = 25.0, 1e-6
+    pl = O.make_plan(z, "helmholtz", math.sqrt(20 / 300), eps, kappa=kappa)
+    q = O.sbd_matvec(pl, f)
+    qd = O.direct_sum(z, f, "helmholtz", kappa)
+    assert np.max(np.abs(q - qd)) <= eps * np.abs(f).sum()
+    assert pl.scale_R >= pl.delta_max and abs(sp.y0(kappa * pl.scale_R)) < 1e-12
+
+
+def test_sbd_invariants(laplace_case):
+    z, f, _ = laplace_case
+    dmin = math.sqrt(20 / 500)
+    pl = O.make_plan(z, "laplace", dmin, 1e-6)
+    g = W.rhs(500, 9)
+    qf, qg = O.sbd_matvec(pl, f), O.sbd_matvec(pl, g)
+    # symmetry <g, A f> = <A g, f> (real symmetric operator for Laplace)
+    assert abs(g @ qf - qg @ f) < 1e-10 * np.abs(qf).sum()
+    # linearity
+    assert np.allclose(O.sbd_matvec(pl, 2 * f - g), 2 * qf - qg, atol=1e-10)
+    # translation invariance: same delta_max, same frequencies, same result
+    pl2 = O.make_plan(z + np.array([3.0, -7.0]), "laplace", dmin, 1e-6)
+    assert pl2.P == pl.P and np.array_equal(pl2.M, pl.M)
+    assert np.max(np.abs(O.sbd_matvec(pl2, f) - qf)) < 1e-9
+    # the close matrix is symmetric with constant diagonal -G_approx(0)
+    rows, cols, vals = O.close_matrix(pl)
+    Dm = np.zeros((500, 500), complex)
+    Dm[rows, cols] = vals
+    assert np.max(np.abs(Dm - Dm.T)) < 1e-12
+    assert np.allclose(np.diag(Dm), -pl.omega.sum())
+
+
+def test_sbd_config1_shape():
+    wl = W.laplace_disk(2000, 1, 1e-6)
+    pl = O.make_plan(wl.z, "laplace", wl.delta_min, wl.eps)
+    assert 50 <= pl.P <= 90
+    assert 0.95 < (pl.M / pl.rho)[-10:].min() and (pl.M / pl.rho)[-10:].max() < 1.2
+    assert 5000 < len(pl.xi) < 15000
+
+
+# --- planted mistakes: each must break a pin ---------------------------------------------------
+
+def test_planted_sign_error_in_rhs_is_caught(laplace_case, monkeypatch):
+    z, f, qd = laplace_case
+    real = O.rhs_quadrature
+    monkeypatch.setattr(O, "rhs_quadrature", lambda *a, **k: -real(*a, **k))
+    pl = O.make_plan(z, "laplace", math.sqrt(20 / 500), 1e-6, P=60)
+    assert np.max(np.abs(O.sbd_matvec(pl, f) - qd)) > 1e-6 * np.abs(f).sum()
+
+
+def test_planted_dropped_constant_term_is_caught(laplace_case):
+    z, f, qd = laplace_case
+    pl = O.make_plan(z, "laplace", math.sqrt(20 / 500), 1e-6)
+    keep = np.any(pl.xi != 0, axis=1)
+    pl.xi, pl.omega = pl.xi[keep], pl.omega[keep]
+    assert np.max(np.abs(O.sbd_matvec(pl, f) - qd)) > 1e-6 * np.abs(f).sum()
+
+
+def test_planted_frequency_scale_error_is_caught(laplace_case):
+    # e.g. circles scaled by the diameter instead of the bound delta_max (reading R2)
+    z, f, qd = laplace_case
+    pl = O.make_plan(z, "laplace", math.sqrt(20 / 500), 1e-6)
+    pl.xi = pl.xi * 1.01
+    assert np.max(np.abs(O.sbd_matvec(pl, f) - qd)) > 1e-6 * np.abs(f).sum()
+
+
+def test_planted_conjugated_transform_is_caught(laplace_case):
+    # NUFFT_- and NUFFT_+ with the same sign: the far part is no longer a convolution
+    z, f, qd = laplace_case
+    pl = O.make_plan(z, "laplace", math.sqrt(20 / 500), 1e-6)
+    fc = f + 1j * W.rhs(500, 11)
+    ok = O.sbd_matvec(pl, fc)
+    fhat = O.nufft_direct(pl.z, pl.xi, fc, +1)
+    bad = O.nufft_direct(pl.xi, pl.z, pl.omega * fhat, +1) + O.close_part(pl, fc)
+    assert np.max(np.abs(bad - ok)) > 1e-3 * np.abs(fc).sum() / 500
