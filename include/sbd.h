@@ -1,0 +1,202 @@
+/*
+ * sbd.h - C ABI of the GB300 Sparse Bessel Decomposition library (libsbd.so).
+ *
+ * The library computes the approximate 2-D discrete convolution
+ *
+ *     q_k = sum_{l != k} G(z_k - z_l) f_l,      k = 1..N            (Introduction, Eq. discreteConv)
+ *
+ * for the Laplace kernel G(x) = -log|x| / (2 pi) and the Helmholtz kernel
+ * G(x) = (i/4) H0^(1)(kappa |x|), by the Sparse Bessel Decomposition of
+ * M. Averseng, arXiv:1711.07877:
+ *
+ *   off-line (sbd_plan, Sec. 1 "Off-line part", Sec. 3-5, Sec. 6.1): fit G on
+ *     [delta_min, delta_max] by a Fourier-Bessel series sum_p alpha_p e_p, turn each
+ *     J0 term into M_p plane waves on a circle of frequencies (circular quadrature),
+ *     and assemble the sparse close-correction matrix D of Eq. (defD);
+ *   on-line (sbd_matvec, Sec. 1 "On-line part", Sec. 6.2): q = q_far + D f with
+ *     q_far = NUFFT_+[z, xi](omega_hat . NUFFT_-[z, xi](f))  (Eq. far convolution).
+ *
+ * Every on-line step runs in this library's CUDA kernels for sm_103a; nothing
+ * falls back to the CPU.  The output satisfies, up to rounding of the chosen
+ * form, |q_k - exact_k| <= eps * sum_l |f_l| (Sec. 1, output bound).
+ *
+ * Conventions for every entry point:
+ *   - Return SBD_OK (0) on success and a negative SBD_E* code on error; nothing
+ *     is written to outputs on argument errors.  sbd_error_string() names a code
+ *     and sbd_last_error_message() gives the calling thread's last detail text.
+ *   - "device" pointers are CUDA device (or managed) memory of the current
+ *     device; "host" pointers are ordinary host memory.  The caller owns every
+ *     buffer it passes; the library owns the plan and its device memory.
+ *   - cuda_stream is a cudaStream_t (NULL = the legacy default stream).  Device
+ *     work is enqueued on it asynchronously unless stated otherwise.
+ *   - Vectors with several right-hand sides are stored right-hand side by
+ *     right-hand side: element l of rhs r is at index r * N + l.
+ *   - Laplace vectors are float64; Helmholtz vectors are complex128 stored as
+ *     interleaved (re, im) float64 pairs.
+ */
+#ifndef SBD_H
+#define SBD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* error codes */
+#define SBD_OK         0
+#define SBD_EINVAL    -1   /* invalid argument (null pointer, size, tolerance, kernel) */
+#define SBD_ENOMEM    -2   /* device or host allocation failed */
+#define SBD_ECUDA     -3   /* a CUDA runtime call failed (no device, launch error, ...) */
+#define SBD_EFIT      -4   /* the SBD fit cannot reach the requested tolerance (Sec. 4.1 floor ~1e-10) */
+#define SBD_ETIMEOUT  -5   /* a bounded device wait expired */
+#define SBD_ENOTSUP   -6   /* combination not supported by this build */
+
+typedef struct sbd_plan_s* sbd_plan_t;   /* opaque; owned by the library */
+
+/* Kernel G (Introduction; Sec. 4.1 Laplace; Sec. 4.2 Helmholtz). */
+typedef enum { SBD_LAPLACE = 0, SBD_HELMHOLTZ = 1 } sbd_kernel_kind;
+typedef struct {
+    int32_t kind;      /* sbd_kernel_kind */
+    double  kappa;     /* wavenumber (> 0) for SBD_HELMHOLTZ; ignored for SBD_LAPLACE */
+} sbd_kernel;
+
+/* Arithmetic of the far part.  FP64: spread, FFT, node step and interpolation in
+ * float64.  FP32: those steps in float32 (coordinates split as an integer cell
+ * plus a float32 fraction computed in float64); the close correction D f and the
+ * final accumulation stay in float64 in both forms. */
+typedef enum { SBD_FORM_FP64 = 0, SBD_FORM_FP32 = 1 } sbd_form;
+
+typedef struct {
+    int32_t form;        /* sbd_form (default SBD_FORM_FP64) */
+    int32_t fixed_P;     /* > 0: use exactly this many Bessel terms; 0: the P search of Sec. 1 */
+    double  nufft_tol;   /* > 0: tolerance of each type-3 transform; 0: automatic from eps */
+    int32_t max_nrhs;    /* largest nrhs a matvec will use (0 = 1); sizes the workspace */
+    int32_t flags;       /* reserved, must be 0 */
+} sbd_options;
+
+/* Plan summary (sbd_plan_info). */
+typedef struct {
+    int64_t n_points;        /* N */
+    int64_t P;               /* Bessel terms of the SBD (Sec. 3.1) */
+    int64_t n_circles;       /* P, plus one J0 circle for Helmholtz */
+    int64_t n_xi;            /* N_xi = sum_p M_p (Sec. 6.1), the xi = 0 node excluded */
+    int64_t nnz;             /* non-zeros of D, the diagonal included */
+    int64_t n_coincident;    /* pairs of distinct points at distance 0 (treated as self pairs) */
+    int32_t grid_x;          /* side of the spreading grid (cells) */
+    int32_t grid_k;          /* side of the stored frequency grid (cells) */
+    int32_t fft_n;           /* FFT length per dimension */
+    int32_t stencil_x;       /* spreading stencil width (cells per dimension) */
+    int32_t stencil_k;       /* node-step stencil width (cells per dimension) */
+    int32_t form;            /* sbd_form */
+    double  delta_max;       /* 2 max_k |z_k - c|, c = bounding-box centre */
+    double  delta_min;
+    double  scale_R;         /* radius scale of the Bessel circles (delta_max, or k'/kappa for Y0) */
+    double  a;               /* delta_min / scale_R */
+    double  fit_err;         /* L_inf error of the fit on its sample set of [a, 1] (kernel units) */
+    double  nufft_tol;       /* tolerance used for each type-3 transform */
+    double  w0_re, w0_im;    /* weight of the xi = 0 term, G(delta_max) for Laplace (Sec. 1) */
+    int64_t device_bytes;    /* device memory held by the plan */
+    double  plan_seconds;    /* wall time of sbd_plan */
+} sbd_plan_stats;
+
+/* ---------------------------------------------------------------------------------
+ * sbd_plan - off-line part (Sec. 1 "Off-line part"; Sec. 3.2 fit, Sec. 5 circular
+ * quadrature, Sec. 6.1 close-correction matrix, Eq. defD).
+ *   points     device, N x 2 float64, interleaved (x, y); copied, so the caller may
+ *              free it when the call returns.
+ *   n          N >= 1.
+ *   kernel     Laplace or Helmholtz (kappa > 0).
+ *   delta_min  near-field radius, 0 < delta_min < delta_max; pairs with
+ *              |z_k - z_l| <= delta_min go to D.
+ *   eps        target accuracy in kernel units, 1e-10 <= eps <= 0.1.
+ *   opt        NULL for defaults.
+ *   out        receives the plan.
+ * Synchronises cuda_stream before returning (the plan is ready to use on any
+ * stream).  Errors: SBD_EINVAL, SBD_ENOMEM, SBD_ECUDA, SBD_EFIT.
+ * ------------------------------------------------------------------------------- */
+int sbd_plan(const double* points, int64_t n, sbd_kernel kernel, double delta_min,
+             double eps, const sbd_options* opt, void* cuda_stream, sbd_plan_t* out);
+
+/* ---------------------------------------------------------------------------------
+ * sbd_matvec - on-line part (Sec. 1 "On-line part"; Sec. 6.2; Eq. far convolution):
+ * q = NUFFT_+(omega_hat . NUFFT_-(f)) + D f for nrhs right-hand sides.
+ *   f, q   device, nrhs x N (float64 for Laplace, complex128 for Helmholtz);
+ *          q is overwritten, f is read only; f and q must not overlap.
+ *   nrhs   1 <= nrhs <= max_nrhs of the plan's options.
+ * Asynchronous on cuda_stream.  The plan's workspace is shared: calls on the same
+ * plan must be ordered (one stream, or events); different plans run concurrently.
+ * ------------------------------------------------------------------------------- */
+int sbd_matvec(sbd_plan_t plan, const void* f, void* q, int32_t nrhs, void* cuda_stream);
+
+/* The two halves of sbd_matvec, same arguments and layout:
+ *   sbd_far   q = NUFFT_+(omega_hat . NUFFT_-(f))   (Eq. far convolution, incl. the xi = 0 term)
+ *   sbd_close q = D f                               (Sec. 1, close correction)                  */
+int sbd_far(sbd_plan_t plan, const void* f, void* q, int32_t nrhs, void* cuda_stream);
+int sbd_close(sbd_plan_t plan, const void* f, void* q, int32_t nrhs, void* cuda_stream);
+
+/* ---------------------------------------------------------------------------------
+ * sbd_nufft_minus - the forward type-3 transform of the plan (Introduction,
+ * NUFFT_-[z, xi]): fhat_nu = sum_l exp(-i z_l . xi_nu) f_l at every quadrature node
+ * xi_nu, nodes ordered circle by circle (circle p = 0..n_circles-1, m = 0..M_p-1,
+ * xi = r_p (cos 2 pi m / M_p, sin 2 pi m / M_p), Eq. defXimp).
+ *   f     device, N complex128.      fhat   device, N_xi complex128.
+ * sbd_nufft_plus is its adjoint: q_l = sum_nu exp(+i z_l . xi_nu) ghat_nu
+ *   ghat  device, N_xi complex128.   q      device, N complex128.
+ * Both run in the plan's form; asynchronous on cuda_stream.
+ * ------------------------------------------------------------------------------- */
+int sbd_nufft_minus(sbd_plan_t plan, const void* f, void* fhat, void* cuda_stream);
+int sbd_nufft_plus(sbd_plan_t plan, const void* ghat, void* q, void* cuda_stream);
+
+/* Plan summary; host struct.  Synchronous, no device work. */
+int sbd_plan_info(sbd_plan_t plan, sbd_plan_stats* out);
+
+/* Copy the plan's SBD data to host arrays of capacity cap (>= n_circles):
+ * rho (J0 roots rho_p, Sec. 2.1), alpha (SBD coefficients on e_p = C_p J0(rho_p r),
+ * Sec. 3.1; 0 for the Helmholtz J0 circle), M (nodes per circle, Sec. 5),
+ * radius (circle radius in frequency units), weight_re/_im (omega_hat per node,
+ * Sec. 6.2, in kernel units).  Any pointer may be NULL.  Synchronous. */
+int sbd_plan_export(sbd_plan_t plan, int64_t cap, double* rho, double* alpha, int32_t* M,
+                    double* radius, double* weight_re, double* weight_im);
+
+/* Copy D (Eq. defD) to host CSR arrays: rowptr (N + 1), col (nnz), val (nnz float64
+ * for Laplace, 2 nnz float64 = complex128 for Helmholtz).  Column order within a
+ * row is unspecified.  Synchronous. */
+int sbd_close_export(sbd_plan_t plan, int64_t* rowptr, int32_t* col, double* val);
+
+/* Release the plan (NULL is accepted).  Waits for the plan's device work. */
+int sbd_destroy(sbd_plan_t plan);
+
+/* ---------------------------------------------------------------------------------
+ * sbd_offline_fit - the SBD fit and circle sizes alone, on the host (Sec. 3.2
+ * Eq. LinearSystem with the explicit A^P; Sec. 1 P search; Sec. 5 sizes).  No GPU.
+ *   kernel, delta_min, delta_max, eps   as for sbd_plan (delta_max given directly).
+ *   fixed_P      > 0 fixes P, 0 searches.
+ *   cap          capacity of rho / alpha / M (>= P, plus 1 for Helmholtz).
+ *   P_out        receives P; n_circles_out receives the number of circles.
+ *   fit_err      receives the L_inf fit error in kernel units.
+ * ------------------------------------------------------------------------------- */
+int sbd_offline_fit(sbd_kernel kernel, double delta_min, double delta_max, double eps,
+                    int32_t fixed_P, int64_t cap, double* rho, double* alpha, int32_t* M,
+                    int64_t* P_out, int64_t* n_circles_out, double* fit_err);
+
+/* ---------------------------------------------------------------------------------
+ * sbd_fft2 - the library's 2-D complex FFT on its own (the transform the far part
+ * uses; exposed for testing): out[j0][j1] = sum_{k0,k1} in[k0][k1]
+ * exp(sign * 2 pi i (j0 k0 / n0 + j1 k1 / n1)), unnormalised, row-major n0 x n1.
+ *   in, out   device, complex64 (form FP32) or complex128 (form FP64); may alias.
+ *   n0, n1    2..65536, each a product of 2, 3 and 5.
+ *   sign      -1 or +1.
+ * Asynchronous on cuda_stream; allocates a temporary of n0 x n1 elements.
+ * ------------------------------------------------------------------------------- */
+int sbd_fft2(const void* in, void* out, int32_t n0, int32_t n1, int32_t sign, int32_t form,
+             void* cuda_stream);
+
+const char* sbd_error_string(int code);
+const char* sbd_last_error_message(void);
+const char* sbd_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SBD_H */

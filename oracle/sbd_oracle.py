@@ -37,7 +37,9 @@ design notes):
       of Y0(k' s) with k' the first root of Y0 >= kappa delta_max, scaled by
       R = k'/kappa (Sec. 4.2).
   R10 The L_inf stopping test of the P search (Sec. 1) is evaluated on the
-      fixed sample set ``fit_error_samples`` of [a, 1], dense near a.
+      fixed sample set ``fit_error_samples`` of [a, 1], dense near a (where the
+      paper advises to monitor it), and the dichotomy stops at a resolution of
+      max(1, P // 128) terms (``choose_P``).
 """
 from __future__ import annotations
 
@@ -216,15 +218,19 @@ def sbd_coefficients(g_prime, a: float, P: int, extra_freq: float = 0.0):
     return rho, C, alpha
 
 
-def fit_error_samples(a: float, P: int) -> np.ndarray:
+def fit_error_samples(a: float, extra_freq: float = 0.0) -> np.ndarray:
     """Sample set of [a, 1] for the L_inf stopping test (reading R10).
 
-    8P + 400 points uniform in [a, 1] plus 400 points geometrically dense near a
-    (the paper monitors the error near delta_min, Sec. 1).
+    512 points a + d (i/511)^2 with d = min(1 - a, 30 a), dense next to a where the
+    paper advises to monitor the error (Sec. 1), plus U = 256 + 4 ceil(extra_freq/pi)
+    uniform points a + (1 - a) j / (U - 1) (extra_freq = 2 k' for the Y0 fit, whose
+    error oscillates at that frequency over the whole interval).
     """
-    uni = np.linspace(a, 1.0, 8 * P + 400)
-    near = a + (np.geomspace(1e-6, 1.0, 400) * min(1.0 - a, 20.0 * a))
-    return np.unique(np.concatenate([uni, near]))
+    d = min(1.0 - a, 30.0 * a)
+    near = a + d * (np.arange(512) / 511.0) ** 2
+    U = 256 + 4 * int(math.ceil(extra_freq / math.pi))
+    uni = a + (1.0 - a) * np.arange(U) / (U - 1.0)
+    return np.unique(np.concatenate([near, uni]))
 
 
 def series_value(s: np.ndarray, rho: np.ndarray, C: np.ndarray, alpha: np.ndarray) -> np.ndarray:
@@ -236,16 +242,27 @@ def series_value(s: np.ndarray, rho: np.ndarray, C: np.ndarray, alpha: np.ndarra
     return out
 
 
-def fit_linf_error(g, rho, C, alpha, a: float) -> float:
+def fit_linf_error(g, rho, C, alpha, a: float, extra_freq: float = 0.0) -> float:
     """max_{s in samples} |g(s) - sum_p alpha_p C_p J0(rho_p s)| (reading R10)."""
-    s = fit_error_samples(a, len(rho))
+    s = fit_error_samples(a, extra_freq)
     return float(np.max(np.abs(g(s) - series_value(s, rho, C, alpha))))
 
 
-def choose_P(g, g_prime, a: float, tol: float, P_start: int, extra_freq: float = 0.0,
-             P_max: int = 4000):
-    """Smallest P whose fit error is <= tol, by doubling then dichotomy (Sec. 1).
+def initial_P(a: float, tol: float, extra_freq: float = 0.0) -> int:
+    """Starting P of the search: gamma = P a from the observed Laplace rate (Sec. 4.1,
+    log10 err ~ -0.5 - 1.5 gamma), plus k'/pi Bessel terms for the Y0 fit (Sec. 4.2)."""
+    gamma = max(0.5, (-math.log10(tol) - 0.5) / 1.5)
+    return max(2, int(math.ceil(gamma / a)) + int(math.ceil(extra_freq / (2.0 * math.pi))))
 
+
+def choose_P(g, g_prime, a: float, tol: float, P_start: int, extra_freq: float = 0.0,
+             P_max: int = 20000):
+    """A P whose fit error is <= tol, by bracketing then dichotomy (Sec. 1).
+
+    Bracket: from P_start, grow by factors 1.1 (ceil) while the error is above tol,
+    or shrink by factors 0.9 (floor) while it is below.  Dichotomy on the bracket
+    (lo fails, hi passes) until hi - lo <= max(1, hi // 128): the smallest
+    passing P when P < 256, within 1% above it beyond.
     Returns (P, rho, C, alpha, err).
     """
     cache = {}
@@ -253,23 +270,25 @@ def choose_P(g, g_prime, a: float, tol: float, P_start: int, extra_freq: float =
     def err_of(P):
         if P not in cache:
             rho, C, alpha = sbd_coefficients(g_prime, a, P, extra_freq)
-            cache[P] = (fit_linf_error(g, rho, C, alpha, a), rho, C, alpha)
+            cache[P] = (fit_linf_error(g, rho, C, alpha, a, extra_freq), rho, C, alpha)
         return cache[P][0]
 
-    hi = max(1, P_start)
-    while err_of(hi) > tol:
-        if hi >= P_max:
-            raise RuntimeError(f"SBD fit does not reach {tol:g} with P <= {P_max}")
-        hi = min(P_max, 2 * hi)
-    lo = 0  # invariant: err(hi) <= tol, and lo == 0 or err(lo) > tol
-    probe = hi // 2
-    while probe > 0 and err_of(probe) <= tol:
-        hi = probe
-        probe //= 2
-    lo = probe
-    while hi - lo > 1:
+    P = max(1, P_start)
+    if err_of(P) > tol:
+        lo, hi = P, int(math.ceil(P * 1.1))
+        while err_of(hi) > tol:
+            if hi >= P_max:
+                raise RuntimeError(f"SBD fit does not reach {tol:g} with P <= {P_max}")
+            lo, hi = hi, min(P_max, int(math.ceil(hi * 1.1)))
+    else:
+        hi, lo = P, int(math.floor(P * 0.9))
+        while lo >= 1 and err_of(lo) <= tol:
+            hi, lo = lo, int(math.floor(lo * 0.9))
+        lo = max(lo, 0)
+    res = max(1, hi // 128)
+    while hi - lo > res:
         mid = (lo + hi) // 2
-        if err_of(mid) <= tol:
+        if mid >= 1 and err_of(mid) <= tol:
             hi = mid
         else:
             lo = mid
@@ -323,7 +342,7 @@ class OraclePlan:
     rho: np.ndarray
     C: np.ndarray
     alpha: np.ndarray
-    fit_err: float
+    fit_err: float          # L_inf error of the fitted g on the sample set (g units)
     M: np.ndarray           # nodes per circle (Bessel circles first; Helmholtz J0 circle last)
     circle_radius: np.ndarray
     circle_weight: np.ndarray   # omega_hat per node of each circle (complex)
@@ -369,11 +388,11 @@ def make_plan(z: np.ndarray, kind: str, delta_min: float, eps: float, kappa: flo
     tol_fit = eps_fit / abs(gscale)
     if P is None:
         if P_start is None:
-            P_start = max(4, int(math.ceil(1.5 / a)) + (int(extra / (2 * math.pi)) if extra else 0))
+            P_start = initial_P(a, tol_fit, extra)
         P, rho, C, alpha, err = choose_P(g, g_prime, a, tol_fit, P_start, extra)
     else:
         rho, C, alpha = sbd_coefficients(g_prime, a, P, extra)
-        err = fit_linf_error(g, rho, C, alpha, a)
+        err = fit_linf_error(g, rho, C, alpha, a, extra)
     coef = gscale * alpha * C      # kernel units: G ~ const + sum_p coef_p J0(rho_p r / scale_R)
     n_circles = P + (1 if kind == "helmholtz" else 0)
     M = np.array([circle_size(float(rho[p]), float(coef[p]), eps_q / n_circles) for p in range(P)],

@@ -165,7 +165,7 @@ def test_y0_root_and_fit():
     for gamma in (2, 3, 4):
         P = int(kp / math.pi + gamma / 0.05)
         rho, C, al = O.sbd_coefficients(lambda s: -kp * sp.y1(kp * s), 0.05, P, 2 * kp)
-        errs.append(O.fit_linf_error(lambda s: sp.y0(kp * s), rho, C, al, 0.05))
+        errs.append(O.fit_linf_error(lambda s: sp.y0(kp * s), rho, C, al, 0.05, 2 * kp))
     assert errs[0] > 10 * errs[1] > 100 * errs[2]
     assert errs[2] < 1e-7
 
