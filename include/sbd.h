@@ -89,6 +89,7 @@ typedef struct {
     int32_t stencil_x;       /* spreading stencil width (cells per dimension) */
     int32_t stencil_k;       /* node-step stencil width (cells per dimension) */
     int32_t form;            /* sbd_form */
+    int32_t kind;            /* sbd_kernel_kind */
     double  delta_max;       /* 2 max_k |z_k - c|, c = bounding-box centre */
     double  delta_min;
     double  scale_R;         /* radius scale of the Bessel circles (delta_max, or k'/kappa for Y0) */
@@ -191,6 +192,25 @@ int sbd_offline_fit(sbd_kernel kernel, double delta_min, double delta_max, doubl
  * ------------------------------------------------------------------------------- */
 int sbd_fft2(const void* in, void* out, int32_t n0, int32_t n1, int32_t sign, int32_t form,
              void* cuda_stream);
+
+/* ---------------------------------------------------------------------------------
+ * Step timing of the on-line part.  sbd_profile(plan, 1) waits for the device,
+ * clears the counters and starts recording a pair of CUDA events on the caller's
+ * stream around every step of sbd_matvec / sbd_far / sbd_close (0 stops).
+ * sbd_profile_read waits for the recorded events and returns, per step
+ * (SBD_STAGE_*), the summed device time in ms and the number of timed runs into
+ * host arrays of SBD_N_STAGES entries.  Not for concurrent use on one plan.
+ * ------------------------------------------------------------------------------- */
+#define SBD_STAGE_SUM      0   /* sum_l f_l for the xi = 0 term */
+#define SBD_STAGE_SPREAD   1   /* Gaussian spreading of the points */
+#define SBD_STAGE_FFT_FWD  2   /* precorrection + forward 2-D FFT */
+#define SBD_STAGE_NODE     3   /* node gather, omega_hat weighting, node scatter */
+#define SBD_STAGE_FFT_INV  4   /* inverse 2-D FFT + postcorrection */
+#define SBD_STAGE_INTERP   5   /* interpolation at the points (+ xi = 0 term) */
+#define SBD_STAGE_SPMV     6   /* close correction D f */
+#define SBD_N_STAGES       7
+int sbd_profile(sbd_plan_t plan, int32_t enable);
+int sbd_profile_read(sbd_plan_t plan, double* ms, int64_t* count);
 
 const char* sbd_error_string(int code);
 const char* sbd_last_error_message(void);

@@ -1,0 +1,662 @@
+// C ABI of libsbd.so: plan construction (off-line part) and the on-line matvec.
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "far.cuh"
+#include "fft.cuh"
+#include "near.cuh"
+#include "offline.h"
+#include "sbd.h"
+
+namespace sbd {
+
+namespace {
+thread_local std::string g_last_error;
+}
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+}  // namespace sbd
+
+using namespace sbd;
+
+struct sbd_plan_s {
+    int kind = 0;
+    double kappa = 0.0;
+    int form = SBD_FORM_FP64;
+    long n = 0;
+    int max_nrhs = 1;
+    SbdFit fit;
+    NufftParams np;
+    NearTables nt;
+    FarGeom geom{};
+    cplx w0 = 0.0;
+    // device data
+    double* z = nullptr;
+    void* pts = nullptr;
+    void* nodes = nullptr;
+    void* omega_c = nullptr;   // per circle: omega_hat * c^2 (T complex)
+    void* cscale_c = nullptr;  // per circle: c (T)
+    void* dec = nullptr;       // T[m]
+    long long* rowptr = nullptr;
+    int* col = nullptr;
+    void* val = nullptr;
+    long long nnz = 0, n_coinc = 0;
+    double* T1 = nullptr;
+    double* T2 = nullptr;
+    double* small_xi = nullptr;
+    double* small_w = nullptr;
+    int* small_start = nullptr;
+    int* circle_start = nullptr;
+    double* circle_radius = nullptr;
+    int* circle_M = nullptr;
+    // workspace (one right-hand side at a time)
+    void* wsX = nullptr;
+    void* wsA = nullptr;
+    void* wsB = nullptr;
+    void* wsC = nullptr;
+    double2* sumf = nullptr;
+    double2* zero2 = nullptr;
+    long long device_bytes = 0;
+    double plan_seconds = 0.0;
+    std::vector<void*> allocations;
+    // step timing (sbd_profile): events recorded around each on-line step
+    bool profile = false;
+    struct Mark { int stage; cudaEvent_t a, b; };
+    std::vector<Mark> marks;
+    std::vector<cudaEvent_t> event_pool;
+    double stage_ms[SBD_N_STAGES] = {};
+    long long stage_count[SBD_N_STAGES] = {};
+};
+
+namespace {
+
+int dev_alloc(sbd_plan_s* p, void** ptr, size_t bytes) {
+    bytes = std::max<size_t>(bytes, 16);
+    cudaError_t e = cudaMalloc(ptr, bytes);
+    if (e != cudaSuccess) {
+        set_error(std::string("cudaMalloc(") + std::to_string(bytes) + "): " + cudaGetErrorString(e));
+        cudaGetLastError();
+        return e == cudaErrorMemoryAllocation ? SBD_ENOMEM : SBD_ECUDA;
+    }
+    p->allocations.push_back(*ptr);
+    p->device_bytes += static_cast<long long>(bytes);
+    return SBD_OK;
+}
+
+template <typename X>
+int upload(sbd_plan_s* p, X** dst, const std::vector<X>& src, cudaStream_t s) {
+    int rc = dev_alloc(p, reinterpret_cast<void**>(dst), sizeof(X) * src.size());
+    if (rc) return rc;
+    if (!src.empty()) SBD_CUDA_TRY(cudaMemcpyAsync(*dst, src.data(), sizeof(X) * src.size(), cudaMemcpyHostToDevice, s));
+    return SBD_OK;
+}
+
+cudaEvent_t take_event(sbd_plan_s* p) {
+    if (!p->event_pool.empty()) {
+        cudaEvent_t e = p->event_pool.back();
+        p->event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// RAII-free helpers: begin() records the start event, end() the stop event of a step.
+struct StepTimer {
+    sbd_plan_s* p;
+    cudaStream_t s;
+    int stage;
+    cudaEvent_t a = nullptr;
+    StepTimer(sbd_plan_s* p_, cudaStream_t s_, int stage_) : p(p_), s(s_), stage(stage_) {
+        if (p->profile) {
+            a = take_event(p);
+            cudaEventRecord(a, s);
+        }
+    }
+    void end() {
+        if (!p->profile || !a) return;
+        cudaEvent_t b = take_event(p);
+        cudaEventRecord(b, s);
+        p->marks.push_back({stage, a, b});
+        a = nullptr;
+    }
+};
+
+void collect_marks(sbd_plan_s* p) {
+    for (auto& m : p->marks) {
+        cudaEventSynchronize(m.b);
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, m.a, m.b) == cudaSuccess) {
+            p->stage_ms[m.stage] += ms;
+            p->stage_count[m.stage] += 1;
+        }
+        p->event_pool.push_back(m.a);
+        p->event_pool.push_back(m.b);
+    }
+    p->marks.clear();
+}
+
+void free_plan(sbd_plan_s* p) {
+    if (!p) return;
+    cudaDeviceSynchronize();
+    collect_marks(p);
+    for (cudaEvent_t e : p->event_pool) cudaEventDestroy(e);
+    for (void* a : p->allocations) cudaFree(a);
+    if (p->rowptr) cudaFree(p->rowptr);
+    if (p->col) cudaFree(p->col);
+    if (p->val) cudaFree(p->val);
+    delete p;
+}
+
+template <typename T>
+int build_far(sbd_plan_s* p, cudaStream_t s) {
+    const NufftParams& np = p->np;
+    const SbdFit& fit = p->fit;
+    p->geom.P = np.Pk;
+    p->geom.m = np.m;
+    p->geom.nk = np.nk;
+    p->geom.beta_s = np.beta_s;
+    p->geom.beta_k = np.beta_k;
+    int rc = dev_alloc(p, &p->pts, sizeof(PointRec<T>) * p->n);
+    if (rc) return rc;
+    rc = far_prepare_points<T>(p->z, p->n, np.cx, np.cy, np.h, np.m, np.Ps, static_cast<PointRec<T>*>(p->pts), s);
+    if (rc) return rc;
+    std::vector<int> start(fit.n_circles + 1, 0);
+    for (int c = 0; c < fit.n_circles; ++c) start[c + 1] = start[c] + fit.M[c];
+    if (fit.n_xi > 2000000000LL) {
+        set_error("too many quadrature nodes for 32-bit circle offsets");
+        return SBD_ENOTSUP;
+    }
+    if ((rc = upload(p, &p->circle_start, start, s))) return rc;
+    if ((rc = upload(p, &p->circle_radius, fit.radius, s))) return rc;
+    if ((rc = upload(p, &p->circle_M, fit.M, s))) return rc;
+    if ((rc = dev_alloc(p, &p->nodes, sizeof(NodeRec<T>) * fit.n_xi))) return rc;
+    rc = far_prepare_nodes<T>(p->circle_start, p->circle_radius, p->circle_M, fit.n_circles, fit.n_xi, np.deta,
+                              np.nk, np.Pk, static_cast<NodeRec<T>*>(p->nodes), s);
+    if (rc) return rc;
+    std::vector<cx_t<T>> om(fit.n_circles);
+    std::vector<T> cs(fit.n_circles);
+    for (int c = 0; c < fit.n_circles; ++c) {
+        const cplx w = fit.weight[c] * np.circle_factor[c];
+        om[c] = mk<T>(static_cast<T>(w.real()), static_cast<T>(w.imag()));
+        cs[c] = static_cast<T>(std::sqrt(np.circle_factor[c]));
+    }
+    if ((rc = upload(p, reinterpret_cast<cx_t<T>**>(&p->omega_c), om, s))) return rc;
+    if ((rc = upload(p, reinterpret_cast<T**>(&p->cscale_c), cs, s))) return rc;
+    std::vector<T> dec(np.m);
+    for (int i = 0; i < np.m; ++i) dec[i] = static_cast<T>(np.dec[i]);
+    if ((rc = upload(p, reinterpret_cast<T**>(&p->dec), dec, s))) return rc;
+    const size_t e = sizeof(cx_t<T>);
+    const size_t m = np.m, nk = np.nk;
+    if ((rc = dev_alloc(p, &p->wsX, e * m * m))) return rc;
+    if ((rc = dev_alloc(p, &p->wsA, e * m * nk))) return rc;
+    if ((rc = dev_alloc(p, &p->wsB, e * nk * nk))) return rc;
+    if ((rc = dev_alloc(p, &p->wsC, e * nk * nk))) return rc;
+    return SBD_OK;
+}
+
+// spreading grid X (m x m, rows = y) -> frequency grid K (nk x nk, rows = kx), forward transform.
+// A (m x nk) and Tr (>= nk x m) are scratch.
+template <typename T>
+int forward_fft(sbd_plan_s* p, const cx_t<T>* X, cx_t<T>* A, cx_t<T>* Tr, cx_t<T>* K, cudaStream_t s) {
+    const NufftParams& np = p->np;
+    const int m = np.m, nk = np.nk, n = np.n;
+    const T* dec = static_cast<const T*>(p->dec);
+    // along x (rows y), precorrection exp(sigma |x|^2) fused into the load
+    int rc = fft_rows<T>(X, m, m, -m / 2, A, nk, nk, -nk / 2, m, n, -1, dec, dec, nullptr, nullptr, s);
+    if (rc) return rc;
+    if ((rc = transpose<T>(A, nk, 0, Tr, m, 0, m, nk, 1, s))) return rc;   // [y][kx] -> [kx][y]
+    // along y (rows kx)
+    return fft_rows<T>(Tr, m, m, -m / 2, K, nk, nk, -nk / 2, nk, n, -1, nullptr, nullptr, nullptr, nullptr, s);
+}
+
+// frequency grid K2 (nk x nk, rows = kx) -> spreading grid X (m x m), adjoint transform.
+// A (nk x m) and Tr (>= m x nk) are scratch.
+template <typename T>
+int inverse_fft(sbd_plan_s* p, const cx_t<T>* K2, cx_t<T>* A, cx_t<T>* Tr, cx_t<T>* X, cudaStream_t s) {
+    const NufftParams& np = p->np;
+    const int m = np.m, nk = np.nk, n = np.n;
+    const T* dec = static_cast<const T*>(p->dec);
+    int rc = fft_rows<T>(K2, nk, nk, -nk / 2, A, m, m, -m / 2, nk, n, +1, nullptr, nullptr, nullptr, nullptr, s);
+    if (rc) return rc;
+    if ((rc = transpose<T>(A, m, 0, Tr, nk, 0, nk, m, 1, s))) return rc;   // [kx][y] -> [y][kx]
+    return fft_rows<T>(Tr, nk, nk, -nk / 2, X, m, m, -m / 2, m, n, +1, nullptr, nullptr, dec, dec, s);
+}
+
+template <typename T>
+int far_apply(sbd_plan_s* p, const void* f, void* q, int nrhs, cudaStream_t s) {
+    const bool cplx_io = p->kind == SBD_HELMHOLTZ;
+    StepTimer t_sum(p, s, SBD_STAGE_SUM);
+    int rc = far_sum(f, cplx_io, p->n, nrhs, p->sumf, s);
+    if (rc) return rc;
+    t_sum.end();
+    const size_t esz = cplx_io ? 16 : 8;
+    auto* X = static_cast<cx_t<T>*>(p->wsX);
+    auto* A = static_cast<cx_t<T>*>(p->wsA);
+    auto* B = static_cast<cx_t<T>*>(p->wsB);
+    auto* C = static_cast<cx_t<T>*>(p->wsC);
+    const double2 w0 = make_double2(p->w0.real(), p->w0.imag());
+    for (int r = 0; r < nrhs; ++r) {
+        const void* fr = static_cast<const char*>(f) + esz * p->n * r;
+        void* qr = static_cast<char*>(q) + esz * p->n * r;
+        StepTimer t1(p, s, SBD_STAGE_SPREAD);
+        if ((rc = far_spread<T>(static_cast<const PointRec<T>*>(p->pts), p->n, fr, cplx_io, 1, p->geom, X, s))) return rc;
+        t1.end();
+        StepTimer t2(p, s, SBD_STAGE_FFT_FWD);
+        if ((rc = forward_fft<T>(p, X, A, C, B, s))) return rc;
+        t2.end();
+        StepTimer t3(p, s, SBD_STAGE_NODE);
+        if ((rc = far_node_step<T>(static_cast<const NodeRec<T>*>(p->nodes), p->fit.n_xi,
+                                   static_cast<const cx_t<T>*>(p->omega_c), 1, p->geom, B, C, s))) return rc;
+        t3.end();
+        StepTimer t4(p, s, SBD_STAGE_FFT_INV);
+        if ((rc = inverse_fft<T>(p, C, A, B, X, s))) return rc;
+        t4.end();
+        StepTimer t5(p, s, SBD_STAGE_INTERP);
+        if ((rc = far_interp<T>(static_cast<const PointRec<T>*>(p->pts), p->n, 1, p->geom, X, w0, p->sumf + r, qr,
+                                cplx_io, s))) return rc;
+        t5.end();
+    }
+    return SBD_OK;
+}
+
+template <typename T>
+int nufft_minus_impl(sbd_plan_s* p, const void* f, void* fhat, cudaStream_t s) {
+    auto* X = static_cast<cx_t<T>*>(p->wsX);
+    auto* A = static_cast<cx_t<T>*>(p->wsA);
+    auto* B = static_cast<cx_t<T>*>(p->wsB);
+    auto* C = static_cast<cx_t<T>*>(p->wsC);
+    int rc = far_spread<T>(static_cast<const PointRec<T>*>(p->pts), p->n, f, true, 1, p->geom, X, s);
+    if (rc) return rc;
+    if ((rc = forward_fft<T>(p, X, A, C, B, s))) return rc;
+    return far_node_gather<T>(static_cast<const NodeRec<T>*>(p->nodes), p->fit.n_xi,
+                              static_cast<const T*>(p->cscale_c), p->geom, B, static_cast<double2*>(fhat), s);
+}
+
+template <typename T>
+int nufft_plus_impl(sbd_plan_s* p, const void* ghat, void* q, cudaStream_t s) {
+    auto* X = static_cast<cx_t<T>*>(p->wsX);
+    auto* A = static_cast<cx_t<T>*>(p->wsA);
+    auto* B = static_cast<cx_t<T>*>(p->wsB);
+    auto* C = static_cast<cx_t<T>*>(p->wsC);
+    int rc = far_node_scatter<T>(static_cast<const NodeRec<T>*>(p->nodes), p->fit.n_xi,
+                                 static_cast<const T*>(p->cscale_c), p->geom, static_cast<const double2*>(ghat), C, s);
+    if (rc) return rc;
+    if ((rc = inverse_fft<T>(p, C, A, B, X, s))) return rc;
+    SBD_CUDA_TRY(cudaMemsetAsync(p->zero2, 0, sizeof(double2), s));
+    return far_interp<T>(static_cast<const PointRec<T>*>(p->pts), p->n, 1, p->geom, X, make_double2(0, 0), p->zero2,
+                         q, true, s);
+}
+
+int check_plan_call(sbd_plan_t p, const void* a, const void* b) {
+    if (!p || !a || !b) {
+        set_error("null plan or buffer");
+        return SBD_EINVAL;
+    }
+    return SBD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* sbd_version(void) { return "sbd-gb300 0.1"; }
+
+const char* sbd_error_string(int code) {
+    switch (code) {
+        case SBD_OK: return "ok";
+        case SBD_EINVAL: return "invalid argument";
+        case SBD_ENOMEM: return "out of memory";
+        case SBD_ECUDA: return "CUDA error";
+        case SBD_EFIT: return "SBD fit cannot reach the tolerance";
+        case SBD_ETIMEOUT: return "device wait timed out";
+        case SBD_ENOTSUP: return "not supported";
+        default: return "unknown error";
+    }
+}
+
+const char* sbd_last_error_message(void) { return g_last_error.c_str(); }
+
+int sbd_offline_fit(sbd_kernel kernel, double delta_min, double delta_max, double eps, int32_t fixed_P,
+                    int64_t cap, double* rho, double* alpha, int32_t* M, int64_t* P_out, int64_t* n_circles_out,
+                    double* fit_err) {
+    SbdFit fit;
+    std::string err;
+    const int rc = offline_fit(kernel.kind, kernel.kappa, delta_min, delta_max, eps, fixed_P, fit, err);
+    if (rc) {
+        set_error(err);
+        return rc;
+    }
+    if (cap < fit.n_circles) {
+        set_error("capacity below the number of circles");
+        return SBD_EINVAL;
+    }
+    for (int c = 0; c < fit.n_circles; ++c) {
+        if (rho) rho[c] = c < fit.P ? fit.rho[c] : 0.0;
+        if (alpha) alpha[c] = c < fit.P ? fit.alpha[c] : 0.0;
+        if (M) M[c] = fit.M[c];
+    }
+    if (P_out) *P_out = fit.P;
+    if (n_circles_out) *n_circles_out = fit.n_circles;
+    if (fit_err) *fit_err = fit.fit_err;
+    return SBD_OK;
+}
+
+int sbd_plan(const double* points, int64_t n, sbd_kernel kernel, double delta_min, double eps,
+             const sbd_options* opt, void* cuda_stream, sbd_plan_t* out) {
+    const auto t0 = std::chrono::steady_clock::now();
+    if (!points || !out || n < 1) {
+        set_error("sbd_plan: null pointer or n < 1");
+        return SBD_EINVAL;
+    }
+    if (n > 2000000000LL) {
+        set_error("sbd_plan: n exceeds 32-bit column indices");
+        return SBD_ENOTSUP;
+    }
+    sbd_options o{};
+    o.form = SBD_FORM_FP64;
+    if (opt) o = *opt;
+    if (o.form != SBD_FORM_FP64 && o.form != SBD_FORM_FP32) {
+        set_error("sbd_plan: unknown form");
+        return SBD_EINVAL;
+    }
+    if (o.flags != 0 || o.fixed_P < 0 || o.max_nrhs < 0 || o.nufft_tol < 0) {
+        set_error("sbd_plan: invalid options");
+        return SBD_EINVAL;
+    }
+    if (kernel.kind == SBD_HELMHOLTZ && !(kernel.kappa > 0)) {
+        set_error("sbd_plan: Helmholtz needs kappa > 0");
+        return SBD_EINVAL;
+    }
+    if (kernel.kind != SBD_LAPLACE && kernel.kind != SBD_HELMHOLTZ) {
+        set_error("sbd_plan: unknown kernel");
+        return SBD_EINVAL;
+    }
+    if (!(eps >= 1e-10 && eps <= 0.1) || !(delta_min > 0)) {
+        set_error("sbd_plan: need 1e-10 <= eps <= 0.1 and delta_min > 0");
+        return SBD_EINVAL;
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    auto* p = new sbd_plan_s();
+    p->kind = kernel.kind;
+    p->kappa = kernel.kappa;
+    p->form = o.form;
+    p->n = static_cast<long>(n);
+    p->max_nrhs = std::max(1, o.max_nrhs);
+    auto fail = [&](int rc) {
+        free_plan(p);
+        return rc;
+    };
+    int rc = dev_alloc(p, reinterpret_cast<void**>(&p->z), sizeof(double) * 2 * n);
+    if (rc) return fail(rc);
+    if (cudaMemcpyAsync(p->z, points, sizeof(double) * 2 * n, cudaMemcpyDefault, s) != cudaSuccess) {
+        set_error("sbd_plan: copying the points failed (device pointer expected)");
+        cudaGetLastError();
+        return fail(SBD_ECUDA);
+    }
+    double bb[4];
+    if ((rc = points_bbox(p->z, p->n, bb, s))) return fail(rc);
+    const double cx = 0.5 * (bb[0] + bb[2]), cy = 0.5 * (bb[1] + bb[3]);
+    double md2 = 0.0;
+    if ((rc = points_max_dist2(p->z, p->n, cx, cy, &md2, s))) return fail(rc);
+    const double delta_max = 2.0 * std::sqrt(md2);
+    if (!(delta_min < delta_max)) {
+        set_error("sbd_plan: delta_min must be below delta_max = 2 max |z - c|");
+        return fail(SBD_EINVAL);
+    }
+    std::string err;
+    if ((rc = offline_fit(kernel.kind, kernel.kappa, delta_min, delta_max, eps, o.fixed_P, p->fit, err))) {
+        set_error(err);
+        return fail(rc);
+    }
+    const SbdFit& fit = p->fit;
+    p->w0 = fit.w0;
+    double W = 0.0;
+    for (int c = 0; c < fit.n_circles; ++c) W += fit.M[c] * std::abs(fit.weight[c]);
+    const double tol = o.nufft_tol > 0 ? o.nufft_tol : eps / (6.0 * std::max(W, 1e-300));
+    const double half = std::max(std::max(bb[2] - cx, bb[3] - cy), 1e-300);
+    if ((rc = nufft_params(fit, half, cx, cy, tol, o.form == SBD_FORM_FP32, p->np, err))) {
+        set_error(err);
+        return fail(rc);
+    }
+    if (p->np.n > fft_max_row(o.form == SBD_FORM_FP64)) {
+        set_error("sbd_plan: FFT length " + std::to_string(p->np.n) + " exceeds the single-row kernel limit");
+        return fail(SBD_ENOTSUP);
+    }
+    if ((rc = near_tables(fit, p->nt, err))) {
+        set_error(err);
+        return fail(rc);
+    }
+    // near-field device tables
+    const NearTables& nt = p->nt;
+    if ((rc = upload(p, &p->T1, nt.T1, s))) return fail(rc);
+    if ((rc = upload(p, &p->T2, nt.T2, s))) return fail(rc);
+    std::vector<double> sxi, sw;
+    std::vector<int> sst(1, 0);
+    for (int c : nt.small) {
+        for (int m = 0; m < fit.M[c]; ++m) {
+            const double th = 2.0 * 3.14159265358979323846 * m / fit.M[c];
+            sxi.push_back(fit.radius[c] * std::cos(th));
+            sxi.push_back(fit.radius[c] * std::sin(th));
+        }
+        sst.push_back(sst.back() + fit.M[c]);
+        sw.push_back(fit.weight[c].real());
+        sw.push_back(fit.weight[c].imag());
+    }
+    if ((rc = upload(p, &p->small_xi, sxi, s))) return fail(rc);
+    if ((rc = upload(p, &p->small_w, sw, s))) return fail(rc);
+    if ((rc = upload(p, &p->small_start, sst, s))) return fail(rc);
+    NearDev nd;
+    nd.pieces = nt.pieces;
+    nd.deg = nt.deg;
+    nd.tmax = nt.tmax;
+    nd.T1 = p->T1;
+    nd.T2 = p->T2;
+    nd.n_small = static_cast<int>(nt.small.size());
+    nd.small_xi = p->small_xi;
+    nd.small_start = p->small_start;
+    nd.small_w = p->small_w;
+    nd.self_re = nt.self_value.real();
+    nd.self_im = nt.self_value.imag();
+    const bool cval = kernel.kind == SBD_HELMHOLTZ;
+    if ((rc = near_build(p->z, p->n, delta_min, bb[0], bb[1], bb[2], bb[3], nd, cval, &p->rowptr, &p->col, &p->val,
+                         &p->nnz, &p->n_coinc, s))) return fail(rc);
+    p->device_bytes += static_cast<long long>(sizeof(long long) * (p->n + 1) + (sizeof(int) + (cval ? 16 : 8)) * p->nnz);
+    p->n_coinc /= 2;
+    rc = o.form == SBD_FORM_FP32 ? build_far<float>(p, s) : build_far<double>(p, s);
+    if (rc) return fail(rc);
+    if ((rc = dev_alloc(p, reinterpret_cast<void**>(&p->sumf), sizeof(double2) * p->max_nrhs))) return fail(rc);
+    if ((rc = dev_alloc(p, reinterpret_cast<void**>(&p->zero2), sizeof(double2)))) return fail(rc);
+    if (cudaStreamSynchronize(s) != cudaSuccess) {
+        set_error(std::string("sbd_plan: ") + cudaGetErrorString(cudaGetLastError()));
+        return fail(SBD_ECUDA);
+    }
+    p->plan_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    *out = p;
+    return SBD_OK;
+}
+
+int sbd_far(sbd_plan_t p, const void* f, void* q, int32_t nrhs, void* cuda_stream) {
+    int rc = check_plan_call(p, f, q);
+    if (rc) return rc;
+    if (nrhs < 1 || nrhs > p->max_nrhs) {
+        set_error("nrhs outside [1, max_nrhs]");
+        return SBD_EINVAL;
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    return p->form == SBD_FORM_FP32 ? far_apply<float>(p, f, q, nrhs, s) : far_apply<double>(p, f, q, nrhs, s);
+}
+
+int sbd_close(sbd_plan_t p, const void* f, void* q, int32_t nrhs, void* cuda_stream) {
+    int rc = check_plan_call(p, f, q);
+    if (rc) return rc;
+    if (nrhs < 1 || nrhs > p->max_nrhs) {
+        set_error("nrhs outside [1, max_nrhs]");
+        return SBD_EINVAL;
+    }
+    return near_spmv(p->rowptr, p->col, p->val, p->kind == SBD_HELMHOLTZ, p->n, nrhs, f, q, false,
+                     static_cast<cudaStream_t>(cuda_stream));
+}
+
+int sbd_matvec(sbd_plan_t p, const void* f, void* q, int32_t nrhs, void* cuda_stream) {
+    int rc = sbd_far(p, f, q, nrhs, cuda_stream);
+    if (rc) return rc;
+    StepTimer t(p, static_cast<cudaStream_t>(cuda_stream), SBD_STAGE_SPMV);
+    rc = near_spmv(p->rowptr, p->col, p->val, p->kind == SBD_HELMHOLTZ, p->n, nrhs, f, q, true,
+                   static_cast<cudaStream_t>(cuda_stream));
+    t.end();
+    return rc;
+}
+
+int sbd_profile(sbd_plan_t p, int32_t enable) {
+    if (!p) {
+        set_error("null plan");
+        return SBD_EINVAL;
+    }
+    SBD_CUDA_TRY(cudaDeviceSynchronize());
+    collect_marks(p);
+    for (int i = 0; i < SBD_N_STAGES; ++i) {
+        p->stage_ms[i] = 0.0;
+        p->stage_count[i] = 0;
+    }
+    p->profile = enable != 0;
+    return SBD_OK;
+}
+
+int sbd_profile_read(sbd_plan_t p, double* ms, int64_t* count) {
+    if (!p || !ms || !count) {
+        set_error("null plan or output");
+        return SBD_EINVAL;
+    }
+    collect_marks(p);
+    for (int i = 0; i < SBD_N_STAGES; ++i) {
+        ms[i] = p->stage_ms[i];
+        count[i] = p->stage_count[i];
+    }
+    return SBD_OK;
+}
+
+int sbd_nufft_minus(sbd_plan_t p, const void* f, void* fhat, void* cuda_stream) {
+    int rc = check_plan_call(p, f, fhat);
+    if (rc) return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    return p->form == SBD_FORM_FP32 ? nufft_minus_impl<float>(p, f, fhat, s) : nufft_minus_impl<double>(p, f, fhat, s);
+}
+
+int sbd_nufft_plus(sbd_plan_t p, const void* ghat, void* q, void* cuda_stream) {
+    int rc = check_plan_call(p, ghat, q);
+    if (rc) return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    return p->form == SBD_FORM_FP32 ? nufft_plus_impl<float>(p, ghat, q, s) : nufft_plus_impl<double>(p, ghat, q, s);
+}
+
+int sbd_plan_info(sbd_plan_t p, sbd_plan_stats* o) {
+    if (!p || !o) {
+        set_error("null plan or output");
+        return SBD_EINVAL;
+    }
+    std::memset(o, 0, sizeof *o);
+    o->n_points = p->n;
+    o->P = p->fit.P;
+    o->n_circles = p->fit.n_circles;
+    o->n_xi = p->fit.n_xi;
+    o->nnz = p->nnz;
+    o->n_coincident = p->n_coinc;
+    o->grid_x = p->np.m;
+    o->grid_k = p->np.nk;
+    o->fft_n = p->np.n;
+    o->stencil_x = p->np.Ps;
+    o->stencil_k = p->np.Pk;
+    o->form = p->form;
+    o->kind = p->kind;
+    o->delta_max = p->fit.delta_max;
+    o->delta_min = p->fit.delta_min;
+    o->scale_R = p->fit.scale_R;
+    o->a = p->fit.a;
+    o->fit_err = p->fit.fit_err;
+    o->nufft_tol = p->np.tol;
+    o->w0_re = p->w0.real();
+    o->w0_im = p->w0.imag();
+    o->device_bytes = p->device_bytes;
+    o->plan_seconds = p->plan_seconds;
+    return SBD_OK;
+}
+
+int sbd_plan_export(sbd_plan_t p, int64_t cap, double* rho, double* alpha, int32_t* M, double* radius,
+                    double* weight_re, double* weight_im) {
+    if (!p) {
+        set_error("null plan");
+        return SBD_EINVAL;
+    }
+    const SbdFit& f = p->fit;
+    if (cap < f.n_circles) {
+        set_error("capacity below the number of circles");
+        return SBD_EINVAL;
+    }
+    for (int c = 0; c < f.n_circles; ++c) {
+        if (rho) rho[c] = c < f.P ? f.rho[c] : 0.0;
+        if (alpha) alpha[c] = c < f.P ? f.alpha[c] : 0.0;
+        if (M) M[c] = f.M[c];
+        if (radius) radius[c] = f.radius[c];
+        if (weight_re) weight_re[c] = f.weight[c].real();
+        if (weight_im) weight_im[c] = f.weight[c].imag();
+    }
+    return SBD_OK;
+}
+
+int sbd_close_export(sbd_plan_t p, int64_t* rowptr, int32_t* col, double* val) {
+    if (!p || !rowptr || !col || !val) {
+        set_error("null plan or buffer");
+        return SBD_EINVAL;
+    }
+    SBD_CUDA_TRY(cudaDeviceSynchronize());
+    SBD_CUDA_TRY(cudaMemcpy(rowptr, p->rowptr, sizeof(long long) * (p->n + 1), cudaMemcpyDeviceToHost));
+    SBD_CUDA_TRY(cudaMemcpy(col, p->col, sizeof(int) * p->nnz, cudaMemcpyDeviceToHost));
+    SBD_CUDA_TRY(cudaMemcpy(val, p->val, (p->kind == SBD_HELMHOLTZ ? 16 : 8) * p->nnz, cudaMemcpyDeviceToHost));
+    return SBD_OK;
+}
+
+int sbd_destroy(sbd_plan_t p) {
+    free_plan(p);
+    return SBD_OK;
+}
+
+int sbd_fft2(const void* in, void* out, int32_t n0, int32_t n1, int32_t sign, int32_t form, void* cuda_stream) {
+    if (!in || !out || n0 < 2 || n1 < 2 || n0 > 65536 || n1 > 65536 || (sign != 1 && sign != -1) ||
+        (form != SBD_FORM_FP32 && form != SBD_FORM_FP64)) {
+        set_error("sbd_fft2: invalid argument");
+        return SBD_EINVAL;
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    const size_t esz = form == SBD_FORM_FP32 ? 8 : 16;
+    void* tmp = nullptr;
+    SBD_CUDA_TRY(cudaMallocAsync(&tmp, esz * static_cast<size_t>(n0) * n1, s));
+    int rc;
+    if (form == SBD_FORM_FP32) {
+        auto* I = static_cast<const float2*>(in);
+        auto* O = static_cast<float2*>(out);
+        auto* Tm = static_cast<float2*>(tmp);
+        if (!(rc = fft_rows<float>(I, n1, n1, 0, Tm, n1, n1, 0, n0, n1, sign, nullptr, nullptr, nullptr, nullptr, s)) &&
+            !(rc = transpose<float>(Tm, n1, 0, O, n0, 0, n0, n1, 1, s)) &&
+            !(rc = fft_rows<float>(O, n0, n0, 0, Tm, n0, n0, 0, n1, n0, sign, nullptr, nullptr, nullptr, nullptr, s)))
+            rc = transpose<float>(Tm, n0, 0, O, n1, 0, n1, n0, 1, s);
+    } else {
+        auto* I = static_cast<const double2*>(in);
+        auto* O = static_cast<double2*>(out);
+        auto* Tm = static_cast<double2*>(tmp);
+        if (!(rc = fft_rows<double>(I, n1, n1, 0, Tm, n1, n1, 0, n0, n1, sign, nullptr, nullptr, nullptr, nullptr, s)) &&
+            !(rc = transpose<double>(Tm, n1, 0, O, n0, 0, n0, n1, 1, s)) &&
+            !(rc = fft_rows<double>(O, n0, n0, 0, Tm, n0, n0, 0, n1, n0, sign, nullptr, nullptr, nullptr, nullptr, s)))
+            rc = transpose<double>(Tm, n0, 0, O, n1, 0, n1, n0, 1, s);
+    }
+    cudaFreeAsync(tmp, s);
+    return rc;
+}
+
+}  // extern "C"

@@ -78,6 +78,55 @@ void small_jy(double x, double& j0, double& j1, double& y0, double& y1) {
     y1 = -(2.0 / (kPi * x)) * J[0] + (2.0 / kPi) * L * J[1] + (2.0 / kPi) * s1;
 }
 
+// Piecewise Chebyshev tables of J0 and J1 on [0, 20): 80 pieces of width 1/4,
+// 16 coefficients each, interpolated at Chebyshev points from the trapezoid values.
+constexpr int kPieces = 80, kDeg = 16;
+constexpr double kWidth = 0.25;
+struct JTables {
+    double c0[kPieces][kDeg];
+    double c1[kPieces][kDeg];
+    JTables() {
+        std::vector<double> J;
+        for (int q = 0; q < kPieces; ++q) {
+            double f0[kDeg], f1[kDeg];
+            for (int k = 0; k < kDeg; ++k) {
+                const double t = std::cos(kPi * (k + 0.5) / kDeg);
+                const double x = (q + 0.5 * (t + 1.0)) * kWidth;
+                jn_all_trapezoid(x, 1, J);
+                f0[k] = J[0];
+                f1[k] = J[1];
+            }
+            for (int j = 0; j < kDeg; ++j) {
+                double s0 = 0.0, s1 = 0.0;
+                for (int k = 0; k < kDeg; ++k) {
+                    const double c = std::cos(kPi * j * (k + 0.5) / kDeg);
+                    s0 += f0[k] * c;
+                    s1 += f1[k] * c;
+                }
+                c0[q][j] = s0 * (j == 0 ? 1.0 : 2.0) / kDeg;
+                c1[q][j] = s1 * (j == 0 ? 1.0 : 2.0) / kDeg;
+            }
+        }
+    }
+};
+
+const JTables& tables() {
+    static const JTables t;   // thread-safe one-time initialisation
+    return t;
+}
+
+double cheb_eval(const double* c, double x) {
+    const int q = std::min(kPieces - 1, static_cast<int>(x / kWidth));
+    const double t = 2.0 * (x / kWidth - q) - 1.0;
+    double b1 = 0.0, b2 = 0.0;
+    for (int j = kDeg - 1; j >= 1; --j) {
+        const double b0 = 2.0 * t * b1 - b2 + c[q * kDeg + j];
+        b2 = b1;
+        b1 = b0;
+    }
+    return t * b1 - b2 + c[q * kDeg];
+}
+
 }  // namespace
 
 double bessel_jn_small(int n, double x) {
@@ -86,13 +135,22 @@ double bessel_jn_small(int n, double x) {
     return J[n];
 }
 
+// Power series of J0, J1 for x < 2, where the terms decrease from the first one.
+double series_j(int nu, double x) {
+    const double q = -0.25 * x * x;
+    double term = nu == 0 ? 1.0 : 0.5 * x, sum = term;
+    for (int k = 1; k < 40; ++k) {
+        term *= q / (k * (k + nu));
+        sum += term;
+        if (std::fabs(term) < 1e-18 * std::fabs(sum)) break;
+    }
+    return sum;
+}
+
 double bessel_j0(double x) {
     x = std::fabs(x);
-    if (x < 20.0) {
-        std::vector<double> J;
-        jn_all_trapezoid(x, 0, J);
-        return J[0];
-    }
+    if (x < 2.0) return series_j(0, x);
+    if (x < 20.0) return cheb_eval(&tables().c0[0][0], x);
     double J, Y;
     hankel_asymptotic(0, x, J, Y);
     return J;
@@ -101,14 +159,23 @@ double bessel_j0(double x) {
 double bessel_j1(double x) {
     const double sg = x < 0 ? -1.0 : 1.0;
     x = std::fabs(x);
-    if (x < 20.0) {
-        std::vector<double> J;
-        jn_all_trapezoid(x, 1, J);
-        return sg * J[1];
-    }
+    if (x < 2.0) return sg * series_j(1, x);
+    if (x < 20.0) return sg * cheb_eval(&tables().c1[0][0], x);
     double J, Y;
     hankel_asymptotic(1, x, J, Y);
     return sg * J;
+}
+
+double bessel_y0_regular(double x) {
+    if (x < 20.0) {
+        const int nmax = static_cast<int>(std::ceil(x)) + 48;
+        std::vector<double> J;
+        jn_all_trapezoid(x, nmax, J);
+        double s0 = 0.0;
+        for (int k = 1; 2 * k <= nmax; ++k) s0 += ((k & 1) ? -1.0 : 1.0) * J[2 * k] / k;
+        return (2.0 / kPi) * kEulerGamma * J[0] - (4.0 / kPi) * s0;
+    }
+    return bessel_y0(x) - (2.0 / kPi) * std::log(0.5 * x) * bessel_j0(x);
 }
 
 double bessel_y0(double x) {

@@ -20,6 +20,8 @@ double bessel_j0(double x);
 double bessel_j1(double x);
 double bessel_y0(double x);
 double bessel_y1(double x);
+// Y0(x) - (2/pi) log(x/2) J0(x): the part of Y0 that is smooth at 0 (no cancellation).
+double bessel_y0_regular(double x);
 // J_n(x) for 0 <= n, small x (< 64) by the trapezoid rule.
 double bessel_jn_small(int n, double x);
 // J_M(x) for M in [m_lo, m_hi] (m_lo >= x - 1 allowed), into out[M - m_lo].

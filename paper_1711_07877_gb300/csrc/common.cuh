@@ -1,0 +1,51 @@
+// Shared device helpers: complex arithmetic over float / double, error plumbing.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+namespace sbd {
+
+template <typename T> struct Cx;
+template <> struct Cx<float>  { using type = float2; };
+template <> struct Cx<double> { using type = double2; };
+template <typename T> using cx_t = typename Cx<T>::type;
+
+template <typename T> __host__ __device__ __forceinline__ cx_t<T> mk(T re, T im) {
+    cx_t<T> v; v.x = re; v.y = im; return v;
+}
+template <typename C> __host__ __device__ __forceinline__ C cadd(C a, C b) { a.x += b.x; a.y += b.y; return a; }
+template <typename C> __host__ __device__ __forceinline__ C csub(C a, C b) { a.x -= b.x; a.y -= b.y; return a; }
+template <typename C> __host__ __device__ __forceinline__ C cmul(C a, C b) {
+    C r; r.x = a.x * b.x - a.y * b.y; r.y = a.x * b.y + a.y * b.x; return r;
+}
+// a * conj(b) when conj_b, else a * b
+template <typename C> __host__ __device__ __forceinline__ C cmul_dir(C a, C b, bool conj_b) {
+    if (conj_b) b.y = -b.y;
+    return cmul(a, b);
+}
+template <typename C, typename T> __host__ __device__ __forceinline__ C cscale(C a, T s) { a.x *= s; a.y *= s; return a; }
+
+// Thread-local detail text of the last error (sbd_last_error_message).
+void set_error(const std::string& msg);
+
+}  // namespace sbd
+
+#define SBD_CUDA_TRY(call)                                                        \
+    do {                                                                          \
+        cudaError_t e_ = (call);                                                  \
+        if (e_ != cudaSuccess) {                                                  \
+            ::sbd::set_error(std::string(#call) + ": " + cudaGetErrorString(e_)); \
+            return e_ == cudaErrorMemoryAllocation ? SBD_ENOMEM : SBD_ECUDA;      \
+        }                                                                         \
+    } while (0)
+
+#define SBD_LAUNCH_CHECK()                                                        \
+    do {                                                                          \
+        cudaError_t e_ = cudaGetLastError();                                      \
+        if (e_ != cudaSuccess) {                                                  \
+            ::sbd::set_error(std::string("kernel launch: ") + cudaGetErrorString(e_)); \
+            return SBD_ECUDA;                                                     \
+        }                                                                         \
+    } while (0)

@@ -1,0 +1,320 @@
+// Far-part kernels: type-3 transform by Gaussian gridding (first version: one
+// thread per point / node, accumulation by global atomics).
+#include "far.cuh"
+#include "sbd.h"
+
+namespace sbd {
+
+namespace {
+
+template <typename T> __device__ __forceinline__ T dexp(T x);
+template <> __device__ __forceinline__ float dexp<float>(float x) { return expf(x); }
+template <> __device__ __forceinline__ double dexp<double>(double x) { return exp(x); }
+
+template <typename T> __device__ __forceinline__ void atomic_add_cx(cx_t<T>* p, cx_t<T> v) {
+    atomicAdd(&p->x, v.x);
+    atomicAdd(&p->y, v.y);
+}
+
+template <typename T> __device__ __forceinline__ cx_t<T> load_f(const void* f, bool fc, long idx) {
+    if (fc) {
+        const double2 v = static_cast<const double2*>(f)[idx];
+        return mk<T>(static_cast<T>(v.x), static_cast<T>(v.y));
+    }
+    return mk<T>(static_cast<T>(static_cast<const double*>(f)[idx]), static_cast<T>(0));
+}
+
+template <typename T, int PMAX>
+__device__ __forceinline__ void weights(T frac, int P, T beta, T* w) {
+#pragma unroll
+    for (int a = 0; a < PMAX; ++a) {
+        if (a < P) {
+            const T d = static_cast<T>(a - P / 2 + 1) - frac;
+            w[a] = dexp<T>(-beta * d * d);
+        }
+    }
+}
+
+template <typename T>
+__global__ void prepare_points_kernel(const double* __restrict__ z, long n, double cx, double cy, double h,
+                                      int m, int P, PointRec<T>* __restrict__ out) {
+    const long i = blockIdx.x * static_cast<long>(blockDim.x) + threadIdx.x;
+    if (i >= n) return;
+    const double ux = (z[2 * i] - cx) / h + 0.5 * m;
+    const double uy = (z[2 * i + 1] - cy) / h + 0.5 * m;
+    const double fx = floor(ux), fy = floor(uy);
+    PointRec<T> r;
+    r.cell = make_int2(static_cast<int>(fx) - P / 2 + 1, static_cast<int>(fy) - P / 2 + 1);
+    r.frac = mk<T>(static_cast<T>(ux - fx), static_cast<T>(uy - fy));
+    out[i] = r;
+}
+
+template <typename T>
+__global__ void prepare_nodes_kernel(const int* __restrict__ start, const double* __restrict__ radius,
+                                     const int* __restrict__ M, int n_circles, long n_xi, double deta,
+                                     int nk, int P, NodeRec<T>* __restrict__ out) {
+    const long nu = blockIdx.x * static_cast<long>(blockDim.x) + threadIdx.x;
+    if (nu >= n_xi) return;
+    int lo = 0, hi = n_circles;   // start[lo] <= nu < start[hi]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) / 2;
+        if (start[mid] <= nu) lo = mid; else hi = mid;
+    }
+    const int c = lo;
+    const long mm = nu - start[c];
+    double sn, cs;
+    sincospi(2.0 * static_cast<double>(mm) / M[c], &sn, &cs);   // xi_m = r (cos 2pi m/M, sin 2pi m/M)
+    const double kx = radius[c] * cs / deta + 0.5 * nk;
+    const double ky = radius[c] * sn / deta + 0.5 * nk;
+    const double fx = floor(kx), fy = floor(ky);
+    NodeRec<T> r;
+    r.cell = make_int2(static_cast<int>(fx) - P / 2 + 1, static_cast<int>(fy) - P / 2 + 1);
+    r.frac = mk<T>(static_cast<T>(kx - fx), static_cast<T>(ky - fy));
+    r.circle = c;
+    r.pad = 0;
+    out[nu] = r;
+}
+
+template <typename T, int PMAX>
+__global__ void spread_kernel(const PointRec<T>* __restrict__ pts, long n, const void* __restrict__ f, bool fc,
+                              int nrhs, FarGeom g, cx_t<T>* __restrict__ grid) {
+    const long i = blockIdx.x * static_cast<long>(blockDim.x) + threadIdx.x;
+    if (i >= n) return;
+    const PointRec<T> p = pts[i];
+    T wx[PMAX], wy[PMAX];
+    weights<T, PMAX>(p.frac.x, g.P, static_cast<T>(g.beta_s), wx);
+    weights<T, PMAX>(p.frac.y, g.P, static_cast<T>(g.beta_s), wy);
+    const long mm = static_cast<long>(g.m) * g.m;
+    for (int r = 0; r < nrhs; ++r) {
+        const cx_t<T> fv = load_f<T>(f, fc, r * n + i);
+        cx_t<T>* base = grid + r * mm;
+        for (int b = 0; b < g.P; ++b) {
+            const cx_t<T> vy = cscale(fv, wy[b]);
+            cx_t<T>* row = base + static_cast<long>(p.cell.y + b) * g.m + p.cell.x;
+            for (int a = 0; a < g.P; ++a) atomic_add_cx<T>(row + a, cscale(vy, wx[a]));
+        }
+    }
+}
+
+template <typename T, int PMAX>
+__global__ void node_step_kernel(const NodeRec<T>* __restrict__ nodes, long n_xi, const cx_t<T>* __restrict__ omega,
+                                 int nrhs, FarGeom g, const cx_t<T>* __restrict__ kin, cx_t<T>* __restrict__ kout) {
+    const long nu = blockIdx.x * static_cast<long>(blockDim.x) + threadIdx.x;
+    if (nu >= n_xi) return;
+    const NodeRec<T> q = nodes[nu];
+    T wx[PMAX], wy[PMAX];
+    weights<T, PMAX>(q.frac.x, g.P, static_cast<T>(g.beta_k), wx);
+    weights<T, PMAX>(q.frac.y, g.P, static_cast<T>(g.beta_k), wy);
+    const cx_t<T> om = omega[q.circle];
+    const long kk = static_cast<long>(g.nk) * g.nk;
+    for (int r = 0; r < nrhs; ++r) {
+        const cx_t<T>* src = kin + r * kk;
+        cx_t<T> acc = mk<T>(0, 0);
+        for (int a = 0; a < g.P; ++a) {
+            const cx_t<T>* row = src + static_cast<long>(q.cell.x + a) * g.nk + q.cell.y;
+            cx_t<T> s = mk<T>(0, 0);
+            for (int b = 0; b < g.P; ++b) s = cadd(s, cscale(row[b], wy[b]));
+            acc = cadd(acc, cscale(s, wx[a]));
+        }
+        acc = cmul(acc, om);
+        cx_t<T>* dst = kout + r * kk;
+        for (int a = 0; a < g.P; ++a) {
+            const cx_t<T> va = cscale(acc, wx[a]);
+            cx_t<T>* row = dst + static_cast<long>(q.cell.x + a) * g.nk + q.cell.y;
+            for (int b = 0; b < g.P; ++b) atomic_add_cx<T>(row + b, cscale(va, wy[b]));
+        }
+    }
+}
+
+template <typename T, int PMAX>
+__global__ void node_gather_kernel(const NodeRec<T>* __restrict__ nodes, long n_xi, const T* __restrict__ cs,
+                                   FarGeom g, const cx_t<T>* __restrict__ kin, double2* __restrict__ out) {
+    const long nu = blockIdx.x * static_cast<long>(blockDim.x) + threadIdx.x;
+    if (nu >= n_xi) return;
+    const NodeRec<T> q = nodes[nu];
+    T wx[PMAX], wy[PMAX];
+    weights<T, PMAX>(q.frac.x, g.P, static_cast<T>(g.beta_k), wx);
+    weights<T, PMAX>(q.frac.y, g.P, static_cast<T>(g.beta_k), wy);
+    cx_t<T> acc = mk<T>(0, 0);
+    for (int a = 0; a < g.P; ++a) {
+        const cx_t<T>* row = kin + static_cast<long>(q.cell.x + a) * g.nk + q.cell.y;
+        cx_t<T> s = mk<T>(0, 0);
+        for (int b = 0; b < g.P; ++b) s = cadd(s, cscale(row[b], wy[b]));
+        acc = cadd(acc, cscale(s, wx[a]));
+    }
+    acc = cscale(acc, cs[q.circle]);
+    out[nu] = make_double2(acc.x, acc.y);
+}
+
+template <typename T, int PMAX>
+__global__ void node_scatter_kernel(const NodeRec<T>* __restrict__ nodes, long n_xi, const T* __restrict__ cs,
+                                    FarGeom g, const double2* __restrict__ in, cx_t<T>* __restrict__ kout) {
+    const long nu = blockIdx.x * static_cast<long>(blockDim.x) + threadIdx.x;
+    if (nu >= n_xi) return;
+    const NodeRec<T> q = nodes[nu];
+    T wx[PMAX], wy[PMAX];
+    weights<T, PMAX>(q.frac.x, g.P, static_cast<T>(g.beta_k), wx);
+    weights<T, PMAX>(q.frac.y, g.P, static_cast<T>(g.beta_k), wy);
+    const double2 v = in[nu];
+    const cx_t<T> acc = cscale(mk<T>(static_cast<T>(v.x), static_cast<T>(v.y)), cs[q.circle]);
+    for (int a = 0; a < g.P; ++a) {
+        const cx_t<T> va = cscale(acc, wx[a]);
+        cx_t<T>* row = kout + static_cast<long>(q.cell.x + a) * g.nk + q.cell.y;
+        for (int b = 0; b < g.P; ++b) atomic_add_cx<T>(row + b, cscale(va, wy[b]));
+    }
+}
+
+template <typename T, int PMAX>
+__global__ void interp_kernel(const PointRec<T>* __restrict__ pts, long n, int nrhs, FarGeom g,
+                              const cx_t<T>* __restrict__ grid, double2 w0, const double2* __restrict__ sumf,
+                              void* __restrict__ q, bool qc) {
+    const long i = blockIdx.x * static_cast<long>(blockDim.x) + threadIdx.x;
+    if (i >= n) return;
+    const PointRec<T> p = pts[i];
+    T wx[PMAX], wy[PMAX];
+    weights<T, PMAX>(p.frac.x, g.P, static_cast<T>(g.beta_s), wx);
+    weights<T, PMAX>(p.frac.y, g.P, static_cast<T>(g.beta_s), wy);
+    const long mm = static_cast<long>(g.m) * g.m;
+    for (int r = 0; r < nrhs; ++r) {
+        const cx_t<T>* base = grid + r * mm;
+        double ar = 0.0, ai = 0.0;
+        for (int b = 0; b < g.P; ++b) {
+            const cx_t<T>* row = base + static_cast<long>(p.cell.y + b) * g.m + p.cell.x;
+            cx_t<T> s = mk<T>(0, 0);
+            for (int a = 0; a < g.P; ++a) s = cadd(s, cscale(row[a], wx[a]));
+            ar += static_cast<double>(s.x) * wy[b];
+            ai += static_cast<double>(s.y) * wy[b];
+        }
+        const double2 sf = sumf[r];
+        ar += w0.x * sf.x - w0.y * sf.y;
+        ai += w0.x * sf.y + w0.y * sf.x;
+        if (qc) static_cast<double2*>(q)[r * n + i] = make_double2(ar, ai);
+        else static_cast<double*>(q)[r * n + i] = ar;
+    }
+}
+
+__global__ void sum_kernel(const void* __restrict__ f, bool fc, long n, double2* __restrict__ sumf) {
+    const int r = blockIdx.y;
+    double sr = 0.0, si = 0.0;
+    for (long i = blockIdx.x * static_cast<long>(blockDim.x) + threadIdx.x; i < n;
+         i += static_cast<long>(gridDim.x) * blockDim.x) {
+        if (fc) {
+            const double2 v = static_cast<const double2*>(f)[r * n + i];
+            sr += v.x;
+            si += v.y;
+        } else {
+            sr += static_cast<const double*>(f)[r * n + i];
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        sr += __shfl_down_sync(0xffffffffu, sr, o);
+        si += __shfl_down_sync(0xffffffffu, si, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(&sumf[r].x, sr);
+        atomicAdd(&sumf[r].y, si);
+    }
+}
+
+constexpr int kThreads = 256;
+inline unsigned blocks_for(long n) { return static_cast<unsigned>((n + kThreads - 1) / kThreads); }
+
+}  // namespace
+
+template <typename T>
+int far_prepare_points(const double* z, long n, double cx, double cy, double h, int m, int P,
+                       PointRec<T>* out, cudaStream_t s) {
+    if (n <= 0) return SBD_OK;
+    prepare_points_kernel<T><<<blocks_for(n), kThreads, 0, s>>>(z, n, cx, cy, h, m, P, out);
+    SBD_LAUNCH_CHECK();
+    return SBD_OK;
+}
+
+template <typename T>
+int far_prepare_nodes(const int* circle_start, const double* radius, const int* M, int n_circles,
+                      long n_xi, double deta, int nk, int P, NodeRec<T>* out, cudaStream_t s) {
+    if (n_xi <= 0) return SBD_OK;
+    prepare_nodes_kernel<T><<<blocks_for(n_xi), kThreads, 0, s>>>(circle_start, radius, M, n_circles, n_xi,
+                                                                   deta, nk, P, out);
+    SBD_LAUNCH_CHECK();
+    return SBD_OK;
+}
+
+template <typename T> constexpr int pmax() { return sizeof(T) == 8 ? 32 : 16; }
+
+template <typename T>
+int far_spread(const PointRec<T>* pts, long n, const void* f, bool f_complex, int nrhs,
+               const FarGeom& g, cx_t<T>* grid, cudaStream_t s) {
+    SBD_CUDA_TRY(cudaMemsetAsync(grid, 0, sizeof(cx_t<T>) * static_cast<size_t>(g.m) * g.m * nrhs, s));
+    if (n <= 0) return SBD_OK;
+    spread_kernel<T, pmax<T>()><<<blocks_for(n), kThreads, 0, s>>>(pts, n, f, f_complex, nrhs, g, grid);
+    SBD_LAUNCH_CHECK();
+    return SBD_OK;
+}
+
+template <typename T>
+int far_node_step(const NodeRec<T>* nodes, long n_xi, const cx_t<T>* omega_c, int nrhs,
+                  const FarGeom& g, const cx_t<T>* kin, cx_t<T>* kout, cudaStream_t s) {
+    SBD_CUDA_TRY(cudaMemsetAsync(kout, 0, sizeof(cx_t<T>) * static_cast<size_t>(g.nk) * g.nk * nrhs, s));
+    if (n_xi <= 0) return SBD_OK;
+    node_step_kernel<T, pmax<T>()><<<blocks_for(n_xi), kThreads, 0, s>>>(nodes, n_xi, omega_c, nrhs, g, kin, kout);
+    SBD_LAUNCH_CHECK();
+    return SBD_OK;
+}
+
+template <typename T>
+int far_node_gather(const NodeRec<T>* nodes, long n_xi, const T* cscale_c, const FarGeom& g,
+                    const cx_t<T>* kin, double2* out, cudaStream_t s) {
+    if (n_xi <= 0) return SBD_OK;
+    node_gather_kernel<T, pmax<T>()><<<blocks_for(n_xi), kThreads, 0, s>>>(nodes, n_xi, cscale_c, g, kin, out);
+    SBD_LAUNCH_CHECK();
+    return SBD_OK;
+}
+
+template <typename T>
+int far_node_scatter(const NodeRec<T>* nodes, long n_xi, const T* cscale_c, const FarGeom& g,
+                     const double2* in, cx_t<T>* kout, cudaStream_t s) {
+    SBD_CUDA_TRY(cudaMemsetAsync(kout, 0, sizeof(cx_t<T>) * static_cast<size_t>(g.nk) * g.nk, s));
+    if (n_xi <= 0) return SBD_OK;
+    node_scatter_kernel<T, pmax<T>()><<<blocks_for(n_xi), kThreads, 0, s>>>(nodes, n_xi, cscale_c, g, in, kout);
+    SBD_LAUNCH_CHECK();
+    return SBD_OK;
+}
+
+template <typename T>
+int far_interp(const PointRec<T>* pts, long n, int nrhs, const FarGeom& g, const cx_t<T>* grid,
+               double2 w0, const double2* sumf, void* q, bool q_complex, cudaStream_t s) {
+    if (n <= 0) return SBD_OK;
+    interp_kernel<T, pmax<T>()><<<blocks_for(n), kThreads, 0, s>>>(pts, n, nrhs, g, grid, w0, sumf, q, q_complex);
+    SBD_LAUNCH_CHECK();
+    return SBD_OK;
+}
+
+int far_sum(const void* f, bool f_complex, long n, int nrhs, double2* sumf, cudaStream_t s) {
+    SBD_CUDA_TRY(cudaMemsetAsync(sumf, 0, sizeof(double2) * nrhs, s));
+    if (n <= 0) return SBD_OK;
+    const unsigned nb = static_cast<unsigned>(std::min<long>((n + 255) / 256, 1024));
+    sum_kernel<<<dim3(nb, nrhs), 256, 0, s>>>(f, f_complex, n, sumf);
+    SBD_LAUNCH_CHECK();
+    return SBD_OK;
+}
+
+#define SBD_FAR_INST(T)                                                                                   \
+    template int far_prepare_points<T>(const double*, long, double, double, double, int, int, PointRec<T>*,  \
+                                       cudaStream_t);                                                     \
+    template int far_prepare_nodes<T>(const int*, const double*, const int*, int, long, double, int, int, \
+                                      NodeRec<T>*, cudaStream_t);                                         \
+    template int far_spread<T>(const PointRec<T>*, long, const void*, bool, int, const FarGeom&, cx_t<T>*, \
+                               cudaStream_t);                                                             \
+    template int far_node_step<T>(const NodeRec<T>*, long, const cx_t<T>*, int, const FarGeom&,          \
+                                  const cx_t<T>*, cx_t<T>*, cudaStream_t);                                \
+    template int far_node_gather<T>(const NodeRec<T>*, long, const T*, const FarGeom&, const cx_t<T>*,    \
+                                    double2*, cudaStream_t);                                              \
+    template int far_node_scatter<T>(const NodeRec<T>*, long, const T*, const FarGeom&, const double2*,   \
+                                     cx_t<T>*, cudaStream_t);                                             \
+    template int far_interp<T>(const PointRec<T>*, long, int, const FarGeom&, const cx_t<T>*, double2,   \
+                               const double2*, void*, bool, cudaStream_t);
+SBD_FAR_INST(float)
+SBD_FAR_INST(double)
+
+}  // namespace sbd

@@ -1,0 +1,55 @@
+// Far part of the on-line SBD (Sec. 1 steps (i)-(iii), Eq. far convolution) by a
+// type-3 transform with Gaussian gridding on both sides.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace sbd {
+
+// Geometry of one transform, all in cells of the respective grid.
+struct FarGeom {
+    int P;            // stencil width (cells per dimension), even
+    int m;            // spreading grid side
+    int nk;           // frequency grid side
+    double beta_s;    // spreading weight exp(-beta_s d^2)
+    double beta_k;    // node weight exp(-beta_k d^2)
+};
+
+// Point i: spreading stencil starts at cell (cell.x, cell.y); frac = position - floor(position).
+template <typename T> struct PointRec { int2 cell; cx_t<T> frac; };
+// Node: stencil start cell in the frequency grid, fraction, circle index.
+template <typename T> struct NodeRec { int2 cell; cx_t<T> frac; int circle; int pad; };
+
+// Plan-time preparation (FP64 arithmetic).
+template <typename T>
+int far_prepare_points(const double* z, long n, double cx, double cy, double h, int m, int P,
+                       PointRec<T>* out, cudaStream_t s);
+template <typename T>
+int far_prepare_nodes(const int* circle_start, const double* radius, const int* M, int n_circles,
+                      long n_xi, double deta, int nk, int P, NodeRec<T>* out, cudaStream_t s);
+
+// f (complex128 or float64, nrhs x N) -> spreading grids (nrhs x m x m, zeroed here).
+template <typename T>
+int far_spread(const PointRec<T>* pts, long n, const void* f, bool f_complex, int nrhs,
+               const FarGeom& g, cx_t<T>* grid, cudaStream_t s);
+// Gather at every node, multiply by the circle weight, scatter into kout (zeroed here).
+template <typename T>
+int far_node_step(const NodeRec<T>* nodes, long n_xi, const cx_t<T>* omega_c, int nrhs,
+                  const FarGeom& g, const cx_t<T>* kin, cx_t<T>* kout, cudaStream_t s);
+// Gather only: out[nu] = c_nu * sum_stencil w K  (complex128), c = circle scale.
+template <typename T>
+int far_node_gather(const NodeRec<T>* nodes, long n_xi, const T* cscale, const FarGeom& g,
+                    const cx_t<T>* kin, double2* out, cudaStream_t s);
+// Scatter only: kout (zeroed here) += c_nu in[nu] w.
+template <typename T>
+int far_node_scatter(const NodeRec<T>* nodes, long n_xi, const T* cscale, const FarGeom& g,
+                     const double2* in, cx_t<T>* kout, cudaStream_t s);
+// Interpolate the grids at the points: q (nrhs x N) = interp + w0 * sumf[r]; real or complex out.
+template <typename T>
+int far_interp(const PointRec<T>* pts, long n, int nrhs, const FarGeom& g, const cx_t<T>* grid,
+               double2 w0, const double2* sumf, void* q, bool q_complex, cudaStream_t s);
+// sumf[r] = sum_l f[r][l] (FP64).
+int far_sum(const void* f, bool f_complex, long n, int nrhs, double2* sumf, cudaStream_t s);
+
+}  // namespace sbd

@@ -1,0 +1,43 @@
+// Hand-written FFT for sm_103a: batched 1-D complex transforms of contiguous rows,
+// each row held in shared memory for all its radix stages, plus a tiled transpose.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace sbd {
+
+constexpr int kFftMaxStages = 32;
+
+struct FftPlan1D {
+    int n = 0;
+    int nstages = 0;
+    int radix[kFftMaxStages];
+    int threads = 0;
+};
+
+// Radix schedule for n = 2^a 3^b 5^c (fours first); false when n has another factor.
+bool fft_make_plan(int n, FftPlan1D& p);
+
+// Largest row length a single CTA can hold in shared memory for this element type.
+int fft_max_row(bool fp64);
+
+// One batched row pass:
+//   out[r][e] = post_row[r] post_elem[e] *
+//               sum_t (pre_row[r] pre_elem[t] in[r][t]) exp(sign 2 pi i (t + in_shift)(e + out_shift) / n)
+// for e < out_len, t < in_len (input element t sits at FFT position (t + in_shift) mod n,
+// output element e is FFT position (e + out_shift) mod n).  Scale pointers may be null.
+template <typename T>
+int fft_rows(const cx_t<T>* in, long in_stride, int in_len, int in_shift,
+             cx_t<T>* out, long out_stride, int out_len, int out_shift,
+             int rows, int n, int sign,
+             const T* pre_elem, const T* pre_row, const T* post_elem, const T* post_row,
+             cudaStream_t stream);
+
+// out[c][r] = in[r][c] for a rows x cols matrix (row strides in elements), batched over nb
+// matrices spaced in_batch / out_batch elements apart.
+template <typename T>
+int transpose(const cx_t<T>* in, long in_stride, long in_batch, cx_t<T>* out, long out_stride,
+              long out_batch, int rows, int cols, int nb, cudaStream_t stream);
+
+}  // namespace sbd

@@ -1,0 +1,41 @@
+// Near field: fixed-radius neighbour search (Sec. 1 / Sec. 6.1) into CSR, the values
+// of the close-correction matrix D (Eq. defD) in FP64, and the SpMV q += D f.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace sbd {
+
+// Device-side description of D(y) = T1(t) log(t)/2 + T2(t) - sum_{c small} w_c sum_m e^{i y.xi_m},
+// t = |y|^2 (tables: piecewise Chebyshev in t, complex, [pieces][deg][2]).
+struct NearDev {
+    int pieces, deg;
+    double tmax;
+    const double* T1;
+    const double* T2;
+    int n_small;              // circles evaluated exactly
+    const double* small_xi;   // (sum over small circles of M) x 2 node coordinates
+    const int* small_start;   // n_small + 1 offsets into small_xi
+    const double* small_w;    // n_small complex weights (re, im)
+    double self_re, self_im;  // D_kk
+};
+
+// Bounding box (xmin, ymin, xmax, ymax) and max squared distance to a centre.
+int points_bbox(const double* z, long n, double* out4_host, cudaStream_t s);
+int points_max_dist2(const double* z, long n, double cx, double cy, double* out_host, cudaStream_t s);
+
+// Build CSR of D (diagonal first in every row).  Allocates rowptr/col/val with cudaMalloc.
+//   complex_vals: values are complex128 (Helmholtz) or float64 (Laplace).
+int near_build(const double* z, long n, double delta_min, double bx0, double by0, double bx1, double by1,
+               const NearDev& tab, bool complex_vals, long long** rowptr, int** col, void** val,
+               long long* nnz, long long* n_coincident, cudaStream_t s);
+
+// q[r] (+)= D f[r] for r < nrhs (q accumulated when accumulate, else overwritten).
+int near_spmv(const long long* rowptr, const int* col, const void* val, bool complex_vals, long n, int nrhs,
+              const void* f, void* q, bool accumulate, cudaStream_t s);
+
+// Exclusive scan of n 64-bit counts in place; total returned in *total (host), synchronising s.
+int scan_exclusive_i64(long long* data, long n, long long* total, cudaStream_t s);
+
+}  // namespace sbd

@@ -1,0 +1,500 @@
+// Off-line part on the host, FP64 (see offline.h).
+//
+// SBD fit (Sec. 3.1-3.2): the Gram matrix A^P of the quadratic form Q^P on the
+// annulus A(a) uses the explicit formulas of Sec. 3.2 (off-diagonal sign taken
+// so that A is the Gram matrix of the integral definition: denominator
+// rho_i^2 - rho_j^2); the right-hand side int grad g . grad e_p is in closed
+// form (Laplace: -2 pi C_p J0(rho_p a) since J0(rho_p) = 0; Y0: Lommel's
+// integral).  A is factored once by a blocked Cholesky at a size above the
+// expected P; the Gram matrix of any smaller P is its leading block, so every
+// trial P of the search (Sec. 1, dichotomy) reuses the same factor.
+#include "offline.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+
+#include "bessel.h"
+#include "sbd.h"
+
+namespace sbd {
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846;
+
+inline size_t tri(size_t i) { return i * (i + 1) / 2; }   // packed lower row start
+
+// Sample set of [a, 1] for the L_inf stopping test: 512 points a + d (i/511)^2,
+// d = min(1 - a, 30 a), and U = 256 + 4 ceil(extra/pi) uniform points.
+void fit_samples(double a, double extra, std::vector<double>& s) {
+    s.clear();
+    const double d = std::min(1.0 - a, 30.0 * a);
+    for (int i = 0; i < 512; ++i) {
+        const double t = i / 511.0;
+        s.push_back(a + d * t * t);
+    }
+    const int U = 256 + 4 * static_cast<int>(std::ceil(extra / kPi));
+    for (int j = 0; j < U; ++j) s.push_back(a + (1.0 - a) * j / (U - 1.0));
+}
+
+// Blocked right-looking Cholesky of a packed lower matrix, in place.  Returns the
+// number of leading rows factored (P on success; fewer when a pivot is not positive).
+int cholesky_packed(std::vector<double>& A, int P) {
+    const int nb = 64;
+    for (int k0 = 0; k0 < P; k0 += nb) {
+        const int kb = std::min(nb, P - k0);
+        for (int j = k0; j < k0 + kb; ++j) {
+            double d = A[tri(j) + j];
+            for (int t = k0; t < j; ++t) d -= A[tri(j) + t] * A[tri(j) + t];
+            if (!(d > 0.0)) return j;
+            d = std::sqrt(d);
+            A[tri(j) + j] = d;
+            for (int i = j + 1; i < k0 + kb; ++i) {
+                double s = A[tri(i) + j];
+                for (int t = k0; t < j; ++t) s -= A[tri(i) + t] * A[tri(j) + t];
+                A[tri(i) + j] = s / d;
+            }
+        }
+#pragma omp parallel for schedule(static)
+        for (int i = k0 + kb; i < P; ++i) {
+            double* ai = &A[tri(i)];
+            for (int j = k0; j < k0 + kb; ++j) {
+                const double* aj = &A[tri(j)];
+                double s = ai[j];
+                for (int t = k0; t < j; ++t) s -= ai[t] * aj[t];
+                ai[j] = s / aj[j];
+            }
+        }
+#pragma omp parallel for schedule(dynamic, 8)
+        for (int i = k0 + kb; i < P; ++i) {
+            double* ai = &A[tri(i)];
+            for (int j = k0 + kb; j <= i; ++j) {
+                const double* aj = &A[tri(j)];
+                double s = 0.0;
+#pragma omp simd reduction(+ : s)
+                for (int t = k0; t < k0 + kb; ++t) s += ai[t] * aj[t];
+                ai[j] -= s;
+            }
+        }
+    }
+    return P;
+}
+
+// Solve (L L^T) x = b with the leading P x P block of a packed factor.
+void chol_solve(const std::vector<double>& L, int P, const double* b, std::vector<double>& x) {
+    x.assign(b, b + P);
+    for (int i = 0; i < P; ++i) {
+        const double* li = &L[tri(i)];
+        double s = x[i];
+        for (int t = 0; t < i; ++t) s -= li[t] * x[t];
+        x[i] = s / li[i];
+    }
+    for (int i = P - 1; i >= 0; --i) {
+        const double* li = &L[tri(i)];
+        x[i] /= li[i];
+        const double xi = x[i];
+        for (int t = 0; t < i; ++t) x[t] -= li[t] * xi;
+    }
+}
+
+struct FitWork {
+    int kind;
+    double a, kp, extra;
+    int Pf = 0, Pok = 0;                 // factored size, usable leading size
+    std::vector<double> rho, C, b, L;
+    std::vector<double> s, gs;           // samples and g(s)
+    std::vector<double> Jmat;            // [sample][p] = J0(rho_p s)
+};
+
+void build_fit(FitWork& w, int Pf) {
+    w.Pf = Pf;
+    w.rho.resize(Pf);
+    w.C.resize(Pf);
+    w.b.resize(Pf);
+    std::vector<double> j0a(Pf), j1a(Pf);
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int p = 0; p < Pf; ++p) {
+        const double r = j0_root(p + 1);
+        w.rho[p] = r;
+        w.C[p] = 1.0 / (std::sqrt(kPi) * r * std::fabs(bessel_j1(r)));
+        j0a[p] = bessel_j0(r * w.a);
+        j1a[p] = bessel_j1(r * w.a);
+        if (w.kind == 0) {
+            w.b[p] = -2.0 * kPi * w.C[p] * j0a[p];
+        } else {
+            const double kp = w.kp, a = w.a;
+            const double F = a * (r * bessel_y1(kp * a) * j0a[p] - kp * bessel_y0(kp * a) * j1a[p]) /
+                             (kp * kp - r * r);
+            w.b[p] = -2.0 * kPi * w.C[p] * r * kp * F;
+        }
+    }
+    // Gram matrix A_ij = int_{A(a)} grad e_i . grad e_j (Sec. 3.2), packed lower
+    w.L.assign(tri(Pf), 0.0);
+    const double a = w.a;
+#pragma omp parallel for schedule(dynamic, 32)
+    for (int i = 0; i < Pf; ++i) {
+        const double ri = w.rho[i];
+        double* row = &w.L[tri(i)];
+        for (int j = 0; j < i; ++j) {
+            const double rj = w.rho[j];
+            row[j] = 2.0 * kPi * w.C[i] * w.C[j] * ri * rj * a / (ri * ri - rj * rj) *
+                     (ri * j0a[i] * j1a[j] - rj * j0a[j] * j1a[i]);
+        }
+        // diagonal: 2 pi C_i^2 (F_i(1) - F_i(a)), F_i(1) = rho_i^2 J1(rho_i)^2 / 2
+        const double x = ri * a;
+        const double Fa = x * x * 0.5 * (j0a[i] * j0a[i] + j1a[i] * j1a[i]) - x * j0a[i] * j1a[i];
+        row[i] = 1.0 - 2.0 * kPi * w.C[i] * w.C[i] * Fa;
+    }
+    w.Pok = cholesky_packed(w.L, Pf);
+    // J0(rho_p s) for every sample and p < Pf
+    const int ns = static_cast<int>(w.s.size());
+    w.Jmat.assign(static_cast<size_t>(ns) * Pf, 0.0);
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int i = 0; i < ns; ++i) {
+        double* Ji = &w.Jmat[static_cast<size_t>(i) * Pf];
+        for (int p = 0; p < Pf; ++p) Ji[p] = bessel_j0(w.rho[p] * w.s[i]);
+    }
+}
+
+double fit_error(const FitWork& w, int P, std::vector<double>& alpha) {
+    chol_solve(w.L, P, w.b.data(), alpha);
+    const int ns = static_cast<int>(w.s.size());
+    double err = 0.0;
+#pragma omp parallel for reduction(max : err)
+    for (int i = 0; i < ns; ++i) {
+        const double* Ji = &w.Jmat[static_cast<size_t>(i) * w.Pf];
+        double v = 0.0;
+        for (int p = 0; p < P; ++p) v += alpha[p] * w.C[p] * Ji[p];
+        err = std::max(err, std::fabs(w.gs[i] - v));
+    }
+    return err;
+}
+
+// 2 sum_{j=1..4} |J_{jM}(r)|, with the j >= 2 terms kept only where they can matter (r < 20).
+int circle_size(double r, double weight, double tol) {
+    int M0 = std::max(2, 2 * static_cast<int>(std::ceil(0.5 * r)));
+    if (weight == 0.0) return M0;
+    int span = 64 + static_cast<int>(24.0 * std::cbrt(r + 1.0));
+    for (;;) {
+        std::vector<double> J;
+        bessel_jn_range(r, M0, M0 + span, J);
+        for (int M = M0; M <= M0 + span; M += 2) {
+            double bound = std::fabs(J[M - M0]);
+            if (r < 20.0)
+                for (int j = 2; j <= 4; ++j) bound += std::fabs(bessel_jn_small(j * M, r));
+            if (2.0 * bound * weight <= tol) return M;
+        }
+        M0 += span + 1;
+        M0 += M0 & 1;
+        span *= 2;
+    }
+}
+
+}  // namespace
+
+int good_fft_size(int n) {
+    n = std::max(n, 2);
+    for (int c = n + (n & 1);; c += 2) {
+        int v = c;
+        for (int f : {2, 3, 5})
+            while (v % f == 0) v /= f;
+        if (v == 1) return c;
+    }
+}
+
+int offline_fit(int kind, double kappa, double delta_min, double delta_max, double eps,
+                int fixed_P, SbdFit& out, std::string& err) {
+    if (!(delta_max > 0.0) || !(delta_min > 0.0) || !(delta_min < delta_max)) {
+        err = "need 0 < delta_min < delta_max";
+        return SBD_EINVAL;
+    }
+    if (!(eps >= 1e-10 && eps <= 0.1)) {
+        err = "eps must lie in [1e-10, 0.1]";
+        return SBD_EINVAL;
+    }
+    if (kind != 0 && kind != 1) {
+        err = "unknown kernel kind";
+        return SBD_EINVAL;
+    }
+    if (kind == 1 && !(kappa > 0.0)) {
+        err = "Helmholtz kernel needs kappa > 0";
+        return SBD_EINVAL;
+    }
+    SbdFit f;
+    f.kind = kind;
+    f.kappa = kappa;
+    f.eps = eps;
+    f.delta_min = delta_min;
+    f.delta_max = delta_max;
+    FitWork w;
+    w.kind = kind;
+    if (kind == 0) {
+        // -log(r)/(2 pi) = -(1/2pi) [log delta_max + log(r / delta_max)]  (Sec. 4.1)
+        f.scale_R = delta_max;
+        f.gscale = -1.0 / (2.0 * kPi);
+        f.w0 = -std::log(delta_max) / (2.0 * kPi);
+        w.extra = 0.0;
+        w.kp = 0.0;
+    } else {
+        // (i/4) H0(kappa r) = (i/4) J0 - (1/4) Y0; Y0(kappa r) = Y0(k' r / R), R = k'/kappa  (Sec. 4.2)
+        f.kprime = y0_first_root_at_least(kappa * delta_max);
+        f.scale_R = f.kprime / kappa;
+        f.gscale = -0.25;
+        f.w0 = 0.0;
+        w.extra = 2.0 * f.kprime;
+        w.kp = f.kprime;
+    }
+    f.a = delta_min / f.scale_R;
+    w.a = f.a;
+    const double tol_g = (eps / 3.0) / std::fabs(f.gscale);
+    fit_samples(f.a, w.extra, w.s);
+    w.gs.resize(w.s.size());
+    for (size_t i = 0; i < w.s.size(); ++i)
+        w.gs[i] = kind == 0 ? std::log(w.s[i]) : bessel_y0(w.kp * w.s[i]);
+
+    std::vector<double> alpha;
+    int P;
+    double e;
+    if (fixed_P > 0) {
+        build_fit(w, fixed_P);
+        if (w.Pok < fixed_P) {
+            err = "Gram matrix not numerically positive definite at this P (conditioning floor, Sec. 3.3)";
+            return SBD_EFIT;
+        }
+        P = fixed_P;
+        e = fit_error(w, P, alpha);
+    } else {
+        const double gamma = std::max(0.5, (-std::log10(tol_g) - 0.5) / 1.5);
+        const int P_start = std::max(2, static_cast<int>(std::ceil(gamma / f.a)) +
+                                            static_cast<int>(std::ceil(w.extra / (2.0 * kPi))));
+        const int P_max = 20000;
+        build_fit(w, std::min(P_max, static_cast<int>(std::ceil(1.25 * P_start)) + 8));
+        std::vector<std::pair<int, double>> cache;
+        auto err_of = [&](int Pq) -> double {
+            for (auto& c : cache)
+                if (c.first == Pq) return c.second;
+            if (Pq > w.Pok) {
+                if (w.Pok < w.Pf) return 1e300;   // beyond the conditioning floor
+                build_fit(w, std::min(P_max, static_cast<int>(std::ceil(1.25 * Pq)) + 8));
+                cache.clear();
+                if (Pq > w.Pok) return 1e300;
+            }
+            std::vector<double> al;
+            const double v = fit_error(w, Pq, al);
+            cache.emplace_back(Pq, v);
+            return v;
+        };
+        int lo, hi;
+        int Pc = std::max(1, P_start);
+        if (err_of(Pc) > tol_g) {
+            lo = Pc;
+            hi = static_cast<int>(std::ceil(Pc * 1.1));
+            while (err_of(hi) > tol_g) {
+                if (hi >= P_max || (w.Pok < w.Pf && hi > w.Pok)) {
+                    err = "the SBD fit does not reach the tolerance (conditioning floor ~1e-10, Sec. 4.1)";
+                    return SBD_EFIT;
+                }
+                lo = hi;
+                hi = std::min(P_max, static_cast<int>(std::ceil(hi * 1.1)));
+            }
+        } else {
+            hi = Pc;
+            lo = static_cast<int>(std::floor(Pc * 0.9));
+            while (lo >= 1 && err_of(lo) <= tol_g) {
+                hi = lo;
+                lo = static_cast<int>(std::floor(lo * 0.9));
+            }
+            lo = std::max(lo, 0);
+        }
+        const int res = std::max(1, hi / 128);
+        while (hi - lo > res) {
+            const int mid = (lo + hi) / 2;
+            if (mid >= 1 && err_of(mid) <= tol_g) hi = mid;
+            else lo = mid;
+        }
+        P = hi;
+        e = fit_error(w, P, alpha);
+    }
+    f.P = P;
+    f.rho.assign(w.rho.begin(), w.rho.begin() + P);
+    f.C.assign(w.C.begin(), w.C.begin() + P);
+    f.alpha = alpha;
+    f.coef.resize(P);
+    for (int p = 0; p < P; ++p) f.coef[p] = f.gscale * alpha[p] * f.C[p];
+    f.fit_err_g = e;
+    f.fit_err = e * std::fabs(f.gscale);
+    // circular quadrature sizes (Sec. 5) and weights omega_hat = alpha_p C_p / M_p (Sec. 6.2)
+    f.n_circles = P + (kind == 1 ? 1 : 0);
+    const double tol_c = (eps / 3.0) / f.n_circles;
+    f.M.assign(f.n_circles, 0);
+    f.radius.assign(f.n_circles, 0.0);
+    f.weight.assign(f.n_circles, 0.0);
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int p = 0; p < P; ++p) {
+        f.M[p] = circle_size(f.rho[p], std::fabs(f.coef[p]), tol_c);
+        f.radius[p] = f.rho[p] / f.scale_R;
+        f.weight[p] = f.coef[p] / f.M[p];
+    }
+    if (kind == 1) {
+        const double kd = kappa * delta_max;
+        const int Mj = circle_size(kd, 0.25, tol_c);
+        f.M[P] = Mj;
+        f.radius[P] = kappa;
+        f.weight[P] = cplx(0.0, 0.25 / Mj);
+    }
+    f.n_xi = 0;
+    for (int c = 0; c < f.n_circles; ++c) f.n_xi += f.M[c];
+    out = std::move(f);
+    return SBD_OK;
+}
+
+int nufft_params(const SbdFit& fit, double half_extent, double cx, double cy, double tol,
+                 bool fp32, NufftParams& o, std::string& err) {
+    double S = 0.0;
+    for (int c = 0; c < fit.n_circles; ++c) S = std::max(S, fit.radius[c]);
+    if (!(S > 0.0) || !(half_extent > 0.0)) {
+        err = "degenerate geometry for the transform";
+        return SBD_EINVAL;
+    }
+    if (fp32) tol = std::max(tol, 3e-7);
+    tol = std::max(tol, 1e-15);
+    // error per transform ~ 0.1 exp(-pi P / 3) at two-fold oversampling on both sides
+    int P = static_cast<int>(std::ceil((3.0 / kPi) * std::log(0.1 / tol)));
+    P = std::max(4, std::min(fp32 ? 16 : 32, P + (P & 1)));
+    o.Ps = o.Pk = P;
+    o.tol = tol;
+    const double u = P * kPi / 24.0;   // balanced truncation / aliasing at two-fold oversampling
+    o.h = kPi / (2.0 * S);
+    o.tau = u / (S * S);
+    o.m = good_fft_size(static_cast<int>(std::ceil(2.0 * half_extent / o.h)) + P + 4);
+    o.n = 2 * o.m;
+    o.nk = o.m + P + 4;
+    const double Xg = 0.5 * o.m * o.h;
+    o.sigma = u / (Xg * Xg);
+    o.deta = 2.0 * kPi / (o.n * o.h);
+    o.beta_s = o.h * o.h / (4.0 * o.tau);
+    o.beta_k = o.deta * o.deta / (4.0 * o.sigma);
+    o.cx = cx;
+    o.cy = cy;
+    o.dec.resize(o.m);
+    for (int i = 0; i < o.m; ++i) {
+        const double x = (i - 0.5 * o.m) * o.h;
+        o.dec[i] = std::exp(o.sigma * x * x);
+    }
+    const double c0 = o.h * o.h * o.deta * o.deta / (16.0 * kPi * kPi * o.tau * o.sigma);
+    o.circle_factor.resize(fit.n_circles);
+    for (int c = 0; c < fit.n_circles; ++c)
+        o.circle_factor[c] = c0 * c0 * std::exp(2.0 * o.tau * fit.radius[c] * fit.radius[c]);
+    return SBD_OK;
+}
+
+int near_tables(const SbdFit& fit, NearTables& o, std::string& err) {
+    const double dmin = fit.delta_min;
+    o.tmax = dmin * dmin;
+    double scale = std::abs(fit.w0);
+    for (int p = 0; p < fit.P; ++p) scale += std::fabs(fit.coef[p]);
+    scale = std::max(1.0, scale);
+    // circles whose aliasing terms (Sec. 5) are not negligible within delta_min
+    o.small.clear();
+    double phase = 0.0;
+    bool j0_circle_small = false;
+    for (int c = 0; c < fit.n_circles; ++c) {
+        const double x = fit.radius[c] * dmin;
+        phase = std::max(phase, x);
+        std::vector<double> J;
+        bessel_jn_range(x, fit.M[c], fit.M[c], J);
+        const double mag = 2.0 * std::fabs(J[0]) * std::abs(fit.weight[c]) * fit.M[c];
+        if (mag > 1e-18 * scale) {
+            o.small.push_back(c);
+            if (fit.kind == 1 && c == fit.P) j0_circle_small = true;
+        }
+    }
+    std::vector<char> is_small(fit.n_circles, 0);
+    for (int c : o.small) is_small[c] = 1;
+    auto T1f = [&](double t) -> cplx {
+        if (fit.kind == 0) return -1.0 / (2.0 * kPi);
+        return -bessel_j0(fit.kappa * std::sqrt(t)) / (2.0 * kPi);
+    };
+    auto T2f = [&](double t) -> cplx {
+        const double r = std::sqrt(t);
+        cplx v = 0.0;
+        if (fit.kind == 0) {
+            v = -fit.w0;
+        } else {
+            const double x = fit.kappa * r;
+            const double j0 = bessel_j0(x);
+            const double yreg = x > 0.0 ? bessel_y0_regular(x) : (2.0 / kPi) * 0.57721566490153286061;
+            v = -std::log(0.5 * fit.kappa) * j0 / (2.0 * kPi) - 0.25 * yreg;
+            if (j0_circle_small) v += cplx(0.0, 0.25 * j0);
+        }
+        for (int p = 0; p < fit.P; ++p)
+            if (!is_small[p]) v -= fit.coef[p] * bessel_j0(fit.rho[p] * r / fit.scale_R);
+        return v;
+    };
+    o.deg = 18;
+    o.pieces = std::max(2, static_cast<int>(std::ceil(phase / 2.0)));
+    for (int attempt = 0; attempt < 6; ++attempt) {
+        const int K = o.pieces, D = o.deg;
+        o.T1.assign(static_cast<size_t>(K) * D * 2, 0.0);
+        o.T2.assign(static_cast<size_t>(K) * D * 2, 0.0);
+        const double wdt = o.tmax / K;
+#pragma omp parallel for schedule(dynamic, 1)
+        for (int q = 0; q < K; ++q) {
+            std::vector<cplx> f1(D), f2(D);
+            for (int k = 0; k < D; ++k) {
+                const double tt = std::cos(kPi * (k + 0.5) / D);
+                const double t = (q + 0.5 * (tt + 1.0)) * wdt;
+                f1[k] = T1f(t);
+                f2[k] = T2f(t);
+            }
+            for (int j = 0; j < D; ++j) {
+                cplx s1 = 0.0, s2 = 0.0;
+                for (int k = 0; k < D; ++k) {
+                    const double c = std::cos(kPi * j * (k + 0.5) / D);
+                    s1 += f1[k] * c;
+                    s2 += f2[k] * c;
+                }
+                const double sc = (j == 0 ? 1.0 : 2.0) / D;
+                o.T1[(static_cast<size_t>(q) * D + j) * 2 + 0] = (s1 * sc).real();
+                o.T1[(static_cast<size_t>(q) * D + j) * 2 + 1] = (s1 * sc).imag();
+                o.T2[(static_cast<size_t>(q) * D + j) * 2 + 0] = (s2 * sc).real();
+                o.T2[(static_cast<size_t>(q) * D + j) * 2 + 1] = (s2 * sc).imag();
+            }
+        }
+        // check against direct evaluation between the interpolation points
+        double worst = 0.0;
+        for (int q = 0; q < K; ++q) {
+            for (int k = 0; k < 7; ++k) {
+                const double tt = -1.0 + 2.0 * (k + 0.37) / 7.0;
+                const double t = (q + 0.5 * (tt + 1.0)) * wdt;
+                cplx b1 = 0.0, b2 = 0.0, c1 = 0.0, c2 = 0.0;
+                for (int j = D - 1; j >= 1; --j) {
+                    const cplx a1(o.T1[(q * D + j) * 2], o.T1[(q * D + j) * 2 + 1]);
+                    const cplx a2(o.T2[(q * D + j) * 2], o.T2[(q * D + j) * 2 + 1]);
+                    const cplx n1 = 2.0 * tt * b1 - c1 + a1;
+                    const cplx n2 = 2.0 * tt * b2 - c2 + a2;
+                    c1 = b1; b1 = n1;
+                    c2 = b2; b2 = n2;
+                }
+                const cplx v1 = tt * b1 - c1 + cplx(o.T1[q * D * 2], o.T1[q * D * 2 + 1]);
+                const cplx v2 = tt * b2 - c2 + cplx(o.T2[q * D * 2], o.T2[q * D * 2 + 1]);
+                worst = std::max(worst, std::abs(v1 - T1f(t)) + std::abs(v2 - T2f(t)));
+            }
+        }
+        if (worst <= 1e-14 * scale) break;
+        if (attempt == 5) {
+            char buf[128];
+            std::snprintf(buf, sizeof buf, "near-field table does not converge (%.3g)", worst);
+            err = buf;
+            return SBD_EFIT;
+        }
+        o.pieces *= 2;
+    }
+    cplx g0 = fit.w0;
+    for (int c = 0; c < fit.n_circles; ++c) g0 += fit.weight[c] * static_cast<double>(fit.M[c]);
+    o.self_value = -g0;
+    return SBD_OK;
+}
+
+}  // namespace sbd

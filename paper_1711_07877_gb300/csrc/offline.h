@@ -1,0 +1,75 @@
+// Off-line part on the host (FP64): SBD fit, P search, circular quadrature sizes,
+// weights, type-3 transform parameters and the near-field tables.
+#pragma once
+#include <complex>
+#include <string>
+#include <vector>
+
+namespace sbd {
+
+using cplx = std::complex<double>;
+
+struct SbdFit {
+    int kind = 0;            // 0 Laplace, 1 Helmholtz
+    double kappa = 0.0;
+    double eps = 0.0;
+    double delta_min = 0.0, delta_max = 0.0;
+    double scale_R = 0.0;    // delta_max (Laplace) or k'/kappa (Helmholtz Y0 part)
+    double a = 0.0;          // delta_min / scale_R
+    double kprime = 0.0;     // k' for Helmholtz
+    double gscale = 0.0;     // kernel = gscale * g(r / scale_R) + ...
+    int P = 0;
+    int n_circles = 0;       // P (+1 Helmholtz J0 circle, stored last)
+    std::vector<double> rho, C, alpha;   // per Bessel term (size P)
+    std::vector<double> coef;            // gscale * alpha_p * C_p (kernel units), size P
+    std::vector<int> M;                  // nodes per circle, size n_circles
+    std::vector<double> radius;          // circle radius in frequency units, size n_circles
+    std::vector<cplx> weight;            // omega_hat per node of the circle, size n_circles
+    cplx w0 = 0.0;                       // weight of the xi = 0 node
+    double fit_err_g = 0.0;              // L_inf fit error of g on the sample set
+    double fit_err = 0.0;                // the same in kernel units
+    long long n_xi = 0;                  // sum M
+};
+
+// Fit for the given geometry bound; fixed_P > 0 skips the P search.
+// Returns 0, or a negative SBD_E* code with a message in err.
+int offline_fit(int kind, double kappa, double delta_min, double delta_max, double eps,
+                int fixed_P, SbdFit& out, std::string& err);
+
+// Parameters of the type-3 transform by Gaussian gridding (both sides Gaussian,
+// two-fold oversampling of the spreading grid and of the FFT).
+struct NufftParams {
+    int Ps = 0, Pk = 0;        // stencil widths (cells per dimension, even)
+    double h = 0.0;            // spreading-grid spacing
+    int m = 0;                 // spreading-grid side (cells), even, 5-smooth
+    int n = 0;                 // FFT length = 2 m
+    int nk = 0;                // stored frequency-grid side (cells), even
+    double deta = 0.0;         // frequency-grid spacing 2 pi / (n h)
+    double tau = 0.0, sigma = 0.0;
+    double beta_s = 0.0;       // h^2 / (4 tau): spreading weight exp(-beta_s d^2), d in cells
+    double beta_k = 0.0;       // deta^2 / (4 sigma): node weight exp(-beta_k d^2), d in cells
+    double cx = 0.0, cy = 0.0; // centre of the point set (bounding box)
+    double tol = 0.0;          // tolerance aimed at for each transform
+    std::vector<double> dec;   // x-grid precorrection exp(sigma x_i^2), size m
+    std::vector<double> circle_factor;   // c(|xi|)^2 per circle: (h^2 deta^2 / (16 pi^2 tau sigma))^2 exp(2 tau r^2)
+};
+
+int nufft_params(const SbdFit& fit, double half_extent, double cx, double cy, double tol,
+                 bool fp32, NufftParams& out, std::string& err);
+
+// Smallest even 5-smooth integer >= n.
+int good_fft_size(int n);
+
+// Near-field tables: D(y) = T1(t) * 0.5 log t + T2(t) - sum_{small circles} w_p sum_m e^{i y.xi},
+// t = |y|^2 in [0, delta_min^2]; T1, T2 piecewise Chebyshev in t (complex, re/im interleaved).
+struct NearTables {
+    int pieces = 0, deg = 0;
+    double tmax = 0.0;
+    std::vector<double> T1, T2;      // [pieces][deg][2]
+    std::vector<int> small;          // circles whose plane-wave sum is evaluated exactly
+    cplx self_value = 0.0;           // D_kk = -G_approx(0)
+};
+
+int near_tables(const SbdFit& fit, NearTables& out, std::string& err);
+
+}  // namespace sbd

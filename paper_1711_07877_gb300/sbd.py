@@ -1,0 +1,224 @@
+"""Thin Python binding of libsbd.so (argument marshalling only).
+
+Every function has the name of the C entry point it wraps (include/sbd.h) and
+passes raw pointers and sizes through ctypes; every step of the computation runs
+in the library's CUDA kernels.  Device buffers are torch CUDA tensors (their
+data_ptr() is passed); streams default to torch's current CUDA stream.  A
+missing library is an ImportError: there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libsbd.so")
+
+SBD_OK, SBD_EINVAL, SBD_ENOMEM, SBD_ECUDA, SBD_EFIT, SBD_ETIMEOUT, SBD_ENOTSUP = 0, -1, -2, -3, -4, -5, -6
+SBD_LAPLACE, SBD_HELMHOLTZ = 0, 1
+SBD_FORM_FP64, SBD_FORM_FP32 = 0, 1
+
+
+class SbdError(RuntimeError):
+    def __init__(self, code: int, where: str, detail: str):
+        super().__init__(f"{where}: {code} ({detail})")
+        self.code = code
+
+
+class sbd_kernel(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("kappa", ctypes.c_double)]
+
+
+class sbd_options(ctypes.Structure):
+    _fields_ = [("form", ctypes.c_int32), ("fixed_P", ctypes.c_int32), ("nufft_tol", ctypes.c_double),
+                ("max_nrhs", ctypes.c_int32), ("flags", ctypes.c_int32)]
+
+
+class sbd_plan_stats(ctypes.Structure):
+    _fields_ = [("n_points", ctypes.c_int64), ("P", ctypes.c_int64), ("n_circles", ctypes.c_int64),
+                ("n_xi", ctypes.c_int64), ("nnz", ctypes.c_int64), ("n_coincident", ctypes.c_int64),
+                ("grid_x", ctypes.c_int32), ("grid_k", ctypes.c_int32), ("fft_n", ctypes.c_int32),
+                ("stencil_x", ctypes.c_int32), ("stencil_k", ctypes.c_int32), ("form", ctypes.c_int32),
+                ("kind", ctypes.c_int32),
+                ("delta_max", ctypes.c_double), ("delta_min", ctypes.c_double), ("scale_R", ctypes.c_double),
+                ("a", ctypes.c_double), ("fit_err", ctypes.c_double), ("nufft_tol", ctypes.c_double),
+                ("w0_re", ctypes.c_double), ("w0_im", ctypes.c_double), ("device_bytes", ctypes.c_int64),
+                ("plan_seconds", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with `python -m paper_1711_07877_gb300.build` "
+                          "(nvcc for sm_103a); there is no CPU fallback")
+    return ctypes.CDLL(LIB_PATH)
+
+
+lib = _load()
+_P = ctypes.c_void_p
+_I32, _I64, _D = ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+_SIGS = {
+    "sbd_plan": ([_P, _I64, sbd_kernel, _D, _D, ctypes.POINTER(sbd_options), _P, ctypes.POINTER(_P)], ctypes.c_int),
+    "sbd_matvec": ([_P, _P, _P, _I32, _P], ctypes.c_int),
+    "sbd_far": ([_P, _P, _P, _I32, _P], ctypes.c_int),
+    "sbd_close": ([_P, _P, _P, _I32, _P], ctypes.c_int),
+    "sbd_nufft_minus": ([_P, _P, _P, _P], ctypes.c_int),
+    "sbd_nufft_plus": ([_P, _P, _P, _P], ctypes.c_int),
+    "sbd_plan_info": ([_P, ctypes.POINTER(sbd_plan_stats)], ctypes.c_int),
+    "sbd_plan_export": ([_P, _I64, _P, _P, _P, _P, _P, _P], ctypes.c_int),
+    "sbd_close_export": ([_P, _P, _P, _P], ctypes.c_int),
+    "sbd_destroy": ([_P], ctypes.c_int),
+    "sbd_offline_fit": ([sbd_kernel, _D, _D, _D, _I32, _I64, _P, _P, _P, _P, _P, _P], ctypes.c_int),
+    "sbd_fft2": ([_P, _P, _I32, _I32, _I32, _I32, _P], ctypes.c_int),
+    "sbd_profile": ([_P, _I32], ctypes.c_int),
+    "sbd_profile_read": ([_P, _P, _P], ctypes.c_int),
+    "sbd_error_string": ([ctypes.c_int], ctypes.c_char_p),
+    "sbd_last_error_message": ([], ctypes.c_char_p),
+    "sbd_version": ([], ctypes.c_char_p),
+}
+EXPORTED = tuple(_SIGS)
+for _name, (_args, _res) in _SIGS.items():
+    _fn = getattr(lib, _name)
+    _fn.argtypes = _args
+    _fn.restype = _res
+
+
+def _check(rc: int, where: str) -> None:
+    if rc != SBD_OK:
+        raise SbdError(rc, where, f"{lib.sbd_error_string(rc).decode()}: {lib.sbd_last_error_message().decode()}")
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return int(stream)
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if hasattr(x, "ctypes"):
+        return x.ctypes.data
+    raise TypeError(type(x))
+
+
+def sbd_error_string(code: int) -> str:
+    return lib.sbd_error_string(code).decode()
+
+
+def sbd_last_error_message() -> str:
+    return lib.sbd_last_error_message().decode()
+
+
+def sbd_version() -> str:
+    return lib.sbd_version().decode()
+
+
+def make_options(form: int = SBD_FORM_FP64, fixed_P: int = 0, nufft_tol: float = 0.0, max_nrhs: int = 1):
+    return sbd_options(form, fixed_P, nufft_tol, max_nrhs, 0)
+
+
+def sbd_plan(points, n: int, kernel_kind: int, kappa: float, delta_min: float, eps: float,
+             options: sbd_options | None = None, stream=None) -> int:
+    """points: device (N, 2) float64 tensor or pointer.  Returns the plan handle (int)."""
+    out = _P()
+    rc = lib.sbd_plan(_ptr(points), n, sbd_kernel(kernel_kind, kappa), delta_min, eps,
+                      ctypes.byref(options) if options is not None else None, _stream(stream), ctypes.byref(out))
+    _check(rc, "sbd_plan")
+    return out.value
+
+
+def sbd_matvec(plan: int, f, q, nrhs: int = 1, stream=None) -> None:
+    _check(lib.sbd_matvec(plan, _ptr(f), _ptr(q), nrhs, _stream(stream)), "sbd_matvec")
+
+
+def sbd_far(plan: int, f, q, nrhs: int = 1, stream=None) -> None:
+    _check(lib.sbd_far(plan, _ptr(f), _ptr(q), nrhs, _stream(stream)), "sbd_far")
+
+
+def sbd_close(plan: int, f, q, nrhs: int = 1, stream=None) -> None:
+    _check(lib.sbd_close(plan, _ptr(f), _ptr(q), nrhs, _stream(stream)), "sbd_close")
+
+
+def sbd_nufft_minus(plan: int, f, fhat, stream=None) -> None:
+    _check(lib.sbd_nufft_minus(plan, _ptr(f), _ptr(fhat), _stream(stream)), "sbd_nufft_minus")
+
+
+def sbd_nufft_plus(plan: int, ghat, q, stream=None) -> None:
+    _check(lib.sbd_nufft_plus(plan, _ptr(ghat), _ptr(q), _stream(stream)), "sbd_nufft_plus")
+
+
+def sbd_plan_info(plan: int) -> dict:
+    st = sbd_plan_stats()
+    _check(lib.sbd_plan_info(plan, ctypes.byref(st)), "sbd_plan_info")
+    return st.as_dict()
+
+
+def sbd_plan_export(plan: int):
+    """Returns dict of numpy arrays rho, alpha, M, radius, weight (complex), one entry per circle."""
+    import numpy as np
+    nc = sbd_plan_info(plan)["n_circles"]
+    rho, alpha, radius, wr, wi = (np.zeros(nc) for _ in range(5))
+    M = np.zeros(nc, dtype=np.int32)
+    _check(lib.sbd_plan_export(plan, nc, rho.ctypes.data, alpha.ctypes.data, M.ctypes.data, radius.ctypes.data,
+                               wr.ctypes.data, wi.ctypes.data), "sbd_plan_export")
+    return {"rho": rho, "alpha": alpha, "M": M, "radius": radius, "weight": wr + 1j * wi}
+
+
+def sbd_close_export(plan: int):
+    """Returns (rowptr int64, col int32, val float64 or complex128) host arrays of D."""
+    import numpy as np
+    info = sbd_plan_info(plan)
+    n, nnz = info["n_points"], info["nnz"]
+    rowptr = np.zeros(n + 1, dtype=np.int64)
+    col = np.zeros(nnz, dtype=np.int32)
+    cplx = info["kind"] == SBD_HELMHOLTZ
+    val = np.zeros(nnz, dtype=np.complex128 if cplx else np.float64)
+    _check(lib.sbd_close_export(plan, rowptr.ctypes.data, col.ctypes.data, val.ctypes.data), "sbd_close_export")
+    return rowptr, col, val
+
+
+STAGES = ("sum", "spread", "fft_fwd", "node", "fft_inv", "interp", "spmv")
+
+
+def sbd_profile(plan: int, enable: bool) -> None:
+    _check(lib.sbd_profile(plan, 1 if enable else 0), "sbd_profile")
+
+
+def sbd_profile_read(plan: int) -> dict:
+    """{stage: (total_ms, count)} for the steps timed since sbd_profile(plan, True)."""
+    import numpy as np
+    ms = np.zeros(len(STAGES))
+    cnt = np.zeros(len(STAGES), dtype=np.int64)
+    _check(lib.sbd_profile_read(plan, ms.ctypes.data, cnt.ctypes.data), "sbd_profile_read")
+    return {s: (float(ms[i]), int(cnt[i])) for i, s in enumerate(STAGES)}
+
+
+def sbd_destroy(plan: int) -> None:
+    _check(lib.sbd_destroy(plan), "sbd_destroy")
+
+
+def sbd_offline_fit(kernel_kind: int, kappa: float, delta_min: float, delta_max: float, eps: float,
+                    fixed_P: int = 0, cap: int = 40000):
+    """Host-only SBD fit: returns dict(P, n_circles, rho, alpha, M, fit_err)."""
+    import numpy as np
+    rho, alpha = np.zeros(cap), np.zeros(cap)
+    M = np.zeros(cap, dtype=np.int32)
+    P, nc, err = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_double()
+    _check(lib.sbd_offline_fit(sbd_kernel(kernel_kind, kappa), delta_min, delta_max, eps, fixed_P, cap,
+                               rho.ctypes.data, alpha.ctypes.data, M.ctypes.data, ctypes.byref(P),
+                               ctypes.byref(nc), ctypes.byref(err)), "sbd_offline_fit")
+    k = nc.value
+    return {"P": P.value, "n_circles": k, "rho": rho[:k].copy(), "alpha": alpha[:k].copy(), "M": M[:k].copy(),
+            "fit_err": err.value}
+
+
+def sbd_fft2(x, out, n0: int, n1: int, sign: int, form: int, stream=None) -> None:
+    _check(lib.sbd_fft2(_ptr(x), _ptr(out), n0, n1, sign, form, _stream(stream)), "sbd_fft2")

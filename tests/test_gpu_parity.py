@@ -1,0 +1,317 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Each comparison uses seeded inputs from ``workloads``; expected values come from
+``oracle`` only.  Tolerances:
+  * FFT: FP64 rel-L2 <= 1e-12, FP32 <= 2e-6 (rounding of a length-n transform).
+  * type-3 transforms: max error <= 10 x the plan's transform tolerance x sum|f|
+    (the Gaussian-gridding error model), FP32 additionally >= 3e-6 (rounding).
+  * close matrix D: identical sparsity (bit-exact), values within 1e-12 x max|D|.
+  * FP64 matvec vs the oracle SBD: rel-L2 <= 1e-10 with the transform run at 1e-13.
+  * any form vs the direct sum: max |q - q*| <= eps sum|f| (Sec. 1 output bound).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import sbd_oracle as O
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def S():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1711_07877_gb300 import build
+    build.build_library()
+    import paper_1711_07877_gb300 as pkg
+    return pkg
+
+
+def dev(x, dtype=None):
+    t = torch.from_numpy(np.ascontiguousarray(x))
+    if dtype is not None:
+        t = t.to(dtype)
+    return t.cuda()
+
+
+def make_plan(S, z, kind, dmin, eps, kappa=0.0, form=0, nufft_tol=0.0, max_nrhs=1, fixed_P=0):
+    zt = dev(z)
+    opt = S.make_options(form=form, nufft_tol=nufft_tol, max_nrhs=max_nrhs, fixed_P=fixed_P)
+    p = S.sbd_plan(zt, len(z), S.SBD_HELMHOLTZ if kind == "helmholtz" else S.SBD_LAPLACE, kappa, dmin, eps, opt)
+    torch.cuda.synchronize()
+    return p
+
+
+def matvec(S, p, f, n, nrhs=1, fn=None):
+    cplx = np.iscomplexobj(f)
+    ft = dev(f)
+    q = torch.empty_like(ft)
+    (fn or S.sbd_matvec)(p, ft, q, nrhs)
+    torch.cuda.synchronize()
+    return q.cpu().numpy()
+
+
+# --- FFT against numpy.fft -----------------------------------------------------------------------
+
+@pytest.mark.parametrize("shape", [(12, 20), (160, 320), (243, 250), (1000, 1536), (6, 12500)])
+@pytest.mark.parametrize("form", [0, 1])
+@pytest.mark.parametrize("sign", [-1, 1])
+def test_fft2_matches_numpy(S, shape, form, sign):
+    rng = np.random.default_rng(sum(shape) + form)
+    x = rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
+    want = np.fft.fft2(x) if sign < 0 else np.fft.ifft2(x) * x.size
+    xt = dev(x, torch.complex64 if form == 1 else torch.complex128)
+    out = torch.empty_like(xt)
+    S.sbd_fft2(xt, out, shape[0], shape[1], sign, form)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy()
+    rel = np.linalg.norm(got - want) / np.linalg.norm(want)
+    assert rel < (2e-6 if form == 1 else 1e-12), rel
+
+
+def test_fft2_rejects_bad_sizes(S):
+    xt = torch.zeros(7, 11, dtype=torch.complex128, device="cuda")
+    with pytest.raises(S.SbdError) as e:
+        S.sbd_fft2(xt, xt, 7, 11, -1, 0)
+    assert e.value.code == S.SBD_ENOTSUP
+    with pytest.raises(S.SbdError) as e:
+        S.sbd_fft2(xt, xt, 7, 11, 0, 0)
+    assert e.value.code == S.SBD_EINVAL
+
+
+# --- shared small Laplace case (config-1 geometry, smaller N for the oracle's direct sums) ------
+
+@pytest.fixture(scope="module")
+def lap_small():
+    z = W.disk_points(700, 11)
+    f = W.rhs(700, 12)
+    dmin = math.sqrt(20 / 700)
+    pl = O.make_plan(z, "laplace", dmin, 1e-6)
+    return z, f, dmin, pl
+
+
+@pytest.mark.parametrize("form", [0, 1])
+def test_nufft_minus_plus_match_direct(S, lap_small, form):
+    z, f, dmin, pl = lap_small
+    p = make_plan(S, z, "laplace", dmin, 1e-6, form=form)
+    try:
+        info = S.sbd_plan_info(p)
+        ex = S.sbd_plan_export(p)
+        assert info["P"] == pl.P and np.array_equal(ex["M"], pl.M)
+        assert np.max(np.abs(ex["radius"] - pl.circle_radius)) < 1e-12 * pl.circle_radius.max()
+        xi = np.concatenate([O.circle_nodes(r, M) for r, M in zip(pl.circle_radius, pl.M)])
+        rng = np.random.default_rng(5)
+        fc = f + 1j * rng.standard_normal(len(f))
+        fhat = torch.empty(len(xi), dtype=torch.complex128, device="cuda")
+        S.sbd_nufft_minus(p, dev(fc), fhat)
+        torch.cuda.synchronize()
+        want = O.nufft_direct(z, xi, fc, -1)
+        err = np.max(np.abs(fhat.cpu().numpy() - want)) / np.abs(fc).sum()
+        tol = 10 * info["nufft_tol"] + (3e-6 if form == 1 else 1e-14)
+        assert err <= tol, (err, tol)
+        g = rng.standard_normal(len(xi)) + 1j * rng.standard_normal(len(xi))
+        q = torch.empty(len(z), dtype=torch.complex128, device="cuda")
+        S.sbd_nufft_plus(p, dev(g), q)
+        torch.cuda.synchronize()
+        want = O.nufft_direct(xi, z, g, +1)
+        err = np.max(np.abs(q.cpu().numpy() - want)) / np.abs(g).sum()
+        assert err <= tol, (err, tol)
+    finally:
+        S.sbd_destroy(p)
+
+
+def _close_compare(S, p, pl):
+    rowptr, col, val = S.sbd_close_export(p)
+    rows, cols, vals = O.close_matrix(pl)
+    n = len(pl.z)
+    got = {}
+    for k in range(n):
+        for j in range(rowptr[k], rowptr[k + 1]):
+            got[(k, int(col[j]))] = val[j]
+    want = {(int(r), int(c)): v for r, c, v in zip(rows, cols, vals)}
+    assert set(got) == set(want)
+    scale = max(abs(v) for v in want.values())
+    worst = max(abs(got[k] - want[k]) for k in want)
+    assert worst <= 1e-12 * scale, (worst, scale)
+
+
+def _assert_no_borderline_pairs(z, dmin):
+    k, l = O.near_pairs(z, dmin * (1 + 1e-9))
+    r2 = np.sum((z[k] - z[l]) ** 2, axis=1)
+    assert np.all(np.abs(r2 / dmin ** 2 - 1) > 1e-12), "reseed: a pair sits on the delta_min boundary"
+
+
+def test_close_matrix_matches_oracle_laplace(S, lap_small):
+    z, f, dmin, pl = lap_small
+    _assert_no_borderline_pairs(z, dmin)
+    p = make_plan(S, z, "laplace", dmin, 1e-6)
+    try:
+        _close_compare(S, p, pl)
+    finally:
+        S.sbd_destroy(p)
+
+
+@pytest.fixture(scope="module")
+def helm_small():
+    z = W.disk_points(400, 21)
+    f = W.rhs(400, 22, complex_valued=True)
+    dmin = math.sqrt(20 / 400)
+    kappa = 25.0
+    pl = O.make_plan(z, "helmholtz", dmin, 1e-6, kappa=kappa)
+    return z, f, dmin, kappa, pl
+
+
+def test_close_matrix_matches_oracle_helmholtz(S, helm_small):
+    z, f, dmin, kappa, pl = helm_small
+    _assert_no_borderline_pairs(z, dmin)
+    p = make_plan(S, z, "helmholtz", dmin, 1e-6, kappa=kappa)
+    try:
+        _close_compare(S, p, pl)
+    finally:
+        S.sbd_destroy(p)
+
+
+# --- whole matvec -----------------------------------------------------------------------------------
+
+@pytest.fixture(scope="module")
+def config1():
+    wl = W.laplace_disk(2000, 1, 1e-6)
+    pl = O.make_plan(wl.z, "laplace", wl.delta_min, wl.eps)
+    q_sbd = O.sbd_matvec(pl, wl.f)
+    q_dir = O.direct_sum(wl.z, wl.f, "laplace")
+    return wl, pl, q_sbd, q_dir
+
+
+def test_matvec_fp64_matches_oracle_sbd(S, config1):
+    wl, pl, q_sbd, q_dir = config1
+    _assert_no_borderline_pairs(wl.z, wl.delta_min)
+    p = make_plan(S, wl.z, "laplace", wl.delta_min, wl.eps, form=0, nufft_tol=1e-13)
+    try:
+        info = S.sbd_plan_info(p)
+        assert info["P"] == pl.P and np.array_equal(S.sbd_plan_export(p)["M"], pl.M)
+        q = matvec(S, p, wl.f, len(wl.z))
+        rel = np.linalg.norm(q - q_sbd) / np.linalg.norm(q_sbd)
+        assert rel <= 1e-10, rel
+        assert np.max(np.abs(q - q_dir)) <= wl.eps * np.abs(wl.f).sum()
+    finally:
+        S.sbd_destroy(p)
+
+
+@pytest.mark.parametrize("form", [0, 1])
+def test_matvec_within_eps_of_direct_sum(S, config1, form):
+    wl, pl, q_sbd, q_dir = config1
+    p = make_plan(S, wl.z, "laplace", wl.delta_min, wl.eps, form=form)
+    try:
+        q = matvec(S, p, wl.f, len(wl.z))
+        assert np.max(np.abs(q - q_dir)) <= wl.eps * np.abs(wl.f).sum()
+        rel = np.linalg.norm(q - q_dir) / np.linalg.norm(q_dir)
+        assert rel <= 1e-5, rel
+        # the two halves add up to the whole
+        far = matvec(S, p, wl.f, len(wl.z), fn=S.sbd_far)
+        close = matvec(S, p, wl.f, len(wl.z), fn=S.sbd_close)
+        assert np.max(np.abs(far + close - q)) <= 1e-12 * np.abs(q).max()
+    finally:
+        S.sbd_destroy(p)
+
+
+def test_matvec_helmholtz(S, helm_small):
+    z, f, dmin, kappa, pl = helm_small
+    q_sbd = O.sbd_matvec(pl, f)
+    q_dir = O.direct_sum(z, f, "helmholtz", kappa)
+    p = make_plan(S, z, "helmholtz", dmin, 1e-6, kappa=kappa, form=0, nufft_tol=1e-13)
+    try:
+        q = matvec(S, p, f, len(z))
+        assert np.linalg.norm(q - q_sbd) / np.linalg.norm(q_sbd) <= 1e-10
+        assert np.max(np.abs(q - q_dir)) <= 1e-6 * np.abs(f).sum()
+    finally:
+        S.sbd_destroy(p)
+    p = make_plan(S, z, "helmholtz", dmin, 1e-6, kappa=kappa, form=1)
+    try:
+        q = matvec(S, p, f, len(z))
+        assert np.max(np.abs(q - q_dir)) <= 1e-6 * np.abs(f).sum()
+    finally:
+        S.sbd_destroy(p)
+
+
+@pytest.mark.parametrize("form", [0, 1])
+def test_nrhs_batch_equals_single_calls(S, lap_small, form):
+    z, f, dmin, pl = lap_small
+    F = np.stack([f, W.rhs(len(z), 31), W.rhs(len(z), 32)])
+    p = make_plan(S, z, "laplace", dmin, 1e-6, form=form, max_nrhs=3)
+    try:
+        qb = matvec(S, p, F, len(z), nrhs=3)
+        for r in range(3):
+            qs = matvec(S, p, F[r], len(z))
+            assert np.max(np.abs(qb[r] - qs)) <= 1e-12 * np.abs(qs).max()
+        with pytest.raises(S.SbdError):
+            S.sbd_matvec(p, dev(F), torch.empty(3 * len(z), dtype=torch.float64, device="cuda"), 4)
+    finally:
+        S.sbd_destroy(p)
+
+
+def test_translation_invariance_and_linearity(S, lap_small):
+    z, f, dmin, pl = lap_small
+    g = W.rhs(len(z), 41)
+    p1 = make_plan(S, z, "laplace", dmin, 1e-6)
+    p2 = make_plan(S, z + np.array([5.0, -3.0]), "laplace", dmin, 1e-6)
+    try:
+        q1, q2 = matvec(S, p1, f, len(z)), matvec(S, p2, f, len(z))
+        assert np.max(np.abs(q1 - q2)) <= 1e-9 * np.abs(q1).max()
+        qg = matvec(S, p1, g, len(z))
+        q12 = matvec(S, p1, 2 * f - g, len(z))
+        assert np.max(np.abs(q12 - (2 * q1 - qg))) <= 1e-11 * np.abs(q12).max()
+        assert abs(g @ q1 - qg @ f) <= 1e-10 * np.abs(q1).sum()   # symmetric operator (Laplace)
+    finally:
+        S.sbd_destroy(p1)
+        S.sbd_destroy(p2)
+
+
+def test_edge_cases(S):
+    # two points: only the far part acts; q_1 = G(|z1 - z2|) f_2
+    z = np.array([[0.0, 0.0], [0.6, 0.8]])
+    f = np.array([1.5, -2.0])
+    p = make_plan(S, z, "laplace", 0.05, 1e-8, form=0)
+    try:
+        q = matvec(S, p, f, 2)
+        assert np.max(np.abs(q - O.direct_sum(z, f, "laplace"))) <= 1e-8 * np.abs(f).sum()
+    finally:
+        S.sbd_destroy(p)
+    # coincident points are treated as the self pair (reading R1) and counted
+    z = np.concatenate([W.disk_points(200, 51), W.disk_points(3, 51)])
+    f = W.rhs(203, 52)
+    p = make_plan(S, z, "laplace", 0.2, 1e-6)
+    try:
+        assert S.sbd_plan_info(p)["n_coincident"] == 3
+        q = matvec(S, p, f, 203)
+        assert np.max(np.abs(q - O.direct_sum(z, f, "laplace"))) <= 1e-6 * np.abs(f).sum()
+    finally:
+        S.sbd_destroy(p)
+    # invalid calls
+    one = dev(np.zeros((1, 2)))
+    for args in [(one, 1, 0, 0.0, 0.1, 1e-6), (one, 0, 0, 0.0, 0.1, 1e-6),
+                 (dev(W.disk_points(10, 1)), 10, 0, 0.0, 5.0, 1e-6),
+                 (dev(W.disk_points(10, 1)), 10, 1, -2.0, 0.1, 1e-6),
+                 (dev(W.disk_points(10, 1)), 10, 0, 0.0, 0.1, 1e-11)]:
+        with pytest.raises(S.SbdError) as e:
+            S.sbd_plan(*args)
+        assert e.value.code == S.SBD_EINVAL
+
+
+def test_config2_sampled_against_direct_sum(S):
+    """Laplace, N = 10^6 on 8 curves, eps = 1e-6, FP32 form (the bench's launch):
+    500 sampled outputs against the FP64 direct sum over all sources."""
+    wl = W.laplace_curves(1_000_000, 2, 1e-6)
+    p = make_plan(S, wl.z, "laplace", wl.delta_min, wl.eps, form=1)
+    try:
+        q = matvec(S, p, wl.f, len(wl.z))
+        idx = np.random.default_rng(7).choice(len(wl.z), 500, replace=False)
+        qd = O.direct_sum(wl.z, wl.f, "laplace", targets=idx, chunk=16)
+        assert np.max(np.abs(q[idx] - qd)) <= wl.eps * np.abs(wl.f).sum()
+        rel = np.linalg.norm(q[idx] - qd) / np.linalg.norm(qd)
+        assert rel <= 1e-5, rel
+    finally:
+        S.sbd_destroy(p)

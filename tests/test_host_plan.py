@@ -1,0 +1,92 @@
+"""CPU tests of the library: it loads, exports every declared symbol, and its host
+off-line plan (SBD fit, P search, circle sizes) agrees with the oracle."""
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import sbd_oracle as O
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="session")
+def S():
+    from paper_1711_07877_gb300 import build
+    build.build_library()
+    import paper_1711_07877_gb300 as pkg
+    return pkg
+
+
+def test_library_exports_every_declared_symbol(S):
+    header = open(os.path.join(ROOT, "include", "sbd.h")).read()
+    declared = set(re.findall(r"^(?:int|const char\*)\s+(sbd_\w+)\s*\(", header, flags=re.M))
+    assert declared, "no declarations parsed"
+    for name in declared:
+        assert hasattr(S.lib, name), name
+    assert declared == set(S.EXPORTED)
+    assert S.sbd_error_string(S.SBD_EFIT)
+    assert S.sbd_version().startswith("sbd-gb300")
+
+
+def test_argument_errors_without_gpu(S):
+    with pytest.raises(S.SbdError) as e:
+        S.sbd_offline_fit(S.SBD_LAPLACE, 0.0, 0.5, 0.4, 1e-6)      # delta_min >= delta_max
+    assert e.value.code == S.SBD_EINVAL
+    with pytest.raises(S.SbdError) as e:
+        S.sbd_offline_fit(S.SBD_LAPLACE, 0.0, 0.1, 2.0, 1e-12)     # eps below the fit floor range
+    assert e.value.code == S.SBD_EINVAL
+    with pytest.raises(S.SbdError) as e:
+        S.sbd_offline_fit(S.SBD_HELMHOLTZ, -1.0, 0.1, 2.0, 1e-6)   # kappa <= 0
+    assert e.value.code == S.SBD_EINVAL
+    with pytest.raises(S.SbdError) as e:
+        S.sbd_plan(0, 10, S.SBD_LAPLACE, 0.0, 0.1, 1e-6, None, 0)  # null points
+    assert e.value.code == S.SBD_EINVAL
+
+
+@pytest.mark.parametrize("eps", [1e-3, 1e-6, 1e-9])
+def test_host_fit_matches_oracle_laplace(S, eps):
+    wl = W.laplace_disk(2000, 1, eps)
+    dmax = W.enclosing_diameter(wl.z)
+    r = S.sbd_offline_fit(S.SBD_LAPLACE, 0.0, wl.delta_min, dmax, eps)
+    pl = O.make_plan(wl.z, "laplace", wl.delta_min, eps)
+    assert r["P"] == pl.P
+    assert np.array_equal(r["rho"], r["rho"]) and np.max(np.abs(r["rho"] - pl.rho)) < 1e-12 * pl.rho.max()
+    assert np.array_equal(r["M"], pl.M)
+    # alpha is ill-determined along the Gram matrix's small eigenvectors; the fitted
+    # function is not: compare the series on the annulus and the error level
+    s = np.linspace(pl.a, 1, 3000)
+    f_cpp = O.series_value(s, pl.rho, pl.C, r["alpha"])
+    f_ora = O.series_value(s, pl.rho, pl.C, pl.alpha)
+    # (g units; the floor 1e-11 reflects rounding in the ill-conditioned Gram solve, Sec. 3.3)
+    assert np.max(np.abs(f_cpp - f_ora)) < max(1e-3 * eps * 2 * math.pi, 1e-11)
+    assert r["fit_err"] == pytest.approx(pl.fit_err / (2 * math.pi), rel=1e-3)
+    assert r["fit_err"] <= eps / 3
+
+
+def test_host_fit_matches_oracle_helmholtz(S):
+    z = W.disk_points(300, 7)
+    dmax = W.enclosing_diameter(z)
+    dmin = math.sqrt(20 / 300)
+    r = S.sbd_offline_fit(S.SBD_HELMHOLTZ, 25.0, dmin, dmax, 1e-6)
+    pl = O.make_plan(z, "helmholtz", dmin, 1e-6, kappa=25.0)
+    assert r["P"] == pl.P and r["n_circles"] == pl.P + 1
+    assert np.array_equal(r["M"], pl.M)
+    assert np.max(np.abs(r["alpha"][:pl.P] - pl.alpha)) < 1e-6 * np.max(np.abs(pl.alpha))
+
+
+def test_host_fit_fixed_P_and_floor(S):
+    r = S.sbd_offline_fit(S.SBD_LAPLACE, 0.0, 0.1, 2.0, 1e-6, fixed_P=40)
+    assert r["P"] == 40
+    rho, C, al = O.sbd_coefficients(lambda s: 1 / s, 0.05, 40)
+    assert np.max(np.abs(r["alpha"] - al)) < 1e-8 * np.max(np.abs(al))
+    # eps = 1e-10 sits at the paper's fit floor (Sec. 4.1, ~1e-10): either a P is found
+    # that meets it or the fit reports SBD_EFIT; it never returns an unmet tolerance
+    try:
+        r = S.sbd_offline_fit(S.SBD_LAPLACE, 0.0, 0.1, 2.0, 1e-10)
+        assert r["fit_err"] <= 1e-10 / 3
+    except S.SbdError as e:
+        assert e.code == S.SBD_EFIT
