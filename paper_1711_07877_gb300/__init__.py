@@ -7,11 +7,16 @@ when the library has not been built (python -m paper_1711_07877_gb300.build);
 there is no fallback.
 """
 import importlib
+import os
+
+_SUBMODULES = {name[:-3] for name in os.listdir(os.path.dirname(__file__)) if name.endswith(".py")}
 
 
 def __getattr__(name):
     if name.startswith("__"):
         raise AttributeError(name)
+    if name in _SUBMODULES:
+        return importlib.import_module(f"{__name__}.{name}")
     mod = importlib.import_module(__name__ + ".sbd")   # loads libsbd.so
     try:
         return getattr(mod, name)
