@@ -275,8 +275,9 @@ int nufft_minus_impl(sbd_plan_s* p, const void* f, void* fhat, cudaStream_t s) {
     int rc = far_spread<T>(static_cast<const PointRec<T>*>(p->pts), p->n, f, true, 1, p->geom, X, s);
     if (rc) return rc;
     if ((rc = forward_fft<T>(p, X, A, C, B, s))) return rc;
+    const NodeFrame fr{p->circle_start, p->circle_radius, p->circle_M, p->fit.n_circles, p->np.cx, p->np.cy};
     return far_node_gather<T>(static_cast<const NodeRec<T>*>(p->nodes), p->fit.n_xi,
-                              static_cast<const T*>(p->cscale_c), p->geom, B, static_cast<double2*>(fhat), s);
+                              static_cast<const T*>(p->cscale_c), p->geom, B, static_cast<double2*>(fhat), fr, s);
 }
 
 template <typename T>
@@ -285,8 +286,10 @@ int nufft_plus_impl(sbd_plan_s* p, const void* ghat, void* q, cudaStream_t s) {
     auto* A = static_cast<cx_t<T>*>(p->wsA);
     auto* B = static_cast<cx_t<T>*>(p->wsB);
     auto* C = static_cast<cx_t<T>*>(p->wsC);
+    const NodeFrame fr{p->circle_start, p->circle_radius, p->circle_M, p->fit.n_circles, p->np.cx, p->np.cy};
     int rc = far_node_scatter<T>(static_cast<const NodeRec<T>*>(p->nodes), p->fit.n_xi,
-                                 static_cast<const T*>(p->cscale_c), p->geom, static_cast<const double2*>(ghat), C, s);
+                                 static_cast<const T*>(p->cscale_c), p->geom, static_cast<const double2*>(ghat), C,
+                                 fr, s);
     if (rc) return rc;
     if ((rc = inverse_fft<T>(p, C, A, B, X, s))) return rc;
     SBD_CUDA_TRY(cudaMemsetAsync(p->zero2, 0, sizeof(double2), s));

@@ -49,6 +49,19 @@ __global__ void prepare_points_kernel(const double* __restrict__ z, long n, doub
     out[i] = r;
 }
 
+// xi of node nu (FP64): circle by binary search in the prefix offsets, then Eq. (defXimp).
+__device__ __forceinline__ double2 node_xi(const int* __restrict__ start, const double* __restrict__ radius,
+                                           const int* __restrict__ M, int n_circles, long nu) {
+    int lo = 0, hi = n_circles;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) / 2;
+        if (start[mid] <= nu) lo = mid; else hi = mid;
+    }
+    double sn, cs;
+    sincospi(2.0 * static_cast<double>(nu - start[lo]) / M[lo], &sn, &cs);
+    return make_double2(radius[lo] * cs, radius[lo] * sn);
+}
+
 template <typename T>
 __global__ void prepare_nodes_kernel(const int* __restrict__ start, const double* __restrict__ radius,
                                      const int* __restrict__ M, int n_circles, long n_xi, double deta,
@@ -128,7 +141,8 @@ __global__ void node_step_kernel(const NodeRec<T>* __restrict__ nodes, long n_xi
 
 template <typename T, int PMAX>
 __global__ void node_gather_kernel(const NodeRec<T>* __restrict__ nodes, long n_xi, const T* __restrict__ cs,
-                                   FarGeom g, const cx_t<T>* __restrict__ kin, double2* __restrict__ out) {
+                                   FarGeom g, const cx_t<T>* __restrict__ kin, double2* __restrict__ out,
+                                   NodeFrame fr) {
     const long nu = blockIdx.x * static_cast<long>(blockDim.x) + threadIdx.x;
     if (nu >= n_xi) return;
     const NodeRec<T> q = nodes[nu];
@@ -143,19 +157,30 @@ __global__ void node_gather_kernel(const NodeRec<T>* __restrict__ nodes, long n_
         acc = cadd(acc, cscale(s, wx[a]));
     }
     acc = cscale(acc, cs[q.circle]);
-    out[nu] = make_double2(acc.x, acc.y);
+    // the grids hold z - c: multiply by exp(-i c.xi) to return sum_l exp(-i z_l.xi) f_l
+    const double2 xi = node_xi(fr.start, fr.radius, fr.M, fr.n_circles, nu);
+    double sn, co;
+    sincos(fr.cx * xi.x + fr.cy * xi.y, &sn, &co);
+    const double ar = acc.x, ai = acc.y;
+    out[nu] = make_double2(ar * co + ai * sn, ai * co - ar * sn);
 }
 
 template <typename T, int PMAX>
 __global__ void node_scatter_kernel(const NodeRec<T>* __restrict__ nodes, long n_xi, const T* __restrict__ cs,
-                                    FarGeom g, const double2* __restrict__ in, cx_t<T>* __restrict__ kout) {
+                                    FarGeom g, const double2* __restrict__ in, cx_t<T>* __restrict__ kout,
+                                    NodeFrame fr) {
     const long nu = blockIdx.x * static_cast<long>(blockDim.x) + threadIdx.x;
     if (nu >= n_xi) return;
     const NodeRec<T> q = nodes[nu];
     T wx[PMAX], wy[PMAX];
     weights<T, PMAX>(q.frac.x, g.P, static_cast<T>(g.beta_k), wx);
     weights<T, PMAX>(q.frac.y, g.P, static_cast<T>(g.beta_k), wy);
-    const double2 v = in[nu];
+    double2 v = in[nu];
+    // q_l = sum_nu exp(i (z_l - c).xi) [exp(i c.xi) ghat_nu]
+    const double2 xi = node_xi(fr.start, fr.radius, fr.M, fr.n_circles, nu);
+    double sn, co;
+    sincos(fr.cx * xi.x + fr.cy * xi.y, &sn, &co);
+    v = make_double2(v.x * co - v.y * sn, v.x * sn + v.y * co);
     const cx_t<T> acc = cscale(mk<T>(static_cast<T>(v.x), static_cast<T>(v.y)), cs[q.circle]);
     for (int a = 0; a < g.P; ++a) {
         const cx_t<T> va = cscale(acc, wx[a]);
@@ -264,19 +289,19 @@ int far_node_step(const NodeRec<T>* nodes, long n_xi, const cx_t<T>* omega_c, in
 
 template <typename T>
 int far_node_gather(const NodeRec<T>* nodes, long n_xi, const T* cscale_c, const FarGeom& g,
-                    const cx_t<T>* kin, double2* out, cudaStream_t s) {
+                    const cx_t<T>* kin, double2* out, const NodeFrame& fr, cudaStream_t s) {
     if (n_xi <= 0) return SBD_OK;
-    node_gather_kernel<T, pmax<T>()><<<blocks_for(n_xi), kThreads, 0, s>>>(nodes, n_xi, cscale_c, g, kin, out);
+    node_gather_kernel<T, pmax<T>()><<<blocks_for(n_xi), kThreads, 0, s>>>(nodes, n_xi, cscale_c, g, kin, out, fr);
     SBD_LAUNCH_CHECK();
     return SBD_OK;
 }
 
 template <typename T>
 int far_node_scatter(const NodeRec<T>* nodes, long n_xi, const T* cscale_c, const FarGeom& g,
-                     const double2* in, cx_t<T>* kout, cudaStream_t s) {
+                     const double2* in, cx_t<T>* kout, const NodeFrame& fr, cudaStream_t s) {
     SBD_CUDA_TRY(cudaMemsetAsync(kout, 0, sizeof(cx_t<T>) * static_cast<size_t>(g.nk) * g.nk, s));
     if (n_xi <= 0) return SBD_OK;
-    node_scatter_kernel<T, pmax<T>()><<<blocks_for(n_xi), kThreads, 0, s>>>(nodes, n_xi, cscale_c, g, in, kout);
+    node_scatter_kernel<T, pmax<T>()><<<blocks_for(n_xi), kThreads, 0, s>>>(nodes, n_xi, cscale_c, g, in, kout, fr);
     SBD_LAUNCH_CHECK();
     return SBD_OK;
 }
@@ -309,9 +334,9 @@ int far_sum(const void* f, bool f_complex, long n, int nrhs, double2* sumf, cuda
     template int far_node_step<T>(const NodeRec<T>*, long, const cx_t<T>*, int, const FarGeom&,          \
                                   const cx_t<T>*, cx_t<T>*, cudaStream_t);                                \
     template int far_node_gather<T>(const NodeRec<T>*, long, const T*, const FarGeom&, const cx_t<T>*,    \
-                                    double2*, cudaStream_t);                                              \
+                                    double2*, const NodeFrame&, cudaStream_t);                            \
     template int far_node_scatter<T>(const NodeRec<T>*, long, const T*, const FarGeom&, const double2*,   \
-                                     cx_t<T>*, cudaStream_t);                                             \
+                                     cx_t<T>*, const NodeFrame&, cudaStream_t);                           \
     template int far_interp<T>(const PointRec<T>*, long, int, const FarGeom&, const cx_t<T>*, double2,   \
                                const double2*, void*, bool, cudaStream_t);
 SBD_FAR_INST(float)

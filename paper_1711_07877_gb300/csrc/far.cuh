@@ -37,14 +37,23 @@ int far_spread(const PointRec<T>* pts, long n, const void* f, bool f_complex, in
 template <typename T>
 int far_node_step(const NodeRec<T>* nodes, long n_xi, const cx_t<T>* omega_c, int nrhs,
                   const FarGeom& g, const cx_t<T>* kin, cx_t<T>* kout, cudaStream_t s);
-// Gather only: out[nu] = c_nu * sum_stencil w K  (complex128), c = circle scale.
+// Circle tables and the centre c of the point set, to place the canonical nodes in
+// absolute coordinates (the grids hold z - c).
+struct NodeFrame {
+    const int* start;
+    const double* radius;
+    const int* M;
+    int n_circles;
+    double cx, cy;
+};
+// Gather only: out[nu] = exp(-i c.xi_nu) c_nu sum_stencil w K  (complex128), c_nu = circle scale.
 template <typename T>
 int far_node_gather(const NodeRec<T>* nodes, long n_xi, const T* cscale, const FarGeom& g,
-                    const cx_t<T>* kin, double2* out, cudaStream_t s);
-// Scatter only: kout (zeroed here) += c_nu in[nu] w.
+                    const cx_t<T>* kin, double2* out, const NodeFrame& fr, cudaStream_t s);
+// Scatter only: kout (zeroed here) += c_nu exp(i c.xi_nu) in[nu] w.
 template <typename T>
 int far_node_scatter(const NodeRec<T>* nodes, long n_xi, const T* cscale, const FarGeom& g,
-                     const double2* in, cx_t<T>* kout, cudaStream_t s);
+                     const double2* in, cx_t<T>* kout, const NodeFrame& fr, cudaStream_t s);
 // Interpolate the grids at the points: q (nrhs x N) = interp + w0 * sumf[r]; real or complex out.
 template <typename T>
 int far_interp(const PointRec<T>* pts, long n, int nrhs, const FarGeom& g, const cx_t<T>* grid,
