@@ -9,6 +9,7 @@
 #include "far.cuh"
 #include "fft.cuh"
 #include "near.cuh"
+#include "node.cuh"
 #include "offline.h"
 #include "sbd.h"
 
@@ -54,6 +55,11 @@ struct sbd_plan_s {
     int* circle_start = nullptr;
     double* circle_radius = nullptr;
     int* circle_M = nullptr;
+    int* node_perm = nullptr;          // sorted record -> canonical node index
+    int* pt_perm = nullptr;            // sorted point record -> original point index
+    long long* pt_tile_start = nullptr;
+    long long* node_tile_start = nullptr;
+    void* ghat = nullptr;              // n_xi weighted node values (scratch)
     // workspace (one right-hand side at a time)
     void* wsX = nullptr;
     void* wsA = nullptr;
@@ -163,10 +169,18 @@ int build_far(sbd_plan_s* p, cudaStream_t s) {
     p->geom.nk = np.nk;
     p->geom.beta_s = np.beta_s;
     p->geom.beta_k = np.beta_k;
-    int rc = dev_alloc(p, &p->pts, sizeof(PointRec<T>) * p->n);
+    PointRec<T>* pts0 = nullptr;
+    SBD_CUDA_TRY(cudaMallocAsync(&pts0, sizeof(PointRec<T>) * p->n, s));
+    int rc = far_prepare_points<T>(p->z, p->n, np.cx, np.cy, np.h, np.m, np.Ps, pts0, s);
     if (rc) return rc;
-    rc = far_prepare_points<T>(p->z, p->n, np.cx, np.cy, np.h, np.m, np.Ps, static_cast<PointRec<T>*>(p->pts), s);
-    if (rc) return rc;
+    const int ntm = (np.m + kNodeTile - 1) / kNodeTile;
+    if ((rc = dev_alloc(p, &p->pts, sizeof(PointRec<T>) * p->n))) return rc;
+    if ((rc = dev_alloc(p, reinterpret_cast<void**>(&p->pt_perm), sizeof(int) * p->n))) return rc;
+    if ((rc = dev_alloc(p, reinterpret_cast<void**>(&p->pt_tile_start),
+                        sizeof(long long) * (static_cast<size_t>(ntm) * ntm + 1)))) return rc;
+    if ((rc = tile_sort<PointRec<T>>(pts0, p->n, np.m, static_cast<PointRec<T>*>(p->pts), p->pt_perm,
+                                     p->pt_tile_start, s))) return rc;
+    SBD_CUDA_TRY(cudaFreeAsync(pts0, s));
     std::vector<int> start(fit.n_circles + 1, 0);
     for (int c = 0; c < fit.n_circles; ++c) start[c + 1] = start[c] + fit.M[c];
     if (fit.n_xi > 2000000000LL) {
@@ -176,10 +190,21 @@ int build_far(sbd_plan_s* p, cudaStream_t s) {
     if ((rc = upload(p, &p->circle_start, start, s))) return rc;
     if ((rc = upload(p, &p->circle_radius, fit.radius, s))) return rc;
     if ((rc = upload(p, &p->circle_M, fit.M, s))) return rc;
-    if ((rc = dev_alloc(p, &p->nodes, sizeof(NodeRec<T>) * fit.n_xi))) return rc;
+    NodeRec<T>* canon = nullptr;
+    SBD_CUDA_TRY(cudaMallocAsync(&canon, sizeof(NodeRec<T>) * std::max<long long>(fit.n_xi, 1), s));
     rc = far_prepare_nodes<T>(p->circle_start, p->circle_radius, p->circle_M, fit.n_circles, fit.n_xi, np.deta,
-                              np.nk, np.Pk, static_cast<NodeRec<T>*>(p->nodes), s);
+                              np.nk, np.Pk, canon, s);
     if (rc) return rc;
+    const int ntx = (np.nk + kNodeTile - 1) / kNodeTile;
+    if ((rc = dev_alloc(p, &p->nodes, sizeof(NodeRec<T>) * fit.n_xi))) return rc;
+    if ((rc = dev_alloc(p, reinterpret_cast<void**>(&p->node_perm), sizeof(int) * fit.n_xi))) return rc;
+    if ((rc = dev_alloc(p, reinterpret_cast<void**>(&p->node_tile_start),
+                        sizeof(long long) * (static_cast<size_t>(ntx) * ntx + 1)))) return rc;
+    rc = tile_sort<NodeRec<T>>(canon, fit.n_xi, np.nk, static_cast<NodeRec<T>*>(p->nodes), p->node_perm,
+                               p->node_tile_start, s);
+    if (rc) return rc;
+    SBD_CUDA_TRY(cudaFreeAsync(canon, s));
+    if ((rc = dev_alloc(p, &p->ghat, sizeof(cx_t<T>) * fit.n_xi))) return rc;
     std::vector<cx_t<T>> om(fit.n_circles);
     std::vector<T> cs(fit.n_circles);
     for (int c = 0; c < fit.n_circles; ++c) {
@@ -246,21 +271,23 @@ int far_apply(sbd_plan_s* p, const void* f, void* q, int nrhs, cudaStream_t s) {
         const void* fr = static_cast<const char*>(f) + esz * p->n * r;
         void* qr = static_cast<char*>(q) + esz * p->n * r;
         StepTimer t1(p, s, SBD_STAGE_SPREAD);
-        if ((rc = far_spread<T>(static_cast<const PointRec<T>*>(p->pts), p->n, fr, cplx_io, 1, p->geom, X, s))) return rc;
+        if ((rc = spread_tiled<T>(static_cast<const PointRec<T>*>(p->pts), p->pt_perm, p->pt_tile_start, p->np.m,
+                                  p->np.Ps, p->np.beta_s, fr, cplx_io, X, s))) return rc;
         t1.end();
         StepTimer t2(p, s, SBD_STAGE_FFT_FWD);
         if ((rc = forward_fft<T>(p, X, A, C, B, s))) return rc;
         t2.end();
         StepTimer t3(p, s, SBD_STAGE_NODE);
-        if ((rc = far_node_step<T>(static_cast<const NodeRec<T>*>(p->nodes), p->fit.n_xi,
-                                   static_cast<const cx_t<T>*>(p->omega_c), 1, p->geom, B, C, s))) return rc;
+        if ((rc = node_step_tiled<T>(static_cast<const NodeRec<T>*>(p->nodes), p->node_tile_start, p->np.nk,
+                                     p->np.Pk, p->np.beta_k, static_cast<const cx_t<T>*>(p->omega_c), B,
+                                     static_cast<cx_t<T>*>(p->ghat), C, s))) return rc;
         t3.end();
         StepTimer t4(p, s, SBD_STAGE_FFT_INV);
         if ((rc = inverse_fft<T>(p, C, A, B, X, s))) return rc;
         t4.end();
         StepTimer t5(p, s, SBD_STAGE_INTERP);
-        if ((rc = far_interp<T>(static_cast<const PointRec<T>*>(p->pts), p->n, 1, p->geom, X, w0, p->sumf + r, qr,
-                                cplx_io, s))) return rc;
+        if ((rc = interp_tiled<T>(static_cast<const PointRec<T>*>(p->pts), p->pt_perm, p->pt_tile_start, p->np.m,
+                                  p->np.Ps, p->np.beta_s, X, w0, p->sumf + r, qr, cplx_io, s))) return rc;
         t5.end();
     }
     return SBD_OK;
@@ -272,10 +299,12 @@ int nufft_minus_impl(sbd_plan_s* p, const void* f, void* fhat, cudaStream_t s) {
     auto* A = static_cast<cx_t<T>*>(p->wsA);
     auto* B = static_cast<cx_t<T>*>(p->wsB);
     auto* C = static_cast<cx_t<T>*>(p->wsC);
-    int rc = far_spread<T>(static_cast<const PointRec<T>*>(p->pts), p->n, f, true, 1, p->geom, X, s);
+    int rc = spread_tiled<T>(static_cast<const PointRec<T>*>(p->pts), p->pt_perm, p->pt_tile_start, p->np.m,
+                             p->np.Ps, p->np.beta_s, f, true, X, s);
     if (rc) return rc;
     if ((rc = forward_fft<T>(p, X, A, C, B, s))) return rc;
-    const NodeFrame fr{p->circle_start, p->circle_radius, p->circle_M, p->fit.n_circles, p->np.cx, p->np.cy};
+    const NodeFrame fr{p->circle_start, p->circle_radius, p->circle_M, p->fit.n_circles, p->np.cx, p->np.cy,
+                       p->node_perm};
     return far_node_gather<T>(static_cast<const NodeRec<T>*>(p->nodes), p->fit.n_xi,
                               static_cast<const T*>(p->cscale_c), p->geom, B, static_cast<double2*>(fhat), fr, s);
 }
@@ -286,15 +315,16 @@ int nufft_plus_impl(sbd_plan_s* p, const void* ghat, void* q, cudaStream_t s) {
     auto* A = static_cast<cx_t<T>*>(p->wsA);
     auto* B = static_cast<cx_t<T>*>(p->wsB);
     auto* C = static_cast<cx_t<T>*>(p->wsC);
-    const NodeFrame fr{p->circle_start, p->circle_radius, p->circle_M, p->fit.n_circles, p->np.cx, p->np.cy};
+    const NodeFrame fr{p->circle_start, p->circle_radius, p->circle_M, p->fit.n_circles, p->np.cx, p->np.cy,
+                       p->node_perm};
     int rc = far_node_scatter<T>(static_cast<const NodeRec<T>*>(p->nodes), p->fit.n_xi,
                                  static_cast<const T*>(p->cscale_c), p->geom, static_cast<const double2*>(ghat), C,
                                  fr, s);
     if (rc) return rc;
     if ((rc = inverse_fft<T>(p, C, A, B, X, s))) return rc;
     SBD_CUDA_TRY(cudaMemsetAsync(p->zero2, 0, sizeof(double2), s));
-    return far_interp<T>(static_cast<const PointRec<T>*>(p->pts), p->n, 1, p->geom, X, make_double2(0, 0), p->zero2,
-                         q, true, s);
+    return interp_tiled<T>(static_cast<const PointRec<T>*>(p->pts), p->pt_perm, p->pt_tile_start, p->np.m, p->np.Ps,
+                           p->np.beta_s, X, make_double2(0, 0), p->zero2, q, true, s);
 }
 
 int check_plan_call(sbd_plan_t p, const void* a, const void* b) {

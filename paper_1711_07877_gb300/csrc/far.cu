@@ -1,5 +1,6 @@
-// Far-part kernels: type-3 transform by Gaussian gridding (first version: one
-// thread per point / node, accumulation by global atomics).
+// Far-part kernels: record preparation (points, quadrature nodes), the per-node
+// gather / scatter of the standalone transforms, and the sum of f for the xi = 0 term.
+// The stencil operations of the matvec are the tiled kernels of node.cu.
 #include "far.cuh"
 #include "sbd.h"
 
@@ -43,9 +44,9 @@ __global__ void prepare_points_kernel(const double* __restrict__ z, long n, doub
     const double ux = (z[2 * i] - cx) / h + 0.5 * m;
     const double uy = (z[2 * i + 1] - cy) / h + 0.5 * m;
     const double fx = floor(ux), fy = floor(uy);
-    PointRec<T> r;
-    r.cell = make_int2(static_cast<int>(fx) - P / 2 + 1, static_cast<int>(fy) - P / 2 + 1);
-    r.frac = mk<T>(static_cast<T>(ux - fx), static_cast<T>(uy - fy));
+    PointRec<T> r;   // (row, column) of the spreading grid = (y, x)
+    r.cell = make_int2(static_cast<int>(fy) - P / 2 + 1, static_cast<int>(fx) - P / 2 + 1);
+    r.frac = mk<T>(static_cast<T>(uy - fy), static_cast<T>(ux - fx));
     out[i] = r;
 }
 
@@ -89,60 +90,10 @@ __global__ void prepare_nodes_kernel(const int* __restrict__ start, const double
 }
 
 template <typename T, int PMAX>
-__global__ void spread_kernel(const PointRec<T>* __restrict__ pts, long n, const void* __restrict__ f, bool fc,
-                              int nrhs, FarGeom g, cx_t<T>* __restrict__ grid) {
-    const long i = blockIdx.x * static_cast<long>(blockDim.x) + threadIdx.x;
-    if (i >= n) return;
-    const PointRec<T> p = pts[i];
-    T wx[PMAX], wy[PMAX];
-    weights<T, PMAX>(p.frac.x, g.P, static_cast<T>(g.beta_s), wx);
-    weights<T, PMAX>(p.frac.y, g.P, static_cast<T>(g.beta_s), wy);
-    const long mm = static_cast<long>(g.m) * g.m;
-    for (int r = 0; r < nrhs; ++r) {
-        const cx_t<T> fv = load_f<T>(f, fc, r * n + i);
-        cx_t<T>* base = grid + r * mm;
-        for (int b = 0; b < g.P; ++b) {
-            const cx_t<T> vy = cscale(fv, wy[b]);
-            cx_t<T>* row = base + static_cast<long>(p.cell.y + b) * g.m + p.cell.x;
-            for (int a = 0; a < g.P; ++a) atomic_add_cx<T>(row + a, cscale(vy, wx[a]));
-        }
-    }
-}
-
-template <typename T, int PMAX>
-__global__ void node_step_kernel(const NodeRec<T>* __restrict__ nodes, long n_xi, const cx_t<T>* __restrict__ omega,
-                                 int nrhs, FarGeom g, const cx_t<T>* __restrict__ kin, cx_t<T>* __restrict__ kout) {
-    const long nu = blockIdx.x * static_cast<long>(blockDim.x) + threadIdx.x;
-    if (nu >= n_xi) return;
-    const NodeRec<T> q = nodes[nu];
-    T wx[PMAX], wy[PMAX];
-    weights<T, PMAX>(q.frac.x, g.P, static_cast<T>(g.beta_k), wx);
-    weights<T, PMAX>(q.frac.y, g.P, static_cast<T>(g.beta_k), wy);
-    const cx_t<T> om = omega[q.circle];
-    const long kk = static_cast<long>(g.nk) * g.nk;
-    for (int r = 0; r < nrhs; ++r) {
-        const cx_t<T>* src = kin + r * kk;
-        cx_t<T> acc = mk<T>(0, 0);
-        for (int a = 0; a < g.P; ++a) {
-            const cx_t<T>* row = src + static_cast<long>(q.cell.x + a) * g.nk + q.cell.y;
-            cx_t<T> s = mk<T>(0, 0);
-            for (int b = 0; b < g.P; ++b) s = cadd(s, cscale(row[b], wy[b]));
-            acc = cadd(acc, cscale(s, wx[a]));
-        }
-        acc = cmul(acc, om);
-        cx_t<T>* dst = kout + r * kk;
-        for (int a = 0; a < g.P; ++a) {
-            const cx_t<T> va = cscale(acc, wx[a]);
-            cx_t<T>* row = dst + static_cast<long>(q.cell.x + a) * g.nk + q.cell.y;
-            for (int b = 0; b < g.P; ++b) atomic_add_cx<T>(row + b, cscale(va, wy[b]));
-        }
-    }
-}
-
-template <typename T, int PMAX>
 __global__ void node_gather_kernel(const NodeRec<T>* __restrict__ nodes, long n_xi, const T* __restrict__ cs,
                                    FarGeom g, const cx_t<T>* __restrict__ kin, double2* __restrict__ out,
                                    NodeFrame fr) {
+    // records may be in tile order: fr.perm maps a record to its canonical node index
     const long nu = blockIdx.x * static_cast<long>(blockDim.x) + threadIdx.x;
     if (nu >= n_xi) return;
     const NodeRec<T> q = nodes[nu];
@@ -158,11 +109,12 @@ __global__ void node_gather_kernel(const NodeRec<T>* __restrict__ nodes, long n_
     }
     acc = cscale(acc, cs[q.circle]);
     // the grids hold z - c: multiply by exp(-i c.xi) to return sum_l exp(-i z_l.xi) f_l
-    const double2 xi = node_xi(fr.start, fr.radius, fr.M, fr.n_circles, nu);
+    const long canon = fr.perm ? fr.perm[nu] : nu;
+    const double2 xi = node_xi(fr.start, fr.radius, fr.M, fr.n_circles, canon);
     double sn, co;
     sincos(fr.cx * xi.x + fr.cy * xi.y, &sn, &co);
     const double ar = acc.x, ai = acc.y;
-    out[nu] = make_double2(ar * co + ai * sn, ai * co - ar * sn);
+    out[canon] = make_double2(ar * co + ai * sn, ai * co - ar * sn);
 }
 
 template <typename T, int PMAX>
@@ -175,9 +127,10 @@ __global__ void node_scatter_kernel(const NodeRec<T>* __restrict__ nodes, long n
     T wx[PMAX], wy[PMAX];
     weights<T, PMAX>(q.frac.x, g.P, static_cast<T>(g.beta_k), wx);
     weights<T, PMAX>(q.frac.y, g.P, static_cast<T>(g.beta_k), wy);
-    double2 v = in[nu];
+    const long canon = fr.perm ? fr.perm[nu] : nu;
+    double2 v = in[canon];
     // q_l = sum_nu exp(i (z_l - c).xi) [exp(i c.xi) ghat_nu]
-    const double2 xi = node_xi(fr.start, fr.radius, fr.M, fr.n_circles, nu);
+    const double2 xi = node_xi(fr.start, fr.radius, fr.M, fr.n_circles, canon);
     double sn, co;
     sincos(fr.cx * xi.x + fr.cy * xi.y, &sn, &co);
     v = make_double2(v.x * co - v.y * sn, v.x * sn + v.y * co);
@@ -186,35 +139,6 @@ __global__ void node_scatter_kernel(const NodeRec<T>* __restrict__ nodes, long n
         const cx_t<T> va = cscale(acc, wx[a]);
         cx_t<T>* row = kout + static_cast<long>(q.cell.x + a) * g.nk + q.cell.y;
         for (int b = 0; b < g.P; ++b) atomic_add_cx<T>(row + b, cscale(va, wy[b]));
-    }
-}
-
-template <typename T, int PMAX>
-__global__ void interp_kernel(const PointRec<T>* __restrict__ pts, long n, int nrhs, FarGeom g,
-                              const cx_t<T>* __restrict__ grid, double2 w0, const double2* __restrict__ sumf,
-                              void* __restrict__ q, bool qc) {
-    const long i = blockIdx.x * static_cast<long>(blockDim.x) + threadIdx.x;
-    if (i >= n) return;
-    const PointRec<T> p = pts[i];
-    T wx[PMAX], wy[PMAX];
-    weights<T, PMAX>(p.frac.x, g.P, static_cast<T>(g.beta_s), wx);
-    weights<T, PMAX>(p.frac.y, g.P, static_cast<T>(g.beta_s), wy);
-    const long mm = static_cast<long>(g.m) * g.m;
-    for (int r = 0; r < nrhs; ++r) {
-        const cx_t<T>* base = grid + r * mm;
-        double ar = 0.0, ai = 0.0;
-        for (int b = 0; b < g.P; ++b) {
-            const cx_t<T>* row = base + static_cast<long>(p.cell.y + b) * g.m + p.cell.x;
-            cx_t<T> s = mk<T>(0, 0);
-            for (int a = 0; a < g.P; ++a) s = cadd(s, cscale(row[a], wx[a]));
-            ar += static_cast<double>(s.x) * wy[b];
-            ai += static_cast<double>(s.y) * wy[b];
-        }
-        const double2 sf = sumf[r];
-        ar += w0.x * sf.x - w0.y * sf.y;
-        ai += w0.x * sf.y + w0.y * sf.x;
-        if (qc) static_cast<double2*>(q)[r * n + i] = make_double2(ar, ai);
-        else static_cast<double*>(q)[r * n + i] = ar;
     }
 }
 
@@ -268,26 +192,6 @@ int far_prepare_nodes(const int* circle_start, const double* radius, const int* 
 template <typename T> constexpr int pmax() { return sizeof(T) == 8 ? 32 : 16; }
 
 template <typename T>
-int far_spread(const PointRec<T>* pts, long n, const void* f, bool f_complex, int nrhs,
-               const FarGeom& g, cx_t<T>* grid, cudaStream_t s) {
-    SBD_CUDA_TRY(cudaMemsetAsync(grid, 0, sizeof(cx_t<T>) * static_cast<size_t>(g.m) * g.m * nrhs, s));
-    if (n <= 0) return SBD_OK;
-    spread_kernel<T, pmax<T>()><<<blocks_for(n), kThreads, 0, s>>>(pts, n, f, f_complex, nrhs, g, grid);
-    SBD_LAUNCH_CHECK();
-    return SBD_OK;
-}
-
-template <typename T>
-int far_node_step(const NodeRec<T>* nodes, long n_xi, const cx_t<T>* omega_c, int nrhs,
-                  const FarGeom& g, const cx_t<T>* kin, cx_t<T>* kout, cudaStream_t s) {
-    SBD_CUDA_TRY(cudaMemsetAsync(kout, 0, sizeof(cx_t<T>) * static_cast<size_t>(g.nk) * g.nk * nrhs, s));
-    if (n_xi <= 0) return SBD_OK;
-    node_step_kernel<T, pmax<T>()><<<blocks_for(n_xi), kThreads, 0, s>>>(nodes, n_xi, omega_c, nrhs, g, kin, kout);
-    SBD_LAUNCH_CHECK();
-    return SBD_OK;
-}
-
-template <typename T>
 int far_node_gather(const NodeRec<T>* nodes, long n_xi, const T* cscale_c, const FarGeom& g,
                     const cx_t<T>* kin, double2* out, const NodeFrame& fr, cudaStream_t s) {
     if (n_xi <= 0) return SBD_OK;
@@ -306,15 +210,6 @@ int far_node_scatter(const NodeRec<T>* nodes, long n_xi, const T* cscale_c, cons
     return SBD_OK;
 }
 
-template <typename T>
-int far_interp(const PointRec<T>* pts, long n, int nrhs, const FarGeom& g, const cx_t<T>* grid,
-               double2 w0, const double2* sumf, void* q, bool q_complex, cudaStream_t s) {
-    if (n <= 0) return SBD_OK;
-    interp_kernel<T, pmax<T>()><<<blocks_for(n), kThreads, 0, s>>>(pts, n, nrhs, g, grid, w0, sumf, q, q_complex);
-    SBD_LAUNCH_CHECK();
-    return SBD_OK;
-}
-
 int far_sum(const void* f, bool f_complex, long n, int nrhs, double2* sumf, cudaStream_t s) {
     SBD_CUDA_TRY(cudaMemsetAsync(sumf, 0, sizeof(double2) * nrhs, s));
     if (n <= 0) return SBD_OK;
@@ -329,16 +224,11 @@ int far_sum(const void* f, bool f_complex, long n, int nrhs, double2* sumf, cuda
                                        cudaStream_t);                                                     \
     template int far_prepare_nodes<T>(const int*, const double*, const int*, int, long, double, int, int, \
                                       NodeRec<T>*, cudaStream_t);                                         \
-    template int far_spread<T>(const PointRec<T>*, long, const void*, bool, int, const FarGeom&, cx_t<T>*, \
-                               cudaStream_t);                                                             \
-    template int far_node_step<T>(const NodeRec<T>*, long, const cx_t<T>*, int, const FarGeom&,          \
-                                  const cx_t<T>*, cx_t<T>*, cudaStream_t);                                \
     template int far_node_gather<T>(const NodeRec<T>*, long, const T*, const FarGeom&, const cx_t<T>*,    \
                                     double2*, const NodeFrame&, cudaStream_t);                            \
     template int far_node_scatter<T>(const NodeRec<T>*, long, const T*, const FarGeom&, const double2*,   \
                                      cx_t<T>*, const NodeFrame&, cudaStream_t);                           \
-    template int far_interp<T>(const PointRec<T>*, long, int, const FarGeom&, const cx_t<T>*, double2,   \
-                               const double2*, void*, bool, cudaStream_t);
+
 SBD_FAR_INST(float)
 SBD_FAR_INST(double)
 

@@ -16,7 +16,8 @@ struct FarGeom {
     double beta_k;    // node weight exp(-beta_k d^2)
 };
 
-// Point i: spreading stencil starts at cell (cell.x, cell.y); frac = position - floor(position).
+// Point i: spreading stencil starts at (row, column) = cell of the spreading grid, whose
+// rows are y; frac = position - floor(position) in the same (row, column) order.
 template <typename T> struct PointRec { int2 cell; cx_t<T> frac; };
 // Node: stencil start cell in the frequency grid, fraction, circle index.
 template <typename T> struct NodeRec { int2 cell; cx_t<T> frac; int circle; int pad; };
@@ -29,14 +30,6 @@ template <typename T>
 int far_prepare_nodes(const int* circle_start, const double* radius, const int* M, int n_circles,
                       long n_xi, double deta, int nk, int P, NodeRec<T>* out, cudaStream_t s);
 
-// f (complex128 or float64, nrhs x N) -> spreading grids (nrhs x m x m, zeroed here).
-template <typename T>
-int far_spread(const PointRec<T>* pts, long n, const void* f, bool f_complex, int nrhs,
-               const FarGeom& g, cx_t<T>* grid, cudaStream_t s);
-// Gather at every node, multiply by the circle weight, scatter into kout (zeroed here).
-template <typename T>
-int far_node_step(const NodeRec<T>* nodes, long n_xi, const cx_t<T>* omega_c, int nrhs,
-                  const FarGeom& g, const cx_t<T>* kin, cx_t<T>* kout, cudaStream_t s);
 // Circle tables and the centre c of the point set, to place the canonical nodes in
 // absolute coordinates (the grids hold z - c).
 struct NodeFrame {
@@ -45,6 +38,7 @@ struct NodeFrame {
     const int* M;
     int n_circles;
     double cx, cy;
+    const int* perm;   // record -> canonical node index (null: records in canonical order)
 };
 // Gather only: out[nu] = exp(-i c.xi_nu) c_nu sum_stencil w K  (complex128), c_nu = circle scale.
 template <typename T>
@@ -54,10 +48,6 @@ int far_node_gather(const NodeRec<T>* nodes, long n_xi, const T* cscale, const F
 template <typename T>
 int far_node_scatter(const NodeRec<T>* nodes, long n_xi, const T* cscale, const FarGeom& g,
                      const double2* in, cx_t<T>* kout, const NodeFrame& fr, cudaStream_t s);
-// Interpolate the grids at the points: q (nrhs x N) = interp + w0 * sumf[r]; real or complex out.
-template <typename T>
-int far_interp(const PointRec<T>* pts, long n, int nrhs, const FarGeom& g, const cx_t<T>* grid,
-               double2 w0, const double2* sumf, void* q, bool q_complex, cudaStream_t s);
 // sumf[r] = sum_l f[r][l] (FP64).
 int far_sum(const void* f, bool f_complex, long n, int nrhs, double2* sumf, cudaStream_t s);
 

@@ -1,0 +1,307 @@
+// Tiled gather / scatter with separable Gaussian stencils on a square grid.
+//
+// Used for the three stencil operations of the far part (Sec. 1 steps (i)-(iii)):
+//   spreading      points -> spreading grid          (scatter, values f)
+//   node step      frequency grid -> nodes -> frequency grid
+//                  (gather, weight by omega'_p of the node's circle, scatter)
+//   interpolation  spreading grid -> points          (gather)
+// Records (points or nodes) carry the first cell (cx, cy) of their P x P stencil and
+// the fractional position; they are sorted by the 64 x 64 tile holding that cell.
+//   gather:  one CTA per tile copies the tile plus a (P-1) halo into shared memory;
+//            a group of 16 (or 32) lanes handles one record at a time, lane = stencil
+//            column, rows summed in registers, columns reduced by shuffles.
+//   scatter: one CTA per output tile accumulates, in shared memory, the clipped
+//            stencils of every record whose stencil meets the tile (records of the
+//            tile and of the three tiles before it), then stores the tile once.
+// No global atomics, and the output grid needs no clearing.
+#include "near.cuh"
+#include "node.cuh"
+#include "sbd.h"
+
+namespace sbd {
+
+namespace {
+
+template <typename T> __device__ __forceinline__ T gexp(T x);
+template <> __device__ __forceinline__ float gexp<float>(float x) { return expf(x); }
+template <> __device__ __forceinline__ double gexp<double>(double x) { return exp(x); }
+
+template <typename Rec>
+__global__ void tile_count_kernel(const Rec* __restrict__ rec, long n, int ntx, long long* __restrict__ count) {
+    const long i = blockIdx.x * static_cast<long>(blockDim.x) + threadIdx.x;
+    if (i >= n) return;
+    const int2 c = rec[i].cell;
+    const int t = (c.x / kNodeTile) * ntx + (c.y / kNodeTile);
+    atomicAdd(reinterpret_cast<unsigned long long*>(&count[t]), 1ULL);
+}
+
+template <typename Rec>
+__global__ void tile_scatter_kernel(const Rec* __restrict__ in, long n, int ntx, const long long* __restrict__ start,
+                                    int* __restrict__ cursor, Rec* __restrict__ out, int* __restrict__ perm) {
+    const long i = blockIdx.x * static_cast<long>(blockDim.x) + threadIdx.x;
+    if (i >= n) return;
+    const Rec r = in[i];
+    const int t = (r.cell.x / kNodeTile) * ntx + (r.cell.y / kNodeTile);
+    const long long pos = start[t] + atomicAdd(&cursor[t], 1);
+    out[pos] = r;
+    perm[pos] = static_cast<int>(i);
+}
+
+// Stencil weights of the group's lane: w(sub - P/2 + 1 - frac) along both dimensions.
+template <typename T>
+__device__ __forceinline__ void lane_weights(int sub, int P, T beta, T fx, T fy, T& wx, T& wy) {
+    wx = 0;
+    wy = 0;
+    if (sub < P) {
+        const T dx = static_cast<T>(sub - P / 2 + 1) - fx;
+        const T dy = static_cast<T>(sub - P / 2 + 1) - fy;
+        wx = gexp<T>(-beta * dx * dx);
+        wy = gexp<T>(-beta * dy * dy);
+    }
+}
+
+// --- value sources / sinks -------------------------------------------------------------------
+
+template <typename T> struct NodeIO {       // node step: gather -> * omega'[circle] -> ghat[i]
+    const cx_t<T>* omega;
+    cx_t<T>* ghat;
+    __device__ __forceinline__ void put(long i, const NodeRec<T>& r, cx_t<T> v) const {
+        ghat[i] = cmul(v, omega[r.circle]);
+    }
+};
+template <typename T> struct NodeVal {      // node step scatter values
+    const cx_t<T>* ghat;
+    __device__ __forceinline__ cx_t<T> get(long i) const { return ghat[i]; }
+};
+template <typename T> struct PointVal {     // spreading values f[perm[i]] (float64 or complex128)
+    const void* f;
+    const int* perm;
+    bool fc;
+    __device__ __forceinline__ cx_t<T> get(long i) const {
+        const long j = perm[i];
+        if (fc) {
+            const double2 v = static_cast<const double2*>(f)[j];
+            return mk<T>(static_cast<T>(v.x), static_cast<T>(v.y));
+        }
+        return mk<T>(static_cast<T>(static_cast<const double*>(f)[j]), static_cast<T>(0));
+    }
+};
+template <typename T> struct PointOut {     // interpolation: q[perm[i]] = v + w0 * sumf
+    void* q;
+    const int* perm;
+    bool qc;
+    double2 w0;
+    const double2* sumf;
+    __device__ __forceinline__ void put(long i, const PointRec<T>&, cx_t<T> v) const {
+        const long j = perm[i];
+        const double2 sf = *sumf;
+        const double re = static_cast<double>(v.x) + w0.x * sf.x - w0.y * sf.y;
+        const double im = static_cast<double>(v.y) + w0.x * sf.y + w0.y * sf.x;
+        if (qc) static_cast<double2*>(q)[j] = make_double2(re, im);
+        else static_cast<double*>(q)[j] = re;
+    }
+};
+
+// --- kernels ----------------------------------------------------------------------------------------
+
+template <typename T, int G, typename Rec, typename Out>
+__global__ void __launch_bounds__(256) gather_tiles_kernel(
+    const Rec* __restrict__ rec, const long long* __restrict__ tile_start, int ntx, int n, int P, T beta,
+    const cx_t<T>* __restrict__ grid, Out out) {
+    using C = cx_t<T>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* s = reinterpret_cast<C*>(smem_raw);
+    const int tile = blockIdx.x;
+    const long long b0 = tile_start[tile], b1 = tile_start[tile + 1];
+    if (b0 == b1) return;
+    const int ox = (tile / ntx) * kNodeTile, oy = (tile % ntx) * kNodeTile;
+    const int W = kNodeTile + P - 1;
+    const int rows = min(W, n - ox), cols = min(W, n - oy);
+    for (int idx = threadIdx.x; idx < W * W; idx += blockDim.x) {
+        const int r = idx / W, c = idx - r * W;
+        C v = mk<T>(0, 0);
+        if (r < rows && c < cols) v = grid[static_cast<long>(ox + r) * n + oy + c];
+        s[idx] = v;
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int sub = lane % G;
+    const unsigned gmask = G == 32 ? 0xffffffffu : (0xffffu << (lane & 16));
+    const int group = threadIdx.x / G, ngroups = blockDim.x / G;
+    for (long long i = b0 + group; i < b1; i += ngroups) {
+        const Rec q = rec[i];
+        const int rx = q.cell.x - ox, ry = q.cell.y - oy;
+        T wx, wy;
+        lane_weights<T>(sub, P, beta, q.frac.x, q.frac.y, wx, wy);
+        T sr = 0, si = 0;
+        const C* col = s + static_cast<long>(rx) * W + ry + sub;
+        for (int a = 0; a < P; ++a) {
+            const T w = __shfl_sync(gmask, wx, a, G);
+            if (sub < P) {
+                const C v = col[a * W];
+                sr += w * v.x;
+                si += w * v.y;
+            }
+        }
+        sr *= wy;
+        si *= wy;
+#pragma unroll
+        for (int o = G / 2; o > 0; o >>= 1) {
+            sr += __shfl_xor_sync(gmask, sr, o, G);
+            si += __shfl_xor_sync(gmask, si, o, G);
+        }
+        if (sub == 0) out.put(i, q, mk<T>(sr, si));
+    }
+}
+
+template <typename T, int G, typename Rec, typename Val>
+__global__ void __launch_bounds__(256) scatter_tiles_kernel(
+    const Rec* __restrict__ rec, const long long* __restrict__ tile_start, int ntx, int n, int P, T beta,
+    Val val, cx_t<T>* __restrict__ grid) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* acc = reinterpret_cast<T*>(smem_raw);          // [kNodeTile][kNodeTile][2]
+    const int tile = blockIdx.x;
+    const int tx = tile / ntx, ty = tile % ntx;
+    const int ox = tx * kNodeTile, oy = ty * kNodeTile;
+    for (int idx = threadIdx.x; idx < 2 * kNodeTile * kNodeTile; idx += blockDim.x) acc[idx] = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int sub = lane % G;
+    const unsigned gmask = G == 32 ? 0xffffffffu : (0xffffu << (lane & 16));
+    const int group = threadIdx.x / G, ngroups = blockDim.x / G;
+    for (int sx = max(tx - 1, 0); sx <= tx; ++sx) {
+        for (int sy = max(ty - 1, 0); sy <= ty; ++sy) {
+            const int st = sx * ntx + sy;
+            const long long b0 = tile_start[st], b1 = tile_start[st + 1];
+            for (long long i = b0 + group; i < b1; i += ngroups) {
+                const Rec q = rec[i];
+                const int rx = q.cell.x - ox, ry = q.cell.y - oy;   // stencil start relative to this tile
+                if (rx + P <= 0 || ry + P <= 0) continue;           // uniform across the group
+                T wx, wy;
+                lane_weights<T>(sub, P, beta, q.frac.x, q.frac.y, wx, wy);
+                const cx_t<T> g = val.get(i);
+                const int c = ry + sub;
+                const bool col_ok = sub < P && c >= 0 && c < kNodeTile;
+                const T gr = g.x * wy, gi = g.y * wy;
+                for (int a = 0; a < P; ++a) {
+                    const T w = __shfl_sync(gmask, wx, a, G);
+                    const int r = rx + a;
+                    if (col_ok && r >= 0 && r < kNodeTile) {
+                        T* cell = acc + 2 * (r * kNodeTile + c);
+                        atomicAdd(cell, gr * w);
+                        atomicAdd(cell + 1, gi * w);
+                    }
+                }
+            }
+        }
+    }
+    __syncthreads();
+    const int rows = min(kNodeTile, n - ox), cols = min(kNodeTile, n - oy);
+    for (int idx = threadIdx.x; idx < kNodeTile * kNodeTile; idx += blockDim.x) {
+        const int r = idx / kNodeTile, c = idx - r * kNodeTile;
+        if (r < rows && c < cols) grid[static_cast<long>(ox + r) * n + oy + c] = mk<T>(acc[2 * idx], acc[2 * idx + 1]);
+    }
+}
+
+inline int tiles_per_side(int n) { return (n + kNodeTile - 1) / kNodeTile; }
+
+template <typename T, typename Rec, typename Out>
+int launch_gather(const Rec* rec, const long long* tile_start, int n, int P, double beta, const cx_t<T>* grid,
+                  Out out, cudaStream_t s) {
+    const int ntx = tiles_per_side(n);
+    const size_t W = kNodeTile + P - 1;
+    const size_t smem = W * W * sizeof(cx_t<T>);
+    const unsigned nt = static_cast<unsigned>(ntx) * ntx;
+    if (P <= 16) {
+        auto k = gather_tiles_kernel<T, 16, Rec, Out>;
+        SBD_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
+        k<<<nt, 256, smem, s>>>(rec, tile_start, ntx, n, P, static_cast<T>(beta), grid, out);
+    } else {
+        auto k = gather_tiles_kernel<T, 32, Rec, Out>;
+        SBD_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
+        k<<<nt, 256, smem, s>>>(rec, tile_start, ntx, n, P, static_cast<T>(beta), grid, out);
+    }
+    SBD_LAUNCH_CHECK();
+    return SBD_OK;
+}
+
+template <typename T, typename Rec, typename Val>
+int launch_scatter(const Rec* rec, const long long* tile_start, int n, int P, double beta, Val val,
+                   cx_t<T>* grid, cudaStream_t s) {
+    const int ntx = tiles_per_side(n);
+    const size_t smem = 2 * sizeof(T) * kNodeTile * kNodeTile;
+    const unsigned nt = static_cast<unsigned>(ntx) * ntx;
+    if (P <= 16) {
+        auto k = scatter_tiles_kernel<T, 16, Rec, Val>;
+        SBD_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
+        k<<<nt, 256, smem, s>>>(rec, tile_start, ntx, n, P, static_cast<T>(beta), val, grid);
+    } else {
+        auto k = scatter_tiles_kernel<T, 32, Rec, Val>;
+        SBD_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
+        k<<<nt, 256, smem, s>>>(rec, tile_start, ntx, n, P, static_cast<T>(beta), val, grid);
+    }
+    SBD_LAUNCH_CHECK();
+    return SBD_OK;
+}
+
+}  // namespace
+
+template <typename Rec>
+int tile_sort(const Rec* in, long n_rec, int n, Rec* sorted, int* perm, long long* tile_start, cudaStream_t s) {
+    const int ntx = tiles_per_side(n);
+    const long ntiles = static_cast<long>(ntx) * ntx;
+    int* cursor = nullptr;
+    SBD_CUDA_TRY(cudaMemsetAsync(tile_start, 0, sizeof(long long) * (ntiles + 1), s));
+    SBD_CUDA_TRY(cudaMallocAsync(&cursor, sizeof(int) * ntiles, s));
+    SBD_CUDA_TRY(cudaMemsetAsync(cursor, 0, sizeof(int) * ntiles, s));
+    const unsigned nb = static_cast<unsigned>((n_rec + 255) / 256);
+    if (n_rec > 0) {
+        tile_count_kernel<Rec><<<nb, 256, 0, s>>>(in, n_rec, ntx, tile_start);
+        SBD_LAUNCH_CHECK();
+    }
+    long long total = 0;
+    int rc = scan_exclusive_i64(tile_start, ntiles + 1, &total, s);
+    if (rc) return rc;
+    if (n_rec > 0) {
+        tile_scatter_kernel<Rec><<<nb, 256, 0, s>>>(in, n_rec, ntx, tile_start, cursor, sorted, perm);
+        SBD_LAUNCH_CHECK();
+    }
+    SBD_CUDA_TRY(cudaFreeAsync(cursor, s));
+    return SBD_OK;
+}
+
+template <typename T>
+int node_step_tiled(const NodeRec<T>* nodes, const long long* tile_start, int nk, int P, double beta,
+                    const cx_t<T>* omega, const cx_t<T>* kin, cx_t<T>* ghat, cx_t<T>* kout, cudaStream_t s) {
+    int rc = launch_gather<T>(nodes, tile_start, nk, P, beta, kin, NodeIO<T>{omega, ghat}, s);
+    if (rc) return rc;
+    return launch_scatter<T>(nodes, tile_start, nk, P, beta, NodeVal<T>{ghat}, kout, s);
+}
+
+template <typename T>
+int spread_tiled(const PointRec<T>* pts, const int* perm, const long long* tile_start, int m, int P, double beta,
+                 const void* f, bool f_complex, cx_t<T>* grid, cudaStream_t s) {
+    return launch_scatter<T>(pts, tile_start, m, P, beta, PointVal<T>{f, perm, f_complex}, grid, s);
+}
+
+template <typename T>
+int interp_tiled(const PointRec<T>* pts, const int* perm, const long long* tile_start, int m, int P, double beta,
+                 const cx_t<T>* grid, double2 w0, const double2* sumf, void* q, bool q_complex, cudaStream_t s) {
+    return launch_gather<T>(pts, tile_start, m, P, beta, grid, PointOut<T>{q, perm, q_complex, w0, sumf}, s);
+}
+
+#define SBD_NODE_INST(T)                                                                                     \
+    template int tile_sort<NodeRec<T>>(const NodeRec<T>*, long, int, NodeRec<T>*, int*, long long*,          \
+                                       cudaStream_t);                                                        \
+    template int tile_sort<PointRec<T>>(const PointRec<T>*, long, int, PointRec<T>*, int*, long long*,       \
+                                        cudaStream_t);                                                       \
+    template int node_step_tiled<T>(const NodeRec<T>*, const long long*, int, int, double, const cx_t<T>*,   \
+                                    const cx_t<T>*, cx_t<T>*, cx_t<T>*, cudaStream_t);                       \
+    template int spread_tiled<T>(const PointRec<T>*, const int*, const long long*, int, int, double,         \
+                                 const void*, bool, cx_t<T>*, cudaStream_t);                                 \
+    template int interp_tiled<T>(const PointRec<T>*, const int*, const long long*, int, int, double,         \
+                                 const cx_t<T>*, double2, const double2*, void*, bool, cudaStream_t);
+SBD_NODE_INST(float)
+SBD_NODE_INST(double)
+
+}  // namespace sbd

@@ -1,0 +1,33 @@
+// Tiled gather / scatter with separable Gaussian stencils (spreading, node step,
+// interpolation); see node.cu.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+#include "far.cuh"
+
+namespace sbd {
+
+constexpr int kNodeTile = 64;   // grid tile side (cells); must be >= stencil width - 1
+
+// Sort records by the tile of their stencil start on an n x n grid; perm[sorted] =
+// original index; tile_start has ceil(n/64)^2 + 1 entries.
+template <typename Rec>
+int tile_sort(const Rec* in, long n_rec, int n, Rec* sorted, int* perm, long long* tile_start, cudaStream_t s);
+
+// kout (nk x nk, fully written) = scatter(omega' * gather(kin)); ghat is n_xi scratch.
+template <typename T>
+int node_step_tiled(const NodeRec<T>* nodes, const long long* tile_start, int nk, int P, double beta,
+                    const cx_t<T>* omega, const cx_t<T>* kin, cx_t<T>* ghat, cx_t<T>* kout, cudaStream_t s);
+
+// grid (m x m, fully written) = spreading of f (float64 or complex128, original order).
+template <typename T>
+int spread_tiled(const PointRec<T>* pts, const int* perm, const long long* tile_start, int m, int P, double beta,
+                 const void* f, bool f_complex, cx_t<T>* grid, cudaStream_t s);
+
+// q[perm[i]] = interpolation of grid at point i + w0 * sumf[0] (float64 or complex128 out).
+template <typename T>
+int interp_tiled(const PointRec<T>* pts, const int* perm, const long long* tile_start, int m, int P, double beta,
+                 const cx_t<T>* grid, double2 w0, const double2* sumf, void* q, bool q_complex, cudaStream_t s);
+
+}  // namespace sbd
