@@ -72,8 +72,12 @@ typedef struct {
     int32_t fixed_P;     /* > 0: use exactly this many Bessel terms; 0: the P search of Sec. 1 */
     double  nufft_tol;   /* > 0: tolerance of each type-3 transform; 0: automatic from eps */
     int32_t max_nrhs;    /* largest nrhs a matvec will use (0 = 1); sizes the workspace */
-    int32_t flags;       /* reserved, must be 0 */
+    int32_t flags;       /* 0, or SBD_FLAG_* bits */
 } sbd_options;
+
+/* sbd_options.flags: use a Gaussian window at the quadrature nodes instead of the
+ * default ES (exponential of semicircle) window, which needs about half the width. */
+#define SBD_FLAG_GAUSSIAN_NODES 1
 
 /* Plan summary (sbd_plan_info). */
 typedef struct {

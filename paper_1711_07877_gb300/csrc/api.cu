@@ -164,9 +164,11 @@ template <typename T>
 int build_far(sbd_plan_s* p, cudaStream_t s) {
     const NufftParams& np = p->np;
     const SbdFit& fit = p->fit;
-    p->geom.P = np.Pk;
+    p->geom.Ps = np.Ps;
+    p->geom.Pk = np.Pk;
     p->geom.m = np.m;
     p->geom.nk = np.nk;
+    p->geom.kwin = np.kwin;
     p->geom.beta_s = np.beta_s;
     p->geom.beta_k = np.beta_k;
     PointRec<T>* pts0 = nullptr;
@@ -271,23 +273,23 @@ int far_apply(sbd_plan_s* p, const void* f, void* q, int nrhs, cudaStream_t s) {
         const void* fr = static_cast<const char*>(f) + esz * p->n * r;
         void* qr = static_cast<char*>(q) + esz * p->n * r;
         StepTimer t1(p, s, SBD_STAGE_SPREAD);
-        if ((rc = spread_tiled<T>(static_cast<const PointRec<T>*>(p->pts), p->pt_perm, p->pt_tile_start, p->np.m,
-                                  p->np.Ps, p->np.beta_s, fr, cplx_io, X, s))) return rc;
+        if ((rc = spread_tiled<T>(static_cast<const PointRec<T>*>(p->pts), p->pt_perm, p->pt_tile_start, p->geom,
+                                  fr, cplx_io, X, s))) return rc;
         t1.end();
         StepTimer t2(p, s, SBD_STAGE_FFT_FWD);
         if ((rc = forward_fft<T>(p, X, A, C, B, s))) return rc;
         t2.end();
         StepTimer t3(p, s, SBD_STAGE_NODE);
-        if ((rc = node_step_tiled<T>(static_cast<const NodeRec<T>*>(p->nodes), p->node_tile_start, p->np.nk,
-                                     p->np.Pk, p->np.beta_k, static_cast<const cx_t<T>*>(p->omega_c), B,
-                                     static_cast<cx_t<T>*>(p->ghat), C, s))) return rc;
+        if ((rc = node_step_tiled<T>(static_cast<const NodeRec<T>*>(p->nodes), p->node_tile_start, p->geom,
+                                     static_cast<const cx_t<T>*>(p->omega_c), B, static_cast<cx_t<T>*>(p->ghat), C,
+                                     s))) return rc;
         t3.end();
         StepTimer t4(p, s, SBD_STAGE_FFT_INV);
         if ((rc = inverse_fft<T>(p, C, A, B, X, s))) return rc;
         t4.end();
         StepTimer t5(p, s, SBD_STAGE_INTERP);
-        if ((rc = interp_tiled<T>(static_cast<const PointRec<T>*>(p->pts), p->pt_perm, p->pt_tile_start, p->np.m,
-                                  p->np.Ps, p->np.beta_s, X, w0, p->sumf + r, qr, cplx_io, s))) return rc;
+        if ((rc = interp_tiled<T>(static_cast<const PointRec<T>*>(p->pts), p->pt_perm, p->pt_tile_start, p->geom, X,
+                                  w0, p->sumf + r, qr, cplx_io, s))) return rc;
         t5.end();
     }
     return SBD_OK;
@@ -299,8 +301,8 @@ int nufft_minus_impl(sbd_plan_s* p, const void* f, void* fhat, cudaStream_t s) {
     auto* A = static_cast<cx_t<T>*>(p->wsA);
     auto* B = static_cast<cx_t<T>*>(p->wsB);
     auto* C = static_cast<cx_t<T>*>(p->wsC);
-    int rc = spread_tiled<T>(static_cast<const PointRec<T>*>(p->pts), p->pt_perm, p->pt_tile_start, p->np.m,
-                             p->np.Ps, p->np.beta_s, f, true, X, s);
+    int rc = spread_tiled<T>(static_cast<const PointRec<T>*>(p->pts), p->pt_perm, p->pt_tile_start, p->geom, f,
+                             true, X, s);
     if (rc) return rc;
     if ((rc = forward_fft<T>(p, X, A, C, B, s))) return rc;
     const NodeFrame fr{p->circle_start, p->circle_radius, p->circle_M, p->fit.n_circles, p->np.cx, p->np.cy,
@@ -323,8 +325,8 @@ int nufft_plus_impl(sbd_plan_s* p, const void* ghat, void* q, cudaStream_t s) {
     if (rc) return rc;
     if ((rc = inverse_fft<T>(p, C, A, B, X, s))) return rc;
     SBD_CUDA_TRY(cudaMemsetAsync(p->zero2, 0, sizeof(double2), s));
-    return interp_tiled<T>(static_cast<const PointRec<T>*>(p->pts), p->pt_perm, p->pt_tile_start, p->np.m, p->np.Ps,
-                           p->np.beta_s, X, make_double2(0, 0), p->zero2, q, true, s);
+    return interp_tiled<T>(static_cast<const PointRec<T>*>(p->pts), p->pt_perm, p->pt_tile_start, p->geom, X,
+                           make_double2(0, 0), p->zero2, q, true, s);
 }
 
 int check_plan_call(sbd_plan_t p, const void* a, const void* b) {
@@ -399,7 +401,7 @@ int sbd_plan(const double* points, int64_t n, sbd_kernel kernel, double delta_mi
         set_error("sbd_plan: unknown form");
         return SBD_EINVAL;
     }
-    if (o.flags != 0 || o.fixed_P < 0 || o.max_nrhs < 0 || o.nufft_tol < 0) {
+    if ((o.flags & ~SBD_FLAG_GAUSSIAN_NODES) != 0 || o.fixed_P < 0 || o.max_nrhs < 0 || o.nufft_tol < 0) {
         set_error("sbd_plan: invalid options");
         return SBD_EINVAL;
     }
@@ -454,7 +456,8 @@ int sbd_plan(const double* points, int64_t n, sbd_kernel kernel, double delta_mi
     for (int c = 0; c < fit.n_circles; ++c) W += fit.M[c] * std::abs(fit.weight[c]);
     const double tol = o.nufft_tol > 0 ? o.nufft_tol : eps / (6.0 * std::max(W, 1e-300));
     const double half = std::max(std::max(bb[2] - cx, bb[3] - cy), 1e-300);
-    if ((rc = nufft_params(fit, half, cx, cy, tol, o.form == SBD_FORM_FP32, p->np, err))) {
+    const int kwin = (o.flags & SBD_FLAG_GAUSSIAN_NODES) ? 0 : 1;
+    if ((rc = nufft_params(fit, half, cx, cy, tol, o.form == SBD_FORM_FP32, kwin, p->np, err))) {
         set_error(err);
         return fail(rc);
     }

@@ -3,36 +3,23 @@
 // The stencil operations of the matvec are the tiled kernels of node.cu.
 #include "far.cuh"
 #include "sbd.h"
+#include "window.cuh"
 
 namespace sbd {
 
 namespace {
-
-template <typename T> __device__ __forceinline__ T dexp(T x);
-template <> __device__ __forceinline__ float dexp<float>(float x) { return expf(x); }
-template <> __device__ __forceinline__ double dexp<double>(double x) { return exp(x); }
 
 template <typename T> __device__ __forceinline__ void atomic_add_cx(cx_t<T>* p, cx_t<T> v) {
     atomicAdd(&p->x, v.x);
     atomicAdd(&p->y, v.y);
 }
 
-template <typename T> __device__ __forceinline__ cx_t<T> load_f(const void* f, bool fc, long idx) {
-    if (fc) {
-        const double2 v = static_cast<const double2*>(f)[idx];
-        return mk<T>(static_cast<T>(v.x), static_cast<T>(v.y));
-    }
-    return mk<T>(static_cast<T>(static_cast<const double*>(f)[idx]), static_cast<T>(0));
-}
-
 template <typename T, int PMAX>
-__device__ __forceinline__ void weights(T frac, int P, T beta, T* w) {
+__device__ __forceinline__ void weights(T frac, int P, const FarGeom& g, T* w) {
+    const Window<T> win{g.kwin, static_cast<T>(g.beta_k), static_cast<T>(2.0 / P)};
 #pragma unroll
     for (int a = 0; a < PMAX; ++a) {
-        if (a < P) {
-            const T d = static_cast<T>(a - P / 2 + 1) - frac;
-            w[a] = dexp<T>(-beta * d * d);
-        }
+        if (a < P) w[a] = win(static_cast<T>(a - P / 2 + 1) - frac);
     }
 }
 
@@ -98,13 +85,13 @@ __global__ void node_gather_kernel(const NodeRec<T>* __restrict__ nodes, long n_
     if (nu >= n_xi) return;
     const NodeRec<T> q = nodes[nu];
     T wx[PMAX], wy[PMAX];
-    weights<T, PMAX>(q.frac.x, g.P, static_cast<T>(g.beta_k), wx);
-    weights<T, PMAX>(q.frac.y, g.P, static_cast<T>(g.beta_k), wy);
+    weights<T, PMAX>(q.frac.x, g.Pk, g, wx);
+    weights<T, PMAX>(q.frac.y, g.Pk, g, wy);
     cx_t<T> acc = mk<T>(0, 0);
-    for (int a = 0; a < g.P; ++a) {
+    for (int a = 0; a < g.Pk; ++a) {
         const cx_t<T>* row = kin + static_cast<long>(q.cell.x + a) * g.nk + q.cell.y;
         cx_t<T> s = mk<T>(0, 0);
-        for (int b = 0; b < g.P; ++b) s = cadd(s, cscale(row[b], wy[b]));
+        for (int b = 0; b < g.Pk; ++b) s = cadd(s, cscale(row[b], wy[b]));
         acc = cadd(acc, cscale(s, wx[a]));
     }
     acc = cscale(acc, cs[q.circle]);
@@ -125,8 +112,8 @@ __global__ void node_scatter_kernel(const NodeRec<T>* __restrict__ nodes, long n
     if (nu >= n_xi) return;
     const NodeRec<T> q = nodes[nu];
     T wx[PMAX], wy[PMAX];
-    weights<T, PMAX>(q.frac.x, g.P, static_cast<T>(g.beta_k), wx);
-    weights<T, PMAX>(q.frac.y, g.P, static_cast<T>(g.beta_k), wy);
+    weights<T, PMAX>(q.frac.x, g.Pk, g, wx);
+    weights<T, PMAX>(q.frac.y, g.Pk, g, wy);
     const long canon = fr.perm ? fr.perm[nu] : nu;
     double2 v = in[canon];
     // q_l = sum_nu exp(i (z_l - c).xi) [exp(i c.xi) ghat_nu]
@@ -135,10 +122,10 @@ __global__ void node_scatter_kernel(const NodeRec<T>* __restrict__ nodes, long n
     sincos(fr.cx * xi.x + fr.cy * xi.y, &sn, &co);
     v = make_double2(v.x * co - v.y * sn, v.x * sn + v.y * co);
     const cx_t<T> acc = cscale(mk<T>(static_cast<T>(v.x), static_cast<T>(v.y)), cs[q.circle]);
-    for (int a = 0; a < g.P; ++a) {
+    for (int a = 0; a < g.Pk; ++a) {
         const cx_t<T> va = cscale(acc, wx[a]);
         cx_t<T>* row = kout + static_cast<long>(q.cell.x + a) * g.nk + q.cell.y;
-        for (int b = 0; b < g.P; ++b) atomic_add_cx<T>(row + b, cscale(va, wy[b]));
+        for (int b = 0; b < g.Pk; ++b) atomic_add_cx<T>(row + b, cscale(va, wy[b]));
     }
 }
 

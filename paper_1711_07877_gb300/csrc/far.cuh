@@ -9,11 +9,13 @@ namespace sbd {
 
 // Geometry of one transform, all in cells of the respective grid.
 struct FarGeom {
-    int P;            // stencil width (cells per dimension), even
+    int Ps;           // spreading stencil width (cells per dimension), even; Gaussian window
+    int Pk;           // node stencil width, even
     int m;            // spreading grid side
     int nk;           // frequency grid side
-    double beta_s;    // spreading weight exp(-beta_s d^2)
-    double beta_k;    // node weight exp(-beta_k d^2)
+    int kwin;         // node window (WindowKind)
+    double beta_s;    // spreading window exp(-beta_s d^2)
+    double beta_k;    // node window parameter
 };
 
 // Point i: spreading stencil starts at (row, column) = cell of the spreading grid, whose

@@ -1,4 +1,4 @@
-// Tiled gather / scatter with separable Gaussian stencils on a square grid.
+// Tiled gather / scatter with separable stencil windows on a square grid.
 //
 // Used for the three stencil operations of the far part (Sec. 1 steps (i)-(iii)):
 //   spreading      points -> spreading grid          (scatter, values f)
@@ -17,14 +17,11 @@
 #include "near.cuh"
 #include "node.cuh"
 #include "sbd.h"
+#include "window.cuh"
 
 namespace sbd {
 
 namespace {
-
-template <typename T> __device__ __forceinline__ T gexp(T x);
-template <> __device__ __forceinline__ float gexp<float>(float x) { return expf(x); }
-template <> __device__ __forceinline__ double gexp<double>(double x) { return exp(x); }
 
 template <typename Rec>
 __global__ void tile_count_kernel(const Rec* __restrict__ rec, long n, int ntx, long long* __restrict__ count) {
@@ -49,14 +46,12 @@ __global__ void tile_scatter_kernel(const Rec* __restrict__ in, long n, int ntx,
 
 // Stencil weights of the group's lane: w(sub - P/2 + 1 - frac) along both dimensions.
 template <typename T>
-__device__ __forceinline__ void lane_weights(int sub, int P, T beta, T fx, T fy, T& wx, T& wy) {
+__device__ __forceinline__ void lane_weights(int sub, int P, const Window<T>& win, T fx, T fy, T& wx, T& wy) {
     wx = 0;
     wy = 0;
     if (sub < P) {
-        const T dx = static_cast<T>(sub - P / 2 + 1) - fx;
-        const T dy = static_cast<T>(sub - P / 2 + 1) - fy;
-        wx = gexp<T>(-beta * dx * dx);
-        wy = gexp<T>(-beta * dy * dy);
+        wx = win(static_cast<T>(sub - P / 2 + 1) - fx);
+        wy = win(static_cast<T>(sub - P / 2 + 1) - fy);
     }
 }
 
@@ -106,7 +101,7 @@ template <typename T> struct PointOut {     // interpolation: q[perm[i]] = v + w
 
 template <typename T, int G, typename Rec, typename Out>
 __global__ void __launch_bounds__(256) gather_tiles_kernel(
-    const Rec* __restrict__ rec, const long long* __restrict__ tile_start, int ntx, int n, int P, T beta,
+    const Rec* __restrict__ rec, const long long* __restrict__ tile_start, int ntx, int n, int P, Window<T> win,
     const cx_t<T>* __restrict__ grid, Out out) {
     using C = cx_t<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -132,7 +127,7 @@ __global__ void __launch_bounds__(256) gather_tiles_kernel(
         const Rec q = rec[i];
         const int rx = q.cell.x - ox, ry = q.cell.y - oy;
         T wx, wy;
-        lane_weights<T>(sub, P, beta, q.frac.x, q.frac.y, wx, wy);
+        lane_weights<T>(sub, P, win, q.frac.x, q.frac.y, wx, wy);
         T sr = 0, si = 0;
         const C* col = s + static_cast<long>(rx) * W + ry + sub;
         for (int a = 0; a < P; ++a) {
@@ -156,7 +151,7 @@ __global__ void __launch_bounds__(256) gather_tiles_kernel(
 
 template <typename T, int G, typename Rec, typename Val>
 __global__ void __launch_bounds__(256) scatter_tiles_kernel(
-    const Rec* __restrict__ rec, const long long* __restrict__ tile_start, int ntx, int n, int P, T beta,
+    const Rec* __restrict__ rec, const long long* __restrict__ tile_start, int ntx, int n, int P, Window<T> win,
     Val val, cx_t<T>* __restrict__ grid) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* acc = reinterpret_cast<T*>(smem_raw);          // [kNodeTile][kNodeTile][2]
@@ -178,7 +173,7 @@ __global__ void __launch_bounds__(256) scatter_tiles_kernel(
                 const int rx = q.cell.x - ox, ry = q.cell.y - oy;   // stencil start relative to this tile
                 if (rx + P <= 0 || ry + P <= 0) continue;           // uniform across the group
                 T wx, wy;
-                lane_weights<T>(sub, P, beta, q.frac.x, q.frac.y, wx, wy);
+                lane_weights<T>(sub, P, win, q.frac.x, q.frac.y, wx, wy);
                 const cx_t<T> g = val.get(i);
                 const int c = ry + sub;
                 const bool col_ok = sub < P && c >= 0 && c < kNodeTile;
@@ -205,9 +200,15 @@ __global__ void __launch_bounds__(256) scatter_tiles_kernel(
 
 inline int tiles_per_side(int n) { return (n + kNodeTile - 1) / kNodeTile; }
 
+template <typename T>
+Window<T> make_window(int kind, double beta, int P) {
+    return Window<T>{kind, static_cast<T>(beta), static_cast<T>(2.0 / P)};
+}
+
 template <typename T, typename Rec, typename Out>
-int launch_gather(const Rec* rec, const long long* tile_start, int n, int P, double beta, const cx_t<T>* grid,
-                  Out out, cudaStream_t s) {
+int launch_gather(const Rec* rec, const long long* tile_start, int n, int P, int kind, double beta,
+                  const cx_t<T>* grid, Out out, cudaStream_t s) {
+    const Window<T> win = make_window<T>(kind, beta, P);
     const int ntx = tiles_per_side(n);
     const size_t W = kNodeTile + P - 1;
     const size_t smem = W * W * sizeof(cx_t<T>);
@@ -215,30 +216,31 @@ int launch_gather(const Rec* rec, const long long* tile_start, int n, int P, dou
     if (P <= 16) {
         auto k = gather_tiles_kernel<T, 16, Rec, Out>;
         SBD_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
-        k<<<nt, 256, smem, s>>>(rec, tile_start, ntx, n, P, static_cast<T>(beta), grid, out);
+        k<<<nt, 256, smem, s>>>(rec, tile_start, ntx, n, P, win, grid, out);
     } else {
         auto k = gather_tiles_kernel<T, 32, Rec, Out>;
         SBD_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
-        k<<<nt, 256, smem, s>>>(rec, tile_start, ntx, n, P, static_cast<T>(beta), grid, out);
+        k<<<nt, 256, smem, s>>>(rec, tile_start, ntx, n, P, win, grid, out);
     }
     SBD_LAUNCH_CHECK();
     return SBD_OK;
 }
 
 template <typename T, typename Rec, typename Val>
-int launch_scatter(const Rec* rec, const long long* tile_start, int n, int P, double beta, Val val,
+int launch_scatter(const Rec* rec, const long long* tile_start, int n, int P, int kind, double beta, Val val,
                    cx_t<T>* grid, cudaStream_t s) {
+    const Window<T> win = make_window<T>(kind, beta, P);
     const int ntx = tiles_per_side(n);
     const size_t smem = 2 * sizeof(T) * kNodeTile * kNodeTile;
     const unsigned nt = static_cast<unsigned>(ntx) * ntx;
     if (P <= 16) {
         auto k = scatter_tiles_kernel<T, 16, Rec, Val>;
         SBD_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
-        k<<<nt, 256, smem, s>>>(rec, tile_start, ntx, n, P, static_cast<T>(beta), val, grid);
+        k<<<nt, 256, smem, s>>>(rec, tile_start, ntx, n, P, win, val, grid);
     } else {
         auto k = scatter_tiles_kernel<T, 32, Rec, Val>;
         SBD_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
-        k<<<nt, 256, smem, s>>>(rec, tile_start, ntx, n, P, static_cast<T>(beta), val, grid);
+        k<<<nt, 256, smem, s>>>(rec, tile_start, ntx, n, P, win, val, grid);
     }
     SBD_LAUNCH_CHECK();
     return SBD_OK;
@@ -271,23 +273,25 @@ int tile_sort(const Rec* in, long n_rec, int n, Rec* sorted, int* perm, long lon
 }
 
 template <typename T>
-int node_step_tiled(const NodeRec<T>* nodes, const long long* tile_start, int nk, int P, double beta,
+int node_step_tiled(const NodeRec<T>* nodes, const long long* tile_start, const FarGeom& g,
                     const cx_t<T>* omega, const cx_t<T>* kin, cx_t<T>* ghat, cx_t<T>* kout, cudaStream_t s) {
-    int rc = launch_gather<T>(nodes, tile_start, nk, P, beta, kin, NodeIO<T>{omega, ghat}, s);
+    int rc = launch_gather<T>(nodes, tile_start, g.nk, g.Pk, g.kwin, g.beta_k, kin, NodeIO<T>{omega, ghat}, s);
     if (rc) return rc;
-    return launch_scatter<T>(nodes, tile_start, nk, P, beta, NodeVal<T>{ghat}, kout, s);
+    return launch_scatter<T>(nodes, tile_start, g.nk, g.Pk, g.kwin, g.beta_k, NodeVal<T>{ghat}, kout, s);
 }
 
 template <typename T>
-int spread_tiled(const PointRec<T>* pts, const int* perm, const long long* tile_start, int m, int P, double beta,
+int spread_tiled(const PointRec<T>* pts, const int* perm, const long long* tile_start, const FarGeom& g,
                  const void* f, bool f_complex, cx_t<T>* grid, cudaStream_t s) {
-    return launch_scatter<T>(pts, tile_start, m, P, beta, PointVal<T>{f, perm, f_complex}, grid, s);
+    return launch_scatter<T>(pts, tile_start, g.m, g.Ps, kWinGauss, g.beta_s, PointVal<T>{f, perm, f_complex}, grid,
+                             s);
 }
 
 template <typename T>
-int interp_tiled(const PointRec<T>* pts, const int* perm, const long long* tile_start, int m, int P, double beta,
+int interp_tiled(const PointRec<T>* pts, const int* perm, const long long* tile_start, const FarGeom& g,
                  const cx_t<T>* grid, double2 w0, const double2* sumf, void* q, bool q_complex, cudaStream_t s) {
-    return launch_gather<T>(pts, tile_start, m, P, beta, grid, PointOut<T>{q, perm, q_complex, w0, sumf}, s);
+    return launch_gather<T>(pts, tile_start, g.m, g.Ps, kWinGauss, g.beta_s, grid,
+                            PointOut<T>{q, perm, q_complex, w0, sumf}, s);
 }
 
 #define SBD_NODE_INST(T)                                                                                     \
@@ -295,11 +299,11 @@ int interp_tiled(const PointRec<T>* pts, const int* perm, const long long* tile_
                                        cudaStream_t);                                                        \
     template int tile_sort<PointRec<T>>(const PointRec<T>*, long, int, PointRec<T>*, int*, long long*,       \
                                         cudaStream_t);                                                       \
-    template int node_step_tiled<T>(const NodeRec<T>*, const long long*, int, int, double, const cx_t<T>*,   \
+    template int node_step_tiled<T>(const NodeRec<T>*, const long long*, const FarGeom&, const cx_t<T>*,     \
                                     const cx_t<T>*, cx_t<T>*, cx_t<T>*, cudaStream_t);                       \
-    template int spread_tiled<T>(const PointRec<T>*, const int*, const long long*, int, int, double,         \
+    template int spread_tiled<T>(const PointRec<T>*, const int*, const long long*, const FarGeom&,           \
                                  const void*, bool, cx_t<T>*, cudaStream_t);                                 \
-    template int interp_tiled<T>(const PointRec<T>*, const int*, const long long*, int, int, double,         \
+    template int interp_tiled<T>(const PointRec<T>*, const int*, const long long*, const FarGeom&,           \
                                  const cx_t<T>*, double2, const double2*, void*, bool, cudaStream_t);
 SBD_NODE_INST(float)
 SBD_NODE_INST(double)

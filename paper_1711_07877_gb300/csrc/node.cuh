@@ -1,4 +1,4 @@
-// Tiled gather / scatter with separable Gaussian stencils (spreading, node step,
+// Tiled gather / scatter with separable stencil windows (spreading, node step,
 // interpolation); see node.cu.
 #pragma once
 #include <cuda_runtime.h>
@@ -17,17 +17,17 @@ int tile_sort(const Rec* in, long n_rec, int n, Rec* sorted, int* perm, long lon
 
 // kout (nk x nk, fully written) = scatter(omega' * gather(kin)); ghat is n_xi scratch.
 template <typename T>
-int node_step_tiled(const NodeRec<T>* nodes, const long long* tile_start, int nk, int P, double beta,
+int node_step_tiled(const NodeRec<T>* nodes, const long long* tile_start, const FarGeom& g,
                     const cx_t<T>* omega, const cx_t<T>* kin, cx_t<T>* ghat, cx_t<T>* kout, cudaStream_t s);
 
 // grid (m x m, fully written) = spreading of f (float64 or complex128, original order).
 template <typename T>
-int spread_tiled(const PointRec<T>* pts, const int* perm, const long long* tile_start, int m, int P, double beta,
+int spread_tiled(const PointRec<T>* pts, const int* perm, const long long* tile_start, const FarGeom& g,
                  const void* f, bool f_complex, cx_t<T>* grid, cudaStream_t s);
 
 // q[perm[i]] = interpolation of grid at point i + w0 * sumf[0] (float64 or complex128 out).
 template <typename T>
-int interp_tiled(const PointRec<T>* pts, const int* perm, const long long* tile_start, int m, int P, double beta,
+int interp_tiled(const PointRec<T>* pts, const int* perm, const long long* tile_start, const FarGeom& g,
                  const cx_t<T>* grid, double2 w0, const double2* sumf, void* q, bool q_complex, cudaStream_t s);
 
 }  // namespace sbd

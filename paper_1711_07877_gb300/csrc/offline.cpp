@@ -349,8 +349,43 @@ int offline_fit(int kind, double kappa, double delta_min, double delta_max, doub
     return SBD_OK;
 }
 
+// Gauss-Legendre nodes and weights on [-1, 1] (Newton on P_n from Tricomi's guess).
+static void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w) {
+    x.resize(n);
+    w.resize(n);
+    for (int i = 0; i < n; ++i) {
+        double z = std::cos(kPi * (i + 0.75) / (n + 0.5));
+        double dp = 1.0;
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = z;
+            for (int k = 2; k <= n; ++k) {
+                const double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+                p0 = p1;
+                p1 = p2;
+            }
+            dp = n * (z * p1 - p0) / (z * z - 1.0);
+            const double dz = p1 / dp;
+            z -= dz;
+            if (std::fabs(dz) < 1e-16) break;
+        }
+        x[i] = z;
+        w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+    }
+}
+
+// Fourier transform of the ES window on [-1, 1]: int exp(beta (sqrt(1 - z^2) - 1)) cos(k z) dz,
+// with z = sin(theta) so the integrand is smooth.
+static double es_hat(double k, double beta, const std::vector<double>& gx, const std::vector<double>& gw) {
+    double s = 0.0;
+    for (size_t i = 0; i < gx.size(); ++i) {
+        const double th = 0.5 * kPi * gx[i];
+        s += gw[i] * std::exp(beta * (std::cos(th) - 1.0)) * std::cos(k * std::sin(th)) * std::cos(th);
+    }
+    return 0.5 * kPi * s;
+}
+
 int nufft_params(const SbdFit& fit, double half_extent, double cx, double cy, double tol,
-                 bool fp32, NufftParams& o, std::string& err) {
+                 bool fp32, int kwin, NufftParams& o, std::string& err) {
     double S = 0.0;
     for (int c = 0; c < fit.n_circles; ++c) S = std::max(S, fit.radius[c]);
     if (!(S > 0.0) || !(half_extent > 0.0)) {
@@ -359,30 +394,56 @@ int nufft_params(const SbdFit& fit, double half_extent, double cx, double cy, do
     }
     if (fp32) tol = std::max(tol, 3e-7);
     tol = std::max(tol, 1e-15);
-    // error per transform ~ 0.1 exp(-pi P / 3) at two-fold oversampling on both sides
-    int P = static_cast<int>(std::ceil((3.0 / kPi) * std::log(0.1 / tol)));
-    P = std::max(4, std::min(fp32 ? 16 : 32, P + (P & 1)));
-    o.Ps = o.Pk = P;
+    const int pmax = fp32 ? 16 : 32;
+    // spreading side, Gaussian: error ~ 0.1 exp(-pi P / 3) per transform at two-fold oversampling
+    int Ps = static_cast<int>(std::ceil((3.0 / kPi) * std::log(0.1 / tol)));
+    Ps = std::max(4, std::min(pmax, Ps + (Ps & 1)));
+    // node side: ES error ~ 10^-P (two-fold oversampling), Gaussian as the spreading side
+    int Pk;
+    if (kwin == 1) {
+        Pk = static_cast<int>(std::ceil(-std::log10(tol)));
+        Pk = std::max(4, std::min(pmax, Pk + (Pk & 1)));
+    } else {
+        Pk = Ps;
+    }
+    o.Ps = Ps;
+    o.Pk = Pk;
+    o.kwin = kwin;
     o.tol = tol;
-    const double u = P * kPi / 24.0;   // balanced truncation / aliasing at two-fold oversampling
+    const double u = Ps * kPi / 24.0;   // balanced truncation / aliasing of the Gaussian at two-fold oversampling
     o.h = kPi / (2.0 * S);
     o.tau = u / (S * S);
-    o.m = good_fft_size(static_cast<int>(std::ceil(2.0 * half_extent / o.h)) + P + 4);
+    o.m = good_fft_size(static_cast<int>(std::ceil(2.0 * half_extent / o.h)) + Ps + 4);
     o.n = 2 * o.m;
-    o.nk = o.m + P + 4;
+    o.nk = o.m + Pk + 4;
     const double Xg = 0.5 * o.m * o.h;
-    o.sigma = u / (Xg * Xg);
     o.deta = 2.0 * kPi / (o.n * o.h);
     o.beta_s = o.h * o.h / (4.0 * o.tau);
-    o.beta_k = o.deta * o.deta / (4.0 * o.sigma);
     o.cx = cx;
     o.cy = cy;
     o.dec.resize(o.m);
-    for (int i = 0; i < o.m; ++i) {
-        const double x = (i - 0.5 * o.m) * o.h;
-        o.dec[i] = std::exp(o.sigma * x * x);
+    double c0;
+    if (kwin == 1) {
+        o.beta_k = 2.3 * Pk;
+        o.sigma = 0.0;
+        const double half = 0.5 * Pk * o.deta;
+        std::vector<double> gx, gw;
+        gauss_legendre(160, gx, gw);
+        for (int i = 0; i < o.m; ++i) {
+            const double x = (i - 0.5 * o.m) * o.h;
+            o.dec[i] = 1.0 / (half * es_hat(x * half, o.beta_k, gx, gw));
+        }
+        c0 = o.h * o.h * o.deta * o.deta / (4.0 * kPi * o.tau);
+    } else {
+        const double v = Pk * kPi / 24.0;
+        o.sigma = v / (Xg * Xg);
+        o.beta_k = o.deta * o.deta / (4.0 * o.sigma);
+        for (int i = 0; i < o.m; ++i) {
+            const double x = (i - 0.5 * o.m) * o.h;
+            o.dec[i] = std::exp(o.sigma * x * x);
+        }
+        c0 = o.h * o.h * o.deta * o.deta / (16.0 * kPi * kPi * o.tau * o.sigma);
     }
-    const double c0 = o.h * o.h * o.deta * o.deta / (16.0 * kPi * kPi * o.tau * o.sigma);
     o.circle_factor.resize(fit.n_circles);
     for (int c = 0; c < fit.n_circles; ++c)
         o.circle_factor[c] = c0 * c0 * std::exp(2.0 * o.tau * fit.radius[c] * fit.radius[c]);

@@ -36,10 +36,12 @@ struct SbdFit {
 int offline_fit(int kind, double kappa, double delta_min, double delta_max, double eps,
                 int fixed_P, SbdFit& out, std::string& err);
 
-// Parameters of the type-3 transform by Gaussian gridding (both sides Gaussian,
-// two-fold oversampling of the spreading grid and of the FFT).
+// Parameters of the type-3 transform: Gaussian spreading of the points (two-fold
+// oversampled spreading grid), a two-fold zero-padded FFT, and a node window that is
+// Gaussian or ES (exponential of semicircle).
 struct NufftParams {
     int Ps = 0, Pk = 0;        // stencil widths (cells per dimension, even)
+    int kwin = 1;              // node window: 0 Gaussian, 1 ES
     double h = 0.0;            // spreading-grid spacing
     int m = 0;                 // spreading-grid side (cells), even, 5-smooth
     int n = 0;                 // FFT length = 2 m
@@ -47,15 +49,15 @@ struct NufftParams {
     double deta = 0.0;         // frequency-grid spacing 2 pi / (n h)
     double tau = 0.0, sigma = 0.0;
     double beta_s = 0.0;       // h^2 / (4 tau): spreading weight exp(-beta_s d^2), d in cells
-    double beta_k = 0.0;       // deta^2 / (4 sigma): node weight exp(-beta_k d^2), d in cells
+    double beta_k = 0.0;       // node window: Gaussian deta^2 / (4 sigma), ES 2.3 Pk
     double cx = 0.0, cy = 0.0; // centre of the point set (bounding box)
     double tol = 0.0;          // tolerance aimed at for each transform
-    std::vector<double> dec;   // x-grid precorrection exp(sigma x_i^2), size m
-    std::vector<double> circle_factor;   // c(|xi|)^2 per circle: (h^2 deta^2 / (16 pi^2 tau sigma))^2 exp(2 tau r^2)
+    std::vector<double> dec;   // spreading-grid precorrection 1 / psi_hat(x_i) (one dimension), size m
+    std::vector<double> circle_factor;   // c(|xi|)^2 per circle, c = h^2 deta^2 exp(tau |xi|^2) / (4 pi tau) [x Gaussian 1/(4 pi sigma)]
 };
 
 int nufft_params(const SbdFit& fit, double half_extent, double cx, double cy, double tol,
-                 bool fp32, NufftParams& out, std::string& err);
+                 bool fp32, int kwin, NufftParams& out, std::string& err);
 
 // Smallest even 5-smooth integer >= n.
 int good_fft_size(int n);

@@ -121,8 +121,12 @@ def sbd_version() -> str:
     return lib.sbd_version().decode()
 
 
-def make_options(form: int = SBD_FORM_FP64, fixed_P: int = 0, nufft_tol: float = 0.0, max_nrhs: int = 1):
-    return sbd_options(form, fixed_P, nufft_tol, max_nrhs, 0)
+SBD_FLAG_GAUSSIAN_NODES = 1
+
+
+def make_options(form: int = SBD_FORM_FP64, fixed_P: int = 0, nufft_tol: float = 0.0, max_nrhs: int = 1,
+                 flags: int = 0):
+    return sbd_options(form, fixed_P, nufft_tol, max_nrhs, flags)
 
 
 def sbd_plan(points, n: int, kernel_kind: int, kappa: float, delta_min: float, eps: float,

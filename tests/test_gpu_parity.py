@@ -38,9 +38,9 @@ def dev(x, dtype=None):
     return t.cuda()
 
 
-def make_plan(S, z, kind, dmin, eps, kappa=0.0, form=0, nufft_tol=0.0, max_nrhs=1, fixed_P=0):
+def make_plan(S, z, kind, dmin, eps, kappa=0.0, form=0, nufft_tol=0.0, max_nrhs=1, fixed_P=0, flags=0):
     zt = dev(z)
-    opt = S.make_options(form=form, nufft_tol=nufft_tol, max_nrhs=max_nrhs, fixed_P=fixed_P)
+    opt = S.make_options(form=form, nufft_tol=nufft_tol, max_nrhs=max_nrhs, fixed_P=fixed_P, flags=flags)
     p = S.sbd_plan(zt, len(z), S.SBD_HELMHOLTZ if kind == "helmholtz" else S.SBD_LAPLACE, kappa, dmin, eps, opt)
     torch.cuda.synchronize()
     return p
@@ -94,10 +94,11 @@ def lap_small():
     return z, f, dmin, pl
 
 
+@pytest.mark.parametrize("flags", [0, 1])   # ES (default) or Gaussian window at the nodes
 @pytest.mark.parametrize("form", [0, 1])
-def test_nufft_minus_plus_match_direct(S, lap_small, form):
+def test_nufft_minus_plus_match_direct(S, lap_small, form, flags):
     z, f, dmin, pl = lap_small
-    p = make_plan(S, z, "laplace", dmin, 1e-6, form=form)
+    p = make_plan(S, z, "laplace", dmin, 1e-6, form=form, flags=flags)
     try:
         info = S.sbd_plan_info(p)
         ex = S.sbd_plan_export(p)
@@ -195,10 +196,11 @@ def config1():
     return wl, pl, q_sbd, q_dir
 
 
-def test_matvec_fp64_matches_oracle_sbd(S, config1):
+@pytest.mark.parametrize("flags", [0, 1])
+def test_matvec_fp64_matches_oracle_sbd(S, config1, flags):
     wl, pl, q_sbd, q_dir = config1
     _assert_no_borderline_pairs(wl.z, wl.delta_min)
-    p = make_plan(S, wl.z, "laplace", wl.delta_min, wl.eps, form=0, nufft_tol=1e-13)
+    p = make_plan(S, wl.z, "laplace", wl.delta_min, wl.eps, form=0, nufft_tol=1e-13, flags=flags)
     try:
         info = S.sbd_plan_info(p)
         assert info["P"] == pl.P and np.array_equal(S.sbd_plan_export(p)["M"], pl.M)
@@ -210,10 +212,11 @@ def test_matvec_fp64_matches_oracle_sbd(S, config1):
         S.sbd_destroy(p)
 
 
+@pytest.mark.parametrize("flags", [0, 1])
 @pytest.mark.parametrize("form", [0, 1])
-def test_matvec_within_eps_of_direct_sum(S, config1, form):
+def test_matvec_within_eps_of_direct_sum(S, config1, form, flags):
     wl, pl, q_sbd, q_dir = config1
-    p = make_plan(S, wl.z, "laplace", wl.delta_min, wl.eps, form=form)
+    p = make_plan(S, wl.z, "laplace", wl.delta_min, wl.eps, form=form, flags=flags)
     try:
         q = matvec(S, p, wl.f, len(wl.z))
         assert np.max(np.abs(q - q_dir)) <= wl.eps * np.abs(wl.f).sum()
