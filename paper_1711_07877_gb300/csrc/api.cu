@@ -461,8 +461,8 @@ int sbd_plan(const double* points, int64_t n, sbd_kernel kernel, double delta_mi
         set_error(err);
         return fail(rc);
     }
-    if (p->np.n > fft_max_row(o.form == SBD_FORM_FP64)) {
-        set_error("sbd_plan: FFT length " + std::to_string(p->np.n) + " exceeds the single-row kernel limit");
+    if (p->np.n > fft_max_length(o.form == SBD_FORM_FP64)) {
+        set_error("sbd_plan: FFT length " + std::to_string(p->np.n) + " exceeds the row kernel limit");
         return fail(SBD_ENOTSUP);
     }
     if ((rc = near_tables(fit, p->nt, err))) {

@@ -111,75 +111,108 @@ template <> struct MaxB<double> { static constexpr int n_max = 14336; };
 
 // Stage of the in-place mixed-radix decimation-in-time FFT: groups of L = Lp * R
 // elements combine R sub-transforms of length Lp (stored as consecutive blocks)
-// into one transform of length L, in place.
+// into one transform of length L, in place.  A thread keeps one offset k within
+// the sub-transforms (so its R - 1 twiddles are loaded once per stage) and walks
+// the groups g; no division per butterfly.
 template <typename T, int R>
 __device__ __forceinline__ void dit_stage(cx_t<T>* s, int n, int Lp, int sign, const cx_t<T>* __restrict__ tw,
-                                          int nthreads) {
+                                          int tw_scale, int nthreads) {
     using C = cx_t<T>;
     const int L = Lp * R;
-    const int nb = n / R;
-    const int tw_step = n / L;
-    for (int b = threadIdx.x; b < nb; b += nthreads) {
-        const int g = b / Lp, k = b - g * Lp;
-        const int base = g * L + k;
-        C v[R];
-#pragma unroll
-        for (int r = 0; r < R; ++r) v[r] = s[base + r * Lp];
+    const int G = n / L;
+    const int tw_step = tw_scale * G;          // twiddle table index step of exp(2 pi i k / L)
+    int k, g0, gstep;
+    if (Lp >= nthreads) {
+        k = threadIdx.x;
+        g0 = 0;
+        gstep = 1;
+    } else {
+        k = threadIdx.x % Lp;
+        g0 = threadIdx.x / Lp;
+        gstep = nthreads / Lp;
+        if (g0 >= gstep) { __syncthreads(); return; }
+    }
+    for (; k < Lp; k += nthreads) {
+        C w[R];
 #pragma unroll
         for (int r = 1; r < R; ++r) {
-            C w = tw[r * k * tw_step];
-            if (sign > 0) w.y = -w.y;
-            v[r] = cmul(v[r], w);
+            C t = tw[r * k * tw_step];
+            if (sign > 0) t.y = -t.y;
+            w[r] = t;
         }
-        small_dft<T, R>(v, sign);
+        for (int g = g0; g < G; g += gstep) {
+            const int base = g * L + k;
+            C v[R];
 #pragma unroll
-        for (int r = 0; r < R; ++r) s[base + r * Lp] = v[r];
+            for (int r = 0; r < R; ++r) v[r] = s[base + r * Lp];
+            if (Lp > 1) {
+#pragma unroll
+                for (int r = 1; r < R; ++r) v[r] = cmul(v[r], w[r]);
+            }
+            small_dft<T, R>(v, sign);
+#pragma unroll
+            for (int r = 0; r < R; ++r) s[base + r * Lp] = v[r];
+        }
     }
     __syncthreads();
 }
 
+// One row (blockIdx.x) and one phase (blockIdx.y) of a length-n transform done as Q
+// transforms of length nq = n / Q (Q = 1 or 2): output k = Q k' + r is the length-nq DFT
+// of y_r[t] = sum_{j < Q} x[t + j nq] w_n^{r (t + j nq)} (fold and twist on the load).
 template <typename T, int NT>
 __global__ void __launch_bounds__(NT) fft_rows_kernel(
     const cx_t<T>* __restrict__ in, long in_stride, int in_len, int in_shift,
     cx_t<T>* __restrict__ out, long out_stride, int out_len, int out_shift,
-    int n, int sign, FftPlan1D plan, const cx_t<T>* __restrict__ tw, const int* __restrict__ perm,
+    int n, int Q, int sign, FftPlan1D plan, const cx_t<T>* __restrict__ tw, const int* __restrict__ perm,
     const T* __restrict__ pre_elem, const T* __restrict__ pre_row,
     const T* __restrict__ post_elem, const T* __restrict__ post_row) {
     using C = cx_t<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* s = reinterpret_cast<C*>(smem_raw);
     const long row = blockIdx.x;
+    const int r = blockIdx.y;
+    const int nq = n / Q;
     const C* src = in + row * in_stride;
     const T rs = pre_row ? pre_row[row] : static_cast<T>(1);
-    // load in digit-reversed order: FFT index i goes to position perm[i]
-    for (int i = threadIdx.x; i < n; i += NT) {
-        int t = i - in_shift;
-        if (t < 0) t += n;
-        C v = mk<T>(0, 0);
-        if (t < in_len) {
-            v = src[t];
-            T sc = rs;
-            if (pre_elem) sc *= pre_elem[t];
-            v = cscale(v, sc);
+    for (int i = threadIdx.x; i < nq; i += NT) {
+        C acc = mk<T>(0, 0);
+        for (int j = 0; j < Q; ++j) {
+            const int idx = i + j * nq;               // FFT index
+            int t = idx - in_shift;
+            if (t < 0) t += n;
+            if (t < in_len) {
+                C v = src[t];
+                T sc = rs;
+                if (pre_elem) sc *= pre_elem[t];
+                v = cscale(v, sc);
+                if (r) {                              // twist w_n^{idx}
+                    C w = tw[idx];
+                    if (sign > 0) w.y = -w.y;
+                    v = cmul(v, w);
+                }
+                acc = cadd(acc, v);
+            }
         }
-        s[perm[i]] = v;
+        s[perm[i]] = acc;
     }
     __syncthreads();
     int Lp = 1;
     for (int st = 0; st < plan.nstages; ++st) {
         const int R = plan.radix[st];
-        if (R == 4)      dit_stage<T, 4>(s, n, Lp, sign, tw, NT);
-        else if (R == 2) dit_stage<T, 2>(s, n, Lp, sign, tw, NT);
-        else if (R == 3) dit_stage<T, 3>(s, n, Lp, sign, tw, NT);
-        else             dit_stage<T, 5>(s, n, Lp, sign, tw, NT);
+        if (R == 4)      dit_stage<T, 4>(s, nq, Lp, sign, tw, Q, NT);
+        else if (R == 2) dit_stage<T, 2>(s, nq, Lp, sign, tw, Q, NT);
+        else if (R == 3) dit_stage<T, 3>(s, nq, Lp, sign, tw, Q, NT);
+        else             dit_stage<T, 5>(s, nq, Lp, sign, tw, Q, NT);
         Lp *= R;
     }
     C* dst = out + row * out_stride;
     const T ps = post_row ? post_row[row] : static_cast<T>(1);
     for (int e = threadIdx.x; e < out_len; e += NT) {
-        int pos = e + out_shift;
-        if (pos >= n) pos -= n;
-        C v = s[pos];
+        int k = e + out_shift;
+        if (k >= n) k -= n;
+        if (Q == 2 && (k & 1) != r) continue;
+        C v = s[Q == 2 ? (k >> 1) : k];
         T sc = ps;
         if (post_elem) sc *= post_elem[e];
         dst[e] = cscale(v, sc);
@@ -263,6 +296,18 @@ int fft_max_row(bool fp64) {
     return fp64 ? std::min(lim, MaxB<double>::n_max) : std::min(lim, MaxB<float>::n_max);
 }
 
+static int fft_phases(int n, bool fp64);
+
+// Phases per row: the smallest Q in {1, 2} whose length n / Q fits one CTA's shared
+// memory, and Q = 2 for long rows so that two CTAs share an SM.
+static int fft_phases(int n, bool fp64) {
+    const int lim = fft_max_row(fp64);
+    if (n % 2 == 0 && (n > lim || n > 8192)) return 2;
+    return 1;
+}
+
+int fft_max_length(bool fp64) { return 2 * fft_max_row(fp64); }
+
 template <typename T>
 int fft_rows(const cx_t<T>* in, long in_stride, int in_len, int in_shift,
              cx_t<T>* out, long out_stride, int out_len, int out_shift,
@@ -270,34 +315,34 @@ int fft_rows(const cx_t<T>* in, long in_stride, int in_len, int in_shift,
              const T* pre_elem, const T* pre_row, const T* post_elem, const T* post_row,
              cudaStream_t stream) {
     if (rows <= 0) return SBD_OK;
+    const bool fp64 = sizeof(T) == 8;
+    const int Q = fft_phases(n, fp64);
+    const int nq = n / Q;
     FftPlan1D plan;
-    if (!fft_make_plan(n, plan) || n > fft_max_row(sizeof(T) == 8)) {
+    if (!fft_make_plan(nq, plan) || nq > fft_max_row(fp64) || n % Q) {
         set_error("FFT length not supported: " + std::to_string(n));
         return SBD_ENOTSUP;
     }
     const cx_t<T>* tw = twiddles<T>(n, stream);
-    if (!tw) {
-        set_error("twiddle table allocation failed");
-        return SBD_ENOMEM;
-    }
     const int* perm = digit_perm(plan, stream);
-    if (!perm) {
-        set_error("permutation table allocation failed");
+    if (!tw || !perm) {
+        set_error("FFT table allocation failed");
         return SBD_ENOMEM;
     }
-    const size_t smem = sizeof(cx_t<T>) * static_cast<size_t>(n);
+    const size_t smem = sizeof(cx_t<T>) * static_cast<size_t>(nq);
     in_shift = ((in_shift % n) + n) % n;
     out_shift = ((out_shift % n) + n) % n;
-    if (n > 2048) {
+    const dim3 grid(static_cast<unsigned>(rows), static_cast<unsigned>(Q));
+    if (nq > 2048) {
         auto k = fft_rows_kernel<T, 1024>;
         SBD_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
-        k<<<rows, 1024, smem, stream>>>(in, in_stride, in_len, in_shift, out, out_stride, out_len, out_shift,
-                                        n, sign, plan, tw, perm, pre_elem, pre_row, post_elem, post_row);
+        k<<<grid, 1024, smem, stream>>>(in, in_stride, in_len, in_shift, out, out_stride, out_len, out_shift,
+                                        n, Q, sign, plan, tw, perm, pre_elem, pre_row, post_elem, post_row);
     } else {
         auto k = fft_rows_kernel<T, 256>;
         SBD_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
-        k<<<rows, 256, smem, stream>>>(in, in_stride, in_len, in_shift, out, out_stride, out_len, out_shift,
-                                       n, sign, plan, tw, perm, pre_elem, pre_row, post_elem, post_row);
+        k<<<grid, 256, smem, stream>>>(in, in_stride, in_len, in_shift, out, out_stride, out_len, out_shift,
+                                       n, Q, sign, plan, tw, perm, pre_elem, pre_row, post_elem, post_row);
     }
     SBD_LAUNCH_CHECK();
     return SBD_OK;

@@ -21,6 +21,8 @@ bool fft_make_plan(int n, FftPlan1D& p);
 
 // Largest row length a single CTA can hold in shared memory for this element type.
 int fft_max_row(bool fp64);
+// Largest transform length fft_rows accepts (two phases of fft_max_row).
+int fft_max_length(bool fp64);
 
 // One batched row pass:
 //   out[r][e] = post_row[r] post_elem[e] *
