@@ -59,7 +59,8 @@ struct sbd_plan_s {
     int* pt_perm = nullptr;            // sorted point record -> original point index
     long long* pt_tile_start = nullptr;
     long long* node_tile_start = nullptr;
-    void* ghat = nullptr;              // n_xi weighted node values (scratch)
+    void* ghat = nullptr;              // n_xi weighted node values (scratch of the two-kernel node step)
+    bool node_fused = true;            // one-kernel node step (shared memory permitting)
     // workspace (one right-hand side at a time)
     void* wsX = nullptr;
     void* wsA = nullptr;
@@ -206,7 +207,10 @@ int build_far(sbd_plan_s* p, cudaStream_t s) {
                                p->node_tile_start, s);
     if (rc) return rc;
     SBD_CUDA_TRY(cudaFreeAsync(canon, s));
-    if ((rc = dev_alloc(p, &p->ghat, sizeof(cx_t<T>) * fit.n_xi))) return rc;
+    // the fused node kernel holds the tile plus halo twice in shared memory
+    const size_t W = kNodeTile + np.Pk - 1;
+    p->node_fused = 2 * W * W * sizeof(cx_t<T>) <= 227 * 1024;
+    if (!p->node_fused && (rc = dev_alloc(p, &p->ghat, sizeof(cx_t<T>) * fit.n_xi))) return rc;
     std::vector<cx_t<T>> om(fit.n_circles);
     std::vector<T> cs(fit.n_circles);
     for (int c = 0; c < fit.n_circles; ++c) {
@@ -280,9 +284,14 @@ int far_apply(sbd_plan_s* p, const void* f, void* q, int nrhs, cudaStream_t s) {
         if ((rc = forward_fft<T>(p, X, A, C, B, s))) return rc;
         t2.end();
         StepTimer t3(p, s, SBD_STAGE_NODE);
-        if ((rc = node_step_tiled<T>(static_cast<const NodeRec<T>*>(p->nodes), p->node_tile_start, p->geom,
-                                     static_cast<const cx_t<T>*>(p->omega_c), B, static_cast<cx_t<T>*>(p->ghat), C,
-                                     s))) return rc;
+        if (p->node_fused) {
+            if ((rc = node_step_fused<T>(static_cast<const NodeRec<T>*>(p->nodes), p->node_tile_start, p->geom,
+                                         static_cast<const cx_t<T>*>(p->omega_c), B, C, s))) return rc;
+        } else if ((rc = node_step_tiled<T>(static_cast<const NodeRec<T>*>(p->nodes), p->node_tile_start, p->geom,
+                                            static_cast<const cx_t<T>*>(p->omega_c), B,
+                                            static_cast<cx_t<T>*>(p->ghat), C, s))) {
+            return rc;
+        }
         t3.end();
         StepTimer t4(p, s, SBD_STAGE_FFT_INV);
         if ((rc = inverse_fft<T>(p, C, A, B, X, s))) return rc;

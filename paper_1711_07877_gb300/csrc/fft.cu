@@ -122,6 +122,7 @@ __device__ __forceinline__ void dit_stage(cx_t<T>* s, int n, int Lp, int sign, c
     const int G = n / L;
     const int tw_step = tw_scale * G;          // twiddle table index step of exp(2 pi i k / L)
     int k, g0, gstep;
+    bool active = true;
     if (Lp >= nthreads) {
         k = threadIdx.x;
         g0 = 0;
@@ -130,9 +131,9 @@ __device__ __forceinline__ void dit_stage(cx_t<T>* s, int n, int Lp, int sign, c
         k = threadIdx.x % Lp;
         g0 = threadIdx.x / Lp;
         gstep = nthreads / Lp;
-        if (g0 >= gstep) { __syncthreads(); return; }
+        active = g0 < gstep;
     }
-    for (; k < Lp; k += nthreads) {
+    for (; active && k < Lp; k += nthreads) {
         C w[R];
 #pragma unroll
         for (int r = 1; r < R; ++r) {

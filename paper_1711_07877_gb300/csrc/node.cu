@@ -198,6 +198,95 @@ __global__ void __launch_bounds__(256) scatter_tiles_kernel(
     }
 }
 
+// Fused node step: gather, weight and scatter every node of one tile, with the
+// tile plus halo of K in shared memory and a shared accumulator of the same size.
+// G lanes per node (G >= P); cells that only this tile's stencils reach (local rows and
+// columns in [P-1, 64)) are stored, the overlap band is added atomically into kout,
+// which the caller clears.
+template <typename T, int G>
+__global__ void __launch_bounds__(256) node_fused_kernel(
+    const NodeRec<T>* __restrict__ rec, const long long* __restrict__ tile_start, int ntx, int n, int P,
+    Window<T> win, const cx_t<T>* __restrict__ omega, const cx_t<T>* __restrict__ kin, cx_t<T>* __restrict__ kout) {
+    using C = cx_t<T>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int tile = blockIdx.x;
+    const long long b0 = tile_start[tile], b1 = tile_start[tile + 1];
+    if (b0 == b1) return;
+    const int W = kNodeTile + P - 1;
+    C* s = reinterpret_cast<C*>(smem_raw);
+    T* acc = reinterpret_cast<T*>(s + W * W);
+    const int ox = (tile / ntx) * kNodeTile, oy = (tile % ntx) * kNodeTile;
+    const int rows = min(W, n - ox), cols = min(W, n - oy);
+    for (int idx = threadIdx.x; idx < W * W; idx += blockDim.x) {
+        const int r = idx / W, c = idx - r * W;
+        C v = mk<T>(0, 0);
+        if (r < rows && c < cols) v = kin[static_cast<long>(ox + r) * n + oy + c];
+        s[idx] = v;
+        acc[2 * idx] = 0;
+        acc[2 * idx + 1] = 0;
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int sub = lane % G;
+    const unsigned gmask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << (lane - sub));
+    const int group = threadIdx.x / G, ngroups = blockDim.x / G;
+    for (long long i = b0 + group; i < b1; i += ngroups) {
+        const NodeRec<T> q = rec[i];
+        const int rx = q.cell.x - ox, ry = q.cell.y - oy;
+        T wx = 0, wy = 0;
+        if (sub < P) {
+            wx = win(static_cast<T>(sub - P / 2 + 1) - q.frac.x);
+            wy = win(static_cast<T>(sub - P / 2 + 1) - q.frac.y);
+        }
+        const int colofs = rx * W + ry + sub;
+        T sr = 0, si = 0;
+#pragma unroll
+        for (int a = 0; a < G; ++a) {
+            if (a < P) {
+                const T w = __shfl_sync(gmask, wx, a, G);
+                if (sub < P) {
+                    const C v = s[colofs + a * W];
+                    sr += w * v.x;
+                    si += w * v.y;
+                }
+            }
+        }
+        sr *= wy;
+        si *= wy;
+#pragma unroll
+        for (int o = G / 2; o > 0; o >>= 1) {
+            sr += __shfl_xor_sync(gmask, sr, o, G);
+            si += __shfl_xor_sync(gmask, si, o, G);
+        }
+        const C g = cmul(mk<T>(sr, si), omega[q.circle]);
+        const T gr = g.x * wy, gi = g.y * wy;
+#pragma unroll
+        for (int a = 0; a < G; ++a) {
+            if (a < P) {
+                const T w = __shfl_sync(gmask, wx, a, G);
+                if (sub < P) {
+                    T* cell = acc + 2 * (colofs + a * W);
+                    atomicAdd(cell, gr * w);
+                    atomicAdd(cell + 1, gi * w);
+                }
+            }
+        }
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < W * W; idx += blockDim.x) {
+        const int r = idx / W, c = idx - r * W;
+        if (r >= rows || c >= cols) continue;
+        const T vr = acc[2 * idx], vi = acc[2 * idx + 1];
+        C* dst = kout + static_cast<long>(ox + r) * n + oy + c;
+        if (r >= P - 1 && c >= P - 1 && r < kNodeTile && c < kNodeTile) {
+            *dst = mk<T>(vr, vi);
+        } else if (vr != 0 || vi != 0) {
+            atomicAdd(&dst->x, vr);
+            atomicAdd(&dst->y, vi);
+        }
+    }
+}
+
 inline int tiles_per_side(int n) { return (n + kNodeTile - 1) / kNodeTile; }
 
 template <typename T>
@@ -273,6 +362,32 @@ int tile_sort(const Rec* in, long n_rec, int n, Rec* sorted, int* perm, long lon
 }
 
 template <typename T>
+int node_step_fused(const NodeRec<T>* nodes, const long long* tile_start, const FarGeom& g, const cx_t<T>* omega,
+                    const cx_t<T>* kin, cx_t<T>* kout, cudaStream_t s) {
+    SBD_CUDA_TRY(cudaMemsetAsync(kout, 0, sizeof(cx_t<T>) * static_cast<size_t>(g.nk) * g.nk, s));
+    const int ntx = tiles_per_side(g.nk);
+    const unsigned nt = static_cast<unsigned>(ntx) * ntx;
+    const size_t W = kNodeTile + g.Pk - 1;
+    const size_t smem = 2 * W * W * sizeof(cx_t<T>);
+    const Window<T> win = make_window<T>(g.kwin, g.beta_k, g.Pk);
+    if (g.Pk <= 8) {
+        auto k = node_fused_kernel<T, 8>;
+        SBD_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
+        k<<<nt, 256, smem, s>>>(nodes, tile_start, ntx, g.nk, g.Pk, win, omega, kin, kout);
+    } else if (g.Pk <= 16) {
+        auto k = node_fused_kernel<T, 16>;
+        SBD_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
+        k<<<nt, 256, smem, s>>>(nodes, tile_start, ntx, g.nk, g.Pk, win, omega, kin, kout);
+    } else {
+        auto k = node_fused_kernel<T, 32>;
+        SBD_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
+        k<<<nt, 256, smem, s>>>(nodes, tile_start, ntx, g.nk, g.Pk, win, omega, kin, kout);
+    }
+    SBD_LAUNCH_CHECK();
+    return SBD_OK;
+}
+
+template <typename T>
 int node_step_tiled(const NodeRec<T>* nodes, const long long* tile_start, const FarGeom& g,
                     const cx_t<T>* omega, const cx_t<T>* kin, cx_t<T>* ghat, cx_t<T>* kout, cudaStream_t s) {
     int rc = launch_gather<T>(nodes, tile_start, g.nk, g.Pk, g.kwin, g.beta_k, kin, NodeIO<T>{omega, ghat}, s);
@@ -301,6 +416,8 @@ int interp_tiled(const PointRec<T>* pts, const int* perm, const long long* tile_
                                         cudaStream_t);                                                       \
     template int node_step_tiled<T>(const NodeRec<T>*, const long long*, const FarGeom&, const cx_t<T>*,     \
                                     const cx_t<T>*, cx_t<T>*, cx_t<T>*, cudaStream_t);                       \
+    template int node_step_fused<T>(const NodeRec<T>*, const long long*, const FarGeom&, const cx_t<T>*,     \
+                                    const cx_t<T>*, cx_t<T>*, cudaStream_t);                                 \
     template int spread_tiled<T>(const PointRec<T>*, const int*, const long long*, const FarGeom&,           \
                                  const void*, bool, cx_t<T>*, cudaStream_t);                                 \
     template int interp_tiled<T>(const PointRec<T>*, const int*, const long long*, const FarGeom&,           \

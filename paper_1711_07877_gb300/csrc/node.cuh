@@ -20,6 +20,12 @@ template <typename T>
 int node_step_tiled(const NodeRec<T>* nodes, const long long* tile_start, const FarGeom& g,
                     const cx_t<T>* omega, const cx_t<T>* kin, cx_t<T>* ghat, cx_t<T>* kout, cudaStream_t s);
 
+// The same in one kernel per tile: gather, weight and scatter into a shared accumulator,
+// whose overlap band is added atomically into kout (cleared here).
+template <typename T>
+int node_step_fused(const NodeRec<T>* nodes, const long long* tile_start, const FarGeom& g, const cx_t<T>* omega,
+                    const cx_t<T>* kin, cx_t<T>* kout, cudaStream_t s);
+
 // grid (m x m, fully written) = spreading of f (float64 or complex128, original order).
 template <typename T>
 int spread_tiled(const PointRec<T>* pts, const int* perm, const long long* tile_start, const FarGeom& g,
