@@ -207,9 +207,8 @@ int build_far(sbd_plan_s* p, cudaStream_t s) {
                                p->node_tile_start, s);
     if (rc) return rc;
     SBD_CUDA_TRY(cudaFreeAsync(canon, s));
-    // the fused node kernel holds the tile plus halo twice in shared memory
-    const size_t W = kNodeTile + np.Pk - 1;
-    p->node_fused = 2 * W * W * sizeof(cx_t<T>) <= 227 * 1024;
+    // the fused node kernel holds the tile plus halo and two accumulator planes in shared memory
+    p->node_fused = node_fused_smem<T>(np.Pk) <= 227 * 1024;
     if (!p->node_fused && (rc = dev_alloc(p, &p->ghat, sizeof(cx_t<T>) * fit.n_xi))) return rc;
     std::vector<cx_t<T>> om(fit.n_circles);
     std::vector<T> cs(fit.n_circles);

@@ -3,6 +3,7 @@
 // placement shift, digit reversal and diagonal scaling fused into the load), all
 // radix stages run in place in shared memory, and only the
 // requested output window is written back.
+#include <algorithm>
 #include <map>
 #include <mutex>
 #include <vector>
@@ -171,8 +172,8 @@ __global__ void __launch_bounds__(NT) fft_rows_kernel(
     using C = cx_t<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* s = reinterpret_cast<C*>(smem_raw);
-    const long row = blockIdx.x;
-    const int r = blockIdx.y;
+    const long row = blockIdx.y;     // phases of a row are adjacent CTAs (they read the same row)
+    const int r = blockIdx.x;
     const int nq = n / Q;
     const C* src = in + row * in_stride;
     const T rs = pre_row ? pre_row[row] : static_cast<T>(1);
@@ -299,11 +300,10 @@ int fft_max_row(bool fp64) {
 
 static int fft_phases(int n, bool fp64);
 
-// Phases per row: the smallest Q in {1, 2} whose length n / Q fits one CTA's shared
-// memory, and Q = 2 for long rows so that two CTAs share an SM.
+// Phases per row: the smallest Q in {1, 2} whose length n / Q fits one CTA's shared memory.
 static int fft_phases(int n, bool fp64) {
     const int lim = fft_max_row(fp64);
-    if (n % 2 == 0 && (n > lim || n > 8192)) return 2;
+    if (n % 2 == 0 && n > lim) return 2;
     return 1;
 }
 
@@ -333,17 +333,25 @@ int fft_rows(const cx_t<T>* in, long in_stride, int in_len, int in_shift,
     const size_t smem = sizeof(cx_t<T>) * static_cast<size_t>(nq);
     in_shift = ((in_shift % n) + n) % n;
     out_shift = ((out_shift % n) + n) % n;
-    const dim3 grid(static_cast<unsigned>(rows), static_cast<unsigned>(Q));
-    if (nq > 2048) {
-        auto k = fft_rows_kernel<T, 1024>;
-        SBD_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
-        k<<<grid, 1024, smem, stream>>>(in, in_stride, in_len, in_shift, out, out_stride, out_len, out_shift,
-                                        n, Q, sign, plan, tw, perm, pre_elem, pre_row, post_elem, post_row);
-    } else {
-        auto k = fft_rows_kernel<T, 256>;
-        SBD_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
-        k<<<grid, 256, smem, stream>>>(in, in_stride, in_len, in_shift, out, out_stride, out_len, out_shift,
-                                       n, Q, sign, plan, tw, perm, pre_elem, pre_row, post_elem, post_row);
+    for (int r0 = 0; r0 < rows; r0 += 65535) {          // grid.y holds at most 65535 rows
+        const int nr = std::min(65535, rows - r0);
+        const dim3 grid(static_cast<unsigned>(Q), static_cast<unsigned>(nr));
+        const cx_t<T>* ip = in + static_cast<long>(r0) * in_stride;
+        cx_t<T>* op = out + static_cast<long>(r0) * out_stride;
+        const T* prr = pre_row ? pre_row + r0 : nullptr;
+        const T* por = post_row ? post_row + r0 : nullptr;
+        if (nq > 2048) {
+            auto k = fft_rows_kernel<T, 1024>;
+            SBD_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
+            k<<<grid, 1024, smem, stream>>>(ip, in_stride, in_len, in_shift, op, out_stride, out_len, out_shift,
+                                            n, Q, sign, plan, tw, perm, pre_elem, prr, post_elem, por);
+        } else {
+            auto k = fft_rows_kernel<T, 256>;
+            SBD_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
+            k<<<grid, 256, smem, stream>>>(ip, in_stride, in_len, in_shift, op, out_stride, out_len, out_shift,
+                                           n, Q, sign, plan, tw, perm, pre_elem, prr, post_elem, por);
+        }
+        SBD_LAUNCH_CHECK();
     }
     SBD_LAUNCH_CHECK();
     return SBD_OK;

@@ -198,77 +198,79 @@ __global__ void __launch_bounds__(256) scatter_tiles_kernel(
     }
 }
 
-// Fused node step: gather, weight and scatter every node of one tile, with the
-// tile plus halo of K in shared memory and a shared accumulator of the same size.
-// G lanes per node (G >= P); cells that only this tile's stencils reach (local rows and
-// columns in [P-1, 64)) are stored, the overlap band is added atomically into kout,
-// which the caller clears.
-template <typename T, int G>
+// Fused node step: one CTA per 64 x 64 tile of the frequency grid, one node per warp.
+// The tile plus a (P-1) halo of K sits in shared memory, and so do two accumulator
+// planes (re, im) of the same size.  Lanes cover the node's P x P stencil as RPI rows
+// x P8 columns per step (P8 = 8, 16 or 32 >= P, RPI = 32 / P8); the shared row stride
+// is congruent to P8 modulo 32, so every shared access of a step hits distinct banks.
+// The gathered value is reduced over the warp, weighted by omega'_p of the node's
+// circle and scattered with shared atomics (distinct cells within the warp).  Cells that
+// only this tile's stencils reach (local rows and columns in [P-1, 64)) are stored, the
+// overlap band is added atomically into kout, which the caller clears.
+template <typename T, int P8>
 __global__ void __launch_bounds__(256) node_fused_kernel(
-    const NodeRec<T>* __restrict__ rec, const long long* __restrict__ tile_start, int ntx, int n, int P,
+    const NodeRec<T>* __restrict__ rec, const long long* __restrict__ tile_start, int ntx, int n, int P, int Ws,
     Window<T> win, const cx_t<T>* __restrict__ omega, const cx_t<T>* __restrict__ kin, cx_t<T>* __restrict__ kout) {
     using C = cx_t<T>;
+    constexpr int RPI = 32 / P8;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int tile = blockIdx.x;
     const long long b0 = tile_start[tile], b1 = tile_start[tile + 1];
     if (b0 == b1) return;
     const int W = kNodeTile + P - 1;
     C* s = reinterpret_cast<C*>(smem_raw);
-    T* acc = reinterpret_cast<T*>(s + W * W);
+    T* acc_re = reinterpret_cast<T*>(s + W * Ws);
+    T* acc_im = acc_re + W * Ws;
     const int ox = (tile / ntx) * kNodeTile, oy = (tile % ntx) * kNodeTile;
     const int rows = min(W, n - ox), cols = min(W, n - oy);
     for (int idx = threadIdx.x; idx < W * W; idx += blockDim.x) {
         const int r = idx / W, c = idx - r * W;
         C v = mk<T>(0, 0);
         if (r < rows && c < cols) v = kin[static_cast<long>(ox + r) * n + oy + c];
-        s[idx] = v;
-        acc[2 * idx] = 0;
-        acc[2 * idx + 1] = 0;
+        s[r * Ws + c] = v;
+        acc_re[r * Ws + c] = 0;
+        acc_im[r * Ws + c] = 0;
     }
     __syncthreads();
     const int lane = threadIdx.x & 31;
-    const int sub = lane % G;
-    const unsigned gmask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << (lane - sub));
-    const int group = threadIdx.x / G, ngroups = blockDim.x / G;
-    for (long long i = b0 + group; i < b1; i += ngroups) {
+    const int a0 = lane / P8, b = lane % P8;
+    const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const int steps = (P + RPI - 1) / RPI;
+    for (long long i = b0 + warp; i < b1; i += nwarps) {
         const NodeRec<T> q = rec[i];
         const int rx = q.cell.x - ox, ry = q.cell.y - oy;
-        T wx = 0, wy = 0;
-        if (sub < P) {
-            wx = win(static_cast<T>(sub - P / 2 + 1) - q.frac.x);
-            wy = win(static_cast<T>(sub - P / 2 + 1) - q.frac.y);
-        }
-        const int colofs = rx * W + ry + sub;
+        // lane l < P holds w(l - P/2 + 1 - frac) for rows (wl) and, via b, for columns (wy)
+        const T wl = lane < P ? win(static_cast<T>(lane - P / 2 + 1) - q.frac.x) : static_cast<T>(0);
+        const T wy = b < P ? win(static_cast<T>(b - P / 2 + 1) - q.frac.y) : static_cast<T>(0);
+        const int base = (rx + a0) * Ws + ry + b;
         T sr = 0, si = 0;
-#pragma unroll
-        for (int a = 0; a < G; ++a) {
-            if (a < P) {
-                const T w = __shfl_sync(gmask, wx, a, G);
-                if (sub < P) {
-                    const C v = s[colofs + a * W];
-                    sr += w * v.x;
-                    si += w * v.y;
-                }
+#pragma unroll 4
+        for (int st = 0; st < steps; ++st) {
+            const int a = a0 + st * RPI;
+            const T w = __shfl_sync(0xffffffffu, wl, a & 31);
+            if (a < P && b < P) {
+                const C v = s[base + st * RPI * Ws];
+                sr += w * v.x;
+                si += w * v.y;
             }
         }
         sr *= wy;
         si *= wy;
 #pragma unroll
-        for (int o = G / 2; o > 0; o >>= 1) {
-            sr += __shfl_xor_sync(gmask, sr, o, G);
-            si += __shfl_xor_sync(gmask, si, o, G);
+        for (int o = 16; o > 0; o >>= 1) {
+            sr += __shfl_xor_sync(0xffffffffu, sr, o);
+            si += __shfl_xor_sync(0xffffffffu, si, o);
         }
         const C g = cmul(mk<T>(sr, si), omega[q.circle]);
         const T gr = g.x * wy, gi = g.y * wy;
-#pragma unroll
-        for (int a = 0; a < G; ++a) {
-            if (a < P) {
-                const T w = __shfl_sync(gmask, wx, a, G);
-                if (sub < P) {
-                    T* cell = acc + 2 * (colofs + a * W);
-                    atomicAdd(cell, gr * w);
-                    atomicAdd(cell + 1, gi * w);
-                }
+#pragma unroll 4
+        for (int st = 0; st < steps; ++st) {
+            const int a = a0 + st * RPI;
+            const T w = __shfl_sync(0xffffffffu, wl, a & 31);
+            if (a < P && b < P) {
+                const int o = base + st * RPI * Ws;
+                atomicAdd(acc_re + o, gr * w);
+                atomicAdd(acc_im + o, gi * w);
             }
         }
     }
@@ -276,7 +278,7 @@ __global__ void __launch_bounds__(256) node_fused_kernel(
     for (int idx = threadIdx.x; idx < W * W; idx += blockDim.x) {
         const int r = idx / W, c = idx - r * W;
         if (r >= rows || c >= cols) continue;
-        const T vr = acc[2 * idx], vi = acc[2 * idx + 1];
+        const T vr = acc_re[r * Ws + c], vi = acc_im[r * Ws + c];
         C* dst = kout + static_cast<long>(ox + r) * n + oy + c;
         if (r >= P - 1 && c >= P - 1 && r < kNodeTile && c < kNodeTile) {
             *dst = mk<T>(vr, vi);
@@ -286,6 +288,15 @@ __global__ void __launch_bounds__(256) node_fused_kernel(
         }
     }
 }
+
+// Shared row stride for the fused node kernel: >= W and congruent to P8 modulo 32.
+inline int fused_stride(int W, int P8) {
+    int ws = W;
+    while (ws % 32 != P8 % 32) ++ws;
+    return ws;
+}
+
+inline int fused_p8(int P) { return P <= 8 ? 8 : (P <= 16 ? 16 : 32); }
 
 inline int tiles_per_side(int n) { return (n + kNodeTile - 1) / kNodeTile; }
 
@@ -362,26 +373,35 @@ int tile_sort(const Rec* in, long n_rec, int n, Rec* sorted, int* perm, long lon
 }
 
 template <typename T>
+size_t node_fused_smem(int Pk) {
+    const int W = kNodeTile + Pk - 1;
+    const int Ws = fused_stride(W, fused_p8(Pk));
+    return static_cast<size_t>(W) * Ws * (sizeof(cx_t<T>) + 2 * sizeof(T));
+}
+
+template <typename T>
 int node_step_fused(const NodeRec<T>* nodes, const long long* tile_start, const FarGeom& g, const cx_t<T>* omega,
                     const cx_t<T>* kin, cx_t<T>* kout, cudaStream_t s) {
     SBD_CUDA_TRY(cudaMemsetAsync(kout, 0, sizeof(cx_t<T>) * static_cast<size_t>(g.nk) * g.nk, s));
     const int ntx = tiles_per_side(g.nk);
     const unsigned nt = static_cast<unsigned>(ntx) * ntx;
-    const size_t W = kNodeTile + g.Pk - 1;
-    const size_t smem = 2 * W * W * sizeof(cx_t<T>);
+    const int W = kNodeTile + g.Pk - 1;
+    const int P8 = fused_p8(g.Pk);
+    const int Ws = fused_stride(W, P8);
+    const size_t smem = node_fused_smem<T>(g.Pk);
     const Window<T> win = make_window<T>(g.kwin, g.beta_k, g.Pk);
-    if (g.Pk <= 8) {
+    if (P8 == 8) {
         auto k = node_fused_kernel<T, 8>;
         SBD_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
-        k<<<nt, 256, smem, s>>>(nodes, tile_start, ntx, g.nk, g.Pk, win, omega, kin, kout);
-    } else if (g.Pk <= 16) {
+        k<<<nt, 256, smem, s>>>(nodes, tile_start, ntx, g.nk, g.Pk, Ws, win, omega, kin, kout);
+    } else if (P8 == 16) {
         auto k = node_fused_kernel<T, 16>;
         SBD_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
-        k<<<nt, 256, smem, s>>>(nodes, tile_start, ntx, g.nk, g.Pk, win, omega, kin, kout);
+        k<<<nt, 256, smem, s>>>(nodes, tile_start, ntx, g.nk, g.Pk, Ws, win, omega, kin, kout);
     } else {
         auto k = node_fused_kernel<T, 32>;
         SBD_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
-        k<<<nt, 256, smem, s>>>(nodes, tile_start, ntx, g.nk, g.Pk, win, omega, kin, kout);
+        k<<<nt, 256, smem, s>>>(nodes, tile_start, ntx, g.nk, g.Pk, Ws, win, omega, kin, kout);
     }
     SBD_LAUNCH_CHECK();
     return SBD_OK;
@@ -416,6 +436,7 @@ int interp_tiled(const PointRec<T>* pts, const int* perm, const long long* tile_
                                         cudaStream_t);                                                       \
     template int node_step_tiled<T>(const NodeRec<T>*, const long long*, const FarGeom&, const cx_t<T>*,     \
                                     const cx_t<T>*, cx_t<T>*, cx_t<T>*, cudaStream_t);                       \
+    template size_t node_fused_smem<T>(int);                                                                 \
     template int node_step_fused<T>(const NodeRec<T>*, const long long*, const FarGeom&, const cx_t<T>*,     \
                                     const cx_t<T>*, cx_t<T>*, cudaStream_t);                                 \
     template int spread_tiled<T>(const PointRec<T>*, const int*, const long long*, const FarGeom&,           \

@@ -23,6 +23,8 @@ int node_step_tiled(const NodeRec<T>* nodes, const long long* tile_start, const 
 // The same in one kernel per tile: gather, weight and scatter into a shared accumulator,
 // whose overlap band is added atomically into kout (cleared here).
 template <typename T>
+size_t node_fused_smem(int Pk);   // dynamic shared memory of the fused kernel
+template <typename T>
 int node_step_fused(const NodeRec<T>* nodes, const long long* tile_start, const FarGeom& g, const cx_t<T>* omega,
                     const cx_t<T>* kin, cx_t<T>* kout, cudaStream_t s);
 
