@@ -193,10 +193,19 @@ int build_far(sbd_plan_s* p, cudaStream_t s) {
     if ((rc = upload(p, &p->circle_start, start, s))) return rc;
     if ((rc = upload(p, &p->circle_radius, fit.radius, s))) return rc;
     if ((rc = upload(p, &p->circle_M, fit.M, s))) return rc;
+    std::vector<cx_t<T>> om(fit.n_circles);
+    std::vector<T> cs(fit.n_circles);
+    for (int c = 0; c < fit.n_circles; ++c) {
+        const cplx w = fit.weight[c] * np.circle_factor[c];
+        om[c] = mk<T>(static_cast<T>(w.real()), static_cast<T>(w.imag()));
+        cs[c] = static_cast<T>(std::sqrt(np.circle_factor[c]));
+    }
+    if ((rc = upload(p, reinterpret_cast<cx_t<T>**>(&p->omega_c), om, s))) return rc;
+    if ((rc = upload(p, reinterpret_cast<T**>(&p->cscale_c), cs, s))) return rc;
     NodeRec<T>* canon = nullptr;
     SBD_CUDA_TRY(cudaMallocAsync(&canon, sizeof(NodeRec<T>) * std::max<long long>(fit.n_xi, 1), s));
     rc = far_prepare_nodes<T>(p->circle_start, p->circle_radius, p->circle_M, fit.n_circles, fit.n_xi, np.deta,
-                              np.nk, np.Pk, canon, s);
+                              np.nk, np.Pk, static_cast<const cx_t<T>*>(p->omega_c), canon, s);
     if (rc) return rc;
     const int ntx = (np.nk + kNodeTile - 1) / kNodeTile;
     if ((rc = dev_alloc(p, &p->nodes, sizeof(NodeRec<T>) * fit.n_xi))) return rc;
@@ -210,15 +219,6 @@ int build_far(sbd_plan_s* p, cudaStream_t s) {
     // the fused node kernel holds the tile plus halo and two accumulator planes in shared memory
     p->node_fused = node_fused_smem<T>(np.Pk) <= 227 * 1024;
     if (!p->node_fused && (rc = dev_alloc(p, &p->ghat, sizeof(cx_t<T>) * fit.n_xi))) return rc;
-    std::vector<cx_t<T>> om(fit.n_circles);
-    std::vector<T> cs(fit.n_circles);
-    for (int c = 0; c < fit.n_circles; ++c) {
-        const cplx w = fit.weight[c] * np.circle_factor[c];
-        om[c] = mk<T>(static_cast<T>(w.real()), static_cast<T>(w.imag()));
-        cs[c] = static_cast<T>(std::sqrt(np.circle_factor[c]));
-    }
-    if ((rc = upload(p, reinterpret_cast<cx_t<T>**>(&p->omega_c), om, s))) return rc;
-    if ((rc = upload(p, reinterpret_cast<T**>(&p->cscale_c), cs, s))) return rc;
     std::vector<T> dec(np.m);
     for (int i = 0; i < np.m; ++i) dec[i] = static_cast<T>(np.dec[i]);
     if ((rc = upload(p, reinterpret_cast<T**>(&p->dec), dec, s))) return rc;
@@ -284,11 +284,10 @@ int far_apply(sbd_plan_s* p, const void* f, void* q, int nrhs, cudaStream_t s) {
         t2.end();
         StepTimer t3(p, s, SBD_STAGE_NODE);
         if (p->node_fused) {
-            if ((rc = node_step_fused<T>(static_cast<const NodeRec<T>*>(p->nodes), p->node_tile_start, p->geom,
-                                         static_cast<const cx_t<T>*>(p->omega_c), B, C, s))) return rc;
+            if ((rc = node_step_fused<T>(static_cast<const NodeRec<T>*>(p->nodes), p->node_tile_start, p->geom, B,
+                                         C, s))) return rc;
         } else if ((rc = node_step_tiled<T>(static_cast<const NodeRec<T>*>(p->nodes), p->node_tile_start, p->geom,
-                                            static_cast<const cx_t<T>*>(p->omega_c), B,
-                                            static_cast<cx_t<T>*>(p->ghat), C, s))) {
+                                            B, static_cast<cx_t<T>*>(p->ghat), C, s))) {
             return rc;
         }
         t3.end();

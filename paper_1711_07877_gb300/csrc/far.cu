@@ -39,7 +39,7 @@ __global__ void prepare_points_kernel(const double* __restrict__ z, long n, doub
 
 // xi of node nu (FP64): circle by binary search in the prefix offsets, then Eq. (defXimp).
 __device__ __forceinline__ double2 node_xi(const int* __restrict__ start, const double* __restrict__ radius,
-                                           const int* __restrict__ M, int n_circles, long nu) {
+                                           const int* __restrict__ M, int n_circles, long nu, int* circle) {
     int lo = 0, hi = n_circles;
     while (hi - lo > 1) {
         const int mid = (lo + hi) / 2;
@@ -47,13 +47,15 @@ __device__ __forceinline__ double2 node_xi(const int* __restrict__ start, const 
     }
     double sn, cs;
     sincospi(2.0 * static_cast<double>(nu - start[lo]) / M[lo], &sn, &cs);
+    *circle = lo;
     return make_double2(radius[lo] * cs, radius[lo] * sn);
 }
 
 template <typename T>
 __global__ void prepare_nodes_kernel(const int* __restrict__ start, const double* __restrict__ radius,
                                      const int* __restrict__ M, int n_circles, long n_xi, double deta,
-                                     int nk, int P, NodeRec<T>* __restrict__ out) {
+                                     int nk, int P, const cx_t<T>* __restrict__ omega_c,
+                                     NodeRec<T>* __restrict__ out) {
     const long nu = blockIdx.x * static_cast<long>(blockDim.x) + threadIdx.x;
     if (nu >= n_xi) return;
     int lo = 0, hi = n_circles;   // start[lo] <= nu < start[hi]
@@ -71,8 +73,7 @@ __global__ void prepare_nodes_kernel(const int* __restrict__ start, const double
     NodeRec<T> r;
     r.cell = make_int2(static_cast<int>(fx) - P / 2 + 1, static_cast<int>(fy) - P / 2 + 1);
     r.frac = mk<T>(static_cast<T>(kx - fx), static_cast<T>(ky - fy));
-    r.circle = c;
-    r.pad = 0;
+    r.omega = omega_c[c];
     out[nu] = r;
 }
 
@@ -94,10 +95,11 @@ __global__ void node_gather_kernel(const NodeRec<T>* __restrict__ nodes, long n_
         for (int b = 0; b < g.Pk; ++b) s = cadd(s, cscale(row[b], wy[b]));
         acc = cadd(acc, cscale(s, wx[a]));
     }
-    acc = cscale(acc, cs[q.circle]);
     // the grids hold z - c: multiply by exp(-i c.xi) to return sum_l exp(-i z_l.xi) f_l
     const long canon = fr.perm ? fr.perm[nu] : nu;
-    const double2 xi = node_xi(fr.start, fr.radius, fr.M, fr.n_circles, canon);
+    int circle;
+    const double2 xi = node_xi(fr.start, fr.radius, fr.M, fr.n_circles, canon, &circle);
+    acc = cscale(acc, cs[circle]);
     double sn, co;
     sincos(fr.cx * xi.x + fr.cy * xi.y, &sn, &co);
     const double ar = acc.x, ai = acc.y;
@@ -117,11 +119,12 @@ __global__ void node_scatter_kernel(const NodeRec<T>* __restrict__ nodes, long n
     const long canon = fr.perm ? fr.perm[nu] : nu;
     double2 v = in[canon];
     // q_l = sum_nu exp(i (z_l - c).xi) [exp(i c.xi) ghat_nu]
-    const double2 xi = node_xi(fr.start, fr.radius, fr.M, fr.n_circles, canon);
+    int circle;
+    const double2 xi = node_xi(fr.start, fr.radius, fr.M, fr.n_circles, canon, &circle);
     double sn, co;
     sincos(fr.cx * xi.x + fr.cy * xi.y, &sn, &co);
     v = make_double2(v.x * co - v.y * sn, v.x * sn + v.y * co);
-    const cx_t<T> acc = cscale(mk<T>(static_cast<T>(v.x), static_cast<T>(v.y)), cs[q.circle]);
+    const cx_t<T> acc = cscale(mk<T>(static_cast<T>(v.x), static_cast<T>(v.y)), cs[circle]);
     for (int a = 0; a < g.Pk; ++a) {
         const cx_t<T> va = cscale(acc, wx[a]);
         cx_t<T>* row = kout + static_cast<long>(q.cell.x + a) * g.nk + q.cell.y;
@@ -168,10 +171,11 @@ int far_prepare_points(const double* z, long n, double cx, double cy, double h, 
 
 template <typename T>
 int far_prepare_nodes(const int* circle_start, const double* radius, const int* M, int n_circles,
-                      long n_xi, double deta, int nk, int P, NodeRec<T>* out, cudaStream_t s) {
+                      long n_xi, double deta, int nk, int P, const cx_t<T>* omega_c, NodeRec<T>* out,
+                      cudaStream_t s) {
     if (n_xi <= 0) return SBD_OK;
     prepare_nodes_kernel<T><<<blocks_for(n_xi), kThreads, 0, s>>>(circle_start, radius, M, n_circles, n_xi,
-                                                                   deta, nk, P, out);
+                                                                   deta, nk, P, omega_c, out);
     SBD_LAUNCH_CHECK();
     return SBD_OK;
 }
@@ -210,7 +214,7 @@ int far_sum(const void* f, bool f_complex, long n, int nrhs, double2* sumf, cuda
     template int far_prepare_points<T>(const double*, long, double, double, double, int, int, PointRec<T>*,  \
                                        cudaStream_t);                                                     \
     template int far_prepare_nodes<T>(const int*, const double*, const int*, int, long, double, int, int, \
-                                      NodeRec<T>*, cudaStream_t);                                         \
+                                      const cx_t<T>*, NodeRec<T>*, cudaStream_t);                         \
     template int far_node_gather<T>(const NodeRec<T>*, long, const T*, const FarGeom&, const cx_t<T>*,    \
                                     double2*, const NodeFrame&, cudaStream_t);                            \
     template int far_node_scatter<T>(const NodeRec<T>*, long, const T*, const FarGeom&, const double2*,   \

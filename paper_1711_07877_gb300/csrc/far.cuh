@@ -21,8 +21,10 @@ struct FarGeom {
 // Point i: spreading stencil starts at (row, column) = cell of the spreading grid, whose
 // rows are y; frac = position - floor(position) in the same (row, column) order.
 template <typename T> struct PointRec { int2 cell; cx_t<T> frac; };
-// Node: stencil start cell in the frequency grid, fraction, circle index.
-template <typename T> struct NodeRec { int2 cell; cx_t<T> frac; int circle; int pad; };
+// Node: stencil start cell in the frequency grid, fraction, and the weight omega'_p of
+// its circle (omega_hat_p times the transform's radial factor), so the node step needs
+// no second lookup.
+template <typename T> struct NodeRec { int2 cell; cx_t<T> frac; cx_t<T> omega; };
 
 // Plan-time preparation (FP64 arithmetic).
 template <typename T>
@@ -30,7 +32,8 @@ int far_prepare_points(const double* z, long n, double cx, double cy, double h, 
                        PointRec<T>* out, cudaStream_t s);
 template <typename T>
 int far_prepare_nodes(const int* circle_start, const double* radius, const int* M, int n_circles,
-                      long n_xi, double deta, int nk, int P, NodeRec<T>* out, cudaStream_t s);
+                      long n_xi, double deta, int nk, int P, const cx_t<T>* omega_c, NodeRec<T>* out,
+                      cudaStream_t s);
 
 // Circle tables and the centre c of the point set, to place the canonical nodes in
 // absolute coordinates (the grids hold z - c).

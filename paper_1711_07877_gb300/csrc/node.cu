@@ -57,11 +57,10 @@ __device__ __forceinline__ void lane_weights(int sub, int P, const Window<T>& wi
 
 // --- value sources / sinks -------------------------------------------------------------------
 
-template <typename T> struct NodeIO {       // node step: gather -> * omega'[circle] -> ghat[i]
-    const cx_t<T>* omega;
+template <typename T> struct NodeIO {       // node step: gather -> * omega' -> ghat[i]
     cx_t<T>* ghat;
     __device__ __forceinline__ void put(long i, const NodeRec<T>& r, cx_t<T> v) const {
-        ghat[i] = cmul(v, omega[r.circle]);
+        ghat[i] = cmul(v, r.omega);
     }
 };
 template <typename T> struct NodeVal {      // node step scatter values
@@ -198,21 +197,20 @@ __global__ void __launch_bounds__(256) scatter_tiles_kernel(
     }
 }
 
-// Fused node step: one CTA per 64 x 64 tile of the frequency grid, one node per warp.
-// The tile plus a (P-1) halo of K sits in shared memory, and so do two accumulator
-// planes (re, im) of the same size.  Lanes cover the node's P x P stencil as RPI rows
-// x P8 columns per step (P8 = 8, 16 or 32 >= P, RPI = 32 / P8); the shared row stride
-// is congruent to P8 modulo 32, so every shared access of a step hits distinct banks.
-// The gathered value is reduced over the warp, weighted by omega'_p of the node's
-// circle and scattered with shared atomics (distinct cells within the warp).  Cells that
-// only this tile's stencils reach (local rows and columns in [P-1, 64)) are stored, the
-// overlap band is added atomically into kout, which the caller clears.
-template <typename T, int P8>
+// Fused node step: one CTA per 64 x 64 tile of the frequency grid.  The tile plus a
+// (P-1) halo of K sits in shared memory, with two accumulator planes (re, im) of the
+// same size.  A group of G lanes (G = 8, 16 or 32 >= P; 32 / G nodes per warp) takes
+// one node at a time, lane = stencil column: rows are accumulated in registers and the
+// columns reduced with shuffles (gather), the value is weighted by the node's omega'
+// and added back with shared atomics (scatter), with the weights computed once.  The
+// next record is loaded while the current one is processed.  Cells that only this
+// tile's stencils reach (local rows and columns in [P-1, 64)) are stored, the overlap
+// band is added atomically into kout, which the caller clears.
+template <typename T, int G>
 __global__ void __launch_bounds__(256) node_fused_kernel(
     const NodeRec<T>* __restrict__ rec, const long long* __restrict__ tile_start, int ntx, int n, int P, int Ws,
-    Window<T> win, const cx_t<T>* __restrict__ omega, const cx_t<T>* __restrict__ kin, cx_t<T>* __restrict__ kout) {
+    Window<T> win, const cx_t<T>* __restrict__ kin, cx_t<T>* __restrict__ kout) {
     using C = cx_t<T>;
-    constexpr int RPI = 32 / P8;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int tile = blockIdx.x;
     const long long b0 = tile_start[tile], b1 = tile_start[tile + 1];
@@ -233,44 +231,51 @@ __global__ void __launch_bounds__(256) node_fused_kernel(
     }
     __syncthreads();
     const int lane = threadIdx.x & 31;
-    const int a0 = lane / P8, b = lane % P8;
-    const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    const int steps = (P + RPI - 1) / RPI;
-    for (long long i = b0 + warp; i < b1; i += nwarps) {
-        const NodeRec<T> q = rec[i];
+    const int sub = lane % G;
+    const unsigned gmask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << (lane - sub));
+    const int group = threadIdx.x / G, ngroups = blockDim.x / G;
+    long long i = b0 + group;
+    NodeRec<T> nxt;
+    if (i < b1) nxt = rec[i];
+    for (; i < b1; i += ngroups) {
+        const NodeRec<T> q = nxt;
+        if (i + ngroups < b1) nxt = rec[i + ngroups];          // prefetch
         const int rx = q.cell.x - ox, ry = q.cell.y - oy;
-        // lane l < P holds w(l - P/2 + 1 - frac) for rows (wl) and, via b, for columns (wy)
-        const T wl = lane < P ? win(static_cast<T>(lane - P / 2 + 1) - q.frac.x) : static_cast<T>(0);
-        const T wy = b < P ? win(static_cast<T>(b - P / 2 + 1) - q.frac.y) : static_cast<T>(0);
-        const int base = (rx + a0) * Ws + ry + b;
+        T wx = 0, wy = 0;
+        if (sub < P) {
+            wx = win(static_cast<T>(sub - P / 2 + 1) - q.frac.x);
+            wy = win(static_cast<T>(sub - P / 2 + 1) - q.frac.y);
+        }
+        const int base = rx * Ws + ry + sub;
         T sr = 0, si = 0;
-#pragma unroll 4
-        for (int st = 0; st < steps; ++st) {
-            const int a = a0 + st * RPI;
-            const T w = __shfl_sync(0xffffffffu, wl, a & 31);
-            if (a < P && b < P) {
-                const C v = s[base + st * RPI * Ws];
-                sr += w * v.x;
-                si += w * v.y;
+#pragma unroll
+        for (int a = 0; a < G; ++a) {
+            if (a < P) {
+                const T w = __shfl_sync(gmask, wx, a, G);
+                if (sub < P) {
+                    const C v = s[base + a * Ws];
+                    sr += w * v.x;
+                    si += w * v.y;
+                }
             }
         }
         sr *= wy;
         si *= wy;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            sr += __shfl_xor_sync(0xffffffffu, sr, o);
-            si += __shfl_xor_sync(0xffffffffu, si, o);
+        for (int o = G / 2; o > 0; o >>= 1) {
+            sr += __shfl_xor_sync(gmask, sr, o, G);
+            si += __shfl_xor_sync(gmask, si, o, G);
         }
-        const C g = cmul(mk<T>(sr, si), omega[q.circle]);
+        const C g = cmul(mk<T>(sr, si), q.omega);
         const T gr = g.x * wy, gi = g.y * wy;
-#pragma unroll 4
-        for (int st = 0; st < steps; ++st) {
-            const int a = a0 + st * RPI;
-            const T w = __shfl_sync(0xffffffffu, wl, a & 31);
-            if (a < P && b < P) {
-                const int o = base + st * RPI * Ws;
-                atomicAdd(acc_re + o, gr * w);
-                atomicAdd(acc_im + o, gi * w);
+#pragma unroll
+        for (int a = 0; a < G; ++a) {
+            if (a < P) {
+                const T w = __shfl_sync(gmask, wx, a, G);
+                if (sub < P) {
+                    atomicAdd(acc_re + base + a * Ws, gr * w);
+                    atomicAdd(acc_im + base + a * Ws, gi * w);
+                }
             }
         }
     }
@@ -380,7 +385,7 @@ size_t node_fused_smem(int Pk) {
 }
 
 template <typename T>
-int node_step_fused(const NodeRec<T>* nodes, const long long* tile_start, const FarGeom& g, const cx_t<T>* omega,
+int node_step_fused(const NodeRec<T>* nodes, const long long* tile_start, const FarGeom& g,
                     const cx_t<T>* kin, cx_t<T>* kout, cudaStream_t s) {
     SBD_CUDA_TRY(cudaMemsetAsync(kout, 0, sizeof(cx_t<T>) * static_cast<size_t>(g.nk) * g.nk, s));
     const int ntx = tiles_per_side(g.nk);
@@ -393,15 +398,15 @@ int node_step_fused(const NodeRec<T>* nodes, const long long* tile_start, const 
     if (P8 == 8) {
         auto k = node_fused_kernel<T, 8>;
         SBD_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
-        k<<<nt, 256, smem, s>>>(nodes, tile_start, ntx, g.nk, g.Pk, Ws, win, omega, kin, kout);
+        k<<<nt, 256, smem, s>>>(nodes, tile_start, ntx, g.nk, g.Pk, Ws, win, kin, kout);
     } else if (P8 == 16) {
         auto k = node_fused_kernel<T, 16>;
         SBD_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
-        k<<<nt, 256, smem, s>>>(nodes, tile_start, ntx, g.nk, g.Pk, Ws, win, omega, kin, kout);
+        k<<<nt, 256, smem, s>>>(nodes, tile_start, ntx, g.nk, g.Pk, Ws, win, kin, kout);
     } else {
         auto k = node_fused_kernel<T, 32>;
         SBD_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
-        k<<<nt, 256, smem, s>>>(nodes, tile_start, ntx, g.nk, g.Pk, Ws, win, omega, kin, kout);
+        k<<<nt, 256, smem, s>>>(nodes, tile_start, ntx, g.nk, g.Pk, Ws, win, kin, kout);
     }
     SBD_LAUNCH_CHECK();
     return SBD_OK;
@@ -409,8 +414,8 @@ int node_step_fused(const NodeRec<T>* nodes, const long long* tile_start, const 
 
 template <typename T>
 int node_step_tiled(const NodeRec<T>* nodes, const long long* tile_start, const FarGeom& g,
-                    const cx_t<T>* omega, const cx_t<T>* kin, cx_t<T>* ghat, cx_t<T>* kout, cudaStream_t s) {
-    int rc = launch_gather<T>(nodes, tile_start, g.nk, g.Pk, g.kwin, g.beta_k, kin, NodeIO<T>{omega, ghat}, s);
+                    const cx_t<T>* kin, cx_t<T>* ghat, cx_t<T>* kout, cudaStream_t s) {
+    int rc = launch_gather<T>(nodes, tile_start, g.nk, g.Pk, g.kwin, g.beta_k, kin, NodeIO<T>{ghat}, s);
     if (rc) return rc;
     return launch_scatter<T>(nodes, tile_start, g.nk, g.Pk, g.kwin, g.beta_k, NodeVal<T>{ghat}, kout, s);
 }
@@ -435,10 +440,10 @@ int interp_tiled(const PointRec<T>* pts, const int* perm, const long long* tile_
     template int tile_sort<PointRec<T>>(const PointRec<T>*, long, int, PointRec<T>*, int*, long long*,       \
                                         cudaStream_t);                                                       \
     template int node_step_tiled<T>(const NodeRec<T>*, const long long*, const FarGeom&, const cx_t<T>*,     \
-                                    const cx_t<T>*, cx_t<T>*, cx_t<T>*, cudaStream_t);                       \
+                                    cx_t<T>*, cx_t<T>*, cudaStream_t);                                       \
     template size_t node_fused_smem<T>(int);                                                                 \
     template int node_step_fused<T>(const NodeRec<T>*, const long long*, const FarGeom&, const cx_t<T>*,     \
-                                    const cx_t<T>*, cx_t<T>*, cudaStream_t);                                 \
+                                    cx_t<T>*, cudaStream_t);                                                 \
     template int spread_tiled<T>(const PointRec<T>*, const int*, const long long*, const FarGeom&,           \
                                  const void*, bool, cx_t<T>*, cudaStream_t);                                 \
     template int interp_tiled<T>(const PointRec<T>*, const int*, const long long*, const FarGeom&,           \

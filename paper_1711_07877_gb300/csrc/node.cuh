@@ -18,14 +18,14 @@ int tile_sort(const Rec* in, long n_rec, int n, Rec* sorted, int* perm, long lon
 // kout (nk x nk, fully written) = scatter(omega' * gather(kin)); ghat is n_xi scratch.
 template <typename T>
 int node_step_tiled(const NodeRec<T>* nodes, const long long* tile_start, const FarGeom& g,
-                    const cx_t<T>* omega, const cx_t<T>* kin, cx_t<T>* ghat, cx_t<T>* kout, cudaStream_t s);
+                    const cx_t<T>* kin, cx_t<T>* ghat, cx_t<T>* kout, cudaStream_t s);
 
 // The same in one kernel per tile: gather, weight and scatter into a shared accumulator,
 // whose overlap band is added atomically into kout (cleared here).
 template <typename T>
 size_t node_fused_smem(int Pk);   // dynamic shared memory of the fused kernel
 template <typename T>
-int node_step_fused(const NodeRec<T>* nodes, const long long* tile_start, const FarGeom& g, const cx_t<T>* omega,
+int node_step_fused(const NodeRec<T>* nodes, const long long* tile_start, const FarGeom& g,
                     const cx_t<T>* kin, cx_t<T>* kout, cudaStream_t s);
 
 // grid (m x m, fully written) = spreading of f (float64 or complex128, original order).
