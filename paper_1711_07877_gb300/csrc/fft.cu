@@ -1,7 +1,7 @@
-// Batched row FFT (mixed radix 2/3/4/5, Stockham autosort in shared memory) and
+// Batched row FFT (mixed radix 2/3/4/5, in-place decimation in time in shared memory) and
 // tiled transpose.  Each CTA owns one row: the row is loaded once (zero padding,
-// placement shift and diagonal scaling fused into the load), all radix stages run
-// between two shared buffers, and only the
+// placement shift, digit reversal and diagonal scaling fused into the load), all
+// radix stages run in place in shared memory, and only the
 // requested output window is written back.
 #include <algorithm>
 #include <map>
@@ -106,56 +106,75 @@ __device__ __forceinline__ void small_dft(cx_t<T>* v, int sign) {
     }
 }
 
-// One radix-R Stockham stage, out of place from src to dst (both in shared memory):
-// butterfly j in [0, nq/R) reads src[j + r nq/R] (consecutive j, consecutive addresses),
-// twiddles by w^(r k) with k = j mod Ns, and writes dst[(j / Ns) Ns R + k + r Ns], so the
-// output of the last stage is in natural order.  j / Ns uses the stage's multiplier.
+template <typename T> struct MaxB;
+template <> struct MaxB<float>  { static constexpr int n_max = 28672; };
+template <> struct MaxB<double> { static constexpr int n_max = 14336; };
+
+// Stage of the in-place mixed-radix decimation-in-time FFT: groups of L = Lp * R
+// elements combine R sub-transforms of length Lp (stored as consecutive blocks)
+// into one transform of length L, in place.  A thread keeps one offset k within
+// the sub-transforms (so its R - 1 twiddles are loaded once per stage) and walks
+// the groups g; no division per butterfly.
 template <typename T, int R>
-__device__ __forceinline__ void stockham_stage(const cx_t<T>* __restrict__ src, cx_t<T>* __restrict__ dst, int nq,
-                                               int Ns, unsigned magic, int sign, const cx_t<T>* __restrict__ tw,
-                                               int tw_unit, int nthreads) {
+__device__ __forceinline__ void dit_stage(cx_t<T>* s, int n, int Lp, int sign, const cx_t<T>* __restrict__ tw,
+                                          int tw_scale, int nthreads) {
     using C = cx_t<T>;
-    const int nb = nq / R;
-    const int tw_step = tw_unit * (nq / (Ns * R));
-    for (int j = threadIdx.x; j < nb; j += nthreads) {
-        const int q = Ns == 1 ? j : static_cast<int>(__umulhi(static_cast<unsigned>(j), magic));
-        const int k = j - q * Ns;
-        C v[R];
-#pragma unroll
-        for (int r = 0; r < R; ++r) v[r] = src[j + r * nb];
-        if (Ns > 1) {
-#pragma unroll
-            for (int r = 1; r < R; ++r) {
-                C w = tw[r * k * tw_step];
-                if (sign > 0) w.y = -w.y;
-                v[r] = cmul(v[r], w);
-            }
-        }
-        small_dft<T, R>(v, sign);
-        const int o = q * Ns * R + k;
-#pragma unroll
-        for (int r = 0; r < R; ++r) dst[o + r * Ns] = v[r];
+    const int L = Lp * R;
+    const int G = n / L;
+    const int tw_step = tw_scale * G;          // twiddle table index step of exp(2 pi i k / L)
+    int k, g0, gstep;
+    bool active = true;
+    if (Lp >= nthreads) {
+        k = threadIdx.x;
+        g0 = 0;
+        gstep = 1;
+    } else {
+        k = threadIdx.x % Lp;
+        g0 = threadIdx.x / Lp;
+        gstep = nthreads / Lp;
+        active = g0 < gstep;
     }
+    for (; active && k < Lp; k += nthreads) {
+        C w[R];
+#pragma unroll
+        for (int r = 1; r < R; ++r) {
+            C t = tw[r * k * tw_step];
+            if (sign > 0) t.y = -t.y;
+            w[r] = t;
+        }
+        for (int g = g0; g < G; g += gstep) {
+            const int base = g * L + k;
+            C v[R];
+#pragma unroll
+            for (int r = 0; r < R; ++r) v[r] = s[base + r * Lp];
+            if (Lp > 1) {
+#pragma unroll
+                for (int r = 1; r < R; ++r) v[r] = cmul(v[r], w[r]);
+            }
+            small_dft<T, R>(v, sign);
+#pragma unroll
+            for (int r = 0; r < R; ++r) s[base + r * Lp] = v[r];
+        }
+    }
+    __syncthreads();
 }
 
-// One row (blockIdx.y) and one phase (blockIdx.x) of a length-n transform done as Q
-// transforms of length nq = n / Q (Q = 1, 2 or 4): output k = Q k' + r is the length-nq
-// DFT of y_r[t] = sum_{j < Q} x[t + j nq] w_n^{r (t + j nq)} (fold and twist on the load).
-// The two shared buffers of nq elements alternate as source and destination.
+// One row (blockIdx.x) and one phase (blockIdx.y) of a length-n transform done as Q
+// transforms of length nq = n / Q (Q = 1 or 2): output k = Q k' + r is the length-nq DFT
+// of y_r[t] = sum_{j < Q} x[t + j nq] w_n^{r (t + j nq)} (fold and twist on the load).
 template <typename T, int NT>
 __global__ void __launch_bounds__(NT) fft_rows_kernel(
     const cx_t<T>* __restrict__ in, long in_stride, int in_len, int in_shift,
     cx_t<T>* __restrict__ out, long out_stride, int out_len, int out_shift,
-    int n, int Q, int sign, FftPlan1D plan, const cx_t<T>* __restrict__ tw,
+    int n, int Q, int sign, FftPlan1D plan, const cx_t<T>* __restrict__ tw, const int* __restrict__ perm,
     const T* __restrict__ pre_elem, const T* __restrict__ pre_row,
     const T* __restrict__ post_elem, const T* __restrict__ post_row) {
     using C = cx_t<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int nq = n / Q;
-    C* buf0 = reinterpret_cast<C*>(smem_raw);
-    C* buf1 = buf0 + nq;
-    const long row = blockIdx.y;     // the phases of a row are adjacent CTAs (they read the same row)
+    C* s = reinterpret_cast<C*>(smem_raw);
+    const long row = blockIdx.y;     // phases of a row are adjacent CTAs (they read the same row)
     const int r = blockIdx.x;
+    const int nq = n / Q;
     const C* src = in + row * in_stride;
     const T rs = pre_row ? pre_row[row] : static_cast<T>(1);
     for (int i = threadIdx.x; i < nq; i += NT) {
@@ -169,42 +188,68 @@ __global__ void __launch_bounds__(NT) fft_rows_kernel(
                 T sc = rs;
                 if (pre_elem) sc *= pre_elem[t];
                 v = cscale(v, sc);
-                if (r) {                              // twist w_n^{r idx}
-                    C w = tw[(static_cast<long>(r) * idx) % n];
+                if (r) {                              // twist w_n^{idx}
+                    C w = tw[idx];
                     if (sign > 0) w.y = -w.y;
                     v = cmul(v, w);
                 }
                 acc = cadd(acc, v);
             }
         }
-        buf0[i] = acc;
+        s[perm[i]] = acc;
     }
     __syncthreads();
-    C* a = buf0;
-    C* b = buf1;
-    int Ns = 1;
+    int Lp = 1;
     for (int st = 0; st < plan.nstages; ++st) {
         const int R = plan.radix[st];
-        const unsigned mg = plan.magic[st];
-        if (R == 4)      stockham_stage<T, 4>(a, b, nq, Ns, mg, sign, tw, Q, NT);
-        else if (R == 2) stockham_stage<T, 2>(a, b, nq, Ns, mg, sign, tw, Q, NT);
-        else if (R == 3) stockham_stage<T, 3>(a, b, nq, Ns, mg, sign, tw, Q, NT);
-        else             stockham_stage<T, 5>(a, b, nq, Ns, mg, sign, tw, Q, NT);
-        __syncthreads();
-        C* t = a; a = b; b = t;
-        Ns *= R;
+        if (R == 4)      dit_stage<T, 4>(s, nq, Lp, sign, tw, Q, NT);
+        else if (R == 2) dit_stage<T, 2>(s, nq, Lp, sign, tw, Q, NT);
+        else if (R == 3) dit_stage<T, 3>(s, nq, Lp, sign, tw, Q, NT);
+        else             dit_stage<T, 5>(s, nq, Lp, sign, tw, Q, NT);
+        Lp *= R;
     }
     C* dst = out + row * out_stride;
     const T ps = post_row ? post_row[row] : static_cast<T>(1);
     for (int e = threadIdx.x; e < out_len; e += NT) {
         int k = e + out_shift;
         if (k >= n) k -= n;
-        if (Q > 1 && (k % Q) != r) continue;
-        C v = a[k / Q];
+        if (Q == 2 && (k & 1) != r) continue;
+        C v = s[Q == 2 ? (k >> 1) : k];
         T sc = ps;
         if (post_elem) sc *= post_elem[e];
         dst[e] = cscale(v, sc);
     }
+}
+
+// Digit-reversal permutation of the decimation-in-time schedule: with radices
+// R_1..R_s applied in that order, index i = sum of digits (least significant digit in
+// base R_s, then R_{s-1}, ...) lands at position sum_k d_k R_1...R_{k-1}.
+const int* digit_perm(const FftPlan1D& plan, cudaStream_t stream) {
+    static std::mutex mu;
+    static std::map<int, int*> cache;
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = cache.find(plan.n);
+    if (it != cache.end()) return it->second;
+    const int n = plan.n;
+    std::vector<int> h(n);
+    std::vector<int> weight(plan.nstages);
+    int w = 1;
+    for (int k = 0; k < plan.nstages; ++k) { weight[k] = w; w *= plan.radix[k]; }
+    for (int i = 0; i < n; ++i) {
+        int v = i, pos = 0;
+        for (int k = plan.nstages - 1; k >= 0; --k) {
+            const int R = plan.radix[k];
+            pos += (v % R) * weight[k];
+            v /= R;
+        }
+        h[i] = pos;
+    }
+    int* d = nullptr;
+    if (cudaMalloc(&d, sizeof(int) * n) != cudaSuccess) return nullptr;
+    cudaMemcpyAsync(d, h.data(), sizeof(int) * n, cudaMemcpyHostToDevice, stream);
+    cudaStreamSynchronize(stream);
+    cache[n] = d;
+    return d;
 }
 
 template <typename T>
@@ -230,24 +275,23 @@ __global__ void transpose_kernel(const cx_t<T>* __restrict__ in, long in_stride,
 }  // namespace
 
 bool fft_make_plan(int n, FftPlan1D& p) {
+    // Odd radices first and the powers of two last: the early stages, whose accesses
+    // are strided by the radix, then use odd strides (distinct shared-memory banks), and
+    // with a single power-of-two stage of radix R at the end, consecutive digit-reversed
+    // load positions are n / R apart, which is odd when n has at most two factors of 2
+    // beyond that radix.
     p.n = n;
     p.nstages = 0;
     int v = n;
     int twos = 0;
     while (v % 2 == 0) { v /= 2; ++twos; }
     std::vector<int> rs;
-    while (twos >= 2) { rs.push_back(4); twos -= 2; }
-    if (twos) rs.push_back(2);
-    while (v % 3 == 0) { v /= 3; rs.push_back(3); }
     while (v % 5 == 0) { v /= 5; rs.push_back(5); }
+    while (v % 3 == 0) { v /= 3; rs.push_back(3); }
+    if (twos & 1) rs.push_back(2);
+    while (twos >= 2) { rs.push_back(4); twos -= 2; }
     if (v != 1 || static_cast<int>(rs.size()) > kFftMaxStages) return false;
-    int Ns = 1;
-    for (size_t i = 0; i < rs.size(); ++i) {
-        p.radix[i] = rs[i];
-        // j / Ns = umulhi(j, ceil(2^32 / Ns)), exact for j, Ns <= 2^15
-        p.magic[i] = Ns == 1 ? 0u : static_cast<unsigned>((0x100000000ULL + Ns - 1) / Ns);
-        Ns *= rs[i];
-    }
+    for (size_t i = 0; i < rs.size(); ++i) p.radix[i] = rs[i];
     p.nstages = static_cast<int>(rs.size());
     p.threads = 1024;
     return true;
@@ -255,21 +299,20 @@ bool fft_make_plan(int n, FftPlan1D& p) {
 
 int fft_max_row(bool fp64) {
     const int smem = 227 * 1024;
-    return std::min(smem / (2 * (fp64 ? 16 : 8)), 32768);
+    const int lim = smem / (fp64 ? 16 : 8);
+    return fp64 ? std::min(lim, MaxB<double>::n_max) : std::min(lim, MaxB<float>::n_max);
 }
 
 static int fft_phases(int n, bool fp64);
 
-// Phases per row: the smallest Q in {1, 2, 4} dividing n whose length n / Q fits one CTA's
-// shared memory twice (source and destination buffers).
+// Phases per row: the smallest Q in {1, 2} whose length n / Q fits one CTA's shared memory.
 static int fft_phases(int n, bool fp64) {
     const int lim = fft_max_row(fp64);
-    for (int Q : {1, 2, 4})
-        if (n % Q == 0 && n / Q <= lim) return Q;
-    return 0;
+    if (n % 2 == 0 && n > lim) return 2;
+    return 1;
 }
 
-int fft_max_length(bool fp64) { return 4 * fft_max_row(fp64); }
+int fft_max_length(bool fp64) { return 2 * fft_max_row(fp64); }
 
 template <typename T>
 int fft_rows(const cx_t<T>* in, long in_stride, int in_len, int in_shift,
@@ -280,18 +323,19 @@ int fft_rows(const cx_t<T>* in, long in_stride, int in_len, int in_shift,
     if (rows <= 0) return SBD_OK;
     const bool fp64 = sizeof(T) == 8;
     const int Q = fft_phases(n, fp64);
+    const int nq = n / Q;
     FftPlan1D plan;
-    if (Q == 0 || !fft_make_plan(n / Q, plan)) {
+    if (!fft_make_plan(nq, plan) || nq > fft_max_row(fp64) || n % Q) {
         set_error("FFT length not supported: " + std::to_string(n));
         return SBD_ENOTSUP;
     }
-    const int nq = n / Q;
     const cx_t<T>* tw = twiddles<T>(n, stream);
-    if (!tw) {
+    const int* perm = digit_perm(plan, stream);
+    if (!tw || !perm) {
         set_error("FFT table allocation failed");
         return SBD_ENOMEM;
     }
-    const size_t smem = 2 * sizeof(cx_t<T>) * static_cast<size_t>(nq);
+    const size_t smem = sizeof(cx_t<T>) * static_cast<size_t>(nq);
     in_shift = ((in_shift % n) + n) % n;
     out_shift = ((out_shift % n) + n) % n;
     for (int r0 = 0; r0 < rows; r0 += 65535) {          // grid.y holds at most 65535 rows
@@ -305,12 +349,12 @@ int fft_rows(const cx_t<T>* in, long in_stride, int in_len, int in_shift,
             auto k = fft_rows_kernel<T, 1024>;
             SBD_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
             k<<<grid, 1024, smem, stream>>>(ip, in_stride, in_len, in_shift, op, out_stride, out_len, out_shift,
-                                            n, Q, sign, plan, tw, pre_elem, prr, post_elem, por);
+                                            n, Q, sign, plan, tw, perm, pre_elem, prr, post_elem, por);
         } else {
             auto k = fft_rows_kernel<T, 256>;
             SBD_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
             k<<<grid, 256, smem, stream>>>(ip, in_stride, in_len, in_shift, op, out_stride, out_len, out_shift,
-                                           n, Q, sign, plan, tw, pre_elem, prr, post_elem, por);
+                                           n, Q, sign, plan, tw, perm, pre_elem, prr, post_elem, por);
         }
         SBD_LAUNCH_CHECK();
     }

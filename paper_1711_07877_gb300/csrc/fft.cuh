@@ -13,16 +13,15 @@ struct FftPlan1D {
     int n = 0;
     int nstages = 0;
     int radix[kFftMaxStages];
-    unsigned magic[kFftMaxStages];   // division by the stage's sub-length Ns via umulhi
     int threads = 0;
 };
 
 // Radix schedule for n = 2^a 3^b 5^c (fours first); false when n has another factor.
 bool fft_make_plan(int n, FftPlan1D& p);
 
-// Largest length a single CTA transforms (two buffers of it in shared memory).
+// Largest row length a single CTA can hold in shared memory for this element type.
 int fft_max_row(bool fp64);
-// Largest transform length fft_rows accepts (four phases of fft_max_row).
+// Largest transform length fft_rows accepts (two phases of fft_max_row).
 int fft_max_length(bool fp64);
 
 // One batched row pass:
