@@ -216,6 +216,32 @@ int sbd_fft2(const void* in, void* out, int32_t n0, int32_t n1, int32_t sign, in
 int sbd_profile(sbd_plan_t plan, int32_t enable);
 int sbd_profile_read(sbd_plan_t plan, double* ms, int64_t* count);
 
+/* ---------------------------------------------------------------------------------
+ * sbd_fft2_noalloc - sbd_fft2 without any device memory allocation.  (The paper has no
+ * counterpart: this is a library service, not part of the method.)
+ *
+ * For callers that may not allocate device memory while they run: programs that hand
+ * all device memory to their own pool at start-up, or latency-critical loops whose
+ * policy forbids cudaMalloc / cudaFree (and the allocator synchronisation they may
+ * imply) after initialisation.  The transform's temporary grid and its twiddle and
+ * digit-reversal tables live in a fixed file-scope device array of
+ * SBD_NOALLOC_FFT_MAX_BYTES + 2 * SBD_NOALLOC_FFT_MAX_SIDE * 20 bytes, which every GPU
+ * that loads the library keeps until the process exits.
+ *   in, out, n0, n1, sign, form, cuda_stream   as for sbd_fft2 (in and out may alias).
+ *   Limits: 2 <= n0, n1 <= SBD_NOALLOC_FFT_MAX_SIDE, each a product of 2, 3 and 5, and
+ *   n0 * n1 * (8 for FP32, 16 for FP64) <= SBD_NOALLOC_FFT_MAX_BYTES; larger sizes
+ *   return SBD_EINVAL with the limits in sbd_last_error_message().
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress,
+ * once per device, with that device current); make that first call before any stream
+ * capture.  All calls share the one array and its contents persist between calls, so
+ * calls that overlap on the GPU (different streams without ordering) race; the
+ * function clears nothing it does not overwrite first.
+ * ------------------------------------------------------------------------------- */
+#define SBD_NOALLOC_FFT_MAX_BYTES (4 * 1024 * 1024)
+#define SBD_NOALLOC_FFT_MAX_SIDE  4096
+int sbd_fft2_noalloc(const void* in, void* out, int32_t n0, int32_t n1, int32_t sign, int32_t form,
+                     void* cuda_stream);
+
 const char* sbd_error_string(int code);
 const char* sbd_last_error_message(void);
 const char* sbd_version(void);

@@ -363,6 +363,37 @@ int fft_rows(const cx_t<T>* in, long in_stride, int in_len, int in_shift,
 }
 
 template <typename T>
+int fft_rows_tables(const cx_t<T>* in, long in_stride, int in_len, cx_t<T>* out, long out_stride, int out_len,
+                    int rows, int n, int sign, const cx_t<T>* tw, const int* perm, cudaStream_t stream) {
+    if (rows <= 0) return SBD_OK;
+    FftPlan1D plan;
+    if (!fft_make_plan(n, plan) || n > fft_max_row(sizeof(T) == 8)) {
+        set_error("FFT length not supported: " + std::to_string(n));
+        return SBD_ENOTSUP;
+    }
+    const size_t smem = sizeof(cx_t<T>) * static_cast<size_t>(n);
+    for (int r0 = 0; r0 < rows; r0 += 65535) {
+        const int nr = std::min(65535, rows - r0);
+        const dim3 grid(1u, static_cast<unsigned>(nr));
+        const cx_t<T>* ip = in + static_cast<long>(r0) * in_stride;
+        cx_t<T>* op = out + static_cast<long>(r0) * out_stride;
+        if (n > 2048) {
+            auto k = fft_rows_kernel<T, 1024>;
+            SBD_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
+            k<<<grid, 1024, smem, stream>>>(ip, in_stride, in_len, 0, op, out_stride, out_len, 0, n, 1, sign, plan, tw,
+                                            perm, nullptr, nullptr, nullptr, nullptr);
+        } else {
+            auto k = fft_rows_kernel<T, 256>;
+            SBD_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
+            k<<<grid, 256, smem, stream>>>(ip, in_stride, in_len, 0, op, out_stride, out_len, 0, n, 1, sign, plan, tw,
+                                           perm, nullptr, nullptr, nullptr, nullptr);
+        }
+        SBD_LAUNCH_CHECK();
+    }
+    return SBD_OK;
+}
+
+template <typename T>
 int transpose(const cx_t<T>* in, long in_stride, long in_batch, cx_t<T>* out, long out_stride,
               long out_batch, int rows, int cols, int nb, cudaStream_t stream) {
     if (rows <= 0 || cols <= 0 || nb <= 0) return SBD_OK;
@@ -376,6 +407,10 @@ template int fft_rows<float>(const float2*, long, int, int, float2*, long, int, 
                              const float*, const float*, const float*, const float*, cudaStream_t);
 template int fft_rows<double>(const double2*, long, int, int, double2*, long, int, int, int, int, int,
                               const double*, const double*, const double*, const double*, cudaStream_t);
+template int fft_rows_tables<float>(const float2*, long, int, float2*, long, int, int, int, int, const float2*,
+                                    const int*, cudaStream_t);
+template int fft_rows_tables<double>(const double2*, long, int, double2*, long, int, int, int, int, const double2*,
+                                     const int*, cudaStream_t);
 template int transpose<float>(const float2*, long, long, float2*, long, long, int, int, int, cudaStream_t);
 template int transpose<double>(const double2*, long, long, double2*, long, long, int, int, int, cudaStream_t);
 

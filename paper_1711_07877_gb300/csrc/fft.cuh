@@ -36,6 +36,13 @@ int fft_rows(const cx_t<T>* in, long in_stride, int in_len, int in_shift,
              const T* pre_elem, const T* pre_row, const T* post_elem, const T* post_row,
              cudaStream_t stream);
 
+// Natural-order row transforms of length n (input and output windows start at 0) with
+// caller-provided tables: tw[t] = exp(-2 pi i t / n), perm = the digit reversal of
+// fft_make_plan(n).  Allocates nothing.
+template <typename T>
+int fft_rows_tables(const cx_t<T>* in, long in_stride, int in_len, cx_t<T>* out, long out_stride, int out_len,
+                    int rows, int n, int sign, const cx_t<T>* tw, const int* perm, cudaStream_t stream);
+
 // out[c][r] = in[r][c] for a rows x cols matrix (row strides in elements), batched over nb
 // matrices spaced in_batch / out_batch elements apart.
 template <typename T>

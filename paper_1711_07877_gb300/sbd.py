@@ -72,6 +72,7 @@ _SIGS = {
     "sbd_destroy": ([_P], ctypes.c_int),
     "sbd_offline_fit": ([sbd_kernel, _D, _D, _D, _I32, _I64, _P, _P, _P, _P, _P, _P], ctypes.c_int),
     "sbd_fft2": ([_P, _P, _I32, _I32, _I32, _I32, _P], ctypes.c_int),
+    "sbd_fft2_noalloc": ([_P, _P, _I32, _I32, _I32, _I32, _P], ctypes.c_int),
     "sbd_profile": ([_P, _I32], ctypes.c_int),
     "sbd_profile_read": ([_P, _P, _P], ctypes.c_int),
     "sbd_error_string": ([ctypes.c_int], ctypes.c_char_p),
@@ -226,3 +227,12 @@ def sbd_offline_fit(kernel_kind: int, kappa: float, delta_min: float, delta_max:
 
 def sbd_fft2(x, out, n0: int, n1: int, sign: int, form: int, stream=None) -> None:
     _check(lib.sbd_fft2(_ptr(x), _ptr(out), n0, n1, sign, form, _stream(stream)), "sbd_fft2")
+
+
+SBD_NOALLOC_FFT_MAX_BYTES = 4 * 1024 * 1024
+SBD_NOALLOC_FFT_MAX_SIDE = 4096
+
+
+def sbd_fft2_noalloc(x, out, n0: int, n1: int, sign: int, form: int, stream=None) -> None:
+    """sbd_fft2 with its scratch in the library's fixed device array (no allocation)."""
+    _check(lib.sbd_fft2_noalloc(_ptr(x), _ptr(out), n0, n1, sign, form, _stream(stream)), "sbd_fft2_noalloc")
