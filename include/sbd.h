@@ -198,6 +198,33 @@ int sbd_fft2(const void* in, void* out, int32_t n0, int32_t n1, int32_t sign, in
              void* cuda_stream);
 
 /* ---------------------------------------------------------------------------------
+ * sbd_gmres - restarted GMRES for (shift I + scale A) x = b, A the plan's matvec: the
+ * iterative solution of boundary-integral systems that motivates the fast convolution
+ * (Introduction).  Arnoldi with two-pass classical Gram-Schmidt, Givens rotations.
+ *   b      device, N (float64 Laplace / complex128 Helmholtz), read only.
+ *   x      device, N: initial guess on entry (zero it for none), solution on return.
+ *   opt    shift, scale (complex; real parts only for Laplace), tol (relative residual
+ *          ||b - (shift I + scale A) x|| / ||b||), restart (Krylov dimension), max_iter.
+ *   iterations, rel_residual   host outputs (may be NULL): Arnoldi steps done; the
+ *          final relative residual (recomputed from b - (shift I + scale A) x when the
+ *          solver stops converged, the Arnoldi estimate when it stops at max_iter).
+ * Errors: SBD_EINVAL for a null plan/b/x/opt, restart < 1, max_iter < 0 or tol <= 0;
+ * SBD_ECUDA from a device failure (x then holds a partial update).
+ * Blocks the calling thread (one device-to-host read per Gram-Schmidt pass); runs its
+ * device work on cuda_stream; allocates (restart + 2) N-vectors of workspace per call.
+ * Calls for different plans may run concurrently from different host threads.
+ * ------------------------------------------------------------------------------- */
+typedef struct {
+    double  shift_re, shift_im;
+    double  scale_re, scale_im;
+    double  tol;
+    int32_t restart;
+    int32_t max_iter;
+} sbd_gmres_options;
+int sbd_gmres(sbd_plan_t plan, const void* b, void* x, const sbd_gmres_options* opt, int32_t* iterations,
+              double* rel_residual, void* cuda_stream);
+
+/* ---------------------------------------------------------------------------------
  * Step timing of the on-line part.  sbd_profile(plan, 1) waits for the device,
  * clears the counters and starts recording a pair of CUDA events on the caller's
  * stream around every step of sbd_matvec / sbd_far / sbd_close (0 stops).

@@ -1,5 +1,7 @@
 // C ABI of libsbd.so: plan construction (off-line part) and the on-line matvec.
 #include <chrono>
+#include <map>
+#include <mutex>
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -20,6 +22,19 @@ thread_local std::string g_last_error;
 }
 
 void set_error(const std::string& msg) { g_last_error = msg; }
+
+int raise_smem_limit_fn(const void* func, size_t bytes) {
+    static std::mutex mu;
+    static std::map<std::pair<int, const void*>, size_t> limit;
+    int dev = 0;
+    SBD_CUDA_TRY(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lock(mu);
+    size_t& cur = limit[{dev, func}];
+    if (cur >= bytes) return SBD_OK;
+    SBD_CUDA_TRY(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(bytes)));
+    cur = bytes;
+    return SBD_OK;
+}
 
 }  // namespace sbd
 

@@ -30,6 +30,15 @@ template <typename C, typename T> __host__ __device__ __forceinline__ C cscale(C
 // Thread-local detail text of the last error (sbd_last_error_message).
 void set_error(const std::string& msg);
 
+// Raises (never lowers) a kernel's dynamic shared-memory limit on the current device to
+// at least `bytes`, under a process-wide lock, so that concurrent host threads launching
+// the same kernel with different sizes never shrink each other's limit.
+int raise_smem_limit_fn(const void* func, size_t bytes);
+template <typename K>
+inline int raise_smem_limit(K* kernel, size_t bytes) {
+    return raise_smem_limit_fn(reinterpret_cast<const void*>(kernel), bytes);
+}
+
 }  // namespace sbd
 
 #define SBD_CUDA_TRY(call)                                                        \
@@ -39,6 +48,12 @@ void set_error(const std::string& msg);
             ::sbd::set_error(std::string(#call) + ": " + cudaGetErrorString(e_)); \
             return e_ == cudaErrorMemoryAllocation ? SBD_ENOMEM : SBD_ECUDA;      \
         }                                                                         \
+    } while (0)
+
+#define SBD_TRY(expr)             \
+    do {                          \
+        const int rc_ = (expr);   \
+        if (rc_ != 0) return rc_; \
     } while (0)
 
 #define SBD_LAUNCH_CHECK()                                                        \

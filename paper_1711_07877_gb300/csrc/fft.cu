@@ -347,12 +347,12 @@ int fft_rows(const cx_t<T>* in, long in_stride, int in_len, int in_shift,
         const T* por = post_row ? post_row + r0 : nullptr;
         if (nq > 2048) {
             auto k = fft_rows_kernel<T, 1024>;
-            SBD_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
+            SBD_TRY(raise_smem_limit(k, smem));
             k<<<grid, 1024, smem, stream>>>(ip, in_stride, in_len, in_shift, op, out_stride, out_len, out_shift,
                                             n, Q, sign, plan, tw, perm, pre_elem, prr, post_elem, por);
         } else {
             auto k = fft_rows_kernel<T, 256>;
-            SBD_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
+            SBD_TRY(raise_smem_limit(k, smem));
             k<<<grid, 256, smem, stream>>>(ip, in_stride, in_len, in_shift, op, out_stride, out_len, out_shift,
                                            n, Q, sign, plan, tw, perm, pre_elem, prr, post_elem, por);
         }
@@ -379,12 +379,12 @@ int fft_rows_tables(const cx_t<T>* in, long in_stride, int in_len, cx_t<T>* out,
         cx_t<T>* op = out + static_cast<long>(r0) * out_stride;
         if (n > 2048) {
             auto k = fft_rows_kernel<T, 1024>;
-            SBD_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
+            SBD_TRY(raise_smem_limit(k, smem));
             k<<<grid, 1024, smem, stream>>>(ip, in_stride, in_len, 0, op, out_stride, out_len, 0, n, 1, sign, plan, tw,
                                             perm, nullptr, nullptr, nullptr, nullptr);
         } else {
             auto k = fft_rows_kernel<T, 256>;
-            SBD_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
+            SBD_TRY(raise_smem_limit(k, smem));
             k<<<grid, 256, smem, stream>>>(ip, in_stride, in_len, 0, op, out_stride, out_len, 0, n, 1, sign, plan, tw,
                                            perm, nullptr, nullptr, nullptr, nullptr);
         }

@@ -320,11 +320,11 @@ int launch_gather(const Rec* rec, const long long* tile_start, int n, int P, int
     const unsigned nt = static_cast<unsigned>(ntx) * ntx;
     if (P <= 16) {
         auto k = gather_tiles_kernel<T, 16, Rec, Out>;
-        SBD_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
+        SBD_TRY(raise_smem_limit(k, smem));
         k<<<nt, 256, smem, s>>>(rec, tile_start, ntx, n, P, win, grid, out);
     } else {
         auto k = gather_tiles_kernel<T, 32, Rec, Out>;
-        SBD_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
+        SBD_TRY(raise_smem_limit(k, smem));
         k<<<nt, 256, smem, s>>>(rec, tile_start, ntx, n, P, win, grid, out);
     }
     SBD_LAUNCH_CHECK();
@@ -340,11 +340,11 @@ int launch_scatter(const Rec* rec, const long long* tile_start, int n, int P, in
     const unsigned nt = static_cast<unsigned>(ntx) * ntx;
     if (P <= 16) {
         auto k = scatter_tiles_kernel<T, 16, Rec, Val>;
-        SBD_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
+        SBD_TRY(raise_smem_limit(k, smem));
         k<<<nt, 256, smem, s>>>(rec, tile_start, ntx, n, P, win, val, grid);
     } else {
         auto k = scatter_tiles_kernel<T, 32, Rec, Val>;
-        SBD_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
+        SBD_TRY(raise_smem_limit(k, smem));
         k<<<nt, 256, smem, s>>>(rec, tile_start, ntx, n, P, win, val, grid);
     }
     SBD_LAUNCH_CHECK();
@@ -397,15 +397,15 @@ int node_step_fused(const NodeRec<T>* nodes, const long long* tile_start, const 
     const Window<T> win = make_window<T>(g.kwin, g.beta_k, g.Pk);
     if (P8 == 8) {
         auto k = node_fused_kernel<T, 8>;
-        SBD_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
+        SBD_TRY(raise_smem_limit(k, smem));
         k<<<nt, 256, smem, s>>>(nodes, tile_start, ntx, g.nk, g.Pk, Ws, win, kin, kout);
     } else if (P8 == 16) {
         auto k = node_fused_kernel<T, 16>;
-        SBD_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
+        SBD_TRY(raise_smem_limit(k, smem));
         k<<<nt, 256, smem, s>>>(nodes, tile_start, ntx, g.nk, g.Pk, Ws, win, kin, kout);
     } else {
         auto k = node_fused_kernel<T, 32>;
-        SBD_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
+        SBD_TRY(raise_smem_limit(k, smem));
         k<<<nt, 256, smem, s>>>(nodes, tile_start, ntx, g.nk, g.Pk, Ws, win, kin, kout);
     }
     SBD_LAUNCH_CHECK();

@@ -34,6 +34,12 @@ class sbd_options(ctypes.Structure):
                 ("max_nrhs", ctypes.c_int32), ("flags", ctypes.c_int32)]
 
 
+class sbd_gmres_options(ctypes.Structure):
+    _fields_ = [("shift_re", ctypes.c_double), ("shift_im", ctypes.c_double), ("scale_re", ctypes.c_double),
+                ("scale_im", ctypes.c_double), ("tol", ctypes.c_double), ("restart", ctypes.c_int32),
+                ("max_iter", ctypes.c_int32)]
+
+
 class sbd_plan_stats(ctypes.Structure):
     _fields_ = [("n_points", ctypes.c_int64), ("P", ctypes.c_int64), ("n_circles", ctypes.c_int64),
                 ("n_xi", ctypes.c_int64), ("nnz", ctypes.c_int64), ("n_coincident", ctypes.c_int64),
@@ -73,6 +79,8 @@ _SIGS = {
     "sbd_offline_fit": ([sbd_kernel, _D, _D, _D, _I32, _I64, _P, _P, _P, _P, _P, _P], ctypes.c_int),
     "sbd_fft2": ([_P, _P, _I32, _I32, _I32, _I32, _P], ctypes.c_int),
     "sbd_fft2_noalloc": ([_P, _P, _I32, _I32, _I32, _I32, _P], ctypes.c_int),
+    "sbd_gmres": ([_P, _P, _P, ctypes.POINTER(sbd_gmres_options), ctypes.POINTER(_I32), ctypes.POINTER(_D), _P],
+                  ctypes.c_int),
     "sbd_profile": ([_P, _I32], ctypes.c_int),
     "sbd_profile_read": ([_P, _P, _P], ctypes.c_int),
     "sbd_error_string": ([ctypes.c_int], ctypes.c_char_p),
@@ -188,6 +196,18 @@ def sbd_close_export(plan: int):
     val = np.zeros(nnz, dtype=np.complex128 if cplx else np.float64)
     _check(lib.sbd_close_export(plan, rowptr.ctypes.data, col.ctypes.data, val.ctypes.data), "sbd_close_export")
     return rowptr, col, val
+
+
+def sbd_gmres(plan: int, b, x, shift=1.0, scale=1.0, tol: float = 1e-6, restart: int = 30,
+              max_iter: int = 300, stream=None):
+    """Solve (shift I + scale A) x = b in place of x (x holds the initial guess).
+    Returns (iterations, relative residual)."""
+    shift, scale = complex(shift), complex(scale)
+    opt = sbd_gmres_options(shift.real, shift.imag, scale.real, scale.imag, tol, restart, max_iter)
+    it, res = _I32(), _D()
+    _check(lib.sbd_gmres(plan, _ptr(b), _ptr(x), ctypes.byref(opt), ctypes.byref(it), ctypes.byref(res),
+                         _stream(stream)), "sbd_gmres")
+    return it.value, res.value
 
 
 STAGES = ("sum", "spread", "fft_fwd", "node", "fft_inv", "interp", "spmv")

@@ -1,0 +1,202 @@
+"""Continuous-batching solve server over the C ABI.
+
+Each request is a boundary-integral-like system (shift I + scale A) x = b on its own
+point cloud, A the SBD convolution of that cloud (Introduction: iterative solvers
+whose cost is the discrete convolution).  The server keeps `slots` worker threads,
+each with its own CUDA stream; a request is admitted when a slot is free and its
+estimated device footprint fits the HBM budget, then planned (sbd_plan), solved
+(sbd_gmres) and released (sbd_destroy) on that slot's stream.  Requests that arrive
+while others run are admitted as slots and memory free up, so their device work
+overlaps.  The library calls release the GIL; the arithmetic is all in libsbd.so.
+"""
+from __future__ import annotations
+
+import threading
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import sbd as S
+
+
+@dataclass
+class Request:
+    rid: int
+    z: np.ndarray                 # (N, 2) float64 points
+    b: np.ndarray                 # (N,) float64 or complex128
+    kind: int                     # S.SBD_LAPLACE / S.SBD_HELMHOLTZ
+    kappa: float
+    delta_min: float
+    eps: float
+    shift: complex = 0.5
+    scale: complex = 1.0
+    arrival: float = 0.0          # seconds after the server's start
+    # results
+    x: np.ndarray | None = None
+    iterations: int = 0
+    residual: float = float("nan")
+    start: float = 0.0
+    done: float = 0.0
+    plan_seconds: float = 0.0
+    device_bytes: int = 0
+    error: str | None = None
+
+
+@dataclass
+class ServerStats:
+    latencies: list = field(default_factory=list)
+    points_matvecs: float = 0.0
+    wall: float = 0.0
+
+    def summary(self) -> dict:
+        lat = np.sort(np.asarray(self.latencies))
+        if lat.size == 0:
+            return {"requests": 0}
+        return {"requests": int(lat.size), "p50_ms": float(np.percentile(lat, 50) * 1e3),
+                "p99_ms": float(np.percentile(lat, 99) * 1e3), "mean_ms": float(lat.mean() * 1e3),
+                "wall_s": self.wall, "gpts_per_s": self.points_matvecs / max(self.wall, 1e-9) / 1e9}
+
+
+class Admission:
+    """Device-memory admission for the server (host logic only).
+
+    Requests wait in arrival order; `admit` returns the first waiting request whose
+    estimated footprint fits the free budget (a smaller request may pass a larger one
+    at the head), or the head itself when nothing is running, so that a request larger
+    than the whole budget still runs, alone.  The per-point estimate only grows, from
+    the footprints that finished plans report.
+    """
+
+    def __init__(self, budget: int, bytes_per_point: float = 8000.0, fixed_bytes: int = 64 << 20):
+        self.budget = int(budget)
+        self.bytes_per_point = float(bytes_per_point)
+        self.fixed_bytes = int(fixed_bytes)
+        self.in_use = 0
+        self.running = 0
+        self.pending: list = []
+
+    def estimate(self, n_points: int) -> int:
+        return int(self.bytes_per_point * n_points) + self.fixed_bytes
+
+    def push(self, req) -> None:
+        self.pending.append(req)
+
+    def admit(self):
+        for i, r in enumerate(self.pending):
+            est = self.estimate(len(r.z))
+            if self.in_use + est <= self.budget or self.running == 0:
+                self.pending.pop(i)
+                self.in_use += est
+                self.running += 1
+                return r, est
+        return None
+
+    def release(self, est: int, n_points: int = 0, device_bytes: int = 0) -> None:
+        self.in_use -= est
+        self.running -= 1
+        if n_points and device_bytes:
+            self.bytes_per_point = max(self.bytes_per_point, 1.2 * device_bytes / n_points)
+
+
+class Server:
+    """slots worker threads; admission by a device-memory budget (bytes)."""
+
+    def __init__(self, slots: int = 4, hbm_budget: int | None = None, form: int = S.SBD_FORM_FP32,
+                 tol: float = 1e-6, restart: int = 30, max_iter: int = 300):
+        import torch
+        self.torch = torch
+        self.slots = slots
+        self.form = form
+        self.tol, self.restart, self.max_iter = tol, restart, max_iter
+        if hbm_budget is None:
+            free, _ = torch.cuda.mem_get_info()
+            hbm_budget = int(free * 0.8)
+        self.adm = Admission(hbm_budget)
+        self.cv = threading.Condition()
+        self.stats = ServerStats()
+        self.t0 = time.perf_counter()
+        self.closed = False
+        self.workers = [threading.Thread(target=self._worker, daemon=True) for _ in range(slots)]
+        for w in self.workers:
+            w.start()
+
+    def now(self) -> float:
+        return time.perf_counter() - self.t0
+
+    def submit(self, req: Request) -> None:
+        with self.cv:
+            req.arrival = self.now() if req.arrival == 0.0 else req.arrival
+            self.adm.push(req)
+            self.cv.notify_all()
+
+    def _worker(self):
+        torch = self.torch
+        stream = torch.cuda.Stream()
+        while True:
+            with self.cv:
+                got = None
+                while not self.closed:
+                    got = self.adm.admit()
+                    if got:
+                        break
+                    self.cv.wait(timeout=0.05)
+                if not got:
+                    return
+            req, est = got
+            req.start = self.now()
+            plan = None
+            try:
+                with torch.cuda.stream(stream):
+                    zt = torch.from_numpy(req.z).to("cuda", non_blocking=True)
+                    bt = torch.from_numpy(req.b).to("cuda", non_blocking=True)
+                    xt = torch.zeros_like(bt)
+                opt = S.make_options(form=self.form)
+                plan = S.sbd_plan(zt, len(req.z), req.kind, req.kappa, req.delta_min, req.eps, opt,
+                                  stream.cuda_stream)
+                info = S.sbd_plan_info(plan)
+                req.plan_seconds = info["plan_seconds"]
+                req.device_bytes = info["device_bytes"]
+                it, res = S.sbd_gmres(plan, bt, xt, req.shift, req.scale, self.tol, self.restart, self.max_iter,
+                                      stream.cuda_stream)
+                stream.synchronize()
+                req.x = xt.cpu().numpy()
+                req.iterations, req.residual = it, res
+            except Exception as e:  # the request fails, the server keeps serving
+                req.error = str(e)
+            finally:
+                if plan:
+                    S.sbd_destroy(plan)
+                req.done = self.now()
+                with self.cv:
+                    self.adm.release(est, len(req.z), req.device_bytes)
+                    if req.error is None:
+                        self.stats.latencies.append(req.done - req.arrival)
+                        self.stats.points_matvecs += len(req.z) * (req.iterations + 2)
+                    self.cv.notify_all()
+
+    def drain(self, requests: list[Request]) -> None:
+        """Wait until every request in the list is done, then stop the workers."""
+        while any(r.done == 0.0 for r in requests):
+            time.sleep(0.002)
+        with self.cv:
+            self.closed = True
+            self.cv.notify_all()
+        for w in self.workers:
+            w.join()
+        self.stats.wall = max(r.done for r in requests) - min(r.arrival for r in requests)
+
+
+def run_poisson(requests: list[Request], mean_gap_s: float, seed: int = 0, **server_kw) -> tuple[Server, dict]:
+    """Submit requests with exponential inter-arrival times; return the server and its summary."""
+    rng = np.random.default_rng(seed)
+    srv = Server(**server_kw)
+    t = 0.0
+    for r in requests:
+        t += rng.exponential(mean_gap_s)
+        while srv.now() < t:
+            time.sleep(min(0.001, t - srv.now()))
+        r.arrival = 0.0
+        srv.submit(r)
+    srv.drain(requests)
+    return srv, srv.stats.summary()

@@ -1,0 +1,160 @@
+"""GPU: the GMRES entry point and the continuous-batching server.
+
+Expected solutions come from a dense solve of the same system built with the oracle's
+exact kernel G (no SBD anywhere): (shift I + scale A) x = b, A_kl = G(|z_k - z_l|) for
+k != l (Eq. discrete convolution, self term excluded).  The SBD matvec differs from A x
+by at most eps sum|x| per entry (Sec. 1), so with scale = 1/N and shift = 1 the system
+is well conditioned and the solution moves by O(eps); GMRES stops at `tol`.
+Bar: ||x - x_dense|| / ||x_dense|| <= 20 (tol + eps).
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import sbd_oracle as O
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def S():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1711_07877_gb300 import build
+    build.build_library()
+    import paper_1711_07877_gb300 as pkg
+    return pkg
+
+
+def dense_matrix(z, kind, kappa=0.0):
+    d = np.hypot(z[:, None, 0] - z[None, :, 0], z[:, None, 1] - z[None, :, 1])
+    np.fill_diagonal(d, 1.0)
+    A = O.kernel_G(d, kind, kappa)
+    np.fill_diagonal(A, 0.0)
+    return A
+
+
+def system(kind, n, seed):
+    if kind == "laplace":
+        z = W.disk_points(n, seed)
+        kappa = 0.0
+        b = W.rhs(n, seed + 100)
+    else:
+        z = W.curve_points(n, seed)
+        kappa = 40.0 / W.enclosing_diameter(z)
+        b = W.rhs(n, seed + 100, complex_valued=True)
+    dmin = float(np.sqrt(20.0 / n))
+    return z, kappa, dmin, b
+
+
+def solve_gpu(S, z, kind, kappa, dmin, eps, b, form, tol, shift, scale, restart=30, max_iter=400):
+    zt = torch.from_numpy(z).cuda()
+    opt = S.make_options(form=form)
+    p = S.sbd_plan(zt, len(z), S.SBD_HELMHOLTZ if kind == "helmholtz" else S.SBD_LAPLACE, kappa, dmin, eps, opt)
+    try:
+        bt = torch.from_numpy(np.ascontiguousarray(b)).cuda()
+        xt = torch.zeros_like(bt)
+        it, res = S.sbd_gmres(p, bt, xt, shift, scale, tol, restart, max_iter)
+        torch.cuda.synchronize()
+        return xt.cpu().numpy(), it, res
+    finally:
+        S.sbd_destroy(p)
+
+
+@pytest.mark.parametrize("kind,form,eps,tol", [
+    ("laplace", 0, 1e-10, 1e-9),
+    ("laplace", 1, 1e-6, 1e-5),
+    ("helmholtz", 0, 1e-10, 1e-9),
+    ("helmholtz", 1, 1e-6, 1e-5),
+])
+def test_gmres_matches_dense_solve(S, kind, form, eps, tol):
+    n = 1800
+    z, kappa, dmin, b = system(kind, n, 11)
+    shift, scale = 1.0, 1.0 / n
+    x, it, res = solve_gpu(S, z, kind, kappa, dmin, eps, b, form, tol, shift, scale)
+    assert 0 < it < 400 and res <= tol * 1.0001, (it, res)
+    A = dense_matrix(z, kind, kappa)
+    M = shift * np.eye(n) + scale * A
+    x_ref = np.linalg.solve(M, b)
+    err = np.linalg.norm(x - x_ref) / np.linalg.norm(x_ref)
+    assert err <= 20 * (tol + eps), err
+    # the residual of the GPU solution against the exact operator
+    r = np.linalg.norm(b - M @ x) / np.linalg.norm(b)
+    assert r <= 20 * (tol + eps), r
+
+
+def test_gmres_restart_small_subspace(S):
+    """restart = 3 forces several cycles; the answer must not change."""
+    n = 1200
+    z, kappa, dmin, b = system("laplace", n, 12)
+    x3, it3, _ = solve_gpu(S, z, "laplace", kappa, dmin, 1e-10, b, 0, 1e-9, 1.0, 1.0 / n, restart=3, max_iter=600)
+    x30, it30, _ = solve_gpu(S, z, "laplace", kappa, dmin, 1e-10, b, 0, 1e-9, 1.0, 1.0 / n, restart=30)
+    assert it3 >= it30
+    assert np.linalg.norm(x3 - x30) / np.linalg.norm(x30) < 1e-7
+
+
+def test_gmres_zero_rhs_and_bad_args(S):
+    n = 500
+    z, kappa, dmin, _ = system("laplace", n, 13)
+    zt = torch.from_numpy(z).cuda()
+    p = S.sbd_plan(zt, n, S.SBD_LAPLACE, 0.0, dmin, 1e-6, S.make_options(form=0))
+    try:
+        b = torch.zeros(n, dtype=torch.float64, device="cuda")
+        x = torch.ones(n, dtype=torch.float64, device="cuda")
+        it, res = S.sbd_gmres(p, b, x, 1.0, 1.0, 1e-8)
+        torch.cuda.synchronize()
+        assert it == 0 and res == 0.0 and float(x.abs().max()) == 0.0
+        for kw in ({"tol": 0.0}, {"restart": 0}, {"max_iter": -1}):
+            args = dict(shift=1.0, scale=1.0, tol=1e-6, restart=10, max_iter=10)
+            args.update(kw)
+            with pytest.raises(S.SbdError) as e:
+                S.sbd_gmres(p, b, x, **args)
+            assert e.value.code == S.SBD_EINVAL
+    finally:
+        S.sbd_destroy(p)
+
+
+def test_gmres_max_iter_reports_residual(S):
+    n = 1500
+    z, kappa, dmin, b = system("helmholtz", n, 14)
+    x, it, res = solve_gpu(S, z, "helmholtz", kappa, dmin, 1e-8, b, 0, 1e-14, 1.0, 1.0 / n, restart=5, max_iter=4)
+    assert it == 4 and res > 1e-14
+
+
+def test_server_results_match_solo_solves(S):
+    """Requests served concurrently (3 slots, Poisson arrivals) give the answers they give alone."""
+    from paper_1711_07877_gb300 import serve
+    reqs, solo = [], []
+    specs = [("laplace", 1500), ("helmholtz", 2000), ("laplace", 3000), ("helmholtz", 1200),
+             ("laplace", 2500), ("laplace", 1000)]
+    tol = 1e-8
+    for i, (kind, n) in enumerate(specs):
+        z, kappa, dmin, b = system(kind, n, 20 + i)
+        reqs.append(serve.Request(rid=i, z=z, b=b, kind=S.SBD_HELMHOLTZ if kind == "helmholtz" else S.SBD_LAPLACE,
+                                  kappa=kappa, delta_min=dmin, eps=1e-10, shift=1.0, scale=1.0 / n))
+        solo.append(solve_gpu(S, z, kind, kappa, dmin, 1e-10, b, 0, tol, 1.0, 1.0 / n)[0])
+    srv, summary = serve.run_poisson(reqs, mean_gap_s=0.004, seed=5, slots=3, form=S.SBD_FORM_FP64, tol=tol)
+    assert summary["requests"] == len(specs)
+    assert 0 < summary["p50_ms"] <= summary["p99_ms"]
+    assert summary["gpts_per_s"] > 0
+    for r, xs in zip(reqs, solo):
+        assert r.error is None, r.error
+        assert r.residual <= tol * 1.0001
+        assert np.linalg.norm(r.x - xs) / np.linalg.norm(xs) < 1e-6, r.rid
+
+
+def test_server_budget_serialises(S):
+    """A budget smaller than any request admits one request at a time."""
+    from paper_1711_07877_gb300 import serve
+    reqs = []
+    for i in range(4):
+        z, kappa, dmin, b = system("laplace", 800 + 200 * i, 40 + i)
+        reqs.append(serve.Request(rid=i, z=z, b=b, kind=S.SBD_LAPLACE, kappa=0.0, delta_min=dmin, eps=1e-6,
+                                  shift=1.0, scale=1.0 / len(z)))
+    srv, summary = serve.run_poisson(reqs, mean_gap_s=0.0005, seed=6, slots=4, hbm_budget=1,
+                                     form=S.SBD_FORM_FP32, tol=1e-5)
+    spans = sorted((r.start, r.done) for r in reqs)
+    for (s0, d0), (s1, d1) in zip(spans, spans[1:]):
+        assert s1 >= d0 - 1e-6
+    assert all(r.error is None for r in reqs)

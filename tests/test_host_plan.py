@@ -45,6 +45,9 @@ def test_argument_errors_without_gpu(S):
     with pytest.raises(S.SbdError) as e:
         S.sbd_plan(0, 10, S.SBD_LAPLACE, 0.0, 0.1, 1e-6, None, 0)  # null points
     assert e.value.code == S.SBD_EINVAL
+    with pytest.raises(S.SbdError) as e:
+        S.sbd_gmres(0, 0, 0, stream=0)                              # null plan
+    assert e.value.code == S.SBD_EINVAL
 
 
 @pytest.mark.parametrize("eps", [1e-3, 1e-6, 1e-9])
