@@ -73,6 +73,10 @@ typedef struct {
     double  nufft_tol;   /* > 0: tolerance of each type-3 transform; 0: automatic from eps */
     int32_t max_nrhs;    /* largest nrhs a matvec will use (0 = 1); sizes the workspace */
     int32_t flags;       /* 0, or SBD_FLAG_* bits */
+    double  delta_max;   /* > 0: the outer radius of the fit (must be >= 2 max |z - c|, else
+                            SBD_EINVAL); 0: 2 max |z - c| (R2).  A caller that rounds delta_max
+                            and delta_min / delta_max to fixed grids makes repeated fits hit the
+                            fit cache below. */
 } sbd_options;
 
 /* sbd_options.flags: use a Gaussian window at the quadrature nodes instead of the
@@ -196,6 +200,25 @@ int sbd_offline_fit(sbd_kernel kernel, double delta_min, double delta_max, doubl
  * ------------------------------------------------------------------------------- */
 int sbd_fft2(const void* in, void* out, int32_t n0, int32_t n1, int32_t sign, int32_t form,
              void* cuda_stream);
+
+/* ---------------------------------------------------------------------------------
+ * Fit cache.  The off-line fit (P search and coefficients, Sec. 3-4) depends only on
+ * the kernel kind, k' (Helmholtz, Sec. 4.2), a = delta_min / scale_R, eps and fixed_P;
+ * sbd_plan and sbd_offline_fit keep the last 64 distinct fits process-wide (thread
+ * safe) and reuse one when these agree (a to a relative 1e-12).  The paper fits once
+ * per geometry and has no counterpart; it serves repeated plans of a solve server.
+ *   sbd_fit_cache_stats  host outputs (each may be NULL): lookups that hit, that
+ *                        missed, entries held.  Always SBD_OK.
+ *   sbd_fit_cache_clear  drops every entry and zeroes the counters.  Always SBD_OK.
+ * ------------------------------------------------------------------------------- */
+int sbd_fit_cache_stats(int64_t* hits, int64_t* misses, int64_t* entries);
+int sbd_fit_cache_clear(void);
+
+/* sbd_y0_root - the k-th positive zero of Y0 (k >= 1) into *root (host).  For Helmholtz
+ * the fit's scale k' is the first such zero >= kappa delta_max (Sec. 4.2), so a caller
+ * that wants repeated fits can pick delta_max just below a zero of its choice.
+ * SBD_EINVAL for k < 1 or a null pointer. */
+int sbd_y0_root(int32_t k, double* root);
 
 /* ---------------------------------------------------------------------------------
  * sbd_gmres - restarted GMRES for (shift I + scale A) x = b, A the plan's matvec: the

@@ -7,6 +7,7 @@
 #include <string>
 #include <vector>
 
+#include "bessel.h"
 #include "common.cuh"
 #include "far.cuh"
 #include "fft.cuh"
@@ -405,6 +406,29 @@ int sbd_offline_fit(sbd_kernel kernel, double delta_min, double delta_max, doubl
     return SBD_OK;
 }
 
+int sbd_fit_cache_stats(int64_t* hits, int64_t* misses, int64_t* entries) {
+    long long h, m, e;
+    fit_cache_stats(h, m, e);
+    if (hits) *hits = h;
+    if (misses) *misses = m;
+    if (entries) *entries = e;
+    return SBD_OK;
+}
+
+int sbd_y0_root(int32_t k, double* root) {
+    if (k < 1 || !root) {
+        set_error("sbd_y0_root: need k >= 1 and an output pointer");
+        return SBD_EINVAL;
+    }
+    *root = y0_root(k);
+    return SBD_OK;
+}
+
+int sbd_fit_cache_clear(void) {
+    fit_cache_clear();
+    return SBD_OK;
+}
+
 int sbd_plan(const double* points, int64_t n, sbd_kernel kernel, double delta_min, double eps,
              const sbd_options* opt, void* cuda_stream, sbd_plan_t* out) {
     const auto t0 = std::chrono::steady_clock::now();
@@ -423,7 +447,8 @@ int sbd_plan(const double* points, int64_t n, sbd_kernel kernel, double delta_mi
         set_error("sbd_plan: unknown form");
         return SBD_EINVAL;
     }
-    if ((o.flags & ~SBD_FLAG_GAUSSIAN_NODES) != 0 || o.fixed_P < 0 || o.max_nrhs < 0 || o.nufft_tol < 0) {
+    if ((o.flags & ~SBD_FLAG_GAUSSIAN_NODES) != 0 || o.fixed_P < 0 || o.max_nrhs < 0 || o.nufft_tol < 0 ||
+        !(o.delta_max >= 0)) {
         set_error("sbd_plan: invalid options");
         return SBD_EINVAL;
     }
@@ -462,7 +487,14 @@ int sbd_plan(const double* points, int64_t n, sbd_kernel kernel, double delta_mi
     const double cx = 0.5 * (bb[0] + bb[2]), cy = 0.5 * (bb[1] + bb[3]);
     double md2 = 0.0;
     if ((rc = points_max_dist2(p->z, p->n, cx, cy, &md2, s))) return fail(rc);
-    const double delta_max = 2.0 * std::sqrt(md2);
+    double delta_max = 2.0 * std::sqrt(md2);
+    if (o.delta_max > 0.0) {
+        if (o.delta_max < delta_max) {
+            set_error("sbd_plan: options.delta_max is below 2 max |z - c| = " + std::to_string(delta_max));
+            return fail(SBD_EINVAL);
+        }
+        delta_max = o.delta_max;
+    }
     if (!(delta_min < delta_max)) {
         set_error("sbd_plan: delta_min must be below delta_max = 2 max |z - c|");
         return fail(SBD_EINVAL);

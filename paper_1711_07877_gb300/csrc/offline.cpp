@@ -10,6 +10,10 @@
 // trial P of the search (Sec. 1, dichotomy) reuses the same factor.
 #include "offline.h"
 
+#include <deque>
+#include <map>
+#include <mutex>
+
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -203,6 +207,81 @@ int good_fft_size(int n) {
     }
 }
 
+// Cache of normalised fits.  The P search and the least-squares coefficients depend
+// only on the kernel kind, k' (Helmholtz), a = delta_min / scale_R, eps and fixed_P
+// (Sec. 3-4: the fit is of g on [a, 1]); a is keyed to a relative resolution of
+// 1e-12, far below what moves the fit error at the eps / 3 target.  Process-wide,
+// under a lock, at most kFitCacheEntries entries (oldest evicted first).
+namespace {
+constexpr size_t kFitCacheEntries = 64;
+struct FitNorm {
+    int P;
+    std::vector<double> rho, C, alpha;
+    double e;
+};
+struct FitCache {
+    std::mutex mu;
+    std::map<FitKey, FitNorm> map;
+    std::deque<FitKey> order;
+    long long hits = 0, misses = 0;
+};
+FitCache& fit_cache() {
+    static FitCache c;
+    return c;
+}
+}  // namespace
+
+FitKey fit_key(int kind, double kp, double a, double eps, int fixed_P) {
+    return FitKey{kind, kp, std::llround(std::log(a) * 1e12), eps, fixed_P};
+}
+
+bool fit_cache_get(const FitKey& k, int& P, std::vector<double>& rho, std::vector<double>& C,
+                   std::vector<double>& alpha, double& e) {
+    FitCache& c = fit_cache();
+    std::lock_guard<std::mutex> lock(c.mu);
+    auto it = c.map.find(k);
+    if (it == c.map.end()) {
+        ++c.misses;
+        return false;
+    }
+    ++c.hits;
+    P = it->second.P;
+    rho = it->second.rho;
+    C = it->second.C;
+    alpha = it->second.alpha;
+    e = it->second.e;
+    return true;
+}
+
+void fit_cache_put(const FitKey& k, int P, const std::vector<double>& rho, const std::vector<double>& C,
+                   const std::vector<double>& alpha, double e) {
+    FitCache& c = fit_cache();
+    std::lock_guard<std::mutex> lock(c.mu);
+    if (c.map.count(k)) return;
+    while (c.map.size() >= kFitCacheEntries && !c.order.empty()) {
+        c.map.erase(c.order.front());
+        c.order.pop_front();
+    }
+    c.map.emplace(k, FitNorm{P, rho, C, alpha, e});
+    c.order.push_back(k);
+}
+
+void fit_cache_stats(long long& hits, long long& misses, long long& entries) {
+    FitCache& c = fit_cache();
+    std::lock_guard<std::mutex> lock(c.mu);
+    hits = c.hits;
+    misses = c.misses;
+    entries = static_cast<long long>(c.map.size());
+}
+
+void fit_cache_clear() {
+    FitCache& c = fit_cache();
+    std::lock_guard<std::mutex> lock(c.mu);
+    c.map.clear();
+    c.order.clear();
+    c.hits = c.misses = 0;
+}
+
 int offline_fit(int kind, double kappa, double delta_min, double delta_max, double eps,
                 int fixed_P, SbdFit& out, std::string& err) {
     if (!(delta_max > 0.0) || !(delta_min > 0.0) || !(delta_min < delta_max)) {
@@ -248,15 +327,21 @@ int offline_fit(int kind, double kappa, double delta_min, double delta_max, doub
     f.a = delta_min / f.scale_R;
     w.a = f.a;
     const double tol_g = (eps / 3.0) / std::fabs(f.gscale);
-    fit_samples(f.a, w.extra, w.s);
-    w.gs.resize(w.s.size());
-    for (size_t i = 0; i < w.s.size(); ++i)
-        w.gs[i] = kind == 0 ? std::log(w.s[i]) : bessel_y0(w.kp * w.s[i]);
+    auto prepare_samples = [&]() {
+        fit_samples(f.a, w.extra, w.s);
+        w.gs.resize(w.s.size());
+        for (size_t i = 0; i < w.s.size(); ++i)
+            w.gs[i] = kind == 0 ? std::log(w.s[i]) : bessel_y0(w.kp * w.s[i]);
+    };
 
     std::vector<double> alpha;
     int P;
     double e;
-    if (fixed_P > 0) {
+    const FitKey key = fit_key(kind, w.kp, f.a, eps, fixed_P);
+    if (fit_cache_get(key, P, f.rho, f.C, alpha, e)) {
+        // the search below would give the same normalised fit
+    } else if (fixed_P > 0) {
+        prepare_samples();
         build_fit(w, fixed_P);
         if (w.Pok < fixed_P) {
             err = "Gram matrix not numerically positive definite at this P (conditioning floor, Sec. 3.3)";
@@ -265,6 +350,7 @@ int offline_fit(int kind, double kappa, double delta_min, double delta_max, doub
         P = fixed_P;
         e = fit_error(w, P, alpha);
     } else {
+        prepare_samples();
         const double gamma = std::max(0.5, (-std::log10(tol_g) - 0.5) / 1.5);
         const int P_start = std::max(2, static_cast<int>(std::ceil(gamma / f.a)) +
                                             static_cast<int>(std::ceil(w.extra / (2.0 * kPi))));
@@ -316,9 +402,12 @@ int offline_fit(int kind, double kappa, double delta_min, double delta_max, doub
         P = hi;
         e = fit_error(w, P, alpha);
     }
+    if (static_cast<int>(f.rho.size()) != P) {   // computed here, not taken from the cache
+        f.rho.assign(w.rho.begin(), w.rho.begin() + P);
+        f.C.assign(w.C.begin(), w.C.begin() + P);
+        fit_cache_put(key, P, f.rho, f.C, alpha, e);
+    }
     f.P = P;
-    f.rho.assign(w.rho.begin(), w.rho.begin() + P);
-    f.C.assign(w.C.begin(), w.C.begin() + P);
     f.alpha = alpha;
     f.coef.resize(P);
     for (int p = 0; p < P; ++p) f.coef[p] = f.gscale * alpha[p] * f.C[p];

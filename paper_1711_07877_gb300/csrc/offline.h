@@ -31,6 +31,29 @@ struct SbdFit {
     long long n_xi = 0;                  // sum M
 };
 
+// Key of the normalised-fit cache used by offline_fit (see offline.cpp).
+struct FitKey {
+    int kind;
+    double kp;
+    long long a_q;
+    double eps;
+    int fixed_P;
+    bool operator<(const FitKey& o) const {
+        if (kind != o.kind) return kind < o.kind;
+        if (kp != o.kp) return kp < o.kp;
+        if (a_q != o.a_q) return a_q < o.a_q;
+        if (eps != o.eps) return eps < o.eps;
+        return fixed_P < o.fixed_P;
+    }
+};
+FitKey fit_key(int kind, double kp, double a, double eps, int fixed_P);
+bool fit_cache_get(const FitKey& k, int& P, std::vector<double>& rho, std::vector<double>& C,
+                   std::vector<double>& alpha, double& e);
+void fit_cache_put(const FitKey& k, int P, const std::vector<double>& rho, const std::vector<double>& C,
+                   const std::vector<double>& alpha, double e);
+void fit_cache_stats(long long& hits, long long& misses, long long& entries);
+void fit_cache_clear();
+
 // Fit for the given geometry bound; fixed_P > 0 skips the P search.
 // Returns 0, or a negative SBD_E* code with a message in err.
 int offline_fit(int kind, double kappa, double delta_min, double delta_max, double eps,

@@ -31,7 +31,7 @@ class sbd_kernel(ctypes.Structure):
 
 class sbd_options(ctypes.Structure):
     _fields_ = [("form", ctypes.c_int32), ("fixed_P", ctypes.c_int32), ("nufft_tol", ctypes.c_double),
-                ("max_nrhs", ctypes.c_int32), ("flags", ctypes.c_int32)]
+                ("max_nrhs", ctypes.c_int32), ("flags", ctypes.c_int32), ("delta_max", ctypes.c_double)]
 
 
 class sbd_gmres_options(ctypes.Structure):
@@ -66,6 +66,9 @@ lib = _load()
 _P = ctypes.c_void_p
 _I32, _I64, _D = ctypes.c_int32, ctypes.c_int64, ctypes.c_double
 _SIGS = {
+    "sbd_fit_cache_stats": ([_P, _P, _P], ctypes.c_int),
+    "sbd_fit_cache_clear": ([], ctypes.c_int),
+    "sbd_y0_root": ([_I32, _P], ctypes.c_int),
     "sbd_plan": ([_P, _I64, sbd_kernel, _D, _D, ctypes.POINTER(sbd_options), _P, ctypes.POINTER(_P)], ctypes.c_int),
     "sbd_matvec": ([_P, _P, _P, _I32, _P], ctypes.c_int),
     "sbd_far": ([_P, _P, _P, _I32, _P], ctypes.c_int),
@@ -134,8 +137,8 @@ SBD_FLAG_GAUSSIAN_NODES = 1
 
 
 def make_options(form: int = SBD_FORM_FP64, fixed_P: int = 0, nufft_tol: float = 0.0, max_nrhs: int = 1,
-                 flags: int = 0):
-    return sbd_options(form, fixed_P, nufft_tol, max_nrhs, flags)
+                 flags: int = 0, delta_max: float = 0.0):
+    return sbd_options(form, fixed_P, nufft_tol, max_nrhs, flags, delta_max)
 
 
 def sbd_plan(points, n: int, kernel_kind: int, kappa: float, delta_min: float, eps: float,
@@ -243,6 +246,22 @@ def sbd_offline_fit(kernel_kind: int, kappa: float, delta_min: float, delta_max:
     k = nc.value
     return {"P": P.value, "n_circles": k, "rho": rho[:k].copy(), "alpha": alpha[:k].copy(), "M": M[:k].copy(),
             "fit_err": err.value}
+
+
+def sbd_fit_cache_stats() -> dict:
+    h, m, e = _I64(), _I64(), _I64()
+    _check(lib.sbd_fit_cache_stats(ctypes.byref(h), ctypes.byref(m), ctypes.byref(e)), "sbd_fit_cache_stats")
+    return {"hits": h.value, "misses": m.value, "entries": e.value}
+
+
+def sbd_y0_root(k: int) -> float:
+    r = _D()
+    _check(lib.sbd_y0_root(k, ctypes.byref(r)), "sbd_y0_root")
+    return r.value
+
+
+def sbd_fit_cache_clear() -> None:
+    _check(lib.sbd_fit_cache_clear(), "sbd_fit_cache_clear")
 
 
 def sbd_fft2(x, out, n0: int, n1: int, sign: int, form: int, stream=None) -> None:

@@ -20,6 +20,46 @@ import numpy as np
 from . import sbd as S
 
 
+def enclosing_diameter(z: np.ndarray) -> float:
+    """2 max |z - c| with c the centre of the bounding box: the plan's delta_max (R2)."""
+    lo, hi = z.min(axis=0), z.max(axis=0)
+    c = 0.5 * (lo + hi)
+    return float(2.0 * np.sqrt(np.max(np.sum((z - c) ** 2, axis=1))))
+
+
+def fit_grid_scales(kind: int, kappa: float, delta_min: float, diameter: float, a_steps: int = 8,
+                    root_step: int = 4) -> tuple[float, float]:
+    """(delta_min', delta_max') on fixed grids, so that requests on different geometries
+    reuse the library's cached normalised fit.
+
+    The fit depends on a = delta_min / scale_R and, for Helmholtz, on k' (Sec. 4.1-4.2).
+    a is rounded down to a power of 2^(1/a_steps): a smaller delta_min keeps the eps
+    bound (the fit is made at the new a) and only moves work from the near field to the
+    far field.  For Helmholtz, delta_max is raised until k' is a zero of Y0 whose index
+    is a multiple of root_step (delta_max' sits just below k' / kappa, so the plan's
+    first zero >= kappa delta_max' is that one)."""
+    dmax = diameter * (1.0 + 1e-9)
+    if kind == S.SBD_LAPLACE:
+        scale_R = dmax
+    else:
+        x = kappa * dmax
+        k = max(1, int(x / np.pi) - 2)
+        while S.sbd_y0_root(k) < x:
+            k += 1
+        k = -(-k // root_step) * root_step
+        while True:
+            root = S.sbd_y0_root(k)
+            dmax_q = root * (1.0 - 1e-12) / kappa
+            if dmax_q >= dmax and kappa * dmax_q > S.sbd_y0_root(k - 1):
+                break
+            k += root_step
+        dmax = dmax_q
+        scale_R = root / kappa
+    a = delta_min / scale_R
+    a_q = 2.0 ** (np.floor(np.log2(a) * a_steps) / a_steps)
+    return float(a_q * scale_R), float(dmax)
+
+
 @dataclass
 class Request:
     rid: int
@@ -103,12 +143,13 @@ class Server:
     """slots worker threads; admission by a device-memory budget (bytes)."""
 
     def __init__(self, slots: int = 4, hbm_budget: int | None = None, form: int = S.SBD_FORM_FP32,
-                 tol: float = 1e-6, restart: int = 30, max_iter: int = 300):
+                 tol: float = 1e-6, restart: int = 30, max_iter: int = 300, fit_grid: bool = True):
         import torch
         self.torch = torch
         self.slots = slots
         self.form = form
         self.tol, self.restart, self.max_iter = tol, restart, max_iter
+        self.fit_grid = fit_grid
         if hbm_budget is None:
             free, _ = torch.cuda.mem_get_info()
             hbm_budget = int(free * 0.8)
@@ -151,9 +192,11 @@ class Server:
                     zt = torch.from_numpy(req.z).to("cuda", non_blocking=True)
                     bt = torch.from_numpy(req.b).to("cuda", non_blocking=True)
                     xt = torch.zeros_like(bt)
-                opt = S.make_options(form=self.form)
-                plan = S.sbd_plan(zt, len(req.z), req.kind, req.kappa, req.delta_min, req.eps, opt,
-                                  stream.cuda_stream)
+                dmin, dmax = req.delta_min, 0.0
+                if self.fit_grid:
+                    dmin, dmax = fit_grid_scales(req.kind, req.kappa, req.delta_min, enclosing_diameter(req.z))
+                opt = S.make_options(form=self.form, delta_max=dmax)
+                plan = S.sbd_plan(zt, len(req.z), req.kind, req.kappa, dmin, req.eps, opt, stream.cuda_stream)
                 info = S.sbd_plan_info(plan)
                 req.plan_seconds = info["plan_seconds"]
                 req.device_bytes = info["device_bytes"]

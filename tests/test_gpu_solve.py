@@ -158,3 +158,38 @@ def test_server_budget_serialises(S):
     for (s0, d0), (s1, d1) in zip(spans, spans[1:]):
         assert s1 >= d0 - 1e-6
     assert all(r.error is None for r in reqs)
+
+
+def test_plan_delta_max_option_and_fit_cache(S):
+    """A larger delta_max (options.delta_max) keeps the eps bound; one below 2 max|z - c| is
+    rejected; a second plan with the same normalised fit is a fit-cache hit."""
+    n = 3000
+    z, _, dmin, _ = system("laplace", n, 31)
+    f = W.rhs(n, 131)
+    zt = torch.from_numpy(z).cuda()
+    ft = torch.from_numpy(f).cuda()
+    lo, hi = z.min(0), z.max(0)
+    diam = 2 * np.sqrt(np.max(np.sum((z - 0.5 * (lo + hi)) ** 2, axis=1)))
+    q_ref = O.direct_sum(z, f, "laplace")
+    S.sbd_fit_cache_clear()
+    for dmax in (0.0, 1.5 * diam):
+        p = S.sbd_plan(zt, n, S.SBD_LAPLACE, 0.0, dmin, 1e-8, S.make_options(form=0, delta_max=dmax))
+        q = torch.empty_like(ft)
+        S.sbd_matvec(p, ft, q)
+        torch.cuda.synchronize()
+        info = S.sbd_plan_info(p)
+        S.sbd_destroy(p)
+        if dmax:
+            assert abs(info["delta_max"] - dmax) < 1e-15 * dmax
+        err = np.max(np.abs(q.cpu().numpy() - q_ref)) / np.abs(f).sum()
+        assert err <= 1e-8, (dmax, err)
+    with pytest.raises(S.SbdError) as e:
+        S.sbd_plan(zt, n, S.SBD_LAPLACE, 0.0, dmin, 1e-8, S.make_options(form=0, delta_max=0.99 * diam))
+    assert e.value.code == S.SBD_EINVAL
+    # same a = delta_min / delta_max on a rescaled copy of the points: a cache hit
+    before = S.sbd_fit_cache_stats()
+    z2 = torch.from_numpy(np.ascontiguousarray(2.0 * z)).cuda()
+    p = S.sbd_plan(z2, n, S.SBD_LAPLACE, 0.0, 2.0 * dmin, 1e-8, S.make_options(form=0, delta_max=2.0 * 1.5 * diam))
+    S.sbd_destroy(p)
+    after = S.sbd_fit_cache_stats()
+    assert after["hits"] == before["hits"] + 1

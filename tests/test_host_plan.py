@@ -93,3 +93,27 @@ def test_host_fit_fixed_P_and_floor(S):
         assert r["fit_err"] <= 1e-10 / 3
     except S.SbdError as e:
         assert e.code == S.SBD_EFIT
+
+
+def test_fit_cache_reuses_normalised_fit(S):
+    """The fit of g on [a, 1] depends on a = delta_min / delta_max only (Laplace, Sec. 4.1):
+    a repeated or rescaled fit is a cache hit and equals a fresh computation."""
+    S.sbd_fit_cache_clear()
+    f1 = S.sbd_offline_fit(S.SBD_LAPLACE, 0.0, 0.01, 2.0, 1e-6)
+    assert S.sbd_fit_cache_stats() == {"hits": 0, "misses": 1, "entries": 1}
+    f2 = S.sbd_offline_fit(S.SBD_LAPLACE, 0.0, 0.02, 4.0, 1e-6)      # same a = 0.005
+    st = S.sbd_fit_cache_stats()
+    assert st["hits"] == 1 and st["entries"] == 1
+    assert f2["P"] == f1["P"] and np.array_equal(f2["rho"], f1["rho"]) and np.array_equal(f2["alpha"], f1["alpha"])
+    S.sbd_fit_cache_clear()
+    f3 = S.sbd_offline_fit(S.SBD_LAPLACE, 0.0, 0.02, 4.0, 1e-6)      # fresh
+    assert S.sbd_fit_cache_stats()["misses"] == 1
+    for k in ("rho", "alpha", "M"):
+        assert np.array_equal(f3[k], f2[k]), k
+    assert f3["fit_err"] == f2["fit_err"]
+    S.sbd_offline_fit(S.SBD_LAPLACE, 0.0, 0.02, 4.0, 1e-7)           # another eps: a miss
+    S.sbd_offline_fit(S.SBD_LAPLACE, 0.0, 0.02, 4.0, 1e-6, fixed_P=f3["P"] - 5)   # fixed P: a miss
+    st = S.sbd_fit_cache_stats()
+    assert st["misses"] == 3 and st["entries"] == 3
+    S.sbd_fit_cache_clear()
+    assert S.sbd_fit_cache_stats() == {"hits": 0, "misses": 0, "entries": 0}

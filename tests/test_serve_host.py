@@ -46,3 +46,30 @@ def test_admission_estimate_grows_from_reports():
     a.release(e, n_points=10, device_bytes=5000)
     assert a.bytes_per_point == 600.0
     assert a.estimate(10) == 6000
+
+
+def test_fit_grid_scales_laplace():
+    from paper_1711_07877_gb300 import serve, sbd as S
+    d1, D1 = serve.fit_grid_scales(S.SBD_LAPLACE, 0.0, 0.0123, 7.9)
+    assert D1 >= 7.9 and D1 < 7.9 * (1 + 1e-8)
+    assert d1 <= 0.0123 and d1 > 0.0123 * 2 ** (-1 / 8)
+    a = d1 / D1
+    assert abs(np.log2(a) * 8 - round(np.log2(a) * 8)) < 1e-9
+    d2, D2 = serve.fit_grid_scales(S.SBD_LAPLACE, 0.0, 0.0124, 8.0)
+    assert abs(d2 / D2 - a) < 1e-15 * a * 8
+
+
+def test_fit_grid_scales_helmholtz():
+    from paper_1711_07877_gb300 import serve, sbd as S
+    for kappa, diam, dmin in ((30.0, 7.9, 0.02), (61.3, 3.1, 0.004), (6.0, 8.5, 0.05)):
+        d, D = serve.fit_grid_scales(S.SBD_HELMHOLTZ, kappa, dmin, diam)
+        assert D >= diam and d <= dmin
+        x = kappa * D
+        # the plan's k' (first zero of Y0 >= kappa delta_max) has an index that is a multiple of 4
+        k = 1
+        while S.sbd_y0_root(k) < x:
+            k += 1
+        assert k % 4 == 0, (kappa, k)
+        assert D < diam * 1.0 + 4.5 * np.pi / kappa
+        a = d * kappa / S.sbd_y0_root(k)
+        assert abs(np.log2(a) * 8 - round(np.log2(a) * 8)) < 1e-9

@@ -156,3 +156,25 @@ def laplace_square(n: int = 10_000_000, seed: int = 4, eps: float = 1e-6, nrhs: 
     delta_min = math.sqrt(neighbours / (math.pi * n))
     return Workload(f"laplace_square_n{n}", z, f, "laplace", 0.0, delta_min, eps,
                     {"seed": seed, "nrhs": nrhs})
+
+
+def serve_requests(count: int = 256, seed: int = 5, n_lo: int = 1_000, n_hi: int = 1_000_000, eps: float = 1e-6,
+                   kd_lo: float = 50.0, kd_hi: float = 500.0, operator_scale: float = 300.0) -> list[dict]:
+    """Solve requests for the server: each a random curve geometry (8 star-shaped curves in
+    [0, 10]^2) with N log-uniform in [n_lo, n_hi], Laplace or Helmholtz with equal odds
+    (kappa * delta_max uniform in [kd_lo, kd_hi]), delta_min from Theorem 1, and the system
+    (I + (operator_scale / N) A) x = b with b ~ N(0, 1) (complex for Helmholtz)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        n = int(round(math.exp(rng.uniform(math.log(n_lo), math.log(n_hi)))))
+        helm = bool(rng.random() < 0.5)
+        kd = float(rng.uniform(kd_lo, kd_hi))
+        gseed = 10_000 + seed * 1_000 + i
+        z = curve_points(n, gseed)
+        dmax = enclosing_diameter(z)
+        out.append({"z": z, "b": rhs(n, gseed + 500_000, complex_valued=helm),
+                    "kernel": "helmholtz" if helm else "laplace", "kappa": kd / dmax if helm else 0.0,
+                    "delta_min": theorem1_delta_min(n, eps, dmax), "eps": eps, "shift": 1.0,
+                    "scale": operator_scale / n})
+    return out
