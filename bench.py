@@ -403,7 +403,7 @@ def run_serve(args, rank, world, local):
            "dtype": "f32" if args.form == "fp32" else "f64", "data": "synthetic",
            "config": {"workload": f"serve {len(reqs)} GMRES requests, Poisson arrivals mean 2 ms, curve geometries "
                                   "N log-uniform [1e3, 1e6], 50/50 Laplace/Helmholtz kappa*delta_max U[50, 500], "
-                                  "(I + (300/N) A) x = b to relative residual 1e-6",
+                                  "(I/2 + (L/N) A) x = b (L = arc length) to relative residual 1e-6, GMRES(30)",
                       "slots": args.slots, "eps": args.eps, "form": args.form, "l2_policy": "n/a (serving)"},
            "latency": {"p50_ms": summ.get("p50_ms"), "p99_ms": summ.get("p99_ms"), "mean_ms": summ.get("mean_ms")},
            "served": {"requests_ok": len(ok), "errors": len(reqs) - len(ok), "wall_s": summ.get("wall_s"),

@@ -206,8 +206,8 @@ __global__ void __launch_bounds__(256) scatter_tiles_kernel(
 // next record is loaded while the current one is processed.  Cells that only this
 // tile's stencils reach (local rows and columns in [P-1, 64)) are stored, the overlap
 // band is added atomically into kout, which the caller clears.
-template <typename T, int G>
-__global__ void __launch_bounds__(256) node_fused_kernel(
+template <typename T, int G, int NT>
+__global__ void __launch_bounds__(NT) node_fused_kernel(
     const NodeRec<T>* __restrict__ rec, const long long* __restrict__ tile_start, int ntx, int n, int P, int Ws,
     Window<T> win, const cx_t<T>* __restrict__ kin, cx_t<T>* __restrict__ kout) {
     using C = cx_t<T>;
@@ -293,6 +293,10 @@ __global__ void __launch_bounds__(256) node_fused_kernel(
         }
     }
 }
+
+// Threads of a fused node-step CTA: 16 warps, so that the two CTAs that fit an SM's
+// shared memory (FP32 form) keep 32 warps in flight for the shared-memory latency.
+constexpr int kNodeThreads = 512;
 
 // Shared row stride for the fused node kernel: >= W and congruent to P8 modulo 32.
 inline int fused_stride(int W, int P8) {
@@ -396,17 +400,17 @@ int node_step_fused(const NodeRec<T>* nodes, const long long* tile_start, const 
     const size_t smem = node_fused_smem<T>(g.Pk);
     const Window<T> win = make_window<T>(g.kwin, g.beta_k, g.Pk);
     if (P8 == 8) {
-        auto k = node_fused_kernel<T, 8>;
+        auto k = node_fused_kernel<T, 8, kNodeThreads>;
         SBD_TRY(raise_smem_limit(k, smem));
-        k<<<nt, 256, smem, s>>>(nodes, tile_start, ntx, g.nk, g.Pk, Ws, win, kin, kout);
+        k<<<nt, kNodeThreads, smem, s>>>(nodes, tile_start, ntx, g.nk, g.Pk, Ws, win, kin, kout);
     } else if (P8 == 16) {
-        auto k = node_fused_kernel<T, 16>;
+        auto k = node_fused_kernel<T, 16, kNodeThreads>;
         SBD_TRY(raise_smem_limit(k, smem));
-        k<<<nt, 256, smem, s>>>(nodes, tile_start, ntx, g.nk, g.Pk, Ws, win, kin, kout);
+        k<<<nt, kNodeThreads, smem, s>>>(nodes, tile_start, ntx, g.nk, g.Pk, Ws, win, kin, kout);
     } else {
-        auto k = node_fused_kernel<T, 32>;
+        auto k = node_fused_kernel<T, 32, kNodeThreads>;
         SBD_TRY(raise_smem_limit(k, smem));
-        k<<<nt, 256, smem, s>>>(nodes, tile_start, ntx, g.nk, g.Pk, Ws, win, kin, kout);
+        k<<<nt, kNodeThreads, smem, s>>>(nodes, tile_start, ntx, g.nk, g.Pk, Ws, win, kin, kout);
     }
     SBD_LAUNCH_CHECK();
     return SBD_OK;

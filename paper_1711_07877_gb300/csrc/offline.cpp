@@ -584,6 +584,11 @@ int near_tables(const SbdFit& fit, NearTables& o, std::string& err) {
     };
     o.deg = 18;
     o.pieces = std::max(2, static_cast<int>(std::ceil(phase / 2.0)));
+    // Refinement aims at 1e-14 x scale.  With thousands of terms the direct evaluation
+    // that checks the table has a rounding floor of a few 1e-14; once refining stops
+    // helping, a table within 1e-3 eps (a negligible share of the eps bound on q) is kept.
+    const double accept = std::max(1e-14 * scale, 1e-3 * fit.eps);
+    double prev_worst = 1e300;
     for (int attempt = 0; attempt < 6; ++attempt) {
         const int K = o.pieces, D = o.deg;
         o.T1.assign(static_cast<size_t>(K) * D * 2, 0.0);
@@ -633,6 +638,8 @@ int near_tables(const SbdFit& fit, NearTables& o, std::string& err) {
             }
         }
         if (worst <= 1e-14 * scale) break;
+        if (worst <= accept && (attempt == 5 || worst > 0.5 * prev_worst)) break;   // at the rounding floor
+        prev_worst = worst;
         if (attempt == 5) {
             char buf[128];
             std::snprintf(buf, sizeof buf, "near-field table does not converge (%.3g)", worst);

@@ -37,7 +37,10 @@ def fit_grid_scales(kind: int, kappa: float, delta_min: float, diameter: float, 
     bound (the fit is made at the new a) and only moves work from the near field to the
     far field.  For Helmholtz, delta_max is raised until k' is a zero of Y0 whose index
     is a multiple of root_step (delta_max' sits just below k' / kappa, so the plan's
-    first zero >= kappa delta_max' is that one)."""
+    first zero >= kappa delta_max' is that one), and delta_min is capped at one
+    wavelength 2 pi / kappa: the Y0 fit needs P a >= k' a / pi + gamma(eps), and past
+    P a ~ 6.7 the Gram matrix reaches the FP64 conditioning floor (Sec. 4.1), so a
+    delta_min several wavelengths long (small N at large kappa delta_max) cannot be fitted."""
     dmax = diameter * (1.0 + 1e-9)
     if kind == S.SBD_LAPLACE:
         scale_R = dmax
@@ -55,6 +58,7 @@ def fit_grid_scales(kind: int, kappa: float, delta_min: float, diameter: float, 
             k += root_step
         dmax = dmax_q
         scale_R = root / kappa
+        delta_min = min(delta_min, 2.0 * np.pi / kappa)
     a = delta_min / scale_R
     a_q = 2.0 ** (np.floor(np.log2(a) * a_steps) / a_steps)
     return float(a_q * scale_R), float(dmax)

@@ -63,7 +63,7 @@ def test_fit_grid_scales_helmholtz():
     from paper_1711_07877_gb300 import serve, sbd as S
     for kappa, diam, dmin in ((30.0, 7.9, 0.02), (61.3, 3.1, 0.004), (6.0, 8.5, 0.05)):
         d, D = serve.fit_grid_scales(S.SBD_HELMHOLTZ, kappa, dmin, diam)
-        assert D >= diam and d <= dmin
+        assert D >= diam and d <= min(dmin, 2 * np.pi / kappa)
         x = kappa * D
         # the plan's k' (first zero of Y0 >= kappa delta_max) has an index that is a multiple of 4
         k = 1
@@ -73,3 +73,14 @@ def test_fit_grid_scales_helmholtz():
         assert D < diam * 1.0 + 4.5 * np.pi / kappa
         a = d * kappa / S.sbd_y0_root(k)
         assert abs(np.log2(a) * 8 - round(np.log2(a) * 8)) < 1e-9
+
+
+def test_fit_grid_caps_delta_min_at_a_wavelength():
+    """Small N at large kappa delta_max: Theorem 1 gives delta_min of several wavelengths,
+    which the Y0 fit cannot reach (conditioning floor); the server caps it."""
+    from paper_1711_07877_gb300 import serve, sbd as S
+    kappa, diam = 437.6 / 9.62, 9.62
+    d, D = serve.fit_grid_scales(S.SBD_HELMHOLTZ, kappa, 0.4639, diam)
+    assert d <= 2 * np.pi / kappa
+    fit = S.sbd_offline_fit(S.SBD_HELMHOLTZ, kappa, d, D, 1e-6)
+    assert fit["fit_err"] <= 1e-6 / 3

@@ -54,21 +54,29 @@ def _star_curve(rng: np.random.Generator):
     return centre, radius, dradius
 
 
-def curve_points(n: int, seed: int, n_curves: int = 8, n_table: int = 1 << 16) -> np.ndarray:
-    """N points uniform in arc length on ``n_curves`` random star-shaped curves."""
-    rng = np.random.default_rng(seed)
+def _curve_tables(rng: np.random.Generator, n_curves: int, n_table: int):
     curves = [_star_curve(rng) for _ in range(n_curves)]
     t = np.linspace(0.0, 2.0 * np.pi, n_table + 1)
     tables = []
-    lengths = []
     for centre, radius, dradius in curves:
         r = radius(t)
         dr = dradius(t)
         speed = np.sqrt(r * r + dr * dr)
-        cum = np.concatenate([[0.0], np.cumsum(0.5 * (speed[1:] + speed[:-1]) * np.diff(t))])
-        tables.append(cum)
-        lengths.append(cum[-1])
-    lengths = np.asarray(lengths)
+        tables.append(np.concatenate([[0.0], np.cumsum(0.5 * (speed[1:] + speed[:-1]) * np.diff(t))]))
+    return curves, t, tables
+
+
+def curve_length(seed: int, n_curves: int = 8, n_table: int = 1 << 16) -> float:
+    """Total arc length of the curves that ``curve_points(., seed)`` samples."""
+    _, _, tables = _curve_tables(np.random.default_rng(seed), n_curves, n_table)
+    return float(sum(c[-1] for c in tables))
+
+
+def curve_points(n: int, seed: int, n_curves: int = 8, n_table: int = 1 << 16) -> np.ndarray:
+    """N points uniform in arc length on ``n_curves`` random star-shaped curves."""
+    rng = np.random.default_rng(seed)
+    curves, t, tables = _curve_tables(rng, n_curves, n_table)
+    lengths = np.asarray([c[-1] for c in tables])
     counts = np.floor(n * lengths / lengths.sum()).astype(np.int64)
     counts[: n - counts.sum()] += 1
     pts = []
@@ -159,11 +167,12 @@ def laplace_square(n: int = 10_000_000, seed: int = 4, eps: float = 1e-6, nrhs: 
 
 
 def serve_requests(count: int = 256, seed: int = 5, n_lo: int = 1_000, n_hi: int = 1_000_000, eps: float = 1e-6,
-                   kd_lo: float = 50.0, kd_hi: float = 500.0, operator_scale: float = 300.0) -> list[dict]:
+                   kd_lo: float = 50.0, kd_hi: float = 500.0) -> list[dict]:
     """Solve requests for the server: each a random curve geometry (8 star-shaped curves in
     [0, 10]^2) with N log-uniform in [n_lo, n_hi], Laplace or Helmholtz with equal odds
-    (kappa * delta_max uniform in [kd_lo, kd_hi]), delta_min from Theorem 1, and the system
-    (I + (operator_scale / N) A) x = b with b ~ N(0, 1) (complex for Helmholtz)."""
+    (kappa * delta_max uniform in [kd_lo, kd_hi]), delta_min from Theorem 1, and the
+    second-kind-like system (I / 2 + (L / N) A) x = b, L the total arc length (the
+    quadrature weight of a point), b ~ N(0, 1) (complex for Helmholtz)."""
     rng = np.random.default_rng(seed)
     out = []
     for i in range(count):
@@ -175,6 +184,6 @@ def serve_requests(count: int = 256, seed: int = 5, n_lo: int = 1_000, n_hi: int
         dmax = enclosing_diameter(z)
         out.append({"z": z, "b": rhs(n, gseed + 500_000, complex_valued=helm),
                     "kernel": "helmholtz" if helm else "laplace", "kappa": kd / dmax if helm else 0.0,
-                    "delta_min": theorem1_delta_min(n, eps, dmax), "eps": eps, "shift": 1.0,
-                    "scale": operator_scale / n})
+                    "delta_min": theorem1_delta_min(n, eps, dmax), "eps": eps, "shift": 0.5,
+                    "scale": curve_length(gseed) / n})
     return out
