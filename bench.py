@@ -141,7 +141,8 @@ def measured_peaks():
 
 def stage_bytes(info, n, nrhs, form, esz=8):
     """Algorithmic bytes per launch of each on-line step (see the design notes).
-    esz: bytes of one input/output value (8 real Laplace, 16 complex Helmholtz)."""
+    esz: bytes of one input/output value (8 real Laplace, 16 complex Helmholtz).
+    Laplace stores node records for half the nodes (the antipodes follow by symmetry)."""
     c = 8 if form == "fp32" else 16          # complex grid element
     pr = 16 if form == "fp32" else 24        # point record: int2 cell + fractions
     nr = 24 if form == "fp32" else 32        # node record
@@ -152,7 +153,7 @@ def stage_bytes(info, n, nrhs, form, esz=8):
         "sum": esz * n * nrhs,
         "spread": pr * n + esz * n + c * m * m,
         "fft_fwd": c * (m * m + nk * nk),
-        "node": nr * nxi + 2 * c * nk * nk,
+        "node": nr * (nxi // 2 if esz == 8 else nxi) + 2 * c * nk * nk,
         "fft_inv": c * (nk * nk + m * m),
         "interp": pr * n + esz * n + c * touched,
         "spmv": (4 + vb) * nnz + 8 * (n + 1) + 2 * esz * n * nrhs,

@@ -71,7 +71,10 @@ struct sbd_plan_s {
     int* circle_start = nullptr;
     double* circle_radius = nullptr;
     int* circle_M = nullptr;
-    int* node_perm = nullptr;          // sorted record -> canonical node index
+    int* node_perm = nullptr;          // sorted record -> record numbering
+    int* half_start = nullptr;         // prefix sums of M_p / 2 (half node set), or null
+    bool half_nodes = false;           // Laplace: records for m < M_p / 2 only (Hermitian symmetry)
+    long long n_rec = 0;               // node records: N_xi, or N_xi / 2 with half_nodes
     int* pt_perm = nullptr;            // sorted point record -> original point index
     long long* pt_tile_start = nullptr;
     long long* node_tile_start = nullptr;
@@ -207,6 +210,19 @@ int build_far(sbd_plan_s* p, cudaStream_t s) {
         return SBD_ENOTSUP;
     }
     if ((rc = upload(p, &p->circle_start, start, s))) return rc;
+    // Laplace: f, the spreading grid and omega' are real, so the frequency grid K is
+    // Hermitian (K(-eta) = conj K(eta)) and the node at -xi gives the conjugate of the
+    // one at xi.  Only the nodes m < M_p / 2 of each circle (M_p is even) are stored;
+    // the node step's output S over those nodes completes to S(eta) + conj(S(-eta)),
+    // which the inverse transform folds into its load.
+    p->half_nodes = p->kind == SBD_LAPLACE;
+    p->n_rec = fit.n_xi;
+    if (p->half_nodes) {
+        std::vector<int> hstart(fit.n_circles + 1, 0);
+        for (int c = 0; c < fit.n_circles; ++c) hstart[c + 1] = hstart[c] + fit.M[c] / 2;
+        if ((rc = upload(p, &p->half_start, hstart, s))) return rc;
+        p->n_rec = hstart[fit.n_circles];
+    }
     if ((rc = upload(p, &p->circle_radius, fit.radius, s))) return rc;
     if ((rc = upload(p, &p->circle_M, fit.M, s))) return rc;
     std::vector<cx_t<T>> om(fit.n_circles);
@@ -219,22 +235,22 @@ int build_far(sbd_plan_s* p, cudaStream_t s) {
     if ((rc = upload(p, reinterpret_cast<cx_t<T>**>(&p->omega_c), om, s))) return rc;
     if ((rc = upload(p, reinterpret_cast<T**>(&p->cscale_c), cs, s))) return rc;
     NodeRec<T>* canon = nullptr;
-    SBD_CUDA_TRY(cudaMallocAsync(&canon, sizeof(NodeRec<T>) * std::max<long long>(fit.n_xi, 1), s));
-    rc = far_prepare_nodes<T>(p->circle_start, p->circle_radius, p->circle_M, fit.n_circles, fit.n_xi, np.deta,
-                              np.nk, np.Pk, static_cast<const cx_t<T>*>(p->omega_c), canon, s);
+    SBD_CUDA_TRY(cudaMallocAsync(&canon, sizeof(NodeRec<T>) * std::max<long long>(p->n_rec, 1), s));
+    rc = far_prepare_nodes<T>(p->circle_start, p->half_start, p->circle_radius, p->circle_M, fit.n_circles,
+                              p->n_rec, np.deta, np.nk, np.Pk, static_cast<const cx_t<T>*>(p->omega_c), canon, s);
     if (rc) return rc;
     const int ntx = (np.nk + kNodeTile - 1) / kNodeTile;
-    if ((rc = dev_alloc(p, &p->nodes, sizeof(NodeRec<T>) * fit.n_xi))) return rc;
-    if ((rc = dev_alloc(p, reinterpret_cast<void**>(&p->node_perm), sizeof(int) * fit.n_xi))) return rc;
+    if ((rc = dev_alloc(p, &p->nodes, sizeof(NodeRec<T>) * p->n_rec))) return rc;
+    if ((rc = dev_alloc(p, reinterpret_cast<void**>(&p->node_perm), sizeof(int) * p->n_rec))) return rc;
     if ((rc = dev_alloc(p, reinterpret_cast<void**>(&p->node_tile_start),
                         sizeof(long long) * (static_cast<size_t>(ntx) * ntx + 1)))) return rc;
-    rc = tile_sort<NodeRec<T>>(canon, fit.n_xi, np.nk, static_cast<NodeRec<T>*>(p->nodes), p->node_perm,
+    rc = tile_sort<NodeRec<T>>(canon, p->n_rec, np.nk, static_cast<NodeRec<T>*>(p->nodes), p->node_perm,
                                p->node_tile_start, s);
     if (rc) return rc;
     SBD_CUDA_TRY(cudaFreeAsync(canon, s));
     // the fused node kernel holds the tile plus halo and two accumulator planes in shared memory
     p->node_fused = node_fused_smem<T>(np.Pk) <= 227 * 1024;
-    if (!p->node_fused && (rc = dev_alloc(p, &p->ghat, sizeof(cx_t<T>) * fit.n_xi))) return rc;
+    if (!p->node_fused && (rc = dev_alloc(p, &p->ghat, sizeof(cx_t<T>) * p->n_rec))) return rc;
     std::vector<T> dec(np.m);
     for (int i = 0; i < np.m; ++i) dec[i] = static_cast<T>(np.dec[i]);
     if ((rc = upload(p, reinterpret_cast<T**>(&p->dec), dec, s))) return rc;
@@ -264,12 +280,16 @@ int forward_fft(sbd_plan_s* p, const cx_t<T>* X, cx_t<T>* A, cx_t<T>* Tr, cx_t<T
 
 // frequency grid K2 (nk x nk, rows = kx) -> spreading grid X (m x m), adjoint transform.
 // A (nk x m) and Tr (>= m x nk) are scratch.
+// With fold, K2 holds the node step's S over the half node set and the transform is
+// taken of S(eta) + conj(S(-eta)).
 template <typename T>
-int inverse_fft(sbd_plan_s* p, const cx_t<T>* K2, cx_t<T>* A, cx_t<T>* Tr, cx_t<T>* X, cudaStream_t s) {
+int inverse_fft(sbd_plan_s* p, const cx_t<T>* K2, cx_t<T>* A, cx_t<T>* Tr, cx_t<T>* X, cudaStream_t s,
+                bool fold) {
     const NufftParams& np = p->np;
     const int m = np.m, nk = np.nk, n = np.n;
     const T* dec = static_cast<const T*>(p->dec);
-    int rc = fft_rows<T>(K2, nk, nk, -nk / 2, A, m, m, -m / 2, nk, n, +1, nullptr, nullptr, nullptr, nullptr, s);
+    int rc = fft_rows<T>(K2, nk, nk, -nk / 2, A, m, m, -m / 2, nk, n, +1, nullptr, nullptr, nullptr, nullptr, s,
+                         fold ? nk : 0);
     if (rc) return rc;
     if ((rc = transpose<T>(A, m, 0, Tr, nk, 0, nk, m, 1, s))) return rc;   // [kx][y] -> [y][kx]
     return fft_rows<T>(Tr, nk, nk, -nk / 2, X, m, m, -m / 2, m, n, +1, nullptr, nullptr, dec, dec, s);
@@ -308,7 +328,7 @@ int far_apply(sbd_plan_s* p, const void* f, void* q, int nrhs, cudaStream_t s) {
         }
         t3.end();
         StepTimer t4(p, s, SBD_STAGE_FFT_INV);
-        if ((rc = inverse_fft<T>(p, C, A, B, X, s))) return rc;
+        if ((rc = inverse_fft<T>(p, C, A, B, X, s, p->half_nodes))) return rc;
         t4.end();
         StepTimer t5(p, s, SBD_STAGE_INTERP);
         if ((rc = interp_tiled<T>(static_cast<const PointRec<T>*>(p->pts), p->pt_perm, p->pt_tile_start, p->geom, X,
@@ -329,8 +349,8 @@ int nufft_minus_impl(sbd_plan_s* p, const void* f, void* fhat, cudaStream_t s) {
     if (rc) return rc;
     if ((rc = forward_fft<T>(p, X, A, C, B, s))) return rc;
     const NodeFrame fr{p->circle_start, p->circle_radius, p->circle_M, p->fit.n_circles, p->np.cx, p->np.cy,
-                       p->node_perm};
-    return far_node_gather<T>(static_cast<const NodeRec<T>*>(p->nodes), p->fit.n_xi,
+                       p->node_perm, p->half_start, p->np.nk};
+    return far_node_gather<T>(static_cast<const NodeRec<T>*>(p->nodes), p->n_rec,
                               static_cast<const T*>(p->cscale_c), p->geom, B, static_cast<double2*>(fhat), fr, s);
 }
 
@@ -341,12 +361,12 @@ int nufft_plus_impl(sbd_plan_s* p, const void* ghat, void* q, cudaStream_t s) {
     auto* B = static_cast<cx_t<T>*>(p->wsB);
     auto* C = static_cast<cx_t<T>*>(p->wsC);
     const NodeFrame fr{p->circle_start, p->circle_radius, p->circle_M, p->fit.n_circles, p->np.cx, p->np.cy,
-                       p->node_perm};
-    int rc = far_node_scatter<T>(static_cast<const NodeRec<T>*>(p->nodes), p->fit.n_xi,
+                       p->node_perm, p->half_start, p->np.nk};
+    int rc = far_node_scatter<T>(static_cast<const NodeRec<T>*>(p->nodes), p->n_rec,
                                  static_cast<const T*>(p->cscale_c), p->geom, static_cast<const double2*>(ghat), C,
                                  fr, s);
     if (rc) return rc;
-    if ((rc = inverse_fft<T>(p, C, A, B, X, s))) return rc;
+    if ((rc = inverse_fft<T>(p, C, A, B, X, s, false))) return rc;
     SBD_CUDA_TRY(cudaMemsetAsync(p->zero2, 0, sizeof(double2), s));
     return interp_tiled<T>(static_cast<const PointRec<T>*>(p->pts), p->pt_perm, p->pt_tile_start, p->geom, X,
                            make_double2(0, 0), p->zero2, q, true, s);

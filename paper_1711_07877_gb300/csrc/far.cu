@@ -37,34 +37,42 @@ __global__ void prepare_points_kernel(const double* __restrict__ z, long n, doub
     out[i] = r;
 }
 
-// xi of node nu (FP64): circle by binary search in the prefix offsets, then Eq. (defXimp).
-__device__ __forceinline__ double2 node_xi(const int* __restrict__ start, const double* __restrict__ radius,
-                                           const int* __restrict__ M, int n_circles, long nu, int* circle) {
+// Circle of record nu: the c with num[c] <= nu < num[c + 1] (binary search).
+__device__ __forceinline__ int find_circle(const int* __restrict__ num, int n_circles, long nu) {
     int lo = 0, hi = n_circles;
     while (hi - lo > 1) {
         const int mid = (lo + hi) / 2;
-        if (start[mid] <= nu) lo = mid; else hi = mid;
+        if (num[mid] <= nu) lo = mid; else hi = mid;
     }
+    return lo;
+}
+
+// Record index -> circle, canonical node index and xi (FP64, Eq. (defXimp)).
+struct NodeId { int circle; long canon; long antipode; double2 xi; };
+__device__ __forceinline__ NodeId node_id(const NodeFrame& fr, long rec) {
+    NodeId id;
+    const int* num = fr.hstart ? fr.hstart : fr.start;
+    const int c = find_circle(num, fr.n_circles, rec);
+    const long mm = rec - num[c];
     double sn, cs;
-    sincospi(2.0 * static_cast<double>(nu - start[lo]) / M[lo], &sn, &cs);
-    *circle = lo;
-    return make_double2(radius[lo] * cs, radius[lo] * sn);
+    sincospi(2.0 * static_cast<double>(mm) / fr.M[c], &sn, &cs);
+    id.circle = c;
+    id.canon = fr.start[c] + mm;
+    id.antipode = fr.start[c] + mm + fr.M[c] / 2;
+    id.xi = make_double2(fr.radius[c] * cs, fr.radius[c] * sn);
+    return id;
 }
 
 template <typename T>
-__global__ void prepare_nodes_kernel(const int* __restrict__ start, const double* __restrict__ radius,
-                                     const int* __restrict__ M, int n_circles, long n_xi, double deta,
-                                     int nk, int P, const cx_t<T>* __restrict__ omega_c,
+__global__ void prepare_nodes_kernel(const int* __restrict__ start, const int* __restrict__ hstart,
+                                     const double* __restrict__ radius, const int* __restrict__ M, int n_circles,
+                                     long n_rec, double deta, int nk, int P, const cx_t<T>* __restrict__ omega_c,
                                      NodeRec<T>* __restrict__ out) {
     const long nu = blockIdx.x * static_cast<long>(blockDim.x) + threadIdx.x;
-    if (nu >= n_xi) return;
-    int lo = 0, hi = n_circles;   // start[lo] <= nu < start[hi]
-    while (hi - lo > 1) {
-        const int mid = (lo + hi) / 2;
-        if (start[mid] <= nu) lo = mid; else hi = mid;
-    }
-    const int c = lo;
-    const long mm = nu - start[c];
+    if (nu >= n_rec) return;
+    const int* num = hstart ? hstart : start;
+    const int c = find_circle(num, n_circles, nu);
+    const long mm = nu - num[c];
     double sn, cs;
     sincospi(2.0 * static_cast<double>(mm) / M[c], &sn, &cs);   // xi_m = r (cos 2pi m/M, sin 2pi m/M)
     const double kx = radius[c] * cs / deta + 0.5 * nk;
@@ -77,58 +85,86 @@ __global__ void prepare_nodes_kernel(const int* __restrict__ start, const double
     out[nu] = r;
 }
 
-template <typename T, int PMAX>
-__global__ void node_gather_kernel(const NodeRec<T>* __restrict__ nodes, long n_xi, const T* __restrict__ cs,
-                                   FarGeom g, const cx_t<T>* __restrict__ kin, double2* __restrict__ out,
-                                   NodeFrame fr) {
-    // records may be in tile order: fr.perm maps a record to its canonical node index
-    const long nu = blockIdx.x * static_cast<long>(blockDim.x) + threadIdx.x;
-    if (nu >= n_xi) return;
-    const NodeRec<T> q = nodes[nu];
-    T wx[PMAX], wy[PMAX];
-    weights<T, PMAX>(q.frac.x, g.Pk, g, wx);
-    weights<T, PMAX>(q.frac.y, g.Pk, g, wy);
+// Stencil at the record (mirror = false) or at its antipode: the window is even, so the
+// antipode's stencil is the point reflection i -> nk - i of the record's, same weights.
+template <typename T>
+__device__ __forceinline__ cx_t<T> stencil_gather(const cx_t<T>* __restrict__ kin, int nk, int2 c0, const T* wx,
+                                                  const T* wy, int P, bool mirror) {
     cx_t<T> acc = mk<T>(0, 0);
-    for (int a = 0; a < g.Pk; ++a) {
-        const cx_t<T>* row = kin + static_cast<long>(q.cell.x + a) * g.nk + q.cell.y;
+    for (int a = 0; a < P; ++a) {
+        const long r = mirror ? nk - (c0.x + a) : c0.x + a;
         cx_t<T> s = mk<T>(0, 0);
-        for (int b = 0; b < g.Pk; ++b) s = cadd(s, cscale(row[b], wy[b]));
+        for (int b = 0; b < P; ++b) {
+            const long col = mirror ? nk - (c0.y + b) : c0.y + b;
+            s = cadd(s, cscale(kin[r * nk + col], wy[b]));
+        }
         acc = cadd(acc, cscale(s, wx[a]));
     }
-    // the grids hold z - c: multiply by exp(-i c.xi) to return sum_l exp(-i z_l.xi) f_l
-    const long canon = fr.perm ? fr.perm[nu] : nu;
-    int circle;
-    const double2 xi = node_xi(fr.start, fr.radius, fr.M, fr.n_circles, canon, &circle);
-    acc = cscale(acc, cs[circle]);
+    return acc;
+}
+
+template <typename T>
+__device__ __forceinline__ void stencil_scatter(cx_t<T>* __restrict__ kout, int nk, int2 c0, const T* wx,
+                                                const T* wy, int P, bool mirror, cx_t<T> v) {
+    for (int a = 0; a < P; ++a) {
+        const long r = mirror ? nk - (c0.x + a) : c0.x + a;
+        const cx_t<T> va = cscale(v, wx[a]);
+        for (int b = 0; b < P; ++b) {
+            const long col = mirror ? nk - (c0.y + b) : c0.y + b;
+            atomic_add_cx<T>(kout + r * nk + col, cscale(va, wy[b]));
+        }
+    }
+}
+
+// exp(-i c.xi) acc (sign -1) or exp(+i c.xi) v (sign +1), FP64
+__device__ __forceinline__ double2 centre_phase(const NodeFrame& fr, double2 xi, double2 v, int sign) {
     double sn, co;
     sincos(fr.cx * xi.x + fr.cy * xi.y, &sn, &co);
-    const double ar = acc.x, ai = acc.y;
-    out[canon] = make_double2(ar * co + ai * sn, ai * co - ar * sn);
+    sn *= sign;
+    return make_double2(v.x * co - v.y * sn, v.x * sn + v.y * co);
 }
 
 template <typename T, int PMAX>
-__global__ void node_scatter_kernel(const NodeRec<T>* __restrict__ nodes, long n_xi, const T* __restrict__ cs,
-                                    FarGeom g, const double2* __restrict__ in, cx_t<T>* __restrict__ kout,
-                                    NodeFrame fr) {
+__global__ void node_gather_kernel(const NodeRec<T>* __restrict__ nodes, long n_rec, const T* __restrict__ cs,
+                                   FarGeom g, const cx_t<T>* __restrict__ kin, double2* __restrict__ out,
+                                   NodeFrame fr) {
     const long nu = blockIdx.x * static_cast<long>(blockDim.x) + threadIdx.x;
-    if (nu >= n_xi) return;
+    if (nu >= n_rec) return;
     const NodeRec<T> q = nodes[nu];
     T wx[PMAX], wy[PMAX];
     weights<T, PMAX>(q.frac.x, g.Pk, g, wx);
     weights<T, PMAX>(q.frac.y, g.Pk, g, wy);
-    const long canon = fr.perm ? fr.perm[nu] : nu;
-    double2 v = in[canon];
+    const NodeId id = node_id(fr, fr.perm ? fr.perm[nu] : nu);
+    // the grids hold z - c: multiply by exp(-i c.xi) to return sum_l exp(-i z_l.xi) f_l
+    const T sc = cs[id.circle];
+    cx_t<T> acc = cscale(stencil_gather<T>(kin, g.nk, q.cell, wx, wy, g.Pk, false), sc);
+    out[id.canon] = centre_phase(fr, id.xi, make_double2(acc.x, acc.y), -1);
+    if (fr.hstart) {
+        acc = cscale(stencil_gather<T>(kin, g.nk, q.cell, wx, wy, g.Pk, true), sc);
+        out[id.antipode] = centre_phase(fr, make_double2(-id.xi.x, -id.xi.y), make_double2(acc.x, acc.y), -1);
+    }
+}
+
+template <typename T, int PMAX>
+__global__ void node_scatter_kernel(const NodeRec<T>* __restrict__ nodes, long n_rec, const T* __restrict__ cs,
+                                    FarGeom g, const double2* __restrict__ in, cx_t<T>* __restrict__ kout,
+                                    NodeFrame fr) {
+    const long nu = blockIdx.x * static_cast<long>(blockDim.x) + threadIdx.x;
+    if (nu >= n_rec) return;
+    const NodeRec<T> q = nodes[nu];
+    T wx[PMAX], wy[PMAX];
+    weights<T, PMAX>(q.frac.x, g.Pk, g, wx);
+    weights<T, PMAX>(q.frac.y, g.Pk, g, wy);
+    const NodeId id = node_id(fr, fr.perm ? fr.perm[nu] : nu);
+    const T sc = cs[id.circle];
     // q_l = sum_nu exp(i (z_l - c).xi) [exp(i c.xi) ghat_nu]
-    int circle;
-    const double2 xi = node_xi(fr.start, fr.radius, fr.M, fr.n_circles, canon, &circle);
-    double sn, co;
-    sincos(fr.cx * xi.x + fr.cy * xi.y, &sn, &co);
-    v = make_double2(v.x * co - v.y * sn, v.x * sn + v.y * co);
-    const cx_t<T> acc = cscale(mk<T>(static_cast<T>(v.x), static_cast<T>(v.y)), cs[circle]);
-    for (int a = 0; a < g.Pk; ++a) {
-        const cx_t<T> va = cscale(acc, wx[a]);
-        cx_t<T>* row = kout + static_cast<long>(q.cell.x + a) * g.nk + q.cell.y;
-        for (int b = 0; b < g.Pk; ++b) atomic_add_cx<T>(row + b, cscale(va, wy[b]));
+    double2 v = centre_phase(fr, id.xi, in[id.canon], +1);
+    stencil_scatter<T>(kout, g.nk, q.cell, wx, wy, g.Pk, false,
+                       cscale(mk<T>(static_cast<T>(v.x), static_cast<T>(v.y)), sc));
+    if (fr.hstart) {
+        v = centre_phase(fr, make_double2(-id.xi.x, -id.xi.y), in[id.antipode], +1);
+        stencil_scatter<T>(kout, g.nk, q.cell, wx, wy, g.Pk, true,
+                           cscale(mk<T>(static_cast<T>(v.x), static_cast<T>(v.y)), sc));
     }
 }
 
@@ -170,12 +206,12 @@ int far_prepare_points(const double* z, long n, double cx, double cy, double h, 
 }
 
 template <typename T>
-int far_prepare_nodes(const int* circle_start, const double* radius, const int* M, int n_circles,
-                      long n_xi, double deta, int nk, int P, const cx_t<T>* omega_c, NodeRec<T>* out,
-                      cudaStream_t s) {
-    if (n_xi <= 0) return SBD_OK;
-    prepare_nodes_kernel<T><<<blocks_for(n_xi), kThreads, 0, s>>>(circle_start, radius, M, n_circles, n_xi,
-                                                                   deta, nk, P, omega_c, out);
+int far_prepare_nodes(const int* circle_start, const int* half_start, const double* radius, const int* M,
+                      int n_circles, long n_rec, double deta, int nk, int P, const cx_t<T>* omega_c,
+                      NodeRec<T>* out, cudaStream_t s) {
+    if (n_rec <= 0) return SBD_OK;
+    prepare_nodes_kernel<T><<<blocks_for(n_rec), kThreads, 0, s>>>(circle_start, half_start, radius, M, n_circles,
+                                                                   n_rec, deta, nk, P, omega_c, out);
     SBD_LAUNCH_CHECK();
     return SBD_OK;
 }
@@ -183,20 +219,22 @@ int far_prepare_nodes(const int* circle_start, const double* radius, const int* 
 template <typename T> constexpr int pmax() { return sizeof(T) == 8 ? 32 : 16; }
 
 template <typename T>
-int far_node_gather(const NodeRec<T>* nodes, long n_xi, const T* cscale_c, const FarGeom& g,
+int far_node_gather(const NodeRec<T>* nodes, long n_rec, const T* cscale_c, const FarGeom& g,
                     const cx_t<T>* kin, double2* out, const NodeFrame& fr, cudaStream_t s) {
-    if (n_xi <= 0) return SBD_OK;
-    node_gather_kernel<T, pmax<T>()><<<blocks_for(n_xi), kThreads, 0, s>>>(nodes, n_xi, cscale_c, g, kin, out, fr);
+    if (n_rec <= 0) return SBD_OK;
+    node_gather_kernel<T, pmax<T>()><<<blocks_for(n_rec), kThreads, 0, s>>>(nodes, n_rec, cscale_c, g, kin, out,
+                                                                            fr);
     SBD_LAUNCH_CHECK();
     return SBD_OK;
 }
 
 template <typename T>
-int far_node_scatter(const NodeRec<T>* nodes, long n_xi, const T* cscale_c, const FarGeom& g,
+int far_node_scatter(const NodeRec<T>* nodes, long n_rec, const T* cscale_c, const FarGeom& g,
                      const double2* in, cx_t<T>* kout, const NodeFrame& fr, cudaStream_t s) {
     SBD_CUDA_TRY(cudaMemsetAsync(kout, 0, sizeof(cx_t<T>) * static_cast<size_t>(g.nk) * g.nk, s));
-    if (n_xi <= 0) return SBD_OK;
-    node_scatter_kernel<T, pmax<T>()><<<blocks_for(n_xi), kThreads, 0, s>>>(nodes, n_xi, cscale_c, g, in, kout, fr);
+    if (n_rec <= 0) return SBD_OK;
+    node_scatter_kernel<T, pmax<T>()><<<blocks_for(n_rec), kThreads, 0, s>>>(nodes, n_rec, cscale_c, g, in, kout,
+                                                                             fr);
     SBD_LAUNCH_CHECK();
     return SBD_OK;
 }
@@ -213,8 +251,8 @@ int far_sum(const void* f, bool f_complex, long n, int nrhs, double2* sumf, cuda
 #define SBD_FAR_INST(T)                                                                                   \
     template int far_prepare_points<T>(const double*, long, double, double, double, int, int, PointRec<T>*,  \
                                        cudaStream_t);                                                     \
-    template int far_prepare_nodes<T>(const int*, const double*, const int*, int, long, double, int, int, \
-                                      const cx_t<T>*, NodeRec<T>*, cudaStream_t);                         \
+    template int far_prepare_nodes<T>(const int*, const int*, const double*, const int*, int, long, double, \
+                                      int, int, const cx_t<T>*, NodeRec<T>*, cudaStream_t);               \
     template int far_node_gather<T>(const NodeRec<T>*, long, const T*, const FarGeom&, const cx_t<T>*,    \
                                     double2*, const NodeFrame&, cudaStream_t);                            \
     template int far_node_scatter<T>(const NodeRec<T>*, long, const T*, const FarGeom&, const double2*,   \

@@ -30,10 +30,15 @@ template <typename T> struct NodeRec { int2 cell; cx_t<T> frac; cx_t<T> omega; }
 template <typename T>
 int far_prepare_points(const double* z, long n, double cx, double cy, double h, int m, int P,
                        PointRec<T>* out, cudaStream_t s);
+// Records of the quadrature nodes.  half_start null: every node, n_rec = N_xi, record
+// numbering = canonical numbering (circle by circle, angle index m).  half_start
+// non-null (prefix sums of M_p / 2; every M_p is even): only the nodes m < M_p / 2 of
+// each circle, whose antipodes -xi the Hermitian-symmetric node step of a real-valued
+// transform supplies by symmetry.
 template <typename T>
-int far_prepare_nodes(const int* circle_start, const double* radius, const int* M, int n_circles,
-                      long n_xi, double deta, int nk, int P, const cx_t<T>* omega_c, NodeRec<T>* out,
-                      cudaStream_t s);
+int far_prepare_nodes(const int* circle_start, const int* half_start, const double* radius, const int* M,
+                      int n_circles, long n_rec, double deta, int nk, int P, const cx_t<T>* omega_c,
+                      NodeRec<T>* out, cudaStream_t s);
 
 // Circle tables and the centre c of the point set, to place the canonical nodes in
 // absolute coordinates (the grids hold z - c).
@@ -43,15 +48,19 @@ struct NodeFrame {
     const int* M;
     int n_circles;
     double cx, cy;
-    const int* perm;   // record -> canonical node index (null: records in canonical order)
+    const int* perm;   // sorted record -> record numbering (null: records in that order)
+    const int* hstart; // non-null: records are the half set (see far_prepare_nodes); the
+                       // gather / scatter also serve each record's antipode
+    int nk;            // frequency-grid side (mirror of cell i is nk - i)
 };
-// Gather only: out[nu] = exp(-i c.xi_nu) c_nu sum_stencil w K  (complex128), c_nu = circle scale.
+// Gather only: out[nu] = exp(-i c.xi_nu) c_nu sum_stencil w K  (complex128), c_nu = circle scale,
+// for every node nu (canonical numbering; n_rec records).
 template <typename T>
-int far_node_gather(const NodeRec<T>* nodes, long n_xi, const T* cscale, const FarGeom& g,
+int far_node_gather(const NodeRec<T>* nodes, long n_rec, const T* cscale, const FarGeom& g,
                     const cx_t<T>* kin, double2* out, const NodeFrame& fr, cudaStream_t s);
 // Scatter only: kout (zeroed here) += c_nu exp(i c.xi_nu) in[nu] w.
 template <typename T>
-int far_node_scatter(const NodeRec<T>* nodes, long n_xi, const T* cscale, const FarGeom& g,
+int far_node_scatter(const NodeRec<T>* nodes, long n_rec, const T* cscale, const FarGeom& g,
                      const double2* in, cx_t<T>* kout, const NodeFrame& fr, cudaStream_t s);
 // sumf[r] = sum_l f[r][l] (FP64).
 int far_sum(const void* f, bool f_complex, long n, int nrhs, double2* sumf, cudaStream_t s);

@@ -162,13 +162,17 @@ __device__ __forceinline__ void dit_stage(cx_t<T>* s, int n, int Lp, int sign, c
 // One row (blockIdx.x) and one phase (blockIdx.y) of a length-n transform done as Q
 // transforms of length nq = n / Q (Q = 1 or 2): output k = Q k' + r is the length-nq DFT
 // of y_r[t] = sum_{j < Q} x[t + j nq] w_n^{r (t + j nq)} (fold and twist on the load).
+// Hermitian fold of the load (see fft_rows): base of the whole grid, its side (0 = off)
+// and the absolute index of this launch's first row.
+template <typename T> struct HermFold { const cx_t<T>* base; int n; long row0; };
+
 template <typename T, int NT>
 __global__ void __launch_bounds__(NT) fft_rows_kernel(
     const cx_t<T>* __restrict__ in, long in_stride, int in_len, int in_shift,
     cx_t<T>* __restrict__ out, long out_stride, int out_len, int out_shift,
     int n, int Q, int sign, FftPlan1D plan, const cx_t<T>* __restrict__ tw, const int* __restrict__ perm,
     const T* __restrict__ pre_elem, const T* __restrict__ pre_row,
-    const T* __restrict__ post_elem, const T* __restrict__ post_row) {
+    const T* __restrict__ post_elem, const T* __restrict__ post_row, HermFold<T> hf) {
     using C = cx_t<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* s = reinterpret_cast<C*>(smem_raw);
@@ -185,6 +189,14 @@ __global__ void __launch_bounds__(NT) fft_rows_kernel(
             if (t < 0) t += n;
             if (t < in_len) {
                 C v = src[t];
+                if (hf.n) {
+                    const long ar = hf.row0 + row;
+                    if (ar >= 1 && t >= 1) {
+                        const C mv = hf.base[(hf.n - ar) * in_stride + (hf.n - t)];
+                        v.x += mv.x;
+                        v.y -= mv.y;
+                    }
+                }
                 T sc = rs;
                 if (pre_elem) sc *= pre_elem[t];
                 v = cscale(v, sc);
@@ -319,8 +331,12 @@ int fft_rows(const cx_t<T>* in, long in_stride, int in_len, int in_shift,
              cx_t<T>* out, long out_stride, int out_len, int out_shift,
              int rows, int n, int sign,
              const T* pre_elem, const T* pre_row, const T* post_elem, const T* post_row,
-             cudaStream_t stream) {
+             cudaStream_t stream, int herm_n) {
     if (rows <= 0) return SBD_OK;
+    if (herm_n && (rows != herm_n || in_len != herm_n)) {
+        set_error("fft_rows: a Hermitian fold needs a square grid read whole");
+        return SBD_EINVAL;
+    }
     const bool fp64 = sizeof(T) == 8;
     const int Q = fft_phases(n, fp64);
     const int nq = n / Q;
@@ -345,16 +361,17 @@ int fft_rows(const cx_t<T>* in, long in_stride, int in_len, int in_shift,
         cx_t<T>* op = out + static_cast<long>(r0) * out_stride;
         const T* prr = pre_row ? pre_row + r0 : nullptr;
         const T* por = post_row ? post_row + r0 : nullptr;
+        const HermFold<T> hf{in, herm_n, r0};
         if (nq > 2048) {
             auto k = fft_rows_kernel<T, 1024>;
             SBD_TRY(raise_smem_limit(k, smem));
             k<<<grid, 1024, smem, stream>>>(ip, in_stride, in_len, in_shift, op, out_stride, out_len, out_shift,
-                                            n, Q, sign, plan, tw, perm, pre_elem, prr, post_elem, por);
+                                            n, Q, sign, plan, tw, perm, pre_elem, prr, post_elem, por, hf);
         } else {
             auto k = fft_rows_kernel<T, 256>;
             SBD_TRY(raise_smem_limit(k, smem));
             k<<<grid, 256, smem, stream>>>(ip, in_stride, in_len, in_shift, op, out_stride, out_len, out_shift,
-                                           n, Q, sign, plan, tw, perm, pre_elem, prr, post_elem, por);
+                                           n, Q, sign, plan, tw, perm, pre_elem, prr, post_elem, por, hf);
         }
         SBD_LAUNCH_CHECK();
     }
@@ -381,12 +398,12 @@ int fft_rows_tables(const cx_t<T>* in, long in_stride, int in_len, cx_t<T>* out,
             auto k = fft_rows_kernel<T, 1024>;
             SBD_TRY(raise_smem_limit(k, smem));
             k<<<grid, 1024, smem, stream>>>(ip, in_stride, in_len, 0, op, out_stride, out_len, 0, n, 1, sign, plan, tw,
-                                            perm, nullptr, nullptr, nullptr, nullptr);
+                                            perm, nullptr, nullptr, nullptr, nullptr, HermFold<T>{nullptr, 0, 0});
         } else {
             auto k = fft_rows_kernel<T, 256>;
             SBD_TRY(raise_smem_limit(k, smem));
             k<<<grid, 256, smem, stream>>>(ip, in_stride, in_len, 0, op, out_stride, out_len, 0, n, 1, sign, plan, tw,
-                                           perm, nullptr, nullptr, nullptr, nullptr);
+                                           perm, nullptr, nullptr, nullptr, nullptr, HermFold<T>{nullptr, 0, 0});
         }
         SBD_LAUNCH_CHECK();
     }
@@ -404,9 +421,9 @@ int transpose(const cx_t<T>* in, long in_stride, long in_batch, cx_t<T>* out, lo
 }
 
 template int fft_rows<float>(const float2*, long, int, int, float2*, long, int, int, int, int, int,
-                             const float*, const float*, const float*, const float*, cudaStream_t);
+                             const float*, const float*, const float*, const float*, cudaStream_t, int);
 template int fft_rows<double>(const double2*, long, int, int, double2*, long, int, int, int, int, int,
-                              const double*, const double*, const double*, const double*, cudaStream_t);
+                              const double*, const double*, const double*, const double*, cudaStream_t, int);
 template int fft_rows_tables<float>(const float2*, long, int, float2*, long, int, int, int, int, const float2*,
                                     const int*, cudaStream_t);
 template int fft_rows_tables<double>(const double2*, long, int, double2*, long, int, int, int, int, const double2*,

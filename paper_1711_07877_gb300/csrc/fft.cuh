@@ -29,12 +29,16 @@ int fft_max_length(bool fp64);
 //               sum_t (pre_row[r] pre_elem[t] in[r][t]) exp(sign 2 pi i (t + in_shift)(e + out_shift) / n)
 // for e < out_len, t < in_len (input element t sits at FFT position (t + in_shift) mod n,
 // output element e is FFT position (e + out_shift) mod n).  Scale pointers may be null.
+//
+// Hermitian fold (herm_n > 0, which needs rows == in_len == herm_n and in == herm_base):
+// the input is read as in[r][t] + conj(in[herm_n - r][herm_n - t]) (the second term
+// only for r, t >= 1), i.e. the transform of S(eta) + conj(S(-eta)) for a centred grid S.
 template <typename T>
 int fft_rows(const cx_t<T>* in, long in_stride, int in_len, int in_shift,
              cx_t<T>* out, long out_stride, int out_len, int out_shift,
              int rows, int n, int sign,
              const T* pre_elem, const T* pre_row, const T* post_elem, const T* post_row,
-             cudaStream_t stream);
+             cudaStream_t stream, int herm_n = 0);
 
 // Natural-order row transforms of length n (input and output windows start at 0) with
 // caller-provided tables: tw[t] = exp(-2 pi i t / n), perm = the digit reversal of

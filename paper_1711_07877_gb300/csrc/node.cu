@@ -148,6 +148,24 @@ __global__ void __launch_bounds__(256) gather_tiles_kernel(
     }
 }
 
+// (re, im) += (a, b) on a shared-memory float2 with one 64-bit compare-and-swap per
+// attempt: sm_103a has no native shared-memory float add (atomicAdd on a shared float
+// is itself a compare-and-swap loop), so one loop for both halves halves the loops.
+// Lock-free: a failed swap means another thread's succeeded.
+__device__ __forceinline__ void shared_add_f2(float2* addr, float a, float b) {
+    auto* p = reinterpret_cast<unsigned long long*>(addr);
+    unsigned long long old = *reinterpret_cast<volatile unsigned long long*>(p);
+    for (;;) {
+        const float x = __uint_as_float(static_cast<unsigned>(old)) + a;
+        const float y = __uint_as_float(static_cast<unsigned>(old >> 32)) + b;
+        const unsigned long long nw =
+            (static_cast<unsigned long long>(__float_as_uint(y)) << 32) | __float_as_uint(x);
+        const unsigned long long prev = atomicCAS(p, old, nw);
+        if (prev == old) return;
+        old = prev;
+    }
+}
+
 template <typename T, int G, typename Rec, typename Val>
 __global__ void __launch_bounds__(256) scatter_tiles_kernel(
     const Rec* __restrict__ rec, const long long* __restrict__ tile_start, int ntx, int n, int P, Window<T> win,
@@ -182,8 +200,12 @@ __global__ void __launch_bounds__(256) scatter_tiles_kernel(
                     const int r = rx + a;
                     if (col_ok && r >= 0 && r < kNodeTile) {
                         T* cell = acc + 2 * (r * kNodeTile + c);
-                        atomicAdd(cell, gr * w);
-                        atomicAdd(cell + 1, gi * w);
+                        if constexpr (sizeof(T) == 4) {
+                            shared_add_f2(reinterpret_cast<float2*>(cell), gr * w, gi * w);
+                        } else {
+                            atomicAdd(cell, gr * w);
+                            atomicAdd(cell + 1, gi * w);
+                        }
                     }
                 }
             }
@@ -198,8 +220,8 @@ __global__ void __launch_bounds__(256) scatter_tiles_kernel(
 }
 
 // Fused node step: one CTA per 64 x 64 tile of the frequency grid.  The tile plus a
-// (P-1) halo of K sits in shared memory, with two accumulator planes (re, im) of the
-// same size.  A group of G lanes (G = 8, 16 or 32 >= P; 32 / G nodes per warp) takes
+// (P-1) halo of K sits in shared memory with an accumulator of the same size
+// (interleaved float2 in FP32, two planes re / im in FP64).  A group of G lanes (G = 8, 16 or 32 >= P; 32 / G nodes per warp) takes
 // one node at a time, lane = stencil column: rows are accumulated in registers and the
 // columns reduced with shuffles (gather), the value is weighted by the node's omega'
 // and added back with shared atomics (scatter), with the weights computed once.  The
@@ -216,9 +238,11 @@ __global__ void __launch_bounds__(NT) node_fused_kernel(
     const long long b0 = tile_start[tile], b1 = tile_start[tile + 1];
     if (b0 == b1) return;
     const int W = kNodeTile + P - 1;
+    constexpr bool kF2 = sizeof(T) == 4;
     C* s = reinterpret_cast<C*>(smem_raw);
     T* acc_re = reinterpret_cast<T*>(s + W * Ws);
     T* acc_im = acc_re + W * Ws;
+    float2* acc2 = reinterpret_cast<float2*>(s + W * Ws);
     const int ox = (tile / ntx) * kNodeTile, oy = (tile % ntx) * kNodeTile;
     const int rows = min(W, n - ox), cols = min(W, n - oy);
     for (int idx = threadIdx.x; idx < W * W; idx += blockDim.x) {
@@ -226,8 +250,12 @@ __global__ void __launch_bounds__(NT) node_fused_kernel(
         C v = mk<T>(0, 0);
         if (r < rows && c < cols) v = kin[static_cast<long>(ox + r) * n + oy + c];
         s[r * Ws + c] = v;
-        acc_re[r * Ws + c] = 0;
-        acc_im[r * Ws + c] = 0;
+        if constexpr (kF2) {
+            acc2[r * Ws + c] = make_float2(0.f, 0.f);
+        } else {
+            acc_re[r * Ws + c] = 0;
+            acc_im[r * Ws + c] = 0;
+        }
     }
     __syncthreads();
     const int lane = threadIdx.x & 31;
@@ -273,8 +301,12 @@ __global__ void __launch_bounds__(NT) node_fused_kernel(
             if (a < P) {
                 const T w = __shfl_sync(gmask, wx, a, G);
                 if (sub < P) {
-                    atomicAdd(acc_re + base + a * Ws, gr * w);
-                    atomicAdd(acc_im + base + a * Ws, gi * w);
+                    if constexpr (kF2) {
+                        shared_add_f2(acc2 + base + a * Ws, gr * w, gi * w);
+                    } else {
+                        atomicAdd(acc_re + base + a * Ws, gr * w);
+                        atomicAdd(acc_im + base + a * Ws, gi * w);
+                    }
                 }
             }
         }
@@ -283,7 +315,15 @@ __global__ void __launch_bounds__(NT) node_fused_kernel(
     for (int idx = threadIdx.x; idx < W * W; idx += blockDim.x) {
         const int r = idx / W, c = idx - r * W;
         if (r >= rows || c >= cols) continue;
-        const T vr = acc_re[r * Ws + c], vi = acc_im[r * Ws + c];
+        T vr, vi;
+        if constexpr (kF2) {
+            const float2 v = acc2[r * Ws + c];
+            vr = v.x;
+            vi = v.y;
+        } else {
+            vr = acc_re[r * Ws + c];
+            vi = acc_im[r * Ws + c];
+        }
         C* dst = kout + static_cast<long>(ox + r) * n + oy + c;
         if (r >= P - 1 && c >= P - 1 && r < kNodeTile && c < kNodeTile) {
             *dst = mk<T>(vr, vi);
