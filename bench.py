@@ -255,6 +255,9 @@ def main():
     stream = torch.cuda.current_stream()
     plan = S.sbd_plan(zt, args.n, S.SBD_HELMHOLTZ if helm else S.SBD_LAPLACE, wl.kappa, wl.delta_min, wl.eps,
                       S.make_options(form=form, max_nrhs=nrhs))
+    t_tune = time.perf_counter()
+    tune_ms = S.sbd_tune(plan, 3, stream.cuda_stream)
+    t_tune = time.perf_counter() - t_tune
     info = S.sbd_plan_info(plan)
 
     def barrier():
@@ -338,8 +341,10 @@ def main():
            "vs_baseline": None, "dtype": "f32" if args.form == "fp32" else "f64", "data": "synthetic",
            "config": workload_config(args, rank), "clocks": clk, "e2e": e2e,
            "gpu_launches": (2 + 9 * nrhs) * args.steps, "roofline": roofline, "stages": stages,
-           "plan": {k: info[k] for k in ("P", "n_xi", "nnz", "grid_x", "grid_k", "fft_n", "stencil_x",
-                                         "nufft_tol", "fit_err", "device_bytes", "plan_seconds")}}
+           "plan": dict({k: info[k] for k in ("P", "n_xi", "n_records", "nnz", "grid_x", "grid_k", "fft_n",
+                                              "stencil_x", "stencil_k", "nufft_tol", "fit_err", "device_bytes",
+                                              "plan_seconds", "node_acc", "node_sched")},
+                        tune_seconds=t_tune, tune_node_ms=tune_ms)}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         qd = qt.cpu().numpy()
         targets = args.cpu_targets if args.n * nrhs <= 2_000_000 else max(8, args.cpu_targets // 20)

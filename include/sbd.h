@@ -107,6 +107,10 @@ typedef struct {
     double  w0_re, w0_im;    /* weight of the xi = 0 term, G(delta_max) for Laplace (Sec. 1) */
     int64_t device_bytes;    /* device memory held by the plan */
     double  plan_seconds;    /* wall time of sbd_plan */
+    int64_t n_records;       /* node records stored: N_xi, or N_xi / 2 for Laplace (the
+                                antipodal nodes follow by Hermitian symmetry) */
+    int32_t node_acc;        /* fused node-kernel variant (sbd_tune): accumulation mode */
+    int32_t node_sched;      /* fused node-kernel variant (sbd_tune): record schedule */
 } sbd_plan_stats;
 
 /* ---------------------------------------------------------------------------------
@@ -200,6 +204,24 @@ int sbd_offline_fit(sbd_kernel kernel, double delta_min, double delta_max, doubl
  * ------------------------------------------------------------------------------- */
 int sbd_fft2(const void* in, void* out, int32_t n0, int32_t n1, int32_t sign, int32_t form,
              void* cuda_stream);
+
+/* ---------------------------------------------------------------------------------
+ * Autotuning of the node step (no counterpart in the paper).  The fused node kernel
+ * has variants that compute the same sums: acc 0 adds re and im into two float planes
+ * (one shared-memory atomic each), acc 1 (FP32 form only) into one float2 plane with
+ * one 64-bit compare-and-swap; sched 0 deals the records of a tile to the lane groups
+ * in turn, sched 1 gives each group a contiguous run.  Results agree to rounding.
+ *   sbd_tune       times every applicable variant on the plan's own records (reps
+ *                  launches each, after one warm-up, CUDA events on cuda_stream; the
+ *                  frequency workspace is zeroed first) and keeps the fastest.
+ *                  ms (host, 4 entries, may be NULL): mean ms per launch of variant
+ *                  acc * 2 + sched, -1 where not applicable.  Blocks until done.
+ *   sbd_set_tuning picks a variant by hand.
+ * SBD_EINVAL for a null plan, reps < 1, or acc / sched outside {0, 1} (acc 1 needs the
+ * FP32 form).  Plans whose node step is the two-kernel fallback ignore the variant.
+ * ------------------------------------------------------------------------------- */
+int sbd_tune(sbd_plan_t plan, int32_t reps, double* ms, void* cuda_stream);
+int sbd_set_tuning(sbd_plan_t plan, int32_t acc, int32_t sched);
 
 /* ---------------------------------------------------------------------------------
  * Fit cache.  The off-line fit (P search and coefficients, Sec. 3-4) depends only on

@@ -80,6 +80,8 @@ struct sbd_plan_s {
     long long* node_tile_start = nullptr;
     void* ghat = nullptr;              // n_xi weighted node values (scratch of the two-kernel node step)
     bool node_fused = true;            // one-kernel node step (shared memory permitting)
+    NodeTuning tuning;                 // fused node-kernel variant (sbd_tune)
+    int tuned = 0;                     // 1 once sbd_tune chose the variant
     // workspace (one right-hand side at a time)
     void* wsX = nullptr;
     void* wsA = nullptr;
@@ -321,7 +323,7 @@ int far_apply(sbd_plan_s* p, const void* f, void* q, int nrhs, cudaStream_t s) {
         StepTimer t3(p, s, SBD_STAGE_NODE);
         if (p->node_fused) {
             if ((rc = node_step_fused<T>(static_cast<const NodeRec<T>*>(p->nodes), p->node_tile_start, p->geom, B,
-                                         C, s))) return rc;
+                                         C, p->tuning, s))) return rc;
         } else if ((rc = node_step_tiled<T>(static_cast<const NodeRec<T>*>(p->nodes), p->node_tile_start, p->geom,
                                             B, static_cast<cx_t<T>*>(p->ghat), C, s))) {
             return rc;
@@ -695,6 +697,76 @@ int sbd_plan_info(sbd_plan_t p, sbd_plan_stats* o) {
     o->w0_im = p->w0.imag();
     o->device_bytes = p->device_bytes;
     o->plan_seconds = p->plan_seconds;
+    o->n_records = p->n_rec;
+    o->node_acc = p->tuning.acc;
+    o->node_sched = p->tuning.sched;
+    return SBD_OK;
+}
+
+int sbd_set_tuning(sbd_plan_t p, int32_t acc, int32_t sched) {
+    if (!p || acc < 0 || acc > 1 || sched < 0 || sched > 1 || (acc == 1 && p->form != SBD_FORM_FP32)) {
+        set_error("sbd_set_tuning: invalid plan or variant");
+        return SBD_EINVAL;
+    }
+    p->tuning.acc = acc;
+    p->tuning.sched = sched;
+    return SBD_OK;
+}
+
+int sbd_tune(sbd_plan_t p, int32_t reps, double* ms, void* cuda_stream) {
+    if (!p || reps < 1) {
+        set_error("sbd_tune: null plan or reps < 1");
+        return SBD_EINVAL;
+    }
+    if (ms)
+        for (int v = 0; v < 4; ++v) ms[v] = -1.0;
+    if (!p->node_fused) return SBD_OK;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    const size_t e = p->form == SBD_FORM_FP32 ? sizeof(cx_t<float>) : sizeof(cx_t<double>);
+    SBD_CUDA_TRY(cudaMemsetAsync(p->wsB, 0, e * static_cast<size_t>(p->np.nk) * p->np.nk, s));
+    cudaEvent_t a, b;
+    SBD_CUDA_TRY(cudaEventCreate(&a));
+    SBD_CUDA_TRY(cudaEventCreate(&b));
+    double best = 1e300;
+    NodeTuning pick = p->tuning;
+    int rc = SBD_OK;
+    for (int acc = 0; acc <= (p->form == SBD_FORM_FP32 ? 1 : 0) && !rc; ++acc) {
+        for (int sched = 0; sched <= 1 && !rc; ++sched) {
+            const NodeTuning t{acc, sched};
+            auto step = [&]() {
+                return p->form == SBD_FORM_FP32
+                           ? node_step_fused<float>(static_cast<const NodeRec<float>*>(p->nodes), p->node_tile_start,
+                                                    p->geom, static_cast<const cx_t<float>*>(p->wsB),
+                                                    static_cast<cx_t<float>*>(p->wsC), t, s)
+                           : node_step_fused<double>(static_cast<const NodeRec<double>*>(p->nodes),
+                                                     p->node_tile_start, p->geom,
+                                                     static_cast<const cx_t<double>*>(p->wsB),
+                                                     static_cast<cx_t<double>*>(p->wsC), t, s);
+            };
+            if ((rc = step())) break;
+            if (cudaEventRecord(a, s) != cudaSuccess) { rc = SBD_ECUDA; break; }
+            for (int r = 0; r < reps && !rc; ++r) rc = step();
+            if (rc) break;
+            float t_ms = 0.f;
+            if (cudaEventRecord(b, s) != cudaSuccess || cudaEventSynchronize(b) != cudaSuccess ||
+                cudaEventElapsedTime(&t_ms, a, b) != cudaSuccess) {
+                set_error("sbd_tune: event timing failed");
+                rc = SBD_ECUDA;
+                break;
+            }
+            const double per = static_cast<double>(t_ms) / reps;
+            if (ms) ms[acc * 2 + sched] = per;
+            if (per < best) {
+                best = per;
+                pick = t;
+            }
+        }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (rc) return rc;
+    p->tuning = pick;
+    p->tuned = 1;
     return SBD_OK;
 }
 

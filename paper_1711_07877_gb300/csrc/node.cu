@@ -228,7 +228,13 @@ __global__ void __launch_bounds__(256) scatter_tiles_kernel(
 // next record is loaded while the current one is processed.  Cells that only this
 // tile's stencils reach (local rows and columns in [P-1, 64)) are stored, the overlap
 // band is added atomically into kout, which the caller clears.
-template <typename T, int G, int NT>
+//
+// Variants (chosen per plan by sbd_tune): ACC = 0 accumulates re and im in two float
+// planes with one atomicAdd each, ACC = 1 (FP32 only) in one float2 plane with one
+// 64-bit compare-and-swap; SCHED = 0 deals the tile's records to the lane groups in
+// turn, SCHED = 1 gives each group one contiguous run of records (the groups of a warp
+// then work on records far apart in the sorted order, which collide less).
+template <typename T, int G, int NT, int ACC, int SCHED>
 __global__ void __launch_bounds__(NT) node_fused_kernel(
     const NodeRec<T>* __restrict__ rec, const long long* __restrict__ tile_start, int ntx, int n, int P, int Ws,
     Window<T> win, const cx_t<T>* __restrict__ kin, cx_t<T>* __restrict__ kout) {
@@ -238,7 +244,7 @@ __global__ void __launch_bounds__(NT) node_fused_kernel(
     const long long b0 = tile_start[tile], b1 = tile_start[tile + 1];
     if (b0 == b1) return;
     const int W = kNodeTile + P - 1;
-    constexpr bool kF2 = sizeof(T) == 4;
+    constexpr bool kF2 = sizeof(T) == 4 && ACC == 1;
     C* s = reinterpret_cast<C*>(smem_raw);
     T* acc_re = reinterpret_cast<T*>(s + W * Ws);
     T* acc_im = acc_re + W * Ws;
@@ -261,13 +267,23 @@ __global__ void __launch_bounds__(NT) node_fused_kernel(
     const int lane = threadIdx.x & 31;
     const int sub = lane % G;
     const unsigned gmask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << (lane - sub));
-    const int group = threadIdx.x / G, ngroups = blockDim.x / G;
-    long long i = b0 + group;
+    const int group = threadIdx.x / G, ngroups = NT / G;
+    long long i, iend, istep;
+    if (SCHED == 0) {
+        i = b0 + group;
+        iend = b1;
+        istep = ngroups;
+    } else {
+        const long long len = (b1 - b0 + ngroups - 1) / ngroups;
+        i = b0 + group * len;
+        iend = min(b1, i + len);
+        istep = 1;
+    }
     NodeRec<T> nxt;
-    if (i < b1) nxt = rec[i];
-    for (; i < b1; i += ngroups) {
+    if (i < iend) nxt = rec[i];
+    for (; i < iend; i += istep) {
         const NodeRec<T> q = nxt;
-        if (i + ngroups < b1) nxt = rec[i + ngroups];          // prefetch
+        if (i + istep < iend) nxt = rec[i + istep];          // prefetch
         const int rx = q.cell.x - ox, ry = q.cell.y - oy;
         T wx = 0, wy = 0;
         if (sub < P) {
@@ -428,9 +444,31 @@ size_t node_fused_smem(int Pk) {
     return static_cast<size_t>(W) * Ws * (sizeof(cx_t<T>) + 2 * sizeof(T));
 }
 
+template <typename T, int G, int ACC, int SCHED>
+int launch_fused(const NodeRec<T>* nodes, const long long* tile_start, unsigned nt, int ntx, const FarGeom& g,
+                 int Ws, size_t smem, const Window<T>& win, const cx_t<T>* kin, cx_t<T>* kout, cudaStream_t s) {
+    auto k = node_fused_kernel<T, G, kNodeThreads, ACC, SCHED>;
+    SBD_TRY(raise_smem_limit(k, smem));
+    k<<<nt, kNodeThreads, smem, s>>>(nodes, tile_start, ntx, g.nk, g.Pk, Ws, win, kin, kout);
+    SBD_LAUNCH_CHECK();
+    return SBD_OK;
+}
+
+template <typename T, int G>
+int launch_fused_g(const NodeRec<T>* nodes, const long long* tile_start, unsigned nt, int ntx, const FarGeom& g,
+                   int Ws, size_t smem, const Window<T>& win, const cx_t<T>* kin, cx_t<T>* kout,
+                   const NodeTuning& t, cudaStream_t s) {
+    if (sizeof(T) == 4 && t.acc == 1) {
+        return t.sched ? launch_fused<T, G, 1, 1>(nodes, tile_start, nt, ntx, g, Ws, smem, win, kin, kout, s)
+                       : launch_fused<T, G, 1, 0>(nodes, tile_start, nt, ntx, g, Ws, smem, win, kin, kout, s);
+    }
+    return t.sched ? launch_fused<T, G, 0, 1>(nodes, tile_start, nt, ntx, g, Ws, smem, win, kin, kout, s)
+                   : launch_fused<T, G, 0, 0>(nodes, tile_start, nt, ntx, g, Ws, smem, win, kin, kout, s);
+}
+
 template <typename T>
 int node_step_fused(const NodeRec<T>* nodes, const long long* tile_start, const FarGeom& g,
-                    const cx_t<T>* kin, cx_t<T>* kout, cudaStream_t s) {
+                    const cx_t<T>* kin, cx_t<T>* kout, const NodeTuning& t, cudaStream_t s) {
     SBD_CUDA_TRY(cudaMemsetAsync(kout, 0, sizeof(cx_t<T>) * static_cast<size_t>(g.nk) * g.nk, s));
     const int ntx = tiles_per_side(g.nk);
     const unsigned nt = static_cast<unsigned>(ntx) * ntx;
@@ -439,21 +477,9 @@ int node_step_fused(const NodeRec<T>* nodes, const long long* tile_start, const 
     const int Ws = fused_stride(W, P8);
     const size_t smem = node_fused_smem<T>(g.Pk);
     const Window<T> win = make_window<T>(g.kwin, g.beta_k, g.Pk);
-    if (P8 == 8) {
-        auto k = node_fused_kernel<T, 8, kNodeThreads>;
-        SBD_TRY(raise_smem_limit(k, smem));
-        k<<<nt, kNodeThreads, smem, s>>>(nodes, tile_start, ntx, g.nk, g.Pk, Ws, win, kin, kout);
-    } else if (P8 == 16) {
-        auto k = node_fused_kernel<T, 16, kNodeThreads>;
-        SBD_TRY(raise_smem_limit(k, smem));
-        k<<<nt, kNodeThreads, smem, s>>>(nodes, tile_start, ntx, g.nk, g.Pk, Ws, win, kin, kout);
-    } else {
-        auto k = node_fused_kernel<T, 32, kNodeThreads>;
-        SBD_TRY(raise_smem_limit(k, smem));
-        k<<<nt, kNodeThreads, smem, s>>>(nodes, tile_start, ntx, g.nk, g.Pk, Ws, win, kin, kout);
-    }
-    SBD_LAUNCH_CHECK();
-    return SBD_OK;
+    if (P8 == 8) return launch_fused_g<T, 8>(nodes, tile_start, nt, ntx, g, Ws, smem, win, kin, kout, t, s);
+    if (P8 == 16) return launch_fused_g<T, 16>(nodes, tile_start, nt, ntx, g, Ws, smem, win, kin, kout, t, s);
+    return launch_fused_g<T, 32>(nodes, tile_start, nt, ntx, g, Ws, smem, win, kin, kout, t, s);
 }
 
 template <typename T>
@@ -487,7 +513,7 @@ int interp_tiled(const PointRec<T>* pts, const int* perm, const long long* tile_
                                     cx_t<T>*, cx_t<T>*, cudaStream_t);                                       \
     template size_t node_fused_smem<T>(int);                                                                 \
     template int node_step_fused<T>(const NodeRec<T>*, const long long*, const FarGeom&, const cx_t<T>*,     \
-                                    cx_t<T>*, cudaStream_t);                                                 \
+                                    cx_t<T>*, const NodeTuning&, cudaStream_t);                              \
     template int spread_tiled<T>(const PointRec<T>*, const int*, const long long*, const FarGeom&,           \
                                  const void*, bool, cx_t<T>*, cudaStream_t);                                 \
     template int interp_tiled<T>(const PointRec<T>*, const int*, const long long*, const FarGeom&,           \

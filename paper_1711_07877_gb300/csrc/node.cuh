@@ -20,13 +20,21 @@ template <typename T>
 int node_step_tiled(const NodeRec<T>* nodes, const long long* tile_start, const FarGeom& g,
                     const cx_t<T>* kin, cx_t<T>* ghat, cx_t<T>* kout, cudaStream_t s);
 
+// Variant of the fused node kernel (see node.cu): acc 0 = two float planes with
+// atomicAdd, 1 = one float2 plane with a 64-bit compare-and-swap (FP32 only); sched 0 =
+// records dealt to the lane groups in turn, 1 = one contiguous run per group.
+struct NodeTuning {
+    int acc = 0;
+    int sched = 0;
+};
+
 // The same in one kernel per tile: gather, weight and scatter into a shared accumulator,
 // whose overlap band is added atomically into kout (cleared here).
 template <typename T>
 size_t node_fused_smem(int Pk);   // dynamic shared memory of the fused kernel
 template <typename T>
 int node_step_fused(const NodeRec<T>* nodes, const long long* tile_start, const FarGeom& g,
-                    const cx_t<T>* kin, cx_t<T>* kout, cudaStream_t s);
+                    const cx_t<T>* kin, cx_t<T>* kout, const NodeTuning& t, cudaStream_t s);
 
 // grid (m x m, fully written) = spreading of f (float64 or complex128, original order).
 template <typename T>

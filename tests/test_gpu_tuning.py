@@ -1,0 +1,79 @@
+"""GPU: the node-kernel variants chosen by sbd_tune compute the same matvec.
+
+Each variant sums the same products in another order (or with another atomic), so
+results agree to FP32 rounding (rel-L2 <= 2e-6 between variants) and each stays
+within eps sum|f| of the oracle's direct sum (Sec. 1 output bound)."""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import sbd_oracle as O
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def S():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1711_07877_gb300 import build
+    build.build_library()
+    import paper_1711_07877_gb300 as pkg
+    return pkg
+
+
+@pytest.mark.parametrize("kind", ["laplace", "helmholtz"])
+def test_variants_agree_and_tune_picks_one(S, kind):
+    n = 6000
+    wl = W.laplace_disk(n, 51, 1e-6) if kind == "laplace" else None
+    if kind == "laplace":
+        z, f, kappa, dmin = wl.z, wl.f, 0.0, wl.delta_min
+    else:
+        z = W.curve_points(n, 52)
+        f = W.rhs(n, 53, complex_valued=True)
+        kappa = 60.0 / W.enclosing_diameter(z)
+        dmin = float(np.sqrt(20.0 / n))
+    zt = torch.from_numpy(z).cuda()
+    ft = torch.from_numpy(f).cuda()
+    p = S.sbd_plan(zt, n, S.SBD_HELMHOLTZ if kind == "helmholtz" else S.SBD_LAPLACE, kappa, dmin, 1e-6,
+                   S.make_options(form=S.SBD_FORM_FP32))
+    try:
+        outs = {}
+        for acc in (0, 1):
+            for sched in (0, 1):
+                S.sbd_set_tuning(p, acc, sched)
+                info = S.sbd_plan_info(p)
+                assert (info["node_acc"], info["node_sched"]) == (acc, sched)
+                q = torch.empty_like(ft)
+                S.sbd_matvec(p, ft, q)
+                torch.cuda.synchronize()
+                outs[(acc, sched)] = q.cpu().numpy()
+        base = outs[(0, 0)]
+        for k, v in outs.items():
+            assert np.linalg.norm(v - base) / np.linalg.norm(base) < 2e-6, k
+        idx = np.random.default_rng(5).choice(n, 300, replace=False)
+        ref = O.direct_sum(z, f, kind, kappa, targets=idx)
+        for k, v in outs.items():
+            assert np.max(np.abs(v[idx] - ref)) <= 1e-6 * np.abs(f).sum(), k
+        ms = S.sbd_tune(p, reps=2)
+        assert all(t > 0 for t in ms)
+        info = S.sbd_plan_info(p)
+        best = int(np.argmin(ms))
+        assert (info["node_acc"], info["node_sched"]) == (best // 2, best % 2)
+    finally:
+        S.sbd_destroy(p)
+
+
+def test_fp64_rejects_cas_variant(S):
+    wl = W.laplace_disk(500, 54, 1e-6)
+    zt = torch.from_numpy(wl.z).cuda()
+    p = S.sbd_plan(zt, 500, S.SBD_LAPLACE, 0.0, wl.delta_min, 1e-6, S.make_options(form=S.SBD_FORM_FP64))
+    try:
+        with pytest.raises(S.SbdError) as e:
+            S.sbd_set_tuning(p, 1, 0)
+        assert e.value.code == S.SBD_EINVAL
+        ms = S.sbd_tune(p, reps=1)
+        assert ms[0] > 0 and ms[1] > 0 and ms[2] == -1 and ms[3] == -1
+    finally:
+        S.sbd_destroy(p)
