@@ -149,11 +149,23 @@ def stage_bytes(info, n, nrhs, form, esz=8):
     m, nk, nxi, nnz, P = info["grid_x"], info["grid_k"], info["n_xi"], info["nnz"], info["stencil_x"]
     touched = min(m * m, n * P * P)
     vb = 16 if esz == 16 else 8              # D value (complex for Helmholtz)
+    if esz == 8:
+        # Laplace: real spreading grid (half a complex element per cell), Hermitian K of
+        # which the half plane kx >= 0 is transformed, half the node records
+        return {
+            "sum": esz * n * nrhs,
+            "spread": pr * n + esz * n + c * m * m // 2,
+            "fft_fwd": c * (m * m // 2 + nk * nk // 2),
+            "node": nr * info["n_records"] + c * nk * nk,
+            "fft_inv": c * (nk * nk // 2 + m * m // 2),
+            "interp": pr * n + esz * n + c * touched // 2,
+            "spmv": (4 + vb) * nnz + 8 * (n + 1) + 2 * esz * n * nrhs,
+        }
     return {
         "sum": esz * n * nrhs,
         "spread": pr * n + esz * n + c * m * m,
         "fft_fwd": c * (m * m + nk * nk),
-        "node": nr * (nxi // 2 if esz == 8 else nxi) + 2 * c * nk * nk,
+        "node": nr * nxi + 2 * c * nk * nk,
         "fft_inv": c * (nk * nk + m * m),
         "interp": pr * n + esz * n + c * touched,
         "spmv": (4 + vb) * nnz + 8 * (n + 1) + 2 * esz * n * nrhs,

@@ -139,6 +139,11 @@ int sbd_plan(const double* points, int64_t n, sbd_kernel kernel, double delta_mi
  *   nrhs   1 <= nrhs <= max_nrhs of the plan's options.
  * Asynchronous on cuda_stream.  The plan's workspace is shared: calls on the same
  * plan must be ordered (one stream, or events); different plans run concurrently.
+ * D is held over the plan's internal point order (the spatial order of its spreading
+ * records): D f is formed first from f gathered into that order, and each point's
+ * value is added as the far part is interpolated to it.  For Laplace the spreading
+ * grid is real and the frequency grid Hermitian, so half the transforms and half the
+ * quadrature nodes are processed (the rest follow by symmetry).
  * ------------------------------------------------------------------------------- */
 int sbd_matvec(sbd_plan_t plan, const void* f, void* q, int32_t nrhs, void* cuda_stream);
 
@@ -213,7 +218,9 @@ int sbd_fft2(const void* in, void* out, int32_t n0, int32_t n1, int32_t sign, in
  * in turn, sched 1 gives each group a contiguous run.  Results agree to rounding.
  *   sbd_tune       times every applicable variant on the plan's own records (reps
  *                  launches each, after one warm-up, CUDA events on cuda_stream; the
- *                  frequency workspace is zeroed first) and keeps the fastest.
+ *                  frequency workspace is first filled with a constant non-zero value,
+ *                  so that concurrent adds to a cell contend as with real data) and
+ *                  keeps the fastest.
  *                  ms (host, 4 entries, may be NULL): mean ms per launch of variant
  *                  acc * 2 + sched, -1 where not applicable.  Blocks until done.
  *   sbd_set_tuning picks a variant by hand.

@@ -1,4 +1,5 @@
 // C ABI of libsbd.so: plan construction (off-line part) and the on-line matvec.
+#include <algorithm>
 #include <chrono>
 #include <map>
 #include <mutex>
@@ -75,7 +76,10 @@ struct sbd_plan_s {
     int* half_start = nullptr;         // prefix sums of M_p / 2 (half node set), or null
     bool half_nodes = false;           // Laplace: records for m < M_p / 2 only (Hermitian symmetry)
     long long n_rec = 0;               // node records: N_xi, or N_xi / 2 with half_nodes
-    int* pt_perm = nullptr;            // sorted point record -> original point index
+    int* pt_perm = nullptr;            // sorted point record -> original point index (the
+                                       // internal order of D's rows and columns)
+    void* f_int = nullptr;             // f in internal order, right-hand sides interleaved
+    void* q_int = nullptr;             // D f in internal order, interleaved
     long long* pt_tile_start = nullptr;
     long long* node_tile_start = nullptr;
     void* ghat = nullptr;              // n_xi weighted node values (scratch of the two-kernel node step)
@@ -297,8 +301,48 @@ int inverse_fft(sbd_plan_s* p, const cx_t<T>* K2, cx_t<T>* A, cx_t<T>* Tr, cx_t<
     return fft_rows<T>(Tr, nk, nk, -nk / 2, X, m, m, -m / 2, m, n, +1, nullptr, nullptr, dec, dec, s);
 }
 
+// Real data (Laplace): the spreading grid X is real, stored as packed row pairs
+// (m / 2 x m complex), and K is Hermitian.  Forward: one transform per row pair,
+// split into the two rows' spectra, of which only kx >= kx_lo (the half plane of the
+// half node set plus the stencil reach) is kept; then the transforms along y for
+// those kx only, into rows kx_lo.. of K.
 template <typename T>
-int far_apply(sbd_plan_s* p, const void* f, void* q, int nrhs, cudaStream_t s) {
+int kx_low(const sbd_plan_s* p) { return p->np.nk / 2 - (p->np.Pk / 2 + 2); }
+
+template <typename T>
+int forward_fft_real(sbd_plan_s* p, const cx_t<T>* Xp, cx_t<T>* A, cx_t<T>* Tr, cx_t<T>* K, cudaStream_t s) {
+    const NufftParams& np = p->np;
+    const int m = np.m, nk = np.nk, n = np.n;
+    const int lo = kx_low<T>(p), w2 = nk - lo;
+    const T* dec = static_cast<const T*>(p->dec);
+    int rc = fft_rows<T>(Xp, m, m, -m / 2, A, w2, w2, lo - nk / 2, m / 2, n, -1, dec, dec, nullptr, nullptr, s, 0, 0,
+                         kIoPairFwd);
+    if (rc) return rc;
+    if ((rc = transpose<T>(A, w2, 0, Tr, m, 0, m, w2, 1, s))) return rc;   // [y][kx] -> [kx][y]
+    return fft_rows<T>(Tr, m, m, -m / 2, K + static_cast<long>(lo) * nk, nk, nk, -nk / 2, w2, n, -1, nullptr, nullptr,
+                       nullptr, nullptr, s);
+}
+
+// Adjoint for real data: S (node step over the half node set) completes to
+// S(eta) + conj(S(-eta)), which is Hermitian, so only kx >= 0 is transformed along y
+// (the fold is applied on the load); then each pair of y rows is one transform along
+// x from its two half spectra, giving the packed real X.
+template <typename T>
+int inverse_fft_real(sbd_plan_s* p, const cx_t<T>* S, cx_t<T>* A, cx_t<T>* Tr, cx_t<T>* Xp, cudaStream_t s) {
+    const NufftParams& np = p->np;
+    const int m = np.m, nk = np.nk, n = np.n;
+    const int J = nk / 2;
+    const T* dec = static_cast<const T*>(p->dec);
+    int rc = fft_rows<T>(S + static_cast<long>(J) * nk, nk, nk, -nk / 2, A, m, m, -m / 2, J, n, +1, nullptr, nullptr,
+                         nullptr, nullptr, s, nk, J);
+    if (rc) return rc;
+    if ((rc = transpose<T>(A, m, 0, Tr, J, 0, J, m, 1, s))) return rc;   // [kx][y] -> [y][kx]
+    return fft_rows<T>(Tr, J, J, 0, Xp, m, m, -m / 2, m / 2, n, +1, nullptr, nullptr, dec, dec, s, 0, 0, kIoPairInv);
+}
+
+// q = far part of f (+ the internal-order near term add[i * nrhs + r] when add is given).
+template <typename T>
+int far_apply(sbd_plan_s* p, const void* f, void* q, int nrhs, cudaStream_t s, const void* add) {
     const bool cplx_io = p->kind == SBD_HELMHOLTZ;
     StepTimer t_sum(p, s, SBD_STAGE_SUM);
     int rc = far_sum(f, cplx_io, p->n, nrhs, p->sumf, s);
@@ -313,12 +357,13 @@ int far_apply(sbd_plan_s* p, const void* f, void* q, int nrhs, cudaStream_t s) {
     for (int r = 0; r < nrhs; ++r) {
         const void* fr = static_cast<const char*>(f) + esz * p->n * r;
         void* qr = static_cast<char*>(q) + esz * p->n * r;
+        const bool real = p->half_nodes;   // Laplace: real grids, half the transforms and nodes
         StepTimer t1(p, s, SBD_STAGE_SPREAD);
         if ((rc = spread_tiled<T>(static_cast<const PointRec<T>*>(p->pts), p->pt_perm, p->pt_tile_start, p->geom,
-                                  fr, cplx_io, X, s))) return rc;
+                                  fr, cplx_io, X, s, real))) return rc;
         t1.end();
         StepTimer t2(p, s, SBD_STAGE_FFT_FWD);
-        if ((rc = forward_fft<T>(p, X, A, C, B, s))) return rc;
+        if ((rc = real ? forward_fft_real<T>(p, X, A, C, B, s) : forward_fft<T>(p, X, A, C, B, s))) return rc;
         t2.end();
         StepTimer t3(p, s, SBD_STAGE_NODE);
         if (p->node_fused) {
@@ -330,11 +375,11 @@ int far_apply(sbd_plan_s* p, const void* f, void* q, int nrhs, cudaStream_t s) {
         }
         t3.end();
         StepTimer t4(p, s, SBD_STAGE_FFT_INV);
-        if ((rc = inverse_fft<T>(p, C, A, B, X, s, p->half_nodes))) return rc;
+        if ((rc = real ? inverse_fft_real<T>(p, C, A, B, X, s) : inverse_fft<T>(p, C, A, B, X, s, false))) return rc;
         t4.end();
         StepTimer t5(p, s, SBD_STAGE_INTERP);
         if ((rc = interp_tiled<T>(static_cast<const PointRec<T>*>(p->pts), p->pt_perm, p->pt_tile_start, p->geom, X,
-                                  w0, p->sumf + r, qr, cplx_io, s))) return rc;
+                                  w0, p->sumf + r, qr, cplx_io, s, real, add, nrhs, r))) return rc;
         t5.end();
     }
     return SBD_OK;
@@ -577,12 +622,26 @@ int sbd_plan(const double* points, int64_t n, sbd_kernel kernel, double delta_mi
     nd.self_re = nt.self_value.real();
     nd.self_im = nt.self_value.imag();
     const bool cval = kernel.kind == SBD_HELMHOLTZ;
-    if ((rc = near_build(p->z, p->n, delta_min, bb[0], bb[1], bb[2], bb[3], nd, cval, &p->rowptr, &p->col, &p->val,
-                         &p->nnz, &p->n_coinc, s))) return fail(rc);
-    p->device_bytes += static_cast<long long>(sizeof(long long) * (p->n + 1) + (sizeof(int) + (cval ? 16 : 8)) * p->nnz);
-    p->n_coinc /= 2;
     rc = o.form == SBD_FORM_FP32 ? build_far<float>(p, s) : build_far<double>(p, s);
     if (rc) return fail(rc);
+    // D over the internal order (the spreading records' tile order): the points of a
+    // row's columns are neighbours in that order too, so D f reads f locally
+    {
+        double* zs = nullptr;
+        SBD_CUDA_TRY(cudaMallocAsync(&zs, sizeof(double) * 2 * p->n, s));
+        if ((rc = near_gather(p->z, true, p->n, 1, p->pt_perm, zs, s))) return fail(rc);
+        rc = near_build(zs, p->n, delta_min, bb[0], bb[1], bb[2], bb[3], nd, cval, &p->rowptr, &p->col, &p->val,
+                        &p->nnz, &p->n_coinc, s);
+        cudaFreeAsync(zs, s);
+        if (rc) return fail(rc);
+    }
+    p->device_bytes += static_cast<long long>(sizeof(long long) * (p->n + 1) + (sizeof(int) + (cval ? 16 : 8)) * p->nnz);
+    p->n_coinc /= 2;
+    {
+        const size_t vb = (cval ? 16 : 8) * static_cast<size_t>(p->n) * p->max_nrhs;
+        if ((rc = dev_alloc(p, &p->f_int, vb))) return fail(rc);
+        if ((rc = dev_alloc(p, &p->q_int, vb))) return fail(rc);
+    }
     if ((rc = dev_alloc(p, reinterpret_cast<void**>(&p->sumf), sizeof(double2) * p->max_nrhs))) return fail(rc);
     if ((rc = dev_alloc(p, reinterpret_cast<void**>(&p->zero2), sizeof(double2)))) return fail(rc);
     if (cudaStreamSynchronize(s) != cudaSuccess) {
@@ -602,8 +661,19 @@ int sbd_far(sbd_plan_t p, const void* f, void* q, int32_t nrhs, void* cuda_strea
         return SBD_EINVAL;
     }
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
-    return p->form == SBD_FORM_FP32 ? far_apply<float>(p, f, q, nrhs, s) : far_apply<double>(p, f, q, nrhs, s);
+    return p->form == SBD_FORM_FP32 ? far_apply<float>(p, f, q, nrhs, s, nullptr)
+                                    : far_apply<double>(p, f, q, nrhs, s, nullptr);
 }
+
+namespace {
+// q_int = D f in the internal order (f gathered into f_int first)
+int close_internal(sbd_plan_s* p, const void* f, int nrhs, cudaStream_t s) {
+    const bool c = p->kind == SBD_HELMHOLTZ;
+    int rc = near_gather(f, c, p->n, nrhs, p->pt_perm, p->f_int, s);
+    if (rc) return rc;
+    return near_spmv_internal(p->rowptr, p->col, p->val, c, p->n, nrhs, p->f_int, p->q_int, s);
+}
+}  // namespace
 
 int sbd_close(sbd_plan_t p, const void* f, void* q, int32_t nrhs, void* cuda_stream) {
     int rc = check_plan_call(p, f, q);
@@ -612,18 +682,25 @@ int sbd_close(sbd_plan_t p, const void* f, void* q, int32_t nrhs, void* cuda_str
         set_error("nrhs outside [1, max_nrhs]");
         return SBD_EINVAL;
     }
-    return near_spmv(p->rowptr, p->col, p->val, p->kind == SBD_HELMHOLTZ, p->n, nrhs, f, q, false,
-                     static_cast<cudaStream_t>(cuda_stream));
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    if ((rc = close_internal(p, f, nrhs, s))) return rc;
+    return near_scatter(p->q_int, p->kind == SBD_HELMHOLTZ, p->n, nrhs, p->pt_perm, q, s);
 }
 
 int sbd_matvec(sbd_plan_t p, const void* f, void* q, int32_t nrhs, void* cuda_stream) {
-    int rc = sbd_far(p, f, q, nrhs, cuda_stream);
+    int rc = check_plan_call(p, f, q);
     if (rc) return rc;
-    StepTimer t(p, static_cast<cudaStream_t>(cuda_stream), SBD_STAGE_SPMV);
-    rc = near_spmv(p->rowptr, p->col, p->val, p->kind == SBD_HELMHOLTZ, p->n, nrhs, f, q, true,
-                   static_cast<cudaStream_t>(cuda_stream));
+    if (nrhs < 1 || nrhs > p->max_nrhs) {
+        set_error("nrhs outside [1, max_nrhs]");
+        return SBD_EINVAL;
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    // D f first, in the internal order; the interpolation adds it as it writes q
+    StepTimer t(p, s, SBD_STAGE_SPMV);
+    if ((rc = close_internal(p, f, nrhs, s))) return rc;
     t.end();
-    return rc;
+    return p->form == SBD_FORM_FP32 ? far_apply<float>(p, f, q, nrhs, s, p->q_int)
+                                    : far_apply<double>(p, f, q, nrhs, s, p->q_int);
 }
 
 int sbd_profile(sbd_plan_t p, int32_t enable) {
@@ -722,8 +799,12 @@ int sbd_tune(sbd_plan_t p, int32_t reps, double* ms, void* cuda_stream) {
         for (int v = 0; v < 4; ++v) ms[v] = -1.0;
     if (!p->node_fused) return SBD_OK;
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
-    const size_t e = p->form == SBD_FORM_FP32 ? sizeof(cx_t<float>) : sizeof(cx_t<double>);
-    SBD_CUDA_TRY(cudaMemsetAsync(p->wsB, 0, e * static_cast<size_t>(p->np.nk) * p->np.nk, s));
+    // non-zero input: with zeros every compare-and-swap would succeed at once, which
+    // hides the retries that concurrent adds to one cell cost with real data
+    const long cells = static_cast<long>(p->np.nk) * p->np.nk;
+    int frc = p->form == SBD_FORM_FP32 ? fill_grid<float>(static_cast<cx_t<float>*>(p->wsB), cells, 1.f, 0.5f, s)
+                                       : fill_grid<double>(static_cast<cx_t<double>*>(p->wsB), cells, 1.0, 0.5, s);
+    if (frc) return frc;
     cudaEvent_t a, b;
     SBD_CUDA_TRY(cudaEventCreate(&a));
     SBD_CUDA_TRY(cudaEventCreate(&b));
@@ -798,9 +879,37 @@ int sbd_close_export(sbd_plan_t p, int64_t* rowptr, int32_t* col, double* val) {
         return SBD_EINVAL;
     }
     SBD_CUDA_TRY(cudaDeviceSynchronize());
-    SBD_CUDA_TRY(cudaMemcpy(rowptr, p->rowptr, sizeof(long long) * (p->n + 1), cudaMemcpyDeviceToHost));
-    SBD_CUDA_TRY(cudaMemcpy(col, p->col, sizeof(int) * p->nnz, cudaMemcpyDeviceToHost));
-    SBD_CUDA_TRY(cudaMemcpy(val, p->val, (p->kind == SBD_HELMHOLTZ ? 16 : 8) * p->nnz, cudaMemcpyDeviceToHost));
+    // the plan holds D over the internal order; map rows and columns back to the
+    // caller's order (row k = internal row inv[k]), diagonal first, then by column
+    const long n = p->n;
+    const size_t vb = p->kind == SBD_HELMHOLTZ ? 16 : 8;
+    std::vector<long long> rp(n + 1);
+    std::vector<int> cl(p->nnz), perm(n);
+    std::vector<unsigned char> vl(vb * p->nnz);
+    SBD_CUDA_TRY(cudaMemcpy(rp.data(), p->rowptr, sizeof(long long) * (n + 1), cudaMemcpyDeviceToHost));
+    SBD_CUDA_TRY(cudaMemcpy(cl.data(), p->col, sizeof(int) * p->nnz, cudaMemcpyDeviceToHost));
+    SBD_CUDA_TRY(cudaMemcpy(vl.data(), p->val, vb * p->nnz, cudaMemcpyDeviceToHost));
+    SBD_CUDA_TRY(cudaMemcpy(perm.data(), p->pt_perm, sizeof(int) * n, cudaMemcpyDeviceToHost));
+    std::vector<long> inv(n);
+    for (long i = 0; i < n; ++i) inv[perm[i]] = i;
+    rowptr[0] = 0;
+    for (long k = 0; k < n; ++k) rowptr[k + 1] = rowptr[k] + (rp[inv[k] + 1] - rp[inv[k]]);
+    std::vector<std::pair<int, long long>> ent;
+    for (long k = 0; k < n; ++k) {
+        const long i = inv[k];
+        ent.clear();
+        for (long long j = rp[i]; j < rp[i + 1]; ++j) ent.emplace_back(perm[cl[j]], j);
+        std::sort(ent.begin(), ent.end(), [k](const std::pair<int, long long>& a, const std::pair<int, long long>& b) {
+            if ((a.first == k) != (b.first == k)) return a.first == k;
+            return a.first < b.first;
+        });
+        long long o = rowptr[k];
+        for (const auto& e : ent) {
+            col[o] = e.first;
+            std::memcpy(reinterpret_cast<unsigned char*>(val) + vb * o, vl.data() + vb * e.second, vb);
+            ++o;
+        }
+    }
     return SBD_OK;
 }
 

@@ -47,18 +47,24 @@ __device__ __forceinline__ int find_circle(const int* __restrict__ num, int n_ci
     return lo;
 }
 
+// Angle index of record mm of its circle: m = mm for the full set; the half set takes
+// m in [-floor(M/4), -floor(M/4) + M/2), the nodes with cos(2 pi m / M) >= 0 (xi_x >= 0),
+// one of each antipodal pair.
+__device__ __forceinline__ long angle_index(bool half, long mm, int M) { return half ? mm - M / 4 : mm; }
+
 // Record index -> circle, canonical node index and xi (FP64, Eq. (defXimp)).
 struct NodeId { int circle; long canon; long antipode; double2 xi; };
 __device__ __forceinline__ NodeId node_id(const NodeFrame& fr, long rec) {
     NodeId id;
     const int* num = fr.hstart ? fr.hstart : fr.start;
     const int c = find_circle(num, fr.n_circles, rec);
-    const long mm = rec - num[c];
+    const int M = fr.M[c];
+    const long m = angle_index(fr.hstart != nullptr, rec - num[c], M);
     double sn, cs;
-    sincospi(2.0 * static_cast<double>(mm) / fr.M[c], &sn, &cs);
+    sincospi(2.0 * static_cast<double>(m) / M, &sn, &cs);
     id.circle = c;
-    id.canon = fr.start[c] + mm;
-    id.antipode = fr.start[c] + mm + fr.M[c] / 2;
+    id.canon = fr.start[c] + ((m % M) + M) % M;
+    id.antipode = fr.start[c] + (((m + M / 2) % M) + M) % M;
     id.xi = make_double2(fr.radius[c] * cs, fr.radius[c] * sn);
     return id;
 }
@@ -72,7 +78,7 @@ __global__ void prepare_nodes_kernel(const int* __restrict__ start, const int* _
     if (nu >= n_rec) return;
     const int* num = hstart ? hstart : start;
     const int c = find_circle(num, n_circles, nu);
-    const long mm = nu - num[c];
+    const long mm = angle_index(hstart != nullptr, nu - num[c], M[c]);
     double sn, cs;
     sincospi(2.0 * static_cast<double>(mm) / M[c], &sn, &cs);   // xi_m = r (cos 2pi m/M, sin 2pi m/M)
     const double kx = radius[c] * cs / deta + 0.5 * nk;

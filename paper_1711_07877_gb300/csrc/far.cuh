@@ -32,9 +32,10 @@ int far_prepare_points(const double* z, long n, double cx, double cy, double h, 
                        PointRec<T>* out, cudaStream_t s);
 // Records of the quadrature nodes.  half_start null: every node, n_rec = N_xi, record
 // numbering = canonical numbering (circle by circle, angle index m).  half_start
-// non-null (prefix sums of M_p / 2; every M_p is even): only the nodes m < M_p / 2 of
-// each circle, whose antipodes -xi the Hermitian-symmetric node step of a real-valued
-// transform supplies by symmetry.
+// non-null (prefix sums of M_p / 2; every M_p is even): per circle only the M_p / 2
+// nodes with xi_x >= 0 (angle index m in [-floor(M_p/4), -floor(M_p/4) + M_p/2)), whose
+// antipodes -xi the Hermitian-symmetric node step of a real-valued transform supplies
+// by symmetry.
 template <typename T>
 int far_prepare_nodes(const int* circle_start, const int* half_start, const double* radius, const int* M,
                       int n_circles, long n_rec, double deta, int nk, int P, const cx_t<T>* omega_c,

@@ -159,12 +159,53 @@ __device__ __forceinline__ void dit_stage(cx_t<T>* s, int n, int Lp, int sign, c
     __syncthreads();
 }
 
-// One row (blockIdx.x) and one phase (blockIdx.y) of a length-n transform done as Q
+// One row (blockIdx.y) and one phase (blockIdx.x) of a length-n transform done as Q
 // transforms of length nq = n / Q (Q = 1 or 2): output k = Q k' + r is the length-nq DFT
 // of y_r[t] = sum_{j < Q} x[t + j nq] w_n^{r (t + j nq)} (fold and twist on the load).
 // Hermitian fold of the load (see fft_rows): base of the whole grid, its side (0 = off)
 // and the absolute index of this launch's first row.
 template <typename T> struct HermFold { const cx_t<T>* base; int n; long row0; };
+
+// Input element at FFT position idx of the current row (has = false: a zero).
+template <typename T>
+__device__ __forceinline__ cx_t<T> load_elem(int io, int idx, int n, const cx_t<T>* __restrict__ src,
+                                             long in_stride, int in_len, int in_shift, long row,
+                                             const HermFold<T>& hf, T rs0, T rs1,
+                                             const T* __restrict__ pre_elem, bool& has) {
+    using C = cx_t<T>;
+    has = false;
+    if (io == kIoPairInv) {
+        // rows 2r, 2r+1 hold frequencies 0..in_len-1 of two Hermitian spectra A0, A1;
+        // z = A0 + i A1 with A(-k) = conj A(k)
+        const int k = idx < n / 2 ? idx : idx - n;
+        const int ka = k < 0 ? -k : k;
+        if (ka >= in_len) return mk<T>(0, 0);
+        C a = src[ka], b = src[in_stride + ka];
+        if (k < 0) {
+            a.y = -a.y;
+            b.y = -b.y;
+        }
+        has = true;
+        return mk<T>(a.x - b.y, a.y + b.x);
+    }
+    int t = idx - in_shift;
+    if (t < 0) t += n;
+    if (t >= in_len) return mk<T>(0, 0);
+    C v = src[t];
+    if (hf.n) {
+        const long ar = hf.row0 + row;
+        if (ar >= 1 && t >= 1) {
+            const C mv = hf.base[(hf.n - ar) * in_stride + (hf.n - t)];
+            v.x += mv.x;
+            v.y -= mv.y;
+        }
+    }
+    const T pe = pre_elem ? pre_elem[t] : static_cast<T>(1);
+    v.x *= rs0 * pe;
+    v.y *= rs1 * pe;
+    has = true;
+    return v;
+}
 
 template <typename T, int NT>
 __global__ void __launch_bounds__(NT) fft_rows_kernel(
@@ -172,34 +213,26 @@ __global__ void __launch_bounds__(NT) fft_rows_kernel(
     cx_t<T>* __restrict__ out, long out_stride, int out_len, int out_shift,
     int n, int Q, int sign, FftPlan1D plan, const cx_t<T>* __restrict__ tw, const int* __restrict__ perm,
     const T* __restrict__ pre_elem, const T* __restrict__ pre_row,
-    const T* __restrict__ post_elem, const T* __restrict__ post_row, HermFold<T> hf) {
+    const T* __restrict__ post_elem, const T* __restrict__ post_row, HermFold<T> hf, int io) {
     using C = cx_t<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* s = reinterpret_cast<C*>(smem_raw);
     const long row = blockIdx.y;     // phases of a row are adjacent CTAs (they read the same row)
     const int r = blockIdx.x;
     const int nq = n / Q;
-    const C* src = in + row * in_stride;
-    const T rs = pre_row ? pre_row[row] : static_cast<T>(1);
+    const C* src = in + row * in_stride * (io == kIoPairInv ? 2 : 1);
+    T rs0 = static_cast<T>(1), rs1 = static_cast<T>(1);
+    if (pre_row) {
+        rs0 = pre_row[io == kIoPairFwd ? 2 * row : row];
+        rs1 = pre_row[io == kIoPairFwd ? 2 * row + 1 : row];
+    }
     for (int i = threadIdx.x; i < nq; i += NT) {
         C acc = mk<T>(0, 0);
         for (int j = 0; j < Q; ++j) {
             const int idx = i + j * nq;               // FFT index
-            int t = idx - in_shift;
-            if (t < 0) t += n;
-            if (t < in_len) {
-                C v = src[t];
-                if (hf.n) {
-                    const long ar = hf.row0 + row;
-                    if (ar >= 1 && t >= 1) {
-                        const C mv = hf.base[(hf.n - ar) * in_stride + (hf.n - t)];
-                        v.x += mv.x;
-                        v.y -= mv.y;
-                    }
-                }
-                T sc = rs;
-                if (pre_elem) sc *= pre_elem[t];
-                v = cscale(v, sc);
+            bool has;
+            C v = load_elem<T>(io, idx, n, src, in_stride, in_len, in_shift, row, hf, rs0, rs1, pre_elem, has);
+            if (has) {
                 if (r) {                              // twist w_n^{idx}
                     C w = tw[idx];
                     if (sign > 0) w.y = -w.y;
@@ -220,16 +253,39 @@ __global__ void __launch_bounds__(NT) fft_rows_kernel(
         else             dit_stage<T, 5>(s, nq, Lp, sign, tw, Q, NT);
         Lp *= R;
     }
+    if (io == kIoPairFwd) {
+        // s = Z^ of z = x0 + i x1 (two real rows): X0(k) = (Z(k) + conj Z(-k)) / 2,
+        // X1(k) = (Z(k) - conj Z(-k)) / 2i, written to grid rows 2 row and 2 row + 1
+        C* d0 = out + 2 * row * out_stride;
+        C* d1 = d0 + out_stride;
+        for (int e = threadIdx.x; e < out_len; e += NT) {
+            int k = e + out_shift;
+            if (k >= n) k -= n;
+            if (Q == 2 && (k & 1) != r) continue;
+            const int km = k == 0 ? 0 : n - k;        // same parity as k (n even)
+            const C zk = s[Q == 2 ? (k >> 1) : k], zm = s[Q == 2 ? (km >> 1) : km];
+            const T h = static_cast<T>(0.5);
+            const T pe = post_elem ? post_elem[e] : static_cast<T>(1);
+            d0[e] = mk<T>(h * pe * (zk.x + zm.x), h * pe * (zk.y - zm.y));
+            d1[e] = mk<T>(h * pe * (zk.y + zm.y), h * pe * (zm.x - zk.x));
+        }
+        return;
+    }
     C* dst = out + row * out_stride;
-    const T ps = post_row ? post_row[row] : static_cast<T>(1);
+    T ps0 = static_cast<T>(1), ps1 = static_cast<T>(1);
+    if (post_row) {
+        ps0 = post_row[io == kIoPairInv ? 2 * row : row];
+        ps1 = post_row[io == kIoPairInv ? 2 * row + 1 : row];
+    }
     for (int e = threadIdx.x; e < out_len; e += NT) {
         int k = e + out_shift;
         if (k >= n) k -= n;
         if (Q == 2 && (k & 1) != r) continue;
         C v = s[Q == 2 ? (k >> 1) : k];
-        T sc = ps;
-        if (post_elem) sc *= post_elem[e];
-        dst[e] = cscale(v, sc);
+        const T pe = post_elem ? post_elem[e] : static_cast<T>(1);
+        v.x *= ps0 * pe;
+        v.y *= ps1 * pe;
+        dst[e] = v;
     }
 }
 
@@ -331,10 +387,14 @@ int fft_rows(const cx_t<T>* in, long in_stride, int in_len, int in_shift,
              cx_t<T>* out, long out_stride, int out_len, int out_shift,
              int rows, int n, int sign,
              const T* pre_elem, const T* pre_row, const T* post_elem, const T* post_row,
-             cudaStream_t stream, int herm_n) {
+             cudaStream_t stream, int herm_n, int herm_row0, int io) {
     if (rows <= 0) return SBD_OK;
-    if (herm_n && (rows != herm_n || in_len != herm_n)) {
-        set_error("fft_rows: a Hermitian fold needs a square grid read whole");
+    if (herm_n && (herm_row0 < 0 || herm_row0 + rows > herm_n || in_len != herm_n || io != kIoPlain)) {
+        set_error("fft_rows: a Hermitian fold needs rows inside a square grid read whole");
+        return SBD_EINVAL;
+    }
+    if (io < kIoPlain || io > kIoPairInv) {
+        set_error("fft_rows: unknown io mode");
         return SBD_EINVAL;
     }
     const bool fp64 = sizeof(T) == 8;
@@ -357,21 +417,24 @@ int fft_rows(const cx_t<T>* in, long in_stride, int in_len, int in_shift,
     for (int r0 = 0; r0 < rows; r0 += 65535) {          // grid.y holds at most 65535 rows
         const int nr = std::min(65535, rows - r0);
         const dim3 grid(static_cast<unsigned>(Q), static_cast<unsigned>(nr));
-        const cx_t<T>* ip = in + static_cast<long>(r0) * in_stride;
-        cx_t<T>* op = out + static_cast<long>(r0) * out_stride;
-        const T* prr = pre_row ? pre_row + r0 : nullptr;
-        const T* por = post_row ? post_row + r0 : nullptr;
-        const HermFold<T> hf{in, herm_n, r0};
+        // pair modes: one launch row is two grid rows on the paired side
+        const long in_rows = io == kIoPairInv ? 2 : 1, out_rows = io == kIoPairFwd ? 2 : 1;
+        const cx_t<T>* ip = in + static_cast<long>(r0) * in_stride * in_rows;
+        cx_t<T>* op = out + static_cast<long>(r0) * out_stride * out_rows;
+        const T* prr = pre_row ? pre_row + r0 * (io == kIoPairFwd ? 2 : 1) : nullptr;
+        const T* por = post_row ? post_row + r0 * (io == kIoPairInv ? 2 : 1) : nullptr;
+        const HermFold<T> hf{in - static_cast<long>(herm_row0) * in_stride, herm_n,
+                             static_cast<long>(herm_row0) + r0};
         if (nq > 2048) {
             auto k = fft_rows_kernel<T, 1024>;
             SBD_TRY(raise_smem_limit(k, smem));
             k<<<grid, 1024, smem, stream>>>(ip, in_stride, in_len, in_shift, op, out_stride, out_len, out_shift,
-                                            n, Q, sign, plan, tw, perm, pre_elem, prr, post_elem, por, hf);
+                                            n, Q, sign, plan, tw, perm, pre_elem, prr, post_elem, por, hf, io);
         } else {
             auto k = fft_rows_kernel<T, 256>;
             SBD_TRY(raise_smem_limit(k, smem));
             k<<<grid, 256, smem, stream>>>(ip, in_stride, in_len, in_shift, op, out_stride, out_len, out_shift,
-                                           n, Q, sign, plan, tw, perm, pre_elem, prr, post_elem, por, hf);
+                                           n, Q, sign, plan, tw, perm, pre_elem, prr, post_elem, por, hf, io);
         }
         SBD_LAUNCH_CHECK();
     }
@@ -398,12 +461,14 @@ int fft_rows_tables(const cx_t<T>* in, long in_stride, int in_len, cx_t<T>* out,
             auto k = fft_rows_kernel<T, 1024>;
             SBD_TRY(raise_smem_limit(k, smem));
             k<<<grid, 1024, smem, stream>>>(ip, in_stride, in_len, 0, op, out_stride, out_len, 0, n, 1, sign, plan, tw,
-                                            perm, nullptr, nullptr, nullptr, nullptr, HermFold<T>{nullptr, 0, 0});
+                                            perm, nullptr, nullptr, nullptr, nullptr, HermFold<T>{nullptr, 0, 0},
+                                            kIoPlain);
         } else {
             auto k = fft_rows_kernel<T, 256>;
             SBD_TRY(raise_smem_limit(k, smem));
             k<<<grid, 256, smem, stream>>>(ip, in_stride, in_len, 0, op, out_stride, out_len, 0, n, 1, sign, plan, tw,
-                                           perm, nullptr, nullptr, nullptr, nullptr, HermFold<T>{nullptr, 0, 0});
+                                           perm, nullptr, nullptr, nullptr, nullptr, HermFold<T>{nullptr, 0, 0},
+                                           kIoPlain);
         }
         SBD_LAUNCH_CHECK();
     }
@@ -421,9 +486,11 @@ int transpose(const cx_t<T>* in, long in_stride, long in_batch, cx_t<T>* out, lo
 }
 
 template int fft_rows<float>(const float2*, long, int, int, float2*, long, int, int, int, int, int,
-                             const float*, const float*, const float*, const float*, cudaStream_t, int);
+                             const float*, const float*, const float*, const float*, cudaStream_t, int, int,
+                             int);
 template int fft_rows<double>(const double2*, long, int, int, double2*, long, int, int, int, int, int,
-                              const double*, const double*, const double*, const double*, cudaStream_t, int);
+                              const double*, const double*, const double*, const double*, cudaStream_t, int, int,
+                              int);
 template int fft_rows_tables<float>(const float2*, long, int, float2*, long, int, int, int, int, const float2*,
                                     const int*, cudaStream_t);
 template int fft_rows_tables<double>(const double2*, long, int, double2*, long, int, int, int, int, const double2*,

@@ -30,15 +30,28 @@ int fft_max_length(bool fp64);
 // for e < out_len, t < in_len (input element t sits at FFT position (t + in_shift) mod n,
 // output element e is FFT position (e + out_shift) mod n).  Scale pointers may be null.
 //
-// Hermitian fold (herm_n > 0, which needs rows == in_len == herm_n and in == herm_base):
-// the input is read as in[r][t] + conj(in[herm_n - r][herm_n - t]) (the second term
-// only for r, t >= 1), i.e. the transform of S(eta) + conj(S(-eta)) for a centred grid S.
+// Hermitian fold (herm_n > 0): in points at row herm_row0 of a herm_n x herm_n grid S
+// (in_len == herm_n) and row r of this call is read as S[a][t] + conj(S[herm_n - a]
+// [herm_n - t]) with a = herm_row0 + r (the second term only for a, t >= 1): the
+// transform of S(eta) + conj(S(-eta)) for a centred grid.
+//
+// io modes for real data (two real rows per transform, "packed pair" rows
+// z = x_{2j} + i x_{2j+1}):
+//   kIoPairFwd  input row j is a packed pair (re scaled by pre_row[2j], im by
+//               pre_row[2j+1]); the outputs are the two transforms X_{2j}, X_{2j+1}
+//               (each Hermitian), written to output rows 2j and 2j + 1.  rows = pairs.
+//   kIoPairInv  input rows 2j, 2j + 1 hold frequencies 0..in_len-1 of two Hermitian
+//               spectra (the negative ones are their conjugates; FFT position idx is
+//               frequency idx, or idx - n past n / 2); the output row j is the packed
+//               pair of the two (real) transforms, re scaled by post_row[2j], im by
+//               post_row[2j+1].  in_shift is unused.  rows = pairs.
+enum { kIoPlain = 0, kIoPairFwd = 1, kIoPairInv = 2 };
 template <typename T>
 int fft_rows(const cx_t<T>* in, long in_stride, int in_len, int in_shift,
              cx_t<T>* out, long out_stride, int out_len, int out_shift,
              int rows, int n, int sign,
              const T* pre_elem, const T* pre_row, const T* post_elem, const T* post_row,
-             cudaStream_t stream, int herm_n = 0);
+             cudaStream_t stream, int herm_n = 0, int herm_row0 = 0, int io = kIoPlain);
 
 // Natural-order row transforms of length n (input and output windows start at 0) with
 // caller-provided tables: tw[t] = exp(-2 pi i t / n), perm = the digit reversal of

@@ -249,6 +249,64 @@ __global__ void spmv_kernel(const long long* __restrict__ rowptr, const int* __r
     }
 }
 
+// Internal (spatially sorted) order: fp[i * nrhs + r] = f[r * n + perm[i]].
+template <bool CPLX>
+__global__ void gather_rows_kernel(const void* __restrict__ f, long n, int nrhs, const int* __restrict__ perm,
+                                   void* __restrict__ fp) {
+    const long t = blockIdx.x * static_cast<long>(blockDim.x) + threadIdx.x;
+    if (t >= n * nrhs) return;
+    const long i = t / nrhs;
+    const int r = static_cast<int>(t - i * nrhs);
+    const long src = static_cast<long>(r) * n + perm[i];
+    if (CPLX) static_cast<double2*>(fp)[t] = static_cast<const double2*>(f)[src];
+    else static_cast<double*>(fp)[t] = static_cast<const double*>(f)[src];
+}
+
+// q[r * n + perm[i]] = qp[i * nrhs + r]
+template <bool CPLX>
+__global__ void scatter_rows_kernel(const void* __restrict__ qp, long n, int nrhs, const int* __restrict__ perm,
+                                    void* __restrict__ q) {
+    const long t = blockIdx.x * static_cast<long>(blockDim.x) + threadIdx.x;
+    if (t >= n * nrhs) return;
+    const long i = t / nrhs;
+    const int r = static_cast<int>(t - i * nrhs);
+    const long dst = static_cast<long>(r) * n + perm[i];
+    if (CPLX) static_cast<double2*>(q)[dst] = static_cast<const double2*>(qp)[t];
+    else static_cast<double*>(q)[dst] = static_cast<const double*>(qp)[t];
+}
+
+// qp = D fp with interleaved right-hand sides, one thread per (row, rhs): the threads
+// of a row share its column and value loads and read fp[col * nrhs + 0..nrhs-1]
+// contiguously.  Rows and columns are in the internal order, so the columns of a row
+// are nearby points whose values sit close together.
+template <bool CPLX>
+__global__ void spmv_rhs_kernel(const long long* __restrict__ rowptr, const int* __restrict__ col,
+                                const void* __restrict__ val, long n, int nrhs, const void* __restrict__ fp,
+                                void* __restrict__ qp) {
+    const long t = blockIdx.x * static_cast<long>(blockDim.x) + threadIdx.x;
+    if (t >= n * nrhs) return;
+    const long row = t / nrhs;
+    const int r = static_cast<int>(t - row * nrhs);
+    const long long b = rowptr[row], e = rowptr[row + 1];
+    if (CPLX) {
+        const double2* v = static_cast<const double2*>(val);
+        const double2* x = static_cast<const double2*>(fp);
+        double sr = 0.0, si = 0.0;
+        for (long long j = b; j < e; ++j) {
+            const double2 a = v[j], y = x[static_cast<long>(col[j]) * nrhs + r];
+            sr += a.x * y.x - a.y * y.y;
+            si += a.x * y.y + a.y * y.x;
+        }
+        static_cast<double2*>(qp)[t] = make_double2(sr, si);
+    } else {
+        const double* v = static_cast<const double*>(val);
+        const double* x = static_cast<const double*>(fp);
+        double acc = 0.0;
+        for (long long j = b; j < e; ++j) acc += v[j] * x[static_cast<long>(col[j]) * nrhs + r];
+        static_cast<double*>(qp)[t] = acc;
+    }
+}
+
 // --- exclusive scan of 64-bit integers: per-chunk scan, chunk totals, offsets ------------
 constexpr int kScanT = 1024, kScanPer = 4, kChunk = kScanT * kScanPer;
 
@@ -427,6 +485,40 @@ int near_spmv(const long long* rowptr, const int* col, const void* val, bool cva
     const long threads = n * 32;
     if (cval) spmv_kernel<true><<<nblk(threads), kT, 0, s>>>(rowptr, col, val, n, nrhs, f, q, accumulate);
     else spmv_kernel<false><<<nblk(threads), kT, 0, s>>>(rowptr, col, val, n, nrhs, f, q, accumulate);
+    SBD_LAUNCH_CHECK();
+    return SBD_OK;
+}
+
+int near_gather(const void* f, bool cplx, long n, int nrhs, const int* perm, void* fp, cudaStream_t s) {
+    if (n <= 0) return SBD_OK;
+    const long t = n * nrhs;
+    if (cplx) gather_rows_kernel<true><<<nblk(t), kT, 0, s>>>(f, n, nrhs, perm, fp);
+    else gather_rows_kernel<false><<<nblk(t), kT, 0, s>>>(f, n, nrhs, perm, fp);
+    SBD_LAUNCH_CHECK();
+    return SBD_OK;
+}
+
+int near_scatter(const void* qp, bool cplx, long n, int nrhs, const int* perm, void* q, cudaStream_t s) {
+    if (n <= 0) return SBD_OK;
+    const long t = n * nrhs;
+    if (cplx) scatter_rows_kernel<true><<<nblk(t), kT, 0, s>>>(qp, n, nrhs, perm, q);
+    else scatter_rows_kernel<false><<<nblk(t), kT, 0, s>>>(qp, n, nrhs, perm, q);
+    SBD_LAUNCH_CHECK();
+    return SBD_OK;
+}
+
+int near_spmv_internal(const long long* rowptr, const int* col, const void* val, bool cval, long n, int nrhs,
+                       const void* fp, void* qp, cudaStream_t s) {
+    if (n <= 0) return SBD_OK;
+    if (nrhs == 1) {   // one warp per row (rows of ~10^2 entries), same layout
+        const long threads = n * 32;
+        if (cval) spmv_kernel<true><<<nblk(threads), kT, 0, s>>>(rowptr, col, val, n, 1, fp, qp, false);
+        else spmv_kernel<false><<<nblk(threads), kT, 0, s>>>(rowptr, col, val, n, 1, fp, qp, false);
+    } else {
+        const long t = n * nrhs;
+        if (cval) spmv_rhs_kernel<true><<<nblk(t), kT, 0, s>>>(rowptr, col, val, n, nrhs, fp, qp);
+        else spmv_rhs_kernel<false><<<nblk(t), kT, 0, s>>>(rowptr, col, val, n, nrhs, fp, qp);
+    }
     SBD_LAUNCH_CHECK();
     return SBD_OK;
 }

@@ -35,6 +35,16 @@ int near_build(const double* z, long n, double delta_min, double bx0, double by0
 int near_spmv(const long long* rowptr, const int* col, const void* val, bool complex_vals, long n, int nrhs,
               const void* f, void* q, bool accumulate, cudaStream_t s);
 
+// The near field in the internal point order (the spreading records' tile order, which
+// keeps the columns of a row close together): fp[i * nrhs + r] = f[r * n + perm[i]]
+// (near_gather), qp = D fp with D over internal indices and interleaved right-hand
+// sides (near_spmv_internal), q[r * n + perm[i]] = qp[i * nrhs + r] (near_scatter).
+// Values are float64 (real) or complex128 (cplx).
+int near_gather(const void* f, bool cplx, long n, int nrhs, const int* perm, void* fp, cudaStream_t s);
+int near_spmv_internal(const long long* rowptr, const int* col, const void* val, bool complex_vals, long n,
+                       int nrhs, const void* fp, void* qp, cudaStream_t s);
+int near_scatter(const void* qp, bool cplx, long n, int nrhs, const int* perm, void* q, cudaStream_t s);
+
 // Exclusive scan of n 64-bit counts in place; total returned in *total (host), synchronising s.
 int scan_exclusive_i64(long long* data, long n, long long* total, cudaStream_t s);
 

@@ -80,17 +80,29 @@ template <typename T> struct PointVal {     // spreading values f[perm[i]] (floa
         return mk<T>(static_cast<T>(static_cast<const double*>(f)[j]), static_cast<T>(0));
     }
 };
-template <typename T> struct PointOut {     // interpolation: q[perm[i]] = v + w0 * sumf
+template <typename T> struct PointOut {     // interpolation: q[perm[i]] = v + w0 * sumf (+ add[i])
     void* q;
     const int* perm;
     bool qc;
     double2 w0;
     const double2* sumf;
+    const void* add;      // optional FP64 term per record (internal order): add[i * add_stride + add_off]
+    int add_stride, add_off;
     __device__ __forceinline__ void put(long i, const PointRec<T>&, cx_t<T> v) const {
         const long j = perm[i];
         const double2 sf = *sumf;
-        const double re = static_cast<double>(v.x) + w0.x * sf.x - w0.y * sf.y;
-        const double im = static_cast<double>(v.y) + w0.x * sf.y + w0.y * sf.x;
+        double re = static_cast<double>(v.x) + w0.x * sf.x - w0.y * sf.y;
+        double im = static_cast<double>(v.y) + w0.x * sf.y + w0.y * sf.x;
+        if (add) {
+            const long k = i * add_stride + add_off;
+            if (qc) {
+                const double2 a = static_cast<const double2*>(add)[k];
+                re += a.x;
+                im += a.y;
+            } else {
+                re += static_cast<const double*>(add)[k];
+            }
+        }
         if (qc) static_cast<double2*>(q)[j] = make_double2(re, im);
         else static_cast<double*>(q)[j] = re;
     }
@@ -98,7 +110,11 @@ template <typename T> struct PointOut {     // interpolation: q[perm[i]] = v + w
 
 // --- kernels ----------------------------------------------------------------------------------------
 
-template <typename T, int G, typename Rec, typename Out>
+// Real grid stored as packed row pairs: cell (R, c) is component R & 1 of complex
+// element (R >> 1, c), i.e. float index ((R >> 1) n + c) 2 + (R & 1).
+__device__ __forceinline__ long packed_index(long R, long c, long n) { return ((R >> 1) * n + c) * 2 + (R & 1); }
+
+template <typename T, int G, typename Rec, typename Out, bool PK>
 __global__ void __launch_bounds__(256) gather_tiles_kernel(
     const Rec* __restrict__ rec, const long long* __restrict__ tile_start, int ntx, int n, int P, Window<T> win,
     const cx_t<T>* __restrict__ grid, Out out) {
@@ -114,7 +130,10 @@ __global__ void __launch_bounds__(256) gather_tiles_kernel(
     for (int idx = threadIdx.x; idx < W * W; idx += blockDim.x) {
         const int r = idx / W, c = idx - r * W;
         C v = mk<T>(0, 0);
-        if (r < rows && c < cols) v = grid[static_cast<long>(ox + r) * n + oy + c];
+        if (r < rows && c < cols) {
+            if (PK) v = mk<T>(reinterpret_cast<const T*>(grid)[packed_index(ox + r, oy + c, n)], static_cast<T>(0));
+            else v = grid[static_cast<long>(ox + r) * n + oy + c];
+        }
         s[idx] = v;
     }
     __syncthreads();
@@ -166,7 +185,7 @@ __device__ __forceinline__ void shared_add_f2(float2* addr, float a, float b) {
     }
 }
 
-template <typename T, int G, typename Rec, typename Val>
+template <typename T, int G, typename Rec, typename Val, bool PK>
 __global__ void __launch_bounds__(256) scatter_tiles_kernel(
     const Rec* __restrict__ rec, const long long* __restrict__ tile_start, int ntx, int n, int P, Window<T> win,
     Val val, cx_t<T>* __restrict__ grid) {
@@ -215,7 +234,10 @@ __global__ void __launch_bounds__(256) scatter_tiles_kernel(
     const int rows = min(kNodeTile, n - ox), cols = min(kNodeTile, n - oy);
     for (int idx = threadIdx.x; idx < kNodeTile * kNodeTile; idx += blockDim.x) {
         const int r = idx / kNodeTile, c = idx - r * kNodeTile;
-        if (r < rows && c < cols) grid[static_cast<long>(ox + r) * n + oy + c] = mk<T>(acc[2 * idx], acc[2 * idx + 1]);
+        if (r < rows && c < cols) {
+            if (PK) reinterpret_cast<T*>(grid)[packed_index(ox + r, oy + c, n)] = acc[2 * idx];
+            else grid[static_cast<long>(ox + r) * n + oy + c] = mk<T>(acc[2 * idx], acc[2 * idx + 1]);
+        }
     }
 }
 
@@ -370,7 +392,7 @@ Window<T> make_window(int kind, double beta, int P) {
     return Window<T>{kind, static_cast<T>(beta), static_cast<T>(2.0 / P)};
 }
 
-template <typename T, typename Rec, typename Out>
+template <typename T, typename Rec, typename Out, bool PK = false>
 int launch_gather(const Rec* rec, const long long* tile_start, int n, int P, int kind, double beta,
                   const cx_t<T>* grid, Out out, cudaStream_t s) {
     const Window<T> win = make_window<T>(kind, beta, P);
@@ -379,11 +401,11 @@ int launch_gather(const Rec* rec, const long long* tile_start, int n, int P, int
     const size_t smem = W * W * sizeof(cx_t<T>);
     const unsigned nt = static_cast<unsigned>(ntx) * ntx;
     if (P <= 16) {
-        auto k = gather_tiles_kernel<T, 16, Rec, Out>;
+        auto k = gather_tiles_kernel<T, 16, Rec, Out, PK>;
         SBD_TRY(raise_smem_limit(k, smem));
         k<<<nt, 256, smem, s>>>(rec, tile_start, ntx, n, P, win, grid, out);
     } else {
-        auto k = gather_tiles_kernel<T, 32, Rec, Out>;
+        auto k = gather_tiles_kernel<T, 32, Rec, Out, PK>;
         SBD_TRY(raise_smem_limit(k, smem));
         k<<<nt, 256, smem, s>>>(rec, tile_start, ntx, n, P, win, grid, out);
     }
@@ -391,7 +413,7 @@ int launch_gather(const Rec* rec, const long long* tile_start, int n, int P, int
     return SBD_OK;
 }
 
-template <typename T, typename Rec, typename Val>
+template <typename T, typename Rec, typename Val, bool PK = false>
 int launch_scatter(const Rec* rec, const long long* tile_start, int n, int P, int kind, double beta, Val val,
                    cx_t<T>* grid, cudaStream_t s) {
     const Window<T> win = make_window<T>(kind, beta, P);
@@ -399,11 +421,11 @@ int launch_scatter(const Rec* rec, const long long* tile_start, int n, int P, in
     const size_t smem = 2 * sizeof(T) * kNodeTile * kNodeTile;
     const unsigned nt = static_cast<unsigned>(ntx) * ntx;
     if (P <= 16) {
-        auto k = scatter_tiles_kernel<T, 16, Rec, Val>;
+        auto k = scatter_tiles_kernel<T, 16, Rec, Val, PK>;
         SBD_TRY(raise_smem_limit(k, smem));
         k<<<nt, 256, smem, s>>>(rec, tile_start, ntx, n, P, win, val, grid);
     } else {
-        auto k = scatter_tiles_kernel<T, 32, Rec, Val>;
+        auto k = scatter_tiles_kernel<T, 32, Rec, Val, PK>;
         SBD_TRY(raise_smem_limit(k, smem));
         k<<<nt, 256, smem, s>>>(rec, tile_start, ntx, n, P, win, val, grid);
     }
@@ -492,16 +514,49 @@ int node_step_tiled(const NodeRec<T>* nodes, const long long* tile_start, const 
 
 template <typename T>
 int spread_tiled(const PointRec<T>* pts, const int* perm, const long long* tile_start, const FarGeom& g,
-                 const void* f, bool f_complex, cx_t<T>* grid, cudaStream_t s) {
+                 const void* f, bool f_complex, cx_t<T>* grid, cudaStream_t s, bool packed) {
+    if (packed) {
+        if (f_complex || (g.m & 1)) {
+            set_error("spread: a packed real grid needs real values and an even side");
+            return SBD_EINVAL;
+        }
+        return launch_scatter<T, PointRec<T>, PointVal<T>, true>(pts, tile_start, g.m, g.Ps, kWinGauss, g.beta_s,
+                                                                  PointVal<T>{f, perm, false}, grid, s);
+    }
     return launch_scatter<T>(pts, tile_start, g.m, g.Ps, kWinGauss, g.beta_s, PointVal<T>{f, perm, f_complex}, grid,
                              s);
 }
 
 template <typename T>
 int interp_tiled(const PointRec<T>* pts, const int* perm, const long long* tile_start, const FarGeom& g,
-                 const cx_t<T>* grid, double2 w0, const double2* sumf, void* q, bool q_complex, cudaStream_t s) {
-    return launch_gather<T>(pts, tile_start, g.m, g.Ps, kWinGauss, g.beta_s, grid,
-                            PointOut<T>{q, perm, q_complex, w0, sumf}, s);
+                 const cx_t<T>* grid, double2 w0, const double2* sumf, void* q, bool q_complex, cudaStream_t s,
+                 bool packed, const void* add, int add_stride, int add_off) {
+    const PointOut<T> out{q, perm, q_complex, w0, sumf, add, add_stride, add_off};
+    if (packed) {
+        if (q_complex || (g.m & 1)) {
+            set_error("interp: a packed real grid needs real output and an even side");
+            return SBD_EINVAL;
+        }
+        return launch_gather<T, PointRec<T>, PointOut<T>, true>(pts, tile_start, g.m, g.Ps, kWinGauss, g.beta_s,
+                                                                grid, out, s);
+    }
+    return launch_gather<T>(pts, tile_start, g.m, g.Ps, kWinGauss, g.beta_s, grid, out, s);
+}
+
+template <typename T>
+__global__ void fill_kernel(cx_t<T>* __restrict__ x, long n, T re, T im) {
+    for (long i = blockIdx.x * static_cast<long>(blockDim.x) + threadIdx.x; i < n;
+         i += static_cast<long>(gridDim.x) * blockDim.x)
+        x[i] = mk<T>(re, im);
+}
+
+template <typename T>
+int fill_grid(cx_t<T>* x, long n, T re, T im, cudaStream_t s) {
+    if (n <= 0) return SBD_OK;
+    const unsigned nb = static_cast<unsigned>(std::min<long>((n + 255) / 256, 152L * 64));
+    fill_kernel<T><<<nb, 256, 0, s>>>(x, n, re, im);
+    SBD_LAUNCH_CHECK();
+    return SBD_OK;
 }
 
 #define SBD_NODE_INST(T)                                                                                     \
@@ -512,12 +567,14 @@ int interp_tiled(const PointRec<T>* pts, const int* perm, const long long* tile_
     template int node_step_tiled<T>(const NodeRec<T>*, const long long*, const FarGeom&, const cx_t<T>*,     \
                                     cx_t<T>*, cx_t<T>*, cudaStream_t);                                       \
     template size_t node_fused_smem<T>(int);                                                                 \
+    template int fill_grid<T>(cx_t<T>*, long, T, T, cudaStream_t);                                          \
     template int node_step_fused<T>(const NodeRec<T>*, const long long*, const FarGeom&, const cx_t<T>*,     \
                                     cx_t<T>*, const NodeTuning&, cudaStream_t);                              \
     template int spread_tiled<T>(const PointRec<T>*, const int*, const long long*, const FarGeom&,           \
-                                 const void*, bool, cx_t<T>*, cudaStream_t);                                 \
+                                 const void*, bool, cx_t<T>*, cudaStream_t, bool);                           \
     template int interp_tiled<T>(const PointRec<T>*, const int*, const long long*, const FarGeom&,           \
-                                 const cx_t<T>*, double2, const double2*, void*, bool, cudaStream_t);
+                                 const cx_t<T>*, double2, const double2*, void*, bool, cudaStream_t, bool,   \
+                                 const void*, int, int);
 SBD_NODE_INST(float)
 SBD_NODE_INST(double)
 

@@ -28,6 +28,10 @@ struct NodeTuning {
     int sched = 0;
 };
 
+// x[i] = re + i im for i < n.
+template <typename T>
+int fill_grid(cx_t<T>* x, long n, T re, T im, cudaStream_t s);
+
 // The same in one kernel per tile: gather, weight and scatter into a shared accumulator,
 // whose overlap band is added atomically into kout (cleared here).
 template <typename T>
@@ -37,13 +41,17 @@ int node_step_fused(const NodeRec<T>* nodes, const long long* tile_start, const 
                     const cx_t<T>* kin, cx_t<T>* kout, const NodeTuning& t, cudaStream_t s);
 
 // grid (m x m, fully written) = spreading of f (float64 or complex128, original order).
+// packed: real f into a real grid stored as packed row pairs (m / 2 x m complex,
+// cell (R, c) = component R & 1 of element (R >> 1, c)).
 template <typename T>
 int spread_tiled(const PointRec<T>* pts, const int* perm, const long long* tile_start, const FarGeom& g,
-                 const void* f, bool f_complex, cx_t<T>* grid, cudaStream_t s);
+                 const void* f, bool f_complex, cx_t<T>* grid, cudaStream_t s, bool packed = false);
 
-// q[perm[i]] = interpolation of grid at point i + w0 * sumf[0] (float64 or complex128 out).
+// q[perm[i]] = interpolation of grid at point i + w0 * sumf[0] (float64 or complex128 out)
+// + add[i * add_stride + add_off] when add is given (same type as q, record order).
 template <typename T>
 int interp_tiled(const PointRec<T>* pts, const int* perm, const long long* tile_start, const FarGeom& g,
-                 const cx_t<T>* grid, double2 w0, const double2* sumf, void* q, bool q_complex, cudaStream_t s);
+                 const cx_t<T>* grid, double2 w0, const double2* sumf, void* q, bool q_complex, cudaStream_t s,
+                 bool packed = false, const void* add = nullptr, int add_stride = 1, int add_off = 0);
 
 }  // namespace sbd
