@@ -185,16 +185,21 @@ __device__ __forceinline__ void shared_add_f2(float2* addr, float a, float b) {
     }
 }
 
-template <typename T, int G, typename Rec, typename Val, bool PK>
+// RV: the values are real (Laplace spreading): one accumulator plane and one atomic per
+// cell; otherwise re and im interleaved, one atomicAdd each (on this GPU a shared-memory
+// float atomicAdd is a compare-and-swap loop; two of them measured faster than one
+// 64-bit compare-and-swap of the pair under contention).
+template <typename T, int G, typename Rec, typename Val, bool PK, bool RV>
 __global__ void __launch_bounds__(256) scatter_tiles_kernel(
     const Rec* __restrict__ rec, const long long* __restrict__ tile_start, int ntx, int n, int P, Window<T> win,
     Val val, cx_t<T>* __restrict__ grid) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* acc = reinterpret_cast<T*>(smem_raw);          // [kNodeTile][kNodeTile][2]
+    T* acc = reinterpret_cast<T*>(smem_raw);          // [kNodeTile][kNodeTile][RV ? 1 : 2]
+    constexpr int kC = RV ? 1 : 2;
     const int tile = blockIdx.x;
     const int tx = tile / ntx, ty = tile % ntx;
     const int ox = tx * kNodeTile, oy = ty * kNodeTile;
-    for (int idx = threadIdx.x; idx < 2 * kNodeTile * kNodeTile; idx += blockDim.x) acc[idx] = 0;
+    for (int idx = threadIdx.x; idx < kC * kNodeTile * kNodeTile; idx += blockDim.x) acc[idx] = 0;
     __syncthreads();
     const int lane = threadIdx.x & 31;
     const int sub = lane % G;
@@ -218,13 +223,9 @@ __global__ void __launch_bounds__(256) scatter_tiles_kernel(
                     const T w = __shfl_sync(gmask, wx, a, G);
                     const int r = rx + a;
                     if (col_ok && r >= 0 && r < kNodeTile) {
-                        T* cell = acc + 2 * (r * kNodeTile + c);
-                        if constexpr (sizeof(T) == 4) {
-                            shared_add_f2(reinterpret_cast<float2*>(cell), gr * w, gi * w);
-                        } else {
-                            atomicAdd(cell, gr * w);
-                            atomicAdd(cell + 1, gi * w);
-                        }
+                        T* cell = acc + kC * (r * kNodeTile + c);
+                        atomicAdd(cell, gr * w);
+                        if (!RV) atomicAdd(cell + 1, gi * w);
                     }
                 }
             }
@@ -235,8 +236,8 @@ __global__ void __launch_bounds__(256) scatter_tiles_kernel(
     for (int idx = threadIdx.x; idx < kNodeTile * kNodeTile; idx += blockDim.x) {
         const int r = idx / kNodeTile, c = idx - r * kNodeTile;
         if (r < rows && c < cols) {
-            if (PK) reinterpret_cast<T*>(grid)[packed_index(ox + r, oy + c, n)] = acc[2 * idx];
-            else grid[static_cast<long>(ox + r) * n + oy + c] = mk<T>(acc[2 * idx], acc[2 * idx + 1]);
+            if (PK) reinterpret_cast<T*>(grid)[packed_index(ox + r, oy + c, n)] = acc[kC * idx];
+            else grid[static_cast<long>(ox + r) * n + oy + c] = mk<T>(acc[kC * idx], RV ? 0 : acc[kC * idx + 1]);
         }
     }
 }
@@ -413,19 +414,19 @@ int launch_gather(const Rec* rec, const long long* tile_start, int n, int P, int
     return SBD_OK;
 }
 
-template <typename T, typename Rec, typename Val, bool PK = false>
+template <typename T, typename Rec, typename Val, bool PK = false, bool RV = false>
 int launch_scatter(const Rec* rec, const long long* tile_start, int n, int P, int kind, double beta, Val val,
                    cx_t<T>* grid, cudaStream_t s) {
     const Window<T> win = make_window<T>(kind, beta, P);
     const int ntx = tiles_per_side(n);
-    const size_t smem = 2 * sizeof(T) * kNodeTile * kNodeTile;
+    const size_t smem = (RV ? 1 : 2) * sizeof(T) * kNodeTile * kNodeTile;
     const unsigned nt = static_cast<unsigned>(ntx) * ntx;
     if (P <= 16) {
-        auto k = scatter_tiles_kernel<T, 16, Rec, Val, PK>;
+        auto k = scatter_tiles_kernel<T, 16, Rec, Val, PK, RV>;
         SBD_TRY(raise_smem_limit(k, smem));
         k<<<nt, 256, smem, s>>>(rec, tile_start, ntx, n, P, win, val, grid);
     } else {
-        auto k = scatter_tiles_kernel<T, 32, Rec, Val, PK>;
+        auto k = scatter_tiles_kernel<T, 32, Rec, Val, PK, RV>;
         SBD_TRY(raise_smem_limit(k, smem));
         k<<<nt, 256, smem, s>>>(rec, tile_start, ntx, n, P, win, val, grid);
     }
@@ -520,8 +521,9 @@ int spread_tiled(const PointRec<T>* pts, const int* perm, const long long* tile_
             set_error("spread: a packed real grid needs real values and an even side");
             return SBD_EINVAL;
         }
-        return launch_scatter<T, PointRec<T>, PointVal<T>, true>(pts, tile_start, g.m, g.Ps, kWinGauss, g.beta_s,
-                                                                  PointVal<T>{f, perm, false}, grid, s);
+        return launch_scatter<T, PointRec<T>, PointVal<T>, true, true>(pts, tile_start, g.m, g.Ps, kWinGauss,
+                                                                        g.beta_s, PointVal<T>{f, perm, false}, grid,
+                                                                        s);
     }
     return launch_scatter<T>(pts, tile_start, g.m, g.Ps, kWinGauss, g.beta_s, PointVal<T>{f, perm, f_complex}, grid,
                              s);
