@@ -207,6 +207,22 @@ def cpu_baseline(z, f, targets_idx, kind="laplace", kappa=0.0):
                       f"sources x {nrhs} rhs in {dt:.2f} s; value = pair rate / N (extrapolated to a full matvec)"}, q
 
 
+def max_over_ranks(ms, world, device):
+    """The slowest rank's time (the whole job finishes when it does); ms on one rank."""
+    if world <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank, world, ms):
+    """Whole-job throughput (Gpts/s) of `world` replicas, each doing units_per_rank in ms."""
+    return units_per_rank * world / (ms * 1e-3) / 1e9
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
@@ -299,12 +315,8 @@ def main():
     e1.record(stream)
     barrier()
     clk = clocks.stop()
-    ms = e0.elapsed_time(e1) / args.steps
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = args.n * nrhs * world / (ms * 1e-3) / 1e9
+    ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, world, "cuda")
+    value = job_rate(args.n * nrhs, world, ms)
 
     # per-step device times on the same stream (library events), for the roofline
     S.sbd_profile(plan, True)
@@ -339,13 +351,9 @@ def main():
         qh.copy_(qt, non_blocking=True)
     e1.record(stream)
     barrier()
-    ms_e2e = e0.elapsed_time(e1) / args.steps
-    if world > 1:
-        t = torch.tensor([ms_e2e], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_e2e = float(t.item())
+    ms_e2e = max_over_ranks(e0.elapsed_time(e1) / args.steps, world, "cuda")
     io_bytes = esz * args.n * nrhs
-    e2e = {"value": args.n * nrhs * world / (ms_e2e * 1e-3) / 1e9, "unit": UNIT,
+    e2e = {"value": job_rate(args.n * nrhs, world, ms_e2e), "unit": UNIT,
            "h2d_bytes_per_step": io_bytes, "d2h_bytes_per_step": io_bytes}
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

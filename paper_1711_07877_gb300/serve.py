@@ -241,8 +241,11 @@ def run_poisson(requests: list[Request], mean_gap_s: float, seed: int = 0, **ser
     t = 0.0
     for r in requests:
         t += rng.exponential(mean_gap_s)
-        while srv.now() < t:
-            time.sleep(min(0.001, t - srv.now()))
+        while True:
+            dt = t - srv.now()
+            if dt <= 0:
+                break
+            time.sleep(min(0.001, dt))
         r.arrival = 0.0
         srv.submit(r)
     srv.drain(requests)
