@@ -214,18 +214,20 @@ int sbd_fft2(const void* in, void* out, int32_t n0, int32_t n1, int32_t sign, in
  * Autotuning of the node step (no counterpart in the paper).  The fused node kernel
  * has variants that compute the same sums: acc 0 adds re and im into two float planes
  * (one shared-memory atomic each), acc 1 (FP32 form only) into one float2 plane with
- * one 64-bit compare-and-swap; sched 0 deals the records of a tile to the lane groups
- * in turn, sched 1 gives each group a contiguous run.  Results agree to rounding.
+ * one 64-bit compare-and-swap, acc 2 (FP32 form only) into two int64 fixed-point
+ * planes with integer atomics (quantum 2^-50 of a per-tile bound on any contribution);
+ * sched 0 deals the records of a tile to the lane groups in turn, sched 1 gives each
+ * group a contiguous run.  Results agree to FP32 rounding.
  *   sbd_tune       times every applicable variant on the plan's own records (reps
  *                  launches each, after one warm-up, CUDA events on cuda_stream; the
  *                  frequency workspace is first filled with a constant non-zero value,
  *                  so that concurrent adds to a cell contend as with real data) and
  *                  keeps the fastest.
- *                  ms (host, 4 entries, may be NULL): mean ms per launch of variant
+ *                  ms (host, 6 entries, may be NULL): mean ms per launch of variant
  *                  acc * 2 + sched, -1 where not applicable.  Blocks until done.
  *   sbd_set_tuning picks a variant by hand.
- * SBD_EINVAL for a null plan, reps < 1, or acc / sched outside {0, 1} (acc 1 needs the
- * FP32 form).  Plans whose node step is the two-kernel fallback ignore the variant.
+ * SBD_EINVAL for a null plan, reps < 1, acc outside {0, 1, 2} or sched outside {0, 1}
+ * (acc 1 and 2 need the FP32 form).  Plans whose node step is the two-kernel fallback ignore the variant.
  * ------------------------------------------------------------------------------- */
 int sbd_tune(sbd_plan_t plan, int32_t reps, double* ms, void* cuda_stream);
 int sbd_set_tuning(sbd_plan_t plan, int32_t acc, int32_t sched);

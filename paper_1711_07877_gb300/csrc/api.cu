@@ -238,6 +238,11 @@ int build_far(sbd_plan_s* p, cudaStream_t s) {
         om[c] = mk<T>(static_cast<T>(w.real()), static_cast<T>(w.imag()));
         cs[c] = static_cast<T>(std::sqrt(np.circle_factor[c]));
     }
+    {
+        double omax = 0.0;
+        for (const auto& w : om) omax = std::max(omax, std::max(std::fabs(double(w.x)), std::fabs(double(w.y))));
+        p->tuning.wbound = static_cast<float>(omax * np.Pk * np.Pk);
+    }
     if ((rc = upload(p, reinterpret_cast<cx_t<T>**>(&p->omega_c), om, s))) return rc;
     if ((rc = upload(p, reinterpret_cast<T**>(&p->cscale_c), cs, s))) return rc;
     NodeRec<T>* canon = nullptr;
@@ -781,7 +786,7 @@ int sbd_plan_info(sbd_plan_t p, sbd_plan_stats* o) {
 }
 
 int sbd_set_tuning(sbd_plan_t p, int32_t acc, int32_t sched) {
-    if (!p || acc < 0 || acc > 1 || sched < 0 || sched > 1 || (acc == 1 && p->form != SBD_FORM_FP32)) {
+    if (!p || acc < 0 || acc > 2 || sched < 0 || sched > 1 || (acc >= 1 && p->form != SBD_FORM_FP32)) {
         set_error("sbd_set_tuning: invalid plan or variant");
         return SBD_EINVAL;
     }
@@ -796,7 +801,7 @@ int sbd_tune(sbd_plan_t p, int32_t reps, double* ms, void* cuda_stream) {
         return SBD_EINVAL;
     }
     if (ms)
-        for (int v = 0; v < 4; ++v) ms[v] = -1.0;
+        for (int v = 0; v < 6; ++v) ms[v] = -1.0;
     if (!p->node_fused) return SBD_OK;
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     // non-zero input: with zeros every compare-and-swap would succeed at once, which
@@ -811,9 +816,11 @@ int sbd_tune(sbd_plan_t p, int32_t reps, double* ms, void* cuda_stream) {
     double best = 1e300;
     NodeTuning pick = p->tuning;
     int rc = SBD_OK;
-    for (int acc = 0; acc <= (p->form == SBD_FORM_FP32 ? 1 : 0) && !rc; ++acc) {
+    const bool fp32 = p->form == SBD_FORM_FP32;
+    for (int acc = 0; acc <= (fp32 ? 2 : 0) && !rc; ++acc) {
+        if (acc == 2 && node_fused_smem<float>(p->np.Pk, 2) > 227 * 1024) continue;
         for (int sched = 0; sched <= 1 && !rc; ++sched) {
-            const NodeTuning t{acc, sched};
+            const NodeTuning t{acc, sched, p->tuning.wbound};
             auto step = [&]() {
                 return p->form == SBD_FORM_FP32
                            ? node_step_fused<float>(static_cast<const NodeRec<float>*>(p->nodes), p->node_tile_start,

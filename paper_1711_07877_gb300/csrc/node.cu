@@ -257,23 +257,34 @@ __global__ void __launch_bounds__(256) scatter_tiles_kernel(
 // 64-bit compare-and-swap; SCHED = 0 deals the tile's records to the lane groups in
 // turn, SCHED = 1 gives each group one contiguous run of records (the groups of a warp
 // then work on records far apart in the sorted order, which collide less).
+//
+// ACC = 2 (FP32 only): fixed-point accumulation in two int64 planes with native integer
+// atomics.  Every contribution g w_a w_b is at most max|K tile| max|omega'| P^2 =: B in
+// each component (window values <= 1), so scaling by 2^e with B 2^e <= 2^50 leaves room
+// for 2^13 contributions of the largest possible size per cell; the quantum is 2^-50 B,
+// far below FP32 rounding.  wbound = max|omega'| P^2.
 template <typename T, int G, int NT, int ACC, int SCHED>
 __global__ void __launch_bounds__(NT) node_fused_kernel(
     const NodeRec<T>* __restrict__ rec, const long long* __restrict__ tile_start, int ntx, int n, int P, int Ws,
-    Window<T> win, const cx_t<T>* __restrict__ kin, cx_t<T>* __restrict__ kout) {
+    Window<T> win, const cx_t<T>* __restrict__ kin, cx_t<T>* __restrict__ kout, float wbound) {
     using C = cx_t<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ float red[NT / 32];
     const int tile = blockIdx.x;
     const long long b0 = tile_start[tile], b1 = tile_start[tile + 1];
     if (b0 == b1) return;
     const int W = kNodeTile + P - 1;
     constexpr bool kF2 = sizeof(T) == 4 && ACC == 1;
+    constexpr bool kI64 = sizeof(T) == 4 && ACC == 2;
     C* s = reinterpret_cast<C*>(smem_raw);
     T* acc_re = reinterpret_cast<T*>(s + W * Ws);
     T* acc_im = acc_re + W * Ws;
     float2* acc2 = reinterpret_cast<float2*>(s + W * Ws);
+    unsigned long long* acc64_re = reinterpret_cast<unsigned long long*>(s + W * Ws);
+    unsigned long long* acc64_im = acc64_re + W * Ws;
     const int ox = (tile / ntx) * kNodeTile, oy = (tile % ntx) * kNodeTile;
     const int rows = min(W, n - ox), cols = min(W, n - oy);
+    float kmax = 0.f;
     for (int idx = threadIdx.x; idx < W * W; idx += blockDim.x) {
         const int r = idx / W, c = idx - r * W;
         C v = mk<T>(0, 0);
@@ -281,10 +292,32 @@ __global__ void __launch_bounds__(NT) node_fused_kernel(
         s[r * Ws + c] = v;
         if constexpr (kF2) {
             acc2[r * Ws + c] = make_float2(0.f, 0.f);
+        } else if constexpr (kI64) {
+            acc64_re[r * Ws + c] = 0ull;
+            acc64_im[r * Ws + c] = 0ull;
+            kmax = fmaxf(kmax, fmaxf(fabsf(static_cast<float>(v.x)), fabsf(static_cast<float>(v.y))));
         } else {
             acc_re[r * Ws + c] = 0;
             acc_im[r * Ws + c] = 0;
         }
+    }
+    float up = 1.f;
+    double down = 1.0;
+    if constexpr (kI64) {
+        for (int o = 16; o > 0; o >>= 1) kmax = fmaxf(kmax, __shfl_xor_sync(0xffffffffu, kmax, o));
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = kmax;
+        __syncthreads();
+        kmax = 0.f;
+        for (int w = 0; w < NT / 32; ++w) kmax = fmaxf(kmax, red[w]);
+        const float B = kmax * wbound;
+        int e = 0;
+        if (B > 0.f) {
+            int ex;
+            frexpf(B, &ex);                      // B < 2^ex
+            e = min(120, max(-120, 50 - ex));
+        }
+        up = ldexpf(1.f, e);
+        down = ldexp(1.0, -e);
     }
     __syncthreads();
     const int lane = threadIdx.x & 31;
@@ -342,6 +375,11 @@ __global__ void __launch_bounds__(NT) node_fused_kernel(
                 if (sub < P) {
                     if constexpr (kF2) {
                         shared_add_f2(acc2 + base + a * Ws, gr * w, gi * w);
+                    } else if constexpr (kI64) {
+                        atomicAdd(acc64_re + base + a * Ws,
+                                  static_cast<unsigned long long>(__float2ll_rn(gr * w * up)));
+                        atomicAdd(acc64_im + base + a * Ws,
+                                  static_cast<unsigned long long>(__float2ll_rn(gi * w * up)));
                     } else {
                         atomicAdd(acc_re + base + a * Ws, gr * w);
                         atomicAdd(acc_im + base + a * Ws, gi * w);
@@ -359,6 +397,9 @@ __global__ void __launch_bounds__(NT) node_fused_kernel(
             const float2 v = acc2[r * Ws + c];
             vr = v.x;
             vi = v.y;
+        } else if constexpr (kI64) {
+            vr = static_cast<T>(static_cast<double>(static_cast<long long>(acc64_re[r * Ws + c])) * down);
+            vi = static_cast<T>(static_cast<double>(static_cast<long long>(acc64_im[r * Ws + c])) * down);
         } else {
             vr = acc_re[r * Ws + c];
             vi = acc_im[r * Ws + c];
@@ -461,32 +502,41 @@ int tile_sort(const Rec* in, long n_rec, int n, Rec* sorted, int* perm, long lon
 }
 
 template <typename T>
-size_t node_fused_smem(int Pk) {
+size_t node_fused_smem(int Pk, int acc) {
     const int W = kNodeTile + Pk - 1;
     const int Ws = fused_stride(W, fused_p8(Pk));
-    return static_cast<size_t>(W) * Ws * (sizeof(cx_t<T>) + 2 * sizeof(T));
+    const size_t accb = acc == 2 ? 2 * sizeof(unsigned long long) : 2 * sizeof(T);
+    return static_cast<size_t>(W) * Ws * (sizeof(cx_t<T>) + accb);
 }
 
 template <typename T, int G, int ACC, int SCHED>
 int launch_fused(const NodeRec<T>* nodes, const long long* tile_start, unsigned nt, int ntx, const FarGeom& g,
-                 int Ws, size_t smem, const Window<T>& win, const cx_t<T>* kin, cx_t<T>* kout, cudaStream_t s) {
-    auto k = node_fused_kernel<T, G, kNodeThreads, ACC, SCHED>;
+                 int Ws, const Window<T>& win, const cx_t<T>* kin, cx_t<T>* kout, float wbound, cudaStream_t s) {
+    // the int64 planes leave room for one CTA per SM: twice the threads keep the warps
+    constexpr int NT = ACC == 2 ? 2 * kNodeThreads : kNodeThreads;
+    const size_t smem = node_fused_smem<T>(g.Pk, ACC);
+    auto k = node_fused_kernel<T, G, NT, ACC, SCHED>;
     SBD_TRY(raise_smem_limit(k, smem));
-    k<<<nt, kNodeThreads, smem, s>>>(nodes, tile_start, ntx, g.nk, g.Pk, Ws, win, kin, kout);
+    k<<<nt, NT, smem, s>>>(nodes, tile_start, ntx, g.nk, g.Pk, Ws, win, kin, kout, wbound);
     SBD_LAUNCH_CHECK();
     return SBD_OK;
 }
 
 template <typename T, int G>
 int launch_fused_g(const NodeRec<T>* nodes, const long long* tile_start, unsigned nt, int ntx, const FarGeom& g,
-                   int Ws, size_t smem, const Window<T>& win, const cx_t<T>* kin, cx_t<T>* kout,
-                   const NodeTuning& t, cudaStream_t s) {
+                   int Ws, const Window<T>& win, const cx_t<T>* kin, cx_t<T>* kout, const NodeTuning& t,
+                   cudaStream_t s) {
+    const float wb = t.wbound;
     if (sizeof(T) == 4 && t.acc == 1) {
-        return t.sched ? launch_fused<T, G, 1, 1>(nodes, tile_start, nt, ntx, g, Ws, smem, win, kin, kout, s)
-                       : launch_fused<T, G, 1, 0>(nodes, tile_start, nt, ntx, g, Ws, smem, win, kin, kout, s);
+        return t.sched ? launch_fused<T, G, 1, 1>(nodes, tile_start, nt, ntx, g, Ws, win, kin, kout, wb, s)
+                       : launch_fused<T, G, 1, 0>(nodes, tile_start, nt, ntx, g, Ws, win, kin, kout, wb, s);
     }
-    return t.sched ? launch_fused<T, G, 0, 1>(nodes, tile_start, nt, ntx, g, Ws, smem, win, kin, kout, s)
-                   : launch_fused<T, G, 0, 0>(nodes, tile_start, nt, ntx, g, Ws, smem, win, kin, kout, s);
+    if (sizeof(T) == 4 && t.acc == 2) {
+        return t.sched ? launch_fused<T, G, 2, 1>(nodes, tile_start, nt, ntx, g, Ws, win, kin, kout, wb, s)
+                       : launch_fused<T, G, 2, 0>(nodes, tile_start, nt, ntx, g, Ws, win, kin, kout, wb, s);
+    }
+    return t.sched ? launch_fused<T, G, 0, 1>(nodes, tile_start, nt, ntx, g, Ws, win, kin, kout, wb, s)
+                   : launch_fused<T, G, 0, 0>(nodes, tile_start, nt, ntx, g, Ws, win, kin, kout, wb, s);
 }
 
 template <typename T>
@@ -498,11 +548,10 @@ int node_step_fused(const NodeRec<T>* nodes, const long long* tile_start, const 
     const int W = kNodeTile + g.Pk - 1;
     const int P8 = fused_p8(g.Pk);
     const int Ws = fused_stride(W, P8);
-    const size_t smem = node_fused_smem<T>(g.Pk);
     const Window<T> win = make_window<T>(g.kwin, g.beta_k, g.Pk);
-    if (P8 == 8) return launch_fused_g<T, 8>(nodes, tile_start, nt, ntx, g, Ws, smem, win, kin, kout, t, s);
-    if (P8 == 16) return launch_fused_g<T, 16>(nodes, tile_start, nt, ntx, g, Ws, smem, win, kin, kout, t, s);
-    return launch_fused_g<T, 32>(nodes, tile_start, nt, ntx, g, Ws, smem, win, kin, kout, t, s);
+    if (P8 == 8) return launch_fused_g<T, 8>(nodes, tile_start, nt, ntx, g, Ws, win, kin, kout, t, s);
+    if (P8 == 16) return launch_fused_g<T, 16>(nodes, tile_start, nt, ntx, g, Ws, win, kin, kout, t, s);
+    return launch_fused_g<T, 32>(nodes, tile_start, nt, ntx, g, Ws, win, kin, kout, t, s);
 }
 
 template <typename T>
@@ -568,7 +617,7 @@ int fill_grid(cx_t<T>* x, long n, T re, T im, cudaStream_t s) {
                                         cudaStream_t);                                                       \
     template int node_step_tiled<T>(const NodeRec<T>*, const long long*, const FarGeom&, const cx_t<T>*,     \
                                     cx_t<T>*, cx_t<T>*, cudaStream_t);                                       \
-    template size_t node_fused_smem<T>(int);                                                                 \
+    template size_t node_fused_smem<T>(int, int);                                                            \
     template int fill_grid<T>(cx_t<T>*, long, T, T, cudaStream_t);                                          \
     template int node_step_fused<T>(const NodeRec<T>*, const long long*, const FarGeom&, const cx_t<T>*,     \
                                     cx_t<T>*, const NodeTuning&, cudaStream_t);                              \

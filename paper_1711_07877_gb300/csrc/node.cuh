@@ -24,8 +24,9 @@ int node_step_tiled(const NodeRec<T>* nodes, const long long* tile_start, const 
 // atomicAdd, 1 = one float2 plane with a 64-bit compare-and-swap (FP32 only); sched 0 =
 // records dealt to the lane groups in turn, 1 = one contiguous run per group.
 struct NodeTuning {
-    int acc = 0;
+    int acc = 0;          // 0 float planes, 1 float2 CAS (FP32), 2 int64 fixed point (FP32)
     int sched = 0;
+    float wbound = 0.f;   // max |omega'| component x P_k^2 (the fixed-point scale bound)
 };
 
 // x[i] = re + i im for i < n.
@@ -35,7 +36,7 @@ int fill_grid(cx_t<T>* x, long n, T re, T im, cudaStream_t s);
 // The same in one kernel per tile: gather, weight and scatter into a shared accumulator,
 // whose overlap band is added atomically into kout (cleared here).
 template <typename T>
-size_t node_fused_smem(int Pk);   // dynamic shared memory of the fused kernel
+size_t node_fused_smem(int Pk, int acc = 0);   // dynamic shared memory of the fused kernel
 template <typename T>
 int node_step_fused(const NodeRec<T>* nodes, const long long* tile_start, const FarGeom& g,
                     const cx_t<T>* kin, cx_t<T>* kout, const NodeTuning& t, cudaStream_t s);

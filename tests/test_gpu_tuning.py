@@ -40,7 +40,7 @@ def test_variants_agree_and_tune_picks_one(S, kind):
                    S.make_options(form=S.SBD_FORM_FP32))
     try:
         outs = {}
-        for acc in (0, 1):
+        for acc in (0, 1, 2):
             for sched in (0, 1):
                 S.sbd_set_tuning(p, acc, sched)
                 info = S.sbd_plan_info(p)
@@ -57,7 +57,7 @@ def test_variants_agree_and_tune_picks_one(S, kind):
         for k, v in outs.items():
             assert np.max(np.abs(v[idx] - ref)) <= 1e-6 * np.abs(f).sum(), k
         ms = S.sbd_tune(p, reps=2)
-        assert all(t > 0 for t in ms)
+        assert len(ms) == 6 and all(t > 0 for t in ms)
         info = S.sbd_plan_info(p)
         best = int(np.argmin(ms))
         assert (info["node_acc"], info["node_sched"]) == (best // 2, best % 2)
@@ -70,10 +70,11 @@ def test_fp64_rejects_cas_variant(S):
     zt = torch.from_numpy(wl.z).cuda()
     p = S.sbd_plan(zt, 500, S.SBD_LAPLACE, 0.0, wl.delta_min, 1e-6, S.make_options(form=S.SBD_FORM_FP64))
     try:
-        with pytest.raises(S.SbdError) as e:
-            S.sbd_set_tuning(p, 1, 0)
-        assert e.value.code == S.SBD_EINVAL
+        for acc in (1, 2):
+            with pytest.raises(S.SbdError) as e:
+                S.sbd_set_tuning(p, acc, 0)
+            assert e.value.code == S.SBD_EINVAL
         ms = S.sbd_tune(p, reps=1)
-        assert ms[0] > 0 and ms[1] > 0 and ms[2] == -1 and ms[3] == -1
+        assert ms[0] > 0 and ms[1] > 0 and all(t == -1 for t in ms[2:])
     finally:
         S.sbd_destroy(p)
