@@ -147,6 +147,16 @@ int sbd_plan(const double* points, int64_t n, sbd_kernel kernel, double delta_mi
  * ------------------------------------------------------------------------------- */
 int sbd_matvec(sbd_plan_t plan, const void* f, void* q, int32_t nrhs, void* cuda_stream);
 
+/* sbd_matvec_graph - sbd_matvec replayed from a CUDA graph (no counterpart in the paper):
+ * the per-kernel launch cost (2 + 9 nrhs kernels per call) matters for small N.  The first
+ * call for a given nrhs runs one matvec on plan-owned buffers and captures a second one
+ * into a graph; every call then copies f into the plan's input buffer, launches the graph
+ * and copies the plan's output buffer to q, on a plan-owned stream ordered after and before
+ * cuda_stream with events (so the legacy default stream works too).  Same arguments,
+ * layout, results and ordering rules as sbd_matvec; holds two extra N x max_nrhs buffers.
+ * Errors: as sbd_matvec, and SBD_ECUDA if capture or instantiation fails. */
+int sbd_matvec_graph(sbd_plan_t plan, const void* f, void* q, int32_t nrhs, void* cuda_stream);
+
 /* The two halves of sbd_matvec, same arguments and layout:
  *   sbd_far   q = NUFFT_+(omega_hat . NUFFT_-(f))   (Eq. far convolution, incl. the xi = 0 term)
  *   sbd_close q = D f                               (Sec. 1, close correction)                  */

@@ -93,6 +93,13 @@ struct sbd_plan_s {
     void* wsC = nullptr;
     double2* sumf = nullptr;
     double2* zero2 = nullptr;
+    // CUDA-graph replay of sbd_matvec (sbd_matvec_graph): fixed input / output buffers,
+    // one instantiated graph per nrhs, recorded and launched on a plan-owned stream
+    void* g_in = nullptr;
+    void* g_out = nullptr;
+    std::vector<cudaGraphExec_t> g_exec;
+    cudaStream_t g_stream = nullptr;
+    cudaEvent_t g_ev_in = nullptr, g_ev_out = nullptr;
     long long device_bytes = 0;
     double plan_seconds = 0.0;
     std::vector<void*> allocations;
@@ -179,6 +186,11 @@ void free_plan(sbd_plan_s* p) {
     cudaDeviceSynchronize();
     collect_marks(p);
     for (cudaEvent_t e : p->event_pool) cudaEventDestroy(e);
+    for (cudaGraphExec_t g : p->g_exec)
+        if (g) cudaGraphExecDestroy(g);
+    if (p->g_ev_in) cudaEventDestroy(p->g_ev_in);
+    if (p->g_ev_out) cudaEventDestroy(p->g_ev_out);
+    if (p->g_stream) cudaStreamDestroy(p->g_stream);
     for (void* a : p->allocations) cudaFree(a);
     if (p->rowptr) cudaFree(p->rowptr);
     if (p->col) cudaFree(p->col);
@@ -706,6 +718,64 @@ int sbd_matvec(sbd_plan_t p, const void* f, void* q, int32_t nrhs, void* cuda_st
     t.end();
     return p->form == SBD_FORM_FP32 ? far_apply<float>(p, f, q, nrhs, s, p->q_int)
                                     : far_apply<double>(p, f, q, nrhs, s, p->q_int);
+}
+
+int sbd_matvec_graph(sbd_plan_t p, const void* f, void* q, int32_t nrhs, void* cuda_stream) {
+    int rc = check_plan_call(p, f, q);
+    if (rc) return rc;
+    if (nrhs < 1 || nrhs > p->max_nrhs) {
+        set_error("nrhs outside [1, max_nrhs]");
+        return SBD_EINVAL;
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    const size_t bytes = (p->kind == SBD_HELMHOLTZ ? 16 : 8) * static_cast<size_t>(p->n) * nrhs;
+    if (!p->g_stream) {
+        SBD_CUDA_TRY(cudaStreamCreateWithFlags(&p->g_stream, cudaStreamNonBlocking));
+        SBD_CUDA_TRY(cudaEventCreateWithFlags(&p->g_ev_in, cudaEventDisableTiming));
+        SBD_CUDA_TRY(cudaEventCreateWithFlags(&p->g_ev_out, cudaEventDisableTiming));
+        const size_t cap = (p->kind == SBD_HELMHOLTZ ? 16 : 8) * static_cast<size_t>(p->n) * p->max_nrhs;
+        if ((rc = dev_alloc(p, &p->g_in, cap)) || (rc = dev_alloc(p, &p->g_out, cap))) return rc;
+        p->g_exec.assign(p->max_nrhs + 1, nullptr);
+    }
+    cudaStream_t g = p->g_stream;
+    // order after the caller's prior work, run on the graph stream, order the caller after it
+    SBD_CUDA_TRY(cudaEventRecord(p->g_ev_in, s));
+    SBD_CUDA_TRY(cudaStreamWaitEvent(g, p->g_ev_in, 0));
+    if (!p->g_exec[nrhs]) {
+        // one plain matvec first (creates every table the kernels use), then the capture;
+        // step timing stays off while capturing
+        SBD_CUDA_TRY(cudaMemsetAsync(p->g_in, 0, bytes, g));
+        if ((rc = sbd_matvec(p, p->g_in, p->g_out, nrhs, g))) return rc;
+        const bool prof = p->profile;
+        p->profile = false;
+        SBD_CUDA_TRY(cudaStreamBeginCapture(g, cudaStreamCaptureModeThreadLocal));
+        rc = sbd_matvec(p, p->g_in, p->g_out, nrhs, g);
+        cudaGraph_t graph = nullptr;
+        const cudaError_t e = cudaStreamEndCapture(g, &graph);
+        p->profile = prof;
+        if (rc) {
+            if (graph) cudaGraphDestroy(graph);
+            return rc;
+        }
+        if (e != cudaSuccess) {
+            set_error(std::string("sbd_matvec_graph: capture failed: ") + cudaGetErrorString(e));
+            return SBD_ECUDA;
+        }
+        cudaGraphExec_t exec = nullptr;
+        const cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ei != cudaSuccess) {
+            set_error(std::string("sbd_matvec_graph: instantiate failed: ") + cudaGetErrorString(ei));
+            return SBD_ECUDA;
+        }
+        p->g_exec[nrhs] = exec;
+    }
+    SBD_CUDA_TRY(cudaMemcpyAsync(p->g_in, f, bytes, cudaMemcpyDeviceToDevice, g));
+    SBD_CUDA_TRY(cudaGraphLaunch(p->g_exec[nrhs], g));
+    SBD_CUDA_TRY(cudaMemcpyAsync(q, p->g_out, bytes, cudaMemcpyDeviceToDevice, g));
+    SBD_CUDA_TRY(cudaEventRecord(p->g_ev_out, g));
+    SBD_CUDA_TRY(cudaStreamWaitEvent(s, p->g_ev_out, 0));
+    return SBD_OK;
 }
 
 int sbd_profile(sbd_plan_t p, int32_t enable) {

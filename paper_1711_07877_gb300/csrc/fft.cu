@@ -289,212 +289,6 @@ __global__ void __launch_bounds__(NT) fft_rows_kernel(
     }
 }
 
-// --- paired-stage row FFT -----------------------------------------------------------------
-// The plan's radix stages are taken two at a time: a thread holds the R1 R2 elements of
-// one (group, offset) pair of consecutive decimation-in-time stages in registers and
-// does both stages before writing back, so a row makes about half as many passes through
-// shared memory.  The first pair reads the row straight from global memory: with radices
-// R1, R2 first, thread t < G = n / (R1 R2) takes the group g = perm[t] / (R1 R2), whose
-// element (r1, r2) (shared position g R1 R2 + r1 + R1 r2) is input index t + G (r2 + R2 r1),
-// so for each (r1, r2) the threads read consecutive inputs; the digit-reversed store of the
-// single-stage kernel disappears.
-template <typename T, int R1, int R2>
-__device__ __forceinline__ void pair_butterflies(cx_t<T> (&v)[R2][R1], int k, int Lp, int nq, int Q, int sign,
-                                                 const cx_t<T>* __restrict__ tw) {
-    using C = cx_t<T>;
-    const int L1 = Lp * R1;
-    // stage A: R2 butterflies of radix R1 on offset k of sub-transforms of length Lp
-    if (Lp > 1) {
-        const int step = Q * (nq / L1);
-#pragma unroll
-        for (int r1 = 1; r1 < R1; ++r1) {
-            C w = tw[r1 * k * step];
-            if (sign > 0) w.y = -w.y;
-#pragma unroll
-            for (int r2 = 0; r2 < R2; ++r2) v[r2][r1] = cmul(v[r2][r1], w);
-        }
-    }
-#pragma unroll
-    for (int r2 = 0; r2 < R2; ++r2) small_dft<T, R1>(v[r2], sign);
-    if (R2 == 1) return;
-    // stage B: R1 butterflies of radix R2 on offsets k + r1 Lp of sub-transforms of length L1
-    const int step2 = Q * (nq / (L1 * R2));
-#pragma unroll
-    for (int r1 = 0; r1 < R1; ++r1) {
-        C u[R2];
-        const int kp = k + r1 * Lp;
-#pragma unroll
-        for (int r2 = 0; r2 < R2; ++r2) {
-            C x = v[r2][r1];
-            if (r2 > 0) {
-                C w = tw[r2 * kp * step2];
-                if (sign > 0) w.y = -w.y;
-                x = cmul(x, w);
-            }
-            u[r2] = x;
-        }
-        small_dft<T, R2>(u, sign);
-#pragma unroll
-        for (int r2 = 0; r2 < R2; ++r2) v[r2][r1] = u[r2];
-    }
-}
-
-template <typename T, int R1, int R2>
-__device__ void pair_stage_smem(cx_t<T>* s, int nq, int Lp, int Q, int sign, const cx_t<T>* __restrict__ tw,
-                                int nthreads) {
-    using C = cx_t<T>;
-    const int L2 = Lp * R1 * R2;
-    const int items = nq / (R1 * R2);
-    for (int w = threadIdx.x; w < items; w += nthreads) {
-        const int k = w % Lp, g = w / Lp;
-        const int base = g * L2 + k;
-        C v[R2][R1];
-#pragma unroll
-        for (int r2 = 0; r2 < R2; ++r2)
-#pragma unroll
-            for (int r1 = 0; r1 < R1; ++r1) v[r2][r1] = s[base + Lp * (r1 + R1 * r2)];
-        pair_butterflies<T, R1, R2>(v, k, Lp, nq, Q, sign, tw);
-#pragma unroll
-        for (int r2 = 0; r2 < R2; ++r2)
-#pragma unroll
-            for (int r1 = 0; r1 < R1; ++r1) s[base + Lp * (r1 + R1 * r2)] = v[r2][r1];
-    }
-}
-
-// First pair: elements from the input row (load_elem, the fold and twist of the Q
-// phases as in the single-stage kernel), result to shared memory.
-template <typename T, int R1, int R2>
-__device__ void pair_stage_first(cx_t<T>* s, int n, int nq, int Q, int r, int sign,
-                                 const cx_t<T>* __restrict__ tw, const int* __restrict__ perm, int io,
-                                 const cx_t<T>* __restrict__ src, long in_stride, int in_len, int in_shift, long row,
-                                 const HermFold<T>& hf, T rs0, T rs1, const T* __restrict__ pre_elem,
-                                 int nthreads) {
-    using C = cx_t<T>;
-    constexpr int L2 = R1 * R2;
-    const int G = nq / L2;
-    for (int t = threadIdx.x; t < G; t += nthreads) {
-        const int g = perm[t] / L2;
-        C v[R2][R1];
-#pragma unroll
-        for (int r2 = 0; r2 < R2; ++r2) {
-#pragma unroll
-            for (int r1 = 0; r1 < R1; ++r1) {
-                const int i = t + G * (r2 + R2 * r1);     // input index of the length-nq transform
-                C acc = mk<T>(0, 0);
-                for (int j = 0; j < Q; ++j) {
-                    const int idx = i + j * nq;
-                    bool has;
-                    C x = load_elem<T>(io, idx, n, src, in_stride, in_len, in_shift, row, hf, rs0, rs1, pre_elem,
-                                       has);
-                    if (has) {
-                        if (r) {
-                            C w = tw[idx];
-                            if (sign > 0) w.y = -w.y;
-                            x = cmul(x, w);
-                        }
-                        acc = cadd(acc, x);
-                    }
-                }
-                v[r2][r1] = acc;
-            }
-        }
-        pair_butterflies<T, R1, R2>(v, 0, 1, nq, Q, sign, tw);
-        const int base = g * L2;
-#pragma unroll
-        for (int r2 = 0; r2 < R2; ++r2)
-#pragma unroll
-            for (int r1 = 0; r1 < R1; ++r1) s[base + r1 + R1 * r2] = v[r2][r1];
-    }
-}
-
-template <typename T, bool FIRST>
-__device__ void pair_stage_dispatch(int R1, int R2, cx_t<T>* s, int n, int nq, int Lp, int Q, int r, int sign,
-                                    const cx_t<T>* __restrict__ tw, const int* __restrict__ perm, int io,
-                                    const cx_t<T>* __restrict__ src, long in_stride, int in_len, int in_shift,
-                                    long row, const HermFold<T>& hf, T rs0, T rs1, const T* __restrict__ pre_elem,
-                                    int nthreads) {
-#define SBD_PAIR(A, B)                                                                                          \
-    if (R1 == A && R2 == B) {                                                                                   \
-        if (FIRST) pair_stage_first<T, A, B>(s, n, nq, Q, r, sign, tw, perm, io, src, in_stride, in_len, in_shift, \
-                                             row, hf, rs0, rs1, pre_elem, nthreads);                             \
-        else pair_stage_smem<T, A, B>(s, nq, Lp, Q, sign, tw, nthreads);                                        \
-        return;                                                                                                 \
-    }
-    SBD_PAIR(5, 5) SBD_PAIR(5, 3) SBD_PAIR(5, 2) SBD_PAIR(5, 4) SBD_PAIR(3, 3) SBD_PAIR(3, 2) SBD_PAIR(3, 4)
-    SBD_PAIR(2, 4) SBD_PAIR(4, 4) SBD_PAIR(5, 1) SBD_PAIR(3, 1) SBD_PAIR(2, 1) SBD_PAIR(4, 1)
-#undef SBD_PAIR
-}
-
-template <typename T, int NT>
-__global__ void __launch_bounds__(NT) fft_rows2_kernel(
-    const cx_t<T>* __restrict__ in, long in_stride, int in_len, int in_shift,
-    cx_t<T>* __restrict__ out, long out_stride, int out_len, int out_shift,
-    int n, int Q, int sign, FftPlan1D plan, const cx_t<T>* __restrict__ tw, const int* __restrict__ perm,
-    const T* __restrict__ pre_elem, const T* __restrict__ pre_row,
-    const T* __restrict__ post_elem, const T* __restrict__ post_row, HermFold<T> hf, int io) {
-    using C = cx_t<T>;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    C* s = reinterpret_cast<C*>(smem_raw);
-    const long row = blockIdx.y;
-    const int r = blockIdx.x;
-    const int nq = n / Q;
-    const C* src = in + row * in_stride * (io == kIoPairInv ? 2 : 1);
-    T rs0 = static_cast<T>(1), rs1 = static_cast<T>(1);
-    if (pre_row) {
-        rs0 = pre_row[io == kIoPairFwd ? 2 * row : row];
-        rs1 = pre_row[io == kIoPairFwd ? 2 * row + 1 : row];
-    }
-    int st = 0, Lp = 1;
-    {
-        const int R1 = plan.radix[0], R2 = plan.nstages > 1 ? plan.radix[1] : 1;
-        pair_stage_dispatch<T, true>(R1, R2, s, n, nq, 1, Q, r, sign, tw, perm, io, src, in_stride, in_len,
-                                     in_shift, row, hf, rs0, rs1, pre_elem, NT);
-        st = plan.nstages > 1 ? 2 : 1;
-        Lp = R1 * R2;
-        __syncthreads();
-    }
-    while (st < plan.nstages) {
-        const int R1 = plan.radix[st], R2 = st + 1 < plan.nstages ? plan.radix[st + 1] : 1;
-        pair_stage_dispatch<T, false>(R1, R2, s, n, nq, Lp, Q, r, sign, tw, perm, io, src, in_stride, in_len,
-                                      in_shift, row, hf, rs0, rs1, pre_elem, NT);
-        st += R2 > 1 ? 2 : 1;
-        Lp *= R1 * R2;
-        __syncthreads();
-    }
-    if (io == kIoPairFwd) {
-        C* d0 = out + 2 * row * out_stride;
-        C* d1 = d0 + out_stride;
-        for (int e = threadIdx.x; e < out_len; e += NT) {
-            int k = e + out_shift;
-            if (k >= n) k -= n;
-            if (Q == 2 && (k & 1) != r) continue;
-            const int km = k == 0 ? 0 : n - k;
-            const C zk = s[Q == 2 ? (k >> 1) : k], zm = s[Q == 2 ? (km >> 1) : km];
-            const T h = static_cast<T>(0.5);
-            const T pe = post_elem ? post_elem[e] : static_cast<T>(1);
-            d0[e] = mk<T>(h * pe * (zk.x + zm.x), h * pe * (zk.y - zm.y));
-            d1[e] = mk<T>(h * pe * (zk.y + zm.y), h * pe * (zm.x - zk.x));
-        }
-        return;
-    }
-    C* dst = out + row * out_stride;
-    T ps0 = static_cast<T>(1), ps1 = static_cast<T>(1);
-    if (post_row) {
-        ps0 = post_row[io == kIoPairInv ? 2 * row : row];
-        ps1 = post_row[io == kIoPairInv ? 2 * row + 1 : row];
-    }
-    for (int e = threadIdx.x; e < out_len; e += NT) {
-        int k = e + out_shift;
-        if (k >= n) k -= n;
-        if (Q == 2 && (k & 1) != r) continue;
-        C v = s[Q == 2 ? (k >> 1) : k];
-        const T pe = post_elem ? post_elem[e] : static_cast<T>(1);
-        v.x *= ps0 * pe;
-        v.y *= ps1 * pe;
-        dst[e] = v;
-    }
-}
-
 // Digit-reversal permutation of the decimation-in-time schedule: with radices
 // R_1..R_s applied in that order, index i = sum of digits (least significant digit in
 // base R_s, then R_{s-1}, ...) lands at position sum_k d_k R_1...R_{k-1}.
@@ -631,12 +425,17 @@ int fft_rows(const cx_t<T>* in, long in_stride, int in_len, int in_shift,
         const T* por = post_row ? post_row + r0 * (io == kIoPairInv ? 2 : 1) : nullptr;
         const HermFold<T> hf{in - static_cast<long>(herm_row0) * in_stride, herm_n,
                              static_cast<long>(herm_row0) + r0};
-        // paired-stage kernel: up to 25 elements per thread in registers, so fewer threads
-        constexpr int kNT = sizeof(T) == 4 ? 512 : 256;
-        auto k = fft_rows2_kernel<T, kNT>;
-        SBD_TRY(raise_smem_limit(k, smem));
-        k<<<grid, kNT, smem, stream>>>(ip, in_stride, in_len, in_shift, op, out_stride, out_len, out_shift, n, Q,
-                                       sign, plan, tw, perm, pre_elem, prr, post_elem, por, hf, io);
+        if (nq > 2048) {
+            auto k = fft_rows_kernel<T, 1024>;
+            SBD_TRY(raise_smem_limit(k, smem));
+            k<<<grid, 1024, smem, stream>>>(ip, in_stride, in_len, in_shift, op, out_stride, out_len, out_shift,
+                                            n, Q, sign, plan, tw, perm, pre_elem, prr, post_elem, por, hf, io);
+        } else {
+            auto k = fft_rows_kernel<T, 256>;
+            SBD_TRY(raise_smem_limit(k, smem));
+            k<<<grid, 256, smem, stream>>>(ip, in_stride, in_len, in_shift, op, out_stride, out_len, out_shift,
+                                           n, Q, sign, plan, tw, perm, pre_elem, prr, post_elem, por, hf, io);
+        }
         SBD_LAUNCH_CHECK();
     }
     SBD_LAUNCH_CHECK();

@@ -169,9 +169,10 @@ struct Solver {
         *out = std::sqrt(std::max(v.x, 0.0));
         return SBD_OK;
     }
-    // y = (shift I + scale A) x
+    // y = (shift I + scale A) x; the matvec replays a CUDA graph (launch cost matters for
+    // the small systems a solver sees)
     int apply(const T* x, T* y) {
-        int rc = sbd_matvec(plan, x, y, 1, s);
+        int rc = sbd_matvec_graph(plan, x, y, 1, s);
         if (rc) return rc;
         axpby_kernel<CPLX><<<nblk, 256, 0, s>>>(n, make_double2(shift.real(), shift.imag()), x,
                                                 make_double2(scale.real(), scale.imag()), y);

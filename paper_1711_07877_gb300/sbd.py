@@ -74,6 +74,7 @@ _SIGS = {
     "sbd_y0_root": ([_I32, _P], ctypes.c_int),
     "sbd_plan": ([_P, _I64, sbd_kernel, _D, _D, ctypes.POINTER(sbd_options), _P, ctypes.POINTER(_P)], ctypes.c_int),
     "sbd_matvec": ([_P, _P, _P, _I32, _P], ctypes.c_int),
+    "sbd_matvec_graph": ([_P, _P, _P, _I32, _P], ctypes.c_int),
     "sbd_far": ([_P, _P, _P, _I32, _P], ctypes.c_int),
     "sbd_close": ([_P, _P, _P, _I32, _P], ctypes.c_int),
     "sbd_nufft_minus": ([_P, _P, _P, _P], ctypes.c_int),
@@ -156,6 +157,10 @@ def sbd_plan(points, n: int, kernel_kind: int, kappa: float, delta_min: float, e
 
 def sbd_matvec(plan: int, f, q, nrhs: int = 1, stream=None) -> None:
     _check(lib.sbd_matvec(plan, _ptr(f), _ptr(q), nrhs, _stream(stream)), "sbd_matvec")
+
+
+def sbd_matvec_graph(plan: int, f, q, nrhs: int = 1, stream=None) -> None:
+    _check(lib.sbd_matvec_graph(plan, _ptr(f), _ptr(q), nrhs, _stream(stream)), "sbd_matvec_graph")
 
 
 def sbd_far(plan: int, f, q, nrhs: int = 1, stream=None) -> None:

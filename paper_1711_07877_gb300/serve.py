@@ -13,6 +13,7 @@ from __future__ import annotations
 
 import threading
 import time
+from collections import OrderedDict
 from dataclasses import dataclass, field
 
 import numpy as np
@@ -75,6 +76,8 @@ class Request:
     eps: float
     shift: complex = 0.5
     scale: complex = 1.0
+    geometry: object = None       # hashable key: requests with the same key share points,
+                                  # kernel and tolerances, and reuse one resident plan
     arrival: float = 0.0          # seconds after the server's start
     # results
     x: np.ndarray | None = None
@@ -110,37 +113,93 @@ class Admission:
     at the head), or the head itself when nothing is running, so that a request larger
     than the whole budget still runs, alone.  The per-point estimate only grows, from
     the footprints that finished plans report.
+
+    Resident plans: a request with a geometry key keeps its plan on the device after it
+    finishes (its bytes stay counted); a later request with the same key reuses it and
+    needs only solver workspace, but waits while another request uses that plan.  When
+    a request does not fit, idle resident plans are evicted oldest-use first; `admit`
+    hands them back so that the caller frees them.
     """
 
-    def __init__(self, budget: int, bytes_per_point: float = 8000.0, fixed_bytes: int = 64 << 20):
+    def __init__(self, budget: int, bytes_per_point: float = 8000.0, fixed_bytes: int = 64 << 20,
+                 solve_bytes_per_point: float = 32 * 16.0):
         self.budget = int(budget)
         self.bytes_per_point = float(bytes_per_point)
         self.fixed_bytes = int(fixed_bytes)
+        self.solve_bytes_per_point = float(solve_bytes_per_point)
         self.in_use = 0
         self.running = 0
         self.pending: list = []
+        self.resident: "OrderedDict" = OrderedDict()   # key -> {"bytes", "busy", "plan"}
 
     def estimate(self, n_points: int) -> int:
         return int(self.bytes_per_point * n_points) + self.fixed_bytes
 
+    def solve_estimate(self, n_points: int) -> int:
+        return int(self.solve_bytes_per_point * n_points)
+
     def push(self, req) -> None:
         self.pending.append(req)
 
+    def _idle_bytes(self, keep) -> int:
+        return sum(v["bytes"] for k, v in self.resident.items() if not v["busy"] and k != keep)
+
     def admit(self):
+        """(request, estimate, [(key, plan) to free]) or None."""
         for i, r in enumerate(self.pending):
-            est = self.estimate(len(r.z))
-            if self.in_use + est <= self.budget or self.running == 0:
-                self.pending.pop(i)
-                self.in_use += est
-                self.running += 1
-                return r, est
+            key = getattr(r, "geometry", None)
+            reuse = key is not None and key in self.resident
+            if reuse and self.resident[key]["busy"]:
+                continue
+            est = self.solve_estimate(len(r.z)) if reuse else self.estimate(len(r.z))
+            evict = []
+            if self.in_use + est > self.budget and self.running > 0:
+                if self.in_use - self._idle_bytes(key) + est > self.budget:
+                    continue
+                for k in list(self.resident):
+                    if self.in_use + est <= self.budget:
+                        break
+                    v = self.resident[k]
+                    if v["busy"] or k == key:
+                        continue
+                    self.in_use -= v["bytes"]
+                    evict.append((k, v["plan"]))
+                    del self.resident[k]
+            elif self.running == 0 and self.in_use + est > self.budget:
+                # alone on the device: free every idle resident plan first
+                for k in list(self.resident):
+                    v = self.resident[k]
+                    if k == key:
+                        continue
+                    self.in_use -= v["bytes"]
+                    evict.append((k, v["plan"]))
+                    del self.resident[k]
+            self.pending.pop(i)
+            self.in_use += est
+            self.running += 1
+            if reuse:
+                self.resident[key]["busy"] = True
+                self.resident.move_to_end(key)
+            return r, est, evict
         return None
 
-    def release(self, est: int, n_points: int = 0, device_bytes: int = 0) -> None:
+    def release(self, est: int, n_points: int = 0, device_bytes: int = 0, key=None, plan=None) -> None:
+        """The request is done.  With a key, its plan (device_bytes) stays resident."""
         self.in_use -= est
         self.running -= 1
         if n_points and device_bytes:
             self.bytes_per_point = max(self.bytes_per_point, 1.2 * device_bytes / n_points)
+        if key is not None:
+            if key in self.resident:
+                self.resident[key]["busy"] = False
+            else:
+                self.resident[key] = {"bytes": int(device_bytes), "busy": False, "plan": plan}
+                self.in_use += int(device_bytes)
+            self.resident.move_to_end(key)
+
+    def plan_of(self, key):
+        v = self.resident.get(key)
+        return v["plan"] if v else None
 
 
 class Server:
@@ -188,22 +247,30 @@ class Server:
                     self.cv.wait(timeout=0.05)
                 if not got:
                     return
-            req, est = got
+            req, est, evict = got
+            for _, old_plan in evict:            # idle resident plans that made room
+                S.sbd_destroy(old_plan)
             req.start = self.now()
-            plan = None
+            key = req.geometry
+            with self.cv:
+                plan = self.adm.plan_of(key) if key is not None else None
+            reused = plan is not None
             try:
                 with torch.cuda.stream(stream):
-                    zt = torch.from_numpy(req.z).to("cuda", non_blocking=True)
                     bt = torch.from_numpy(req.b).to("cuda", non_blocking=True)
                     xt = torch.zeros_like(bt)
-                dmin, dmax = req.delta_min, 0.0
-                if self.fit_grid:
-                    dmin, dmax = fit_grid_scales(req.kind, req.kappa, req.delta_min, enclosing_diameter(req.z))
-                opt = S.make_options(form=self.form, delta_max=dmax)
-                plan = S.sbd_plan(zt, len(req.z), req.kind, req.kappa, dmin, req.eps, opt, stream.cuda_stream)
-                info = S.sbd_plan_info(plan)
-                req.plan_seconds = info["plan_seconds"]
-                req.device_bytes = info["device_bytes"]
+                if not reused:
+                    with torch.cuda.stream(stream):
+                        zt = torch.from_numpy(req.z).to("cuda", non_blocking=True)
+                    dmin, dmax = req.delta_min, 0.0
+                    if self.fit_grid:
+                        dmin, dmax = fit_grid_scales(req.kind, req.kappa, req.delta_min,
+                                                     enclosing_diameter(req.z))
+                    opt = S.make_options(form=self.form, delta_max=dmax)
+                    plan = S.sbd_plan(zt, len(req.z), req.kind, req.kappa, dmin, req.eps, opt, stream.cuda_stream)
+                    info = S.sbd_plan_info(plan)
+                    req.plan_seconds = info["plan_seconds"]
+                    req.device_bytes = info["device_bytes"]
                 it, res = S.sbd_gmres(plan, bt, xt, req.shift, req.scale, self.tol, self.restart, self.max_iter,
                                       stream.cuda_stream)
                 stream.synchronize()
@@ -212,25 +279,40 @@ class Server:
             except Exception as e:  # the request fails, the server keeps serving
                 req.error = str(e)
             finally:
-                if plan:
+                keep = key is not None and plan is not None and req.error is None
+                if plan is not None and not keep and not reused:
                     S.sbd_destroy(plan)
                 req.done = self.now()
                 with self.cv:
-                    self.adm.release(est, len(req.z), req.device_bytes)
+                    if keep:
+                        self.adm.release(est, len(req.z), req.device_bytes, key=key, plan=plan)
+                    elif reused:
+                        # a reused plan whose solve failed stays resident
+                        self.adm.release(est, key=key, plan=plan)
+                    else:
+                        self.adm.release(est, len(req.z), req.device_bytes)
                     if req.error is None:
                         self.stats.latencies.append(req.done - req.arrival)
                         self.stats.points_matvecs += len(req.z) * (req.iterations + 2)
                     self.cv.notify_all()
 
-    def drain(self, requests: list[Request]) -> None:
-        """Wait until every request in the list is done, then stop the workers."""
-        while any(r.done == 0.0 for r in requests):
-            time.sleep(0.002)
+    def close(self) -> None:
+        """Stop the workers and free every resident plan."""
         with self.cv:
             self.closed = True
             self.cv.notify_all()
         for w in self.workers:
             w.join()
+        for v in list(self.adm.resident.values()):
+            if v["plan"]:
+                S.sbd_destroy(v["plan"])
+        self.adm.resident.clear()
+
+    def drain(self, requests: list[Request]) -> None:
+        """Wait until every request in the list is done, then stop the workers."""
+        while any(r.done == 0.0 for r in requests):
+            time.sleep(0.002)
+        self.close()
         self.stats.wall = max(r.done for r in requests) - min(r.arrival for r in requests)
 
 

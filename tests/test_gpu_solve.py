@@ -193,3 +193,52 @@ def test_plan_delta_max_option_and_fit_cache(S):
     S.sbd_destroy(p)
     after = S.sbd_fit_cache_stats()
     assert after["hits"] == before["hits"] + 1
+
+
+@pytest.mark.parametrize("kind,form", [("laplace", 0), ("helmholtz", 1)])
+def test_matvec_graph_equals_matvec(S, kind, form):
+    """The graph replay computes the same matvec, on the default stream and on a side
+    stream, for several inputs and for nrhs = 1 and 2."""
+    n = 2500
+    z, kappa, dmin, _ = system(kind, n, 61)
+    zt = torch.from_numpy(z).cuda()
+    p = S.sbd_plan(zt, n, S.SBD_HELMHOLTZ if kind == "helmholtz" else S.SBD_LAPLACE, kappa, dmin, 1e-8,
+                   S.make_options(form=form, max_nrhs=2))
+    try:
+        side = torch.cuda.Stream()
+        for trial, stream in enumerate((None, side, None)):
+            for nrhs in (1, 2):
+                f = W.rhs(n, 70 + trial, nrhs=nrhs, complex_valued=kind == "helmholtz")
+                ft = torch.from_numpy(np.ascontiguousarray(f)).cuda()
+                q0, q1 = torch.empty_like(ft), torch.empty_like(ft)
+                S.sbd_matvec(p, ft, q0, nrhs)
+                torch.cuda.synchronize()
+                sid = None if stream is None else stream.cuda_stream
+                if stream is not None:
+                    stream.wait_stream(torch.cuda.current_stream())
+                S.sbd_matvec_graph(p, ft, q1, nrhs, sid)
+                torch.cuda.synchronize()
+                a, b = q0.cpu().numpy(), q1.cpu().numpy()
+                tol = 1e-12 if form == 0 else 2e-6
+                assert np.linalg.norm(a - b) / np.linalg.norm(a) < tol, (trial, nrhs)
+    finally:
+        S.sbd_destroy(p)
+
+
+def test_server_reuses_resident_plans(S):
+    """Requests with the same geometry key reuse one resident plan (no second plan build)
+    and give the answer of a fresh solve."""
+    from paper_1711_07877_gb300 import serve
+    z, kappa, dmin, b = system("laplace", 2000, 81)
+    b2 = W.rhs(2000, 82)
+    mk = lambda rid, rhs: serve.Request(rid=rid, z=z, b=rhs, kind=S.SBD_LAPLACE, kappa=0.0, delta_min=dmin,
+                                        eps=1e-10, shift=1.0, scale=1.0 / 2000, geometry="g1")
+    reqs = [mk(0, b), mk(1, b2), mk(2, b)]
+    srv, summary = serve.run_poisson(reqs, mean_gap_s=0.001, seed=3, slots=2, form=S.SBD_FORM_FP64, tol=1e-9)
+    assert all(r.error is None for r in reqs)
+    built = [r for r in reqs if r.plan_seconds > 0]
+    assert len(built) == 1                      # one plan build, two reuses
+    assert np.linalg.norm(reqs[0].x - reqs[2].x) / np.linalg.norm(reqs[0].x) < 1e-8
+    solo = solve_gpu(S, z, "laplace", 0.0, dmin, 1e-10, b2, 0, 1e-9, 1.0, 1.0 / 2000)[0]
+    assert np.linalg.norm(reqs[1].x - solo) / np.linalg.norm(solo) < 1e-6
+    assert not srv.adm.resident                # close() freed the resident plan
