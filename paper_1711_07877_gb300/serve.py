@@ -131,6 +131,7 @@ class Admission:
         self.running = 0
         self.pending: list = []
         self.resident: "OrderedDict" = OrderedDict()   # key -> {"bytes", "busy", "plan"}
+        self.building: set = set()                     # keys whose plan a running request builds
 
     def estimate(self, n_points: int) -> int:
         return int(self.bytes_per_point * n_points) + self.fixed_bytes
@@ -148,6 +149,8 @@ class Admission:
         """(request, estimate, [(key, plan) to free]) or None."""
         for i, r in enumerate(self.pending):
             key = getattr(r, "geometry", None)
+            if key is not None and key in self.building:
+                continue                                # its plan is being built: wait for it
             reuse = key is not None and key in self.resident
             if reuse and self.resident[key]["busy"]:
                 continue
@@ -180,16 +183,22 @@ class Admission:
             if reuse:
                 self.resident[key]["busy"] = True
                 self.resident.move_to_end(key)
+            elif key is not None:
+                self.building.add(key)
             return r, est, evict
         return None
 
-    def release(self, est: int, n_points: int = 0, device_bytes: int = 0, key=None, plan=None) -> None:
-        """The request is done.  With a key, its plan (device_bytes) stays resident."""
+    def release(self, est: int, n_points: int = 0, device_bytes: int = 0, key=None, plan=None,
+                keep: bool = True) -> None:
+        """The request is done.  With a key and keep, its plan (device_bytes) stays
+        resident; keep = False (the build failed) only ends the build."""
         self.in_use -= est
         self.running -= 1
         if n_points and device_bytes:
             self.bytes_per_point = max(self.bytes_per_point, 1.2 * device_bytes / n_points)
         if key is not None:
+            self.building.discard(key)
+        if key is not None and keep:
             if key in self.resident:
                 self.resident[key]["busy"] = False
             else:
@@ -290,7 +299,7 @@ class Server:
                         # a reused plan whose solve failed stays resident
                         self.adm.release(est, key=key, plan=plan)
                     else:
-                        self.adm.release(est, len(req.z), req.device_bytes)
+                        self.adm.release(est, len(req.z), req.device_bytes, key=key, keep=False)
                     if req.error is None:
                         self.stats.latencies.append(req.done - req.arrival)
                         self.stats.points_matvecs += len(req.z) * (req.iterations + 2)

@@ -129,3 +129,22 @@ def test_resident_plan_in_use_is_never_evicted():
     a.release(e, key="A", plan="plan-A")
     r, e2, ev = a.admit()
     assert [k for k, _ in ev] == ["A"]
+
+
+def test_second_request_waits_while_its_plan_is_built():
+    a = Admission(budget=10_000, bytes_per_point=1.0, fixed_bytes=0, solve_bytes_per_point=0.1)
+    a.push(req(300, "A"))
+    a.push(req(300, "A"))
+    a.push(req(100))
+    r, e, _ = a.admit()
+    r2, e2, _ = a.admit()
+    assert r2.geometry is None               # the second "A" waits, the other one passes
+    assert a.admit() is None
+    a.release(e, 300, device_bytes=300, key="A", plan="pA")
+    r3, e3, _ = a.admit()
+    assert r3.geometry == "A" and e3 == 30   # reuses the resident plan
+    # a failed build releases the key without a resident plan
+    a.push(req(50, "B"))
+    rb, eb, _ = a.admit()
+    a.release(eb, key="B", keep=False)
+    assert "B" not in a.building and a.plan_of("B") is None
