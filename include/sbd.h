@@ -111,6 +111,8 @@ typedef struct {
                                 antipodal nodes follow by Hermitian symmetry) */
     int32_t node_acc;        /* fused node-kernel variant (sbd_tune): accumulation mode */
     int32_t node_sched;      /* fused node-kernel variant (sbd_tune): record schedule */
+    int32_t fft_split;       /* row-FFT phases (sbd_tune): 0 one where it fits, 2 always two */
+    int32_t reserved;
 } sbd_plan_stats;
 
 /* ---------------------------------------------------------------------------------
@@ -233,14 +235,18 @@ int sbd_fft2(const void* in, void* out, int32_t n0, int32_t n1, int32_t sign, in
  *                  frequency workspace is first filled with a constant non-zero value,
  *                  so that concurrent adds to a cell contend as with real data) and
  *                  keeps the fastest.
- *                  ms (host, 6 entries, may be NULL): mean ms per launch of variant
- *                  acc * 2 + sched, -1 where not applicable.  Blocks until done.
- *   sbd_set_tuning picks a variant by hand.
- * SBD_EINVAL for a null plan, reps < 1, acc outside {0, 1, 2} or sched outside {0, 1}
- * (acc 1 and 2 need the FP32 form).  Plans whose node step is the two-kernel fallback ignore the variant.
+ *                  ms (host, 8 entries, may be NULL): mean ms per launch of variant
+ *                  acc * 2 + sched, -1 where not applicable; ms[6], ms[7]: mean ms of
+ *                  the forward 2-D transform with rows in one phase where they fit, and
+ *                  with every row split into two half-length phases (two CTAs of 512
+ *                  threads per SM instead of one of 1024); the faster is kept too.
+ *                  Blocks until done.
+ *   sbd_set_tuning picks a variant by hand (fft_split 0 or 2).
+ * SBD_EINVAL for a null plan, reps < 1, acc outside {0, 1, 2}, sched outside {0, 1} or
+ * fft_split outside {0, 2} (acc 1 and 2 need the FP32 form).  Plans whose node step is the two-kernel fallback ignore the variant.
  * ------------------------------------------------------------------------------- */
 int sbd_tune(sbd_plan_t plan, int32_t reps, double* ms, void* cuda_stream);
-int sbd_set_tuning(sbd_plan_t plan, int32_t acc, int32_t sched);
+int sbd_set_tuning(sbd_plan_t plan, int32_t acc, int32_t sched, int32_t fft_split);
 
 /* ---------------------------------------------------------------------------------
  * Fit cache.  The off-line fit (P search and coefficients, Sec. 3-4) depends only on

@@ -25,6 +25,11 @@ thread_local std::string g_last_error;
 
 void set_error(const std::string& msg) { g_last_error = msg; }
 
+std::shared_mutex& capture_mutex() {
+    static std::shared_mutex mu;
+    return mu;
+}
+
 int raise_smem_limit_fn(const void* func, size_t bytes) {
     static std::mutex mu;
     static std::map<std::pair<int, const void*>, size_t> limit;
@@ -85,6 +90,7 @@ struct sbd_plan_s {
     void* ghat = nullptr;              // n_xi weighted node values (scratch of the two-kernel node step)
     bool node_fused = true;            // one-kernel node step (shared memory permitting)
     NodeTuning tuning;                 // fused node-kernel variant (sbd_tune)
+    int fft_split = 0;                 // row-FFT phases (sbd_tune): 0 as needed, 2 always two
     int tuned = 0;                     // 1 once sbd_tune chose the variant
     // workspace (one right-hand side at a time)
     void* wsX = nullptr;
@@ -116,7 +122,11 @@ namespace {
 
 int dev_alloc(sbd_plan_s* p, void** ptr, size_t bytes) {
     bytes = std::max<size_t>(bytes, 16);
-    cudaError_t e = cudaMalloc(ptr, bytes);
+    cudaError_t e;
+    {
+        std::unique_lock<std::shared_mutex> lock(capture_mutex());
+        e = cudaMalloc(ptr, bytes);
+    }
     if (e != cudaSuccess) {
         set_error(std::string("cudaMalloc(") + std::to_string(bytes) + "): " + cudaGetErrorString(e));
         cudaGetLastError();
@@ -183,6 +193,7 @@ void collect_marks(sbd_plan_s* p) {
 
 void free_plan(sbd_plan_s* p) {
     if (!p) return;
+    std::unique_lock<std::shared_mutex> lock(capture_mutex());
     cudaDeviceSynchronize();
     collect_marks(p);
     for (cudaEvent_t e : p->event_pool) cudaEventDestroy(e);
@@ -294,11 +305,14 @@ int forward_fft(sbd_plan_s* p, const cx_t<T>* X, cx_t<T>* A, cx_t<T>* Tr, cx_t<T
     const int m = np.m, nk = np.nk, n = np.n;
     const T* dec = static_cast<const T*>(p->dec);
     // along x (rows y), precorrection exp(sigma |x|^2) fused into the load
-    int rc = fft_rows<T>(X, m, m, -m / 2, A, nk, nk, -nk / 2, m, n, -1, dec, dec, nullptr, nullptr, s);
+    const int sp = p->fft_split;
+    int rc = fft_rows<T>(X, m, m, -m / 2, A, nk, nk, -nk / 2, m, n, -1, dec, dec, nullptr, nullptr, s, 0, 0, kIoPlain,
+                         sp);
     if (rc) return rc;
     if ((rc = transpose<T>(A, nk, 0, Tr, m, 0, m, nk, 1, s))) return rc;   // [y][kx] -> [kx][y]
     // along y (rows kx)
-    return fft_rows<T>(Tr, m, m, -m / 2, K, nk, nk, -nk / 2, nk, n, -1, nullptr, nullptr, nullptr, nullptr, s);
+    return fft_rows<T>(Tr, m, m, -m / 2, K, nk, nk, -nk / 2, nk, n, -1, nullptr, nullptr, nullptr, nullptr, s, 0, 0,
+                       kIoPlain, sp);
 }
 
 // frequency grid K2 (nk x nk, rows = kx) -> spreading grid X (m x m), adjoint transform.
@@ -311,11 +325,13 @@ int inverse_fft(sbd_plan_s* p, const cx_t<T>* K2, cx_t<T>* A, cx_t<T>* Tr, cx_t<
     const NufftParams& np = p->np;
     const int m = np.m, nk = np.nk, n = np.n;
     const T* dec = static_cast<const T*>(p->dec);
+    const int sp = p->fft_split;
     int rc = fft_rows<T>(K2, nk, nk, -nk / 2, A, m, m, -m / 2, nk, n, +1, nullptr, nullptr, nullptr, nullptr, s,
-                         fold ? nk : 0);
+                         fold ? nk : 0, 0, kIoPlain, sp);
     if (rc) return rc;
     if ((rc = transpose<T>(A, m, 0, Tr, nk, 0, nk, m, 1, s))) return rc;   // [kx][y] -> [y][kx]
-    return fft_rows<T>(Tr, nk, nk, -nk / 2, X, m, m, -m / 2, m, n, +1, nullptr, nullptr, dec, dec, s);
+    return fft_rows<T>(Tr, nk, nk, -nk / 2, X, m, m, -m / 2, m, n, +1, nullptr, nullptr, dec, dec, s, 0, 0, kIoPlain,
+                       sp);
 }
 
 // Real data (Laplace): the spreading grid X is real, stored as packed row pairs
@@ -332,12 +348,13 @@ int forward_fft_real(sbd_plan_s* p, const cx_t<T>* Xp, cx_t<T>* A, cx_t<T>* Tr, 
     const int m = np.m, nk = np.nk, n = np.n;
     const int lo = kx_low<T>(p), w2 = nk - lo;
     const T* dec = static_cast<const T*>(p->dec);
+    const int sp = p->fft_split;
     int rc = fft_rows<T>(Xp, m, m, -m / 2, A, w2, w2, lo - nk / 2, m / 2, n, -1, dec, dec, nullptr, nullptr, s, 0, 0,
-                         kIoPairFwd);
+                         kIoPairFwd, sp);
     if (rc) return rc;
     if ((rc = transpose<T>(A, w2, 0, Tr, m, 0, m, w2, 1, s))) return rc;   // [y][kx] -> [kx][y]
     return fft_rows<T>(Tr, m, m, -m / 2, K + static_cast<long>(lo) * nk, nk, nk, -nk / 2, w2, n, -1, nullptr, nullptr,
-                       nullptr, nullptr, s);
+                       nullptr, nullptr, s, 0, 0, kIoPlain, sp);
 }
 
 // Adjoint for real data: S (node step over the half node set) completes to
@@ -350,11 +367,13 @@ int inverse_fft_real(sbd_plan_s* p, const cx_t<T>* S, cx_t<T>* A, cx_t<T>* Tr, c
     const int m = np.m, nk = np.nk, n = np.n;
     const int J = nk / 2;
     const T* dec = static_cast<const T*>(p->dec);
+    const int sp = p->fft_split;
     int rc = fft_rows<T>(S + static_cast<long>(J) * nk, nk, nk, -nk / 2, A, m, m, -m / 2, J, n, +1, nullptr, nullptr,
-                         nullptr, nullptr, s, nk, J);
+                         nullptr, nullptr, s, nk, J, kIoPlain, sp);
     if (rc) return rc;
     if ((rc = transpose<T>(A, m, 0, Tr, J, 0, J, m, 1, s))) return rc;   // [kx][y] -> [y][kx]
-    return fft_rows<T>(Tr, J, J, 0, Xp, m, m, -m / 2, m / 2, n, +1, nullptr, nullptr, dec, dec, s, 0, 0, kIoPairInv);
+    return fft_rows<T>(Tr, J, J, 0, Xp, m, m, -m / 2, m / 2, n, +1, nullptr, nullptr, dec, dec, s, 0, 0, kIoPairInv,
+                       sp);
 }
 
 // q = far part of f (+ the internal-order near term add[i * nrhs + r] when add is given).
@@ -748,10 +767,14 @@ int sbd_matvec_graph(sbd_plan_t p, const void* f, void* q, int32_t nrhs, void* c
         if ((rc = sbd_matvec(p, p->g_in, p->g_out, nrhs, g))) return rc;
         const bool prof = p->profile;
         p->profile = false;
-        SBD_CUDA_TRY(cudaStreamBeginCapture(g, cudaStreamCaptureModeThreadLocal));
-        rc = sbd_matvec(p, p->g_in, p->g_out, nrhs, g);
         cudaGraph_t graph = nullptr;
-        const cudaError_t e = cudaStreamEndCapture(g, &graph);
+        cudaError_t e;
+        {
+            std::shared_lock<std::shared_mutex> lock(capture_mutex());
+            SBD_CUDA_TRY(cudaStreamBeginCapture(g, cudaStreamCaptureModeThreadLocal));
+            rc = sbd_matvec(p, p->g_in, p->g_out, nrhs, g);
+            e = cudaStreamEndCapture(g, &graph);
+        }
         p->profile = prof;
         if (rc) {
             if (graph) cudaGraphDestroy(graph);
@@ -783,6 +806,7 @@ int sbd_profile(sbd_plan_t p, int32_t enable) {
         set_error("null plan");
         return SBD_EINVAL;
     }
+    std::unique_lock<std::shared_mutex> sync_lock(capture_mutex());
     SBD_CUDA_TRY(cudaDeviceSynchronize());
     collect_marks(p);
     for (int i = 0; i < SBD_N_STAGES; ++i) {
@@ -852,16 +876,19 @@ int sbd_plan_info(sbd_plan_t p, sbd_plan_stats* o) {
     o->n_records = p->n_rec;
     o->node_acc = p->tuning.acc;
     o->node_sched = p->tuning.sched;
+    o->fft_split = p->fft_split;
     return SBD_OK;
 }
 
-int sbd_set_tuning(sbd_plan_t p, int32_t acc, int32_t sched) {
-    if (!p || acc < 0 || acc > 2 || sched < 0 || sched > 1 || (acc >= 1 && p->form != SBD_FORM_FP32)) {
+int sbd_set_tuning(sbd_plan_t p, int32_t acc, int32_t sched, int32_t fft_split) {
+    if (!p || acc < 0 || acc > 2 || sched < 0 || sched > 1 || (acc >= 1 && p->form != SBD_FORM_FP32) ||
+        (fft_split != 0 && fft_split != 2)) {
         set_error("sbd_set_tuning: invalid plan or variant");
         return SBD_EINVAL;
     }
     p->tuning.acc = acc;
     p->tuning.sched = sched;
+    p->fft_split = fft_split;
     return SBD_OK;
 }
 
@@ -871,9 +898,52 @@ int sbd_tune(sbd_plan_t p, int32_t reps, double* ms, void* cuda_stream) {
         return SBD_EINVAL;
     }
     if (ms)
-        for (int v = 0; v < 6; ++v) ms[v] = -1.0;
-    if (!p->node_fused) return SBD_OK;
+        for (int v = 0; v < 8; ++v) ms[v] = -1.0;
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    // row-FFT phases: time the forward transform with split 0 and 2, keep the faster
+    {
+        cudaEvent_t a, b;
+        SBD_CUDA_TRY(cudaEventCreate(&a));
+        SBD_CUDA_TRY(cudaEventCreate(&b));
+        double best = 1e300;
+        int pick = 0, rc = SBD_OK;
+        for (int sp : {0, 2}) {
+            p->fft_split = sp;
+            auto fwd = [&]() {
+                if (p->form == SBD_FORM_FP32) {
+                    auto* X = static_cast<cx_t<float>*>(p->wsX);
+                    auto* A = static_cast<cx_t<float>*>(p->wsA);
+                    auto* B = static_cast<cx_t<float>*>(p->wsB);
+                    auto* C = static_cast<cx_t<float>*>(p->wsC);
+                    return p->half_nodes ? forward_fft_real<float>(p, X, A, C, B, s) : forward_fft<float>(p, X, A, C, B, s);
+                }
+                auto* X = static_cast<cx_t<double>*>(p->wsX);
+                auto* A = static_cast<cx_t<double>*>(p->wsA);
+                auto* B = static_cast<cx_t<double>*>(p->wsB);
+                auto* C = static_cast<cx_t<double>*>(p->wsC);
+                return p->half_nodes ? forward_fft_real<double>(p, X, A, C, B, s) : forward_fft<double>(p, X, A, C, B, s);
+            };
+            if ((rc = fwd())) break;
+            cudaEventRecord(a, s);
+            for (int r = 0; r < reps && !rc; ++r) rc = fwd();
+            if (rc) break;
+            float t_ms = 0.f;
+            cudaEventRecord(b, s);
+            cudaEventSynchronize(b);
+            cudaEventElapsedTime(&t_ms, a, b);
+            const double per = static_cast<double>(t_ms) / reps;
+            if (ms) ms[sp == 0 ? 6 : 7] = per;
+            if (per < best) {
+                best = per;
+                pick = sp;
+            }
+        }
+        cudaEventDestroy(a);
+        cudaEventDestroy(b);
+        p->fft_split = pick;
+        if (rc) return rc;
+    }
+    if (!p->node_fused) return SBD_OK;
     // non-zero input: with zeros every compare-and-swap would succeed at once, which
     // hides the retries that concurrent adds to one cell cost with real data
     const long cells = static_cast<long>(p->np.nk) * p->np.nk;
@@ -955,6 +1025,7 @@ int sbd_close_export(sbd_plan_t p, int64_t* rowptr, int32_t* col, double* val) {
         set_error("null plan or buffer");
         return SBD_EINVAL;
     }
+    std::unique_lock<std::shared_mutex> sync_lock(capture_mutex());
     SBD_CUDA_TRY(cudaDeviceSynchronize());
     // the plan holds D over the internal order; map rows and columns back to the
     // caller's order (row k = internal row inv[k]), diagonal first, then by column

@@ -3,6 +3,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
+#include <shared_mutex>
 #include <string>
 
 namespace sbd {
@@ -34,6 +36,12 @@ void set_error(const std::string& msg);
 // at least `bytes`, under a process-wide lock, so that concurrent host threads launching
 // the same kernel with different sizes never shrink each other's limit.
 int raise_smem_limit_fn(const void* func, size_t bytes);
+
+// Process-wide lock between CUDA-graph capture (held shared while a thread captures) and
+// calls that synchronise with every stream of the device or may (device synchronise,
+// cudaFree, cudaMalloc, synchronous copies; held exclusive): those calls would otherwise
+// invalidate a capture running in another thread.
+std::shared_mutex& capture_mutex();
 template <typename K>
 inline int raise_smem_limit(K* kernel, size_t bytes) {
     return raise_smem_limit_fn(reinterpret_cast<const void*>(kernel), bytes);

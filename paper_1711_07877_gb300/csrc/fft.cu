@@ -52,7 +52,10 @@ const cx_t<T>* twiddles(int n, cudaStream_t stream) {
         h[t] = mk<T>(static_cast<T>(c), static_cast<T>(-s));
     }
     cx_t<T>* d = nullptr;
-    if (cudaMalloc(&d, sizeof(cx_t<T>) * n) != cudaSuccess) return nullptr;
+    {
+        std::unique_lock<std::shared_mutex> lock(capture_mutex());
+        if (cudaMalloc(&d, sizeof(cx_t<T>) * n) != cudaSuccess) return nullptr;
+    }
     cudaMemcpyAsync(d, h.data(), sizeof(cx_t<T>) * n, cudaMemcpyHostToDevice, stream);
     cudaStreamSynchronize(stream);
     cache[n] = d;
@@ -313,7 +316,10 @@ const int* digit_perm(const FftPlan1D& plan, cudaStream_t stream) {
         h[i] = pos;
     }
     int* d = nullptr;
-    if (cudaMalloc(&d, sizeof(int) * n) != cudaSuccess) return nullptr;
+    {
+        std::unique_lock<std::shared_mutex> lock(capture_mutex());
+        if (cudaMalloc(&d, sizeof(int) * n) != cudaSuccess) return nullptr;
+    }
     cudaMemcpyAsync(d, h.data(), sizeof(int) * n, cudaMemcpyHostToDevice, stream);
     cudaStreamSynchronize(stream);
     cache[n] = d;
@@ -387,7 +393,7 @@ int fft_rows(const cx_t<T>* in, long in_stride, int in_len, int in_shift,
              cx_t<T>* out, long out_stride, int out_len, int out_shift,
              int rows, int n, int sign,
              const T* pre_elem, const T* pre_row, const T* post_elem, const T* post_row,
-             cudaStream_t stream, int herm_n, int herm_row0, int io) {
+             cudaStream_t stream, int herm_n, int herm_row0, int io, int split) {
     if (rows <= 0) return SBD_OK;
     if (herm_n && (herm_row0 < 0 || herm_row0 + rows > herm_n || in_len != herm_n || io != kIoPlain)) {
         set_error("fft_rows: a Hermitian fold needs rows inside a square grid read whole");
@@ -398,7 +404,7 @@ int fft_rows(const cx_t<T>* in, long in_stride, int in_len, int in_shift,
         return SBD_EINVAL;
     }
     const bool fp64 = sizeof(T) == 8;
-    const int Q = fft_phases(n, fp64);
+    const int Q = split == 2 && n % 2 == 0 ? 2 : fft_phases(n, fp64);
     const int nq = n / Q;
     FftPlan1D plan;
     if (!fft_make_plan(nq, plan) || nq > fft_max_row(fp64) || n % Q) {
@@ -425,7 +431,14 @@ int fft_rows(const cx_t<T>* in, long in_stride, int in_len, int in_shift,
         const T* por = post_row ? post_row + r0 * (io == kIoPairInv ? 2 : 1) : nullptr;
         const HermFold<T> hf{in - static_cast<long>(herm_row0) * in_stride, herm_n,
                              static_cast<long>(herm_row0) + r0};
-        if (nq > 2048) {
+        if (nq > 2048 && split == 2) {
+            // half-length phases: two CTAs of 512 threads share an SM (registers and shared
+            // memory both allow it), instead of one 1024-thread CTA per full-length row
+            auto k = fft_rows_kernel<T, 512>;
+            SBD_TRY(raise_smem_limit(k, smem));
+            k<<<grid, 512, smem, stream>>>(ip, in_stride, in_len, in_shift, op, out_stride, out_len, out_shift,
+                                           n, Q, sign, plan, tw, perm, pre_elem, prr, post_elem, por, hf, io);
+        } else if (nq > 2048) {
             auto k = fft_rows_kernel<T, 1024>;
             SBD_TRY(raise_smem_limit(k, smem));
             k<<<grid, 1024, smem, stream>>>(ip, in_stride, in_len, in_shift, op, out_stride, out_len, out_shift,
@@ -487,10 +500,10 @@ int transpose(const cx_t<T>* in, long in_stride, long in_batch, cx_t<T>* out, lo
 
 template int fft_rows<float>(const float2*, long, int, int, float2*, long, int, int, int, int, int,
                              const float*, const float*, const float*, const float*, cudaStream_t, int, int,
-                             int);
+                             int, int);
 template int fft_rows<double>(const double2*, long, int, int, double2*, long, int, int, int, int, int,
                               const double*, const double*, const double*, const double*, cudaStream_t, int, int,
-                              int);
+                              int, int);
 template int fft_rows_tables<float>(const float2*, long, int, float2*, long, int, int, int, int, const float2*,
                                     const int*, cudaStream_t);
 template int fft_rows_tables<double>(const double2*, long, int, double2*, long, int, int, int, int, const double2*,

@@ -50,7 +50,7 @@ class sbd_plan_stats(ctypes.Structure):
                 ("a", ctypes.c_double), ("fit_err", ctypes.c_double), ("nufft_tol", ctypes.c_double),
                 ("w0_re", ctypes.c_double), ("w0_im", ctypes.c_double), ("device_bytes", ctypes.c_int64),
                 ("plan_seconds", ctypes.c_double), ("n_records", ctypes.c_int64), ("node_acc", ctypes.c_int32),
-                ("node_sched", ctypes.c_int32)]
+                ("node_sched", ctypes.c_int32), ("fft_split", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -69,7 +69,7 @@ _I32, _I64, _D = ctypes.c_int32, ctypes.c_int64, ctypes.c_double
 _SIGS = {
     "sbd_fit_cache_stats": ([_P, _P, _P], ctypes.c_int),
     "sbd_tune": ([_P, _I32, _P, _P], ctypes.c_int),
-    "sbd_set_tuning": ([_P, _I32, _I32], ctypes.c_int),
+    "sbd_set_tuning": ([_P, _I32, _I32, _I32], ctypes.c_int),
     "sbd_fit_cache_clear": ([], ctypes.c_int),
     "sbd_y0_root": ([_I32, _P], ctypes.c_int),
     "sbd_plan": ([_P, _I64, sbd_kernel, _D, _D, ctypes.POINTER(sbd_options), _P, ctypes.POINTER(_P)], ctypes.c_int),
@@ -265,13 +265,13 @@ def sbd_fit_cache_stats() -> dict:
 def sbd_tune(plan: int, reps: int = 3, stream=None) -> list:
     """Time the node-kernel variants, keep the fastest; returns ms per variant (acc * 2 + sched)."""
     import numpy as np
-    ms = np.zeros(6)
+    ms = np.zeros(8)
     _check(lib.sbd_tune(plan, reps, ms.ctypes.data, _stream(stream)), "sbd_tune")
     return ms.tolist()
 
 
-def sbd_set_tuning(plan: int, acc: int, sched: int) -> None:
-    _check(lib.sbd_set_tuning(plan, acc, sched), "sbd_set_tuning")
+def sbd_set_tuning(plan: int, acc: int, sched: int, fft_split: int = 0) -> None:
+    _check(lib.sbd_set_tuning(plan, acc, sched, fft_split), "sbd_set_tuning")
 
 
 def sbd_y0_root(k: int) -> float:

@@ -135,6 +135,7 @@ def test_server_results_match_solo_solves(S):
                                   kappa=kappa, delta_min=dmin, eps=1e-10, shift=1.0, scale=1.0 / n))
         solo.append(solve_gpu(S, z, kind, kappa, dmin, 1e-10, b, 0, tol, 1.0, 1.0 / n)[0])
     srv, summary = serve.run_poisson(reqs, mean_gap_s=0.004, seed=5, slots=3, form=S.SBD_FORM_FP64, tol=tol)
+    assert [r.error for r in reqs] == [None] * len(reqs)
     assert summary["requests"] == len(specs)
     assert 0 < summary["p50_ms"] <= summary["p99_ms"]
     assert summary["gpts_per_s"] > 0

@@ -42,14 +42,15 @@ def test_variants_agree_and_tune_picks_one(S, kind):
         outs = {}
         for acc in (0, 1, 2):
             for sched in (0, 1):
-                S.sbd_set_tuning(p, acc, sched)
-                info = S.sbd_plan_info(p)
-                assert (info["node_acc"], info["node_sched"]) == (acc, sched)
-                q = torch.empty_like(ft)
-                S.sbd_matvec(p, ft, q)
-                torch.cuda.synchronize()
-                outs[(acc, sched)] = q.cpu().numpy()
-        base = outs[(0, 0)]
+                for split in (0, 2):
+                    S.sbd_set_tuning(p, acc, sched, split)
+                    info = S.sbd_plan_info(p)
+                    assert (info["node_acc"], info["node_sched"], info["fft_split"]) == (acc, sched, split)
+                    q = torch.empty_like(ft)
+                    S.sbd_matvec(p, ft, q)
+                    torch.cuda.synchronize()
+                    outs[(acc, sched, split)] = q.cpu().numpy()
+        base = outs[(0, 0, 0)]
         for k, v in outs.items():
             assert np.linalg.norm(v - base) / np.linalg.norm(base) < 2e-6, k
         idx = np.random.default_rng(5).choice(n, 300, replace=False)
@@ -57,9 +58,9 @@ def test_variants_agree_and_tune_picks_one(S, kind):
         for k, v in outs.items():
             assert np.max(np.abs(v[idx] - ref)) <= 1e-6 * np.abs(f).sum(), k
         ms = S.sbd_tune(p, reps=2)
-        assert len(ms) == 6 and all(t > 0 for t in ms)
+        assert len(ms) == 8 and all(t > 0 for t in ms)
         info = S.sbd_plan_info(p)
-        best = int(np.argmin(ms))
+        best = int(np.argmin(ms[:6]))
         assert (info["node_acc"], info["node_sched"]) == (best // 2, best % 2)
     finally:
         S.sbd_destroy(p)
@@ -72,9 +73,9 @@ def test_fp64_rejects_cas_variant(S):
     try:
         for acc in (1, 2):
             with pytest.raises(S.SbdError) as e:
-                S.sbd_set_tuning(p, acc, 0)
+                S.sbd_set_tuning(p, acc, 0, 0)
             assert e.value.code == S.SBD_EINVAL
         ms = S.sbd_tune(p, reps=1)
-        assert ms[0] > 0 and ms[1] > 0 and all(t == -1 for t in ms[2:])
+        assert ms[0] > 0 and ms[1] > 0 and all(t == -1 for t in ms[2:6]) and ms[6] > 0 and ms[7] > 0
     finally:
         S.sbd_destroy(p)
