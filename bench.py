@@ -41,7 +41,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--form", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--workload", default="laplace_curves",
-                    choices=["laplace_curves", "helmholtz_curves", "laplace_square", "serve"])
+                    choices=["laplace_curves", "helmholtz_curves", "laplace_square", "serve", "batch"])
+    ap.add_argument("--instances", type=int, default=64, help="batch: number of plans in the graph")
     ap.add_argument("--n", type=int, default=0, help="points (0: the workload's own size)")
     ap.add_argument("--nrhs", type=int, default=0, help="right-hand sides (0: the workload's own)")
     ap.add_argument("--requests", type=int, default=256, help="serve: number of solve requests")
@@ -263,6 +264,9 @@ def main():
     if args.workload == "serve":
         run_serve(args, rank, world, local)
         return
+    if args.workload == "batch":
+        run_batch(args, rank, world, local)
+        return
     import numpy as np
     import torch
     import torch.distributed as dist
@@ -381,6 +385,88 @@ def main():
         print(json.dumps(out))
     if world > 1:
         dist.destroy_process_group()
+
+
+def run_batch(args, rank, world, local):
+    """Many small plans of uneven size: one batch-graph launch against one matvec after another."""
+    import torch
+
+    import paper_1711_07877_gb300 as S
+    import workloads as W
+
+    torch.cuda.set_device(local)
+    rng = np.random.default_rng(11 + rank)
+    form = S.SBD_FORM_FP32 if args.form == "fp32" else S.SBD_FORM_FP64
+    plans, fs, qs, ns = [], [], [], []
+    for i in range(args.instances):
+        n = int(round(math.exp(rng.uniform(math.log(1e3), math.log(1e5)))))
+        z = W.curve_points(n, 20_000 + 100 * rank + i)
+        dmax = W.enclosing_diameter(z)
+        p = S.sbd_plan(torch.from_numpy(z).cuda(), n, S.SBD_LAPLACE, 0.0, W.theorem1_delta_min(n, args.eps, dmax),
+                       args.eps, S.make_options(form=form))
+        plans.append(p)
+        ns.append(n)
+        fs.append(torch.from_numpy(W.rhs(n, 30_000 + i)).cuda())
+        qs.append(torch.empty_like(fs[-1]))
+    units = sum(ns)
+    stream = torch.cuda.current_stream()
+    b = S.sbd_batch_create(plans, fs, qs)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / args.steps
+
+    def seq():
+        for p, f, q in zip(plans, fs, qs):
+            S.sbd_matvec(p, f, q, 1, stream.cuda_stream)
+
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(local).uuid)
+    except Exception:
+        pass
+    clocks = ClockSampler(uuid)
+    clocks.start()
+    ms_batch = max_over_ranks(timed(lambda: S.sbd_batch_launch(b, stream.cuda_stream)), world, "cuda")
+    ms_seq = max_over_ranks(timed(seq), world, "cuda")
+    clk = clocks.stop()
+    # end to end: host f in, batch launch, host q out (pinned buffers)
+    fh = [f.cpu().pin_memory() for f in fs]
+    qh = [torch.empty_like(x).pin_memory() for x in fh]
+
+    def e2e():
+        for f, h in zip(fs, fh):
+            f.copy_(h, non_blocking=True)
+        S.sbd_batch_launch(b, stream.cuda_stream)
+        for q, h in zip(qs, qh):
+            h.copy_(q, non_blocking=True)
+    ms_e2e = max_over_ranks(timed(e2e), world, "cuda")
+    S.sbd_batch_destroy(b)
+    for p in plans:
+        S.sbd_destroy(p)
+    out = {"metric": METRIC, "value": job_rate(units, world, ms_batch), "unit": UNIT, "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_batch, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.form == "fp32" else "f64",
+           "data": "synthetic",
+           "config": {"workload": f"batch of {args.instances} Laplace plans, N log-uniform in [1e3, 1e5] on curve "
+                                  f"geometries, eps={args.eps:g}, one CUDA-graph launch per step",
+                      "instances": args.instances, "points_total": units, "form": args.form,
+                      "l2_policy": "per-instance grids small; the whole batch exceeds L2"},
+           "sequential": {"ms_per_step": ms_seq, "value": job_rate(units, world, ms_seq),
+                          "note": "the same matvecs, one sbd_matvec after another on one stream"},
+           "e2e": {"value": job_rate(units, world, ms_e2e), "unit": UNIT, "h2d_bytes_per_step": 8 * units,
+                   "d2h_bytes_per_step": 8 * units},
+           "clocks": clk, "roofline": None, "gpu_launches": 11 * args.instances}
+    if rank == 0:
+        print(json.dumps(out))
 
 
 def run_serve(args, rank, world, local):

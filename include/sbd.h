@@ -159,6 +159,27 @@ int sbd_matvec(sbd_plan_t plan, const void* f, void* q, int32_t nrhs, void* cuda
  * Errors: as sbd_matvec, and SBD_ECUDA if capture or instantiation fails. */
 int sbd_matvec_graph(sbd_plan_t plan, const void* f, void* q, int32_t nrhs, void* cuda_stream);
 
+/* ---------------------------------------------------------------------------------
+ * Batches of instances (no counterpart in the paper): the matvecs of several plans in
+ * one CUDA graph, each plan on its own branch, so that one launch runs instances of
+ * uneven size side by side on the device.
+ *   sbd_batch_create   plans[count] (distinct), nrhs[i] (1..max_nrhs of plan i), device
+ *                      buffers f[i], q[i] (layout of sbd_matvec) that stay valid and fixed
+ *                      while the batch lives; runs one matvec per plan, then captures the
+ *                      graph.  Blocks until done.
+ *   sbd_batch_launch   q[i] = matvec of plan i on f[i] for every i, one graph launch,
+ *                      asynchronous on cuda_stream.  The plans must not be used elsewhere
+ *                      while a launch runs (their workspace is in the graph).
+ *   sbd_batch_destroy  frees the graph (not the plans).  NULL-safe.
+ * Errors: SBD_EINVAL (null pointers, count < 1, a plan twice, nrhs out of range),
+ * SBD_ECUDA (capture or instantiation failed), and those of sbd_matvec.
+ * ------------------------------------------------------------------------------- */
+typedef struct sbd_batch_s* sbd_batch_t;
+int sbd_batch_create(const sbd_plan_t* plans, const int32_t* nrhs, int32_t count, const void* const* f,
+                     void* const* q, sbd_batch_t* out);
+int sbd_batch_launch(sbd_batch_t batch, void* cuda_stream);
+int sbd_batch_destroy(sbd_batch_t batch);
+
 /* The two halves of sbd_matvec, same arguments and layout:
  *   sbd_far   q = NUFFT_+(omega_hat . NUFFT_-(f))   (Eq. far convolution, incl. the xi = 0 term)
  *   sbd_close q = D f                               (Sec. 1, close correction)                  */

@@ -1066,6 +1066,124 @@ int sbd_destroy(sbd_plan_t p) {
     return SBD_OK;
 }
 
+// A batch: one CUDA graph holding the matvecs of several plans, each on its own branch
+// (forked from the launch stream with events, joined at the end), so one launch runs
+// instances of uneven size side by side on the device.
+struct sbd_batch_s {
+    cudaGraphExec_t exec = nullptr;
+    int count = 0;
+};
+
+int sbd_batch_create(const sbd_plan_t* plans, const int32_t* nrhs, int32_t count, const void* const* f,
+                     void* const* q, sbd_batch_t* out) {
+    if (!plans || !nrhs || !f || !q || !out || count < 1) {
+        set_error("sbd_batch_create: null argument or count < 1");
+        return SBD_EINVAL;
+    }
+    for (int i = 0; i < count; ++i) {
+        if (!plans[i] || !f[i] || !q[i] || nrhs[i] < 1 || nrhs[i] > plans[i]->max_nrhs) {
+            set_error("sbd_batch_create: invalid entry " + std::to_string(i));
+            return SBD_EINVAL;
+        }
+        for (int j = 0; j < i; ++j)
+            if (plans[j] == plans[i]) {
+                set_error("sbd_batch_create: a plan appears twice (its workspace is shared)");
+                return SBD_EINVAL;
+            }
+    }
+    cudaStream_t origin = nullptr;
+    std::vector<cudaStream_t> br(count, nullptr);
+    std::vector<cudaEvent_t> ev(count + 1, nullptr);
+    auto cleanup = [&]() {
+        for (cudaStream_t x : br)
+            if (x) cudaStreamDestroy(x);
+        for (cudaEvent_t e : ev)
+            if (e) cudaEventDestroy(e);
+        if (origin) cudaStreamDestroy(origin);
+    };
+    int rc = SBD_OK;
+    SBD_CUDA_TRY(cudaStreamCreateWithFlags(&origin, cudaStreamNonBlocking));
+    for (int i = 0; i < count; ++i) {
+        if (cudaStreamCreateWithFlags(&br[i], cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming) != cudaSuccess) {
+            cleanup();
+            set_error("sbd_batch_create: stream or event creation failed");
+            return SBD_ECUDA;
+        }
+    }
+    if (cudaEventCreateWithFlags(&ev[count], cudaEventDisableTiming) != cudaSuccess) {
+        cleanup();
+        set_error("sbd_batch_create: event creation failed");
+        return SBD_ECUDA;
+    }
+    // one plain matvec per plan first: creates every table the kernels use
+    for (int i = 0; i < count && !rc; ++i) rc = sbd_matvec(plans[i], f[i], q[i], nrhs[i], br[i]);
+    for (int i = 0; i < count; ++i) cudaStreamSynchronize(br[i]);
+    if (rc) {
+        cleanup();
+        return rc;
+    }
+    std::vector<bool> prof(count);
+    for (int i = 0; i < count; ++i) {
+        prof[i] = plans[i]->profile;
+        plans[i]->profile = false;
+    }
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaSuccess;
+    {
+        std::shared_lock<std::shared_mutex> lock(capture_mutex());
+        e = cudaStreamBeginCapture(origin, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[count], origin);
+        for (int i = 0; i < count && e == cudaSuccess && !rc; ++i) {
+            e = cudaStreamWaitEvent(br[i], ev[count], 0);               // fork
+            if (e == cudaSuccess) rc = sbd_matvec(plans[i], f[i], q[i], nrhs[i], br[i]);
+            if (e == cudaSuccess && !rc) e = cudaEventRecord(ev[i], br[i]);
+            if (e == cudaSuccess && !rc) e = cudaStreamWaitEvent(origin, ev[i], 0);   // join
+        }
+        const cudaError_t e2 = cudaStreamEndCapture(origin, &graph);
+        if (e == cudaSuccess) e = e2;
+    }
+    for (int i = 0; i < count; ++i) plans[i]->profile = prof[i];
+    if (rc || e != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        cleanup();
+        if (!rc) {
+            set_error(std::string("sbd_batch_create: capture failed: ") + cudaGetErrorString(e));
+            rc = SBD_ECUDA;
+        }
+        return rc;
+    }
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    cleanup();
+    if (e != cudaSuccess) {
+        set_error(std::string("sbd_batch_create: instantiate failed: ") + cudaGetErrorString(e));
+        return SBD_ECUDA;
+    }
+    auto* b = new sbd_batch_s();
+    b->exec = exec;
+    b->count = count;
+    *out = b;
+    return SBD_OK;
+}
+
+int sbd_batch_launch(sbd_batch_t b, void* cuda_stream) {
+    if (!b) {
+        set_error("sbd_batch_launch: null batch");
+        return SBD_EINVAL;
+    }
+    SBD_CUDA_TRY(cudaGraphLaunch(b->exec, static_cast<cudaStream_t>(cuda_stream)));
+    return SBD_OK;
+}
+
+int sbd_batch_destroy(sbd_batch_t b) {
+    if (!b) return SBD_OK;
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    delete b;
+    return SBD_OK;
+}
+
 int sbd_fft2(const void* in, void* out, int32_t n0, int32_t n1, int32_t sign, int32_t form, void* cuda_stream) {
     if (!in || !out || n0 < 2 || n1 < 2 || n0 > 65536 || n1 > 65536 || (sign != 1 && sign != -1) ||
         (form != SBD_FORM_FP32 && form != SBD_FORM_FP64)) {

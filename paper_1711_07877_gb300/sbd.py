@@ -75,6 +75,9 @@ _SIGS = {
     "sbd_plan": ([_P, _I64, sbd_kernel, _D, _D, ctypes.POINTER(sbd_options), _P, ctypes.POINTER(_P)], ctypes.c_int),
     "sbd_matvec": ([_P, _P, _P, _I32, _P], ctypes.c_int),
     "sbd_matvec_graph": ([_P, _P, _P, _I32, _P], ctypes.c_int),
+    "sbd_batch_create": ([_P, _P, _I32, _P, _P, ctypes.POINTER(_P)], ctypes.c_int),
+    "sbd_batch_launch": ([_P, _P], ctypes.c_int),
+    "sbd_batch_destroy": ([_P], ctypes.c_int),
     "sbd_far": ([_P, _P, _P, _I32, _P], ctypes.c_int),
     "sbd_close": ([_P, _P, _P, _I32, _P], ctypes.c_int),
     "sbd_nufft_minus": ([_P, _P, _P, _P], ctypes.c_int),
@@ -161,6 +164,27 @@ def sbd_matvec(plan: int, f, q, nrhs: int = 1, stream=None) -> None:
 
 def sbd_matvec_graph(plan: int, f, q, nrhs: int = 1, stream=None) -> None:
     _check(lib.sbd_matvec_graph(plan, _ptr(f), _ptr(q), nrhs, _stream(stream)), "sbd_matvec_graph")
+
+
+def sbd_batch_create(plans, f, q, nrhs=None) -> int:
+    """One CUDA graph with the matvecs of several plans (f[i], q[i] device tensors that stay put)."""
+    k = len(plans)
+    nrhs = nrhs or [1] * k
+    P = (_P * k)(*plans)
+    R = (_I32 * k)(*nrhs)
+    F = (_P * k)(*[_ptr(x) for x in f])
+    Qp = (_P * k)(*[_ptr(x) for x in q])
+    out = _P()
+    _check(lib.sbd_batch_create(P, R, k, F, Qp, ctypes.byref(out)), "sbd_batch_create")
+    return out.value
+
+
+def sbd_batch_launch(batch: int, stream=None) -> None:
+    _check(lib.sbd_batch_launch(batch, _stream(stream)), "sbd_batch_launch")
+
+
+def sbd_batch_destroy(batch: int) -> None:
+    _check(lib.sbd_batch_destroy(batch), "sbd_batch_destroy")
 
 
 def sbd_far(plan: int, f, q, nrhs: int = 1, stream=None) -> None:
