@@ -44,6 +44,61 @@ __global__ void tile_scatter_kernel(const Rec* __restrict__ in, long n, int ntx,
     perm[pos] = static_cast<int>(i);
 }
 
+// Deterministic order inside each tile: the records of a tile (in the nondeterministic
+// order of the scatter above) sorted by their original index with a bitonic sort in
+// shared memory, so that a plan's records, and therefore its FP32 sums, are the same on
+// every run, and consecutive records of a tile run along a circle.  Tiles with more than
+// kTileSortCap records keep the scatter order.
+constexpr int kTileSortCap = 4096;
+
+template <typename Rec>
+__global__ void __launch_bounds__(256) tile_order_kernel(const Rec* __restrict__ tmp, const int* __restrict__ tmp_perm,
+                                                         const long long* __restrict__ start, Rec* __restrict__ out,
+                                                         int* __restrict__ perm) {
+    __shared__ int key[kTileSortCap];
+    __shared__ short idx[kTileSortCap];
+    const long long b = start[blockIdx.x], e = start[blockIdx.x + 1];
+    const int c = static_cast<int>(e - b);
+    if (c == 0) return;                                   // uniform per block
+    if (c > kTileSortCap) {                               // uniform per block
+        for (long long i = b + threadIdx.x; i < e; i += blockDim.x) {
+            out[i] = tmp[i];
+            perm[i] = tmp_perm[i];
+        }
+        return;
+    }
+    int L = 1;
+    while (L < c) L <<= 1;
+    for (int i = threadIdx.x; i < L; i += blockDim.x) {
+        key[i] = i < c ? tmp_perm[b + i] : 0x7fffffff;
+        idx[i] = static_cast<short>(i);
+    }
+    __syncthreads();
+    for (int k = 2; k <= L; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = threadIdx.x; i < L; i += blockDim.x) {
+                const int ixj = i ^ j;
+                if (ixj > i) {
+                    const bool up = (i & k) == 0;
+                    if ((key[i] > key[ixj]) == up) {
+                        const int tk = key[i];
+                        key[i] = key[ixj];
+                        key[ixj] = tk;
+                        const short ti = idx[i];
+                        idx[i] = idx[ixj];
+                        idx[ixj] = ti;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    for (int i = threadIdx.x; i < c; i += blockDim.x) {
+        out[b + i] = tmp[b + idx[i]];
+        perm[b + i] = key[i];
+    }
+}
+
 // Stencil weights of the group's lane: w(sub - P/2 + 1 - frac) along both dimensions.
 template <typename T>
 __device__ __forceinline__ void lane_weights(int sub, int P, const Window<T>& win, T fx, T fy, T& wx, T& wy) {
@@ -510,8 +565,16 @@ int tile_sort(const Rec* in, long n_rec, int n, Rec* sorted, int* perm, long lon
     int rc = scan_exclusive_i64(tile_start, ntiles + 1, &total, s);
     if (rc) return rc;
     if (n_rec > 0) {
-        tile_scatter_kernel<Rec><<<nb, 256, 0, s>>>(in, n_rec, ntx, tile_start, cursor, sorted, perm);
+        Rec* tmp = nullptr;
+        int* tmp_perm = nullptr;
+        SBD_CUDA_TRY(cudaMallocAsync(&tmp, sizeof(Rec) * n_rec, s));
+        SBD_CUDA_TRY(cudaMallocAsync(&tmp_perm, sizeof(int) * n_rec, s));
+        tile_scatter_kernel<Rec><<<nb, 256, 0, s>>>(in, n_rec, ntx, tile_start, cursor, tmp, tmp_perm);
         SBD_LAUNCH_CHECK();
+        tile_order_kernel<Rec><<<static_cast<unsigned>(ntiles), 256, 0, s>>>(tmp, tmp_perm, tile_start, sorted, perm);
+        SBD_LAUNCH_CHECK();
+        SBD_CUDA_TRY(cudaFreeAsync(tmp, s));
+        SBD_CUDA_TRY(cudaFreeAsync(tmp_perm, s));
     }
     SBD_CUDA_TRY(cudaFreeAsync(cursor, s));
     return SBD_OK;
