@@ -500,7 +500,7 @@ def run_serve(args, rank, world, local):
     clocks.start()
     torch.cuda.synchronize()
     srv, summ = serve.run_poisson(reqs, mean_gap_s=0.002, seed=9 + rank, slots=args.slots, form=form, tol=1e-6,
-                                  max_iter=600)
+                                  max_iter=600, timeout_s=600.0)
     torch.cuda.synchronize()
     clk = clocks.stop()
     ok = [r for r in reqs if r.error is None]
@@ -518,7 +518,8 @@ def run_serve(args, rank, world, local):
                                   "(I/2 + (L/N) A) x = b (L = arc length) to relative residual 1e-6, GMRES(30)",
                       "slots": args.slots, "eps": args.eps, "form": args.form, "l2_policy": "n/a (serving)"},
            "latency": {"p50_ms": summ.get("p50_ms"), "p99_ms": summ.get("p99_ms"), "mean_ms": summ.get("mean_ms")},
-           "served": {"requests_ok": len(ok), "errors": len(reqs) - len(ok), "wall_s": summ.get("wall_s"),
+           "served": {"requests_ok": len(ok), "errors": len(reqs) - len(ok), "incomplete": summ.get("incomplete"),
+                      "wall_s": summ.get("wall_s"),
                       "matvecs_mean": float(np.mean(its)) if its else None,
                       "matvecs_max": int(max(its)) if its else None,
                       "points_mean": float(np.mean([len(r.z) for r in ok])) if ok else None,

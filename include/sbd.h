@@ -215,8 +215,14 @@ int sbd_plan_export(sbd_plan_t plan, int64_t cap, double* rho, double* alpha, in
  * row is unspecified.  Synchronous. */
 int sbd_close_export(sbd_plan_t plan, int64_t* rowptr, int32_t* col, double* val);
 
-/* Release the plan (NULL is accepted).  Waits for the plan's device work. */
+/* Release the plan (NULL is accepted).  sbd_destroy first waits for the whole device, so
+ * any pending use of the plan on any stream is safe.  sbd_destroy_async waits only for
+ * the plan's own graph stream and orders the frees on cuda_stream after the caller's work
+ * there: every other use of the plan must already be complete or ordered before that
+ * point on cuda_stream.  Plan memory is stream-ordered and returns to the device's memory
+ * pool (kept, not released to the system, so that later plans reuse it). */
 int sbd_destroy(sbd_plan_t plan);
+int sbd_destroy_async(sbd_plan_t plan, void* cuda_stream);
 
 /* ---------------------------------------------------------------------------------
  * sbd_offline_fit - the SBD fit and circle sizes alone, on the host (Sec. 3.2

@@ -106,6 +106,7 @@ struct sbd_plan_s {
     std::vector<cudaGraphExec_t> g_exec;
     cudaStream_t g_stream = nullptr;
     cudaEvent_t g_ev_in = nullptr, g_ev_out = nullptr;
+    cudaStream_t alloc_stream = nullptr;   // stream of the allocations being made
     long long device_bytes = 0;
     double plan_seconds = 0.0;
     std::vector<void*> allocations;
@@ -120,15 +121,15 @@ struct sbd_plan_s {
 
 namespace {
 
+// Plan memory is stream-ordered (cudaMallocAsync on the stream the plan is being built or
+// extended on, p->alloc_stream; cudaFreeAsync on destroy), so that building and destroying
+// plans never synchronises the whole device, and freed memory stays in the device's pool
+// for the next plan.
 int dev_alloc(sbd_plan_s* p, void** ptr, size_t bytes) {
     bytes = std::max<size_t>(bytes, 16);
-    cudaError_t e;
-    {
-        std::unique_lock<std::shared_mutex> lock(capture_mutex());
-        e = cudaMalloc(ptr, bytes);
-    }
+    const cudaError_t e = cudaMallocAsync(ptr, bytes, p->alloc_stream);
     if (e != cudaSuccess) {
-        set_error(std::string("cudaMalloc(") + std::to_string(bytes) + "): " + cudaGetErrorString(e));
+        set_error(std::string("cudaMallocAsync(") + std::to_string(bytes) + "): " + cudaGetErrorString(e));
         cudaGetLastError();
         return e == cudaErrorMemoryAllocation ? SBD_ENOMEM : SBD_ECUDA;
     }
@@ -191,10 +192,17 @@ void collect_marks(sbd_plan_s* p) {
     p->marks.clear();
 }
 
-void free_plan(sbd_plan_s* p) {
+// Frees the plan.  wait_device: first wait for the whole device (sbd_destroy, safe for any
+// use of the plan on any stream); otherwise the frees are ordered on stream s after the
+// caller's work there (sbd_destroy_async), with only this plan's own graph stream waited for.
+void free_plan(sbd_plan_s* p, bool wait_device, cudaStream_t s) {
     if (!p) return;
-    std::unique_lock<std::shared_mutex> lock(capture_mutex());
-    cudaDeviceSynchronize();
+    if (wait_device) {
+        std::unique_lock<std::shared_mutex> lock(capture_mutex());
+        cudaDeviceSynchronize();
+    } else if (p->g_stream) {
+        cudaStreamSynchronize(p->g_stream);
+    }
     collect_marks(p);
     for (cudaEvent_t e : p->event_pool) cudaEventDestroy(e);
     for (cudaGraphExec_t g : p->g_exec)
@@ -202,11 +210,26 @@ void free_plan(sbd_plan_s* p) {
     if (p->g_ev_in) cudaEventDestroy(p->g_ev_in);
     if (p->g_ev_out) cudaEventDestroy(p->g_ev_out);
     if (p->g_stream) cudaStreamDestroy(p->g_stream);
-    for (void* a : p->allocations) cudaFree(a);
-    if (p->rowptr) cudaFree(p->rowptr);
-    if (p->col) cudaFree(p->col);
-    if (p->val) cudaFree(p->val);
+    for (void* a : p->allocations) cudaFreeAsync(a, s);
+    if (p->rowptr) cudaFreeAsync(p->rowptr, s);
+    if (p->col) cudaFreeAsync(p->col, s);
+    if (p->val) cudaFreeAsync(p->val, s);
+    if (wait_device) cudaStreamSynchronize(s);
     delete p;
+}
+
+// Keep freed plan memory in the device's default pool (plans of a server come and go).
+void keep_pool_memory() {
+    static std::once_flag once;
+    std::call_once(once, []() {
+        int dev = 0;
+        cudaMemPool_t pool;
+        if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+            unsigned long long keep = ~0ull;
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        }
+        cudaGetLastError();
+    });
 }
 
 template <typename T>
@@ -568,14 +591,17 @@ int sbd_plan(const double* points, int64_t n, sbd_kernel kernel, double delta_mi
         return SBD_EINVAL;
     }
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    keep_pool_memory();
     auto* p = new sbd_plan_s();
+    p->alloc_stream = s;
     p->kind = kernel.kind;
     p->kappa = kernel.kappa;
     p->form = o.form;
     p->n = static_cast<long>(n);
     p->max_nrhs = std::max(1, o.max_nrhs);
     auto fail = [&](int rc) {
-        free_plan(p);
+        free_plan(p, false, s);
+        cudaStreamSynchronize(s);
         return rc;
     };
     int rc = dev_alloc(p, reinterpret_cast<void**>(&p->z), sizeof(double) * 2 * n);
@@ -753,6 +779,7 @@ int sbd_matvec_graph(sbd_plan_t p, const void* f, void* q, int32_t nrhs, void* c
         SBD_CUDA_TRY(cudaEventCreateWithFlags(&p->g_ev_in, cudaEventDisableTiming));
         SBD_CUDA_TRY(cudaEventCreateWithFlags(&p->g_ev_out, cudaEventDisableTiming));
         const size_t cap = (p->kind == SBD_HELMHOLTZ ? 16 : 8) * static_cast<size_t>(p->n) * p->max_nrhs;
+        p->alloc_stream = p->g_stream;
         if ((rc = dev_alloc(p, &p->g_in, cap)) || (rc = dev_alloc(p, &p->g_out, cap))) return rc;
         p->g_exec.assign(p->max_nrhs + 1, nullptr);
     }
@@ -1062,7 +1089,12 @@ int sbd_close_export(sbd_plan_t p, int64_t* rowptr, int32_t* col, double* val) {
 }
 
 int sbd_destroy(sbd_plan_t p) {
-    free_plan(p);
+    free_plan(p, true, nullptr);
+    return SBD_OK;
+}
+
+int sbd_destroy_async(sbd_plan_t p, void* cuda_stream) {
+    free_plan(p, false, static_cast<cudaStream_t>(cuda_stream));
     return SBD_OK;
 }
 

@@ -449,10 +449,7 @@ int near_build(const double* z, long n, double delta_min, double bx0, double by0
     SBD_LAUNCH_CHECK();
     const double d2 = delta_min * delta_min;
     long long* rowptr = nullptr;
-    {
-        std::unique_lock<std::shared_mutex> lock(capture_mutex());
-        SBD_CUDA_TRY(cudaMalloc(&rowptr, sizeof(long long) * (n + 1)));
-    }
+    SBD_CUDA_TRY(cudaMallocAsync(&rowptr, sizeof(long long) * (n + 1), s));
     SBD_CUDA_TRY(cudaMemsetAsync(rowptr, 0, sizeof(long long) * (n + 1), s));
     neighbour_count_kernel<<<nblk(n), kT, 0, s>>>(z, n, g, d2, cstart, sorted, rowptr);
     SBD_LAUNCH_CHECK();
@@ -461,11 +458,8 @@ int near_build(const double* z, long n, double delta_min, double bx0, double by0
     if (rc) return rc;
     int* col = nullptr;
     void* val = nullptr;
-    {
-        std::unique_lock<std::shared_mutex> lock(capture_mutex());
-        SBD_CUDA_TRY(cudaMalloc(&col, sizeof(int) * std::max<long long>(nnz, 1)));
-        SBD_CUDA_TRY(cudaMalloc(&val, (cval ? 16 : 8) * std::max<long long>(nnz, 1)));
-    }
+    SBD_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&col), sizeof(int) * std::max<long long>(nnz, 1), s));
+    SBD_CUDA_TRY(cudaMallocAsync(&val, (cval ? 16 : 8) * std::max<long long>(nnz, 1), s));
     neighbour_fill_kernel<<<nblk(n, 128), 128, 0, s>>>(z, n, g, d2, cstart, sorted, rowptr, col, val, cval, tab,
                                                        coinc);
     SBD_LAUNCH_CHECK();

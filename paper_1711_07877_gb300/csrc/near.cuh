@@ -25,7 +25,8 @@ struct NearDev {
 int points_bbox(const double* z, long n, double* out4_host, cudaStream_t s);
 int points_max_dist2(const double* z, long n, double cx, double cy, double* out_host, cudaStream_t s);
 
-// Build CSR of D (diagonal first in every row).  Allocates rowptr/col/val with cudaMalloc.
+// Build CSR of D (diagonal first in every row).  Allocates rowptr/col/val stream-ordered
+// on s (cudaMallocAsync; free them with cudaFreeAsync).
 //   complex_vals: values are complex128 (Helmholtz) or float64 (Laplace).
 int near_build(const double* z, long n, double delta_min, double bx0, double by0, double bx1, double by1,
                const NearDev& tab, bool complex_vals, long long** rowptr, int** col, void** val,

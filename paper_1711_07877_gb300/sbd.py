@@ -86,6 +86,7 @@ _SIGS = {
     "sbd_plan_export": ([_P, _I64, _P, _P, _P, _P, _P, _P], ctypes.c_int),
     "sbd_close_export": ([_P, _P, _P, _P], ctypes.c_int),
     "sbd_destroy": ([_P], ctypes.c_int),
+    "sbd_destroy_async": ([_P, _P], ctypes.c_int),
     "sbd_offline_fit": ([sbd_kernel, _D, _D, _D, _I32, _I64, _P, _P, _P, _P, _P, _P], ctypes.c_int),
     "sbd_fft2": ([_P, _P, _I32, _I32, _I32, _I32, _P], ctypes.c_int),
     "sbd_fft2_noalloc": ([_P, _P, _I32, _I32, _I32, _I32, _P], ctypes.c_int),
@@ -263,6 +264,10 @@ def sbd_profile_read(plan: int) -> dict:
 
 def sbd_destroy(plan: int) -> None:
     _check(lib.sbd_destroy(plan), "sbd_destroy")
+
+
+def sbd_destroy_async(plan: int, stream=None) -> None:
+    _check(lib.sbd_destroy_async(plan, _stream(stream)), "sbd_destroy_async")
 
 
 def sbd_offline_fit(kernel_kind: int, kappa: float, delta_min: float, delta_max: float, eps: float,

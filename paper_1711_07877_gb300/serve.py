@@ -258,7 +258,7 @@ class Server:
                     return
             req, est, evict = got
             for _, old_plan in evict:            # idle resident plans that made room
-                S.sbd_destroy(old_plan)
+                S.sbd_destroy_async(old_plan, stream.cuda_stream)
             req.start = self.now()
             key = req.geometry
             with self.cv:
@@ -290,7 +290,8 @@ class Server:
             finally:
                 keep = key is not None and plan is not None and req.error is None
                 if plan is not None and not keep and not reused:
-                    S.sbd_destroy(plan)
+                    stream.synchronize()
+                    S.sbd_destroy_async(plan, stream.cuda_stream)   # no device-wide wait
                 req.done = self.now()
                 with self.cv:
                     if keep:
@@ -317,16 +318,29 @@ class Server:
                 S.sbd_destroy(v["plan"])
         self.adm.resident.clear()
 
-    def drain(self, requests: list[Request]) -> None:
-        """Wait until every request in the list is done, then stop the workers."""
+    def drain(self, requests: list[Request], timeout_s: float | None = None) -> bool:
+        """Wait until every request in the list is done, then stop the workers.  With a
+        timeout, give up after timeout_s seconds: the requests still open are marked
+        failed, the workers are left running (daemon threads) and False is returned."""
+        t0 = time.perf_counter()
         while any(r.done == 0.0 for r in requests):
+            if timeout_s is not None and time.perf_counter() - t0 > timeout_s:
+                for r in requests:
+                    if r.done == 0.0:
+                        r.error = "not finished within the drain timeout"
+                done = [r.done for r in requests if r.done > 0.0]
+                self.stats.wall = (max(done) if done else self.now()) - min(r.arrival for r in requests)
+                return False
             time.sleep(0.002)
         self.close()
         self.stats.wall = max(r.done for r in requests) - min(r.arrival for r in requests)
+        return True
 
 
-def run_poisson(requests: list[Request], mean_gap_s: float, seed: int = 0, **server_kw) -> tuple[Server, dict]:
-    """Submit requests with exponential inter-arrival times; return the server and its summary."""
+def run_poisson(requests: list[Request], mean_gap_s: float, seed: int = 0, timeout_s: float | None = None,
+                **server_kw) -> tuple[Server, dict]:
+    """Submit requests with exponential inter-arrival times; return the server and its summary
+    (with "incomplete": the number of requests still open when timeout_s ran out)."""
     rng = np.random.default_rng(seed)
     srv = Server(**server_kw)
     t = 0.0
@@ -339,5 +353,7 @@ def run_poisson(requests: list[Request], mean_gap_s: float, seed: int = 0, **ser
             time.sleep(min(0.001, dt))
         r.arrival = 0.0
         srv.submit(r)
-    srv.drain(requests)
-    return srv, srv.stats.summary()
+    finished = srv.drain(requests, timeout_s)
+    summ = srv.stats.summary()
+    summ["incomplete"] = 0 if finished else sum(r.error == "not finished within the drain timeout" for r in requests)
+    return srv, summ

@@ -196,7 +196,7 @@ def test_plan_delta_max_option_and_fit_cache(S):
     assert after["hits"] == before["hits"] + 1
 
 
-@pytest.mark.parametrize("kind,form", [("laplace", 0), ("helmholtz", 1)])
+@pytest.mark.parametrize("kind,form", [("laplace", 0), ("laplace", 1), ("helmholtz", 0), ("helmholtz", 1)])
 def test_matvec_graph_equals_matvec(S, kind, form):
     """The graph replay computes the same matvec, on the default stream and on a side
     stream, for several inputs and for nrhs = 1 and 2."""
