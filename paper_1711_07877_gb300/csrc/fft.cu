@@ -18,8 +18,68 @@ namespace {
 
 constexpr double kPi = 3.14159265358979323846;
 
-// exp(-2 pi i t / n), t in [0, n), per (n, precision); built on the host in FP64
-// with the angle reduced to the first octant before calling cos/sin.
+// exp(-2 pi i t / n) on the host in FP64, the angle reduced to the first octant before
+// calling cos/sin.
+void host_twiddle(long long t, long long n, double& re, double& im) {
+    t %= n;
+    const long long k8 = 8LL * t;  // octant arithmetic in integers
+    const int oct = static_cast<int>(k8 / n);        // 0..7
+    const double rem = static_cast<double>(k8 - oct * n) / (8.0 * n);   // fraction of a turn in [0, 1/8)
+    double c, s;
+    const double th = 2.0 * kPi * rem;
+    const double ct = std::cos(th), st = std::sin(th);
+    const double r2 = 0.70710678118654752440;
+    const double cq = (ct - st) * r2, sq = (ct + st) * r2;  // angle + pi/4
+    switch (oct) {
+        case 0: c = ct;  s = st;  break;
+        case 1: c = cq;  s = sq;  break;
+        case 2: c = -st; s = ct;  break;
+        case 3: c = -sq; s = cq;  break;
+        case 4: c = -ct; s = -st; break;
+        case 5: c = -cq; s = -sq; break;
+        case 6: c = st;  s = -ct; break;
+        default: c = sq; s = -cq; break;
+    }
+    re = c;
+    im = -s;
+}
+
+// Two-level table of exp(-2 pi i t / n): lo[j] for j < kTwLo, then hi[i] = the twiddle of
+// t = kTwLo i for i < ceil(n / kTwLo); tw(t) = hi[t / kTwLo] lo[t % kTwLo].  Small enough to
+// sit in shared memory beside the row (a few KB), so the radix stages take their twiddles
+// from there instead of from a global table of n entries.
+constexpr int kTwLo = 128;
+inline int tw2_size(int n) { return kTwLo + (n + kTwLo - 1) / kTwLo; }
+
+template <typename T>
+const cx_t<T>* twiddles2(int n, cudaStream_t stream) {
+    static std::mutex mu;
+    static std::map<int, cx_t<T>*> cache;
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = cache.find(n);
+    if (it != cache.end()) return it->second;
+    std::vector<cx_t<T>> h(tw2_size(n));
+    double re, im;
+    for (int j = 0; j < kTwLo; ++j) {
+        host_twiddle(j, n, re, im);
+        h[j] = mk<T>(static_cast<T>(re), static_cast<T>(im));
+    }
+    for (int i = 0; kTwLo + i < static_cast<int>(h.size()); ++i) {
+        host_twiddle(static_cast<long long>(kTwLo) * i, n, re, im);
+        h[kTwLo + i] = mk<T>(static_cast<T>(re), static_cast<T>(im));
+    }
+    cx_t<T>* d = nullptr;
+    {
+        std::unique_lock<std::shared_mutex> lock(capture_mutex());
+        if (cudaMalloc(&d, sizeof(cx_t<T>) * h.size()) != cudaSuccess) return nullptr;
+    }
+    cudaMemcpyAsync(d, h.data(), sizeof(cx_t<T>) * h.size(), cudaMemcpyHostToDevice, stream);
+    cudaStreamSynchronize(stream);
+    cache[n] = d;
+    return d;
+}
+
+// exp(-2 pi i t / n), t in [0, n), per (n, precision).
 template <typename T>
 const cx_t<T>* twiddles(int n, cudaStream_t stream) {
     static std::mutex mu;
@@ -29,27 +89,9 @@ const cx_t<T>* twiddles(int n, cudaStream_t stream) {
     if (it != cache.end()) return it->second;
     std::vector<cx_t<T>> h(n);
     for (int t = 0; t < n; ++t) {
-        // angle 2 pi t / n, reduced via symmetries so cos/sin see |angle| <= pi/4
-        long long k8 = 8LL * t;  // octant arithmetic in integers
-        const long long nn = n;
-        const int oct = static_cast<int>(k8 / nn);       // 0..7
-        const double rem = static_cast<double>(k8 - oct * nn) / (8.0 * nn);   // fraction of a turn in [0, 1/8)
-        double c, s;
-        const double th = 2.0 * kPi * rem;
-        const double ct = std::cos(th), st = std::sin(th);
-        const double r2 = 0.70710678118654752440;
-        const double cq = (ct - st) * r2, sq = (ct + st) * r2;  // angle + pi/4
-        switch (oct) {
-            case 0: c = ct;  s = st;  break;
-            case 1: c = cq;  s = sq;  break;
-            case 2: c = -st; s = ct;  break;
-            case 3: c = -sq; s = cq;  break;
-            case 4: c = -ct; s = -st; break;
-            case 5: c = -cq; s = -sq; break;
-            case 6: c = st;  s = -ct; break;
-            default: c = sq; s = -cq; break;
-        }
-        h[t] = mk<T>(static_cast<T>(c), static_cast<T>(-s));
+        double re, im;
+        host_twiddle(t, n, re, im);
+        h[t] = mk<T>(static_cast<T>(re), static_cast<T>(im));
     }
     cx_t<T>* d = nullptr;
     {
@@ -60,6 +102,14 @@ const cx_t<T>* twiddles(int n, cudaStream_t stream) {
     cudaStreamSynchronize(stream);
     cache[n] = d;
     return d;
+}
+
+// Twiddle t of the row's table: from the two-level shared-memory table (tws non-null) or
+// from the full global table.
+template <typename T>
+__device__ __forceinline__ cx_t<T> twid(const cx_t<T>* __restrict__ tw, const cx_t<T>* tws, int t) {
+    if (tws) return cmul(tws[kTwLo + (t >> 7)], tws[t & (kTwLo - 1)]);
+    return tw[t];
 }
 
 template <typename C> __device__ __forceinline__ C mul_mi(C a, int sign) {
@@ -120,7 +170,7 @@ template <> struct MaxB<double> { static constexpr int n_max = 14336; };
 // the groups g; no division per butterfly.
 template <typename T, int R>
 __device__ __forceinline__ void dit_stage(cx_t<T>* s, int n, int Lp, int sign, const cx_t<T>* __restrict__ tw,
-                                          int tw_scale, int nthreads) {
+                                          const cx_t<T>* tws, int tw_scale, int nthreads) {
     using C = cx_t<T>;
     const int L = Lp * R;
     const int G = n / L;
@@ -141,7 +191,7 @@ __device__ __forceinline__ void dit_stage(cx_t<T>* s, int n, int Lp, int sign, c
         C w[R];
 #pragma unroll
         for (int r = 1; r < R; ++r) {
-            C t = tw[r * k * tw_step];
+            C t = twid<T>(tw, tws, r * k * tw_step);
             if (sign > 0) t.y = -t.y;
             w[r] = t;
         }
@@ -216,13 +266,22 @@ __global__ void __launch_bounds__(NT) fft_rows_kernel(
     cx_t<T>* __restrict__ out, long out_stride, int out_len, int out_shift,
     int n, int Q, int sign, FftPlan1D plan, const cx_t<T>* __restrict__ tw, const int* __restrict__ perm,
     const T* __restrict__ pre_elem, const T* __restrict__ pre_row,
-    const T* __restrict__ post_elem, const T* __restrict__ post_row, HermFold<T> hf, int io) {
+    const T* __restrict__ post_elem, const T* __restrict__ post_row, HermFold<T> hf, int io,
+    const cx_t<T>* __restrict__ tw2) {
     using C = cx_t<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* s = reinterpret_cast<C*>(smem_raw);
     const long row = blockIdx.y;     // phases of a row are adjacent CTAs (they read the same row)
     const int r = blockIdx.x;
     const int nq = n / Q;
+    // two-level twiddle table (if given) in shared memory after the row
+    C* tws = nullptr;
+    if (tw2) {
+        tws = s + nq;
+        const int ntw = kTwLo + (n + kTwLo - 1) / kTwLo;
+        for (int i = threadIdx.x; i < ntw; i += NT) tws[i] = tw2[i];
+        __syncthreads();
+    }
     const C* src = in + row * in_stride * (io == kIoPairInv ? 2 : 1);
     T rs0 = static_cast<T>(1), rs1 = static_cast<T>(1);
     if (pre_row) {
@@ -237,7 +296,7 @@ __global__ void __launch_bounds__(NT) fft_rows_kernel(
             C v = load_elem<T>(io, idx, n, src, in_stride, in_len, in_shift, row, hf, rs0, rs1, pre_elem, has);
             if (has) {
                 if (r) {                              // twist w_n^{idx}
-                    C w = tw[idx];
+                    C w = twid<T>(tw, tws, idx);
                     if (sign > 0) w.y = -w.y;
                     v = cmul(v, w);
                 }
@@ -250,10 +309,10 @@ __global__ void __launch_bounds__(NT) fft_rows_kernel(
     int Lp = 1;
     for (int st = 0; st < plan.nstages; ++st) {
         const int R = plan.radix[st];
-        if (R == 4)      dit_stage<T, 4>(s, nq, Lp, sign, tw, Q, NT);
-        else if (R == 2) dit_stage<T, 2>(s, nq, Lp, sign, tw, Q, NT);
-        else if (R == 3) dit_stage<T, 3>(s, nq, Lp, sign, tw, Q, NT);
-        else             dit_stage<T, 5>(s, nq, Lp, sign, tw, Q, NT);
+        if (R == 4)      dit_stage<T, 4>(s, nq, Lp, sign, tw, tws, Q, NT);
+        else if (R == 2) dit_stage<T, 2>(s, nq, Lp, sign, tw, tws, Q, NT);
+        else if (R == 3) dit_stage<T, 3>(s, nq, Lp, sign, tw, tws, Q, NT);
+        else             dit_stage<T, 5>(s, nq, Lp, sign, tw, tws, Q, NT);
         Lp *= R;
     }
     if (io == kIoPairFwd) {
@@ -417,7 +476,11 @@ int fft_rows(const cx_t<T>* in, long in_stride, int in_len, int in_shift,
         set_error("FFT table allocation failed");
         return SBD_ENOMEM;
     }
-    const size_t smem = sizeof(cx_t<T>) * static_cast<size_t>(nq);
+    // the two-level twiddle table rides in shared memory when it fits beside the row
+    const size_t row_bytes = sizeof(cx_t<T>) * static_cast<size_t>(nq);
+    const size_t tw2_bytes = sizeof(cx_t<T>) * static_cast<size_t>(tw2_size(n));
+    const cx_t<T>* tw2 = row_bytes + tw2_bytes <= 227u * 1024u ? twiddles2<T>(n, stream) : nullptr;
+    const size_t smem = row_bytes + (tw2 ? tw2_bytes : 0);
     in_shift = ((in_shift % n) + n) % n;
     out_shift = ((out_shift % n) + n) % n;
     for (int r0 = 0; r0 < rows; r0 += 65535) {          // grid.y holds at most 65535 rows
@@ -437,17 +500,17 @@ int fft_rows(const cx_t<T>* in, long in_stride, int in_len, int in_shift,
             auto k = fft_rows_kernel<T, 512>;
             SBD_TRY(raise_smem_limit(k, smem));
             k<<<grid, 512, smem, stream>>>(ip, in_stride, in_len, in_shift, op, out_stride, out_len, out_shift,
-                                           n, Q, sign, plan, tw, perm, pre_elem, prr, post_elem, por, hf, io);
+                                           n, Q, sign, plan, tw, perm, pre_elem, prr, post_elem, por, hf, io, tw2);
         } else if (nq > 2048) {
             auto k = fft_rows_kernel<T, 1024>;
             SBD_TRY(raise_smem_limit(k, smem));
             k<<<grid, 1024, smem, stream>>>(ip, in_stride, in_len, in_shift, op, out_stride, out_len, out_shift,
-                                            n, Q, sign, plan, tw, perm, pre_elem, prr, post_elem, por, hf, io);
+                                            n, Q, sign, plan, tw, perm, pre_elem, prr, post_elem, por, hf, io, tw2);
         } else {
             auto k = fft_rows_kernel<T, 256>;
             SBD_TRY(raise_smem_limit(k, smem));
             k<<<grid, 256, smem, stream>>>(ip, in_stride, in_len, in_shift, op, out_stride, out_len, out_shift,
-                                           n, Q, sign, plan, tw, perm, pre_elem, prr, post_elem, por, hf, io);
+                                           n, Q, sign, plan, tw, perm, pre_elem, prr, post_elem, por, hf, io, tw2);
         }
         SBD_LAUNCH_CHECK();
     }
@@ -475,13 +538,13 @@ int fft_rows_tables(const cx_t<T>* in, long in_stride, int in_len, cx_t<T>* out,
             SBD_TRY(raise_smem_limit(k, smem));
             k<<<grid, 1024, smem, stream>>>(ip, in_stride, in_len, 0, op, out_stride, out_len, 0, n, 1, sign, plan, tw,
                                             perm, nullptr, nullptr, nullptr, nullptr, HermFold<T>{nullptr, 0, 0},
-                                            kIoPlain);
+                                            kIoPlain, nullptr);
         } else {
             auto k = fft_rows_kernel<T, 256>;
             SBD_TRY(raise_smem_limit(k, smem));
             k<<<grid, 256, smem, stream>>>(ip, in_stride, in_len, 0, op, out_stride, out_len, 0, n, 1, sign, plan, tw,
                                            perm, nullptr, nullptr, nullptr, nullptr, HermFold<T>{nullptr, 0, 0},
-                                           kIoPlain);
+                                           kIoPlain, nullptr);
         }
         SBD_LAUNCH_CHECK();
     }

@@ -198,17 +198,22 @@ int gmres_impl(sbd_plan_t plan, long n, const void* b, void* x, const sbd_gmres_
     S.shift = zc(o.shift_re, o.shift_im);
     S.scale = zc(o.scale_re, o.scale_im);
     S.nblk = static_cast<int>(std::min<long>(1024, (n + 255) / 256));
-    SBD_CUDA_TRY(cudaMallocAsync(&S.Vb, sizeof(T) * n * (m + 1), s));
-    SBD_CUDA_TRY(cudaMallocAsync(&S.tmp, sizeof(T) * n, s));
-    SBD_CUDA_TRY(cudaMallocAsync(&S.partial, sizeof(double2) * S.nblk * (m + 1), s));
-    SBD_CUDA_TRY(cudaMallocAsync(&S.hd, sizeof(double2) * (m + 1), s));
     auto release = [&]() {
-        cudaFreeAsync(S.Vb, s);
-        cudaFreeAsync(S.tmp, s);
-        cudaFreeAsync(S.partial, s);
-        cudaFreeAsync(S.hd, s);
+        if (S.Vb) cudaFreeAsync(S.Vb, s);
+        if (S.tmp) cudaFreeAsync(S.tmp, s);
+        if (S.partial) cudaFreeAsync(S.partial, s);
+        if (S.hd) cudaFreeAsync(S.hd, s);
         cudaStreamSynchronize(s);
     };
+    if (cudaMallocAsync(&S.Vb, sizeof(T) * n * (m + 1), s) != cudaSuccess ||
+        cudaMallocAsync(&S.tmp, sizeof(T) * n, s) != cudaSuccess ||
+        cudaMallocAsync(&S.partial, sizeof(double2) * S.nblk * (m + 1), s) != cudaSuccess ||
+        cudaMallocAsync(&S.hd, sizeof(double2) * (m + 1), s) != cudaSuccess) {
+        cudaGetLastError();
+        release();
+        set_error("sbd_gmres: workspace allocation failed");
+        return SBD_ENOMEM;
+    }
     const T* bb = static_cast<const T*>(b);
     T* xx = static_cast<T*>(x);
     int rc = SBD_OK;
