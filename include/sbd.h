@@ -254,9 +254,7 @@ int sbd_fft2(const void* in, void* out, int32_t n0, int32_t n1, int32_t sign, in
  * has variants that compute the same sums: acc 0 adds re and im into two float planes
  * (one shared-memory atomic each), acc 1 (FP32 form only) into one float2 plane with
  * one 64-bit compare-and-swap, acc 2 (FP32 form only) into two int64 fixed-point
- * planes with integer atomics (quantum 2^-50 of a per-tile bound on any contribution),
- * acc 3 (FP32 only) into the two float planes of acc 0 with a plain 32-bit
- * compare-and-swap loop;
+ * planes with integer atomics (quantum 2^-50 of a per-tile bound on any contribution);
  * sched 0 deals the records of a tile to the lane groups in turn, sched 1 gives each
  * group a contiguous run.  Results agree to FP32 rounding.
  *   sbd_tune       times every applicable variant on the plan's own records (reps
@@ -264,15 +262,15 @@ int sbd_fft2(const void* in, void* out, int32_t n0, int32_t n1, int32_t sign, in
  *                  frequency workspace is first filled with a constant non-zero value,
  *                  so that concurrent adds to a cell contend as with real data) and
  *                  keeps the fastest.
- *                  ms (host, 10 entries, may be NULL): mean ms per launch of variant
- *                  acc * 2 + sched, -1 where not applicable; ms[8], ms[9]: mean ms of
+ *                  ms (host, 8 entries, may be NULL): mean ms per launch of variant
+ *                  acc * 2 + sched, -1 where not applicable; ms[6], ms[7]: mean ms of
  *                  the forward 2-D transform with rows in one phase where they fit, and
  *                  with every row split into two half-length phases (two CTAs of 512
  *                  threads per SM instead of one of 1024); the faster is kept too.
  *                  Blocks until done.
  *   sbd_set_tuning picks a variant by hand (fft_split 0 or 2).
- * SBD_EINVAL for a null plan, reps < 1, acc outside {0, 1, 2, 3}, sched outside {0, 1}
- * or fft_split outside {0, 2} (acc 1, 2 and 3 need the FP32 form).  Plans whose node step is the two-kernel fallback ignore the variant.
+ * SBD_EINVAL for a null plan, reps < 1, acc outside {0, 1, 2}, sched outside {0, 1} or
+ * fft_split outside {0, 2} (acc 1 and 2 need the FP32 form).  Plans whose node step is the two-kernel fallback ignore the variant.
  * ------------------------------------------------------------------------------- */
 int sbd_tune(sbd_plan_t plan, int32_t reps, double* ms, void* cuda_stream);
 int sbd_set_tuning(sbd_plan_t plan, int32_t acc, int32_t sched, int32_t fft_split);

@@ -908,7 +908,7 @@ int sbd_plan_info(sbd_plan_t p, sbd_plan_stats* o) {
 }
 
 int sbd_set_tuning(sbd_plan_t p, int32_t acc, int32_t sched, int32_t fft_split) {
-    if (!p || acc < 0 || acc > 3 || sched < 0 || sched > 1 || (acc >= 1 && p->form != SBD_FORM_FP32) ||
+    if (!p || acc < 0 || acc > 2 || sched < 0 || sched > 1 || (acc >= 1 && p->form != SBD_FORM_FP32) ||
         (fft_split != 0 && fft_split != 2)) {
         set_error("sbd_set_tuning: invalid plan or variant");
         return SBD_EINVAL;
@@ -925,7 +925,7 @@ int sbd_tune(sbd_plan_t p, int32_t reps, double* ms, void* cuda_stream) {
         return SBD_EINVAL;
     }
     if (ms)
-        for (int v = 0; v < 10; ++v) ms[v] = -1.0;
+        for (int v = 0; v < 8; ++v) ms[v] = -1.0;
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     // row-FFT phases: time the forward transform with split 0 and 2, keep the faster
     {
@@ -959,7 +959,7 @@ int sbd_tune(sbd_plan_t p, int32_t reps, double* ms, void* cuda_stream) {
             cudaEventSynchronize(b);
             cudaEventElapsedTime(&t_ms, a, b);
             const double per = static_cast<double>(t_ms) / reps;
-            if (ms) ms[sp == 0 ? 8 : 9] = per;
+            if (ms) ms[sp == 0 ? 6 : 7] = per;
             if (per < best) {
                 best = per;
                 pick = sp;
@@ -984,7 +984,7 @@ int sbd_tune(sbd_plan_t p, int32_t reps, double* ms, void* cuda_stream) {
     NodeTuning pick = p->tuning;
     int rc = SBD_OK;
     const bool fp32 = p->form == SBD_FORM_FP32;
-    for (int acc = 0; acc <= (fp32 ? 3 : 0) && !rc; ++acc) {
+    for (int acc = 0; acc <= (fp32 ? 2 : 0) && !rc; ++acc) {
         if (acc == 2 && node_fused_smem<float>(p->np.Pk, 2) > 227 * 1024) continue;
         for (int sched = 0; sched <= 1 && !rc; ++sched) {
             const NodeTuning t{acc, sched, p->tuning.wbound};

@@ -44,6 +44,38 @@ void host_twiddle(long long t, long long n, double& re, double& im) {
     im = -s;
 }
 
+// Process-wide cache of device tables keyed by an int.  Its lock is held only to read or
+// to insert: a miss builds and uploads the table without it, because allocating takes the
+// capture lock exclusively while a thread capturing a graph holds that lock shared and may
+// be waiting here for a table it already has.  A miss on a capturing stream fails instead
+// of allocating (the caller reports SBD_ENOMEM); plans run one plain call before capturing.
+template <typename V>
+struct TableCache {
+    std::mutex mu;
+    std::map<int, V*> map;
+    V* find(int key) {
+        std::lock_guard<std::mutex> lock(mu);
+        auto it = map.find(key);
+        return it == map.end() ? nullptr : it->second;
+    }
+    V* upload(int key, const std::vector<V>& h, cudaStream_t stream) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(stream, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return nullptr;
+        V* d = nullptr;
+        {
+            std::unique_lock<std::shared_mutex> lock(capture_mutex());
+            if (cudaMalloc(&d, sizeof(V) * h.size()) != cudaSuccess) return nullptr;
+        }
+        cudaMemcpyAsync(d, h.data(), sizeof(V) * h.size(), cudaMemcpyHostToDevice, stream);
+        cudaStreamSynchronize(stream);
+        std::lock_guard<std::mutex> lock(mu);
+        auto it = map.find(key);
+        if (it != map.end()) return it->second;     // another thread built it meanwhile (ours stays unused)
+        map[key] = d;
+        return d;
+    }
+};
+
 // Two-level table of exp(-2 pi i t / n): lo[j] for j < kTwLo, then hi[i] = the twiddle of
 // t = kTwLo i for i < ceil(n / kTwLo); tw(t) = hi[t / kTwLo] lo[t % kTwLo].  Small enough to
 // sit in shared memory beside the row (a few KB), so the radix stages take their twiddles
@@ -53,11 +85,8 @@ inline int tw2_size(int n) { return kTwLo + (n + kTwLo - 1) / kTwLo; }
 
 template <typename T>
 const cx_t<T>* twiddles2(int n, cudaStream_t stream) {
-    static std::mutex mu;
-    static std::map<int, cx_t<T>*> cache;
-    std::lock_guard<std::mutex> lock(mu);
-    auto it = cache.find(n);
-    if (it != cache.end()) return it->second;
+    static TableCache<cx_t<T>> cache;
+    if (const cx_t<T>* d = cache.find(n)) return d;
     std::vector<cx_t<T>> h(tw2_size(n));
     double re, im;
     for (int j = 0; j < kTwLo; ++j) {
@@ -68,41 +97,23 @@ const cx_t<T>* twiddles2(int n, cudaStream_t stream) {
         host_twiddle(static_cast<long long>(kTwLo) * i, n, re, im);
         h[kTwLo + i] = mk<T>(static_cast<T>(re), static_cast<T>(im));
     }
-    cx_t<T>* d = nullptr;
-    {
-        std::unique_lock<std::shared_mutex> lock(capture_mutex());
-        if (cudaMalloc(&d, sizeof(cx_t<T>) * h.size()) != cudaSuccess) return nullptr;
-    }
-    cudaMemcpyAsync(d, h.data(), sizeof(cx_t<T>) * h.size(), cudaMemcpyHostToDevice, stream);
-    cudaStreamSynchronize(stream);
-    cache[n] = d;
-    return d;
+    return cache.upload(n, h, stream);
 }
 
 // exp(-2 pi i t / n), t in [0, n), per (n, precision).
 template <typename T>
 const cx_t<T>* twiddles(int n, cudaStream_t stream) {
-    static std::mutex mu;
-    static std::map<int, cx_t<T>*> cache;
-    std::lock_guard<std::mutex> lock(mu);
-    auto it = cache.find(n);
-    if (it != cache.end()) return it->second;
+    static TableCache<cx_t<T>> cache;
+    if (const cx_t<T>* d = cache.find(n)) return d;
     std::vector<cx_t<T>> h(n);
     for (int t = 0; t < n; ++t) {
         double re, im;
         host_twiddle(t, n, re, im);
         h[t] = mk<T>(static_cast<T>(re), static_cast<T>(im));
     }
-    cx_t<T>* d = nullptr;
-    {
-        std::unique_lock<std::shared_mutex> lock(capture_mutex());
-        if (cudaMalloc(&d, sizeof(cx_t<T>) * n) != cudaSuccess) return nullptr;
-    }
-    cudaMemcpyAsync(d, h.data(), sizeof(cx_t<T>) * n, cudaMemcpyHostToDevice, stream);
-    cudaStreamSynchronize(stream);
-    cache[n] = d;
-    return d;
+    return cache.upload(n, h, stream);
 }
+
 
 // Twiddle t of the row's table: from the two-level shared-memory table (tws non-null) or
 // from the full global table.
@@ -355,11 +366,8 @@ __global__ void __launch_bounds__(NT) fft_rows_kernel(
 // R_1..R_s applied in that order, index i = sum of digits (least significant digit in
 // base R_s, then R_{s-1}, ...) lands at position sum_k d_k R_1...R_{k-1}.
 const int* digit_perm(const FftPlan1D& plan, cudaStream_t stream) {
-    static std::mutex mu;
-    static std::map<int, int*> cache;
-    std::lock_guard<std::mutex> lock(mu);
-    auto it = cache.find(plan.n);
-    if (it != cache.end()) return it->second;
+    static TableCache<int> cache;
+    if (const int* d = cache.find(plan.n)) return d;
     const int n = plan.n;
     std::vector<int> h(n);
     std::vector<int> weight(plan.nstages);
@@ -374,15 +382,7 @@ const int* digit_perm(const FftPlan1D& plan, cudaStream_t stream) {
         }
         h[i] = pos;
     }
-    int* d = nullptr;
-    {
-        std::unique_lock<std::shared_mutex> lock(capture_mutex());
-        if (cudaMalloc(&d, sizeof(int) * n) != cudaSuccess) return nullptr;
-    }
-    cudaMemcpyAsync(d, h.data(), sizeof(int) * n, cudaMemcpyHostToDevice, stream);
-    cudaStreamSynchronize(stream);
-    cache[n] = d;
-    return d;
+    return cache.upload(n, h, stream);
 }
 
 template <typename T>

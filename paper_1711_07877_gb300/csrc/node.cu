@@ -297,18 +297,6 @@ __global__ void __launch_bounds__(256) scatter_tiles_kernel(
     }
 }
 
-// x += v on a shared-memory float with a plain 32-bit compare-and-swap loop (no warp-level
-// aggregation of equal addresses, which the records of a warp rarely share).  Lock-free.
-__device__ __forceinline__ void shared_add_cas(float* addr, float v) {
-    auto* p = reinterpret_cast<unsigned*>(addr);
-    unsigned old = *reinterpret_cast<volatile unsigned*>(p);
-    for (;;) {
-        const unsigned prev = atomicCAS(p, old, __float_as_uint(__uint_as_float(old) + v));
-        if (prev == old) return;
-        old = prev;
-    }
-}
-
 // Fused node step: one CTA per 64 x 64 tile of the frequency grid.  The tile plus a
 // (P-1) halo of K sits in shared memory with an accumulator of the same size
 // (interleaved float2 in FP32, two planes re / im in FP64).  A group of G lanes (G = 8, 16 or 32 >= P; 32 / G nodes per warp) takes
@@ -325,7 +313,6 @@ __device__ __forceinline__ void shared_add_cas(float* addr, float v) {
 // turn, SCHED = 1 gives each group one contiguous run of records (the groups of a warp
 // then work on records far apart in the sorted order, which collide less).
 //
-// ACC = 3 (FP32 only): the two float planes of ACC = 0 with a hand-written 32-bit CAS loop.
 // ACC = 2 (FP32 only): fixed-point accumulation in two int64 planes with native integer
 // atomics.  Every contribution g w_a w_b is at most max|K tile| max|omega'| P^2 =: B in
 // each component (window values <= 1), so scaling by 2^e with B 2^e <= 2^50 leaves room
@@ -448,9 +435,6 @@ __global__ void __launch_bounds__(NT) node_fused_kernel(
                                   static_cast<unsigned long long>(__float2ll_rn(gr * w * up)));
                         atomicAdd(acc64_im + base + a * Ws,
                                   static_cast<unsigned long long>(__float2ll_rn(gi * w * up)));
-                    } else if constexpr (sizeof(T) == 4 && ACC == 3) {
-                        shared_add_cas(reinterpret_cast<float*>(acc_re) + base + a * Ws, gr * w);
-                        shared_add_cas(reinterpret_cast<float*>(acc_im) + base + a * Ws, gi * w);
                     } else {
                         atomicAdd(acc_re + base + a * Ws, gr * w);
                         atomicAdd(acc_im + base + a * Ws, gi * w);
@@ -613,10 +597,6 @@ int launch_fused_g(const NodeRec<T>* nodes, const long long* tile_start, unsigne
     if (sizeof(T) == 4 && t.acc == 2) {
         return t.sched ? launch_fused<T, G, 2, 1>(nodes, tile_start, nt, ntx, g, Ws, win, kin, kout, wb, s)
                        : launch_fused<T, G, 2, 0>(nodes, tile_start, nt, ntx, g, Ws, win, kin, kout, wb, s);
-    }
-    if (sizeof(T) == 4 && t.acc == 3) {
-        return t.sched ? launch_fused<T, G, 3, 1>(nodes, tile_start, nt, ntx, g, Ws, win, kin, kout, wb, s)
-                       : launch_fused<T, G, 3, 0>(nodes, tile_start, nt, ntx, g, Ws, win, kin, kout, wb, s);
     }
     return t.sched ? launch_fused<T, G, 0, 1>(nodes, tile_start, nt, ntx, g, Ws, win, kin, kout, wb, s)
                    : launch_fused<T, G, 0, 0>(nodes, tile_start, nt, ntx, g, Ws, win, kin, kout, wb, s);

@@ -24,8 +24,7 @@ int node_step_tiled(const NodeRec<T>* nodes, const long long* tile_start, const 
 // atomicAdd, 1 = one float2 plane with a 64-bit compare-and-swap (FP32 only); sched 0 =
 // records dealt to the lane groups in turn, 1 = one contiguous run per group.
 struct NodeTuning {
-    int acc = 0;          // 0 float planes, 1 float2 CAS (FP32), 2 int64 fixed point (FP32),
-                          // 3 float planes with a plain 32-bit CAS loop (FP32)
+    int acc = 0;          // 0 float planes, 1 float2 CAS (FP32), 2 int64 fixed point (FP32)
     int sched = 0;
     float wbound = 0.f;   // max |omega'| component x P_k^2 (the fixed-point scale bound)
 };

@@ -294,7 +294,7 @@ def sbd_fit_cache_stats() -> dict:
 def sbd_tune(plan: int, reps: int = 3, stream=None) -> list:
     """Time the node-kernel variants, keep the fastest; returns ms per variant (acc * 2 + sched)."""
     import numpy as np
-    ms = np.zeros(10)
+    ms = np.zeros(8)
     _check(lib.sbd_tune(plan, reps, ms.ctypes.data, _stream(stream)), "sbd_tune")
     return ms.tolist()
 
