@@ -23,6 +23,9 @@
 
 namespace sbd {
 
+// Q-point Gauss-Legendre nodes and weights on [0, a].
+void gauss_legendre_0a(int Q, double a, std::vector<double>& s, std::vector<double>& w);
+
 namespace {
 
 constexpr double kPi = 3.14159265358979323846;
@@ -109,9 +112,26 @@ struct FitWork {
     std::vector<double> rho, C, b, L;
     std::vector<double> s, gs;           // samples and g(s)
     std::vector<double> Jmat;            // [sample][p] = J0(rho_p s)
+    // Low-rank form of the Gram matrix: A = I - F F^T exactly (to rounding), because the
+    // e_p are orthonormal on the unit disk (A(0) = I) and the disk of radius a contributes
+    // B_ij = 2 pi C_i C_j rho_i rho_j int_0^a s J1(rho_i s) J1(rho_j s) ds, which a Q-point
+    // Gauss-Legendre rule on [0, a] integrates exactly: F_ik = sqrt(2 pi w_k s_k) C_i rho_i
+    // J1(rho_i s_k).  A^-1 b = b + F (I - F^T F)^-1 F^T b (Woodbury) costs O(P Q^2) instead
+    // of the O(P^3) Cholesky of A.  Near the Gram conditioning floor (Sec. 4.1) the
+    // cancellation in I - F^T F costs accuracy, so it is used only for tolerances above it.
+    bool lowrank = false;
+    int Q = 0;
+    std::vector<double> F;               // [p][k], p < Pf, k < Q
 };
 
+
+void build_fit_lowrank(FitWork& w, int Pf);
+
 void build_fit(FitWork& w, int Pf) {
+    if (w.lowrank) {
+        build_fit_lowrank(w, Pf);
+        return;
+    }
     w.Pf = Pf;
     w.rho.resize(Pf);
     w.C.resize(Pf);
@@ -161,8 +181,109 @@ void build_fit(FitWork& w, int Pf) {
     }
 }
 
+// J0(rho_p s) for every sample and p < Pf (shared by both forms)
+void fill_jmat(FitWork& w) {
+    const int ns = static_cast<int>(w.s.size());
+    w.Jmat.assign(static_cast<size_t>(ns) * w.Pf, 0.0);
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int i = 0; i < ns; ++i) {
+        double* Ji = &w.Jmat[static_cast<size_t>(i) * w.Pf];
+        for (int p = 0; p < w.Pf; ++p) Ji[p] = bessel_j0(w.rho[p] * w.s[i]);
+    }
+}
+
+void build_fit_lowrank(FitWork& w, int Pf) {
+    w.Pf = Pf;
+    w.rho.resize(Pf);
+    w.C.resize(Pf);
+    w.b.resize(Pf);
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int p = 0; p < Pf; ++p) {
+        const double r = j0_root(p + 1);
+        w.rho[p] = r;
+        w.C[p] = 1.0 / (std::sqrt(kPi) * r * std::fabs(bessel_j1(r)));
+        const double j0a = bessel_j0(r * w.a), j1a = bessel_j1(r * w.a);
+        if (w.kind == 0) {
+            w.b[p] = -2.0 * kPi * w.C[p] * j0a;
+        } else {
+            const double kp = w.kp, a = w.a;
+            const double Fv = a * (r * bessel_y1(kp * a) * j0a - kp * bessel_y0(kp * a) * j1a) / (kp * kp - r * r);
+            w.b[p] = -2.0 * kPi * w.C[p] * r * kp * Fv;
+        }
+    }
+    // the integrand s J1(rho_i s) J1(rho_j s) on [0, a] oscillates at most 2 rho_max a / (2 pi)
+    // times: Q = rho_max a + 40 nodes (and at least 64) integrate it to rounding
+    w.Q = std::max(64, static_cast<int>(std::ceil(w.rho[Pf - 1] * w.a)) + 40);
+    std::vector<double> sq, wq;
+    gauss_legendre_0a(w.Q, w.a, sq, wq);
+    w.F.assign(static_cast<size_t>(Pf) * w.Q, 0.0);
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int p = 0; p < Pf; ++p) {
+        double* Fp = &w.F[static_cast<size_t>(p) * w.Q];
+        for (int k = 0; k < w.Q; ++k)
+            Fp[k] = std::sqrt(2.0 * kPi * wq[k] * sq[k]) * w.C[p] * w.rho[p] * bessel_j1(w.rho[p] * sq[k]);
+    }
+    w.Pok = Pf;
+    fill_jmat(w);
+}
+
+// alpha = A_P^-1 b_P with A_P = I - F_P F_P^T; false when I - F_P^T F_P is not positive
+// definite (beyond the conditioning floor).
+bool lowrank_solve(const FitWork& w, int P, std::vector<double>& alpha) {
+    const int Q = w.Q;
+    std::vector<double> M(static_cast<size_t>(Q) * Q, 0.0), y(Q, 0.0);
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int k = 0; k < Q; ++k) {
+        for (int l = 0; l <= k; ++l) {
+            double g = 0.0;
+            for (int p = 0; p < P; ++p) g += w.F[static_cast<size_t>(p) * Q + k] * w.F[static_cast<size_t>(p) * Q + l];
+            M[static_cast<size_t>(k) * Q + l] = (k == l ? 1.0 : 0.0) - g;
+        }
+    }
+    for (int k = 0; k < Q; ++k) {
+        double t = 0.0;
+        for (int p = 0; p < P; ++p) t += w.F[static_cast<size_t>(p) * Q + k] * w.b[p];
+        y[k] = t;
+    }
+    // dense Cholesky of the Q x Q matrix (lower triangle)
+    for (int j = 0; j < Q; ++j) {
+        double d = M[static_cast<size_t>(j) * Q + j];
+        for (int t = 0; t < j; ++t) d -= M[static_cast<size_t>(j) * Q + t] * M[static_cast<size_t>(j) * Q + t];
+        if (!(d > 0.0)) return false;
+        d = std::sqrt(d);
+        M[static_cast<size_t>(j) * Q + j] = d;
+        for (int i = j + 1; i < Q; ++i) {
+            double v = M[static_cast<size_t>(i) * Q + j];
+            for (int t = 0; t < j; ++t) v -= M[static_cast<size_t>(i) * Q + t] * M[static_cast<size_t>(j) * Q + t];
+            M[static_cast<size_t>(i) * Q + j] = v / d;
+        }
+    }
+    for (int i = 0; i < Q; ++i) {                       // forward
+        double v = y[i];
+        for (int t = 0; t < i; ++t) v -= M[static_cast<size_t>(i) * Q + t] * y[t];
+        y[i] = v / M[static_cast<size_t>(i) * Q + i];
+    }
+    for (int i = Q - 1; i >= 0; --i) {                  // backward
+        double v = y[i];
+        for (int t = i + 1; t < Q; ++t) v -= M[static_cast<size_t>(t) * Q + i] * y[t];
+        y[i] = v / M[static_cast<size_t>(i) * Q + i];
+    }
+    alpha.assign(P, 0.0);
+#pragma omp parallel for schedule(static)
+    for (int p = 0; p < P; ++p) {
+        double v = w.b[p];
+        for (int k = 0; k < Q; ++k) v += w.F[static_cast<size_t>(p) * Q + k] * y[k];
+        alpha[p] = v;
+    }
+    return true;
+}
+
 double fit_error(const FitWork& w, int P, std::vector<double>& alpha) {
-    chol_solve(w.L, P, w.b.data(), alpha);
+    if (w.lowrank) {
+        if (!lowrank_solve(w, P, alpha)) return 1e300;
+    } else {
+        chol_solve(w.L, P, w.b.data(), alpha);
+    }
     const int ns = static_cast<int>(w.s.size());
     double err = 0.0;
 #pragma omp parallel for reduction(max : err)
@@ -327,6 +448,9 @@ int offline_fit(int kind, double kappa, double delta_min, double delta_max, doub
     f.a = delta_min / f.scale_R;
     w.a = f.a;
     const double tol_g = (eps / 3.0) / std::fabs(f.gscale);
+    // the low-rank Gram solve for the P search, unless the target is near the
+    // conditioning floor (there the factor of the full Gram matrix is more accurate)
+    w.lowrank = fixed_P == 0 && tol_g >= 5e-9;
     auto prepare_samples = [&]() {
         fit_samples(f.a, w.extra, w.s);
         w.gs.resize(w.s.size());
@@ -439,6 +563,18 @@ int offline_fit(int kind, double kappa, double delta_min, double delta_max, doub
 }
 
 // Gauss-Legendre nodes and weights on [-1, 1] (Newton on P_n from Tricomi's guess).
+static void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w);
+
+void gauss_legendre_0a(int Q, double a, std::vector<double>& s, std::vector<double>& w) {
+    std::vector<double> x;
+    gauss_legendre(Q, x, w);
+    s.resize(Q);
+    for (int k = 0; k < Q; ++k) {
+        s[k] = 0.5 * a * (x[k] + 1.0);
+        w[k] *= 0.5 * a;
+    }
+}
+
 static void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w) {
     x.resize(n);
     w.resize(n);
