@@ -117,3 +117,17 @@ def test_fit_cache_reuses_normalised_fit(S):
     assert st["misses"] == 3 and st["entries"] == 3
     S.sbd_fit_cache_clear()
     assert S.sbd_fit_cache_stats() == {"hits": 0, "misses": 0, "entries": 0}
+
+
+@pytest.mark.parametrize("kind,kappa,dmin,dmax", [("laplace", 0.0, 0.004, 1.0), ("helmholtz", 60.0, 0.004, 1.0)])
+def test_lowrank_fit_agrees_with_cholesky(S, kind, kappa, dmin, dmax):
+    """The P search solves with A = I - F F^T (Woodbury); a fixed-P fit factors the full Gram
+    matrix.  At the same P the coefficients agree to the conditioning of A (gamma ~ 4)."""
+    k = S.SBD_HELMHOLTZ if kind == "helmholtz" else S.SBD_LAPLACE
+    S.sbd_fit_cache_clear()
+    f = S.sbd_offline_fit(k, kappa, dmin, dmax, 1e-6)
+    g = S.sbd_offline_fit(k, kappa, dmin, dmax, 1e-6, fixed_P=f["P"])
+    P = f["P"]
+    rel = np.linalg.norm(f["alpha"][:P] - g["alpha"][:P]) / np.linalg.norm(g["alpha"][:P])
+    assert rel < 1e-6, rel
+    assert abs(f["fit_err"] - g["fit_err"]) <= 1e-3 * g["fit_err"] + 1e-15
