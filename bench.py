@@ -343,6 +343,38 @@ def main():
                 "frac": achieved / hbm, "traffic": traffic_for(dom, args.workload, args.form),
                 "peak_source": f"{peak_src} (hbm_gbs)"}
 
+    # cuFFT (through torch.fft), timed only as a comparison for the forward transform: the
+    # same row transforms (length n, the rows that carry data), full outputs, plus the
+    # transpose between the two passes
+    fft_cmp = None
+    try:
+        m_, nk_, n_ = info["grid_x"], info["grid_k"], info["fft_n"]
+        rows1 = m_ // 2 if not helm else m_
+        rows2 = nk_ // 2 + info["stencil_k"] // 2 + 2 if not helm else nk_
+        cdt = torch.complex64 if args.form == "fp32" else torch.complex128
+        a1 = torch.randn(rows1, m_, dtype=cdt, device="cuda")
+        a2 = torch.randn(rows2, m_, dtype=cdt, device="cuda")
+
+        def cufft_fwd():
+            y1 = torch.fft.fft(a1, n=n_, dim=1)
+            t = y1[:, :rows2].t().contiguous() if rows2 <= n_ else y1.t().contiguous()
+            return torch.fft.fft(a2, n=n_, dim=1), t
+        for _ in range(2):
+            cufft_fwd()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(5):
+            cufft_fwd()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        fft_cmp = {"ours_fft_fwd_ms": stages["fft_fwd"]["ms"], "cufft_ms": e0.elapsed_time(e1) / 5,
+                   "note": "torch.fft (cuFFT) on the same row counts and length, full outputs, plus one "
+                           "transpose; comparison only, not on the matvec path"}
+        del a1, a2
+        torch.cuda.empty_cache()
+    except Exception as exc:  # a comparison only
+        fft_cmp = {"error": str(exc)[:200]}
+
     # end to end through the public API: pinned host f -> device, matvec, q -> pinned host
     fh = torch.from_numpy(np.ascontiguousarray(wl.f)).pin_memory()
     qh = torch.empty_like(fh).pin_memory()
@@ -365,6 +397,7 @@ def main():
            "vs_baseline": None, "dtype": "f32" if args.form == "fp32" else "f64", "data": "synthetic",
            "config": workload_config(args, rank), "clocks": clk, "e2e": e2e,
            "gpu_launches": (2 + 9 * nrhs) * args.steps, "roofline": roofline, "stages": stages,
+           "fft_comparison": fft_cmp,
            "plan": dict({k: info[k] for k in ("P", "n_xi", "n_records", "nnz", "grid_x", "grid_k", "fft_n",
                                               "stencil_x", "stencil_k", "nufft_tol", "fit_err", "device_bytes",
                                               "plan_seconds", "node_acc", "node_sched")},
