@@ -6,6 +6,7 @@
 #include <algorithm>
 #include <map>
 #include <mutex>
+#include <type_traits>
 #include <vector>
 #include <cmath>
 
@@ -299,7 +300,8 @@ __global__ void __launch_bounds__(NT) fft_rows_kernel(
         rs0 = pre_row[io == kIoPairFwd ? 2 * row : row];
         rs1 = pre_row[io == kIoPairFwd ? 2 * row + 1 : row];
     }
-    for (int i = threadIdx.x; i < nq; i += NT) {
+    // element i of the length-nq transform: the Q phases folded and twisted
+    auto fetch = [&](int i) -> C {
         C acc = mk<T>(0, 0);
         for (int j = 0; j < Q; ++j) {
             const int idx = i + j * nq;               // FFT index
@@ -314,11 +316,33 @@ __global__ void __launch_bounds__(NT) fft_rows_kernel(
                 acc = cadd(acc, v);
             }
         }
-        s[perm[i]] = acc;
-    }
+        return acc;
+    };
+    // first radix stage straight from the input: in the digit-reversed order the group g of
+    // stage one (shared positions g R1 + q) holds input elements t + G1 q, where t is the
+    // index with perm[t] = g R1; threads take consecutive t, so each of their R1 reads is
+    // coalesced, and the stage's butterflies run before anything is stored
+    const int R1 = plan.radix[0];
+    auto first_stage = [&](auto radix) {
+        constexpr int R = decltype(radix)::value;
+        const int G1 = nq / R;
+        for (int t = threadIdx.x; t < G1; t += NT) {
+            const int base = perm[t];                 // = g R
+            C v[R];
+#pragma unroll
+            for (int q = 0; q < R; ++q) v[q] = fetch(t + G1 * q);
+            small_dft<T, R>(v, sign);
+#pragma unroll
+            for (int q = 0; q < R; ++q) s[base + q] = v[q];
+        }
+    };
+    if (R1 == 5) first_stage(std::integral_constant<int, 5>{});
+    else if (R1 == 4) first_stage(std::integral_constant<int, 4>{});
+    else if (R1 == 3) first_stage(std::integral_constant<int, 3>{});
+    else first_stage(std::integral_constant<int, 2>{});
     __syncthreads();
-    int Lp = 1;
-    for (int st = 0; st < plan.nstages; ++st) {
+    int Lp = R1;
+    for (int st = 1; st < plan.nstages; ++st) {
         const int R = plan.radix[st];
         if (R == 4)      dit_stage<T, 4>(s, nq, Lp, sign, tw, tws, Q, NT);
         else if (R == 2) dit_stage<T, 2>(s, nq, Lp, sign, tw, tws, Q, NT);
