@@ -224,6 +224,30 @@ __device__ __forceinline__ void dit_stage(cx_t<T>* s, int n, int Lp, int sign, c
     __syncthreads();
 }
 
+// The last stage (G = 1, so one butterfly per offset k), writing its outputs straight to
+// the destination through put(position in s, value) instead of back to shared memory.
+template <typename T, int R, typename Put>
+__device__ __forceinline__ void dit_stage_out(const cx_t<T>* s, int n, int Lp, int sign,
+                                              const cx_t<T>* __restrict__ tw, const cx_t<T>* tws, int tw_scale,
+                                              int nthreads, Put put) {
+    using C = cx_t<T>;
+    const int tw_step = tw_scale * (n / (Lp * R));
+    for (int k = threadIdx.x; k < Lp; k += nthreads) {
+        C v[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = s[k + r * Lp];
+#pragma unroll
+        for (int r = 1; r < R; ++r) {
+            C t = twid<T>(tw, tws, r * k * tw_step);
+            if (sign > 0) t.y = -t.y;
+            v[r] = cmul(v[r], t);
+        }
+        small_dft<T, R>(v, sign);
+#pragma unroll
+        for (int r = 0; r < R; ++r) put(k + r * Lp, v[r]);
+    }
+}
+
 // One row (blockIdx.y) and one phase (blockIdx.x) of a length-n transform done as Q
 // transforms of length nq = n / Q (Q = 1 or 2): output k = Q k' + r is the length-nq DFT
 // of y_r[t] = sum_{j < Q} x[t + j nq] w_n^{r (t + j nq)} (fold and twist on the load).
@@ -342,8 +366,36 @@ __global__ void __launch_bounds__(NT) fft_rows_kernel(
     else first_stage(std::integral_constant<int, 2>{});
     __syncthreads();
     int Lp = R1;
+    // output scaling of the direct store (plain and pair-inverse rows)
+    T ps0 = static_cast<T>(1), ps1 = static_cast<T>(1);
+    if (post_row) {
+        ps0 = post_row[io == kIoPairInv ? 2 * row : row];
+        ps1 = post_row[io == kIoPairInv ? 2 * row + 1 : row];
+    }
+    C* dst = out + row * out_stride;
+    // s position p holds FFT position Q p + r; element e of the output window is FFT
+    // position (e + out_shift) mod n
+    auto put = [&](int pos, C v) {
+        const int kk = Q == 2 ? 2 * pos + r : pos;
+        int e = kk - out_shift;
+        if (e < 0) e += n;
+        if (e < out_len) {
+            const T pe = post_elem ? post_elem[e] : static_cast<T>(1);
+            v.x *= ps0 * pe;
+            v.y *= ps1 * pe;
+            dst[e] = v;
+        }
+    };
     for (int st = 1; st < plan.nstages; ++st) {
         const int R = plan.radix[st];
+        if (st == plan.nstages - 1 && io != kIoPairFwd) {
+            // last stage: outputs go straight to global memory (uniform branch, no barrier after)
+            if (R == 4)      dit_stage_out<T, 4>(s, nq, Lp, sign, tw, tws, Q, NT, put);
+            else if (R == 2) dit_stage_out<T, 2>(s, nq, Lp, sign, tw, tws, Q, NT, put);
+            else if (R == 3) dit_stage_out<T, 3>(s, nq, Lp, sign, tw, tws, Q, NT, put);
+            else             dit_stage_out<T, 5>(s, nq, Lp, sign, tw, tws, Q, NT, put);
+            return;
+        }
         if (R == 4)      dit_stage<T, 4>(s, nq, Lp, sign, tw, tws, Q, NT);
         else if (R == 2) dit_stage<T, 2>(s, nq, Lp, sign, tw, tws, Q, NT);
         else if (R == 3) dit_stage<T, 3>(s, nq, Lp, sign, tw, tws, Q, NT);
@@ -368,13 +420,7 @@ __global__ void __launch_bounds__(NT) fft_rows_kernel(
         }
         return;
     }
-    C* dst = out + row * out_stride;
-    T ps0 = static_cast<T>(1), ps1 = static_cast<T>(1);
-    if (post_row) {
-        ps0 = post_row[io == kIoPairInv ? 2 * row : row];
-        ps1 = post_row[io == kIoPairInv ? 2 * row + 1 : row];
-    }
-    for (int e = threadIdx.x; e < out_len; e += NT) {
+    for (int e = threadIdx.x; e < out_len; e += NT) {       // single-stage rows only
         int k = e + out_shift;
         if (k >= n) k -= n;
         if (Q == 2 && (k & 1) != r) continue;
