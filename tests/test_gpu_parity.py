@@ -320,11 +320,48 @@ def test_config2_sampled_against_direct_sum(S):
     wl = W.laplace_curves(1_000_000, 2, 1e-6)
     p = make_plan(S, wl.z, "laplace", wl.delta_min, wl.eps, form=1)
     try:
+        S.sbd_tune(p, 2)                                  # the bench runs the tuned variant
         q = matvec(S, p, wl.f, len(wl.z))
         idx = np.random.default_rng(7).choice(len(wl.z), 500, replace=False)
         qd = O.direct_sum(wl.z, wl.f, "laplace", targets=idx, chunk=16)
         assert np.max(np.abs(q[idx] - qd)) <= wl.eps * np.abs(wl.f).sum()
         rel = np.linalg.norm(q[idx] - qd) / np.linalg.norm(qd)
         assert rel <= 1e-5, rel
+    finally:
+        S.sbd_destroy(p)
+
+
+def test_config3_sampled_against_direct_sum(S):
+    """Helmholtz, kappa delta_max = 500, N = 10^6 on the curves, eps = 1e-6, FP32 and FP64
+    forms, tuned: 60 sampled outputs against the FP64 direct sum over all sources."""
+    wl = W.helmholtz_curves(1_000_000, 3, 1e-6)
+    idx = np.random.default_rng(8).choice(len(wl.z), 60, replace=False)
+    qd = O.direct_sum(wl.z, wl.f, "helmholtz", wl.kappa, targets=idx, chunk=4)
+    for form in (1, 0):
+        p = make_plan(S, wl.z, "helmholtz", wl.delta_min, wl.eps, kappa=wl.kappa, form=form)
+        try:
+            S.sbd_tune(p, 1)
+            q = matvec(S, p, wl.f, len(wl.z))
+            assert np.max(np.abs(q[idx] - qd)) <= wl.eps * np.abs(wl.f).sum(), form
+            rel = np.linalg.norm(q[idx] - qd) / np.linalg.norm(qd)
+            assert rel <= 1e-5, (form, rel)
+        finally:
+            S.sbd_destroy(p)
+
+
+def test_config4_sampled_against_direct_sum(S):
+    """Laplace, N = 10^7 in the unit square, 16 right-hand sides in one call, FP32 form,
+    tuned: 6 sampled outputs of 4 of the right-hand sides against the FP64 direct sum."""
+    wl = W.laplace_square(10_000_000, 4, 1e-6, 16)
+    p = make_plan(S, wl.z, "laplace", wl.delta_min, wl.eps, form=1, max_nrhs=16)
+    try:
+        S.sbd_tune(p, 1)
+        q = matvec(S, p, wl.f, len(wl.z), nrhs=16)
+        idx = np.random.default_rng(9).choice(len(wl.z), 6, replace=False)
+        for r in (0, 5, 10, 15):
+            qd = O.direct_sum(wl.z, wl.f[r], "laplace", targets=idx, chunk=2)
+            assert np.max(np.abs(q[r][idx] - qd)) <= wl.eps * np.abs(wl.f[r]).sum(), r
+            rel = np.linalg.norm(q[r][idx] - qd) / np.linalg.norm(qd)
+            assert rel <= 1e-5, (r, rel)
     finally:
         S.sbd_destroy(p)
