@@ -77,6 +77,10 @@ typedef struct {
                             SBD_EINVAL); 0: 2 max |z - c| (R2).  A caller that rounds delta_max
                             and delta_min / delta_max to fixed grids makes repeated fits hit the
                             fit cache below. */
+    int32_t host_threads;/* > 0: OpenMP threads for the host part of sbd_plan (fit, tables);
+                            0: the OpenMP default.  Servers that build several plans at
+                            once give each a share of the cores. */
+    int32_t reserved;
 } sbd_options;
 
 /* sbd_options.flags: use a Gaussian window at the quadrature nodes instead of the

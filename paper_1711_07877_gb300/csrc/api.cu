@@ -8,6 +8,8 @@
 #include <string>
 #include <vector>
 
+#include <omp.h>
+
 #include "bessel.h"
 #include "common.cuh"
 #include "far.cuh"
@@ -574,7 +576,7 @@ int sbd_plan(const double* points, int64_t n, sbd_kernel kernel, double delta_mi
         return SBD_EINVAL;
     }
     if ((o.flags & ~SBD_FLAG_GAUSSIAN_NODES) != 0 || o.fixed_P < 0 || o.max_nrhs < 0 || o.nufft_tol < 0 ||
-        !(o.delta_max >= 0)) {
+        !(o.delta_max >= 0) || o.host_threads < 0) {
         set_error("sbd_plan: invalid options");
         return SBD_EINVAL;
     }
@@ -591,6 +593,7 @@ int sbd_plan(const double* points, int64_t n, sbd_kernel kernel, double delta_mi
         return SBD_EINVAL;
     }
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    if (o.host_threads > 0) omp_set_num_threads(o.host_threads);   // this thread's parallel regions
     keep_pool_memory();
     auto* p = new sbd_plan_s();
     p->alloc_stream = s;

@@ -31,7 +31,8 @@ class sbd_kernel(ctypes.Structure):
 
 class sbd_options(ctypes.Structure):
     _fields_ = [("form", ctypes.c_int32), ("fixed_P", ctypes.c_int32), ("nufft_tol", ctypes.c_double),
-                ("max_nrhs", ctypes.c_int32), ("flags", ctypes.c_int32), ("delta_max", ctypes.c_double)]
+                ("max_nrhs", ctypes.c_int32), ("flags", ctypes.c_int32), ("delta_max", ctypes.c_double),
+                ("host_threads", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class sbd_gmres_options(ctypes.Structure):
@@ -145,8 +146,8 @@ SBD_FLAG_GAUSSIAN_NODES = 1
 
 
 def make_options(form: int = SBD_FORM_FP64, fixed_P: int = 0, nufft_tol: float = 0.0, max_nrhs: int = 1,
-                 flags: int = 0, delta_max: float = 0.0):
-    return sbd_options(form, fixed_P, nufft_tol, max_nrhs, flags, delta_max)
+                 flags: int = 0, delta_max: float = 0.0, host_threads: int = 0):
+    return sbd_options(form, fixed_P, nufft_tol, max_nrhs, flags, delta_max, host_threads, 0)
 
 
 def sbd_plan(points, n: int, kernel_kind: int, kappa: float, delta_min: float, eps: float,

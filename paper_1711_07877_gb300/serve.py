@@ -11,6 +11,7 @@ overlaps.  The library calls release the GIL; the arithmetic is all in libsbd.so
 """
 from __future__ import annotations
 
+import os
 import threading
 import time
 from collections import OrderedDict
@@ -222,6 +223,8 @@ class Server:
         self.form = form
         self.tol, self.restart, self.max_iter = tol, restart, max_iter
         self.fit_grid = fit_grid
+        # the host part of concurrent plan builds shares the cores
+        self.host_threads = max(1, (os.cpu_count() or slots) // slots)
         if hbm_budget is None:
             free, _ = torch.cuda.mem_get_info()
             hbm_budget = int(free * 0.8)
@@ -275,7 +278,7 @@ class Server:
                     if self.fit_grid:
                         dmin, dmax = fit_grid_scales(req.kind, req.kappa, req.delta_min,
                                                      enclosing_diameter(req.z))
-                    opt = S.make_options(form=self.form, delta_max=dmax)
+                    opt = S.make_options(form=self.form, delta_max=dmax, host_threads=self.host_threads)
                     plan = S.sbd_plan(zt, len(req.z), req.kind, req.kappa, dmin, req.eps, opt, stream.cuda_stream)
                     info = S.sbd_plan_info(plan)
                     req.plan_seconds = info["plan_seconds"]
