@@ -91,6 +91,7 @@ struct sbd_plan_s {
     long long* node_tile_start = nullptr;
     void* ghat = nullptr;              // n_xi weighted node values (scratch of the two-kernel node step)
     bool node_fused = true;            // one-kernel node step (shared memory permitting)
+    bool node_binned = false;          // the binned node kernel applies (records sorted by bin)
     NodeTuning tuning;                 // fused node-kernel variant (sbd_tune)
     int fft_split = 0;                 // row-FFT phases (sbd_tune): 0 as needed, 2 always two
     int tuned = 0;                     // 1 once sbd_tune chose the variant
@@ -303,12 +304,24 @@ int build_far(sbd_plan_s* p, cudaStream_t s) {
     if ((rc = dev_alloc(p, reinterpret_cast<void**>(&p->node_perm), sizeof(int) * p->n_rec))) return rc;
     if ((rc = dev_alloc(p, reinterpret_cast<void**>(&p->node_tile_start),
                         sizeof(long long) * (static_cast<size_t>(ntx) * ntx + 1)))) return rc;
+    // FP32 records go in bin order (the binned node kernel needs it; the others take any)
+    const bool by_bin = sizeof(T) == 4 && np.Pk <= kBinSide;
     rc = tile_sort<NodeRec<T>>(canon, p->n_rec, np.nk, static_cast<NodeRec<T>*>(p->nodes), p->node_perm,
-                               p->node_tile_start, s);
+                               p->node_tile_start, s, by_bin);
     if (rc) return rc;
     SBD_CUDA_TRY(cudaFreeAsync(canon, s));
     // the fused node kernel holds the tile plus halo and two accumulator planes in shared memory
     p->node_fused = node_fused_smem<T>(np.Pk) <= 227 * 1024;
+    if (by_bin) {
+        // the binned kernel also needs every tile sorted, i.e. within the sort's capacity
+        std::vector<long long> ts(static_cast<size_t>(ntx) * ntx + 1);
+        SBD_CUDA_TRY(cudaMemcpyAsync(ts.data(), p->node_tile_start, sizeof(long long) * ts.size(),
+                                     cudaMemcpyDeviceToHost, s));
+        SBD_CUDA_TRY(cudaStreamSynchronize(s));
+        long long most = 0;
+        for (size_t t = 0; t + 1 < ts.size(); ++t) most = std::max(most, ts[t + 1] - ts[t]);
+        p->node_binned = p->node_fused && most <= kTileSortMax && node_fused_smem<T>(np.Pk, 3) <= 227 * 1024;
+    }
     if (!p->node_fused && (rc = dev_alloc(p, &p->ghat, sizeof(cx_t<T>) * p->n_rec))) return rc;
     std::vector<T> dec(np.m);
     for (int i = 0; i < np.m; ++i) dec[i] = static_cast<T>(np.dec[i]);
@@ -907,12 +920,13 @@ int sbd_plan_info(sbd_plan_t p, sbd_plan_stats* o) {
     o->node_acc = p->tuning.acc;
     o->node_sched = p->tuning.sched;
     o->fft_split = p->fft_split;
+    o->node_binned = p->node_binned ? 1 : 0;
     return SBD_OK;
 }
 
 int sbd_set_tuning(sbd_plan_t p, int32_t acc, int32_t sched, int32_t fft_split) {
-    if (!p || acc < 0 || acc > 2 || sched < 0 || sched > 1 || (acc >= 1 && p->form != SBD_FORM_FP32) ||
-        (fft_split != 0 && fft_split != 2)) {
+    if (!p || acc < 0 || acc > 3 || sched < 0 || sched > 1 || (acc >= 1 && p->form != SBD_FORM_FP32) ||
+        (acc == 3 && !p->node_binned) || (fft_split != 0 && fft_split != 2)) {
         set_error("sbd_set_tuning: invalid plan or variant");
         return SBD_EINVAL;
     }
@@ -928,7 +942,7 @@ int sbd_tune(sbd_plan_t p, int32_t reps, double* ms, void* cuda_stream) {
         return SBD_EINVAL;
     }
     if (ms)
-        for (int v = 0; v < 8; ++v) ms[v] = -1.0;
+        for (int v = 0; v < 10; ++v) ms[v] = -1.0;
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     // row-FFT phases: time the forward transform with split 0 and 2, keep the faster
     {
@@ -962,7 +976,7 @@ int sbd_tune(sbd_plan_t p, int32_t reps, double* ms, void* cuda_stream) {
             cudaEventSynchronize(b);
             cudaEventElapsedTime(&t_ms, a, b);
             const double per = static_cast<double>(t_ms) / reps;
-            if (ms) ms[sp == 0 ? 6 : 7] = per;
+            if (ms) ms[sp == 0 ? 8 : 9] = per;
             if (per < best) {
                 best = per;
                 pick = sp;
@@ -987,8 +1001,9 @@ int sbd_tune(sbd_plan_t p, int32_t reps, double* ms, void* cuda_stream) {
     NodeTuning pick = p->tuning;
     int rc = SBD_OK;
     const bool fp32 = p->form == SBD_FORM_FP32;
-    for (int acc = 0; acc <= (fp32 ? 2 : 0) && !rc; ++acc) {
+    for (int acc = 0; acc <= (fp32 ? 3 : 0) && !rc; ++acc) {
         if (acc == 2 && node_fused_smem<float>(p->np.Pk, 2) > 227 * 1024) continue;
+        if (acc == 3 && !p->node_binned) continue;
         for (int sched = 0; sched <= 1 && !rc; ++sched) {
             const NodeTuning t{acc, sched, p->tuning.wbound};
             auto step = [&]() {

@@ -14,6 +14,8 @@
 //            stencils of every record whose stencil meets the tile (records of the
 //            tile and of the three tiles before it), then stores the tile once.
 // No global atomics, and the output grid needs no clearing.
+#include <type_traits>
+
 #include "near.cuh"
 #include "node.cuh"
 #include "sbd.h"
@@ -47,15 +49,22 @@ __global__ void tile_scatter_kernel(const Rec* __restrict__ in, long n, int ntx,
 // Deterministic order inside each tile: the records of a tile (in the nondeterministic
 // order of the scatter above) sorted by their original index with a bitonic sort in
 // shared memory, so that a plan's records, and therefore its FP32 sums, are the same on
-// every run, and consecutive records of a tile run along a circle.  Tiles with more than
+// every run, and consecutive records of a tile run along a circle.  BIN puts the key
+// (bin of the stencil start, original index) first: the 8 x 8 bins of kBinSide cells,
+// row-major in the tile, that the binned node kernel walks.  Tiles with more than
 // kTileSortCap records keep the scatter order.
-constexpr int kTileSortCap = 4096;
+constexpr int kTileSortCap = kTileSortMax;
 
-template <typename Rec>
+__device__ __forceinline__ int bin_in_tile(int2 cell) {
+    return ((cell.x % kNodeTile) / kBinSide) * (kNodeTile / kBinSide) + (cell.y % kNodeTile) / kBinSide;
+}
+
+template <typename Rec, bool BIN>
 __global__ void __launch_bounds__(256) tile_order_kernel(const Rec* __restrict__ tmp, const int* __restrict__ tmp_perm,
                                                          const long long* __restrict__ start, Rec* __restrict__ out,
                                                          int* __restrict__ perm) {
-    __shared__ int key[kTileSortCap];
+    using Key = typename std::conditional<BIN, long long, int>::type;
+    __shared__ Key key[kTileSortCap];
     __shared__ short idx[kTileSortCap];
     const long long b = start[blockIdx.x], e = start[blockIdx.x + 1];
     const int c = static_cast<int>(e - b);
@@ -70,7 +79,12 @@ __global__ void __launch_bounds__(256) tile_order_kernel(const Rec* __restrict__
     int L = 1;
     while (L < c) L <<= 1;
     for (int i = threadIdx.x; i < L; i += blockDim.x) {
-        key[i] = i < c ? tmp_perm[b + i] : 0x7fffffff;
+        Key k = BIN ? static_cast<Key>(0x7fffffffffffffffLL) : static_cast<Key>(0x7fffffff);
+        if (i < c) {
+            k = tmp_perm[b + i];
+            if constexpr (BIN) k |= static_cast<long long>(bin_in_tile(tmp[b + i].cell)) << 32;
+        }
+        key[i] = k;
         idx[i] = static_cast<short>(i);
     }
     __syncthreads();
@@ -81,7 +95,7 @@ __global__ void __launch_bounds__(256) tile_order_kernel(const Rec* __restrict__
                 if (ixj > i) {
                     const bool up = (i & k) == 0;
                     if ((key[i] > key[ixj]) == up) {
-                        const int tk = key[i];
+                        const Key tk = key[i];
                         key[i] = key[ixj];
                         key[ixj] = tk;
                         const short ti = idx[i];
@@ -95,7 +109,7 @@ __global__ void __launch_bounds__(256) tile_order_kernel(const Rec* __restrict__
     }
     for (int i = threadIdx.x; i < c; i += blockDim.x) {
         out[b + i] = tmp[b + idx[i]];
-        perm[b + i] = key[i];
+        perm[b + i] = static_cast<int>(key[i] & 0x7fffffff);
     }
 }
 
@@ -469,6 +483,164 @@ __global__ void __launch_bounds__(NT) node_fused_kernel(
     }
 }
 
+// Binned node step (FP32, stencils of at most kBinSide cells): no atomics in shared
+// memory.  The records of a tile are sorted by the 8 x 8 bin of their stencil start
+// (tile_sort with by_bin); a record of bin (bx, by) writes only cells
+// [8 bx, 8 bx + 15) x [8 by, 8 by + 15), so two bins of the same colour
+// (bx & 1, by & 1) never write the same cell.  Each colour adds into its own shared
+// accumulator; a warp takes whole bins (from a shared counter) and walks a bin's records
+// four at a time:
+//   window  lanes 8k..8k+7 evaluate w(j - P/2 + 1 - frac) for record k of the four;
+//   gather  lane l covers cells (l / 4, l % 4) and (l / 4, l % 4 + 4) of every record's
+//           stencil (weights fetched by shuffles), and a butterfly reduce-scatter leaves
+//           record k's sum in lanes 8k..8k+7, which multiply it by omega'_k;
+//   scatter one record after the other (a warp barrier between them, the stencils of one
+//           bin overlap), plain loads and stores into the colour's accumulator.
+// Every accumulator cell thus receives the records of one bin, in a fixed order, and
+// the four colours are summed in a fixed order: the result is the same on every run.
+constexpr int kBinW = kNodeTile + kBinSide - 1;                 // 71: rows / cols any stencil reaches
+constexpr int kBins = (kNodeTile / kBinSide) * (kNodeTile / kBinSide);
+
+// Shared row stride of the binned kernel (float2 units): >= kBinW and = 12 (mod 16), so
+// that the 4 x 8-word row pieces of one 16-lane phase of a 64-bit access fill the 32
+// banks once.
+constexpr int kBinWs = 76;
+static_assert(kBinWs >= kBinW && kBinWs % 16 == 12, "binned stride");
+
+template <int NT>
+__global__ void __launch_bounds__(NT, 1) node_binned_kernel(
+    const NodeRec<float>* __restrict__ rec, const long long* __restrict__ tile_start, int ntx, int n, int P,
+    Window<float> win, const float2* __restrict__ kin, float2* __restrict__ kout) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int bstart[kBins + 1];
+    __shared__ int next_bin;
+    const int tile = blockIdx.x;
+    const long long b0 = tile_start[tile], b1 = tile_start[tile + 1];
+    if (b0 == b1) return;                                           // uniform per block
+    const int cnt = static_cast<int>(b1 - b0);
+    constexpr int plane = kBinW * kBinWs;
+    float2* s = reinterpret_cast<float2*>(smem_raw);                 // input tile
+    float2* acc = s + plane;                                        // four colour accumulators
+    const int ox = (tile / ntx) * kNodeTile, oy = (tile % ntx) * kNodeTile;
+    const int W = kNodeTile + P - 1;
+    const int rows = min(W, n - ox), cols = min(W, n - oy);
+    const int tid = threadIdx.x;
+    for (int idx = tid; idx < kBinW * kBinW; idx += NT) {
+        const int r = idx / kBinW, c = idx - r * kBinW;
+        float2 v = make_float2(0.f, 0.f);
+        if (r < rows && c < cols) v = kin[static_cast<long>(ox + r) * n + oy + c];
+        const int o = r * kBinWs + c;
+        s[o] = v;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) acc[k * plane + o] = make_float2(0.f, 0.f);
+    }
+    for (int k = tid; k <= kBins; k += NT) bstart[k] = cnt;
+    if (tid == 0) next_bin = 0;
+    __syncthreads();
+    // bin starts: record i opens bins (bin(i - 1), bin(i)] (records sorted by bin)
+    for (int i = tid; i < cnt; i += NT) {
+        const int bi = bin_in_tile(rec[b0 + i].cell);
+        const int bp = i > 0 ? bin_in_tile(rec[b0 + i - 1].cell) : -1;
+        for (int k = bp + 1; k <= bi; ++k) bstart[k] = i;
+    }
+    __syncthreads();
+    const unsigned full = 0xffffffffu;
+    const int lane = tid & 31;
+    const int kown = lane >> 3, sub = lane & 7;                     // window lane: record, offset
+    const int ca = lane >> 2, cb = lane & 3;                        // cells (ca, cb), (ca, cb + 4)
+    const float offw = static_cast<float>(sub - P / 2 + 1);
+    const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4;
+    for (;;) {
+        int bin = 0;
+        if (lane == 0) bin = atomicAdd(&next_bin, 1);
+        bin = __shfl_sync(full, bin, 0);
+        if (bin >= kBins) break;
+        float2* ac = acc + (((bin / (kNodeTile / kBinSide)) & 1) * 2 + (bin & 1)) * plane;
+        const int e0 = min(bstart[bin], cnt), e1 = min(max(bstart[bin + 1], e0), cnt);
+        for (int j = e0; j < e1; j += 4) {
+            const int jr = j + kown;
+            int base = 0;
+            float wx = 0.f, wy = 0.f;
+            float2 om = make_float2(0.f, 0.f);
+            if (jr < e1) {
+                const NodeRec<float> q = rec[b0 + jr];
+                base = (q.cell.x - ox) * kBinWs + (q.cell.y - oy);
+                if (sub < P) {
+                    wx = win(offw - q.frac.x);
+                    wy = win(offw - q.frac.y);
+                }
+                om = q.omega;
+            }
+            float x[8], w1[4], w2[4];
+            int bk[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                bk[k] = __shfl_sync(full, base, 8 * k) + ca * kBinWs + cb;
+                const float wa = __shfl_sync(full, wx, 8 * k + ca);
+                w1[k] = wa * __shfl_sync(full, wy, 8 * k + cb);
+                w2[k] = wa * __shfl_sync(full, wy, 8 * k + cb + 4);
+                const float2 s1 = s[bk[k]], s2 = s[bk[k] + 4];
+                x[2 * k] = w1[k] * s1.x + w2[k] * s2.x;
+                x[2 * k + 1] = w1[k] * s1.y + w2[k] * s2.y;
+            }
+            // reduce-scatter: afterwards lane l holds x[(l >> 2) & 7] summed over the warp,
+            // i.e. part (l >> 2) & 1 (re, im) of record (l >> 3)
+            float y[4], z[2];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const float send = b4 ? x[i] : x[4 + i], keep = b4 ? x[4 + i] : x[i];
+                y[i] = keep + __shfl_xor_sync(full, send, 16);
+            }
+#pragma unroll
+            for (int i = 0; i < 2; ++i) {
+                const float send = b3 ? y[i] : y[2 + i], keep = b3 ? y[2 + i] : y[i];
+                z[i] = keep + __shfl_xor_sync(full, send, 8);
+            }
+            float u = (b2 ? z[1] : z[0]) + __shfl_xor_sync(full, b2 ? z[0] : z[1], 4);
+            u += __shfl_xor_sync(full, u, 2);
+            u += __shfl_xor_sync(full, u, 1);
+            const float o = __shfl_xor_sync(full, u, 4);
+            const float sr = b2 ? o : u, si = b2 ? u : o;
+            const float gr = sr * om.x - si * om.y, gi = sr * om.y + si * om.x;
+            const int nl = min(4, e1 - j);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                if (k < nl) {                                       // uniform per warp
+                    const float hr = __shfl_sync(full, gr, 8 * k), hi = __shfl_sync(full, gi, 8 * k);
+                    float2* p1 = ac + bk[k];
+                    float2 t1 = p1[0], t2 = p1[4];
+                    t1.x += hr * w1[k];
+                    t1.y += hi * w1[k];
+                    t2.x += hr * w2[k];
+                    t2.y += hi * w2[k];
+                    p1[0] = t1;
+                    p1[4] = t2;
+                    __syncwarp();
+                }
+            }
+        }
+    }
+    __syncthreads();
+    for (int idx = tid; idx < W * W; idx += NT) {
+        const int r = idx / W, c = idx - r * W;
+        if (r >= rows || c >= cols) continue;
+        const int o = r * kBinWs + c;
+        float vr = acc[o].x, vi = acc[o].y;
+#pragma unroll
+        for (int k = 1; k < 4; ++k) {
+            vr += acc[k * plane + o].x;
+            vi += acc[k * plane + o].y;
+        }
+        float2* dst = kout + static_cast<long>(ox + r) * n + oy + c;
+        if (r >= P - 1 && c >= P - 1 && r < kNodeTile && c < kNodeTile) {
+            *dst = make_float2(vr, vi);
+        } else if (vr != 0.f || vi != 0.f) {
+            atomicAdd(&dst->x, vr);
+            atomicAdd(&dst->y, vi);
+        }
+    }
+}
+
 // Threads of a fused node-step CTA: 16 warps, so that the two CTAs that fit an SM's
 // shared memory (FP32 form) keep 32 warps in flight for the shared-memory latency.
 constexpr int kNodeThreads = 512;
@@ -533,7 +705,8 @@ int launch_scatter(const Rec* rec, const long long* tile_start, int n, int P, in
 }  // namespace
 
 template <typename Rec>
-int tile_sort(const Rec* in, long n_rec, int n, Rec* sorted, int* perm, long long* tile_start, cudaStream_t s) {
+int tile_sort(const Rec* in, long n_rec, int n, Rec* sorted, int* perm, long long* tile_start, cudaStream_t s,
+              bool by_bin) {
     const int ntx = tiles_per_side(n);
     const long ntiles = static_cast<long>(ntx) * ntx;
     int* cursor = nullptr;
@@ -555,7 +728,12 @@ int tile_sort(const Rec* in, long n_rec, int n, Rec* sorted, int* perm, long lon
         SBD_CUDA_TRY(cudaMallocAsync(&tmp_perm, sizeof(int) * n_rec, s));
         tile_scatter_kernel<Rec><<<nb, 256, 0, s>>>(in, n_rec, ntx, tile_start, cursor, tmp, tmp_perm);
         SBD_LAUNCH_CHECK();
-        tile_order_kernel<Rec><<<static_cast<unsigned>(ntiles), 256, 0, s>>>(tmp, tmp_perm, tile_start, sorted, perm);
+        if (by_bin)
+            tile_order_kernel<Rec, true><<<static_cast<unsigned>(ntiles), 256, 0, s>>>(tmp, tmp_perm, tile_start,
+                                                                                       sorted, perm);
+        else
+            tile_order_kernel<Rec, false><<<static_cast<unsigned>(ntiles), 256, 0, s>>>(tmp, tmp_perm, tile_start,
+                                                                                        sorted, perm);
         SBD_LAUNCH_CHECK();
         SBD_CUDA_TRY(cudaFreeAsync(tmp, s));
         SBD_CUDA_TRY(cudaFreeAsync(tmp_perm, s));
@@ -566,6 +744,7 @@ int tile_sort(const Rec* in, long n_rec, int n, Rec* sorted, int* perm, long lon
 
 template <typename T>
 size_t node_fused_smem(int Pk, int acc) {
+    if (acc == 3) return static_cast<size_t>(5) * kBinW * kBinWs * sizeof(float2);
     const int W = kNodeTile + Pk - 1;
     const int Ws = fused_stride(W, fused_p8(Pk));
     const size_t accb = acc == 2 ? 2 * sizeof(unsigned long long) : 2 * sizeof(T);
@@ -602,12 +781,34 @@ int launch_fused_g(const NodeRec<T>* nodes, const long long* tile_start, unsigne
                    : launch_fused<T, G, 0, 0>(nodes, tile_start, nt, ntx, g, Ws, win, kin, kout, wb, s);
 }
 
+template <int NT>
+int launch_binned(const NodeRec<float>* nodes, const long long* tile_start, unsigned nt, int ntx, const FarGeom& g,
+                  const Window<float>& win, const float2* kin, float2* kout, cudaStream_t s) {
+    const size_t smem = node_fused_smem<float>(g.Pk, 3);
+    auto k = node_binned_kernel<NT>;
+    SBD_TRY(raise_smem_limit(k, smem));
+    k<<<nt, NT, smem, s>>>(nodes, tile_start, ntx, g.nk, g.Pk, win, kin, kout);
+    SBD_LAUNCH_CHECK();
+    return SBD_OK;
+}
+
 template <typename T>
 int node_step_fused(const NodeRec<T>* nodes, const long long* tile_start, const FarGeom& g,
                     const cx_t<T>* kin, cx_t<T>* kout, const NodeTuning& t, cudaStream_t s) {
     SBD_CUDA_TRY(cudaMemsetAsync(kout, 0, sizeof(cx_t<T>) * static_cast<size_t>(g.nk) * g.nk, s));
     const int ntx = tiles_per_side(g.nk);
     const unsigned nt = static_cast<unsigned>(ntx) * ntx;
+    if constexpr (sizeof(T) == 4) {
+        if (t.acc == 3) {
+            if (g.Pk > kBinSide) {
+                set_error("node step: the binned kernel needs a stencil of at most 8 cells");
+                return SBD_EINVAL;
+            }
+            const Window<float> win = make_window<float>(g.kwin, g.beta_k, g.Pk);
+            return t.sched ? launch_binned<2 * kNodeThreads>(nodes, tile_start, nt, ntx, g, win, kin, kout, s)
+                           : launch_binned<kNodeThreads>(nodes, tile_start, nt, ntx, g, win, kin, kout, s);
+        }
+    }
     const int W = kNodeTile + g.Pk - 1;
     const int P8 = fused_p8(g.Pk);
     const int Ws = fused_stride(W, P8);
@@ -675,9 +876,9 @@ int fill_grid(cx_t<T>* x, long n, T re, T im, cudaStream_t s) {
 
 #define SBD_NODE_INST(T)                                                                                     \
     template int tile_sort<NodeRec<T>>(const NodeRec<T>*, long, int, NodeRec<T>*, int*, long long*,          \
-                                       cudaStream_t);                                                        \
+                                       cudaStream_t, bool);                                                  \
     template int tile_sort<PointRec<T>>(const PointRec<T>*, long, int, PointRec<T>*, int*, long long*,       \
-                                        cudaStream_t);                                                       \
+                                        cudaStream_t, bool);                                                 \
     template int node_step_tiled<T>(const NodeRec<T>*, const long long*, const FarGeom&, const cx_t<T>*,     \
                                     cx_t<T>*, cx_t<T>*, cudaStream_t);                                       \
     template size_t node_fused_smem<T>(int, int);                                                            \

@@ -9,11 +9,16 @@
 namespace sbd {
 
 constexpr int kNodeTile = 64;   // grid tile side (cells); must be >= stencil width - 1
+constexpr int kBinSide = 8;     // bin side (cells) of the binned node kernel: >= stencil width
 
 // Sort records by the tile of their stencil start on an n x n grid; perm[sorted] =
-// original index; tile_start has ceil(n/64)^2 + 1 entries.
+// original index; tile_start has ceil(n/64)^2 + 1 entries.  Inside a tile of at most
+// kTileSortMax records: by original index, or with by_bin by (8 x 8 bin of the stencil
+// start, original index).
+constexpr int kTileSortMax = 4096;
 template <typename Rec>
-int tile_sort(const Rec* in, long n_rec, int n, Rec* sorted, int* perm, long long* tile_start, cudaStream_t s);
+int tile_sort(const Rec* in, long n_rec, int n, Rec* sorted, int* perm, long long* tile_start, cudaStream_t s,
+              bool by_bin = false);
 
 // kout (nk x nk, fully written) = scatter(omega' * gather(kin)); ghat is n_xi scratch.
 template <typename T>
@@ -21,10 +26,13 @@ int node_step_tiled(const NodeRec<T>* nodes, const long long* tile_start, const 
                     const cx_t<T>* kin, cx_t<T>* ghat, cx_t<T>* kout, cudaStream_t s);
 
 // Variant of the fused node kernel (see node.cu): acc 0 = two float planes with
-// atomicAdd, 1 = one float2 plane with a 64-bit compare-and-swap (FP32 only); sched 0 =
-// records dealt to the lane groups in turn, 1 = one contiguous run per group.
+// atomicAdd, 1 = one float2 plane with a 64-bit compare-and-swap (FP32 only), 2 = int64
+// fixed point (FP32 only), 3 = binned, no atomics in shared memory (FP32 only; records
+// sorted by tile_sort with by_bin, every tile within kTileSortMax records, stencil <= 8).
+// acc 0-2: sched 0 = records dealt to the lane groups in turn, 1 = one contiguous run per
+// group; acc 3: sched 0 = 512 threads per CTA, 1 = 1024.
 struct NodeTuning {
-    int acc = 0;          // 0 float planes, 1 float2 CAS (FP32), 2 int64 fixed point (FP32)
+    int acc = 0;
     int sched = 0;
     float wbound = 0.f;   // max |omega'| component x P_k^2 (the fixed-point scale bound)
 };

@@ -51,7 +51,7 @@ class sbd_plan_stats(ctypes.Structure):
                 ("a", ctypes.c_double), ("fit_err", ctypes.c_double), ("nufft_tol", ctypes.c_double),
                 ("w0_re", ctypes.c_double), ("w0_im", ctypes.c_double), ("device_bytes", ctypes.c_int64),
                 ("plan_seconds", ctypes.c_double), ("n_records", ctypes.c_int64), ("node_acc", ctypes.c_int32),
-                ("node_sched", ctypes.c_int32), ("fft_split", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("node_sched", ctypes.c_int32), ("fft_split", ctypes.c_int32), ("node_binned", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -293,9 +293,10 @@ def sbd_fit_cache_stats() -> dict:
 
 
 def sbd_tune(plan: int, reps: int = 3, stream=None) -> list:
-    """Time the node-kernel variants, keep the fastest; returns ms per variant (acc * 2 + sched)."""
+    """Time the node-kernel and row-FFT variants, keep the fastest; returns ms per node variant
+    (index acc * 2 + sched, -1 where not applicable) and, at 8 and 9, per FFT split (0, 2)."""
     import numpy as np
-    ms = np.zeros(8)
+    ms = np.zeros(10)
     _check(lib.sbd_tune(plan, reps, ms.ctypes.data, _stream(stream)), "sbd_tune")
     return ms.tolist()
 

@@ -1,8 +1,9 @@
 """GPU: the node-kernel variants chosen by sbd_tune compute the same matvec.
 
-Each variant sums the same products in another order (or with another atomic), so
-results agree to FP32 rounding (rel-L2 <= 2e-6 between variants) and each stays
-within eps sum|f| of the oracle's direct sum (Sec. 1 output bound)."""
+Each variant sums the same products in another order (with another atomic, or bin by
+bin without atomics), so results agree to FP32 rounding (rel-L2 <= 2e-6 between
+variants) and each stays within eps sum|f| of the oracle's direct sum (Sec. 1 output
+bound)."""
 import numpy as np
 import pytest
 
@@ -39,8 +40,9 @@ def test_variants_agree_and_tune_picks_one(S, kind):
     p = S.sbd_plan(zt, n, S.SBD_HELMHOLTZ if kind == "helmholtz" else S.SBD_LAPLACE, kappa, dmin, 1e-6,
                    S.make_options(form=S.SBD_FORM_FP32))
     try:
+        assert S.sbd_plan_info(p)["node_binned"] == 1          # FP32, 8-cell stencils, small tiles
         outs = {}
-        for acc in (0, 1, 2):
+        for acc in (0, 1, 2, 3):
             for sched in (0, 1):
                 for split in (0, 2):
                     S.sbd_set_tuning(p, acc, sched, split)
@@ -58,9 +60,9 @@ def test_variants_agree_and_tune_picks_one(S, kind):
         for k, v in outs.items():
             assert np.max(np.abs(v[idx] - ref)) <= 1e-6 * np.abs(f).sum(), k
         ms = S.sbd_tune(p, reps=2)
-        assert len(ms) == 8 and all(t > 0 for t in ms)
+        assert len(ms) == 10 and all(t > 0 for t in ms)
         info = S.sbd_plan_info(p)
-        best = int(np.argmin(ms[:6]))
+        best = int(np.argmin(ms[:8]))
         assert (info["node_acc"], info["node_sched"]) == (best // 2, best % 2)
     finally:
         S.sbd_destroy(p)
@@ -71,11 +73,12 @@ def test_fp64_rejects_cas_variant(S):
     zt = torch.from_numpy(wl.z).cuda()
     p = S.sbd_plan(zt, 500, S.SBD_LAPLACE, 0.0, wl.delta_min, 1e-6, S.make_options(form=S.SBD_FORM_FP64))
     try:
-        for acc in (1, 2):
+        assert S.sbd_plan_info(p)["node_binned"] == 0
+        for acc in (1, 2, 3):
             with pytest.raises(S.SbdError) as e:
                 S.sbd_set_tuning(p, acc, 0, 0)
             assert e.value.code == S.SBD_EINVAL
         ms = S.sbd_tune(p, reps=1)
-        assert ms[0] > 0 and ms[1] > 0 and all(t == -1 for t in ms[2:6]) and ms[6] > 0 and ms[7] > 0
+        assert ms[0] > 0 and ms[1] > 0 and all(t == -1 for t in ms[2:8]) and ms[8] > 0 and ms[9] > 0
     finally:
         S.sbd_destroy(p)
