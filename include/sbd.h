@@ -263,8 +263,8 @@ int sbd_fft2(const void* in, void* out, int32_t n0, int32_t n1, int32_t sign, in
  * gives each group a contiguous run.  acc 3 (FP32 form, node stencil of at most 8
  * cells, every 64 x 64 tile of the frequency grid holding at most 4096 records) takes
  * the records bin by bin (8 x 8 stencil starts; four accumulators, one per bin colour,
- * so that no two warps write one cell and no atomics are needed); sched 0 runs 512
- * threads per CTA, sched 1 1024.  Results agree to FP32 rounding.
+ * so that no two warps write one cell and no atomics are needed); for it sched 0 runs
+ * 512 threads per CTA, sched 1 1024.  Results agree to FP32 rounding.
  *   sbd_tune       times every applicable variant on the plan's own records (reps
  *                  launches each, after one warm-up, CUDA events on cuda_stream; the
  *                  frequency workspace is first filled with a constant non-zero value,

@@ -321,6 +321,7 @@ int build_far(sbd_plan_s* p, cudaStream_t s) {
         long long most = 0;
         for (size_t t = 0; t + 1 < ts.size(); ++t) most = std::max(most, ts[t + 1] - ts[t]);
         p->node_binned = p->node_fused && most <= kTileSortMax && node_fused_smem<T>(np.Pk, 3) <= 227 * 1024;
+        if (p->node_binned) p->tuning.acc = 3, p->tuning.sched = 1;   // the fastest untuned choice
     }
     if (!p->node_fused && (rc = dev_alloc(p, &p->ghat, sizeof(cx_t<T>) * p->n_rec))) return rc;
     std::vector<T> dec(np.m);

@@ -496,6 +496,7 @@ __global__ void __launch_bounds__(NT) node_fused_kernel(
 //           record k's sum in lanes 8k..8k+7, which multiply it by omega'_k;
 //   scatter one record after the other (a warp barrier between them, the stencils of one
 //           bin overlap), plain loads and stores into the colour's accumulator.
+// Bins go out largest first, which shortens the tail of the tile.
 // Every accumulator cell thus receives the records of one bin, in a fixed order, and
 // the four colours are summed in a fixed order: the result is the same on every run.
 constexpr int kBinW = kNodeTile + kBinSide - 1;                 // 71: rows / cols any stencil reaches
@@ -513,6 +514,7 @@ __global__ void __launch_bounds__(NT, 1) node_binned_kernel(
     Window<float> win, const float2* __restrict__ kin, float2* __restrict__ kout) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int bstart[kBins + 1];
+    __shared__ int border[kBins];                                   // bins, largest first
     __shared__ int next_bin;
     const int tile = blockIdx.x;
     const long long b0 = tile_start[tile], b1 = tile_start[tile + 1];
@@ -544,6 +546,23 @@ __global__ void __launch_bounds__(NT, 1) node_binned_kernel(
         for (int k = bp + 1; k <= bi; ++k) bstart[k] = i;
     }
     __syncthreads();
+    // largest bins first (ties by bin): C threads rank one bin against 64 / C others each
+    {
+        constexpr int C = NT / kBins;
+        static_assert(C >= 1 && C <= 32 && (C & (C - 1)) == 0, "rank split");
+        const int t = tid / C, c = tid % C;
+        const int nt = bstart[t + 1] - bstart[t];
+        int rank = 0;
+#pragma unroll
+        for (int u = c * (kBins / C); u < (c + 1) * (kBins / C); ++u) {
+            const int nu = bstart[u + 1] - bstart[u];
+            rank += (nu > nt || (nu == nt && u < t)) ? 1 : 0;
+        }
+#pragma unroll
+        for (int o = C / 2; o > 0; o >>= 1) rank += __shfl_xor_sync(0xffffffffu, rank, o, C);
+        if (c == 0) border[rank] = t;
+    }
+    __syncthreads();
     const unsigned full = 0xffffffffu;
     const int lane = tid & 31;
     const int kown = lane >> 3, sub = lane & 7;                     // window lane: record, offset
@@ -551,19 +570,23 @@ __global__ void __launch_bounds__(NT, 1) node_binned_kernel(
     const float offw = static_cast<float>(sub - P / 2 + 1);
     const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4;
     for (;;) {
-        int bin = 0;
-        if (lane == 0) bin = atomicAdd(&next_bin, 1);
-        bin = __shfl_sync(full, bin, 0);
-        if (bin >= kBins) break;
+        int slot = 0;
+        if (lane == 0) slot = atomicAdd(&next_bin, 1);
+        slot = __shfl_sync(full, slot, 0);
+        if (slot >= kBins) break;
+        const int bin = border[slot];
         float2* ac = acc + (((bin / (kNodeTile / kBinSide)) & 1) * 2 + (bin & 1)) * plane;
         const int e0 = min(bstart[bin], cnt), e1 = min(max(bstart[bin + 1], e0), cnt);
+        NodeRec<float> nxt;                                         // record of the next quad
+        if (e0 + kown < e1) nxt = rec[b0 + e0 + kown];
         for (int j = e0; j < e1; j += 4) {
             const int jr = j + kown;
             int base = 0;
             float wx = 0.f, wy = 0.f;
             float2 om = make_float2(0.f, 0.f);
             if (jr < e1) {
-                const NodeRec<float> q = rec[b0 + jr];
+                const NodeRec<float> q = nxt;
+                if (jr + 4 < e1) nxt = rec[b0 + jr + 4];
                 base = (q.cell.x - ox) * kBinWs + (q.cell.y - oy);
                 if (sub < P) {
                     wx = win(offw - q.frac.x);
