@@ -61,10 +61,12 @@ typedef struct {
     double  kappa;     /* wavenumber (> 0) for SBD_HELMHOLTZ; ignored for SBD_LAPLACE */
 } sbd_kernel;
 
-/* Arithmetic of the far part.  FP64: spread, FFT, node step and interpolation in
- * float64.  FP32: those steps in float32 (coordinates split as an integer cell
- * plus a float32 fraction computed in float64); the close correction D f and the
- * final accumulation stay in float64 in both forms. */
+/* Arithmetic of the on-line part.  FP64: spread, FFT, node step and interpolation in
+ * float64, D (computed in float64) stored and applied in float64.  FP32: those steps
+ * in float32 (coordinates split as an integer cell plus a float32 fraction computed
+ * in float64), D rounded to float32 once built and applied to f rounded to float32
+ * (products and per-thread partial sums in float32, the partials of a row added in
+ * float64); the xi = 0 term and the final accumulation stay in float64 in both forms. */
 typedef enum { SBD_FORM_FP64 = 0, SBD_FORM_FP32 = 1 } sbd_form;
 
 typedef struct {
@@ -215,8 +217,9 @@ int sbd_plan_export(sbd_plan_t plan, int64_t cap, double* rho, double* alpha, in
                     double* radius, double* weight_re, double* weight_im);
 
 /* Copy D (Eq. defD) to host CSR arrays: rowptr (N + 1), col (nnz), val (nnz float64
- * for Laplace, 2 nnz float64 = complex128 for Helmholtz).  Column order within a
- * row is unspecified.  Synchronous. */
+ * for Laplace, 2 nnz float64 = complex128 for Helmholtz; an FP32-form plan's values
+ * are the float32 ones it stores, widened).  Column order within a row is
+ * unspecified.  Synchronous. */
 int sbd_close_export(sbd_plan_t plan, int64_t* rowptr, int32_t* col, double* val);
 
 /* Release the plan (NULL is accepted).  sbd_destroy first waits for the whole device, so

@@ -87,6 +87,7 @@ struct sbd_plan_s {
                                        // internal order of D's rows and columns)
     void* f_int = nullptr;             // f in internal order, right-hand sides interleaved
     void* q_int = nullptr;             // D f in internal order, interleaved
+    bool d32 = false;                  // D's values and f_int in FP32 (the FP32 form)
     long long* pt_tile_start = nullptr;
     long long* node_tile_start = nullptr;
     void* ghat = nullptr;              // n_xi weighted node values (scratch of the two-kernel node step)
@@ -109,6 +110,10 @@ struct sbd_plan_s {
     std::vector<cudaGraphExec_t> g_exec;
     cudaStream_t g_stream = nullptr;
     cudaEvent_t g_ev_in = nullptr, g_ev_out = nullptr;
+    // the near-field product D f runs on its own stream, beside the far part, and joins it
+    // before the interpolation (which adds D f)
+    cudaStream_t near_stream = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     cudaStream_t alloc_stream = nullptr;   // stream of the allocations being made
     long long device_bytes = 0;
     double plan_seconds = 0.0;
@@ -213,6 +218,9 @@ void free_plan(sbd_plan_s* p, bool wait_device, cudaStream_t s) {
     if (p->g_ev_in) cudaEventDestroy(p->g_ev_in);
     if (p->g_ev_out) cudaEventDestroy(p->g_ev_out);
     if (p->g_stream) cudaStreamDestroy(p->g_stream);
+    if (p->ev_fork) cudaEventDestroy(p->ev_fork);
+    if (p->ev_join) cudaEventDestroy(p->ev_join);
+    if (p->near_stream) cudaStreamDestroy(p->near_stream);
     for (void* a : p->allocations) cudaFreeAsync(a, s);
     if (p->rowptr) cudaFreeAsync(p->rowptr, s);
     if (p->col) cudaFreeAsync(p->col, s);
@@ -417,7 +425,8 @@ int inverse_fft_real(sbd_plan_s* p, const cx_t<T>* S, cx_t<T>* A, cx_t<T>* Tr, c
 
 // q = far part of f (+ the internal-order near term add[i * nrhs + r] when add is given).
 template <typename T>
-int far_apply(sbd_plan_s* p, const void* f, void* q, int nrhs, cudaStream_t s, const void* add) {
+int far_apply(sbd_plan_s* p, const void* f, void* q, int nrhs, cudaStream_t s, const void* add,
+              cudaEvent_t join = nullptr) {
     const bool cplx_io = p->kind == SBD_HELMHOLTZ;
     StepTimer t_sum(p, s, SBD_STAGE_SUM);
     int rc = far_sum(f, cplx_io, p->n, nrhs, p->sumf, s);
@@ -452,6 +461,7 @@ int far_apply(sbd_plan_s* p, const void* f, void* q, int nrhs, cudaStream_t s, c
         StepTimer t4(p, s, SBD_STAGE_FFT_INV);
         if ((rc = real ? inverse_fft_real<T>(p, C, A, B, X, s) : inverse_fft<T>(p, C, A, B, X, s, false))) return rc;
         t4.end();
+        if (join && r == 0) SBD_CUDA_TRY(cudaStreamWaitEvent(s, join, 0));   // D f is ready
         StepTimer t5(p, s, SBD_STAGE_INTERP);
         if ((rc = interp_tiled<T>(static_cast<const PointRec<T>*>(p->pts), p->pt_perm, p->pt_tile_start, p->geom, X,
                                   w0, p->sumf + r, qr, cplx_io, s, real, add, nrhs, r))) return rc;
@@ -610,6 +620,13 @@ int sbd_plan(const double* points, int64_t n, sbd_kernel kernel, double delta_mi
     if (o.host_threads > 0) omp_set_num_threads(o.host_threads);   // this thread's parallel regions
     keep_pool_memory();
     auto* p = new sbd_plan_s();
+    if (cudaStreamCreateWithFlags(&p->near_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+        set_error("sbd_plan: cannot create the plan's stream and events");
+        free_plan(p, false, s);
+        return SBD_ECUDA;
+    }
     p->alloc_stream = s;
     p->kind = kernel.kind;
     p->kappa = kernel.kappa;
@@ -714,11 +731,16 @@ int sbd_plan(const double* points, int64_t n, sbd_kernel kernel, double delta_mi
         cudaFreeAsync(zs, s);
         if (rc) return fail(rc);
     }
-    p->device_bytes += static_cast<long long>(sizeof(long long) * (p->n + 1) + (sizeof(int) + (cval ? 16 : 8)) * p->nnz);
+    // the FP32 form keeps D and the gathered f in FP32 (D f is one more FP32-level term of
+    // the output; GB300's FP64 rate would otherwise bound the product)
+    p->d32 = o.form == SBD_FORM_FP32;
+    if (p->d32 && (rc = near_values_to_f32(&p->val, p->nnz, cval, s))) return fail(rc);
+    const size_t dvb = (cval ? 2 : 1) * (p->d32 ? sizeof(float) : sizeof(double));
+    p->device_bytes += static_cast<long long>(sizeof(long long) * (p->n + 1) + (sizeof(int) + dvb) * p->nnz);
     p->n_coinc /= 2;
     {
         const size_t vb = (cval ? 16 : 8) * static_cast<size_t>(p->n) * p->max_nrhs;
-        if ((rc = dev_alloc(p, &p->f_int, vb))) return fail(rc);
+        if ((rc = dev_alloc(p, &p->f_int, dvb * static_cast<size_t>(p->n) * p->max_nrhs))) return fail(rc);
         if ((rc = dev_alloc(p, &p->q_int, vb))) return fail(rc);
     }
     if ((rc = dev_alloc(p, reinterpret_cast<void**>(&p->sumf), sizeof(double2) * p->max_nrhs))) return fail(rc);
@@ -748,9 +770,9 @@ namespace {
 // q_int = D f in the internal order (f gathered into f_int first)
 int close_internal(sbd_plan_s* p, const void* f, int nrhs, cudaStream_t s) {
     const bool c = p->kind == SBD_HELMHOLTZ;
-    int rc = near_gather(f, c, p->n, nrhs, p->pt_perm, p->f_int, s);
+    int rc = near_gather(f, c, p->n, nrhs, p->pt_perm, p->f_int, s, p->d32);
     if (rc) return rc;
-    return near_spmv_internal(p->rowptr, p->col, p->val, c, p->n, nrhs, p->f_int, p->q_int, s);
+    return near_spmv_internal(p->rowptr, p->col, p->val, c, p->n, nrhs, p->f_int, p->q_int, s, p->d32);
 }
 }  // namespace
 
@@ -774,12 +796,22 @@ int sbd_matvec(sbd_plan_t p, const void* f, void* q, int32_t nrhs, void* cuda_st
         return SBD_EINVAL;
     }
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
-    // D f first, in the internal order; the interpolation adds it as it writes q
-    StepTimer t(p, s, SBD_STAGE_SPMV);
-    if ((rc = close_internal(p, f, nrhs, s))) return rc;
-    t.end();
-    return p->form == SBD_FORM_FP32 ? far_apply<float>(p, f, q, nrhs, s, p->q_int)
-                                    : far_apply<double>(p, f, q, nrhs, s, p->q_int);
+    if (p->profile) {
+        // step timing: D f first, alone, then the far part (the interpolation adds D f)
+        StepTimer t(p, s, SBD_STAGE_SPMV);
+        if ((rc = close_internal(p, f, nrhs, s))) return rc;
+        t.end();
+        return p->form == SBD_FORM_FP32 ? far_apply<float>(p, f, q, nrhs, s, p->q_int)
+                                        : far_apply<double>(p, f, q, nrhs, s, p->q_int);
+    }
+    // D f (memory-bound) on the near stream while the far part's first steps (bound by
+    // arithmetic and shared memory) run on s; s waits for it before the interpolation
+    SBD_CUDA_TRY(cudaEventRecord(p->ev_fork, s));
+    SBD_CUDA_TRY(cudaStreamWaitEvent(p->near_stream, p->ev_fork, 0));
+    if ((rc = close_internal(p, f, nrhs, p->near_stream))) return rc;
+    SBD_CUDA_TRY(cudaEventRecord(p->ev_join, p->near_stream));
+    return p->form == SBD_FORM_FP32 ? far_apply<float>(p, f, q, nrhs, s, p->q_int, p->ev_join)
+                                    : far_apply<double>(p, f, q, nrhs, s, p->q_int, p->ev_join);
 }
 
 int sbd_matvec_graph(sbd_plan_t p, const void* f, void* q, int32_t nrhs, void* cuda_stream) {
@@ -1082,7 +1114,14 @@ int sbd_close_export(sbd_plan_t p, int64_t* rowptr, int32_t* col, double* val) {
     std::vector<unsigned char> vl(vb * p->nnz);
     SBD_CUDA_TRY(cudaMemcpy(rp.data(), p->rowptr, sizeof(long long) * (n + 1), cudaMemcpyDeviceToHost));
     SBD_CUDA_TRY(cudaMemcpy(cl.data(), p->col, sizeof(int) * p->nnz, cudaMemcpyDeviceToHost));
-    SBD_CUDA_TRY(cudaMemcpy(vl.data(), p->val, vb * p->nnz, cudaMemcpyDeviceToHost));
+    if (p->d32) {   // stored in FP32: widen
+        std::vector<float> v32(vb / 8 * p->nnz);
+        SBD_CUDA_TRY(cudaMemcpy(v32.data(), p->val, sizeof(float) * v32.size(), cudaMemcpyDeviceToHost));
+        double* vd = reinterpret_cast<double*>(vl.data());
+        for (size_t i = 0; i < v32.size(); ++i) vd[i] = v32[i];
+    } else {
+        SBD_CUDA_TRY(cudaMemcpy(vl.data(), p->val, vb * p->nnz, cudaMemcpyDeviceToHost));
+    }
     SBD_CUDA_TRY(cudaMemcpy(perm.data(), p->pt_perm, sizeof(int) * n, cudaMemcpyDeviceToHost));
     std::vector<long> inv(n);
     for (long i = 0; i < n; ++i) inv[perm[i]] = i;

@@ -250,7 +250,7 @@ __global__ void spmv_kernel(const long long* __restrict__ rowptr, const int* __r
 }
 
 // Internal (spatially sorted) order: fp[i * nrhs + r] = f[r * n + perm[i]].
-template <bool CPLX>
+template <bool CPLX, bool F32>
 __global__ void gather_rows_kernel(const void* __restrict__ f, long n, int nrhs, const int* __restrict__ perm,
                                    void* __restrict__ fp) {
     const long t = blockIdx.x * static_cast<long>(blockDim.x) + threadIdx.x;
@@ -258,8 +258,15 @@ __global__ void gather_rows_kernel(const void* __restrict__ f, long n, int nrhs,
     const long i = t / nrhs;
     const int r = static_cast<int>(t - i * nrhs);
     const long src = static_cast<long>(r) * n + perm[i];
-    if (CPLX) static_cast<double2*>(fp)[t] = static_cast<const double2*>(f)[src];
-    else static_cast<double*>(fp)[t] = static_cast<const double*>(f)[src];
+    if (CPLX) {
+        const double2 v = static_cast<const double2*>(f)[src];
+        if (F32) static_cast<float2*>(fp)[t] = make_float2(static_cast<float>(v.x), static_cast<float>(v.y));
+        else static_cast<double2*>(fp)[t] = v;
+    } else {
+        const double v = static_cast<const double*>(f)[src];
+        if (F32) static_cast<float*>(fp)[t] = static_cast<float>(v);
+        else static_cast<double*>(fp)[t] = v;
+    }
 }
 
 // q[r * n + perm[i]] = qp[i * nrhs + r]
@@ -305,6 +312,74 @@ __global__ void spmv_rhs_kernel(const long long* __restrict__ rowptr, const int*
         for (long long j = b; j < e; ++j) acc += v[j] * x[static_cast<long>(col[j]) * nrhs + r];
         static_cast<double*>(qp)[t] = acc;
     }
+}
+
+// FP32 storage of D and of the gathered f (the FP32 form): products and the per-lane
+// (per-thread) partial sums in FP32, the partials of a row combined in FP64.
+template <bool CPLX> struct F32Val;
+template <> struct F32Val<false> { using V = float; };
+template <> struct F32Val<true> { using V = float2; };
+__device__ __forceinline__ void mac32(float& sr, float& si, float a, float x) { sr = fmaf(a, x, sr); (void)si; }
+__device__ __forceinline__ void mac32(float& sr, float& si, float2 a, float2 x) {
+    sr = fmaf(a.x, x.x, fmaf(-a.y, x.y, sr));
+    si = fmaf(a.x, x.y, fmaf(a.y, x.x, si));
+}
+
+template <bool CPLX>
+__global__ void spmv32_kernel(const long long* __restrict__ rowptr, const int* __restrict__ col,
+                              const void* __restrict__ val, long n, const void* __restrict__ fp,
+                              void* __restrict__ qp) {
+    using V = typename F32Val<CPLX>::V;
+    const long row = (blockIdx.x * static_cast<long>(blockDim.x) + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (row >= n) return;
+    const long long b = rowptr[row], e = rowptr[row + 1];
+    const V* v = static_cast<const V*>(val);
+    const V* x = static_cast<const V*>(fp);
+    float pr = 0.f, pi = 0.f;
+    for (long long j = b + lane; j < e; j += 32) mac32(pr, pi, v[j], x[col[j]]);
+    double sr = pr, si = pi;
+    for (int o = 16; o > 0; o >>= 1) {
+        sr += __shfl_down_sync(0xffffffffu, sr, o);
+        if (CPLX) si += __shfl_down_sync(0xffffffffu, si, o);
+    }
+    if (lane == 0) {
+        if (CPLX) static_cast<double2*>(qp)[row] = make_double2(sr, si);
+        else static_cast<double*>(qp)[row] = sr;
+    }
+}
+
+template <bool CPLX>
+__global__ void spmv32_rhs_kernel(const long long* __restrict__ rowptr, const int* __restrict__ col,
+                                  const void* __restrict__ val, long n, int nrhs, const void* __restrict__ fp,
+                                  void* __restrict__ qp) {
+    using V = typename F32Val<CPLX>::V;
+    const long t = blockIdx.x * static_cast<long>(blockDim.x) + threadIdx.x;
+    if (t >= n * nrhs) return;
+    const long row = t / nrhs;
+    const int r = static_cast<int>(t - row * nrhs);
+    const long long b = rowptr[row], e = rowptr[row + 1];
+    const V* v = static_cast<const V*>(val);
+    const V* x = static_cast<const V*>(fp);
+    // two partial sums (entries of even and odd offset) keep two loads in flight
+    float ar = 0.f, ai = 0.f, br = 0.f, bi = 0.f;
+    long long j = b;
+    for (; j + 1 < e; j += 2) {
+        const int c0 = col[j], c1 = col[j + 1];
+        const V a0 = v[j], a1 = v[j + 1];
+        const V x0 = x[static_cast<long>(c0) * nrhs + r], x1 = x[static_cast<long>(c1) * nrhs + r];
+        mac32(ar, ai, a0, x0);
+        mac32(br, bi, a1, x1);
+    }
+    if (j < e) mac32(ar, ai, v[j], x[static_cast<long>(col[j]) * nrhs + r]);
+    const double sr = static_cast<double>(ar) + br, si = static_cast<double>(ai) + bi;
+    if (CPLX) static_cast<double2*>(qp)[t] = make_double2(sr, si);
+    else static_cast<double*>(qp)[t] = sr;
+}
+
+__global__ void to_f32_kernel(const double* __restrict__ in, long count, float* __restrict__ out) {
+    const long i = blockIdx.x * static_cast<long>(blockDim.x) + threadIdx.x;
+    if (i < count) out[i] = static_cast<float>(in[i]);
 }
 
 // --- exclusive scan of 64-bit integers: per-chunk scan, chunk totals, offsets ------------
@@ -489,12 +564,30 @@ int near_spmv(const long long* rowptr, const int* col, const void* val, bool cva
     return SBD_OK;
 }
 
-int near_gather(const void* f, bool cplx, long n, int nrhs, const int* perm, void* fp, cudaStream_t s) {
+int near_gather(const void* f, bool cplx, long n, int nrhs, const int* perm, void* fp, cudaStream_t s, bool f32) {
     if (n <= 0) return SBD_OK;
     const long t = n * nrhs;
-    if (cplx) gather_rows_kernel<true><<<nblk(t), kT, 0, s>>>(f, n, nrhs, perm, fp);
-    else gather_rows_kernel<false><<<nblk(t), kT, 0, s>>>(f, n, nrhs, perm, fp);
+    if (cplx) {
+        if (f32) gather_rows_kernel<true, true><<<nblk(t), kT, 0, s>>>(f, n, nrhs, perm, fp);
+        else gather_rows_kernel<true, false><<<nblk(t), kT, 0, s>>>(f, n, nrhs, perm, fp);
+    } else {
+        if (f32) gather_rows_kernel<false, true><<<nblk(t), kT, 0, s>>>(f, n, nrhs, perm, fp);
+        else gather_rows_kernel<false, false><<<nblk(t), kT, 0, s>>>(f, n, nrhs, perm, fp);
+    }
     SBD_LAUNCH_CHECK();
+    return SBD_OK;
+}
+
+int near_values_to_f32(void** val, long long nnz, bool cplx, cudaStream_t s) {
+    const long count = static_cast<long>(nnz) * (cplx ? 2 : 1);
+    float* out = nullptr;
+    SBD_CUDA_TRY(cudaMallocAsync(&out, sizeof(float) * std::max(count, 1L), s));
+    if (count > 0) {
+        to_f32_kernel<<<nblk(count), kT, 0, s>>>(static_cast<const double*>(*val), count, out);
+        SBD_LAUNCH_CHECK();
+    }
+    SBD_CUDA_TRY(cudaFreeAsync(*val, s));
+    *val = out;
     return SBD_OK;
 }
 
@@ -508,9 +601,19 @@ int near_scatter(const void* qp, bool cplx, long n, int nrhs, const int* perm, v
 }
 
 int near_spmv_internal(const long long* rowptr, const int* col, const void* val, bool cval, long n, int nrhs,
-                       const void* fp, void* qp, cudaStream_t s) {
+                       const void* fp, void* qp, cudaStream_t s, bool f32) {
     if (n <= 0) return SBD_OK;
-    if (nrhs == 1) {   // one warp per row (rows of ~10^2 entries), same layout
+    if (f32) {
+        if (nrhs == 1) {
+            const long threads = n * 32;
+            if (cval) spmv32_kernel<true><<<nblk(threads), kT, 0, s>>>(rowptr, col, val, n, fp, qp);
+            else spmv32_kernel<false><<<nblk(threads), kT, 0, s>>>(rowptr, col, val, n, fp, qp);
+        } else {
+            const long t = n * nrhs;
+            if (cval) spmv32_rhs_kernel<true><<<nblk(t), kT, 0, s>>>(rowptr, col, val, n, nrhs, fp, qp);
+            else spmv32_rhs_kernel<false><<<nblk(t), kT, 0, s>>>(rowptr, col, val, n, nrhs, fp, qp);
+        }
+    } else if (nrhs == 1) {   // one warp per row (rows of ~10^2 entries), same layout
         const long threads = n * 32;
         if (cval) spmv_kernel<true><<<nblk(threads), kT, 0, s>>>(rowptr, col, val, n, 1, fp, qp, false);
         else spmv_kernel<false><<<nblk(threads), kT, 0, s>>>(rowptr, col, val, n, 1, fp, qp, false);

@@ -1,5 +1,6 @@
 // Near field: fixed-radius neighbour search (Sec. 1 / Sec. 6.1) into CSR, the values
-// of the close-correction matrix D (Eq. defD) in FP64, and the SpMV q += D f.
+// of the close-correction matrix D (Eq. defD) in FP64 (optionally stored as FP32), and
+// the SpMV q += D f.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -40,10 +41,15 @@ int near_spmv(const long long* rowptr, const int* col, const void* val, bool com
 // keeps the columns of a row close together): fp[i * nrhs + r] = f[r * n + perm[i]]
 // (near_gather), qp = D fp with D over internal indices and interleaved right-hand
 // sides (near_spmv_internal), q[r * n + perm[i]] = qp[i * nrhs + r] (near_scatter).
-// Values are float64 (real) or complex128 (cplx).
-int near_gather(const void* f, bool cplx, long n, int nrhs, const int* perm, void* fp, cudaStream_t s);
+// f and qp are float64 (real) or complex128 (cplx).  f32: D's values (near_values_to_f32)
+// and fp are float32 / complex64, products and per-thread partial sums FP32, the partial
+// sums of a row combined in FP64; qp stays float64 / complex128.
+int near_gather(const void* f, bool cplx, long n, int nrhs, const int* perm, void* fp, cudaStream_t s,
+                bool f32 = false);
 int near_spmv_internal(const long long* rowptr, const int* col, const void* val, bool complex_vals, long n,
-                       int nrhs, const void* fp, void* qp, cudaStream_t s);
+                       int nrhs, const void* fp, void* qp, cudaStream_t s, bool f32 = false);
+// Replaces the FP64 values *val (nnz entries, complex when cplx) by FP32 ones (stream-ordered).
+int near_values_to_f32(void** val, long long nnz, bool cplx, cudaStream_t s);
 int near_scatter(const void* qp, bool cplx, long n, int nrhs, const int* perm, void* q, cudaStream_t s);
 
 // Exclusive scan of n 64-bit counts in place; total returned in *total (host), synchronising s.
