@@ -296,15 +296,18 @@ __device__ __forceinline__ cx_t<T> load_elem(int io, int idx, int n, const cx_t<
     return v;
 }
 
-template <typename T, int NT>
+// SIGN (-1 forward, +1 inverse) is a template argument: the factors +-i of the butterflies
+// and the conjugation of the twiddles fold into the arithmetic.
+template <typename T, int NT, int SIGN>
 __global__ void __launch_bounds__(NT) fft_rows_kernel(
     const cx_t<T>* __restrict__ in, long in_stride, int in_len, int in_shift,
     cx_t<T>* __restrict__ out, long out_stride, int out_len, int out_shift,
-    int n, int Q, int sign, FftPlan1D plan, const cx_t<T>* __restrict__ tw, const int* __restrict__ perm,
+    int n, int Q, FftPlan1D plan, const cx_t<T>* __restrict__ tw, const int* __restrict__ perm,
     const T* __restrict__ pre_elem, const T* __restrict__ pre_row,
     const T* __restrict__ post_elem, const T* __restrict__ post_row, HermFold<T> hf, int io,
     const cx_t<T>* __restrict__ tw2) {
     using C = cx_t<T>;
+    constexpr int sign = SIGN;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* s = reinterpret_cast<C*>(smem_raw);
     const long row = blockIdx.y;     // phases of a row are adjacent CTAs (they read the same row)
@@ -517,6 +520,22 @@ static int fft_phases(int n, bool fp64) {
 
 int fft_max_length(bool fp64) { return 2 * fft_max_row(fp64); }
 
+// Launches fft_rows_kernel<T, NT, sign> with the given arguments (sign -1 or +1).
+template <typename T, int NT, typename... A>
+int launch_fft_rows(int sign, dim3 grid, size_t smem, cudaStream_t stream, A... args) {
+    if (sign < 0) {
+        auto k = fft_rows_kernel<T, NT, -1>;
+        SBD_TRY(raise_smem_limit(k, smem));
+        k<<<grid, NT, smem, stream>>>(args...);
+    } else {
+        auto k = fft_rows_kernel<T, NT, 1>;
+        SBD_TRY(raise_smem_limit(k, smem));
+        k<<<grid, NT, smem, stream>>>(args...);
+    }
+    SBD_LAUNCH_CHECK();
+    return SBD_OK;
+}
+
 template <typename T>
 int fft_rows(const cx_t<T>* in, long in_stride, int in_len, int in_shift,
              cx_t<T>* out, long out_stride, int out_len, int out_shift,
@@ -564,25 +583,23 @@ int fft_rows(const cx_t<T>* in, long in_stride, int in_len, int in_shift,
         const T* por = post_row ? post_row + r0 * (io == kIoPairInv ? 2 : 1) : nullptr;
         const HermFold<T> hf{in - static_cast<long>(herm_row0) * in_stride, herm_n,
                              static_cast<long>(herm_row0) + r0};
+        int rc;
         if (nq > 2048 && split == 2) {
             // half-length phases: two CTAs of 512 threads share an SM (registers and shared
             // memory both allow it), instead of one 1024-thread CTA per full-length row
-            auto k = fft_rows_kernel<T, 512>;
-            SBD_TRY(raise_smem_limit(k, smem));
-            k<<<grid, 512, smem, stream>>>(ip, in_stride, in_len, in_shift, op, out_stride, out_len, out_shift,
-                                           n, Q, sign, plan, tw, perm, pre_elem, prr, post_elem, por, hf, io, tw2);
+            rc = launch_fft_rows<T, 512>(sign, grid, smem, stream, ip, in_stride, in_len, in_shift, op, out_stride,
+                                         out_len, out_shift, n, Q, plan, tw, perm, pre_elem, prr, post_elem, por, hf,
+                                         io, tw2);
         } else if (nq > 2048) {
-            auto k = fft_rows_kernel<T, 1024>;
-            SBD_TRY(raise_smem_limit(k, smem));
-            k<<<grid, 1024, smem, stream>>>(ip, in_stride, in_len, in_shift, op, out_stride, out_len, out_shift,
-                                            n, Q, sign, plan, tw, perm, pre_elem, prr, post_elem, por, hf, io, tw2);
+            rc = launch_fft_rows<T, 1024>(sign, grid, smem, stream, ip, in_stride, in_len, in_shift, op, out_stride,
+                                          out_len, out_shift, n, Q, plan, tw, perm, pre_elem, prr, post_elem, por, hf,
+                                          io, tw2);
         } else {
-            auto k = fft_rows_kernel<T, 256>;
-            SBD_TRY(raise_smem_limit(k, smem));
-            k<<<grid, 256, smem, stream>>>(ip, in_stride, in_len, in_shift, op, out_stride, out_len, out_shift,
-                                           n, Q, sign, plan, tw, perm, pre_elem, prr, post_elem, por, hf, io, tw2);
+            rc = launch_fft_rows<T, 256>(sign, grid, smem, stream, ip, in_stride, in_len, in_shift, op, out_stride,
+                                         out_len, out_shift, n, Q, plan, tw, perm, pre_elem, prr, post_elem, por, hf,
+                                         io, tw2);
         }
-        SBD_LAUNCH_CHECK();
+        if (rc) return rc;
     }
     SBD_LAUNCH_CHECK();
     return SBD_OK;
@@ -603,20 +620,19 @@ int fft_rows_tables(const cx_t<T>* in, long in_stride, int in_len, cx_t<T>* out,
         const dim3 grid(1u, static_cast<unsigned>(nr));
         const cx_t<T>* ip = in + static_cast<long>(r0) * in_stride;
         cx_t<T>* op = out + static_cast<long>(r0) * out_stride;
-        if (n > 2048) {
-            auto k = fft_rows_kernel<T, 1024>;
-            SBD_TRY(raise_smem_limit(k, smem));
-            k<<<grid, 1024, smem, stream>>>(ip, in_stride, in_len, 0, op, out_stride, out_len, 0, n, 1, sign, plan, tw,
-                                            perm, nullptr, nullptr, nullptr, nullptr, HermFold<T>{nullptr, 0, 0},
-                                            kIoPlain, nullptr);
-        } else {
-            auto k = fft_rows_kernel<T, 256>;
-            SBD_TRY(raise_smem_limit(k, smem));
-            k<<<grid, 256, smem, stream>>>(ip, in_stride, in_len, 0, op, out_stride, out_len, 0, n, 1, sign, plan, tw,
-                                           perm, nullptr, nullptr, nullptr, nullptr, HermFold<T>{nullptr, 0, 0},
-                                           kIoPlain, nullptr);
-        }
-        SBD_LAUNCH_CHECK();
+        const T* none = nullptr;
+        int rc;
+        if (n > 2048)
+            rc = launch_fft_rows<T, 1024>(sign, grid, smem, stream, ip, in_stride, in_len, 0, op, out_stride, out_len,
+                                          0, n, 1, plan, tw, perm, none, none, none, none,
+                                          HermFold<T>{nullptr, 0, 0}, static_cast<int>(kIoPlain),
+                                          static_cast<const cx_t<T>*>(nullptr));
+        else
+            rc = launch_fft_rows<T, 256>(sign, grid, smem, stream, ip, in_stride, in_len, 0, op, out_stride, out_len,
+                                         0, n, 1, plan, tw, perm, none, none, none, none,
+                                         HermFold<T>{nullptr, 0, 0}, static_cast<int>(kIoPlain),
+                                         static_cast<const cx_t<T>*>(nullptr));
+        if (rc) return rc;
     }
     return SBD_OK;
 }
