@@ -50,6 +50,7 @@ def parse():
     ap.add_argument("--eps", type=float, default=1e-6)
     ap.add_argument("--cpu-targets", type=int, default=400, help="targets of the oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-balance", action="store_true", help="skip the delta_min balance (sbd_plan_balanced)")
     return ap.parse_args()
 
 
@@ -208,6 +209,32 @@ def cpu_baseline(z, f, targets_idx, kind="laplace", kappa=0.0):
                       f"sources x {nrhs} rhs in {dt:.2f} s; value = pair rate / N (extrapolated to a full matvec)"}, q
 
 
+def stage_report(S, plan, step, f_dev, args, info, nrhs, esz, workload_key):
+    """Per-step device times of `args.steps` matvecs (library events on the launching stream),
+    algorithmic bytes per step and the roofline entry of the step that takes longest."""
+    import torch
+    S.sbd_profile(plan, True)
+    for _ in range(args.steps):
+        step(f_dev)
+    torch.cuda.synchronize()
+    prof = S.sbd_profile_read(plan)
+    S.sbd_profile(plan, False)
+    sb = stage_bytes(info, args.n, nrhs, args.form, esz)
+    hbm, peak_src = measured_peaks()
+    stages = {}
+    for st, (tot, cnt) in prof.items():
+        if cnt:
+            avg = tot / cnt
+            stages[st] = {"ms": avg, "launches_per_step": cnt // args.steps, "algorithmic_bytes": sb[st],
+                          "GBps": sb[st] / (avg * 1e-3) / 1e9}
+    dom = max(stages, key=lambda s_: stages[s_]["ms"] * stages[s_]["launches_per_step"])
+    achieved = stages[dom]["GBps"]
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": achieved / hbm, "traffic": traffic_for(dom, workload_key, args.form),
+                "peak_source": f"{peak_src} (hbm_gbs)"}
+    return stages, roofline
+
+
 def max_over_ranks(ms, world, device):
     """The slowest rank's time (the whole job finishes when it does); ms on one rank."""
     if world <= 1:
@@ -323,25 +350,44 @@ def main():
     value = job_rate(args.n * nrhs, world, ms)
 
     # per-step device times on the same stream (library events), for the roofline
-    S.sbd_profile(plan, True)
-    for _ in range(args.steps):
-        step(ft)
-    torch.cuda.synchronize()
-    prof = S.sbd_profile_read(plan)
-    S.sbd_profile(plan, False)
-    sb = stage_bytes(info, args.n, nrhs, args.form, esz)
-    hbm, peak_src = measured_peaks()
-    stages = {}
-    for st, (tot, cnt) in prof.items():
-        if cnt:
-            avg = tot / cnt
-            stages[st] = {"ms": avg, "launches_per_step": cnt // args.steps, "algorithmic_bytes": sb[st],
-                          "GBps": sb[st] / (avg * 1e-3) / 1e9}
-    dom = max(stages, key=lambda s: stages[s]["ms"] * stages[s]["launches_per_step"])
-    achieved = stages[dom]["GBps"]
-    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                "frac": achieved / hbm, "traffic": traffic_for(dom, args.workload, args.form),
-                "peak_source": f"{peak_src} (hbm_gbs)"}
+    stages, roofline = stage_report(S, plan, step, ft, args, info, nrhs, esz, args.workload)
+
+    # delta_min by measurement (Theorem 1 leaves alpha in [0, 1/6] free): the same points, f,
+    # eps and form, planned at the fastest alpha; reported beside the headline (alpha = 0)
+    balanced, q_bal = None, None
+    if args.workload in ("laplace_curves", "helmholtz_curves") and not args.no_balance:
+        alphas = [0.0, 1 / 24, 1 / 12, 5 / 48, 1 / 8, 1 / 6]
+        pb, cand_ms, ci = S.sbd_plan_balanced(zt, args.n, S.SBD_HELMHOLTZ if helm else S.SBD_LAPLACE, wl.kappa,
+                                              wl.eps, alphas, nrhs, 5, S.make_options(form=form, max_nrhs=nrhs),
+                                              stream.cuda_stream)
+        infob = S.sbd_plan_info(pb)
+        qb = torch.empty_like(ft)
+
+        def step_b(f_in):
+            S.sbd_matvec(pb, f_in, qb, nrhs, stream.cuda_stream)
+        for _ in range(args.warmup):
+            step_b(ft)
+        barrier()
+        e0b, e1b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0b.record(stream)
+        for _ in range(args.steps):
+            step_b(ft)
+        e1b.record(stream)
+        barrier()
+        msb = max_over_ranks(e0b.elapsed_time(e1b) / args.steps, world, "cuda")
+        stages_b, roof_b = stage_report(S, pb, step_b, ft, args, infob, nrhs, esz, args.workload + "_balanced")
+        balanced = {"alpha": alphas[ci], "delta_min": infob["delta_min"], "a": infob["a"],
+                    "value": job_rate(args.n * nrhs, world, msb), "unit": UNIT, "ms_per_step": msb,
+                    "candidates": [{"alpha": a_, "ms": m_} for a_, m_ in zip(alphas, cand_ms)],
+                    "roofline": roof_b, "stages": stages_b,
+                    "plan": {k: infob[k] for k in ("P", "n_xi", "nnz", "grid_x", "grid_k", "fft_n", "fit_err",
+                                                    "device_bytes", "plan_seconds")},
+                    "note": "delta_min = a delta_max, a = |log eps|^(2/3) / N^(2/3 - alpha) (Theorem 1) at the "
+                            "fastest alpha of the candidates (sbd_plan_balanced: each planned, tuned and timed); "
+                            "same points, f, eps and form as the headline line, which keeps alpha = 0"}
+        q_bal = qb.cpu().numpy()
+        S.sbd_destroy(pb)
+        del qb
 
     # cuFFT (through torch.fft), timed only as a comparison for the forward transform: the
     # same row transforms (length n, the rows that carry data), full outputs, plus the
@@ -397,7 +443,7 @@ def main():
            "vs_baseline": None, "dtype": "f32" if args.form == "fp32" else "f64", "data": "synthetic",
            "config": workload_config(args, rank), "clocks": clk, "e2e": e2e,
            "gpu_launches": (2 + 9 * nrhs) * args.steps, "roofline": roofline, "stages": stages,
-           "fft_comparison": fft_cmp,
+           "fft_comparison": fft_cmp, "balanced_delta_min": balanced,
            "plan": dict({k: info[k] for k in ("P", "n_xi", "n_records", "nnz", "grid_x", "grid_k", "fft_n",
                                               "stencil_x", "stencil_k", "nufft_tol", "fit_err", "device_bytes",
                                               "plan_seconds", "node_acc", "node_sched")},
@@ -413,6 +459,11 @@ def main():
         out["accuracy"] = {"targets": len(idx), "reference": "oracle direct sum (FP64)",
                            "rel_l2_vs_direct_sum": float(np.linalg.norm(qs - qref) / np.linalg.norm(qref)),
                            "max_err_over_sum_abs_f": float(np.max(np.abs(qs - qref) / f_abs))}
+        if balanced is not None:
+            qbs = q_bal[..., idx]
+            balanced["accuracy"] = {"targets": len(idx), "reference": "oracle direct sum (FP64)",
+                                    "rel_l2_vs_direct_sum": float(np.linalg.norm(qbs - qref) / np.linalg.norm(qref)),
+                                    "max_err_over_sum_abs_f": float(np.max(np.abs(qbs - qref) / f_abs))}
     S.sbd_destroy(plan)
     if rank == 0:
         print(json.dumps(out))

@@ -289,6 +289,35 @@ int sbd_tune(sbd_plan_t plan, int32_t reps, double* ms, void* cuda_stream);
 int sbd_set_tuning(sbd_plan_t plan, int32_t acc, int32_t sched, int32_t fft_split);
 
 /* ---------------------------------------------------------------------------------
+ * sbd_plan_balanced - sbd_plan with delta_min chosen by measurement (Introduction,
+ * Theorem 1, and Sec. 6: delta_min = a delta_max with a = |log eps|^(2/3) / N^(2/3 - alpha)
+ * for some alpha in [0, 1/6], chosen so that the far and the close parts balance; the
+ * constants of that balance depend on the machine, so it is found here by timing).
+ * For each candidate alphas[i] the call builds the plan of sbd_plan with that delta_min
+ * (delta_max = 2 max |z - c|, or options.delta_max when larger), tunes it (sbd_tune, 3
+ * launches per variant), runs one warm-up matvec and times `reps` matvecs with nrhs
+ * right-hand sides (a library-owned constant non-zero f; CUDA events on cuda_stream),
+ * and keeps the fastest plan; every other plan is destroyed before the next is built,
+ * so at most two plans are held at once.
+ *   points, n, kernel, eps, opt   as for sbd_plan (options.max_nrhs is raised to nrhs).
+ *   alphas     host, count values in [0, 1/6]; 1 <= count <= 16.
+ *   nrhs       right-hand sides per timed matvec (>= 1).
+ *   reps       timed matvecs per candidate (>= 1).
+ *   out        receives the fastest plan (owned by the caller; free with sbd_destroy).
+ *   ms         host, count entries (may be NULL): mean ms per matvec of candidate i,
+ *              -1 where it could not be planned (delta_min >= delta_max, the fit could
+ *              not reach eps, out of memory).
+ *   chosen     host (may be NULL): index of the kept candidate.
+ * Blocks until done.  SBD_EINVAL for null points/out/alphas, n < 1, count outside
+ * [1, 16], an alpha outside [0, 1/6], nrhs or reps < 1, eps outside [1e-10, 0.1]; when no
+ * candidate could be planned, the last candidate's error code (its message in
+ * sbd_last_error_message).
+ * ------------------------------------------------------------------------------- */
+int sbd_plan_balanced(const double* points, int64_t n, sbd_kernel kernel, double eps, const double* alphas,
+                      int32_t count, int32_t nrhs, int32_t reps, const sbd_options* opt, void* cuda_stream,
+                      sbd_plan_t* out, double* ms, int32_t* chosen);
+
+/* ---------------------------------------------------------------------------------
  * Fit cache.  The off-line fit (P search and coefficients, Sec. 3-4) depends only on
  * the kernel kind, k' (Helmholtz, Sec. 4.2), a = delta_min / scale_R, eps and fixed_P;
  * sbd_plan and sbd_offline_fit keep the last 64 distinct fits process-wide (thread

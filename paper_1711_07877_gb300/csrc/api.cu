@@ -1076,6 +1076,107 @@ int sbd_tune(sbd_plan_t p, int32_t reps, double* ms, void* cuda_stream) {
     return SBD_OK;
 }
 
+// delta_min by measurement: Theorem 1 leaves alpha in [0, 1/6] free and the Introduction asks
+// that delta_min balance the far and the close parts, whose costs on this device are known only
+// by running them.  One plan per candidate, timed on the caller's stream, the fastest kept.
+int sbd_plan_balanced(const double* points, int64_t n, sbd_kernel kernel, double eps, const double* alphas,
+                      int32_t count, int32_t nrhs, int32_t reps, const sbd_options* opt, void* cuda_stream,
+                      sbd_plan_t* out, double* ms, int32_t* chosen) {
+    if (!points || !out || !alphas || n < 1 || count < 1 || count > 16 || nrhs < 1 || reps < 1 ||
+        !(eps >= 1e-10 && eps <= 0.1)) {
+        set_error("sbd_plan_balanced: null pointer, n < 1, count outside [1, 16], nrhs or reps < 1, "
+                  "or eps outside [1e-10, 0.1]");
+        return SBD_EINVAL;
+    }
+    for (int i = 0; i < count; ++i)
+        if (!(alphas[i] >= 0.0 && alphas[i] <= 1.0 / 6.0 + 1e-12)) {
+            set_error("sbd_plan_balanced: alpha outside [0, 1/6] (Theorem 1)");
+            return SBD_EINVAL;
+        }
+    sbd_options o{};
+    o.form = SBD_FORM_FP64;
+    if (opt) o = *opt;
+    o.max_nrhs = std::max(o.max_nrhs, nrhs);
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    double bb[4], md2 = 0.0;
+    int rc = points_bbox(points, static_cast<long>(n), bb, s);
+    if (!rc) rc = points_max_dist2(points, static_cast<long>(n), 0.5 * (bb[0] + bb[2]), 0.5 * (bb[1] + bb[3]), &md2, s);
+    if (rc) return rc;
+    const double delta_max = std::max(2.0 * std::sqrt(md2), o.delta_max);
+    const size_t vbytes = (kernel.kind == SBD_HELMHOLTZ ? 16 : 8) * static_cast<size_t>(n) * nrhs;
+    void *f = nullptr, *q = nullptr;
+    if (cudaMallocAsync(&f, vbytes, s) != cudaSuccess || cudaMallocAsync(&q, vbytes, s) != cudaSuccess) {
+        cudaGetLastError();
+        if (f) cudaFreeAsync(f, s);
+        set_error("sbd_plan_balanced: cannot allocate the timing vectors");
+        return SBD_ENOMEM;
+    }
+    cudaMemsetAsync(f, 0x3f, vbytes, s);   // every float64 = 4.8e-4: non-zero, finite
+    cudaEvent_t ea = nullptr, eb = nullptr;
+    cudaEventCreate(&ea);
+    cudaEventCreate(&eb);
+    if (ms)
+        for (int i = 0; i < count; ++i) ms[i] = -1.0;
+    sbd_plan_t best = nullptr;
+    double best_ms = 1e300;
+    int best_i = -1, last_rc = SBD_OK;
+    std::string last_err;
+    const double lg = std::pow(std::abs(std::log(eps)), 2.0 / 3.0);
+    for (int i = 0; i < count; ++i) {
+        const double a = lg / std::pow(static_cast<double>(n), 2.0 / 3.0 - alphas[i]);
+        const double dmin = a * delta_max;
+        if (!(dmin < delta_max)) {
+            last_rc = SBD_EINVAL;
+            last_err = "sbd_plan_balanced: delta_min reaches delta_max for alpha " + std::to_string(alphas[i]);
+            continue;
+        }
+        sbd_plan_t p = nullptr;
+        int r = sbd_plan(points, n, kernel, dmin, eps, &o, cuda_stream, &p);
+        if (!r) r = sbd_tune(p, 3, nullptr, cuda_stream);
+        if (!r) r = sbd_matvec(p, f, q, nrhs, cuda_stream);
+        float t_ms = 0.f;
+        if (!r && cudaEventRecord(ea, s) != cudaSuccess) r = SBD_ECUDA;
+        for (int k = 0; k < reps && !r; ++k) r = sbd_matvec(p, f, q, nrhs, cuda_stream);
+        if (!r && (cudaEventRecord(eb, s) != cudaSuccess || cudaEventSynchronize(eb) != cudaSuccess ||
+                   cudaEventElapsedTime(&t_ms, ea, eb) != cudaSuccess)) {
+            set_error("sbd_plan_balanced: event timing failed");
+            r = SBD_ECUDA;
+        }
+        if (r) {
+            last_rc = r;
+            last_err = g_last_error;
+            if (p) sbd_destroy_async(p, cuda_stream);
+            continue;
+        }
+        const double per = static_cast<double>(t_ms) / reps;
+        if (ms) ms[i] = per;
+        if (per < best_ms) {
+            if (best) sbd_destroy_async(best, cuda_stream);
+            best = p;
+            best_ms = per;
+            best_i = i;
+        } else {
+            sbd_destroy_async(p, cuda_stream);
+        }
+    }
+    cudaFreeAsync(f, s);
+    cudaFreeAsync(q, s);
+    cudaEventDestroy(ea);
+    cudaEventDestroy(eb);
+    if (cudaStreamSynchronize(s) != cudaSuccess && best) {
+        set_error(std::string("sbd_plan_balanced: ") + cudaGetErrorString(cudaGetLastError()));
+        sbd_destroy(best);
+        return SBD_ECUDA;
+    }
+    if (!best) {
+        set_error(last_err);
+        return last_rc ? last_rc : SBD_ECUDA;
+    }
+    *out = best;
+    if (chosen) *chosen = best_i;
+    return SBD_OK;
+}
+
 int sbd_plan_export(sbd_plan_t p, int64_t cap, double* rho, double* alpha, int32_t* M, double* radius,
                     double* weight_re, double* weight_im) {
     if (!p) {

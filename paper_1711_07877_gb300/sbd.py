@@ -71,6 +71,8 @@ _SIGS = {
     "sbd_fit_cache_stats": ([_P, _P, _P], ctypes.c_int),
     "sbd_tune": ([_P, _I32, _P, _P], ctypes.c_int),
     "sbd_set_tuning": ([_P, _I32, _I32, _I32], ctypes.c_int),
+    "sbd_plan_balanced": ([_P, _I64, sbd_kernel, _D, _P, _I32, _I32, _I32, ctypes.POINTER(sbd_options), _P,
+                           ctypes.POINTER(_P), _P, ctypes.POINTER(_I32)], ctypes.c_int),
     "sbd_fit_cache_clear": ([], ctypes.c_int),
     "sbd_y0_root": ([_I32, _P], ctypes.c_int),
     "sbd_plan": ([_P, _I64, sbd_kernel, _D, _D, ctypes.POINTER(sbd_options), _P, ctypes.POINTER(_P)], ctypes.c_int),
@@ -299,6 +301,21 @@ def sbd_tune(plan: int, reps: int = 3, stream=None) -> list:
     ms = np.zeros(10)
     _check(lib.sbd_tune(plan, reps, ms.ctypes.data, _stream(stream)), "sbd_tune")
     return ms.tolist()
+
+
+def sbd_plan_balanced(points, n: int, kernel_kind: int, kappa: float, eps: float, alphas, nrhs: int = 1,
+                      reps: int = 5, options: sbd_options | None = None, stream=None):
+    """Plan with delta_min from Theorem 1 at the fastest of the candidate alphas.
+    Returns (plan, ms per candidate (-1 where it could not be planned), chosen index)."""
+    import numpy as np
+    al = np.ascontiguousarray(alphas, dtype=np.float64)
+    ms = np.zeros(len(al))
+    out, chosen = _P(), _I32()
+    rc = lib.sbd_plan_balanced(_ptr(points), n, sbd_kernel(kernel_kind, kappa), eps, al.ctypes.data, len(al), nrhs,
+                               reps, ctypes.byref(options) if options is not None else None, _stream(stream),
+                               ctypes.byref(out), ms.ctypes.data, ctypes.byref(chosen))
+    _check(rc, "sbd_plan_balanced")
+    return out.value, ms.tolist(), chosen.value
 
 
 def sbd_set_tuning(plan: int, acc: int, sched: int, fft_split: int = 0) -> None:
