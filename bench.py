@@ -150,7 +150,7 @@ def stage_bytes(info, n, nrhs, form, esz=8):
     nr = 24 if form == "fp32" else 32        # node record
     m, nk, nxi, nnz, P = info["grid_x"], info["grid_k"], info["n_xi"], info["nnz"], info["stencil_x"]
     touched = min(m * m, n * P * P)
-    vb = 16 if esz == 16 else 8              # D value (complex for Helmholtz)
+    vb = (16 if esz == 16 else 8) // (2 if form == "fp32" else 1)   # D value: complex for Helmholtz, FP32 form in float32
     if esz == 8:
         # Laplace: real spreading grid (half a complex element per cell), Hermitian K of
         # which the half plane kx >= 0 is transformed, half the node records

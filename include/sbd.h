@@ -85,9 +85,13 @@ typedef struct {
     int32_t reserved;
 } sbd_options;
 
-/* sbd_options.flags: use a Gaussian window at the quadrature nodes instead of the
- * default ES (exponential of semicircle) window, which needs about half the width. */
+/* sbd_options.flags: use a Gaussian window at the quadrature nodes (GAUSSIAN_NODES) or
+ * for spreading the points (GAUSSIAN_SPREAD) instead of the default ES (exponential of
+ * semicircle) window, which needs about half the width at the same accuracy.  The
+ * Gaussian's Fourier transform is radial, so its deconvolution is one factor per circle;
+ * the ES window's is a factor per node, folded into the node weights at plan time. */
 #define SBD_FLAG_GAUSSIAN_NODES 1
+#define SBD_FLAG_GAUSSIAN_SPREAD 2
 
 /* Plan summary (sbd_plan_info). */
 typedef struct {

@@ -66,6 +66,7 @@ struct sbd_plan_s {
     void* nodes = nullptr;
     void* omega_c = nullptr;   // per circle: omega_hat * c^2 (T complex)
     void* cscale_c = nullptr;  // per circle: c (T)
+    double* psi = nullptr;     // Chebyshev series of the ES spreading deconvolution (null: Gaussian)
     void* dec = nullptr;       // T[m]
     long long* rowptr = nullptr;
     int* col = nullptr;
@@ -243,6 +244,11 @@ void keep_pool_memory() {
     });
 }
 
+SpreadDeconv spread_deconv_of(const sbd_plan_s* p) {
+    if (!p->psi) return SpreadDeconv{nullptr, 0, 0.0, 0.0};
+    return SpreadDeconv{p->psi, static_cast<int>(p->np.psi.size()), 1.0 / (p->np.kmax * p->np.kmax), p->np.h};
+}
+
 template <typename T>
 int build_far(sbd_plan_s* p, cudaStream_t s) {
     const NufftParams& np = p->np;
@@ -254,6 +260,11 @@ int build_far(sbd_plan_s* p, cudaStream_t s) {
     p->geom.kwin = np.kwin;
     p->geom.beta_s = np.beta_s;
     p->geom.beta_k = np.beta_k;
+    p->geom.swin = np.swin;
+    if (np.swin == 1) {
+        const int urc = upload(p, &p->psi, np.psi, s);
+        if (urc) return urc;
+    }
     PointRec<T>* pts0 = nullptr;
     SBD_CUDA_TRY(cudaMallocAsync(&pts0, sizeof(PointRec<T>) * p->n, s));
     int rc = far_prepare_points<T>(p->z, p->n, np.cx, np.cy, np.h, np.m, np.Ps, pts0, s);
@@ -298,14 +309,17 @@ int build_far(sbd_plan_s* p, cudaStream_t s) {
     {
         double omax = 0.0;
         for (const auto& w : om) omax = std::max(omax, std::max(std::fabs(double(w.x)), std::fabs(double(w.y))));
-        p->tuning.wbound = static_cast<float>(omax * np.Pk * np.Pk);
+        // the ES spreading deconvolution multiplies a node's weight by at most psi_max^4
+        const double pm2 = np.swin == 1 ? np.psi_max * np.psi_max : 1.0;
+        p->tuning.wbound = static_cast<float>(omax * pm2 * pm2 * np.Pk * np.Pk);
     }
     if ((rc = upload(p, reinterpret_cast<cx_t<T>**>(&p->omega_c), om, s))) return rc;
     if ((rc = upload(p, reinterpret_cast<T**>(&p->cscale_c), cs, s))) return rc;
     NodeRec<T>* canon = nullptr;
     SBD_CUDA_TRY(cudaMallocAsync(&canon, sizeof(NodeRec<T>) * std::max<long long>(p->n_rec, 1), s));
     rc = far_prepare_nodes<T>(p->circle_start, p->half_start, p->circle_radius, p->circle_M, fit.n_circles,
-                              p->n_rec, np.deta, np.nk, np.Pk, static_cast<const cx_t<T>*>(p->omega_c), canon, s);
+                              p->n_rec, np.deta, np.nk, np.Pk, static_cast<const cx_t<T>*>(p->omega_c),
+                              spread_deconv_of(p), canon, s);
     if (rc) return rc;
     const int ntx = (np.nk + kNodeTile - 1) / kNodeTile;
     if ((rc = dev_alloc(p, &p->nodes, sizeof(NodeRec<T>) * p->n_rec))) return rc;
@@ -481,7 +495,7 @@ int nufft_minus_impl(sbd_plan_s* p, const void* f, void* fhat, cudaStream_t s) {
     if (rc) return rc;
     if ((rc = forward_fft<T>(p, X, A, C, B, s))) return rc;
     const NodeFrame fr{p->circle_start, p->circle_radius, p->circle_M, p->fit.n_circles, p->np.cx, p->np.cy,
-                       p->node_perm, p->half_start, p->np.nk};
+                       p->node_perm, p->half_start, p->np.nk, spread_deconv_of(p)};
     return far_node_gather<T>(static_cast<const NodeRec<T>*>(p->nodes), p->n_rec,
                               static_cast<const T*>(p->cscale_c), p->geom, B, static_cast<double2*>(fhat), fr, s);
 }
@@ -493,7 +507,7 @@ int nufft_plus_impl(sbd_plan_s* p, const void* ghat, void* q, cudaStream_t s) {
     auto* B = static_cast<cx_t<T>*>(p->wsB);
     auto* C = static_cast<cx_t<T>*>(p->wsC);
     const NodeFrame fr{p->circle_start, p->circle_radius, p->circle_M, p->fit.n_circles, p->np.cx, p->np.cy,
-                       p->node_perm, p->half_start, p->np.nk};
+                       p->node_perm, p->half_start, p->np.nk, spread_deconv_of(p)};
     int rc = far_node_scatter<T>(static_cast<const NodeRec<T>*>(p->nodes), p->n_rec,
                                  static_cast<const T*>(p->cscale_c), p->geom, static_cast<const double2*>(ghat), C,
                                  fr, s);
@@ -599,7 +613,7 @@ int sbd_plan(const double* points, int64_t n, sbd_kernel kernel, double delta_mi
         set_error("sbd_plan: unknown form");
         return SBD_EINVAL;
     }
-    if ((o.flags & ~SBD_FLAG_GAUSSIAN_NODES) != 0 || o.fixed_P < 0 || o.max_nrhs < 0 || o.nufft_tol < 0 ||
+    if ((o.flags & ~(SBD_FLAG_GAUSSIAN_NODES | SBD_FLAG_GAUSSIAN_SPREAD)) != 0 || o.fixed_P < 0 || o.max_nrhs < 0 || o.nufft_tol < 0 ||
         !(o.delta_max >= 0) || o.host_threads < 0) {
         set_error("sbd_plan: invalid options");
         return SBD_EINVAL;
@@ -674,7 +688,8 @@ int sbd_plan(const double* points, int64_t n, sbd_kernel kernel, double delta_mi
     const double tol = o.nufft_tol > 0 ? o.nufft_tol : eps / (6.0 * std::max(W, 1e-300));
     const double half = std::max(std::max(bb[2] - cx, bb[3] - cy), 1e-300);
     const int kwin = (o.flags & SBD_FLAG_GAUSSIAN_NODES) ? 0 : 1;
-    if ((rc = nufft_params(fit, half, cx, cy, tol, o.form == SBD_FORM_FP32, kwin, p->np, err))) {
+    const int swin = (o.flags & SBD_FLAG_GAUSSIAN_SPREAD) ? 0 : 1;
+    if ((rc = nufft_params(fit, half, cx, cy, tol, o.form == SBD_FORM_FP32, kwin, swin, p->np, err))) {
         set_error(err);
         return fail(rc);
     }

@@ -73,7 +73,7 @@ template <typename T>
 __global__ void prepare_nodes_kernel(const int* __restrict__ start, const int* __restrict__ hstart,
                                      const double* __restrict__ radius, const int* __restrict__ M, int n_circles,
                                      long n_rec, double deta, int nk, int P, const cx_t<T>* __restrict__ omega_c,
-                                     NodeRec<T>* __restrict__ out) {
+                                     SpreadDeconv sd, NodeRec<T>* __restrict__ out) {
     const long nu = blockIdx.x * static_cast<long>(blockDim.x) + threadIdx.x;
     if (nu >= n_rec) return;
     const int* num = hstart ? hstart : start;
@@ -87,7 +87,10 @@ __global__ void prepare_nodes_kernel(const int* __restrict__ start, const int* _
     NodeRec<T> r;
     r.cell = make_int2(static_cast<int>(fx) - P / 2 + 1, static_cast<int>(fy) - P / 2 + 1);
     r.frac = mk<T>(static_cast<T>(kx - fx), static_cast<T>(ky - fy));
-    r.omega = omega_c[c];
+    // both transforms divide by the spreading window's transform at xi: the square of its factor
+    const double sf = spread_deconv(sd, make_double2(radius[c] * cs, radius[c] * sn));
+    r.omega = mk<T>(static_cast<T>(static_cast<double>(omega_c[c].x) * sf * sf),
+                    static_cast<T>(static_cast<double>(omega_c[c].y) * sf * sf));
     out[nu] = r;
 }
 
@@ -142,7 +145,7 @@ __global__ void node_gather_kernel(const NodeRec<T>* __restrict__ nodes, long n_
     weights<T, PMAX>(q.frac.y, g.Pk, g, wy);
     const NodeId id = node_id(fr, fr.perm ? fr.perm[nu] : nu);
     // the grids hold z - c: multiply by exp(-i c.xi) to return sum_l exp(-i z_l.xi) f_l
-    const T sc = cs[id.circle];
+    const T sc = static_cast<T>(static_cast<double>(cs[id.circle]) * spread_deconv(fr.sd, id.xi));
     cx_t<T> acc = cscale(stencil_gather<T>(kin, g.nk, q.cell, wx, wy, g.Pk, false), sc);
     out[id.canon] = centre_phase(fr, id.xi, make_double2(acc.x, acc.y), -1);
     if (fr.hstart) {
@@ -162,7 +165,7 @@ __global__ void node_scatter_kernel(const NodeRec<T>* __restrict__ nodes, long n
     weights<T, PMAX>(q.frac.x, g.Pk, g, wx);
     weights<T, PMAX>(q.frac.y, g.Pk, g, wy);
     const NodeId id = node_id(fr, fr.perm ? fr.perm[nu] : nu);
-    const T sc = cs[id.circle];
+    const T sc = static_cast<T>(static_cast<double>(cs[id.circle]) * spread_deconv(fr.sd, id.xi));
     // q_l = sum_nu exp(i (z_l - c).xi) [exp(i c.xi) ghat_nu]
     double2 v = centre_phase(fr, id.xi, in[id.canon], +1);
     stencil_scatter<T>(kout, g.nk, q.cell, wx, wy, g.Pk, false,
@@ -214,10 +217,10 @@ int far_prepare_points(const double* z, long n, double cx, double cy, double h, 
 template <typename T>
 int far_prepare_nodes(const int* circle_start, const int* half_start, const double* radius, const int* M,
                       int n_circles, long n_rec, double deta, int nk, int P, const cx_t<T>* omega_c,
-                      NodeRec<T>* out, cudaStream_t s) {
+                      const SpreadDeconv& sd, NodeRec<T>* out, cudaStream_t s) {
     if (n_rec <= 0) return SBD_OK;
     prepare_nodes_kernel<T><<<blocks_for(n_rec), kThreads, 0, s>>>(circle_start, half_start, radius, M, n_circles,
-                                                                   n_rec, deta, nk, P, omega_c, out);
+                                                                   n_rec, deta, nk, P, omega_c, sd, out);
     SBD_LAUNCH_CHECK();
     return SBD_OK;
 }
@@ -258,7 +261,8 @@ int far_sum(const void* f, bool f_complex, long n, int nrhs, double2* sumf, cuda
     template int far_prepare_points<T>(const double*, long, double, double, double, int, int, PointRec<T>*,  \
                                        cudaStream_t);                                                     \
     template int far_prepare_nodes<T>(const int*, const int*, const double*, const int*, int, long, double, \
-                                      int, int, const cx_t<T>*, NodeRec<T>*, cudaStream_t);               \
+                                      int, int, const cx_t<T>*, const SpreadDeconv&, NodeRec<T>*,         \
+                                      cudaStream_t);                                                       \
     template int far_node_gather<T>(const NodeRec<T>*, long, const T*, const FarGeom&, const cx_t<T>*,    \
                                     double2*, const NodeFrame&, cudaStream_t);                            \
     template int far_node_scatter<T>(const NodeRec<T>*, long, const T*, const FarGeom&, const double2*,   \

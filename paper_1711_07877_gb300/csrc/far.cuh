@@ -1,5 +1,6 @@
 // Far part of the on-line SBD (Sec. 1 steps (i)-(iii), Eq. far convolution) by a
-// type-3 transform with Gaussian gridding on both sides.
+// type-3 transform: points spread with a separable window (ES or Gaussian) onto a
+// two-fold oversampled grid, a zero-padded FFT, and a node window (ES or Gaussian).
 #pragma once
 #include <cuda_runtime.h>
 
@@ -9,21 +10,47 @@ namespace sbd {
 
 // Geometry of one transform, all in cells of the respective grid.
 struct FarGeom {
-    int Ps;           // spreading stencil width (cells per dimension), even; Gaussian window
+    int Ps;           // spreading stencil width (cells per dimension), even
     int Pk;           // node stencil width, even
     int m;            // spreading grid side
     int nk;           // frequency grid side
     int kwin;         // node window (WindowKind)
-    double beta_s;    // spreading window exp(-beta_s d^2)
+    double beta_s;    // spreading window parameter
     double beta_k;    // node window parameter
+    int swin;         // spreading window (WindowKind)
 };
+
+// Deconvolution of the ES spreading window at a node: psi(k) = 1 / phi_hat_s(k) with
+// k = xi h, as a Chebyshev series in 2 (k / kmax)^2 - 1; the node xi takes the factor
+// psi(xi_x h) psi(xi_y h).  coef null: Gaussian spreading, whose factor exp(tau |xi|^2) is
+// radial and sits in the circle's weight.  FP64.
+struct SpreadDeconv {
+    const double* coef;
+    int n;              // coefficients
+    double inv_kmax2;   // 1 / kmax^2
+    double h;           // spreading-grid spacing
+};
+__device__ __forceinline__ double spread_psi(const SpreadDeconv& d, double k) {
+    const double x = 2.0 * k * k * d.inv_kmax2 - 1.0;
+    double b1 = 0.0, b2 = 0.0;
+    for (int i = d.n - 1; i >= 1; --i) {
+        const double t = 2.0 * x * b1 - b2 + d.coef[i];
+        b2 = b1;
+        b1 = t;
+    }
+    return x * b1 - b2 + d.coef[0];
+}
+__device__ __forceinline__ double spread_deconv(const SpreadDeconv& d, double2 xi) {
+    if (!d.coef) return 1.0;
+    return spread_psi(d, xi.x * d.h) * spread_psi(d, xi.y * d.h);
+}
 
 // Point i: spreading stencil starts at (row, column) = cell of the spreading grid, whose
 // rows are y; frac = position - floor(position) in the same (row, column) order.
 template <typename T> struct PointRec { int2 cell; cx_t<T> frac; };
-// Node: stencil start cell in the frequency grid, fraction, and the weight omega'_p of
-// its circle (omega_hat_p times the transform's radial factor), so the node step needs
-// no second lookup.
+// Node: stencil start cell in the frequency grid, fraction, and its weight omega'_nu
+// (omega_hat_p of its circle times the transform's scale factors at xi_nu), so the node
+// step needs no second lookup.
 template <typename T> struct NodeRec { int2 cell; cx_t<T> frac; cx_t<T> omega; };
 
 // Plan-time preparation (FP64 arithmetic).
@@ -39,7 +66,7 @@ int far_prepare_points(const double* z, long n, double cx, double cy, double h, 
 template <typename T>
 int far_prepare_nodes(const int* circle_start, const int* half_start, const double* radius, const int* M,
                       int n_circles, long n_rec, double deta, int nk, int P, const cx_t<T>* omega_c,
-                      NodeRec<T>* out, cudaStream_t s);
+                      const SpreadDeconv& sd, NodeRec<T>* out, cudaStream_t s);
 
 // Circle tables and the centre c of the point set, to place the canonical nodes in
 // absolute coordinates (the grids hold z - c).
@@ -53,8 +80,10 @@ struct NodeFrame {
     const int* hstart; // non-null: records are the half set (see far_prepare_nodes); the
                        // gather / scatter also serve each record's antipode
     int nk;            // frequency-grid side (mirror of cell i is nk - i)
+    SpreadDeconv sd;   // per-node factor of the spreading window (coef null: none)
 };
-// Gather only: out[nu] = exp(-i c.xi_nu) c_nu sum_stencil w K  (complex128), c_nu = circle scale,
+// Gather only: out[nu] = exp(-i c.xi_nu) c_nu sum_stencil w K  (complex128), c_nu = circle
+// scale times the node's spreading deconvolution,
 // for every node nu (canonical numbering; n_rec records).
 template <typename T>
 int far_node_gather(const NodeRec<T>* nodes, long n_rec, const T* cscale, const FarGeom& g,

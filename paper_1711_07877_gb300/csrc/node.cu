@@ -208,7 +208,7 @@ __global__ void __launch_bounds__(256) gather_tiles_kernel(
     __syncthreads();
     const int lane = threadIdx.x & 31;
     const int sub = lane % G;
-    const unsigned gmask = G == 32 ? 0xffffffffu : (0xffffu << (lane & 16));
+    const unsigned gmask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << (lane & ~(G - 1)));
     const int group = threadIdx.x / G, ngroups = blockDim.x / G;
     for (long long i = b0 + group; i < b1; i += ngroups) {
         const Rec q = rec[i];
@@ -272,7 +272,7 @@ __global__ void __launch_bounds__(256) scatter_tiles_kernel(
     __syncthreads();
     const int lane = threadIdx.x & 31;
     const int sub = lane % G;
-    const unsigned gmask = G == 32 ? 0xffffffffu : (0xffffu << (lane & 16));
+    const unsigned gmask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << (lane & ~(G - 1)));
     const int group = threadIdx.x / G, ngroups = blockDim.x / G;
     for (int sx = max(tx - 1, 0); sx <= tx; ++sx) {
         for (int sy = max(ty - 1, 0); sy <= ty; ++sy) {
@@ -692,7 +692,11 @@ int launch_gather(const Rec* rec, const long long* tile_start, int n, int P, int
     const size_t W = kNodeTile + P - 1;
     const size_t smem = W * W * sizeof(cx_t<T>);
     const unsigned nt = static_cast<unsigned>(ntx) * ntx;
-    if (P <= 16) {
+    if (P <= 8) {
+        auto k = gather_tiles_kernel<T, 8, Rec, Out, PK>;
+        SBD_TRY(raise_smem_limit(k, smem));
+        k<<<nt, 256, smem, s>>>(rec, tile_start, ntx, n, P, win, grid, out);
+    } else if (P <= 16) {
         auto k = gather_tiles_kernel<T, 16, Rec, Out, PK>;
         SBD_TRY(raise_smem_limit(k, smem));
         k<<<nt, 256, smem, s>>>(rec, tile_start, ntx, n, P, win, grid, out);
@@ -712,7 +716,11 @@ int launch_scatter(const Rec* rec, const long long* tile_start, int n, int P, in
     const int ntx = tiles_per_side(n);
     const size_t smem = (RV ? 1 : 2) * sizeof(T) * kNodeTile * kNodeTile;
     const unsigned nt = static_cast<unsigned>(ntx) * ntx;
-    if (P <= 16) {
+    if (P <= 8) {
+        auto k = scatter_tiles_kernel<T, 8, Rec, Val, PK, RV>;
+        SBD_TRY(raise_smem_limit(k, smem));
+        k<<<nt, 256, smem, s>>>(rec, tile_start, ntx, n, P, win, val, grid);
+    } else if (P <= 16) {
         auto k = scatter_tiles_kernel<T, 16, Rec, Val, PK, RV>;
         SBD_TRY(raise_smem_limit(k, smem));
         k<<<nt, 256, smem, s>>>(rec, tile_start, ntx, n, P, win, val, grid);
@@ -857,11 +865,11 @@ int spread_tiled(const PointRec<T>* pts, const int* perm, const long long* tile_
             set_error("spread: a packed real grid needs real values and an even side");
             return SBD_EINVAL;
         }
-        return launch_scatter<T, PointRec<T>, PointVal<T>, true, true>(pts, tile_start, g.m, g.Ps, kWinGauss,
+        return launch_scatter<T, PointRec<T>, PointVal<T>, true, true>(pts, tile_start, g.m, g.Ps, g.swin,
                                                                         g.beta_s, PointVal<T>{f, perm, false}, grid,
                                                                         s);
     }
-    return launch_scatter<T>(pts, tile_start, g.m, g.Ps, kWinGauss, g.beta_s, PointVal<T>{f, perm, f_complex}, grid,
+    return launch_scatter<T>(pts, tile_start, g.m, g.Ps, g.swin, g.beta_s, PointVal<T>{f, perm, f_complex}, grid,
                              s);
 }
 
@@ -875,10 +883,10 @@ int interp_tiled(const PointRec<T>* pts, const int* perm, const long long* tile_
             set_error("interp: a packed real grid needs real output and an even side");
             return SBD_EINVAL;
         }
-        return launch_gather<T, PointRec<T>, PointOut<T>, true>(pts, tile_start, g.m, g.Ps, kWinGauss, g.beta_s,
+        return launch_gather<T, PointRec<T>, PointOut<T>, true>(pts, tile_start, g.m, g.Ps, g.swin, g.beta_s,
                                                                 grid, out, s);
     }
-    return launch_gather<T>(pts, tile_start, g.m, g.Ps, kWinGauss, g.beta_s, grid, out, s);
+    return launch_gather<T>(pts, tile_start, g.m, g.Ps, g.swin, g.beta_s, grid, out, s);
 }
 
 template <typename T>

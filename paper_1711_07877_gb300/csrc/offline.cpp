@@ -609,8 +609,58 @@ static double es_hat(double k, double beta, const std::vector<double>& gx, const
     return 0.5 * kPi * s;
 }
 
+static double cheb_eval(const std::vector<double>& c, double x) {
+    double b1 = 0.0, b2 = 0.0;
+    for (size_t i = c.size() - 1; i >= 1; --i) {
+        const double t = 2.0 * x * b1 - b2 + c[i];
+        b2 = b1;
+        b1 = t;
+    }
+    return x * b1 - b2 + c[0];
+}
+
+// Chebyshev series of psi(k) = 1 / phi_hat(k) in x = 2 (k / kmax)^2 - 1 on [0, kmax] (psi is
+// even in k), phi_hat(k) = (P/2) es_hat(k P / 2, beta) the Fourier transform of the ES window of
+// width P cells; the degree is doubled until 257 check points agree with the quadrature to
+// 1e-14 relative.
+static int es_deconv_series(int P, double beta, double kmax, std::vector<double>& coef, double& psi_max,
+                            std::string& err) {
+    std::vector<double> gx, gw;
+    gauss_legendre(200, gx, gw);
+    auto psi = [&](double k) { return 1.0 / (0.5 * P * es_hat(0.5 * P * k, beta, gx, gw)); };
+    for (int deg = 24; deg <= 192; deg *= 2) {
+        const int nn = deg + 1;
+        std::vector<double> fv(nn);
+        for (int j = 0; j < nn; ++j) {
+            const double x = std::cos(kPi * (j + 0.5) / nn);
+            fv[j] = psi(kmax * std::sqrt(0.5 * (x + 1.0)));
+        }
+        coef.assign(nn, 0.0);
+        for (int i = 0; i < nn; ++i) {
+            double acc = 0.0;
+            for (int j = 0; j < nn; ++j) acc += fv[j] * std::cos(kPi * i * (j + 0.5) / nn);
+            coef[i] = (i == 0 ? 1.0 : 2.0) * acc / nn;
+        }
+        double worst = 0.0, most = 0.0;
+        for (int t = 0; t <= 256; ++t) {
+            const double k = kmax * t / 256.0;
+            const double want = psi(k);
+            const double got = cheb_eval(coef, 2.0 * (k / kmax) * (k / kmax) - 1.0);
+            if (!(want > 0.0)) break;
+            worst = std::max(worst, std::fabs(got - want) / want);
+            most = std::max(most, want);
+        }
+        if (worst <= 1e-14) {
+            psi_max = most;
+            return SBD_OK;
+        }
+    }
+    err = "the ES deconvolution series does not reach 1e-14";
+    return SBD_ENOTSUP;
+}
+
 int nufft_params(const SbdFit& fit, double half_extent, double cx, double cy, double tol,
-                 bool fp32, int kwin, NufftParams& o, std::string& err) {
+                 bool fp32, int kwin, int swin, NufftParams& o, std::string& err) {
     double S = 0.0;
     for (int c = 0; c < fit.n_circles; ++c) S = std::max(S, fit.radius[c]);
     if (!(S > 0.0) || !(half_extent > 0.0)) {
@@ -620,8 +670,13 @@ int nufft_params(const SbdFit& fit, double half_extent, double cx, double cy, do
     if (fp32) tol = std::max(tol, 3e-7);
     tol = std::max(tol, 1e-15);
     const int pmax = fp32 ? 16 : 32;
-    // spreading side, Gaussian: error ~ 0.1 exp(-pi P / 3) per transform at two-fold oversampling
-    int Ps = static_cast<int>(std::ceil((3.0 / kPi) * std::log(0.1 / tol)));
+    // spreading side: ES error ~ 10^-(P - 1) at two-fold oversampling; Gaussian ~ 0.1 exp(-pi P / 3)
+    int Ps;
+    if (swin == 1) {
+        Ps = static_cast<int>(std::ceil(-std::log10(tol))) + 1;
+    } else {
+        Ps = static_cast<int>(std::ceil((3.0 / kPi) * std::log(0.1 / tol)));
+    }
     Ps = std::max(4, std::min(pmax, Ps + (Ps & 1)));
     // node side: ES error ~ 10^-P (two-fold oversampling), Gaussian as the spreading side
     int Pk;
@@ -629,25 +684,32 @@ int nufft_params(const SbdFit& fit, double half_extent, double cx, double cy, do
         Pk = static_cast<int>(std::ceil(-std::log10(tol)));
         Pk = std::max(4, std::min(pmax, Pk + (Pk & 1)));
     } else {
-        Pk = Ps;
+        Pk = static_cast<int>(std::ceil((3.0 / kPi) * std::log(0.1 / tol)));
+        Pk = std::max(4, std::min(pmax, Pk + (Pk & 1)));
     }
     o.Ps = Ps;
     o.Pk = Pk;
     o.kwin = kwin;
+    o.swin = swin;
     o.tol = tol;
-    const double u = Ps * kPi / 24.0;   // balanced truncation / aliasing of the Gaussian at two-fold oversampling
     o.h = kPi / (2.0 * S);
-    o.tau = u / (S * S);
+    if (swin == 1) {
+        o.tau = 0.0;
+        o.beta_s = 2.3 * Ps;
+    } else {
+        const double u = Ps * kPi / 24.0;   // balanced truncation / aliasing of the Gaussian at two-fold oversampling
+        o.tau = u / (S * S);
+        o.beta_s = o.h * o.h / (4.0 * o.tau);
+    }
     o.m = good_fft_size(static_cast<int>(std::ceil(2.0 * half_extent / o.h)) + Ps + 4);
     o.n = 2 * o.m;
     o.nk = o.m + Pk + 4;
     const double Xg = 0.5 * o.m * o.h;
     o.deta = 2.0 * kPi / (o.n * o.h);
-    o.beta_s = o.h * o.h / (4.0 * o.tau);
     o.cx = cx;
     o.cy = cy;
     o.dec.resize(o.m);
-    double c0;
+    double knode;   // node-side constant of the per-node scale c(xi)
     if (kwin == 1) {
         o.beta_k = 2.3 * Pk;
         o.sigma = 0.0;
@@ -658,7 +720,7 @@ int nufft_params(const SbdFit& fit, double half_extent, double cx, double cy, do
             const double x = (i - 0.5 * o.m) * o.h;
             o.dec[i] = 1.0 / (half * es_hat(x * half, o.beta_k, gx, gw));
         }
-        c0 = o.h * o.h * o.deta * o.deta / (4.0 * kPi * o.tau);
+        knode = o.deta * o.deta;
     } else {
         const double v = Pk * kPi / 24.0;
         o.sigma = v / (Xg * Xg);
@@ -667,11 +729,24 @@ int nufft_params(const SbdFit& fit, double half_extent, double cx, double cy, do
             const double x = (i - 0.5 * o.m) * o.h;
             o.dec[i] = std::exp(o.sigma * x * x);
         }
-        c0 = o.h * o.h * o.deta * o.deta / (16.0 * kPi * kPi * o.tau * o.sigma);
+        knode = o.deta * o.deta / (4.0 * kPi * o.sigma);
     }
     o.circle_factor.resize(fit.n_circles);
-    for (int c = 0; c < fit.n_circles; ++c)
-        o.circle_factor[c] = c0 * c0 * std::exp(2.0 * o.tau * fit.radius[c] * fit.radius[c]);
+    o.psi.clear();
+    o.kmax = 0.0;
+    o.psi_max = 1.0;
+    if (swin == 1) {
+        // c(xi) = knode psi(xi_x h) psi(xi_y h): the circle keeps knode^2, the node the rest
+        for (int c = 0; c < fit.n_circles; ++c) o.circle_factor[c] = knode * knode;
+        o.kmax = S * o.h * (1.0 + 1e-12);
+        int rc = es_deconv_series(Ps, o.beta_s, o.kmax, o.psi, o.psi_max, err);
+        if (rc) return rc;
+    } else {
+        // c(|xi|) = knode h^2 exp(tau |xi|^2) / (4 pi tau), radial: one factor per circle
+        const double c0 = knode * o.h * o.h / (4.0 * kPi * o.tau);
+        for (int c = 0; c < fit.n_circles; ++c)
+            o.circle_factor[c] = c0 * c0 * std::exp(2.0 * o.tau * fit.radius[c] * fit.radius[c]);
+    }
     return SBD_OK;
 }
 

@@ -59,28 +59,38 @@ void fit_cache_clear();
 int offline_fit(int kind, double kappa, double delta_min, double delta_max, double eps,
                 int fixed_P, SbdFit& out, std::string& err);
 
-// Parameters of the type-3 transform: Gaussian spreading of the points (two-fold
-// oversampled spreading grid), a two-fold zero-padded FFT, and a node window that is
-// Gaussian or ES (exponential of semicircle).
+// Parameters of the type-3 transform: spreading of the points with an ES (exponential of
+// semicircle) or Gaussian window on a two-fold oversampled spreading grid, a two-fold
+// zero-padded FFT, and a node window that is ES or Gaussian.
 struct NufftParams {
     int Ps = 0, Pk = 0;        // stencil widths (cells per dimension, even)
     int kwin = 1;              // node window: 0 Gaussian, 1 ES
+    int swin = 1;              // spreading window: 0 Gaussian, 1 ES
     double h = 0.0;            // spreading-grid spacing
     int m = 0;                 // spreading-grid side (cells), even, 5-smooth
     int n = 0;                 // FFT length = 2 m
     int nk = 0;                // stored frequency-grid side (cells), even
     double deta = 0.0;         // frequency-grid spacing 2 pi / (n h)
     double tau = 0.0, sigma = 0.0;
-    double beta_s = 0.0;       // h^2 / (4 tau): spreading weight exp(-beta_s d^2), d in cells
+    double beta_s = 0.0;       // spreading window: Gaussian h^2 / (4 tau) (weight exp(-beta_s d^2), d in
+                               // cells), ES 2.3 Ps
     double beta_k = 0.0;       // node window: Gaussian deta^2 / (4 sigma), ES 2.3 Pk
     double cx = 0.0, cy = 0.0; // centre of the point set (bounding box)
     double tol = 0.0;          // tolerance aimed at for each transform
     std::vector<double> dec;   // spreading-grid precorrection 1 / psi_hat(x_i) (one dimension), size m
     std::vector<double> circle_factor;   // c(|xi|)^2 per circle, c = h^2 deta^2 exp(tau |xi|^2) / (4 pi tau) [x Gaussian 1/(4 pi sigma)]
+                                         // for the Gaussian spreading window; deta^4 [/(4 pi sigma)^2] for ES,
+                                         // whose deconvolution is a per-node factor (psi below)
+    // ES spreading window: psi(k) = 1 / phi_hat_s(k), phi_hat_s(k) = sum over the window of
+    // exp(-i k d) (d in cells, k = xi h in [0, kmax], kmax = S h = pi / 2), as a Chebyshev series
+    // in 2 (k / kmax)^2 - 1; the node xi = (xi_x, xi_y) takes the factor psi(xi_x h) psi(xi_y h).
+    std::vector<double> psi;
+    double kmax = 0.0;
+    double psi_max = 1.0;      // psi(kmax), the largest value of psi on [0, kmax]
 };
 
 int nufft_params(const SbdFit& fit, double half_extent, double cx, double cy, double tol,
-                 bool fp32, int kwin, NufftParams& out, std::string& err);
+                 bool fp32, int kwin, int swin, NufftParams& out, std::string& err);
 
 // Smallest even 5-smooth integer >= n.
 int good_fft_size(int n);

@@ -4,7 +4,7 @@ Each comparison uses seeded inputs from ``workloads``; expected values come from
 ``oracle`` only.  Tolerances:
   * FFT: FP64 rel-L2 <= 1e-12, FP32 <= 2e-6 (rounding of a length-n transform).
   * type-3 transforms: max error <= 10 x the plan's transform tolerance x sum|f|
-    (the Gaussian-gridding error model), FP32 additionally >= 3e-6 (rounding).
+    (the error models of the windows), FP32 additionally >= 3e-6 (rounding).
   * close matrix D: identical sparsity (bit-exact), values within 1e-12 x max|D|.
   * FP64 matvec vs the oracle SBD: rel-L2 <= 1e-10 with the transform run at 1e-13.
   * any form vs the direct sum: max |q - q*| <= eps sum|f| (Sec. 1 output bound).
@@ -94,7 +94,8 @@ def lap_small():
     return z, f, dmin, pl
 
 
-@pytest.mark.parametrize("flags", [0, 1])   # ES (default) or Gaussian window at the nodes
+# flags: ES windows (default), Gaussian at the nodes (1), Gaussian spreading (2), both Gaussian (3)
+@pytest.mark.parametrize("flags", [0, 1, 2, 3])
 @pytest.mark.parametrize("form", [0, 1])
 def test_nufft_minus_plus_match_direct(S, lap_small, form, flags):
     z, f, dmin, pl = lap_small
@@ -196,7 +197,7 @@ def config1():
     return wl, pl, q_sbd, q_dir
 
 
-@pytest.mark.parametrize("flags", [0, 1])
+@pytest.mark.parametrize("flags", [0, 1, 2, 3])
 def test_matvec_fp64_matches_oracle_sbd(S, config1, flags):
     wl, pl, q_sbd, q_dir = config1
     _assert_no_borderline_pairs(wl.z, wl.delta_min)
@@ -212,7 +213,7 @@ def test_matvec_fp64_matches_oracle_sbd(S, config1, flags):
         S.sbd_destroy(p)
 
 
-@pytest.mark.parametrize("flags", [0, 1])
+@pytest.mark.parametrize("flags", [0, 1, 2])
 @pytest.mark.parametrize("form", [0, 1])
 def test_matvec_within_eps_of_direct_sum(S, config1, form, flags):
     wl, pl, q_sbd, q_dir = config1
