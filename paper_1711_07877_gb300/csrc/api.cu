@@ -90,6 +90,7 @@ struct sbd_plan_s {
     void* q_int = nullptr;             // D f in internal order, interleaved
     bool d32 = false;                  // D's values and f_int in FP32 (the FP32 form)
     long long* pt_tile_start = nullptr;
+    PointWork pt_work{nullptr, nullptr, 0};   // chunks of the point records (spread, interp)
     long long* node_tile_start = nullptr;
     void* ghat = nullptr;              // n_xi weighted node values (scratch of the two-kernel node step)
     bool node_fused = true;            // one-kernel node step (shared memory permitting)
@@ -277,6 +278,20 @@ int build_far(sbd_plan_s* p, cudaStream_t s) {
     if ((rc = tile_sort<PointRec<T>>(pts0, p->n, np.m, static_cast<PointRec<T>*>(p->pts), p->pt_perm,
                                      p->pt_tile_start, s))) return rc;
     SBD_CUDA_TRY(cudaFreeAsync(pts0, s));
+    {
+        // work list of the point kernels: each tile's records in chunks of at most kPointChunk
+        std::vector<long long> ts(static_cast<size_t>(ntm) * ntm + 1), wb;
+        std::vector<int> wt;
+        SBD_CUDA_TRY(cudaMemcpyAsync(ts.data(), p->pt_tile_start, sizeof(long long) * ts.size(),
+                                     cudaMemcpyDeviceToHost, s));
+        SBD_CUDA_TRY(cudaStreamSynchronize(s));
+        point_work_list(ts, wb, wt);
+        long long* wbd = nullptr;
+        int* wtd = nullptr;
+        if ((rc = upload(p, &wbd, wb, s))) return rc;
+        if ((rc = upload(p, &wtd, wt, s))) return rc;
+        p->pt_work = PointWork{wbd, wtd, static_cast<int>(wt.size())};
+    }
     std::vector<int> start(fit.n_circles + 1, 0);
     for (int c = 0; c < fit.n_circles; ++c) start[c + 1] = start[c] + fit.M[c];
     if (fit.n_xi > 2000000000LL) {
@@ -457,7 +472,7 @@ int far_apply(sbd_plan_s* p, const void* f, void* q, int nrhs, cudaStream_t s, c
         void* qr = static_cast<char*>(q) + esz * p->n * r;
         const bool real = p->half_nodes;   // Laplace: real grids, half the transforms and nodes
         StepTimer t1(p, s, SBD_STAGE_SPREAD);
-        if ((rc = spread_tiled<T>(static_cast<const PointRec<T>*>(p->pts), p->pt_perm, p->pt_tile_start, p->geom,
+        if ((rc = spread_tiled<T>(static_cast<const PointRec<T>*>(p->pts), p->pt_perm, p->pt_work, p->geom,
                                   fr, cplx_io, X, s, real))) return rc;
         t1.end();
         StepTimer t2(p, s, SBD_STAGE_FFT_FWD);
@@ -477,7 +492,7 @@ int far_apply(sbd_plan_s* p, const void* f, void* q, int nrhs, cudaStream_t s, c
         t4.end();
         if (join && r == 0) SBD_CUDA_TRY(cudaStreamWaitEvent(s, join, 0));   // D f is ready
         StepTimer t5(p, s, SBD_STAGE_INTERP);
-        if ((rc = interp_tiled<T>(static_cast<const PointRec<T>*>(p->pts), p->pt_perm, p->pt_tile_start, p->geom, X,
+        if ((rc = interp_tiled<T>(static_cast<const PointRec<T>*>(p->pts), p->pt_perm, p->pt_work, p->geom, X,
                                   w0, p->sumf + r, qr, cplx_io, s, real, add, nrhs, r))) return rc;
         t5.end();
     }
@@ -490,7 +505,7 @@ int nufft_minus_impl(sbd_plan_s* p, const void* f, void* fhat, cudaStream_t s) {
     auto* A = static_cast<cx_t<T>*>(p->wsA);
     auto* B = static_cast<cx_t<T>*>(p->wsB);
     auto* C = static_cast<cx_t<T>*>(p->wsC);
-    int rc = spread_tiled<T>(static_cast<const PointRec<T>*>(p->pts), p->pt_perm, p->pt_tile_start, p->geom, f,
+    int rc = spread_tiled<T>(static_cast<const PointRec<T>*>(p->pts), p->pt_perm, p->pt_work, p->geom, f,
                              true, X, s);
     if (rc) return rc;
     if ((rc = forward_fft<T>(p, X, A, C, B, s))) return rc;
@@ -514,7 +529,7 @@ int nufft_plus_impl(sbd_plan_s* p, const void* ghat, void* q, cudaStream_t s) {
     if (rc) return rc;
     if ((rc = inverse_fft<T>(p, C, A, B, X, s, false))) return rc;
     SBD_CUDA_TRY(cudaMemsetAsync(p->zero2, 0, sizeof(double2), s));
-    return interp_tiled<T>(static_cast<const PointRec<T>*>(p->pts), p->pt_perm, p->pt_tile_start, p->geom, X,
+    return interp_tiled<T>(static_cast<const PointRec<T>*>(p->pts), p->pt_perm, p->pt_work, p->geom, X,
                            make_double2(0, 0), p->zero2, q, true, s);
 }
 

@@ -311,6 +311,116 @@ __global__ void __launch_bounds__(256) scatter_tiles_kernel(
     }
 }
 
+// Interpolation by work item (PointWork): the CTA loads its tile plus the (P-1) halo of the
+// grid into shared memory and takes the records of its chunk, a group of G lanes per record
+// (lane = stencil column, rows accumulated in registers, columns reduced with shuffles).
+template <typename T, int G, bool PK>
+__global__ void __launch_bounds__(256) interp_chunks_kernel(
+    const PointRec<T>* __restrict__ rec, PointWork work, int ntx, int n, int P, Window<T> win,
+    const cx_t<T>* __restrict__ grid, PointOut<T> out) {
+    using C = cx_t<T>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* s = reinterpret_cast<C*>(smem_raw);
+    const int tile = work.tile[blockIdx.x];
+    const long long b0 = work.begin[blockIdx.x], b1 = work.begin[blockIdx.x + 1];
+    const int ox = (tile / ntx) * kNodeTile, oy = (tile % ntx) * kNodeTile;
+    const int W = kNodeTile + P - 1;
+    const int rows = min(W, n - ox), cols = min(W, n - oy);
+    for (int idx = threadIdx.x; idx < W * W; idx += blockDim.x) {
+        const int r = idx / W, c = idx - r * W;
+        C v = mk<T>(0, 0);
+        if (r < rows && c < cols) {
+            if (PK) v = mk<T>(reinterpret_cast<const T*>(grid)[packed_index(ox + r, oy + c, n)], static_cast<T>(0));
+            else v = grid[static_cast<long>(ox + r) * n + oy + c];
+        }
+        s[idx] = v;
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int sub = lane % G;
+    const unsigned gmask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << (lane & ~(G - 1)));
+    const int group = threadIdx.x / G, ngroups = blockDim.x / G;
+    for (long long i = b0 + group; i < b1; i += ngroups) {
+        const PointRec<T> q = rec[i];
+        const int rx = q.cell.x - ox, ry = q.cell.y - oy;   // in [0, 64): the record's own tile
+        T wx, wy;
+        lane_weights<T>(sub, P, win, q.frac.x, q.frac.y, wx, wy);
+        T sr = 0, si = 0;
+        const C* col = s + static_cast<long>(rx) * W + ry + sub;
+        for (int a = 0; a < P; ++a) {
+            const T w = __shfl_sync(gmask, wx, a, G);
+            if (sub < P) {
+                const C v = col[a * W];
+                sr += w * v.x;
+                si += w * v.y;
+            }
+        }
+        sr *= wy;
+        si *= wy;
+#pragma unroll
+        for (int o = G / 2; o > 0; o >>= 1) {
+            sr += __shfl_xor_sync(gmask, sr, o, G);
+            si += __shfl_xor_sync(gmask, si, o, G);
+        }
+        if (sub == 0) out.put(i, q, mk<T>(sr, si));
+    }
+}
+
+// Spreading by work item (PointWork): the CTA accumulates the stencils of its chunk's records
+// into a shared (64 + P - 1)^2 window with shared-memory atomics, then adds every cell it
+// reached into the (cleared) grid with global atomics.  RV: real values, one plane.
+template <typename T, int G, bool PK, bool RV>
+__global__ void __launch_bounds__(256) spread_chunks_kernel(
+    const PointRec<T>* __restrict__ rec, PointWork work, int ntx, int n, int P, Window<T> win, PointVal<T> val,
+    cx_t<T>* __restrict__ grid) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* acc = reinterpret_cast<T*>(smem_raw);          // [W][W][RV ? 1 : 2]
+    constexpr int kC = RV ? 1 : 2;
+    const int W = kNodeTile + P - 1;
+    const int tile = work.tile[blockIdx.x];
+    const long long b0 = work.begin[blockIdx.x], b1 = work.begin[blockIdx.x + 1];
+    const int ox = (tile / ntx) * kNodeTile, oy = (tile % ntx) * kNodeTile;
+    for (int idx = threadIdx.x; idx < kC * W * W; idx += blockDim.x) acc[idx] = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int sub = lane % G;
+    const unsigned gmask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << (lane & ~(G - 1)));
+    const int group = threadIdx.x / G, ngroups = blockDim.x / G;
+    for (long long i = b0 + group; i < b1; i += ngroups) {
+        const PointRec<T> q = rec[i];
+        const int rx = q.cell.x - ox, ry = q.cell.y - oy;   // in [0, 64): the record's own tile
+        T wx, wy;
+        lane_weights<T>(sub, P, win, q.frac.x, q.frac.y, wx, wy);
+        const cx_t<T> g = val.get(i);
+        const T gr = g.x * wy, gi = g.y * wy;
+        T* cell = acc + kC * (rx * W + ry + sub);
+        for (int a = 0; a < P; ++a) {
+            const T w = __shfl_sync(gmask, wx, a, G);
+            if (sub < P) {
+                atomicAdd(cell + kC * a * W, gr * w);
+                if (!RV) atomicAdd(cell + kC * a * W + 1, gi * w);
+            }
+        }
+    }
+    __syncthreads();
+    const int rows = min(W, n - ox), cols = min(W, n - oy);
+    for (int idx = threadIdx.x; idx < W * W; idx += blockDim.x) {
+        const int r = idx / W, c = idx - r * W;
+        if (r >= rows || c >= cols) continue;
+        const T vr = acc[kC * idx];
+        if (PK) {
+            if (vr != static_cast<T>(0)) atomicAdd(reinterpret_cast<T*>(grid) + packed_index(ox + r, oy + c, n), vr);
+        } else {
+            T* g = reinterpret_cast<T*>(grid + static_cast<long>(ox + r) * n + oy + c);
+            if (vr != static_cast<T>(0)) atomicAdd(g, vr);
+            if (!RV) {
+                const T vi = acc[kC * idx + 1];
+                if (vi != static_cast<T>(0)) atomicAdd(g + 1, vi);
+            }
+        }
+    }
+}
+
 // Fused node step: one CTA per 64 x 64 tile of the frequency grid.  The tile plus a
 // (P-1) halo of K sits in shared memory with an accumulator of the same size
 // (interleaved float2 in FP32, two planes re / im in FP64).  A group of G lanes (G = 8, 16 or 32 >= P; 32 / G nodes per warp) takes
@@ -857,36 +967,97 @@ int node_step_tiled(const NodeRec<T>* nodes, const long long* tile_start, const 
     return launch_scatter<T>(nodes, tile_start, g.nk, g.Pk, g.kwin, g.beta_k, NodeVal<T>{ghat}, kout, s);
 }
 
-template <typename T>
-int spread_tiled(const PointRec<T>* pts, const int* perm, const long long* tile_start, const FarGeom& g,
-                 const void* f, bool f_complex, cx_t<T>* grid, cudaStream_t s, bool packed) {
-    if (packed) {
-        if (f_complex || (g.m & 1)) {
-            set_error("spread: a packed real grid needs real values and an even side");
-            return SBD_EINVAL;
+void point_work_list(const std::vector<long long>& tile_start, std::vector<long long>& begin,
+                     std::vector<int>& tile) {
+    begin.clear();
+    tile.clear();
+    for (size_t t = 0; t + 1 < tile_start.size(); ++t)
+        for (long long b = tile_start[t]; b < tile_start[t + 1]; b += kPointChunk) {
+            begin.push_back(b);
+            tile.push_back(static_cast<int>(t));
         }
-        return launch_scatter<T, PointRec<T>, PointVal<T>, true, true>(pts, tile_start, g.m, g.Ps, g.swin,
-                                                                        g.beta_s, PointVal<T>{f, perm, false}, grid,
-                                                                        s);
-    }
-    return launch_scatter<T>(pts, tile_start, g.m, g.Ps, g.swin, g.beta_s, PointVal<T>{f, perm, f_complex}, grid,
-                             s);
+    begin.push_back(tile_start.empty() ? 0 : tile_start.back());
+}
+
+template <typename T, int G, bool PK, bool RV>
+int launch_spread_chunks(const PointRec<T>* pts, const PointWork& work, const FarGeom& g, PointVal<T> val,
+                         cx_t<T>* grid, cudaStream_t s) {
+    const Window<T> win = make_window<T>(g.swin, g.beta_s, g.Ps);
+    const size_t W = kNodeTile + g.Ps - 1;
+    const size_t smem = (RV ? 1 : 2) * sizeof(T) * W * W;
+    auto k = spread_chunks_kernel<T, G, PK, RV>;
+    SBD_TRY(raise_smem_limit(k, smem));
+    k<<<work.count, 256, smem, s>>>(pts, work, tiles_per_side(g.m), g.m, g.Ps, win, val, grid);
+    SBD_LAUNCH_CHECK();
+    return SBD_OK;
+}
+
+template <typename T, int G, bool PK>
+int launch_interp_chunks(const PointRec<T>* pts, const PointWork& work, const FarGeom& g, const cx_t<T>* grid,
+                         const PointOut<T>& out, cudaStream_t s) {
+    const Window<T> win = make_window<T>(g.swin, g.beta_s, g.Ps);
+    const size_t W = kNodeTile + g.Ps - 1;
+    const size_t smem = W * W * sizeof(cx_t<T>);
+    auto k = interp_chunks_kernel<T, G, PK>;
+    SBD_TRY(raise_smem_limit(k, smem));
+    k<<<work.count, 256, smem, s>>>(pts, work, tiles_per_side(g.m), g.m, g.Ps, win, grid, out);
+    SBD_LAUNCH_CHECK();
+    return SBD_OK;
 }
 
 template <typename T>
-int interp_tiled(const PointRec<T>* pts, const int* perm, const long long* tile_start, const FarGeom& g,
+int spread_tiled(const PointRec<T>* pts, const int* perm, const PointWork& work, const FarGeom& g,
+                 const void* f, bool f_complex, cx_t<T>* grid, cudaStream_t s, bool packed) {
+    if (packed && (f_complex || (g.m & 1))) {
+        set_error("spread: a packed real grid needs real values and an even side");
+        return SBD_EINVAL;
+    }
+    if (g.Ps > 32) {
+        set_error("spread: stencil wider than 32 cells");
+        return SBD_ENOTSUP;
+    }
+    const size_t cells = static_cast<size_t>(g.m) * g.m;
+    SBD_CUDA_TRY(cudaMemsetAsync(grid, 0, packed ? sizeof(T) * cells : sizeof(cx_t<T>) * cells, s));
+    if (work.count <= 0) return SBD_OK;
+    const PointVal<T> val{f, perm, packed ? false : f_complex};
+    const bool rv = packed || !f_complex;
+    if (packed) {
+        if (g.Ps <= 8) return launch_spread_chunks<T, 8, true, true>(pts, work, g, val, grid, s);
+        if (g.Ps <= 16) return launch_spread_chunks<T, 16, true, true>(pts, work, g, val, grid, s);
+        return launch_spread_chunks<T, 32, true, true>(pts, work, g, val, grid, s);
+    }
+    if (rv) {
+        if (g.Ps <= 8) return launch_spread_chunks<T, 8, false, true>(pts, work, g, val, grid, s);
+        if (g.Ps <= 16) return launch_spread_chunks<T, 16, false, true>(pts, work, g, val, grid, s);
+        return launch_spread_chunks<T, 32, false, true>(pts, work, g, val, grid, s);
+    }
+    if (g.Ps <= 8) return launch_spread_chunks<T, 8, false, false>(pts, work, g, val, grid, s);
+    if (g.Ps <= 16) return launch_spread_chunks<T, 16, false, false>(pts, work, g, val, grid, s);
+    return launch_spread_chunks<T, 32, false, false>(pts, work, g, val, grid, s);
+}
+
+template <typename T>
+int interp_tiled(const PointRec<T>* pts, const int* perm, const PointWork& work, const FarGeom& g,
                  const cx_t<T>* grid, double2 w0, const double2* sumf, void* q, bool q_complex, cudaStream_t s,
                  bool packed, const void* add, int add_stride, int add_off) {
     const PointOut<T> out{q, perm, q_complex, w0, sumf, add, add_stride, add_off};
-    if (packed) {
-        if (q_complex || (g.m & 1)) {
-            set_error("interp: a packed real grid needs real output and an even side");
-            return SBD_EINVAL;
-        }
-        return launch_gather<T, PointRec<T>, PointOut<T>, true>(pts, tile_start, g.m, g.Ps, g.swin, g.beta_s,
-                                                                grid, out, s);
+    if (packed && (q_complex || (g.m & 1))) {
+        set_error("interp: a packed real grid needs real output and an even side");
+        return SBD_EINVAL;
     }
-    return launch_gather<T>(pts, tile_start, g.m, g.Ps, g.swin, g.beta_s, grid, out, s);
+    if (g.Ps > 32) {
+        set_error("interp: stencil wider than 32 cells");
+        return SBD_ENOTSUP;
+    }
+    if (work.count <= 0) return SBD_OK;
+    if (packed) {
+        if (g.Ps <= 8) return launch_interp_chunks<T, 8, true>(pts, work, g, grid, out, s);
+        if (g.Ps <= 16) return launch_interp_chunks<T, 16, true>(pts, work, g, grid, out, s);
+        return launch_interp_chunks<T, 32, true>(pts, work, g, grid, out, s);
+    }
+    if (g.Ps <= 8) return launch_interp_chunks<T, 8, false>(pts, work, g, grid, out, s);
+    if (g.Ps <= 16) return launch_interp_chunks<T, 16, false>(pts, work, g, grid, out, s);
+    return launch_interp_chunks<T, 32, false>(pts, work, g, grid, out, s);
 }
 
 template <typename T>
@@ -916,9 +1087,9 @@ int fill_grid(cx_t<T>* x, long n, T re, T im, cudaStream_t s) {
     template int fill_grid<T>(cx_t<T>*, long, T, T, cudaStream_t);                                          \
     template int node_step_fused<T>(const NodeRec<T>*, const long long*, const FarGeom&, const cx_t<T>*,     \
                                     cx_t<T>*, const NodeTuning&, cudaStream_t);                              \
-    template int spread_tiled<T>(const PointRec<T>*, const int*, const long long*, const FarGeom&,           \
+    template int spread_tiled<T>(const PointRec<T>*, const int*, const PointWork&, const FarGeom&,           \
                                  const void*, bool, cx_t<T>*, cudaStream_t, bool);                           \
-    template int interp_tiled<T>(const PointRec<T>*, const int*, const long long*, const FarGeom&,           \
+    template int interp_tiled<T>(const PointRec<T>*, const int*, const PointWork&, const FarGeom&,           \
                                  const cx_t<T>*, double2, const double2*, void*, bool, cudaStream_t, bool,   \
                                  const void*, int, int);
 SBD_NODE_INST(float)

@@ -3,6 +3,8 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <vector>
+
 #include "common.cuh"
 #include "far.cuh"
 
@@ -49,17 +51,33 @@ template <typename T>
 int node_step_fused(const NodeRec<T>* nodes, const long long* tile_start, const FarGeom& g,
                     const cx_t<T>* kin, cx_t<T>* kout, const NodeTuning& t, cudaStream_t s);
 
+// Work list of the point kernels (spreading, interpolation): item w is the records
+// [begin[w], begin[w + 1]) of the 64 x 64 tile tile[w], at most kPointChunk of them; the
+// records of a tile (sorted by tile_sort) are split into consecutive chunks, so that a tile
+// where many points crowd becomes several CTAs instead of one long one.
+constexpr int kPointChunk = 512;
+struct PointWork {
+    const long long* begin;   // count + 1 entries (device)
+    const int* tile;          // count entries (device)
+    int count;
+};
+// Host: the chunk list of a tile_start table (ntiles + 1 prefix offsets).
+void point_work_list(const std::vector<long long>& tile_start, std::vector<long long>& begin,
+                     std::vector<int>& tile);
+
 // grid (m x m, fully written) = spreading of f (float64 or complex128, original order).
 // packed: real f into a real grid stored as packed row pairs (m / 2 x m complex,
-// cell (R, c) = component R & 1 of element (R >> 1, c)).
+// cell (R, c) = component R & 1 of element (R >> 1, c)).  The grid is cleared, then each
+// work item accumulates its chunk in shared memory and adds the cells it reached into the
+// grid with global atomics.
 template <typename T>
-int spread_tiled(const PointRec<T>* pts, const int* perm, const long long* tile_start, const FarGeom& g,
+int spread_tiled(const PointRec<T>* pts, const int* perm, const PointWork& work, const FarGeom& g,
                  const void* f, bool f_complex, cx_t<T>* grid, cudaStream_t s, bool packed = false);
 
 // q[perm[i]] = interpolation of grid at point i + w0 * sumf[0] (float64 or complex128 out)
 // + add[i * add_stride + add_off] when add is given (same type as q, record order).
 template <typename T>
-int interp_tiled(const PointRec<T>* pts, const int* perm, const long long* tile_start, const FarGeom& g,
+int interp_tiled(const PointRec<T>* pts, const int* perm, const PointWork& work, const FarGeom& g,
                  const cx_t<T>* grid, double2 w0, const double2* sumf, void* q, bool q_complex, cudaStream_t s,
                  bool packed = false, const void* add = nullptr, int add_stride = 1, int add_off = 0);
 
