@@ -26,9 +26,12 @@ struct Window {
     T inv_half;   // 2 / P (ES only)
     __device__ __forceinline__ T operator()(T d) const {
         if (kind == kWinGauss) return wexp<T>(-beta * d * d);
+        // sqrt(1 - z^2) - 1 = -z^2 / (1 + sqrt(1 - z^2)): no cancellation near the centre,
+        // where the weights are largest (the difference form loses ~1e-5 relative there in FP32)
         const T z = d * inv_half;
-        const T r = static_cast<T>(1) - z * z;
-        return r > static_cast<T>(0) ? wexp<T>(beta * (wsqrt<T>(r) - static_cast<T>(1))) : static_cast<T>(0);
+        const T z2 = z * z;
+        const T r = static_cast<T>(1) - z2;
+        return r > static_cast<T>(0) ? wexp<T>(-beta * z2 / (static_cast<T>(1) + wsqrt<T>(r))) : static_cast<T>(0);
     }
 };
 
