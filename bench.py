@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--requests", type=int, default=256, help="serve: number of solve requests")
     ap.add_argument("--slots", type=int, default=8, help="serve: concurrent requests")
     ap.add_argument("--eps", type=float, default=1e-6)
+    ap.add_argument("--alpha", type=float, default=0.0,
+                    help="curve workloads: delta_min by Theorem 1 with this alpha in [0, 1/6]")
     ap.add_argument("--cpu-targets", type=int, default=400, help="targets of the oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-balance", action="store_true", help="skip the delta_min balance (sbd_plan_balanced)")
@@ -74,17 +76,20 @@ def make_workload(args, rank):
     import workloads as W
     seed = WORKLOADS[args.workload][2] + rank
     if args.workload == "laplace_curves":
-        return W.laplace_curves(args.n, seed, args.eps)
+        return W.laplace_curves(args.n, seed, args.eps, args.alpha)
     if args.workload == "helmholtz_curves":
-        return W.helmholtz_curves(args.n, seed, args.eps)
+        return W.helmholtz_curves(args.n, seed, args.eps, alpha=args.alpha)
     return W.laplace_square(args.n, seed, args.eps, args.nrhs)
 
 
 def workload_config(args, rank):
     desc = WORKLOADS[args.workload][3]
+    if args.alpha and args.workload.endswith("curves"):
+        desc = desc.replace("alpha=0", f"alpha={args.alpha:g}")
     return {"workload": f"{args.workload} N={args.n} nrhs={args.nrhs} eps={args.eps:g} ({desc})",
             "kernel": "helmholtz" if args.workload.startswith("helmholtz") else "laplace",
             "n_points": args.n, "nrhs": args.nrhs, "eps": args.eps, "seed": WORKLOADS[args.workload][2] + rank,
+            "alpha": args.alpha if args.workload.endswith("curves") else None,
             "form": args.form, "l2_policy": "inputs larger than L2 (each grid and D exceed 129 MB)",
             "scaling_mode": "replicas (one independent instance per rank)"}
 
