@@ -92,6 +92,14 @@ typedef struct {
  * the ES window's is a factor per node, folded into the node weights at plan time. */
 #define SBD_FLAG_GAUSSIAN_NODES 1
 #define SBD_FLAG_GAUSSIAN_SPREAD 2
+/* Oversampling sigma of the spreading grid (spacing pi / (sigma S), S the largest circle
+ * radius).  By default the plan takes 1.5 (ES window of about 10 cells at the FP32
+ * tolerance) where the grid at sigma = 2 would have more than 20 cells per point, which
+ * shrinks the spreading grid and the FFT rows by a quarter, else 2 (8 cells).  These flags
+ * force one or the other; SPREAD_SIGMA_15 with GAUSSIAN_SPREAD, or both flags, is
+ * SBD_EINVAL. */
+#define SBD_FLAG_SPREAD_SIGMA_2 4
+#define SBD_FLAG_SPREAD_SIGMA_15 8
 
 /* Plan summary (sbd_plan_info). */
 typedef struct {

@@ -628,7 +628,10 @@ int sbd_plan(const double* points, int64_t n, sbd_kernel kernel, double delta_mi
         set_error("sbd_plan: unknown form");
         return SBD_EINVAL;
     }
-    if ((o.flags & ~(SBD_FLAG_GAUSSIAN_NODES | SBD_FLAG_GAUSSIAN_SPREAD)) != 0 || o.fixed_P < 0 || o.max_nrhs < 0 || o.nufft_tol < 0 ||
+    if ((o.flags & ~(SBD_FLAG_GAUSSIAN_NODES | SBD_FLAG_GAUSSIAN_SPREAD | SBD_FLAG_SPREAD_SIGMA_2 |
+                     SBD_FLAG_SPREAD_SIGMA_15)) != 0 ||
+        ((o.flags & SBD_FLAG_SPREAD_SIGMA_2) && (o.flags & SBD_FLAG_SPREAD_SIGMA_15)) ||
+        ((o.flags & SBD_FLAG_GAUSSIAN_SPREAD) && (o.flags & SBD_FLAG_SPREAD_SIGMA_15)) || o.fixed_P < 0 || o.max_nrhs < 0 || o.nufft_tol < 0 ||
         !(o.delta_max >= 0) || o.host_threads < 0) {
         set_error("sbd_plan: invalid options");
         return SBD_EINVAL;
@@ -704,7 +707,9 @@ int sbd_plan(const double* points, int64_t n, sbd_kernel kernel, double delta_mi
     const double half = std::max(std::max(bb[2] - cx, bb[3] - cy), 1e-300);
     const int kwin = (o.flags & SBD_FLAG_GAUSSIAN_NODES) ? 0 : 1;
     const int swin = (o.flags & SBD_FLAG_GAUSSIAN_SPREAD) ? 0 : 1;
-    if ((rc = nufft_params(fit, half, cx, cy, tol, o.form == SBD_FORM_FP32, kwin, swin, p->np, err))) {
+    const int sigma_mode = (o.flags & SBD_FLAG_SPREAD_SIGMA_15) ? 1 : (o.flags & SBD_FLAG_SPREAD_SIGMA_2) ? 2 : 0;
+    if ((rc = nufft_params(fit, half, cx, cy, tol, o.form == SBD_FORM_FP32, kwin, swin, sigma_mode, p->n, p->np,
+                           err))) {
         set_error(err);
         return fail(rc);
     }

@@ -660,7 +660,8 @@ static int es_deconv_series(int P, double beta, double kmax, std::vector<double>
 }
 
 int nufft_params(const SbdFit& fit, double half_extent, double cx, double cy, double tol,
-                 bool fp32, int kwin, int swin, NufftParams& o, std::string& err) {
+                 bool fp32, int kwin, int swin, int sigma_mode, long n_points, NufftParams& o,
+                 std::string& err) {
     double S = 0.0;
     for (int c = 0; c < fit.n_circles; ++c) S = std::max(S, fit.radius[c]);
     if (!(S > 0.0) || !(half_extent > 0.0)) {
@@ -670,10 +671,24 @@ int nufft_params(const SbdFit& fit, double half_extent, double cx, double cy, do
     if (fp32) tol = std::max(tol, 3e-7);
     tol = std::max(tol, 1e-15);
     const int pmax = fp32 ? 16 : 32;
-    // spreading side: ES error ~ 10^-(P - 1) at two-fold oversampling; Gaussian ~ 0.1 exp(-pi P / 3)
+    // Oversampling of the spreading grid (spacing h = pi / (sigma S)): 2, or 1.5 with the ES
+    // window, which shrinks the spreading grid and the FFT rows by a quarter for a wider
+    // stencil.  Automatic: 1.5 where the grid of sigma = 2 has more than 20 cells per point
+    // (there the transforms outweigh the point stencils; measured break-even on GB300).
+    double sig = 2.0;
+    if (swin == 1) {
+        if (sigma_mode == 1) {
+            sig = 1.5;
+        } else if (sigma_mode == 0) {
+            const double m2 = 2.0 * half_extent * (2.0 * S) / kPi;   // cells per side at sigma = 2
+            if (m2 * m2 > 20.0 * static_cast<double>(n_points)) sig = 1.5;
+        }
+    }
+    // spreading side: ES error ~ 10 exp(-pi P sqrt(1 - 1 / sigma)) (10^-(P - 1) at sigma = 2);
+    // Gaussian ~ 0.1 exp(-pi P / 3) at sigma = 2
     int Ps;
     if (swin == 1) {
-        Ps = static_cast<int>(std::ceil(-std::log10(tol))) + 1;
+        Ps = static_cast<int>(std::ceil(std::log(10.0 / tol) / (kPi * std::sqrt(1.0 - 1.0 / sig))));
     } else {
         Ps = static_cast<int>(std::ceil((3.0 / kPi) * std::log(0.1 / tol)));
     }
@@ -692,10 +707,11 @@ int nufft_params(const SbdFit& fit, double half_extent, double cx, double cy, do
     o.kwin = kwin;
     o.swin = swin;
     o.tol = tol;
-    o.h = kPi / (2.0 * S);
+    o.sigma_s = sig;
+    o.h = kPi / (sig * S);
     if (swin == 1) {
         o.tau = 0.0;
-        o.beta_s = 2.3 * Ps;
+        o.beta_s = 2.3 * Ps * (1.0 - 0.5 / sig) / 0.75;   // 2.3 P at sigma = 2
     } else {
         const double u = Ps * kPi / 24.0;   // balanced truncation / aliasing of the Gaussian at two-fold oversampling
         o.tau = u / (S * S);
@@ -703,9 +719,20 @@ int nufft_params(const SbdFit& fit, double half_extent, double cx, double cy, do
     }
     o.m = good_fft_size(static_cast<int>(std::ceil(2.0 * half_extent / o.h)) + Ps + 4);
     o.n = 2 * o.m;
-    o.nk = o.m + Pk + 4;
     const double Xg = 0.5 * o.m * o.h;
     o.deta = 2.0 * kPi / (o.n * o.h);
+    {
+        // stored frequency grid: every node (|xi| <= S) with its stencil; m + Pk + 4 at sigma = 2
+        const int nk = static_cast<int>(std::ceil(2.0 * S / o.deta - 1e-9)) + Pk + 4;
+        o.nk = nk + (nk & 1);
+    }
+    if (o.nk > o.n) {
+        // a very small grid: the node stencils at sigma = 1.5 reach past the FFT length
+        if (sigma_mode == 0 && sig != 2.0)
+            return nufft_params(fit, half_extent, cx, cy, tol, fp32, kwin, swin, 2, n_points, o, err);
+        err = "the frequency grid exceeds the FFT length (grid too small for this oversampling)";
+        return SBD_ENOTSUP;
+    }
     o.cx = cx;
     o.cy = cy;
     o.dec.resize(o.m);

@@ -66,10 +66,11 @@ struct NufftParams {
     int Ps = 0, Pk = 0;        // stencil widths (cells per dimension, even)
     int kwin = 1;              // node window: 0 Gaussian, 1 ES
     int swin = 1;              // spreading window: 0 Gaussian, 1 ES
-    double h = 0.0;            // spreading-grid spacing
+    double h = 0.0;            // spreading-grid spacing pi / (sigma_s S)
+    double sigma_s = 2.0;      // oversampling of the spreading grid (2, or 1.5 with the ES window)
     int m = 0;                 // spreading-grid side (cells), even, 5-smooth
     int n = 0;                 // FFT length = 2 m
-    int nk = 0;                // stored frequency-grid side (cells), even
+    int nk = 0;                // stored frequency-grid side (cells), even: 2 S / deta + Pk + 4
     double deta = 0.0;         // frequency-grid spacing 2 pi / (n h)
     double tau = 0.0, sigma = 0.0;
     double beta_s = 0.0;       // spreading window: Gaussian h^2 / (4 tau) (weight exp(-beta_s d^2), d in
@@ -89,8 +90,11 @@ struct NufftParams {
     double psi_max = 1.0;      // psi(kmax), the largest value of psi on [0, kmax]
 };
 
+// sigma_mode: 0 automatic, 1 spreading oversampling 1.5, 2 oversampling 2 (the Gaussian
+// spreading window always uses 2); n_points feeds the automatic choice.
 int nufft_params(const SbdFit& fit, double half_extent, double cx, double cy, double tol,
-                 bool fp32, int kwin, int swin, NufftParams& out, std::string& err);
+                 bool fp32, int kwin, int swin, int sigma_mode, long n_points, NufftParams& out,
+                 std::string& err);
 
 // Smallest even 5-smooth integer >= n.
 int good_fft_size(int n);

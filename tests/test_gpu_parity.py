@@ -94,8 +94,9 @@ def lap_small():
     return z, f, dmin, pl
 
 
-# flags: ES windows (default), Gaussian at the nodes (1), Gaussian spreading (2), both Gaussian (3)
-@pytest.mark.parametrize("flags", [0, 1, 2, 3])
+# flags: ES windows (default), Gaussian at the nodes (1), Gaussian spreading (2), both Gaussian (3),
+# spreading oversampling forced to 2 (4) or 1.5 (8)
+@pytest.mark.parametrize("flags", [0, 1, 2, 3, 4, 8])
 @pytest.mark.parametrize("form", [0, 1])
 def test_nufft_minus_plus_match_direct(S, lap_small, form, flags):
     z, f, dmin, pl = lap_small
@@ -197,7 +198,7 @@ def config1():
     return wl, pl, q_sbd, q_dir
 
 
-@pytest.mark.parametrize("flags", [0, 1, 2, 3])
+@pytest.mark.parametrize("flags", [0, 1, 2, 3, 4, 8])
 def test_matvec_fp64_matches_oracle_sbd(S, config1, flags):
     wl, pl, q_sbd, q_dir = config1
     _assert_no_borderline_pairs(wl.z, wl.delta_min)
@@ -213,7 +214,7 @@ def test_matvec_fp64_matches_oracle_sbd(S, config1, flags):
         S.sbd_destroy(p)
 
 
-@pytest.mark.parametrize("flags", [0, 1, 2])
+@pytest.mark.parametrize("flags", [0, 1, 2, 4, 8])
 @pytest.mark.parametrize("form", [0, 1])
 def test_matvec_within_eps_of_direct_sum(S, config1, form, flags):
     wl, pl, q_sbd, q_dir = config1
@@ -229,6 +230,30 @@ def test_matvec_within_eps_of_direct_sum(S, config1, form, flags):
         assert np.max(np.abs(far + close - q)) <= (2e-6 if form == 1 else 1e-11) * np.abs(q).max()
     finally:
         S.sbd_destroy(p)
+
+
+def test_spreading_oversampling_choice(S, lap_small):
+    """Automatic oversampling of the spreading grid: 1.5 (wider stencil, grid side about 3/4)
+    where the grid at 2 has more than 20 cells per point, else 2; the flags force either, and
+    contradictory flags are rejected."""
+    z, f, dmin, pl = lap_small
+    info = {}
+    for flags in (0, 4, 8):
+        p = make_plan(S, z, "laplace", dmin, 1e-6, form=1, flags=flags)
+        try:
+            info[flags] = S.sbd_plan_info(p)
+        finally:
+            S.sbd_destroy(p)
+    m2, m15 = info[4]["grid_x"], info[8]["grid_x"]
+    assert info[4]["stencil_x"] == 8 and info[8]["stencil_x"] == 10
+    assert m15 < m2 and info[8]["grid_k"] <= 2 * m15
+    ratio = (m2 - 8 - 4) ** 2 / (20 * len(z))        # ~ cells per point at 2, over 20
+    if not 0.8 < ratio < 1.25:                       # away from the rounding of the grid side
+        assert info[0]["grid_x"] == info[8 if ratio > 1 else 4]["grid_x"]
+    for flags in (4 | 8, 2 | 8):
+        with pytest.raises(S.SbdError) as e:
+            make_plan(S, z, "laplace", dmin, 1e-6, form=1, flags=flags)
+        assert e.value.code == S.SBD_EINVAL
 
 
 def test_matvec_helmholtz(S, helm_small):
