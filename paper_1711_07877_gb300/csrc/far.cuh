@@ -21,9 +21,9 @@ struct FarGeom {
 };
 
 // Deconvolution of the ES spreading window at a node: psi(k) = 1 / phi_hat_s(k) with
-// k = xi h, as a Chebyshev series in 2 (k / kmax)^2 - 1; the node xi takes the factor
-// psi(xi_x h) psi(xi_y h).  coef null: Gaussian spreading, whose factor exp(tau |xi|^2) is
-// radial and sits in the circle's weight.  FP64.
+// k = xi h, log psi as a Chebyshev series in 2 (k / kmax)^2 - 1; the node xi takes the
+// factor psi(xi_x h) psi(xi_y h).  coef null: Gaussian spreading, whose factor
+// exp(tau |xi|^2) is radial and sits in the circle's weight.  FP64.
 struct SpreadDeconv {
     const double* coef;
     int n;              // coefficients
@@ -38,7 +38,7 @@ __device__ __forceinline__ double spread_psi(const SpreadDeconv& d, double k) {
         b2 = b1;
         b1 = t;
     }
-    return x * b1 - b2 + d.coef[0];
+    return exp(x * b1 - b2 + d.coef[0]);
 }
 __device__ __forceinline__ double spread_deconv(const SpreadDeconv& d, double2 xi) {
     if (!d.coef) return 1.0;

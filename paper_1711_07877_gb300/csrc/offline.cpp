@@ -619,21 +619,23 @@ static double cheb_eval(const std::vector<double>& c, double x) {
     return x * b1 - b2 + c[0];
 }
 
-// Chebyshev series of psi(k) = 1 / phi_hat(k) in x = 2 (k / kmax)^2 - 1 on [0, kmax] (psi is
-// even in k), phi_hat(k) = (P/2) es_hat(k P / 2, beta) the Fourier transform of the ES window of
-// width P cells; the degree is doubled until 257 check points agree with the quadrature to
-// 1e-14 relative.
+// Chebyshev series of log psi(k), psi(k) = 1 / phi_hat(k), in x = 2 (k / kmax)^2 - 1 on
+// [0, kmax] (psi is even in k and positive), phi_hat(k) = (P/2) es_hat(k P / 2, beta) the
+// Fourier transform of the ES window of width P cells.  The logarithm keeps the relative
+// accuracy of psi where it is small (psi spans up to 10^3 over the band for wide windows);
+// the degree is doubled until 257 check points agree with the quadrature to 1e-13 (the
+// quadrature's own rounding: phi_hat falls to ~1e-3 of its peak at the band edge).
 static int es_deconv_series(int P, double beta, double kmax, std::vector<double>& coef, double& psi_max,
                             std::string& err) {
     std::vector<double> gx, gw;
     gauss_legendre(200, gx, gw);
-    auto psi = [&](double k) { return 1.0 / (0.5 * P * es_hat(0.5 * P * k, beta, gx, gw)); };
+    auto log_psi = [&](double k) { return -std::log(0.5 * P * es_hat(0.5 * P * k, beta, gx, gw)); };
     for (int deg = 24; deg <= 192; deg *= 2) {
         const int nn = deg + 1;
         std::vector<double> fv(nn);
         for (int j = 0; j < nn; ++j) {
             const double x = std::cos(kPi * (j + 0.5) / nn);
-            fv[j] = psi(kmax * std::sqrt(0.5 * (x + 1.0)));
+            fv[j] = log_psi(kmax * std::sqrt(0.5 * (x + 1.0)));
         }
         coef.assign(nn, 0.0);
         for (int i = 0; i < nn; ++i) {
@@ -641,21 +643,26 @@ static int es_deconv_series(int P, double beta, double kmax, std::vector<double>
             for (int j = 0; j < nn; ++j) acc += fv[j] * std::cos(kPi * i * (j + 0.5) / nn);
             coef[i] = (i == 0 ? 1.0 : 2.0) * acc / nn;
         }
-        double worst = 0.0, most = 0.0;
+        double worst = 0.0, most = -1e300;
+        bool finite = true;
         for (int t = 0; t <= 256; ++t) {
             const double k = kmax * t / 256.0;
-            const double want = psi(k);
+            const double want = log_psi(k);
+            if (!std::isfinite(want)) {
+                finite = false;
+                break;
+            }
             const double got = cheb_eval(coef, 2.0 * (k / kmax) * (k / kmax) - 1.0);
-            if (!(want > 0.0)) break;
-            worst = std::max(worst, std::fabs(got - want) / want);
+            worst = std::max(worst, std::fabs(got - want));
             most = std::max(most, want);
         }
-        if (worst <= 1e-14) {
-            psi_max = most;
+        if (!finite) break;
+        if (worst <= 1e-13) {
+            psi_max = std::exp(most);
             return SBD_OK;
         }
     }
-    err = "the ES deconvolution series does not reach 1e-14";
+    err = "the ES deconvolution series does not reach 1e-13";
     return SBD_ENOTSUP;
 }
 
@@ -767,6 +774,8 @@ int nufft_params(const SbdFit& fit, double half_extent, double cx, double cy, do
         for (int c = 0; c < fit.n_circles; ++c) o.circle_factor[c] = knode * knode;
         o.kmax = S * o.h * (1.0 + 1e-12);
         int rc = es_deconv_series(Ps, o.beta_s, o.kmax, o.psi, o.psi_max, err);
+        if (rc && sigma_mode == 0 && sig != 2.0)
+            return nufft_params(fit, half_extent, cx, cy, tol, fp32, kwin, swin, 2, n_points, o, err);
         if (rc) return rc;
     } else {
         // c(|xi|) = knode h^2 exp(tau |xi|^2) / (4 pi tau), radial: one factor per circle

@@ -82,9 +82,10 @@ struct NufftParams {
     std::vector<double> circle_factor;   // c(|xi|)^2 per circle, c = h^2 deta^2 exp(tau |xi|^2) / (4 pi tau) [x Gaussian 1/(4 pi sigma)]
                                          // for the Gaussian spreading window; deta^4 [/(4 pi sigma)^2] for ES,
                                          // whose deconvolution is a per-node factor (psi below)
-    // ES spreading window: psi(k) = 1 / phi_hat_s(k), phi_hat_s(k) = sum over the window of
-    // exp(-i k d) (d in cells, k = xi h in [0, kmax], kmax = S h = pi / 2), as a Chebyshev series
-    // in 2 (k / kmax)^2 - 1; the node xi = (xi_x, xi_y) takes the factor psi(xi_x h) psi(xi_y h).
+    // ES spreading window: psi(k) = 1 / phi_hat_s(k), phi_hat_s(k) = integral over the window of
+    // exp(-i k d) (d in cells, k = xi h in [0, kmax], kmax = S h = pi / sigma_s); log psi as a
+    // Chebyshev series in 2 (k / kmax)^2 - 1; the node xi = (xi_x, xi_y) takes the factor
+    // psi(xi_x h) psi(xi_y h).
     std::vector<double> psi;
     double kmax = 0.0;
     double psi_max = 1.0;      // psi(kmax), the largest value of psi on [0, kmax]
