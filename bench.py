@@ -179,9 +179,14 @@ def stage_bytes(info, n, nrhs, form, esz=8):
     }
 
 
-def traffic_key(workload, alpha):
-    """Key of a workload's entries in the committed traffic table (delta_min by Theorem 1 at alpha)."""
-    return workload if not alpha else f"{workload}_alpha{alpha:g}"
+def traffic_key(args, alpha):
+    """Key of a workload's entries in the committed traffic table: the workload at its own size
+    and right-hand sides, delta_min by Theorem 1 at alpha (curve workloads)."""
+    n0, r0, _, _ = WORKLOADS[args.workload]
+    key = args.workload
+    if args.n != n0 or args.nrhs != r0:
+        key += f"_n{args.n}_rhs{args.nrhs}"
+    return key if not alpha else f"{key}_alpha{alpha:g}"
 
 
 def traffic_for(stage, workload, form):
@@ -360,7 +365,7 @@ def main():
     value = job_rate(args.n * nrhs, world, ms)
 
     # per-step device times on the same stream (library events), for the roofline
-    stages, roofline = stage_report(S, plan, step, ft, args, info, nrhs, esz, traffic_key(args.workload, args.alpha))
+    stages, roofline = stage_report(S, plan, step, ft, args, info, nrhs, esz, traffic_key(args, args.alpha))
 
     # delta_min by measurement (Theorem 1 leaves alpha in [0, 1/6] free): the same points, f,
     # eps and form, planned at the fastest alpha; reported beside the headline (alpha = 0)
@@ -386,7 +391,7 @@ def main():
         barrier()
         msb = max_over_ranks(e0b.elapsed_time(e1b) / args.steps, world, "cuda")
         stages_b, roof_b = stage_report(S, pb, step_b, ft, args, infob, nrhs, esz,
-                                        traffic_key(args.workload, alphas[ci]))
+                                        traffic_key(args, alphas[ci]))
         balanced = {"alpha": alphas[ci], "delta_min": infob["delta_min"], "a": infob["a"],
                     "value": job_rate(args.n * nrhs, world, msb), "unit": UNIT, "ms_per_step": msb,
                     "candidates": [{"alpha": a_, "ms": m_} for a_, m_ in zip(alphas, cand_ms)],

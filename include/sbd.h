@@ -384,7 +384,7 @@ int sbd_gmres(sbd_plan_t plan, const void* b, void* x, const sbd_gmres_options* 
  * host arrays of SBD_N_STAGES entries.  Not for concurrent use on one plan.
  * ------------------------------------------------------------------------------- */
 #define SBD_STAGE_SUM      0   /* sum_l f_l for the xi = 0 term */
-#define SBD_STAGE_SPREAD   1   /* Gaussian spreading of the points */
+#define SBD_STAGE_SPREAD   1   /* spreading of the points onto the grid */
 #define SBD_STAGE_FFT_FWD  2   /* precorrection + forward 2-D FFT */
 #define SBD_STAGE_NODE     3   /* node gather, omega_hat weighting, node scatter */
 #define SBD_STAGE_FFT_INV  4   /* inverse 2-D FFT + postcorrection */
