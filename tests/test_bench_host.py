@@ -1,0 +1,40 @@
+"""Host logic of bench.py (no GPU): algorithmic bytes per step and the keys of the committed
+ncu traffic table."""
+import argparse
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+
+INFO = {"grid_x": 1000, "grid_k": 1012, "n_xi": 50_000, "n_records": 25_000, "nnz": 2_000_000, "stencil_x": 8}
+
+
+def test_spmv_bytes_follow_the_stored_value_type():
+    n = 10_000
+    fp32 = bench.stage_bytes(INFO, n, 1, "fp32", esz=8)["spmv"]
+    fp64 = bench.stage_bytes(INFO, n, 1, "fp64", esz=8)["spmv"]
+    # column index 4 B + value 4 B (FP32 form) or 8 B (FP64 form) per non-zero
+    assert fp64 - fp32 == 4 * INFO["nnz"]
+    assert fp32 == 8 * INFO["nnz"] + 8 * (n + 1) + 2 * 8 * n
+    helm32 = bench.stage_bytes(INFO, n, 1, "fp32", esz=16)["spmv"]
+    assert helm32 == (4 + 8) * INFO["nnz"] + 8 * (n + 1) + 2 * 16 * n
+
+
+def test_laplace_steps_count_half_the_grid_and_records():
+    b = bench.stage_bytes(INFO, 10_000, 1, "fp32", esz=8)
+    m, nk = INFO["grid_x"], INFO["grid_k"]
+    assert b["node"] == 24 * INFO["n_records"] + 8 * nk * nk
+    assert b["fft_fwd"] == 8 * (m * m // 2 + nk * nk // 2)
+    assert b["spread"] == 16 * 10_000 + 8 * 10_000 + 8 * m * m // 2
+
+
+def test_traffic_keys_name_size_and_alpha():
+    a = argparse.Namespace(workload="laplace_curves", n=1_000_000, nrhs=1)
+    assert bench.traffic_key(a, 0.0) == "laplace_curves"
+    assert bench.traffic_key(a, 0.125) == "laplace_curves_alpha0.125"
+    a.n = 300_000
+    assert bench.traffic_key(a, 0.0) == "laplace_curves_n300000_rhs1"
+    assert bench.traffic_for("node", "no_such_workload", "fp32") is None
