@@ -1,6 +1,7 @@
 // Far part of the on-line SBD (Sec. 1 steps (i)-(iii), Eq. far convolution) by a
 // type-3 transform: points spread with a separable window (ES or Gaussian) onto a
-// two-fold oversampled grid, a zero-padded FFT, and a node window (ES or Gaussian).
+// grid oversampled 1.5- or 2-fold, a two-fold zero-padded FFT, and a node window (ES or
+// Gaussian).
 #pragma once
 #include <cuda_runtime.h>
 

@@ -60,7 +60,7 @@ int offline_fit(int kind, double kappa, double delta_min, double delta_max, doub
                 int fixed_P, SbdFit& out, std::string& err);
 
 // Parameters of the type-3 transform: spreading of the points with an ES (exponential of
-// semicircle) or Gaussian window on a two-fold oversampled spreading grid, a two-fold
+// semicircle) or Gaussian window on a spreading grid oversampled 1.5- or 2-fold, a two-fold
 // zero-padded FFT, and a node window that is ES or Gaussian.
 struct NufftParams {
     int Ps = 0, Pk = 0;        // stencil widths (cells per dimension, even)

@@ -1,5 +1,5 @@
 // Separable stencil windows of the type-3 transform.
-//   Gaussian        w(d) = exp(-beta d^2)                          (spreading side)
+//   Gaussian        w(d) = exp(-beta d^2)
 //   ES ("exponential of semicircle", Barnett-Magland-af Klinteberg 2019)
 //                   w(d) = exp(beta (sqrt(1 - (d / (P/2))^2) - 1)), |d| < P/2
 // d is the signed distance in cells between a stencil cell and the record position.
