@@ -257,6 +257,41 @@ int sbd_offline_fit(sbd_kernel kernel, double delta_min, double delta_max, doubl
                     int64_t* P_out, int64_t* n_circles_out, double* fit_err);
 
 /* ---------------------------------------------------------------------------------
+ * sbd_transform_params - the sizes sbd_plan would choose for the type-3 transforms of
+ * the far part (Sec. 1 steps (i)-(iii); Sec. 6.2), on the host, without a GPU: the fit
+ * (as sbd_offline_fit) and from it the per-transform tolerance, the spreading window,
+ * its oversampling and width, the spreading-grid, frequency-grid and FFT sizes.  For
+ * sizing device memory before planning, and for choosing options.
+ *   kernel, delta_min, delta_max, eps   as for sbd_offline_fit.
+ *   n_points     N (>= 1); feeds the automatic spreading oversampling.
+ *   half_extent  half the side of the points' bounding box (> 0): the larger of its
+ *                half width and half height, as sbd_plan measures it.
+ *   opt          NULL for defaults (form, flags, nufft_tol and fixed_P are used).
+ *   out          host, receives the sizes.
+ * SBD_EINVAL for a null out, n_points < 1, half_extent <= 0, delta_min outside
+ * (0, delta_max), eps outside [1e-10, 0.1], invalid options or kernel; SBD_EFIT when the
+ * fit cannot reach eps; SBD_ENOTSUP when the FFT length exceeds the row kernels' limit.
+ * ------------------------------------------------------------------------------- */
+typedef struct {
+    double  sigma_s;         /* oversampling of the spreading grid: 1.5 or 2 */
+    double  h;               /* spreading-grid spacing, pi / (sigma_s S), S the largest circle radius */
+    double  deta;            /* frequency-grid spacing, 2 pi / (fft_n h) */
+    double  nufft_tol;       /* tolerance of each type-3 transform */
+    int32_t grid_x;          /* side of the spreading grid (cells) */
+    int32_t grid_k;          /* side of the stored frequency grid (cells) */
+    int32_t fft_n;           /* FFT length per dimension (2 grid_x) */
+    int32_t stencil_x;       /* spreading stencil width (cells per dimension) */
+    int32_t stencil_k;       /* node stencil width */
+    int32_t spread_window;   /* 1 ES, 0 Gaussian */
+    int64_t P;               /* Bessel terms */
+    int64_t n_circles;       /* circles (P, plus one for Helmholtz) */
+    int64_t n_xi;            /* quadrature nodes */
+} sbd_transform_stats;
+int sbd_transform_params(sbd_kernel kernel, double delta_min, double delta_max, double eps,
+                         int64_t n_points, double half_extent, const sbd_options* opt,
+                         sbd_transform_stats* out);
+
+/* ---------------------------------------------------------------------------------
  * sbd_fft2 - the library's 2-D complex FFT on its own (the transform the far part
  * uses; exposed for testing): out[j0][j1] = sum_{k0,k1} in[k0][k1]
  * exp(sign * 2 pi i (j0 k0 / n0 + j1 k1 / n1)), unnormalised, row-major n0 x n1.

@@ -541,6 +541,37 @@ int check_plan_call(sbd_plan_t p, const void* a, const void* b) {
     return SBD_OK;
 }
 
+// Options that every entry point taking sbd_options accepts: a known form and flag set,
+// non-negative counts and tolerances.
+bool options_valid(const sbd_options& o) {
+    const int known = SBD_FLAG_GAUSSIAN_NODES | SBD_FLAG_GAUSSIAN_SPREAD | SBD_FLAG_SPREAD_SIGMA_2 |
+                      SBD_FLAG_SPREAD_SIGMA_15;
+    return (o.form == SBD_FORM_FP64 || o.form == SBD_FORM_FP32) && (o.flags & ~known) == 0 &&
+           !((o.flags & SBD_FLAG_SPREAD_SIGMA_2) && (o.flags & SBD_FLAG_SPREAD_SIGMA_15)) &&
+           !((o.flags & SBD_FLAG_GAUSSIAN_SPREAD) && (o.flags & SBD_FLAG_SPREAD_SIGMA_15)) && o.fixed_P >= 0 &&
+           o.max_nrhs >= 0 && o.nufft_tol >= 0 && o.delta_max >= 0 && o.host_threads >= 0;
+}
+
+// Transform parameters of a plan (sbd_plan and sbd_transform_params): each type-3 transform
+// gets eps / (6 sum_nu |omega_nu|) unless options.nufft_tol is given, with the windows and
+// spreading oversampling the flags select; half = half side of the points' bounding box.
+int plan_transform_params(const SbdFit& fit, const sbd_options& o, double eps, double half, double cx, double cy,
+                          long n, NufftParams& np, std::string& err) {
+    double W = 0.0;
+    for (int c = 0; c < fit.n_circles; ++c) W += fit.M[c] * std::abs(fit.weight[c]);
+    const double tol = o.nufft_tol > 0 ? o.nufft_tol : eps / (6.0 * std::max(W, 1e-300));
+    const int kwin = (o.flags & SBD_FLAG_GAUSSIAN_NODES) ? 0 : 1;
+    const int swin = (o.flags & SBD_FLAG_GAUSSIAN_SPREAD) ? 0 : 1;
+    const int sigma_mode = (o.flags & SBD_FLAG_SPREAD_SIGMA_15) ? 1 : (o.flags & SBD_FLAG_SPREAD_SIGMA_2) ? 2 : 0;
+    int rc = nufft_params(fit, half, cx, cy, tol, o.form == SBD_FORM_FP32, kwin, swin, sigma_mode, n, np, err);
+    if (rc) return rc;
+    if (np.n > fft_max_length(o.form == SBD_FORM_FP64)) {
+        err = "sbd_plan: FFT length " + std::to_string(np.n) + " exceeds the row kernel limit";
+        return SBD_ENOTSUP;
+    }
+    return SBD_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -587,6 +618,44 @@ int sbd_offline_fit(sbd_kernel kernel, double delta_min, double delta_max, doubl
     return SBD_OK;
 }
 
+int sbd_transform_params(sbd_kernel kernel, double delta_min, double delta_max, double eps, int64_t n_points,
+                         double half_extent, const sbd_options* opt, sbd_transform_stats* out) {
+    sbd_options o{};
+    o.form = SBD_FORM_FP64;
+    if (opt) o = *opt;
+    if (!out || n_points < 1 || !(half_extent > 0) || !(delta_min > 0) || !(delta_min < delta_max) ||
+        !(eps >= 1e-10 && eps <= 0.1) || !options_valid(o) ||
+        (kernel.kind != SBD_LAPLACE && kernel.kind != SBD_HELMHOLTZ) ||
+        (kernel.kind == SBD_HELMHOLTZ && !(kernel.kappa > 0))) {
+        set_error("sbd_transform_params: null output, n_points < 1, half_extent <= 0, delta_min outside "
+                  "(0, delta_max), eps outside [1e-10, 0.1], invalid options or kernel");
+        return SBD_EINVAL;
+    }
+    SbdFit fit;
+    NufftParams np;
+    std::string err;
+    int rc = offline_fit(kernel.kind, kernel.kappa, delta_min, delta_max, eps, o.fixed_P, fit, err);
+    if (!rc) rc = plan_transform_params(fit, o, eps, half_extent, 0.0, 0.0, static_cast<long>(n_points), np, err);
+    if (rc) {
+        set_error(err);
+        return rc;
+    }
+    out->sigma_s = np.sigma_s;
+    out->h = np.h;
+    out->deta = np.deta;
+    out->nufft_tol = np.tol;
+    out->grid_x = np.m;
+    out->grid_k = np.nk;
+    out->fft_n = np.n;
+    out->stencil_x = np.Ps;
+    out->stencil_k = np.Pk;
+    out->spread_window = np.swin;
+    out->P = fit.P;
+    out->n_circles = fit.n_circles;
+    out->n_xi = fit.n_xi;
+    return SBD_OK;
+}
+
 int sbd_fit_cache_stats(int64_t* hits, int64_t* misses, int64_t* entries) {
     long long h, m, e;
     fit_cache_stats(h, m, e);
@@ -624,16 +693,8 @@ int sbd_plan(const double* points, int64_t n, sbd_kernel kernel, double delta_mi
     sbd_options o{};
     o.form = SBD_FORM_FP64;
     if (opt) o = *opt;
-    if (o.form != SBD_FORM_FP64 && o.form != SBD_FORM_FP32) {
-        set_error("sbd_plan: unknown form");
-        return SBD_EINVAL;
-    }
-    if ((o.flags & ~(SBD_FLAG_GAUSSIAN_NODES | SBD_FLAG_GAUSSIAN_SPREAD | SBD_FLAG_SPREAD_SIGMA_2 |
-                     SBD_FLAG_SPREAD_SIGMA_15)) != 0 ||
-        ((o.flags & SBD_FLAG_SPREAD_SIGMA_2) && (o.flags & SBD_FLAG_SPREAD_SIGMA_15)) ||
-        ((o.flags & SBD_FLAG_GAUSSIAN_SPREAD) && (o.flags & SBD_FLAG_SPREAD_SIGMA_15)) || o.fixed_P < 0 || o.max_nrhs < 0 || o.nufft_tol < 0 ||
-        !(o.delta_max >= 0) || o.host_threads < 0) {
-        set_error("sbd_plan: invalid options");
+    if (!options_valid(o)) {
+        set_error("sbd_plan: invalid options (form, flags or a negative count or tolerance)");
         return SBD_EINVAL;
     }
     if (kernel.kind == SBD_HELMHOLTZ && !(kernel.kappa > 0)) {
@@ -701,21 +762,10 @@ int sbd_plan(const double* points, int64_t n, sbd_kernel kernel, double delta_mi
     }
     const SbdFit& fit = p->fit;
     p->w0 = fit.w0;
-    double W = 0.0;
-    for (int c = 0; c < fit.n_circles; ++c) W += fit.M[c] * std::abs(fit.weight[c]);
-    const double tol = o.nufft_tol > 0 ? o.nufft_tol : eps / (6.0 * std::max(W, 1e-300));
     const double half = std::max(std::max(bb[2] - cx, bb[3] - cy), 1e-300);
-    const int kwin = (o.flags & SBD_FLAG_GAUSSIAN_NODES) ? 0 : 1;
-    const int swin = (o.flags & SBD_FLAG_GAUSSIAN_SPREAD) ? 0 : 1;
-    const int sigma_mode = (o.flags & SBD_FLAG_SPREAD_SIGMA_15) ? 1 : (o.flags & SBD_FLAG_SPREAD_SIGMA_2) ? 2 : 0;
-    if ((rc = nufft_params(fit, half, cx, cy, tol, o.form == SBD_FORM_FP32, kwin, swin, sigma_mode, p->n, p->np,
-                           err))) {
+    if ((rc = plan_transform_params(fit, o, eps, half, cx, cy, p->n, p->np, err))) {
         set_error(err);
         return fail(rc);
-    }
-    if (p->np.n > fft_max_length(o.form == SBD_FORM_FP64)) {
-        set_error("sbd_plan: FFT length " + std::to_string(p->np.n) + " exceeds the row kernel limit");
-        return fail(SBD_ENOTSUP);
     }
     if ((rc = near_tables(fit, p->nt, err))) {
         set_error(err);

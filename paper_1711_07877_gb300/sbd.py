@@ -35,6 +35,17 @@ class sbd_options(ctypes.Structure):
                 ("host_threads", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
+class sbd_transform_stats(ctypes.Structure):
+    _fields_ = [("sigma_s", ctypes.c_double), ("h", ctypes.c_double), ("deta", ctypes.c_double),
+                ("nufft_tol", ctypes.c_double), ("grid_x", ctypes.c_int32), ("grid_k", ctypes.c_int32),
+                ("fft_n", ctypes.c_int32), ("stencil_x", ctypes.c_int32), ("stencil_k", ctypes.c_int32),
+                ("spread_window", ctypes.c_int32), ("P", ctypes.c_int64), ("n_circles", ctypes.c_int64),
+                ("n_xi", ctypes.c_int64)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class sbd_gmres_options(ctypes.Structure):
     _fields_ = [("shift_re", ctypes.c_double), ("shift_im", ctypes.c_double), ("scale_re", ctypes.c_double),
                 ("scale_im", ctypes.c_double), ("tol", ctypes.c_double), ("restart", ctypes.c_int32),
@@ -91,6 +102,8 @@ _SIGS = {
     "sbd_destroy": ([_P], ctypes.c_int),
     "sbd_destroy_async": ([_P, _P], ctypes.c_int),
     "sbd_offline_fit": ([sbd_kernel, _D, _D, _D, _I32, _I64, _P, _P, _P, _P, _P, _P], ctypes.c_int),
+    "sbd_transform_params": ([sbd_kernel, _D, _D, _D, _I64, _D, ctypes.POINTER(sbd_options),
+                              ctypes.POINTER(sbd_transform_stats)], ctypes.c_int),
     "sbd_fft2": ([_P, _P, _I32, _I32, _I32, _I32, _P], ctypes.c_int),
     "sbd_fft2_noalloc": ([_P, _P, _I32, _I32, _I32, _I32, _P], ctypes.c_int),
     "sbd_gmres": ([_P, _P, _P, ctypes.POINTER(sbd_gmres_options), ctypes.POINTER(_I32), ctypes.POINTER(_D), _P],
@@ -289,6 +302,16 @@ def sbd_offline_fit(kernel_kind: int, kappa: float, delta_min: float, delta_max:
     k = nc.value
     return {"P": P.value, "n_circles": k, "rho": rho[:k].copy(), "alpha": alpha[:k].copy(), "M": M[:k].copy(),
             "fit_err": err.value}
+
+
+def sbd_transform_params(kernel_kind: int, kappa: float, delta_min: float, delta_max: float, eps: float,
+                         n_points: int, half_extent: float, options: sbd_options | None = None) -> dict:
+    """Host only: the transform sizes sbd_plan would choose (no GPU needed)."""
+    out = sbd_transform_stats()
+    _check(lib.sbd_transform_params(sbd_kernel(kernel_kind, kappa), delta_min, delta_max, eps, n_points, half_extent,
+                                    ctypes.byref(options) if options is not None else None, ctypes.byref(out)),
+           "sbd_transform_params")
+    return out.as_dict()
 
 
 def sbd_fit_cache_stats() -> dict:
