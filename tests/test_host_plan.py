@@ -48,6 +48,18 @@ def test_argument_errors_without_gpu(S):
     with pytest.raises(S.SbdError) as e:
         S.sbd_gmres(0, 0, 0, stream=0)                              # null plan
     assert e.value.code == S.SBD_EINVAL
+    # the balanced planner checks its arguments before any device work (the points pointer is
+    # only tested for null here, so a host buffer stands in for it)
+    host = np.zeros((4, 2))
+    for alphas, nrhs, reps, eps in [([0.2], 1, 1, 1e-6), ([], 1, 1, 1e-6), ([-0.1], 1, 1, 1e-6),
+                                    ([0.0], 0, 1, 1e-6), ([0.0], 1, 0, 1e-6), ([0.0], 1, 1, 0.5),
+                                    ([0.0] * 17, 1, 1, 1e-6)]:
+        with pytest.raises(S.SbdError) as e:
+            S.sbd_plan_balanced(host, 4, S.SBD_LAPLACE, 0.0, eps, alphas, nrhs=nrhs, reps=reps, stream=0)
+        assert e.value.code == S.SBD_EINVAL
+    with pytest.raises(S.SbdError) as e:
+        S.sbd_plan_balanced(0, 4, S.SBD_LAPLACE, 0.0, 1e-6, [0.0], stream=0)   # null points
+    assert e.value.code == S.SBD_EINVAL
 
 
 @pytest.mark.parametrize("eps", [1e-3, 1e-6, 1e-9])
