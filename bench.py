@@ -5,7 +5,14 @@ Default workload: Laplace kernel, N = 10^6 points uniform in arc length on 8
 random star-shaped curves in [0, 10]^2, f ~ N(0, 1), eps = 1e-6, delta_min from
 Theorem 1 (alpha = 0), FP32 form (FP64 near field and accumulation).  One step =
 one sbd_matvec over the whole point set, inputs resident in HBM.  The grids
-(~0.8 GB each) and D (~2.6 GB) exceed the 129 MB L2, so no flush is needed.
+(~0.8 GB each) and D (~2.1 GB) exceed the 129 MB L2, so no flush is needed.
+
+The default line also carries (N = 1 only, after the headline's timed region):
+balanced_delta_min (delta_min by measurement), near_fp32 (the same plan with D f in
+float32), fp64_form (the same workload in the FP64 form), helmholtz (kappa delta_max
+= 500, FP32 and FP64 forms), served (a short serving run: p50/p99 latency with a
+queue / plan / solve breakdown), and cpu_baseline (the oracle's direct sum over all
+host cores, plus the oracle SBD timed on the N = 2000 disk).
 
   python bench.py [--gpus N --steps K --warmup W] [--form fp32|fp64] [--impl reference]
 
@@ -53,6 +60,9 @@ def parse():
     ap.add_argument("--cpu-targets", type=int, default=400, help="targets of the oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-balance", action="store_true", help="skip the delta_min balance (sbd_plan_balanced)")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the FP64-form, near-FP32, Helmholtz and serving keys of the default line")
+    ap.add_argument("--served-requests", type=int, default=64, help="requests of the serving key")
     return ap.parse_args()
 
 
@@ -146,16 +156,17 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def stage_bytes(info, n, nrhs, form, esz=8):
+def stage_bytes(info, n, nrhs, form, esz=8, near32=False):
     """Algorithmic bytes per launch of each on-line step (see the design notes).
     esz: bytes of one input/output value (8 real Laplace, 16 complex Helmholtz).
-    Laplace stores node records for half the nodes (the antipodes follow by symmetry)."""
+    Laplace stores node records for half the nodes (the antipodes follow by symmetry).
+    near32: D's values stored in float32 (SBD_FLAG_NEAR_FP32), else float64."""
     c = 8 if form == "fp32" else 16          # complex grid element
     pr = 16 if form == "fp32" else 24        # point record: int2 cell + fractions
     nr = 24 if form == "fp32" else 32        # node record
     m, nk, nxi, nnz, P = info["grid_x"], info["grid_k"], info["n_xi"], info["nnz"], info["stencil_x"]
     touched = min(m * m, n * P * P)
-    vb = (16 if esz == 16 else 8) // (2 if form == "fp32" else 1)   # D value: complex for Helmholtz, FP32 form in float32
+    vb = (16 if esz == 16 else 8) // (2 if near32 else 1)   # D value: complex for Helmholtz, float32 with the flag
     if esz == 8:
         # Laplace: real spreading grid (half a complex element per cell), Hermitian K of
         # which the half plane kx >= 0 is transformed, half the node records
@@ -209,43 +220,109 @@ def traffic_for(stage, workload, form):
         return None
 
 
-def cpu_baseline(z, f, targets_idx, kind="laplace", kappa=0.0):
-    """Time the oracle's direct sum on a sample of targets (host cores); return (rate info, q)."""
+_THREAD_VARS = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
+_ORACLE_DATA = None
+
+
+def _oracle_init(z, f, kind, kappa):
+    global _ORACLE_DATA
+    _ORACLE_DATA = (z, f, kind, kappa)
+
+
+def _oracle_direct(idx):
     from oracle import sbd_oracle as O
-    t0 = time.perf_counter()
-    q = O.direct_sum(z, f, kind, kappa, targets=targets_idx, chunk=16)
-    dt = time.perf_counter() - t0
-    nrhs = 1 if np.ndim(f) == 1 else f.shape[0]
-    pairs = len(targets_idx) * len(z) * nrhs
+    z, f, kind, kappa = _ORACLE_DATA
+    return O.direct_sum(z, f, kind, kappa, targets=idx, chunk=16)
+
+
+class OraclePool:
+    """The oracle's direct sum over the host cores: one spawned worker process per core (single-
+    threaded numpy each), every worker holding the points and f, targets split evenly."""
+
+    def __init__(self, z, f, kind="laplace", kappa=0.0, cores=None):
+        import multiprocessing as mp
+        self.cores = max(1, cores or os.cpu_count() or 1)
+        saved = {k: os.environ.get(k) for k in _THREAD_VARS}
+        for k in _THREAD_VARS:
+            os.environ[k] = "1"
+        try:
+            self.pool = mp.get_context("spawn").Pool(self.cores, initializer=_oracle_init,
+                                                      initargs=(z, f, kind, kappa))
+        finally:
+            for k, v in saved.items():
+                if v is None:
+                    os.environ.pop(k, None)
+                else:
+                    os.environ[k] = v
+        self.n = len(z)
+        self.nrhs = 1 if np.ndim(f) == 1 else f.shape[0]
+        self.pool.map(_oracle_direct, [np.array([i]) for i in range(self.cores)], chunksize=1)   # warm
+
+    def direct_sum(self, idx):
+        """(q at the targets, seconds, workers used)."""
+        parts = [c for c in np.array_split(np.asarray(idx), min(self.cores, len(idx))) if len(c)]
+        t0 = time.perf_counter()
+        out = self.pool.map(_oracle_direct, parts, chunksize=1)
+        dt = time.perf_counter() - t0
+        return np.concatenate(out, axis=-1), dt, len(parts)
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+
+
+def cpu_baseline(pool, targets_idx):
+    """Time the oracle's direct sum on a sample of targets over the host cores; return (rate info, q)."""
+    q, dt, used = pool.direct_sum(targets_idx)
+    pairs = len(targets_idx) * pool.n * pool.nrhs
     # a full matvec needs N^2 pair evaluations: Gpts/s = N / (N^2 / pair rate)
-    value = (pairs / dt) / len(z) / 1e9
-    return {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"direct sum (Eq. discreteConv) at {len(targets_idx)} sampled targets over all {len(z)} "
-                      f"sources x {nrhs} rhs in {dt:.2f} s; value = pair rate / N (extrapolated to a full matvec)"}, q
+    value = (pairs / dt) / pool.n / 1e9
+    return {"value": value, "unit": UNIT, "cores": used, "kind": "oracle",
+            "sample": f"direct sum (Eq. discreteConv) at {len(targets_idx)} sampled targets over all {pool.n} "
+                      f"sources x {pool.nrhs} rhs in {dt:.2f} s on {used} worker processes (one per host core, "
+                      f"os.cpu_count() = {os.cpu_count()}); value = pair rate / N (extrapolated to a full matvec)"}, q
 
 
-def stage_report(S, plan, step, f_dev, args, info, nrhs, esz, workload_key):
-    """Per-step device times of `args.steps` matvecs (library events on the launching stream),
+def oracle_sbd_timing(n=2000, seed=1, eps=1e-6):
+    """The oracle SBD (plain SBD: direct exponential sums, brute-force near pairs) on the
+    N = 2000 disk workload, timed whole on one core: plan (fit, circles, D) and one matvec."""
+    import workloads as W
+    from oracle import sbd_oracle as O
+    wl = W.laplace_disk(n, seed, eps)
+    t0 = time.perf_counter()
+    pl = O.make_plan(wl.z, "laplace", wl.delta_min, wl.eps)
+    pl.D = O.close_matrix(pl)
+    t1 = time.perf_counter()
+    O.sbd_matvec(pl, wl.f)
+    t2 = time.perf_counter()
+    return {"workload": f"laplace_disk N={n} eps={eps:g}", "cores": 1, "plan_s": t1 - t0, "matvec_s": t2 - t1,
+            "value": n / (t2 - t1) / 1e9, "unit": UNIT, "P": int(pl.P), "n_xi": int(len(pl.xi))}
+
+
+def stage_report(S, plan, step, f_dev, args, info, nrhs, esz, workload_key, form=None, near32=False, steps=None):
+    """Per-step device times of `steps` matvecs (library events on the launching stream),
     algorithmic bytes per step and the roofline entry of the step that takes longest."""
     import torch
+    form = form or args.form
+    steps = steps or args.steps
     S.sbd_profile(plan, True)
-    for _ in range(args.steps):
+    for _ in range(steps):
         step(f_dev)
     torch.cuda.synchronize()
     prof = S.sbd_profile_read(plan)
     S.sbd_profile(plan, False)
-    sb = stage_bytes(info, args.n, nrhs, args.form, esz)
+    sb = stage_bytes(info, args.n, nrhs, form, esz, near32)
     hbm, peak_src = measured_peaks()
     stages = {}
     for st, (tot, cnt) in prof.items():
         if cnt:
             avg = tot / cnt
-            stages[st] = {"ms": avg, "launches_per_step": cnt // args.steps, "algorithmic_bytes": sb[st],
+            stages[st] = {"ms": avg, "launches_per_step": cnt // steps, "algorithmic_bytes": sb[st],
                           "GBps": sb[st] / (avg * 1e-3) / 1e9}
     dom = max(stages, key=lambda s_: stages[s_]["ms"] * stages[s_]["launches_per_step"])
     achieved = stages[dom]["GBps"]
     roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                "frac": achieved / hbm, "traffic": traffic_for(dom, workload_key, args.form),
+                "frac": achieved / hbm, "traffic": traffic_for(dom, workload_key, form),
                 "peak_source": f"{peak_src} (hbm_gbs)"}
     return stages, roofline
 
@@ -269,30 +346,81 @@ def job_rate(units_per_rank, world, ms):
 def run_reference(args, rank, world):
     if rank != 0:
         return
-    if args.workload == "serve":
-        print(json.dumps({"impl": "reference", "unavailable": "the oracle has no solve server; the serving "
-                                                              "line is compared against matvec lines instead"}))
+    if args.workload in ("serve", "batch"):
+        print(json.dumps({"impl": "reference", "unavailable": "the oracle has no solve server or batch runner; "
+                                                              "those lines are compared against matvec lines"}))
         return
     wl = make_workload(args, 0)
+    pool = OraclePool(wl.z, wl.f, wl.kernel, wl.kappa)
     rng = np.random.default_rng(123)
-    times = []
+    k = max(4 * pool.cores, args.cpu_targets // max(args.steps, 1) // args.nrhs)
     for _ in range(args.warmup):
-        cpu_baseline(wl.z, wl.f, rng.choice(args.n, 4, replace=False), wl.kernel, wl.kappa)
-    k = max(4, args.cpu_targets // max(args.steps, 1) // args.nrhs)
+        cpu_baseline(pool, rng.choice(args.n, pool.cores, replace=False))
+    times, used = [], pool.cores
     for _ in range(args.steps):
-        idx = rng.choice(args.n, k, replace=False)
-        info, _ = cpu_baseline(wl.z, wl.f, idx, wl.kernel, wl.kappa)
+        info, _ = cpu_baseline(pool, rng.choice(args.n, k, replace=False))
         times.append(info["value"])
+        used = info["cores"]
+    pool.close()
     value = statistics.median(times)
     ms = args.n * args.nrhs / (value * 1e9) * 1e3
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic", "config": workload_config(args, 0),
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": used, "kind": "oracle",
                          "sample": f"direct sum at {k} sampled targets per step over all {args.n} sources "
-                                   f"x {args.nrhs} rhs"},
+                                   f"x {args.nrhs} rhs, targets split over {used} worker processes; "
+                                   f"ms_per_step extrapolates the pair rate to a full N x N matvec"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+
+
+def accuracy(q, qref, f, idx):
+    """Errors at the sampled targets against the oracle's direct sum: rel-L2 and max / sum|f|."""
+    qs = q[..., idx]
+    f_abs = np.abs(f).sum(axis=-1, keepdims=True) if np.ndim(f) > 1 else np.abs(f).sum()
+    return {"targets": len(idx), "reference": "oracle direct sum (FP64)",
+            "rel_l2_vs_direct_sum": float(np.linalg.norm(qs - qref) / np.linalg.norm(qref)),
+            "max_err_over_sum_abs_f": float(np.max(np.abs(qs - qref) / f_abs))}
+
+
+class Runner:
+    """One plan of a workload on the device: planned, tuned, warmed up and timed with CUDA events
+    on the launching stream (the same protocol as the headline)."""
+
+    def __init__(self, S, torch, stream, zt, ft, wl, form, nrhs, flags=0, tune=True):
+        self.S, self.torch, self.stream, self.ft, self.nrhs = S, torch, stream, ft, nrhs
+        kind = S.SBD_HELMHOLTZ if wl.kernel == "helmholtz" else S.SBD_LAPLACE
+        self.plan = S.sbd_plan(zt, len(wl.z), kind, wl.kappa, wl.delta_min, wl.eps,
+                               S.make_options(form=form, max_nrhs=nrhs, flags=flags))
+        self.tune_ms = S.sbd_tune(self.plan, 3, stream.cuda_stream) if tune else None
+        self.info = S.sbd_plan_info(self.plan)
+        self.q = torch.empty_like(ft)
+
+    def step(self, f_in):
+        self.S.sbd_matvec(self.plan, f_in, self.q, self.nrhs, self.stream.cuda_stream)
+
+    def time(self, steps, warmup):
+        torch = self.torch
+        for _ in range(warmup):
+            self.step(self.ft)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(self.stream)
+        for _ in range(steps):
+            self.step(self.ft)
+        e1.record(self.stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps
+
+    def close(self):
+        self.S.sbd_destroy(self.plan)
+        self.q = None
+
+
+def plan_keys(info):
+    return {k: info[k] for k in ("P", "n_xi", "nnz", "grid_x", "grid_k", "fft_n", "fit_err", "device_bytes",
+                                 "plan_seconds")}
 
 
 def main():
@@ -304,12 +432,13 @@ def main():
         run_reference(args, rank, world)
         return
     if args.workload == "serve":
-        run_serve(args, rank, world, local)
+        out = run_serve(args, rank, world, local)
+        if rank == 0:
+            print(json.dumps(out))
         return
     if args.workload == "batch":
         run_batch(args, rank, world, local)
         return
-    import numpy as np
     import torch
     import torch.distributed as dist
 
@@ -325,22 +454,16 @@ def main():
     form = S.SBD_FORM_FP32 if args.form == "fp32" else S.SBD_FORM_FP64
     zt = torch.from_numpy(wl.z).cuda()
     ft = torch.from_numpy(np.ascontiguousarray(wl.f)).cuda()
-    qt = torch.empty_like(ft)
     stream = torch.cuda.current_stream()
-    plan = S.sbd_plan(zt, args.n, S.SBD_HELMHOLTZ if helm else S.SBD_LAPLACE, wl.kappa, wl.delta_min, wl.eps,
-                      S.make_options(form=form, max_nrhs=nrhs))
     t_tune = time.perf_counter()
-    tune_ms = S.sbd_tune(plan, 3, stream.cuda_stream)
-    t_tune = time.perf_counter() - t_tune
-    info = S.sbd_plan_info(plan)
+    head = Runner(S, torch, stream, zt, ft, wl, form, nrhs)
+    t_tune = time.perf_counter() - t_tune - head.info["plan_seconds"]
+    plan, qt, info, step = head.plan, head.q, head.info, head.step
 
     def barrier():
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize()
-
-    def step(f_in):
-        S.sbd_matvec(plan, f_in, qt, nrhs, stream.cuda_stream)
 
     for _ in range(args.warmup):
         step(ft)
@@ -395,9 +518,7 @@ def main():
         balanced = {"alpha": alphas[ci], "delta_min": infob["delta_min"], "a": infob["a"],
                     "value": job_rate(args.n * nrhs, world, msb), "unit": UNIT, "ms_per_step": msb,
                     "candidates": [{"alpha": a_, "ms": m_} for a_, m_ in zip(alphas, cand_ms)],
-                    "roofline": roof_b, "stages": stages_b,
-                    "plan": {k: infob[k] for k in ("P", "n_xi", "nnz", "grid_x", "grid_k", "fft_n", "fit_err",
-                                                    "device_bytes", "plan_seconds")},
+                    "roofline": roof_b, "stages": stages_b, "plan": plan_keys(infob),
                     "note": "delta_min = a delta_max, a = |log eps|^(2/3) / N^(2/3 - alpha) (Theorem 1) at the "
                             "fastest alpha of the candidates (sbd_plan_balanced: each planned, tuned and timed); "
                             "same points, f, eps and form as the headline line, which keeps alpha = 0"}
@@ -465,28 +586,108 @@ def main():
            "plan": dict({k: info[k] for k in ("P", "n_xi", "n_records", "nnz", "grid_x", "grid_k", "fft_n",
                                               "stencil_x", "stencil_k", "nufft_tol", "fit_err", "device_bytes",
                                               "plan_seconds", "node_acc", "node_sched")},
-                        tune_seconds=t_tune, tune_node_ms=tune_ms)}
+                        tune_seconds=t_tune, tune_node_ms=head.tune_ms)}
+    q_head = qt.cpu().numpy()
+    head.close()
+    extra = rank == 0 and world == 1 and not args.no_extras
+    pool, idx, qref = None, None, None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        qd = qt.cpu().numpy()
+        pool = OraclePool(wl.z, wl.f, wl.kernel, wl.kappa)
         targets = args.cpu_targets if args.n * nrhs <= 2_000_000 else max(8, args.cpu_targets // 20)
         idx = np.random.default_rng(7).choice(args.n, targets, replace=False)
-        cb, qref = cpu_baseline(wl.z, wl.f, idx, wl.kernel, wl.kappa)
+        cb, qref = cpu_baseline(pool, idx)
+        if extra:
+            cb["oracle_sbd"] = oracle_sbd_timing()
         out["cpu_baseline"] = cb
-        qs = qd[..., idx]
-        f_abs = np.abs(wl.f).sum(axis=-1, keepdims=True) if nrhs > 1 else np.abs(wl.f).sum()
-        out["accuracy"] = {"targets": len(idx), "reference": "oracle direct sum (FP64)",
-                           "rel_l2_vs_direct_sum": float(np.linalg.norm(qs - qref) / np.linalg.norm(qref)),
-                           "max_err_over_sum_abs_f": float(np.max(np.abs(qs - qref) / f_abs))}
+        out["accuracy"] = accuracy(q_head, qref, wl.f, idx)
         if balanced is not None:
-            qbs = q_bal[..., idx]
-            balanced["accuracy"] = {"targets": len(idx), "reference": "oracle direct sum (FP64)",
-                                    "rel_l2_vs_direct_sum": float(np.linalg.norm(qbs - qref) / np.linalg.norm(qref)),
-                                    "max_err_over_sum_abs_f": float(np.max(np.abs(qbs - qref) / f_abs))}
-    S.sbd_destroy(plan)
+            balanced["accuracy"] = accuracy(q_bal, qref, wl.f, idx)
+    if extra and args.workload == "laplace_curves":
+        out["near_fp32"] = near_fp32_line(S, torch, stream, zt, ft, wl, args, nrhs, esz, stages, pool, idx, qref)
+        out["fp64_form"] = form_line(S, torch, stream, zt, ft, wl, args, nrhs, esz, S.SBD_FORM_FP64, pool, idx,
+                                     qref, value)
+    if pool is not None:
+        pool.close()
+    del zt, ft
+    torch.cuda.empty_cache()
+    if extra and args.workload == "laplace_curves":
+        out["helmholtz"] = helmholtz_lines(S, torch, stream, args)
+        out["served"] = run_serve(args, rank, world, local, requests=args.served_requests, short=True)
     if rank == 0:
         print(json.dumps(out))
     if world > 1:
         dist.destroy_process_group()
+
+
+def near_fp32_line(S, torch, stream, zt, ft, wl, args, nrhs, esz, stages, pool, idx, qref):
+    """The headline plan with SBD_FLAG_NEAR_FP32: D f in float32 beside the default float64 D f."""
+    r = Runner(S, torch, stream, zt, ft, wl, S.SBD_FORM_FP32, nrhs, flags=S.SBD_FLAG_NEAR_FP32)
+    try:
+        ms = r.time(min(args.steps, 10), 2)
+        st, _ = stage_report(S, r.plan, r.step, ft, args, r.info, nrhs, esz, "none", form="fp32", near32=True,
+                             steps=3)
+        line = {"flags": "SBD_FLAG_NEAR_FP32", "ms_per_step": ms, "value": args.n * nrhs / (ms * 1e-3) / 1e9,
+                "unit": UNIT, "spmv_ms": st["spmv"]["ms"], "spmv_GBps": st["spmv"]["GBps"],
+                "spmv_ms_fp64_near": stages["spmv"]["ms"], "spmv_GBps_fp64_near": stages["spmv"]["GBps"],
+                "note": "D rounded to float32 and applied to float32 f (row partials in float64) against the "
+                        "default float64 D f of the headline"}
+        if pool is not None:
+            line["accuracy"] = accuracy(r.q.cpu().numpy(), qref, wl.f, idx)
+        return line
+    finally:
+        r.close()
+
+
+def form_line(S, torch, stream, zt, ft, wl, args, nrhs, esz, form, pool, idx, qref, fp32_value):
+    """The same workload in the FP64 form (spread, FFT, node step and interpolation in float64)."""
+    r = Runner(S, torch, stream, zt, ft, wl, form, nrhs)
+    try:
+        ms = r.time(min(args.steps, 5), 2)
+        st, roof = stage_report(S, r.plan, r.step, ft, args, r.info, nrhs, esz, "none", form="fp64", steps=2)
+        value = args.n * nrhs / (ms * 1e-3) / 1e9
+        line = {"form": "fp64", "dtype": "f64", "ms_per_step": ms, "value": value, "unit": UNIT,
+                "fp32_over_fp64": fp32_value / value, "stages": st, "roofline": roof, "plan": plan_keys(r.info)}
+        if pool is not None:
+            line["accuracy"] = accuracy(r.q.cpu().numpy(), qref, wl.f, idx)
+        return line
+    finally:
+        r.close()
+
+
+def helmholtz_lines(S, torch, stream, args):
+    """Helmholtz, kappa delta_max = 500, N = 10^6 on the curves (eps = 1e-6): FP32 and FP64 forms,
+    errors against the oracle's direct sum at sampled targets (over the host cores)."""
+    import workloads as W
+    wl = W.helmholtz_curves(args.n, 3, args.eps)
+    zt = torch.from_numpy(wl.z).cuda()
+    ft = torch.from_numpy(np.ascontiguousarray(wl.f)).cuda()
+    out = {"workload": f"helmholtz_curves N={args.n} nrhs=1 eps={args.eps:g} (kappa delta_max = 500, complex f, "
+                       "delta_min by Theorem 1 alpha=0)"}
+    qs = {}
+    for name, form in (("fp32", S.SBD_FORM_FP32), ("fp64", S.SBD_FORM_FP64)):
+        r = Runner(S, torch, stream, zt, ft, wl, form, 1)
+        try:
+            ms = r.time(min(args.steps, 10 if name == "fp32" else 4), 2)
+            st, roof = stage_report(S, r.plan, r.step, ft, args, r.info, 1, 16, "none", form=name, steps=2)
+            out[name] = {"ms_per_step": ms, "value": args.n / (ms * 1e-3) / 1e9, "unit": UNIT, "stages": st,
+                         "roofline": roof, "plan": plan_keys(r.info)}
+            qs[name] = r.q.cpu().numpy()
+        finally:
+            r.close()
+    out["fp32_over_fp64"] = out["fp32"]["value"] / out["fp64"]["value"]
+    if not args.no_cpu_baseline:
+        idx = np.random.default_rng(8).choice(args.n, 64, replace=False)
+        pool = OraclePool(wl.z, wl.f, "helmholtz", wl.kappa)
+        try:
+            qref, dt, used = pool.direct_sum(idx)
+        finally:
+            pool.close()
+        for name in qs:
+            out[name]["accuracy"] = accuracy(qs[name], qref, wl.f, idx)
+        out["oracle_seconds"] = dt
+    del zt, ft
+    torch.cuda.empty_cache()
+    return out
 
 
 def run_batch(args, rank, world, local):
@@ -571,9 +772,10 @@ def run_batch(args, rank, world, local):
         print(json.dumps(out))
 
 
-def run_serve(args, rank, world, local):
-    """Continuous-batching solve server over a Poisson stream of GMRES requests."""
-    import numpy as np
+def run_serve(args, rank, world, local, requests=None, short=False):
+    """Continuous-batching solve server over a Poisson stream of GMRES requests; returns the line
+    (or, with short, the key the default line carries) with p50/p99 latency and a per-request
+    breakdown into queueing (arrival to admission), planning and solving."""
     import torch
 
     import paper_1711_07877_gb300 as S
@@ -581,7 +783,8 @@ def run_serve(args, rank, world, local):
     import workloads as W
 
     torch.cuda.set_device(local)
-    specs = W.serve_requests(args.requests, seed=5 + rank, eps=args.eps)
+    count = requests or args.requests
+    specs = W.serve_requests(count, seed=5 + rank, eps=args.eps)
     form = S.SBD_FORM_FP32 if args.form == "fp32" else S.SBD_FORM_FP64
     reqs = [serve.Request(rid=i, z=r["z"], b=r["b"],
                           kind=S.SBD_HELMHOLTZ if r["kernel"] == "helmholtz" else S.SBD_LAPLACE,
@@ -611,29 +814,39 @@ def run_serve(args, rank, world, local):
     cache = S.sbd_fit_cache_stats()
     h2d = sum(r.z.nbytes + r.b.nbytes for r in ok)
     d2h = sum(r.b.nbytes for r in ok)
-    out = {"metric": METRIC, "value": summ["gpts_per_s"], "unit": UNIT, "n_gpus": world,
-           "steps": len(reqs), "warmup": len(warm), "ms_per_step": summ["wall_s"] * 1e3 / max(len(reqs), 1),
-           "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-           "dtype": "f32" if args.form == "fp32" else "f64", "data": "synthetic",
-           "config": {"workload": f"serve {len(reqs)} GMRES requests, Poisson arrivals mean 2 ms, curve geometries "
-                                  "N log-uniform [1e3, 1e6], 50/50 Laplace/Helmholtz kappa*delta_max U[50, 500], "
-                                  "(I/2 + (L/N) A) x = b (L = arc length) to relative residual 1e-6, GMRES(30)",
-                      "slots": args.slots, "eps": args.eps, "form": args.form, "l2_policy": "n/a (serving)"},
-           "latency": {"p50_ms": summ.get("p50_ms"), "p99_ms": summ.get("p99_ms"), "mean_ms": summ.get("mean_ms")},
-           "served": {"requests_ok": len(ok), "errors": len(reqs) - len(ok), "incomplete": summ.get("incomplete"),
-                      "wall_s": summ.get("wall_s"),
-                      "matvecs_mean": float(np.mean(its)) if its else None,
-                      "matvecs_max": int(max(its)) if its else None,
-                      "points_mean": float(np.mean([len(r.z) for r in ok])) if ok else None,
-                      "plan_s_p50": float(np.median(plan_s)) if plan_s else None,
-                      "max_residual": float(max(r.residual for r in ok)) if ok else None,
-                      "fit_cache": cache},
-           "e2e": {"value": summ["gpts_per_s"], "unit": UNIT, "h2d_bytes_per_step": h2d // max(len(ok), 1),
-                   "d2h_bytes_per_step": d2h // max(len(ok), 1),
-                   "note": "each request copies points and b from host and reads x back"},
-           "clocks": clk, "roofline": None, "gpu_launches": None}
-    if rank == 0:
-        print(json.dumps(out))
+
+    def pct(xs):
+        return {"p50_ms": float(np.percentile(xs, 50) * 1e3), "p99_ms": float(np.percentile(xs, 99) * 1e3),
+                "mean_ms": float(np.mean(xs) * 1e3)} if xs else None
+    breakdown = {"queue": pct([r.start - r.arrival for r in ok]), "plan": pct(plan_s),
+                 "solve": pct([r.done - r.start - r.plan_seconds for r in ok]),
+                 "note": "queue = arrival to admission, plan = sbd_plan, solve = the rest of the request "
+                         "(GMRES, copies); arrivals of all requests span ~2 ms x count"}
+    workload = (f"serve {len(reqs)} GMRES requests, Poisson arrivals mean 2 ms, curve geometries "
+                "N log-uniform [1e3, 1e6], 50/50 Laplace/Helmholtz kappa*delta_max U[50, 500], "
+                "(I/2 + (L/N) A) x = b (L = arc length) to relative residual 1e-6, GMRES(30)")
+    served = {"requests_ok": len(ok), "errors": len(reqs) - len(ok), "incomplete": summ.get("incomplete"),
+              "wall_s": summ.get("wall_s"),
+              "matvecs_mean": float(np.mean(its)) if its else None,
+              "matvecs_max": int(max(its)) if its else None,
+              "points_mean": float(np.mean([len(r.z) for r in ok])) if ok else None,
+              "max_residual": float(max(r.residual for r in ok)) if ok else None,
+              "fit_cache": cache, "breakdown": breakdown}
+    latency = {"p50_ms": summ.get("p50_ms"), "p99_ms": summ.get("p99_ms"), "mean_ms": summ.get("mean_ms")}
+    if short:
+        return {"workload": workload, "slots": args.slots, "form": args.form, "value": summ.get("gpts_per_s"),
+                "unit": UNIT, "latency": latency, "served": served, "clocks": clk}
+    return {"metric": METRIC, "value": summ["gpts_per_s"], "unit": UNIT, "n_gpus": world,
+            "steps": len(reqs), "warmup": len(warm), "ms_per_step": summ["wall_s"] * 1e3 / max(len(reqs), 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if args.form == "fp32" else "f64", "data": "synthetic",
+            "config": {"workload": workload, "slots": args.slots, "eps": args.eps, "form": args.form,
+                       "l2_policy": "n/a (serving)"},
+            "latency": latency, "served": served,
+            "e2e": {"value": summ["gpts_per_s"], "unit": UNIT, "h2d_bytes_per_step": h2d // max(len(ok), 1),
+                    "d2h_bytes_per_step": d2h // max(len(ok), 1),
+                    "note": "each request copies points and b from host and reads x back"},
+            "clocks": clk, "roofline": None, "gpu_launches": None}
 
 
 if __name__ == "__main__":

@@ -62,11 +62,14 @@ typedef struct {
 } sbd_kernel;
 
 /* Arithmetic of the on-line part.  FP64: spread, FFT, node step and interpolation in
- * float64, D (computed in float64) stored and applied in float64.  FP32: those steps
- * in float32 (coordinates split as an integer cell plus a float32 fraction computed
- * in float64), D rounded to float32 once built and applied to f rounded to float32
- * (products and per-thread partial sums in float32, the partials of a row added in
- * float64); the xi = 0 term and the final accumulation stay in float64 in both forms. */
+ * float64.  FP32: those steps in float32 (coordinates split as an integer cell plus a
+ * float32 fraction computed in float64).  In both forms the close correction D (computed
+ * in float64, where G - G_approx cancels) is stored and applied in float64 (float64 f,
+ * products and row sums), and the xi = 0 term and the final accumulation are float64.
+ * SBD_FLAG_NEAR_FP32 (FP32 form only) instead rounds D to float32 once built and applies
+ * it to f rounded to float32: products and per-lane partial sums in float32, the partials
+ * of a row added in float64 (half the bytes of D and no FP64 products, at an error of
+ * float32 rounding on the near term). */
 typedef enum { SBD_FORM_FP64 = 0, SBD_FORM_FP32 = 1 } sbd_form;
 
 typedef struct {
@@ -100,6 +103,8 @@ typedef struct {
  * SBD_EINVAL. */
 #define SBD_FLAG_SPREAD_SIGMA_2 4
 #define SBD_FLAG_SPREAD_SIGMA_15 8
+/* Close correction D f in float32 (see sbd_form); with SBD_FORM_FP64 it is SBD_EINVAL. */
+#define SBD_FLAG_NEAR_FP32 16
 
 /* Plan summary (sbd_plan_info). */
 typedef struct {
@@ -156,7 +161,8 @@ int sbd_plan(const double* points, int64_t n, sbd_kernel kernel, double delta_mi
  * q = NUFFT_+(omega_hat . NUFFT_-(f)) + D f for nrhs right-hand sides.
  *   f, q   device, nrhs x N (float64 for Laplace, complex128 for Helmholtz);
  *          q is overwritten, f is read only; f and q must not overlap.
- *   nrhs   1 <= nrhs <= max_nrhs of the plan's options.
+ *   nrhs   1 <= nrhs <= max_nrhs of the plan's options.  Every step takes all nrhs
+ *          right-hand sides in one launch (the plan's grids hold max_nrhs of each).
  * Asynchronous on cuda_stream.  The plan's workspace is shared: calls on the same
  * plan must be ordered (one stream, or events); different plans run concurrently.
  * D is held over the plan's internal point order (the spatial order of its spreading
@@ -168,7 +174,7 @@ int sbd_plan(const double* points, int64_t n, sbd_kernel kernel, double delta_mi
 int sbd_matvec(sbd_plan_t plan, const void* f, void* q, int32_t nrhs, void* cuda_stream);
 
 /* sbd_matvec_graph - sbd_matvec replayed from a CUDA graph (no counterpart in the paper):
- * the per-kernel launch cost (2 + 9 nrhs kernels per call) matters for small N.  The first
+ * the per-kernel launch cost (12 kernels per call, whatever nrhs) matters for small N.  The first
  * call for a given nrhs runs one matvec on plan-owned buffers and captures a second one
  * into a graph; every call then copies f into the plan's input buffer, launches the graph
  * and copies the plan's output buffer to q, on a plan-owned stream ordered after and before
@@ -229,9 +235,9 @@ int sbd_plan_export(sbd_plan_t plan, int64_t cap, double* rho, double* alpha, in
                     double* radius, double* weight_re, double* weight_im);
 
 /* Copy D (Eq. defD) to host CSR arrays: rowptr (N + 1), col (nnz), val (nnz float64
- * for Laplace, 2 nnz float64 = complex128 for Helmholtz; an FP32-form plan's values
- * are the float32 ones it stores, widened).  Column order within a row is
- * unspecified.  Synchronous. */
+ * for Laplace, 2 nnz float64 = complex128 for Helmholtz; a plan made with
+ * SBD_FLAG_NEAR_FP32 gives the float32 values it stores, widened).  Rows are in the
+ * caller's point order, each row's diagonal first, then by column.  Synchronous. */
 int sbd_close_export(sbd_plan_t plan, int64_t* rowptr, int32_t* col, double* val);
 
 /* Release the plan (NULL is accepted).  sbd_destroy first waits for the whole device, so
@@ -446,9 +452,13 @@ int sbd_profile_read(sbd_plan_t plan, double* ms, int64_t* count);
  *   return SBD_EINVAL with the limits in sbd_last_error_message().
  * The first call on a device looks up the array's device address (cudaGetSymbolAddress,
  * once per device, with that device current); make that first call before any stream
- * capture.  All calls share the one array and its contents persist between calls, so
- * calls that overlap on the GPU (different streams without ordering) race; the
- * function clears nothing it does not overwrite first.
+ * capture.  The address is kept per device ordinal for the life of the process and is
+ * not looked up again after a cudaDeviceReset, so do not call this function after
+ * resetting a device.  All calls share the one array and its contents persist between
+ * calls, so calls that overlap on the GPU (different streams without ordering) race; the
+ * function clears nothing it does not overwrite first.  Each call rebuilds the twiddle and
+ * digit-reversal tables of both sides in the array (4 small launches before the 4 launches
+ * of the transform), so no state carries over from one call to the next.
  * ------------------------------------------------------------------------------- */
 #define SBD_NOALLOC_FFT_MAX_BYTES (4 * 1024 * 1024)
 #define SBD_NOALLOC_FFT_MAX_SIDE  4096

@@ -88,7 +88,7 @@ struct sbd_plan_s {
                                        // internal order of D's rows and columns)
     void* f_int = nullptr;             // f in internal order, right-hand sides interleaved
     void* q_int = nullptr;             // D f in internal order, interleaved
-    bool d32 = false;                  // D's values and f_int in FP32 (the FP32 form)
+    bool d32 = false;                  // D's values and f_int in FP32 (SBD_FLAG_NEAR_FP32)
     long long* pt_tile_start = nullptr;
     PointWork pt_work{nullptr, nullptr, 0};   // chunks of the point records (spread, interp)
     long long* node_tile_start = nullptr;
@@ -98,7 +98,7 @@ struct sbd_plan_s {
     NodeTuning tuning;                 // fused node-kernel variant (sbd_tune)
     int fft_split = 0;                 // row-FFT phases (sbd_tune): 0 as needed, 2 always two
     int tuned = 0;                     // 1 once sbd_tune chose the variant
-    // workspace (one right-hand side at a time)
+    // workspace grids, max_nrhs right-hand sides each (see GridStrides)
     void* wsX = nullptr;
     void* wsA = nullptr;
     void* wsB = nullptr;
@@ -364,7 +364,8 @@ int build_far(sbd_plan_s* p, cudaStream_t s) {
     std::vector<T> dec(np.m);
     for (int i = 0; i < np.m; ++i) dec[i] = static_cast<T>(np.dec[i]);
     if ((rc = upload(p, reinterpret_cast<T**>(&p->dec), dec, s))) return rc;
-    const size_t e = sizeof(cx_t<T>);
+    // workspace grids for max_nrhs right-hand sides at once (grid r at r times the grid size)
+    const size_t e = sizeof(cx_t<T>) * static_cast<size_t>(p->max_nrhs);
     const size_t m = np.m, nk = np.nk;
     if ((rc = dev_alloc(p, &p->wsX, e * m * m))) return rc;
     if ((rc = dev_alloc(p, &p->wsA, e * m * nk))) return rc;
@@ -373,22 +374,34 @@ int build_far(sbd_plan_s* p, cudaStream_t s) {
     return SBD_OK;
 }
 
+// Workspace grids hold nb right-hand sides each, grid b at b times the grid's size (complex
+// elements): X (spreading grid) m x m, or m^2 / 2 for the packed real grid of Laplace, A
+// (row-pass scratch) m x nk, B and C (frequency grids) nk x nk.
+struct GridStrides {
+    long X, A, K;
+};
+GridStrides grid_strides(const NufftParams& np, bool real = false) {
+    const long m = np.m, nk = np.nk;
+    return {real ? m * m / 2 : m * m, m * nk, nk * nk};
+}
+
 // spreading grid X (m x m, rows = y) -> frequency grid K (nk x nk, rows = kx), forward transform.
-// A (m x nk) and Tr (>= nk x m) are scratch.
+// A (m x nk) and Tr (>= nk x m) are scratch.  nb grids in one pass each.
 template <typename T>
-int forward_fft(sbd_plan_s* p, const cx_t<T>* X, cx_t<T>* A, cx_t<T>* Tr, cx_t<T>* K, cudaStream_t s) {
+int forward_fft(sbd_plan_s* p, const cx_t<T>* X, cx_t<T>* A, cx_t<T>* Tr, cx_t<T>* K, cudaStream_t s, int nb = 1) {
     const NufftParams& np = p->np;
     const int m = np.m, nk = np.nk, n = np.n;
+    const GridStrides g = grid_strides(np);
     const T* dec = static_cast<const T*>(p->dec);
     // along x (rows y), precorrection exp(sigma |x|^2) fused into the load
     const int sp = p->fft_split;
     int rc = fft_rows<T>(X, m, m, -m / 2, A, nk, nk, -nk / 2, m, n, -1, dec, dec, nullptr, nullptr, s, 0, 0, kIoPlain,
-                         sp);
+                         sp, nb, g.X, g.A);
     if (rc) return rc;
-    if ((rc = transpose<T>(A, nk, 0, Tr, m, 0, m, nk, 1, s))) return rc;   // [y][kx] -> [kx][y]
+    if ((rc = transpose<T>(A, nk, g.A, Tr, m, g.K, m, nk, nb, s))) return rc;   // [y][kx] -> [kx][y]
     // along y (rows kx)
     return fft_rows<T>(Tr, m, m, -m / 2, K, nk, nk, -nk / 2, nk, n, -1, nullptr, nullptr, nullptr, nullptr, s, 0, 0,
-                       kIoPlain, sp);
+                       kIoPlain, sp, nb, g.K, g.K);
 }
 
 // frequency grid K2 (nk x nk, rows = kx) -> spreading grid X (m x m), adjoint transform.
@@ -397,17 +410,18 @@ int forward_fft(sbd_plan_s* p, const cx_t<T>* X, cx_t<T>* A, cx_t<T>* Tr, cx_t<T
 // taken of S(eta) + conj(S(-eta)).
 template <typename T>
 int inverse_fft(sbd_plan_s* p, const cx_t<T>* K2, cx_t<T>* A, cx_t<T>* Tr, cx_t<T>* X, cudaStream_t s,
-                bool fold) {
+                bool fold, int nb = 1) {
     const NufftParams& np = p->np;
     const int m = np.m, nk = np.nk, n = np.n;
+    const GridStrides g = grid_strides(np);
     const T* dec = static_cast<const T*>(p->dec);
     const int sp = p->fft_split;
     int rc = fft_rows<T>(K2, nk, nk, -nk / 2, A, m, m, -m / 2, nk, n, +1, nullptr, nullptr, nullptr, nullptr, s,
-                         fold ? nk : 0, 0, kIoPlain, sp);
+                         fold ? nk : 0, 0, kIoPlain, sp, nb, g.K, g.A);
     if (rc) return rc;
-    if ((rc = transpose<T>(A, m, 0, Tr, nk, 0, nk, m, 1, s))) return rc;   // [kx][y] -> [y][kx]
+    if ((rc = transpose<T>(A, m, g.A, Tr, nk, g.K, nk, m, nb, s))) return rc;   // [kx][y] -> [y][kx]
     return fft_rows<T>(Tr, nk, nk, -nk / 2, X, m, m, -m / 2, m, n, +1, nullptr, nullptr, dec, dec, s, 0, 0, kIoPlain,
-                       sp);
+                       sp, nb, g.K, g.X);
 }
 
 // Real data (Laplace): the spreading grid X is real, stored as packed row pairs
@@ -419,18 +433,20 @@ template <typename T>
 int kx_low(const sbd_plan_s* p) { return p->np.nk / 2 - (p->np.Pk / 2 + 2); }
 
 template <typename T>
-int forward_fft_real(sbd_plan_s* p, const cx_t<T>* Xp, cx_t<T>* A, cx_t<T>* Tr, cx_t<T>* K, cudaStream_t s) {
+int forward_fft_real(sbd_plan_s* p, const cx_t<T>* Xp, cx_t<T>* A, cx_t<T>* Tr, cx_t<T>* K, cudaStream_t s,
+                     int nb = 1) {
     const NufftParams& np = p->np;
     const int m = np.m, nk = np.nk, n = np.n;
+    const GridStrides g = grid_strides(np, true);
     const int lo = kx_low<T>(p), w2 = nk - lo;
     const T* dec = static_cast<const T*>(p->dec);
     const int sp = p->fft_split;
     int rc = fft_rows<T>(Xp, m, m, -m / 2, A, w2, w2, lo - nk / 2, m / 2, n, -1, dec, dec, nullptr, nullptr, s, 0, 0,
-                         kIoPairFwd, sp);
+                         kIoPairFwd, sp, nb, g.X, g.A);
     if (rc) return rc;
-    if ((rc = transpose<T>(A, w2, 0, Tr, m, 0, m, w2, 1, s))) return rc;   // [y][kx] -> [kx][y]
+    if ((rc = transpose<T>(A, w2, g.A, Tr, m, g.K, m, w2, nb, s))) return rc;   // [y][kx] -> [kx][y]
     return fft_rows<T>(Tr, m, m, -m / 2, K + static_cast<long>(lo) * nk, nk, nk, -nk / 2, w2, n, -1, nullptr, nullptr,
-                       nullptr, nullptr, s, 0, 0, kIoPlain, sp);
+                       nullptr, nullptr, s, 0, 0, kIoPlain, sp, nb, g.K, g.K);
 }
 
 // Adjoint for real data: S (node step over the half node set) completes to
@@ -438,21 +454,25 @@ int forward_fft_real(sbd_plan_s* p, const cx_t<T>* Xp, cx_t<T>* A, cx_t<T>* Tr, 
 // (the fold is applied on the load); then each pair of y rows is one transform along
 // x from its two half spectra, giving the packed real X.
 template <typename T>
-int inverse_fft_real(sbd_plan_s* p, const cx_t<T>* S, cx_t<T>* A, cx_t<T>* Tr, cx_t<T>* Xp, cudaStream_t s) {
+int inverse_fft_real(sbd_plan_s* p, const cx_t<T>* S, cx_t<T>* A, cx_t<T>* Tr, cx_t<T>* Xp, cudaStream_t s,
+                     int nb = 1) {
     const NufftParams& np = p->np;
     const int m = np.m, nk = np.nk, n = np.n;
+    const GridStrides g = grid_strides(np, true);
     const int J = nk / 2;
     const T* dec = static_cast<const T*>(p->dec);
     const int sp = p->fft_split;
     int rc = fft_rows<T>(S + static_cast<long>(J) * nk, nk, nk, -nk / 2, A, m, m, -m / 2, J, n, +1, nullptr, nullptr,
-                         nullptr, nullptr, s, nk, J, kIoPlain, sp);
+                         nullptr, nullptr, s, nk, J, kIoPlain, sp, nb, g.K, g.A);
     if (rc) return rc;
-    if ((rc = transpose<T>(A, m, 0, Tr, J, 0, J, m, 1, s))) return rc;   // [kx][y] -> [y][kx]
+    if ((rc = transpose<T>(A, m, g.A, Tr, J, g.K, J, m, nb, s))) return rc;   // [kx][y] -> [y][kx]
     return fft_rows<T>(Tr, J, J, 0, Xp, m, m, -m / 2, m / 2, n, +1, nullptr, nullptr, dec, dec, s, 0, 0, kIoPairInv,
-                       sp);
+                       sp, nb, g.K, g.X);
 }
 
 // q = far part of f (+ the internal-order near term add[i * nrhs + r] when add is given).
+// Every step takes all nrhs right-hand sides in one launch (grids stored right-hand side
+// by right-hand side in the workspace): 9 launches per call whatever nrhs.
 template <typename T>
 int far_apply(sbd_plan_s* p, const void* f, void* q, int nrhs, cudaStream_t s, const void* add,
               cudaEvent_t join = nullptr) {
@@ -461,41 +481,37 @@ int far_apply(sbd_plan_s* p, const void* f, void* q, int nrhs, cudaStream_t s, c
     int rc = far_sum(f, cplx_io, p->n, nrhs, p->sumf, s);
     if (rc) return rc;
     t_sum.end();
-    const size_t esz = cplx_io ? 16 : 8;
     auto* X = static_cast<cx_t<T>*>(p->wsX);
     auto* A = static_cast<cx_t<T>*>(p->wsA);
     auto* B = static_cast<cx_t<T>*>(p->wsB);
     auto* C = static_cast<cx_t<T>*>(p->wsC);
     const double2 w0 = make_double2(p->w0.real(), p->w0.imag());
-    for (int r = 0; r < nrhs; ++r) {
-        const void* fr = static_cast<const char*>(f) + esz * p->n * r;
-        void* qr = static_cast<char*>(q) + esz * p->n * r;
-        const bool real = p->half_nodes;   // Laplace: real grids, half the transforms and nodes
-        StepTimer t1(p, s, SBD_STAGE_SPREAD);
-        if ((rc = spread_tiled<T>(static_cast<const PointRec<T>*>(p->pts), p->pt_perm, p->pt_work, p->geom,
-                                  fr, cplx_io, X, s, real))) return rc;
-        t1.end();
-        StepTimer t2(p, s, SBD_STAGE_FFT_FWD);
-        if ((rc = real ? forward_fft_real<T>(p, X, A, C, B, s) : forward_fft<T>(p, X, A, C, B, s))) return rc;
-        t2.end();
-        StepTimer t3(p, s, SBD_STAGE_NODE);
-        if (p->node_fused) {
-            if ((rc = node_step_fused<T>(static_cast<const NodeRec<T>*>(p->nodes), p->node_tile_start, p->geom, B,
-                                         C, p->tuning, s))) return rc;
-        } else if ((rc = node_step_tiled<T>(static_cast<const NodeRec<T>*>(p->nodes), p->node_tile_start, p->geom,
-                                            B, static_cast<cx_t<T>*>(p->ghat), C, s))) {
-            return rc;
-        }
-        t3.end();
-        StepTimer t4(p, s, SBD_STAGE_FFT_INV);
-        if ((rc = real ? inverse_fft_real<T>(p, C, A, B, X, s) : inverse_fft<T>(p, C, A, B, X, s, false))) return rc;
-        t4.end();
-        if (join && r == 0) SBD_CUDA_TRY(cudaStreamWaitEvent(s, join, 0));   // D f is ready
-        StepTimer t5(p, s, SBD_STAGE_INTERP);
-        if ((rc = interp_tiled<T>(static_cast<const PointRec<T>*>(p->pts), p->pt_perm, p->pt_work, p->geom, X,
-                                  w0, p->sumf + r, qr, cplx_io, s, real, add, nrhs, r))) return rc;
-        t5.end();
+    const bool real = p->half_nodes;   // Laplace: real grids, half the transforms and nodes
+    StepTimer t1(p, s, SBD_STAGE_SPREAD);
+    if ((rc = spread_tiled<T>(static_cast<const PointRec<T>*>(p->pts), p->pt_perm, p->pt_work, p->geom, f, cplx_io,
+                              X, s, real, nrhs, p->n))) return rc;
+    t1.end();
+    StepTimer t2(p, s, SBD_STAGE_FFT_FWD);
+    if ((rc = real ? forward_fft_real<T>(p, X, A, C, B, s, nrhs) : forward_fft<T>(p, X, A, C, B, s, nrhs))) return rc;
+    t2.end();
+    StepTimer t3(p, s, SBD_STAGE_NODE);
+    if (p->node_fused) {
+        if ((rc = node_step_fused<T>(static_cast<const NodeRec<T>*>(p->nodes), p->node_tile_start, p->geom, B, C,
+                                     p->tuning, s, nrhs))) return rc;
+    } else if ((rc = node_step_tiled<T>(static_cast<const NodeRec<T>*>(p->nodes), p->node_tile_start, p->geom, B,
+                                        static_cast<cx_t<T>*>(p->ghat), C, s, nrhs))) {
+        return rc;
     }
+    t3.end();
+    StepTimer t4(p, s, SBD_STAGE_FFT_INV);
+    if ((rc = real ? inverse_fft_real<T>(p, C, A, B, X, s, nrhs) : inverse_fft<T>(p, C, A, B, X, s, false, nrhs)))
+        return rc;
+    t4.end();
+    if (join) SBD_CUDA_TRY(cudaStreamWaitEvent(s, join, 0));   // D f is ready
+    StepTimer t5(p, s, SBD_STAGE_INTERP);
+    if ((rc = interp_tiled<T>(static_cast<const PointRec<T>*>(p->pts), p->pt_perm, p->pt_work, p->geom, X, w0,
+                              p->sumf, q, cplx_io, s, real, add, nrhs, nrhs, p->n))) return rc;
+    t5.end();
     return SBD_OK;
 }
 
@@ -545,8 +561,9 @@ int check_plan_call(sbd_plan_t p, const void* a, const void* b) {
 // non-negative counts and tolerances.
 bool options_valid(const sbd_options& o) {
     const int known = SBD_FLAG_GAUSSIAN_NODES | SBD_FLAG_GAUSSIAN_SPREAD | SBD_FLAG_SPREAD_SIGMA_2 |
-                      SBD_FLAG_SPREAD_SIGMA_15;
+                      SBD_FLAG_SPREAD_SIGMA_15 | SBD_FLAG_NEAR_FP32;
     return (o.form == SBD_FORM_FP64 || o.form == SBD_FORM_FP32) && (o.flags & ~known) == 0 &&
+           !((o.flags & SBD_FLAG_NEAR_FP32) && o.form != SBD_FORM_FP32) &&
            !((o.flags & SBD_FLAG_SPREAD_SIGMA_2) && (o.flags & SBD_FLAG_SPREAD_SIGMA_15)) &&
            !((o.flags & SBD_FLAG_GAUSSIAN_SPREAD) && (o.flags & SBD_FLAG_SPREAD_SIGMA_15)) && o.fixed_P >= 0 &&
            o.max_nrhs >= 0 && o.nufft_tol >= 0 && o.delta_max >= 0 && o.host_threads >= 0;
@@ -816,9 +833,9 @@ int sbd_plan(const double* points, int64_t n, sbd_kernel kernel, double delta_mi
         cudaFreeAsync(zs, s);
         if (rc) return fail(rc);
     }
-    // the FP32 form keeps D and the gathered f in FP32 (D f is one more FP32-level term of
-    // the output; GB300's FP64 rate would otherwise bound the product)
-    p->d32 = o.form == SBD_FORM_FP32;
+    // D f stays FP64 in both forms (the near correction is where G - G_approx cancels);
+    // SBD_FLAG_NEAR_FP32 keeps D and the gathered f in FP32 instead (FP32 form only)
+    p->d32 = (o.flags & SBD_FLAG_NEAR_FP32) != 0;
     if (p->d32 && (rc = near_values_to_f32(&p->val, p->nnz, cval, s))) return fail(rc);
     const size_t dvb = (cval ? 2 : 1) * (p->d32 ? sizeof(float) : sizeof(double));
     p->device_bytes += static_cast<long long>(sizeof(long long) * (p->n + 1) + (sizeof(int) + dvb) * p->nnz);

@@ -305,11 +305,15 @@ __global__ void __launch_bounds__(NT) fft_rows_kernel(
     int n, int Q, FftPlan1D plan, const cx_t<T>* __restrict__ tw, const int* __restrict__ perm,
     const T* __restrict__ pre_elem, const T* __restrict__ pre_row,
     const T* __restrict__ post_elem, const T* __restrict__ post_row, HermFold<T> hf, int io,
-    const cx_t<T>* __restrict__ tw2) {
+    const cx_t<T>* __restrict__ tw2, long in_batch, long out_batch) {
     using C = cx_t<T>;
     constexpr int sign = SIGN;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* s = reinterpret_cast<C*>(smem_raw);
+    // blockIdx.z: grid of a batch of equal grids (right-hand sides), in_batch / out_batch apart
+    in += blockIdx.z * in_batch;
+    out += blockIdx.z * out_batch;
+    if (hf.n) hf.base += blockIdx.z * in_batch;
     const long row = blockIdx.y;     // phases of a row are adjacent CTAs (they read the same row)
     const int r = blockIdx.x;
     const int nq = n / Q;
@@ -541,8 +545,13 @@ int fft_rows(const cx_t<T>* in, long in_stride, int in_len, int in_shift,
              cx_t<T>* out, long out_stride, int out_len, int out_shift,
              int rows, int n, int sign,
              const T* pre_elem, const T* pre_row, const T* post_elem, const T* post_row,
-             cudaStream_t stream, int herm_n, int herm_row0, int io, int split) {
-    if (rows <= 0) return SBD_OK;
+             cudaStream_t stream, int herm_n, int herm_row0, int io, int split, int nb, long in_batch,
+             long out_batch) {
+    if (rows <= 0 || nb <= 0) return SBD_OK;
+    if (nb > 65535) {
+        set_error("fft_rows: at most 65535 grids per batch");
+        return SBD_EINVAL;
+    }
     if (herm_n && (herm_row0 < 0 || herm_row0 + rows > herm_n || in_len != herm_n || io != kIoPlain)) {
         set_error("fft_rows: a Hermitian fold needs rows inside a square grid read whole");
         return SBD_EINVAL;
@@ -574,7 +583,7 @@ int fft_rows(const cx_t<T>* in, long in_stride, int in_len, int in_shift,
     out_shift = ((out_shift % n) + n) % n;
     for (int r0 = 0; r0 < rows; r0 += 65535) {          // grid.y holds at most 65535 rows
         const int nr = std::min(65535, rows - r0);
-        const dim3 grid(static_cast<unsigned>(Q), static_cast<unsigned>(nr));
+        const dim3 grid(static_cast<unsigned>(Q), static_cast<unsigned>(nr), static_cast<unsigned>(nb));
         // pair modes: one launch row is two grid rows on the paired side
         const long in_rows = io == kIoPairInv ? 2 : 1, out_rows = io == kIoPairFwd ? 2 : 1;
         const cx_t<T>* ip = in + static_cast<long>(r0) * in_stride * in_rows;
@@ -589,15 +598,15 @@ int fft_rows(const cx_t<T>* in, long in_stride, int in_len, int in_shift,
             // memory both allow it), instead of one 1024-thread CTA per full-length row
             rc = launch_fft_rows<T, 512>(sign, grid, smem, stream, ip, in_stride, in_len, in_shift, op, out_stride,
                                          out_len, out_shift, n, Q, plan, tw, perm, pre_elem, prr, post_elem, por, hf,
-                                         io, tw2);
+                                         io, tw2, in_batch, out_batch);
         } else if (nq > 2048) {
             rc = launch_fft_rows<T, 1024>(sign, grid, smem, stream, ip, in_stride, in_len, in_shift, op, out_stride,
                                           out_len, out_shift, n, Q, plan, tw, perm, pre_elem, prr, post_elem, por, hf,
-                                          io, tw2);
+                                          io, tw2, in_batch, out_batch);
         } else {
             rc = launch_fft_rows<T, 256>(sign, grid, smem, stream, ip, in_stride, in_len, in_shift, op, out_stride,
                                          out_len, out_shift, n, Q, plan, tw, perm, pre_elem, prr, post_elem, por, hf,
-                                         io, tw2);
+                                         io, tw2, in_batch, out_batch);
         }
         if (rc) return rc;
     }
@@ -626,12 +635,12 @@ int fft_rows_tables(const cx_t<T>* in, long in_stride, int in_len, cx_t<T>* out,
             rc = launch_fft_rows<T, 1024>(sign, grid, smem, stream, ip, in_stride, in_len, 0, op, out_stride, out_len,
                                           0, n, 1, plan, tw, perm, none, none, none, none,
                                           HermFold<T>{nullptr, 0, 0}, static_cast<int>(kIoPlain),
-                                          static_cast<const cx_t<T>*>(nullptr));
+                                          static_cast<const cx_t<T>*>(nullptr), 0L, 0L);
         else
             rc = launch_fft_rows<T, 256>(sign, grid, smem, stream, ip, in_stride, in_len, 0, op, out_stride, out_len,
                                          0, n, 1, plan, tw, perm, none, none, none, none,
                                          HermFold<T>{nullptr, 0, 0}, static_cast<int>(kIoPlain),
-                                         static_cast<const cx_t<T>*>(nullptr));
+                                         static_cast<const cx_t<T>*>(nullptr), 0L, 0L);
         if (rc) return rc;
     }
     return SBD_OK;
@@ -649,10 +658,10 @@ int transpose(const cx_t<T>* in, long in_stride, long in_batch, cx_t<T>* out, lo
 
 template int fft_rows<float>(const float2*, long, int, int, float2*, long, int, int, int, int, int,
                              const float*, const float*, const float*, const float*, cudaStream_t, int, int,
-                             int, int);
+                             int, int, int, long, long);
 template int fft_rows<double>(const double2*, long, int, int, double2*, long, int, int, int, int, int,
                               const double*, const double*, const double*, const double*, cudaStream_t, int, int,
-                              int, int);
+                              int, int, int, long, long);
 template int fft_rows_tables<float>(const float2*, long, int, float2*, long, int, int, int, int, const float2*,
                                     const int*, cudaStream_t);
 template int fft_rows_tables<double>(const double2*, long, int, double2*, long, int, int, int, int, const double2*,

@@ -249,6 +249,50 @@ __global__ void spmv_kernel(const long long* __restrict__ rowptr, const int* __r
     }
 }
 
+// qp = D fp for one right-hand side in FP64 (values, products and sums), G lanes per row:
+// a warp takes 32 / G rows, and the G lanes of a row read consecutive entries, so one
+// warp-wide load covers 32 / G rows' contiguous segments.  Against a warp per row this
+// cuts the FP64 shuffle-adds of the row reduction from 5 per row to log2(G) per 32 / G
+// rows (GB300's FP64 pipe is narrow, and with ~10^2 entries a row the warp-wide
+// reduction cost as much FP64 issue as the products).  Whole warps run the reduction
+// (rows past n only contribute zeros), so the shuffles see every lane.
+template <bool CPLX, int G>
+__global__ void spmv_group_kernel(const long long* __restrict__ rowptr, const int* __restrict__ col,
+                                  const void* __restrict__ val, long n, const void* __restrict__ fp,
+                                  void* __restrict__ qp) {
+    const long row = (blockIdx.x * static_cast<long>(blockDim.x) + threadIdx.x) / G;
+    const int sub = threadIdx.x & (G - 1);
+    const bool live = row < n;
+    long long b = 0, e = 0;
+    if (live) {
+        b = rowptr[row];
+        e = rowptr[row + 1];
+    }
+    double sr = 0.0, si = 0.0;
+    if (CPLX) {
+        const double2* v = static_cast<const double2*>(val);
+        const double2* x = static_cast<const double2*>(fp);
+        for (long long j = b + sub; j < e; j += G) {
+            const double2 a = v[j], y = x[col[j]];
+            sr = fma(a.x, y.x, fma(-a.y, y.y, sr));
+            si = fma(a.x, y.y, fma(a.y, y.x, si));
+        }
+    } else {
+        const double* v = static_cast<const double*>(val);
+        const double* x = static_cast<const double*>(fp);
+        for (long long j = b + sub; j < e; j += G) sr = fma(v[j], x[col[j]], sr);
+    }
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) {
+        sr += __shfl_down_sync(0xffffffffu, sr, o, G);
+        if (CPLX) si += __shfl_down_sync(0xffffffffu, si, o, G);
+    }
+    if (live && sub == 0) {
+        if (CPLX) static_cast<double2*>(qp)[row] = make_double2(sr, si);
+        else static_cast<double*>(qp)[row] = sr;
+    }
+}
+
 // Internal (spatially sorted) order: fp[i * nrhs + r] = f[r * n + perm[i]].
 template <bool CPLX, bool F32>
 __global__ void gather_rows_kernel(const void* __restrict__ f, long n, int nrhs, const int* __restrict__ perm,
@@ -613,10 +657,11 @@ int near_spmv_internal(const long long* rowptr, const int* col, const void* val,
             if (cval) spmv32_rhs_kernel<true><<<nblk(t), kT, 0, s>>>(rowptr, col, val, n, nrhs, fp, qp);
             else spmv32_rhs_kernel<false><<<nblk(t), kT, 0, s>>>(rowptr, col, val, n, nrhs, fp, qp);
         }
-    } else if (nrhs == 1) {   // one warp per row (rows of ~10^2 entries), same layout
-        const long threads = n * 32;
-        if (cval) spmv_kernel<true><<<nblk(threads), kT, 0, s>>>(rowptr, col, val, n, 1, fp, qp, false);
-        else spmv_kernel<false><<<nblk(threads), kT, 0, s>>>(rowptr, col, val, n, 1, fp, qp, false);
+    } else if (nrhs == 1) {   // 8 lanes per row (rows of ~10^2 entries), FP64 throughout
+        constexpr int G = 8;
+        const long threads = n * G;
+        if (cval) spmv_group_kernel<true, G><<<nblk(threads), kT, 0, s>>>(rowptr, col, val, n, fp, qp);
+        else spmv_group_kernel<false, G><<<nblk(threads), kT, 0, s>>>(rowptr, col, val, n, fp, qp);
     } else {
         const long t = n * nrhs;
         if (cval) spmv_rhs_kernel<true><<<nblk(t), kT, 0, s>>>(rowptr, col, val, n, nrhs, fp, qp);

@@ -136,12 +136,13 @@ template <typename T> struct NodeVal {      // node step scatter values
     const cx_t<T>* ghat;
     __device__ __forceinline__ cx_t<T> get(long i) const { return ghat[i]; }
 };
-template <typename T> struct PointVal {     // spreading values f[perm[i]] (float64 or complex128)
+template <typename T> struct PointVal {     // spreading values f[r * stride + perm[i]] (float64 or complex128)
     const void* f;
     const int* perm;
     bool fc;
-    __device__ __forceinline__ cx_t<T> get(long i) const {
-        const long j = perm[i];
+    long stride;          // elements between right-hand sides
+    __device__ __forceinline__ cx_t<T> get(long i, int r = 0) const {
+        const long j = perm[i] + r * stride;
         if (fc) {
             const double2 v = static_cast<const double2*>(f)[j];
             return mk<T>(static_cast<T>(v.x), static_cast<T>(v.y));
@@ -149,21 +150,22 @@ template <typename T> struct PointVal {     // spreading values f[perm[i]] (floa
         return mk<T>(static_cast<T>(static_cast<const double*>(f)[j]), static_cast<T>(0));
     }
 };
-template <typename T> struct PointOut {     // interpolation: q[perm[i]] = v + w0 * sumf (+ add[i])
+template <typename T> struct PointOut {     // interpolation: q[r][perm[i]] = v + w0 * sumf[r] (+ add)
     void* q;
     const int* perm;
     bool qc;
     double2 w0;
     const double2* sumf;
-    const void* add;      // optional FP64 term per record (internal order): add[i * add_stride + add_off]
+    const void* add;      // optional FP64 term per record (internal order): add[i * add_stride + add_off + r]
     int add_stride, add_off;
-    __device__ __forceinline__ void put(long i, const PointRec<T>&, cx_t<T> v) const {
-        const long j = perm[i];
-        const double2 sf = *sumf;
+    long stride;          // elements of q between right-hand sides
+    __device__ __forceinline__ void put(long i, const PointRec<T>&, cx_t<T> v, int r = 0) const {
+        const long j = perm[i] + r * stride;
+        const double2 sf = sumf[r];
         double re = static_cast<double>(v.x) + w0.x * sf.x - w0.y * sf.y;
         double im = static_cast<double>(v.y) + w0.x * sf.y + w0.y * sf.x;
         if (add) {
-            const long k = i * add_stride + add_off;
+            const long k = i * add_stride + add_off + r;
             if (qc) {
                 const double2 a = static_cast<const double2*>(add)[k];
                 re += a.x;
@@ -314,26 +316,36 @@ __global__ void __launch_bounds__(256) scatter_tiles_kernel(
 // Interpolation by work item (PointWork): the CTA loads its tile plus the (P-1) halo of the
 // grid into shared memory and takes the records of its chunk, a group of G lanes per record
 // (lane = stencil column, rows accumulated in registers, columns reduced with shuffles).
+// Right-hand sides: blockIdx.y takes rg of them (grids gstride elements apart), whose tiles
+// sit in shared memory side by side (kC = 1 plane for a packed real grid, else re / im), so
+// each record's window weights are evaluated once for the rg values it produces.
 template <typename T, int G, bool PK>
 __global__ void __launch_bounds__(256) interp_chunks_kernel(
     const PointRec<T>* __restrict__ rec, PointWork work, int ntx, int n, int P, Window<T> win,
-    const cx_t<T>* __restrict__ grid, PointOut<T> out) {
-    using C = cx_t<T>;
+    const cx_t<T>* __restrict__ grid, PointOut<T> out, int nrhs, int rg, long gstride) {
+    constexpr int kC = PK ? 1 : 2;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    C* s = reinterpret_cast<C*>(smem_raw);
+    T* s = reinterpret_cast<T*>(smem_raw);                    // [rg][W][W][kC]
     const int tile = work.tile[blockIdx.x];
     const long long b0 = work.begin[blockIdx.x], b1 = work.begin[blockIdx.x + 1];
+    const int r0 = blockIdx.y * rg, nr = min(rg, nrhs - r0);
     const int ox = (tile / ntx) * kNodeTile, oy = (tile % ntx) * kNodeTile;
     const int W = kNodeTile + P - 1;
     const int rows = min(W, n - ox), cols = min(W, n - oy);
-    for (int idx = threadIdx.x; idx < W * W; idx += blockDim.x) {
-        const int r = idx / W, c = idx - r * W;
-        C v = mk<T>(0, 0);
-        if (r < rows && c < cols) {
-            if (PK) v = mk<T>(reinterpret_cast<const T*>(grid)[packed_index(ox + r, oy + c, n)], static_cast<T>(0));
-            else v = grid[static_cast<long>(ox + r) * n + oy + c];
+    for (int rr = 0; rr < nr; ++rr) {
+        const cx_t<T>* gr = grid + (r0 + rr) * gstride;
+        T* sr = s + static_cast<long>(rr) * kC * W * W;
+        for (int idx = threadIdx.x; idx < W * W; idx += blockDim.x) {
+            const int r = idx / W, c = idx - r * W;
+            if (PK) {
+                sr[idx] = r < rows && c < cols ? reinterpret_cast<const T*>(gr)[packed_index(ox + r, oy + c, n)]
+                                               : static_cast<T>(0);
+            } else {
+                const cx_t<T> v = r < rows && c < cols ? gr[static_cast<long>(ox + r) * n + oy + c] : mk<T>(0, 0);
+                sr[2 * idx] = v.x;
+                sr[2 * idx + 1] = v.y;
+            }
         }
-        s[idx] = v;
     }
     __syncthreads();
     const int lane = threadIdx.x & 31;
@@ -345,42 +357,47 @@ __global__ void __launch_bounds__(256) interp_chunks_kernel(
         const int rx = q.cell.x - ox, ry = q.cell.y - oy;   // in [0, 64): the record's own tile
         T wx, wy;
         lane_weights<T>(sub, P, win, q.frac.x, q.frac.y, wx, wy);
-        T sr = 0, si = 0;
-        const C* col = s + static_cast<long>(rx) * W + ry + sub;
-        for (int a = 0; a < P; ++a) {
-            const T w = __shfl_sync(gmask, wx, a, G);
-            if (sub < P) {
-                const C v = col[a * W];
-                sr += w * v.x;
-                si += w * v.y;
+        for (int rr = 0; rr < nr; ++rr) {
+            T sr = 0, si = 0;
+            const T* col = s + static_cast<long>(rr) * kC * W * W + kC * (static_cast<long>(rx) * W + ry + sub);
+            for (int a = 0; a < P; ++a) {
+                const T w = __shfl_sync(gmask, wx, a, G);
+                if (sub < P) {
+                    sr += w * col[kC * a * W];
+                    if (!PK) si += w * col[kC * a * W + 1];
+                }
             }
-        }
-        sr *= wy;
-        si *= wy;
+            sr *= wy;
+            si *= wy;
 #pragma unroll
-        for (int o = G / 2; o > 0; o >>= 1) {
-            sr += __shfl_xor_sync(gmask, sr, o, G);
-            si += __shfl_xor_sync(gmask, si, o, G);
+            for (int o = G / 2; o > 0; o >>= 1) {
+                sr += __shfl_xor_sync(gmask, sr, o, G);
+                if (!PK) si += __shfl_xor_sync(gmask, si, o, G);
+            }
+            if (sub == 0) out.put(i, q, mk<T>(sr, si), r0 + rr);
         }
-        if (sub == 0) out.put(i, q, mk<T>(sr, si));
     }
 }
 
 // Spreading by work item (PointWork): the CTA accumulates the stencils of its chunk's records
 // into a shared (64 + P - 1)^2 window with shared-memory atomics, then adds every cell it
 // reached into the (cleared) grid with global atomics.  RV: real values, one plane.
+// Right-hand sides: blockIdx.y takes rg of them (one window each, grids gstride elements
+// apart); each record's window weights are evaluated once for its rg values.
 template <typename T, int G, bool PK, bool RV>
 __global__ void __launch_bounds__(256) spread_chunks_kernel(
     const PointRec<T>* __restrict__ rec, PointWork work, int ntx, int n, int P, Window<T> win, PointVal<T> val,
-    cx_t<T>* __restrict__ grid) {
+    cx_t<T>* __restrict__ grid, int nrhs, int rg, long gstride) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* acc = reinterpret_cast<T*>(smem_raw);          // [W][W][RV ? 1 : 2]
+    T* acc = reinterpret_cast<T*>(smem_raw);          // [rg][W][W][RV ? 1 : 2]
     constexpr int kC = RV ? 1 : 2;
     const int W = kNodeTile + P - 1;
+    const long plane = static_cast<long>(kC) * W * W;
     const int tile = work.tile[blockIdx.x];
     const long long b0 = work.begin[blockIdx.x], b1 = work.begin[blockIdx.x + 1];
+    const int r0 = blockIdx.y * rg, nr = min(rg, nrhs - r0);
     const int ox = (tile / ntx) * kNodeTile, oy = (tile % ntx) * kNodeTile;
-    for (int idx = threadIdx.x; idx < kC * W * W; idx += blockDim.x) acc[idx] = 0;
+    for (long idx = threadIdx.x; idx < nr * plane; idx += blockDim.x) acc[idx] = 0;
     __syncthreads();
     const int lane = threadIdx.x & 31;
     const int sub = lane % G;
@@ -391,31 +408,37 @@ __global__ void __launch_bounds__(256) spread_chunks_kernel(
         const int rx = q.cell.x - ox, ry = q.cell.y - oy;   // in [0, 64): the record's own tile
         T wx, wy;
         lane_weights<T>(sub, P, win, q.frac.x, q.frac.y, wx, wy);
-        const cx_t<T> g = val.get(i);
-        const T gr = g.x * wy, gi = g.y * wy;
-        T* cell = acc + kC * (rx * W + ry + sub);
-        for (int a = 0; a < P; ++a) {
-            const T w = __shfl_sync(gmask, wx, a, G);
-            if (sub < P) {
-                atomicAdd(cell + kC * a * W, gr * w);
-                if (!RV) atomicAdd(cell + kC * a * W + 1, gi * w);
+        for (int rr = 0; rr < nr; ++rr) {
+            const cx_t<T> g = val.get(i, r0 + rr);
+            const T gr = g.x * wy, gi = g.y * wy;
+            T* cell = acc + rr * plane + kC * (rx * W + ry + sub);
+            for (int a = 0; a < P; ++a) {
+                const T w = __shfl_sync(gmask, wx, a, G);
+                if (sub < P) {
+                    atomicAdd(cell + kC * a * W, gr * w);
+                    if (!RV) atomicAdd(cell + kC * a * W + 1, gi * w);
+                }
             }
         }
     }
     __syncthreads();
     const int rows = min(W, n - ox), cols = min(W, n - oy);
-    for (int idx = threadIdx.x; idx < W * W; idx += blockDim.x) {
-        const int r = idx / W, c = idx - r * W;
-        if (r >= rows || c >= cols) continue;
-        const T vr = acc[kC * idx];
-        if (PK) {
-            if (vr != static_cast<T>(0)) atomicAdd(reinterpret_cast<T*>(grid) + packed_index(ox + r, oy + c, n), vr);
-        } else {
-            T* g = reinterpret_cast<T*>(grid + static_cast<long>(ox + r) * n + oy + c);
-            if (vr != static_cast<T>(0)) atomicAdd(g, vr);
-            if (!RV) {
-                const T vi = acc[kC * idx + 1];
-                if (vi != static_cast<T>(0)) atomicAdd(g + 1, vi);
+    for (int rr = 0; rr < nr; ++rr) {
+        cx_t<T>* gr = grid + (r0 + rr) * gstride;
+        const T* ar = acc + rr * plane;
+        for (int idx = threadIdx.x; idx < W * W; idx += blockDim.x) {
+            const int r = idx / W, c = idx - r * W;
+            if (r >= rows || c >= cols) continue;
+            const T vr = ar[kC * idx];
+            if (PK) {
+                if (vr != static_cast<T>(0)) atomicAdd(reinterpret_cast<T*>(gr) + packed_index(ox + r, oy + c, n), vr);
+            } else {
+                T* g = reinterpret_cast<T*>(gr + static_cast<long>(ox + r) * n + oy + c);
+                if (vr != static_cast<T>(0)) atomicAdd(g, vr);
+                if (!RV) {
+                    const T vi = ar[kC * idx + 1];
+                    if (vi != static_cast<T>(0)) atomicAdd(g + 1, vi);
+                }
             }
         }
     }
@@ -445,10 +468,12 @@ __global__ void __launch_bounds__(256) spread_chunks_kernel(
 template <typename T, int G, int NT, int ACC, int SCHED>
 __global__ void __launch_bounds__(NT) node_fused_kernel(
     const NodeRec<T>* __restrict__ rec, const long long* __restrict__ tile_start, int ntx, int n, int P, int Ws,
-    Window<T> win, const cx_t<T>* __restrict__ kin, cx_t<T>* __restrict__ kout, float wbound) {
+    Window<T> win, const cx_t<T>* __restrict__ kin, cx_t<T>* __restrict__ kout, float wbound, long kbatch) {
     using C = cx_t<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ float red[NT / 32];
+    kin += blockIdx.y * kbatch;                       // right-hand side blockIdx.y
+    kout += blockIdx.y * kbatch;
     const int tile = blockIdx.x;
     const long long b0 = tile_start[tile], b1 = tile_start[tile + 1];
     if (b0 == b1) return;
@@ -621,11 +646,13 @@ static_assert(kBinWs >= kBinW && kBinWs % 16 == 12, "binned stride");
 template <int NT>
 __global__ void __launch_bounds__(NT, 1) node_binned_kernel(
     const NodeRec<float>* __restrict__ rec, const long long* __restrict__ tile_start, int ntx, int n, int P,
-    Window<float> win, const float2* __restrict__ kin, float2* __restrict__ kout) {
+    Window<float> win, const float2* __restrict__ kin, float2* __restrict__ kout, long kbatch) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int bstart[kBins + 1];
     __shared__ int border[kBins];                                   // bins, largest first
     __shared__ int next_bin;
+    kin += blockIdx.y * kbatch;                                     // right-hand side blockIdx.y
+    kout += blockIdx.y * kbatch;
     const int tile = blockIdx.x;
     const long long b0 = tile_start[tile], b1 = tile_start[tile + 1];
     if (b0 == b1) return;                                           // uniform per block
@@ -893,52 +920,58 @@ size_t node_fused_smem(int Pk, int acc) {
 }
 
 template <typename T, int G, int ACC, int SCHED>
-int launch_fused(const NodeRec<T>* nodes, const long long* tile_start, unsigned nt, int ntx, const FarGeom& g,
-                 int Ws, const Window<T>& win, const cx_t<T>* kin, cx_t<T>* kout, float wbound, cudaStream_t s) {
+int launch_fused(const NodeRec<T>* nodes, const long long* tile_start, dim3 nt, int ntx, const FarGeom& g,
+                 int Ws, const Window<T>& win, const cx_t<T>* kin, cx_t<T>* kout, float wbound, long kb,
+                 cudaStream_t s) {
     // the int64 planes leave room for one CTA per SM: twice the threads keep the warps
     constexpr int NT = ACC == 2 ? 2 * kNodeThreads : kNodeThreads;
     const size_t smem = node_fused_smem<T>(g.Pk, ACC);
     auto k = node_fused_kernel<T, G, NT, ACC, SCHED>;
     SBD_TRY(raise_smem_limit(k, smem));
-    k<<<nt, NT, smem, s>>>(nodes, tile_start, ntx, g.nk, g.Pk, Ws, win, kin, kout, wbound);
+    k<<<nt, NT, smem, s>>>(nodes, tile_start, ntx, g.nk, g.Pk, Ws, win, kin, kout, wbound, kb);
     SBD_LAUNCH_CHECK();
     return SBD_OK;
 }
 
 template <typename T, int G>
-int launch_fused_g(const NodeRec<T>* nodes, const long long* tile_start, unsigned nt, int ntx, const FarGeom& g,
-                   int Ws, const Window<T>& win, const cx_t<T>* kin, cx_t<T>* kout, const NodeTuning& t,
+int launch_fused_g(const NodeRec<T>* nodes, const long long* tile_start, dim3 nt, int ntx, const FarGeom& g,
+                   int Ws, const Window<T>& win, const cx_t<T>* kin, cx_t<T>* kout, const NodeTuning& t, long kb,
                    cudaStream_t s) {
     const float wb = t.wbound;
     if (sizeof(T) == 4 && t.acc == 1) {
-        return t.sched ? launch_fused<T, G, 1, 1>(nodes, tile_start, nt, ntx, g, Ws, win, kin, kout, wb, s)
-                       : launch_fused<T, G, 1, 0>(nodes, tile_start, nt, ntx, g, Ws, win, kin, kout, wb, s);
+        return t.sched ? launch_fused<T, G, 1, 1>(nodes, tile_start, nt, ntx, g, Ws, win, kin, kout, wb, kb, s)
+                       : launch_fused<T, G, 1, 0>(nodes, tile_start, nt, ntx, g, Ws, win, kin, kout, wb, kb, s);
     }
     if (sizeof(T) == 4 && t.acc == 2) {
-        return t.sched ? launch_fused<T, G, 2, 1>(nodes, tile_start, nt, ntx, g, Ws, win, kin, kout, wb, s)
-                       : launch_fused<T, G, 2, 0>(nodes, tile_start, nt, ntx, g, Ws, win, kin, kout, wb, s);
+        return t.sched ? launch_fused<T, G, 2, 1>(nodes, tile_start, nt, ntx, g, Ws, win, kin, kout, wb, kb, s)
+                       : launch_fused<T, G, 2, 0>(nodes, tile_start, nt, ntx, g, Ws, win, kin, kout, wb, kb, s);
     }
-    return t.sched ? launch_fused<T, G, 0, 1>(nodes, tile_start, nt, ntx, g, Ws, win, kin, kout, wb, s)
-                   : launch_fused<T, G, 0, 0>(nodes, tile_start, nt, ntx, g, Ws, win, kin, kout, wb, s);
+    return t.sched ? launch_fused<T, G, 0, 1>(nodes, tile_start, nt, ntx, g, Ws, win, kin, kout, wb, kb, s)
+                   : launch_fused<T, G, 0, 0>(nodes, tile_start, nt, ntx, g, Ws, win, kin, kout, wb, kb, s);
 }
 
 template <int NT>
-int launch_binned(const NodeRec<float>* nodes, const long long* tile_start, unsigned nt, int ntx, const FarGeom& g,
-                  const Window<float>& win, const float2* kin, float2* kout, cudaStream_t s) {
+int launch_binned(const NodeRec<float>* nodes, const long long* tile_start, dim3 nt, int ntx, const FarGeom& g,
+                  const Window<float>& win, const float2* kin, float2* kout, long kb, cudaStream_t s) {
     const size_t smem = node_fused_smem<float>(g.Pk, 3);
     auto k = node_binned_kernel<NT>;
     SBD_TRY(raise_smem_limit(k, smem));
-    k<<<nt, NT, smem, s>>>(nodes, tile_start, ntx, g.nk, g.Pk, win, kin, kout);
+    k<<<nt, NT, smem, s>>>(nodes, tile_start, ntx, g.nk, g.Pk, win, kin, kout, kb);
     SBD_LAUNCH_CHECK();
     return SBD_OK;
 }
 
 template <typename T>
 int node_step_fused(const NodeRec<T>* nodes, const long long* tile_start, const FarGeom& g,
-                    const cx_t<T>* kin, cx_t<T>* kout, const NodeTuning& t, cudaStream_t s) {
-    SBD_CUDA_TRY(cudaMemsetAsync(kout, 0, sizeof(cx_t<T>) * static_cast<size_t>(g.nk) * g.nk, s));
+                    const cx_t<T>* kin, cx_t<T>* kout, const NodeTuning& t, cudaStream_t s, int nb) {
+    if (nb < 1 || nb > 65535) {
+        set_error("node step: 1 to 65535 right-hand sides per launch");
+        return SBD_EINVAL;
+    }
+    const long kb = static_cast<long>(g.nk) * g.nk;
+    SBD_CUDA_TRY(cudaMemsetAsync(kout, 0, sizeof(cx_t<T>) * static_cast<size_t>(kb) * nb, s));
     const int ntx = tiles_per_side(g.nk);
-    const unsigned nt = static_cast<unsigned>(ntx) * ntx;
+    const dim3 nt(static_cast<unsigned>(ntx) * ntx, static_cast<unsigned>(nb));
     if constexpr (sizeof(T) == 4) {
         if (t.acc == 3) {
             if (g.Pk > kBinSide) {
@@ -946,25 +979,30 @@ int node_step_fused(const NodeRec<T>* nodes, const long long* tile_start, const 
                 return SBD_EINVAL;
             }
             const Window<float> win = make_window<float>(g.kwin, g.beta_k, g.Pk);
-            return t.sched ? launch_binned<2 * kNodeThreads>(nodes, tile_start, nt, ntx, g, win, kin, kout, s)
-                           : launch_binned<kNodeThreads>(nodes, tile_start, nt, ntx, g, win, kin, kout, s);
+            return t.sched ? launch_binned<2 * kNodeThreads>(nodes, tile_start, nt, ntx, g, win, kin, kout, kb, s)
+                           : launch_binned<kNodeThreads>(nodes, tile_start, nt, ntx, g, win, kin, kout, kb, s);
         }
     }
     const int W = kNodeTile + g.Pk - 1;
     const int P8 = fused_p8(g.Pk);
     const int Ws = fused_stride(W, P8);
     const Window<T> win = make_window<T>(g.kwin, g.beta_k, g.Pk);
-    if (P8 == 8) return launch_fused_g<T, 8>(nodes, tile_start, nt, ntx, g, Ws, win, kin, kout, t, s);
-    if (P8 == 16) return launch_fused_g<T, 16>(nodes, tile_start, nt, ntx, g, Ws, win, kin, kout, t, s);
-    return launch_fused_g<T, 32>(nodes, tile_start, nt, ntx, g, Ws, win, kin, kout, t, s);
+    if (P8 == 8) return launch_fused_g<T, 8>(nodes, tile_start, nt, ntx, g, Ws, win, kin, kout, t, kb, s);
+    if (P8 == 16) return launch_fused_g<T, 16>(nodes, tile_start, nt, ntx, g, Ws, win, kin, kout, t, kb, s);
+    return launch_fused_g<T, 32>(nodes, tile_start, nt, ntx, g, Ws, win, kin, kout, t, kb, s);
 }
 
 template <typename T>
 int node_step_tiled(const NodeRec<T>* nodes, const long long* tile_start, const FarGeom& g,
-                    const cx_t<T>* kin, cx_t<T>* ghat, cx_t<T>* kout, cudaStream_t s) {
-    int rc = launch_gather<T>(nodes, tile_start, g.nk, g.Pk, g.kwin, g.beta_k, kin, NodeIO<T>{ghat}, s);
-    if (rc) return rc;
-    return launch_scatter<T>(nodes, tile_start, g.nk, g.Pk, g.kwin, g.beta_k, NodeVal<T>{ghat}, kout, s);
+                    const cx_t<T>* kin, cx_t<T>* ghat, cx_t<T>* kout, cudaStream_t s, int nb) {
+    const long kb = static_cast<long>(g.nk) * g.nk;
+    for (int r = 0; r < nb; ++r) {   // fallback for stencils too wide for the fused kernel: one grid at a time
+        int rc = launch_gather<T>(nodes, tile_start, g.nk, g.Pk, g.kwin, g.beta_k, kin + r * kb, NodeIO<T>{ghat}, s);
+        if (rc) return rc;
+        rc = launch_scatter<T>(nodes, tile_start, g.nk, g.Pk, g.kwin, g.beta_k, NodeVal<T>{ghat}, kout + r * kb, s);
+        if (rc) return rc;
+    }
+    return SBD_OK;
 }
 
 void point_work_list(const std::vector<long long>& tile_start, std::vector<long long>& begin,
@@ -979,35 +1017,50 @@ void point_work_list(const std::vector<long long>& tile_start, std::vector<long 
     begin.push_back(tile_start.empty() ? 0 : tile_start.back());
 }
 
+// Right-hand sides per CTA of the point kernels: as many shared windows of `per` bytes as
+// fit a quarter of the SM's shared memory (four 256-thread CTAs stay resident), at most 4.
+inline int rhs_group(size_t per, int nrhs) {
+    int rg = static_cast<int>((56u * 1024u) / (per > 0 ? per : 1));
+    if (rg > 4) rg = 4;
+    if (rg > nrhs) rg = nrhs;
+    return rg < 1 ? 1 : rg;
+}
+
 template <typename T, int G, bool PK, bool RV>
 int launch_spread_chunks(const PointRec<T>* pts, const PointWork& work, const FarGeom& g, PointVal<T> val,
-                         cx_t<T>* grid, cudaStream_t s) {
+                         cx_t<T>* grid, int nrhs, long gstride, cudaStream_t s) {
     const Window<T> win = make_window<T>(g.swin, g.beta_s, g.Ps);
     const size_t W = kNodeTile + g.Ps - 1;
-    const size_t smem = (RV ? 1 : 2) * sizeof(T) * W * W;
+    const size_t per = (RV ? 1 : 2) * sizeof(T) * W * W;
+    const int rg = rhs_group(per, nrhs);
+    const size_t smem = per * rg;
     auto k = spread_chunks_kernel<T, G, PK, RV>;
     SBD_TRY(raise_smem_limit(k, smem));
-    k<<<work.count, 256, smem, s>>>(pts, work, tiles_per_side(g.m), g.m, g.Ps, win, val, grid);
+    const dim3 grd(static_cast<unsigned>(work.count), static_cast<unsigned>((nrhs + rg - 1) / rg));
+    k<<<grd, 256, smem, s>>>(pts, work, tiles_per_side(g.m), g.m, g.Ps, win, val, grid, nrhs, rg, gstride);
     SBD_LAUNCH_CHECK();
     return SBD_OK;
 }
 
 template <typename T, int G, bool PK>
 int launch_interp_chunks(const PointRec<T>* pts, const PointWork& work, const FarGeom& g, const cx_t<T>* grid,
-                         const PointOut<T>& out, cudaStream_t s) {
+                         const PointOut<T>& out, int nrhs, long gstride, cudaStream_t s) {
     const Window<T> win = make_window<T>(g.swin, g.beta_s, g.Ps);
     const size_t W = kNodeTile + g.Ps - 1;
-    const size_t smem = W * W * sizeof(cx_t<T>);
+    const size_t per = (PK ? 1 : 2) * sizeof(T) * W * W;
+    const int rg = rhs_group(per, nrhs);
+    const size_t smem = per * rg;
     auto k = interp_chunks_kernel<T, G, PK>;
     SBD_TRY(raise_smem_limit(k, smem));
-    k<<<work.count, 256, smem, s>>>(pts, work, tiles_per_side(g.m), g.m, g.Ps, win, grid, out);
+    const dim3 grd(static_cast<unsigned>(work.count), static_cast<unsigned>((nrhs + rg - 1) / rg));
+    k<<<grd, 256, smem, s>>>(pts, work, tiles_per_side(g.m), g.m, g.Ps, win, grid, out, nrhs, rg, gstride);
     SBD_LAUNCH_CHECK();
     return SBD_OK;
 }
 
 template <typename T>
 int spread_tiled(const PointRec<T>* pts, const int* perm, const PointWork& work, const FarGeom& g,
-                 const void* f, bool f_complex, cx_t<T>* grid, cudaStream_t s, bool packed) {
+                 const void* f, bool f_complex, cx_t<T>* grid, cudaStream_t s, bool packed, int nrhs, long n_pts) {
     if (packed && (f_complex || (g.m & 1))) {
         set_error("spread: a packed real grid needs real values and an even side");
         return SBD_EINVAL;
@@ -1016,31 +1069,41 @@ int spread_tiled(const PointRec<T>* pts, const int* perm, const PointWork& work,
         set_error("spread: stencil wider than 32 cells");
         return SBD_ENOTSUP;
     }
-    const size_t cells = static_cast<size_t>(g.m) * g.m;
-    SBD_CUDA_TRY(cudaMemsetAsync(grid, 0, packed ? sizeof(T) * cells : sizeof(cx_t<T>) * cells, s));
+    if (nrhs < 1 || nrhs > 65535 * 4) {
+        set_error("spread: right-hand sides out of range");
+        return SBD_EINVAL;
+    }
+    // grid b at b * cells complex elements (the packed real grid is half a complex grid)
+    const long cells = static_cast<long>(g.m) * g.m / (packed ? 2 : 1);
+    SBD_CUDA_TRY(cudaMemsetAsync(grid, 0, sizeof(cx_t<T>) * cells * nrhs, s));
     if (work.count <= 0) return SBD_OK;
-    const PointVal<T> val{f, perm, packed ? false : f_complex};
+    const PointVal<T> val{f, perm, packed ? false : f_complex, n_pts};
     const bool rv = packed || !f_complex;
     if (packed) {
-        if (g.Ps <= 8) return launch_spread_chunks<T, 8, true, true>(pts, work, g, val, grid, s);
-        if (g.Ps <= 16) return launch_spread_chunks<T, 16, true, true>(pts, work, g, val, grid, s);
-        return launch_spread_chunks<T, 32, true, true>(pts, work, g, val, grid, s);
+        if (g.Ps <= 8) return launch_spread_chunks<T, 8, true, true>(pts, work, g, val, grid, nrhs, cells, s);
+        if (g.Ps <= 16) return launch_spread_chunks<T, 16, true, true>(pts, work, g, val, grid, nrhs, cells, s);
+        return launch_spread_chunks<T, 32, true, true>(pts, work, g, val, grid, nrhs, cells, s);
     }
     if (rv) {
-        if (g.Ps <= 8) return launch_spread_chunks<T, 8, false, true>(pts, work, g, val, grid, s);
-        if (g.Ps <= 16) return launch_spread_chunks<T, 16, false, true>(pts, work, g, val, grid, s);
-        return launch_spread_chunks<T, 32, false, true>(pts, work, g, val, grid, s);
+        if (g.Ps <= 8) return launch_spread_chunks<T, 8, false, true>(pts, work, g, val, grid, nrhs, cells, s);
+        if (g.Ps <= 16) return launch_spread_chunks<T, 16, false, true>(pts, work, g, val, grid, nrhs, cells, s);
+        return launch_spread_chunks<T, 32, false, true>(pts, work, g, val, grid, nrhs, cells, s);
     }
-    if (g.Ps <= 8) return launch_spread_chunks<T, 8, false, false>(pts, work, g, val, grid, s);
-    if (g.Ps <= 16) return launch_spread_chunks<T, 16, false, false>(pts, work, g, val, grid, s);
-    return launch_spread_chunks<T, 32, false, false>(pts, work, g, val, grid, s);
+    if (g.Ps <= 8) return launch_spread_chunks<T, 8, false, false>(pts, work, g, val, grid, nrhs, cells, s);
+    if (g.Ps <= 16) return launch_spread_chunks<T, 16, false, false>(pts, work, g, val, grid, nrhs, cells, s);
+    return launch_spread_chunks<T, 32, false, false>(pts, work, g, val, grid, nrhs, cells, s);
 }
 
 template <typename T>
 int interp_tiled(const PointRec<T>* pts, const int* perm, const PointWork& work, const FarGeom& g,
                  const cx_t<T>* grid, double2 w0, const double2* sumf, void* q, bool q_complex, cudaStream_t s,
-                 bool packed, const void* add, int add_stride, int add_off) {
-    const PointOut<T> out{q, perm, q_complex, w0, sumf, add, add_stride, add_off};
+                 bool packed, const void* add, int add_stride, int nrhs, long n_pts) {
+    if (nrhs < 1 || nrhs > 65535 * 4) {
+        set_error("interp: right-hand sides out of range");
+        return SBD_EINVAL;
+    }
+    const PointOut<T> out{q, perm, q_complex, w0, sumf, add, add_stride, 0, n_pts};
+    const long cells = static_cast<long>(g.m) * g.m / (packed ? 2 : 1);
     if (packed && (q_complex || (g.m & 1))) {
         set_error("interp: a packed real grid needs real output and an even side");
         return SBD_EINVAL;
@@ -1051,13 +1114,13 @@ int interp_tiled(const PointRec<T>* pts, const int* perm, const PointWork& work,
     }
     if (work.count <= 0) return SBD_OK;
     if (packed) {
-        if (g.Ps <= 8) return launch_interp_chunks<T, 8, true>(pts, work, g, grid, out, s);
-        if (g.Ps <= 16) return launch_interp_chunks<T, 16, true>(pts, work, g, grid, out, s);
-        return launch_interp_chunks<T, 32, true>(pts, work, g, grid, out, s);
+        if (g.Ps <= 8) return launch_interp_chunks<T, 8, true>(pts, work, g, grid, out, nrhs, cells, s);
+        if (g.Ps <= 16) return launch_interp_chunks<T, 16, true>(pts, work, g, grid, out, nrhs, cells, s);
+        return launch_interp_chunks<T, 32, true>(pts, work, g, grid, out, nrhs, cells, s);
     }
-    if (g.Ps <= 8) return launch_interp_chunks<T, 8, false>(pts, work, g, grid, out, s);
-    if (g.Ps <= 16) return launch_interp_chunks<T, 16, false>(pts, work, g, grid, out, s);
-    return launch_interp_chunks<T, 32, false>(pts, work, g, grid, out, s);
+    if (g.Ps <= 8) return launch_interp_chunks<T, 8, false>(pts, work, g, grid, out, nrhs, cells, s);
+    if (g.Ps <= 16) return launch_interp_chunks<T, 16, false>(pts, work, g, grid, out, nrhs, cells, s);
+    return launch_interp_chunks<T, 32, false>(pts, work, g, grid, out, nrhs, cells, s);
 }
 
 template <typename T>
@@ -1082,16 +1145,16 @@ int fill_grid(cx_t<T>* x, long n, T re, T im, cudaStream_t s) {
     template int tile_sort<PointRec<T>>(const PointRec<T>*, long, int, PointRec<T>*, int*, long long*,       \
                                         cudaStream_t, bool);                                                 \
     template int node_step_tiled<T>(const NodeRec<T>*, const long long*, const FarGeom&, const cx_t<T>*,     \
-                                    cx_t<T>*, cx_t<T>*, cudaStream_t);                                       \
+                                    cx_t<T>*, cx_t<T>*, cudaStream_t, int);                                  \
     template size_t node_fused_smem<T>(int, int);                                                            \
     template int fill_grid<T>(cx_t<T>*, long, T, T, cudaStream_t);                                          \
     template int node_step_fused<T>(const NodeRec<T>*, const long long*, const FarGeom&, const cx_t<T>*,     \
-                                    cx_t<T>*, const NodeTuning&, cudaStream_t);                              \
+                                    cx_t<T>*, const NodeTuning&, cudaStream_t, int);                         \
     template int spread_tiled<T>(const PointRec<T>*, const int*, const PointWork&, const FarGeom&,           \
-                                 const void*, bool, cx_t<T>*, cudaStream_t, bool);                           \
+                                 const void*, bool, cx_t<T>*, cudaStream_t, bool, int, long);                \
     template int interp_tiled<T>(const PointRec<T>*, const int*, const PointWork&, const FarGeom&,           \
                                  const cx_t<T>*, double2, const double2*, void*, bool, cudaStream_t, bool,   \
-                                 const void*, int, int);
+                                 const void*, int, int, long);
 SBD_NODE_INST(float)
 SBD_NODE_INST(double)
 

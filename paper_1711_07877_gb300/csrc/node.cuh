@@ -23,9 +23,10 @@ int tile_sort(const Rec* in, long n_rec, int n, Rec* sorted, int* perm, long lon
               bool by_bin = false);
 
 // kout (nk x nk, fully written) = scatter(omega' * gather(kin)); ghat is n_xi scratch.
+// nb grids (right-hand sides), nk^2 elements apart, one after the other.
 template <typename T>
 int node_step_tiled(const NodeRec<T>* nodes, const long long* tile_start, const FarGeom& g,
-                    const cx_t<T>* kin, cx_t<T>* ghat, cx_t<T>* kout, cudaStream_t s);
+                    const cx_t<T>* kin, cx_t<T>* ghat, cx_t<T>* kout, cudaStream_t s, int nb = 1);
 
 // Variant of the fused node kernel (see node.cu): acc 0 = two float planes with
 // atomicAdd, 1 = one float2 plane with a 64-bit compare-and-swap (FP32 only), 2 = int64
@@ -44,12 +45,13 @@ template <typename T>
 int fill_grid(cx_t<T>* x, long n, T re, T im, cudaStream_t s);
 
 // The same in one kernel per tile: gather, weight and scatter into a shared accumulator,
-// whose overlap band is added atomically into kout (cleared here).
+// whose overlap band is added atomically into kout (cleared here).  nb grids (right-hand
+// sides, nk^2 elements apart) in one launch: blockIdx.y is the right-hand side.
 template <typename T>
 size_t node_fused_smem(int Pk, int acc = 0);   // dynamic shared memory of the fused kernel
 template <typename T>
 int node_step_fused(const NodeRec<T>* nodes, const long long* tile_start, const FarGeom& g,
-                    const cx_t<T>* kin, cx_t<T>* kout, const NodeTuning& t, cudaStream_t s);
+                    const cx_t<T>* kin, cx_t<T>* kout, const NodeTuning& t, cudaStream_t s, int nb = 1);
 
 // Work list of the point kernels (spreading, interpolation): item w is the records
 // [begin[w], begin[w + 1]) of the 64 x 64 tile tile[w], at most kPointChunk of them; the
@@ -69,16 +71,20 @@ void point_work_list(const std::vector<long long>& tile_start, std::vector<long 
 // packed: real f into a real grid stored as packed row pairs (m / 2 x m complex,
 // cell (R, c) = component R & 1 of element (R >> 1, c)).  The grid is cleared, then each
 // work item accumulates its chunk in shared memory and adds the cells it reached into the
-// grid with global atomics.
+// grid with global atomics.  nrhs right-hand sides in one launch: f[r * n_pts + l] goes to
+// grid r at grid + r m^2; a CTA takes a group of them (window weights evaluated once per
+// record for the group).
 template <typename T>
 int spread_tiled(const PointRec<T>* pts, const int* perm, const PointWork& work, const FarGeom& g,
-                 const void* f, bool f_complex, cx_t<T>* grid, cudaStream_t s, bool packed = false);
+                 const void* f, bool f_complex, cx_t<T>* grid, cudaStream_t s, bool packed = false, int nrhs = 1,
+                 long n_pts = 0);
 
-// q[perm[i]] = interpolation of grid at point i + w0 * sumf[0] (float64 or complex128 out)
-// + add[i * add_stride + add_off] when add is given (same type as q, record order).
+// q[r * n_pts + perm[i]] = interpolation of grid r (at grid + r m^2) at point i
+// + w0 * sumf[r] (float64 or complex128 out) + add[i * add_stride + r] when add is given
+// (same type as q, record order), for r < nrhs, in one launch.
 template <typename T>
 int interp_tiled(const PointRec<T>* pts, const int* perm, const PointWork& work, const FarGeom& g,
                  const cx_t<T>* grid, double2 w0, const double2* sumf, void* q, bool q_complex, cudaStream_t s,
-                 bool packed = false, const void* add = nullptr, int add_stride = 1, int add_off = 0);
+                 bool packed = false, const void* add = nullptr, int add_stride = 1, int nrhs = 1, long n_pts = 0);
 
 }  // namespace sbd

@@ -16,11 +16,15 @@ def test_spmv_bytes_follow_the_stored_value_type():
     n = 10_000
     fp32 = bench.stage_bytes(INFO, n, 1, "fp32", esz=8)["spmv"]
     fp64 = bench.stage_bytes(INFO, n, 1, "fp64", esz=8)["spmv"]
-    # column index 4 B + value 4 B (FP32 form) or 8 B (FP64 form) per non-zero
-    assert fp64 - fp32 == 4 * INFO["nnz"]
-    assert fp32 == 8 * INFO["nnz"] + 8 * (n + 1) + 2 * 8 * n
-    helm32 = bench.stage_bytes(INFO, n, 1, "fp32", esz=16)["spmv"]
+    near32 = bench.stage_bytes(INFO, n, 1, "fp32", esz=8, near32=True)["spmv"]
+    # D is float64 in both forms (column index 4 B + value 8 B per non-zero); the
+    # float32-D flag stores 4 B values
+    assert fp64 == fp32 == 12 * INFO["nnz"] + 8 * (n + 1) + 2 * 8 * n
+    assert fp32 - near32 == 4 * INFO["nnz"]
+    helm32 = bench.stage_bytes(INFO, n, 1, "fp32", esz=16, near32=True)["spmv"]
     assert helm32 == (4 + 8) * INFO["nnz"] + 8 * (n + 1) + 2 * 16 * n
+    helm = bench.stage_bytes(INFO, n, 1, "fp32", esz=16)["spmv"]
+    assert helm == (4 + 16) * INFO["nnz"] + 8 * (n + 1) + 2 * 16 * n
 
 
 def test_laplace_steps_count_half_the_grid_and_records():
