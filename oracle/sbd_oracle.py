@@ -351,6 +351,9 @@ class OraclePlan:
     omega: np.ndarray       # (N_xi,) complex
     pairs: tuple | None = None
     D: np.ndarray | None = None   # values per pair (k, l), aligned with pairs
+    x: np.ndarray | None = None   # targets, when they differ from the sources (make_plan_st)
+    y: np.ndarray | None = None   # sources (make_plan_st)
+    D_st: tuple | None = None     # rectangular close matrix (close_matrix_st)
 
 
 def make_plan(z: np.ndarray, kind: str, delta_min: float, eps: float, kappa: float = 0.0,
@@ -508,6 +511,89 @@ def sbd_matvec(plan: OraclePlan, f: np.ndarray) -> np.ndarray:
     if f.ndim == 2:
         return np.stack([sbd_matvec(plan, fi) for fi in f])
     q = far_part(plan, f) + close_part(plan, f)
+    if plan.kind == "laplace" and not np.iscomplexobj(f):
+        return q.real
+    return q
+
+
+# ---------------------------------------------------------------------------
+# Separate targets and sources (Sec. 7.1 and Table 2: q_k = sum_l G(x_k - y_l) f_l for two
+# independent point sets x and y)
+# ---------------------------------------------------------------------------
+
+def direct_sum_st(x: np.ndarray, y: np.ndarray, f: np.ndarray, kind: str, kappa: float = 0.0,
+                  targets: np.ndarray | None = None, chunk: int = 512) -> np.ndarray:
+    """q_k = sum_l G(x_k - y_l) f_l over all sources y_l, for targets x_k (Sec. 7.1).
+
+    A target that coincides with a source takes no contribution from it (reading R1 carried
+    over: G is singular there; with x = y this is Eq. discreteConv).  ``targets`` (indices
+    into x) restricts k; f may be (N_y,) or (nrhs, N_y).
+    """
+    x = np.asarray(x, dtype=np.float64)
+    y = np.asarray(y, dtype=np.float64)
+    f = np.asarray(f)
+    single = f.ndim == 1
+    F = f[None, :] if single else f
+    idx = np.arange(len(x)) if targets is None else np.asarray(targets)
+    out_dtype = np.complex128 if (kind == "helmholtz" or np.iscomplexobj(F)) else np.float64
+    q = np.zeros((F.shape[0], len(idx)), dtype=out_dtype)
+    for s in range(0, len(idx), chunk):
+        ks = idx[s:s + chunk]
+        d = np.hypot(x[ks, 0][:, None] - y[None, :, 0], x[ks, 1][:, None] - y[None, :, 1])
+        zero = d == 0.0
+        g = kernel_G(np.where(zero, 1.0, d), kind, kappa)
+        g = np.where(zero, 0.0, g)
+        q[:, s:s + len(ks)] = (g @ F.T).T
+    return q[0] if single else q
+
+
+def make_plan_st(x: np.ndarray, y: np.ndarray, kind: str, delta_min: float, eps: float, kappa: float = 0.0,
+                 P: int | None = None) -> OraclePlan:
+    """Off-line part for targets x and sources y: the fit, circles and weights of make_plan
+    taken for the union of the two sets, whose delta_max (R2) bounds every |x_k - y_l|."""
+    x = np.asarray(x, dtype=np.float64)
+    y = np.asarray(y, dtype=np.float64)
+    pl = make_plan(np.concatenate([x, y]), kind, delta_min, eps, kappa, P=P)
+    pl.x, pl.y = x, y
+    return pl
+
+
+def near_pairs_st(x: np.ndarray, y: np.ndarray, delta_min: float):
+    """All pairs (k, l) with |x_k - y_l| <= delta_min (R8), by brute force, coincident ones included."""
+    rows, cols = [], []
+    for s in range(0, len(x), 1024):
+        d2 = (x[s:s + 1024, 0][:, None] - y[None, :, 0]) ** 2 + (x[s:s + 1024, 1][:, None] - y[None, :, 1]) ** 2
+        k, l = np.nonzero(d2 <= delta_min * delta_min)
+        rows.append(k + s)
+        cols.append(l)
+    return np.concatenate(rows), np.concatenate(cols)
+
+
+def close_matrix_st(plan: OraclePlan):
+    """Rectangular D of Eq. (defD): G(x_k - y_l) - G_approx(x_k - y_l) on near pairs, with G taken
+    as 0 at distance 0 (so that D_kl = -G_approx(0) cancels the far part there, as the diagonal
+    of the square case does).  Returns (rows, cols, values)."""
+    k, l = near_pairs_st(plan.x, plan.y, plan.delta_min)
+    d = plan.x[k] - plan.y[l]
+    r = np.hypot(d[:, 0], d[:, 1])
+    gap = g_approx_direct(d, plan.xi, plan.omega)
+    zero = r == 0.0
+    gval = np.where(zero, 0.0, kernel_G(np.where(zero, 1.0, r), plan.kind, plan.kappa))
+    return k, l, gval - gap
+
+
+def sbd_matvec_st(plan: OraclePlan, f: np.ndarray) -> np.ndarray:
+    """q = NUFFT_+[x, xi](omega_hat . NUFFT_-[y, xi](f)) + D f (Sec. 1 on-line part with the
+    sources y in the forward transform and the targets x in the backward one)."""
+    f = np.asarray(f)
+    if f.ndim == 2:
+        return np.stack([sbd_matvec_st(plan, fi) for fi in f])
+    fhat = nufft_direct(plan.y, plan.xi, f, -1)                  # (i)  sources -> Fourier
+    q = nufft_direct(plan.xi, plan.x, plan.omega * fhat, +1)     # (ii), (iii) Fourier -> targets
+    if plan.D_st is None:
+        plan.D_st = close_matrix_st(plan)
+    rows, cols, vals = plan.D_st
+    np.add.at(q, rows, vals * f[cols])
     if plan.kind == "laplace" and not np.iscomplexobj(f):
         return q.real
     return q

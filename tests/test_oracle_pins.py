@@ -321,6 +321,102 @@ def test_sbd_config1_shape():
     assert 5000 < len(pl.xi) < 15000
 
 
+# --- Sec. 7.1 / Table 2: separate targets and sources ------------------------------------------
+
+def test_direct_sum_st_bruteforce_tiny():
+    rng = np.random.default_rng(21)
+    x = rng.uniform(0, 1, (6, 2))
+    y = rng.uniform(0, 1, (9, 2))
+    y[3] = x[0]                                   # a coincident target / source pair takes no term
+    f = rng.standard_normal(9) + 1j * rng.standard_normal(9)
+    q = O.direct_sum_st(x, y, f, "laplace")
+    qh = O.direct_sum_st(x, y, f, "helmholtz", 7.0)
+    for k in range(6):
+        want = sum(-math.log(math.hypot(*(x[k] - y[l]))) / (2 * math.pi) * f[l]
+                   for l in range(9) if not np.array_equal(x[k], y[l]))
+        want_h = sum(complex(0.25j * mpmath.hankel1(0, 7.0 * math.hypot(*(x[k] - y[l])))) * f[l]
+                     for l in range(9) if not np.array_equal(x[k], y[l]))
+        assert abs(q[k] - want) < 1e-13 * max(1.0, abs(want))
+        assert abs(qh[k] - want_h) < 1e-12 * max(1.0, abs(want_h))
+
+
+def test_direct_sum_st_with_equal_sets_is_the_square_sum():
+    z = W.disk_points(300, 22)
+    f = W.rhs(300, 23)
+    assert np.max(np.abs(O.direct_sum_st(z, z, f, "laplace") - O.direct_sum(z, f, "laplace"))) < 1e-12
+
+
+def test_near_pairs_st_against_kdtree():
+    from scipy.spatial import cKDTree
+    x = W.square_points(300, 24)
+    y = W.square_points(500, 25)
+    r = 0.06
+    k, l = O.near_pairs_st(x, y, r)
+    got = set(zip(k.tolist(), l.tolist()))
+    hits = cKDTree(y).query_ball_point(x, r * (1 + 1e-12))
+    want = {(i, j) for i, js in enumerate(hits) for j in js if math.hypot(*(x[i] - y[j])) <= r}
+    assert got == want and len(want) > 1000
+
+
+@pytest.fixture(scope="module")
+def st_case():
+    x = W.square_points(400, 26)
+    y = W.square_points(600, 27)
+    f = W.rhs(600, 28)
+    return x, y, f, O.direct_sum_st(x, y, f, "laplace")
+
+
+@pytest.mark.parametrize("eps", [1e-3, 1e-6])
+def test_sbd_st_laplace_within_eps(st_case, eps):
+    x, y, f, qd = st_case
+    pl = O.make_plan_st(x, y, "laplace", 0.07, eps)
+    q = O.sbd_matvec_st(pl, f)
+    assert q.shape == (400,)
+    assert np.max(np.abs(q - qd)) <= eps * np.abs(f).sum()          # Sec. 1 output bound
+
+
+def test_sbd_st_helmholtz_within_eps():
+    x = W.square_points(250, 29)
+    y = W.square_points(350, 30)
+    f = W.rhs(350, 31, complex_valued=True)
+    pl = O.make_plan_st(x, y, "helmholtz", 0.08, 1e-6, kappa=30.0)
+    qd = O.direct_sum_st(x, y, f, "helmholtz", 30.0)
+    assert np.max(np.abs(O.sbd_matvec_st(pl, f) - qd)) <= 1e-6 * np.abs(f).sum()
+
+
+def test_sbd_st_adjoint_and_square_reduction(st_case):
+    x, y, f, _ = st_case
+    g = W.rhs(400, 32)
+    # G is even, so the x <- y operator is the transpose of the y <- x one; both plans fit the
+    # same union, hence share every weight and frequency
+    pxy = O.make_plan_st(x, y, "laplace", 0.07, 1e-6)
+    pyx = O.make_plan_st(y, x, "laplace", 0.07, 1e-6)
+    assert pxy.P == pyx.P and np.array_equal(pxy.M, pyx.M)
+    lhs = g @ O.sbd_matvec_st(pxy, f)
+    rhs = f @ O.sbd_matvec_st(pyx, g)
+    assert abs(lhs - rhs) < 1e-10 * (np.abs(g).sum() + np.abs(f).sum())
+    # with x = y the rectangular matvec is the square one (coincident pairs = the diagonal)
+    z = W.disk_points(300, 33)
+    fz = W.rhs(300, 34)
+    p1 = O.make_plan(z, "laplace", 0.1, 1e-6)
+    p2 = O.make_plan_st(z, z, "laplace", 0.1, 1e-6)
+    assert np.max(np.abs(O.sbd_matvec_st(p2, fz) - O.sbd_matvec(p1, fz))) < 1e-11 * np.abs(fz).sum()
+
+
+def test_planted_swapped_point_sets_are_caught():
+    # the forward transform taken over the targets instead of the sources (equal set sizes, so
+    # the mistake runs): the result leaves the Sec. 1 output bound
+    x = W.square_points(400, 26)
+    y = W.square_points(400, 36)
+    f = W.rhs(400, 37)
+    qd = O.direct_sum_st(x, y, f, "laplace")
+    pl = O.make_plan_st(x, y, "laplace", 0.07, 1e-6)
+    assert np.max(np.abs(O.sbd_matvec_st(pl, f) - qd)) <= 1e-6 * np.abs(f).sum()
+    pl.y = x
+    pl.D_st = None
+    assert np.max(np.abs(O.sbd_matvec_st(pl, f) - qd)) > 1e-6 * np.abs(f).sum()
+
+
 # --- planted mistakes: each must break a pin ---------------------------------------------------
 
 def test_planted_sign_error_in_rhs_is_caught(laplace_case, monkeypatch):

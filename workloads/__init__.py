@@ -124,6 +124,7 @@ class Workload:
     delta_min: float
     eps: float
     meta: dict = field(default_factory=dict)
+    y: np.ndarray | None = None   # sources when they differ from the targets z (else None)
 
 
 def laplace_disk(n: int = 2000, seed: int = 1, eps: float = 1e-6, neighbours: float = 20.0) -> Workload:
@@ -164,6 +165,18 @@ def laplace_square(n: int = 10_000_000, seed: int = 4, eps: float = 1e-6, nrhs: 
     delta_min = math.sqrt(neighbours / (math.pi * n))
     return Workload(f"laplace_square_n{n}", z, f, "laplace", 0.0, delta_min, eps,
                     {"seed": seed, "nrhs": nrhs})
+
+
+def laplace_square_st(n: int = 1_000_000, seed: int = 6, eps: float = 1e-6, alpha: float = 0.0) -> Workload:
+    """Laplace kernel with separate targets and sources (the Sec. 7.1 / Table 2 setting): targets
+    z and sources y, each N points uniform in [0,1]^2 and drawn independently, f ~ N(0, 1) on the
+    sources, delta_min by Theorem 1 with delta_max bounding the union of the two sets."""
+    x = square_points(n, seed)
+    y = square_points(n, seed + 500)
+    f = rhs(n, seed + 1000)
+    dmax = enclosing_diameter(np.concatenate([x, y]))
+    return Workload(f"laplace_square_st_n{n}", x, f, "laplace", 0.0, theorem1_delta_min(n, eps, dmax, alpha), eps,
+                    {"seed": seed, "delta_max": dmax, "alpha": alpha}, y=y)
 
 
 def serve_requests(count: int = 256, seed: int = 5, n_lo: int = 1_000, n_hi: int = 1_000_000, eps: float = 1e-6,
