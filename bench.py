@@ -10,9 +10,10 @@ one sbd_matvec over the whole point set, inputs resident in HBM.  The grids
 The default line also carries (N = 1 only, after the headline's timed region):
 balanced_delta_min (delta_min by measurement), near_fp32 (the same plan with D f in
 float32), fp64_form (the same workload in the FP64 form), helmholtz (kappa delta_max
-= 500, FP32 and FP64 forms), served (a short serving run: p50/p99 latency with a
-queue / plan / solve breakdown), and cpu_baseline (the oracle's direct sum over all
-host cores, plus the oracle SBD timed on the N = 2000 disk).
+= 500, FP32 and FP64 forms), table2 (separate targets and sources, the Table 2 setting),
+served (a short serving run: p50/p99 latency with a queue / plan / solve breakdown), and
+cpu_baseline (the oracle's direct sum over all host cores, plus the oracle SBD timed on
+the N = 2000 disk).
 
   python bench.py [--gpus N --steps K --warmup W] [--form fp32|fp64] [--impl reference]
 
@@ -167,26 +168,27 @@ def stage_bytes(info, n, nrhs, form, esz=8, near32=False):
     m, nk, nxi, nnz, P = info["grid_x"], info["grid_k"], info["n_xi"], info["nnz"], info["stencil_x"]
     touched = min(m * m, n * P * P)
     vb = (16 if esz == 16 else 8) // (2 if near32 else 1)   # D value: complex for Helmholtz, float32 with the flag
+    r = nrhs   # every step takes all right-hand sides in one launch: grid and value terms scale with r
     if esz == 8:
         # Laplace: real spreading grid (half a complex element per cell), Hermitian K of
         # which the half plane kx >= 0 is transformed, half the node records
         return {
-            "sum": esz * n * nrhs,
-            "spread": pr * n + esz * n + c * m * m // 2,
-            "fft_fwd": c * (m * m // 2 + nk * nk // 2),
-            "node": nr * info["n_records"] + c * nk * nk,
-            "fft_inv": c * (nk * nk // 2 + m * m // 2),
-            "interp": pr * n + esz * n + c * touched // 2,
-            "spmv": (4 + vb) * nnz + 8 * (n + 1) + 2 * esz * n * nrhs,
+            "sum": esz * n * r,
+            "spread": pr * n + (esz * n + c * m * m // 2) * r,
+            "fft_fwd": c * (m * m // 2 + nk * nk // 2) * r,
+            "node": nr * info["n_records"] + c * nk * nk * r,
+            "fft_inv": c * (nk * nk // 2 + m * m // 2) * r,
+            "interp": pr * n + (esz * n + c * touched // 2) * r,
+            "spmv": (4 + vb) * nnz + 8 * (n + 1) + 2 * esz * n * r,
         }
     return {
-        "sum": esz * n * nrhs,
-        "spread": pr * n + esz * n + c * m * m,
-        "fft_fwd": c * (m * m + nk * nk),
-        "node": nr * nxi + 2 * c * nk * nk,
-        "fft_inv": c * (nk * nk + m * m),
-        "interp": pr * n + esz * n + c * touched,
-        "spmv": (4 + vb) * nnz + 8 * (n + 1) + 2 * esz * n * nrhs,
+        "sum": esz * n * r,
+        "spread": pr * n + (esz * n + c * m * m) * r,
+        "fft_fwd": c * (m * m + nk * nk) * r,
+        "node": nr * nxi + 2 * c * nk * nk * r,
+        "fft_inv": c * (nk * nk + m * m) * r,
+        "interp": pr * n + (esz * n + c * touched) * r,
+        "spmv": (4 + vb) * nnz + 8 * (n + 1) + 2 * esz * n * r,
     }
 
 
@@ -224,22 +226,25 @@ _THREAD_VARS = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
 _ORACLE_DATA = None
 
 
-def _oracle_init(z, f, kind, kappa):
+def _oracle_init(z, f, kind, kappa, y):
     global _ORACLE_DATA
-    _ORACLE_DATA = (z, f, kind, kappa)
+    _ORACLE_DATA = (z, f, kind, kappa, y)
 
 
 def _oracle_direct(idx):
     from oracle import sbd_oracle as O
-    z, f, kind, kappa = _ORACLE_DATA
+    z, f, kind, kappa, y = _ORACLE_DATA
+    if y is not None:
+        return O.direct_sum_st(z, y, f, kind, kappa, targets=idx, chunk=16)
     return O.direct_sum(z, f, kind, kappa, targets=idx, chunk=16)
 
 
 class OraclePool:
     """The oracle's direct sum over the host cores: one spawned worker process per core (single-
-    threaded numpy each), every worker holding the points and f, targets split evenly."""
+    threaded numpy each), every worker holding the points and f, targets split evenly.  With y
+    given, z are the targets and y the sources (the direct sum of separate sets)."""
 
-    def __init__(self, z, f, kind="laplace", kappa=0.0, cores=None):
+    def __init__(self, z, f, kind="laplace", kappa=0.0, cores=None, y=None):
         import multiprocessing as mp
         self.cores = max(1, cores or os.cpu_count() or 1)
         saved = {k: os.environ.get(k) for k in _THREAD_VARS}
@@ -247,14 +252,14 @@ class OraclePool:
             os.environ[k] = "1"
         try:
             self.pool = mp.get_context("spawn").Pool(self.cores, initializer=_oracle_init,
-                                                      initargs=(z, f, kind, kappa))
+                                                      initargs=(z, f, kind, kappa, y))
         finally:
             for k, v in saved.items():
                 if v is None:
                     os.environ.pop(k, None)
                 else:
                     os.environ[k] = v
-        self.n = len(z)
+        self.n = len(z) if y is None else len(y)      # sources: pairs per target
         self.nrhs = 1 if np.ndim(f) == 1 else f.shape[0]
         self.pool.map(_oracle_direct, [np.array([i]) for i in range(self.cores)], chunksize=1)   # warm
 
@@ -579,9 +584,9 @@ def main():
            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32" if args.form == "fp32" else "f64", "data": "synthetic",
            "config": workload_config(args, rank), "clocks": clk, "e2e": e2e,
-           # per matvec: f gather, D f, sum of f, then per right-hand side spread, 2 x (2 row FFTs
-           # + transpose) around the node step, and the interpolation (the ncu launch list shows 12)
-           "gpu_launches": (3 + 9 * nrhs) * args.steps, "roofline": roofline, "stages": stages,
+           # per matvec, all right-hand sides together: f gather, D f, sum of f, spread, 2 x (2 row
+           # FFTs + transpose) around the node step, and the interpolation (the ncu launch list shows 12)
+           "gpu_launches": 12 * args.steps, "roofline": roofline, "stages": stages,
            "fft_comparison": fft_cmp, "balanced_delta_min": balanced,
            "plan": dict({k: info[k] for k in ("P", "n_xi", "n_records", "nnz", "grid_x", "grid_k", "fft_n",
                                               "stencil_x", "stencil_k", "nufft_tol", "fit_err", "device_bytes",
@@ -612,6 +617,7 @@ def main():
     torch.cuda.empty_cache()
     if extra and args.workload == "laplace_curves":
         out["helmholtz"] = helmholtz_lines(S, torch, stream, args)
+        out["table2"] = table2_line(S, torch, stream, args)
         out["served"] = run_serve(args, rank, world, local, requests=args.served_requests, short=True)
     if rank == 0:
         print(json.dumps(out))
@@ -652,6 +658,52 @@ def form_line(S, torch, stream, zt, ft, wl, args, nrhs, esz, form, pool, idx, qr
         return line
     finally:
         r.close()
+
+
+def table2_line(S, torch, stream, args):
+    """Separate targets and sources, the Sec. 7.1 / Table 2 benchmark: N targets and N sources
+    uniform in the unit square (independent), Laplace, FP32 form, delta_min by Theorem 1."""
+    import workloads as W
+    wl = W.laplace_square_st(args.n, 6, args.eps)
+    xt = torch.from_numpy(wl.z).cuda()
+    yt = torch.from_numpy(wl.y).cuda()
+    ft = torch.from_numpy(np.ascontiguousarray(wl.f)).cuda()
+    plan = S.sbd_plan_st(xt, args.n, yt, args.n, S.SBD_LAPLACE, 0.0, wl.delta_min, wl.eps,
+                         S.make_options(form=S.SBD_FORM_FP32))
+    try:
+        S.sbd_tune(plan, 3, stream.cuda_stream)
+        info = S.sbd_plan_info(plan)
+        q = torch.empty(args.n, dtype=torch.float64, device="cuda")
+        for _ in range(2):
+            S.sbd_matvec(plan, ft, q, 1, stream.cuda_stream)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        steps = min(args.steps, 10)
+        e0.record(stream)
+        for _ in range(steps):
+            S.sbd_matvec(plan, ft, q, 1, stream.cuda_stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        out = {"workload": f"laplace_square_st N={args.n} targets and N sources uniform in [0,1]^2 (independent), "
+                           f"eps={args.eps:g}, FP32 form, delta_min by Theorem 1 alpha=0",
+               "ms_per_step": ms, "value": args.n / (ms * 1e-3) / 1e9, "unit": UNIT,
+               "plan": plan_keys(info),
+               "paper_table2": {"N": 1_000_000, "online_s": 2.6, "hardware": "a laptop at 1.6 GHz, 32 GB (Table 2)",
+                                "note": "context only: another machine, precision and eps not stated"}}
+        if not args.no_cpu_baseline:
+            idx = np.random.default_rng(13).choice(args.n, 64, replace=False)
+            pool = OraclePool(wl.z, wl.f, "laplace", 0.0, y=wl.y)
+            try:
+                qref, _, _ = pool.direct_sum(idx)
+            finally:
+                pool.close()
+            out["accuracy"] = accuracy(q.cpu().numpy(), qref, wl.f, idx)
+        return out
+    finally:
+        S.sbd_destroy(plan)
+        del xt, yt, ft
+        torch.cuda.empty_cache()
 
 
 def helmholtz_lines(S, torch, stream, args):

@@ -136,6 +136,9 @@ typedef struct {
     int32_t node_sched;      /* fused node-kernel variant (sbd_tune): record schedule */
     int32_t fft_split;       /* row-FFT phases (sbd_tune): 0 one where it fits, 2 always two */
     int32_t node_binned;     /* 1 when the binned node kernel (acc 3) applies to the plan */
+    int64_t n_targets;       /* targets (rows of D, length of q): n_points unless sbd_plan_st */
+    int32_t separate_targets;/* 1 for a plan of sbd_plan_st */
+    int32_t reserved2;
 } sbd_plan_stats;
 
 /* ---------------------------------------------------------------------------------
@@ -157,9 +160,32 @@ int sbd_plan(const double* points, int64_t n, sbd_kernel kernel, double delta_mi
              double eps, const sbd_options* opt, void* cuda_stream, sbd_plan_t* out);
 
 /* ---------------------------------------------------------------------------------
+ * sbd_plan_st - the off-line part for separate targets and sources (Sec. 7.1 and Table 2:
+ * q_k = sum_l G(x_k - y_l) f_l for two independent point sets; the sound-cancelling example
+ * of Sec. 7.2 evaluates sources on a separate zone the same way).
+ *   targets    device, n_targets x 2 float64 (x_k), copied.
+ *   sources    device, n_sources x 2 float64 (y_l), copied.
+ *   kernel, delta_min, eps, opt, cuda_stream, out   as for sbd_plan.
+ * The fit is the one sbd_plan makes for the union of the two sets (delta_max = 2 max |z - c|
+ * over both, c the centre of their joint bounding box), so every |x_k - y_l| is covered.
+ * The forward transform takes the sources, the backward one the targets, and D is the
+ * n_targets x n_sources matrix of Eq. defD over the pairs with |x_k - y_l| <= delta_min; a
+ * target that coincides with a source takes no G term from it (reading R1 carried over: D
+ * holds -G_approx(0) there, counted in n_coincident).
+ * sbd_matvec / sbd_far / sbd_close / sbd_matvec_graph then read f with n_sources entries per
+ * right-hand side and write q with n_targets entries; sbd_nufft_minus takes f on the sources,
+ * sbd_nufft_plus writes q on the targets.  sbd_gmres rejects such a plan (not a square system).
+ * Errors: as sbd_plan (SBD_EINVAL also for null targets or n_targets < 1).
+ * ------------------------------------------------------------------------------- */
+int sbd_plan_st(const double* targets, int64_t n_targets, const double* sources, int64_t n_sources,
+                sbd_kernel kernel, double delta_min, double eps, const sbd_options* opt, void* cuda_stream,
+                sbd_plan_t* out);
+
+/* ---------------------------------------------------------------------------------
  * sbd_matvec - on-line part (Sec. 1 "On-line part"; Sec. 6.2; Eq. far convolution):
  * q = NUFFT_+(omega_hat . NUFFT_-(f)) + D f for nrhs right-hand sides.
- *   f, q   device, nrhs x N (float64 for Laplace, complex128 for Helmholtz);
+ *   f, q   device, nrhs x N (float64 for Laplace, complex128 for Helmholtz; for a plan of
+ *          sbd_plan_st f has n_sources and q n_targets entries per right-hand side);
  *          q is overwritten, f is read only; f and q must not overlap.
  *   nrhs   1 <= nrhs <= max_nrhs of the plan's options.  Every step takes all nrhs
  *          right-hand sides in one launch (the plan's grids hold max_nrhs of each).
@@ -234,10 +260,11 @@ int sbd_plan_info(sbd_plan_t plan, sbd_plan_stats* out);
 int sbd_plan_export(sbd_plan_t plan, int64_t cap, double* rho, double* alpha, int32_t* M,
                     double* radius, double* weight_re, double* weight_im);
 
-/* Copy D (Eq. defD) to host CSR arrays: rowptr (N + 1), col (nnz), val (nnz float64
+/* Copy D (Eq. defD) to host CSR arrays: rowptr (n_targets + 1), col (nnz), val (nnz float64
  * for Laplace, 2 nnz float64 = complex128 for Helmholtz; a plan made with
- * SBD_FLAG_NEAR_FP32 gives the float32 values it stores, widened).  Rows are in the
- * caller's point order, each row's diagonal first, then by column.  Synchronous. */
+ * SBD_FLAG_NEAR_FP32 gives the float32 values it stores, widened).  Rows (targets) and
+ * columns (sources) are in the caller's point orders; each row holds its diagonal first
+ * (plans of one point set), then its columns in increasing order.  Synchronous. */
 int sbd_close_export(sbd_plan_t plan, int64_t* rowptr, int32_t* col, double* val);
 
 /* Release the plan (NULL is accepted).  sbd_destroy first waits for the whole device, so

@@ -86,10 +86,17 @@ struct sbd_plan_s {
     long long n_rec = 0;               // node records: N_xi, or N_xi / 2 with half_nodes
     int* pt_perm = nullptr;            // sorted point record -> original point index (the
                                        // internal order of D's rows and columns)
+    // separate targets (sbd_plan_st): their own records for the interpolation, D's rows in
+    // their internal order; for a plan of one point set these alias the source records
+    bool separate = false;
+    long n_tgt = 0;
+    double* zt = nullptr;
+    void* tpts = nullptr;
+    int* tpt_perm = nullptr;
+    PointWork tpt_work{nullptr, nullptr, 0};
     void* f_int = nullptr;             // f in internal order, right-hand sides interleaved
     void* q_int = nullptr;             // D f in internal order, interleaved
     bool d32 = false;                  // D's values and f_int in FP32 (SBD_FLAG_NEAR_FP32)
-    long long* pt_tile_start = nullptr;
     PointWork pt_work{nullptr, nullptr, 0};   // chunks of the point records (spread, interp)
     long long* node_tile_start = nullptr;
     void* ghat = nullptr;              // n_xi weighted node values (scratch of the two-kernel node step)
@@ -250,6 +257,38 @@ SpreadDeconv spread_deconv_of(const sbd_plan_s* p) {
     return SpreadDeconv{p->psi, static_cast<int>(p->np.psi.size()), 1.0 / (p->np.kmax * p->np.kmax), p->np.h};
 }
 
+// Records of n points z (stencil start cell and fraction on the spreading grid), sorted by
+// 64 x 64 tile (perm: record -> point index), and the work list of the point kernels: each
+// tile's records in chunks of at most kPointChunk.
+template <typename T>
+int point_records(sbd_plan_s* p, const double* z, long n, void** recs, int** perm, PointWork* work, cudaStream_t s) {
+    const NufftParams& np = p->np;
+    PointRec<T>* pts0 = nullptr;
+    SBD_CUDA_TRY(cudaMallocAsync(&pts0, sizeof(PointRec<T>) * n, s));
+    int rc = far_prepare_points<T>(z, n, np.cx, np.cy, np.h, np.m, np.Ps, pts0, s);
+    if (rc) return rc;
+    const int ntm = (np.m + kNodeTile - 1) / kNodeTile;
+    long long* tile_start = nullptr;
+    if ((rc = dev_alloc(p, recs, sizeof(PointRec<T>) * n))) return rc;
+    if ((rc = dev_alloc(p, reinterpret_cast<void**>(perm), sizeof(int) * n))) return rc;
+    if ((rc = dev_alloc(p, reinterpret_cast<void**>(&tile_start),
+                        sizeof(long long) * (static_cast<size_t>(ntm) * ntm + 1)))) return rc;
+    if ((rc = tile_sort<PointRec<T>>(pts0, n, np.m, static_cast<PointRec<T>*>(*recs), *perm, tile_start, s)))
+        return rc;
+    SBD_CUDA_TRY(cudaFreeAsync(pts0, s));
+    std::vector<long long> ts(static_cast<size_t>(ntm) * ntm + 1), wb;
+    std::vector<int> wt;
+    SBD_CUDA_TRY(cudaMemcpyAsync(ts.data(), tile_start, sizeof(long long) * ts.size(), cudaMemcpyDeviceToHost, s));
+    SBD_CUDA_TRY(cudaStreamSynchronize(s));
+    point_work_list(ts, wb, wt);
+    long long* wbd = nullptr;
+    int* wtd = nullptr;
+    if ((rc = upload(p, &wbd, wb, s))) return rc;
+    if ((rc = upload(p, &wtd, wt, s))) return rc;
+    *work = PointWork{wbd, wtd, static_cast<int>(wt.size())};
+    return SBD_OK;
+}
+
 template <typename T>
 int build_far(sbd_plan_s* p, cudaStream_t s) {
     const NufftParams& np = p->np;
@@ -266,31 +305,14 @@ int build_far(sbd_plan_s* p, cudaStream_t s) {
         const int urc = upload(p, &p->psi, np.psi, s);
         if (urc) return urc;
     }
-    PointRec<T>* pts0 = nullptr;
-    SBD_CUDA_TRY(cudaMallocAsync(&pts0, sizeof(PointRec<T>) * p->n, s));
-    int rc = far_prepare_points<T>(p->z, p->n, np.cx, np.cy, np.h, np.m, np.Ps, pts0, s);
+    int rc = point_records<T>(p, p->z, p->n, &p->pts, &p->pt_perm, &p->pt_work, s);
     if (rc) return rc;
-    const int ntm = (np.m + kNodeTile - 1) / kNodeTile;
-    if ((rc = dev_alloc(p, &p->pts, sizeof(PointRec<T>) * p->n))) return rc;
-    if ((rc = dev_alloc(p, reinterpret_cast<void**>(&p->pt_perm), sizeof(int) * p->n))) return rc;
-    if ((rc = dev_alloc(p, reinterpret_cast<void**>(&p->pt_tile_start),
-                        sizeof(long long) * (static_cast<size_t>(ntm) * ntm + 1)))) return rc;
-    if ((rc = tile_sort<PointRec<T>>(pts0, p->n, np.m, static_cast<PointRec<T>*>(p->pts), p->pt_perm,
-                                     p->pt_tile_start, s))) return rc;
-    SBD_CUDA_TRY(cudaFreeAsync(pts0, s));
-    {
-        // work list of the point kernels: each tile's records in chunks of at most kPointChunk
-        std::vector<long long> ts(static_cast<size_t>(ntm) * ntm + 1), wb;
-        std::vector<int> wt;
-        SBD_CUDA_TRY(cudaMemcpyAsync(ts.data(), p->pt_tile_start, sizeof(long long) * ts.size(),
-                                     cudaMemcpyDeviceToHost, s));
-        SBD_CUDA_TRY(cudaStreamSynchronize(s));
-        point_work_list(ts, wb, wt);
-        long long* wbd = nullptr;
-        int* wtd = nullptr;
-        if ((rc = upload(p, &wbd, wb, s))) return rc;
-        if ((rc = upload(p, &wtd, wt, s))) return rc;
-        p->pt_work = PointWork{wbd, wtd, static_cast<int>(wt.size())};
+    if (p->separate) {
+        if ((rc = point_records<T>(p, p->zt, p->n_tgt, &p->tpts, &p->tpt_perm, &p->tpt_work, s))) return rc;
+    } else {
+        p->tpts = p->pts;
+        p->tpt_perm = p->pt_perm;
+        p->tpt_work = p->pt_work;
     }
     std::vector<int> start(fit.n_circles + 1, 0);
     for (int c = 0; c < fit.n_circles; ++c) start[c + 1] = start[c] + fit.M[c];
@@ -509,8 +531,8 @@ int far_apply(sbd_plan_s* p, const void* f, void* q, int nrhs, cudaStream_t s, c
     t4.end();
     if (join) SBD_CUDA_TRY(cudaStreamWaitEvent(s, join, 0));   // D f is ready
     StepTimer t5(p, s, SBD_STAGE_INTERP);
-    if ((rc = interp_tiled<T>(static_cast<const PointRec<T>*>(p->pts), p->pt_perm, p->pt_work, p->geom, X, w0,
-                              p->sumf, q, cplx_io, s, real, add, nrhs, nrhs, p->n))) return rc;
+    if ((rc = interp_tiled<T>(static_cast<const PointRec<T>*>(p->tpts), p->tpt_perm, p->tpt_work, p->geom, X, w0,
+                              p->sumf, q, cplx_io, s, real, add, nrhs, nrhs, p->n_tgt))) return rc;
     t5.end();
     return SBD_OK;
 }
@@ -545,7 +567,7 @@ int nufft_plus_impl(sbd_plan_s* p, const void* ghat, void* q, cudaStream_t s) {
     if (rc) return rc;
     if ((rc = inverse_fft<T>(p, C, A, B, X, s, false))) return rc;
     SBD_CUDA_TRY(cudaMemsetAsync(p->zero2, 0, sizeof(double2), s));
-    return interp_tiled<T>(static_cast<const PointRec<T>*>(p->pts), p->pt_perm, p->pt_work, p->geom, X,
+    return interp_tiled<T>(static_cast<const PointRec<T>*>(p->tpts), p->tpt_perm, p->tpt_work, p->geom, X,
                            make_double2(0, 0), p->zero2, q, true, s);
 }
 
@@ -696,15 +718,22 @@ int sbd_fit_cache_clear(void) {
     return SBD_OK;
 }
 
-int sbd_plan(const double* points, int64_t n, sbd_kernel kernel, double delta_min, double eps,
-             const sbd_options* opt, void* cuda_stream, sbd_plan_t* out) {
+}  // extern "C"
+
+namespace {
+
+// The off-line part for sources `points` (n) and, when targets is non-null, separate targets
+// (n_t); targets null is the plan of one point set (D square, its diagonal the self pairs).
+int plan_impl(const double* targets, int64_t n_t, const double* points, int64_t n, sbd_kernel kernel,
+              double delta_min, double eps, const sbd_options* opt, void* cuda_stream, sbd_plan_t* out) {
     const auto t0 = std::chrono::steady_clock::now();
-    if (!points || !out || n < 1) {
-        set_error("sbd_plan: null pointer or n < 1");
+    const bool separate = targets != nullptr;
+    if (!points || !out || n < 1 || (separate && n_t < 1)) {
+        set_error("sbd_plan: null pointer or a point count below 1");
         return SBD_EINVAL;
     }
-    if (n > 2000000000LL) {
-        set_error("sbd_plan: n exceeds 32-bit column indices");
+    if (n > 2000000000LL || n_t > 2000000000LL) {
+        set_error("sbd_plan: point count exceeds 32-bit column indices");
         return SBD_ENOTSUP;
     }
     sbd_options o{};
@@ -742,6 +771,8 @@ int sbd_plan(const double* points, int64_t n, sbd_kernel kernel, double delta_mi
     p->kappa = kernel.kappa;
     p->form = o.form;
     p->n = static_cast<long>(n);
+    p->separate = separate;
+    p->n_tgt = separate ? static_cast<long>(n_t) : p->n;
     p->max_nrhs = std::max(1, o.max_nrhs);
     auto fail = [&](int rc) {
         free_plan(p, false, s);
@@ -755,11 +786,34 @@ int sbd_plan(const double* points, int64_t n, sbd_kernel kernel, double delta_mi
         cudaGetLastError();
         return fail(SBD_ECUDA);
     }
+    if (separate) {
+        if ((rc = dev_alloc(p, reinterpret_cast<void**>(&p->zt), sizeof(double) * 2 * n_t))) return fail(rc);
+        if (cudaMemcpyAsync(p->zt, targets, sizeof(double) * 2 * n_t, cudaMemcpyDefault, s) != cudaSuccess) {
+            set_error("sbd_plan_st: copying the targets failed (device pointer expected)");
+            cudaGetLastError();
+            return fail(SBD_ECUDA);
+        }
+    }
+    // bounding box and delta_max of all the points (targets and sources): every x_k - y_l is
+    // then within delta_max (R2)
     double bb[4];
     if ((rc = points_bbox(p->z, p->n, bb, s))) return fail(rc);
+    if (separate) {
+        double bt[4];
+        if ((rc = points_bbox(p->zt, p->n_tgt, bt, s))) return fail(rc);
+        bb[0] = std::min(bb[0], bt[0]);
+        bb[1] = std::min(bb[1], bt[1]);
+        bb[2] = std::max(bb[2], bt[2]);
+        bb[3] = std::max(bb[3], bt[3]);
+    }
     const double cx = 0.5 * (bb[0] + bb[2]), cy = 0.5 * (bb[1] + bb[3]);
     double md2 = 0.0;
     if ((rc = points_max_dist2(p->z, p->n, cx, cy, &md2, s))) return fail(rc);
+    if (separate) {
+        double mt2 = 0.0;
+        if ((rc = points_max_dist2(p->zt, p->n_tgt, cx, cy, &mt2, s))) return fail(rc);
+        md2 = std::max(md2, mt2);
+    }
     double delta_max = 2.0 * std::sqrt(md2);
     if (o.delta_max > 0.0) {
         if (o.delta_max < delta_max) {
@@ -780,7 +834,7 @@ int sbd_plan(const double* points, int64_t n, sbd_kernel kernel, double delta_mi
     const SbdFit& fit = p->fit;
     p->w0 = fit.w0;
     const double half = std::max(std::max(bb[2] - cx, bb[3] - cy), 1e-300);
-    if ((rc = plan_transform_params(fit, o, eps, half, cx, cy, p->n, p->np, err))) {
+    if ((rc = plan_transform_params(fit, o, eps, half, cx, cy, std::max(p->n, p->n_tgt), p->np, err))) {
         set_error(err);
         return fail(rc);
     }
@@ -822,15 +876,21 @@ int sbd_plan(const double* points, int64_t n, sbd_kernel kernel, double delta_mi
     const bool cval = kernel.kind == SBD_HELMHOLTZ;
     rc = o.form == SBD_FORM_FP32 ? build_far<float>(p, s) : build_far<double>(p, s);
     if (rc) return fail(rc);
-    // D over the internal order (the spreading records' tile order): the points of a
-    // row's columns are neighbours in that order too, so D f reads f locally
+    // D over the internal orders (the point records' tile order): the points of a row's
+    // columns are neighbours in that order too, so D f reads f locally.  Rows are the
+    // targets, columns the sources (the same set for a plan of one point set).
     {
-        double* zs = nullptr;
+        double *zs = nullptr, *zq = nullptr;
         SBD_CUDA_TRY(cudaMallocAsync(&zs, sizeof(double) * 2 * p->n, s));
         if ((rc = near_gather(p->z, true, p->n, 1, p->pt_perm, zs, s))) return fail(rc);
+        if (separate) {
+            SBD_CUDA_TRY(cudaMallocAsync(&zq, sizeof(double) * 2 * p->n_tgt, s));
+            if ((rc = near_gather(p->zt, true, p->n_tgt, 1, p->tpt_perm, zq, s))) return fail(rc);
+        }
         rc = near_build(zs, p->n, delta_min, bb[0], bb[1], bb[2], bb[3], nd, cval, &p->rowptr, &p->col, &p->val,
-                        &p->nnz, &p->n_coinc, s);
+                        &p->nnz, &p->n_coinc, s, zq, p->n_tgt);
         cudaFreeAsync(zs, s);
+        if (zq) cudaFreeAsync(zq, s);
         if (rc) return fail(rc);
     }
     // D f stays FP64 in both forms (the near correction is where G - G_approx cancels);
@@ -838,10 +898,10 @@ int sbd_plan(const double* points, int64_t n, sbd_kernel kernel, double delta_mi
     p->d32 = (o.flags & SBD_FLAG_NEAR_FP32) != 0;
     if (p->d32 && (rc = near_values_to_f32(&p->val, p->nnz, cval, s))) return fail(rc);
     const size_t dvb = (cval ? 2 : 1) * (p->d32 ? sizeof(float) : sizeof(double));
-    p->device_bytes += static_cast<long long>(sizeof(long long) * (p->n + 1) + (sizeof(int) + dvb) * p->nnz);
-    p->n_coinc /= 2;
+    p->device_bytes += static_cast<long long>(sizeof(long long) * (p->n_tgt + 1) + (sizeof(int) + dvb) * p->nnz);
+    if (!separate) p->n_coinc /= 2;   // each coincident pair was met from both of its points
     {
-        const size_t vb = (cval ? 16 : 8) * static_cast<size_t>(p->n) * p->max_nrhs;
+        const size_t vb = (cval ? 16 : 8) * static_cast<size_t>(p->n_tgt) * p->max_nrhs;
         if ((rc = dev_alloc(p, &p->f_int, dvb * static_cast<size_t>(p->n) * p->max_nrhs))) return fail(rc);
         if ((rc = dev_alloc(p, &p->q_int, vb))) return fail(rc);
     }
@@ -854,6 +914,25 @@ int sbd_plan(const double* points, int64_t n, sbd_kernel kernel, double delta_mi
     p->plan_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     *out = p;
     return SBD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int sbd_plan(const double* points, int64_t n, sbd_kernel kernel, double delta_min, double eps,
+             const sbd_options* opt, void* cuda_stream, sbd_plan_t* out) {
+    return plan_impl(nullptr, 0, points, n, kernel, delta_min, eps, opt, cuda_stream, out);
+}
+
+int sbd_plan_st(const double* targets, int64_t n_targets, const double* sources, int64_t n_sources,
+                sbd_kernel kernel, double delta_min, double eps, const sbd_options* opt, void* cuda_stream,
+                sbd_plan_t* out) {
+    if (!targets) {
+        set_error("sbd_plan_st: null targets");
+        return SBD_EINVAL;
+    }
+    return plan_impl(targets, n_targets, sources, n_sources, kernel, delta_min, eps, opt, cuda_stream, out);
 }
 
 int sbd_far(sbd_plan_t p, const void* f, void* q, int32_t nrhs, void* cuda_stream) {
@@ -874,7 +953,7 @@ int close_internal(sbd_plan_s* p, const void* f, int nrhs, cudaStream_t s) {
     const bool c = p->kind == SBD_HELMHOLTZ;
     int rc = near_gather(f, c, p->n, nrhs, p->pt_perm, p->f_int, s, p->d32);
     if (rc) return rc;
-    return near_spmv_internal(p->rowptr, p->col, p->val, c, p->n, nrhs, p->f_int, p->q_int, s, p->d32);
+    return near_spmv_internal(p->rowptr, p->col, p->val, c, p->n_tgt, nrhs, p->f_int, p->q_int, s, p->d32);
 }
 }  // namespace
 
@@ -887,7 +966,7 @@ int sbd_close(sbd_plan_t p, const void* f, void* q, int32_t nrhs, void* cuda_str
     }
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     if ((rc = close_internal(p, f, nrhs, s))) return rc;
-    return near_scatter(p->q_int, p->kind == SBD_HELMHOLTZ, p->n, nrhs, p->pt_perm, q, s);
+    return near_scatter(p->q_int, p->kind == SBD_HELMHOLTZ, p->n_tgt, nrhs, p->tpt_perm, q, s);
 }
 
 int sbd_matvec(sbd_plan_t p, const void* f, void* q, int32_t nrhs, void* cuda_stream) {
@@ -924,14 +1003,15 @@ int sbd_matvec_graph(sbd_plan_t p, const void* f, void* q, int32_t nrhs, void* c
         return SBD_EINVAL;
     }
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
-    const size_t bytes = (p->kind == SBD_HELMHOLTZ ? 16 : 8) * static_cast<size_t>(p->n) * nrhs;
+    const size_t esz = p->kind == SBD_HELMHOLTZ ? 16 : 8;
+    const size_t bytes = esz * static_cast<size_t>(p->n) * nrhs, out_bytes = esz * static_cast<size_t>(p->n_tgt) * nrhs;
     if (!p->g_stream) {
         SBD_CUDA_TRY(cudaStreamCreateWithFlags(&p->g_stream, cudaStreamNonBlocking));
         SBD_CUDA_TRY(cudaEventCreateWithFlags(&p->g_ev_in, cudaEventDisableTiming));
         SBD_CUDA_TRY(cudaEventCreateWithFlags(&p->g_ev_out, cudaEventDisableTiming));
-        const size_t cap = (p->kind == SBD_HELMHOLTZ ? 16 : 8) * static_cast<size_t>(p->n) * p->max_nrhs;
         p->alloc_stream = p->g_stream;
-        if ((rc = dev_alloc(p, &p->g_in, cap)) || (rc = dev_alloc(p, &p->g_out, cap))) return rc;
+        if ((rc = dev_alloc(p, &p->g_in, esz * static_cast<size_t>(p->n) * p->max_nrhs)) ||
+            (rc = dev_alloc(p, &p->g_out, esz * static_cast<size_t>(p->n_tgt) * p->max_nrhs))) return rc;
         p->g_exec.assign(p->max_nrhs + 1, nullptr);
     }
     cudaStream_t g = p->g_stream;
@@ -973,7 +1053,7 @@ int sbd_matvec_graph(sbd_plan_t p, const void* f, void* q, int32_t nrhs, void* c
     }
     SBD_CUDA_TRY(cudaMemcpyAsync(p->g_in, f, bytes, cudaMemcpyDeviceToDevice, g));
     SBD_CUDA_TRY(cudaGraphLaunch(p->g_exec[nrhs], g));
-    SBD_CUDA_TRY(cudaMemcpyAsync(q, p->g_out, bytes, cudaMemcpyDeviceToDevice, g));
+    SBD_CUDA_TRY(cudaMemcpyAsync(q, p->g_out, out_bytes, cudaMemcpyDeviceToDevice, g));
     SBD_CUDA_TRY(cudaEventRecord(p->g_ev_out, g));
     SBD_CUDA_TRY(cudaStreamWaitEvent(s, p->g_ev_out, 0));
     return SBD_OK;
@@ -1029,6 +1109,8 @@ int sbd_plan_info(sbd_plan_t p, sbd_plan_stats* o) {
     }
     std::memset(o, 0, sizeof *o);
     o->n_points = p->n;
+    o->n_targets = p->n_tgt;
+    o->separate_targets = p->separate ? 1 : 0;
     o->P = p->fit.P;
     o->n_circles = p->fit.n_circles;
     o->n_xi = p->fit.n_xi;
@@ -1308,14 +1390,14 @@ int sbd_close_export(sbd_plan_t p, int64_t* rowptr, int32_t* col, double* val) {
     }
     std::unique_lock<std::shared_mutex> sync_lock(capture_mutex());
     SBD_CUDA_TRY(cudaDeviceSynchronize());
-    // the plan holds D over the internal order; map rows and columns back to the
-    // caller's order (row k = internal row inv[k]), diagonal first, then by column
-    const long n = p->n;
+    // the plan holds D over the internal orders; map rows (targets) and columns (sources) back
+    // to the caller's order (row k = internal row inv[k]), diagonal first, then by column
+    const long n = p->n, nr = p->n_tgt;
     const size_t vb = p->kind == SBD_HELMHOLTZ ? 16 : 8;
-    std::vector<long long> rp(n + 1);
-    std::vector<int> cl(p->nnz), perm(n);
+    std::vector<long long> rp(nr + 1);
+    std::vector<int> cl(p->nnz), perm(n), tperm(nr);
     std::vector<unsigned char> vl(vb * p->nnz);
-    SBD_CUDA_TRY(cudaMemcpy(rp.data(), p->rowptr, sizeof(long long) * (n + 1), cudaMemcpyDeviceToHost));
+    SBD_CUDA_TRY(cudaMemcpy(rp.data(), p->rowptr, sizeof(long long) * (nr + 1), cudaMemcpyDeviceToHost));
     SBD_CUDA_TRY(cudaMemcpy(cl.data(), p->col, sizeof(int) * p->nnz, cudaMemcpyDeviceToHost));
     if (p->d32) {   // stored in FP32: widen
         std::vector<float> v32(vb / 8 * p->nnz);
@@ -1326,17 +1408,20 @@ int sbd_close_export(sbd_plan_t p, int64_t* rowptr, int32_t* col, double* val) {
         SBD_CUDA_TRY(cudaMemcpy(vl.data(), p->val, vb * p->nnz, cudaMemcpyDeviceToHost));
     }
     SBD_CUDA_TRY(cudaMemcpy(perm.data(), p->pt_perm, sizeof(int) * n, cudaMemcpyDeviceToHost));
-    std::vector<long> inv(n);
-    for (long i = 0; i < n; ++i) inv[perm[i]] = i;
+    SBD_CUDA_TRY(cudaMemcpy(tperm.data(), p->tpt_perm, sizeof(int) * nr, cudaMemcpyDeviceToHost));
+    std::vector<long> inv(nr);
+    for (long i = 0; i < nr; ++i) inv[tperm[i]] = i;
     rowptr[0] = 0;
-    for (long k = 0; k < n; ++k) rowptr[k + 1] = rowptr[k] + (rp[inv[k] + 1] - rp[inv[k]]);
+    for (long k = 0; k < nr; ++k) rowptr[k + 1] = rowptr[k] + (rp[inv[k] + 1] - rp[inv[k]]);
+    const long diag = p->separate ? -1 : 0;   // a plan of one point set puts each row's diagonal first
     std::vector<std::pair<int, long long>> ent;
-    for (long k = 0; k < n; ++k) {
+    for (long k = 0; k < nr; ++k) {
         const long i = inv[k];
+        const long kd = diag < 0 ? -1 : k;
         ent.clear();
         for (long long j = rp[i]; j < rp[i + 1]; ++j) ent.emplace_back(perm[cl[j]], j);
-        std::sort(ent.begin(), ent.end(), [k](const std::pair<int, long long>& a, const std::pair<int, long long>& b) {
-            if ((a.first == k) != (b.first == k)) return a.first == k;
+        std::sort(ent.begin(), ent.end(), [kd](const std::pair<int, long long>& a, const std::pair<int, long long>& b) {
+            if ((a.first == kd) != (b.first == kd)) return a.first == kd;
             return a.first < b.first;
         });
         long long o = rowptr[k];

@@ -325,6 +325,10 @@ extern "C" int sbd_gmres(sbd_plan_t plan, const void* b, void* x, const sbd_gmre
     sbd_plan_stats st;
     int rc = sbd_plan_info(plan, &st);
     if (rc) return rc;
+    if (st.separate_targets) {
+        set_error("sbd_gmres: the plan maps sources to separate targets (not a square system)");
+        return SBD_EINVAL;
+    }
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     return st.kind == SBD_HELMHOLTZ
                ? gmres_impl<true>(plan, st.n_points, b, x, *opt, iterations, rel_residual, s)

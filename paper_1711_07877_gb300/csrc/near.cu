@@ -118,20 +118,22 @@ __global__ void cell_sort_kernel(long ncells, const long long* __restrict__ star
     }
 }
 
-__global__ void neighbour_count_kernel(const double* __restrict__ z, long n, CellGrid g, double d2,
-                                       const long long* __restrict__ start, const int* __restrict__ sorted,
-                                       long long* __restrict__ cnt) {
+// Row k of D: the query point zq[k] (a target) against the points z (the sources) in the 3 x 3
+// cells around it.  square: zq is z, the row holds its diagonal first and skips l == k.
+__global__ void neighbour_count_kernel(const double* __restrict__ z, const double* __restrict__ zq, long nq,
+                                       bool square, CellGrid g, double d2, const long long* __restrict__ start,
+                                       const int* __restrict__ sorted, long long* __restrict__ cnt) {
     const long k = blockIdx.x * static_cast<long>(blockDim.x) + threadIdx.x;
-    if (k >= n) return;
-    const double x = z[2 * k], y = z[2 * k + 1];
+    if (k >= nq) return;
+    const double x = zq[2 * k], y = zq[2 * k + 1];
     const int2 c = cell_of(g, x, y);
-    long long m = 1;   // the diagonal
+    long long m = square ? 1 : 0;   // the diagonal
     for (int cy = max(c.y - 1, 0); cy <= min(c.y + 1, g.ncy - 1); ++cy)
         for (int cx = max(c.x - 1, 0); cx <= min(c.x + 1, g.ncx - 1); ++cx) {
             const int id = cy * g.ncx + cx;
             for (long long j = start[id]; j < start[id + 1]; ++j) {
                 const int l = sorted[j];
-                if (l == k) continue;
+                if (square && l == k) continue;
                 if (dist2(x, y, z[2 * l], z[2 * l + 1]) <= d2) ++m;
             }
         }
@@ -169,27 +171,30 @@ __device__ double2 d_value(const NearDev& tb, double yx, double yy) {
     return make_double2(vr, vi);
 }
 
-__global__ void neighbour_fill_kernel(const double* __restrict__ z, long n, CellGrid g, double d2,
+__global__ void neighbour_fill_kernel(const double* __restrict__ z, const double* __restrict__ zq, long nq,
+                                      bool square, CellGrid g, double d2,
                                       const long long* __restrict__ start, const int* __restrict__ sorted,
                                       const long long* __restrict__ rowptr, int* __restrict__ col,
                                       void* __restrict__ val, bool cval, NearDev tb,
                                       unsigned long long* __restrict__ n_coinc) {
     const long k = blockIdx.x * static_cast<long>(blockDim.x) + threadIdx.x;
-    if (k >= n) return;
-    const double x = z[2 * k], y = z[2 * k + 1];
+    if (k >= nq) return;
+    const double x = zq[2 * k], y = zq[2 * k + 1];
     const int2 c = cell_of(g, x, y);
     long long o = rowptr[k];
     const long long o_end = rowptr[k + 1];
-    col[o] = static_cast<int>(k);
-    if (cval) static_cast<double2*>(val)[o] = make_double2(tb.self_re, tb.self_im);
-    else static_cast<double*>(val)[o] = tb.self_re;
-    ++o;
+    if (square) {
+        col[o] = static_cast<int>(k);
+        if (cval) static_cast<double2*>(val)[o] = make_double2(tb.self_re, tb.self_im);
+        else static_cast<double*>(val)[o] = tb.self_re;
+        ++o;
+    }
     for (int cy = max(c.y - 1, 0); cy <= min(c.y + 1, g.ncy - 1); ++cy)
         for (int cx = max(c.x - 1, 0); cx <= min(c.x + 1, g.ncx - 1); ++cx) {
             const int id = cy * g.ncx + cx;
             for (long long j = start[id]; j < start[id + 1]; ++j) {
                 const int l = sorted[j];
-                if (l == k) continue;
+                if (square && l == k) continue;
                 const double t = dist2(x, y, z[2 * l], z[2 * l + 1]);
                 if (t > d2 || o >= o_end) continue;
                 const double dx = x - z[2 * l], dy = y - z[2 * l + 1];
@@ -526,7 +531,12 @@ int points_max_dist2(const double* z, long n, double cx, double cy, double* out_
 
 int near_build(const double* z, long n, double delta_min, double bx0, double by0, double bx1, double by1,
                const NearDev& tab, bool cval, long long** rowptr_out, int** col_out, void** val_out,
-               long long* nnz_out, long long* n_coinc_out, cudaStream_t s) {
+               long long* nnz_out, long long* n_coinc_out, cudaStream_t s, const double* zq, long nq) {
+    const bool square = zq == nullptr;
+    if (square) {
+        zq = z;
+        nq = n;
+    }
     CellGrid g;
     double cell = delta_min;
     // keep the cell table modest: enlarge cells (still >= delta_min) if needed
@@ -568,19 +578,19 @@ int near_build(const double* z, long n, double delta_min, double bx0, double by0
     SBD_LAUNCH_CHECK();
     const double d2 = delta_min * delta_min;
     long long* rowptr = nullptr;
-    SBD_CUDA_TRY(cudaMallocAsync(&rowptr, sizeof(long long) * (n + 1), s));
-    SBD_CUDA_TRY(cudaMemsetAsync(rowptr, 0, sizeof(long long) * (n + 1), s));
-    neighbour_count_kernel<<<nblk(n), kT, 0, s>>>(z, n, g, d2, cstart, sorted, rowptr);
+    SBD_CUDA_TRY(cudaMallocAsync(&rowptr, sizeof(long long) * (nq + 1), s));
+    SBD_CUDA_TRY(cudaMemsetAsync(rowptr, 0, sizeof(long long) * (nq + 1), s));
+    neighbour_count_kernel<<<nblk(nq), kT, 0, s>>>(z, zq, nq, square, g, d2, cstart, sorted, rowptr);
     SBD_LAUNCH_CHECK();
     long long nnz = 0;
-    rc = scan_exclusive_i64(rowptr, n + 1, &nnz, s);
+    rc = scan_exclusive_i64(rowptr, nq + 1, &nnz, s);
     if (rc) return rc;
     int* col = nullptr;
     void* val = nullptr;
     SBD_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&col), sizeof(int) * std::max<long long>(nnz, 1), s));
     SBD_CUDA_TRY(cudaMallocAsync(&val, (cval ? 16 : 8) * std::max<long long>(nnz, 1), s));
-    neighbour_fill_kernel<<<nblk(n, 128), 128, 0, s>>>(z, n, g, d2, cstart, sorted, rowptr, col, val, cval, tab,
-                                                       coinc);
+    neighbour_fill_kernel<<<nblk(nq, 128), 128, 0, s>>>(z, zq, nq, square, g, d2, cstart, sorted, rowptr, col, val,
+                                                        cval, tab, coinc);
     SBD_LAUNCH_CHECK();
     unsigned long long nc = 0;
     SBD_CUDA_TRY(cudaMemcpyAsync(&nc, coinc, sizeof nc, cudaMemcpyDeviceToHost, s));

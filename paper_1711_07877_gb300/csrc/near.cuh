@@ -26,12 +26,15 @@ struct NearDev {
 int points_bbox(const double* z, long n, double* out4_host, cudaStream_t s);
 int points_max_dist2(const double* z, long n, double cx, double cy, double* out_host, cudaStream_t s);
 
-// Build CSR of D (diagonal first in every row).  Allocates rowptr/col/val stream-ordered
-// on s (cudaMallocAsync; free them with cudaFreeAsync).
+// Build CSR of D.  Square (zq null): rows and columns are the n points z, the diagonal
+// first in every row.  Otherwise rows are the nq targets zq and columns the n sources z
+// (every source within delta_min of the target, a coincident one with the self value).
+// The box (bx0, by0)-(bx1, by1) must hold both sets.  Allocates rowptr/col/val
+// stream-ordered on s (cudaMallocAsync; free them with cudaFreeAsync).
 //   complex_vals: values are complex128 (Helmholtz) or float64 (Laplace).
 int near_build(const double* z, long n, double delta_min, double bx0, double by0, double bx1, double by1,
                const NearDev& tab, bool complex_vals, long long** rowptr, int** col, void** val,
-               long long* nnz, long long* n_coincident, cudaStream_t s);
+               long long* nnz, long long* n_coincident, cudaStream_t s, const double* zq = nullptr, long nq = 0);
 
 // q[r] (+)= D f[r] for r < nrhs (q accumulated when accumulate, else overwritten).
 int near_spmv(const long long* rowptr, const int* col, const void* val, bool complex_vals, long n, int nrhs,

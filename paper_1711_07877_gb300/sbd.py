@@ -62,7 +62,8 @@ class sbd_plan_stats(ctypes.Structure):
                 ("a", ctypes.c_double), ("fit_err", ctypes.c_double), ("nufft_tol", ctypes.c_double),
                 ("w0_re", ctypes.c_double), ("w0_im", ctypes.c_double), ("device_bytes", ctypes.c_int64),
                 ("plan_seconds", ctypes.c_double), ("n_records", ctypes.c_int64), ("node_acc", ctypes.c_int32),
-                ("node_sched", ctypes.c_int32), ("fft_split", ctypes.c_int32), ("node_binned", ctypes.c_int32)]
+                ("node_sched", ctypes.c_int32), ("fft_split", ctypes.c_int32), ("node_binned", ctypes.c_int32),
+                ("n_targets", ctypes.c_int64), ("separate_targets", ctypes.c_int32), ("reserved2", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -87,6 +88,8 @@ _SIGS = {
     "sbd_fit_cache_clear": ([], ctypes.c_int),
     "sbd_y0_root": ([_I32, _P], ctypes.c_int),
     "sbd_plan": ([_P, _I64, sbd_kernel, _D, _D, ctypes.POINTER(sbd_options), _P, ctypes.POINTER(_P)], ctypes.c_int),
+    "sbd_plan_st": ([_P, _I64, _P, _I64, sbd_kernel, _D, _D, ctypes.POINTER(sbd_options), _P, ctypes.POINTER(_P)],
+                    ctypes.c_int),
     "sbd_matvec": ([_P, _P, _P, _I32, _P], ctypes.c_int),
     "sbd_matvec_graph": ([_P, _P, _P, _I32, _P], ctypes.c_int),
     "sbd_batch_create": ([_P, _P, _I32, _P, _P, ctypes.POINTER(_P)], ctypes.c_int),
@@ -179,6 +182,17 @@ def sbd_plan(points, n: int, kernel_kind: int, kappa: float, delta_min: float, e
     return out.value
 
 
+def sbd_plan_st(targets, n_targets: int, sources, n_sources: int, kernel_kind: int, kappa: float,
+                delta_min: float, eps: float, options: sbd_options | None = None, stream=None) -> int:
+    """targets, sources: device (N, 2) float64 tensors or pointers.  Returns the plan handle (int)."""
+    out = _P()
+    rc = lib.sbd_plan_st(_ptr(targets), n_targets, _ptr(sources), n_sources, sbd_kernel(kernel_kind, kappa),
+                         delta_min, eps, ctypes.byref(options) if options is not None else None, _stream(stream),
+                         ctypes.byref(out))
+    _check(rc, "sbd_plan_st")
+    return out.value
+
+
 def sbd_matvec(plan: int, f, q, nrhs: int = 1, stream=None) -> None:
     _check(lib.sbd_matvec(plan, _ptr(f), _ptr(q), nrhs, _stream(stream)), "sbd_matvec")
 
@@ -245,7 +259,7 @@ def sbd_close_export(plan: int):
     """Returns (rowptr int64, col int32, val float64 or complex128) host arrays of D."""
     import numpy as np
     info = sbd_plan_info(plan)
-    n, nnz = info["n_points"], info["nnz"]
+    n, nnz = info["n_targets"], info["nnz"]
     rowptr = np.zeros(n + 1, dtype=np.int64)
     col = np.zeros(nnz, dtype=np.int32)
     cplx = info["kind"] == SBD_HELMHOLTZ

@@ -42,3 +42,13 @@ def test_traffic_keys_name_size_and_alpha():
     a.n = 300_000
     assert bench.traffic_key(a, 0.0) == "laplace_curves_n300000_rhs1"
     assert bench.traffic_for("node", "no_such_workload", "fp32") is None
+
+
+def test_step_bytes_scale_with_right_hand_sides():
+    one = bench.stage_bytes(INFO, 10_000, 1, "fp32", esz=8)
+    four = bench.stage_bytes(INFO, 10_000, 4, "fp32", esz=8)
+    for st in ("fft_fwd", "fft_inv", "sum"):
+        assert four[st] == 4 * one[st]
+    # the records are read once per launch, the grids and values once per right-hand side
+    assert four["spread"] - 16 * 10_000 == 4 * (one["spread"] - 16 * 10_000)
+    assert four["node"] - 24 * INFO["n_records"] == 4 * (one["node"] - 24 * INFO["n_records"])
