@@ -792,6 +792,9 @@ def run_batch(args, rank, world, local):
     clocks.start()
     ms_batch = max_over_ranks(timed(lambda: S.sbd_batch_launch(b, stream.cuda_stream)), world, "cuda")
     ms_seq = max_over_ranks(timed(seq), world, "cuda")
+    ms_batched = max_over_ranks(timed(lambda: S.sbd_matvec_batched(plans, fs, qs, stream=stream.cuda_stream)),
+                                world, "cuda")
+    batched_status = S.sbd_device_status(stream.cuda_stream)
     clk = clocks.stop()
     # end to end: host f in, batch launch, host q out (pinned buffers)
     fh = [f.cpu().pin_memory() for f in fs]
@@ -817,6 +820,11 @@ def run_batch(args, rank, world, local):
                       "l2_policy": "per-instance grids small; the whole batch exceeds L2"},
            "sequential": {"ms_per_step": ms_seq, "value": job_rate(units, world, ms_seq),
                           "note": "the same matvecs, one sbd_matvec after another on one stream"},
+           "matvec_batched": {"ms_per_step": ms_batched, "value": job_rate(units, world, ms_batched),
+                              "status": batched_status,
+                              "note": "sbd_matvec_batched: one spreading, one node-step and one interpolation "
+                                      "launch over all instances (persistent CTAs, work queues), the FFTs per "
+                                      "instance on their own streams"},
            "e2e": {"value": job_rate(units, world, ms_e2e), "unit": UNIT, "h2d_bytes_per_step": 8 * units,
                    "d2h_bytes_per_step": 8 * units},
            "clocks": clk, "roofline": None, "gpu_launches": 12 * args.instances * args.steps}

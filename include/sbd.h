@@ -230,6 +230,45 @@ int sbd_batch_create(const sbd_plan_t* plans, const int32_t* nrhs, int32_t count
 int sbd_batch_launch(sbd_batch_t batch, void* cuda_stream);
 int sbd_batch_destroy(sbd_batch_t batch);
 
+/* ---------------------------------------------------------------------------------
+ * sbd_matvec_batched - the matvecs of several plans (instances of uneven size, Laplace and
+ * Helmholtz mixed, separate-target plans included) in one call: q[i] = matvec of plans[i]
+ * on f[i] with nrhs[i] right-hand sides (Sec. 1 on-line part for each; batching itself has
+ * no counterpart in the paper).  The steps that walk points and nodes run once for the
+ * whole batch: a persistent cooperative spreading kernel over every (instance, chunk of a
+ * tile's points, right-hand-side group), a node-step kernel over every (instance, tile,
+ * right-hand side) and a persistent interpolation kernel over every (instance, chunk,
+ * right-hand-side group), each taking work items from a counter; the two cooperative ones
+ * first clear the grids they accumulate into and meet at a grid-wide barrier.  The FFTs run
+ * per instance, each plan on its own stream, and the near part D f on each plan's near stream.
+ *   plans     host, count distinct plans of one form (SBD_ENOTSUP otherwise).
+ *   f, q      host arrays of count device pointers, layout of sbd_matvec per plan.
+ *   nrhs      host, count values, 1 <= nrhs[i] <= max_nrhs of plan i.
+ *   count     1 .. 64.
+ * Asynchronous on cuda_stream; the plans must not be used elsewhere until it completes.
+ * Every device-side wait (the grid barriers) gives up after the limit of
+ * sbd_set_device_wait; the kernel then skips its remaining work, the results are invalid,
+ * and sbd_device_status reports SBD_ETIMEOUT.
+ * Errors: SBD_EINVAL (null pointers, count or nrhs out of range, a plan twice), SBD_ENOTSUP
+ * (mixed forms, or a kernel that does not fit an SM), SBD_ECUDA.
+ * ------------------------------------------------------------------------------- */
+int sbd_matvec_batched(const sbd_plan_t* plans, const void* const* f, void* const* q, const int32_t* nrhs,
+                       int32_t count, void* cuda_stream);
+
+/* sbd_set_device_wait - bound of every device-side wait of the batched launches (no
+ * counterpart in the paper): a CTA that waits longer than limit_seconds (default 2 s;
+ * (0, 600]) at a grid barrier stops waiting, records SBD_ETIMEOUT and returns, so that a
+ * fault elsewhere cannot hang the GPU.  phantom_arrivals (0 in use, at most 1024) makes each
+ * barrier wait for that many CTAs beyond those launched, which never arrive: a
+ * fault-injection knob that lets a test watch the wait run out.  Process-wide; applies to
+ * launches made after the call. */
+int sbd_set_device_wait(double limit_seconds, int32_t phantom_arrivals);
+
+/* sbd_device_status - synchronises cuda_stream, then returns and clears the process-wide
+ * status of the bounded device waits: SBD_OK, or SBD_ETIMEOUT when a wait of a batched
+ * launch ran out since the last call (a CUDA error of the synchronisation returns SBD_ECUDA). */
+int sbd_device_status(void* cuda_stream);
+
 /* The two halves of sbd_matvec, same arguments and layout:
  *   sbd_far   q = NUFFT_+(omega_hat . NUFFT_-(f))   (Eq. far convolution, incl. the xi = 0 term)
  *   sbd_close q = D f                               (Sec. 1, close correction)                  */

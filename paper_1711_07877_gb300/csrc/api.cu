@@ -123,6 +123,10 @@ struct sbd_plan_s {
     // before the interpolation (which adds D f)
     cudaStream_t near_stream = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    // sbd_matvec_batched: the plan's transforms run on their own stream beside the other
+    // instances' (created on the plan's first batched call)
+    cudaStream_t b_stream = nullptr;
+    cudaEvent_t b_ev = nullptr;
     cudaStream_t alloc_stream = nullptr;   // stream of the allocations being made
     long long device_bytes = 0;
     double plan_seconds = 0.0;
@@ -230,6 +234,8 @@ void free_plan(sbd_plan_s* p, bool wait_device, cudaStream_t s) {
     if (p->ev_fork) cudaEventDestroy(p->ev_fork);
     if (p->ev_join) cudaEventDestroy(p->ev_join);
     if (p->near_stream) cudaStreamDestroy(p->near_stream);
+    if (p->b_ev) cudaEventDestroy(p->b_ev);
+    if (p->b_stream) cudaStreamDestroy(p->b_stream);
     for (void* a : p->allocations) cudaFreeAsync(a, s);
     if (p->rowptr) cudaFreeAsync(p->rowptr, s);
     if (p->col) cudaFreeAsync(p->col, s);
@@ -1560,6 +1566,266 @@ int sbd_batch_destroy(sbd_batch_t b) {
     if (b->exec) cudaGraphExecDestroy(b->exec);
     delete b;
     return SBD_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Bounded device waits (the grid barriers of the batched launches): the limit, the phantom
+// arrivals of a fault-injection test, and the process-wide status word they report to (host
+// memory mapped into the device's address space, so the host reads it after a sync).
+std::mutex g_wait_mu;
+double g_wait_limit_s = 2.0;
+unsigned g_wait_phantom = 0;
+volatile int* g_status = nullptr;   // host view
+int* g_status_dev = nullptr;        // device view
+
+int status_word() {
+    std::lock_guard<std::mutex> lock(g_wait_mu);
+    if (g_status) return SBD_OK;
+    void* h = nullptr;
+    {
+        std::unique_lock<std::shared_mutex> cap(capture_mutex());
+        SBD_CUDA_TRY(cudaHostAlloc(&h, sizeof(int), cudaHostAllocMapped | cudaHostAllocPortable));
+    }
+    *static_cast<volatile int*>(h) = SBD_OK;
+    void* d = nullptr;
+    SBD_CUDA_TRY(cudaHostGetDevicePointer(&d, h, 0));
+    g_status_dev = static_cast<int*>(d);
+    g_status = static_cast<volatile int*>(h);
+    return SBD_OK;
+}
+
+int lane_group(int P) { return P <= 8 ? 8 : P <= 16 ? 16 : 32; }
+
+template <typename T>
+int batched_impl(const sbd_plan_t* plans, const void* const* f, void* const* q, const int32_t* nrhs, int count,
+                 cudaStream_t s) {
+    int rc = status_word();
+    if (rc) return rc;
+    unsigned phantom;
+    unsigned long long limit_ns;
+    {
+        std::lock_guard<std::mutex> lock(g_wait_mu);
+        phantom = g_wait_phantom;
+        limit_ns = static_cast<unsigned long long>(g_wait_limit_s * 1e9);
+    }
+    for (int i = 0; i < count; ++i) {
+        sbd_plan_s* p = plans[i];
+        if (!p->b_stream) {
+            SBD_CUDA_TRY(cudaStreamCreateWithFlags(&p->b_stream, cudaStreamNonBlocking));
+            SBD_CUDA_TRY(cudaEventCreateWithFlags(&p->b_ev, cudaEventDisableTiming));
+        }
+    }
+    constexpr int kSync = 8;
+    BatchSync* sync = nullptr;
+    SBD_CUDA_TRY(cudaMallocAsync(&sync, sizeof(BatchSync) * kSync, s));
+    SBD_CUDA_TRY(cudaMemsetAsync(sync, 0, sizeof(BatchSync) * kSync, s));
+    int used = 0;
+    auto next_sync = [&]() { return sync + std::min(used++, kSync - 1); };
+    // near parts on the plans' near streams, the sums of f on s
+    for (int i = 0; i < count; ++i) {
+        sbd_plan_s* p = plans[i];
+        SBD_CUDA_TRY(cudaEventRecord(p->ev_fork, s));
+        SBD_CUDA_TRY(cudaStreamWaitEvent(p->near_stream, p->ev_fork, 0));
+        if ((rc = close_internal(p, f[i], nrhs[i], p->near_stream))) return rc;
+        SBD_CUDA_TRY(cudaEventRecord(p->ev_join, p->near_stream));
+        if ((rc = far_sum(f[i], p->kind == SBD_HELMHOLTZ, p->n, nrhs[i], p->sumf, s))) return rc;
+    }
+    // spreading: one cooperative launch per lane-group class (clear, barrier, work items)
+    for (int G : {8, 16, 32}) {
+        PointJobs J{};
+        for (int i = 0; i < count; ++i) {
+            sbd_plan_s* p = plans[i];
+            if (lane_group(p->np.Ps) != G || p->pt_work.count <= 0) continue;
+            PointJob& jb = J.job[J.count];
+            const bool packed = p->half_nodes, cplx = p->kind == SBD_HELMHOLTZ;
+            jb.rec = p->pts;
+            jb.perm = p->pt_perm;
+            jb.work = p->pt_work;
+            jb.m = p->np.m;
+            jb.ntx = (jb.m + kNodeTile - 1) / kNodeTile;
+            jb.P = p->np.Ps;
+            jb.win_kind = p->np.swin;
+            jb.win_beta = p->np.beta_s;
+            jb.f = f[i];
+            jb.n_pts = p->n;
+            jb.grid = p->wsX;
+            jb.gstride = static_cast<long>(jb.m) * jb.m / (packed ? 2 : 1);
+            jb.clear_elems = 2 * jb.gstride * nrhs[i];
+            jb.nrhs = nrhs[i];
+            jb.rg = point_rhs_group<T>(jb.P, cplx && !packed, nrhs[i]);
+            jb.packed = packed;
+            jb.complex_io = cplx;
+            J.first[J.count] = J.total;
+            J.total += jb.work.count * ((jb.nrhs + jb.rg - 1) / jb.rg);
+            ++J.count;
+        }
+        if (J.count && (rc = spread_batch<T>(J, G, next_sync(), phantom, limit_ns, g_status_dev, s))) return rc;
+    }
+    // a plan with no point records spreads nothing: its grids are cleared here
+    for (int i = 0; i < count; ++i) {
+        sbd_plan_s* p = plans[i];
+        if (p->pt_work.count <= 0) {
+            const long g = static_cast<long>(p->np.m) * p->np.m;
+            SBD_CUDA_TRY(cudaMemsetAsync(p->wsX, 0, sizeof(cx_t<T>) * g * nrhs[i], s));
+        }
+    }
+    // forward transforms, each plan on its own stream
+    auto fork_join = [&](auto body) -> int {
+        cudaEvent_t e = plans[0]->b_ev;   // fork point: recorded on s, then reused as plan 0's join
+        SBD_CUDA_TRY(cudaEventRecord(e, s));
+        for (int i = 0; i < count; ++i) SBD_CUDA_TRY(cudaStreamWaitEvent(plans[i]->b_stream, e, 0));
+        for (int i = 0; i < count; ++i) {
+            sbd_plan_s* p = plans[i];
+            const int r = body(p, i);
+            if (r) return r;
+            SBD_CUDA_TRY(cudaEventRecord(p->b_ev, p->b_stream));
+        }
+        for (int i = 0; i < count; ++i) SBD_CUDA_TRY(cudaStreamWaitEvent(s, plans[i]->b_ev, 0));
+        return SBD_OK;
+    };
+    rc = fork_join([&](sbd_plan_s* p, int i) {
+        auto* X = static_cast<cx_t<T>*>(p->wsX);
+        auto* A = static_cast<cx_t<T>*>(p->wsA);
+        auto* B = static_cast<cx_t<T>*>(p->wsB);
+        auto* C = static_cast<cx_t<T>*>(p->wsC);
+        return p->half_nodes ? forward_fft_real<T>(p, X, A, C, B, p->b_stream, nrhs[i])
+                             : forward_fft<T>(p, X, A, C, B, p->b_stream, nrhs[i]);
+    });
+    if (rc) return rc;
+    // node step: one cooperative launch per kernel family; the two-kernel fallback per plan
+    for (int fam = 0; fam < 2; ++fam) {   // 0: binned, 1: fused
+        NodeJobs J{};
+        for (int i = 0; i < count; ++i) {
+            sbd_plan_s* p = plans[i];
+            const bool binned = sizeof(T) == 4 && p->node_binned && p->tuning.acc == 3;
+            if (!p->node_fused || binned != (fam == 0)) continue;
+            NodeJob& jb = J.job[J.count];
+            jb.rec = p->nodes;
+            jb.tile_start = p->node_tile_start;
+            jb.nk = p->np.nk;
+            jb.ntx = (jb.nk + kNodeTile - 1) / kNodeTile;
+            jb.ntiles = jb.ntx * jb.ntx;
+            jb.P = p->np.Pk;
+            jb.Ws = node_fused_stride(jb.P);
+            jb.win_kind = p->np.kwin;
+            jb.win_beta = p->np.beta_k;
+            jb.kin = p->wsB;
+            jb.kout = p->wsC;
+            jb.kbatch = static_cast<long>(jb.nk) * jb.nk;
+            jb.nrhs = nrhs[i];
+            J.first[J.count] = J.total;
+            J.total += jb.ntiles * nrhs[i];
+            ++J.count;
+        }
+        if (J.count && (rc = node_batch<T>(J, fam == 0, next_sync(), phantom, limit_ns, g_status_dev, s))) return rc;
+    }
+    for (int i = 0; i < count; ++i) {
+        sbd_plan_s* p = plans[i];
+        if (!p->node_fused &&
+            (rc = node_step_tiled<T>(static_cast<const NodeRec<T>*>(p->nodes), p->node_tile_start, p->geom,
+                                     static_cast<const cx_t<T>*>(p->wsB), static_cast<cx_t<T>*>(p->ghat),
+                                     static_cast<cx_t<T>*>(p->wsC), s, nrhs[i]))) return rc;
+    }
+    // inverse transforms, each plan on its own stream
+    rc = fork_join([&](sbd_plan_s* p, int i) {
+        auto* X = static_cast<cx_t<T>*>(p->wsX);
+        auto* A = static_cast<cx_t<T>*>(p->wsA);
+        auto* B = static_cast<cx_t<T>*>(p->wsB);
+        auto* C = static_cast<cx_t<T>*>(p->wsC);
+        return p->half_nodes ? inverse_fft_real<T>(p, C, A, B, X, p->b_stream, nrhs[i])
+                             : inverse_fft<T>(p, C, A, B, X, p->b_stream, false, nrhs[i]);
+    });
+    if (rc) return rc;
+    for (int i = 0; i < count; ++i) SBD_CUDA_TRY(cudaStreamWaitEvent(s, plans[i]->ev_join, 0));   // D f ready
+    // interpolation at every plan's targets (+ xi = 0 term + D f): persistent CTAs per class
+    for (int G : {8, 16, 32}) {
+        PointJobs J{};
+        for (int i = 0; i < count; ++i) {
+            sbd_plan_s* p = plans[i];
+            if (lane_group(p->np.Ps) != G || p->tpt_work.count <= 0) continue;
+            PointJob& jb = J.job[J.count];
+            const bool packed = p->half_nodes, cplx = p->kind == SBD_HELMHOLTZ;
+            jb.rec = p->tpts;
+            jb.perm = p->tpt_perm;
+            jb.work = p->tpt_work;
+            jb.m = p->np.m;
+            jb.ntx = (jb.m + kNodeTile - 1) / kNodeTile;
+            jb.P = p->np.Ps;
+            jb.win_kind = p->np.swin;
+            jb.win_beta = p->np.beta_s;
+            jb.q = q[i];
+            jb.n_pts = p->n_tgt;
+            jb.grid = p->wsX;
+            jb.gstride = static_cast<long>(jb.m) * jb.m / (packed ? 2 : 1);
+            jb.nrhs = nrhs[i];
+            jb.rg = point_rhs_group<T>(jb.P, !packed, nrhs[i]);
+            jb.packed = packed;
+            jb.complex_io = cplx;
+            jb.w0 = make_double2(p->w0.real(), p->w0.imag());
+            jb.sumf = p->sumf;
+            jb.add = p->q_int;
+            J.first[J.count] = J.total;
+            J.total += jb.work.count * ((jb.nrhs + jb.rg - 1) / jb.rg);
+            ++J.count;
+        }
+        if (J.count && (rc = interp_batch<T>(J, G, next_sync(), s))) return rc;
+    }
+    SBD_CUDA_TRY(cudaFreeAsync(sync, s));
+    return SBD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int sbd_matvec_batched(const sbd_plan_t* plans, const void* const* f, void* const* q, const int32_t* nrhs,
+                       int32_t count, void* cuda_stream) {
+    if (!plans || !f || !q || !nrhs || count < 1 || count > kMaxBatch) {
+        set_error("sbd_matvec_batched: null argument or count outside [1, " + std::to_string(kMaxBatch) + "]");
+        return SBD_EINVAL;
+    }
+    for (int i = 0; i < count; ++i) {
+        if (!plans[i] || !f[i] || !q[i] || nrhs[i] < 1 || nrhs[i] > plans[i]->max_nrhs) {
+            set_error("sbd_matvec_batched: invalid entry " + std::to_string(i));
+            return SBD_EINVAL;
+        }
+        if (plans[i]->form != plans[0]->form) {
+            set_error("sbd_matvec_batched: the plans of one call must share the form");
+            return SBD_ENOTSUP;
+        }
+        for (int j = 0; j < i; ++j)
+            if (plans[j] == plans[i]) {
+                set_error("sbd_matvec_batched: a plan appears twice (its workspace is shared)");
+                return SBD_EINVAL;
+            }
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    return plans[0]->form == SBD_FORM_FP32 ? batched_impl<float>(plans, f, q, nrhs, count, s)
+                                           : batched_impl<double>(plans, f, q, nrhs, count, s);
+}
+
+int sbd_set_device_wait(double limit_seconds, int32_t phantom_arrivals) {
+    if (!(limit_seconds > 0) || limit_seconds > 600 || phantom_arrivals < 0 || phantom_arrivals > 1024) {
+        set_error("sbd_set_device_wait: limit outside (0, 600] s or phantom arrivals outside [0, 1024]");
+        return SBD_EINVAL;
+    }
+    std::lock_guard<std::mutex> lock(g_wait_mu);
+    g_wait_limit_s = limit_seconds;
+    g_wait_phantom = static_cast<unsigned>(phantom_arrivals);
+    return SBD_OK;
+}
+
+int sbd_device_status(void* cuda_stream) {
+    SBD_CUDA_TRY(cudaStreamSynchronize(static_cast<cudaStream_t>(cuda_stream)));
+    std::lock_guard<std::mutex> lock(g_wait_mu);
+    if (!g_status) return SBD_OK;
+    const int v = *g_status;
+    *g_status = SBD_OK;
+    if (v != SBD_OK) set_error("a bounded device wait of a batched launch ran out");
+    return v;
 }
 
 int sbd_fft2(const void* in, void* out, int32_t n0, int32_t n1, int32_t sign, int32_t form, void* cuda_stream) {

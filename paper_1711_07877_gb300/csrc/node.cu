@@ -316,19 +316,21 @@ __global__ void __launch_bounds__(256) scatter_tiles_kernel(
 // Interpolation by work item (PointWork): the CTA loads its tile plus the (P-1) halo of the
 // grid into shared memory and takes the records of its chunk, a group of G lanes per record
 // (lane = stencil column, rows accumulated in registers, columns reduced with shuffles).
-// Right-hand sides: blockIdx.y takes rg of them (grids gstride elements apart), whose tiles
-// sit in shared memory side by side (kC = 1 plane for a packed real grid, else re / im), so
-// each record's window weights are evaluated once for the rg values it produces.
+// Right-hand sides: a CTA takes rg of them (grids gstride elements apart), whose tiles sit in
+// shared memory side by side (kC = 1 plane for a packed real grid, else re / im), so each
+// record's window weights are evaluated once for the rg values it produces.  The body serves
+// the single-plan kernel (item = blockIdx.x, group = blockIdx.y) and the batched one.
 template <typename T, int G, bool PK>
-__global__ void __launch_bounds__(256) interp_chunks_kernel(
-    const PointRec<T>* __restrict__ rec, PointWork work, int ntx, int n, int P, Window<T> win,
-    const cx_t<T>* __restrict__ grid, PointOut<T> out, int nrhs, int rg, long gstride) {
+__device__ __forceinline__ void interp_chunk_body(const PointRec<T>* __restrict__ rec, const PointWork& work, int item,
+                                                  int ntx, int n, int P, const Window<T>& win,
+                                                  const cx_t<T>* __restrict__ grid, const PointOut<T>& out, int nrhs,
+                                                  int rg, int grp, long gstride) {
     constexpr int kC = PK ? 1 : 2;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* s = reinterpret_cast<T*>(smem_raw);                    // [rg][W][W][kC]
-    const int tile = work.tile[blockIdx.x];
-    const long long b0 = work.begin[blockIdx.x], b1 = work.begin[blockIdx.x + 1];
-    const int r0 = blockIdx.y * rg, nr = min(rg, nrhs - r0);
+    const int tile = work.tile[item];
+    const long long b0 = work.begin[item], b1 = work.begin[item + 1];
+    const int r0 = grp * rg, nr = min(rg, nrhs - r0);
     const int ox = (tile / ntx) * kNodeTile, oy = (tile % ntx) * kNodeTile;
     const int W = kNodeTile + P - 1;
     const int rows = min(W, n - ox), cols = min(W, n - oy);
@@ -379,23 +381,31 @@ __global__ void __launch_bounds__(256) interp_chunks_kernel(
     }
 }
 
+template <typename T, int G, bool PK>
+__global__ void __launch_bounds__(256) interp_chunks_kernel(
+    const PointRec<T>* __restrict__ rec, PointWork work, int ntx, int n, int P, Window<T> win,
+    const cx_t<T>* __restrict__ grid, PointOut<T> out, int nrhs, int rg, long gstride) {
+    interp_chunk_body<T, G, PK>(rec, work, blockIdx.x, ntx, n, P, win, grid, out, nrhs, rg, blockIdx.y, gstride);
+}
+
 // Spreading by work item (PointWork): the CTA accumulates the stencils of its chunk's records
 // into a shared (64 + P - 1)^2 window with shared-memory atomics, then adds every cell it
 // reached into the (cleared) grid with global atomics.  RV: real values, one plane.
-// Right-hand sides: blockIdx.y takes rg of them (one window each, grids gstride elements
-// apart); each record's window weights are evaluated once for its rg values.
+// Right-hand sides: a CTA takes rg of them (one window each, grids gstride elements apart);
+// each record's window weights are evaluated once for its rg values.
 template <typename T, int G, bool PK, bool RV>
-__global__ void __launch_bounds__(256) spread_chunks_kernel(
-    const PointRec<T>* __restrict__ rec, PointWork work, int ntx, int n, int P, Window<T> win, PointVal<T> val,
-    cx_t<T>* __restrict__ grid, int nrhs, int rg, long gstride) {
+__device__ __forceinline__ void spread_chunk_body(const PointRec<T>* __restrict__ rec, const PointWork& work,
+                                                  int item, int ntx, int n, int P, const Window<T>& win,
+                                                  const PointVal<T>& val, cx_t<T>* __restrict__ grid, int nrhs,
+                                                  int rg, int grp, long gstride) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* acc = reinterpret_cast<T*>(smem_raw);          // [rg][W][W][RV ? 1 : 2]
     constexpr int kC = RV ? 1 : 2;
     const int W = kNodeTile + P - 1;
     const long plane = static_cast<long>(kC) * W * W;
-    const int tile = work.tile[blockIdx.x];
-    const long long b0 = work.begin[blockIdx.x], b1 = work.begin[blockIdx.x + 1];
-    const int r0 = blockIdx.y * rg, nr = min(rg, nrhs - r0);
+    const int tile = work.tile[item];
+    const long long b0 = work.begin[item], b1 = work.begin[item + 1];
+    const int r0 = grp * rg, nr = min(rg, nrhs - r0);
     const int ox = (tile / ntx) * kNodeTile, oy = (tile % ntx) * kNodeTile;
     for (long idx = threadIdx.x; idx < nr * plane; idx += blockDim.x) acc[idx] = 0;
     __syncthreads();
@@ -444,6 +454,143 @@ __global__ void __launch_bounds__(256) spread_chunks_kernel(
     }
 }
 
+template <typename T, int G, bool PK, bool RV>
+__global__ void __launch_bounds__(256) spread_chunks_kernel(
+    const PointRec<T>* __restrict__ rec, PointWork work, int ntx, int n, int P, Window<T> win, PointVal<T> val,
+    cx_t<T>* __restrict__ grid, int nrhs, int rg, long gstride) {
+    spread_chunk_body<T, G, PK, RV>(rec, work, blockIdx.x, ntx, n, P, win, val, grid, nrhs, rg, blockIdx.y, gstride);
+}
+
+// --- batched point kernels (sbd_matvec_batched): persistent CTAs over the work items of every
+// instance of the batch ----------------------------------------------------------------------------
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Grid-wide barrier of a cooperative launch (every CTA resident), by generation: a CTA reads
+// the generation, arrives, and the last of `expected` arrivals opens the next generation.  The
+// wait is bounded: past limit_ns the CTA gives up, writes SBD_ETIMEOUT to the status word and
+// returns false (its caller then skips the rest of its work and returns).  expected is
+// gridDim.x plus any phantom arrivals of a fault-injection test, which then never complete.
+__device__ bool grid_barrier(BatchSync* st, unsigned expected, unsigned long long limit_ns, volatile int* status) {
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned* gen = &st->gen;
+        const unsigned g0 = *gen;
+        __threadfence();
+        const unsigned a = atomicAdd(&st->arrive, 1u);
+        ok = 1;
+        if (a == expected - 1) {
+            st->arrive = 0;
+            __threadfence();
+            atomicAdd(&st->gen, 1u);
+        } else {
+            const unsigned long long t0 = global_ns();
+            while (*gen == g0) {
+                if (global_ns() - t0 > limit_ns) {
+                    ok = 0;
+                    *status = SBD_ETIMEOUT;
+                    __threadfence_system();
+                    break;
+                }
+                __nanosleep(256);
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+// Item `it` of the batch: the job whose item range holds it (jobs sorted by first item).
+template <typename Jobs>
+__device__ __forceinline__ int find_job(const Jobs& J, int it) {
+    int j = 0;
+    while (j + 1 < J.count && J.first[j + 1] <= it) ++j;
+    return j;
+}
+
+template <typename T>
+__device__ __forceinline__ Window<T> job_window(const PointJob& jb) {
+    return Window<T>{jb.win_kind, static_cast<T>(jb.win_beta), static_cast<T>(2.0 / jb.P)};
+}
+
+// Spreading of the whole batch in one cooperative launch: every CTA first clears its share of
+// all the instances' grids, then (after the bounded grid barrier) takes work items (instance,
+// chunk, right-hand-side group) from a counter until none are left.
+template <typename T, int G>
+__global__ void __launch_bounds__(256) spread_batch_kernel(PointJobs J, BatchSync* st, unsigned phantom,
+                                                           unsigned long long limit_ns, volatile int* status) {
+    for (int j = 0; j < J.count; ++j) {
+        const PointJob& jb = J.job[j];
+        T* g = static_cast<T*>(jb.grid);
+        for (long e = blockIdx.x * static_cast<long>(blockDim.x) + threadIdx.x; e < jb.clear_elems;
+             e += static_cast<long>(gridDim.x) * blockDim.x)
+            g[e] = static_cast<T>(0);
+    }
+    if (!grid_barrier(st, gridDim.x + phantom, limit_ns, status)) return;
+    __shared__ int item;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) item = static_cast<int>(atomicAdd(&st->items, 1u));
+        __syncthreads();
+        const int it = item;
+        if (it >= J.total) break;
+        const int j = find_job(J, it);
+        const PointJob& jb = J.job[j];
+        const int local = it - J.first[j];
+        const int chunk = local % jb.work.count, grp = local / jb.work.count;
+        const Window<T> win = job_window<T>(jb);
+        const PointVal<T> val{jb.f, jb.perm, jb.complex_io != 0 && jb.packed == 0, jb.n_pts};
+        const auto* rec = static_cast<const PointRec<T>*>(jb.rec);
+        auto* grid = static_cast<cx_t<T>*>(jb.grid);
+        if (jb.packed)
+            spread_chunk_body<T, G, true, true>(rec, jb.work, chunk, jb.ntx, jb.m, jb.P, win, val, grid, jb.nrhs,
+                                                jb.rg, grp, jb.gstride);
+        else if (!jb.complex_io)
+            spread_chunk_body<T, G, false, true>(rec, jb.work, chunk, jb.ntx, jb.m, jb.P, win, val, grid, jb.nrhs,
+                                                 jb.rg, grp, jb.gstride);
+        else
+            spread_chunk_body<T, G, false, false>(rec, jb.work, chunk, jb.ntx, jb.m, jb.P, win, val, grid, jb.nrhs,
+                                                  jb.rg, grp, jb.gstride);
+    }
+}
+
+// Interpolation of the whole batch: persistent CTAs take work items from a counter.
+template <typename T, int G>
+__global__ void __launch_bounds__(256) interp_batch_kernel(PointJobs J, BatchSync* st) {
+    __shared__ int item;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) item = static_cast<int>(atomicAdd(&st->items, 1u));
+        __syncthreads();
+        const int it = item;
+        if (it >= J.total) break;
+        const int j = find_job(J, it);
+        const PointJob& jb = J.job[j];
+        const int local = it - J.first[j];
+        const int chunk = local % jb.work.count, grp = local / jb.work.count;
+        const Window<T> win = job_window<T>(jb);
+        const PointOut<T> out{jb.q, jb.perm, jb.complex_io != 0, jb.w0, jb.sumf, jb.add, jb.nrhs, 0, jb.n_pts};
+        const auto* rec = static_cast<const PointRec<T>*>(jb.rec);
+        const auto* grid = static_cast<const cx_t<T>*>(jb.grid);
+        if (jb.packed)
+            interp_chunk_body<T, G, true>(rec, jb.work, chunk, jb.ntx, jb.m, jb.P, win, grid, out, jb.nrhs, jb.rg,
+                                          grp, jb.gstride);
+        else
+            interp_chunk_body<T, G, false>(rec, jb.work, chunk, jb.ntx, jb.m, jb.P, win, grid, out, jb.nrhs, jb.rg,
+                                           grp, jb.gstride);
+    }
+}
+
+// Threads of a fused node-step CTA: 16 warps, so that the two CTAs that fit an SM's
+// shared memory (FP32 form) keep 32 warps in flight for the shared-memory latency.
+constexpr int kNodeThreads = 512;
+
 // Fused node step: one CTA per 64 x 64 tile of the frequency grid.  The tile plus a
 // (P-1) halo of K sits in shared memory with an accumulator of the same size
 // (interleaved float2 in FP32, two planes re / im in FP64).  A group of G lanes (G = 8, 16 or 32 >= P; 32 / G nodes per warp) takes
@@ -466,15 +613,12 @@ __global__ void __launch_bounds__(256) spread_chunks_kernel(
 // for 2^13 contributions of the largest possible size per cell; the quantum is 2^-50 B,
 // far below FP32 rounding.  wbound = max|omega'| P^2.
 template <typename T, int G, int NT, int ACC, int SCHED>
-__global__ void __launch_bounds__(NT) node_fused_kernel(
+__device__ __forceinline__ void node_fused_body(
     const NodeRec<T>* __restrict__ rec, const long long* __restrict__ tile_start, int ntx, int n, int P, int Ws,
-    Window<T> win, const cx_t<T>* __restrict__ kin, cx_t<T>* __restrict__ kout, float wbound, long kbatch) {
+    const Window<T>& win, const cx_t<T>* __restrict__ kin, cx_t<T>* __restrict__ kout, float wbound, int tile) {
     using C = cx_t<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ float red[NT / 32];
-    kin += blockIdx.y * kbatch;                       // right-hand side blockIdx.y
-    kout += blockIdx.y * kbatch;
-    const int tile = blockIdx.x;
     const long long b0 = tile_start[tile], b1 = tile_start[tile + 1];
     if (b0 == b1) return;
     const int W = kNodeTile + P - 1;
@@ -618,6 +762,15 @@ __global__ void __launch_bounds__(NT) node_fused_kernel(
     }
 }
 
+template <typename T, int G, int NT, int ACC, int SCHED>
+__global__ void __launch_bounds__(NT) node_fused_kernel(
+    const NodeRec<T>* __restrict__ rec, const long long* __restrict__ tile_start, int ntx, int n, int P, int Ws,
+    Window<T> win, const cx_t<T>* __restrict__ kin, cx_t<T>* __restrict__ kout, float wbound, long kbatch) {
+    // tile blockIdx.x of right-hand side blockIdx.y
+    node_fused_body<T, G, NT, ACC, SCHED>(rec, tile_start, ntx, n, P, Ws, win, kin + blockIdx.y * kbatch,
+                                          kout + blockIdx.y * kbatch, wbound, blockIdx.x);
+}
+
 // Binned node step (FP32, stencils of at most kBinSide cells): no atomics in shared
 // memory.  The records of a tile are sorted by the 8 x 8 bin of their stencil start
 // (tile_sort with by_bin); a record of bin (bx, by) writes only cells
@@ -644,16 +797,13 @@ constexpr int kBinWs = 76;
 static_assert(kBinWs >= kBinW && kBinWs % 16 == 12, "binned stride");
 
 template <int NT>
-__global__ void __launch_bounds__(NT, 1) node_binned_kernel(
+__device__ __forceinline__ void node_binned_body(
     const NodeRec<float>* __restrict__ rec, const long long* __restrict__ tile_start, int ntx, int n, int P,
-    Window<float> win, const float2* __restrict__ kin, float2* __restrict__ kout, long kbatch) {
+    const Window<float>& win, const float2* __restrict__ kin, float2* __restrict__ kout, int tile) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int bstart[kBins + 1];
     __shared__ int border[kBins];                                   // bins, largest first
     __shared__ int next_bin;
-    kin += blockIdx.y * kbatch;                                     // right-hand side blockIdx.y
-    kout += blockIdx.y * kbatch;
-    const int tile = blockIdx.x;
     const long long b0 = tile_start[tile], b1 = tile_start[tile + 1];
     if (b0 == b1) return;                                           // uniform per block
     const int cnt = static_cast<int>(b1 - b0);
@@ -801,9 +951,56 @@ __global__ void __launch_bounds__(NT, 1) node_binned_kernel(
     }
 }
 
-// Threads of a fused node-step CTA: 16 warps, so that the two CTAs that fit an SM's
-// shared memory (FP32 form) keep 32 warps in flight for the shared-memory latency.
-constexpr int kNodeThreads = 512;
+template <int NT>
+__global__ void __launch_bounds__(NT, 1) node_binned_kernel(
+    const NodeRec<float>* __restrict__ rec, const long long* __restrict__ tile_start, int ntx, int n, int P,
+    Window<float> win, const float2* __restrict__ kin, float2* __restrict__ kout, long kbatch) {
+    // tile blockIdx.x of right-hand side blockIdx.y
+    node_binned_body<NT>(rec, tile_start, ntx, n, P, win, kin + blockIdx.y * kbatch, kout + blockIdx.y * kbatch,
+                         blockIdx.x);
+}
+
+// Node step of a whole batch (sbd_matvec_batched), one cooperative launch of persistent CTAs:
+// each CTA clears its share of every instance's output grids, passes the bounded grid barrier
+// (see grid_barrier), then takes items (instance, tile, right-hand side; tile fastest) from a
+// counter.  BINNED: every instance runs the binned body (FP32, all binned); otherwise the fused
+// body with two float planes and records dealt in turn (ACC 0, SCHED 0), G lanes per record.
+template <typename T, int G, bool BINNED>
+__global__ void __launch_bounds__(kNodeThreads * (BINNED ? 2 : 1), 1) node_batch_kernel(
+    NodeJobs J, BatchSync* st, unsigned phantom, unsigned long long limit_ns, volatile int* status) {
+    for (int j = 0; j < J.count; ++j) {
+        const NodeJob& jb = J.job[j];
+        T* g = static_cast<T*>(jb.kout);
+        const long elems = 2 * jb.kbatch * jb.nrhs;
+        for (long e = blockIdx.x * static_cast<long>(blockDim.x) + threadIdx.x; e < elems;
+             e += static_cast<long>(gridDim.x) * blockDim.x)
+            g[e] = static_cast<T>(0);
+    }
+    if (!grid_barrier(st, gridDim.x + phantom, limit_ns, status)) return;
+    __shared__ int item;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) item = static_cast<int>(atomicAdd(&st->items, 1u));
+        __syncthreads();
+        const int it = item;
+        if (it >= J.total) break;
+        const int j = find_job(J, it);
+        const NodeJob& jb = J.job[j];
+        const int local = it - J.first[j];
+        const int tile = local % jb.ntiles, r = local / jb.ntiles;
+        const auto* kin = static_cast<const cx_t<T>*>(jb.kin) + r * jb.kbatch;
+        auto* kout = static_cast<cx_t<T>*>(jb.kout) + r * jb.kbatch;
+        const Window<T> win{jb.win_kind, static_cast<T>(jb.win_beta), static_cast<T>(2.0 / jb.P)};
+        if constexpr (BINNED) {
+            if constexpr (sizeof(T) == 4)
+                node_binned_body<2 * kNodeThreads>(static_cast<const NodeRec<float>*>(jb.rec), jb.tile_start,
+                                                   jb.ntx, jb.nk, jb.P, win, kin, kout, tile);
+        } else {
+            node_fused_body<T, G, kNodeThreads, 0, 0>(static_cast<const NodeRec<T>*>(jb.rec), jb.tile_start, jb.ntx,
+                                                      jb.nk, jb.P, jb.Ws, win, kin, kout, 0.f, tile);
+        }
+    }
+}
 
 // Shared row stride for the fused node kernel: >= W and congruent to P8 modulo 32.
 inline int fused_stride(int W, int P8) {
@@ -1139,6 +1336,109 @@ int fill_grid(cx_t<T>* x, long n, T re, T im, cudaStream_t s) {
     return SBD_OK;
 }
 
+template <typename T>
+int point_rhs_group(int P, bool two_planes, int nrhs) {
+    const size_t W = kNodeTile + P - 1;
+    return rhs_group((two_planes ? 2 : 1) * sizeof(T) * W * W, nrhs);
+}
+
+int node_fused_stride(int Pk) { return fused_stride(kNodeTile + Pk - 1, fused_p8(Pk)); }
+
+namespace {
+
+int sm_count() {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
+                                                  cudaSuccess)
+        return 0;
+    return sms;
+}
+
+// A cooperative launch of the most CTAs that can be resident at once (so the grid barrier can
+// complete), at least one.
+template <typename K, typename... A>
+int launch_cooperative(K kernel, int threads, size_t smem, cudaStream_t s, A... args) {
+    SBD_TRY(raise_smem_limit(kernel, smem));
+    int per_sm = 0;
+    SBD_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem));
+    const int sms = sm_count();
+    if (per_sm < 1 || sms < 1) {
+        set_error("batched launch: kernel does not fit an SM");
+        return SBD_ENOTSUP;
+    }
+    void* argv[] = {static_cast<void*>(&args)...};
+    SBD_CUDA_TRY(cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(kernel), dim3(per_sm * sms),
+                                             dim3(threads), argv, smem, s));
+    return SBD_OK;
+}
+
+template <typename T>
+size_t point_batch_smem(const PointJobs& J, bool interp) {
+    size_t smem = 0;
+    for (int j = 0; j < J.count; ++j) {
+        const PointJob& jb = J.job[j];
+        const size_t W = kNodeTile + jb.P - 1;
+        const bool two = interp ? !jb.packed : (jb.complex_io && !jb.packed);
+        smem = std::max(smem, (two ? 2 : 1) * sizeof(T) * W * W * jb.rg);
+    }
+    return smem;
+}
+
+}  // namespace
+
+template <typename T>
+int spread_batch(const PointJobs& J, int G, BatchSync* sync, unsigned phantom, unsigned long long limit_ns,
+                 volatile int* status, cudaStream_t s) {
+    const size_t smem = point_batch_smem<T>(J, false);
+    if (G == 8) return launch_cooperative(spread_batch_kernel<T, 8>, 256, smem, s, J, sync, phantom, limit_ns, status);
+    if (G == 16)
+        return launch_cooperative(spread_batch_kernel<T, 16>, 256, smem, s, J, sync, phantom, limit_ns, status);
+    return launch_cooperative(spread_batch_kernel<T, 32>, 256, smem, s, J, sync, phantom, limit_ns, status);
+}
+
+template <typename T>
+int interp_batch(const PointJobs& J, int G, BatchSync* sync, cudaStream_t s) {
+    const size_t smem = point_batch_smem<T>(J, true);
+    auto launch = [&](auto kernel) {
+        SBD_TRY(raise_smem_limit(kernel, smem));
+        int per_sm = 0;
+        SBD_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 256, smem));
+        const int grid = std::max(1, std::min(std::max(per_sm, 1) * std::max(sm_count(), 1), J.total));
+        kernel<<<grid, 256, smem, s>>>(J, sync);
+        SBD_LAUNCH_CHECK();
+        return SBD_OK;
+    };
+    if (G == 8) return launch(interp_batch_kernel<T, 8>);
+    if (G == 16) return launch(interp_batch_kernel<T, 16>);
+    return launch(interp_batch_kernel<T, 32>);
+}
+
+template <typename T>
+int node_batch(const NodeJobs& J, bool binned, BatchSync* sync, unsigned phantom, unsigned long long limit_ns,
+               volatile int* status, cudaStream_t s) {
+    if (binned) {
+        if constexpr (sizeof(T) == 4)
+            return launch_cooperative(node_batch_kernel<float, 8, true>, 2 * kNodeThreads,
+                                      node_fused_smem<float>(J.job[0].P, 3), s, J, sync, phantom, limit_ns, status);
+        set_error("node_batch: the binned kernel is FP32 only");
+        return SBD_EINVAL;
+    }
+    size_t smem = 0;
+    int P8 = 8;
+    for (int j = 0; j < J.count; ++j) {
+        smem = std::max(smem, node_fused_smem<T>(J.job[j].P, 0));
+        P8 = std::max(P8, fused_p8(J.job[j].P));
+    }
+    if (P8 == 8)
+        return launch_cooperative(node_batch_kernel<T, 8, false>, kNodeThreads, smem, s, J, sync, phantom, limit_ns,
+                                  status);
+    if (P8 == 16)
+        return launch_cooperative(node_batch_kernel<T, 16, false>, kNodeThreads, smem, s, J, sync, phantom, limit_ns,
+                                  status);
+    return launch_cooperative(node_batch_kernel<T, 32, false>, kNodeThreads, smem, s, J, sync, phantom, limit_ns,
+                              status);
+}
+
 #define SBD_NODE_INST(T)                                                                                     \
     template int tile_sort<NodeRec<T>>(const NodeRec<T>*, long, int, NodeRec<T>*, int*, long long*,          \
                                        cudaStream_t, bool);                                                  \
@@ -1154,7 +1454,13 @@ int fill_grid(cx_t<T>* x, long n, T re, T im, cudaStream_t s) {
                                  const void*, bool, cx_t<T>*, cudaStream_t, bool, int, long);                \
     template int interp_tiled<T>(const PointRec<T>*, const int*, const PointWork&, const FarGeom&,           \
                                  const cx_t<T>*, double2, const double2*, void*, bool, cudaStream_t, bool,   \
-                                 const void*, int, int, long);
+                                 const void*, int, int, long);                                          \
+    template int point_rhs_group<T>(int, bool, int);                                                         \
+    template int spread_batch<T>(const PointJobs&, int, BatchSync*, unsigned, unsigned long long,            \
+                                 volatile int*, cudaStream_t);                                              \
+    template int interp_batch<T>(const PointJobs&, int, BatchSync*, cudaStream_t);                           \
+    template int node_batch<T>(const NodeJobs&, bool, BatchSync*, unsigned, unsigned long long, volatile int*, \
+                               cudaStream_t);
 SBD_NODE_INST(float)
 SBD_NODE_INST(double)
 

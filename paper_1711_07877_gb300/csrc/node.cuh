@@ -87,4 +87,85 @@ int interp_tiled(const PointRec<T>* pts, const int* perm, const PointWork& work,
                  const cx_t<T>* grid, double2 w0, const double2* sumf, void* q, bool q_complex, cudaStream_t s,
                  bool packed = false, const void* add = nullptr, int add_stride = 1, int nrhs = 1, long n_pts = 0);
 
+// --- batches of instances (sbd_matvec_batched) ------------------------------------------------
+
+constexpr int kMaxBatch = 64;      // instances per batched launch (the job tables ride in kernel parameters)
+
+// Synchronisation word of a batched launch: work-item counter and the generation barrier.
+struct BatchSync {
+    unsigned items;
+    unsigned arrive;
+    unsigned gen;
+    unsigned pad;
+};
+
+// One instance of a batched spreading or interpolation launch.
+struct PointJob {
+    const void* rec;        // PointRec<T> records of the instance (sources or targets), tile sorted
+    const int* perm;        // record -> point index
+    PointWork work;         // chunks of the records
+    int ntx, m, P, win_kind;
+    double win_beta;
+    const void* f;          // spreading: values (float64 / complex128), point l of rhs r at r * n_pts + l
+    void* q;                // interpolation: output, same layout
+    long n_pts;
+    void* grid;             // nrhs grids gstride complex elements apart
+    long gstride;
+    long clear_elems;       // spreading: T elements of the grids cleared before spreading
+    int nrhs, rg;           // right-hand sides and right-hand sides per CTA
+    int packed, complex_io; // packed real grid (Laplace); complex values (Helmholtz)
+    double2 w0;             // interpolation: weight of the xi = 0 term, its sums sum_l f_l per rhs,
+    const double2* sumf;
+    const void* add;        // and the near term add[i * nrhs + r] in the record order
+};
+struct PointJobs {
+    int count, total;       // instances, work items of all of them
+    int first[kMaxBatch];   // first item of each instance (items: chunk fastest, then rhs group)
+    PointJob job[kMaxBatch];
+};
+
+// One instance of a batched node-step launch: items are (tile, rhs), tile fastest.
+struct NodeJob {
+    const void* rec;
+    const long long* tile_start;
+    int ntx, nk, P, Ws, ntiles, win_kind;
+    double win_beta;
+    const void* kin;
+    void* kout;             // cleared by the launch before the node step
+    long kbatch;            // complex elements between the right-hand sides' grids
+    int nrhs, pad;
+};
+struct NodeJobs {
+    int count, total;
+    int first[kMaxBatch];
+    NodeJob job[kMaxBatch];
+};
+
+// The job tables travel as kernel parameters (at most 32764 bytes per launch).
+static_assert(sizeof(PointJobs) + 64 <= 32764, "point job table too large for kernel parameters");
+static_assert(sizeof(NodeJobs) + 64 <= 32764, "node job table too large for kernel parameters");
+
+// Host side of a batched launch.  spread_batch: clears every job's grids and spreads all of
+// them in one cooperative launch of persistent CTAs; the barrier between the two phases waits
+// at most limit_ns and then writes SBD_ETIMEOUT to *status (phantom: arrivals the barrier
+// waits for beyond the launched CTAs, for fault-injection tests; 0 in use).  sync: a
+// zeroed BatchSync of this launch.  interp_batch: persistent CTAs over all jobs' items
+// (sync zeroed).  node_batch: like spread_batch, clearing every job's output grids before
+// the barrier; binned (FP32, every job binned) or the fused kernel with two float planes.
+// G (8, 16 or 32): lane group of the point kernels, >= every job's stencil (the caller
+// launches one group of jobs per class).
+template <typename T>
+int spread_batch(const PointJobs& J, int G, BatchSync* sync, unsigned phantom, unsigned long long limit_ns,
+                 volatile int* status, cudaStream_t s);
+template <typename T>
+int interp_batch(const PointJobs& J, int G, BatchSync* sync, cudaStream_t s);
+template <typename T>
+int node_batch(const NodeJobs& J, bool binned, BatchSync* sync, unsigned phantom, unsigned long long limit_ns,
+               volatile int* status, cudaStream_t s);
+// Right-hand sides per CTA of the point kernels for stencil width P (complex or packed / real grid).
+template <typename T>
+int point_rhs_group(int P, bool two_planes, int nrhs);
+// Dynamic shared memory of the fused node kernel's stride for stencil P.
+int node_fused_stride(int Pk);
+
 }  // namespace sbd

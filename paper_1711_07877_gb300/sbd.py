@@ -94,6 +94,9 @@ _SIGS = {
     "sbd_matvec_graph": ([_P, _P, _P, _I32, _P], ctypes.c_int),
     "sbd_batch_create": ([_P, _P, _I32, _P, _P, ctypes.POINTER(_P)], ctypes.c_int),
     "sbd_batch_launch": ([_P, _P], ctypes.c_int),
+    "sbd_matvec_batched": ([_P, _P, _P, _P, _I32, _P], ctypes.c_int),
+    "sbd_set_device_wait": ([_D, _I32], ctypes.c_int),
+    "sbd_device_status": ([_P], ctypes.c_int),
     "sbd_batch_destroy": ([_P], ctypes.c_int),
     "sbd_far": ([_P, _P, _P, _I32, _P], ctypes.c_int),
     "sbd_close": ([_P, _P, _P, _I32, _P], ctypes.c_int),
@@ -212,6 +215,26 @@ def sbd_batch_create(plans, f, q, nrhs=None) -> int:
     out = _P()
     _check(lib.sbd_batch_create(P, R, k, F, Qp, ctypes.byref(out)), "sbd_batch_create")
     return out.value
+
+
+def sbd_matvec_batched(plans, f, q, nrhs=None, stream=None) -> None:
+    """q[i] = matvec of plans[i] on f[i] (device tensors) for every i, in one batched call."""
+    k = len(plans)
+    nrhs = nrhs or [1] * k
+    P = (_P * k)(*plans)
+    F = (_P * k)(*[_ptr(x) for x in f])
+    Qp = (_P * k)(*[_ptr(x) for x in q])
+    R = (_I32 * k)(*nrhs)
+    _check(lib.sbd_matvec_batched(P, F, Qp, R, k, _stream(stream)), "sbd_matvec_batched")
+
+
+def sbd_set_device_wait(limit_seconds: float, phantom_arrivals: int = 0) -> None:
+    _check(lib.sbd_set_device_wait(limit_seconds, phantom_arrivals), "sbd_set_device_wait")
+
+
+def sbd_device_status(stream=None) -> int:
+    """Synchronise the stream; return (and clear) the status of the bounded device waits."""
+    return lib.sbd_device_status(_stream(stream))
 
 
 def sbd_batch_launch(batch: int, stream=None) -> None:
