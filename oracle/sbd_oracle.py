@@ -597,3 +597,44 @@ def sbd_matvec_st(plan: OraclePlan, f: np.ndarray) -> np.ndarray:
     if plan.kind == "laplace" and not np.iscomplexobj(f):
         return q.real
     return q
+
+
+# ---------------------------------------------------------------------------
+# The SBD without its circular quadrature (the uniform-grid multiplier variant): the far
+# part uses the fitted series itself, G_fit(r) = const + sum_p c_p J0(rho_p r / R) (Sec. 1,
+# before the J0 terms are turned into plane waves on circles in Sec. 5), the near pairs G.
+# ---------------------------------------------------------------------------
+
+def series_kernel(plan: OraclePlan, r: np.ndarray) -> np.ndarray:
+    """G_fit(r) in kernel units: Laplace w0 - (1/2pi) sum_p alpha_p C_p J0(rho_p r / delta_max)
+    (Sec. 4.1, reading R4); Helmholtz -(1/4) sum_p alpha_p C_p J0(rho_p r / R) + (i/4) J0(kappa r)
+    (Sec. 4.2, reading R9: the J0 part is exact, without its circle)."""
+    r = np.atleast_1d(np.asarray(r, dtype=np.float64))
+    s = r / plan.scale_R
+    if plan.kind == "laplace":
+        return plan.w0 - series_value(s, plan.rho, plan.C, plan.alpha) / TWO_PI
+    return -0.25 * series_value(s, plan.rho, plan.C, plan.alpha) + 0.25j * sp.j0(plan.kappa * r)
+
+
+def series_matvec(plan: OraclePlan, f: np.ndarray, chunk: int = 256) -> np.ndarray:
+    """q_k = sum_{l != k} K(|z_k - z_l|) f_l with K = G on the near pairs (|z_k - z_l| <= delta_min,
+    reading R8) and K = G_fit beyond: the on-line output of the SBD when each J0 term is summed
+    exactly instead of by its circle of plane waves (coincident points as the self pair, R1)."""
+    z = plan.z
+    f = np.asarray(f)
+    if f.ndim == 2:
+        return np.stack([series_matvec(plan, fi, chunk) for fi in f])
+    out_dtype = np.complex128 if (plan.kind == "helmholtz" or np.iscomplexobj(f)) else np.float64
+    q = np.zeros(len(z), dtype=out_dtype)
+    for s in range(0, len(z), chunk):
+        d = np.hypot(z[s:s + chunk, 0][:, None] - z[None, :, 0], z[s:s + chunk, 1][:, None] - z[None, :, 1])
+        near = d <= plan.delta_min
+        zero = d == 0.0
+        kfit = series_kernel(plan, d.ravel()).reshape(d.shape)
+        kg = kernel_G(np.where(zero, 1.0, d), plan.kind, plan.kappa)
+        k = np.where(near, kg, kfit)
+        k = np.where(zero, 0.0, k)
+        q[s:s + chunk] = k @ f
+    if plan.kind == "laplace" and not np.iscomplexobj(f):
+        return q.real
+    return q

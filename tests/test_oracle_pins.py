@@ -417,6 +417,69 @@ def test_planted_swapped_point_sets_are_caught():
     assert np.max(np.abs(O.sbd_matvec_st(pl, f) - qd)) > 1e-6 * np.abs(f).sum()
 
 
+# --- the SBD without its circle quadrature (uniform-grid multiplier variant) ---------------------
+
+def test_series_kernel_is_the_fit_in_kernel_units():
+    # G_fit follows G within the fit tolerance (eps / 3, reading R7) on [delta_min, delta_max]
+    z = W.disk_points(400, 61)
+    for kind, kappa in (("laplace", 0.0), ("helmholtz", 20.0)):
+        pl = O.make_plan(z, kind, 0.1, 1e-6, kappa=kappa)
+        r = np.linspace(pl.delta_min, pl.delta_max, 3001)
+        err = np.max(np.abs(O.series_kernel(pl, r) - O.kernel_G(r, kind, kappa)))
+        assert err <= 1e-6 / 3 * 1.0001, (kind, err)
+
+
+def test_series_kernel_bruteforce_tiny():
+    z = W.disk_points(50, 62)
+    pl = O.make_plan(z, "helmholtz", 0.2, 1e-4, kappa=12.0)
+    for r in (0.0, 0.3, 1.1):
+        want = sum(-0.25 * float(a * c) * float(mpmath.besselj(0, float(rho) * r / pl.scale_R))
+                   for a, c, rho in zip(pl.alpha, pl.C, pl.rho)) + 0.25j * float(mpmath.besselj(0, 12.0 * r))
+        assert abs(O.series_kernel(pl, r)[0] - want) < 1e-12
+
+
+@pytest.mark.parametrize("kind", ["laplace", "helmholtz"])
+def test_series_matvec_within_eps_of_direct_sum_and_of_the_quadrature(kind):
+    z = W.disk_points(400, 63)
+    f = W.rhs(400, 64, complex_valued=kind == "helmholtz")
+    kappa = 25.0 if kind == "helmholtz" else 0.0
+    pl = O.make_plan(z, kind, math.sqrt(20 / 400), 1e-6, kappa=kappa)
+    qs = O.series_matvec(pl, f)
+    qd = O.direct_sum(z, f, kind, kappa)
+    assert np.max(np.abs(qs - qd)) <= 1e-6 / 3 * np.abs(f).sum() * 1.0001     # the fit's share of eps (R7)
+    # the circle quadrature adds at most its own share (eps / 3) on top
+    assert np.max(np.abs(qs - O.sbd_matvec(pl, f))) <= 1e-6 / 3 * np.abs(f).sum()
+
+
+def test_series_matvec_bruteforce_tiny():
+    z = W.disk_points(12, 65)
+    z[5] = z[2]                                              # a coincident pair: the self pair (R1)
+    f = W.rhs(12, 66)
+    pl = O.make_plan(z, "laplace", 0.35, 1e-5)
+    q = O.series_matvec(pl, f)
+    for k in range(12):
+        want = 0.0
+        for l in range(12):
+            r = math.hypot(*(z[k] - z[l]))
+            if l == k or r == 0.0:
+                continue
+            if r <= pl.delta_min:
+                want += -math.log(r) / (2 * math.pi) * f[l]
+            else:
+                want += (pl.w0.real - sum(float(a * c) * float(mpmath.besselj(0, float(rho) * r / pl.delta_max))
+                                          for a, c, rho in zip(pl.alpha, pl.C, pl.rho)) / (2 * math.pi)) * f[l]
+        assert abs(q[k] - want) < 1e-12 * max(1.0, abs(want))
+
+
+def test_planted_dropped_constant_in_series_is_caught(monkeypatch):
+    z = W.disk_points(300, 67)
+    f = W.rhs(300, 68)
+    pl = O.make_plan(z, "laplace", math.sqrt(20 / 300), 1e-6)
+    qd = O.direct_sum(z, f, "laplace")
+    pl.w0 = 0.0
+    assert np.max(np.abs(O.series_matvec(pl, f) - qd)) > 1e-6 * np.abs(f).sum()
+
+
 # --- planted mistakes: each must break a pin ---------------------------------------------------
 
 def test_planted_sign_error_in_rhs_is_caught(laplace_case, monkeypatch):
