@@ -611,8 +611,8 @@ def series_kernel(plan: OraclePlan, r: np.ndarray) -> np.ndarray:
     (Sec. 4.2, reading R9: the J0 part is exact, without its circle)."""
     r = np.atleast_1d(np.asarray(r, dtype=np.float64))
     s = r / plan.scale_R
-    if plan.kind == "laplace":
-        return plan.w0 - series_value(s, plan.rho, plan.C, plan.alpha) / TWO_PI
+    if plan.kind == "laplace":   # a real kernel (Sec. 4.1): w0 is stored as a complex weight
+        return complex(plan.w0).real - series_value(s, plan.rho, plan.C, plan.alpha) / TWO_PI
     return -0.25 * series_value(s, plan.rho, plan.C, plan.alpha) + 0.25j * sp.j0(plan.kappa * r)
 
 
