@@ -8,7 +8,8 @@ one sbd_matvec over the whole point set, inputs resident in HBM.  The grids
 (~0.8 GB each) and D (~2.1 GB) exceed the 129 MB L2, so no flush is needed.
 
 The default line also carries (N = 1 only, after the headline's timed region):
-balanced_delta_min (delta_min by measurement), near_fp32 (the same plan with D f in
+balanced_delta_min (delta_min by measurement), uniform_grid (the same workload with the
+node step replaced by a multiplication on the frequency grid), near_fp32 (the same plan with D f in
 float32), fp64_form (the same workload in the FP64 form), helmholtz (kappa delta_max
 = 500, FP32 and FP64 forms), table2 (separate targets and sources, the Table 2 setting),
 served (a short serving run: p50/p99 latency with a queue / plan / solve breakdown), and
@@ -169,6 +170,14 @@ def stage_bytes(info, n, nrhs, form, esz=8, near32=False):
     touched = min(m * m, n * P * P)
     vb = (16 if esz == 16 else 8) // (2 if near32 else 1)   # D value: complex for Helmholtz, float32 with the flag
     r = nrhs   # every step takes all right-hand sides in one launch: grid and value terms scale with r
+    if info.get("uniform_grid"):
+        # uniform-grid variant: the node step is one multiplication per stored frequency (grid in and
+        # out, and the coefficients: real for Laplace over the half plane, complex for Helmholtz)
+        cb = c // 2 if esz == 8 else c
+        node = (c * nk * nk + cb * nk * nk // 2) if esz == 8 else (2 * c * nk * nk + cb * nk * nk)
+        out = stage_bytes(dict(info, uniform_grid=0), n, nrhs, form, esz, near32)
+        out["node"] = node * r if esz == 8 else node * r
+        return out
     if esz == 8:
         # Laplace: real spreading grid (half a complex element per cell), Hermitian K of
         # which the half plane kx >= 0 is transformed, half the node records
@@ -608,6 +617,7 @@ def main():
         if balanced is not None:
             balanced["accuracy"] = accuracy(q_bal, qref, wl.f, idx)
     if extra and args.workload == "laplace_curves":
+        out["uniform_grid"] = uniform_line(S, torch, stream, zt, ft, wl, args, nrhs, esz, pool, idx, qref, value)
         out["near_fp32"] = near_fp32_line(S, torch, stream, zt, ft, wl, args, nrhs, esz, stages, pool, idx, qref)
         out["fp64_form"] = form_line(S, torch, stream, zt, ft, wl, args, nrhs, esz, S.SBD_FORM_FP64, pool, idx,
                                      qref, value)
@@ -623,6 +633,26 @@ def main():
         print(json.dumps(out))
     if world > 1:
         dist.destroy_process_group()
+
+
+def uniform_line(S, torch, stream, zt, ft, wl, args, nrhs, esz, pool, idx, qref, type3_value):
+    """The headline workload with SBD_FLAG_UNIFORM_GRID: the node step replaced by a multiplication by
+    the Fourier coefficients of the windowed series (no circle quadrature), FP32 form."""
+    r = Runner(S, torch, stream, zt, ft, wl, S.SBD_FORM_FP32, nrhs, flags=S.SBD_FLAG_UNIFORM_GRID)
+    try:
+        ms = r.time(min(args.steps, 20), 3)
+        st, roof = stage_report(S, r.plan, r.step, ft, args, r.info, nrhs, esz, "none", form="fp32", steps=3)
+        value = args.n * nrhs / (ms * 1e-3) / 1e9
+        line = {"flags": "SBD_FLAG_UNIFORM_GRID", "ms_per_step": ms, "value": value, "unit": UNIT,
+                "over_type3": value / type3_value, "stages": st, "roofline": roof,
+                "plan": dict(plan_keys(r.info), n_records=r.info["n_records"]),
+                "note": "node step = multiplication by the coefficients of the windowed, periodised series G_fit "
+                        "(each J0 term whole, no circle quadrature); stage 'node' is that multiplication"}
+        if pool is not None:
+            line["accuracy"] = accuracy(r.q.cpu().numpy(), qref, wl.f, idx)
+        return line
+    finally:
+        r.close()
 
 
 def near_fp32_line(S, torch, stream, zt, ft, wl, args, nrhs, esz, stages, pool, idx, qref):
@@ -891,6 +921,7 @@ def run_serve(args, rank, world, local, requests=None, short=False):
               "matvecs_max": int(max(its)) if its else None,
               "points_mean": float(np.mean([len(r.z) for r in ok])) if ok else None,
               "max_residual": float(max(r.residual for r in ok)) if ok else None,
+              "requeued_after_enomem": summ.get("requeued"), "deadline_dropped": summ.get("deadline_dropped"),
               "fit_cache": cache, "breakdown": breakdown}
     latency = {"p50_ms": summ.get("p50_ms"), "p99_ms": summ.get("p99_ms"), "mean_ms": summ.get("mean_ms")}
     if short:

@@ -105,6 +105,15 @@ typedef struct {
 #define SBD_FLAG_SPREAD_SIGMA_15 8
 /* Close correction D f in float32 (see sbd_form); with SBD_FORM_FP64 it is SBD_EINVAL. */
 #define SBD_FLAG_NEAR_FP32 16
+/* Uniform-grid multiplier variant of the far part (the fast summation the paper cites as the
+ * alternative to its type-3 transforms; no counterpart in its algorithm): each J0 term of the
+ * fit is kept whole instead of being turned into a circle of plane waves (Sec. 5), the series
+ * G_fit is windowed to the points' differences and periodised on the FFT period, and its
+ * Fourier coefficients on the frequency grid (computed in FP64 at plan time) replace the node
+ * step by one multiplication per frequency.  D is G - G_fit on the near pairs.  The operator
+ * is then the SBD without its quadrature error.  Not with the Gaussian windows;
+ * sbd_nufft_minus / sbd_nufft_plus return SBD_ENOTSUP for such a plan. */
+#define SBD_FLAG_UNIFORM_GRID 32
 
 /* Plan summary (sbd_plan_info). */
 typedef struct {
@@ -138,7 +147,9 @@ typedef struct {
     int32_t node_binned;     /* 1 when the binned node kernel (acc 3) applies to the plan */
     int64_t n_targets;       /* targets (rows of D, length of q): n_points unless sbd_plan_st */
     int32_t separate_targets;/* 1 for a plan of sbd_plan_st */
-    int32_t reserved2;
+    int32_t uniform_grid;    /* 1 for a plan made with SBD_FLAG_UNIFORM_GRID */
+    int32_t point_chunk;     /* records per work item of the spreading / interpolation kernels */
+    int32_t tuned;           /* 0 untuned, 1 tuned by timing, 2 tuned from the tuning cache */
 } sbd_plan_stats;
 
 /* ---------------------------------------------------------------------------------
@@ -406,6 +417,30 @@ int sbd_fft2(const void* in, void* out, int32_t n0, int32_t n1, int32_t sign, in
  * ------------------------------------------------------------------------------- */
 int sbd_tune(sbd_plan_t plan, int32_t reps, double* ms, void* cuda_stream);
 int sbd_set_tuning(sbd_plan_t plan, int32_t acc, int32_t sched, int32_t fft_split);
+
+/* Point-kernel work items (no counterpart in the paper): the spreading and interpolation
+ * kernels take each 64 x 64 tile's records in chunks (one CTA each); crowded tiles become
+ * several CTAs.  sbd_tune also times spreading plus interpolation for chunks of 128, 256,
+ * 512, 1024 and 2048 records and keeps the fastest (after the node variants and the FFT
+ * split).  sbd_tune_points runs that search alone (ms: host, 5 entries, mean ms per
+ * spreading + interpolation, may be NULL); sbd_set_point_chunk sets a chunk by hand
+ * (128 .. 2^20).  Blocking.  SBD_EINVAL for a null plan, reps < 1 or a chunk out of range. */
+int sbd_tune_points(sbd_plan_t plan, int32_t reps, double* ms, void* cuda_stream);
+int sbd_set_point_chunk(sbd_plan_t plan, int32_t chunk);
+
+/* Tuning cache (no counterpart in the paper): sbd_tune keeps its choice (node variant, FFT
+ * split, point chunk) per plan class (form, kernel, separate targets, uniform grid, binned
+ * node kernel, float32 near field, the grid sizes, N to a half octave) and applies a class's
+ * choice without timing when it meets the class again (sbd_plan_info's tuned = 2).
+ * Process-wide and thread safe.
+ *   sbd_tune_cache_stats   host outputs (each may be NULL): lookups that hit, missed, entries.
+ *   sbd_tune_cache_save    writes the cache as a JSON object {"class": [acc, sched, split, chunk]}.
+ *   sbd_tune_cache_load    merges such a file into the cache (SBD_EINVAL if unreadable or malformed).
+ *   sbd_tune_cache_clear   drops every entry and zeroes the counters. */
+int sbd_tune_cache_stats(int64_t* hits, int64_t* misses, int64_t* entries);
+int sbd_tune_cache_save(const char* path);
+int sbd_tune_cache_load(const char* path);
+int sbd_tune_cache_clear(void);
 
 /* ---------------------------------------------------------------------------------
  * sbd_plan_balanced - sbd_plan with delta_min chosen by measurement (Introduction,

@@ -4,6 +4,7 @@
 #include <map>
 #include <mutex>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -18,6 +19,7 @@
 #include "node.cuh"
 #include "offline.h"
 #include "sbd.h"
+#include "uniform.cuh"
 
 namespace sbd {
 
@@ -82,7 +84,10 @@ struct sbd_plan_s {
     int* circle_M = nullptr;
     int* node_perm = nullptr;          // sorted record -> record numbering
     int* half_start = nullptr;         // prefix sums of M_p / 2 (half node set), or null
-    bool half_nodes = false;           // Laplace: records for m < M_p / 2 only (Hermitian symmetry)
+    bool half_nodes = false;           // Laplace: records for m < M_p / 2 only (Hermitian symmetry); also
+                                       // the real-grid path of the transforms
+    bool uniform = false;              // uniform-grid variant: the node step is a multiplication by ucoef
+    void* ucoef = nullptr;             // nk x nk coefficients (T real for Laplace, cx_t<T> for Helmholtz)
     long long n_rec = 0;               // node records: N_xi, or N_xi / 2 with half_nodes
     int* pt_perm = nullptr;            // sorted point record -> original point index (the
                                        // internal order of D's rows and columns)
@@ -98,6 +103,8 @@ struct sbd_plan_s {
     void* q_int = nullptr;             // D f in internal order, interleaved
     bool d32 = false;                  // D's values and f_int in FP32 (SBD_FLAG_NEAR_FP32)
     PointWork pt_work{nullptr, nullptr, 0};   // chunks of the point records (spread, interp)
+    std::vector<long long> pt_ts, tpt_ts;     // tile starts of the source / target records (host)
+    int pt_chunk = kPointChunk;               // records per work item (sbd_tune)
     long long* node_tile_start = nullptr;
     void* ghat = nullptr;              // n_xi weighted node values (scratch of the two-kernel node step)
     bool node_fused = true;            // one-kernel node step (shared memory permitting)
@@ -263,11 +270,27 @@ SpreadDeconv spread_deconv_of(const sbd_plan_s* p) {
     return SpreadDeconv{p->psi, static_cast<int>(p->np.psi.size()), 1.0 / (p->np.kmax * p->np.kmax), p->np.h};
 }
 
+// Fills the work list arrays of *work (capacity for the smallest chunk) from tile starts ts.
+int fill_work(const std::vector<long long>& ts, int chunk, PointWork* work, cudaStream_t s) {
+    std::vector<long long> wb;
+    std::vector<int> wt;
+    point_work_list(ts, chunk, wb, wt);
+    SBD_CUDA_TRY(cudaMemcpyAsync(const_cast<long long*>(work->begin), wb.data(), sizeof(long long) * wb.size(),
+                                 cudaMemcpyHostToDevice, s));
+    SBD_CUDA_TRY(cudaMemcpyAsync(const_cast<int*>(work->tile), wt.data(), sizeof(int) * wt.size(),
+                                 cudaMemcpyHostToDevice, s));
+    SBD_CUDA_TRY(cudaStreamSynchronize(s));   // the host vectors go out of scope
+    work->count = static_cast<int>(wt.size());
+    return SBD_OK;
+}
+
 // Records of n points z (stencil start cell and fraction on the spreading grid), sorted by
-// 64 x 64 tile (perm: record -> point index), and the work list of the point kernels: each
-// tile's records in chunks of at most kPointChunk.
+// 64 x 64 tile (perm: record -> point index), the tile starts (host, ts) and the work list of
+// the point kernels: each tile's records in chunks of at most p->pt_chunk (arrays sized for
+// the smallest chunk sbd_tune tries).
 template <typename T>
-int point_records(sbd_plan_s* p, const double* z, long n, void** recs, int** perm, PointWork* work, cudaStream_t s) {
+int point_records(sbd_plan_s* p, const double* z, long n, void** recs, int** perm, PointWork* work,
+                  std::vector<long long>& ts, cudaStream_t s) {
     const NufftParams& np = p->np;
     PointRec<T>* pts0 = nullptr;
     SBD_CUDA_TRY(cudaMallocAsync(&pts0, sizeof(PointRec<T>) * n, s));
@@ -282,17 +305,17 @@ int point_records(sbd_plan_s* p, const double* z, long n, void** recs, int** per
     if ((rc = tile_sort<PointRec<T>>(pts0, n, np.m, static_cast<PointRec<T>*>(*recs), *perm, tile_start, s)))
         return rc;
     SBD_CUDA_TRY(cudaFreeAsync(pts0, s));
-    std::vector<long long> ts(static_cast<size_t>(ntm) * ntm + 1), wb;
-    std::vector<int> wt;
+    ts.assign(static_cast<size_t>(ntm) * ntm + 1, 0);
     SBD_CUDA_TRY(cudaMemcpyAsync(ts.data(), tile_start, sizeof(long long) * ts.size(), cudaMemcpyDeviceToHost, s));
     SBD_CUDA_TRY(cudaStreamSynchronize(s));
-    point_work_list(ts, wb, wt);
+    long long cap = 0;
+    for (size_t t = 0; t + 1 < ts.size(); ++t) cap += (ts[t + 1] - ts[t] + kPointChunks[0] - 1) / kPointChunks[0];
     long long* wbd = nullptr;
     int* wtd = nullptr;
-    if ((rc = upload(p, &wbd, wb, s))) return rc;
-    if ((rc = upload(p, &wtd, wt, s))) return rc;
-    *work = PointWork{wbd, wtd, static_cast<int>(wt.size())};
-    return SBD_OK;
+    if ((rc = dev_alloc(p, reinterpret_cast<void**>(&wbd), sizeof(long long) * (cap + 1)))) return rc;
+    if ((rc = dev_alloc(p, reinterpret_cast<void**>(&wtd), sizeof(int) * std::max<long long>(cap, 1)))) return rc;
+    *work = PointWork{wbd, wtd, 0};
+    return fill_work(ts, p->pt_chunk, work, s);
 }
 
 template <typename T>
@@ -311,14 +334,32 @@ int build_far(sbd_plan_s* p, cudaStream_t s) {
         const int urc = upload(p, &p->psi, np.psi, s);
         if (urc) return urc;
     }
-    int rc = point_records<T>(p, p->z, p->n, &p->pts, &p->pt_perm, &p->pt_work, s);
+    int rc = point_records<T>(p, p->z, p->n, &p->pts, &p->pt_perm, &p->pt_work, p->pt_ts, s);
     if (rc) return rc;
     if (p->separate) {
-        if ((rc = point_records<T>(p, p->zt, p->n_tgt, &p->tpts, &p->tpt_perm, &p->tpt_work, s))) return rc;
+        if ((rc = point_records<T>(p, p->zt, p->n_tgt, &p->tpts, &p->tpt_perm, &p->tpt_work, p->tpt_ts, s)))
+            return rc;
     } else {
         p->tpts = p->pts;
         p->tpt_perm = p->pt_perm;
         p->tpt_work = p->pt_work;
+    }
+    if (p->uniform) {
+        // no quadrature nodes: the coefficients of the windowed series on the frequency grid
+        p->half_nodes = p->kind == SBD_LAPLACE;
+        p->n_rec = 0;
+        p->node_fused = false;
+        const bool cc = p->kind == SBD_HELMHOLTZ;
+        const size_t nk = np.nk;
+        if ((rc = dev_alloc(p, &p->ucoef, (cc ? sizeof(cx_t<T>) : sizeof(T)) * nk * nk))) return rc;
+        if ((rc = uniform_coefficients<T>(fit, np, spread_deconv_of(p), cc, p->ucoef, s))) return rc;
+        const size_t e = sizeof(cx_t<T>) * static_cast<size_t>(p->max_nrhs);
+        const size_t m = np.m;
+        if ((rc = dev_alloc(p, &p->wsX, e * m * m))) return rc;
+        if ((rc = dev_alloc(p, &p->wsA, e * m * nk))) return rc;
+        if ((rc = dev_alloc(p, &p->wsB, e * nk * nk))) return rc;
+        if ((rc = dev_alloc(p, &p->wsC, e * nk * nk))) return rc;
+        return SBD_OK;
     }
     std::vector<int> start(fit.n_circles + 1, 0);
     for (int c = 0; c < fit.n_circles; ++c) start[c + 1] = start[c] + fit.M[c];
@@ -420,7 +461,7 @@ int forward_fft(sbd_plan_s* p, const cx_t<T>* X, cx_t<T>* A, cx_t<T>* Tr, cx_t<T
     const NufftParams& np = p->np;
     const int m = np.m, nk = np.nk, n = np.n;
     const GridStrides g = grid_strides(np);
-    const T* dec = static_cast<const T*>(p->dec);
+    const T* dec = p->uniform ? nullptr : static_cast<const T*>(p->dec);
     // along x (rows y), precorrection exp(sigma |x|^2) fused into the load
     const int sp = p->fft_split;
     int rc = fft_rows<T>(X, m, m, -m / 2, A, nk, nk, -nk / 2, m, n, -1, dec, dec, nullptr, nullptr, s, 0, 0, kIoPlain,
@@ -442,7 +483,7 @@ int inverse_fft(sbd_plan_s* p, const cx_t<T>* K2, cx_t<T>* A, cx_t<T>* Tr, cx_t<
     const NufftParams& np = p->np;
     const int m = np.m, nk = np.nk, n = np.n;
     const GridStrides g = grid_strides(np);
-    const T* dec = static_cast<const T*>(p->dec);
+    const T* dec = p->uniform ? nullptr : static_cast<const T*>(p->dec);
     const int sp = p->fft_split;
     int rc = fft_rows<T>(K2, nk, nk, -nk / 2, A, m, m, -m / 2, nk, n, +1, nullptr, nullptr, nullptr, nullptr, s,
                          fold ? nk : 0, 0, kIoPlain, sp, nb, g.K, g.A);
@@ -467,7 +508,7 @@ int forward_fft_real(sbd_plan_s* p, const cx_t<T>* Xp, cx_t<T>* A, cx_t<T>* Tr, 
     const int m = np.m, nk = np.nk, n = np.n;
     const GridStrides g = grid_strides(np, true);
     const int lo = kx_low<T>(p), w2 = nk - lo;
-    const T* dec = static_cast<const T*>(p->dec);
+    const T* dec = p->uniform ? nullptr : static_cast<const T*>(p->dec);
     const int sp = p->fft_split;
     int rc = fft_rows<T>(Xp, m, m, -m / 2, A, w2, w2, lo - nk / 2, m / 2, n, -1, dec, dec, nullptr, nullptr, s, 0, 0,
                          kIoPairFwd, sp, nb, g.X, g.A);
@@ -488,10 +529,12 @@ int inverse_fft_real(sbd_plan_s* p, const cx_t<T>* S, cx_t<T>* A, cx_t<T>* Tr, c
     const int m = np.m, nk = np.nk, n = np.n;
     const GridStrides g = grid_strides(np, true);
     const int J = nk / 2;
-    const T* dec = static_cast<const T*>(p->dec);
+    const T* dec = p->uniform ? nullptr : static_cast<const T*>(p->dec);
     const int sp = p->fft_split;
+    // the node step's S completes by the Hermitian fold; the uniform variant's product is whole
+    const int herm = p->uniform ? 0 : nk;
     int rc = fft_rows<T>(S + static_cast<long>(J) * nk, nk, nk, -nk / 2, A, m, m, -m / 2, J, n, +1, nullptr, nullptr,
-                         nullptr, nullptr, s, nk, J, kIoPlain, sp, nb, g.K, g.A);
+                         nullptr, nullptr, s, herm, herm ? J : 0, kIoPlain, sp, nb, g.K, g.A);
     if (rc) return rc;
     if ((rc = transpose<T>(A, m, g.A, Tr, J, g.K, J, m, nb, s))) return rc;   // [kx][y] -> [y][kx]
     return fft_rows<T>(Tr, J, J, 0, Xp, m, m, -m / 2, m / 2, n, +1, nullptr, nullptr, dec, dec, s, 0, 0, kIoPairInv,
@@ -523,7 +566,12 @@ int far_apply(sbd_plan_s* p, const void* f, void* q, int nrhs, cudaStream_t s, c
     if ((rc = real ? forward_fft_real<T>(p, X, A, C, B, s, nrhs) : forward_fft<T>(p, X, A, C, B, s, nrhs))) return rc;
     t2.end();
     StepTimer t3(p, s, SBD_STAGE_NODE);
-    if (p->node_fused) {
+    if (p->uniform) {
+        // rows kx >= 0 (the real path's inverse reads only those) or all rows
+        const int nk = p->np.nk;
+        if ((rc = uniform_multiply<T>(B, p->ucoef, p->kind == SBD_HELMHOLTZ, C, nk, real ? nk / 2 : 0, nrhs,
+                                      static_cast<long>(nk) * nk, s))) return rc;
+    } else if (p->node_fused) {
         if ((rc = node_step_fused<T>(static_cast<const NodeRec<T>*>(p->nodes), p->node_tile_start, p->geom, B, C,
                                      p->tuning, s, nrhs))) return rc;
     } else if ((rc = node_step_tiled<T>(static_cast<const NodeRec<T>*>(p->nodes), p->node_tile_start, p->geom, B,
@@ -589,8 +637,10 @@ int check_plan_call(sbd_plan_t p, const void* a, const void* b) {
 // non-negative counts and tolerances.
 bool options_valid(const sbd_options& o) {
     const int known = SBD_FLAG_GAUSSIAN_NODES | SBD_FLAG_GAUSSIAN_SPREAD | SBD_FLAG_SPREAD_SIGMA_2 |
-                      SBD_FLAG_SPREAD_SIGMA_15 | SBD_FLAG_NEAR_FP32;
+                      SBD_FLAG_SPREAD_SIGMA_15 | SBD_FLAG_NEAR_FP32 | SBD_FLAG_UNIFORM_GRID;
+    const int not_uniform = SBD_FLAG_GAUSSIAN_NODES | SBD_FLAG_GAUSSIAN_SPREAD;
     return (o.form == SBD_FORM_FP64 || o.form == SBD_FORM_FP32) && (o.flags & ~known) == 0 &&
+           !((o.flags & SBD_FLAG_UNIFORM_GRID) && (o.flags & not_uniform)) &&
            !((o.flags & SBD_FLAG_NEAR_FP32) && o.form != SBD_FORM_FP32) &&
            !((o.flags & SBD_FLAG_SPREAD_SIGMA_2) && (o.flags & SBD_FLAG_SPREAD_SIGMA_15)) &&
            !((o.flags & SBD_FLAG_GAUSSIAN_SPREAD) && (o.flags & SBD_FLAG_SPREAD_SIGMA_15)) && o.fixed_P >= 0 &&
@@ -608,7 +658,9 @@ int plan_transform_params(const SbdFit& fit, const sbd_options& o, double eps, d
     const int kwin = (o.flags & SBD_FLAG_GAUSSIAN_NODES) ? 0 : 1;
     const int swin = (o.flags & SBD_FLAG_GAUSSIAN_SPREAD) ? 0 : 1;
     const int sigma_mode = (o.flags & SBD_FLAG_SPREAD_SIGMA_15) ? 1 : (o.flags & SBD_FLAG_SPREAD_SIGMA_2) ? 2 : 0;
-    int rc = nufft_params(fit, half, cx, cy, tol, o.form == SBD_FORM_FP32, kwin, swin, sigma_mode, n, np, err);
+    int rc = (o.flags & SBD_FLAG_UNIFORM_GRID)
+                 ? uniform_params(fit, half, cx, cy, tol, o.form == SBD_FORM_FP32, swin, sigma_mode, n, np, err)
+                 : nufft_params(fit, half, cx, cy, tol, o.form == SBD_FORM_FP32, kwin, swin, sigma_mode, n, np, err);
     if (rc) return rc;
     if (np.n > fft_max_length(o.form == SBD_FORM_FP64)) {
         err = "sbd_plan: FFT length " + std::to_string(np.n) + " exceeds the row kernel limit";
@@ -844,7 +896,8 @@ int plan_impl(const double* targets, int64_t n_t, const double* points, int64_t 
         set_error(err);
         return fail(rc);
     }
-    if ((rc = near_tables(fit, p->nt, err))) {
+    p->uniform = (o.flags & SBD_FLAG_UNIFORM_GRID) != 0;
+    if ((rc = near_tables(fit, p->nt, err, p->uniform))) {
         set_error(err);
         return fail(rc);
     }
@@ -1097,6 +1150,10 @@ int sbd_profile_read(sbd_plan_t p, double* ms, int64_t* count) {
 int sbd_nufft_minus(sbd_plan_t p, const void* f, void* fhat, void* cuda_stream) {
     int rc = check_plan_call(p, f, fhat);
     if (rc) return rc;
+    if (p->uniform) {
+        set_error("sbd_nufft_minus: a uniform-grid plan has no quadrature nodes");
+        return SBD_ENOTSUP;
+    }
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     return p->form == SBD_FORM_FP32 ? nufft_minus_impl<float>(p, f, fhat, s) : nufft_minus_impl<double>(p, f, fhat, s);
 }
@@ -1104,6 +1161,10 @@ int sbd_nufft_minus(sbd_plan_t p, const void* f, void* fhat, void* cuda_stream) 
 int sbd_nufft_plus(sbd_plan_t p, const void* ghat, void* q, void* cuda_stream) {
     int rc = check_plan_call(p, ghat, q);
     if (rc) return rc;
+    if (p->uniform) {
+        set_error("sbd_nufft_plus: a uniform-grid plan has no quadrature nodes");
+        return SBD_ENOTSUP;
+    }
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     return p->form == SBD_FORM_FP32 ? nufft_plus_impl<float>(p, ghat, q, s) : nufft_plus_impl<double>(p, ghat, q, s);
 }
@@ -1117,6 +1178,9 @@ int sbd_plan_info(sbd_plan_t p, sbd_plan_stats* o) {
     o->n_points = p->n;
     o->n_targets = p->n_tgt;
     o->separate_targets = p->separate ? 1 : 0;
+    o->uniform_grid = p->uniform ? 1 : 0;
+    o->point_chunk = p->pt_chunk;
+    o->tuned = p->tuned;
     o->P = p->fit.P;
     o->n_circles = p->fit.n_circles;
     o->n_xi = p->fit.n_xi;
@@ -1159,6 +1223,207 @@ int sbd_set_tuning(sbd_plan_t p, int32_t acc, int32_t sched, int32_t fft_split) 
     return SBD_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+// Tuning cache: the tuner's choice per plan class, so that plans of the same class (a
+// server's repeated geometries, a bench's reruns) skip the timing.  Process-wide, thread safe;
+// sbd_tune_cache_save / _load persist it as a JSON object {"key": [acc, sched, fft_split, chunk]}.
+struct TuneChoice {
+    int acc, sched, fft_split, chunk;
+};
+std::mutex g_tune_mu;
+std::map<std::string, TuneChoice> g_tune;
+long long g_tune_hits = 0, g_tune_misses = 0;
+
+std::string tune_key(const sbd_plan_s* p) {
+    // form, kind, separate targets, uniform grid, binned node kernel, float32 near field, the grid
+    // sizes and N to a half octave
+    const int nclass = static_cast<int>(std::lround(2.0 * std::log2(std::max(1.0, static_cast<double>(p->n)))));
+    char buf[160];
+    std::snprintf(buf, sizeof buf, "f%d_k%d_s%d_u%d_b%d_d%d_m%d_nk%d_n%d_N%d", p->form, p->kind, p->separate ? 1 : 0,
+                  p->uniform ? 1 : 0, p->node_binned ? 1 : 0, p->d32 ? 1 : 0, p->np.m, p->np.nk, p->np.n, nclass);
+    return buf;
+}
+
+int set_chunk(sbd_plan_s* p, int chunk, cudaStream_t s) {
+    p->pt_chunk = chunk;
+    int rc = fill_work(p->pt_ts, chunk, &p->pt_work, s);
+    if (rc) return rc;
+    if (p->separate) return fill_work(p->tpt_ts, chunk, &p->tpt_work, s);
+    p->tpt_work = p->pt_work;
+    return SBD_OK;
+}
+
+// Times spreading plus interpolation (reps launches each, after one warm-up, on a constant
+// non-zero f) for every chunk of kPointChunks; keeps the fastest.  ms: kNumPointChunks entries.
+template <typename T>
+int tune_chunks(sbd_plan_s* p, int reps, double* ms, cudaStream_t s) {
+    const bool cplx = p->kind == SBD_HELMHOLTZ;
+    const size_t esz = cplx ? 16 : 8;
+    void *f = nullptr, *q = nullptr;
+    if (cudaMallocAsync(&f, esz * p->n, s) != cudaSuccess || cudaMallocAsync(&q, esz * p->n_tgt, s) != cudaSuccess) {
+        cudaGetLastError();
+        if (f) cudaFreeAsync(f, s);
+        set_error("sbd_tune: cannot allocate the timing vectors");
+        return SBD_ENOMEM;
+    }
+    SBD_CUDA_TRY(cudaMemsetAsync(f, 0x3f, esz * p->n, s));
+    SBD_CUDA_TRY(cudaMemsetAsync(p->sumf, 0, sizeof(double2), s));
+    cudaEvent_t a = nullptr, b = nullptr;
+    SBD_CUDA_TRY(cudaEventCreate(&a));
+    SBD_CUDA_TRY(cudaEventCreate(&b));
+    auto* X = static_cast<cx_t<T>*>(p->wsX);
+    const bool real = p->half_nodes;
+    auto pass = [&]() {
+        int r = spread_tiled<T>(static_cast<const PointRec<T>*>(p->pts), p->pt_perm, p->pt_work, p->geom, f, cplx, X, s,
+                                real, 1, p->n);
+        if (!r) r = interp_tiled<T>(static_cast<const PointRec<T>*>(p->tpts), p->tpt_perm, p->tpt_work, p->geom, X,
+                                    make_double2(0, 0), p->sumf, q, cplx, s, real, nullptr, 1, 1, p->n_tgt);
+        return r;
+    };
+    double best = 1e300;
+    int pick = p->pt_chunk, rc = SBD_OK;
+    for (int c = 0; c < kNumPointChunks && !rc; ++c) {
+        if ((rc = set_chunk(p, kPointChunks[c], s)) || (rc = pass())) break;
+        SBD_CUDA_TRY(cudaEventRecord(a, s));
+        for (int r = 0; r < reps && !rc; ++r) rc = pass();
+        if (rc) break;
+        float t_ms = 0.f;
+        SBD_CUDA_TRY(cudaEventRecord(b, s));
+        SBD_CUDA_TRY(cudaEventSynchronize(b));
+        SBD_CUDA_TRY(cudaEventElapsedTime(&t_ms, a, b));
+        const double per = static_cast<double>(t_ms) / reps;
+        if (ms) ms[c] = per;
+        if (per < best) {
+            best = per;
+            pick = kPointChunks[c];
+        }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    cudaFreeAsync(f, s);
+    cudaFreeAsync(q, s);
+    if (rc) return rc;
+    return set_chunk(p, pick, s);
+}
+
+// The last step of sbd_tune: the point chunk, then the class's choice into the cache.
+int finish_tune(sbd_plan_s* p, int reps, const std::string& key, cudaStream_t s) {
+    int rc = p->form == SBD_FORM_FP32 ? tune_chunks<float>(p, reps, nullptr, s) : tune_chunks<double>(p, reps, nullptr, s);
+    if (rc) return rc;
+    p->tuned = 1;
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tune[key] = TuneChoice{p->tuning.acc, p->tuning.sched, p->fft_split, p->pt_chunk};
+    return SBD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int sbd_tune_points(sbd_plan_t p, int32_t reps, double* ms, void* cuda_stream) {
+    if (!p || reps < 1) {
+        set_error("sbd_tune_points: null plan or reps < 1");
+        return SBD_EINVAL;
+    }
+    if (ms)
+        for (int c = 0; c < kNumPointChunks; ++c) ms[c] = -1.0;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    return p->form == SBD_FORM_FP32 ? tune_chunks<float>(p, reps, ms, s) : tune_chunks<double>(p, reps, ms, s);
+}
+
+int sbd_set_point_chunk(sbd_plan_t p, int32_t chunk) {
+    if (!p || chunk < kPointChunks[0] || chunk > (1 << 20)) {
+        set_error("sbd_set_point_chunk: null plan or chunk outside [128, 2^20]");
+        return SBD_EINVAL;
+    }
+    return set_chunk(p, chunk, p->alloc_stream);
+}
+
+int sbd_tune_cache_stats(int64_t* hits, int64_t* misses, int64_t* entries) {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    if (hits) *hits = g_tune_hits;
+    if (misses) *misses = g_tune_misses;
+    if (entries) *entries = static_cast<int64_t>(g_tune.size());
+    return SBD_OK;
+}
+
+int sbd_tune_cache_clear(void) {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tune.clear();
+    g_tune_hits = g_tune_misses = 0;
+    return SBD_OK;
+}
+
+int sbd_tune_cache_save(const char* path) {
+    if (!path) {
+        set_error("sbd_tune_cache_save: null path");
+        return SBD_EINVAL;
+    }
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    FILE* fp = std::fopen(path, "w");
+    if (!fp) {
+        set_error(std::string("sbd_tune_cache_save: cannot open ") + path);
+        return SBD_EINVAL;
+    }
+    std::fprintf(fp, "{");
+    bool first = true;
+    for (const auto& kv : g_tune) {
+        std::fprintf(fp, "%s\n  \"%s\": [%d, %d, %d, %d]", first ? "" : ",", kv.first.c_str(), kv.second.acc,
+                     kv.second.sched, kv.second.fft_split, kv.second.chunk);
+        first = false;
+    }
+    std::fprintf(fp, "\n}\n");
+    std::fclose(fp);
+    return SBD_OK;
+}
+
+int sbd_tune_cache_load(const char* path) {
+    if (!path) {
+        set_error("sbd_tune_cache_load: null path");
+        return SBD_EINVAL;
+    }
+    FILE* fp = std::fopen(path, "r");
+    if (!fp) {
+        set_error(std::string("sbd_tune_cache_load: cannot open ") + path);
+        return SBD_EINVAL;
+    }
+    std::string text;
+    char buf[4096];
+    size_t got;
+    while ((got = std::fread(buf, 1, sizeof buf, fp)) > 0) text.append(buf, got);
+    std::fclose(fp);
+    // a flat object of "key": [acc, sched, fft_split, chunk] entries
+    std::map<std::string, TuneChoice> read;
+    size_t i = text.find('{');
+    if (i == std::string::npos) {
+        set_error("sbd_tune_cache_load: not a JSON object");
+        return SBD_EINVAL;
+    }
+    for (;;) {
+        const size_t k0 = text.find('"', i + 1);
+        if (k0 == std::string::npos) break;
+        const size_t k1 = text.find('"', k0 + 1);
+        const size_t l0 = text.find('[', k1 == std::string::npos ? k0 : k1);
+        const size_t l1 = text.find(']', l0 == std::string::npos ? k0 : l0);
+        TuneChoice c{};
+        if (k1 == std::string::npos || l0 == std::string::npos || l1 == std::string::npos ||
+            std::sscanf(text.c_str() + l0 + 1, "%d , %d , %d , %d", &c.acc, &c.sched, &c.fft_split, &c.chunk) != 4 ||
+            c.acc < 0 || c.acc > 3 || c.sched < 0 || c.sched > 1 || (c.fft_split != 0 && c.fft_split != 2) ||
+            c.chunk < kPointChunks[0] || c.chunk > (1 << 20)) {
+            set_error("sbd_tune_cache_load: malformed entry");
+            return SBD_EINVAL;
+        }
+        read[text.substr(k0 + 1, k1 - k0 - 1)] = c;
+        i = l1;
+    }
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    for (const auto& kv : read) g_tune[kv.first] = kv.second;
+    return SBD_OK;
+}
+
 int sbd_tune(sbd_plan_t p, int32_t reps, double* ms, void* cuda_stream) {
     if (!p || reps < 1) {
         set_error("sbd_tune: null plan or reps < 1");
@@ -1167,6 +1432,29 @@ int sbd_tune(sbd_plan_t p, int32_t reps, double* ms, void* cuda_stream) {
     if (ms)
         for (int v = 0; v < 10; ++v) ms[v] = -1.0;
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    const std::string key = tune_key(p);
+    {
+        TuneChoice c{};
+        bool hit = false;
+        {
+            std::lock_guard<std::mutex> lock(g_tune_mu);
+            auto it = g_tune.find(key);
+            if (it != g_tune.end()) {
+                c = it->second;
+                hit = true;
+                ++g_tune_hits;
+            } else {
+                ++g_tune_misses;
+            }
+        }
+        if (hit) {   // the class was tuned before: apply its choice without timing
+            p->tuning.acc = c.acc;
+            p->tuning.sched = c.sched;
+            p->fft_split = c.fft_split;
+            p->tuned = 2;
+            return set_chunk(p, c.chunk, s);
+        }
+    }
     // row-FFT phases: time the forward transform with split 0 and 2, keep the faster
     {
         cudaEvent_t a, b;
@@ -1210,7 +1498,7 @@ int sbd_tune(sbd_plan_t p, int32_t reps, double* ms, void* cuda_stream) {
         p->fft_split = pick;
         if (rc) return rc;
     }
-    if (!p->node_fused) return SBD_OK;
+    if (!p->node_fused) return finish_tune(p, reps, key, s);
     // non-zero input: with zeros every compare-and-swap would succeed at once, which
     // hides the retries that concurrent adds to one cell cost with real data
     const long cells = static_cast<long>(p->np.nk) * p->np.nk;
@@ -1262,8 +1550,7 @@ int sbd_tune(sbd_plan_t p, int32_t reps, double* ms, void* cuda_stream) {
     cudaEventDestroy(b);
     if (rc) return rc;
     p->tuning = pick;
-    p->tuned = 1;
-    return SBD_OK;
+    return finish_tune(p, reps, key, s);
 }
 
 // delta_min by measurement: Theorem 1 leaves alpha in [0, 1/6] free and the Introduction asks
@@ -1691,8 +1978,14 @@ int batched_impl(const sbd_plan_t* plans, const void* const* f, void* const* q, 
         auto* A = static_cast<cx_t<T>*>(p->wsA);
         auto* B = static_cast<cx_t<T>*>(p->wsB);
         auto* C = static_cast<cx_t<T>*>(p->wsC);
-        return p->half_nodes ? forward_fft_real<T>(p, X, A, C, B, p->b_stream, nrhs[i])
-                             : forward_fft<T>(p, X, A, C, B, p->b_stream, nrhs[i]);
+        int r = p->half_nodes ? forward_fft_real<T>(p, X, A, C, B, p->b_stream, nrhs[i])
+                              : forward_fft<T>(p, X, A, C, B, p->b_stream, nrhs[i]);
+        if (!r && p->uniform) {   // the uniform-grid plans' node step: the multiplication, on their stream
+            const int nk = p->np.nk;
+            r = uniform_multiply<T>(B, p->ucoef, p->kind == SBD_HELMHOLTZ, C, nk, p->half_nodes ? nk / 2 : 0,
+                                    nrhs[i], static_cast<long>(nk) * nk, p->b_stream);
+        }
+        return r;
     });
     if (rc) return rc;
     // node step: one cooperative launch per kernel family; the two-kernel fallback per plan
@@ -1701,7 +1994,7 @@ int batched_impl(const sbd_plan_t* plans, const void* const* f, void* const* q, 
         for (int i = 0; i < count; ++i) {
             sbd_plan_s* p = plans[i];
             const bool binned = sizeof(T) == 4 && p->node_binned && p->tuning.acc == 3;
-            if (!p->node_fused || binned != (fam == 0)) continue;
+            if (p->uniform || !p->node_fused || binned != (fam == 0)) continue;
             NodeJob& jb = J.job[J.count];
             jb.rec = p->nodes;
             jb.tile_start = p->node_tile_start;
@@ -1724,7 +2017,7 @@ int batched_impl(const sbd_plan_t* plans, const void* const* f, void* const* q, 
     }
     for (int i = 0; i < count; ++i) {
         sbd_plan_s* p = plans[i];
-        if (!p->node_fused &&
+        if (!p->node_fused && !p->uniform &&
             (rc = node_step_tiled<T>(static_cast<const NodeRec<T>*>(p->nodes), p->node_tile_start, p->geom,
                                      static_cast<const cx_t<T>*>(p->wsB), static_cast<cx_t<T>*>(p->ghat),
                                      static_cast<cx_t<T>*>(p->wsC), s, nrhs[i]))) return rc;

@@ -1202,12 +1202,12 @@ int node_step_tiled(const NodeRec<T>* nodes, const long long* tile_start, const 
     return SBD_OK;
 }
 
-void point_work_list(const std::vector<long long>& tile_start, std::vector<long long>& begin,
+void point_work_list(const std::vector<long long>& tile_start, int chunk, std::vector<long long>& begin,
                      std::vector<int>& tile) {
     begin.clear();
     tile.clear();
     for (size_t t = 0; t + 1 < tile_start.size(); ++t)
-        for (long long b = tile_start[t]; b < tile_start[t + 1]; b += kPointChunk) {
+        for (long long b = tile_start[t]; b < tile_start[t + 1]; b += chunk) {
             begin.push_back(b);
             tile.push_back(static_cast<int>(t));
         }

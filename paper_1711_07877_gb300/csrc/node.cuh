@@ -54,17 +54,20 @@ int node_step_fused(const NodeRec<T>* nodes, const long long* tile_start, const 
                     const cx_t<T>* kin, cx_t<T>* kout, const NodeTuning& t, cudaStream_t s, int nb = 1);
 
 // Work list of the point kernels (spreading, interpolation): item w is the records
-// [begin[w], begin[w + 1]) of the 64 x 64 tile tile[w], at most kPointChunk of them; the
+// [begin[w], begin[w + 1]) of the 64 x 64 tile tile[w], at most `chunk` of them; the
 // records of a tile (sorted by tile_sort) are split into consecutive chunks, so that a tile
-// where many points crowd becomes several CTAs instead of one long one.
+// where many points crowd becomes several CTAs instead of one long one.  The chunk is a
+// plan parameter chosen by sbd_tune among kPointChunks (default kPointChunk).
 constexpr int kPointChunk = 512;
+constexpr int kPointChunks[] = {128, 256, 512, 1024, 2048};
+constexpr int kNumPointChunks = 5;
 struct PointWork {
     const long long* begin;   // count + 1 entries (device)
     const int* tile;          // count entries (device)
     int count;
 };
 // Host: the chunk list of a tile_start table (ntiles + 1 prefix offsets).
-void point_work_list(const std::vector<long long>& tile_start, std::vector<long long>& begin,
+void point_work_list(const std::vector<long long>& tile_start, int chunk, std::vector<long long>& begin,
                      std::vector<int>& tile);
 
 // grid (m x m, fully written) = spreading of f (float64 or complex128, original order).

@@ -786,7 +786,118 @@ int nufft_params(const SbdFit& fit, double half_extent, double cx, double cy, do
     return SBD_OK;
 }
 
-int near_tables(const SbdFit& fit, NearTables& o, std::string& err) {
+int uniform_params(const SbdFit& fit, double half_extent, double cx, double cy, double tol, bool fp32, int swin,
+                   int sigma_mode, long n_points, NufftParams& o, std::string& err) {
+    double S = 0.0;
+    for (int c = 0; c < fit.n_circles; ++c) S = std::max(S, fit.radius[c]);
+    if (!(S > 0.0) || !(half_extent > 0.0)) {
+        err = "degenerate geometry for the transform";
+        return SBD_EINVAL;
+    }
+    if (fp32) tol = std::max(tol, 3e-7);
+    tol = std::max(tol, 1e-15);
+    // window of the periodised series: flat on the differences of the points (|t| <= 2 half),
+    // an ES-bump transition over a tenth of that; its spectrum reaches B = 2 beta / tau
+    o.uniform = true;
+    o.wa = 2.0 * half_extent;
+    o.wtau = 0.1 * o.wa;
+    o.wbeta = std::max(8.0, 1.1 * std::log(1.0 / tol));
+    const double B = 2.0 * o.wbeta / o.wtau;
+    o.kcut = S + B;
+    // spreading: the rules of nufft_params, with K in place of S
+    double sig = 2.0;
+    if (swin == 1) {
+        if (sigma_mode == 1) {
+            sig = 1.5;
+        } else if (sigma_mode == 0) {
+            const double m2 = 2.0 * half_extent * (2.0 * o.kcut) / kPi;
+            if (m2 * m2 > 20.0 * static_cast<double>(n_points)) sig = 1.5;
+        }
+    }
+    const int pmax = fp32 ? 16 : 32;
+    int Ps;
+    if (swin == 1) Ps = static_cast<int>(std::ceil(std::log(10.0 / tol) / (kPi * std::sqrt(1.0 - 1.0 / sig))));
+    else Ps = static_cast<int>(std::ceil((3.0 / kPi) * std::log(0.1 / tol)));
+    Ps = std::max(4, std::min(pmax, Ps + (Ps & 1)));
+    o.Ps = Ps;
+    o.Pk = 0;
+    o.kwin = 1;
+    o.swin = swin;
+    o.tol = tol;
+    o.sigma_s = sig;
+    o.h = kPi / (sig * o.kcut);
+    if (swin == 1) {
+        o.tau = 0.0;
+        o.beta_s = 2.3 * Ps * (1.0 - 0.5 / sig) / 0.75;
+    } else {
+        const double u = Ps * kPi / 24.0;
+        o.tau = u / (o.kcut * o.kcut);
+        o.beta_s = o.h * o.h / (4.0 * o.tau);
+    }
+    o.m = good_fft_size(static_cast<int>(std::ceil(2.0 * half_extent / o.h)) + Ps + 4);
+    o.n = good_fft_size(std::max(o.m + Ps + 4, static_cast<int>(std::ceil(2.0 * (o.wa + o.wtau) / o.h)) + 2));
+    o.deta = 2.0 * kPi / (o.n * o.h);
+    {
+        const int nk = 2 * static_cast<int>(std::ceil(o.kcut / o.deta)) + 2;
+        o.nk = nk + (nk & 1);
+    }
+    if (o.nk > o.n) {
+        err = "uniform grid: the frequency window exceeds the FFT length";
+        return SBD_ENOTSUP;
+    }
+    o.cx = cx;
+    o.cy = cy;
+    o.dec.assign(o.m, 1.0);           // no node window: nothing to precorrect on the spreading grid
+    o.beta_k = 0.0;
+    o.sigma = 0.0;
+    o.circle_factor.assign(fit.n_circles, 1.0);
+    o.psi.clear();
+    o.kmax = 0.0;
+    o.psi_max = 1.0;
+    if (swin == 1) {
+        o.kmax = o.kcut * o.h * (1.0 + 1e-12);
+        int rc = es_deconv_series(Ps, o.beta_s, o.kmax, o.psi, o.psi_max, err);
+        if (rc) return rc;
+    }
+    // psi_w at the FFT positions: 1 - (integral of the ES bump over [0, (|t| - wa) / wtau]) / (its total)
+    std::vector<double> gx, gw;
+    gauss_legendre(64, gx, gw);
+    auto bump = [&](double u) { const double v = 2.0 * u - 1.0; return std::exp(o.wbeta * (std::sqrt(std::max(0.0, 1.0 - v * v)) - 1.0)); };
+    // the integral over [0, 1] in 8 panels (the bump is peaked)
+    double total = 0.0;
+    for (int k = 0; k < 8; ++k) {
+        double acc = 0.0;
+        for (size_t j = 0; j < gx.size(); ++j) acc += gw[j] * bump((k + 0.5 * (gx[j] + 1.0)) / 8.0);
+        total += acc / 16.0;
+    }
+    o.wtab.resize(o.n);
+    for (int i = 0; i < o.n; ++i) {
+        const double t = std::fabs((i - 0.5 * o.n) * o.h);
+        if (t <= o.wa) o.wtab[i] = 1.0;
+        else if (t >= o.wa + o.wtau) o.wtab[i] = 0.0;
+        else {
+            const double u = (t - o.wa) / o.wtau;
+            // piecewise: panels of 1/8 below u, Gauss-Legendre on each
+            double acc = 0.0;
+            const int full = static_cast<int>(u * 8.0);
+            for (int k = 0; k < full; ++k) {
+                double pa = 0.0;
+                for (size_t j = 0; j < gx.size(); ++j) pa += gw[j] * bump((k + 0.5 * (gx[j] + 1.0)) / 8.0);
+                acc += pa / 16.0;
+            }
+            const double u0 = full / 8.0, du = u - u0;
+            if (du > 0.0) {
+                double pa = 0.0;
+                for (size_t j = 0; j < gx.size(); ++j) pa += gw[j] * bump(u0 + 0.5 * du * (gx[j] + 1.0));
+                acc += 0.5 * du * pa;
+            }
+            o.wtab[i] = std::max(0.0, std::min(1.0, 1.0 - acc / total));
+        }
+    }
+    return SBD_OK;
+}
+
+int near_tables(const SbdFit& fit, NearTables& o, std::string& err, bool radial) {
     const double dmin = fit.delta_min;
     o.tmax = dmin * dmin;
     double scale = std::abs(fit.w0);
@@ -802,7 +913,7 @@ int near_tables(const SbdFit& fit, NearTables& o, std::string& err) {
         std::vector<double> J;
         bessel_jn_range(x, fit.M[c], fit.M[c], J);
         const double mag = 2.0 * std::fabs(J[0]) * std::abs(fit.weight[c]) * fit.M[c];
-        if (mag > 1e-18 * scale) {
+        if (!radial && mag > 1e-18 * scale) {
             o.small.push_back(c);
             if (fit.kind == 1 && c == fit.P) j0_circle_small = true;
         }

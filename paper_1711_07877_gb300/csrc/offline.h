@@ -89,7 +89,23 @@ struct NufftParams {
     std::vector<double> psi;
     double kmax = 0.0;
     double psi_max = 1.0;      // psi(kmax), the largest value of psi on [0, kmax]
+    // Uniform-grid variant (uniform_params): the series G_fit, windowed by psi_w(y_x) psi_w(y_y)
+    // and periodised on the FFT period L = n h, enters as Fourier coefficients on the frequency
+    // grid; psi_w = 1 on |t| <= wa (the points' differences), 0 beyond wa + wtau, an ES bump's
+    // integral in between.
+    bool uniform = false;
+    double wa = 0.0, wtau = 0.0, wbeta = 0.0;
+    double kcut = 0.0;         // largest frequency kept, S + the window's spectral reach
+    std::vector<double> wtab;  // psi_w at the n FFT positions, t = (i - n / 2) h
 };
+
+// Parameters of the uniform-grid variant (the fast summation the paper cites: the node step
+// replaced by a multiplication on the frequency grid): same spreading windows and rules as
+// nufft_params; the spreading grid resolves K = S + B, B the spectral reach of the window
+// psi_w; the FFT length n covers the period L >= 2 (2 half + wtau) so that the periodised
+// window never overlaps itself on the points' differences; nk covers |k| <= K.
+int uniform_params(const SbdFit& fit, double half_extent, double cx, double cy, double tol, bool fp32, int swin,
+                   int sigma_mode, long n_points, NufftParams& out, std::string& err);
 
 // sigma_mode: 0 automatic, 1 spreading oversampling 1.5, 2 oversampling 2 (the Gaussian
 // spreading window always uses 2); n_points feeds the automatic choice.
@@ -110,6 +126,8 @@ struct NearTables {
     cplx self_value = 0.0;           // D_kk = -G_approx(0)
 };
 
-int near_tables(const SbdFit& fit, NearTables& out, std::string& err);
+// radial: every circle enters as its exact J0 term (no plane-wave sums): D = G - G_fit for the
+// uniform-grid variant, whose far part uses the series without the circle quadrature.
+int near_tables(const SbdFit& fit, NearTables& out, std::string& err, bool radial = false);
 
 }  // namespace sbd

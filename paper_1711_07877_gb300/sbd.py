@@ -63,7 +63,8 @@ class sbd_plan_stats(ctypes.Structure):
                 ("w0_re", ctypes.c_double), ("w0_im", ctypes.c_double), ("device_bytes", ctypes.c_int64),
                 ("plan_seconds", ctypes.c_double), ("n_records", ctypes.c_int64), ("node_acc", ctypes.c_int32),
                 ("node_sched", ctypes.c_int32), ("fft_split", ctypes.c_int32), ("node_binned", ctypes.c_int32),
-                ("n_targets", ctypes.c_int64), ("separate_targets", ctypes.c_int32), ("reserved2", ctypes.c_int32)]
+                ("n_targets", ctypes.c_int64), ("separate_targets", ctypes.c_int32), ("uniform_grid", ctypes.c_int32),
+                ("point_chunk", ctypes.c_int32), ("tuned", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -83,6 +84,12 @@ _SIGS = {
     "sbd_fit_cache_stats": ([_P, _P, _P], ctypes.c_int),
     "sbd_tune": ([_P, _I32, _P, _P], ctypes.c_int),
     "sbd_set_tuning": ([_P, _I32, _I32, _I32], ctypes.c_int),
+    "sbd_tune_points": ([_P, _I32, _P, _P], ctypes.c_int),
+    "sbd_set_point_chunk": ([_P, _I32], ctypes.c_int),
+    "sbd_tune_cache_stats": ([_P, _P, _P], ctypes.c_int),
+    "sbd_tune_cache_save": ([ctypes.c_char_p], ctypes.c_int),
+    "sbd_tune_cache_load": ([ctypes.c_char_p], ctypes.c_int),
+    "sbd_tune_cache_clear": ([], ctypes.c_int),
     "sbd_plan_balanced": ([_P, _I64, sbd_kernel, _D, _P, _I32, _I32, _I32, ctypes.POINTER(sbd_options), _P,
                            ctypes.POINTER(_P), _P, ctypes.POINTER(_I32)], ctypes.c_int),
     "sbd_fit_cache_clear": ([], ctypes.c_int),
@@ -168,6 +175,7 @@ SBD_FLAG_GAUSSIAN_SPREAD = 2
 SBD_FLAG_SPREAD_SIGMA_2 = 4
 SBD_FLAG_SPREAD_SIGMA_15 = 8
 SBD_FLAG_NEAR_FP32 = 16
+SBD_FLAG_UNIFORM_GRID = 32
 
 
 def make_options(form: int = SBD_FORM_FP64, fixed_P: int = 0, nufft_tol: float = 0.0, max_nrhs: int = 1,
@@ -380,6 +388,36 @@ def sbd_plan_balanced(points, n: int, kernel_kind: int, kappa: float, eps: float
                                ctypes.byref(out), ms.ctypes.data, ctypes.byref(chosen))
     _check(rc, "sbd_plan_balanced")
     return out.value, ms.tolist(), chosen.value
+
+
+def sbd_tune_points(plan: int, reps: int = 3, stream=None) -> list:
+    """Times spreading + interpolation per point chunk (128 .. 2048), keeps the fastest."""
+    import numpy as np
+    ms = np.zeros(5)
+    _check(lib.sbd_tune_points(plan, reps, ms.ctypes.data, _stream(stream)), "sbd_tune_points")
+    return ms.tolist()
+
+
+def sbd_set_point_chunk(plan: int, chunk: int) -> None:
+    _check(lib.sbd_set_point_chunk(plan, chunk), "sbd_set_point_chunk")
+
+
+def sbd_tune_cache_stats() -> dict:
+    h, m, e = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    _check(lib.sbd_tune_cache_stats(ctypes.byref(h), ctypes.byref(m), ctypes.byref(e)), "sbd_tune_cache_stats")
+    return {"hits": h.value, "misses": m.value, "entries": e.value}
+
+
+def sbd_tune_cache_save(path: str) -> None:
+    _check(lib.sbd_tune_cache_save(path.encode()), "sbd_tune_cache_save")
+
+
+def sbd_tune_cache_load(path: str) -> None:
+    _check(lib.sbd_tune_cache_load(path.encode()), "sbd_tune_cache_load")
+
+
+def sbd_tune_cache_clear() -> None:
+    _check(lib.sbd_tune_cache_clear(), "sbd_tune_cache_clear")
 
 
 def sbd_set_tuning(plan: int, acc: int, sched: int, fft_split: int = 0) -> None:

@@ -89,6 +89,9 @@ class Request:
     plan_seconds: float = 0.0
     device_bytes: int = 0
     error: str | None = None
+    attempts: int = 0             # re-admissions after running out of device memory
+    deadline_s: float | None = None   # give up if still queued this long after arrival
+    late: bool = False            # finished after its deadline
 
 
 @dataclass
@@ -212,30 +215,82 @@ class Admission:
         return v["plan"] if v else None
 
 
-class Server:
-    """slots worker threads; admission by a device-memory budget (bytes)."""
+class CudaBackend:
+    """The device side of a request, through the library's entry points (the server's host
+    logic talks only to this, so that it can be exercised on the host with a stand-in)."""
 
-    def __init__(self, slots: int = 4, hbm_budget: int | None = None, form: int = S.SBD_FORM_FP32,
-                 tol: float = 1e-6, restart: int = 30, max_iter: int = 300, fit_grid: bool = True):
+    def __init__(self):
         import torch
         self.torch = torch
+
+    def stream(self):
+        return self.torch.cuda.Stream()
+
+    def free_bytes(self) -> int:
+        return int(self.torch.cuda.mem_get_info()[0])
+
+    def plan(self, req, stream, delta_min: float, delta_max: float, form: int, host_threads: int):
+        torch = self.torch
+        with torch.cuda.stream(stream):
+            zt = torch.from_numpy(req.z).to("cuda", non_blocking=True)
+        opt = S.make_options(form=form, delta_max=delta_max, host_threads=host_threads)
+        plan = S.sbd_plan(zt, len(req.z), req.kind, req.kappa, delta_min, req.eps, opt, stream.cuda_stream)
+        return plan, S.sbd_plan_info(plan)
+
+    def solve(self, plan, req, stream, tol: float, restart: int, max_iter: int):
+        torch = self.torch
+        with torch.cuda.stream(stream):
+            bt = torch.from_numpy(req.b).to("cuda", non_blocking=True)
+            xt = torch.zeros_like(bt)
+        it, res = S.sbd_gmres(plan, bt, xt, req.shift, req.scale, tol, restart, max_iter, stream.cuda_stream)
+        stream.synchronize()
+        return xt.cpu().numpy(), it, res
+
+    def synchronize(self, stream) -> None:
+        stream.synchronize()
+
+    def destroy(self, plan, stream) -> None:
+        S.sbd_destroy_async(plan, stream.cuda_stream)   # no device-wide wait
+
+    def destroy_now(self, plan) -> None:
+        S.sbd_destroy(plan)
+
+
+class Server:
+    """slots worker threads; admission by a device-memory budget (bytes).
+
+    Failure handling on the host: a request whose plan or solve runs out of device memory
+    (SBD_ENOMEM) goes back to the head of the queue, at most `retries` times, after the
+    admission's per-point estimate grows by half (so that it next waits for more room); a
+    request with a deadline (Request.deadline_s, seconds after arrival) that is still queued
+    when it passes is dropped by a watchdog thread with an error, and one that finishes after
+    it is marked late (its result is kept)."""
+
+    def __init__(self, slots: int = 4, hbm_budget: int | None = None, form: int = S.SBD_FORM_FP32,
+                 tol: float = 1e-6, restart: int = 30, max_iter: int = 300, fit_grid: bool = True,
+                 backend=None, retries: int = 3, watchdog_s: float = 0.01):
+        self.backend = backend or CudaBackend()
         self.slots = slots
         self.form = form
         self.tol, self.restart, self.max_iter = tol, restart, max_iter
         self.fit_grid = fit_grid
+        self.retries = retries
         # the host part of concurrent plan builds shares the cores
         self.host_threads = max(1, (os.cpu_count() or slots) // slots)
         if hbm_budget is None:
-            free, _ = torch.cuda.mem_get_info()
-            hbm_budget = int(free * 0.8)
+            hbm_budget = int(self.backend.free_bytes() * 0.8)
         self.adm = Admission(hbm_budget)
         self.cv = threading.Condition()
         self.stats = ServerStats()
         self.t0 = time.perf_counter()
         self.closed = False
+        self.requeued = 0
+        self.dropped = 0
         self.workers = [threading.Thread(target=self._worker, daemon=True) for _ in range(slots)]
         for w in self.workers:
             w.start()
+        self.watchdog = threading.Thread(target=self._watch, args=(watchdog_s,), daemon=True)
+        self.watchdog.start()
 
     def now(self) -> float:
         return time.perf_counter() - self.t0
@@ -246,9 +301,27 @@ class Server:
             self.adm.push(req)
             self.cv.notify_all()
 
+    def _watch(self, period: float) -> None:
+        """Drops queued requests whose deadline has passed."""
+        while True:
+            with self.cv:
+                if self.closed:
+                    return
+                now = self.now()
+                late = [r for r in self.adm.pending
+                        if getattr(r, "deadline_s", None) is not None and now - r.arrival > r.deadline_s]
+                for r in late:
+                    self.adm.pending.remove(r)
+                    r.error = f"deadline of {r.deadline_s:.3f} s passed while queued"
+                    r.done = now
+                    self.dropped += 1
+                if late:
+                    self.cv.notify_all()
+            time.sleep(period)
+
     def _worker(self):
-        torch = self.torch
-        stream = torch.cuda.Stream()
+        be = self.backend
+        stream = be.stream()
         while True:
             with self.cv:
                 got = None
@@ -261,41 +334,42 @@ class Server:
                     return
             req, est, evict = got
             for _, old_plan in evict:            # idle resident plans that made room
-                S.sbd_destroy_async(old_plan, stream.cuda_stream)
+                be.destroy(old_plan, stream)
             req.start = self.now()
             key = req.geometry
             with self.cv:
                 plan = self.adm.plan_of(key) if key is not None else None
             reused = plan is not None
+            requeue = False
             try:
-                with torch.cuda.stream(stream):
-                    bt = torch.from_numpy(req.b).to("cuda", non_blocking=True)
-                    xt = torch.zeros_like(bt)
                 if not reused:
-                    with torch.cuda.stream(stream):
-                        zt = torch.from_numpy(req.z).to("cuda", non_blocking=True)
                     dmin, dmax = req.delta_min, 0.0
                     if self.fit_grid:
                         dmin, dmax = fit_grid_scales(req.kind, req.kappa, req.delta_min,
                                                      enclosing_diameter(req.z))
-                    opt = S.make_options(form=self.form, delta_max=dmax, host_threads=self.host_threads)
-                    plan = S.sbd_plan(zt, len(req.z), req.kind, req.kappa, dmin, req.eps, opt, stream.cuda_stream)
-                    info = S.sbd_plan_info(plan)
+                    plan, info = be.plan(req, stream, dmin, dmax, self.form, self.host_threads)
                     req.plan_seconds = info["plan_seconds"]
                     req.device_bytes = info["device_bytes"]
-                it, res = S.sbd_gmres(plan, bt, xt, req.shift, req.scale, self.tol, self.restart, self.max_iter,
-                                      stream.cuda_stream)
-                stream.synchronize()
-                req.x = xt.cpu().numpy()
-                req.iterations, req.residual = it, res
-            except Exception as e:  # the request fails, the server keeps serving
-                req.error = str(e)
+                req.x, req.iterations, req.residual = be.solve(plan, req, stream, self.tol, self.restart,
+                                                               self.max_iter)
+            except Exception as e:  # the request fails (or waits again), the server keeps serving
+                if getattr(e, "code", None) == S.SBD_ENOMEM and req.attempts < self.retries:
+                    requeue = True
+                    req.attempts += 1
+                else:
+                    req.error = str(e)
             finally:
-                keep = key is not None and plan is not None and req.error is None
+                failed = req.error is not None or requeue
+                keep = key is not None and plan is not None and not failed
                 if plan is not None and not keep and not reused:
-                    stream.synchronize()
-                    S.sbd_destroy_async(plan, stream.cuda_stream)   # no device-wide wait
-                req.done = self.now()
+                    be.synchronize(stream)
+                    be.destroy(plan, stream)
+                    if not reused:
+                        plan = None
+                if not requeue:
+                    req.done = self.now()
+                    if getattr(req, "deadline_s", None) is not None and req.done - req.arrival > req.deadline_s:
+                        req.late = True
                 with self.cv:
                     if keep:
                         self.adm.release(est, len(req.z), req.device_bytes, key=key, plan=plan)
@@ -304,7 +378,12 @@ class Server:
                         self.adm.release(est, key=key, plan=plan)
                     else:
                         self.adm.release(est, len(req.z), req.device_bytes, key=key, keep=False)
-                    if req.error is None:
+                    if requeue:
+                        # out of memory: the footprint was underestimated; wait for more room
+                        self.adm.bytes_per_point *= 1.5
+                        self.adm.pending.insert(0, req)
+                        self.requeued += 1
+                    elif req.error is None:
                         self.stats.latencies.append(req.done - req.arrival)
                         self.stats.points_matvecs += len(req.z) * (req.iterations + 2)
                     self.cv.notify_all()
@@ -316,9 +395,10 @@ class Server:
             self.cv.notify_all()
         for w in self.workers:
             w.join()
+        self.watchdog.join()
         for v in list(self.adm.resident.values()):
             if v["plan"]:
-                S.sbd_destroy(v["plan"])
+                self.backend.destroy_now(v["plan"])
         self.adm.resident.clear()
 
     def drain(self, requests: list[Request], timeout_s: float | None = None) -> bool:
@@ -359,4 +439,7 @@ def run_poisson(requests: list[Request], mean_gap_s: float, seed: int = 0, timeo
     finished = srv.drain(requests, timeout_s)
     summ = srv.stats.summary()
     summ["incomplete"] = 0 if finished else sum(r.error == "not finished within the drain timeout" for r in requests)
+    summ["requeued"] = srv.requeued
+    summ["deadline_dropped"] = srv.dropped
+    summ["late"] = sum(1 for r in requests if r.late)
     return srv, summ

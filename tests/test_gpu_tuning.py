@@ -37,6 +37,7 @@ def test_variants_agree_and_tune_picks_one(S, kind):
         dmin = float(np.sqrt(20.0 / n))
     zt = torch.from_numpy(z).cuda()
     ft = torch.from_numpy(f).cuda()
+    S.sbd_tune_cache_clear()                                  # time every variant (no cached choice)
     p = S.sbd_plan(zt, n, S.SBD_HELMHOLTZ if kind == "helmholtz" else S.SBD_LAPLACE, kappa, dmin, 1e-6,
                    S.make_options(form=S.SBD_FORM_FP32))
     try:
@@ -70,6 +71,7 @@ def test_variants_agree_and_tune_picks_one(S, kind):
 
 def test_fp64_rejects_cas_variant(S):
     wl = W.laplace_disk(500, 54, 1e-6)
+    S.sbd_tune_cache_clear()
     zt = torch.from_numpy(wl.z).cuda()
     p = S.sbd_plan(zt, 500, S.SBD_LAPLACE, 0.0, wl.delta_min, 1e-6, S.make_options(form=S.SBD_FORM_FP64))
     try:
@@ -82,3 +84,43 @@ def test_fp64_rejects_cas_variant(S):
         assert ms[0] > 0 and ms[1] > 0 and all(t == -1 for t in ms[2:8]) and ms[8] > 0 and ms[9] > 0
     finally:
         S.sbd_destroy(p)
+
+
+def test_point_chunk_search_and_tuning_cache(S):
+    """sbd_tune also picks the point chunk; a second plan of the same class takes the cached
+    choice without timing (tuned = 2); every chunk gives the same matvec to FP32 rounding."""
+    S.sbd_tune_cache_clear()
+    wl = W.laplace_curves(120_000, 81, 1e-6)
+    zt = torch.from_numpy(wl.z).cuda()
+    ft = torch.from_numpy(wl.f).cuda()
+    opt = S.make_options(form=S.SBD_FORM_FP32)
+    p1 = S.sbd_plan(zt, len(wl.z), S.SBD_LAPLACE, 0.0, wl.delta_min, wl.eps, opt)
+    p2 = S.sbd_plan(zt, len(wl.z), S.SBD_LAPLACE, 0.0, wl.delta_min, wl.eps, opt)
+    try:
+        ms = S.sbd_tune_points(p1, 2)
+        assert len(ms) == 5 and all(t > 0 for t in ms)
+        outs = []
+        for chunk in (128, 512, 2048):
+            S.sbd_set_point_chunk(p1, chunk)
+            assert S.sbd_plan_info(p1)["point_chunk"] == chunk
+            q = torch.empty_like(ft)
+            S.sbd_matvec(p1, ft, q)
+            torch.cuda.synchronize()
+            outs.append(q.cpu().numpy())
+        for o in outs[1:]:
+            assert np.linalg.norm(o - outs[0]) / np.linalg.norm(outs[0]) < 2e-6
+        S.sbd_tune(p1, 2)
+        i1 = S.sbd_plan_info(p1)
+        assert i1["tuned"] == 1 and S.sbd_tune_cache_stats()["misses"] == 1
+        S.sbd_tune(p2, 2)
+        i2 = S.sbd_plan_info(p2)
+        assert i2["tuned"] == 2 and S.sbd_tune_cache_stats()["hits"] == 1
+        for k in ("node_acc", "node_sched", "fft_split", "point_chunk"):
+            assert i1[k] == i2[k], k
+        with pytest.raises(S.SbdError) as e:
+            S.sbd_set_point_chunk(p1, 64)
+        assert e.value.code == S.SBD_EINVAL
+    finally:
+        S.sbd_destroy(p1)
+        S.sbd_destroy(p2)
+        S.sbd_tune_cache_clear()

@@ -143,3 +143,29 @@ def test_lowrank_fit_agrees_with_cholesky(S, kind, kappa, dmin, dmax):
     rel = np.linalg.norm(f["alpha"][:P] - g["alpha"][:P]) / np.linalg.norm(g["alpha"][:P])
     assert rel < 1e-6, rel
     assert abs(f["fit_err"] - g["fit_err"]) <= 1e-3 * g["fit_err"] + 1e-15
+
+
+def test_tune_cache_file_round_trip(S, tmp_path):
+    """The tuning cache (no GPU needed): a JSON object of "class": [acc, sched, fft_split, chunk]
+    entries loads, merges, saves and reloads; malformed files are rejected."""
+    import json
+    S.sbd_tune_cache_clear()
+    src = tmp_path / "tune.json"
+    src.write_text(json.dumps({"f1_k0_s0_u0_b1_d0_m8192_nk10936_n16384_N40": [3, 1, 0, 512],
+                               "f0_k1_s0_u0_b0_d0_m4096_nk5000_n8192_N30": [0, 0, 2, 1024]}))
+    S.sbd_tune_cache_load(str(src))
+    assert S.sbd_tune_cache_stats()["entries"] == 2
+    out = tmp_path / "out.json"
+    S.sbd_tune_cache_save(str(out))
+    assert json.loads(out.read_text()) == json.loads(src.read_text())
+    S.sbd_tune_cache_clear()
+    S.sbd_tune_cache_load(str(out))
+    assert S.sbd_tune_cache_stats() == {"hits": 0, "misses": 0, "entries": 2}
+    for bad in ('{"x": [5, 0, 0, 512]}', '{"x": [0, 0, 1, 512]}', '{"x": [0, 0, 0, 64]}', "[]"):
+        (tmp_path / "bad.json").write_text(bad)
+        with pytest.raises(S.SbdError) as e:
+            S.sbd_tune_cache_load(str(tmp_path / "bad.json"))
+        assert e.value.code == S.SBD_EINVAL
+    with pytest.raises(S.SbdError):
+        S.sbd_tune_cache_load(str(tmp_path / "missing.json"))
+    S.sbd_tune_cache_clear()

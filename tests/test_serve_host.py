@@ -148,3 +148,93 @@ def test_second_request_waits_while_its_plan_is_built():
     rb, eb, _ = a.admit()
     a.release(eb, key="B", keep=False)
     assert "B" not in a.building and a.plan_of("B") is None
+
+
+# --- failure paths of the server, on the host: a stand-in backend raises the library's errors ----
+
+import threading
+import time
+
+from paper_1711_07877_gb300 import sbd as S
+from paper_1711_07877_gb300.serve import Request, Server
+
+
+class FakeBackend:
+    """Host stand-in for the device: plans fail with SBD_ENOMEM a set number of times, solves
+    take a set time; records what happened."""
+
+    def __init__(self, enomem=0, solve_s=0.0):
+        self.enomem = enomem
+        self.solve_s = solve_s
+        self.plans = 0
+        self.destroyed = 0
+        self.lock = threading.Lock()
+
+    def stream(self):
+        return object()
+
+    def free_bytes(self):
+        return 10 ** 12
+
+    def plan(self, req, stream, delta_min, delta_max, form, host_threads):
+        with self.lock:
+            self.plans += 1
+            if self.enomem > 0:
+                self.enomem -= 1
+                raise S.SbdError(S.SBD_ENOMEM, "sbd_plan", "out of memory: cudaMallocAsync")
+        return object(), {"plan_seconds": 1e-3, "device_bytes": 1000 * len(req.z)}
+
+    def solve(self, plan, req, stream, tol, restart, max_iter):
+        time.sleep(self.solve_s)
+        return np.zeros_like(req.b), 3, 1e-7
+
+    def synchronize(self, stream):
+        pass
+
+    def destroy(self, plan, stream):
+        with self.lock:
+            self.destroyed += 1
+
+    def destroy_now(self, plan):
+        self.destroy(plan, None)
+
+
+def mk(i, n=100, deadline=None):
+    return Request(rid=i, z=np.zeros((n, 2)), b=np.ones(n), kind=S.SBD_LAPLACE, kappa=0.0, delta_min=0.1,
+                   eps=1e-6, deadline_s=deadline)
+
+
+def test_out_of_memory_requeues_then_succeeds():
+    be = FakeBackend(enomem=2)
+    srv = Server(slots=1, hbm_budget=10 ** 9, backend=be, fit_grid=False)
+    r = mk(0)
+    srv.submit(r)
+    assert srv.drain([r], timeout_s=10)
+    assert r.error is None and r.attempts == 2 and srv.requeued == 2
+    assert be.plans == 3
+    assert srv.adm.bytes_per_point >= 8000.0 * 1.5 ** 2   # the estimate grew by half per retry
+
+
+def test_out_of_memory_fails_after_the_retries():
+    be = FakeBackend(enomem=10)
+    srv = Server(slots=1, hbm_budget=10 ** 9, backend=be, fit_grid=False, retries=3)
+    r = mk(0)
+    srv.submit(r)
+    assert srv.drain([r], timeout_s=10)
+    assert r.error is not None and "out of memory" in r.error and r.attempts == 3
+    assert be.plans == 4 and srv.adm.running == 0 and srv.adm.in_use == 0
+
+
+def test_deadline_drops_queued_requests_and_marks_late_ones():
+    be = FakeBackend(solve_s=0.3)
+    srv = Server(slots=1, hbm_budget=10 ** 9, backend=be, fit_grid=False)
+    slow = mk(0, deadline=0.1)          # admitted at once, finishes after its deadline: late
+    queued = mk(1, deadline=0.1)        # waits behind it past its deadline: dropped
+    free = mk(2)                        # no deadline: served after the slow one
+    for r in (slow, queued, free):
+        srv.submit(r)
+    assert srv.drain([slow, queued, free], timeout_s=10)
+    assert slow.error is None and slow.late
+    assert queued.error is not None and "deadline" in queued.error and srv.dropped == 1
+    assert free.error is None and not free.late
+    assert be.destroyed == 2            # the two solved requests released their plans
