@@ -12,7 +12,8 @@ balanced_delta_min (delta_min by measurement), uniform_grid (the same workload w
 node step replaced by a multiplication on the frequency grid), near_fp32 (the same plan with D f in
 float32), fp64_form (the same workload in the FP64 form), helmholtz (kappa delta_max
 = 500, FP32 and FP64 forms), table2 (separate targets and sources, the Table 2 setting),
-served (a short serving run: p50/p99 latency with a queue / plan / solve breakdown), and
+served and served_batched (a short serving run, the second with the solves' matvecs merged into
+batched launches: p50/p99 latency with a queue / plan / solve breakdown), and
 cpu_baseline (the oracle's direct sum over all host cores, plus the oracle SBD timed on
 the N = 2000 disk).
 
@@ -56,6 +57,8 @@ def parse():
     ap.add_argument("--nrhs", type=int, default=0, help="right-hand sides (0: the workload's own)")
     ap.add_argument("--requests", type=int, default=256, help="serve: number of solve requests")
     ap.add_argument("--slots", type=int, default=8, help="serve: concurrent requests")
+    ap.add_argument("--batch-matvecs", action="store_true",
+                    help="serve: merge the solves' matvecs into batched launches (iteration-level batching)")
     ap.add_argument("--eps", type=float, default=1e-6)
     ap.add_argument("--alpha", type=float, default=0.0,
                     help="curve workloads: delta_min by Theorem 1 with this alpha in [0, 1/6]")
@@ -628,7 +631,10 @@ def main():
     if extra and args.workload == "laplace_curves":
         out["helmholtz"] = helmholtz_lines(S, torch, stream, args)
         out["table2"] = table2_line(S, torch, stream, args)
-        out["served"] = run_serve(args, rank, world, local, requests=args.served_requests, short=True)
+        out["served"] = run_serve(args, rank, world, local, requests=args.served_requests, short=True,
+                                  batch_matvecs=False)
+        out["served_batched"] = run_serve(args, rank, world, local, requests=args.served_requests, short=True,
+                                          batch_matvecs=True)
     if rank == 0:
         print(json.dumps(out))
     if world > 1:
@@ -862,7 +868,7 @@ def run_batch(args, rank, world, local):
         print(json.dumps(out))
 
 
-def run_serve(args, rank, world, local, requests=None, short=False):
+def run_serve(args, rank, world, local, requests=None, short=False, batch_matvecs=None):
     """Continuous-batching solve server over a Poisson stream of GMRES requests; returns the line
     (or, with short, the key the default line carries) with p50/p99 latency and a per-request
     breakdown into queueing (arrival to admission), planning and solving."""
@@ -894,8 +900,9 @@ def run_serve(args, rank, world, local, requests=None, short=False):
     clocks = ClockSampler(uuid)
     clocks.start()
     torch.cuda.synchronize()
+    batched = args.batch_matvecs if batch_matvecs is None else batch_matvecs
     srv, summ = serve.run_poisson(reqs, mean_gap_s=0.002, seed=9 + rank, slots=args.slots, form=form, tol=1e-6,
-                                  max_iter=600, timeout_s=600.0)
+                                  max_iter=600, timeout_s=600.0, batch_matvecs=batched)
     torch.cuda.synchronize()
     clk = clocks.stop()
     ok = [r for r in reqs if r.error is None]
@@ -922,6 +929,8 @@ def run_serve(args, rank, world, local, requests=None, short=False):
               "points_mean": float(np.mean([len(r.z) for r in ok])) if ok else None,
               "max_residual": float(max(r.residual for r in ok)) if ok else None,
               "requeued_after_enomem": summ.get("requeued"), "deadline_dropped": summ.get("deadline_dropped"),
+              "batch_matvecs": batched, "matvec_batches": summ.get("matvec_batches"),
+              "matvecs_batched": summ.get("matvecs_batched"),
               "fit_cache": cache, "breakdown": breakdown}
     latency = {"p50_ms": summ.get("p50_ms"), "p99_ms": summ.get("p99_ms"), "mean_ms": summ.get("mean_ms")}
     if short:

@@ -518,6 +518,30 @@ int sbd_gmres(sbd_plan_t plan, const void* b, void* x, const sbd_gmres_options* 
               double* rel_residual, void* cuda_stream);
 
 /* ---------------------------------------------------------------------------------
+ * GMRES as a resumable session (no counterpart in the paper): the iteration of sbd_gmres,
+ * stopped wherever it needs a matvec of its plan, so that a caller can compute the matvecs
+ * of many solves together (sbd_matvec_batched) while each solve keeps its own Krylov basis.
+ *   sbd_gmres_begin    plan, b, x, opt as for sbd_gmres (x: initial guess); allocates the
+ *                      workspace ((restart + 2) N-vectors) and computes ||b|| on cuda_stream,
+ *                      which the session's own kernels use from then on.  *out: the session.
+ *   sbd_gmres_next     1 when the session needs out = A in: the plan's plain matvec (sbd_matvec
+ *                      semantics, one right-hand side; the shift and scale are the session's),
+ *                      with *in and *out device vectors of the session; 0 when it has finished.
+ *   sbd_gmres_advance  after the caller wrote out = A in (ordered before the session's stream,
+ *                      e.g. with an event): the work up to the next matvec (Gram-Schmidt,
+ *                      rotations, updates of x).  Blocks the calling thread (reads projections).
+ *   sbd_gmres_end      iterations and the final relative residual (as sbd_gmres; may be NULL),
+ *                      frees the session (NULL-safe).  x holds the solution.
+ * Errors: as sbd_gmres.  One session is driven by one thread at a time.
+ * ------------------------------------------------------------------------------- */
+typedef struct sbd_gmres_session_s* sbd_gmres_session_t;
+int sbd_gmres_begin(sbd_plan_t plan, const void* b, void* x, const sbd_gmres_options* opt, void* cuda_stream,
+                    sbd_gmres_session_t* out);
+int sbd_gmres_next(sbd_gmres_session_t session, const void** in, void** out);
+int sbd_gmres_advance(sbd_gmres_session_t session);
+int sbd_gmres_end(sbd_gmres_session_t session, int32_t* iterations, double* rel_residual);
+
+/* ---------------------------------------------------------------------------------
  * Step timing of the on-line part.  sbd_profile(plan, 1) waits for the device,
  * clears the counters and starts recording a pair of CUDA events on the caller's
  * stream around every step of sbd_matvec / sbd_far / sbd_close (0 stops).

@@ -1,4 +1,6 @@
-// Restarted GMRES on (shift I + scale A) x = b with A the SBD matvec of a plan.
+// Restarted GMRES on (shift I + scale A) x = b with A the SBD matvec of a plan, as a
+// resumable session whose matvecs the caller computes (sbd_gmres runs one session alone with
+// the plan's graph matvec; a server merges many sessions' matvecs into batched calls).
 //
 // The paper's motivation (Introduction): boundary-element systems are solved by
 // iterative methods whose cost is the discrete convolution.  Arnoldi with two-pass
@@ -169,16 +171,6 @@ struct Solver {
         *out = std::sqrt(std::max(v.x, 0.0));
         return SBD_OK;
     }
-    // y = (shift I + scale A) x; the matvec replays a CUDA graph (launch cost matters for
-    // the small systems a solver sees)
-    int apply(const T* x, T* y) {
-        int rc = sbd_matvec_graph(plan, x, y, 1, s);
-        if (rc) return rc;
-        axpby_kernel<CPLX><<<nblk, 256, 0, s>>>(n, make_double2(shift.real(), shift.imag()), x,
-                                                make_double2(scale.real(), scale.imag()), y);
-        SBD_LAUNCH_CHECK();
-        return SBD_OK;
-    }
     int scal(T* x, zc a) {
         scale_kernel<CPLX><<<nblk, 256, 0, s>>>(n, make_double2(a.real(), a.imag()), x);
         SBD_LAUNCH_CHECK();
@@ -186,139 +178,200 @@ struct Solver {
     }
 };
 
+// GMRES as a resumable session: the solver stops wherever it needs y = A v (the plan's plain
+// matvec; the shift and scale are applied here), so that a caller can compute many sessions'
+// matvecs together.  States: RESIDUAL (v = x, y = V0: r = b - (shift I + scale A) x),
+// ARNOLDI (v = V_j, y = V_{j+1}), CHECK (v = x, y = tmp: the true residual before stopping).
+struct SessionBase {
+    virtual ~SessionBase() = default;
+    virtual int next(const void** in, void** out) = 0;
+    virtual int advance() = 0;
+    virtual void finish(int32_t* iters, double* rel) = 0;
+};
+
 template <bool CPLX>
-int gmres_impl(sbd_plan_t plan, long n, const void* b, void* x, const sbd_gmres_options& o, int32_t* iters,
-               double* rel_res, cudaStream_t s) {
+struct Session : SessionBase {
     using T = typename V<CPLX>::t;
-    const int m = std::max(1, o.restart);
+    enum State { RESIDUAL, ARNOLDI, CHECK, DONE };
     Solver<CPLX> S;
-    S.plan = plan;
-    S.n = n;
-    S.s = s;
-    S.shift = zc(o.shift_re, o.shift_im);
-    S.scale = zc(o.scale_re, o.scale_im);
-    S.nblk = static_cast<int>(std::min<long>(1024, (n + 255) / 256));
-    auto release = [&]() {
-        if (S.Vb) cudaFreeAsync(S.Vb, s);
-        if (S.tmp) cudaFreeAsync(S.tmp, s);
-        if (S.partial) cudaFreeAsync(S.partial, s);
-        if (S.hd) cudaFreeAsync(S.hd, s);
-        cudaStreamSynchronize(s);
-    };
-    if (cudaMallocAsync(&S.Vb, sizeof(T) * n * (m + 1), s) != cudaSuccess ||
-        cudaMallocAsync(&S.tmp, sizeof(T) * n, s) != cudaSuccess ||
-        cudaMallocAsync(&S.partial, sizeof(double2) * S.nblk * (m + 1), s) != cudaSuccess ||
-        cudaMallocAsync(&S.hd, sizeof(double2) * (m + 1), s) != cudaSuccess) {
-        cudaGetLastError();
-        release();
-        set_error("sbd_gmres: workspace allocation failed");
-        return SBD_ENOMEM;
+    sbd_gmres_options o{};
+    int m = 1;
+    const T* bb = nullptr;
+    T* xx = nullptr;
+    double bnorm = 0.0, rel = 1.0;
+    int total = 0, j = 0;
+    State st = RESIDUAL;
+    std::vector<zc> h, h2, cs, sn, g;
+    std::vector<std::vector<zc>> H;
+
+    ~Session() override {
+        if (S.Vb) cudaFreeAsync(S.Vb, S.s);
+        if (S.tmp) cudaFreeAsync(S.tmp, S.s);
+        if (S.partial) cudaFreeAsync(S.partial, S.s);
+        if (S.hd) cudaFreeAsync(S.hd, S.s);
+        cudaStreamSynchronize(S.s);
     }
-    const T* bb = static_cast<const T*>(b);
-    T* xx = static_cast<T*>(x);
-    int rc = SBD_OK;
-    double bnorm = 0.0;
-    int total = 0;
-    double rel = 1.0;
-    std::vector<zc> h, h2;
-    std::vector<std::vector<zc>> H(m + 1, std::vector<zc>(m, zc(0)));
-    std::vector<zc> cs(m), sn(m), g(m + 1);
-    do {
-        if ((rc = S.norm(bb, &bnorm))) break;
+
+    int begin(sbd_plan_t plan, long n, const void* b, void* x, const sbd_gmres_options& opt, cudaStream_t s) {
+        o = opt;
+        m = std::max(1, o.restart);
+        S.plan = plan;
+        S.n = n;
+        S.s = s;
+        S.shift = zc(o.shift_re, o.shift_im);
+        S.scale = zc(o.scale_re, o.scale_im);
+        S.nblk = static_cast<int>(std::min<long>(1024, (n + 255) / 256));
+        if (cudaMallocAsync(&S.Vb, sizeof(T) * n * (m + 1), s) != cudaSuccess ||
+            cudaMallocAsync(&S.tmp, sizeof(T) * n, s) != cudaSuccess ||
+            cudaMallocAsync(&S.partial, sizeof(double2) * S.nblk * (m + 1), s) != cudaSuccess ||
+            cudaMallocAsync(&S.hd, sizeof(double2) * (m + 1), s) != cudaSuccess) {
+            cudaGetLastError();
+            set_error("sbd_gmres: workspace allocation failed");
+            return SBD_ENOMEM;
+        }
+        bb = static_cast<const T*>(b);
+        xx = static_cast<T*>(x);
+        H.assign(m + 1, std::vector<zc>(m, zc(0)));
+        cs.assign(m, zc(0));
+        sn.assign(m, zc(0));
+        g.assign(m + 1, zc(0));
+        int rc = S.norm(bb, &bnorm);
+        if (rc) return rc;
         if (bnorm == 0.0) {
             SBD_CUDA_TRY(cudaMemsetAsync(xx, 0, sizeof(T) * n, s));
             rel = 0.0;
-            break;
+            st = DONE;
+        } else if (total >= o.max_iter) {
+            st = DONE;
         }
-        while (total < o.max_iter) {
-            // r = b - A x, stored as V0
+        return SBD_OK;
+    }
+
+    int next(const void** in, void** out) override {
+        switch (st) {
+            case RESIDUAL: *in = xx; *out = S.Vb; return 1;
+            case ARNOLDI: *in = S.Vb + static_cast<long>(j) * S.n; *out = S.Vb + static_cast<long>(j + 1) * S.n; return 1;
+            case CHECK: *in = xx; *out = S.tmp; return 1;
+            default: *in = nullptr; *out = nullptr; return 0;
+        }
+    }
+
+    // y = shift v + scale y (y held A v)
+    void shifted(const T* v, T* y) {
+        axpby_kernel<CPLX><<<S.nblk, 256, 0, S.s>>>(S.n, make_double2(S.shift.real(), S.shift.imag()), v,
+                                                    make_double2(S.scale.real(), S.scale.imag()), y);
+    }
+
+    // x += V y after j Arnoldi steps (upper triangular solve on the host)
+    int update_x() {
+        std::vector<zc> y(j);
+        for (int i = j - 1; i >= 0; --i) {
+            zc t = g[i];
+            for (int k = i + 1; k < j; ++k) t -= H[i][k] * y[k];
+            y[i] = H[i][i] != zc(0) ? t / H[i][i] : zc(0);
+        }
+        return j > 0 ? S.axpy(j, y, +1, xx) : SBD_OK;
+    }
+
+    int advance() override {
+        int rc = SBD_OK;
+        const long n = S.n;
+        if (st == RESIDUAL) {
             T* v0 = S.Vb;
-            if ((rc = S.apply(xx, v0))) break;
-            axpby_kernel<CPLX><<<S.nblk, 256, 0, s>>>(n, make_double2(1, 0), bb, make_double2(-1, 0), v0);
+            shifted(xx, v0);
+            axpby_kernel<CPLX><<<S.nblk, 256, 0, S.s>>>(n, make_double2(1, 0), bb, make_double2(-1, 0), v0);
+            SBD_LAUNCH_CHECK();
             double beta;
-            if ((rc = S.norm(v0, &beta))) break;
+            if ((rc = S.norm(v0, &beta))) return rc;
             rel = beta / bnorm;
-            if (rel <= o.tol) break;
-            if ((rc = S.scal(v0, zc(1.0 / beta, 0)))) break;
+            if (rel <= o.tol) {
+                st = DONE;
+                return SBD_OK;
+            }
+            if ((rc = S.scal(v0, zc(1.0 / beta, 0)))) return rc;
             std::fill(g.begin(), g.end(), zc(0));
             g[0] = beta;
-            int j = 0;
-            for (; j < m && total < o.max_iter; ++j) {
-                T* w = S.Vb + static_cast<long>(j + 1) * n;
-                if ((rc = S.apply(S.Vb + static_cast<long>(j) * n, w))) break;
-                if ((rc = S.dots(j + 1, w, h)) || (rc = S.axpy(j + 1, h, -1, w))) break;
-                if ((rc = S.dots(j + 1, w, h2)) || (rc = S.axpy(j + 1, h2, -1, w))) break;   // second pass
-                for (int i = 0; i <= j; ++i) H[i][j] = h[i] + h2[i];
-                double hn;
-                if ((rc = S.norm(w, &hn))) break;
-                H[j + 1][j] = hn;
-                if (hn > 0) {
-                    if ((rc = S.scal(w, zc(1.0 / hn, 0)))) break;
-                }
-                for (int i = 0; i < j; ++i) {   // previous rotations
-                    const zc t = cs[i] * H[i][j] + sn[i] * H[i + 1][j];
-                    H[i + 1][j] = -std::conj(sn[i]) * H[i][j] + cs[i] * H[i + 1][j];
-                    H[i][j] = t;
-                }
-                // rotation [c s; -conj(s) c] (c real) zeroing H[j+1][j]
-                const zc a = H[j][j], bq = H[j + 1][j];
-                const double den = std::sqrt(std::norm(a) + std::norm(bq));
-                if (den == 0.0) {
-                    cs[j] = 1.0;
-                    sn[j] = 0.0;
-                } else if (std::abs(a) == 0.0) {
-                    cs[j] = 0.0;
-                    sn[j] = 1.0;
-                } else {
-                    cs[j] = std::abs(a) / den;
-                    sn[j] = (a / std::abs(a)) * std::conj(bq) / den;
-                }
-                const zc hjj = cs[j] * H[j][j] + sn[j] * H[j + 1][j];
-                H[j + 1][j] = 0.0;
-                H[j][j] = hjj;
-                g[j + 1] = -std::conj(sn[j]) * g[j];
-                g[j] = cs[j] * g[j];
-                ++total;
-                rel = std::abs(g[j + 1]) / bnorm;
-                if (rel <= o.tol) {
-                    ++j;
-                    break;
-                }
-            }
-            if (rc) break;
-            // y = H^{-1} g (upper triangular j x j), x += V y
-            std::vector<zc> y(j);
-            for (int i = j - 1; i >= 0; --i) {
-                zc t = g[i];
-                for (int k = i + 1; k < j; ++k) t -= H[i][k] * y[k];
-                y[i] = H[i][i] != zc(0) ? t / H[i][i] : zc(0);
-            }
-            if (j > 0 && (rc = S.axpy(j, y, +1, xx))) break;
-            if (rel <= o.tol) {
-                // confirm with the true residual
-                if ((rc = S.apply(xx, S.tmp))) break;
-                axpby_kernel<CPLX><<<S.nblk, 256, 0, s>>>(n, make_double2(1, 0), bb, make_double2(-1, 0), S.tmp);
-                double r2;
-                if ((rc = S.norm(S.tmp, &r2))) break;
-                rel = r2 / bnorm;
-                if (rel <= o.tol * 1.0000001 || total >= o.max_iter) break;
-            }
+            j = 0;
+            st = ARNOLDI;
+            return SBD_OK;
         }
-    } while (false);
-    release();
-    if (iters) *iters = total;
-    if (rel_res) *rel_res = rel;
-    return rc;
-}
+        if (st == ARNOLDI) {
+            T* w = S.Vb + static_cast<long>(j + 1) * n;
+            shifted(S.Vb + static_cast<long>(j) * n, w);
+            SBD_LAUNCH_CHECK();
+            if ((rc = S.dots(j + 1, w, h)) || (rc = S.axpy(j + 1, h, -1, w))) return rc;
+            if ((rc = S.dots(j + 1, w, h2)) || (rc = S.axpy(j + 1, h2, -1, w))) return rc;   // second pass
+            for (int i = 0; i <= j; ++i) H[i][j] = h[i] + h2[i];
+            double hn;
+            if ((rc = S.norm(w, &hn))) return rc;
+            H[j + 1][j] = hn;
+            if (hn > 0 && (rc = S.scal(w, zc(1.0 / hn, 0)))) return rc;
+            for (int i = 0; i < j; ++i) {   // previous rotations
+                const zc t = cs[i] * H[i][j] + sn[i] * H[i + 1][j];
+                H[i + 1][j] = -std::conj(sn[i]) * H[i][j] + cs[i] * H[i + 1][j];
+                H[i][j] = t;
+            }
+            // rotation [c s; -conj(s) c] (c real) zeroing H[j+1][j]
+            const zc a = H[j][j], bq = H[j + 1][j];
+            const double den = std::sqrt(std::norm(a) + std::norm(bq));
+            if (den == 0.0) {
+                cs[j] = 1.0;
+                sn[j] = 0.0;
+            } else if (std::abs(a) == 0.0) {
+                cs[j] = 0.0;
+                sn[j] = 1.0;
+            } else {
+                cs[j] = std::abs(a) / den;
+                sn[j] = (a / std::abs(a)) * std::conj(bq) / den;
+            }
+            const zc hjj = cs[j] * H[j][j] + sn[j] * H[j + 1][j];
+            H[j + 1][j] = 0.0;
+            H[j][j] = hjj;
+            g[j + 1] = -std::conj(sn[j]) * g[j];
+            g[j] = cs[j] * g[j];
+            ++total;
+            rel = std::abs(g[j + 1]) / bnorm;
+            ++j;
+            if (rel <= o.tol) {
+                if ((rc = update_x())) return rc;
+                st = CHECK;                      // confirm with the true residual
+            } else if (j == m || total >= o.max_iter) {
+                if ((rc = update_x())) return rc;
+                st = total >= o.max_iter ? DONE : RESIDUAL;   // restart
+            }
+            return SBD_OK;
+        }
+        if (st == CHECK) {
+            shifted(xx, S.tmp);
+            axpby_kernel<CPLX><<<S.nblk, 256, 0, S.s>>>(n, make_double2(1, 0), bb, make_double2(-1, 0), S.tmp);
+            SBD_LAUNCH_CHECK();
+            double r2;
+            if ((rc = S.norm(S.tmp, &r2))) return rc;
+            rel = r2 / bnorm;
+            st = (rel <= o.tol * 1.0000001 || total >= o.max_iter) ? DONE : RESIDUAL;
+            return SBD_OK;
+        }
+        return SBD_OK;
+    }
+
+    void finish(int32_t* iters, double* rel_res) override {
+        if (iters) *iters = total;
+        if (rel_res) *rel_res = rel;
+    }
+};
 
 }  // namespace
 
 }  // namespace sbd
 
-extern "C" int sbd_gmres(sbd_plan_t plan, const void* b, void* x, const sbd_gmres_options* opt, int32_t* iterations,
-                         double* rel_residual, void* cuda_stream) {
+struct sbd_gmres_session_s {
+    sbd::SessionBase* impl = nullptr;
+};
+
+extern "C" int sbd_gmres_begin(sbd_plan_t plan, const void* b, void* x, const sbd_gmres_options* opt,
+                               void* cuda_stream, sbd_gmres_session_t* out) {
     using namespace sbd;
-    if (!plan || !b || !x || !opt || opt->restart < 1 || opt->max_iter < 0 || !(opt->tol > 0)) {
+    if (!plan || !b || !x || !opt || !out || opt->restart < 1 || opt->max_iter < 0 || !(opt->tol > 0)) {
         set_error("sbd_gmres: invalid argument");
         return SBD_EINVAL;
     }
@@ -330,7 +383,62 @@ extern "C" int sbd_gmres(sbd_plan_t plan, const void* b, void* x, const sbd_gmre
         return SBD_EINVAL;
     }
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
-    return st.kind == SBD_HELMHOLTZ
-               ? gmres_impl<true>(plan, st.n_points, b, x, *opt, iterations, rel_residual, s)
-               : gmres_impl<false>(plan, st.n_points, b, x, *opt, iterations, rel_residual, s);
+    auto* h = new sbd_gmres_session_s();
+    if (st.kind == SBD_HELMHOLTZ) {
+        auto* ss = new Session<true>();
+        h->impl = ss;
+        rc = ss->begin(plan, st.n_points, b, x, *opt, s);
+    } else {
+        auto* ss = new Session<false>();
+        h->impl = ss;
+        rc = ss->begin(plan, st.n_points, b, x, *opt, s);
+    }
+    if (rc) {
+        delete h->impl;
+        delete h;
+        return rc;
+    }
+    *out = h;
+    return SBD_OK;
+}
+
+extern "C" int sbd_gmres_next(sbd_gmres_session_t sess, const void** in, void** out) {
+    if (!sess || !in || !out) {
+        sbd::set_error("sbd_gmres_next: null argument");
+        return SBD_EINVAL;
+    }
+    return sess->impl->next(in, out);
+}
+
+extern "C" int sbd_gmres_advance(sbd_gmres_session_t sess) {
+    if (!sess) {
+        sbd::set_error("sbd_gmres_advance: null session");
+        return SBD_EINVAL;
+    }
+    return sess->impl->advance();
+}
+
+extern "C" int sbd_gmres_end(sbd_gmres_session_t sess, int32_t* iterations, double* rel_residual) {
+    if (!sess) return SBD_OK;
+    sess->impl->finish(iterations, rel_residual);
+    delete sess->impl;
+    delete sess;
+    return SBD_OK;
+}
+
+extern "C" int sbd_gmres(sbd_plan_t plan, const void* b, void* x, const sbd_gmres_options* opt, int32_t* iterations,
+                         double* rel_residual, void* cuda_stream) {
+    sbd_gmres_session_t sess = nullptr;
+    int rc = sbd_gmres_begin(plan, b, x, opt, cuda_stream, &sess);
+    if (rc) return rc;
+    // the matvecs replay the plan's CUDA graph (launch cost matters for the small systems a
+    // solver sees)
+    const void* in = nullptr;
+    void* out = nullptr;
+    while (!rc && sbd_gmres_next(sess, &in, &out) == 1) {
+        rc = sbd_matvec_graph(plan, in, out, 1, cuda_stream);
+        if (!rc) rc = sbd_gmres_advance(sess);
+    }
+    sbd_gmres_end(sess, iterations, rel_residual);
+    return rc;
 }

@@ -121,6 +121,10 @@ _SIGS = {
     "sbd_fft2_noalloc": ([_P, _P, _I32, _I32, _I32, _I32, _P], ctypes.c_int),
     "sbd_gmres": ([_P, _P, _P, ctypes.POINTER(sbd_gmres_options), ctypes.POINTER(_I32), ctypes.POINTER(_D), _P],
                   ctypes.c_int),
+    "sbd_gmres_begin": ([_P, _P, _P, ctypes.POINTER(sbd_gmres_options), _P, ctypes.POINTER(_P)], ctypes.c_int),
+    "sbd_gmres_next": ([_P, ctypes.POINTER(_P), ctypes.POINTER(_P)], ctypes.c_int),
+    "sbd_gmres_advance": ([_P], ctypes.c_int),
+    "sbd_gmres_end": ([_P, ctypes.POINTER(_I32), ctypes.POINTER(_D)], ctypes.c_int),
     "sbd_profile": ([_P, _I32], ctypes.c_int),
     "sbd_profile_read": ([_P, _P, _P], ctypes.c_int),
     "sbd_error_string": ([ctypes.c_int], ctypes.c_char_p),
@@ -312,6 +316,37 @@ def sbd_gmres(plan: int, b, x, shift=1.0, scale=1.0, tol: float = 1e-6, restart:
 
 
 STAGES = ("sum", "spread", "fft_fwd", "node", "fft_inv", "interp", "spmv")
+
+
+def sbd_gmres_begin(plan: int, b, x, shift=1.0, scale=1.0, tol: float = 1e-6, restart: int = 30,
+                    max_iter: int = 300, stream=None) -> int:
+    """A resumable GMRES session on (shift I + scale A) x = b; returns its handle."""
+    sh, sc = complex(shift), complex(scale)
+    opt = sbd_gmres_options(sh.real, sh.imag, sc.real, sc.imag, tol, restart, max_iter)
+    out = _P()
+    _check(lib.sbd_gmres_begin(plan, _ptr(b), _ptr(x), ctypes.byref(opt), _stream(stream), ctypes.byref(out)),
+           "sbd_gmres_begin")
+    return out.value
+
+
+def sbd_gmres_next(session: int):
+    """(in, out) device pointers of the matvec the session needs, or None when it has finished."""
+    pi, po = _P(), _P()
+    rc = lib.sbd_gmres_next(session, ctypes.byref(pi), ctypes.byref(po))
+    if rc < 0:
+        _check(rc, "sbd_gmres_next")
+    return (pi.value, po.value) if rc == 1 else None
+
+
+def sbd_gmres_advance(session: int) -> None:
+    _check(lib.sbd_gmres_advance(session), "sbd_gmres_advance")
+
+
+def sbd_gmres_end(session: int):
+    """Frees the session; returns (iterations, relative residual)."""
+    it, res = _I32(), _D()
+    _check(lib.sbd_gmres_end(session, ctypes.byref(it), ctypes.byref(res)), "sbd_gmres_end")
+    return it.value, res.value
 
 
 def sbd_profile(plan: int, enable: bool) -> None:

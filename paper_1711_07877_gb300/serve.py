@@ -246,6 +246,39 @@ class CudaBackend:
         stream.synchronize()
         return xt.cpu().numpy(), it, res
 
+    def solve_batched(self, plan, req, stream, tol: float, restart: int, max_iter: int, sched):
+        """GMRES as a session whose matvecs go through the scheduler (merged with other solves')."""
+        torch = self.torch
+        with torch.cuda.stream(stream):
+            bt = torch.from_numpy(req.b).to("cuda", non_blocking=True)
+            xt = torch.zeros_like(bt)
+        sess = S.sbd_gmres_begin(plan, bt, xt, req.shift, req.scale, tol, restart, max_iter, stream.cuda_stream)
+        try:
+            while True:
+                io = S.sbd_gmres_next(sess)
+                if io is None:
+                    break
+                ready = torch.cuda.Event()
+                ready.record(stream)
+                done = sched.submit(plan, io[0], io[1], ready)
+                stream.wait_event(done)
+                S.sbd_gmres_advance(sess)
+        finally:
+            it, res = S.sbd_gmres_end(sess)
+        stream.synchronize()
+        return xt.cpu().numpy(), it, res
+
+    def matvec_batched(self, tickets, stream):
+        """One sbd_matvec_batched for the tickets' matvecs (distinct plans) on stream, after each
+        ticket's ready event; returns the event that marks the batch done."""
+        for t in tickets:
+            stream.wait_event(t.ready)
+        S.sbd_matvec_batched([t.plan for t in tickets], [t.inp for t in tickets], [t.out for t in tickets],
+                             stream=stream.cuda_stream)
+        done = self.torch.cuda.Event()
+        done.record(stream)
+        return done
+
     def synchronize(self, stream) -> None:
         stream.synchronize()
 
@@ -254,6 +287,96 @@ class CudaBackend:
 
     def destroy_now(self, plan) -> None:
         S.sbd_destroy(plan)
+
+
+@dataclass
+class _Ticket:
+    plan: object
+    inp: object
+    out: object
+    ready: object
+    done: object = None
+    error: Exception | None = None
+    flag: threading.Event = field(default_factory=threading.Event)
+
+
+class MatvecScheduler:
+    """Iteration-level batching of the server's solves: a worker whose GMRES session needs a
+    matvec submits it (plan, in, out, an event on its stream) and waits until the batch that
+    holds it is enqueued; the scheduler thread takes the pending matvecs of distinct plans
+    (at most max_batch), waiting up to window_s for every solving worker to submit, launches
+    them as one sbd_matvec_batched on its own stream and hands each worker the batch's event,
+    which the worker's stream waits on before the session continues."""
+
+    def __init__(self, backend, max_batch: int = 64, window_s: float = 0.0005):
+        self.backend = backend
+        self.max_batch = max_batch
+        self.window_s = window_s
+        self.stream = backend.stream()
+        self.cv = threading.Condition()
+        self.pending: list[_Ticket] = []
+        self.active = 0          # workers inside a solve
+        self.closed = False
+        self.batches = 0
+        self.matvecs = 0
+        self.thread = threading.Thread(target=self._run, daemon=True)
+        self.thread.start()
+
+    def enter(self) -> None:
+        with self.cv:
+            self.active += 1
+
+    def leave(self) -> None:
+        with self.cv:
+            self.active -= 1
+            self.cv.notify_all()
+
+    def submit(self, plan, inp, out, ready):
+        t = _Ticket(plan, inp, out, ready)
+        with self.cv:
+            self.pending.append(t)
+            self.cv.notify_all()
+        t.flag.wait()
+        if t.error is not None:
+            raise t.error
+        return t.done
+
+    def close(self) -> None:
+        with self.cv:
+            self.closed = True
+            self.cv.notify_all()
+        self.thread.join()
+
+    def _run(self) -> None:
+        while True:
+            with self.cv:
+                while not self.pending and not self.closed:
+                    self.cv.wait(timeout=0.05)
+                if self.closed and not self.pending:
+                    return
+                end = time.perf_counter() + self.window_s
+                while len(self.pending) < self.active and not self.closed:
+                    left = end - time.perf_counter()
+                    if left <= 0:
+                        break
+                    self.cv.wait(timeout=left)
+                take, seen = [], set()
+                for t in list(self.pending):
+                    if len(take) < self.max_batch and t.plan not in seen:
+                        take.append(t)
+                        seen.add(t.plan)
+                        self.pending.remove(t)
+            try:
+                done = self.backend.matvec_batched(take, self.stream)
+                for t in take:
+                    t.done = done
+            except Exception as e:   # every matvec of the batch fails with it
+                for t in take:
+                    t.error = e
+            self.batches += 1
+            self.matvecs += len(take)
+            for t in take:
+                t.flag.set()
 
 
 class Server:
@@ -268,8 +391,10 @@ class Server:
 
     def __init__(self, slots: int = 4, hbm_budget: int | None = None, form: int = S.SBD_FORM_FP32,
                  tol: float = 1e-6, restart: int = 30, max_iter: int = 300, fit_grid: bool = True,
-                 backend=None, retries: int = 3, watchdog_s: float = 0.01):
+                 backend=None, retries: int = 3, watchdog_s: float = 0.01, batch_matvecs: bool = False):
         self.backend = backend or CudaBackend()
+        # batch_matvecs: the solves' matvecs merge into batched launches (MatvecScheduler)
+        self.sched = MatvecScheduler(self.backend) if batch_matvecs else None
         self.slots = slots
         self.form = form
         self.tol, self.restart, self.max_iter = tol, restart, max_iter
@@ -350,8 +475,16 @@ class Server:
                     plan, info = be.plan(req, stream, dmin, dmax, self.form, self.host_threads)
                     req.plan_seconds = info["plan_seconds"]
                     req.device_bytes = info["device_bytes"]
-                req.x, req.iterations, req.residual = be.solve(plan, req, stream, self.tol, self.restart,
-                                                               self.max_iter)
+                if self.sched is not None:
+                    self.sched.enter()
+                    try:
+                        req.x, req.iterations, req.residual = be.solve_batched(plan, req, stream, self.tol,
+                                                                               self.restart, self.max_iter, self.sched)
+                    finally:
+                        self.sched.leave()
+                else:
+                    req.x, req.iterations, req.residual = be.solve(plan, req, stream, self.tol, self.restart,
+                                                                   self.max_iter)
             except Exception as e:  # the request fails (or waits again), the server keeps serving
                 if getattr(e, "code", None) == S.SBD_ENOMEM and req.attempts < self.retries:
                     requeue = True
@@ -396,6 +529,8 @@ class Server:
         for w in self.workers:
             w.join()
         self.watchdog.join()
+        if self.sched is not None:
+            self.sched.close()
         for v in list(self.adm.resident.values()):
             if v["plan"]:
                 self.backend.destroy_now(v["plan"])
@@ -440,6 +575,9 @@ def run_poisson(requests: list[Request], mean_gap_s: float, seed: int = 0, timeo
     summ = srv.stats.summary()
     summ["incomplete"] = 0 if finished else sum(r.error == "not finished within the drain timeout" for r in requests)
     summ["requeued"] = srv.requeued
+    if srv.sched is not None:
+        summ["matvec_batches"] = srv.sched.batches
+        summ["matvecs_batched"] = srv.sched.matvecs
     summ["deadline_dropped"] = srv.dropped
     summ["late"] = sum(1 for r in requests if r.late)
     return srv, summ

@@ -145,6 +145,54 @@ def test_server_results_match_solo_solves(S):
         assert np.linalg.norm(r.x - xs) / np.linalg.norm(xs) < 1e-6, r.rid
 
 
+def test_server_batched_matvecs_match_solo_solves(S):
+    """The same requests with the solves' matvecs merged into batched launches (iteration-level
+    batching): the answers of the solo solves, and most launches carry several solves."""
+    from paper_1711_07877_gb300 import serve
+    reqs, solo = [], []
+    specs = [("laplace", 1500), ("helmholtz", 2000), ("laplace", 3000), ("helmholtz", 1200),
+             ("laplace", 2500), ("laplace", 1000)]
+    tol = 1e-8
+    for i, (kind, n) in enumerate(specs):
+        z, kappa, dmin, b = system(kind, n, 20 + i)
+        reqs.append(serve.Request(rid=i, z=z, b=b, kind=S.SBD_HELMHOLTZ if kind == "helmholtz" else S.SBD_LAPLACE,
+                                  kappa=kappa, delta_min=dmin, eps=1e-10, shift=1.0, scale=1.0 / n))
+        solo.append(solve_gpu(S, z, kind, kappa, dmin, 1e-10, b, 0, tol, 1.0, 1.0 / n)[0])
+    srv, summary = serve.run_poisson(reqs, mean_gap_s=0.0005, seed=5, slots=6, form=S.SBD_FORM_FP64, tol=tol,
+                                     batch_matvecs=True)
+    assert [r.error for r in reqs] == [None] * len(reqs)
+    assert summary["matvecs_batched"] >= sum(r.iterations for r in reqs)
+    assert summary["matvec_batches"] < summary["matvecs_batched"]
+    for r, xs in zip(reqs, solo):
+        assert r.residual <= tol * 1.0001
+        assert np.linalg.norm(r.x - xs) / np.linalg.norm(xs) < 1e-6, r.rid
+
+
+def test_gmres_session_equals_gmres(S):
+    """The session API driven by hand (plain matvecs) gives sbd_gmres's answer."""
+    z, kappa, dmin, b = system("helmholtz", 1800, 60)
+    x_ref, it_ref, res_ref = solve_gpu(S, z, "helmholtz", kappa, dmin, 1e-8, b, 0, 1e-6, 0.5, 1.0 / 1800)
+    p = S.sbd_plan(torch.from_numpy(z).cuda(), 1800, S.SBD_HELMHOLTZ, kappa, dmin, 1e-8, S.make_options(form=0))
+    try:
+        bt = torch.from_numpy(b).cuda()
+        xt = torch.zeros_like(bt)
+        sess = S.sbd_gmres_begin(p, bt, xt, 0.5, 1.0 / 1800, 1e-6)
+        steps = 0
+        while True:
+            io = S.sbd_gmres_next(sess)
+            if io is None:
+                break
+            S.sbd_matvec(p, io[0], io[1])
+            S.sbd_gmres_advance(sess)
+            steps += 1
+        it, res = S.sbd_gmres_end(sess)
+        torch.cuda.synchronize()
+        assert abs(it - it_ref) <= 1 and res <= 1e-6 and steps >= it
+        assert np.linalg.norm(xt.cpu().numpy() - x_ref) / np.linalg.norm(x_ref) < 1e-6
+    finally:
+        S.sbd_destroy(p)
+
+
 def test_server_budget_serialises(S):
     """A budget smaller than any request admits one request at a time."""
     from paper_1711_07877_gb300 import serve

@@ -238,3 +238,36 @@ def test_deadline_drops_queued_requests_and_marks_late_ones():
     assert queued.error is not None and "deadline" in queued.error and srv.dropped == 1
     assert free.error is None and not free.late
     assert be.destroyed == 2            # the two solved requests released their plans
+
+
+class FakeBatchedBackend(FakeBackend):
+    """Stand-in whose solves ask for `steps` matvecs through the scheduler."""
+
+    def __init__(self, steps=20):
+        super().__init__()
+        self.steps = steps
+        self.batch_sizes = []
+
+    def solve_batched(self, plan, req, stream, tol, restart, max_iter, sched):
+        for _ in range(self.steps):
+            sched.submit(plan, None, None, None)
+            time.sleep(0.0005)                 # the session's own work between matvecs
+        return np.zeros_like(req.b), self.steps, 1e-7
+
+    def matvec_batched(self, tickets, stream):
+        assert len({id(t.plan) for t in tickets}) == len(tickets)   # distinct plans per batch
+        self.batch_sizes.append(len(tickets))
+        return None
+
+
+def test_scheduler_merges_the_solves_matvecs():
+    be = FakeBatchedBackend(steps=20)
+    srv = Server(slots=4, hbm_budget=10 ** 9, backend=be, fit_grid=False, batch_matvecs=True)
+    reqs = [mk(i) for i in range(8)]
+    for r in reqs:
+        srv.submit(r)
+    assert srv.drain(reqs, timeout_s=30)
+    assert all(r.error is None and r.iterations == 20 for r in reqs)
+    assert srv.sched.matvecs == 8 * 20 == sum(be.batch_sizes)
+    assert srv.sched.batches < srv.sched.matvecs / 2          # most launches carry several solves
+    assert max(be.batch_sizes) <= 4                           # at most one matvec per solving worker
