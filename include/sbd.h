@@ -103,6 +103,10 @@ typedef struct {
  * SBD_EINVAL. */
 #define SBD_FLAG_SPREAD_SIGMA_2 4
 #define SBD_FLAG_SPREAD_SIGMA_15 8
+/* Oversampling 1.25 (ES window of about 14 cells at the FP32 tolerance): a further sixth off
+ * the grid and FFT sides for wider point stencils.  With another oversampling flag or
+ * GAUSSIAN_SPREAD it is SBD_EINVAL. */
+#define SBD_FLAG_SPREAD_SIGMA_125 64
 /* Close correction D f in float32 (see sbd_form); with SBD_FORM_FP64 it is SBD_EINVAL. */
 #define SBD_FLAG_NEAR_FP32 16
 /* Uniform-grid multiplier variant of the far part (the fast summation the paper cites as the

@@ -637,13 +637,16 @@ int check_plan_call(sbd_plan_t p, const void* a, const void* b) {
 // non-negative counts and tolerances.
 bool options_valid(const sbd_options& o) {
     const int known = SBD_FLAG_GAUSSIAN_NODES | SBD_FLAG_GAUSSIAN_SPREAD | SBD_FLAG_SPREAD_SIGMA_2 |
-                      SBD_FLAG_SPREAD_SIGMA_15 | SBD_FLAG_NEAR_FP32 | SBD_FLAG_UNIFORM_GRID;
+                      SBD_FLAG_SPREAD_SIGMA_15 | SBD_FLAG_NEAR_FP32 | SBD_FLAG_UNIFORM_GRID |
+                      SBD_FLAG_SPREAD_SIGMA_125;
+    const int sig = o.flags & (SBD_FLAG_SPREAD_SIGMA_2 | SBD_FLAG_SPREAD_SIGMA_15 | SBD_FLAG_SPREAD_SIGMA_125);
     const int not_uniform = SBD_FLAG_GAUSSIAN_NODES | SBD_FLAG_GAUSSIAN_SPREAD;
     return (o.form == SBD_FORM_FP64 || o.form == SBD_FORM_FP32) && (o.flags & ~known) == 0 &&
            !((o.flags & SBD_FLAG_UNIFORM_GRID) && (o.flags & not_uniform)) &&
            !((o.flags & SBD_FLAG_NEAR_FP32) && o.form != SBD_FORM_FP32) &&
-           !((o.flags & SBD_FLAG_SPREAD_SIGMA_2) && (o.flags & SBD_FLAG_SPREAD_SIGMA_15)) &&
-           !((o.flags & SBD_FLAG_GAUSSIAN_SPREAD) && (o.flags & SBD_FLAG_SPREAD_SIGMA_15)) && o.fixed_P >= 0 &&
+           (sig & (sig - 1)) == 0 &&   // at most one oversampling flag
+           !((o.flags & SBD_FLAG_GAUSSIAN_SPREAD) && (o.flags & (SBD_FLAG_SPREAD_SIGMA_15 | SBD_FLAG_SPREAD_SIGMA_125))) &&
+           o.fixed_P >= 0 &&
            o.max_nrhs >= 0 && o.nufft_tol >= 0 && o.delta_max >= 0 && o.host_threads >= 0;
 }
 
@@ -657,7 +660,10 @@ int plan_transform_params(const SbdFit& fit, const sbd_options& o, double eps, d
     const double tol = o.nufft_tol > 0 ? o.nufft_tol : eps / (6.0 * std::max(W, 1e-300));
     const int kwin = (o.flags & SBD_FLAG_GAUSSIAN_NODES) ? 0 : 1;
     const int swin = (o.flags & SBD_FLAG_GAUSSIAN_SPREAD) ? 0 : 1;
-    const int sigma_mode = (o.flags & SBD_FLAG_SPREAD_SIGMA_15) ? 1 : (o.flags & SBD_FLAG_SPREAD_SIGMA_2) ? 2 : 0;
+    const int sigma_mode = (o.flags & SBD_FLAG_SPREAD_SIGMA_15)    ? 1
+                           : (o.flags & SBD_FLAG_SPREAD_SIGMA_2)   ? 2
+                           : (o.flags & SBD_FLAG_SPREAD_SIGMA_125) ? 3
+                                                                   : 0;
     int rc = (o.flags & SBD_FLAG_UNIFORM_GRID)
                  ? uniform_params(fit, half, cx, cy, tol, o.form == SBD_FORM_FP32, swin, sigma_mode, n, np, err)
                  : nufft_params(fit, half, cx, cy, tol, o.form == SBD_FORM_FP32, kwin, swin, sigma_mode, n, np, err);

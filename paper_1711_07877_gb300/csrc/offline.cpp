@@ -686,6 +686,8 @@ int nufft_params(const SbdFit& fit, double half_extent, double cx, double cy, do
     if (swin == 1) {
         if (sigma_mode == 1) {
             sig = 1.5;
+        } else if (sigma_mode == 3) {
+            sig = 1.25;
         } else if (sigma_mode == 0) {
             const double m2 = 2.0 * half_extent * (2.0 * S) / kPi;   // cells per side at sigma = 2
             if (m2 * m2 > 20.0 * static_cast<double>(n_points)) sig = 1.5;
@@ -809,6 +811,8 @@ int uniform_params(const SbdFit& fit, double half_extent, double cx, double cy, 
     if (swin == 1) {
         if (sigma_mode == 1) {
             sig = 1.5;
+        } else if (sigma_mode == 3) {
+            sig = 1.25;
         } else if (sigma_mode == 0) {
             const double m2 = 2.0 * half_extent * (2.0 * o.kcut) / kPi;
             if (m2 * m2 > 20.0 * static_cast<double>(n_points)) sig = 1.5;

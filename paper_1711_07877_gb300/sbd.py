@@ -180,6 +180,7 @@ SBD_FLAG_SPREAD_SIGMA_2 = 4
 SBD_FLAG_SPREAD_SIGMA_15 = 8
 SBD_FLAG_NEAR_FP32 = 16
 SBD_FLAG_UNIFORM_GRID = 32
+SBD_FLAG_SPREAD_SIGMA_125 = 64
 
 
 def make_options(form: int = SBD_FORM_FP64, fixed_P: int = 0, nufft_tol: float = 0.0, max_nrhs: int = 1,

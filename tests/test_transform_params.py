@@ -110,7 +110,7 @@ def test_invalid_arguments(curves):
     bad = [
         dict(flags=S.SBD_FLAG_SPREAD_SIGMA_2 | S.SBD_FLAG_SPREAD_SIGMA_15),
         dict(flags=S.SBD_FLAG_GAUSSIAN_SPREAD | S.SBD_FLAG_SPREAD_SIGMA_15),
-        dict(flags=64),
+        dict(flags=1 << 20),
     ]
     for kw in bad:
         with pytest.raises(S.SbdError) as e:
