@@ -265,24 +265,25 @@ def test_matvec_within_eps_of_direct_sum(S, config1, form, flags):
 
 
 def test_spreading_oversampling_choice(S, lap_small):
-    """Automatic oversampling of the spreading grid: 1.5 (wider stencil, grid side about 3/4)
-    where the grid at 2 has more than 20 cells per point, else 2; the flags force either, and
+    """Automatic oversampling of the spreading grid: 1.25 (widest stencil, smallest grid) where the
+    grid at 2 has more than 60 cells per point, 1.5 above 20, else 2; the flags force each, and
     contradictory flags are rejected."""
     z, f, dmin, pl = lap_small
     info = {}
-    for flags in (0, 4, 8):
+    for flags in (0, 4, 8, 64):
         p = make_plan(S, z, "laplace", dmin, 1e-6, form=1, flags=flags)
         try:
             info[flags] = S.sbd_plan_info(p)
         finally:
             S.sbd_destroy(p)
-    m2, m15 = info[4]["grid_x"], info[8]["grid_x"]
-    assert info[4]["stencil_x"] == 8 and info[8]["stencil_x"] == 10
-    assert m15 < m2 and info[8]["grid_k"] <= 2 * m15
-    ratio = (m2 - 8 - 4) ** 2 / (20 * len(z))        # ~ cells per point at 2, over 20
-    if not 0.8 < ratio < 1.25:                       # away from the rounding of the grid side
-        assert info[0]["grid_x"] == info[8 if ratio > 1 else 4]["grid_x"]
-    for flags in (4 | 8, 2 | 8):
+    m2, m15, m125 = info[4]["grid_x"], info[8]["grid_x"], info[64]["grid_x"]
+    assert info[4]["stencil_x"] == 8 and info[8]["stencil_x"] == 10 and info[64]["stencil_x"] == 14
+    assert m125 < m15 < m2 and info[8]["grid_k"] <= 2 * m15
+    cells = (m2 - 8 - 4) ** 2 / len(z)               # ~ cells per point at 2
+    if not (16 < cells < 25 or 48 < cells < 75):      # away from the rounding of the grid side
+        want = 64 if cells > 60 else 8 if cells > 20 else 4
+        assert info[0]["grid_x"] == info[want]["grid_x"]
+    for flags in (4 | 8, 2 | 8, 8 | 64, 2 | 64):
         with pytest.raises(S.SbdError) as e:
             make_plan(S, z, "laplace", dmin, 1e-6, form=1, flags=flags)
         assert e.value.code == S.SBD_EINVAL

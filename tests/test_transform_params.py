@@ -48,16 +48,18 @@ def _params(curves, alpha=0.0, form=1, flags=0, kind=0, kappa=0.0):
 def test_sizes_follow_their_definitions(curves):
     n, dmax, half = curves
     t, dmin = _params(curves)
-    # large grid per point at alpha = 0: oversampling 1.5 and the ES width rule for it
-    assert t["sigma_s"] == 1.5 and t["spread_window"] == 1
-    assert t["nufft_tol"] == pytest.approx(3e-7)            # the FP32 floor
-    assert t["stencil_x"] == _even(math.ceil(math.log(10 / 3e-7) / (math.pi * math.sqrt(1 - 1 / 1.5))))
-    assert t["stencil_k"] == _even(math.ceil(-math.log10(3e-7)))
-    # h = pi / (sigma S), S = largest circle radius rho_P / delta_max (Laplace: scale delta_max)
     fit = S.sbd_offline_fit(S.SBD_LAPLACE, 0.0, dmin, dmax, EPS)
     assert fit["P"] == t["P"] and int(np.sum(fit["M"])) == t["n_xi"]
     s_max = fit["rho"][-1] / dmax
-    assert t["h"] == pytest.approx(math.pi / (1.5 * s_max), rel=1e-12)
+    # the oversampling rule: cells per point of the grid at 2 past 60 -> 1.25, past 20 -> 1.5, else 2
+    cells = (2 * half * 2 * s_max / math.pi) ** 2 / n
+    sig = 1.25 if cells > 60 else 1.5 if cells > 20 else 2.0
+    assert cells > 60 and t["sigma_s"] == sig and t["spread_window"] == 1   # a large grid per point at alpha = 0
+    assert t["nufft_tol"] == pytest.approx(3e-7)            # the FP32 floor
+    assert t["stencil_x"] == _even(math.ceil(math.log(10 / 3e-7) / (math.pi * math.sqrt(1 - 1 / sig))))
+    assert t["stencil_k"] == _even(math.ceil(-math.log10(3e-7)))
+    # h = pi / (sigma S), S = largest circle radius rho_P / delta_max (Laplace: scale delta_max)
+    assert t["h"] == pytest.approx(math.pi / (sig * s_max), rel=1e-12)
     assert t["grid_x"] == _good(math.ceil(2 * half / t["h"]) + t["stencil_x"] + 4)
     assert t["fft_n"] == 2 * t["grid_x"]
     assert t["deta"] == pytest.approx(2 * math.pi / (t["fft_n"] * t["h"]), rel=1e-12)
@@ -69,9 +71,12 @@ def test_sizes_follow_their_definitions(curves):
 def test_oversampling_choice_and_flags(curves):
     auto, _ = _params(curves)
     two, _ = _params(curves, flags=S.SBD_FLAG_SPREAD_SIGMA_2)
+    one5, _ = _params(curves, flags=S.SBD_FLAG_SPREAD_SIGMA_15)
     assert two["sigma_s"] == 2.0 and two["stencil_x"] == 8
+    assert one5["sigma_s"] == 1.5 and one5["stencil_x"] == 10
+    assert auto["sigma_s"] == 1.25 and auto["stencil_x"] == 14
     # the smaller spreading grid, the same frequency grid (it is set by S and the point extent)
-    assert 1.2 < two["grid_x"] / auto["grid_x"] < 1.45
+    assert 1.2 < two["grid_x"] / one5["grid_x"] < 1.45 and 1.1 < one5["grid_x"] / auto["grid_x"] < 1.3
     assert abs(two["grid_k"] - auto["grid_k"]) <= 0.05 * two["grid_k"]
     # few cells per point (alpha = 1/8: larger delta_min, fewer circles, a coarser grid): oversampling 2,
     # and the grid at 2 indeed holds fewer than ~20 cells per point
