@@ -10,7 +10,8 @@ one sbd_matvec over the whole point set, inputs resident in HBM.  The grids
 The default line also carries (N = 1 only, after the headline's timed region):
 balanced_delta_min (delta_min by measurement), uniform_grid (the same workload with the
 node step replaced by a multiplication on the frequency grid), near_fp32 (the same plan with D f in
-float32), fp64_form (the same workload in the FP64 form), helmholtz (kappa delta_max
+float32), fp64_form (the same workload in the FP64 form), eps_sweep (the same points and f at
+eps = 1e-3 and 1e-9, with the fit's Gram factorisation time), helmholtz (kappa delta_max
 = 500, FP32 and FP64 forms), table2 (separate targets and sources, the Table 2 setting),
 served and served_batched (a short serving run, the second with the solves' matvecs merged into
 batched launches: p50/p99 latency with a queue / plan / solve breakdown), and
@@ -26,6 +27,7 @@ instance (seed 2 + rank) and value is the sum over ranks (weak scaling).
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import json
 import math
 import os
@@ -624,6 +626,7 @@ def main():
         out["near_fp32"] = near_fp32_line(S, torch, stream, zt, ft, wl, args, nrhs, esz, stages, pool, idx, qref)
         out["fp64_form"] = form_line(S, torch, stream, zt, ft, wl, args, nrhs, esz, S.SBD_FORM_FP64, pool, idx,
                                      qref, value)
+        out["eps_sweep"] = eps_sweep(S, torch, stream, zt, ft, wl, args, nrhs, pool, idx, qref)
     if pool is not None:
         pool.close()
     del zt, ft
@@ -694,6 +697,35 @@ def form_line(S, torch, stream, zt, ft, wl, args, nrhs, esz, form, pool, idx, qr
         return line
     finally:
         r.close()
+
+
+def eps_sweep(S, torch, stream, zt, ft, wl, args, nrhs, pool, idx, qref):
+    """The headline points and f at the other tolerances of the curve workload, eps = 1e-3 and 1e-9
+    (delta_min by Theorem 1 at each eps): the FP64 form at both, the FP32 form at 1e-3 (its floor is
+    ~3e-7).  At 1e-9 the fit needs its full Gram Cholesky (P ~ 7000), factored on the device."""
+    import workloads as W
+    out = {}
+    for eps, forms in ((1e-3, ("fp32", "fp64")), (1e-9, ("fp64",))):
+        w = dataclasses.replace(wl, delta_min=W.theorem1_delta_min(args.n, eps, wl.meta["delta_max"], args.alpha),
+                                eps=eps)
+        line = {"delta_min": w.delta_min}
+        for name in forms:
+            S.sbd_fit_cache_clear()
+            r = Runner(S, torch, stream, zt, ft, w, S.SBD_FORM_FP32 if name == "fp32" else S.SBD_FORM_FP64, nrhs)
+            try:
+                fit_s, fit_where = S.sbd_fit_last_factorisation()
+                ms = r.time(min(args.steps, 5 if name == "fp64" else 20), 2)
+                d = {"ms_per_step": ms, "value": args.n * nrhs / (ms * 1e-3) / 1e9, "unit": UNIT,
+                     "plan": plan_keys(r.info)}
+                if fit_where:
+                    d["fit_factorisation"] = {"seconds": fit_s, "on": "device" if fit_where == 2 else "host"}
+                if pool is not None:
+                    d["accuracy"] = accuracy(r.q.cpu().numpy(), qref, w.f, idx)
+                line[name] = d
+            finally:
+                r.close()
+        out[f"{eps:g}"] = line
+    return out
 
 
 def table2_line(S, torch, stream, args):

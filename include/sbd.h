@@ -332,7 +332,8 @@ int sbd_destroy_async(sbd_plan_t plan, void* cuda_stream);
 
 /* ---------------------------------------------------------------------------------
  * sbd_offline_fit - the SBD fit and circle sizes alone, on the host (Sec. 3.2
- * Eq. LinearSystem with the explicit A^P; Sec. 1 P search; Sec. 5 sizes).  No GPU.
+ * Eq. LinearSystem with the explicit A^P; Sec. 1 P search; Sec. 5 sizes).  Needs no GPU;
+ * the full Cholesky of A^P (tolerances below 5e-9) runs on one when sbd_set_fit_device says so.
  *   kernel, delta_min, delta_max, eps   as for sbd_plan (delta_max given directly).
  *   fixed_P      > 0 fixes P, 0 searches.
  *   cap          capacity of rho / alpha / M (>= P, plus 1 for Helmholtz).
@@ -487,6 +488,17 @@ int sbd_plan_balanced(const double* points, int64_t n, sbd_kernel kernel, double
  * ------------------------------------------------------------------------------- */
 int sbd_fit_cache_stats(int64_t* hits, int64_t* misses, int64_t* entries);
 int sbd_fit_cache_clear(void);
+
+/* sbd_set_fit_device - where the off-line fit factors A^P when it needs its full Cholesky
+ * (fit tolerances below 5e-9, e.g. eps = 1e-9; Sec. 3.2, the O(P^3) step of Sec. 6.1): the
+ * matrix is then built and factored in FP64 on the current CUDA device and the factor copied
+ * back.  mode 0 (default): the device when one is present and P >= 3000, else the host;
+ * 1: always the host; 2: the device whenever one is present.  A device failure (no memory,
+ * a CUDA error) falls back to the host.  Process-wide.  SBD_EINVAL for another mode.
+ * sbd_fit_last_factorisation - host outputs (each may be NULL): the seconds of the last full
+ * factorisation and where it ran (0 none yet, 1 host, 2 device).  Always SBD_OK. */
+int sbd_set_fit_device(int32_t mode);
+int sbd_fit_last_factorisation(double* seconds, int32_t* where);
 
 /* sbd_y0_root - the k-th positive zero of Y0 (k >= 1) into *root (host).  For Helmholtz
  * the fit's scale k' is the first such zero >= kappa delta_max (Sec. 4.2), so a caller

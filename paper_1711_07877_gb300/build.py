@@ -16,8 +16,8 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libsbd.so")
-SOURCES = ["api.cu", "fft.cu", "far.cu", "node.cu", "near.cu", "noalloc.cu", "gmres.cu", "uniform.cu", "offline.cpp",
-           "bessel.cpp"]
+SOURCES = ["api.cu", "fft.cu", "far.cu", "node.cu", "near.cu", "noalloc.cu", "gmres.cu", "uniform.cu", "fit_gpu.cu",
+           "offline.cpp", "bessel.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -390,13 +390,6 @@ int build_far(sbd_plan_s* p, cudaStream_t s) {
         om[c] = mk<T>(static_cast<T>(w.real()), static_cast<T>(w.imag()));
         cs[c] = static_cast<T>(std::sqrt(np.circle_factor[c]));
     }
-    {
-        double omax = 0.0;
-        for (const auto& w : om) omax = std::max(omax, std::max(std::fabs(double(w.x)), std::fabs(double(w.y))));
-        // the ES spreading deconvolution multiplies a node's weight by at most psi_max^4
-        const double pm2 = np.swin == 1 ? np.psi_max * np.psi_max : 1.0;
-        p->tuning.wbound = static_cast<float>(omax * pm2 * pm2 * np.Pk * np.Pk);
-    }
     if ((rc = upload(p, reinterpret_cast<cx_t<T>**>(&p->omega_c), om, s))) return rc;
     if ((rc = upload(p, reinterpret_cast<T**>(&p->cscale_c), cs, s))) return rc;
     NodeRec<T>* canon = nullptr;
@@ -405,6 +398,13 @@ int build_far(sbd_plan_s* p, cudaStream_t s) {
                               p->n_rec, np.deta, np.nk, np.Pk, static_cast<const cx_t<T>*>(p->omega_c),
                               spread_deconv_of(p), canon, s);
     if (rc) return rc;
+    {
+        // bound of one product g w_a w_b of the fixed-point node variant: the largest record weight
+        // (deconvolution included) x 2 (complex product) x P_k^2 (window values <= 1)
+        double wmax = 0.0;
+        if ((rc = far_weight_max<T>(canon, p->n_rec, &wmax, s))) return rc;
+        p->tuning.wbound = static_cast<float>(2.0 * wmax * np.Pk * np.Pk);
+    }
     const int ntx = (np.nk + kNodeTile - 1) / kNodeTile;
     if ((rc = dev_alloc(p, &p->nodes, sizeof(NodeRec<T>) * p->n_rec))) return rc;
     if ((rc = dev_alloc(p, reinterpret_cast<void**>(&p->node_perm), sizeof(int) * p->n_rec))) return rc;
@@ -774,6 +774,22 @@ int sbd_y0_root(int32_t k, double* root) {
         return SBD_EINVAL;
     }
     *root = y0_root(k);
+    return SBD_OK;
+}
+
+int sbd_set_fit_device(int32_t mode) {
+    if (mode < 0 || mode > 2) {
+        set_error("sbd_set_fit_device: mode outside 0..2");
+        return SBD_EINVAL;
+    }
+    set_fit_device(mode);
+    return SBD_OK;
+}
+
+int sbd_fit_last_factorisation(double* seconds, int32_t* where) {
+    int w = 0;
+    last_factorisation(seconds, &w);
+    if (where) *where = w;
     return SBD_OK;
 }
 

@@ -1,6 +1,7 @@
 // Far-part kernels: record preparation (points, quadrature nodes), the per-node
 // gather / scatter of the standalone transforms, and the sum of f for the xi = 0 term.
 // The stencil operations of the matvec are the tiled kernels of node.cu.
+#include <cstring>
 #include "far.cuh"
 #include "sbd.h"
 #include "window.cuh"
@@ -257,7 +258,47 @@ int far_sum(const void* f, bool f_complex, long n, int nrhs, double2* sumf, cuda
     return SBD_OK;
 }
 
+namespace {
+// largest |component| of the records' weights; non-negative floats order as their bit patterns
+template <typename T>
+__global__ void weight_max_kernel(const NodeRec<T>* __restrict__ rec, long n, unsigned* __restrict__ out) {
+    float m = 0.f;
+    for (long i = blockIdx.x * static_cast<long>(blockDim.x) + threadIdx.x; i < n;
+         i += static_cast<long>(gridDim.x) * blockDim.x) {
+        const cx_t<T> w = rec[i].omega;
+        m = fmaxf(m, fmaxf(fabsf(static_cast<float>(w.x)), fabsf(static_cast<float>(w.y))));
+    }
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(m));
+}
+}  // namespace
+
+template <typename T>
+int far_weight_max(const NodeRec<T>* rec, long n, double* wmax, cudaStream_t s) {
+    unsigned* d = nullptr;
+    SBD_CUDA_TRY(cudaMallocAsync(&d, sizeof(unsigned), s));
+    unsigned h = 0;
+    cudaError_t e = cudaMemsetAsync(d, 0, sizeof(unsigned), s);
+    if (e == cudaSuccess && n > 0) {
+        const unsigned nb = static_cast<unsigned>(std::min<long>((n + 255) / 256, 2048));
+        weight_max_kernel<T><<<nb, 256, 0, s>>>(rec, n, d);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, d, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
+    cudaFreeAsync(d, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return SBD_ECUDA;
+    }
+    float f;
+    std::memcpy(&f, &h, sizeof f);
+    *wmax = f;
+    return SBD_OK;
+}
+
 #define SBD_FAR_INST(T)                                                                                   \
+    template int far_weight_max<T>(const NodeRec<T>*, long, double*, cudaStream_t);                       \
     template int far_prepare_points<T>(const double*, long, double, double, double, int, int, PointRec<T>*,  \
                                        cudaStream_t);                                                     \
     template int far_prepare_nodes<T>(const int*, const int*, const double*, const int*, int, long, double, \

@@ -68,6 +68,9 @@ template <typename T>
 int far_prepare_nodes(const int* circle_start, const int* half_start, const double* radius, const int* M,
                       int n_circles, long n_rec, double deta, int nk, int P, const cx_t<T>* omega_c,
                       const SpreadDeconv& sd, NodeRec<T>* out, cudaStream_t s);
+// *wmax (host) = max over the records of max(|Re omega'|, |Im omega'|) (synchronises s).
+template <typename T>
+int far_weight_max(const NodeRec<T>* rec, long n, double* wmax, cudaStream_t s);
 
 // Circle tables and the centre c of the point set, to place the canonical nodes in
 // absolute coordinates (the grids hold z - c).

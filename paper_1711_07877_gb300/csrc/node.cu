@@ -608,10 +608,11 @@ constexpr int kNodeThreads = 512;
 // then work on records far apart in the sorted order, which collide less).
 //
 // ACC = 2 (FP32 only): fixed-point accumulation in two int64 planes with native integer
-// atomics.  Every contribution g w_a w_b is at most max|K tile| max|omega'| P^2 =: B in
+// atomics.  Every contribution g w_a w_b is at most max|K tile| wbound =: B in
 // each component (window values <= 1), so scaling by 2^e with B 2^e <= 2^50 leaves room
 // for 2^13 contributions of the largest possible size per cell; the quantum is 2^-50 B,
-// far below FP32 rounding.  wbound = max|omega'| P^2.
+// far below FP32 rounding.  wbound = 2 max|omega'| P^2 (the 2 of the complex product),
+// taken from the plan's records, whose weights include the spreading deconvolution.
 template <typename T, int G, int NT, int ACC, int SCHED>
 __device__ __forceinline__ void node_fused_body(
     const NodeRec<T>* __restrict__ rec, const long long* __restrict__ tile_start, int ntx, int n, int P, int Ws,

@@ -15,6 +15,8 @@
 #include <mutex>
 
 #include <algorithm>
+#include <atomic>
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 
@@ -29,6 +31,10 @@ void gauss_legendre_0a(int Q, double a, std::vector<double>& s, std::vector<doub
 namespace {
 
 constexpr double kPi = 3.14159265358979323846;
+
+std::atomic<int> g_fit_device{0};
+std::atomic<int> g_last_where{0};
+std::atomic<double> g_last_seconds{0.0};
 
 inline size_t tri(size_t i) { return i * (i + 1) / 2; }   // packed lower row start
 
@@ -170,7 +176,23 @@ void build_fit(FitWork& w, int Pf) {
         const double Fa = x * x * 0.5 * (j0a[i] * j0a[i] + j1a[i] * j1a[i]) - x * j0a[i] * j1a[i];
         row[i] = 1.0 - 2.0 * kPi * w.C[i] * w.C[i] * Fa;
     }
-    w.Pok = cholesky_packed(w.L, Pf);
+    const auto t0 = std::chrono::steady_clock::now();
+    const int mode = fit_device_mode();
+    bool done = false;
+    if ((mode == 2 || (mode == 0 && Pf >= 3000)) && fit_gpu_available()) {
+        std::string err;
+        int pok = 0;
+        if (gram_cholesky_gpu(w.rho, w.C, j0a, j1a, a, Pf, w.L, &pok, err) == 0) {
+            w.Pok = pok;
+            done = true;
+            g_last_where = 2;
+        }
+    }
+    if (!done) {
+        w.Pok = cholesky_packed(w.L, Pf);
+        g_last_where = 1;
+    }
+    g_last_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     // J0(rho_p s) for every sample and p < Pf
     const int ns = static_cast<int>(w.s.size());
     w.Jmat.assign(static_cast<size_t>(ns) * Pf, 0.0);
@@ -741,9 +763,12 @@ int nufft_params(const SbdFit& fit, double half_extent, double cx, double cy, do
         o.nk = nk + (nk & 1);
     }
     if (o.nk > o.n) {
-        // a very small grid: the node stencils at sigma = 1.5 reach past the FFT length
+        // a very small grid: the node stencils at sigma < 2 reach past the FFT length
         if (sigma_mode == 0 && sig != 2.0)
-            return nufft_params(fit, half_extent, cx, cy, tol, fp32, kwin, swin, 2, n_points, o, err);
+            return nufft_params(fit, half_extent, cx, cy, tol, fp32, kwin, swin, sig < 1.5 ? 1 : 2, n_points, o,
+                                err) == SBD_OK
+                       ? SBD_OK
+                       : nufft_params(fit, half_extent, cx, cy, tol, fp32, kwin, swin, 2, n_points, o, err);
         err = "the frequency grid exceeds the FFT length (grid too small for this oversampling)";
         return SBD_ENOTSUP;
     }
@@ -781,6 +806,10 @@ int nufft_params(const SbdFit& fit, double half_extent, double cx, double cy, do
         for (int c = 0; c < fit.n_circles; ++c) o.circle_factor[c] = knode * knode;
         o.kmax = S * o.h * (1.0 + 1e-12);
         int rc = es_deconv_series(Ps, o.beta_s, o.kmax, o.psi, o.psi_max, err);
+        // automatic oversampling below 2 whose window series cannot be set up: 1.5, then 2
+        if (rc && sigma_mode == 0 && sig < 1.5 &&
+            nufft_params(fit, half_extent, cx, cy, tol, fp32, kwin, swin, 1, n_points, o, err) == SBD_OK)
+            return SBD_OK;
         if (rc && sigma_mode == 0 && sig != 2.0)
             return nufft_params(fit, half_extent, cx, cy, tol, fp32, kwin, swin, 2, n_points, o, err);
         if (rc) return rc;
@@ -853,6 +882,11 @@ int uniform_params(const SbdFit& fit, double half_extent, double cx, double cy, 
         o.nk = nk + (nk & 1);
     }
     if (o.nk > o.n) {
+        if (sigma_mode == 0 && sig != 2.0)
+            return uniform_params(fit, half_extent, cx, cy, tol, fp32, swin, sig < 1.5 ? 1 : 2, n_points, o, err) ==
+                           SBD_OK
+                       ? SBD_OK
+                       : uniform_params(fit, half_extent, cx, cy, tol, fp32, swin, 2, n_points, o, err);
         err = "uniform grid: the frequency window exceeds the FFT length";
         return SBD_ENOTSUP;
     }
@@ -868,6 +902,12 @@ int uniform_params(const SbdFit& fit, double half_extent, double cx, double cy, 
     if (swin == 1) {
         o.kmax = o.kcut * o.h * (1.0 + 1e-12);
         int rc = es_deconv_series(Ps, o.beta_s, o.kmax, o.psi, o.psi_max, err);
+        // as nufft_params: automatic oversampling falls back to 1.5, then 2
+        if (rc && sigma_mode == 0 && sig < 1.5 &&
+            uniform_params(fit, half_extent, cx, cy, tol, fp32, swin, 1, n_points, o, err) == SBD_OK)
+            return SBD_OK;
+        if (rc && sigma_mode == 0 && sig != 2.0)
+            return uniform_params(fit, half_extent, cx, cy, tol, fp32, swin, 2, n_points, o, err);
         if (rc) return rc;
     }
     // psi_w at the FFT positions: 1 - (integral of the ES bump over [0, (|t| - wa) / wtau]) / (its total)
@@ -1021,6 +1061,13 @@ int near_tables(const SbdFit& fit, NearTables& o, std::string& err, bool radial)
     for (int c = 0; c < fit.n_circles; ++c) g0 += fit.weight[c] * static_cast<double>(fit.M[c]);
     o.self_value = -g0;
     return SBD_OK;
+}
+
+void set_fit_device(int mode) { g_fit_device = mode; }
+int fit_device_mode() { return g_fit_device; }
+void last_factorisation(double* seconds, int* where) {
+    if (seconds) *seconds = g_last_seconds;
+    if (where) *where = g_last_where;
 }
 
 }  // namespace sbd

@@ -31,6 +31,20 @@ struct SbdFit {
     long long n_xi = 0;                  // sum M
 };
 
+// The Gram matrix of Eq. LinearSystem built and Cholesky-factored on the GPU (fit_gpu.cu):
+// packed receives the lower factor in the host's packed layout (row i at i (i + 1) / 2), *Pok
+// the number of leading rows factored (P, or the first non-positive pivot).
+int gram_cholesky_gpu(const std::vector<double>& rho, const std::vector<double>& C, const std::vector<double>& j0a,
+                      const std::vector<double>& j1a, double a, int P, std::vector<double>& packed, int* Pok,
+                      std::string& err);
+bool fit_gpu_available();
+// Where the fit's full Cholesky runs: 0 the device for P >= 3000 when one is present, else the
+// host; 1 always the host; 2 the device when present (sbd_set_fit_device).
+void set_fit_device(int mode);
+int fit_device_mode();
+// Seconds of the last full factorisation and where it ran (1 host, 2 device); for tests.
+void last_factorisation(double* seconds, int* where);
+
 // Key of the normalised-fit cache used by offline_fit (see offline.cpp).
 struct FitKey {
     int kind;

@@ -93,6 +93,8 @@ _SIGS = {
     "sbd_plan_balanced": ([_P, _I64, sbd_kernel, _D, _P, _I32, _I32, _I32, ctypes.POINTER(sbd_options), _P,
                            ctypes.POINTER(_P), _P, ctypes.POINTER(_I32)], ctypes.c_int),
     "sbd_fit_cache_clear": ([], ctypes.c_int),
+    "sbd_set_fit_device": ([_I32], ctypes.c_int),
+    "sbd_fit_last_factorisation": ([_P, _P], ctypes.c_int),
     "sbd_y0_root": ([_I32, _P], ctypes.c_int),
     "sbd_plan": ([_P, _I64, sbd_kernel, _D, _D, ctypes.POINTER(sbd_options), _P, ctypes.POINTER(_P)], ctypes.c_int),
     "sbd_plan_st": ([_P, _I64, _P, _I64, sbd_kernel, _D, _D, ctypes.POINTER(sbd_options), _P, ctypes.POINTER(_P)],
@@ -468,6 +470,18 @@ def sbd_y0_root(k: int) -> float:
 
 def sbd_fit_cache_clear() -> None:
     _check(lib.sbd_fit_cache_clear(), "sbd_fit_cache_clear")
+
+
+def sbd_set_fit_device(mode: int) -> None:
+    """Where the fit's full Cholesky runs: 0 auto (device for P >= 3000), 1 host, 2 device."""
+    _check(lib.sbd_set_fit_device(mode), "sbd_set_fit_device")
+
+
+def sbd_fit_last_factorisation() -> tuple[float, int]:
+    """(seconds, where) of the last full factorisation; where 0 none, 1 host, 2 device."""
+    sec, w = ctypes.c_double(), ctypes.c_int32()
+    _check(lib.sbd_fit_last_factorisation(ctypes.byref(sec), ctypes.byref(w)), "sbd_fit_last_factorisation")
+    return sec.value, w.value
 
 
 def sbd_fft2(x, out, n0: int, n1: int, sign: int, form: int, stream=None) -> None:

@@ -62,6 +62,30 @@ def test_argument_errors_without_gpu(S):
     assert e.value.code == S.SBD_EINVAL
 
 
+def test_fit_device_switch(S):
+    """sbd_set_fit_device takes modes 0-2; without a device the fit's full Cholesky runs on the host
+    in every mode (the device path is compared with the host one by the GPU tests)."""
+    torch = pytest.importorskip("torch")
+    for bad in (-1, 3):
+        with pytest.raises(S.SbdError) as e:
+            S.sbd_set_fit_device(bad)
+        assert e.value.code == S.SBD_EINVAL
+    try:
+        S.sbd_set_fit_device(1)
+        S.sbd_fit_cache_clear()
+        f = S.sbd_offline_fit(S.SBD_LAPLACE, 0.0, 0.01, 1.0, 1e-9)   # eps 1e-9: the full Cholesky
+        sec, where = S.sbd_fit_last_factorisation()
+        assert where == 1 and sec > 0 and f["P"] > 500
+        S.sbd_set_fit_device(2)
+        S.sbd_fit_cache_clear()
+        g = S.sbd_offline_fit(S.SBD_LAPLACE, 0.0, 0.01, 1.0, 1e-9)
+        assert S.sbd_fit_last_factorisation()[1] == (2 if torch.cuda.is_available() else 1)
+        assert g["P"] == f["P"]
+    finally:
+        S.sbd_set_fit_device(0)
+        S.sbd_fit_cache_clear()
+
+
 @pytest.mark.parametrize("eps", [1e-3, 1e-6, 1e-9])
 def test_host_fit_matches_oracle_laplace(S, eps):
     wl = W.laplace_disk(2000, 1, eps)
