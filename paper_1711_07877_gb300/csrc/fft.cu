@@ -171,17 +171,192 @@ __device__ __forceinline__ void small_dft(cx_t<T>* v, int sign) {
     }
 }
 
+// ---- roots of unity as compile-time constants ------------------------------------------
+// cos and sin of 2 pi j / R for the fixed twiddles inside a radix-R butterfly: Taylor series
+// on [0, pi/4) after reducing j / R to that octant in integer arithmetic, evaluated by the
+// compiler in double precision.
+__host__ __device__ constexpr double ct_sin(double x) {
+    double x2 = x * x, term = x, sum = x;
+    for (int k = 1; k <= 12; ++k) {
+        term *= -x2 / ((2.0 * k) * (2.0 * k + 1.0));
+        sum += term;
+    }
+    return sum;
+}
+__host__ __device__ constexpr double ct_cos(double x) {
+    double x2 = x * x, term = 1.0, sum = 1.0;
+    for (int k = 1; k <= 12; ++k) {
+        term *= -x2 / ((2.0 * k - 1.0) * (2.0 * k));
+        sum += term;
+    }
+    return sum;
+}
+struct CtRoot {
+    double c, s;
+};
+__host__ __device__ constexpr CtRoot ct_root(int j, int R) {
+    j %= R;
+    if (j < 0) j += R;
+    const int oct = 8 * j / R;
+    const int rem = 8 * j - oct * R;   // angle = 2 pi (oct R + rem) / (8 R)
+    const double th = 2.0 * 3.14159265358979323846 * rem / (8.0 * R);
+    const double ct = ct_cos(th), st = ct_sin(th);
+    const double h = 0.70710678118654752440;
+    const double cq = (ct - st) * h, sq = (ct + st) * h;   // angle + pi / 4
+    switch (oct) {
+        case 0: return {ct, st};
+        case 1: return {cq, sq};
+        case 2: return {-st, ct};
+        case 3: return {-sq, cq};
+        case 4: return {-ct, -st};
+        case 5: return {-cq, -sq};
+        case 6: return {st, -ct};
+        default: return {sq, -cq};
+    }
+}
+
+template <int I, int N, typename F>
+__device__ __forceinline__ void static_for(F&& f) {
+    if constexpr (I < N) {
+        f(std::integral_constant<int, I>{});
+        static_for<I + 1, N>(f);
+    }
+}
+
+// a exp(SIGN 2 pi i J / R), J and R fixed at compile time (quarter turns as swaps)
+template <typename T, int R, int J, int SIGN>
+__device__ __forceinline__ cx_t<T> mul_root(cx_t<T> a) {
+    constexpr int j = ((J % R) + R) % R;
+    if constexpr (j == 0) {
+        return a;
+    } else if constexpr (2 * j == R) {
+        return mk<T>(-a.x, -a.y);
+    } else if constexpr (4 * j == R) {
+        return mul_mi(a, SIGN);
+    } else if constexpr (4 * j == 3 * R) {
+        return mul_mi(a, -SIGN);
+    } else {
+        constexpr CtRoot w = ct_root(j, R);
+        constexpr T c = static_cast<T>(w.c), sn = static_cast<T>(SIGN * w.s);
+        return mk<T>(a.x * c - a.y * sn, a.x * sn + a.y * c);
+    }
+}
+
+// In-register DFT of length R = 2^a 3^b 5^c: v[k] = sum_n v[n] exp(SIGN 2 pi i n k / R).
+// Composite R = a b: with n = b n1 + n2 and k = k1 + a k2, b transforms of length a over
+// n1, the twiddles exp(SIGN 2 pi i n2 k1 / R), then a transforms of length b over n2.
+template <typename T, int R, int SIGN>
+__device__ __forceinline__ void dft(cx_t<T>* v) {
+    if constexpr (R == 2 || R == 3 || R == 4 || R == 5) {
+        small_dft<T, R>(v, SIGN);
+    } else {
+        constexpr int a = R % 4 == 0 ? 4 : R % 2 == 0 ? 2 : R % 3 == 0 ? 3 : 5;
+        constexpr int b = R / a;
+        cx_t<T> y[R];
+        static_for<0, b>([&](auto n2c) {
+            constexpr int n2 = decltype(n2c)::value;
+            cx_t<T> u[a];
+#pragma unroll
+            for (int n1 = 0; n1 < a; ++n1) u[n1] = v[b * n1 + n2];
+            small_dft<T, a>(u, SIGN);
+            static_for<0, a>([&](auto k1c) {
+                constexpr int k1 = decltype(k1c)::value;
+                y[n2 * a + k1] = mul_root<T, R, n2 * k1, SIGN>(u[k1]);
+            });
+        });
+#pragma unroll
+        for (int k1 = 0; k1 < a; ++k1) {
+            cx_t<T> u[b];
+#pragma unroll
+            for (int n2 = 0; n2 < b; ++n2) u[n2] = y[n2 * a + k1];
+            dft<T, b, SIGN>(u);
+#pragma unroll
+            for (int k2 = 0; k2 < b; ++k2) v[k1 + a * k2] = u[k2];
+        }
+    }
+}
+
+// Twiddles of one butterfly of a stage: w_j = W^{j t} (W = the row's root, conjugated for
+// SIGN = +1) for j = 1 .. R - 1.  The powers j in {1, 2, 3, 4, 8, 16} come from the table;
+// the others are products of those (at most three deep: j = 16 + 8 + 4 + 3), so that each
+// twiddle carries a few roundings at most.
+template <typename T>
+struct StageTw {
+    cx_t<T> p1, p2, p3, p4, p8, p16;
+};
+
+template <typename T, int SIGN, int R>
+__device__ __forceinline__ StageTw<T> stage_lookups(const cx_t<T>* __restrict__ tw, const cx_t<T>* tws, int t) {
+    StageTw<T> w;
+    auto get = [&](int j) {
+        cx_t<T> x = twid<T>(tw, tws, j * t);
+        if (SIGN > 0) x.y = -x.y;
+        return x;
+    };
+    w.p1 = get(1);
+    if constexpr (R > 2) w.p2 = get(2);
+    if constexpr (R > 3) w.p3 = get(3);
+    if constexpr (R > 4) w.p4 = get(4);
+    if constexpr (R > 8) w.p8 = get(8);
+    if constexpr (R > 16) w.p16 = get(16);
+    return w;
+}
+
+template <typename T, int J>
+__device__ __forceinline__ cx_t<T> tw_pow(const StageTw<T>& w) {
+    if constexpr (J == 1) return w.p1;
+    else if constexpr (J == 2) return w.p2;
+    else if constexpr (J == 3) return w.p3;
+    else if constexpr (J == 4) return w.p4;
+    else if constexpr (J == 8) return w.p8;
+    else if constexpr (J == 16) return w.p16;
+    else if constexpr (J > 16) return cmul(w.p16, tw_pow<T, J - 16>(w));
+    else if constexpr (J > 8) return cmul(w.p8, tw_pow<T, J - 8>(w));
+    else return cmul(w.p4, tw_pow<T, J - 4>(w));
+}
+
+template <typename T, int R>
+__device__ __forceinline__ void apply_stage_tw(cx_t<T>* v, const StageTw<T>& w) {
+    static_for<1, R>([&](auto jc) {
+        constexpr int j = decltype(jc)::value;
+        v[j] = cmul(v[j], tw_pow<T, j>(w));
+    });
+}
+
 template <typename T> struct MaxB;
 template <> struct MaxB<float>  { static constexpr int n_max = 28672; };
 template <> struct MaxB<double> { static constexpr int n_max = 14336; };
 
+// Radices of the in-register butterflies: prime powers up to 32 (FP32) or 16 (FP64, twice
+// the registers per element).  f(integral_constant<R>) for the runtime radix R.
+template <typename T, typename F>
+__device__ __forceinline__ void with_radix(int R, F&& f) {
+    switch (R) {
+        case 2: f(std::integral_constant<int, 2>{}); break;
+        case 3: f(std::integral_constant<int, 3>{}); break;
+        case 4: f(std::integral_constant<int, 4>{}); break;
+        case 5: f(std::integral_constant<int, 5>{}); break;
+        case 8: f(std::integral_constant<int, 8>{}); break;
+        case 9: f(std::integral_constant<int, 9>{}); break;
+        case 16: f(std::integral_constant<int, 16>{}); break;
+        default:
+            if constexpr (sizeof(T) == 4) {
+                if (R == 25) f(std::integral_constant<int, 25>{});
+                else if (R == 27) f(std::integral_constant<int, 27>{});
+                else f(std::integral_constant<int, 32>{});
+            }
+            break;
+    }
+}
+
 // Stage of the in-place mixed-radix decimation-in-time FFT: groups of L = Lp * R
 // elements combine R sub-transforms of length Lp (stored as consecutive blocks)
 // into one transform of length L, in place.  A thread keeps one offset k within
-// the sub-transforms (so its R - 1 twiddles are loaded once per stage) and walks
-// the groups g; no division per butterfly.
+// the sub-transforms (so its twiddles are looked up once per stage) and walks
+// the groups g; no division per butterfly.  The inverse transform (inv) runs the
+// forward butterfly on conjugated data: conj DFT(conj x) = the sum with exp(+...).
 template <typename T, int R>
-__device__ __forceinline__ void dit_stage(cx_t<T>* s, int n, int Lp, int sign, const cx_t<T>* __restrict__ tw,
+__device__ __forceinline__ void dit_stage(cx_t<T>* s, int n, int Lp, bool inv, const cx_t<T>* __restrict__ tw,
                                           const cx_t<T>* tws, int tw_scale, int nthreads) {
     using C = cx_t<T>;
     const int L = Lp * R;
@@ -200,25 +375,23 @@ __device__ __forceinline__ void dit_stage(cx_t<T>* s, int n, int Lp, int sign, c
         active = g0 < gstep;
     }
     for (; active && k < Lp; k += nthreads) {
-        C w[R];
-#pragma unroll
-        for (int r = 1; r < R; ++r) {
-            C t = twid<T>(tw, tws, r * k * tw_step);
-            if (sign > 0) t.y = -t.y;
-            w[r] = t;
-        }
+        StageTw<T> w{};
+        if (Lp > 1) w = stage_lookups<T, -1, R>(tw, tws, k * tw_step);
         for (int g = g0; g < G; g += gstep) {
             const int base = g * L + k;
             C v[R];
 #pragma unroll
-            for (int r = 0; r < R; ++r) v[r] = s[base + r * Lp];
-            if (Lp > 1) {
-#pragma unroll
-                for (int r = 1; r < R; ++r) v[r] = cmul(v[r], w[r]);
+            for (int r = 0; r < R; ++r) {
+                v[r] = s[base + r * Lp];
+                if (inv) v[r].y = -v[r].y;
             }
-            small_dft<T, R>(v, sign);
+            if (Lp > 1) apply_stage_tw<T, R>(v, w);
+            dft<T, R, -1>(v);
 #pragma unroll
-            for (int r = 0; r < R; ++r) s[base + r * Lp] = v[r];
+            for (int r = 0; r < R; ++r) {
+                if (inv) v[r].y = -v[r].y;
+                s[base + r * Lp] = v[r];
+            }
         }
     }
     __syncthreads();
@@ -227,7 +400,7 @@ __device__ __forceinline__ void dit_stage(cx_t<T>* s, int n, int Lp, int sign, c
 // The last stage (G = 1, so one butterfly per offset k), writing its outputs straight to
 // the destination through put(position in s, value) instead of back to shared memory.
 template <typename T, int R, typename Put>
-__device__ __forceinline__ void dit_stage_out(const cx_t<T>* s, int n, int Lp, int sign,
+__device__ __forceinline__ void dit_stage_out(const cx_t<T>* s, int n, int Lp, bool inv,
                                               const cx_t<T>* __restrict__ tw, const cx_t<T>* tws, int tw_scale,
                                               int nthreads, Put put) {
     using C = cx_t<T>;
@@ -235,16 +408,17 @@ __device__ __forceinline__ void dit_stage_out(const cx_t<T>* s, int n, int Lp, i
     for (int k = threadIdx.x; k < Lp; k += nthreads) {
         C v[R];
 #pragma unroll
-        for (int r = 0; r < R; ++r) v[r] = s[k + r * Lp];
-#pragma unroll
-        for (int r = 1; r < R; ++r) {
-            C t = twid<T>(tw, tws, r * k * tw_step);
-            if (sign > 0) t.y = -t.y;
-            v[r] = cmul(v[r], t);
+        for (int r = 0; r < R; ++r) {
+            v[r] = s[k + r * Lp];
+            if (inv) v[r].y = -v[r].y;
         }
-        small_dft<T, R>(v, sign);
+        if (Lp > 1) apply_stage_tw<T, R>(v, stage_lookups<T, -1, R>(tw, tws, k * tw_step));
+        dft<T, R, -1>(v);
 #pragma unroll
-        for (int r = 0; r < R; ++r) put(k + r * Lp, v[r]);
+        for (int r = 0; r < R; ++r) {
+            if (inv) v[r].y = -v[r].y;
+            put(k + r * Lp, v[r]);
+        }
     }
 }
 
@@ -296,18 +470,20 @@ __device__ __forceinline__ cx_t<T> load_elem(int io, int idx, int n, const cx_t<
     return v;
 }
 
-// SIGN (-1 forward, +1 inverse) is a template argument: the factors +-i of the butterflies
-// and the conjugation of the twiddles fold into the arithmetic.
-template <typename T, int NT, int SIGN>
-__global__ void __launch_bounds__(NT) fft_rows_kernel(
+// One kernel per precision: the direction (sign) is a run-time argument (inverse =
+// conjugated forward butterflies) and the CTA size blockDim.x (256 or 512), which keeps
+// the number of instantiated butterflies, and the build time, small.
+template <typename T>
+__global__ void __launch_bounds__(512) fft_rows_kernel(
     const cx_t<T>* __restrict__ in, long in_stride, int in_len, int in_shift,
     cx_t<T>* __restrict__ out, long out_stride, int out_len, int out_shift,
     int n, int Q, FftPlan1D plan, const cx_t<T>* __restrict__ tw, const int* __restrict__ perm,
     const T* __restrict__ pre_elem, const T* __restrict__ pre_row,
     const T* __restrict__ post_elem, const T* __restrict__ post_row, HermFold<T> hf, int io,
-    const cx_t<T>* __restrict__ tw2, long in_batch, long out_batch) {
+    const cx_t<T>* __restrict__ tw2, long in_batch, long out_batch, int sign) {
     using C = cx_t<T>;
-    constexpr int sign = SIGN;
+    const int NT = blockDim.x;
+    const bool inv = sign > 0;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* s = reinterpret_cast<C*>(smem_raw);
     // blockIdx.z: grid of a batch of equal grids (right-hand sides), in_batch / out_batch apart
@@ -331,48 +507,27 @@ __global__ void __launch_bounds__(NT) fft_rows_kernel(
         rs0 = pre_row[io == kIoPairFwd ? 2 * row : row];
         rs1 = pre_row[io == kIoPairFwd ? 2 * row + 1 : row];
     }
-    // element i of the length-nq transform: the Q phases folded and twisted
-    auto fetch = [&](int i) -> C {
+    // load pass: element i of the length-nq transform (the Q phases folded and twisted) goes
+    // to its digit-reversed position; consecutive threads read consecutive inputs
+    for (int i = threadIdx.x; i < nq; i += NT) {
         C acc = mk<T>(0, 0);
         for (int j = 0; j < Q; ++j) {
             const int idx = i + j * nq;               // FFT index
             bool has;
             C v = load_elem<T>(io, idx, n, src, in_stride, in_len, in_shift, row, hf, rs0, rs1, pre_elem, has);
             if (has) {
-                if (r) {                              // twist w_n^{idx}
+                if (r) {                              // twist w_n^{+-idx}
                     C w = twid<T>(tw, tws, idx);
-                    if (sign > 0) w.y = -w.y;
+                    if (inv) w.y = -w.y;
                     v = cmul(v, w);
                 }
                 acc = cadd(acc, v);
             }
         }
-        return acc;
-    };
-    // first radix stage straight from the input: in the digit-reversed order the group g of
-    // stage one (shared positions g R1 + q) holds input elements t + G1 q, where t is the
-    // index with perm[t] = g R1; threads take consecutive t, so each of their R1 reads is
-    // coalesced, and the stage's butterflies run before anything is stored
-    const int R1 = plan.radix[0];
-    auto first_stage = [&](auto radix) {
-        constexpr int R = decltype(radix)::value;
-        const int G1 = nq / R;
-        for (int t = threadIdx.x; t < G1; t += NT) {
-            const int base = perm[t];                 // = g R
-            C v[R];
-#pragma unroll
-            for (int q = 0; q < R; ++q) v[q] = fetch(t + G1 * q);
-            small_dft<T, R>(v, sign);
-#pragma unroll
-            for (int q = 0; q < R; ++q) s[base + q] = v[q];
-        }
-    };
-    if (R1 == 5) first_stage(std::integral_constant<int, 5>{});
-    else if (R1 == 4) first_stage(std::integral_constant<int, 4>{});
-    else if (R1 == 3) first_stage(std::integral_constant<int, 3>{});
-    else first_stage(std::integral_constant<int, 2>{});
+        s[perm[i]] = acc;
+    }
     __syncthreads();
-    int Lp = R1;
+    int Lp = 1;
     // output scaling of the direct store (plain and pair-inverse rows)
     T ps0 = static_cast<T>(1), ps1 = static_cast<T>(1);
     if (post_row) {
@@ -393,58 +548,42 @@ __global__ void __launch_bounds__(NT) fft_rows_kernel(
             dst[e] = v;
         }
     };
-    for (int st = 1; st < plan.nstages; ++st) {
+    for (int st = 0; st < plan.nstages; ++st) {
         const int R = plan.radix[st];
         if (st == plan.nstages - 1 && io != kIoPairFwd) {
             // last stage: outputs go straight to global memory (uniform branch, no barrier after)
-            if (R == 4)      dit_stage_out<T, 4>(s, nq, Lp, sign, tw, tws, Q, NT, put);
-            else if (R == 2) dit_stage_out<T, 2>(s, nq, Lp, sign, tw, tws, Q, NT, put);
-            else if (R == 3) dit_stage_out<T, 3>(s, nq, Lp, sign, tw, tws, Q, NT, put);
-            else             dit_stage_out<T, 5>(s, nq, Lp, sign, tw, tws, Q, NT, put);
+            with_radix<T>(R, [&](auto rc) {
+                dit_stage_out<T, decltype(rc)::value>(s, nq, Lp, inv, tw, tws, Q, NT, put);
+            });
             return;
         }
-        if (R == 4)      dit_stage<T, 4>(s, nq, Lp, sign, tw, tws, Q, NT);
-        else if (R == 2) dit_stage<T, 2>(s, nq, Lp, sign, tw, tws, Q, NT);
-        else if (R == 3) dit_stage<T, 3>(s, nq, Lp, sign, tw, tws, Q, NT);
-        else             dit_stage<T, 5>(s, nq, Lp, sign, tw, tws, Q, NT);
+        with_radix<T>(R, [&](auto rc) { dit_stage<T, decltype(rc)::value>(s, nq, Lp, inv, tw, tws, Q, NT); });
         Lp *= R;
     }
-    if (io == kIoPairFwd) {
-        // s = Z^ of z = x0 + i x1 (two real rows): X0(k) = (Z(k) + conj Z(-k)) / 2,
-        // X1(k) = (Z(k) - conj Z(-k)) / 2i, written to grid rows 2 row and 2 row + 1
-        C* d0 = out + 2 * row * out_stride;
-        C* d1 = d0 + out_stride;
-        for (int e = threadIdx.x; e < out_len; e += NT) {
-            int k = e + out_shift;
-            if (k >= n) k -= n;
-            if (Q == 2 && (k & 1) != r) continue;
-            const int km = k == 0 ? 0 : n - k;        // same parity as k (n even)
-            const C zk = s[Q == 2 ? (k >> 1) : k], zm = s[Q == 2 ? (km >> 1) : km];
-            const T h = static_cast<T>(0.5);
-            const T pe = post_elem ? post_elem[e] : static_cast<T>(1);
-            d0[e] = mk<T>(h * pe * (zk.x + zm.x), h * pe * (zk.y - zm.y));
-            d1[e] = mk<T>(h * pe * (zk.y + zm.y), h * pe * (zm.x - zk.x));
-        }
-        return;
-    }
-    for (int e = threadIdx.x; e < out_len; e += NT) {       // single-stage rows only
+    // kIoPairFwd: s = Z^ of z = x0 + i x1 (two real rows): X0(k) = (Z(k) + conj Z(-k)) / 2,
+    // X1(k) = (Z(k) - conj Z(-k)) / 2i, written to grid rows 2 row and 2 row + 1
+    C* d0 = out + 2 * row * out_stride;
+    C* d1 = d0 + out_stride;
+    for (int e = threadIdx.x; e < out_len; e += NT) {
         int k = e + out_shift;
         if (k >= n) k -= n;
         if (Q == 2 && (k & 1) != r) continue;
-        C v = s[Q == 2 ? (k >> 1) : k];
+        const int km = k == 0 ? 0 : n - k;        // same parity as k (n even)
+        const C zk = s[Q == 2 ? (k >> 1) : k], zm = s[Q == 2 ? (km >> 1) : km];
+        const T h = static_cast<T>(0.5);
         const T pe = post_elem ? post_elem[e] : static_cast<T>(1);
-        v.x *= ps0 * pe;
-        v.y *= ps1 * pe;
-        dst[e] = v;
+        d0[e] = mk<T>(h * pe * (zk.x + zm.x), h * pe * (zk.y - zm.y));
+        d1[e] = mk<T>(h * pe * (zk.y + zm.y), h * pe * (zm.x - zk.x));
     }
 }
 
 // Digit-reversal permutation of the decimation-in-time schedule: with radices
 // R_1..R_s applied in that order, index i = sum of digits (least significant digit in
 // base R_s, then R_{s-1}, ...) lands at position sum_k d_k R_1...R_{k-1}.
-const int* digit_perm(const FftPlan1D& plan, cudaStream_t stream) {
+const int* digit_perm(const FftPlan1D& plan, bool fp64, cudaStream_t stream) {
     static TableCache<int> cache;
-    if (const int* d = cache.find(plan.n)) return d;
+    const int key = 2 * plan.n + (fp64 ? 1 : 0);     // the schedule depends on the precision
+    if (const int* d = cache.find(key)) return d;
     const int n = plan.n;
     std::vector<int> h(n);
     std::vector<int> weight(plan.nstages);
@@ -459,7 +598,7 @@ const int* digit_perm(const FftPlan1D& plan, cudaStream_t stream) {
         }
         h[i] = pos;
     }
-    return cache.upload(n, h, stream);
+    return cache.upload(key, h, stream);
 }
 
 template <typename T>
@@ -484,26 +623,39 @@ __global__ void transpose_kernel(const cx_t<T>* __restrict__ in, long in_stride,
 
 }  // namespace
 
-bool fft_make_plan(int n, FftPlan1D& p) {
-    // Odd radices first and the powers of two last: the early stages, whose accesses
-    // are strided by the radix, then use odd strides (distinct shared-memory banks), and
-    // with a single power-of-two stage of radix R at the end, consecutive digit-reversed
-    // load positions are n / R apart, which is odd when n has at most two factors of 2
-    // beyond that radix.
+bool fft_make_plan(int n, FftPlan1D& p, bool fp64) {
+    // Few stages of large radices: n = 2^a 3^b 5^c split into prime-power chunks of at most
+    // 32 (FP32; 16 for FP64), each an in-register butterfly, the exponents of a prime spread
+    // evenly over its chunks.  Odd radices first and the powers of two last: the early
+    // stages, whose accesses are strided by the radix, then use odd strides (distinct
+    // shared-memory banks), and the last stage, one butterfly per offset, writes
+    // consecutive positions.
     p.n = n;
     p.nstages = 0;
-    int v = n;
-    int twos = 0;
-    while (v % 2 == 0) { v /= 2; ++twos; }
+    if (n < 2) return false;
+    int v = n, e2 = 0, e3 = 0, e5 = 0;
+    while (v % 2 == 0) { v /= 2; ++e2; }
+    while (v % 3 == 0) { v /= 3; ++e3; }
+    while (v % 5 == 0) { v /= 5; ++e5; }
+    if (v != 1) return false;
     std::vector<int> rs;
-    while (v % 5 == 0) { v /= 5; rs.push_back(5); }
-    while (v % 3 == 0) { v /= 3; rs.push_back(3); }
-    if (twos & 1) rs.push_back(2);
-    while (twos >= 2) { rs.push_back(4); twos -= 2; }
-    if (v != 1 || static_cast<int>(rs.size()) > kFftMaxStages) return false;
+    auto chunks = [&](int prime, int e, int emax) {
+        if (e == 0) return;
+        const int parts = (e + emax - 1) / emax;
+        for (int i = 0; i < parts; ++i) {
+            const int ei = e / parts + (i < e % parts ? 1 : 0);
+            int r = 1;
+            for (int j = 0; j < ei; ++j) r *= prime;
+            rs.push_back(r);
+        }
+    };
+    chunks(5, e5, fp64 ? 1 : 2);
+    chunks(3, e3, 2 + (fp64 ? 0 : 1));
+    chunks(2, e2, fp64 ? 4 : 5);
+    if (static_cast<int>(rs.size()) > kFftMaxStages) return false;
     for (size_t i = 0; i < rs.size(); ++i) p.radix[i] = rs[i];
     p.nstages = static_cast<int>(rs.size());
-    p.threads = 1024;
+    p.threads = 512;
     return true;
 }
 
@@ -524,18 +676,12 @@ static int fft_phases(int n, bool fp64) {
 
 int fft_max_length(bool fp64) { return 2 * fft_max_row(fp64); }
 
-// Launches fft_rows_kernel<T, NT, sign> with the given arguments (sign -1 or +1).
-template <typename T, int NT, typename... A>
-int launch_fft_rows(int sign, dim3 grid, size_t smem, cudaStream_t stream, A... args) {
-    if (sign < 0) {
-        auto k = fft_rows_kernel<T, NT, -1>;
-        SBD_TRY(raise_smem_limit(k, smem));
-        k<<<grid, NT, smem, stream>>>(args...);
-    } else {
-        auto k = fft_rows_kernel<T, NT, 1>;
-        SBD_TRY(raise_smem_limit(k, smem));
-        k<<<grid, NT, smem, stream>>>(args...);
-    }
+// Launches fft_rows_kernel<T> with nt threads per CTA.
+template <typename T, typename... A>
+int launch_fft_rows(int nt, dim3 grid, size_t smem, cudaStream_t stream, A... args) {
+    auto k = fft_rows_kernel<T>;
+    SBD_TRY(raise_smem_limit(k, smem));
+    k<<<grid, nt, smem, stream>>>(args...);
     SBD_LAUNCH_CHECK();
     return SBD_OK;
 }
@@ -564,12 +710,12 @@ int fft_rows(const cx_t<T>* in, long in_stride, int in_len, int in_shift,
     const int Q = split == 2 && n % 2 == 0 ? 2 : fft_phases(n, fp64);
     const int nq = n / Q;
     FftPlan1D plan;
-    if (!fft_make_plan(nq, plan) || nq > fft_max_row(fp64) || n % Q) {
+    if (!fft_make_plan(nq, plan, fp64) || nq > fft_max_row(fp64) || n % Q) {
         set_error("FFT length not supported: " + std::to_string(n));
         return SBD_ENOTSUP;
     }
     const cx_t<T>* tw = twiddles<T>(n, stream);
-    const int* perm = digit_perm(plan, stream);
+    const int* perm = digit_perm(plan, fp64, stream);
     if (!tw || !perm) {
         set_error("FFT table allocation failed");
         return SBD_ENOMEM;
@@ -592,22 +738,11 @@ int fft_rows(const cx_t<T>* in, long in_stride, int in_len, int in_shift,
         const T* por = post_row ? post_row + r0 * (io == kIoPairInv ? 2 : 1) : nullptr;
         const HermFold<T> hf{in - static_cast<long>(herm_row0) * in_stride, herm_n,
                              static_cast<long>(herm_row0) + r0};
-        int rc;
-        if (nq > 2048 && split == 2) {
-            // half-length phases: two CTAs of 512 threads share an SM (registers and shared
-            // memory both allow it), instead of one 1024-thread CTA per full-length row
-            rc = launch_fft_rows<T, 512>(sign, grid, smem, stream, ip, in_stride, in_len, in_shift, op, out_stride,
-                                         out_len, out_shift, n, Q, plan, tw, perm, pre_elem, prr, post_elem, por, hf,
-                                         io, tw2, in_batch, out_batch);
-        } else if (nq > 2048) {
-            rc = launch_fft_rows<T, 1024>(sign, grid, smem, stream, ip, in_stride, in_len, in_shift, op, out_stride,
-                                          out_len, out_shift, n, Q, plan, tw, perm, pre_elem, prr, post_elem, por, hf,
-                                          io, tw2, in_batch, out_batch);
-        } else {
-            rc = launch_fft_rows<T, 256>(sign, grid, smem, stream, ip, in_stride, in_len, in_shift, op, out_stride,
-                                         out_len, out_shift, n, Q, plan, tw, perm, pre_elem, prr, post_elem, por, hf,
-                                         io, tw2, in_batch, out_batch);
-        }
+        // 512 threads for long rows (the in-register butterflies of up to 32 elements take up to
+        // 128 registers a thread); half-length phases (split) fit more CTAs per SM
+        const int rc = launch_fft_rows<T>(nq > 2048 ? 512 : 256, grid, smem, stream, ip, in_stride, in_len, in_shift,
+                                          op, out_stride, out_len, out_shift, n, Q, plan, tw, perm, pre_elem, prr,
+                                          post_elem, por, hf, io, tw2, in_batch, out_batch, sign);
         if (rc) return rc;
     }
     SBD_LAUNCH_CHECK();
@@ -619,7 +754,7 @@ int fft_rows_tables(const cx_t<T>* in, long in_stride, int in_len, cx_t<T>* out,
                     int rows, int n, int sign, const cx_t<T>* tw, const int* perm, cudaStream_t stream) {
     if (rows <= 0) return SBD_OK;
     FftPlan1D plan;
-    if (!fft_make_plan(n, plan) || n > fft_max_row(sizeof(T) == 8)) {
+    if (!fft_make_plan(n, plan, sizeof(T) == 8) || n > fft_max_row(sizeof(T) == 8)) {
         set_error("FFT length not supported: " + std::to_string(n));
         return SBD_ENOTSUP;
     }
@@ -630,17 +765,10 @@ int fft_rows_tables(const cx_t<T>* in, long in_stride, int in_len, cx_t<T>* out,
         const cx_t<T>* ip = in + static_cast<long>(r0) * in_stride;
         cx_t<T>* op = out + static_cast<long>(r0) * out_stride;
         const T* none = nullptr;
-        int rc;
-        if (n > 2048)
-            rc = launch_fft_rows<T, 1024>(sign, grid, smem, stream, ip, in_stride, in_len, 0, op, out_stride, out_len,
-                                          0, n, 1, plan, tw, perm, none, none, none, none,
+        const int rc = launch_fft_rows<T>(n > 2048 ? 512 : 256, grid, smem, stream, ip, in_stride, in_len, 0, op,
+                                          out_stride, out_len, 0, n, 1, plan, tw, perm, none, none, none, none,
                                           HermFold<T>{nullptr, 0, 0}, static_cast<int>(kIoPlain),
-                                          static_cast<const cx_t<T>*>(nullptr), 0L, 0L);
-        else
-            rc = launch_fft_rows<T, 256>(sign, grid, smem, stream, ip, in_stride, in_len, 0, op, out_stride, out_len,
-                                         0, n, 1, plan, tw, perm, none, none, none, none,
-                                         HermFold<T>{nullptr, 0, 0}, static_cast<int>(kIoPlain),
-                                         static_cast<const cx_t<T>*>(nullptr), 0L, 0L);
+                                          static_cast<const cx_t<T>*>(nullptr), 0L, 0L, sign);
         if (rc) return rc;
     }
     return SBD_OK;

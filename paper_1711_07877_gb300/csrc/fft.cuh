@@ -16,8 +16,9 @@ struct FftPlan1D {
     int threads = 0;
 };
 
-// Radix schedule for n = 2^a 3^b 5^c (fours first); false when n has another factor.
-bool fft_make_plan(int n, FftPlan1D& p);
+// Radix schedule for n = 2^a 3^b 5^c (prime-power radices up to 32, or 16 for FP64, odd
+// ones first); false when n has another factor.
+bool fft_make_plan(int n, FftPlan1D& p, bool fp64);
 
 // Largest row length a single CTA can hold in shared memory for this element type.
 int fft_max_row(bool fp64);

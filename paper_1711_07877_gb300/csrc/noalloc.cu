@@ -83,7 +83,7 @@ int run(const void* in, void* out, int n0, int n1, int sign, cudaStream_t s) {
     C* tw0 = reinterpret_cast<C*>(base + kDataBytes + kTableBytes);
     int* perm0 = reinterpret_cast<int*>(base + kDataBytes + kTableBytes + static_cast<size_t>(kMaxSide) * 16);
     FftPlan1D p0, p1;
-    if (!fft_make_plan(n0, p0) || !fft_make_plan(n1, p1)) {
+    if (!fft_make_plan(n0, p0, sizeof(T) == 8) || !fft_make_plan(n1, p1, sizeof(T) == 8)) {
         set_error("sbd_fft2_noalloc: sides must be products of 2, 3 and 5");
         return SBD_ENOTSUP;
     }
