@@ -64,6 +64,8 @@ def matvec(S, p, f, n, nrhs=1, fn=None):
 @pytest.mark.parametrize("form", [0, 1])
 @pytest.mark.parametrize("sign", [-1, 1])
 def test_fft2_matches_numpy(S, shape, form, sign):
+    if form == 0 and max(shape) > 28672:
+        pytest.skip("FP64 rows hold at most 2 x 14336 points")
     rng = np.random.default_rng(sum(shape) + form)
     x = rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
     want = np.fft.fft2(x) if sign < 0 else np.fft.ifft2(x) * x.size
