@@ -84,6 +84,13 @@ struct TableCache {
 constexpr int kTwLo = 128;
 inline int tw2_size(int n) { return kTwLo + (n + kTwLo - 1) / kTwLo; }
 
+// Shared-memory position of row element a: one spare slot after every 16 elements.  The
+// load pass stores consecutive inputs nq / R_last apart (digit reversal), a multiple of
+// 16 elements for most rows, which without the spare slots puts a half-warp's stores in
+// one bank; with them the stride is odd modulo 16 (conflict-free for 8- and 16-byte elements).
+__host__ __device__ __forceinline__ int spad(int a) { return a + (a >> 4); }
+inline int padded_len(int n) { return n + (n >> 4) + 1; }
+
 template <typename T>
 const cx_t<T>* twiddles2(int n, cudaStream_t stream) {
     static TableCache<cx_t<T>> cache;
@@ -327,8 +334,9 @@ template <typename T> struct MaxB;
 template <> struct MaxB<float>  { static constexpr int n_max = 28672; };
 template <> struct MaxB<double> { static constexpr int n_max = 14336; };
 
-// Radices of the in-register butterflies: prime powers up to 32 (FP32) or 16 (FP64, twice
-// the registers per element).  f(integral_constant<R>) for the runtime radix R.
+// Radices of the in-register butterflies: prime powers up to 16 (FP32) or 9 (FP64, twice
+// the registers per element), which fit the 80 registers of three CTAs per SM.
+// f(integral_constant<R>) for the runtime radix R.
 template <typename T, typename F>
 __device__ __forceinline__ void with_radix(int R, F&& f) {
     switch (R) {
@@ -337,13 +345,12 @@ __device__ __forceinline__ void with_radix(int R, F&& f) {
         case 4: f(std::integral_constant<int, 4>{}); break;
         case 5: f(std::integral_constant<int, 5>{}); break;
         case 8: f(std::integral_constant<int, 8>{}); break;
-        case 9: f(std::integral_constant<int, 9>{}); break;
-        case 16: f(std::integral_constant<int, 16>{}); break;
         default:
             if constexpr (sizeof(T) == 4) {
-                if (R == 25) f(std::integral_constant<int, 25>{});
-                else if (R == 27) f(std::integral_constant<int, 27>{});
-                else f(std::integral_constant<int, 32>{});
+                if (R == 16) f(std::integral_constant<int, 16>{});
+                else f(std::integral_constant<int, 9>{});
+            } else {
+                f(std::integral_constant<int, 9>{});
             }
             break;
     }
@@ -382,7 +389,7 @@ __device__ __forceinline__ void dit_stage(cx_t<T>* s, int n, int Lp, bool inv, c
             C v[R];
 #pragma unroll
             for (int r = 0; r < R; ++r) {
-                v[r] = s[base + r * Lp];
+                v[r] = s[spad(base + r * Lp)];
                 if (inv) v[r].y = -v[r].y;
             }
             if (Lp > 1) apply_stage_tw<T, R>(v, w);
@@ -390,7 +397,7 @@ __device__ __forceinline__ void dit_stage(cx_t<T>* s, int n, int Lp, bool inv, c
 #pragma unroll
             for (int r = 0; r < R; ++r) {
                 if (inv) v[r].y = -v[r].y;
-                s[base + r * Lp] = v[r];
+                s[spad(base + r * Lp)] = v[r];
             }
         }
     }
@@ -409,7 +416,7 @@ __device__ __forceinline__ void dit_stage_out(const cx_t<T>* s, int n, int Lp, b
         C v[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-            v[r] = s[k + r * Lp];
+            v[r] = s[spad(k + r * Lp)];
             if (inv) v[r].y = -v[r].y;
         }
         if (Lp > 1) apply_stage_tw<T, R>(v, stage_lookups<T, -1, R>(tw, tws, k * tw_step));
@@ -471,10 +478,13 @@ __device__ __forceinline__ cx_t<T> load_elem(int io, int idx, int n, const cx_t<
 }
 
 // One kernel per precision: the direction (sign) is a run-time argument (inverse =
-// conjugated forward butterflies) and the CTA size blockDim.x (256 or 512), which keeps
-// the number of instantiated butterflies, and the build time, small.
+// conjugated forward butterflies), which keeps the number of instantiated butterflies, and
+// the build time, small.  256 threads and at most 80 registers a thread (launch bounds for
+// three CTAs per SM): three 6912-point rows share an SM, so that one row's loads overlap
+// the others' butterflies.
+constexpr int kFftThreads = 256;
 template <typename T>
-__global__ void __launch_bounds__(512) fft_rows_kernel(
+__global__ void __launch_bounds__(kFftThreads, 3) fft_rows_kernel(
     const cx_t<T>* __restrict__ in, long in_stride, int in_len, int in_shift,
     cx_t<T>* __restrict__ out, long out_stride, int out_len, int out_shift,
     int n, int Q, FftPlan1D plan, const cx_t<T>* __restrict__ tw, const int* __restrict__ perm,
@@ -496,7 +506,7 @@ __global__ void __launch_bounds__(512) fft_rows_kernel(
     // two-level twiddle table (if given) in shared memory after the row
     C* tws = nullptr;
     if (tw2) {
-        tws = s + nq;
+        tws = s + nq + (nq >> 4) + 1;              // after the padded row
         const int ntw = kTwLo + (n + kTwLo - 1) / kTwLo;
         for (int i = threadIdx.x; i < ntw; i += NT) tws[i] = tw2[i];
         __syncthreads();
@@ -509,6 +519,7 @@ __global__ void __launch_bounds__(512) fft_rows_kernel(
     }
     // load pass: element i of the length-nq transform (the Q phases folded and twisted) goes
     // to its digit-reversed position; consecutive threads read consecutive inputs
+#pragma unroll 4
     for (int i = threadIdx.x; i < nq; i += NT) {
         C acc = mk<T>(0, 0);
         for (int j = 0; j < Q; ++j) {
@@ -524,7 +535,7 @@ __global__ void __launch_bounds__(512) fft_rows_kernel(
                 acc = cadd(acc, v);
             }
         }
-        s[perm[i]] = acc;
+        s[spad(perm[i])] = acc;
     }
     __syncthreads();
     int Lp = 1;
@@ -569,7 +580,7 @@ __global__ void __launch_bounds__(512) fft_rows_kernel(
         if (k >= n) k -= n;
         if (Q == 2 && (k & 1) != r) continue;
         const int km = k == 0 ? 0 : n - k;        // same parity as k (n even)
-        const C zk = s[Q == 2 ? (k >> 1) : k], zm = s[Q == 2 ? (km >> 1) : km];
+        const C zk = s[spad(Q == 2 ? (k >> 1) : k)], zm = s[spad(Q == 2 ? (km >> 1) : km)];
         const T h = static_cast<T>(0.5);
         const T pe = post_elem ? post_elem[e] : static_cast<T>(1);
         d0[e] = mk<T>(h * pe * (zk.x + zm.x), h * pe * (zk.y - zm.y));
@@ -624,8 +635,8 @@ __global__ void transpose_kernel(const cx_t<T>* __restrict__ in, long in_stride,
 }  // namespace
 
 bool fft_make_plan(int n, FftPlan1D& p, bool fp64) {
-    // Few stages of large radices: n = 2^a 3^b 5^c split into prime-power chunks of at most
-    // 32 (FP32; 16 for FP64), each an in-register butterfly, the exponents of a prime spread
+    // Few stages of large radices: n = 2^a 3^b 5^c split into prime-power chunks (FP32: 16,
+    // 9, 5; FP64: 8, 9, 5), each an in-register butterfly, the exponents of a prime spread
     // evenly over its chunks.  Odd radices first and the powers of two last: the early
     // stages, whose accesses are strided by the radix, then use odd strides (distinct
     // shared-memory banks), and the last stage, one butterfly per offset, writes
@@ -649,19 +660,19 @@ bool fft_make_plan(int n, FftPlan1D& p, bool fp64) {
             rs.push_back(r);
         }
     };
-    chunks(5, e5, fp64 ? 1 : 2);
-    chunks(3, e3, 2 + (fp64 ? 0 : 1));
-    chunks(2, e2, fp64 ? 4 : 5);
+    chunks(5, e5, 1);
+    chunks(3, e3, 2);
+    chunks(2, e2, fp64 ? 3 : 4);
     if (static_cast<int>(rs.size()) > kFftMaxStages) return false;
     for (size_t i = 0; i < rs.size(); ++i) p.radix[i] = rs[i];
     p.nstages = static_cast<int>(rs.size());
-    p.threads = 512;
+    p.threads = kFftThreads;
     return true;
 }
 
 int fft_max_row(bool fp64) {
     const int smem = 227 * 1024;
-    const int lim = smem / (fp64 ? 16 : 8);
+    const int lim = (smem / (fp64 ? 16 : 8)) * 16 / 17 - 1;          // the padded row fits
     return fp64 ? std::min(lim, MaxB<double>::n_max) : std::min(lim, MaxB<float>::n_max);
 }
 
@@ -681,6 +692,12 @@ template <typename T, typename... A>
 int launch_fft_rows(int nt, dim3 grid, size_t smem, cudaStream_t stream, A... args) {
     auto k = fft_rows_kernel<T>;
     SBD_TRY(raise_smem_limit(k, smem));
+    static const bool carve = [&] {   // all of the SM's unified memory as shared memory
+        cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        cudaGetLastError();
+        return true;
+    }();
+    (void)carve;
     k<<<grid, nt, smem, stream>>>(args...);
     SBD_LAUNCH_CHECK();
     return SBD_OK;
@@ -721,7 +738,7 @@ int fft_rows(const cx_t<T>* in, long in_stride, int in_len, int in_shift,
         return SBD_ENOMEM;
     }
     // the two-level twiddle table rides in shared memory when it fits beside the row
-    const size_t row_bytes = sizeof(cx_t<T>) * static_cast<size_t>(nq);
+    const size_t row_bytes = sizeof(cx_t<T>) * static_cast<size_t>(padded_len(nq));
     const size_t tw2_bytes = sizeof(cx_t<T>) * static_cast<size_t>(tw2_size(n));
     const cx_t<T>* tw2 = row_bytes + tw2_bytes <= 227u * 1024u ? twiddles2<T>(n, stream) : nullptr;
     const size_t smem = row_bytes + (tw2 ? tw2_bytes : 0);
@@ -738,9 +755,8 @@ int fft_rows(const cx_t<T>* in, long in_stride, int in_len, int in_shift,
         const T* por = post_row ? post_row + r0 * (io == kIoPairInv ? 2 : 1) : nullptr;
         const HermFold<T> hf{in - static_cast<long>(herm_row0) * in_stride, herm_n,
                              static_cast<long>(herm_row0) + r0};
-        // 512 threads for long rows (the in-register butterflies of up to 32 elements take up to
-        // 128 registers a thread); half-length phases (split) fit more CTAs per SM
-        const int rc = launch_fft_rows<T>(nq > 2048 ? 512 : 256, grid, smem, stream, ip, in_stride, in_len, in_shift,
+        // half-length phases (split) fit more CTAs per SM
+        const int rc = launch_fft_rows<T>(kFftThreads, grid, smem, stream, ip, in_stride, in_len, in_shift,
                                           op, out_stride, out_len, out_shift, n, Q, plan, tw, perm, pre_elem, prr,
                                           post_elem, por, hf, io, tw2, in_batch, out_batch, sign);
         if (rc) return rc;
@@ -758,14 +774,14 @@ int fft_rows_tables(const cx_t<T>* in, long in_stride, int in_len, cx_t<T>* out,
         set_error("FFT length not supported: " + std::to_string(n));
         return SBD_ENOTSUP;
     }
-    const size_t smem = sizeof(cx_t<T>) * static_cast<size_t>(n);
+    const size_t smem = sizeof(cx_t<T>) * static_cast<size_t>(padded_len(n));
     for (int r0 = 0; r0 < rows; r0 += 65535) {
         const int nr = std::min(65535, rows - r0);
         const dim3 grid(1u, static_cast<unsigned>(nr));
         const cx_t<T>* ip = in + static_cast<long>(r0) * in_stride;
         cx_t<T>* op = out + static_cast<long>(r0) * out_stride;
         const T* none = nullptr;
-        const int rc = launch_fft_rows<T>(n > 2048 ? 512 : 256, grid, smem, stream, ip, in_stride, in_len, 0, op,
+        const int rc = launch_fft_rows<T>(kFftThreads, grid, smem, stream, ip, in_stride, in_len, 0, op,
                                           out_stride, out_len, 0, n, 1, plan, tw, perm, none, none, none, none,
                                           HermFold<T>{nullptr, 0, 0}, static_cast<int>(kIoPlain),
                                           static_cast<const cx_t<T>*>(nullptr), 0L, 0L, sign);
