@@ -360,10 +360,9 @@ __device__ __forceinline__ void with_radix(int R, F&& f) {
 // elements combine R sub-transforms of length Lp (stored as consecutive blocks)
 // into one transform of length L, in place.  A thread keeps one offset k within
 // the sub-transforms (so its twiddles are looked up once per stage) and walks
-// the groups g; no division per butterfly.  The inverse transform (inv) runs the
-// forward butterfly on conjugated data: conj DFT(conj x) = the sum with exp(+...).
-template <typename T, int R>
-__device__ __forceinline__ void dit_stage(cx_t<T>* s, int n, int Lp, bool inv, const cx_t<T>* __restrict__ tw,
+// the groups g; no division per butterfly.
+template <typename T, int R, int SIGN>
+__device__ __forceinline__ void dit_stage(cx_t<T>* s, int n, int Lp, const cx_t<T>* __restrict__ tw,
                                           const cx_t<T>* tws, int tw_scale, int nthreads) {
     using C = cx_t<T>;
     const int L = Lp * R;
@@ -383,22 +382,16 @@ __device__ __forceinline__ void dit_stage(cx_t<T>* s, int n, int Lp, bool inv, c
     }
     for (; active && k < Lp; k += nthreads) {
         StageTw<T> w{};
-        if (Lp > 1) w = stage_lookups<T, -1, R>(tw, tws, k * tw_step);
+        if (Lp > 1) w = stage_lookups<T, SIGN, R>(tw, tws, k * tw_step);
         for (int g = g0; g < G; g += gstep) {
             const int base = g * L + k;
             C v[R];
 #pragma unroll
-            for (int r = 0; r < R; ++r) {
-                v[r] = s[spad(base + r * Lp)];
-                if (inv) v[r].y = -v[r].y;
-            }
+            for (int r = 0; r < R; ++r) v[r] = s[spad(base + r * Lp)];
             if (Lp > 1) apply_stage_tw<T, R>(v, w);
-            dft<T, R, -1>(v);
+            dft<T, R, SIGN>(v);
 #pragma unroll
-            for (int r = 0; r < R; ++r) {
-                if (inv) v[r].y = -v[r].y;
-                s[spad(base + r * Lp)] = v[r];
-            }
+            for (int r = 0; r < R; ++r) s[spad(base + r * Lp)] = v[r];
         }
     }
     __syncthreads();
@@ -406,26 +399,19 @@ __device__ __forceinline__ void dit_stage(cx_t<T>* s, int n, int Lp, bool inv, c
 
 // The last stage (G = 1, so one butterfly per offset k), writing its outputs straight to
 // the destination through put(position in s, value) instead of back to shared memory.
-template <typename T, int R, typename Put>
-__device__ __forceinline__ void dit_stage_out(const cx_t<T>* s, int n, int Lp, bool inv,
-                                              const cx_t<T>* __restrict__ tw, const cx_t<T>* tws, int tw_scale,
-                                              int nthreads, Put put) {
+template <typename T, int R, int SIGN, typename Put>
+__device__ __forceinline__ void dit_stage_out(const cx_t<T>* s, int n, int Lp, const cx_t<T>* __restrict__ tw,
+                                              const cx_t<T>* tws, int tw_scale, int nthreads, Put put) {
     using C = cx_t<T>;
     const int tw_step = tw_scale * (n / (Lp * R));
     for (int k = threadIdx.x; k < Lp; k += nthreads) {
         C v[R];
 #pragma unroll
-        for (int r = 0; r < R; ++r) {
-            v[r] = s[spad(k + r * Lp)];
-            if (inv) v[r].y = -v[r].y;
-        }
-        if (Lp > 1) apply_stage_tw<T, R>(v, stage_lookups<T, -1, R>(tw, tws, k * tw_step));
-        dft<T, R, -1>(v);
+        for (int r = 0; r < R; ++r) v[r] = s[spad(k + r * Lp)];
+        if (Lp > 1) apply_stage_tw<T, R>(v, stage_lookups<T, SIGN, R>(tw, tws, k * tw_step));
+        dft<T, R, SIGN>(v);
 #pragma unroll
-        for (int r = 0; r < R; ++r) {
-            if (inv) v[r].y = -v[r].y;
-            put(k + r * Lp, v[r]);
-        }
+        for (int r = 0; r < R; ++r) put(k + r * Lp, v[r]);
     }
 }
 
@@ -477,23 +463,22 @@ __device__ __forceinline__ cx_t<T> load_elem(int io, int idx, int n, const cx_t<
     return v;
 }
 
-// One kernel per precision: the direction (sign) is a run-time argument (inverse =
-// conjugated forward butterflies), which keeps the number of instantiated butterflies, and
-// the build time, small.  256 threads and at most 80 registers a thread (launch bounds for
-// three CTAs per SM): three 6912-point rows share an SM, so that one row's loads overlap
-// the others' butterflies.
+// SIGN (-1 forward, +1 inverse) is a template argument: the factors +-i of the butterflies
+// and the conjugation of the twiddles fold into the arithmetic.  256 threads and at most 80
+// registers a thread (launch bounds for three CTAs per SM): three 6912-point rows share an
+// SM, so that one row's loads overlap the others' butterflies.
 constexpr int kFftThreads = 256;
-template <typename T>
+template <typename T, int SIGN>
 __global__ void __launch_bounds__(kFftThreads, 3) fft_rows_kernel(
     const cx_t<T>* __restrict__ in, long in_stride, int in_len, int in_shift,
     cx_t<T>* __restrict__ out, long out_stride, int out_len, int out_shift,
     int n, int Q, FftPlan1D plan, const cx_t<T>* __restrict__ tw, const int* __restrict__ perm,
     const T* __restrict__ pre_elem, const T* __restrict__ pre_row,
     const T* __restrict__ post_elem, const T* __restrict__ post_row, HermFold<T> hf, int io,
-    const cx_t<T>* __restrict__ tw2, long in_batch, long out_batch, int sign) {
+    const cx_t<T>* __restrict__ tw2, long in_batch, long out_batch) {
     using C = cx_t<T>;
-    const int NT = blockDim.x;
-    const bool inv = sign > 0;
+    constexpr int NT = kFftThreads;
+    constexpr bool inv = SIGN > 0;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* s = reinterpret_cast<C*>(smem_raw);
     // blockIdx.z: grid of a batch of equal grids (right-hand sides), in_batch / out_batch apart
@@ -564,11 +549,11 @@ __global__ void __launch_bounds__(kFftThreads, 3) fft_rows_kernel(
         if (st == plan.nstages - 1 && io != kIoPairFwd) {
             // last stage: outputs go straight to global memory (uniform branch, no barrier after)
             with_radix<T>(R, [&](auto rc) {
-                dit_stage_out<T, decltype(rc)::value>(s, nq, Lp, inv, tw, tws, Q, NT, put);
+                dit_stage_out<T, decltype(rc)::value, SIGN>(s, nq, Lp, tw, tws, Q, NT, put);
             });
             return;
         }
-        with_radix<T>(R, [&](auto rc) { dit_stage<T, decltype(rc)::value>(s, nq, Lp, inv, tw, tws, Q, NT); });
+        with_radix<T>(R, [&](auto rc) { dit_stage<T, decltype(rc)::value, SIGN>(s, nq, Lp, tw, tws, Q, NT); });
         Lp *= R;
     }
     // kIoPairFwd: s = Z^ of z = x0 + i x1 (two real rows): X0(k) = (Z(k) + conj Z(-k)) / 2,
@@ -687,20 +672,27 @@ static int fft_phases(int n, bool fp64) {
 
 int fft_max_length(bool fp64) { return 2 * fft_max_row(fp64); }
 
-// Launches fft_rows_kernel<T> with nt threads per CTA.
-template <typename T, typename... A>
-int launch_fft_rows(int nt, dim3 grid, size_t smem, cudaStream_t stream, A... args) {
-    auto k = fft_rows_kernel<T>;
+// Launches fft_rows_kernel<T, sign> (sign -1 or +1) with the shared-memory carveout at its
+// maximum (all of the SM's unified memory as shared memory).
+template <typename T, int SIGN, typename... A>
+int launch_fft_rows_sign(dim3 grid, size_t smem, cudaStream_t stream, A... args) {
+    auto k = fft_rows_kernel<T, SIGN>;
     SBD_TRY(raise_smem_limit(k, smem));
-    static const bool carve = [&] {   // all of the SM's unified memory as shared memory
+    static const bool carve = [&] {
         cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
         cudaGetLastError();
         return true;
     }();
     (void)carve;
-    k<<<grid, nt, smem, stream>>>(args...);
+    k<<<grid, kFftThreads, smem, stream>>>(args...);
     SBD_LAUNCH_CHECK();
     return SBD_OK;
+}
+
+template <typename T, typename... A>
+int launch_fft_rows(int sign, dim3 grid, size_t smem, cudaStream_t stream, A... args) {
+    return sign < 0 ? launch_fft_rows_sign<T, -1>(grid, smem, stream, args...)
+                    : launch_fft_rows_sign<T, 1>(grid, smem, stream, args...);
 }
 
 template <typename T>
@@ -756,9 +748,9 @@ int fft_rows(const cx_t<T>* in, long in_stride, int in_len, int in_shift,
         const HermFold<T> hf{in - static_cast<long>(herm_row0) * in_stride, herm_n,
                              static_cast<long>(herm_row0) + r0};
         // half-length phases (split) fit more CTAs per SM
-        const int rc = launch_fft_rows<T>(kFftThreads, grid, smem, stream, ip, in_stride, in_len, in_shift,
-                                          op, out_stride, out_len, out_shift, n, Q, plan, tw, perm, pre_elem, prr,
-                                          post_elem, por, hf, io, tw2, in_batch, out_batch, sign);
+        const int rc = launch_fft_rows<T>(sign, grid, smem, stream, ip, in_stride, in_len, in_shift, op, out_stride,
+                                          out_len, out_shift, n, Q, plan, tw, perm, pre_elem, prr, post_elem, por,
+                                          hf, io, tw2, in_batch, out_batch);
         if (rc) return rc;
     }
     SBD_LAUNCH_CHECK();
@@ -781,10 +773,10 @@ int fft_rows_tables(const cx_t<T>* in, long in_stride, int in_len, cx_t<T>* out,
         const cx_t<T>* ip = in + static_cast<long>(r0) * in_stride;
         cx_t<T>* op = out + static_cast<long>(r0) * out_stride;
         const T* none = nullptr;
-        const int rc = launch_fft_rows<T>(kFftThreads, grid, smem, stream, ip, in_stride, in_len, 0, op,
-                                          out_stride, out_len, 0, n, 1, plan, tw, perm, none, none, none, none,
+        const int rc = launch_fft_rows<T>(sign, grid, smem, stream, ip, in_stride, in_len, 0, op, out_stride,
+                                          out_len, 0, n, 1, plan, tw, perm, none, none, none, none,
                                           HermFold<T>{nullptr, 0, 0}, static_cast<int>(kIoPlain),
-                                          static_cast<const cx_t<T>*>(nullptr), 0L, 0L, sign);
+                                          static_cast<const cx_t<T>*>(nullptr), 0L, 0L);
         if (rc) return rc;
     }
     return SBD_OK;
