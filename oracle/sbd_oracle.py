@@ -40,6 +40,16 @@ design notes):
       fixed sample set ``fit_error_samples`` of [a, 1], dense near a (where the
       paper advises to monitor it), and the dichotomy stops at a resolution of
       max(1, P // 128) terms (``choose_P``).
+  R14 General radial kernels (Sec. 4.3), in the scaled variable s = r / delta_max:
+      K(s) = sum_t mu_t J0(omega_t s) / J0(omega_t) with the n conditions
+      (-Delta)^j (g - K)(1) = 0, j = 1..n, i.e. M mu = lambda with M_jt =
+      (-1)^j omega_t^(2j) and lambda_j = Delta^j g(1) (the printed system pairs
+      (-1)^j in M with (-Delta)^j in lambda, which differ by (-1)^j; the
+      condition itself is the multi-Dirichlet one of Sec. 2.2).  The order-0
+      condition is met by the constant c = g(1) - K(1), carried by the xi = 0
+      node.  omega' = sqrt of the mean |lambda_{j+1} / lambda_j| over
+      j = 1..n (n + 1 iterates); omega_1..omega_n are the roots of J1 nearest
+      omega', nearest first.  The SBD then fits h = g - K - c.
 """
 from __future__ import annotations
 
@@ -54,12 +64,31 @@ TWO_PI = 2.0 * math.pi
 
 
 # ---------------------------------------------------------------------------
-# Kernels and the direct sum (Introduction, Eq. discreteConv; Sec. 4.1, 4.2)
+# Kernels and the direct sum (Introduction, Eq. discreteConv; Sec. 4.1, 4.2, 4.3)
 # ---------------------------------------------------------------------------
 
-def kernel_G(r: np.ndarray, kind: str, kappa: float = 0.0) -> np.ndarray:
-    """G(r): Laplace -log(r)/(2 pi) (Introduction) or Helmholtz (i/4) H0^(1)(kappa r) (R9)."""
+@dataclass
+class RadialKernel:
+    """A real radial kernel of Sec. 4.3, given by functions of r > 0: value(r) = G(r),
+    deriv(r) = G'(r), and lap(j, r) = (Delta^j G)(r) for j >= 1, Delta = d^2/dr^2 + (1/r) d/dr
+    the radial Laplacian.  log_coef is c in G = c log r + (a function smooth at 0); the oracle
+    does not use it (the CUDA path tabulates the near field with it)."""
+    value: object
+    deriv: object
+    lap: object
+    log_coef: float = 0.0
+
+
+def is_complex_kind(kind) -> bool:
+    return isinstance(kind, str) and kind == "helmholtz"
+
+
+def kernel_G(r: np.ndarray, kind, kappa: float = 0.0) -> np.ndarray:
+    """G(r): Laplace -log(r)/(2 pi) (Introduction) or Helmholtz (i/4) H0^(1)(kappa r) (R9); for a
+    RadialKernel (Sec. 4.3) its own value."""
     r = np.asarray(r, dtype=np.float64)
+    if isinstance(kind, RadialKernel):
+        return kind.value(r)
     if kind == "laplace":
         return -np.log(r) / TWO_PI
     if kind == "helmholtz":
@@ -79,7 +108,7 @@ def direct_sum(z: np.ndarray, f: np.ndarray, kind: str, kappa: float = 0.0,
     single = f.ndim == 1
     F = f[None, :] if single else f
     idx = np.arange(len(z)) if targets is None else np.asarray(targets)
-    out_dtype = np.complex128 if (kind == "helmholtz" or np.iscomplexobj(F)) else np.float64
+    out_dtype = np.complex128 if (is_complex_kind(kind) or np.iscomplexobj(F)) else np.float64
     q = np.zeros((F.shape[0], len(idx)), dtype=out_dtype)
     for s in range(0, len(idx), chunk):
         ks = idx[s:s + chunk]
@@ -354,6 +383,7 @@ class OraclePlan:
     x: np.ndarray | None = None   # targets, when they differ from the sources (make_plan_st)
     y: np.ndarray | None = None   # sources (make_plan_st)
     D_st: tuple | None = None     # rectangular close matrix (close_matrix_st)
+    enforce: tuple | None = None  # general kernel (make_plan_radial): (omega, mu, c) of reading R14
 
 
 def make_plan(z: np.ndarray, kind: str, delta_min: float, eps: float, kappa: float = 0.0,
@@ -511,7 +541,7 @@ def sbd_matvec(plan: OraclePlan, f: np.ndarray) -> np.ndarray:
     if f.ndim == 2:
         return np.stack([sbd_matvec(plan, fi) for fi in f])
     q = far_part(plan, f) + close_part(plan, f)
-    if plan.kind == "laplace" and not np.iscomplexobj(f):
+    if not is_complex_kind(plan.kind) and not np.iscomplexobj(f):
         return q.real
     return q
 
@@ -638,3 +668,111 @@ def series_matvec(plan: OraclePlan, f: np.ndarray, chunk: int = 256) -> np.ndarr
     if plan.kind == "laplace" and not np.iscomplexobj(f):
         return q.real
     return q
+
+
+# ---------------------------------------------------------------------------
+# General radial kernels: the multi-Dirichlet condition enforced by a few J0 terms (Sec. 4.3)
+# ---------------------------------------------------------------------------
+
+def dirichlet_frequencies(lam: np.ndarray, n: int) -> np.ndarray:
+    """omega_1..omega_n of Sec. 4.3 (reading R14): omega' = sqrt of the mean ratio |lam_{j+1} /
+    lam_j| of successive iterates (lam holds Delta^j g(1) for j = 1..n+1), then the roots of J1
+    nearest omega', nearest first."""
+    ratios = [abs(lam[j + 1] / lam[j]) for j in range(n) if lam[j] != 0.0]
+    w = math.sqrt(sum(ratios) / len(ratios)) if ratios else 1.0
+    roots = sp.jn_zeros(1, int(w / math.pi) + n + 4)
+    order = np.argsort(np.abs(roots - w), kind="stable")
+    return np.sort(roots[order[:n]])
+
+
+def dirichlet_correction(lam: np.ndarray, n: int):
+    """(omega, mu) of K(s) = sum_t mu_t J0(omega_t s) / J0(omega_t) with Delta^j K(1) = lam_j for
+    j = 1..n: the system M mu = lam of Sec. 4.3, M_jt = (-1)^j omega_t^(2j) (reading R14)."""
+    if n == 0:
+        return np.zeros(0), np.zeros(0)
+    omega = dirichlet_frequencies(lam, n)
+    j = np.arange(1, n + 1)[:, None]
+    M = (-1.0) ** j * omega[None, :] ** (2 * j)
+    mu = np.linalg.solve(M, np.asarray(lam[:n], dtype=np.float64))
+    return omega, mu
+
+
+def correction_value(s, omega, mu):
+    """K(s) = sum_t mu_t J0(omega_t s) / J0(omega_t)."""
+    s = np.atleast_1d(np.asarray(s, dtype=np.float64))
+    if len(omega) == 0:
+        return np.zeros(s.shape)
+    return (sp.j0(np.outer(s, omega)) / sp.j0(omega)[None, :]) @ mu
+
+
+def correction_deriv(s, omega, mu):
+    """K'(s) = -sum_t mu_t omega_t J1(omega_t s) / J0(omega_t)."""
+    s = np.atleast_1d(np.asarray(s, dtype=np.float64))
+    if len(omega) == 0:
+        return np.zeros(s.shape)
+    return -(sp.j1(np.outer(s, omega)) * (omega / sp.j0(omega))[None, :]) @ mu
+
+
+def radial_fit(kern: RadialKernel, R: float, a: float, tol: float, n_enforce: int = 0, P: int | None = None):
+    """The SBD of a general real radial kernel on (a, 1) in s = r / R (Sec. 4.3 with Sec. 3):
+    lambda_j = Delta_s^j g(1) = R^(2j) (Delta^j G)(R) for j = 1..n+1, the correction K and constant
+    c of reading R14, then the Sec. 3 fit of h = g - K - c, its P chosen by choose_P against tol
+    (kernel units) unless given.  Returns (P, rho, C, alpha, err, omega, mu, c)."""
+    lam = np.array([R ** (2 * j) * float(kern.lap(j, R)) for j in range(1, n_enforce + 2)])
+    omega, mu = dirichlet_correction(lam, n_enforce)
+    cst = float(kern.value(R)) - float(correction_value(1.0, omega, mu)[0])
+    h = lambda s: kern.value(R * s) - correction_value(s, omega, mu) - cst  # noqa: E731
+    h_prime = lambda s: R * kern.deriv(R * s) - correction_deriv(s, omega, mu)  # noqa: E731
+    extra = 2.0 * float(omega.max()) if len(omega) else 0.0
+    if P is None:
+        P, rho, C, alpha, err = choose_P(h, h_prime, a, tol, initial_P(a, tol, extra), extra)
+    else:
+        rho, C, alpha = sbd_coefficients(h_prime, a, P, extra)
+        err = fit_linf_error(h, rho, C, alpha, a, extra)
+    return P, rho, C, alpha, err, omega, mu, cst
+
+
+def make_plan_radial(z: np.ndarray, kern: RadialKernel, delta_min: float, eps: float, n_enforce: int = 0,
+                     P: int | None = None) -> OraclePlan:
+    """Off-line part for a general real radial kernel (Sec. 4.3; circles of Sec. 5): radial_fit
+    with R = delta_max, one circle per Bessel term of h and per term of K (Sec. 1 identity), and
+    the constant c at xi = 0.  The plan's alpha holds h's coefficients in the e_p basis."""
+    z = np.asarray(z, dtype=np.float64)
+    c0 = 0.5 * (z.min(axis=0) + z.max(axis=0))
+    delta_max = 2.0 * float(np.sqrt(np.max(np.sum((z - c0) ** 2, axis=1))))   # R2
+    if not (0.0 < delta_min < delta_max):
+        raise ValueError("need 0 < delta_min < delta_max")
+    eps_fit, eps_q = eps / 3.0, eps / 3.0      # R7
+    R = delta_max
+    a = delta_min / R
+    P, rho, C, alpha, err, omega, mu, cst = radial_fit(kern, R, a, eps_fit, n_enforce, P)
+    coef = alpha * C                          # kernel units (no scale: the kernel is G itself)
+    n_circles = P + len(omega)
+    M = [circle_size(float(rho[p]), float(coef[p]), eps_q / n_circles) for p in range(P)]
+    radius = list(rho / R)
+    weight = list(coef / np.array(M, dtype=np.float64))
+    for om, m in zip(omega, mu):
+        wt = float(m / sp.j0(om))
+        Mt = circle_size(float(om), wt, eps_q / n_circles)
+        M.append(Mt)
+        radius.append(om / R)
+        weight.append(wt / Mt)
+    M = np.array(M, dtype=np.int64)
+    radius = np.array(radius)
+    weight = np.array(weight, dtype=np.complex128)
+    w0 = complex(cst)
+    xi = [np.zeros((1, 2))]
+    om_list = [np.array([w0])]
+    for Mp, rp, wp in zip(M, radius, weight):
+        xi.append(circle_nodes(float(rp), int(Mp)))
+        om_list.append(np.full(int(Mp), wp, dtype=np.complex128))
+    return OraclePlan(kern, 0.0, z, delta_min, delta_max, eps, R, a, P, rho, C, alpha, err, M, radius, weight,
+                      w0, np.concatenate(xi, axis=0), np.concatenate(om_list), enforce=(omega, mu, cst))
+
+
+def radial_series_kernel(plan: OraclePlan, r) -> np.ndarray:
+    """G_fit(r) = c + K(s) + sum_p alpha_p C_p J0(rho_p s), s = r / delta_max: the general-kernel
+    series whose circles the plan quadratures (Sec. 4.3, R14)."""
+    omega, mu, cst = plan.enforce
+    s = np.atleast_1d(np.asarray(r, dtype=np.float64)) / plan.scale_R
+    return cst + correction_value(s, omega, mu) + series_value(s, plan.rho, plan.C, plan.alpha)

@@ -84,12 +84,6 @@ struct TableCache {
 constexpr int kTwLo = 128;
 inline int tw2_size(int n) { return kTwLo + (n + kTwLo - 1) / kTwLo; }
 
-// Shared-memory position of row element a: one spare slot after every 16 elements.  The
-// load pass stores consecutive inputs nq / R_last apart (digit reversal), a multiple of
-// 16 elements for most rows, which without the spare slots puts a half-warp's stores in
-// one bank; with them the stride is odd modulo 16 (conflict-free for 8- and 16-byte elements).
-__host__ __device__ __forceinline__ int spad(int a) { return a + (a >> 4); }
-inline int padded_len(int n) { return n + (n >> 4) + 1; }
 
 template <typename T>
 const cx_t<T>* twiddles2(int n, cudaStream_t stream) {
@@ -387,11 +381,11 @@ __device__ __forceinline__ void dit_stage(cx_t<T>* s, int n, int Lp, const cx_t<
             const int base = g * L + k;
             C v[R];
 #pragma unroll
-            for (int r = 0; r < R; ++r) v[r] = s[spad(base + r * Lp)];
+            for (int r = 0; r < R; ++r) v[r] = s[base + r * Lp];
             if (Lp > 1) apply_stage_tw<T, R>(v, w);
             dft<T, R, SIGN>(v);
 #pragma unroll
-            for (int r = 0; r < R; ++r) s[spad(base + r * Lp)] = v[r];
+            for (int r = 0; r < R; ++r) s[base + r * Lp] = v[r];
         }
     }
     __syncthreads();
@@ -407,7 +401,7 @@ __device__ __forceinline__ void dit_stage_out(const cx_t<T>* s, int n, int Lp, c
     for (int k = threadIdx.x; k < Lp; k += nthreads) {
         C v[R];
 #pragma unroll
-        for (int r = 0; r < R; ++r) v[r] = s[spad(k + r * Lp)];
+        for (int r = 0; r < R; ++r) v[r] = s[k + r * Lp];
         if (Lp > 1) apply_stage_tw<T, R>(v, stage_lookups<T, SIGN, R>(tw, tws, k * tw_step));
         dft<T, R, SIGN>(v);
 #pragma unroll
@@ -491,7 +485,7 @@ __global__ void __launch_bounds__(kFftThreads, 3) fft_rows_kernel(
     // two-level twiddle table (if given) in shared memory after the row
     C* tws = nullptr;
     if (tw2) {
-        tws = s + nq + (nq >> 4) + 1;              // after the padded row
+        tws = s + nq;
         const int ntw = kTwLo + (n + kTwLo - 1) / kTwLo;
         for (int i = threadIdx.x; i < ntw; i += NT) tws[i] = tw2[i];
         __syncthreads();
@@ -520,7 +514,7 @@ __global__ void __launch_bounds__(kFftThreads, 3) fft_rows_kernel(
                 acc = cadd(acc, v);
             }
         }
-        s[spad(perm[i])] = acc;
+        s[perm[i]] = acc;
     }
     __syncthreads();
     int Lp = 1;
@@ -565,7 +559,7 @@ __global__ void __launch_bounds__(kFftThreads, 3) fft_rows_kernel(
         if (k >= n) k -= n;
         if (Q == 2 && (k & 1) != r) continue;
         const int km = k == 0 ? 0 : n - k;        // same parity as k (n even)
-        const C zk = s[spad(Q == 2 ? (k >> 1) : k)], zm = s[spad(Q == 2 ? (km >> 1) : km)];
+        const C zk = s[Q == 2 ? (k >> 1) : k], zm = s[Q == 2 ? (km >> 1) : km];
         const T h = static_cast<T>(0.5);
         const T pe = post_elem ? post_elem[e] : static_cast<T>(1);
         d0[e] = mk<T>(h * pe * (zk.x + zm.x), h * pe * (zk.y - zm.y));
@@ -657,7 +651,7 @@ bool fft_make_plan(int n, FftPlan1D& p, bool fp64) {
 
 int fft_max_row(bool fp64) {
     const int smem = 227 * 1024;
-    const int lim = (smem / (fp64 ? 16 : 8)) * 16 / 17 - 1;          // the padded row fits
+    const int lim = smem / (fp64 ? 16 : 8);
     return fp64 ? std::min(lim, MaxB<double>::n_max) : std::min(lim, MaxB<float>::n_max);
 }
 
@@ -730,7 +724,7 @@ int fft_rows(const cx_t<T>* in, long in_stride, int in_len, int in_shift,
         return SBD_ENOMEM;
     }
     // the two-level twiddle table rides in shared memory when it fits beside the row
-    const size_t row_bytes = sizeof(cx_t<T>) * static_cast<size_t>(padded_len(nq));
+    const size_t row_bytes = sizeof(cx_t<T>) * static_cast<size_t>(nq);
     const size_t tw2_bytes = sizeof(cx_t<T>) * static_cast<size_t>(tw2_size(n));
     const cx_t<T>* tw2 = row_bytes + tw2_bytes <= 227u * 1024u ? twiddles2<T>(n, stream) : nullptr;
     const size_t smem = row_bytes + (tw2 ? tw2_bytes : 0);
@@ -766,7 +760,7 @@ int fft_rows_tables(const cx_t<T>* in, long in_stride, int in_len, cx_t<T>* out,
         set_error("FFT length not supported: " + std::to_string(n));
         return SBD_ENOTSUP;
     }
-    const size_t smem = sizeof(cx_t<T>) * static_cast<size_t>(padded_len(n));
+    const size_t smem = sizeof(cx_t<T>) * static_cast<size_t>(n);
     for (int r0 = 0; r0 < rows; r0 += 65535) {
         const int nr = std::min(65535, rows - r0);
         const dim3 grid(1u, static_cast<unsigned>(nr));

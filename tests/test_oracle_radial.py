@@ -1,0 +1,126 @@
+"""CPU pins of the oracle's general radial kernels (Sec. 4.3), each fixed by something other than
+the oracle's own formulas:
+  * the multi-Dirichlet property (-Delta)^j h(1) = 0 of h = g - K - c, differentiated symbolically
+    by sympy (its own Bessel calculus, high precision) for j = 0..n;
+  * the paper's observations for G = log r + sin(w r): enforcing the condition lowers the fit
+    error at fixed P (Sec. 4.3, Fig. badSit and Fig. figArbitraryKernel: 100 terms, n <= 3);
+  * an exact case: G = J0(beta r) with beta delta_max a root of J1 is its own correction
+    (h = 0, alpha = 0);
+  * the reduction to the Laplace kernel (no iterate to enforce): the same P, coefficients and
+    matvec as the Laplace plan of Sec. 4.1;
+  * the Sec. 1 output bound against the direct sum."""
+import math
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import sbd_oracle as O
+
+sy = pytest.importorskip("sympy")
+R_ = sy.symbols("r", positive=True)
+
+
+def kernel_from(expr, log_coef=0.0):
+    """RadialKernel from a sympy expression of r: value, derivative and radial-Laplacian iterates
+    all derived by sympy."""
+    f = sy.lambdify(R_, expr, "numpy")
+    d = sy.lambdify(R_, sy.diff(expr, R_), "numpy")
+    laps, cur = {}, expr
+    for j in range(1, 7):
+        cur = sy.diff(cur, R_, 2) + sy.diff(cur, R_) / R_
+        laps[j] = sy.lambdify(R_, cur, "numpy")
+    return O.RadialKernel(lambda r: f(np.asarray(r, dtype=np.float64)),
+                          lambda r: d(np.asarray(r, dtype=np.float64)),
+                          lambda j, r: float(laps[j](r)), log_coef)
+
+
+@pytest.mark.parametrize("w,n", [(3.0, 1), (3.0, 3), (40.0, 2)])
+def test_enforced_iterates_vanish(w, n):
+    """(-Delta)^j (g - K - c)(1) = 0 for j = 0..n, with K rebuilt in sympy from (omega, mu) and
+    differentiated symbolically (mpmath Bessel functions, 30 digits)."""
+    G = sy.log(R_) + sy.sin(w * R_)
+    kern = kernel_from(G, 1.0)
+    R = 1.7
+    _, _, _, _, _, omega, mu, cst = O.radial_fit(kern, R, 0.2, 1e-8, n, P=20)
+    s = sy.symbols("s", positive=True)
+    K = sum(sy.Float(m, 30) * sy.besselj(0, sy.Float(o, 30) * s) / sy.besselj(0, sy.Float(o, 30))
+            for o, m in zip(omega, mu))
+    h = G.subs(R_, R * s) - K - sy.Float(cst, 30)
+    cur = h
+    for j in range(0, n + 1):
+        val = complex(sy.N(cur.subs(s, 1), 30))
+        scale = abs(complex(sy.N((G.subs(R_, R * s) if j == 0 else
+                                  _lap_iter(G.subs(R_, R * s), s, j)).subs(s, 1), 30))) + 1.0
+        assert abs(val) <= 1e-9 * scale, (j, val, scale)
+        cur = sy.diff(cur, s, 2) + sy.diff(cur, s) / s
+
+
+def _lap_iter(e, s, j):
+    for _ in range(j):
+        e = sy.diff(e, s, 2) + sy.diff(e, s) / s
+    return e
+
+
+def test_frequencies_are_the_nearest_j1_roots():
+    """omega' from the ratio of successive iterates; for sin(w r) the ratio tends to w^2 R^2, so the
+    frequencies are the J1 roots nearest w R (Sec. 4.3)."""
+    from scipy.special import jn_zeros
+    kern = kernel_from(sy.sin(250 * R_))
+    _, _, _, _, _, omega, _, _ = O.radial_fit(kern, 1.0, 0.1, 1e-6, 3, P=40)
+    roots = jn_zeros(1, 100)
+    near = np.sort(roots[np.argsort(np.abs(roots - 250.0))[:3]])
+    assert np.allclose(omega, near)
+
+
+def test_enforcement_lowers_the_fit_error():
+    """Sec. 4.3: without the condition the error stagnates (near r = 1); with it the decay resumes."""
+    k1 = kernel_from(sy.log(R_) + sy.sin(R_), 1.0)
+    e = [O.radial_fit(k1, 1.0, 0.05, 1e-12, n, P=100)[4] for n in (0, 1)]
+    assert e[1] < e[0] / 20, e
+    k250 = kernel_from(sy.log(R_) + sy.sin(250 * R_), 1.0)      # the paper's 100-term example
+    e = [O.radial_fit(k250, 1.0, 0.05, 1e-12, n, P=100)[4] for n in (0, 1, 2)]
+    assert e[0] > 0.1 and e[1] < 1e-2 and e[2] < 1e-4, e
+
+
+def test_j0_kernel_is_its_own_correction():
+    from scipy.special import j0, jn_zeros
+    R = 2.0
+    beta = jn_zeros(1, 5)[-1] / R
+    kern = O.RadialKernel(lambda r: j0(beta * np.asarray(r)), lambda r: -beta * __import__("scipy.special").special.j1(
+        beta * np.asarray(r)), lambda j, r: (-beta * beta) ** j * j0(beta * r))
+    P, rho, C, alpha, err, omega, mu, cst = O.radial_fit(kern, R, 0.1, 1e-9, 1, P=30)
+    assert np.isclose(omega[0], beta * R) and np.isclose(mu[0] / j0(omega[0]), 1.0 / j0(beta * R) * j0(beta * R))
+    assert abs(cst) < 1e-14 and err < 1e-13 and np.max(np.abs(alpha)) < 1e-12
+
+
+def test_laplace_kernel_reduces_to_the_laplace_plan():
+    z = W.disk_points(600, 11)
+    f = W.rhs(600, 12)
+    dmin = math.sqrt(20 / 600)
+    kern = O.RadialKernel(lambda r: -np.log(r) / O.TWO_PI, lambda r: -1.0 / (O.TWO_PI * np.asarray(r)),
+                          lambda j, r: 0.0, -1.0 / O.TWO_PI)
+    pr = O.make_plan_radial(z, kern, dmin, 1e-6, n_enforce=0)
+    pl = O.make_plan(z, "laplace", dmin, 1e-6)
+    assert pr.P == pl.P and np.allclose(pr.M, pl.M)
+    np.testing.assert_allclose(pr.alpha, -pl.alpha / O.TWO_PI, rtol=1e-9, atol=1e-14)
+    assert abs(pr.w0 - pl.w0) < 1e-14
+    np.testing.assert_allclose(O.sbd_matvec(pr, f), O.sbd_matvec(pl, f), rtol=0, atol=1e-12 * np.abs(f).sum())
+
+
+@pytest.mark.parametrize("w,n", [(3.0, 2), (25.0, 3)])
+def test_radial_matvec_meets_the_output_bound(w, n):
+    z = W.disk_points(1200, 21)
+    f = W.rhs(1200, 22)
+    dmin = math.sqrt(20 / 1200)
+    kern = kernel_from(sy.log(R_) + sy.sin(w * R_), 1.0)
+    pl = O.make_plan_radial(z, kern, dmin, 1e-6, n_enforce=n)
+    q = O.sbd_matvec(pl, f)
+    qd = O.direct_sum(z, f, kern)
+    assert np.max(np.abs(q - qd)) <= 1e-6 * np.abs(f).sum()
+    # and the series (each J0 term whole) against the plane-wave circles: the quadrature's share
+    r = np.linspace(dmin, pl.delta_max, 200)
+    xi = np.stack([r, np.zeros_like(r)], axis=1)
+    gap = O.g_approx_direct(xi, pl.xi, pl.omega).real
+    assert np.max(np.abs(gap - O.radial_series_kernel(pl, r))) <= 1e-6 / 3
+    assert np.max(np.abs(O.radial_series_kernel(pl, r) - kern.value(r))) <= 1e-6 / 3 * 1.01
