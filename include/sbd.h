@@ -55,7 +55,7 @@ extern "C" {
 typedef struct sbd_plan_s* sbd_plan_t;   /* opaque; owned by the library */
 
 /* Kernel G (Introduction; Sec. 4.1 Laplace; Sec. 4.2 Helmholtz). */
-typedef enum { SBD_LAPLACE = 0, SBD_HELMHOLTZ = 1 } sbd_kernel_kind;
+typedef enum { SBD_LAPLACE = 0, SBD_HELMHOLTZ = 1, SBD_RADIAL = 2 } sbd_kernel_kind;
 typedef struct {
     int32_t kind;      /* sbd_kernel_kind */
     double  kappa;     /* wavenumber (> 0) for SBD_HELMHOLTZ; ignored for SBD_LAPLACE */
@@ -195,6 +195,52 @@ int sbd_plan(const double* points, int64_t n, sbd_kernel kernel, double delta_mi
 int sbd_plan_st(const double* targets, int64_t n_targets, const double* sources, int64_t n_sources,
                 sbd_kernel kernel, double delta_min, double eps, const sbd_options* opt, void* cuda_stream,
                 sbd_plan_t* out);
+
+/* ---------------------------------------------------------------------------------
+ * sbd_plan_radial - the off-line part for a general real radial kernel G (Sec. 4.3):
+ * the multi-Dirichlet condition of Sec. 2.2 is enforced at r = delta_max up to order
+ * n_enforce by K(s) = sum_t mu_t J0(omega_t s) / J0(omega_t), s = r / delta_max, with
+ * omega_t the roots of J1 nearest omega' (the square root of the mean ratio of successive
+ * iterates Delta^j G(delta_max), j = 1..n_enforce + 1) and mu solving
+ * sum_t (-1)^j omega_t^(2j) mu_t = delta_max^(2j) Delta^j G(delta_max), j = 1..n_enforce;
+ * the constant c = G(delta_max) - K(1) is the xi = 0 term, and h = G - K - c is fitted by
+ * the SBD of Sec. 3 (right-hand side by quadrature of h').  The far part has one circle per
+ * Bessel term of h and one per term of K; D = G - G_approx as for sbd_plan, tabulated in r
+ * on [0, delta_min] as log_coef log r + a Chebyshev series (so G - log_coef log r must be
+ * smooth on [0, delta_min]).  The kernel is real: f and q are float64, as for Laplace.
+ *   kernel->value(r, ctx)         G(r), r > 0.
+ *   kernel->deriv(r, ctx)         G'(r), r > 0.
+ *   kernel->laplacian(j, r, ctx)  (Delta^j G)(r) for 1 <= j <= n_enforce + 1, Delta =
+ *                                 d^2/dr^2 + (1/r) d/dr; may be NULL when n_enforce = 0.
+ *   kernel->log_coef              c with G(r) - c log r smooth at r = 0.
+ *   kernel->n_enforce             0 .. 8 iterates enforced.
+ * The callbacks run on the calling thread, only during this call (never afterwards), and
+ * may be called from several OpenMP threads at once (they must be thread safe).  Other
+ * arguments as sbd_plan; the plan works with every on-line call except those of the
+ * uniform-grid variant (SBD_FLAG_UNIFORM_GRID gives SBD_ENOTSUP) and is never taken from
+ * or put in the fit cache.  Errors: as sbd_plan; SBD_EINVAL also for a null kernel or
+ * callback, n_enforce outside [0, 8], or a non-finite G(delta_max).
+ * ------------------------------------------------------------------------------- */
+typedef struct {
+    double (*value)(double r, void* ctx);
+    double (*deriv)(double r, void* ctx);
+    double (*laplacian)(int32_t j, double r, void* ctx);
+    void* ctx;
+    double log_coef;
+    int32_t n_enforce;
+} sbd_radial_kernel;
+
+int sbd_plan_radial(const double* points, int64_t n, const sbd_radial_kernel* kernel, double delta_min,
+                    double eps, const sbd_options* opt, void* cuda_stream, sbd_plan_t* out);
+
+/* sbd_offline_fit_radial - the fit of sbd_plan_radial alone, on the host (as sbd_offline_fit,
+ * with delta_max given): rho / alpha / M receive the circles (P Bessel terms, whose alpha
+ * are h's coefficients in the e_p basis, then the n_enforce terms of K: rho = omega_t,
+ * alpha = mu_t / J0(omega_t)); *w0_out receives c.  No GPU needed (the Cholesky may use one,
+ * see sbd_set_fit_device). */
+int sbd_offline_fit_radial(const sbd_radial_kernel* kernel, double delta_min, double delta_max, double eps,
+                           int32_t fixed_P, int64_t cap, double* rho, double* alpha, int32_t* M, int64_t* P_out,
+                           int64_t* n_circles_out, double* fit_err, double* w0_out);
 
 /* ---------------------------------------------------------------------------------
  * sbd_matvec - on-line part (Sec. 1 "On-line part"; Sec. 6.2; Eq. far convolution):

@@ -47,6 +47,17 @@ int raise_smem_limit_fn(const void* func, size_t bytes) {
     return SBD_OK;
 }
 
+RadialKernel radial_of(const sbd_radial_kernel& k) {
+    RadialKernel r;
+    r.value = k.value;
+    r.deriv = k.deriv;
+    r.laplacian = k.laplacian;
+    r.ctx = k.ctx;
+    r.log_coef = k.log_coef;
+    r.n_enforce = k.n_enforce;
+    return r;
+}
+
 }  // namespace sbd
 
 using namespace sbd;
@@ -346,7 +357,7 @@ int build_far(sbd_plan_s* p, cudaStream_t s) {
     }
     if (p->uniform) {
         // no quadrature nodes: the coefficients of the windowed series on the frequency grid
-        p->half_nodes = p->kind == SBD_LAPLACE;
+        p->half_nodes = p->kind != SBD_HELMHOLTZ;
         p->n_rec = 0;
         p->node_fused = false;
         const bool cc = p->kind == SBD_HELMHOLTZ;
@@ -373,7 +384,7 @@ int build_far(sbd_plan_s* p, cudaStream_t s) {
     // one at xi.  Only the nodes m < M_p / 2 of each circle (M_p is even) are stored;
     // the node step's output S over those nodes completes to S(eta) + conj(S(-eta)),
     // which the inverse transform folds into its load.
-    p->half_nodes = p->kind == SBD_LAPLACE;
+    p->half_nodes = p->kind != SBD_HELMHOLTZ;
     p->n_rec = fit.n_xi;
     if (p->half_nodes) {
         std::vector<int> hstart(fit.n_circles + 1, 0);
@@ -721,6 +732,38 @@ int sbd_offline_fit(sbd_kernel kernel, double delta_min, double delta_max, doubl
     return SBD_OK;
 }
 
+int sbd_offline_fit_radial(const sbd_radial_kernel* kernel, double delta_min, double delta_max, double eps,
+                           int32_t fixed_P, int64_t cap, double* rho, double* alpha, int32_t* M, int64_t* P_out,
+                           int64_t* n_circles_out, double* fit_err, double* w0_out) {
+    if (!kernel) {
+        set_error("sbd_offline_fit_radial: null kernel");
+        return SBD_EINVAL;
+    }
+    SbdFit fit;
+    std::string err;
+    const int rc = offline_fit_radial(radial_of(*kernel), delta_min, delta_max, eps, fixed_P, fit, err);
+    if (rc) {
+        set_error(err);
+        return rc;
+    }
+    if (cap < fit.n_circles) {
+        set_error("capacity below the number of circles");
+        return SBD_EINVAL;
+    }
+    for (int c = 0; c < fit.n_circles; ++c) {
+        const bool bessel = c < fit.P;
+        const int t = c - fit.P;
+        if (rho) rho[c] = bessel ? fit.rho[c] : fit.enf_omega[t];
+        if (alpha) alpha[c] = bessel ? fit.alpha[c] : fit.enf_mu[t] / bessel_j0(fit.enf_omega[t]);
+        if (M) M[c] = fit.M[c];
+    }
+    if (P_out) *P_out = fit.P;
+    if (n_circles_out) *n_circles_out = fit.n_circles;
+    if (fit_err) *fit_err = fit.fit_err;
+    if (w0_out) *w0_out = fit.w0.real();
+    return SBD_OK;
+}
+
 int sbd_transform_params(sbd_kernel kernel, double delta_min, double delta_max, double eps, int64_t n_points,
                          double half_extent, const sbd_options* opt, sbd_transform_stats* out) {
     sbd_options o{};
@@ -805,7 +848,8 @@ namespace {
 // The off-line part for sources `points` (n) and, when targets is non-null, separate targets
 // (n_t); targets null is the plan of one point set (D square, its diagonal the self pairs).
 int plan_impl(const double* targets, int64_t n_t, const double* points, int64_t n, sbd_kernel kernel,
-              double delta_min, double eps, const sbd_options* opt, void* cuda_stream, sbd_plan_t* out) {
+              double delta_min, double eps, const sbd_options* opt, void* cuda_stream, sbd_plan_t* out,
+              const RadialKernel* radial = nullptr) {
     const auto t0 = std::chrono::steady_clock::now();
     const bool separate = targets != nullptr;
     if (!points || !out || n < 1 || (separate && n_t < 1)) {
@@ -827,9 +871,13 @@ int plan_impl(const double* targets, int64_t n_t, const double* points, int64_t 
         set_error("sbd_plan: Helmholtz needs kappa > 0");
         return SBD_EINVAL;
     }
-    if (kernel.kind != SBD_LAPLACE && kernel.kind != SBD_HELMHOLTZ) {
+    if (kernel.kind != SBD_LAPLACE && kernel.kind != SBD_HELMHOLTZ && !(kernel.kind == SBD_RADIAL && radial)) {
         set_error("sbd_plan: unknown kernel");
         return SBD_EINVAL;
+    }
+    if (radial && (o.flags & SBD_FLAG_UNIFORM_GRID)) {
+        set_error("sbd_plan_radial: the uniform-grid variant takes the Laplace and Helmholtz kernels only");
+        return SBD_ENOTSUP;
     }
     if (!(eps >= 1e-10 && eps <= 0.1) || !(delta_min > 0)) {
         set_error("sbd_plan: need 1e-10 <= eps <= 0.1 and delta_min > 0");
@@ -907,7 +955,9 @@ int plan_impl(const double* targets, int64_t n_t, const double* points, int64_t 
         return fail(SBD_EINVAL);
     }
     std::string err;
-    if ((rc = offline_fit(kernel.kind, kernel.kappa, delta_min, delta_max, eps, o.fixed_P, p->fit, err))) {
+    rc = radial ? offline_fit_radial(*radial, delta_min, delta_max, eps, o.fixed_P, p->fit, err)
+                : offline_fit(kernel.kind, kernel.kappa, delta_min, delta_max, eps, o.fixed_P, p->fit, err);
+    if (rc) {
         set_error(err);
         return fail(rc);
     }
@@ -923,6 +973,7 @@ int plan_impl(const double* targets, int64_t n_t, const double* points, int64_t 
         set_error(err);
         return fail(rc);
     }
+    p->fit.radial = RadialKernel{};   // the callbacks are not called after the plan is built
     // near-field device tables
     const NearTables& nt = p->nt;
     if ((rc = upload(p, &p->T1, nt.T1, s))) return fail(rc);
@@ -946,6 +997,7 @@ int plan_impl(const double* targets, int64_t n_t, const double* points, int64_t 
     nd.pieces = nt.pieces;
     nd.deg = nt.deg;
     nd.tmax = nt.tmax;
+    nd.in_r = nt.in_r ? 1 : 0;
     nd.T1 = p->T1;
     nd.T2 = p->T2;
     nd.n_small = static_cast<int>(nt.small.size());
@@ -1004,6 +1056,18 @@ extern "C" {
 int sbd_plan(const double* points, int64_t n, sbd_kernel kernel, double delta_min, double eps,
              const sbd_options* opt, void* cuda_stream, sbd_plan_t* out) {
     return plan_impl(nullptr, 0, points, n, kernel, delta_min, eps, opt, cuda_stream, out);
+}
+
+int sbd_plan_radial(const double* points, int64_t n, const sbd_radial_kernel* kernel, double delta_min,
+                    double eps, const sbd_options* opt, void* cuda_stream, sbd_plan_t* out) {
+    if (!kernel) {
+        set_error("sbd_plan_radial: null kernel");
+        return SBD_EINVAL;
+    }
+    const RadialKernel rk = radial_of(*kernel);
+    sbd_kernel k{};
+    k.kind = SBD_RADIAL;
+    return plan_impl(nullptr, 0, points, n, k, delta_min, eps, opt, cuda_stream, out, &rk);
 }
 
 int sbd_plan_st(const double* targets, int64_t n_targets, const double* sources, int64_t n_sources,

@@ -259,6 +259,20 @@ double j0_root(int k) {
     return x;
 }
 
+double j1_root(int k) {
+    // McMahon's expansion (order 1) as the starting point, then Newton on J1 (J1' = J0 - J1 / x)
+    const double beta = (k + 0.25) * kPi;
+    double x = beta - 3.0 / (8.0 * beta);
+    for (int it = 0; it < 50; ++it) {
+        const double f = bessel_j1(x);
+        const double d = bessel_j0(x) - f / x;
+        const double dx = f / d;
+        x -= dx;
+        if (std::fabs(dx) < 1e-16 * x) break;
+    }
+    return x;
+}
+
 double y0_root(int k) {
     const double beta = (k - 0.75) * kPi;
     const double b8 = 8.0 * beta;

@@ -26,8 +26,9 @@ double bessel_y0_regular(double x);
 double bessel_jn_small(int n, double x);
 // J_M(x) for M in [m_lo, m_hi] (m_lo >= x - 1 allowed), into out[M - m_lo].
 void bessel_jn_range(double x, int m_lo, int m_hi, std::vector<double>& out);
-// k-th positive root of J0 (k >= 1), and of Y0.
+// k-th positive root of J0 (k >= 1), of J1, and of Y0.
 double j0_root(int k);
+double j1_root(int k);
 double y0_root(int k);
 // The first root of Y0 that is >= x.
 double y0_first_root_at_least(double x);

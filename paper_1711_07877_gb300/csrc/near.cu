@@ -153,10 +153,11 @@ __device__ double2 clenshaw2(const double* __restrict__ c, int deg, double tt) {
 
 __device__ double2 d_value(const NearDev& tb, double yx, double yy) {
     const double t = yx * yx + yy * yy;
+    const double u = tb.in_r ? sqrt(t) : t;          // the tables' variable
     const double w = tb.tmax / tb.pieces;
-    int q = static_cast<int>(t / w);
+    int q = static_cast<int>(u / w);
     q = min(q, tb.pieces - 1);
-    const double tt = 2.0 * (t / w - q) - 1.0;
+    const double tt = 2.0 * (u / w - q) - 1.0;
     const double2 a1 = clenshaw2(tb.T1 + static_cast<long>(q) * tb.deg * 2, tb.deg, tt);
     const double2 a2 = clenshaw2(tb.T2 + static_cast<long>(q) * tb.deg * 2, tb.deg, tt);
     const double lg = 0.5 * log(t);

@@ -12,7 +12,8 @@ namespace sbd {
 // t = |y|^2 (tables: piecewise Chebyshev in t, complex, [pieces][deg][2]).
 struct NearDev {
     int pieces, deg;
-    double tmax;
+    double tmax;              // table range in r^2, or in r when in_r
+    int in_r;
     const double* T1;
     const double* T2;
     int n_small;              // circles evaluated exactly

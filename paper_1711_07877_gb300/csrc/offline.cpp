@@ -114,6 +114,10 @@ void chol_solve(const std::vector<double>& L, int P, const double* b, std::vecto
 struct FitWork {
     int kind;
     double a, kp, extra;
+    // general radial kernel (kind 2): h(s) = G(R s) - K(s) - c with K(s) = sum_t kmu_t J0(kom_t s)
+    const RadialKernel* rk = nullptr;
+    double R = 0.0, c = 0.0;
+    std::vector<double> kom, kmu;
     int Pf = 0, Pok = 0;                 // factored size, usable leading size
     std::vector<double> rho, C, b, L;
     std::vector<double> s, gs;           // samples and g(s)
@@ -132,6 +136,19 @@ struct FitWork {
 
 
 void build_fit_lowrank(FitWork& w, int Pf);
+void radial_rhs(FitWork& w, int Pf);
+
+// h(s) and h'(s) of a general kernel's fit (kind 2)
+double radial_h(const FitWork& w, double s) {
+    double v = w.rk->value(w.R * s, w.rk->ctx) - w.c;
+    for (size_t t = 0; t < w.kom.size(); ++t) v -= w.kmu[t] * bessel_j0(w.kom[t] * s);
+    return v;
+}
+double radial_dh(const FitWork& w, double s) {
+    double v = w.R * w.rk->deriv(w.R * s, w.rk->ctx);
+    for (size_t t = 0; t < w.kom.size(); ++t) v += w.kmu[t] * w.kom[t] * bessel_j1(w.kom[t] * s);
+    return v;
+}
 
 void build_fit(FitWork& w, int Pf) {
     if (w.lowrank) {
@@ -150,7 +167,9 @@ void build_fit(FitWork& w, int Pf) {
         w.C[p] = 1.0 / (std::sqrt(kPi) * r * std::fabs(bessel_j1(r)));
         j0a[p] = bessel_j0(r * w.a);
         j1a[p] = bessel_j1(r * w.a);
-        if (w.kind == 0) {
+        if (w.kind == 2) {
+            // by quadrature below
+        } else if (w.kind == 0) {
             w.b[p] = -2.0 * kPi * w.C[p] * j0a[p];
         } else {
             const double kp = w.kp, a = w.a;
@@ -159,6 +178,7 @@ void build_fit(FitWork& w, int Pf) {
             w.b[p] = -2.0 * kPi * w.C[p] * r * kp * F;
         }
     }
+    if (w.kind == 2) radial_rhs(w, Pf);
     // Gram matrix A_ij = int_{A(a)} grad e_i . grad e_j (Sec. 3.2), packed lower
     w.L.assign(tri(Pf), 0.0);
     const double a = w.a;
@@ -225,7 +245,9 @@ void build_fit_lowrank(FitWork& w, int Pf) {
         w.rho[p] = r;
         w.C[p] = 1.0 / (std::sqrt(kPi) * r * std::fabs(bessel_j1(r)));
         const double j0a = bessel_j0(r * w.a), j1a = bessel_j1(r * w.a);
-        if (w.kind == 0) {
+        if (w.kind == 2) {
+            // by quadrature below
+        } else if (w.kind == 0) {
             w.b[p] = -2.0 * kPi * w.C[p] * j0a;
         } else {
             const double kp = w.kp, a = w.a;
@@ -233,6 +255,7 @@ void build_fit_lowrank(FitWork& w, int Pf) {
             w.b[p] = -2.0 * kPi * w.C[p] * r * kp * Fv;
         }
     }
+    if (w.kind == 2) radial_rhs(w, Pf);
     // the integrand s J1(rho_i s) J1(rho_j s) on [0, a] oscillates at most 2 rho_max a / (2 pi)
     // times: Q = rho_max a + 40 nodes (and at least 64) integrate it to rounding
     w.Q = std::max(64, static_cast<int>(std::ceil(w.rho[Pf - 1] * w.a)) + 40);
@@ -425,8 +448,88 @@ void fit_cache_clear() {
     c.hits = c.misses = 0;
 }
 
+namespace {
+int offline_fit_impl(int kind, double kappa, const RadialKernel* rk, double delta_min, double delta_max,
+                     double eps, int fixed_P, SbdFit& out, std::string& err);
+}
+
 int offline_fit(int kind, double kappa, double delta_min, double delta_max, double eps,
                 int fixed_P, SbdFit& out, std::string& err) {
+    if (kind != 0 && kind != 1) {
+        err = "unknown kernel kind";
+        return SBD_EINVAL;
+    }
+    return offline_fit_impl(kind, kappa, nullptr, delta_min, delta_max, eps, fixed_P, out, err);
+}
+
+int offline_fit_radial(const RadialKernel& k, double delta_min, double delta_max, double eps, int fixed_P,
+                       SbdFit& out, std::string& err) {
+    if (!k.value || !k.deriv || (k.n_enforce > 0 && !k.laplacian) || k.n_enforce < 0 || k.n_enforce > 8) {
+        err = "radial kernel: value and deriv callbacks, laplacian when n_enforce > 0, n_enforce in [0, 8]";
+        return SBD_EINVAL;
+    }
+    return offline_fit_impl(2, 0.0, &k, delta_min, delta_max, eps, fixed_P, out, err);
+}
+
+namespace {
+// Sec. 4.3 (the reading of the oracle's R14): lambda_j = Delta_s^j g(1) = R^(2j) (Delta^j G)(R),
+// omega' = sqrt of the mean |lambda_{j+1} / lambda_j|, omega_t = the roots of J1 nearest omega',
+// and mu solving sum_t (-1)^j omega_t^(2j) mu_t = lambda_j (j = 1..n) by Gaussian elimination
+// with partial pivoting; K(s) = sum_t mu_t J0(omega_t s) / J0(omega_t).
+int dirichlet_correction(const RadialKernel& k, double R, std::vector<double>& om, std::vector<double>& mu,
+                         std::string& err) {
+    const int n = k.n_enforce;
+    om.clear();
+    mu.clear();
+    if (n == 0) return SBD_OK;
+    std::vector<double> lam(n + 1);
+    for (int j = 1; j <= n + 1; ++j) lam[j - 1] = std::pow(R, 2.0 * j) * k.laplacian(j, R, k.ctx);
+    double sum = 0.0;
+    int cnt = 0;
+    for (int j = 0; j < n; ++j)
+        if (lam[j] != 0.0) {
+            sum += std::fabs(lam[j + 1] / lam[j]);
+            ++cnt;
+        }
+    const double wp = cnt ? std::sqrt(sum / cnt) : 1.0;
+    // roots of J1 around wp: the candidates k0 - n .. k0 + n, the n nearest in order
+    const int k0 = std::max(1, static_cast<int>(wp / kPi));
+    std::vector<double> cand;
+    for (int q = std::max(1, k0 - n - 1); q <= k0 + n + 1; ++q) cand.push_back(j1_root(q));
+    std::stable_sort(cand.begin(), cand.end(),
+                     [&](double x, double y) { return std::fabs(x - wp) < std::fabs(y - wp); });
+    om.assign(cand.begin(), cand.begin() + n);
+    std::sort(om.begin(), om.end());
+    std::vector<double> M(static_cast<size_t>(n) * n), rhs(lam.begin(), lam.begin() + n);
+    for (int j = 1; j <= n; ++j)
+        for (int t = 0; t < n; ++t) M[(j - 1) * n + t] = ((j & 1) ? -1.0 : 1.0) * std::pow(om[t], 2.0 * j);
+    for (int c = 0; c < n; ++c) {
+        int piv = c;
+        for (int r = c + 1; r < n; ++r)
+            if (std::fabs(M[r * n + c]) > std::fabs(M[piv * n + c])) piv = r;
+        if (M[piv * n + c] == 0.0) {
+            err = "radial kernel: singular Dirichlet correction system";
+            return SBD_EFIT;
+        }
+        for (int t = 0; t < n; ++t) std::swap(M[c * n + t], M[piv * n + t]);
+        std::swap(rhs[c], rhs[piv]);
+        for (int r = c + 1; r < n; ++r) {
+            const double f = M[r * n + c] / M[c * n + c];
+            for (int t = c; t < n; ++t) M[r * n + t] -= f * M[c * n + t];
+            rhs[r] -= f * rhs[c];
+        }
+    }
+    mu.assign(n, 0.0);
+    for (int c = n - 1; c >= 0; --c) {
+        double v = rhs[c];
+        for (int t = c + 1; t < n; ++t) v -= M[c * n + t] * mu[t];
+        mu[c] = v / M[c * n + c];
+    }
+    return SBD_OK;
+}
+
+int offline_fit_impl(int kind, double kappa, const RadialKernel* rk, double delta_min, double delta_max,
+                     double eps, int fixed_P, SbdFit& out, std::string& err) {
     if (!(delta_max > 0.0) || !(delta_min > 0.0) || !(delta_min < delta_max)) {
         err = "need 0 < delta_min < delta_max";
         return SBD_EINVAL;
@@ -435,7 +538,7 @@ int offline_fit(int kind, double kappa, double delta_min, double delta_max, doub
         err = "eps must lie in [1e-10, 0.1]";
         return SBD_EINVAL;
     }
-    if (kind != 0 && kind != 1) {
+    if (kind != 0 && kind != 1 && !(kind == 2 && rk)) {
         err = "unknown kernel kind";
         return SBD_EINVAL;
     }
@@ -458,7 +561,7 @@ int offline_fit(int kind, double kappa, double delta_min, double delta_max, doub
         f.w0 = -std::log(delta_max) / (2.0 * kPi);
         w.extra = 0.0;
         w.kp = 0.0;
-    } else {
+    } else if (kind == 1) {
         // (i/4) H0(kappa r) = (i/4) J0 - (1/4) Y0; Y0(kappa r) = Y0(k' r / R), R = k'/kappa  (Sec. 4.2)
         f.kprime = y0_first_root_at_least(kappa * delta_max);
         f.scale_R = f.kprime / kappa;
@@ -466,6 +569,30 @@ int offline_fit(int kind, double kappa, double delta_min, double delta_max, doub
         f.w0 = 0.0;
         w.extra = 2.0 * f.kprime;
         w.kp = f.kprime;
+    } else {
+        // general radial kernel (Sec. 4.3): h = g - K - c fitted in kernel units, c at xi = 0
+        f.radial = *rk;
+        f.scale_R = delta_max;
+        f.gscale = 1.0;
+        int rc = dirichlet_correction(*rk, delta_max, f.enf_omega, f.enf_mu, err);
+        if (rc) return rc;
+        w.rk = &f.radial;
+        w.R = delta_max;
+        w.kom = f.enf_omega;
+        w.kmu.resize(f.enf_mu.size());
+        double k1 = 0.0;
+        for (size_t t = 0; t < f.enf_mu.size(); ++t) {
+            w.kmu[t] = f.enf_mu[t] / bessel_j0(f.enf_omega[t]);
+            k1 += f.enf_mu[t];                      // K(1)
+        }
+        w.c = rk->value(delta_max, rk->ctx) - k1;
+        if (!std::isfinite(w.c)) {
+            err = "radial kernel: G(delta_max) or its iterates are not finite";
+            return SBD_EINVAL;
+        }
+        f.w0 = w.c;
+        w.extra = f.enf_omega.empty() ? 0.0 : 2.0 * f.enf_omega.back();
+        w.kp = 0.0;
     }
     f.a = delta_min / f.scale_R;
     w.a = f.a;
@@ -477,14 +604,14 @@ int offline_fit(int kind, double kappa, double delta_min, double delta_max, doub
         fit_samples(f.a, w.extra, w.s);
         w.gs.resize(w.s.size());
         for (size_t i = 0; i < w.s.size(); ++i)
-            w.gs[i] = kind == 0 ? std::log(w.s[i]) : bessel_y0(w.kp * w.s[i]);
+            w.gs[i] = kind == 0 ? std::log(w.s[i]) : kind == 1 ? bessel_y0(w.kp * w.s[i]) : radial_h(w, w.s[i]);
     };
 
     std::vector<double> alpha;
     int P;
     double e;
     const FitKey key = fit_key(kind, w.kp, f.a, eps, fixed_P);
-    if (fit_cache_get(key, P, f.rho, f.C, alpha, e)) {
+    if (kind != 2 && fit_cache_get(key, P, f.rho, f.C, alpha, e)) {
         // the search below would give the same normalised fit
     } else if (fixed_P > 0) {
         prepare_samples();
@@ -518,17 +645,36 @@ int offline_fit(int kind, double kappa, double delta_min, double delta_max, doub
             return v;
         };
         int lo, hi;
-        int Pc = std::max(1, P_start);
+        // start no higher than the factor reaches: near the Gram conditioning floor (Sec. 3.3)
+        // the larger factorisation stops early, and the search then proceeds from below
+        int Pc = std::max(1, std::min(P_start, w.Pok));
         if (err_of(Pc) > tol_g) {
             lo = Pc;
             hi = static_cast<int>(std::ceil(Pc * 1.1));
+            bool found = true;
             while (err_of(hi) > tol_g) {
                 if (hi >= P_max || (w.Pok < w.Pf && hi > w.Pok)) {
-                    err = "the SBD fit does not reach the tolerance (conditioning floor ~1e-10, Sec. 4.1)";
-                    return SBD_EFIT;
+                    found = false;
+                    break;
                 }
                 lo = hi;
                 hi = std::min(P_max, static_cast<int>(std::ceil(hi * 1.1)));
+            }
+            if (!found) {
+                // at the conditioning floor the error stops falling with P (Sec. 3.3): a smaller P
+                // whose rounding is lower may still pass; scan down from the start in small steps
+                const int step = std::max(1, Pc / 32);
+                hi = -1;
+                for (int q = Pc - step; q >= 1 && q >= Pc / 2; q -= step)
+                    if (err_of(q) <= tol_g) {
+                        hi = q;
+                        lo = std::max(0, q - step);
+                        break;
+                    }
+                if (hi < 0) {
+                    err = "the SBD fit does not reach the tolerance (conditioning floor ~1e-10, Sec. 4.1)";
+                    return SBD_EFIT;
+                }
             }
         } else {
             hi = Pc;
@@ -551,7 +697,7 @@ int offline_fit(int kind, double kappa, double delta_min, double delta_max, doub
     if (static_cast<int>(f.rho.size()) != P) {   // computed here, not taken from the cache
         f.rho.assign(w.rho.begin(), w.rho.begin() + P);
         f.C.assign(w.C.begin(), w.C.begin() + P);
-        fit_cache_put(key, P, f.rho, f.C, alpha, e);
+        if (kind != 2) fit_cache_put(key, P, f.rho, f.C, alpha, e);
     }
     f.P = P;
     f.alpha = alpha;
@@ -560,7 +706,8 @@ int offline_fit(int kind, double kappa, double delta_min, double delta_max, doub
     f.fit_err_g = e;
     f.fit_err = e * std::fabs(f.gscale);
     // circular quadrature sizes (Sec. 5) and weights omega_hat = alpha_p C_p / M_p (Sec. 6.2)
-    f.n_circles = P + (kind == 1 ? 1 : 0);
+    const int n_enf = static_cast<int>(f.enf_omega.size());
+    f.n_circles = P + (kind == 1 ? 1 : 0) + n_enf;
     const double tol_c = (eps / 3.0) / f.n_circles;
     f.M.assign(f.n_circles, 0);
     f.radius.assign(f.n_circles, 0.0);
@@ -578,11 +725,20 @@ int offline_fit(int kind, double kappa, double delta_min, double delta_max, doub
         f.radius[P] = kappa;
         f.weight[P] = cplx(0.0, 0.25 / Mj);
     }
+    for (int t = 0; t < n_enf; ++t) {
+        // K's terms: mu_t / J0(omega_t) J0(omega_t r / delta_max), exact circles (Sec. 1 identity)
+        const double wt = f.enf_mu[t] / bessel_j0(f.enf_omega[t]);
+        const int Mt = circle_size(f.enf_omega[t], std::fabs(wt), tol_c);
+        f.M[P + t] = Mt;
+        f.radius[P + t] = f.enf_omega[t] / delta_max;
+        f.weight[P + t] = wt / Mt;
+    }
     f.n_xi = 0;
     for (int c = 0; c < f.n_circles; ++c) f.n_xi += f.M[c];
     out = std::move(f);
     return SBD_OK;
 }
+}  // namespace
 
 // Gauss-Legendre nodes and weights on [-1, 1] (Newton on P_n from Tricomi's guess).
 static void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w);
@@ -619,6 +775,48 @@ static void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w
         w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
     }
 }
+
+namespace {
+// Composite 24-point Gauss-Legendre rule on [a, b], panels of length <= h growing from a (each
+// twice the previous, starting at min(h, a)), so that integrands singular at 0 stay resolved.
+void composite_gl(double a, double b, double h, std::vector<double>& s, std::vector<double>& wt) {
+    std::vector<double> x, w;
+    gauss_legendre(24, x, w);
+    s.clear();
+    wt.clear();
+    double lo = a, step = a > 0.0 ? std::min(h, a) : h;
+    while (lo < b) {
+        const double hi = std::min(b, lo + step);
+        const double mid = 0.5 * (lo + hi), half = 0.5 * (hi - lo);
+        for (int k = 0; k < 24; ++k) {
+            s.push_back(mid + half * x[k]);
+            wt.push_back(half * w[k]);
+        }
+        lo = hi;
+        step = std::min(h, 2.0 * step);
+    }
+}
+}  // namespace
+
+namespace {
+// b_p = int_{A(a)} grad h . grad e_p = -2 pi C_p rho_p int_a^1 s h'(s) J1(rho_p s) ds for p < Pf
+// (Eq. LinearSystem's right-hand side), by the composite rule: the integrand oscillates with
+// angular frequency <= rho_max + the correction's largest frequency, and a 24-point panel
+// spanning about one period integrates it to rounding.
+void radial_rhs(FitWork& w, int Pf) {
+    const double fmax = w.rho[Pf - 1] + 0.5 * w.extra;
+    std::vector<double> sq, wq;
+    composite_gl(w.a, 1.0, std::min(0.125, 3.0 / fmax), sq, wq);
+    std::vector<double> hw(sq.size());
+    for (size_t k = 0; k < sq.size(); ++k) hw[k] = wq[k] * sq[k] * radial_dh(w, sq[k]);
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int p = 0; p < Pf; ++p) {
+        double acc = 0.0;
+        for (size_t k = 0; k < sq.size(); ++k) acc += hw[k] * bessel_j1(w.rho[p] * sq[k]);
+        w.b[p] = -2.0 * kPi * w.C[p] * w.rho[p] * acc;
+    }
+}
+}  // namespace
 
 // Fourier transform of the ES window on [-1, 1]: int exp(beta (sqrt(1 - z^2) - 1)) cos(k z) dz,
 // with z = sin(theta) so the integrand is smooth.
@@ -950,7 +1148,9 @@ int uniform_params(const SbdFit& fit, double half_extent, double cx, double cy, 
 
 int near_tables(const SbdFit& fit, NearTables& o, std::string& err, bool radial) {
     const double dmin = fit.delta_min;
-    o.tmax = dmin * dmin;
+    // tables in t = r^2 (the kernels' smooth parts are even in r), or in r for a general kernel
+    o.in_r = fit.kind == 2;
+    o.tmax = o.in_r ? dmin : dmin * dmin;
     double scale = std::abs(fit.w0);
     for (int p = 0; p < fit.P; ++p) scale += std::fabs(fit.coef[p]);
     scale = std::max(1.0, scale);
@@ -971,13 +1171,21 @@ int near_tables(const SbdFit& fit, NearTables& o, std::string& err, bool radial)
     }
     std::vector<char> is_small(fit.n_circles, 0);
     for (int c : o.small) is_small[c] = 1;
-    auto T1f = [&](double t) -> cplx {
+    auto T1f = [&](double u) -> cplx {
         if (fit.kind == 0) return -1.0 / (2.0 * kPi);
-        return -bessel_j0(fit.kappa * std::sqrt(t)) / (2.0 * kPi);
+        if (fit.kind == 2) return fit.radial.log_coef;
+        return -bessel_j0(fit.kappa * std::sqrt(u)) / (2.0 * kPi);
     };
-    auto T2f = [&](double t) -> cplx {
-        const double r = std::sqrt(t);
+    auto T2f = [&](double u) -> cplx {
+        const double r = o.in_r ? u : std::sqrt(u);
         cplx v = 0.0;
+        if (fit.kind == 2) {
+            // G - c log r, smooth at 0, minus the series of every circle not summed exactly
+            v = fit.radial.value(r, fit.radial.ctx) - fit.radial.log_coef * std::log(r) - fit.w0;
+            for (int c = 0; c < fit.n_circles; ++c)
+                if (!is_small[c]) v -= fit.weight[c] * static_cast<double>(fit.M[c]) * bessel_j0(fit.radius[c] * r);
+            return v;
+        }
         if (fit.kind == 0) {
             v = -fit.w0;
         } else {

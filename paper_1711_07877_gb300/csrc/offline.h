@@ -9,8 +9,21 @@ namespace sbd {
 
 using cplx = std::complex<double>;
 
+// A general real radial kernel (Sec. 4.3) given on the host by callbacks, which are called
+// only while a plan is built: value(r) = G(r) and deriv(r) = G'(r) for r > 0, laplacian(j, r)
+// = (Delta^j G)(r) for j >= 1 (Delta the radial Laplacian), log_coef = c with G - c log r
+// smooth at 0, and n_enforce the number of iterates the multi-Dirichlet correction enforces.
+struct RadialKernel {
+    double (*value)(double r, void* ctx) = nullptr;
+    double (*deriv)(double r, void* ctx) = nullptr;
+    double (*laplacian)(int j, double r, void* ctx) = nullptr;
+    void* ctx = nullptr;
+    double log_coef = 0.0;
+    int n_enforce = 0;
+};
+
 struct SbdFit {
-    int kind = 0;            // 0 Laplace, 1 Helmholtz
+    int kind = 0;            // 0 Laplace, 1 Helmholtz, 2 general radial (Sec. 4.3)
     double kappa = 0.0;
     double eps = 0.0;
     double delta_min = 0.0, delta_max = 0.0;
@@ -29,6 +42,10 @@ struct SbdFit {
     double fit_err_g = 0.0;              // L_inf fit error of g on the sample set
     double fit_err = 0.0;                // the same in kernel units
     long long n_xi = 0;                  // sum M
+    // general radial kernel: the callbacks (valid while the plan is built) and the correction
+    // K(s) = sum_t enf_mu_t J0(enf_omega_t s) / J0(enf_omega_t), s = r / scale_R (Sec. 4.3)
+    RadialKernel radial;
+    std::vector<double> enf_omega, enf_mu;
 };
 
 // The Gram matrix of Eq. LinearSystem built and Cholesky-factored on the GPU (fit_gpu.cu):
@@ -44,6 +61,13 @@ void set_fit_device(int mode);
 int fit_device_mode();
 // Seconds of the last full factorisation and where it ran (1 host, 2 device); for tests.
 void last_factorisation(double* seconds, int* where);
+
+// The fit of a general real radial kernel (Sec. 4.3 with Sec. 3): the correction K and the
+// constant c enforce the multi-Dirichlet condition up to order n_enforce at r = delta_max, the
+// SBD fits h = g - K - c (g(s) = G(delta_max s)); circles: P Bessel terms, then the n_enforce
+// terms of K; w0 = c.  Not cached (the callbacks are arbitrary).
+int offline_fit_radial(const RadialKernel& k, double delta_min, double delta_max, double eps, int fixed_P,
+                       SbdFit& out, std::string& err);
 
 // Key of the normalised-fit cache used by offline_fit (see offline.cpp).
 struct FitKey {
@@ -134,7 +158,8 @@ int good_fft_size(int n);
 // t = |y|^2 in [0, delta_min^2]; T1, T2 piecewise Chebyshev in t (complex, re/im interleaved).
 struct NearTables {
     int pieces = 0, deg = 0;
-    double tmax = 0.0;
+    double tmax = 0.0;               // table range: r^2 in [0, tmax], or r in [0, tmax] when in_r
+    bool in_r = false;               // tables in r (general kernels, whose smooth part may be odd in r)
     std::vector<double> T1, T2;      // [pieces][deg][2]
     std::vector<int> small;          // circles whose plane-wave sum is evaluated exactly
     cplx self_value = 0.0;           // D_kk = -G_approx(0)

@@ -15,7 +15,7 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(PKG, "libsbd.so")
 
 SBD_OK, SBD_EINVAL, SBD_ENOMEM, SBD_ECUDA, SBD_EFIT, SBD_ETIMEOUT, SBD_ENOTSUP = 0, -1, -2, -3, -4, -5, -6
-SBD_LAPLACE, SBD_HELMHOLTZ = 0, 1
+SBD_LAPLACE, SBD_HELMHOLTZ, SBD_RADIAL = 0, 1, 2
 SBD_FORM_FP64, SBD_FORM_FP32 = 0, 1
 
 
@@ -27,6 +27,29 @@ class SbdError(RuntimeError):
 
 class sbd_kernel(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("kappa", ctypes.c_double)]
+
+
+RADIAL_VALUE = ctypes.CFUNCTYPE(ctypes.c_double, ctypes.c_double, ctypes.c_void_p)
+RADIAL_LAPLACIAN = ctypes.CFUNCTYPE(ctypes.c_double, ctypes.c_int32, ctypes.c_double, ctypes.c_void_p)
+
+
+class sbd_radial_kernel(ctypes.Structure):
+    _fields_ = [("value", RADIAL_VALUE), ("deriv", RADIAL_VALUE), ("laplacian", RADIAL_LAPLACIAN),
+                ("ctx", ctypes.c_void_p), ("log_coef", ctypes.c_double), ("n_enforce", ctypes.c_int32)]
+
+
+def radial_kernel(value, deriv, laplacian=None, log_coef: float = 0.0, n_enforce: int = 0) -> sbd_radial_kernel:
+    """sbd_radial_kernel from Python callables value(r), deriv(r), laplacian(j, r) (floats in, float
+    out).  Keep the returned object alive while a plan is built with it."""
+    k = sbd_radial_kernel()
+    k._keep = (RADIAL_VALUE(lambda r, _c: float(value(r))), RADIAL_VALUE(lambda r, _c: float(deriv(r))),
+               RADIAL_LAPLACIAN(lambda j, r, _c: float(laplacian(j, r))) if laplacian is not None
+               else RADIAL_LAPLACIAN())
+    k.value, k.deriv, k.laplacian = k._keep
+    k.ctx = None
+    k.log_coef = log_coef
+    k.n_enforce = n_enforce
+    return k
 
 
 class sbd_options(ctypes.Structure):
@@ -99,6 +122,10 @@ _SIGS = {
     "sbd_plan": ([_P, _I64, sbd_kernel, _D, _D, ctypes.POINTER(sbd_options), _P, ctypes.POINTER(_P)], ctypes.c_int),
     "sbd_plan_st": ([_P, _I64, _P, _I64, sbd_kernel, _D, _D, ctypes.POINTER(sbd_options), _P, ctypes.POINTER(_P)],
                     ctypes.c_int),
+    "sbd_plan_radial": ([_P, _I64, ctypes.POINTER(sbd_radial_kernel), _D, _D, ctypes.POINTER(sbd_options), _P,
+                         ctypes.POINTER(_P)], ctypes.c_int),
+    "sbd_offline_fit_radial": ([ctypes.POINTER(sbd_radial_kernel), _D, _D, _D, _I32, _I64, _P, _P, _P, _P, _P,
+                                _P, _P], ctypes.c_int),
     "sbd_matvec": ([_P, _P, _P, _I32, _P], ctypes.c_int),
     "sbd_matvec_graph": ([_P, _P, _P, _I32, _P], ctypes.c_int),
     "sbd_batch_create": ([_P, _P, _I32, _P, _P, ctypes.POINTER(_P)], ctypes.c_int),
@@ -198,6 +225,33 @@ def sbd_plan(points, n: int, kernel_kind: int, kappa: float, delta_min: float, e
                       ctypes.byref(options) if options is not None else None, _stream(stream), ctypes.byref(out))
     _check(rc, "sbd_plan")
     return out.value
+
+
+def sbd_plan_radial(points, n: int, kernel: sbd_radial_kernel, delta_min: float, eps: float,
+                    options: sbd_options | None = None, stream=None) -> int:
+    """A plan for a general real radial kernel (Sec. 4.3), kernel from radial_kernel()."""
+    out = _P()
+    rc = lib.sbd_plan_radial(_ptr(points), n, ctypes.byref(kernel), delta_min, eps,
+                             ctypes.byref(options) if options is not None else None, _stream(stream),
+                             ctypes.byref(out))
+    _check(rc, "sbd_plan_radial")
+    return out.value
+
+
+def sbd_offline_fit_radial(kernel: sbd_radial_kernel, delta_min: float, delta_max: float, eps: float,
+                           fixed_P: int = 0, cap: int = 40000) -> dict:
+    """Host-only fit of a general radial kernel: dict(P, n_circles, rho, alpha, M, fit_err, w0); the
+    circles after the first P are the correction's terms (rho = omega_t, alpha = mu_t / J0(omega_t))."""
+    import numpy as np
+    rho, alpha = np.zeros(cap), np.zeros(cap)
+    M = np.zeros(cap, dtype=np.int32)
+    P, nc, err, w0 = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_double(), ctypes.c_double()
+    _check(lib.sbd_offline_fit_radial(ctypes.byref(kernel), delta_min, delta_max, eps, fixed_P, cap, rho.ctypes.data,
+                                      alpha.ctypes.data, M.ctypes.data, ctypes.byref(P), ctypes.byref(nc),
+                                      ctypes.byref(err), ctypes.byref(w0)), "sbd_offline_fit_radial")
+    k = nc.value
+    return {"P": P.value, "n_circles": k, "rho": rho[:k].copy(), "alpha": alpha[:k].copy(), "M": M[:k].copy(),
+            "fit_err": err.value, "w0": w0.value}
 
 
 def sbd_plan_st(targets, n_targets: int, sources, n_sources: int, kernel_kind: int, kappa: float,

@@ -1,0 +1,137 @@
+"""GPU parity of general real radial kernels (sbd_plan_radial, Sec. 4.3) against the oracle.
+
+Kernel: G(r) = log r + J0(beta r) + r^2 / 2 (its radial-Laplacian iterates in closed form), with
+n iterates enforced.  The plan and the oracle (make_plan_radial) use the same P (fixed_P).
+Bars, as for the Laplace and Helmholtz kernels:
+  * FP64 form (transforms at 1e-13) vs the oracle SBD: rel-L2 <= 1e-10;
+  * FP32 form vs the oracle SBD: rel-L2 and max|dq| / max|q| <= 1e-6;
+  * both vs the direct sum: max |q - q*| <= eps sum|f| (Sec. 1 bound);
+  * D against the oracle's G - G_approx with the plan's own circles: within 1e-11 of max|D|.
+"""
+import dataclasses
+import math
+
+import numpy as np
+import pytest
+from scipy.special import j0, j1
+
+import workloads as W
+from oracle import sbd_oracle as O
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def S():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1711_07877_gb300 import build
+    build.build_library()
+    import paper_1711_07877_gb300 as pkg
+    return pkg
+
+
+def kernel_a(beta):
+    value = lambda r: np.log(r) + j0(beta * r) + 0.5 * np.square(r)  # noqa: E731
+    deriv = lambda r: 1.0 / np.asarray(r) - beta * j1(beta * r) + np.asarray(r)  # noqa: E731
+    lap = lambda j, r: (-beta * beta) ** j * j0(beta * r) + (2.0 if j == 1 else 0.0)  # noqa: E731
+    return value, deriv, lap
+
+
+def dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def plan(S, z, beta, n, dmin, eps, form, fixed_P=0, nufft_tol=0.0):
+    value, deriv, lap = kernel_a(beta)
+    ck = S.radial_kernel(value, deriv, lap, 1.0, n)
+    p = S.sbd_plan_radial(dev(z), len(z), ck, dmin, eps,
+                          S.make_options(form=form, fixed_P=fixed_P, nufft_tol=nufft_tol))
+    torch.cuda.synchronize()
+    return p
+
+
+def run(S, p, f):
+    ft = dev(f)
+    q = torch.empty_like(ft)
+    S.sbd_matvec(p, ft, q)
+    torch.cuda.synchronize()
+    return q.cpu().numpy()
+
+
+@pytest.fixture(scope="module", params=[(9.0, 2), (30.0, 3)])
+def case(request):
+    beta, n = request.param
+    z = W.disk_points(1500, 31)
+    f = W.rhs(1500, 32)
+    dmin = math.sqrt(20 / 1500)
+    kern = O.RadialKernel(*kernel_a(beta), 1.0)
+    pl = O.make_plan_radial(z, kern, dmin, 1e-6, n_enforce=n)
+    return beta, n, z, f, dmin, kern, pl, O.sbd_matvec(pl, f), O.direct_sum(z, f, kern)
+
+
+@pytest.mark.parametrize("form", [0, 1])
+def test_radial_matches_oracle_sbd(S, case, form):
+    beta, n, z, f, dmin, kern, pl, q_sbd, q_dir = case
+    p = plan(S, z, beta, n, dmin, 1e-6, form, fixed_P=pl.P, nufft_tol=1e-13 if form == 0 else 0.0)
+    try:
+        info = S.sbd_plan_info(p)
+        assert info["P"] == pl.P and info["n_circles"] == pl.P + n and info["kind"] == S.SBD_RADIAL
+        q = run(S, p, f)
+        rel = np.linalg.norm(q - q_sbd) / np.linalg.norm(q_sbd)
+        worst = np.max(np.abs(q - q_sbd)) / np.max(np.abs(q_sbd))
+        if form == 0:
+            assert rel <= 1e-10, rel
+        else:
+            assert rel <= 1e-6 and worst <= 1e-6, (rel, worst)
+        assert np.max(np.abs(q - q_dir)) <= 1e-6 * np.abs(f).sum()
+    finally:
+        S.sbd_destroy(p)
+
+
+def test_radial_close_matrix_with_plan_weights(S, case):
+    beta, n, z, f, dmin, kern, pl, _, _ = case
+    k, l = O.near_pairs(z, dmin * (1 + 1e-9))
+    r2 = np.sum((z[k] - z[l]) ** 2, axis=1)
+    assert np.all(np.abs(r2 / dmin ** 2 - 1) > 1e-12), "reseed: a pair sits on the delta_min boundary"
+    p = plan(S, z, beta, n, dmin, 1e-6, 0)
+    try:
+        ex = S.sbd_plan_export(p)
+        info = S.sbd_plan_info(p)
+        w0 = complex(info["w0_re"], info["w0_im"])
+        xi = [np.zeros((1, 2))]
+        om = [np.array([w0])]
+        for rad, M, w in zip(ex["radius"], ex["M"], ex["weight"]):
+            xi.append(O.circle_nodes(float(rad), int(M)))
+            om.append(np.full(int(M), w, dtype=np.complex128))
+        pl2 = dataclasses.replace(pl, xi=np.concatenate(xi), omega=np.concatenate(om), D=None)
+        rowptr, col, val = S.sbd_close_export(p)
+        rows, cols, vals = O.close_matrix(pl2)
+        got = {(kk, int(col[j])): val[j] for kk in range(len(z)) for j in range(rowptr[kk], rowptr[kk + 1])}
+        want = {(int(a), int(b)): v.real for a, b, v in zip(rows, cols, vals)}
+        assert set(got) == set(want)
+        scale = max(abs(v) for v in want.values())
+        assert max(abs(got[q] - want[q]) for q in want) <= 1e-11 * scale
+    finally:
+        S.sbd_destroy(p)
+
+
+def test_radial_curves_sampled_against_direct_sum(S):
+    """The curve family at N = 2 10^5, FP32 form, automatic P: 300 sampled outputs against the
+    oracle's direct sum over all sources."""
+    n = 200_000
+    z = W.curve_points(n, 33)
+    f = W.rhs(n, 34)
+    dmin = W.theorem1_delta_min(n, 1e-6, W.enclosing_diameter(z))
+    p = plan(S, z, 5.0, 2, dmin, 1e-6, 1)
+    try:
+        S.sbd_tune(p, 1)
+        q = run(S, p, f)
+        kern = O.RadialKernel(*kernel_a(5.0), 1.0)
+        idx = np.random.default_rng(35).choice(n, 300, replace=False)
+        qd = O.direct_sum(z, f, kern, targets=idx, chunk=32)
+        assert np.max(np.abs(q[idx] - qd)) <= 1e-6 * np.abs(f).sum()
+        assert np.linalg.norm(q[idx] - qd) / np.linalg.norm(qd) <= 1e-6
+    finally:
+        S.sbd_destroy(p)
