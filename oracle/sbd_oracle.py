@@ -50,6 +50,15 @@ design notes):
       node.  omega' = sqrt of the mean |lambda_{j+1} / lambda_j| over
       j = 1..n (n + 1 iterates); omega_1..omega_n are the roots of J1 nearest
       omega', nearest first.  The SBD then fits h = g - K - c.
+  R15 Low-wavenumber Helmholtz (Sec. 4.2, third case, with the Dini series of
+      Sec. 2.3): used when kappa delta_max is below half the first root of Y0
+      (where the first-root scaling of R9 would stretch R beyond 2 delta_max).
+      g(s) = Y0(k s), k = kappa delta_max, fitted on (a, 1) in the Dini basis
+      e_p = C_p J0(rho_p s), rho_p the positive roots of rho J1(rho) = H J0(rho)
+      (rho J0'(rho) + H J0(rho) = 0), H = k Y1(k) / Y0(k) (> 0 there), C_p
+      normalising e_p in a_H(u, v) = int_B grad u . grad v + H int_C u v.  The
+      coefficients minimise the same form restricted to the annulus: the
+      gradient term over A(a) plus the boundary term H int_C at r = 1.
 """
 from __future__ import annotations
 
@@ -285,20 +294,22 @@ def initial_P(a: float, tol: float, extra_freq: float = 0.0) -> int:
 
 
 def choose_P(g, g_prime, a: float, tol: float, P_start: int, extra_freq: float = 0.0,
-             P_max: int = 20000):
+             P_max: int = 20000, coefficients=None):
     """A P whose fit error is <= tol, by bracketing then dichotomy (Sec. 1).
 
     Bracket: from P_start, grow by factors 1.1 (ceil) while the error is above tol,
     or shrink by factors 0.9 (floor) while it is below.  Dichotomy on the bracket
     (lo fails, hi passes) until hi - lo <= max(1, hi // 128): the smallest
     passing P when P < 256, within 1% above it beyond.
+    ``coefficients(P)`` replaces the Dirichlet fit (the Robin basis of R15).
     Returns (P, rho, C, alpha, err).
     """
     cache = {}
 
     def err_of(P):
         if P not in cache:
-            rho, C, alpha = sbd_coefficients(g_prime, a, P, extra_freq)
+            rho, C, alpha = (coefficients(P) if coefficients is not None
+                             else sbd_coefficients(g_prime, a, P, extra_freq))
             cache[P] = (fit_linf_error(g, rho, C, alpha, a, extra_freq), rho, C, alpha)
         return cache[P][0]
 
@@ -323,6 +334,59 @@ def choose_P(g, g_prime, a: float, tol: float, P_start: int, extra_freq: float =
             lo = mid
     e, rho, C, alpha = cache[hi]
     return hi, rho, C, alpha, e
+
+
+# ---------------------------------------------------------------------------
+# Robin boundary condition: the Dini series (Sec. 2.3) for low-wavenumber Helmholtz (Sec. 4.2, R15)
+# ---------------------------------------------------------------------------
+
+def robin_applies(k: float) -> bool:
+    """R15: the Dini series of Y0(k s) is used when k = kappa delta_max is below half the first
+    root of Y0."""
+    return k < 0.5 * float(sp.y0_zeros(1)[0][0].real)
+
+
+def robin_H(k: float) -> float:
+    """H = -k Y0'(k) / Y0(k) = k Y1(k) / Y0(k): the Robin constant that Y0(k s) satisfies at s = 1
+    (Sec. 4.2)."""
+    return float(k * sp.y1(k) / sp.y0(k))
+
+
+def dini_roots(H: float, P: int) -> np.ndarray:
+    """The first P positive roots of rho J0'(rho) + H J0(rho) = 0, i.e. rho J1(rho) = H J0(rho)
+    (Sec. 2.3), H > 0: the p-th lies between the (p-1)-th root of J1 (0 for p = 1) and the p-th
+    root of J0, where the function changes sign; brentq on each bracket."""
+    from scipy.optimize import brentq
+    f = lambda x: x * sp.j1(x) - H * sp.j0(x)  # noqa: E731
+    j1z = np.concatenate([[0.0], sp.jn_zeros(1, P)])
+    j0z = sp.jn_zeros(0, P)
+    return np.array([brentq(f, j1z[p], j0z[p], xtol=1e-15, rtol=1e-15, maxiter=200) for p in range(P)])
+
+
+def dini_C(rho: np.ndarray, H: float) -> np.ndarray:
+    """C_p with a_H(e_p, e_p) = 1 (Sec. 2.3): 1 / C_p^2 = 2 pi (rho_p^2 int_0^1 s J1(rho_p s)^2 ds
+    + H J0(rho_p)^2), the integral by Gauss-Legendre quadrature of its definition."""
+    s, w = gauss_legendre(0.0, 1.0, _panel_length(float(rho.max())))
+    J = sp.j1(rho[:, None] * s[None, :])
+    integ = (J * J * (w * s)[None, :]).sum(axis=1)
+    return 1.0 / np.sqrt(TWO_PI * (rho * rho * integ + H * sp.j0(rho) ** 2))
+
+
+def robin_coefficients(g, g_prime, a: float, P: int, H: float, extra_freq: float = 0.0):
+    """Coefficients of g in the Dini basis e_p = C_p J0(rho_p s) (R15): the minimiser of
+    int_{A(a)} |grad(g - sum t_p e_p)|^2 + H int_C (g - sum t_p e_p)^2, by Cholesky of its Gram
+    matrix (quadrature of the gradient term, the boundary term 2 pi H e_p(1) e_q(1))."""
+    rho = dini_roots(H, P)
+    C = dini_C(rho, H)
+    s, w = gauss_legendre(a, 1.0, _panel_length(float(rho.max()), extra_freq))
+    B = (C * rho)[:, None] * sp.j1(rho[:, None] * s[None, :])
+    A = TWO_PI * (B * (w * s)[None, :]) @ B.T
+    e1 = C * sp.j0(rho)
+    A += TWO_PI * H * np.outer(e1, e1)
+    b = -TWO_PI * (B * (w * s * g_prime(s))[None, :]).sum(axis=1) + TWO_PI * H * float(g(1.0)) * e1
+    L = np.linalg.cholesky(A)
+    alpha = sla.solve_triangular(L.T, sla.solve_triangular(L, b, lower=True), lower=False)
+    return rho, C, alpha
 
 
 # ---------------------------------------------------------------------------
@@ -407,6 +471,15 @@ def make_plan(z: np.ndarray, kind: str, delta_min: float, eps: float, kappa: flo
         gscale = -1.0 / TWO_PI
         extra = 0.0
         w0 = complex(-math.log(delta_max) / TWO_PI)      # G(delta_max): the xi = 0 term (Sec. 1)
+    elif kind == "helmholtz" and robin_applies(kappa * delta_max):
+        # low wavenumber: Dini series of Y0(k s), k = kappa delta_max, on (a, 1)  (R15)
+        k = kappa * delta_max
+        scale_R = delta_max
+        g = lambda s: sp.y0(k * s)  # noqa: E731
+        g_prime = lambda s: -k * sp.y1(k * s)  # noqa: E731
+        gscale = -0.25
+        extra = 2.0 * k
+        w0 = 0.0j
     elif kind == "helmholtz":
         kp = y0_first_root_at_least(kappa * delta_max)   # k' (Sec. 4.2)
         scale_R = kp / kappa
@@ -419,12 +492,17 @@ def make_plan(z: np.ndarray, kind: str, delta_min: float, eps: float, kappa: flo
         raise ValueError(kind)
     a = delta_min / scale_R
     tol_fit = eps_fit / abs(gscale)
+    robin = kind == "helmholtz" and robin_applies(kappa * delta_max)
+    coefficients = None
+    if robin:
+        H = robin_H(kappa * delta_max)
+        coefficients = lambda Pq: robin_coefficients(g, g_prime, a, Pq, H, extra)  # noqa: E731
     if P is None:
         if P_start is None:
             P_start = initial_P(a, tol_fit, extra)
-        P, rho, C, alpha, err = choose_P(g, g_prime, a, tol_fit, P_start, extra)
+        P, rho, C, alpha, err = choose_P(g, g_prime, a, tol_fit, P_start, extra, coefficients=coefficients)
     else:
-        rho, C, alpha = sbd_coefficients(g_prime, a, P, extra)
+        rho, C, alpha = coefficients(P) if robin else sbd_coefficients(g_prime, a, P, extra)
         err = fit_linf_error(g, rho, C, alpha, a, extra)
     coef = gscale * alpha * C      # kernel units: G ~ const + sum_p coef_p J0(rho_p r / scale_R)
     n_circles = P + (1 if kind == "helmholtz" else 0)
