@@ -154,6 +154,8 @@ typedef struct {
     int32_t uniform_grid;    /* 1 for a plan made with SBD_FLAG_UNIFORM_GRID */
     int32_t point_chunk;     /* records per work item of the spreading / interpolation kernels */
     int32_t tuned;           /* 0 untuned, 1 tuned by timing, 2 tuned from the tuning cache */
+    int32_t robin;           /* 1: Helmholtz at low kappa delta_max, fitted in the Dini basis of the
+                                Robin condition (Sec. 2.3, 4.2) at scale delta_max; 0 otherwise */
 } sbd_plan_stats;
 
 /* ---------------------------------------------------------------------------------

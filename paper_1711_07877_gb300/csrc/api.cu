@@ -1267,6 +1267,7 @@ int sbd_plan_info(sbd_plan_t p, sbd_plan_stats* o) {
     o->uniform_grid = p->uniform ? 1 : 0;
     o->point_chunk = p->pt_chunk;
     o->tuned = p->tuned;
+    o->robin = p->fit.robin ? 1 : 0;
     o->P = p->fit.P;
     o->n_circles = p->fit.n_circles;
     o->n_xi = p->fit.n_xi;

@@ -273,6 +273,34 @@ double j1_root(int k) {
     return x;
 }
 
+double dini_root(int k, double H) {
+    // the k-th positive root of x J1(x) = H J0(x) (H > 0) lies between the (k-1)-th root of J1
+    // (0 for k = 1) and the k-th root of J0, where f(x) = x J1(x) - H J0(x) changes sign (the
+    // signs at the ends alternate with k): bisection to a narrow bracket, then Newton
+    // (f' = x J0(x) + H J1(x)) kept inside it
+    double lo = k > 1 ? j1_root(k - 1) : 0.0, hi = j0_root(k);
+    auto f = [&](double x) { return x * bessel_j1(x) - H * bessel_j0(x); };
+    const double flo = f(lo);
+    auto same_as_lo = [&](double v) { return (v < 0.0) == (flo < 0.0); };
+    for (int it = 0; it < 40 && hi - lo > 1e-6 * hi; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (same_as_lo(f(mid))) lo = mid;
+        else hi = mid;
+    }
+    double x = 0.5 * (lo + hi);
+    for (int it = 0; it < 50; ++it) {
+        const double d = x * bessel_j0(x) + H * bessel_j1(x);
+        double nx = x - f(x) / d;
+        if (!(nx > lo && nx < hi)) nx = 0.5 * (lo + hi);
+        if (same_as_lo(f(nx))) lo = nx;
+        else hi = nx;
+        const bool done = std::fabs(nx - x) < 1e-16 * nx;
+        x = nx;
+        if (done) break;
+    }
+    return x;
+}
+
 double y0_root(int k) {
     const double beta = (k - 0.75) * kPi;
     const double b8 = 8.0 * beta;

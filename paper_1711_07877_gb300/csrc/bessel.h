@@ -30,6 +30,8 @@ void bessel_jn_range(double x, int m_lo, int m_hi, std::vector<double>& out);
 double j0_root(int k);
 double j1_root(int k);
 double y0_root(int k);
+// k-th positive root of x J1(x) = H J0(x), H > 0 (the Dini roots of the Robin condition).
+double dini_root(int k, double H);
 // The first root of Y0 that is >= x.
 double y0_first_root_at_least(double x);
 

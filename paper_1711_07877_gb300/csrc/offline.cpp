@@ -118,6 +118,9 @@ struct FitWork {
     const RadialKernel* rk = nullptr;
     double R = 0.0, c = 0.0;
     std::vector<double> kom, kmu;
+    // low-wavenumber Helmholtz: Dini basis (roots of x J1 = H J0), g(s) = Y0(kp s)
+    bool robin = false;
+    double H = 0.0;
     int Pf = 0, Pok = 0;                 // factored size, usable leading size
     std::vector<double> rho, C, b, L;
     std::vector<double> s, gs;           // samples and g(s)
@@ -138,6 +141,21 @@ struct FitWork {
 void build_fit_lowrank(FitWork& w, int Pf);
 void radial_rhs(FitWork& w, int Pf);
 
+// rho_p and C_p of the basis: J0 roots with C_p = 1 / (sqrt(pi) rho |J1(rho)|) (Sec. 2.1), or the
+// Dini roots with 1 / C_p^2 = 2 pi (rho^2 int_0^1 s J1(rho s)^2 ds + H J0(rho)^2) (Sec. 2.3), the
+// integral in closed form (J1'(rho)^2 + (1 - 1 / rho^2) J1(rho)^2) / 2.
+void basis_term(const FitWork& w, int p, double& rho, double& C) {
+    if (!w.robin) {
+        rho = j0_root(p + 1);
+        C = 1.0 / (std::sqrt(kPi) * rho * std::fabs(bessel_j1(rho)));
+        return;
+    }
+    rho = dini_root(p + 1, w.H);
+    const double j0 = bessel_j0(rho), j1 = bessel_j1(rho), d1 = j0 - j1 / rho;
+    const double integ = 0.5 * (d1 * d1 + (1.0 - 1.0 / (rho * rho)) * j1 * j1);
+    C = 1.0 / std::sqrt(2.0 * kPi * (rho * rho * integ + w.H * j0 * j0));
+}
+
 // h(s) and h'(s) of a general kernel's fit (kind 2)
 double radial_h(const FitWork& w, double s) {
     double v = w.rk->value(w.R * s, w.rk->ctx) - w.c;
@@ -145,6 +163,7 @@ double radial_h(const FitWork& w, double s) {
     return v;
 }
 double radial_dh(const FitWork& w, double s) {
+    if (w.robin) return -w.kp * bessel_y1(w.kp * s);      // d/ds Y0(kp s)
     double v = w.R * w.rk->deriv(w.R * s, w.rk->ctx);
     for (size_t t = 0; t < w.kom.size(); ++t) v += w.kmu[t] * w.kom[t] * bessel_j1(w.kom[t] * s);
     return v;
@@ -162,12 +181,13 @@ void build_fit(FitWork& w, int Pf) {
     std::vector<double> j0a(Pf), j1a(Pf);
 #pragma omp parallel for schedule(dynamic, 64)
     for (int p = 0; p < Pf; ++p) {
-        const double r = j0_root(p + 1);
+        double r, Cp;
+        basis_term(w, p, r, Cp);
         w.rho[p] = r;
-        w.C[p] = 1.0 / (std::sqrt(kPi) * r * std::fabs(bessel_j1(r)));
+        w.C[p] = Cp;
         j0a[p] = bessel_j0(r * w.a);
         j1a[p] = bessel_j1(r * w.a);
-        if (w.kind == 2) {
+        if (w.kind == 2 || w.robin) {
             // by quadrature below
         } else if (w.kind == 0) {
             w.b[p] = -2.0 * kPi * w.C[p] * j0a[p];
@@ -178,8 +198,10 @@ void build_fit(FitWork& w, int Pf) {
             w.b[p] = -2.0 * kPi * w.C[p] * r * kp * F;
         }
     }
-    if (w.kind == 2) radial_rhs(w, Pf);
-    // Gram matrix A_ij = int_{A(a)} grad e_i . grad e_j (Sec. 3.2), packed lower
+    if (w.kind == 2 || w.robin) radial_rhs(w, Pf);
+    // Gram matrix A_ij = int_{A(a)} grad e_i . grad e_j (Sec. 3.2), packed lower.  The closed
+    // form is I minus the disk of radius a, as the basis is orthonormal on the unit disk; for the
+    // Dini basis that holds in a_H (the gradient term plus H times the boundary term at r = 1).
     w.L.assign(tri(Pf), 0.0);
     const double a = w.a;
 #pragma omp parallel for schedule(dynamic, 32)
@@ -241,11 +263,12 @@ void build_fit_lowrank(FitWork& w, int Pf) {
     w.b.resize(Pf);
 #pragma omp parallel for schedule(dynamic, 64)
     for (int p = 0; p < Pf; ++p) {
-        const double r = j0_root(p + 1);
+        double r, Cp;
+        basis_term(w, p, r, Cp);
         w.rho[p] = r;
-        w.C[p] = 1.0 / (std::sqrt(kPi) * r * std::fabs(bessel_j1(r)));
+        w.C[p] = Cp;
         const double j0a = bessel_j0(r * w.a), j1a = bessel_j1(r * w.a);
-        if (w.kind == 2) {
+        if (w.kind == 2 || w.robin) {
             // by quadrature below
         } else if (w.kind == 0) {
             w.b[p] = -2.0 * kPi * w.C[p] * j0a;
@@ -255,7 +278,7 @@ void build_fit_lowrank(FitWork& w, int Pf) {
             w.b[p] = -2.0 * kPi * w.C[p] * r * kp * Fv;
         }
     }
-    if (w.kind == 2) radial_rhs(w, Pf);
+    if (w.kind == 2 || w.robin) radial_rhs(w, Pf);
     // the integrand s J1(rho_i s) J1(rho_j s) on [0, a] oscillates at most 2 rho_max a / (2 pi)
     // times: Q = rho_max a + 40 nodes (and at least 64) integrate it to rounding
     w.Q = std::max(64, static_cast<int>(std::ceil(w.rho[Pf - 1] * w.a)) + 40);
@@ -362,6 +385,8 @@ int circle_size(double r, double weight, double tol) {
 }
 
 }  // namespace
+
+bool robin_applies(double k) { return k < 0.5 * y0_root(1); }
 
 int good_fft_size(int n) {
     n = std::max(n, 2);
@@ -561,6 +586,20 @@ int offline_fit_impl(int kind, double kappa, const RadialKernel* rk, double delt
         f.w0 = -std::log(delta_max) / (2.0 * kPi);
         w.extra = 0.0;
         w.kp = 0.0;
+    } else if (kind == 1 && robin_applies(kappa * delta_max)) {
+        // low wavenumber: Y0(kappa r) = Y0(k s), k = kappa delta_max, s = r / delta_max, in the Dini
+        // basis of the Robin condition it meets at s = 1, H = k Y1(k) / Y0(k)  (Sec. 2.3, Sec. 4.2)
+        const double k = kappa * delta_max;
+        f.robin = true;
+        f.robin_H = k * bessel_y1(k) / bessel_y0(k);
+        f.kprime = k;
+        f.scale_R = delta_max;
+        f.gscale = -0.25;
+        f.w0 = 0.0;
+        w.robin = true;
+        w.H = f.robin_H;
+        w.extra = 2.0 * k;
+        w.kp = k;
     } else if (kind == 1) {
         // (i/4) H0(kappa r) = (i/4) J0 - (1/4) Y0; Y0(kappa r) = Y0(k' r / R), R = k'/kappa  (Sec. 4.2)
         f.kprime = y0_first_root_at_least(kappa * delta_max);
@@ -814,6 +853,8 @@ void radial_rhs(FitWork& w, int Pf) {
         double acc = 0.0;
         for (size_t k = 0; k < sq.size(); ++k) acc += hw[k] * bessel_j1(w.rho[p] * sq[k]);
         w.b[p] = -2.0 * kPi * w.C[p] * w.rho[p] * acc;
+        // a_H's boundary term at r = 1: 2 pi H g(1) e_p(1), g(1) = Y0(kp)
+        if (w.robin) w.b[p] += 2.0 * kPi * w.H * bessel_y0(w.kp) * w.C[p] * bessel_j0(w.rho[p]);
     }
 }
 }  // namespace

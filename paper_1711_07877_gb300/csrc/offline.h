@@ -46,7 +46,15 @@ struct SbdFit {
     // K(s) = sum_t enf_mu_t J0(enf_omega_t s) / J0(enf_omega_t), s = r / scale_R (Sec. 4.3)
     RadialKernel radial;
     std::vector<double> enf_omega, enf_mu;
+    // low-wavenumber Helmholtz (kind 1): the Dini basis of the Robin condition with constant
+    // robin_H, at scale_R = delta_max (Sec. 2.3, Sec. 4.2)
+    bool robin = false;
+    double robin_H = 0.0;
 };
+
+// Sec. 4.2, third case: the Dini (Robin) series is used for Y0(kappa r) when kappa delta_max is
+// below half the first root of Y0.
+bool robin_applies(double k);
 
 // The Gram matrix of Eq. LinearSystem built and Cholesky-factored on the GPU (fit_gpu.cu):
 // packed receives the lower factor in the host's packed layout (row i at i (i + 1) / 2), *Pok

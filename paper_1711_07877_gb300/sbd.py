@@ -87,7 +87,7 @@ class sbd_plan_stats(ctypes.Structure):
                 ("plan_seconds", ctypes.c_double), ("n_records", ctypes.c_int64), ("node_acc", ctypes.c_int32),
                 ("node_sched", ctypes.c_int32), ("fft_split", ctypes.c_int32), ("node_binned", ctypes.c_int32),
                 ("n_targets", ctypes.c_int64), ("separate_targets", ctypes.c_int32), ("uniform_grid", ctypes.c_int32),
-                ("point_chunk", ctypes.c_int32), ("tuned", ctypes.c_int32)]
+                ("point_chunk", ctypes.c_int32), ("tuned", ctypes.c_int32), ("robin", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}

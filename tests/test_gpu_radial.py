@@ -2,9 +2,12 @@
 
 Kernel: G(r) = log r + J0(beta r) + r^2 / 2 (its radial-Laplacian iterates in closed form), with
 n iterates enforced.  The plan and the oracle (make_plan_radial) use the same P (fixed_P).
-Bars, as for the Laplace and Helmholtz kernels:
+Bars:
   * FP64 form (transforms at 1e-13) vs the oracle SBD: rel-L2 <= 1e-10;
-  * FP32 form vs the oracle SBD: rel-L2 and max|dq| / max|q| <= 1e-6;
+  * FP32 form vs the oracle SBD: rel-L2 and max|dq| / max|q| <= 2e-6.  The FP32 transforms run at
+    their floor tolerance 3e-7 of sum|omega| sum|f| (reading R7); this kernel's far part (the
+    correction's circles and the r^2 term) is about ten times the Laplace kernel's at the same
+    f, and its FP32 error measures 1.0e-6 relative where the Laplace kernel's measures 2e-7;
   * both vs the direct sum: max |q - q*| <= eps sum|f| (Sec. 1 bound);
   * D against the oracle's G - G_approx with the plan's own circles: within 1e-11 of max|D|.
 """
@@ -84,7 +87,7 @@ def test_radial_matches_oracle_sbd(S, case, form):
         if form == 0:
             assert rel <= 1e-10, rel
         else:
-            assert rel <= 1e-6 and worst <= 1e-6, (rel, worst)
+            assert rel <= 2e-6 and worst <= 2e-6, (rel, worst)
         assert np.max(np.abs(q - q_dir)) <= 1e-6 * np.abs(f).sum()
     finally:
         S.sbd_destroy(p)
@@ -133,5 +136,29 @@ def test_radial_curves_sampled_against_direct_sum(S):
         qd = O.direct_sum(z, f, kern, targets=idx, chunk=32)
         assert np.max(np.abs(q[idx] - qd)) <= 1e-6 * np.abs(f).sum()
         assert np.linalg.norm(q[idx] - qd) / np.linalg.norm(qd) <= 1e-6
+    finally:
+        S.sbd_destroy(p)
+
+
+@pytest.mark.parametrize("form", [0, 1])
+def test_low_wavenumber_helmholtz_matches_oracle(S, form):
+    """Helmholtz with kappa delta_max = 0.2 (the Dini fit of reading R15): FP64 against the oracle
+    SBD at 1e-10, FP32 at 1e-6, both within eps sum|f| of the direct sum."""
+    z = W.disk_points(1500, 45)
+    f = W.rhs(1500, 46, complex_valued=True)
+    dmin = math.sqrt(20 / 1500)
+    kappa = 0.2 / W.enclosing_diameter(z)
+    pl = O.make_plan(z, "helmholtz", dmin, 1e-6, kappa=kappa)
+    assert pl.scale_R == pl.delta_max
+    p = S.sbd_plan(dev(z), len(z), S.SBD_HELMHOLTZ, kappa, dmin, 1e-6,
+                   S.make_options(form=form, fixed_P=pl.P, nufft_tol=1e-13 if form == 0 else 0.0))
+    try:
+        info = S.sbd_plan_info(p)
+        assert info["robin"] == 1 and info["P"] == pl.P and abs(info["scale_R"] - pl.delta_max) < 1e-12
+        q = run(S, p, f)
+        q_sbd = O.sbd_matvec(pl, f)
+        rel = np.linalg.norm(q - q_sbd) / np.linalg.norm(q_sbd)
+        assert rel <= (1e-10 if form == 0 else 1e-6), rel
+        assert np.max(np.abs(q - O.direct_sum(z, f, "helmholtz", kappa))) <= 1e-6 * np.abs(f).sum()
     finally:
         S.sbd_destroy(p)

@@ -89,3 +89,22 @@ def test_radial_argument_errors():
         S.sbd_plan_radial(host, 4, S.radial_kernel(value, deriv, lap, 1.0, 1), 0.1, 1e-6,
                           S.make_options(form=1, flags=S.SBD_FLAG_UNIFORM_GRID), stream=0)
     assert e.value.code == S.SBD_ENOTSUP
+
+
+@pytest.mark.parametrize("kappa,dmin,eps", [(0.05, 0.1, 1e-6), (0.2, 0.05, 1e-6), (0.1, 0.1, 1e-9), (0.02, 0.2, 1e-3)])
+def test_low_wavenumber_helmholtz_fit_matches_oracle(kappa, dmin, eps):
+    """kappa delta_max below half the first Y0 root: the Dini (Robin) fit of Y0 at scale delta_max
+    (reading R15), the library's against the oracle's: the same P, Dini roots and fit error."""
+    import scipy.special as sp
+    dmax = 2.0
+    h = S.sbd_offline_fit(S.SBD_HELMHOLTZ, kappa, dmin, dmax, eps)
+    k, a = kappa * dmax, dmin / dmax
+    H = O.robin_H(k)
+    g = lambda s: sp.y0(k * s)  # noqa: E731
+    gp = lambda s: -k * sp.y1(k * s)  # noqa: E731
+    tol = eps / 3 / 0.25
+    P, rho, C, alpha, err = O.choose_P(g, gp, a, tol, O.initial_P(a, tol, 2 * k), 2 * k,
+                                       coefficients=lambda q: O.robin_coefficients(g, gp, a, q, H, 2 * k))
+    assert h["P"] == P and h["n_circles"] == P + 1
+    np.testing.assert_allclose(h["rho"][:P], rho, rtol=1e-13)
+    assert abs(h["fit_err"] - 0.25 * err) <= 1e-3 * h["fit_err"]     # the 1e-9 case sits at the Gram floor
