@@ -166,12 +166,14 @@ def measured_peaks():
 def stage_bytes(info, n, nrhs, form, esz=8, near32=False):
     """Algorithmic bytes per launch of each on-line step (see the design notes).
     esz: bytes of one input/output value (8 real Laplace, 16 complex Helmholtz).
-    Laplace stores node records for half the nodes (the antipodes follow by symmetry).
+    The node step counts a read and a write of the frequency cells it covers (the half plane for
+    Laplace) and no node data: the nodes and their weights are a function of (p, m) and a P-vector,
+    so the method need not move them (the plan's stored records, which the kernels do stream, are
+    reported apart as node_records_bytes).
     near32: D's values stored in float32 (SBD_FLAG_NEAR_FP32), else float64."""
     c = 8 if form == "fp32" else 16          # complex grid element
     pr = 16 if form == "fp32" else 24        # point record: int2 cell + fractions
-    nr = 24 if form == "fp32" else 32        # node record
-    m, nk, nxi, nnz, P = info["grid_x"], info["grid_k"], info["n_xi"], info["nnz"], info["stencil_x"]
+    m, nk, nnz, P = info["grid_x"], info["grid_k"], info["nnz"], info["stencil_x"]
     touched = min(m * m, n * P * P)
     vb = (16 if esz == 16 else 8) // (2 if near32 else 1)   # D value: complex for Helmholtz, float32 with the flag
     r = nrhs   # every step takes all right-hand sides in one launch: grid and value terms scale with r
@@ -190,7 +192,7 @@ def stage_bytes(info, n, nrhs, form, esz=8, near32=False):
             "sum": esz * n * r,
             "spread": pr * n + (esz * n + c * m * m // 2) * r,
             "fft_fwd": c * (m * m // 2 + nk * nk // 2) * r,
-            "node": nr * info["n_records"] + c * nk * nk * r,
+            "node": c * nk * nk * r,
             "fft_inv": c * (nk * nk // 2 + m * m // 2) * r,
             "interp": pr * n + (esz * n + c * touched // 2) * r,
             "spmv": (4 + vb) * nnz + 8 * (n + 1) + 2 * esz * n * r,
@@ -199,11 +201,16 @@ def stage_bytes(info, n, nrhs, form, esz=8, near32=False):
         "sum": esz * n * r,
         "spread": pr * n + (esz * n + c * m * m) * r,
         "fft_fwd": c * (m * m + nk * nk) * r,
-        "node": nr * nxi + 2 * c * nk * nk * r,
+        "node": 2 * c * nk * nk * r,
         "fft_inv": c * (nk * nk + m * m) * r,
         "interp": pr * n + (esz * n + c * touched) * r,
         "spmv": (4 + vb) * nnz + 8 * (n + 1) + 2 * esz * n * r,
     }
+
+
+def node_records_bytes(info, form):
+    """Bytes of the node records the node step streams per launch (stored at plan time)."""
+    return (24 if form == "fp32" else 32) * info["n_records"]
 
 
 def traffic_key(args, alpha):
@@ -338,6 +345,8 @@ def stage_report(S, plan, step, f_dev, args, info, nrhs, esz, workload_key, form
             avg = tot / cnt
             stages[st] = {"ms": avg, "launches_per_step": cnt // steps, "algorithmic_bytes": sb[st],
                           "GBps": sb[st] / (avg * 1e-3) / 1e9}
+    if "node" in stages and not info.get("uniform_grid"):
+        stages["node"]["node_records_bytes"] = node_records_bytes(info, form)
     dom = max(stages, key=lambda s_: stages[s_]["ms"] * stages[s_]["launches_per_step"])
     achieved = stages[dom]["GBps"]
     roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",

@@ -27,10 +27,14 @@ def test_spmv_bytes_follow_the_stored_value_type():
     assert helm == (4 + 16) * INFO["nnz"] + 8 * (n + 1) + 2 * 16 * n
 
 
-def test_laplace_steps_count_half_the_grid_and_records():
+def test_laplace_steps_count_half_the_grid_and_no_node_data():
+    """The node step moves a read and a write of the half plane's cells; node data counts 0 (the
+    nodes are a function of (p, m)); the stored records it streams are reported apart."""
     b = bench.stage_bytes(INFO, 10_000, 1, "fp32", esz=8)
     m, nk = INFO["grid_x"], INFO["grid_k"]
-    assert b["node"] == 24 * INFO["n_records"] + 8 * nk * nk
+    assert b["node"] == 8 * nk * nk
+    assert bench.stage_bytes(INFO, 10_000, 1, "fp32", esz=16)["node"] == 2 * 8 * nk * nk
+    assert bench.node_records_bytes(INFO, "fp32") == 24 * INFO["n_records"]
     assert b["fft_fwd"] == 8 * (m * m // 2 + nk * nk // 2)
     assert b["spread"] == 16 * 10_000 + 8 * 10_000 + 8 * m * m // 2
 
@@ -47,8 +51,7 @@ def test_traffic_keys_name_size_and_alpha():
 def test_step_bytes_scale_with_right_hand_sides():
     one = bench.stage_bytes(INFO, 10_000, 1, "fp32", esz=8)
     four = bench.stage_bytes(INFO, 10_000, 4, "fp32", esz=8)
-    for st in ("fft_fwd", "fft_inv", "sum"):
+    for st in ("fft_fwd", "fft_inv", "sum", "node"):
         assert four[st] == 4 * one[st]
-    # the records are read once per launch, the grids and values once per right-hand side
+    # the point records are read once per launch, the grids and values once per right-hand side
     assert four["spread"] - 16 * 10_000 == 4 * (one["spread"] - 16 * 10_000)
-    assert four["node"] - 24 * INFO["n_records"] == 4 * (one["node"] - 24 * INFO["n_records"])
