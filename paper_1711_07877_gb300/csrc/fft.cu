@@ -416,15 +416,16 @@ __device__ __forceinline__ void dit_stage_out(const cx_t<T>* s, int n, int Lp, c
 // and the absolute index of this launch's first row.
 template <typename T> struct HermFold { const cx_t<T>* base; int n; long row0; };
 
-// Input element at FFT position idx of the current row (has = false: a zero).
-template <typename T>
-__device__ __forceinline__ cx_t<T> load_elem(int io, int idx, int n, const cx_t<T>* __restrict__ src,
+// Input element at FFT position idx of the current row (has = false: a zero).  The io mode and
+// whether a Hermitian fold applies are compile-time, so each load loop carries only its own case.
+template <typename T, int IO, bool FOLD>
+__device__ __forceinline__ cx_t<T> load_elem(int idx, int n, const cx_t<T>* __restrict__ src,
                                              long in_stride, int in_len, int in_shift, long row,
                                              const HermFold<T>& hf, T rs0, T rs1,
                                              const T* __restrict__ pre_elem, bool& has) {
     using C = cx_t<T>;
     has = false;
-    if (io == kIoPairInv) {
+    if constexpr (IO == kIoPairInv) {
         // rows 2r, 2r+1 hold frequencies 0..in_len-1 of two Hermitian spectra A0, A1;
         // z = A0 + i A1 with A(-k) = conj A(k)
         const int k = idx < n / 2 ? idx : idx - n;
@@ -442,7 +443,7 @@ __device__ __forceinline__ cx_t<T> load_elem(int io, int idx, int n, const cx_t<
     if (t < 0) t += n;
     if (t >= in_len) return mk<T>(0, 0);
     C v = src[t];
-    if (hf.n) {
+    if constexpr (FOLD) {
         const long ar = hf.row0 + row;
         if (ar >= 1 && t >= 1) {
             const C mv = hf.base[(hf.n - ar) * in_stride + (hf.n - t)];
@@ -497,25 +498,45 @@ __global__ void __launch_bounds__(kFftThreads, 3) fft_rows_kernel(
         rs1 = pre_row[io == kIoPairFwd ? 2 * row + 1 : row];
     }
     // load pass: element i of the length-nq transform (the Q phases folded and twisted) goes
-    // to its digit-reversed position; consecutive threads read consecutive inputs
+    // to its digit-reversed position; consecutive threads read consecutive inputs.  One loop per
+    // (io mode, fold, phases, twist), chosen once per CTA.
+    auto load_pass = [&](auto io_c, auto fold_c, auto q_c, auto twist_c) {
+        constexpr int IO = decltype(io_c)::value;
+        constexpr bool FOLD = decltype(fold_c)::value;
+        constexpr int QQ = decltype(q_c)::value;
+        constexpr bool TWIST = decltype(twist_c)::value;
 #pragma unroll 4
-    for (int i = threadIdx.x; i < nq; i += NT) {
-        C acc = mk<T>(0, 0);
-        for (int j = 0; j < Q; ++j) {
-            const int idx = i + j * nq;               // FFT index
-            bool has;
-            C v = load_elem<T>(io, idx, n, src, in_stride, in_len, in_shift, row, hf, rs0, rs1, pre_elem, has);
-            if (has) {
-                if (r) {                              // twist w_n^{+-idx}
-                    C w = twid<T>(tw, tws, idx);
-                    if (inv) w.y = -w.y;
-                    v = cmul(v, w);
+        for (int i = threadIdx.x; i < nq; i += NT) {
+            C acc = mk<T>(0, 0);
+#pragma unroll
+            for (int j = 0; j < QQ; ++j) {
+                const int idx = i + j * nq;           // FFT index
+                bool has;
+                C v = load_elem<T, IO, FOLD>(idx, n, src, in_stride, in_len, in_shift, row, hf, rs0, rs1, pre_elem,
+                                             has);
+                if (has) {
+                    if constexpr (TWIST) {            // twist w_n^{+-idx}
+                        C w = twid<T>(tw, tws, idx);
+                        if (inv) w.y = -w.y;
+                        v = cmul(v, w);
+                    }
+                    acc = cadd(acc, v);
                 }
-                acc = cadd(acc, v);
             }
+            s[perm[i]] = acc;
         }
-        s[perm[i]] = acc;
-    }
+    };
+    auto with_phases = [&](auto io_c, auto fold_c) {
+        using one = std::integral_constant<int, 1>;
+        using two = std::integral_constant<int, 2>;
+        if (Q == 1) load_pass(io_c, fold_c, one{}, std::false_type{});
+        else if (r) load_pass(io_c, fold_c, two{}, std::true_type{});
+        else load_pass(io_c, fold_c, two{}, std::false_type{});
+    };
+    if (io == kIoPairInv) with_phases(std::integral_constant<int, kIoPairInv>{}, std::false_type{});
+    else if (io == kIoPairFwd) with_phases(std::integral_constant<int, kIoPairFwd>{}, std::false_type{});
+    else if (hf.n) with_phases(std::integral_constant<int, kIoPlain>{}, std::true_type{});
+    else with_phases(std::integral_constant<int, kIoPlain>{}, std::false_type{});
     __syncthreads();
     int Lp = 1;
     // output scaling of the direct store (plain and pair-inverse rows)
