@@ -499,14 +499,22 @@ __global__ void __launch_bounds__(kFftThreads, 3) fft_rows_kernel(
     }
     // load pass: element i of the length-nq transform (the Q phases folded and twisted) goes
     // to its digit-reversed position; consecutive threads read consecutive inputs.  One loop per
-    // (io mode, fold, phases, twist), chosen once per CTA.
-    auto load_pass = [&](auto io_c, auto fold_c, auto q_c, auto twist_c) {
+    // (io mode, fold, phases), chosen once per CTA.
+    // With two or more stages the first one runs here too: in the digit-reversed order the group
+    // of stage one at shared positions perm[t] + q (q < R1) holds the elements t + G1 q,
+    // G1 = nq / R1; consecutive threads take consecutive t, so each of the R1 reads is coalesced,
+    // and the group's butterfly runs before anything is stored.
+    // (Fused for the odd first radices 3, 5 and 9, which every row length here has; a row of
+    // 2^k points takes the plain load, which keeps the number of instantiated loops small.)
+    const int R1 = plan.radix[0];
+    const bool fuse1 = plan.nstages >= 2 && (R1 == 3 || R1 == 5 || R1 == 9);
+    const bool twist = Q == 2 && r != 0;
+    auto load_pass = [&](auto io_c, auto fold_c, auto q_c) {
         constexpr int IO = decltype(io_c)::value;
         constexpr bool FOLD = decltype(fold_c)::value;
         constexpr int QQ = decltype(q_c)::value;
-        constexpr bool TWIST = decltype(twist_c)::value;
-#pragma unroll 4
-        for (int i = threadIdx.x; i < nq; i += NT) {
+        // element i of the length-nq transform: the Q phases folded and twisted
+        auto fetch = [&](int i) -> C {
             C acc = mk<T>(0, 0);
 #pragma unroll
             for (int j = 0; j < QQ; ++j) {
@@ -515,7 +523,7 @@ __global__ void __launch_bounds__(kFftThreads, 3) fft_rows_kernel(
                 C v = load_elem<T, IO, FOLD>(idx, n, src, in_stride, in_len, in_shift, row, hf, rs0, rs1, pre_elem,
                                              has);
                 if (has) {
-                    if constexpr (TWIST) {            // twist w_n^{+-idx}
+                    if (QQ == 2 && twist) {           // twist w_n^{+-idx}
                         C w = twid<T>(tw, tws, idx);
                         if (inv) w.y = -w.y;
                         v = cmul(v, w);
@@ -523,22 +531,40 @@ __global__ void __launch_bounds__(kFftThreads, 3) fft_rows_kernel(
                     acc = cadd(acc, v);
                 }
             }
-            s[perm[i]] = acc;
+            return acc;
+        };
+        if (fuse1) {
+            auto first = [&](auto rc) {
+                constexpr int R = decltype(rc)::value;
+                const int G1 = nq / R;
+                for (int t = threadIdx.x; t < G1; t += NT) {
+                    C v[R];
+#pragma unroll
+                    for (int q = 0; q < R; ++q) v[q] = fetch(t + G1 * q);
+                    dft<T, R, SIGN>(v);
+                    const int base = perm[t];
+#pragma unroll
+                    for (int q = 0; q < R; ++q) s[base + q] = v[q];
+                }
+            };
+            if (R1 == 3) first(std::integral_constant<int, 3>{});
+            else if (R1 == 5) first(std::integral_constant<int, 5>{});
+            else first(std::integral_constant<int, 9>{});
+        } else {
+#pragma unroll 4
+            for (int i = threadIdx.x; i < nq; i += NT) s[perm[i]] = fetch(i);
         }
     };
     auto with_phases = [&](auto io_c, auto fold_c) {
-        using one = std::integral_constant<int, 1>;
-        using two = std::integral_constant<int, 2>;
-        if (Q == 1) load_pass(io_c, fold_c, one{}, std::false_type{});
-        else if (r) load_pass(io_c, fold_c, two{}, std::true_type{});
-        else load_pass(io_c, fold_c, two{}, std::false_type{});
+        if (Q == 1) load_pass(io_c, fold_c, std::integral_constant<int, 1>{});
+        else load_pass(io_c, fold_c, std::integral_constant<int, 2>{});
     };
     if (io == kIoPairInv) with_phases(std::integral_constant<int, kIoPairInv>{}, std::false_type{});
     else if (io == kIoPairFwd) with_phases(std::integral_constant<int, kIoPairFwd>{}, std::false_type{});
     else if (hf.n) with_phases(std::integral_constant<int, kIoPlain>{}, std::true_type{});
     else with_phases(std::integral_constant<int, kIoPlain>{}, std::false_type{});
     __syncthreads();
-    int Lp = 1;
+    int Lp = fuse1 ? R1 : 1;
     // output scaling of the direct store (plain and pair-inverse rows)
     T ps0 = static_cast<T>(1), ps1 = static_cast<T>(1);
     if (post_row) {
@@ -559,7 +585,7 @@ __global__ void __launch_bounds__(kFftThreads, 3) fft_rows_kernel(
             dst[e] = v;
         }
     };
-    for (int st = 0; st < plan.nstages; ++st) {
+    for (int st = fuse1 ? 1 : 0; st < plan.nstages; ++st) {
         const int R = plan.radix[st];
         if (st == plan.nstages - 1 && io != kIoPairFwd) {
             // last stage: outputs go straight to global memory (uniform branch, no barrier after)
