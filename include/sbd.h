@@ -148,7 +148,7 @@ typedef struct {
     int32_t node_acc;        /* fused node-kernel variant (sbd_tune): accumulation mode */
     int32_t node_sched;      /* fused node-kernel variant (sbd_tune): record schedule */
     int32_t fft_split;       /* row-FFT phases (sbd_tune): 0 one where it fits, 2 always two */
-    int32_t node_binned;     /* 1 when the binned node kernel (acc 3) applies to the plan */
+    int32_t node_binned;     /* 1 when the binned node kernels (acc 3, 4) apply to the plan */
     int64_t n_targets;       /* targets (rows of D, length of q): n_points unless sbd_plan_st */
     int32_t separate_targets;/* 1 for a plan of sbd_plan_st */
     int32_t uniform_grid;    /* 1 for a plan made with SBD_FLAG_UNIFORM_GRID */
@@ -450,22 +450,25 @@ int sbd_fft2(const void* in, void* out, int32_t n0, int32_t n1, int32_t sign, in
  * cells, every 64 x 64 tile of the frequency grid holding at most 4096 records) takes
  * the records bin by bin (8 x 8 stencil starts; four accumulators, one per bin colour,
  * so that no two warps write one cell and no atomics are needed); for it sched 0 runs
- * 512 threads per CTA, sched 1 1024.  Results agree to FP32 rounding.
+ * 512 threads per CTA, sched 1 1024.  acc 4 (where acc 3 applies) takes the same bins two at
+ * a time per warp, one per half-warp, each half-warp carrying one record at a time with
+ * bank-conflict-free accesses (sched as for acc 3).  Results agree to FP32 rounding.
  *   sbd_tune       times every applicable variant on the plan's own records (reps
  *                  launches each, after one warm-up, CUDA events on cuda_stream; the
  *                  frequency workspace is first filled with a constant non-zero value,
  *                  so that concurrent adds to a cell contend as with real data) and
  *                  keeps the fastest.
- *                  ms (host, 10 entries, may be NULL): mean ms per launch of variant
- *                  acc * 2 + sched, -1 where not applicable; ms[8], ms[9]: mean ms of
+ *                  ms (host, 12 entries, may be NULL): mean ms per launch of variant
+ *                  acc * 2 + sched for acc <= 3 and 10 + sched for acc 4, -1 where not
+ *                  applicable; ms[8], ms[9]: mean ms of
  *                  the forward 2-D transform with rows in one phase where they fit, and
  *                  with every row split into two half-length phases (two CTAs of 512
  *                  threads per SM instead of one of 1024); the faster is kept too.
  *                  Blocks until done.
  *   sbd_set_tuning picks a variant by hand (fft_split 0 or 2).
- * SBD_EINVAL for a null plan, reps < 1, acc outside {0, 1, 2, 3}, sched outside {0, 1}
- * or fft_split outside {0, 2} (acc 1 to 3 need the FP32 form, acc 3 a plan where it
- * applies; sbd_plan_info's node_binned says so).  Plans whose node step is the two-kernel
+ * SBD_EINVAL for a null plan, reps < 1, acc outside {0, .., 4}, sched outside {0, 1}
+ * or fft_split outside {0, 2} (acc 1 to 4 need the FP32 form, acc 3 and 4 a plan where
+ * they apply; sbd_plan_info's node_binned says so).  Plans whose node step is the two-kernel
  * fallback ignore the variant.
  * ------------------------------------------------------------------------------- */
 int sbd_tune(sbd_plan_t plan, int32_t reps, double* ms, void* cuda_stream);

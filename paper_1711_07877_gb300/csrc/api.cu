@@ -1299,8 +1299,8 @@ int sbd_plan_info(sbd_plan_t p, sbd_plan_stats* o) {
 }
 
 int sbd_set_tuning(sbd_plan_t p, int32_t acc, int32_t sched, int32_t fft_split) {
-    if (!p || acc < 0 || acc > 3 || sched < 0 || sched > 1 || (acc >= 1 && p->form != SBD_FORM_FP32) ||
-        (acc == 3 && !p->node_binned) || (fft_split != 0 && fft_split != 2)) {
+    if (!p || acc < 0 || acc > 4 || sched < 0 || sched > 1 || (acc >= 1 && p->form != SBD_FORM_FP32) ||
+        (acc >= 3 && !p->node_binned) || (fft_split != 0 && fft_split != 2)) {
         set_error("sbd_set_tuning: invalid plan or variant");
         return SBD_EINVAL;
     }
@@ -1498,7 +1498,7 @@ int sbd_tune_cache_load(const char* path) {
         TuneChoice c{};
         if (k1 == std::string::npos || l0 == std::string::npos || l1 == std::string::npos ||
             std::sscanf(text.c_str() + l0 + 1, "%d , %d , %d , %d", &c.acc, &c.sched, &c.fft_split, &c.chunk) != 4 ||
-            c.acc < 0 || c.acc > 3 || c.sched < 0 || c.sched > 1 || (c.fft_split != 0 && c.fft_split != 2) ||
+            c.acc < 0 || c.acc > 4 || c.sched < 0 || c.sched > 1 || (c.fft_split != 0 && c.fft_split != 2) ||
             c.chunk < kPointChunks[0] || c.chunk > (1 << 20)) {
             set_error("sbd_tune_cache_load: malformed entry");
             return SBD_EINVAL;
@@ -1517,7 +1517,7 @@ int sbd_tune(sbd_plan_t p, int32_t reps, double* ms, void* cuda_stream) {
         return SBD_EINVAL;
     }
     if (ms)
-        for (int v = 0; v < 10; ++v) ms[v] = -1.0;
+        for (int v = 0; v < 12; ++v) ms[v] = -1.0;
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     const std::string key = tune_key(p);
     {
@@ -1599,9 +1599,9 @@ int sbd_tune(sbd_plan_t p, int32_t reps, double* ms, void* cuda_stream) {
     NodeTuning pick = p->tuning;
     int rc = SBD_OK;
     const bool fp32 = p->form == SBD_FORM_FP32;
-    for (int acc = 0; acc <= (fp32 ? 3 : 0) && !rc; ++acc) {
+    for (int acc = 0; acc <= (fp32 ? 4 : 0) && !rc; ++acc) {
         if (acc == 2 && node_fused_smem<float>(p->np.Pk, 2) > 227 * 1024) continue;
-        if (acc == 3 && !p->node_binned) continue;
+        if (acc >= 3 && !p->node_binned) continue;
         for (int sched = 0; sched <= 1 && !rc; ++sched) {
             const NodeTuning t{acc, sched, p->tuning.wbound};
             auto step = [&]() {
@@ -1626,7 +1626,7 @@ int sbd_tune(sbd_plan_t p, int32_t reps, double* ms, void* cuda_stream) {
                 break;
             }
             const double per = static_cast<double>(t_ms) / reps;
-            if (ms) ms[acc * 2 + sched] = per;
+            if (ms) ms[acc < 4 ? acc * 2 + sched : 10 + sched] = per;   // 8, 9: the row FFT's phases
             if (per < best) {
                 best = per;
                 pick = t;
@@ -2080,7 +2080,7 @@ int batched_impl(const sbd_plan_t* plans, const void* const* f, void* const* q, 
         NodeJobs J{};
         for (int i = 0; i < count; ++i) {
             sbd_plan_s* p = plans[i];
-            const bool binned = sizeof(T) == 4 && p->node_binned && p->tuning.acc == 3;
+            const bool binned = sizeof(T) == 4 && p->node_binned && p->tuning.acc >= 3;
             if (p->uniform || !p->node_fused || binned != (fam == 0)) continue;
             NodeJob& jb = J.job[J.count];
             jb.rec = p->nodes;

@@ -797,7 +797,16 @@ constexpr int kBins = (kNodeTile / kBinSide) * (kNodeTile / kBinSide);
 constexpr int kBinWs = 76;
 static_assert(kBinWs >= kBinW && kBinWs % 16 == 12, "binned stride");
 
-template <int NT>
+// HALF (the tuner's acc 4): each half-warp carries records of its own bin, the warp taking two
+// bins at a time and walking them in step (the half-warp of the shorter bin idles at its end).
+// Lane (rh, c) of a half covers column c of the 8 x 8 stencil in rows {0, 1, 4, 5} + 2 rh, so
+// that the two row sets of one access sit 2 rows = 152 float2 apart, i.e. in the other 8 of
+// the 16 64-bit bank pairs: every 64-bit access of a half-warp is free of bank conflicts for
+// any stencil start.  Per record: 4 gather and 8 scatter accesses per lane, 4 shuffles for the
+// row weights and 8 for the sum over the half, and no serialisation between the records of a
+// quad (the two bins never share a cell: same-colour bins are disjoint, the others write other
+// planes).
+template <int NT, bool HALF = false>
 __device__ __forceinline__ void node_binned_body(
     const NodeRec<float>* __restrict__ rec, const long long* __restrict__ tile_start, int ntx, int n, int P,
     const Window<float>& win, const float2* __restrict__ kin, float2* __restrict__ kout, int tile) {
@@ -853,11 +862,78 @@ __device__ __forceinline__ void node_binned_body(
     __syncthreads();
     const unsigned full = 0xffffffffu;
     const int lane = tid & 31;
+    if constexpr (HALF) {
+        const int half = lane >> 4, hl = lane & 15;
+        const int cb = hl & 7, rh = hl >> 3;
+        const float offw = static_cast<float>(cb - P / 2 + 1);
+        int rowk[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) rowk[k] = (k & 1) + 4 * (k >> 1) + 2 * rh;
+        for (;;) {
+            int slot = 0;
+            if (lane == 0) slot = atomicAdd(&next_bin, 2);
+            slot = __shfl_sync(full, slot, 0);
+            if (slot >= kBins) break;
+            const int mine = slot + half;
+            const bool has_bin = mine < kBins;
+            const int bin = has_bin ? border[mine] : 0;
+            float2* ac = acc + (((bin / (kNodeTile / kBinSide)) & 1) * 2 + (bin & 1)) * plane;
+            const int e0 = has_bin ? min(bstart[bin], cnt) : 0;
+            const int e1 = has_bin ? min(max(bstart[bin + 1], e0), cnt) : 0;
+            const int len = e1 - e0;
+            const int steps = max(len, __shfl_xor_sync(full, len, 16));
+            NodeRec<float> nxt;
+            if (len > 0) nxt = rec[b0 + e0];
+            for (int j = 0; j < steps; ++j) {
+                const bool act = j < len;
+                int base = 0;
+                float wx = 0.f, wy = 0.f;
+                float2 om = make_float2(0.f, 0.f);
+                if (act) {
+                    const NodeRec<float> q = nxt;
+                    if (j + 1 < len) nxt = rec[b0 + e0 + j + 1];
+                    base = (q.cell.x - ox) * kBinWs + (q.cell.y - oy);
+                    if (cb < P) {
+                        wx = win(offw - q.frac.x);
+                        wy = win(offw - q.frac.y);
+                    }
+                    om = q.omega;
+                }
+                float wr[4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) wr[k] = wy * __shfl_sync(full, wx, (half << 4) + rowk[k]);
+                float sr = 0.f, si = 0.f;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const float2 v = s[base + rowk[k] * kBinWs + cb];
+                    sr += wr[k] * v.x;
+                    si += wr[k] * v.y;
+                }
+#pragma unroll
+                for (int o = 8; o > 0; o >>= 1) {            // the sum over the half-warp
+                    sr += __shfl_xor_sync(full, sr, o);
+                    si += __shfl_xor_sync(full, si, o);
+                }
+                const float gr = sr * om.x - si * om.y, gi = sr * om.y + si * om.x;
+                if (act) {
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        float2* pc = ac + base + rowk[k] * kBinWs + cb;
+                        float2 t = *pc;
+                        t.x += gr * wr[k];
+                        t.y += gi * wr[k];
+                        *pc = t;
+                    }
+                }
+                __syncwarp();
+            }
+        }
+    }
     const int kown = lane >> 3, sub = lane & 7;                     // window lane: record, offset
     const int ca = lane >> 2, cb = lane & 3;                        // cells (ca, cb), (ca, cb + 4)
     const float offw = static_cast<float>(sub - P / 2 + 1);
     const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4;
-    for (;;) {
+    for (; !HALF;) {
         int slot = 0;
         if (lane == 0) slot = atomicAdd(&next_bin, 1);
         slot = __shfl_sync(full, slot, 0);
@@ -952,13 +1028,13 @@ __device__ __forceinline__ void node_binned_body(
     }
 }
 
-template <int NT>
+template <int NT, bool HALF>
 __global__ void __launch_bounds__(NT, 1) node_binned_kernel(
     const NodeRec<float>* __restrict__ rec, const long long* __restrict__ tile_start, int ntx, int n, int P,
     Window<float> win, const float2* __restrict__ kin, float2* __restrict__ kout, long kbatch) {
     // tile blockIdx.x of right-hand side blockIdx.y
-    node_binned_body<NT>(rec, tile_start, ntx, n, P, win, kin + blockIdx.y * kbatch, kout + blockIdx.y * kbatch,
-                         blockIdx.x);
+    node_binned_body<NT, HALF>(rec, tile_start, ntx, n, P, win, kin + blockIdx.y * kbatch,
+                               kout + blockIdx.y * kbatch, blockIdx.x);
 }
 
 // Node step of a whole batch (sbd_matvec_batched), one cooperative launch of persistent CTAs:
@@ -1148,11 +1224,11 @@ int launch_fused_g(const NodeRec<T>* nodes, const long long* tile_start, dim3 nt
                    : launch_fused<T, G, 0, 0>(nodes, tile_start, nt, ntx, g, Ws, win, kin, kout, wb, kb, s);
 }
 
-template <int NT>
+template <int NT, bool HALF = false>
 int launch_binned(const NodeRec<float>* nodes, const long long* tile_start, dim3 nt, int ntx, const FarGeom& g,
                   const Window<float>& win, const float2* kin, float2* kout, long kb, cudaStream_t s) {
     const size_t smem = node_fused_smem<float>(g.Pk, 3);
-    auto k = node_binned_kernel<NT>;
+    auto k = node_binned_kernel<NT, HALF>;
     SBD_TRY(raise_smem_limit(k, smem));
     k<<<nt, NT, smem, s>>>(nodes, tile_start, ntx, g.nk, g.Pk, win, kin, kout, kb);
     SBD_LAUNCH_CHECK();
@@ -1171,12 +1247,16 @@ int node_step_fused(const NodeRec<T>* nodes, const long long* tile_start, const 
     const int ntx = tiles_per_side(g.nk);
     const dim3 nt(static_cast<unsigned>(ntx) * ntx, static_cast<unsigned>(nb));
     if constexpr (sizeof(T) == 4) {
-        if (t.acc == 3) {
+        if (t.acc == 3 || t.acc == 4) {
             if (g.Pk > kBinSide) {
                 set_error("node step: the binned kernel needs a stencil of at most 8 cells");
                 return SBD_EINVAL;
             }
             const Window<float> win = make_window<float>(g.kwin, g.beta_k, g.Pk);
+            if (t.acc == 4)
+                return t.sched
+                           ? launch_binned<2 * kNodeThreads, true>(nodes, tile_start, nt, ntx, g, win, kin, kout, kb, s)
+                           : launch_binned<kNodeThreads, true>(nodes, tile_start, nt, ntx, g, win, kin, kout, kb, s);
             return t.sched ? launch_binned<2 * kNodeThreads>(nodes, tile_start, nt, ntx, g, win, kin, kout, kb, s)
                            : launch_binned<kNodeThreads>(nodes, tile_start, nt, ntx, g, win, kin, kout, kb, s);
         }

@@ -33,7 +33,8 @@ int node_step_tiled(const NodeRec<T>* nodes, const long long* tile_start, const 
 // fixed point (FP32 only), 3 = binned, no atomics in shared memory (FP32 only; records
 // sorted by tile_sort with by_bin, every tile within kTileSortMax records, stencil <= 8).
 // acc 0-2: sched 0 = records dealt to the lane groups in turn, 1 = one contiguous run per
-// group; acc 3: sched 0 = 512 threads per CTA, 1 = 1024.
+// group; acc 3: sched 0 = 512 threads per CTA, 1 = 1024.  acc 4: acc 3's bins two per warp,
+// one per half-warp, one record per half-warp at a time (see node_binned_body); sched as acc 3.
 struct NodeTuning {
     int acc = 0;
     int sched = 0;

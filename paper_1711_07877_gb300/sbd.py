@@ -460,9 +460,10 @@ def sbd_fit_cache_stats() -> dict:
 
 def sbd_tune(plan: int, reps: int = 3, stream=None) -> list:
     """Time the node-kernel and row-FFT variants, keep the fastest; returns ms per node variant
-    (index acc * 2 + sched, -1 where not applicable) and, at 8 and 9, per FFT split (0, 2)."""
+    (index acc * 2 + sched for acc <= 3, 10 + sched for acc 4, -1 where not applicable) and, at 8
+    and 9, per FFT split (0, 2)."""
     import numpy as np
-    ms = np.zeros(10)
+    ms = np.zeros(12)
     _check(lib.sbd_tune(plan, reps, ms.ctypes.data, _stream(stream)), "sbd_tune")
     return ms.tolist()
 

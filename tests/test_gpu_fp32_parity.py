@@ -93,17 +93,18 @@ def test_fp32_matvec_matches_oracle_sbd_config1(S, config1, flags):
         S.sbd_destroy(p)
 
 
+@pytest.mark.parametrize("acc", [3, 4])
 @pytest.mark.parametrize("sched", [0, 1])
-def test_fp32_binned_node_kernel_matches_oracle_far_part(S, sched):
-    """The binned node kernel (variant acc 3, the one the N = 10^6 bench runs) against the
-    oracle's far part by direct sums, N = 6000 in the disk."""
+def test_fp32_binned_node_kernel_matches_oracle_far_part(S, sched, acc):
+    """The binned node kernels (variants acc 3 and 4, the ones the tuner picks from at N = 10^6)
+    against the oracle's far part by direct sums, N = 6000 in the disk."""
     wl = W.laplace_disk(6000, 51, 1e-6)
     pl = O.make_plan(wl.z, "laplace", wl.delta_min, wl.eps)
     p = plan(S, wl.z, "laplace", wl.delta_min, wl.eps)
     try:
         same_fit(S, p, pl)
         assert S.sbd_plan_info(p)["node_binned"] == 1
-        S.sbd_set_tuning(p, 3, sched, 0)
+        S.sbd_set_tuning(p, acc, sched, 0)
         far = run(S, p, wl.f, fn=S.sbd_far)
         want = O.far_part(pl, wl.f).real
         assert_close(far, want)

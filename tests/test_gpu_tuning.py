@@ -43,7 +43,7 @@ def test_variants_agree_and_tune_picks_one(S, kind):
     try:
         assert S.sbd_plan_info(p)["node_binned"] == 1          # FP32, 8-cell stencils, small tiles
         outs = {}
-        for acc in (0, 1, 2, 3):
+        for acc in (0, 1, 2, 3, 4):
             for sched in (0, 1):
                 for split in (0, 2):
                     S.sbd_set_tuning(p, acc, sched, split)
@@ -61,10 +61,10 @@ def test_variants_agree_and_tune_picks_one(S, kind):
         for k, v in outs.items():
             assert np.max(np.abs(v[idx] - ref)) <= 1e-6 * np.abs(f).sum(), k
         ms = S.sbd_tune(p, reps=2)
-        assert len(ms) == 10 and all(t > 0 for t in ms)
+        assert len(ms) == 12 and all(t > 0 for t in ms)
         info = S.sbd_plan_info(p)
-        best = int(np.argmin(ms[:8]))
-        assert (info["node_acc"], info["node_sched"]) == (best // 2, best % 2)
+        node = {(a, sc): ms[a * 2 + sc] if a < 4 else ms[10 + sc] for a in range(5) for sc in (0, 1)}
+        assert (info["node_acc"], info["node_sched"]) == min(node, key=node.get)
     finally:
         S.sbd_destroy(p)
 
@@ -76,12 +76,13 @@ def test_fp64_rejects_cas_variant(S):
     p = S.sbd_plan(zt, 500, S.SBD_LAPLACE, 0.0, wl.delta_min, 1e-6, S.make_options(form=S.SBD_FORM_FP64))
     try:
         assert S.sbd_plan_info(p)["node_binned"] == 0
-        for acc in (1, 2, 3):
+        for acc in (1, 2, 3, 4, 5):
             with pytest.raises(S.SbdError) as e:
                 S.sbd_set_tuning(p, acc, 0, 0)
             assert e.value.code == S.SBD_EINVAL
         ms = S.sbd_tune(p, reps=1)
         assert ms[0] > 0 and ms[1] > 0 and all(t == -1 for t in ms[2:8]) and ms[8] > 0 and ms[9] > 0
+        assert ms[10] == -1 and ms[11] == -1
     finally:
         S.sbd_destroy(p)
 
