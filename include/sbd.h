@@ -263,7 +263,7 @@ int sbd_offline_fit_radial(const sbd_radial_kernel* kernel, double delta_min, do
 int sbd_matvec(sbd_plan_t plan, const void* f, void* q, int32_t nrhs, void* cuda_stream);
 
 /* sbd_matvec_graph - sbd_matvec replayed from a CUDA graph (no counterpart in the paper):
- * the per-kernel launch cost (12 kernels per call, whatever nrhs) matters for small N.  The first
+ * the per-kernel launch cost (10 kernels per call, whatever nrhs) matters for small N.  The first
  * call for a given nrhs runs one matvec on plan-owned buffers and captures a second one
  * into a graph; every call then copies f into the plan's input buffer, launches the graph
  * and copies the plan's output buffer to q, on a plan-owned stream ordered after and before

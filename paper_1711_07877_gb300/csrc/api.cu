@@ -125,7 +125,6 @@ struct sbd_plan_s {
     int tuned = 0;                     // 1 once sbd_tune chose the variant
     // workspace grids, max_nrhs right-hand sides each (see GridStrides)
     void* wsX = nullptr;
-    void* wsA = nullptr;
     void* wsB = nullptr;
     void* wsC = nullptr;
     double2* sumf = nullptr;
@@ -367,7 +366,6 @@ int build_far(sbd_plan_s* p, cudaStream_t s) {
         const size_t e = sizeof(cx_t<T>) * static_cast<size_t>(p->max_nrhs);
         const size_t m = np.m;
         if ((rc = dev_alloc(p, &p->wsX, e * m * m))) return rc;
-        if ((rc = dev_alloc(p, &p->wsA, e * m * nk))) return rc;
         if ((rc = dev_alloc(p, &p->wsB, e * nk * nk))) return rc;
         if ((rc = dev_alloc(p, &p->wsC, e * nk * nk))) return rc;
         return SBD_OK;
@@ -448,58 +446,57 @@ int build_far(sbd_plan_s* p, cudaStream_t s) {
     const size_t e = sizeof(cx_t<T>) * static_cast<size_t>(p->max_nrhs);
     const size_t m = np.m, nk = np.nk;
     if ((rc = dev_alloc(p, &p->wsX, e * m * m))) return rc;
-    if ((rc = dev_alloc(p, &p->wsA, e * m * nk))) return rc;
     if ((rc = dev_alloc(p, &p->wsB, e * nk * nk))) return rc;
     if ((rc = dev_alloc(p, &p->wsC, e * nk * nk))) return rc;
     return SBD_OK;
 }
 
 // Workspace grids hold nb right-hand sides each, grid b at b times the grid's size (complex
-// elements): X (spreading grid) m x m, or m^2 / 2 for the packed real grid of Laplace, A
-// (row-pass scratch) m x nk, B and C (frequency grids) nk x nk.
+// elements): X (spreading grid) m x m, or m^2 / 2 for the packed real grid of Laplace, B and C
+// (frequency grids) nk x nk, which also hold the transposed first pass (nk x m) of a transform.
 struct GridStrides {
-    long X, A, K;
+    long X, K;
 };
 GridStrides grid_strides(const NufftParams& np, bool real = false) {
     const long m = np.m, nk = np.nk;
-    return {real ? m * m / 2 : m * m, m * nk, nk * nk};
+    return {real ? m * m / 2 : m * m, nk * nk};
 }
 
 // spreading grid X (m x m, rows = y) -> frequency grid K (nk x nk, rows = kx), forward transform.
-// A (m x nk) and Tr (>= nk x m) are scratch.  nb grids in one pass each.
+// Tr (>= nk x m) is scratch.  nb grids in one pass each.
 template <typename T>
-int forward_fft(sbd_plan_s* p, const cx_t<T>* X, cx_t<T>* A, cx_t<T>* Tr, cx_t<T>* K, cudaStream_t s, int nb = 1) {
+int forward_fft(sbd_plan_s* p, const cx_t<T>* X, cx_t<T>* Tr, cx_t<T>* K, cudaStream_t s, int nb = 1) {
     const NufftParams& np = p->np;
     const int m = np.m, nk = np.nk, n = np.n;
     const GridStrides g = grid_strides(np);
     const T* dec = p->uniform ? nullptr : static_cast<const T*>(p->dec);
     // along x (rows y), precorrection exp(sigma |x|^2) fused into the load
     const int sp = p->fft_split;
-    int rc = fft_rows<T>(X, m, m, -m / 2, A, nk, nk, -nk / 2, m, n, -1, dec, dec, nullptr, nullptr, s, 0, 0, kIoPlain,
-                         sp, nb, g.X, g.A);
+    // written transposed: [kx][y], the rows of the pass along y
+    int rc = fft_rows<T>(X, m, m, -m / 2, Tr, 1, nk, -nk / 2, m, n, -1, dec, dec, nullptr, nullptr, s, 0, 0, kIoPlain,
+                         sp, nb, g.X, g.K, m);
     if (rc) return rc;
-    if ((rc = transpose<T>(A, nk, g.A, Tr, m, g.K, m, nk, nb, s))) return rc;   // [y][kx] -> [kx][y]
     // along y (rows kx)
     return fft_rows<T>(Tr, m, m, -m / 2, K, nk, nk, -nk / 2, nk, n, -1, nullptr, nullptr, nullptr, nullptr, s, 0, 0,
                        kIoPlain, sp, nb, g.K, g.K);
 }
 
 // frequency grid K2 (nk x nk, rows = kx) -> spreading grid X (m x m), adjoint transform.
-// A (nk x m) and Tr (>= m x nk) are scratch.
+// Tr (>= m x nk) is scratch.
 // With fold, K2 holds the node step's S over the half node set and the transform is
 // taken of S(eta) + conj(S(-eta)).
 template <typename T>
-int inverse_fft(sbd_plan_s* p, const cx_t<T>* K2, cx_t<T>* A, cx_t<T>* Tr, cx_t<T>* X, cudaStream_t s,
+int inverse_fft(sbd_plan_s* p, const cx_t<T>* K2, cx_t<T>* Tr, cx_t<T>* X, cudaStream_t s,
                 bool fold, int nb = 1) {
     const NufftParams& np = p->np;
     const int m = np.m, nk = np.nk, n = np.n;
     const GridStrides g = grid_strides(np);
     const T* dec = p->uniform ? nullptr : static_cast<const T*>(p->dec);
     const int sp = p->fft_split;
-    int rc = fft_rows<T>(K2, nk, nk, -nk / 2, A, m, m, -m / 2, nk, n, +1, nullptr, nullptr, nullptr, nullptr, s,
-                         fold ? nk : 0, 0, kIoPlain, sp, nb, g.K, g.A);
+    // written transposed: [y][kx]
+    int rc = fft_rows<T>(K2, nk, nk, -nk / 2, Tr, 1, m, -m / 2, nk, n, +1, nullptr, nullptr, nullptr, nullptr, s,
+                         fold ? nk : 0, 0, kIoPlain, sp, nb, g.K, g.K, nk);
     if (rc) return rc;
-    if ((rc = transpose<T>(A, m, g.A, Tr, nk, g.K, nk, m, nb, s))) return rc;   // [kx][y] -> [y][kx]
     return fft_rows<T>(Tr, nk, nk, -nk / 2, X, m, m, -m / 2, m, n, +1, nullptr, nullptr, dec, dec, s, 0, 0, kIoPlain,
                        sp, nb, g.K, g.X);
 }
@@ -513,7 +510,7 @@ template <typename T>
 int kx_low(const sbd_plan_s* p) { return p->np.nk / 2 - (p->np.Pk / 2 + 2); }
 
 template <typename T>
-int forward_fft_real(sbd_plan_s* p, const cx_t<T>* Xp, cx_t<T>* A, cx_t<T>* Tr, cx_t<T>* K, cudaStream_t s,
+int forward_fft_real(sbd_plan_s* p, const cx_t<T>* Xp, cx_t<T>* Tr, cx_t<T>* K, cudaStream_t s,
                      int nb = 1) {
     const NufftParams& np = p->np;
     const int m = np.m, nk = np.nk, n = np.n;
@@ -521,10 +518,10 @@ int forward_fft_real(sbd_plan_s* p, const cx_t<T>* Xp, cx_t<T>* A, cx_t<T>* Tr, 
     const int lo = kx_low<T>(p), w2 = nk - lo;
     const T* dec = p->uniform ? nullptr : static_cast<const T*>(p->dec);
     const int sp = p->fft_split;
-    int rc = fft_rows<T>(Xp, m, m, -m / 2, A, w2, w2, lo - nk / 2, m / 2, n, -1, dec, dec, nullptr, nullptr, s, 0, 0,
-                         kIoPairFwd, sp, nb, g.X, g.A);
+    // written transposed: [kx][y]
+    int rc = fft_rows<T>(Xp, m, m, -m / 2, Tr, 1, w2, lo - nk / 2, m / 2, n, -1, dec, dec, nullptr, nullptr, s, 0, 0,
+                         kIoPairFwd, sp, nb, g.X, g.K, m);
     if (rc) return rc;
-    if ((rc = transpose<T>(A, w2, g.A, Tr, m, g.K, m, w2, nb, s))) return rc;   // [y][kx] -> [kx][y]
     return fft_rows<T>(Tr, m, m, -m / 2, K + static_cast<long>(lo) * nk, nk, nk, -nk / 2, w2, n, -1, nullptr, nullptr,
                        nullptr, nullptr, s, 0, 0, kIoPlain, sp, nb, g.K, g.K);
 }
@@ -534,7 +531,7 @@ int forward_fft_real(sbd_plan_s* p, const cx_t<T>* Xp, cx_t<T>* A, cx_t<T>* Tr, 
 // (the fold is applied on the load); then each pair of y rows is one transform along
 // x from its two half spectra, giving the packed real X.
 template <typename T>
-int inverse_fft_real(sbd_plan_s* p, const cx_t<T>* S, cx_t<T>* A, cx_t<T>* Tr, cx_t<T>* Xp, cudaStream_t s,
+int inverse_fft_real(sbd_plan_s* p, const cx_t<T>* S, cx_t<T>* Tr, cx_t<T>* Xp, cudaStream_t s,
                      int nb = 1) {
     const NufftParams& np = p->np;
     const int m = np.m, nk = np.nk, n = np.n;
@@ -544,10 +541,10 @@ int inverse_fft_real(sbd_plan_s* p, const cx_t<T>* S, cx_t<T>* A, cx_t<T>* Tr, c
     const int sp = p->fft_split;
     // the node step's S completes by the Hermitian fold; the uniform variant's product is whole
     const int herm = p->uniform ? 0 : nk;
-    int rc = fft_rows<T>(S + static_cast<long>(J) * nk, nk, nk, -nk / 2, A, m, m, -m / 2, J, n, +1, nullptr, nullptr,
-                         nullptr, nullptr, s, herm, herm ? J : 0, kIoPlain, sp, nb, g.K, g.A);
+    // written transposed: [y][kx]
+    int rc = fft_rows<T>(S + static_cast<long>(J) * nk, nk, nk, -nk / 2, Tr, 1, m, -m / 2, J, n, +1, nullptr, nullptr,
+                         nullptr, nullptr, s, herm, herm ? J : 0, kIoPlain, sp, nb, g.K, g.K, J);
     if (rc) return rc;
-    if ((rc = transpose<T>(A, m, g.A, Tr, J, g.K, J, m, nb, s))) return rc;   // [kx][y] -> [y][kx]
     return fft_rows<T>(Tr, J, J, 0, Xp, m, m, -m / 2, m / 2, n, +1, nullptr, nullptr, dec, dec, s, 0, 0, kIoPairInv,
                        sp, nb, g.K, g.X);
 }
@@ -564,7 +561,6 @@ int far_apply(sbd_plan_s* p, const void* f, void* q, int nrhs, cudaStream_t s, c
     if (rc) return rc;
     t_sum.end();
     auto* X = static_cast<cx_t<T>*>(p->wsX);
-    auto* A = static_cast<cx_t<T>*>(p->wsA);
     auto* B = static_cast<cx_t<T>*>(p->wsB);
     auto* C = static_cast<cx_t<T>*>(p->wsC);
     const double2 w0 = make_double2(p->w0.real(), p->w0.imag());
@@ -574,7 +570,7 @@ int far_apply(sbd_plan_s* p, const void* f, void* q, int nrhs, cudaStream_t s, c
                               X, s, real, nrhs, p->n))) return rc;
     t1.end();
     StepTimer t2(p, s, SBD_STAGE_FFT_FWD);
-    if ((rc = real ? forward_fft_real<T>(p, X, A, C, B, s, nrhs) : forward_fft<T>(p, X, A, C, B, s, nrhs))) return rc;
+    if ((rc = real ? forward_fft_real<T>(p, X, C, B, s, nrhs) : forward_fft<T>(p, X, C, B, s, nrhs))) return rc;
     t2.end();
     StepTimer t3(p, s, SBD_STAGE_NODE);
     if (p->uniform) {
@@ -591,7 +587,7 @@ int far_apply(sbd_plan_s* p, const void* f, void* q, int nrhs, cudaStream_t s, c
     }
     t3.end();
     StepTimer t4(p, s, SBD_STAGE_FFT_INV);
-    if ((rc = real ? inverse_fft_real<T>(p, C, A, B, X, s, nrhs) : inverse_fft<T>(p, C, A, B, X, s, false, nrhs)))
+    if ((rc = real ? inverse_fft_real<T>(p, C, B, X, s, nrhs) : inverse_fft<T>(p, C, B, X, s, false, nrhs)))
         return rc;
     t4.end();
     if (join) SBD_CUDA_TRY(cudaStreamWaitEvent(s, join, 0));   // D f is ready
@@ -605,13 +601,12 @@ int far_apply(sbd_plan_s* p, const void* f, void* q, int nrhs, cudaStream_t s, c
 template <typename T>
 int nufft_minus_impl(sbd_plan_s* p, const void* f, void* fhat, cudaStream_t s) {
     auto* X = static_cast<cx_t<T>*>(p->wsX);
-    auto* A = static_cast<cx_t<T>*>(p->wsA);
     auto* B = static_cast<cx_t<T>*>(p->wsB);
     auto* C = static_cast<cx_t<T>*>(p->wsC);
     int rc = spread_tiled<T>(static_cast<const PointRec<T>*>(p->pts), p->pt_perm, p->pt_work, p->geom, f,
                              true, X, s);
     if (rc) return rc;
-    if ((rc = forward_fft<T>(p, X, A, C, B, s))) return rc;
+    if ((rc = forward_fft<T>(p, X, C, B, s))) return rc;
     const NodeFrame fr{p->circle_start, p->circle_radius, p->circle_M, p->fit.n_circles, p->np.cx, p->np.cy,
                        p->node_perm, p->half_start, p->np.nk, spread_deconv_of(p)};
     return far_node_gather<T>(static_cast<const NodeRec<T>*>(p->nodes), p->n_rec,
@@ -621,7 +616,6 @@ int nufft_minus_impl(sbd_plan_s* p, const void* f, void* fhat, cudaStream_t s) {
 template <typename T>
 int nufft_plus_impl(sbd_plan_s* p, const void* ghat, void* q, cudaStream_t s) {
     auto* X = static_cast<cx_t<T>*>(p->wsX);
-    auto* A = static_cast<cx_t<T>*>(p->wsA);
     auto* B = static_cast<cx_t<T>*>(p->wsB);
     auto* C = static_cast<cx_t<T>*>(p->wsC);
     const NodeFrame fr{p->circle_start, p->circle_radius, p->circle_M, p->fit.n_circles, p->np.cx, p->np.cy,
@@ -630,7 +624,7 @@ int nufft_plus_impl(sbd_plan_s* p, const void* ghat, void* q, cudaStream_t s) {
                                  static_cast<const T*>(p->cscale_c), p->geom, static_cast<const double2*>(ghat), C,
                                  fr, s);
     if (rc) return rc;
-    if ((rc = inverse_fft<T>(p, C, A, B, X, s, false))) return rc;
+    if ((rc = inverse_fft<T>(p, C, B, X, s, false))) return rc;
     SBD_CUDA_TRY(cudaMemsetAsync(p->zero2, 0, sizeof(double2), s));
     return interp_tiled<T>(static_cast<const PointRec<T>*>(p->tpts), p->tpt_perm, p->tpt_work, p->geom, X,
                            make_double2(0, 0), p->zero2, q, true, s);
@@ -1554,16 +1548,14 @@ int sbd_tune(sbd_plan_t p, int32_t reps, double* ms, void* cuda_stream) {
             auto fwd = [&]() {
                 if (p->form == SBD_FORM_FP32) {
                     auto* X = static_cast<cx_t<float>*>(p->wsX);
-                    auto* A = static_cast<cx_t<float>*>(p->wsA);
                     auto* B = static_cast<cx_t<float>*>(p->wsB);
                     auto* C = static_cast<cx_t<float>*>(p->wsC);
-                    return p->half_nodes ? forward_fft_real<float>(p, X, A, C, B, s) : forward_fft<float>(p, X, A, C, B, s);
+                    return p->half_nodes ? forward_fft_real<float>(p, X, C, B, s) : forward_fft<float>(p, X, C, B, s);
                 }
                 auto* X = static_cast<cx_t<double>*>(p->wsX);
-                auto* A = static_cast<cx_t<double>*>(p->wsA);
                 auto* B = static_cast<cx_t<double>*>(p->wsB);
                 auto* C = static_cast<cx_t<double>*>(p->wsC);
-                return p->half_nodes ? forward_fft_real<double>(p, X, A, C, B, s) : forward_fft<double>(p, X, A, C, B, s);
+                return p->half_nodes ? forward_fft_real<double>(p, X, C, B, s) : forward_fft<double>(p, X, C, B, s);
             };
             if ((rc = fwd())) break;
             cudaEventRecord(a, s);
@@ -2062,11 +2054,10 @@ int batched_impl(const sbd_plan_t* plans, const void* const* f, void* const* q, 
     };
     rc = fork_join([&](sbd_plan_s* p, int i) {
         auto* X = static_cast<cx_t<T>*>(p->wsX);
-        auto* A = static_cast<cx_t<T>*>(p->wsA);
         auto* B = static_cast<cx_t<T>*>(p->wsB);
         auto* C = static_cast<cx_t<T>*>(p->wsC);
-        int r = p->half_nodes ? forward_fft_real<T>(p, X, A, C, B, p->b_stream, nrhs[i])
-                              : forward_fft<T>(p, X, A, C, B, p->b_stream, nrhs[i]);
+        int r = p->half_nodes ? forward_fft_real<T>(p, X, C, B, p->b_stream, nrhs[i])
+                              : forward_fft<T>(p, X, C, B, p->b_stream, nrhs[i]);
         if (!r && p->uniform) {   // the uniform-grid plans' node step: the multiplication, on their stream
             const int nk = p->np.nk;
             r = uniform_multiply<T>(B, p->ucoef, p->kind == SBD_HELMHOLTZ, C, nk, p->half_nodes ? nk / 2 : 0,
@@ -2112,11 +2103,10 @@ int batched_impl(const sbd_plan_t* plans, const void* const* f, void* const* q, 
     // inverse transforms, each plan on its own stream
     rc = fork_join([&](sbd_plan_s* p, int i) {
         auto* X = static_cast<cx_t<T>*>(p->wsX);
-        auto* A = static_cast<cx_t<T>*>(p->wsA);
         auto* B = static_cast<cx_t<T>*>(p->wsB);
         auto* C = static_cast<cx_t<T>*>(p->wsC);
-        return p->half_nodes ? inverse_fft_real<T>(p, C, A, B, X, p->b_stream, nrhs[i])
-                             : inverse_fft<T>(p, C, A, B, X, p->b_stream, false, nrhs[i]);
+        return p->half_nodes ? inverse_fft_real<T>(p, C, B, X, p->b_stream, nrhs[i])
+                             : inverse_fft<T>(p, C, B, X, p->b_stream, false, nrhs[i]);
     });
     if (rc) return rc;
     for (int i = 0; i < count; ++i) SBD_CUDA_TRY(cudaStreamWaitEvent(s, plans[i]->ev_join, 0));   // D f ready

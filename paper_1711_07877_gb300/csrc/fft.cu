@@ -470,7 +470,7 @@ __global__ void __launch_bounds__(kFftThreads, 3) fft_rows_kernel(
     int n, int Q, FftPlan1D plan, const cx_t<T>* __restrict__ tw, const int* __restrict__ perm,
     const T* __restrict__ pre_elem, const T* __restrict__ pre_row,
     const T* __restrict__ post_elem, const T* __restrict__ post_row, HermFold<T> hf, int io,
-    const cx_t<T>* __restrict__ tw2, long in_batch, long out_batch) {
+    const cx_t<T>* __restrict__ tw2, long in_batch, long out_batch, long out_es) {
     using C = cx_t<T>;
     constexpr int NT = kFftThreads;
     constexpr bool inv = SIGN > 0;
@@ -582,7 +582,7 @@ __global__ void __launch_bounds__(kFftThreads, 3) fft_rows_kernel(
             const T pe = post_elem ? post_elem[e] : static_cast<T>(1);
             v.x *= ps0 * pe;
             v.y *= ps1 * pe;
-            dst[e] = v;
+            dst[e * out_es] = v;
         }
     };
     for (int st = fuse1 ? 1 : 0; st < plan.nstages; ++st) {
@@ -609,8 +609,16 @@ __global__ void __launch_bounds__(kFftThreads, 3) fft_rows_kernel(
         const C zk = s[Q == 2 ? (k >> 1) : k], zm = s[Q == 2 ? (km >> 1) : km];
         const T h = static_cast<T>(0.5);
         const T pe = post_elem ? post_elem[e] : static_cast<T>(1);
-        d0[e] = mk<T>(h * pe * (zk.x + zm.x), h * pe * (zk.y - zm.y));
-        d1[e] = mk<T>(h * pe * (zk.y + zm.y), h * pe * (zm.x - zk.x));
+        const C v0 = mk<T>(h * pe * (zk.x + zm.x), h * pe * (zk.y - zm.y));
+        const C v1 = mk<T>(h * pe * (zk.y + zm.y), h * pe * (zm.x - zk.x));
+        if constexpr (sizeof(T) == 4) {
+            if (out_stride == 1) {        // written transposed: the two rows' values are neighbours
+                *reinterpret_cast<float4*>(d0 + e * out_es) = make_float4(v0.x, v0.y, v1.x, v1.y);
+                continue;
+            }
+        }
+        d0[e * out_es] = v0;
+        d1[e * out_es] = v1;
     }
 }
 
@@ -742,7 +750,7 @@ int fft_rows(const cx_t<T>* in, long in_stride, int in_len, int in_shift,
              int rows, int n, int sign,
              const T* pre_elem, const T* pre_row, const T* post_elem, const T* post_row,
              cudaStream_t stream, int herm_n, int herm_row0, int io, int split, int nb, long in_batch,
-             long out_batch) {
+             long out_batch, long out_es) {
     if (rows <= 0 || nb <= 0) return SBD_OK;
     if (nb > 65535) {
         set_error("fft_rows: at most 65535 grids per batch");
@@ -791,7 +799,7 @@ int fft_rows(const cx_t<T>* in, long in_stride, int in_len, int in_shift,
         // half-length phases (split) fit more CTAs per SM
         const int rc = launch_fft_rows<T>(sign, grid, smem, stream, ip, in_stride, in_len, in_shift, op, out_stride,
                                           out_len, out_shift, n, Q, plan, tw, perm, pre_elem, prr, post_elem, por,
-                                          hf, io, tw2, in_batch, out_batch);
+                                          hf, io, tw2, in_batch, out_batch, out_es);
         if (rc) return rc;
     }
     SBD_LAUNCH_CHECK();
@@ -817,7 +825,7 @@ int fft_rows_tables(const cx_t<T>* in, long in_stride, int in_len, cx_t<T>* out,
         const int rc = launch_fft_rows<T>(sign, grid, smem, stream, ip, in_stride, in_len, 0, op, out_stride,
                                           out_len, 0, n, 1, plan, tw, perm, none, none, none, none,
                                           HermFold<T>{nullptr, 0, 0}, static_cast<int>(kIoPlain),
-                                          static_cast<const cx_t<T>*>(nullptr), 0L, 0L);
+                                          static_cast<const cx_t<T>*>(nullptr), 0L, 0L, 1L);
         if (rc) return rc;
     }
     return SBD_OK;
@@ -835,10 +843,10 @@ int transpose(const cx_t<T>* in, long in_stride, long in_batch, cx_t<T>* out, lo
 
 template int fft_rows<float>(const float2*, long, int, int, float2*, long, int, int, int, int, int,
                              const float*, const float*, const float*, const float*, cudaStream_t, int, int,
-                             int, int, int, long, long);
+                             int, int, int, long, long, long);
 template int fft_rows<double>(const double2*, long, int, int, double2*, long, int, int, int, int, int,
                               const double*, const double*, const double*, const double*, cudaStream_t, int, int,
-                              int, int, int, long, long);
+                              int, int, int, long, long, long);
 template int fft_rows_tables<float>(const float2*, long, int, float2*, long, int, int, int, int, const float2*,
                                     const int*, cudaStream_t);
 template int fft_rows_tables<double>(const double2*, long, int, double2*, long, int, int, int, int, const double2*,

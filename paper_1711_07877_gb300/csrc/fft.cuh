@@ -53,12 +53,15 @@ int fft_rows(const cx_t<T>* in, long in_stride, int in_len, int in_shift,
              int rows, int n, int sign,
              const T* pre_elem, const T* pre_row, const T* post_elem, const T* post_row,
              cudaStream_t stream, int herm_n = 0, int herm_row0 = 0, int io = kIoPlain, int split = 0,
-             int nb = 1, long in_batch = 0, long out_batch = 0);
+             int nb = 1, long in_batch = 0, long out_batch = 0, long out_es = 1);
 // split = 2: run every even length as two half-length phases (two 512-thread CTAs per row,
 // two rows' worth of CTAs per SM) even when the whole row would fit; 0: only when it must.
 // nb > 1: the same pass over nb grids (right-hand sides) in one launch, grid b's input and
 // output (and Hermitian fold base) offset by b in_batch / b out_batch elements; the row
 // scale vectors are shared.
+// out_es: element e of output row r goes to out[r * out_stride + e * out_es]; out_stride = 1
+// with out_es = the row count writes the pass transposed (the next pass's rows), in place of a
+// separate transpose.
 
 // Natural-order row transforms of length n (input and output windows start at 0) with
 // caller-provided tables: tw[t] = exp(-2 pi i t / n), perm = the digit reversal of
