@@ -543,7 +543,7 @@ int inverse_fft_real(sbd_plan_s* p, const cx_t<T>* S, cx_t<T>* Tr, cx_t<T>* Xp, 
     const int herm = p->uniform ? 0 : nk;
     // written transposed: [y][kx]
     int rc = fft_rows<T>(S + static_cast<long>(J) * nk, nk, nk, -nk / 2, Tr, 1, m, -m / 2, J, n, +1, nullptr, nullptr,
-                         nullptr, nullptr, s, herm, herm ? J : 0, kIoPlain, sp, nb, g.K, g.K, J);
+                         nullptr, nullptr, s, herm, herm ? J : 0, kIoPlain, sp, nb, g.K, g.K, J, kx_low<T>(p));
     if (rc) return rc;
     return fft_rows<T>(Tr, J, J, 0, Xp, m, m, -m / 2, m / 2, n, +1, nullptr, nullptr, dec, dec, s, 0, 0, kIoPairInv,
                        sp, nb, g.K, g.X);

@@ -414,7 +414,8 @@ __device__ __forceinline__ void dit_stage_out(const cx_t<T>* s, int n, int Lp, c
 // of y_r[t] = sum_{j < Q} x[t + j nq] w_n^{r (t + j nq)} (fold and twist on the load).
 // Hermitian fold of the load (see fft_rows): base of the whole grid, its side (0 = off)
 // and the absolute index of this launch's first row.
-template <typename T> struct HermFold { const cx_t<T>* base; int n; long row0; };
+// lo: rows of the grid below lo are zero, so a row whose mirror row n - row lies below lo needs no fold.
+template <typename T> struct HermFold { const cx_t<T>* base; int n; long row0; int lo; };
 
 // Input element at FFT position idx of the current row (has = false: a zero).  The io mode and
 // whether a Hermitian fold applies are compile-time, so each load loop carries only its own case.
@@ -561,7 +562,8 @@ __global__ void __launch_bounds__(kFftThreads, 3) fft_rows_kernel(
     };
     if (io == kIoPairInv) with_phases(std::integral_constant<int, kIoPairInv>{}, std::false_type{});
     else if (io == kIoPairFwd) with_phases(std::integral_constant<int, kIoPairFwd>{}, std::false_type{});
-    else if (hf.n) with_phases(std::integral_constant<int, kIoPlain>{}, std::true_type{});
+    else if (hf.n && hf.n - (hf.row0 + row) >= hf.lo)
+        with_phases(std::integral_constant<int, kIoPlain>{}, std::true_type{});
     else with_phases(std::integral_constant<int, kIoPlain>{}, std::false_type{});
     __syncthreads();
     int Lp = fuse1 ? R1 : 1;
@@ -750,7 +752,7 @@ int fft_rows(const cx_t<T>* in, long in_stride, int in_len, int in_shift,
              int rows, int n, int sign,
              const T* pre_elem, const T* pre_row, const T* post_elem, const T* post_row,
              cudaStream_t stream, int herm_n, int herm_row0, int io, int split, int nb, long in_batch,
-             long out_batch, long out_es) {
+             long out_batch, long out_es, int herm_lo) {
     if (rows <= 0 || nb <= 0) return SBD_OK;
     if (nb > 65535) {
         set_error("fft_rows: at most 65535 grids per batch");
@@ -795,7 +797,7 @@ int fft_rows(const cx_t<T>* in, long in_stride, int in_len, int in_shift,
         const T* prr = pre_row ? pre_row + r0 * (io == kIoPairFwd ? 2 : 1) : nullptr;
         const T* por = post_row ? post_row + r0 * (io == kIoPairInv ? 2 : 1) : nullptr;
         const HermFold<T> hf{in - static_cast<long>(herm_row0) * in_stride, herm_n,
-                             static_cast<long>(herm_row0) + r0};
+                             static_cast<long>(herm_row0) + r0, herm_lo};
         // half-length phases (split) fit more CTAs per SM
         const int rc = launch_fft_rows<T>(sign, grid, smem, stream, ip, in_stride, in_len, in_shift, op, out_stride,
                                           out_len, out_shift, n, Q, plan, tw, perm, pre_elem, prr, post_elem, por,
@@ -824,7 +826,7 @@ int fft_rows_tables(const cx_t<T>* in, long in_stride, int in_len, cx_t<T>* out,
         const T* none = nullptr;
         const int rc = launch_fft_rows<T>(sign, grid, smem, stream, ip, in_stride, in_len, 0, op, out_stride,
                                           out_len, 0, n, 1, plan, tw, perm, none, none, none, none,
-                                          HermFold<T>{nullptr, 0, 0}, static_cast<int>(kIoPlain),
+                                          HermFold<T>{nullptr, 0, 0, 0}, static_cast<int>(kIoPlain),
                                           static_cast<const cx_t<T>*>(nullptr), 0L, 0L, 1L);
         if (rc) return rc;
     }
@@ -843,10 +845,10 @@ int transpose(const cx_t<T>* in, long in_stride, long in_batch, cx_t<T>* out, lo
 
 template int fft_rows<float>(const float2*, long, int, int, float2*, long, int, int, int, int, int,
                              const float*, const float*, const float*, const float*, cudaStream_t, int, int,
-                             int, int, int, long, long, long);
+                             int, int, int, long, long, long, int);
 template int fft_rows<double>(const double2*, long, int, int, double2*, long, int, int, int, int, int,
                               const double*, const double*, const double*, const double*, cudaStream_t, int, int,
-                              int, int, int, long, long, long);
+                              int, int, int, long, long, long, int);
 template int fft_rows_tables<float>(const float2*, long, int, float2*, long, int, int, int, int, const float2*,
                                     const int*, cudaStream_t);
 template int fft_rows_tables<double>(const double2*, long, int, double2*, long, int, int, int, int, const double2*,

@@ -34,7 +34,8 @@ int fft_max_length(bool fp64);
 // Hermitian fold (herm_n > 0): in points at row herm_row0 of a herm_n x herm_n grid S
 // (in_len == herm_n) and row r of this call is read as S[a][t] + conj(S[herm_n - a]
 // [herm_n - t]) with a = herm_row0 + r (the second term only for a, t >= 1): the
-// transform of S(eta) + conj(S(-eta)) for a centred grid.
+// transform of S(eta) + conj(S(-eta)) for a centred grid.  herm_lo: rows of S below it are
+// zero, so rows a whose mirror herm_n - a lies below it are read plainly.
 //
 // io modes for real data (two real rows per transform, "packed pair" rows
 // z = x_{2j} + i x_{2j+1}):
@@ -53,7 +54,7 @@ int fft_rows(const cx_t<T>* in, long in_stride, int in_len, int in_shift,
              int rows, int n, int sign,
              const T* pre_elem, const T* pre_row, const T* post_elem, const T* post_row,
              cudaStream_t stream, int herm_n = 0, int herm_row0 = 0, int io = kIoPlain, int split = 0,
-             int nb = 1, long in_batch = 0, long out_batch = 0, long out_es = 1);
+             int nb = 1, long in_batch = 0, long out_batch = 0, long out_es = 1, int herm_lo = 0);
 // split = 2: run every even length as two half-length phases (two 512-thread CTAs per row,
 // two rows' worth of CTAs per SM) even when the whole row would fit; 0: only when it must.
 // nb > 1: the same pass over nb grids (right-hand sides) in one launch, grid b's input and
