@@ -603,10 +603,12 @@ __global__ void __launch_bounds__(kFftThreads, 3) fft_rows_kernel(
     // X1(k) = (Z(k) - conj Z(-k)) / 2i, written to grid rows 2 row and 2 row + 1
     C* d0 = out + 2 * row * out_stride;
     C* d1 = d0 + out_stride;
-    for (int e = threadIdx.x; e < out_len; e += NT) {
+    // with two phases this CTA holds the positions k of parity r: the elements e with e + out_shift
+    // of that parity (n even), every other one
+    const int e0 = Q == 2 ? ((r - out_shift) & 1) : 0;
+    for (int e = e0 + Q * threadIdx.x; e < out_len; e += Q * NT) {
         int k = e + out_shift;
         if (k >= n) k -= n;
-        if (Q == 2 && (k & 1) != r) continue;
         const int km = k == 0 ? 0 : n - k;        // same parity as k (n even)
         const C zk = s[Q == 2 ? (k >> 1) : k], zm = s[Q == 2 ? (km >> 1) : km];
         const T h = static_cast<T>(0.5);
