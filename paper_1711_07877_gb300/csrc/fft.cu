@@ -328,8 +328,8 @@ template <typename T> struct MaxB;
 template <> struct MaxB<float>  { static constexpr int n_max = 28672; };
 template <> struct MaxB<double> { static constexpr int n_max = 14336; };
 
-// Radices of the in-register butterflies: prime powers up to 16 (FP32) or 9 (FP64, twice
-// the registers per element), which fit the 80 registers of three CTAs per SM.
+// Radices of the in-register butterflies: prime powers up to 16 and 15 (FP32) or up to 9
+// (FP64, twice the registers per element), which fit the 80 registers of three CTAs per SM.
 // f(integral_constant<R>) for the runtime radix R.
 template <typename T, typename F>
 __device__ __forceinline__ void with_radix(int R, F&& f) {
@@ -342,6 +342,7 @@ __device__ __forceinline__ void with_radix(int R, F&& f) {
         default:
             if constexpr (sizeof(T) == 4) {
                 if (R == 16) f(std::integral_constant<int, 16>{});
+                else if (R == 15) f(std::integral_constant<int, 15>{});
                 else f(std::integral_constant<int, 9>{});
             } else {
                 f(std::integral_constant<int, 9>{});
@@ -505,10 +506,10 @@ __global__ void __launch_bounds__(kFftThreads, 3) fft_rows_kernel(
     // of stage one at shared positions perm[t] + q (q < R1) holds the elements t + G1 q,
     // G1 = nq / R1; consecutive threads take consecutive t, so each of the R1 reads is coalesced,
     // and the group's butterfly runs before anything is stored.
-    // (Fused for the odd first radices 3, 5 and 9, which every row length here has; a row of
+    // (Fused for the odd first radices 3, 5, 9 and 15, which every row length here has; a row of
     // 2^k points takes the plain load, which keeps the number of instantiated loops small.)
     const int R1 = plan.radix[0];
-    const bool fuse1 = plan.nstages >= 2 && (R1 == 3 || R1 == 5 || R1 == 9);
+    const bool fuse1 = plan.nstages >= 2 && (R1 == 3 || R1 == 5 || R1 == 9 || R1 == 15);
     const bool twist = Q == 2 && r != 0;
     auto load_pass = [&](auto io_c, auto fold_c, auto q_c) {
         constexpr int IO = decltype(io_c)::value;
@@ -550,6 +551,7 @@ __global__ void __launch_bounds__(kFftThreads, 3) fft_rows_kernel(
             };
             if (R1 == 3) first(std::integral_constant<int, 3>{});
             else if (R1 == 5) first(std::integral_constant<int, 5>{});
+            else if (sizeof(T) == 4 && R1 == 15) first(std::integral_constant<int, sizeof(T) == 4 ? 15 : 9>{});
             else first(std::integral_constant<int, 9>{});
         } else {
 #pragma unroll 4
@@ -698,8 +700,12 @@ bool fft_make_plan(int n, FftPlan1D& p, bool fp64) {
             rs.push_back(r);
         }
     };
-    chunks(5, e5, 1);
-    chunks(3, e3, 2);
+    if (!fp64 && e3 == 1 && e5 == 1) {
+        rs.push_back(15);                 // a lone 3 and a lone 5: one radix-15 stage (FP32)
+    } else {
+        chunks(5, e5, 1);
+        chunks(3, e3, 2);
+    }
     chunks(2, e2, fp64 ? 3 : 4);
     if (static_cast<int>(rs.size()) > kFftMaxStages) return false;
     for (size_t i = 0; i < rs.size(); ++i) p.radix[i] = rs[i];

@@ -61,7 +61,7 @@ def matvec(S, p, f, n, nrhs=1, fn=None):
 
 @pytest.mark.parametrize("shape", [(12, 20), (160, 320), (243, 250), (1000, 1536), (6, 12500), (3, 6912),
                                    (2, 13824), (4, 10800), (2, 40000), (13824, 2), (64, 2048), (4, 16384),
-                                   (27, 54)])
+                                   (27, 54), (120, 7680)])
 @pytest.mark.parametrize("form", [0, 1])
 @pytest.mark.parametrize("sign", [-1, 1])
 def test_fft2_matches_numpy(S, shape, form, sign):
