@@ -344,6 +344,21 @@ int build_far(sbd_plan_s* p, cudaStream_t s) {
         const int urc = upload(p, &p->psi, np.psi, s);
         if (urc) return urc;
     }
+    p->geom.kpoly = p->geom.spoly = nullptr;
+    if constexpr (sizeof(T) == 4) {   // the FP32 kernels' polynomial windows, where the fit holds
+        std::vector<float4> tab(kWinPolyEntries);
+        float4* d = nullptr;
+        if (window_poly(np.kwin, np.beta_k, np.Pk, np.tol, tab.data())) {
+            const int urc = upload(p, &d, tab, s);
+            if (urc) return urc;
+            p->geom.kpoly = d;
+        }
+        if (window_poly(np.swin, np.beta_s, np.Ps, np.tol, tab.data())) {
+            const int urc = upload(p, &d, tab, s);
+            if (urc) return urc;
+            p->geom.spoly = d;
+        }
+    }
     int rc = point_records<T>(p, p->z, p->n, &p->pts, &p->pt_perm, &p->pt_work, p->pt_ts, s);
     if (rc) return rc;
     if (p->separate) {
@@ -579,8 +594,9 @@ int far_apply(sbd_plan_s* p, const void* f, void* q, int nrhs, cudaStream_t s, c
         if ((rc = uniform_multiply<T>(B, p->ucoef, p->kind == SBD_HELMHOLTZ, C, nk, real ? nk / 2 : 0, nrhs,
                                       static_cast<long>(nk) * nk, s))) return rc;
     } else if (p->node_fused) {
+        // the real path's inverse reads rows kx_low.. only
         if ((rc = node_step_fused<T>(static_cast<const NodeRec<T>*>(p->nodes), p->node_tile_start, p->geom, B, C,
-                                     p->tuning, s, nrhs))) return rc;
+                                     p->tuning, s, nrhs, real ? kx_low<T>(p) : 0))) return rc;
     } else if ((rc = node_step_tiled<T>(static_cast<const NodeRec<T>*>(p->nodes), p->node_tile_start, p->geom, B,
                                         static_cast<cx_t<T>*>(p->ghat), C, s, nrhs))) {
         return rc;
@@ -1591,6 +1607,7 @@ int sbd_tune(sbd_plan_t p, int32_t reps, double* ms, void* cuda_stream) {
     NodeTuning pick = p->tuning;
     int rc = SBD_OK;
     const bool fp32 = p->form == SBD_FORM_FP32;
+    const int row0 = p->half_nodes ? kx_low<float>(p) : 0;   // as in the matvec
     for (int acc = 0; acc <= (fp32 ? 4 : 0) && !rc; ++acc) {
         if (acc == 2 && node_fused_smem<float>(p->np.Pk, 2) > 227 * 1024) continue;
         if (acc >= 3 && !p->node_binned) continue;
@@ -1600,11 +1617,11 @@ int sbd_tune(sbd_plan_t p, int32_t reps, double* ms, void* cuda_stream) {
                 return p->form == SBD_FORM_FP32
                            ? node_step_fused<float>(static_cast<const NodeRec<float>*>(p->nodes), p->node_tile_start,
                                                     p->geom, static_cast<const cx_t<float>*>(p->wsB),
-                                                    static_cast<cx_t<float>*>(p->wsC), t, s)
+                                                    static_cast<cx_t<float>*>(p->wsC), t, s, 1, row0)
                            : node_step_fused<double>(static_cast<const NodeRec<double>*>(p->nodes),
                                                      p->node_tile_start, p->geom,
                                                      static_cast<const cx_t<double>*>(p->wsB),
-                                                     static_cast<cx_t<double>*>(p->wsC), t, s);
+                                                     static_cast<cx_t<double>*>(p->wsC), t, s, 1, row0);
             };
             if ((rc = step())) break;
             if (cudaEventRecord(a, s) != cudaSuccess) { rc = SBD_ECUDA; break; }
@@ -2015,6 +2032,7 @@ int batched_impl(const sbd_plan_t* plans, const void* const* f, void* const* q, 
             jb.P = p->np.Ps;
             jb.win_kind = p->np.swin;
             jb.win_beta = p->np.beta_s;
+            jb.win_poly = p->geom.spoly;
             jb.f = f[i];
             jb.n_pts = p->n;
             jb.grid = p->wsX;
@@ -2083,6 +2101,7 @@ int batched_impl(const sbd_plan_t* plans, const void* const* f, void* const* q, 
             jb.Ws = node_fused_stride(jb.P);
             jb.win_kind = p->np.kwin;
             jb.win_beta = p->np.beta_k;
+            jb.win_poly = p->geom.kpoly;
             jb.kin = p->wsB;
             jb.kout = p->wsC;
             jb.kbatch = static_cast<long>(jb.nk) * jb.nk;
@@ -2126,6 +2145,7 @@ int batched_impl(const sbd_plan_t* plans, const void* const* f, void* const* q, 
             jb.P = p->np.Ps;
             jb.win_kind = p->np.swin;
             jb.win_beta = p->np.beta_s;
+            jb.win_poly = nullptr;   // the gather evaluates the window directly, as launch_interp_chunks
             jb.q = q[i];
             jb.n_pts = p->n_tgt;
             jb.grid = p->wsX;

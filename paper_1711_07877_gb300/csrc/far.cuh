@@ -19,6 +19,8 @@ struct FarGeom {
     double beta_s;    // spreading window parameter
     double beta_k;    // node window parameter
     int swin;         // spreading window (WindowKind)
+    const float4* kpoly;   // FP32 plans: polynomial tables of the node and spreading windows
+    const float4* spoly;   // (window.cuh), or null where the window is evaluated directly
 };
 
 // Deconvolution of the ES spreading window at a node: psi(k) = 1 / phi_hat_s(k) with

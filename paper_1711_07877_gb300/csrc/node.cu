@@ -14,6 +14,8 @@
 //            stencils of every record whose stencil meets the tile (records of the
 //            tile and of the three tiles before it), then stores the tile once.
 // No global atomics, and the output grid needs no clearing.
+#include <algorithm>
+#include <cmath>
 #include <type_traits>
 
 #include "near.cuh"
@@ -121,6 +123,48 @@ __device__ __forceinline__ void lane_weights(int sub, int P, const Window<T>& wi
     if (sub < P) {
         wx = win(static_cast<T>(sub - P / 2 + 1) - fx);
         wy = win(static_cast<T>(sub - P / 2 + 1) - fy);
+    }
+}
+
+// The same weights, for the point kernels: in FP32 with a polynomial table (window.cuh), copied
+// to shared memory by the caller (tab), each record's weights are two Horner chains on the
+// lane's offset instead of the window's square root, division and exponential.
+template <typename T>
+struct LaneWin {
+    Window<T> win;
+    int sub, P;
+    __device__ __forceinline__ LaneWin(const Window<T>& w, int sub_, int P_, const float4*) : win(w), sub(sub_), P(P_) {}
+    __device__ __forceinline__ void operator()(T fx, T fy, T& wx, T& wy) const {
+        lane_weights<T>(sub, P, win, fx, fy, wx, wy);
+    }
+};
+
+template <>
+struct LaneWin<float> {
+    Window<float> win;
+    int sub, P;
+    const float4* tab;   // shared copy of win.poly, or null
+    __device__ __forceinline__ LaneWin(const Window<float>& w, int sub_, int P_, const float4* tab_)
+        : win(w), sub(sub_), P(P_), tab(w.poly != nullptr && sub_ < kWinPolyOffsets ? tab_ : nullptr) {}
+    __device__ __forceinline__ void operator()(float fx, float fy, float& wx, float& wy) const {
+        if (win.poly != nullptr) {
+            wx = 0.f;
+            wy = 0.f;
+            if (tab != nullptr)
+                poly_weights(tab[sub], tab[kWinPolyOffsets + sub], tab[2 * kWinPolyOffsets + sub], fx, fy, wx, wy);
+        } else {
+            lane_weights<float>(sub, P, win, fx, fy, wx, wy);
+        }
+    }
+};
+
+// Shared copy of a window's polynomial table (FP32 kernels; nothing otherwise), made before
+// the caller's next __syncthreads.
+template <typename T>
+__device__ __forceinline__ void copy_poly(const Window<T>& win, float4* tab) {
+    if constexpr (sizeof(T) == 4) {
+        if (win.poly != nullptr)
+            for (int e = threadIdx.x; e < kWinPolyEntries; e += blockDim.x) tab[e] = win.poly[e];
     }
 }
 
@@ -354,11 +398,12 @@ __device__ __forceinline__ void interp_chunk_body(const PointRec<T>* __restrict_
     const int sub = lane % G;
     const unsigned gmask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << (lane & ~(G - 1)));
     const int group = threadIdx.x / G, ngroups = blockDim.x / G;
+    const LaneWin<T> lw(win, sub, P, nullptr);
     for (long long i = b0 + group; i < b1; i += ngroups) {
         const PointRec<T> q = rec[i];
         const int rx = q.cell.x - ox, ry = q.cell.y - oy;   // in [0, 64): the record's own tile
         T wx, wy;
-        lane_weights<T>(sub, P, win, q.frac.x, q.frac.y, wx, wy);
+        lw(q.frac.x, q.frac.y, wx, wy);
         for (int rr = 0; rr < nr; ++rr) {
             T sr = 0, si = 0;
             const T* col = s + static_cast<long>(rr) * kC * W * W + kC * (static_cast<long>(rx) * W + ry + sub);
@@ -400,6 +445,8 @@ __device__ __forceinline__ void spread_chunk_body(const PointRec<T>* __restrict_
                                                   int rg, int grp, long gstride) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* acc = reinterpret_cast<T*>(smem_raw);          // [rg][W][W][RV ? 1 : 2]
+    __shared__ float4 wtab[kWinPolyEntries];
+    copy_poly(win, wtab);
     constexpr int kC = RV ? 1 : 2;
     const int W = kNodeTile + P - 1;
     const long plane = static_cast<long>(kC) * W * W;
@@ -413,11 +460,12 @@ __device__ __forceinline__ void spread_chunk_body(const PointRec<T>* __restrict_
     const int sub = lane % G;
     const unsigned gmask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << (lane & ~(G - 1)));
     const int group = threadIdx.x / G, ngroups = blockDim.x / G;
+    const LaneWin<T> lw(win, sub, P, wtab);
     for (long long i = b0 + group; i < b1; i += ngroups) {
         const PointRec<T> q = rec[i];
         const int rx = q.cell.x - ox, ry = q.cell.y - oy;   // in [0, 64): the record's own tile
         T wx, wy;
-        lane_weights<T>(sub, P, win, q.frac.x, q.frac.y, wx, wy);
+        lw(q.frac.x, q.frac.y, wx, wy);
         for (int rr = 0; rr < nr; ++rr) {
             const cx_t<T> g = val.get(i, r0 + rr);
             const T gr = g.x * wy, gi = g.y * wy;
@@ -516,7 +564,8 @@ __device__ __forceinline__ int find_job(const Jobs& J, int it) {
 
 template <typename T>
 __device__ __forceinline__ Window<T> job_window(const PointJob& jb) {
-    return Window<T>{jb.win_kind, static_cast<T>(jb.win_beta), static_cast<T>(2.0 / jb.P)};
+    return Window<T>{jb.win_kind, static_cast<T>(jb.win_beta), static_cast<T>(2.0 / jb.P),
+                     sizeof(T) == 4 ? jb.win_poly : nullptr};
 }
 
 // Spreading of the whole batch in one cooperative launch: every CTA first clears its share of
@@ -620,8 +669,10 @@ __device__ __forceinline__ void node_fused_body(
     using C = cx_t<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ float red[NT / 32];
+    __shared__ float4 wtab[kWinPolyEntries];
     const long long b0 = tile_start[tile], b1 = tile_start[tile + 1];
     if (b0 == b1) return;
+    copy_poly(win, wtab);
     const int W = kNodeTile + P - 1;
     constexpr bool kF2 = sizeof(T) == 4 && ACC == 1;
     constexpr bool kI64 = sizeof(T) == 4 && ACC == 2;
@@ -684,17 +735,15 @@ __device__ __forceinline__ void node_fused_body(
         iend = min(b1, i + len);
         istep = 1;
     }
+    const LaneWin<T> lw(win, sub, P, wtab);
     NodeRec<T> nxt;
     if (i < iend) nxt = rec[i];
     for (; i < iend; i += istep) {
         const NodeRec<T> q = nxt;
         if (i + istep < iend) nxt = rec[i + istep];          // prefetch
         const int rx = q.cell.x - ox, ry = q.cell.y - oy;
-        T wx = 0, wy = 0;
-        if (sub < P) {
-            wx = win(static_cast<T>(sub - P / 2 + 1) - q.frac.x);
-            wy = win(static_cast<T>(sub - P / 2 + 1) - q.frac.y);
-        }
+        T wx, wy;
+        lw(q.frac.x, q.frac.y, wx, wy);
         const int base = rx * Ws + ry + sub;
         T sr = 0, si = 0;
 #pragma unroll
@@ -835,6 +884,7 @@ __device__ __forceinline__ void node_binned_body(
     }
     for (int k = tid; k <= kBins; k += NT) bstart[k] = cnt;
     if (tid == 0) next_bin = 0;
+    const bool poly = win.poly != nullptr;   // window weights from the polynomial table (registers)
     __syncthreads();
     // bin starts: record i opens bins (bin(i - 1), bin(i)] (records sorted by bin)
     for (int i = tid; i < cnt; i += NT) {
@@ -866,6 +916,12 @@ __device__ __forceinline__ void node_binned_body(
         const int half = lane >> 4, hl = lane & 15;
         const int cb = hl & 7, rh = hl >> 3;
         const float offw = static_cast<float>(cb - P / 2 + 1);
+        float4 pc0 = make_float4(0.f, 0.f, 0.f, 0.f), pc1 = pc0, pc2 = pc0;
+        if (poly) {
+            pc0 = __ldg(win.poly + cb);
+            pc1 = __ldg(win.poly + kWinPolyOffsets + cb);
+            pc2 = __ldg(win.poly + 2 * kWinPolyOffsets + cb);
+        }
         int rowk[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k) rowk[k] = (k & 1) + 4 * (k >> 1) + 2 * rh;
@@ -893,7 +949,9 @@ __device__ __forceinline__ void node_binned_body(
                     const NodeRec<float> q = nxt;
                     if (j + 1 < len) nxt = rec[b0 + e0 + j + 1];
                     base = (q.cell.x - ox) * kBinWs + (q.cell.y - oy);
-                    if (cb < P) {
+                    if (poly) {
+                        poly_weights(pc0, pc1, pc2, q.frac.x, q.frac.y, wx, wy);
+                    } else if (cb < P) {
                         wx = win(offw - q.frac.x);
                         wy = win(offw - q.frac.y);
                     }
@@ -933,6 +991,12 @@ __device__ __forceinline__ void node_binned_body(
     const int ca = lane >> 2, cb = lane & 3;                        // cells (ca, cb), (ca, cb + 4)
     const float offw = static_cast<float>(sub - P / 2 + 1);
     const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4;
+    float4 pc0 = make_float4(0.f, 0.f, 0.f, 0.f), pc1 = pc0, pc2 = pc0;
+    if (poly) {
+        pc0 = __ldg(win.poly + sub);
+        pc1 = __ldg(win.poly + kWinPolyOffsets + sub);
+        pc2 = __ldg(win.poly + 2 * kWinPolyOffsets + sub);
+    }
     for (; !HALF;) {
         int slot = 0;
         if (lane == 0) slot = atomicAdd(&next_bin, 1);
@@ -952,7 +1016,9 @@ __device__ __forceinline__ void node_binned_body(
                 const NodeRec<float> q = nxt;
                 if (jr + 4 < e1) nxt = rec[b0 + jr + 4];
                 base = (q.cell.x - ox) * kBinWs + (q.cell.y - oy);
-                if (sub < P) {
+                if (poly) {
+                    poly_weights(pc0, pc1, pc2, q.frac.x, q.frac.y, wx, wy);
+                } else if (sub < P) {
                     wx = win(offw - q.frac.x);
                     wy = win(offw - q.frac.y);
                 }
@@ -1067,7 +1133,8 @@ __global__ void __launch_bounds__(kNodeThreads * (BINNED ? 2 : 1), 1) node_batch
         const int tile = local % jb.ntiles, r = local / jb.ntiles;
         const auto* kin = static_cast<const cx_t<T>*>(jb.kin) + r * jb.kbatch;
         auto* kout = static_cast<cx_t<T>*>(jb.kout) + r * jb.kbatch;
-        const Window<T> win{jb.win_kind, static_cast<T>(jb.win_beta), static_cast<T>(2.0 / jb.P)};
+        const Window<T> win{jb.win_kind, static_cast<T>(jb.win_beta), static_cast<T>(2.0 / jb.P),
+                            sizeof(T) == 4 ? jb.win_poly : nullptr};
         if constexpr (BINNED) {
             if constexpr (sizeof(T) == 4)
                 node_binned_body<2 * kNodeThreads>(static_cast<const NodeRec<float>*>(jb.rec), jb.tile_start,
@@ -1091,8 +1158,8 @@ inline int fused_p8(int P) { return P <= 8 ? 8 : (P <= 16 ? 16 : 32); }
 inline int tiles_per_side(int n) { return (n + kNodeTile - 1) / kNodeTile; }
 
 template <typename T>
-Window<T> make_window(int kind, double beta, int P) {
-    return Window<T>{kind, static_cast<T>(beta), static_cast<T>(2.0 / P)};
+Window<T> make_window(int kind, double beta, int P, const float4* poly = nullptr) {
+    return Window<T>{kind, static_cast<T>(beta), static_cast<T>(2.0 / P), sizeof(T) == 4 ? poly : nullptr};
 }
 
 template <typename T, typename Rec, typename Out, bool PK = false>
@@ -1145,6 +1212,60 @@ int launch_scatter(const Rec* rec, const long long* tile_start, int n, int P, in
 }
 
 }  // namespace
+
+bool window_poly(int kind, double beta, int P, double tol, float4* table) {
+    constexpr int K = kWinPolyDeg + 1;
+    for (int e = 0; e < kWinPolyEntries; ++e) table[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (P < 1 || P > kWinPolyOffsets || !(beta > 0.0)) return false;
+    const double pi = 3.14159265358979323846;
+    auto window = [&](double d) {   // the window of window.cuh, in FP64
+        if (kind == kWinGauss) return std::exp(-beta * d * d);
+        const double z = d * 2.0 / P, r = 1.0 - z * z;
+        return r > 0.0 ? std::exp(-beta * z * z / (1.0 + std::sqrt(r))) : 0.0;
+    };
+    const double bound = std::max(1.2e-7, 0.01 * tol);
+    for (int j = 0; j < P; ++j) {
+        const double off = j - P / 2 + 1;
+        // Chebyshev interpolation in s = 2 f - 1 at the K Chebyshev points (first kind)
+        double y[K], a[K];
+        for (int k = 0; k < K; ++k) y[k] = window(off - 0.5 * (std::cos(pi * (k + 0.5) / K) + 1.0));
+        for (int i = 0; i < K; ++i) {
+            double acc = 0.0;
+            for (int k = 0; k < K; ++k) acc += y[k] * std::cos(pi * i * (k + 0.5) / K);
+            a[i] = (i == 0 ? 1.0 : 2.0) * acc / K;
+        }
+        // sum_i a_i T_i(s) in powers of s (T_{i+1} = 2 s T_i - T_{i-1})
+        double mono[K] = {}, t0[K] = {}, t1[K] = {}, t2[K];
+        t0[0] = 1.0;
+        t1[1] = 1.0;
+        mono[0] = a[0];
+        for (int e = 0; e < K; ++e) mono[e] += a[1] * t1[e];
+        for (int i = 2; i < K; ++i) {
+            for (int e = 0; e < K; ++e) t2[e] = (e > 0 ? 2.0 * t1[e - 1] : 0.0) - t0[e];
+            for (int e = 0; e < K; ++e) {
+                mono[e] += a[i] * t2[e];
+                t0[e] = t1[e];
+                t1[e] = t2[e];
+            }
+        }
+        float c[K];
+        for (int k = 0; k < K; ++k) c[k] = static_cast<float>(mono[kWinPolyDeg - k]);   // highest first
+        for (int q = 0; q < kWinPolyQuads; ++q)
+            table[q * kWinPolyOffsets + j] = make_float4(c[4 * q], c[4 * q + 1], c[4 * q + 2], c[4 * q + 3]);
+        // the kernels' FP32 Horner evaluation against the window
+        for (int t = 0; t < 1024; ++t) {
+            const float f = (t + 0.5f) / 1024.f;
+            const float sv = std::fma(2.f, f, -1.f);
+            float acc = c[0];
+            for (int k = 1; k < K; ++k) acc = std::fma(acc, sv, c[k]);
+            if (std::fabs(static_cast<double>(acc) - window(off - static_cast<double>(f))) > bound) {
+                for (int e = 0; e < kWinPolyEntries; ++e) table[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+                return false;
+            }
+        }
+    }
+    return true;
+}
 
 template <typename Rec>
 int tile_sort(const Rec* in, long n_rec, int n, Rec* sorted, int* perm, long long* tile_start, cudaStream_t s,
@@ -1237,13 +1358,23 @@ int launch_binned(const NodeRec<float>* nodes, const long long* tile_start, dim3
 
 template <typename T>
 int node_step_fused(const NodeRec<T>* nodes, const long long* tile_start, const FarGeom& g,
-                    const cx_t<T>* kin, cx_t<T>* kout, const NodeTuning& t, cudaStream_t s, int nb) {
+                    const cx_t<T>* kin, cx_t<T>* kout, const NodeTuning& t, cudaStream_t s, int nb, int row0) {
     if (nb < 1 || nb > 65535) {
         set_error("node step: 1 to 65535 right-hand sides per launch");
         return SBD_EINVAL;
     }
+    if (row0 < 0 || row0 >= g.nk) {
+        set_error("node step: first cleared row outside the grid");
+        return SBD_EINVAL;
+    }
     const long kb = static_cast<long>(g.nk) * g.nk;
-    SBD_CUDA_TRY(cudaMemsetAsync(kout, 0, sizeof(cx_t<T>) * static_cast<size_t>(kb) * nb, s));
+    // the stencils add into a cleared grid: rows row0.. (the rows the caller reads) of each grid
+    const size_t row_bytes = sizeof(cx_t<T>) * static_cast<size_t>(g.nk);
+    if (nb == 1)
+        SBD_CUDA_TRY(cudaMemsetAsync(kout + static_cast<long>(row0) * g.nk, 0, row_bytes * (g.nk - row0), s));
+    else
+        SBD_CUDA_TRY(cudaMemset2DAsync(kout + static_cast<long>(row0) * g.nk, sizeof(cx_t<T>) * kb, 0,
+                                       row_bytes * (g.nk - row0), nb, s));
     const int ntx = tiles_per_side(g.nk);
     const dim3 nt(static_cast<unsigned>(ntx) * ntx, static_cast<unsigned>(nb));
     if constexpr (sizeof(T) == 4) {
@@ -1252,7 +1383,7 @@ int node_step_fused(const NodeRec<T>* nodes, const long long* tile_start, const 
                 set_error("node step: the binned kernel needs a stencil of at most 8 cells");
                 return SBD_EINVAL;
             }
-            const Window<float> win = make_window<float>(g.kwin, g.beta_k, g.Pk);
+            const Window<float> win = make_window<float>(g.kwin, g.beta_k, g.Pk, g.kpoly);
             if (t.acc == 4)
                 return t.sched
                            ? launch_binned<2 * kNodeThreads, true>(nodes, tile_start, nt, ntx, g, win, kin, kout, kb, s)
@@ -1264,7 +1395,7 @@ int node_step_fused(const NodeRec<T>* nodes, const long long* tile_start, const 
     const int W = kNodeTile + g.Pk - 1;
     const int P8 = fused_p8(g.Pk);
     const int Ws = fused_stride(W, P8);
-    const Window<T> win = make_window<T>(g.kwin, g.beta_k, g.Pk);
+    const Window<T> win = make_window<T>(g.kwin, g.beta_k, g.Pk, g.kpoly);
     if (P8 == 8) return launch_fused_g<T, 8>(nodes, tile_start, nt, ntx, g, Ws, win, kin, kout, t, kb, s);
     if (P8 == 16) return launch_fused_g<T, 16>(nodes, tile_start, nt, ntx, g, Ws, win, kin, kout, t, kb, s);
     return launch_fused_g<T, 32>(nodes, tile_start, nt, ntx, g, Ws, win, kin, kout, t, kb, s);
@@ -1307,7 +1438,7 @@ inline int rhs_group(size_t per, int nrhs) {
 template <typename T, int G, bool PK, bool RV>
 int launch_spread_chunks(const PointRec<T>* pts, const PointWork& work, const FarGeom& g, PointVal<T> val,
                          cx_t<T>* grid, int nrhs, long gstride, cudaStream_t s) {
-    const Window<T> win = make_window<T>(g.swin, g.beta_s, g.Ps);
+    const Window<T> win = make_window<T>(g.swin, g.beta_s, g.Ps, g.spoly);
     const size_t W = kNodeTile + g.Ps - 1;
     const size_t per = (RV ? 1 : 2) * sizeof(T) * W * W;
     const int rg = rhs_group(per, nrhs);
@@ -1323,6 +1454,8 @@ int launch_spread_chunks(const PointRec<T>* pts, const PointWork& work, const Fa
 template <typename T, int G, bool PK>
 int launch_interp_chunks(const PointRec<T>* pts, const PointWork& work, const FarGeom& g, const cx_t<T>* grid,
                          const PointOut<T>& out, int nrhs, long gstride, cudaStream_t s) {
+    // the window evaluated directly: the table's shared-memory reads cost this gather loop more
+    // than they save (it is bound by shared-memory wavefronts; 0.26 against 0.33 ms at N = 10^6)
     const Window<T> win = make_window<T>(g.swin, g.beta_s, g.Ps);
     const size_t W = kNodeTile + g.Ps - 1;
     const size_t per = (PK ? 1 : 2) * sizeof(T) * W * W;
@@ -1530,7 +1663,7 @@ int node_batch(const NodeJobs& J, bool binned, BatchSync* sync, unsigned phantom
     template size_t node_fused_smem<T>(int, int);                                                            \
     template int fill_grid<T>(cx_t<T>*, long, T, T, cudaStream_t);                                          \
     template int node_step_fused<T>(const NodeRec<T>*, const long long*, const FarGeom&, const cx_t<T>*,     \
-                                    cx_t<T>*, const NodeTuning&, cudaStream_t, int);                         \
+                                    cx_t<T>*, const NodeTuning&, cudaStream_t, int, int);                    \
     template int spread_tiled<T>(const PointRec<T>*, const int*, const PointWork&, const FarGeom&,           \
                                  const void*, bool, cx_t<T>*, cudaStream_t, bool, int, long);                \
     template int interp_tiled<T>(const PointRec<T>*, const int*, const PointWork&, const FarGeom&,           \

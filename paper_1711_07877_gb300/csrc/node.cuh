@@ -7,6 +7,7 @@
 
 #include "common.cuh"
 #include "far.cuh"
+#include "window.cuh"
 
 namespace sbd {
 
@@ -52,7 +53,8 @@ template <typename T>
 size_t node_fused_smem(int Pk, int acc = 0);   // dynamic shared memory of the fused kernel
 template <typename T>
 int node_step_fused(const NodeRec<T>* nodes, const long long* tile_start, const FarGeom& g,
-                    const cx_t<T>* kin, cx_t<T>* kout, const NodeTuning& t, cudaStream_t s, int nb = 1);
+                    const cx_t<T>* kin, cx_t<T>* kout, const NodeTuning& t, cudaStream_t s, int nb = 1,
+                    int row0 = 0);
 
 // Work list of the point kernels (spreading, interpolation): item w is the records
 // [begin[w], begin[w + 1]) of the 64 x 64 tile tile[w], at most `chunk` of them; the
@@ -110,6 +112,7 @@ struct PointJob {
     PointWork work;         // chunks of the records
     int ntx, m, P, win_kind;
     double win_beta;
+    const float4* win_poly; // FP32: the window's polynomial table, or null
     const void* f;          // spreading: values (float64 / complex128), point l of rhs r at r * n_pts + l
     void* q;                // interpolation: output, same layout
     long n_pts;
@@ -134,6 +137,7 @@ struct NodeJob {
     const long long* tile_start;
     int ntx, nk, P, Ws, ntiles, win_kind;
     double win_beta;
+    const float4* win_poly; // FP32: the window's polynomial table, or null
     const void* kin;
     void* kout;             // cleared by the launch before the node step
     long kbatch;            // complex elements between the right-hand sides' grids
@@ -171,5 +175,10 @@ template <typename T>
 int point_rhs_group(int P, bool two_planes, int nrhs);
 // Dynamic shared memory of the fused node kernel's stride for stencil P.
 int node_fused_stride(int Pk);
+// Polynomial table of a window for the FP32 stencil kernels (layout: window.cuh), kWinPolyEntries
+// entries for a stencil of P <= 16 cells, fitted in FP64.  Returns false (the kernels then
+// evaluate the window directly) where P > 16 or where the table, evaluated in FP32 as the kernels
+// do, departs from the window by more than max(1.2e-7, tol / 100) at a fraction in (0, 1).
+bool window_poly(int kind, double beta, int P, double tol, float4* table);
 
 }  // namespace sbd

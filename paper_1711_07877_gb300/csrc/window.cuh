@@ -19,11 +19,44 @@ template <typename T> __device__ __forceinline__ T wsqrt(T x);
 template <> __device__ __forceinline__ float wsqrt<float>(float x) { return sqrtf(x); }
 template <> __device__ __forceinline__ double wsqrt<double>(double x) { return sqrt(x); }
 
+// Polynomial form of a window for the FP32 stencil kernels (stencils of at most 16 cells):
+// the weight of stencil offset j (0 <= j < P) at fraction f in [0, 1), w(j - P/2 + 1 - f), is a
+// polynomial of degree kWinPolyDeg in s = 2 f - 1 (Chebyshev interpolation of the window in
+// FP64 on the host, converted to powers of s).  Layout: coefficient k (highest power first) of
+// offset j is component k % 4 of entry (k / 4) * 16 + j, so the three float4 of one offset sit
+// 16 entries apart and a warp's reads of one group touch consecutive 16-byte slots; offsets
+// j >= P hold zeros.
+constexpr int kWinPolyDeg = 11;
+constexpr int kWinPolyOffsets = 16;
+constexpr int kWinPolyQuads = (kWinPolyDeg + 4) / 4;              // float4 per offset
+constexpr int kWinPolyEntries = kWinPolyQuads * kWinPolyOffsets;  // float4 per table
+
+__device__ __forceinline__ float poly_quad(float acc, const float4 c, float s) {
+    acc = fmaf(acc, s, c.x);
+    acc = fmaf(acc, s, c.y);
+    acc = fmaf(acc, s, c.z);
+    return fmaf(acc, s, c.w);
+}
+
+// Weights of one offset at the fractions fx, fy (Horner in s, the two chains interleaved).
+__device__ __forceinline__ void poly_weights(const float4 c0, const float4 c1, const float4 c2, float fx, float fy,
+                                             float& wx, float& wy) {
+    static_assert(kWinPolyQuads == 3, "three coefficient groups");
+    const float sx = fmaf(2.f, fx, -1.f), sy = fmaf(2.f, fy, -1.f);
+    float ax = fmaf(fmaf(fmaf(c0.x, sx, c0.y), sx, c0.z), sx, c0.w);
+    float ay = fmaf(fmaf(fmaf(c0.x, sy, c0.y), sy, c0.z), sy, c0.w);
+    ax = poly_quad(ax, c1, sx);
+    ay = poly_quad(ay, c1, sy);
+    wx = poly_quad(ax, c2, sx);
+    wy = poly_quad(ay, c2, sy);
+}
+
 template <typename T>
 struct Window {
     int kind;
     T beta;
-    T inv_half;   // 2 / P (ES only)
+    T inv_half;                     // 2 / P (ES only)
+    const float4* poly = nullptr;   // FP32 kernels: the polynomial table (device), or null
     __device__ __forceinline__ T operator()(T d) const {
         if (kind == kWinGauss) return wexp<T>(-beta * d * d);
         // sqrt(1 - z^2) - 1 = -z^2 / (1 + sqrt(1 - z^2)): no cancellation near the centre,
