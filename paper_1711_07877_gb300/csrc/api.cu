@@ -345,6 +345,7 @@ int build_far(sbd_plan_s* p, cudaStream_t s) {
         if (urc) return urc;
     }
     p->geom.kpoly = p->geom.spoly = nullptr;
+    p->geom.node_bins = nullptr;
     if constexpr (sizeof(T) == 4) {   // the FP32 kernels' polynomial windows, where the fit holds
         std::vector<float4> tab(kWinPolyEntries);
         float4* d = nullptr;
@@ -451,7 +452,17 @@ int build_far(sbd_plan_s* p, cudaStream_t s) {
         long long most = 0;
         for (size_t t = 0; t + 1 < ts.size(); ++t) most = std::max(most, ts[t + 1] - ts[t]);
         p->node_binned = p->node_fused && most <= kTileSortMax && node_fused_smem<T>(np.Pk, 3) <= 227 * 1024;
-        if (p->node_binned) p->tuning.acc = 3, p->tuning.sched = 1;   // the fastest untuned choice
+        if (p->node_binned) {
+            p->tuning.acc = 3, p->tuning.sched = 1;   // the fastest untuned choice
+            if constexpr (sizeof(T) == 4) {
+                void* bins = nullptr;
+                const int ntiles = ntx * ntx;
+                if ((rc = dev_alloc(p, &bins, sizeof(BinTable) * static_cast<size_t>(ntiles)))) return rc;
+                if ((rc = node_bin_tables(static_cast<const NodeRec<float>*>(p->nodes), p->node_tile_start, ntiles,
+                                          static_cast<BinTable*>(bins), s))) return rc;
+                p->geom.node_bins = bins;
+            }
+        }
     }
     if (!p->node_fused && (rc = dev_alloc(p, &p->ghat, sizeof(cx_t<T>) * p->n_rec))) return rc;
     std::vector<T> dec(np.m);
@@ -2102,6 +2113,7 @@ int batched_impl(const sbd_plan_t* plans, const void* const* f, void* const* q, 
             jb.win_kind = p->np.kwin;
             jb.win_beta = p->np.beta_k;
             jb.win_poly = p->geom.kpoly;
+            jb.bins = p->geom.node_bins;
             jb.kin = p->wsB;
             jb.kout = p->wsC;
             jb.kbatch = static_cast<long>(jb.nk) * jb.nk;

@@ -857,11 +857,11 @@ static_assert(kBinWs >= kBinW && kBinWs % 16 == 12, "binned stride");
 // planes).
 template <int NT, bool HALF = false>
 __device__ __forceinline__ void node_binned_body(
-    const NodeRec<float>* __restrict__ rec, const long long* __restrict__ tile_start, int ntx, int n, int P,
-    const Window<float>& win, const float2* __restrict__ kin, float2* __restrict__ kout, int tile) {
+    const NodeRec<float>* __restrict__ rec, const long long* __restrict__ tile_start,
+    const BinTable* __restrict__ bins, int ntx, int n, int P, const Window<float>& win,
+    const float2* __restrict__ kin, float2* __restrict__ kout, int tile) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ int bstart[kBins + 1];
-    __shared__ int border[kBins];                                   // bins, largest first
+    __shared__ __align__(16) BinTable tab;                          // bin starts, bins largest first
     __shared__ int next_bin;
     const long long b0 = tile_start[tile], b1 = tile_start[tile + 1];
     if (b0 == b1) return;                                           // uniform per block
@@ -873,6 +873,8 @@ __device__ __forceinline__ void node_binned_body(
     const int W = kNodeTile + P - 1;
     const int rows = min(W, n - ox), cols = min(W, n - oy);
     const int tid = threadIdx.x;
+    constexpr int kTabVec = sizeof(BinTable) / sizeof(int4);
+    if (tid < kTabVec) reinterpret_cast<int4*>(&tab)[tid] = reinterpret_cast<const int4*>(bins + tile)[tid];
     for (int idx = tid; idx < kBinW * kBinW; idx += NT) {
         const int r = idx / kBinW, c = idx - r * kBinW;
         float2 v = make_float2(0.f, 0.f);
@@ -882,33 +884,8 @@ __device__ __forceinline__ void node_binned_body(
 #pragma unroll
         for (int k = 0; k < 4; ++k) acc[k * plane + o] = make_float2(0.f, 0.f);
     }
-    for (int k = tid; k <= kBins; k += NT) bstart[k] = cnt;
     if (tid == 0) next_bin = 0;
     const bool poly = win.poly != nullptr;   // window weights from the polynomial table (registers)
-    __syncthreads();
-    // bin starts: record i opens bins (bin(i - 1), bin(i)] (records sorted by bin)
-    for (int i = tid; i < cnt; i += NT) {
-        const int bi = bin_in_tile(rec[b0 + i].cell);
-        const int bp = i > 0 ? bin_in_tile(rec[b0 + i - 1].cell) : -1;
-        for (int k = bp + 1; k <= bi; ++k) bstart[k] = i;
-    }
-    __syncthreads();
-    // largest bins first (ties by bin): C threads rank one bin against 64 / C others each
-    {
-        constexpr int C = NT / kBins;
-        static_assert(C >= 1 && C <= 32 && (C & (C - 1)) == 0, "rank split");
-        const int t = tid / C, c = tid % C;
-        const int nt = bstart[t + 1] - bstart[t];
-        int rank = 0;
-#pragma unroll
-        for (int u = c * (kBins / C); u < (c + 1) * (kBins / C); ++u) {
-            const int nu = bstart[u + 1] - bstart[u];
-            rank += (nu > nt || (nu == nt && u < t)) ? 1 : 0;
-        }
-#pragma unroll
-        for (int o = C / 2; o > 0; o >>= 1) rank += __shfl_xor_sync(0xffffffffu, rank, o, C);
-        if (c == 0) border[rank] = t;
-    }
     __syncthreads();
     const unsigned full = 0xffffffffu;
     const int lane = tid & 31;
@@ -932,10 +909,10 @@ __device__ __forceinline__ void node_binned_body(
             if (slot >= kBins) break;
             const int mine = slot + half;
             const bool has_bin = mine < kBins;
-            const int bin = has_bin ? border[mine] : 0;
+            const int bin = has_bin ? tab.order[mine] : 0;
             float2* ac = acc + (((bin / (kNodeTile / kBinSide)) & 1) * 2 + (bin & 1)) * plane;
-            const int e0 = has_bin ? min(bstart[bin], cnt) : 0;
-            const int e1 = has_bin ? min(max(bstart[bin + 1], e0), cnt) : 0;
+            const int e0 = has_bin ? min(static_cast<int>(tab.start[bin]), cnt) : 0;
+            const int e1 = has_bin ? min(max(static_cast<int>(tab.start[bin + 1]), e0), cnt) : 0;
             const int len = e1 - e0;
             const int steps = max(len, __shfl_xor_sync(full, len, 16));
             NodeRec<float> nxt;
@@ -1002,9 +979,10 @@ __device__ __forceinline__ void node_binned_body(
         if (lane == 0) slot = atomicAdd(&next_bin, 1);
         slot = __shfl_sync(full, slot, 0);
         if (slot >= kBins) break;
-        const int bin = border[slot];
+        const int bin = tab.order[slot];
         float2* ac = acc + (((bin / (kNodeTile / kBinSide)) & 1) * 2 + (bin & 1)) * plane;
-        const int e0 = min(bstart[bin], cnt), e1 = min(max(bstart[bin + 1], e0), cnt);
+        const int e0 = min(static_cast<int>(tab.start[bin]), cnt);
+        const int e1 = min(max(static_cast<int>(tab.start[bin + 1]), e0), cnt);
         NodeRec<float> nxt;                                         // record of the next quad
         if (e0 + kown < e1) nxt = rec[b0 + e0 + kown];
         for (int j = e0; j < e1; j += 4) {
@@ -1096,11 +1074,52 @@ __device__ __forceinline__ void node_binned_body(
 
 template <int NT, bool HALF>
 __global__ void __launch_bounds__(NT, 1) node_binned_kernel(
-    const NodeRec<float>* __restrict__ rec, const long long* __restrict__ tile_start, int ntx, int n, int P,
-    Window<float> win, const float2* __restrict__ kin, float2* __restrict__ kout, long kbatch) {
+    const NodeRec<float>* __restrict__ rec, const long long* __restrict__ tile_start,
+    const BinTable* __restrict__ bins, int ntx, int n, int P, Window<float> win, const float2* __restrict__ kin,
+    float2* __restrict__ kout, long kbatch) {
     // tile blockIdx.x of right-hand side blockIdx.y
-    node_binned_body<NT, HALF>(rec, tile_start, ntx, n, P, win, kin + blockIdx.y * kbatch,
+    node_binned_body<NT, HALF>(rec, tile_start, bins, ntx, n, P, win, kin + blockIdx.y * kbatch,
                                kout + blockIdx.y * kbatch, blockIdx.x);
+}
+
+// Plan time: the bin table of tile blockIdx.x (BinTable).  Bin starts: record i opens the bins
+// (bin(i - 1), bin(i)] (records sorted by bin); then C threads rank one bin against 64 / C others
+// each, larger bins first and ties by bin index.
+__global__ void __launch_bounds__(256) bin_table_kernel(const NodeRec<float>* __restrict__ rec,
+                                                        const long long* __restrict__ tile_start,
+                                                        BinTable* __restrict__ out) {
+    constexpr int NT = 256;
+    __shared__ int bstart[kBins + 1];
+    __shared__ __align__(16) BinTable tab;
+    const int tile = blockIdx.x, tid = threadIdx.x;
+    const long long b0 = tile_start[tile];
+    const int cnt = static_cast<int>(tile_start[tile + 1] - b0);
+    for (int k = tid; k <= kBins; k += NT) bstart[k] = cnt;
+    __syncthreads();
+    for (int i = tid; i < cnt; i += NT) {
+        const int bi = bin_in_tile(rec[b0 + i].cell);
+        const int bp = i > 0 ? bin_in_tile(rec[b0 + i - 1].cell) : -1;
+        for (int k = bp + 1; k <= bi; ++k) bstart[k] = i;
+    }
+    __syncthreads();
+    constexpr int C = NT / kBins;
+    static_assert(C >= 1 && C <= 32 && (C & (C - 1)) == 0, "rank split");
+    const int t = tid / C, c = tid % C;
+    const int nt = bstart[t + 1] - bstart[t];
+    int rank = 0;
+#pragma unroll
+    for (int u = c * (kBins / C); u < (c + 1) * (kBins / C); ++u) {
+        const int nu = bstart[u + 1] - bstart[u];
+        rank += (nu > nt || (nu == nt && u < t)) ? 1 : 0;
+    }
+#pragma unroll
+    for (int o = C / 2; o > 0; o >>= 1) rank += __shfl_xor_sync(0xffffffffu, rank, o, C);
+    if (c == 0) tab.order[rank] = static_cast<unsigned char>(t);
+    for (int k = tid; k <= kBins; k += NT) tab.start[k] = static_cast<unsigned short>(bstart[k]);
+    for (int k = tid; k < static_cast<int>(sizeof(tab.pad)); k += NT) tab.pad[k] = 0;
+    __syncthreads();
+    constexpr int kTabVec = sizeof(BinTable) / sizeof(int4);
+    if (tid < kTabVec) reinterpret_cast<int4*>(out + tile)[tid] = reinterpret_cast<const int4*>(&tab)[tid];
 }
 
 // Node step of a whole batch (sbd_matvec_batched), one cooperative launch of persistent CTAs:
@@ -1138,7 +1157,8 @@ __global__ void __launch_bounds__(kNodeThreads * (BINNED ? 2 : 1), 1) node_batch
         if constexpr (BINNED) {
             if constexpr (sizeof(T) == 4)
                 node_binned_body<2 * kNodeThreads>(static_cast<const NodeRec<float>*>(jb.rec), jb.tile_start,
-                                                   jb.ntx, jb.nk, jb.P, win, kin, kout, tile);
+                                                   static_cast<const BinTable*>(jb.bins), jb.ntx, jb.nk, jb.P,
+                                                   win, kin, kout, tile);
         } else {
             node_fused_body<T, G, kNodeThreads, 0, 0>(static_cast<const NodeRec<T>*>(jb.rec), jb.tile_start, jb.ntx,
                                                       jb.nk, jb.P, jb.Ws, win, kin, kout, 0.f, tile);
@@ -1212,6 +1232,14 @@ int launch_scatter(const Rec* rec, const long long* tile_start, int n, int P, in
 }
 
 }  // namespace
+
+int node_bin_tables(const NodeRec<float>* rec, const long long* tile_start, int ntiles, BinTable* out,
+                    cudaStream_t s) {
+    if (ntiles <= 0) return SBD_OK;
+    bin_table_kernel<<<ntiles, 256, 0, s>>>(rec, tile_start, out);
+    SBD_LAUNCH_CHECK();
+    return SBD_OK;
+}
 
 bool window_poly(int kind, double beta, int P, double tol, float4* table) {
     constexpr int K = kWinPolyDeg + 1;
@@ -1349,9 +1377,14 @@ template <int NT, bool HALF = false>
 int launch_binned(const NodeRec<float>* nodes, const long long* tile_start, dim3 nt, int ntx, const FarGeom& g,
                   const Window<float>& win, const float2* kin, float2* kout, long kb, cudaStream_t s) {
     const size_t smem = node_fused_smem<float>(g.Pk, 3);
+    if (g.node_bins == nullptr) {
+        set_error("node step: the binned kernel needs the plan's bin table");
+        return SBD_EINVAL;
+    }
     auto k = node_binned_kernel<NT, HALF>;
     SBD_TRY(raise_smem_limit(k, smem));
-    k<<<nt, NT, smem, s>>>(nodes, tile_start, ntx, g.nk, g.Pk, win, kin, kout, kb);
+    k<<<nt, NT, smem, s>>>(nodes, tile_start, static_cast<const BinTable*>(g.node_bins), ntx, g.nk, g.Pk, win, kin,
+                           kout, kb);
     SBD_LAUNCH_CHECK();
     return SBD_OK;
 }

@@ -138,6 +138,7 @@ struct NodeJob {
     int ntx, nk, P, Ws, ntiles, win_kind;
     double win_beta;
     const float4* win_poly; // FP32: the window's polynomial table, or null
+    const void* bins;       // binned: the per-tile bin table (BinTable)
     const void* kin;
     void* kout;             // cleared by the launch before the node step
     long kbatch;            // complex elements between the right-hand sides' grids
@@ -175,6 +176,20 @@ template <typename T>
 int point_rhs_group(int P, bool two_planes, int nrhs);
 // Dynamic shared memory of the fused node kernel's stride for stencil P.
 int node_fused_stride(int Pk);
+// Bin table of one 64 x 64 tile for the binned node kernels (records sorted by the 8 x 8 bin of
+// their stencil start): start[k] = first record of bin k relative to the tile's first record
+// (start[64] = the tile's record count), order = the 64 bins largest first (ties by bin index).
+// Built once per plan (node_bin_tables) instead of by every node-step launch.
+constexpr int kNodeBins = (kNodeTile / kBinSide) * (kNodeTile / kBinSide);
+struct BinTable {
+    unsigned short start[kNodeBins + 1];
+    unsigned char order[kNodeBins];
+    unsigned char pad[256 - 2 * (kNodeBins + 1) - kNodeBins];
+};
+static_assert(sizeof(BinTable) == 256, "bin table entry: 16 x 16 bytes");
+// One table entry per tile (ntiles = tiles per side squared) from bin-sorted FP32 records.
+int node_bin_tables(const NodeRec<float>* rec, const long long* tile_start, int ntiles, BinTable* out,
+                    cudaStream_t s);
 // Polynomial table of a window for the FP32 stencil kernels (layout: window.cuh), kWinPolyEntries
 // entries for a stencil of P <= 16 cells, fitted in FP64.  Returns false (the kernels then
 // evaluate the window directly) where P > 16 or where the table, evaluated in FP32 as the kernels
