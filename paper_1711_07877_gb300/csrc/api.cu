@@ -346,6 +346,8 @@ int build_far(sbd_plan_s* p, cudaStream_t s) {
     }
     p->geom.kpoly = p->geom.spoly = nullptr;
     p->geom.node_bins = nullptr;
+    p->geom.node_order = nullptr;
+    p->geom.n_node_tiles = 0;
     if constexpr (sizeof(T) == 4) {   // the FP32 kernels' polynomial windows, where the fit holds
         std::vector<float4> tab(kWinPolyEntries);
         float4* d = nullptr;
@@ -461,6 +463,18 @@ int build_far(sbd_plan_s* p, cudaStream_t s) {
                 if ((rc = node_bin_tables(static_cast<const NodeRec<float>*>(p->nodes), p->node_tile_start, ntiles,
                                           static_cast<BinTable*>(bins), s))) return rc;
                 p->geom.node_bins = bins;
+                // the persistent kernel's walk: tiles with records, most first (ties by tile)
+                std::vector<int> order;
+                for (int t = 0; t < ntiles; ++t)
+                    if (ts[t + 1] > ts[t]) order.push_back(t);
+                std::stable_sort(order.begin(), order.end(),
+                                 [&](int a, int b) { return ts[a + 1] - ts[a] > ts[b + 1] - ts[b]; });
+                if (!order.empty()) {
+                    int* d = nullptr;
+                    if ((rc = upload(p, &d, order, s))) return rc;
+                    p->geom.node_order = d;
+                    p->geom.n_node_tiles = static_cast<int>(order.size());
+                }
             }
         }
     }

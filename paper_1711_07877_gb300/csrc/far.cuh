@@ -21,7 +21,9 @@ struct FarGeom {
     int swin;         // spreading window (WindowKind)
     const float4* kpoly;   // FP32 plans: polynomial tables of the node and spreading windows
     const float4* spoly;   // (window.cuh), or null where the window is evaluated directly
-    const void* node_bins; // binned node kernels: the per-tile bin table (node.cuh BinTable), or null
+    const void* node_bins; // binned node kernels: the per-tile bin table (node.cuh BinTable), or null,
+    const int* node_order; // the tiles holding records, most records first,
+    int n_node_tiles;      // and their number
 };
 
 // Deconvolution of the ES spreading window at a node: psi(k) = 1 / phi_hat_s(k) with

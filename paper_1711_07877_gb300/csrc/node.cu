@@ -855,38 +855,16 @@ static_assert(kBinWs >= kBinW && kBinWs % 16 == 12, "binned stride");
 // row weights and 8 for the sum over the half, and no serialisation between the records of a
 // quad (the two bins never share a cell: same-colour bins are disjoint, the others write other
 // planes).
-template <int NT, bool HALF = false>
-__device__ __forceinline__ void node_binned_body(
-    const NodeRec<float>* __restrict__ rec, const long long* __restrict__ tile_start,
-    const BinTable* __restrict__ bins, int ntx, int n, int P, const Window<float>& win,
-    const float2* __restrict__ kin, float2* __restrict__ kout, int tile) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ __align__(16) BinTable tab;                          // bin starts, bins largest first
-    __shared__ int next_bin;
-    const long long b0 = tile_start[tile], b1 = tile_start[tile + 1];
-    if (b0 == b1) return;                                           // uniform per block
-    const int cnt = static_cast<int>(b1 - b0);
+// Record loop of the binned kernels: the CTA's input tile in s, the four colour accumulators in
+// acc (zero on entry), the tile's bin table in tab and next_bin = 0 (all visible to every thread);
+// warps take bins from next_bin until none are left.
+template <int NT, bool HALF>
+__device__ __forceinline__ void binned_records(const NodeRec<float>* __restrict__ rec, long long b0, int cnt,
+                                               const BinTable& tab, int& next_bin, int ox, int oy, int P,
+                                               const Window<float>& win, const float2* s, float2* acc) {
     constexpr int plane = kBinW * kBinWs;
-    float2* s = reinterpret_cast<float2*>(smem_raw);                 // input tile
-    float2* acc = s + plane;                                        // four colour accumulators
-    const int ox = (tile / ntx) * kNodeTile, oy = (tile % ntx) * kNodeTile;
-    const int W = kNodeTile + P - 1;
-    const int rows = min(W, n - ox), cols = min(W, n - oy);
     const int tid = threadIdx.x;
-    constexpr int kTabVec = sizeof(BinTable) / sizeof(int4);
-    if (tid < kTabVec) reinterpret_cast<int4*>(&tab)[tid] = reinterpret_cast<const int4*>(bins + tile)[tid];
-    for (int idx = tid; idx < kBinW * kBinW; idx += NT) {
-        const int r = idx / kBinW, c = idx - r * kBinW;
-        float2 v = make_float2(0.f, 0.f);
-        if (r < rows && c < cols) v = kin[static_cast<long>(ox + r) * n + oy + c];
-        const int o = r * kBinWs + c;
-        s[o] = v;
-#pragma unroll
-        for (int k = 0; k < 4; ++k) acc[k * plane + o] = make_float2(0.f, 0.f);
-    }
-    if (tid == 0) next_bin = 0;
     const bool poly = win.poly != nullptr;   // window weights from the polynomial table (registers)
-    __syncthreads();
     const unsigned full = 0xffffffffu;
     const int lane = tid & 31;
     if constexpr (HALF) {
@@ -1051,25 +1029,86 @@ __device__ __forceinline__ void node_binned_body(
             }
         }
     }
-    __syncthreads();
-    for (int idx = tid; idx < W * W; idx += NT) {
-        const int r = idx / W, c = idx - r * W;
-        if (r >= rows || c >= cols) continue;
+}
+
+// Flush of a binned tile: the four planes summed into the tile's window of kout (cells only this
+// tile reaches stored, the overlap band added atomically; kout cleared beforehand).  FUSED (the
+// persistent kernel): the planes are cleared for the next tile, and the next tile's input
+// (kin_next, origin (nox, noy), extent nrows x ncols; kin_next null: none) is loaded into s in
+// the same pass, so its loads overlap the flush's stores.
+template <int NT, bool FUSED>
+__device__ __forceinline__ void binned_flush(float2* acc, float2* __restrict__ kout, int ox, int oy, int rows,
+                                             int cols, int n, int P, float2* s = nullptr,
+                                             const float2* __restrict__ kin_next = nullptr, int nox = 0,
+                                             int noy = 0, int nrows = 0, int ncols = 0) {
+    constexpr int plane = kBinW * kBinWs;
+    const int W = kNodeTile + P - 1;
+    const int span = FUSED ? kBinW : W;
+    for (int idx = threadIdx.x; idx < span * span; idx += NT) {
+        const int r = idx / span, c = idx - r * span;
         const int o = r * kBinWs + c;
-        float vr = acc[o].x, vi = acc[o].y;
+        float2 v = make_float2(0.f, 0.f);
+        if (FUSED && kin_next != nullptr && r < nrows && c < ncols)
+            v = kin_next[static_cast<long>(nox + r) * n + noy + c];
+        if (r < W && c < W) {
+            float vr = acc[o].x, vi = acc[o].y;
 #pragma unroll
-        for (int k = 1; k < 4; ++k) {
-            vr += acc[k * plane + o].x;
-            vi += acc[k * plane + o].y;
+            for (int k = 1; k < 4; ++k) {
+                vr += acc[k * plane + o].x;
+                vi += acc[k * plane + o].y;
+            }
+            if (FUSED) {
+#pragma unroll
+                for (int k = 0; k < 4; ++k) acc[k * plane + o] = make_float2(0.f, 0.f);
+            }
+            if (r < rows && c < cols) {
+                float2* dst = kout + static_cast<long>(ox + r) * n + oy + c;
+                if (r >= P - 1 && c >= P - 1 && r < kNodeTile && c < kNodeTile) {
+                    *dst = make_float2(vr, vi);
+                } else if (vr != 0.f || vi != 0.f) {
+                    atomicAdd(&dst->x, vr);
+                    atomicAdd(&dst->y, vi);
+                }
+            }
         }
-        float2* dst = kout + static_cast<long>(ox + r) * n + oy + c;
-        if (r >= P - 1 && c >= P - 1 && r < kNodeTile && c < kNodeTile) {
-            *dst = make_float2(vr, vi);
-        } else if (vr != 0.f || vi != 0.f) {
-            atomicAdd(&dst->x, vr);
-            atomicAdd(&dst->y, vi);
-        }
+        if (FUSED) s[o] = v;
     }
+}
+
+template <int NT, bool HALF = false>
+__device__ __forceinline__ void node_binned_body(
+    const NodeRec<float>* __restrict__ rec, const long long* __restrict__ tile_start,
+    const BinTable* __restrict__ bins, int ntx, int n, int P, const Window<float>& win,
+    const float2* __restrict__ kin, float2* __restrict__ kout, int tile) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ __align__(16) BinTable tab;                          // bin starts, bins largest first
+    __shared__ int next_bin;
+    const long long b0 = tile_start[tile], b1 = tile_start[tile + 1];
+    if (b0 == b1) return;                                           // uniform per block
+    const int cnt = static_cast<int>(b1 - b0);
+    constexpr int plane = kBinW * kBinWs;
+    float2* s = reinterpret_cast<float2*>(smem_raw);                 // input tile
+    float2* acc = s + plane;                                        // four colour accumulators
+    const int ox = (tile / ntx) * kNodeTile, oy = (tile % ntx) * kNodeTile;
+    const int W = kNodeTile + P - 1;
+    const int rows = min(W, n - ox), cols = min(W, n - oy);
+    const int tid = threadIdx.x;
+    constexpr int kTabVec = sizeof(BinTable) / sizeof(int4);
+    if (tid < kTabVec) reinterpret_cast<int4*>(&tab)[tid] = reinterpret_cast<const int4*>(bins + tile)[tid];
+    for (int idx = tid; idx < kBinW * kBinW; idx += NT) {
+        const int r = idx / kBinW, c = idx - r * kBinW;
+        float2 v = make_float2(0.f, 0.f);
+        if (r < rows && c < cols) v = kin[static_cast<long>(ox + r) * n + oy + c];
+        const int o = r * kBinWs + c;
+        s[o] = v;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) acc[k * plane + o] = make_float2(0.f, 0.f);
+    }
+    if (tid == 0) next_bin = 0;
+    __syncthreads();
+    binned_records<NT, HALF>(rec, b0, cnt, tab, next_bin, ox, oy, P, win, s, acc);
+    __syncthreads();
+    binned_flush<NT, false>(acc, kout, ox, oy, rows, cols, n, P);
 }
 
 template <int NT, bool HALF>
@@ -1080,6 +1119,74 @@ __global__ void __launch_bounds__(NT, 1) node_binned_kernel(
     // tile blockIdx.x of right-hand side blockIdx.y
     node_binned_body<NT, HALF>(rec, tile_start, bins, ntx, n, P, win, kin + blockIdx.y * kbatch,
                                kout + blockIdx.y * kbatch, blockIdx.x);
+}
+
+// Persistent binned node step: one CTA per SM walks the items (tile, right-hand side), the tiles
+// of the plan's non-empty list (largest first) fastest, taking items blockIdx.x + k gridDim.x; the
+// flush of each tile clears the planes and loads the next item's input in the same pass
+// (binned_flush), so no CTA starts cold and the next tile's loads overlap this tile's stores.
+template <int NT, bool HALF>
+__global__ void __launch_bounds__(NT, 1) node_binned_persistent_kernel(
+    const NodeRec<float>* __restrict__ rec, const long long* __restrict__ tile_start,
+    const BinTable* __restrict__ bins, const int* __restrict__ order, int ntl, int ntx, int n, int P,
+    Window<float> win, const float2* __restrict__ kin, float2* __restrict__ kout, long kbatch, int nb) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ __align__(16) BinTable tab;
+    __shared__ int next_bin;
+    constexpr int plane = kBinW * kBinWs;
+    constexpr int kTabVec = sizeof(BinTable) / sizeof(int4);
+    float2* s = reinterpret_cast<float2*>(smem_raw);                 // input tile
+    float2* acc = s + plane;                                        // four colour accumulators
+    const int items = ntl * nb;
+    int it = blockIdx.x;
+    if (it >= items) return;                                        // uniform per block
+    const int W = kNodeTile + P - 1;
+    const int tid = threadIdx.x;
+    // item i: tile order[i mod ntl] of right-hand side i / ntl (grid offset returned)
+    auto where = [&](int i, int& tile, int& ox, int& oy, int& rows, int& cols) -> long {
+        tile = order[i % ntl];
+        ox = (tile / ntx) * kNodeTile;
+        oy = (tile % ntx) * kNodeTile;
+        rows = min(W, n - ox);
+        cols = min(W, n - oy);
+        return static_cast<long>(i / ntl) * kbatch;
+    };
+    int tile, ox, oy, rows, cols;
+    long off = where(it, tile, ox, oy, rows, cols);
+    for (int idx = tid; idx < 4 * plane; idx += NT) acc[idx] = make_float2(0.f, 0.f);
+    for (int idx = tid; idx < kBinW * kBinW; idx += NT) {
+        const int r = idx / kBinW, c = idx - r * kBinW;
+        float2 v = make_float2(0.f, 0.f);
+        if (r < rows && c < cols) v = kin[off + static_cast<long>(ox + r) * n + oy + c];
+        s[r * kBinWs + c] = v;
+    }
+    if (tid < kTabVec) reinterpret_cast<int4*>(&tab)[tid] = reinterpret_cast<const int4*>(bins + tile)[tid];
+    if (tid == 0) next_bin = 0;
+    __syncthreads();
+    for (;;) {
+        const long long b0 = tile_start[tile];
+        const int cnt = static_cast<int>(tile_start[tile + 1] - b0);
+        binned_records<NT, HALF>(rec, b0, cnt, tab, next_bin, ox, oy, P, win, s, acc);
+        __syncthreads();
+        const int nx = it + static_cast<int>(gridDim.x);
+        const bool more = nx < items;                               // uniform per block
+        int ntile = 0, nox = 0, noy = 0, nrows = 0, ncols = 0;
+        long noff = 0;
+        if (more) noff = where(nx, ntile, nox, noy, nrows, ncols);
+        binned_flush<NT, true>(acc, kout + off, ox, oy, rows, cols, n, P, s, more ? kin + noff : nullptr, nox, noy,
+                               nrows, ncols);
+        if (!more) break;
+        if (tid < kTabVec) reinterpret_cast<int4*>(&tab)[tid] = reinterpret_cast<const int4*>(bins + ntile)[tid];
+        if (tid == 0) next_bin = 0;
+        __syncthreads();
+        it = nx;
+        tile = ntile;
+        ox = nox;
+        oy = noy;
+        rows = nrows;
+        cols = ncols;
+        off = noff;
+    }
 }
 
 // Plan time: the bin table of tile blockIdx.x (BinTable).  Bin starts: record i opens the bins
@@ -1373,6 +1480,10 @@ int launch_fused_g(const NodeRec<T>* nodes, const long long* tile_start, dim3 nt
                    : launch_fused<T, G, 0, 0>(nodes, tile_start, nt, ntx, g, Ws, win, kin, kout, wb, kb, s);
 }
 
+namespace {
+int sm_count();   // SMs of the current device (defined with the batched launches)
+}
+
 template <int NT, bool HALF = false>
 int launch_binned(const NodeRec<float>* nodes, const long long* tile_start, dim3 nt, int ntx, const FarGeom& g,
                   const Window<float>& win, const float2* kin, float2* kout, long kb, cudaStream_t s) {
@@ -1381,10 +1492,13 @@ int launch_binned(const NodeRec<float>* nodes, const long long* tile_start, dim3
         set_error("node step: the binned kernel needs the plan's bin table");
         return SBD_EINVAL;
     }
-    auto k = node_binned_kernel<NT, HALF>;
+    if (g.node_order == nullptr || g.n_node_tiles <= 0) return SBD_OK;   // no records: kout stays cleared
+    auto k = node_binned_persistent_kernel<NT, HALF>;
     SBD_TRY(raise_smem_limit(k, smem));
-    k<<<nt, NT, smem, s>>>(nodes, tile_start, static_cast<const BinTable*>(g.node_bins), ntx, g.nk, g.Pk, win, kin,
-                           kout, kb);
+    const int items = g.n_node_tiles * static_cast<int>(nt.y);
+    const int grid = std::max(1, std::min(items, sm_count()));
+    k<<<grid, NT, smem, s>>>(nodes, tile_start, static_cast<const BinTable*>(g.node_bins), g.node_order,
+                             g.n_node_tiles, ntx, g.nk, g.Pk, win, kin, kout, kb, static_cast<int>(nt.y));
     SBD_LAUNCH_CHECK();
     return SBD_OK;
 }
