@@ -1111,16 +1111,6 @@ __device__ __forceinline__ void node_binned_body(
     binned_flush<NT, false>(acc, kout, ox, oy, rows, cols, n, P);
 }
 
-template <int NT, bool HALF>
-__global__ void __launch_bounds__(NT, 1) node_binned_kernel(
-    const NodeRec<float>* __restrict__ rec, const long long* __restrict__ tile_start,
-    const BinTable* __restrict__ bins, int ntx, int n, int P, Window<float> win, const float2* __restrict__ kin,
-    float2* __restrict__ kout, long kbatch) {
-    // tile blockIdx.x of right-hand side blockIdx.y
-    node_binned_body<NT, HALF>(rec, tile_start, bins, ntx, n, P, win, kin + blockIdx.y * kbatch,
-                               kout + blockIdx.y * kbatch, blockIdx.x);
-}
-
 // Persistent binned node step: one CTA per SM walks the items (tile, right-hand side), the tiles
 // of the plan's non-empty list (largest first) fastest, taking items blockIdx.x + k gridDim.x; the
 // flush of each tile clears the planes and loads the next item's input in the same pass
