@@ -345,6 +345,21 @@ int build_far(sbd_plan_s* p, cudaStream_t s) {
         if (urc) return urc;
     }
     p->geom.kpoly = p->geom.spoly = nullptr;
+    p->geom.kpoly64 = p->geom.spoly64 = nullptr;
+    if constexpr (sizeof(T) == 8) {   // the FP64 kernels' polynomial windows, where the fit holds
+        std::vector<double> tab(kWinPolyEntries64);
+        double* d = nullptr;
+        if (window_poly64(np.kwin, np.beta_k, np.Pk, np.tol, tab.data())) {
+            const int urc = upload(p, &d, tab, s);
+            if (urc) return urc;
+            p->geom.kpoly64 = d;
+        }
+        if (window_poly64(np.swin, np.beta_s, np.Ps, np.tol, tab.data())) {
+            const int urc = upload(p, &d, tab, s);
+            if (urc) return urc;
+            p->geom.spoly64 = d;
+        }
+    }
     p->geom.node_bins = nullptr;
     p->geom.node_order = nullptr;
     p->geom.n_node_tiles = 0;

@@ -21,6 +21,8 @@ struct FarGeom {
     int swin;         // spreading window (WindowKind)
     const float4* kpoly;   // FP32 plans: polynomial tables of the node and spreading windows
     const float4* spoly;   // (window.cuh), or null where the window is evaluated directly
+    const double* kpoly64; // FP64 plans: the same for the FP64 kernels
+    const double* spoly64;
     const void* node_bins; // binned node kernels: the per-tile bin table (node.cuh BinTable), or null,
     const int* node_order; // the tiles holding records, most records first,
     int n_node_tiles;      // and their number

@@ -135,6 +135,15 @@ struct LaneWin {
     int sub, P;
     __device__ __forceinline__ LaneWin(const Window<T>& w, int sub_, int P_, const float4*) : win(w), sub(sub_), P(P_) {}
     __device__ __forceinline__ void operator()(T fx, T fy, T& wx, T& wy) const {
+        if constexpr (sizeof(T) == 8) {
+            // FP64 table: a Horner chain per axis instead of the FP64 square root, division and exponential
+            if (win.poly64 != nullptr) {
+                wx = 0;
+                wy = 0;
+                if (sub < kWinPolyOffsets) poly_weights64(win.poly64, sub, fx, fy, wx, wy);
+                return;
+            }
+        }
         lane_weights<T>(sub, P, win, fx, fy, wx, wy);
     }
 };
@@ -1279,8 +1288,9 @@ inline int fused_p8(int P) { return P <= 8 ? 8 : (P <= 16 ? 16 : 32); }
 inline int tiles_per_side(int n) { return (n + kNodeTile - 1) / kNodeTile; }
 
 template <typename T>
-Window<T> make_window(int kind, double beta, int P, const float4* poly = nullptr) {
-    return Window<T>{kind, static_cast<T>(beta), static_cast<T>(2.0 / P), sizeof(T) == 4 ? poly : nullptr};
+Window<T> make_window(int kind, double beta, int P, const float4* poly = nullptr, const double* poly64 = nullptr) {
+    return Window<T>{kind, static_cast<T>(beta), static_cast<T>(2.0 / P), sizeof(T) == 4 ? poly : nullptr,
+                     sizeof(T) == 8 ? poly64 : nullptr};
 }
 
 template <typename T, typename Rec, typename Out, bool PK = false>
@@ -1333,6 +1343,53 @@ int launch_scatter(const Rec* rec, const long long* tile_start, int n, int P, in
 }
 
 }  // namespace
+
+bool window_poly64(int kind, double beta, int P, double tol, double* table) {
+    constexpr int K = kWinPolyDeg64 + 1;
+    for (int e = 0; e < kWinPolyEntries64; ++e) table[e] = 0.0;
+    if (P < 1 || P > kWinPolyOffsets || !(beta > 0.0) || !(tol > 0.0)) return false;
+    const double pi = 3.14159265358979323846;
+    auto window = [&](double d) {   // the window of window.cuh, in FP64
+        if (kind == kWinGauss) return std::exp(-beta * d * d);
+        const double z = d * 2.0 / P, r = 1.0 - z * z;
+        return r > 0.0 ? std::exp(-beta * z * z / (1.0 + std::sqrt(r))) : 0.0;
+    };
+    const double bound = 0.25 * tol;
+    for (int j = 0; j < P; ++j) {
+        const double off = j - P / 2 + 1;
+        double y[K], a[K];
+        for (int k = 0; k < K; ++k) y[k] = window(off - 0.5 * (std::cos(pi * (k + 0.5) / K) + 1.0));
+        for (int i = 0; i < K; ++i) {
+            double acc = 0.0;
+            for (int k = 0; k < K; ++k) acc += y[k] * std::cos(pi * i * (k + 0.5) / K);
+            a[i] = (i == 0 ? 1.0 : 2.0) * acc / K;
+        }
+        double mono[K] = {}, t0[K] = {}, t1[K] = {}, t2[K];
+        t0[0] = 1.0;
+        t1[1] = 1.0;
+        mono[0] = a[0];
+        for (int e = 0; e < K; ++e) mono[e] += a[1] * t1[e];
+        for (int i = 2; i < K; ++i) {
+            for (int e = 0; e < K; ++e) t2[e] = (e > 0 ? 2.0 * t1[e - 1] : 0.0) - t0[e];
+            for (int e = 0; e < K; ++e) {
+                mono[e] += a[i] * t2[e];
+                t0[e] = t1[e];
+                t1[e] = t2[e];
+            }
+        }
+        for (int k = 0; k < K; ++k) table[k * kWinPolyOffsets + j] = mono[kWinPolyDeg64 - k];   // highest first
+        for (int t = 0; t < 2048; ++t) {
+            const double f = (t + 0.5) / 2048.0, sv = std::fma(2.0, f, -1.0);
+            double acc = table[j];
+            for (int k = 1; k < K; ++k) acc = std::fma(acc, sv, table[k * kWinPolyOffsets + j]);
+            if (std::fabs(acc - window(off - f)) > bound) {
+                for (int e = 0; e < kWinPolyEntries64; ++e) table[e] = 0.0;
+                return false;
+            }
+        }
+    }
+    return true;
+}
 
 int node_bin_tables(const NodeRec<float>* rec, const long long* tile_start, int ntiles, BinTable* out,
                     cudaStream_t s) {
@@ -1536,7 +1593,7 @@ int node_step_fused(const NodeRec<T>* nodes, const long long* tile_start, const 
     const int W = kNodeTile + g.Pk - 1;
     const int P8 = fused_p8(g.Pk);
     const int Ws = fused_stride(W, P8);
-    const Window<T> win = make_window<T>(g.kwin, g.beta_k, g.Pk, g.kpoly);
+    const Window<T> win = make_window<T>(g.kwin, g.beta_k, g.Pk, g.kpoly, g.kpoly64);
     if (P8 == 8) return launch_fused_g<T, 8>(nodes, tile_start, nt, ntx, g, Ws, win, kin, kout, t, kb, s);
     if (P8 == 16) return launch_fused_g<T, 16>(nodes, tile_start, nt, ntx, g, Ws, win, kin, kout, t, kb, s);
     return launch_fused_g<T, 32>(nodes, tile_start, nt, ntx, g, Ws, win, kin, kout, t, kb, s);
@@ -1579,7 +1636,7 @@ inline int rhs_group(size_t per, int nrhs) {
 template <typename T, int G, bool PK, bool RV>
 int launch_spread_chunks(const PointRec<T>* pts, const PointWork& work, const FarGeom& g, PointVal<T> val,
                          cx_t<T>* grid, int nrhs, long gstride, cudaStream_t s) {
-    const Window<T> win = make_window<T>(g.swin, g.beta_s, g.Ps, g.spoly);
+    const Window<T> win = make_window<T>(g.swin, g.beta_s, g.Ps, g.spoly, g.spoly64);
     const size_t W = kNodeTile + g.Ps - 1;
     const size_t per = (RV ? 1 : 2) * sizeof(T) * W * W;
     const int rg = rhs_group(per, nrhs);
@@ -1595,9 +1652,10 @@ int launch_spread_chunks(const PointRec<T>* pts, const PointWork& work, const Fa
 template <typename T, int G, bool PK>
 int launch_interp_chunks(const PointRec<T>* pts, const PointWork& work, const FarGeom& g, const cx_t<T>* grid,
                          const PointOut<T>& out, int nrhs, long gstride, cudaStream_t s) {
-    // the window evaluated directly: the table's shared-memory reads cost this gather loop more
-    // than they save (it is bound by shared-memory wavefronts; 0.26 against 0.33 ms at N = 10^6)
-    const Window<T> win = make_window<T>(g.swin, g.beta_s, g.Ps);
+    // FP32: the window evaluated directly, the table's shared-memory reads cost this gather loop more
+    // than they save (it is bound by shared-memory wavefronts; 0.26 against 0.33 ms at N = 10^6);
+    // FP64: the FP64 table (the FP64 pipe is the bound there)
+    const Window<T> win = make_window<T>(g.swin, g.beta_s, g.Ps, nullptr, g.spoly64);
     const size_t W = kNodeTile + g.Ps - 1;
     const size_t per = (PK ? 1 : 2) * sizeof(T) * W * W;
     const int rg = rhs_group(per, nrhs);

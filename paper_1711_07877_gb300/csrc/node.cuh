@@ -195,5 +195,8 @@ int node_bin_tables(const NodeRec<float>* rec, const long long* tile_start, int 
 // evaluate the window directly) where P > 16 or where the table, evaluated in FP32 as the kernels
 // do, departs from the window by more than max(1.2e-7, tol / 100) at a fraction in (0, 1).
 bool window_poly(int kind, double beta, int P, double tol, float4* table);
+// The FP64 kernels' table (kWinPolyEntries64 doubles, degree kWinPolyDeg64), accepted where its FP64
+// evaluation stays within tol / 4 of the window at fractions in (0, 1); false: evaluated directly.
+bool window_poly64(int kind, double beta, int P, double tol, double* table);
 
 }  // namespace sbd

@@ -51,12 +51,34 @@ __device__ __forceinline__ void poly_weights(const float4 c0, const float4 c1, c
     wy = poly_quad(ay, c2, sy);
 }
 
+// The FP64 kernels' table: degree kWinPolyDeg64 in the same s, coefficient k (highest power
+// first) of offset j at entry k * kWinPolyOffsets + j (a warp's reads of one coefficient touch
+// consecutive doubles).
+constexpr int kWinPolyDeg64 = 19;
+constexpr int kWinPolyEntries64 = (kWinPolyDeg64 + 1) * kWinPolyOffsets;
+
+// Weights of offset j at the fractions fx, fy from the FP64 table (Horner, two chains).
+__device__ __forceinline__ void poly_weights64(const double* __restrict__ c, int j, double fx, double fy,
+                                               double& wx, double& wy) {
+    const double sx = fma(2.0, fx, -1.0), sy = fma(2.0, fy, -1.0);
+    double ax = __ldg(c + j), ay = ax;
+#pragma unroll
+    for (int k = 1; k <= kWinPolyDeg64; ++k) {
+        const double ck = __ldg(c + k * kWinPolyOffsets + j);
+        ax = fma(ax, sx, ck);
+        ay = fma(ay, sy, ck);
+    }
+    wx = ax;
+    wy = ay;
+}
+
 template <typename T>
 struct Window {
     int kind;
     T beta;
     T inv_half;                     // 2 / P (ES only)
     const float4* poly = nullptr;   // FP32 kernels: the polynomial table (device), or null
+    const double* poly64 = nullptr; // FP64 kernels: the polynomial table (device), or null
     __device__ __forceinline__ T operator()(T d) const {
         if (kind == kWinGauss) return wexp<T>(-beta * d * d);
         // sqrt(1 - z^2) - 1 = -z^2 / (1 + sqrt(1 - z^2)): no cancellation near the centre,
