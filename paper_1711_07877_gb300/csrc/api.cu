@@ -2073,6 +2073,7 @@ int batched_impl(const sbd_plan_t* plans, const void* const* f, void* const* q, 
             jb.win_kind = p->np.swin;
             jb.win_beta = p->np.beta_s;
             jb.win_poly = p->geom.spoly;
+            jb.win_poly64 = p->geom.spoly64;
             jb.f = f[i];
             jb.n_pts = p->n;
             jb.grid = p->wsX;
@@ -2142,6 +2143,7 @@ int batched_impl(const sbd_plan_t* plans, const void* const* f, void* const* q, 
             jb.win_kind = p->np.kwin;
             jb.win_beta = p->np.beta_k;
             jb.win_poly = p->geom.kpoly;
+            jb.win_poly64 = p->geom.kpoly64;
             jb.bins = p->geom.node_bins;
             jb.kin = p->wsB;
             jb.kout = p->wsC;
@@ -2186,7 +2188,8 @@ int batched_impl(const sbd_plan_t* plans, const void* const* f, void* const* q, 
             jb.P = p->np.Ps;
             jb.win_kind = p->np.swin;
             jb.win_beta = p->np.beta_s;
-            jb.win_poly = nullptr;   // the gather evaluates the window directly, as launch_interp_chunks
+            jb.win_poly = nullptr;   // FP32: the gather evaluates the window directly, as launch_interp_chunks
+            jb.win_poly64 = p->geom.spoly64;
             jb.q = q[i];
             jb.n_pts = p->n_tgt;
             jb.grid = p->wsX;

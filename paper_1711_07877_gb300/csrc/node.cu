@@ -578,7 +578,7 @@ __device__ __forceinline__ int find_job(const Jobs& J, int it) {
 template <typename T>
 __device__ __forceinline__ Window<T> job_window(const PointJob& jb) {
     return Window<T>{jb.win_kind, static_cast<T>(jb.win_beta), static_cast<T>(2.0 / jb.P),
-                     sizeof(T) == 4 ? jb.win_poly : nullptr};
+                     sizeof(T) == 4 ? jb.win_poly : nullptr, sizeof(T) == 8 ? jb.win_poly64 : nullptr};
 }
 
 // Spreading of the whole batch in one cooperative launch: every CTA first clears its share of
@@ -1263,7 +1263,7 @@ __global__ void __launch_bounds__(kNodeThreads * (BINNED ? 2 : 1), 1) node_batch
         const auto* kin = static_cast<const cx_t<T>*>(jb.kin) + r * jb.kbatch;
         auto* kout = static_cast<cx_t<T>*>(jb.kout) + r * jb.kbatch;
         const Window<T> win{jb.win_kind, static_cast<T>(jb.win_beta), static_cast<T>(2.0 / jb.P),
-                            sizeof(T) == 4 ? jb.win_poly : nullptr};
+                            sizeof(T) == 4 ? jb.win_poly : nullptr, sizeof(T) == 8 ? jb.win_poly64 : nullptr};
         if constexpr (BINNED) {
             if constexpr (sizeof(T) == 4)
                 node_binned_body<2 * kNodeThreads>(static_cast<const NodeRec<float>*>(jb.rec), jb.tile_start,

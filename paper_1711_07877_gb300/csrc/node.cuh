@@ -113,6 +113,7 @@ struct PointJob {
     int ntx, m, P, win_kind;
     double win_beta;
     const float4* win_poly; // FP32: the window's polynomial table, or null
+    const double* win_poly64; // FP64: the same (the single-plan launches' table, so both give the same sums)
     const void* f;          // spreading: values (float64 / complex128), point l of rhs r at r * n_pts + l
     void* q;                // interpolation: output, same layout
     long n_pts;
@@ -138,6 +139,7 @@ struct NodeJob {
     int ntx, nk, P, Ws, ntiles, win_kind;
     double win_beta;
     const float4* win_poly; // FP32: the window's polynomial table, or null
+    const double* win_poly64; // FP64: the same
     const void* bins;       // binned: the per-tile bin table (BinTable)
     const void* kin;
     void* kout;             // cleared by the launch before the node step
