@@ -341,7 +341,7 @@ template <> struct MaxB<float>  { static constexpr int n_max = 28672; };
 template <> struct MaxB<double> { static constexpr int n_max = 14336; };
 
 // Radices of the in-register butterflies: prime powers up to 16 and 15 (FP32) or up to 9
-// (FP64, twice the registers per element), which fit the 80 registers of three CTAs per SM.
+// (FP64, twice the registers per element), which fit the 80 registers a thread of the launch bounds.
 // f(integral_constant<R>) for the runtime radix R.
 template <typename T, typename F>
 __device__ __forceinline__ void with_radix(int R, F&& f) {
@@ -473,12 +473,14 @@ __device__ __forceinline__ cx_t<T> load_elem(int idx, int n, const cx_t<T>* __re
 }
 
 // SIGN (-1 forward, +1 inverse) is a template argument: the factors +-i of the butterflies
-// and the conjugation of the twiddles fold into the arithmetic.  256 threads and at most 80
-// registers a thread (launch bounds for three CTAs per SM): three 6912-point rows share an
-// SM, so that one row's loads overlap the others' butterflies.
-constexpr int kFftThreads = 256;
+// and the conjugation of the twiddles fold into the arithmetic.  384 threads and at most 80
+// registers a thread (launch bounds for two CTAs per SM): two 13824-point rows (110 KB each)
+// share an SM with 24 warps between them, so that one row's loads overlap the other's
+// butterflies (256-thread CTAs left such rows at 16 warps an SM: 0.96 against 0.83 ms per
+// forward transform at N = 10^6).
+constexpr int kFftThreads = 384;
 template <typename T, int SIGN>
-__global__ void __launch_bounds__(kFftThreads, 3) fft_rows_kernel(
+__global__ void __launch_bounds__(kFftThreads, 2) fft_rows_kernel(
     const cx_t<T>* __restrict__ in, long in_stride, int in_len, int in_shift,
     cx_t<T>* __restrict__ out, long out_stride, int out_len, int out_shift,
     int n, int Q, FftPlan1D plan, const cx_t<T>* __restrict__ tw, const int* __restrict__ perm,
