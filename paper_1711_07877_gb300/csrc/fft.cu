@@ -473,14 +473,16 @@ __device__ __forceinline__ cx_t<T> load_elem(int idx, int n, const cx_t<T>* __re
 }
 
 // SIGN (-1 forward, +1 inverse) is a template argument: the factors +-i of the butterflies
-// and the conjugation of the twiddles fold into the arithmetic.  384 threads and at most 80
-// registers a thread (launch bounds for two CTAs per SM): two 13824-point rows (110 KB each)
-// share an SM with 24 warps between them, so that one row's loads overlap the other's
-// butterflies (256-thread CTAs left such rows at 16 warps an SM: 0.96 against 0.83 ms per
-// forward transform at N = 10^6).
-constexpr int kFftThreads = 384;
-template <typename T, int SIGN>
-__global__ void __launch_bounds__(kFftThreads, 2) fft_rows_kernel(
+// and the conjugation of the twiddles fold into the arithmetic.  NT threads and at most 80
+// registers a thread: 256 threads and three CTAs per SM where three rows fit the SM's shared
+// memory, 384 threads and two CTAs per SM where only two do (13824-point FP32 rows, 110 KB), so
+// that an SM holds 24 warps either way and one row's loads overlap the others' butterflies
+// (measured at N = 10^6: 13824-point rows 0.96 -> 0.83 ms per forward transform with 384 threads;
+// 6912- and 7680-point phases slower with 384 threads and two CTAs than with 256 and three).
+template <int NT> struct FftCtas { static constexpr int value = NT == 384 ? 2 : 3; };
+constexpr size_t kFftSmemThird = 228u * 1024u / 3u - 1024u;   // bytes a CTA may take for three per SM
+template <typename T, int SIGN, int NT>
+__global__ void __launch_bounds__(NT, FftCtas<NT>::value) fft_rows_kernel(
     const cx_t<T>* __restrict__ in, long in_stride, int in_len, int in_shift,
     cx_t<T>* __restrict__ out, long out_stride, int out_len, int out_shift,
     int n, int Q, FftPlan1D plan, const cx_t<T>* __restrict__ tw, const int* __restrict__ perm,
@@ -488,7 +490,6 @@ __global__ void __launch_bounds__(kFftThreads, 2) fft_rows_kernel(
     const T* __restrict__ post_elem, const T* __restrict__ post_row, HermFold<T> hf, int io,
     const cx_t<T>* __restrict__ tw2, long in_batch, long out_batch, long out_es) {
     using C = cx_t<T>;
-    constexpr int NT = kFftThreads;
     constexpr bool inv = SIGN > 0;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* s = reinterpret_cast<C*>(smem_raw);
@@ -724,7 +725,6 @@ bool fft_make_plan(int n, FftPlan1D& p, bool fp64) {
     if (static_cast<int>(rs.size()) > kFftMaxStages) return false;
     for (size_t i = 0; i < rs.size(); ++i) p.radix[i] = rs[i];
     p.nstages = static_cast<int>(rs.size());
-    p.threads = kFftThreads;
     return true;
 }
 
@@ -748,9 +748,9 @@ int fft_max_length(bool fp64) { return 2 * fft_max_row(fp64); }
 
 // Launches fft_rows_kernel<T, sign> (sign -1 or +1) with the shared-memory carveout at its
 // maximum (all of the SM's unified memory as shared memory).
-template <typename T, int SIGN, typename... A>
-int launch_fft_rows_sign(dim3 grid, size_t smem, cudaStream_t stream, A... args) {
-    auto k = fft_rows_kernel<T, SIGN>;
+template <typename T, int SIGN, int NT, typename... A>
+int launch_fft_rows_nt(dim3 grid, size_t smem, cudaStream_t stream, A... args) {
+    auto k = fft_rows_kernel<T, SIGN, NT>;
     SBD_TRY(raise_smem_limit(k, smem));
     static const bool carve = [&] {
         cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
@@ -758,9 +758,16 @@ int launch_fft_rows_sign(dim3 grid, size_t smem, cudaStream_t stream, A... args)
         return true;
     }();
     (void)carve;
-    k<<<grid, kFftThreads, smem, stream>>>(args...);
+    k<<<grid, NT, smem, stream>>>(args...);
     SBD_LAUNCH_CHECK();
     return SBD_OK;
+}
+
+// 384 threads where a CTA's shared memory leaves room for two CTAs per SM only, else 256 (three).
+template <typename T, int SIGN, typename... A>
+int launch_fft_rows_sign(dim3 grid, size_t smem, cudaStream_t stream, A... args) {
+    if (smem > kFftSmemThird) return launch_fft_rows_nt<T, SIGN, 384>(grid, smem, stream, args...);
+    return launch_fft_rows_nt<T, SIGN, 256>(grid, smem, stream, args...);
 }
 
 template <typename T, typename... A>

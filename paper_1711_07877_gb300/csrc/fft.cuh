@@ -13,11 +13,10 @@ struct FftPlan1D {
     int n = 0;
     int nstages = 0;
     int radix[kFftMaxStages];
-    int threads = 0;
 };
 
-// Radix schedule for n = 2^a 3^b 5^c (prime-power radices up to 32, or 16 for FP64, odd
-// ones first); false when n has another factor.
+// Radix schedule for n = 2^a 3^b 5^c (prime-power radices up to 16, and 15, for FP32; up to 9
+// for FP64; odd ones first); false when n has another factor.
 bool fft_make_plan(int n, FftPlan1D& p, bool fp64);
 
 // Largest row length a single CTA can hold in shared memory for this element type.
