@@ -478,7 +478,8 @@ __device__ __forceinline__ cx_t<T> load_elem(int idx, int n, const cx_t<T>* __re
 // memory, 384 threads and two CTAs per SM where only two do (13824-point FP32 rows, 110 KB), so
 // that an SM holds 24 warps either way and one row's loads overlap the others' butterflies
 // (measured at N = 10^6: 13824-point rows 0.96 -> 0.83 ms per forward transform with 384 threads;
-// 6912- and 7680-point phases slower with 384 threads and two CTAs than with 256 and three).
+// the 6912-point rows of a smaller grid and the uniform-grid variant's 15360-point rows were slower
+// with 384 threads everywhere: 0.16 -> 0.19 and 1.25 -> 1.53 ms).
 template <int NT> struct FftCtas { static constexpr int value = NT == 384 ? 2 : 3; };
 constexpr size_t kFftSmemThird = 228u * 1024u / 3u - 1024u;   // bytes a CTA may take for three per SM
 template <typename T, int SIGN, int NT>
