@@ -450,9 +450,10 @@ int sbd_fft2(const void* in, void* out, int32_t n0, int32_t n1, int32_t sign, in
  * cells, every 64 x 64 tile of the frequency grid holding at most 4096 records) takes
  * the records bin by bin (8 x 8 stencil starts; four accumulators, one per bin colour,
  * so that no two warps write one cell and no atomics are needed); for it sched 0 runs
- * 512 threads per CTA, sched 1 1024.  acc 4 (where acc 3 applies) takes the same bins two at
- * a time per warp, one per half-warp, each half-warp carrying one record at a time with
- * bank-conflict-free accesses (sched as for acc 3).  Results agree to FP32 rounding.
+ * 512 threads per CTA, sched 1 1024, one persistent CTA per SM walking the plan's tiles
+ * with records.  acc 4 (where acc 3 applies) takes the same bins two at a time per warp,
+ * one per half-warp, each half-warp carrying one record at a time with bank-conflict-free
+ * accesses (sched as for acc 3).  Results agree to FP32 rounding.
  *   sbd_tune       times every applicable variant on the plan's own records (reps
  *                  launches each, after one warm-up, CUDA events on cuda_stream; the
  *                  frequency workspace is first filled with a constant non-zero value,
@@ -462,8 +463,8 @@ int sbd_fft2(const void* in, void* out, int32_t n0, int32_t n1, int32_t sign, in
  *                  acc * 2 + sched for acc <= 3 and 10 + sched for acc 4, -1 where not
  *                  applicable; ms[8], ms[9]: mean ms of
  *                  the forward 2-D transform with rows in one phase where they fit, and
- *                  with every row split into two half-length phases (two CTAs of 512
- *                  threads per SM instead of one of 1024); the faster is kept too.
+ *                  with every row split into two half-length phases (half the shared
+ *                  memory per CTA, so more CTAs per SM); the faster is kept too.
  *                  Blocks until done.
  *   sbd_set_tuning picks a variant by hand (fft_split 0 or 2).
  * SBD_EINVAL for a null plan, reps < 1, acc outside {0, .., 4}, sched outside {0, 1}
